@@ -1,0 +1,1139 @@
+/*
+ * oracle.c -- plain, slow, FP64 CPU reference of the SN-like DLR time step
+ * (Haut et al., Section 4, Algorithm 1) on a 2-D Cartesian mesh with a DG0
+ * (piecewise-constant, upwind "step") spatial discretisation.
+ *
+ * TEST INFRASTRUCTURE ONLY: used by the tests, the smoke check and the CPU
+ * baseline of the benchmark, never by the product library.  It shares no
+ * code with the CUDA path.  Every function cites the passage it follows.
+ * Readings of the paper used here (where it is silent or garbled):
+ *   R1  Newton-linearised coefficients derived from Eq. (T, backward Euler):
+ *       D = rho_cv + 4 pi dt sigma B'(T0),  T = T0 + dt sigma (phi - 4 pi B0)/D,
+ *       sigma_s = sigma (4 pi dt sigma B')/D,  q = sigma B0 rho_cv / D.
+ *       (The printed q and T-update carry an extra rho_cv T0 term that breaks
+ *       equilibrium; the derivation is redone from the backward-Euler form.)
+ *   R2  B(T) = a c T^4/(4 pi)  (gray Planck), so B' = a c T^3 / pi.
+ *   R4  isotropic inflow psi_edge on an edge for directions entering it.
+ *   R5  product quadrature: Gauss-Legendre in mu x equispaced azimuths.
+ *   R6  DG0 upwind cells: the lowest-order member of the paper's upwind DG.
+ *   R7  SI stops when max|phi_new - phi| <= tol * max|phi_new|.
+ *   R8  angle choice: column-pivoted Householder QR of W^T (default) or the
+ *       greedy DEIM of Section 4.2; ties go to the lowest index within a
+ *       relative 1e-12 of the maximum.
+ *   R10 What_ij = W_j(Om^(i)); Psi = What K; phi = beta^T What^{-1} Psi.
+ *   R11 initial factors: psi0(x, Om) = B(T0(x)), S0 = diag(s0, 0, ...).
+ *   R12 the temperature update uses phi of the final factors, X S beta.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_PI 3.14159265358979323846
+#define TIE_REL 1e-12
+
+/* ------------------------------------------------------------------ */
+/* Physics: Section 2.1 (Eq. TRT psi, TRT T) and Section 2.2.          */
+/* ------------------------------------------------------------------ */
+
+double oracle_planck(double a_rad, double c, double T) {
+  return a_rad * c * T * T * T * T / (4.0 * ORACLE_PI);
+}
+
+/* dB/dT of the gray Planck function (reading R2). */
+static double planck_deriv(double a_rad, double c, double T) {
+  return a_rad * c * T * T * T / ORACLE_PI;
+}
+
+/* Section 2.2: Newton linearisation of the backward-Euler temperature
+ * equation about T0 gives the pseudo-scattering sigma_s (Eq. effective
+ * scattering) and the source q (Eq. effective source; reading R1). */
+void oracle_coefficients(const oracle_problem *p, const double *T0,
+                         double *sigma_s, double *q, double *B0, double *D) {
+  int Nx = p->nx * p->ny;
+  for (int c = 0; c < Nx; c++) {
+    double sig = p->sigma[c];
+    double B = oracle_planck(p->a_rad, p->c, T0[c]);
+    double dB = planck_deriv(p->a_rad, p->c, T0[c]);
+    double Dc = p->rho_cv[c] + 4.0 * ORACLE_PI * p->dt * sig * dB;
+    sigma_s[c] = sig * (4.0 * ORACLE_PI * p->dt * sig * dB) / Dc;
+    q[c] = sig * B - sig * dB * (4.0 * ORACLE_PI * p->dt * sig * B) / Dc;
+    if (B0) B0[c] = B;
+    if (D) D[c] = Dc;
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* Quadrature (reading R5).                                            */
+/* ------------------------------------------------------------------ */
+
+/* Legendre P_n and its derivative at z by the three-term recurrence. */
+static void legendre(int n, double z, double *Pn, double *dPn) {
+  double p0 = 1.0, p1 = z;
+  if (n == 0) { *Pn = 1.0; *dPn = 0.0; return; }
+  for (int k = 2; k <= n; k++) {
+    double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+    p0 = p1;
+    p1 = p2;
+  }
+  *Pn = p1;
+  *dPn = n * (z * p1 - p0) / (z * z - 1.0);
+}
+
+/* Gauss-Legendre nodes (ascending) and weights on [-1, 1]: roots of P_n by
+ * Newton's method, weights 2 / ((1 - z^2) P_n'(z)^2). */
+static void gauss_legendre(int n, double *x, double *w) {
+  for (int i = 0; i < n; i++) {
+    double z = cos(ORACLE_PI * (i + 0.75) / (n + 0.5));
+    double Pn, dPn;
+    for (int it = 0; it < 200; it++) {
+      legendre(n, z, &Pn, &dPn);
+      double dz = Pn / dPn;
+      z -= dz;
+      if (fabs(dz) < 1e-15) {
+        legendre(n, z, &Pn, &dPn);
+        z -= Pn / dPn;
+        break;
+      }
+    }
+    legendre(n, z, &Pn, &dPn);
+    x[n - 1 - i] = z;
+    w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dPn * dPn);
+  }
+}
+
+void oracle_quadrature(int n_polar, int n_azim, double *ox, double *oy,
+                       double *oz, double *w) {
+  double *mu = (double *)malloc(sizeof(double) * n_polar);
+  double *wp = (double *)malloc(sizeof(double) * n_polar);
+  gauss_legendre(n_polar, mu, wp);
+  for (int p = 0; p < n_polar; p++) {
+    double s = sqrt(1.0 - mu[p] * mu[p]);
+    for (int a = 0; a < n_azim; a++) {
+      double phi = (a + 0.5) * 2.0 * ORACLE_PI / n_azim;
+      int k = p * n_azim + a;
+      ox[k] = s * cos(phi);
+      oy[k] = s * sin(phi);
+      oz[k] = mu[p];
+      w[k] = wp[p] * 2.0 * ORACLE_PI / n_azim;
+    }
+  }
+  free(mu);
+  free(wp);
+}
+
+/* ------------------------------------------------------------------ */
+/* DG0 upwind transport sweep (Section 4.4 discretisation, reading R6). */
+/* ------------------------------------------------------------------ */
+
+/* Inflow value entering through the x-face of the first cell of a row for
+ * direction sign ox, and through the y-face for oy (reading R4). */
+static double inflow_x(const oracle_problem *p, double ox) {
+  return ox > 0 ? p->psi_edge[0] : (ox < 0 ? p->psi_edge[1] : 0.0);
+}
+static double inflow_y(const oracle_problem *p, double oy) {
+  return oy > 0 ? p->psi_edge[2] : (oy < 0 ? p->psi_edge[3] : 0.0);
+}
+
+/* Cell balance of the upwind scheme: integrating Om.grad psi over cell c and
+ * taking the upwind face values gives
+ *   |ox|/hx (psi_c - psi_west) + |oy|/hy (psi_c - psi_south)
+ *       + sigma_t,c psi_c = src_c,
+ * where west/south are the upwind neighbours (or the edge inflow).  The
+ * sweep solves this lower-triangular system cell by cell in upwind order. */
+void oracle_sweep(const oracle_problem *p, double ox, double oy,
+                  const double *sigma_t, const double *src, double *psi) {
+  int nx = p->nx, ny = p->ny;
+  double hx = p->lx / nx, hy = p->ly / ny;
+  double ax = fabs(ox) / hx, ay = fabs(oy) / hy;
+  int sx = ox >= 0 ? 1 : -1, sy = oy >= 0 ? 1 : -1;
+  double in_x = inflow_x(p, ox), in_y = inflow_y(p, oy);
+  for (int jj = 0; jj < ny; jj++) {
+    int iy = sy > 0 ? jj : ny - 1 - jj;
+    for (int ii = 0; ii < nx; ii++) {
+      int ix = sx > 0 ? ii : nx - 1 - ii;
+      int c = iy * nx + ix;
+      double up_x = ii == 0 ? in_x : psi[iy * nx + (ix - sx)];
+      double up_y = jj == 0 ? in_y : psi[(iy - sy) * nx + ix];
+      psi[c] = (src[c] + ax * up_x + ay * up_y) / (sigma_t[c] + ax + ay);
+    }
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* Dense linear algebra.                                               */
+/* ------------------------------------------------------------------ */
+
+/* LU with partial pivoting of the n x n column-major A, in place; piv[i] is
+ * the row swapped into position i.  Returns -1 if a pivot is exactly 0. */
+static int lu_factor(int n, double *A, int *piv) {
+  for (int j = 0; j < n; j++) {
+    int pr = j;
+    double best = fabs(A[j + n * j]);
+    for (int i = j + 1; i < n; i++)
+      if (fabs(A[i + n * j]) > best) { best = fabs(A[i + n * j]); pr = i; }
+    piv[j] = pr;
+    if (best == 0.0) return -1;
+    if (pr != j)
+      for (int k = 0; k < n; k++) {
+        double t = A[j + n * k]; A[j + n * k] = A[pr + n * k]; A[pr + n * k] = t;
+      }
+    for (int i = j + 1; i < n; i++) {
+      double l = A[i + n * j] / A[j + n * j];
+      A[i + n * j] = l;
+      for (int k = j + 1; k < n; k++) A[i + n * k] -= l * A[j + n * k];
+    }
+  }
+  return 0;
+}
+
+static void lu_solve_inplace(int n, const double *LU, const int *piv,
+                             double *b) {
+  for (int i = 0; i < n; i++) {
+    double t = b[i]; b[i] = b[piv[i]]; b[piv[i]] = t;
+  }
+  for (int i = 0; i < n; i++)
+    for (int k = 0; k < i; k++) b[i] -= LU[i + n * k] * b[k];
+  for (int i = n - 1; i >= 0; i--) {
+    for (int k = i + 1; k < n; k++) b[i] -= LU[i + n * k] * b[k];
+    b[i] /= LU[i + n * i];
+  }
+}
+
+/* Solves A Xout = B for nrhs right-hand sides (column-major). */
+int oracle_lu_solve(int n, const double *A, int nrhs, const double *B,
+                    double *Xout) {
+  double *LU = (double *)malloc(sizeof(double) * n * n);
+  int *piv = (int *)malloc(sizeof(int) * n);
+  memcpy(LU, A, sizeof(double) * n * n);
+  int rc = lu_factor(n, LU, piv);
+  if (rc == 0) {
+    memcpy(Xout, B, sizeof(double) * n * nrhs);
+    for (int j = 0; j < nrhs; j++) lu_solve_inplace(n, LU, piv, Xout + n * j);
+  }
+  free(LU);
+  free(piv);
+  return rc;
+}
+
+/* Thin Householder QR, A (m x n, m >= n) = Q (m x n) R (n x n), R with a
+ * non-negative diagonal.  A zero column leaves its reflector the identity,
+ * so Q stays orthonormal when A is rank deficient. */
+void oracle_householder_qr(int m, int n, const double *A, double *Q,
+                           double *R) {
+  double *V = (double *)malloc(sizeof(double) * m * n); /* reduced A */
+  double *H = (double *)calloc((size_t)m * n, sizeof(double)); /* reflectors */
+  double *hn = (double *)calloc(n, sizeof(double)); /* |v|^2 */
+  memcpy(V, A, sizeof(double) * m * n);
+  for (int j = 0; j < n; j++) {
+    double nrm = 0;
+    for (int i = j; i < m; i++) nrm += V[i + m * j] * V[i + m * j];
+    nrm = sqrt(nrm);
+    double alpha = V[j + m * j] >= 0 ? -nrm : nrm;
+    for (int i = j; i < m; i++) H[i + m * j] = V[i + m * j];
+    H[j + m * j] -= alpha;
+    double vv = 0;
+    for (int i = j; i < m; i++) vv += H[i + m * j] * H[i + m * j];
+    hn[j] = vv;
+    if (vv > 0) {
+      for (int k = j; k < n; k++) {
+        double d = 0;
+        for (int i = j; i < m; i++) d += H[i + m * j] * V[i + m * k];
+        double f = 2.0 * d / vv;
+        for (int i = j; i < m; i++) V[i + m * k] -= f * H[i + m * j];
+      }
+    }
+  }
+  for (int j = 0; j < n; j++)
+    for (int i = 0; i < n; i++) R[i + n * j] = i <= j ? V[i + m * j] : 0.0;
+  /* Q = H_0 H_1 ... H_{n-1} [I; 0] */
+  for (int j = 0; j < n; j++)
+    for (int i = 0; i < m; i++) Q[i + m * j] = i == j ? 1.0 : 0.0;
+  for (int j = n - 1; j >= 0; j--) {
+    if (hn[j] == 0) continue;
+    for (int k = 0; k < n; k++) {
+      double d = 0;
+      for (int i = j; i < m; i++) d += H[i + m * j] * Q[i + m * k];
+      double f = 2.0 * d / hn[j];
+      for (int i = j; i < m; i++) Q[i + m * k] -= f * H[i + m * j];
+    }
+  }
+  for (int j = 0; j < n; j++)
+    if (R[j + n * j] < 0) {
+      for (int k = 0; k < n; k++) R[j + n * k] = -R[j + n * k];
+      for (int i = 0; i < m; i++) Q[i + m * j] = -Q[i + m * j];
+    }
+  free(V);
+  free(H);
+  free(hn);
+}
+
+/* One-sided (Hestenes) Jacobi SVD of the square A = U diag(s) V^T,
+ * singular values descending; columns for zero singular values are
+ * completed to an orthonormal basis. */
+int oracle_jacobi_svd(int n, const double *A, double *U, double *s,
+                      double *V) {
+  double *Uw = (double *)malloc(sizeof(double) * n * n);
+  double *Vw = (double *)malloc(sizeof(double) * n * n);
+  memcpy(Uw, A, sizeof(double) * n * n);
+  for (int j = 0; j < n; j++)
+    for (int i = 0; i < n; i++) Vw[i + n * j] = i == j ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 100; sweep++) {
+    int rotated = 0;
+    for (int i = 0; i < n - 1; i++)
+      for (int j = i + 1; j < n; j++) {
+        double al = 0, be = 0, ga = 0;
+        for (int k = 0; k < n; k++) {
+          al += Uw[k + n * i] * Uw[k + n * i];
+          be += Uw[k + n * j] * Uw[k + n * j];
+          ga += Uw[k + n * i] * Uw[k + n * j];
+        }
+        if (ga == 0.0 || fabs(ga) <= 1e-15 * sqrt(al * be)) continue;
+        rotated = 1;
+        double zeta = (be - al) / (2.0 * ga);
+        double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+        for (int k = 0; k < n; k++) {
+          double ui = Uw[k + n * i], uj = Uw[k + n * j];
+          Uw[k + n * i] = cs * ui - sn * uj;
+          Uw[k + n * j] = sn * ui + cs * uj;
+          double vi = Vw[k + n * i], vj = Vw[k + n * j];
+          Vw[k + n * i] = cs * vi - sn * vj;
+          Vw[k + n * j] = sn * vi + cs * vj;
+        }
+      }
+    if (!rotated) break;
+  }
+  /* singular values and descending order (stable in the column index) */
+  double *sv = (double *)malloc(sizeof(double) * n);
+  int *ord = (int *)malloc(sizeof(int) * n);
+  for (int j = 0; j < n; j++) {
+    double t = 0;
+    for (int k = 0; k < n; k++) t += Uw[k + n * j] * Uw[k + n * j];
+    sv[j] = sqrt(t);
+    ord[j] = j;
+  }
+  for (int a = 1; a < n; a++) {
+    int key = ord[a], b = a - 1;
+    while (b >= 0 && sv[ord[b]] < sv[key]) { ord[b + 1] = ord[b]; b--; }
+    ord[b + 1] = key;
+  }
+  double smax = n > 0 ? sv[ord[0]] : 0.0;
+  for (int j = 0; j < n; j++) {
+    int o = ord[j];
+    s[j] = sv[o];
+    for (int k = 0; k < n; k++) V[k + n * j] = Vw[k + n * o];
+    if (sv[o] > 1e-300 && sv[o] > 1e-15 * smax) {
+      for (int k = 0; k < n; k++) U[k + n * j] = Uw[k + n * o] / sv[o];
+    } else {
+      for (int k = 0; k < n; k++) U[k + n * j] = 0.0;
+      s[j] = sv[o];
+    }
+  }
+  /* complete U columns of (numerically) zero singular values */
+  for (int j = 0; j < n; j++) {
+    double t = 0;
+    for (int k = 0; k < n; k++) t += U[k + n * j] * U[k + n * j];
+    if (t > 0.5) continue;
+    for (int e = 0; e < n; e++) {
+      double *u = U + n * j;
+      for (int k = 0; k < n; k++) u[k] = k == e ? 1.0 : 0.0;
+      for (int pass = 0; pass < 2; pass++)
+        for (int l = 0; l < n; l++) {
+          if (l == j) continue;
+          double d = 0, ll = 0;
+          for (int k = 0; k < n; k++) { d += U[k + n * l] * u[k]; ll += U[k + n * l] * U[k + n * l]; }
+          if (ll < 0.5) continue;
+          for (int k = 0; k < n; k++) u[k] -= d * U[k + n * l];
+        }
+      double nn = 0;
+      for (int k = 0; k < n; k++) nn += u[k] * u[k];
+      if (nn > 1e-2) {
+        nn = sqrt(nn);
+        for (int k = 0; k < n; k++) u[k] /= nn;
+        break;
+      }
+    }
+  }
+  free(Uw);
+  free(Vw);
+  free(sv);
+  free(ord);
+  return 0;
+}
+
+/* Argmax with the tie rule of reading R8: the lowest index whose value is
+ * within a relative TIE_REL of the maximum; entries with skip[k] != 0 are
+ * excluded. */
+static int argmax_tie(int n, const double *v, const int *skip) {
+  double m = -1.0;
+  for (int k = 0; k < n; k++)
+    if (!(skip && skip[k]) && v[k] > m) m = v[k];
+  for (int k = 0; k < n; k++)
+    if (!(skip && skip[k]) && v[k] >= m * (1.0 - TIE_REL)) return k;
+  return -1;
+}
+
+/* Angle selection by column-pivoted Householder QR (Businger-Golub) of the
+ * r x n matrix W^T: the pivot at step s is the column of largest remaining
+ * norm below row s; idx = the first r pivots. */
+int oracle_qdeim(int n, int r, const double *W, int *idx) {
+  double *A = (double *)malloc(sizeof(double) * r * n); /* A = W^T, r x n */
+  double *nrm = (double *)malloc(sizeof(double) * n);
+  int *used = (int *)calloc(n, sizeof(int));
+  double *v = (double *)malloc(sizeof(double) * r);
+  for (int k = 0; k < n; k++)
+    for (int j = 0; j < r; j++) A[j + r * k] = W[k + n * j];
+  for (int s = 0; s < r; s++) {
+    for (int k = 0; k < n; k++) {
+      double t = 0;
+      for (int i = s; i < r; i++) t += A[i + r * k] * A[i + r * k];
+      nrm[k] = sqrt(t);
+    }
+    int piv = argmax_tie(n, nrm, used);
+    idx[s] = piv;
+    used[piv] = 1;
+    /* Householder reflector zeroing A[s+1:, piv]; applied to every column */
+    double alpha = A[s + r * piv] >= 0 ? -nrm[piv] : nrm[piv];
+    for (int i = s; i < r; i++) v[i] = A[i + r * piv];
+    v[s] -= alpha;
+    double vv = 0;
+    for (int i = s; i < r; i++) vv += v[i] * v[i];
+    if (vv > 0)
+      for (int k = 0; k < n; k++) {
+        double d = 0;
+        for (int i = s; i < r; i++) d += v[i] * A[i + r * k];
+        double f = 2.0 * d / vv;
+        for (int i = s; i < r; i++) A[i + r * k] -= f * v[i];
+      }
+  }
+  free(A);
+  free(nrm);
+  free(used);
+  free(v);
+  return 0;
+}
+
+/* Greedy DEIM of Section 4.2: Om_1 = argmax |W_1|; then the next point
+ * maximises the residual of W_j after interpolation on the points so far. */
+int oracle_deim(int n, int r, const double *W, int *idx) {
+  double *res = (double *)malloc(sizeof(double) * n);
+  double *M = (double *)malloc(sizeof(double) * r * r);
+  double *rhs = (double *)malloc(sizeof(double) * r);
+  double *cf = (double *)malloc(sizeof(double) * r);
+  int *used = (int *)calloc(n, sizeof(int));
+  int rc = 0;
+  for (int j = 0; j < r; j++) {
+    for (int k = 0; k < n; k++) res[k] = W[k + n * j];
+    if (j > 0) {
+      /* interpolation coefficients: sum_l c_l W_l(Om_i) = W_j(Om_i) */
+      for (int i = 0; i < j; i++) {
+        rhs[i] = W[idx[i] + n * j];
+        for (int l = 0; l < j; l++) M[i + j * l] = W[idx[i] + n * l];
+      }
+      if (oracle_lu_solve(j, M, 1, rhs, cf) != 0) { rc = -1; break; }
+      for (int k = 0; k < n; k++)
+        for (int l = 0; l < j; l++) res[k] -= cf[l] * W[k + n * l];
+    }
+    for (int k = 0; k < n; k++) res[k] = fabs(res[k]);
+    idx[j] = argmax_tie(n, res, used);
+    used[idx[j]] = 1;
+  }
+  free(res);
+  free(M);
+  free(rhs);
+  free(cf);
+  free(used);
+  return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Initial factors (reading R11).                                      */
+/* ------------------------------------------------------------------ */
+
+/* Appends candidate vector v (length m) to the orthonormal set Q (m x *cnt)
+ * under the weighted inner product sum_i wt_i a_i b_i by two passes of
+ * modified Gram-Schmidt; skipped if less than 1e-8 of it survives. */
+static void gs_append(int m, const double *wt, double *Q, int *cnt,
+                      const double *v) {
+  double *u = (double *)malloc(sizeof(double) * m);
+  memcpy(u, v, sizeof(double) * m);
+  double n0 = 0;
+  for (int i = 0; i < m; i++) n0 += wt[i] * u[i] * u[i];
+  n0 = sqrt(n0);
+  if (n0 == 0) { free(u); return; }
+  for (int pass = 0; pass < 2; pass++)
+    for (int l = 0; l < *cnt; l++) {
+      double d = 0;
+      for (int i = 0; i < m; i++) d += wt[i] * Q[i + m * l] * u[i];
+      for (int i = 0; i < m; i++) u[i] -= d * Q[i + m * l];
+    }
+  double n1 = 0;
+  for (int i = 0; i < m; i++) n1 += wt[i] * u[i] * u[i];
+  n1 = sqrt(n1);
+  if (n1 > 1e-8 * n0) {
+    for (int i = 0; i < m; i++) Q[i + m * (*cnt)] = u[i] / n1;
+    (*cnt)++;
+  }
+  free(u);
+}
+
+/* X0: f = B(T0) first, then cos(pi k x^)cos(pi l y^) modes in (k+l, k)
+ * order; W0: monomials Om_x^a Om_y^b by degree (a descending), then the
+ * same times Om_z; S0 = diag(|f| sqrt(4 pi), 0, ...), so X0 S0 W0^T = f. */
+int oracle_initial_factors(const oracle_problem *p, const double *T0, int r,
+                           double *X0, double *S0, double *W0) {
+  int nx = p->nx, ny = p->ny, Nx = nx * ny, NOm = p->n_polar * p->n_azim;
+  double hx = p->lx / nx, hy = p->ly / ny, h2 = hx * hy;
+  if (r < 1 || r > Nx || r > NOm) return -1;
+  double *wt = (double *)malloc(sizeof(double) * Nx);
+  double *v = (double *)malloc(sizeof(double) * (Nx > NOm ? Nx : NOm));
+  double *Q = (double *)malloc(sizeof(double) * Nx * r);
+  for (int c = 0; c < Nx; c++) wt[c] = h2;
+  int cnt = 0;
+  double fn = 0;
+  for (int c = 0; c < Nx; c++) {
+    v[c] = oracle_planck(p->a_rad, p->c, T0[c]);
+    fn += h2 * v[c] * v[c];
+  }
+  fn = sqrt(fn);
+  gs_append(Nx, wt, Q, &cnt, v);
+  for (int d = 0; d <= nx + ny - 2 && cnt < r; d++)
+    for (int k = 0; k <= d && cnt < r; k++) {
+      int l = d - k;
+      if (k >= nx || l >= ny) continue;
+      for (int iy = 0; iy < ny; iy++)
+        for (int ix = 0; ix < nx; ix++)
+          v[iy * nx + ix] = cos(ORACLE_PI * k * (ix + 0.5) / nx) *
+                            cos(ORACLE_PI * l * (iy + 0.5) / ny);
+      gs_append(Nx, wt, Q, &cnt, v);
+    }
+  if (cnt < r) { free(wt); free(v); free(Q); return -1; }
+  memcpy(X0, Q, sizeof(double) * Nx * r);
+  free(Q);
+
+  double *ox = (double *)malloc(sizeof(double) * NOm);
+  double *oy = (double *)malloc(sizeof(double) * NOm);
+  double *oz = (double *)malloc(sizeof(double) * NOm);
+  double *w = (double *)malloc(sizeof(double) * NOm);
+  double *QW = (double *)malloc(sizeof(double) * NOm * r);
+  oracle_quadrature(p->n_polar, p->n_azim, ox, oy, oz, w);
+  cnt = 0;
+  for (int e = 0; e <= 1 && cnt < r; e++)
+    for (int d = 0; d <= 12 && cnt < r; d++)
+      for (int a = d; a >= 0 && cnt < r; a--) {
+        int b = d - a;
+        for (int k = 0; k < NOm; k++)
+          v[k] = pow(ox[k], a) * pow(oy[k], b) * (e ? oz[k] : 1.0);
+        gs_append(NOm, w, QW, &cnt, v);
+      }
+  int rc = cnt < r ? -1 : 0;
+  if (rc == 0) memcpy(W0, QW, sizeof(double) * NOm * r);
+  for (int i = 0; i < r * r; i++) S0[i] = 0.0;
+  S0[0] = fn * sqrt(4.0 * ORACLE_PI);
+  free(ox); free(oy); free(oz); free(w); free(QW); free(wt); free(v);
+  return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* L-step (Algorithm 1 step 7; Eq. L step; solution by the C-bar device */
+/* of Section 3.3).                                                    */
+/* ------------------------------------------------------------------ */
+
+/* Upwind difference D^{+-} of the DG0 scheme with zero inflow (the inflow
+ * value is moved to the right-hand side): dir = +1 uses the west/south
+ * neighbour, -1 the east/north one.  axis 0 = x, 1 = y. */
+static void upwind_diff(const oracle_problem *p, int axis, int dir,
+                        const double *u, double *out) {
+  int nx = p->nx, ny = p->ny;
+  double h = axis == 0 ? p->lx / nx : p->ly / ny;
+  for (int iy = 0; iy < ny; iy++)
+    for (int ix = 0; ix < nx; ix++) {
+      int jx = axis == 0 ? ix - dir : ix, jy = axis == 1 ? iy - dir : iy;
+      double up = (jx >= 0 && jx < nx && jy >= 0 && jy < ny) ? u[jy * nx + jx] : 0.0;
+      out[iy * nx + ix] = (u[iy * nx + ix] - up) / h;
+    }
+}
+
+int oracle_lstep(const oracle_problem *p, int r, const double *X,
+                 const double *sigma_t, const double *sigma_s,
+                 const double *q, const double *Lt0, double *L) {
+  int nx = p->nx, ny = p->ny, Nx = nx * ny, NOm = p->n_polar * p->n_azim;
+  double hx = p->lx / nx, hy = p->ly / ny, h2 = hx * hy;
+  double *ox = (double *)malloc(sizeof(double) * NOm);
+  double *oy = (double *)malloc(sizeof(double) * NOm);
+  double *oz = (double *)malloc(sizeof(double) * NOm);
+  double *w = (double *)malloc(sizeof(double) * NOm);
+  oracle_quadrature(p->n_polar, p->n_azim, ox, oy, oz, w);
+
+  /* Galerkin operators <D X_j, X_i>, M_t, M_s, <q, X_i>, edge sums */
+  double *Ax[2], *Ay[2]; /* [0] = '+' (west/south upwind), [1] = '-' */
+  for (int s = 0; s < 2; s++) {
+    Ax[s] = (double *)calloc(r * r, sizeof(double));
+    Ay[s] = (double *)calloc(r * r, sizeof(double));
+  }
+  double *Mt = (double *)calloc(r * r, sizeof(double));
+  double *Ms = (double *)calloc(r * r, sizeof(double));
+  double *qh = (double *)calloc(r, sizeof(double));
+  double *bE[4];
+  for (int e = 0; e < 4; e++) bE[e] = (double *)calloc(r, sizeof(double));
+  double *Du = (double *)malloc(sizeof(double) * Nx);
+  for (int j = 0; j < r; j++) {
+    const double *Xj = X + (size_t)Nx * j;
+    for (int s = 0; s < 2; s++) {
+      upwind_diff(p, 0, s == 0 ? 1 : -1, Xj, Du);
+      for (int i = 0; i < r; i++) {
+        double t = 0;
+        for (int c = 0; c < Nx; c++) t += X[c + (size_t)Nx * i] * Du[c];
+        Ax[s][i + r * j] = h2 * t;
+      }
+      upwind_diff(p, 1, s == 0 ? 1 : -1, Xj, Du);
+      for (int i = 0; i < r; i++) {
+        double t = 0;
+        for (int c = 0; c < Nx; c++) t += X[c + (size_t)Nx * i] * Du[c];
+        Ay[s][i + r * j] = h2 * t;
+      }
+    }
+    for (int i = 0; i < r; i++) {
+      double tt = 0, ts = 0;
+      for (int c = 0; c < Nx; c++) {
+        double xx = X[c + (size_t)Nx * i] * Xj[c];
+        tt += sigma_t[c] * xx;
+        ts += sigma_s[c] * xx;
+      }
+      Mt[i + r * j] = h2 * tt;
+      Ms[i + r * j] = h2 * ts;
+    }
+    double tq = 0;
+    for (int c = 0; c < Nx; c++) tq += q[c] * Xj[c];
+    qh[j] = h2 * tq;
+    for (int iy = 0; iy < ny; iy++) {
+      bE[0][j] += hy * Xj[iy * nx + 0];
+      bE[1][j] += hy * Xj[iy * nx + nx - 1];
+    }
+    for (int ix = 0; ix < nx; ix++) {
+      bE[2][j] += hx * Xj[ix];
+      bE[3][j] += hx * Xj[(ny - 1) * nx + ix];
+    }
+  }
+
+  /* per angle: B_k = |ox| Ax^s + |oy| Ay^s + M_t, Q_k = q^ + Lt0_k/(c dt)
+   * + inflow terms; Cbar = sum w B^-1, zeta = sum w B^-1 Q */
+  double inv_cdt = 1.0 / (p->c * p->dt);
+  double *Bk = (double *)malloc(sizeof(double) * r * r * NOm);
+  double *Qk = (double *)malloc(sizeof(double) * r * NOm);
+  double *Cbar = (double *)calloc(r * r, sizeof(double));
+  double *zeta = (double *)calloc(r, sizeof(double));
+  double *I_r = (double *)calloc(r * r, sizeof(double));
+  double *Binv = (double *)malloc(sizeof(double) * r * r);
+  double *BQ = (double *)malloc(sizeof(double) * r);
+  for (int i = 0; i < r; i++) I_r[i + r * i] = 1.0;
+  int rc = 0;
+  for (int k = 0; k < NOm && rc == 0; k++) {
+    int sx = ox[k] > 0 ? 0 : 1, sy = oy[k] > 0 ? 0 : 1;
+    double *B = Bk + (size_t)r * r * k;
+    for (int e = 0; e < r * r; e++)
+      B[e] = fabs(ox[k]) * Ax[sx][e] + fabs(oy[k]) * Ay[sy][e] + Mt[e];
+    double *Q = Qk + (size_t)r * k;
+    double psx = ox[k] > 0 ? p->psi_edge[0] : p->psi_edge[1];
+    double psy = oy[k] > 0 ? p->psi_edge[2] : p->psi_edge[3];
+    const double *bx = ox[k] > 0 ? bE[0] : bE[1];
+    const double *by = oy[k] > 0 ? bE[2] : bE[3];
+    for (int i = 0; i < r; i++)
+      Q[i] = qh[i] + inv_cdt * Lt0[i + r * k] + fabs(ox[k]) * psx * bx[i] +
+             fabs(oy[k]) * psy * by[i];
+    rc = oracle_lu_solve(r, B, r, I_r, Binv);
+    if (rc) break;
+    rc = oracle_lu_solve(r, B, 1, Q, BQ);
+    for (int e = 0; e < r * r; e++) Cbar[e] += w[k] * Binv[e];
+    for (int i = 0; i < r; i++) zeta[i] += w[k] * BQ[i];
+  }
+  /* (I - Cbar Ms / 4pi) Lbar = zeta;  L_k = B_k^{-1} (Q_k + Ms Lbar / 4pi) */
+  double *Msys = (double *)malloc(sizeof(double) * r * r);
+  double *Lbar = (double *)malloc(sizeof(double) * r);
+  double *rhs = (double *)malloc(sizeof(double) * r);
+  if (rc == 0) {
+    for (int i = 0; i < r; i++)
+      for (int j = 0; j < r; j++) {
+        double t = 0;
+        for (int l = 0; l < r; l++) t += Cbar[i + r * l] * Ms[l + r * j];
+        Msys[i + r * j] = (i == j ? 1.0 : 0.0) - t / (4.0 * ORACLE_PI);
+      }
+    rc = oracle_lu_solve(r, Msys, 1, zeta, Lbar);
+  }
+  for (int k = 0; k < NOm && rc == 0; k++) {
+    for (int i = 0; i < r; i++) {
+      double t = 0;
+      for (int l = 0; l < r; l++) t += Ms[i + r * l] * Lbar[l];
+      rhs[i] = Qk[i + (size_t)r * k] + t / (4.0 * ORACLE_PI);
+    }
+    rc = oracle_lu_solve(r, Bk + (size_t)r * r * k, 1, rhs, L + (size_t)r * k);
+  }
+  for (int s = 0; s < 2; s++) { free(Ax[s]); free(Ay[s]); }
+  for (int e = 0; e < 4; e++) free(bE[e]);
+  free(Mt); free(Ms); free(qh); free(Du); free(Bk); free(Qk); free(Cbar);
+  free(zeta); free(I_r); free(Binv); free(BQ); free(Msys); free(Lbar);
+  free(rhs); free(ox); free(oy); free(oz); free(w);
+  return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Energy bookkeeping (Section 2.1: d/dt[rho_cv T + phi/c] + div F = 0). */
+/* ------------------------------------------------------------------ */
+
+static double energy(const oracle_problem *p, const double *T,
+                     const double *phi) {
+  int Nx = p->nx * p->ny;
+  double h2 = (p->lx / p->nx) * (p->ly / p->ny), E = 0;
+  for (int c = 0; c < Nx; c++) E += h2 * (p->rho_cv[c] * T[c] + phi[c] / p->c);
+  return E;
+}
+
+/* Boundary energy rates for angular values psi(c, k) = get(c, k): outflow
+ * uses the upwind (cell) value, inflow the prescribed edge value. */
+typedef double (*psi_getter)(const void *ctx, int c, int k);
+static void boundary_rates(const oracle_problem *p, const double *ox,
+                           const double *oy, const double *w, psi_getter get,
+                           const void *ctx, double *out, double *in) {
+  int nx = p->nx, ny = p->ny, NOm = p->n_polar * p->n_azim;
+  double hx = p->lx / nx, hy = p->ly / ny;
+  double o = 0, i_ = 0;
+  for (int k = 0; k < NOm; k++) {
+    for (int iy = 0; iy < ny; iy++) { /* left (n = -x) and right (n = +x) */
+      if (ox[k] < 0) o += w[k] * (-ox[k]) * hy * get(ctx, iy * nx, k);
+      else i_ += w[k] * ox[k] * hy * p->psi_edge[0];
+      if (ox[k] > 0) o += w[k] * ox[k] * hy * get(ctx, iy * nx + nx - 1, k);
+      else i_ += w[k] * (-ox[k]) * hy * p->psi_edge[1];
+    }
+    for (int ix = 0; ix < nx; ix++) { /* bottom (n = -y) and top (n = +y) */
+      if (oy[k] < 0) o += w[k] * (-oy[k]) * hx * get(ctx, ix, k);
+      else i_ += w[k] * oy[k] * hx * p->psi_edge[2];
+      if (oy[k] > 0) o += w[k] * oy[k] * hx * get(ctx, (ny - 1) * nx + ix, k);
+      else i_ += w[k] * (-oy[k]) * hx * p->psi_edge[3];
+    }
+  }
+  *out = o;
+  *in = i_;
+}
+
+typedef struct { const double *X, *L; int Nx, r; } xl_ctx;
+static double get_xl(const void *ctx, int c, int k) {
+  const xl_ctx *g = (const xl_ctx *)ctx;
+  double t = 0;
+  for (int i = 0; i < g->r; i++) t += g->X[c + (size_t)g->Nx * i] * g->L[i + g->r * k];
+  return t;
+}
+typedef struct { const double *psi; int Nx; } full_ctx;
+static double get_full(const void *ctx, int c, int k) {
+  const full_ctx *g = (const full_ctx *)ctx;
+  return g->psi[c + (size_t)g->Nx * k];
+}
+
+/* phi_c = sum_k w_k psi(c, Om_k) = sum_ij X_ci S_ij beta_j, beta_j = sum_k w_k W_kj */
+static void phi_from_factors(int Nx, int NOm, int r, const double *X,
+                             const double *S, const double *W,
+                             const double *w, double *phi) {
+  double *beta = (double *)calloc(r, sizeof(double));
+  double *Sb = (double *)calloc(r, sizeof(double));
+  for (int j = 0; j < r; j++)
+    for (int k = 0; k < NOm; k++) beta[j] += w[k] * W[k + (size_t)NOm * j];
+  for (int i = 0; i < r; i++)
+    for (int j = 0; j < r; j++) Sb[i] += S[i + r * j] * beta[j];
+  for (int c = 0; c < Nx; c++) {
+    double t = 0;
+    for (int i = 0; i < r; i++) t += X[c + (size_t)Nx * i] * Sb[i];
+    phi[c] = t;
+  }
+  free(beta);
+  free(Sb);
+}
+
+/* ------------------------------------------------------------------ */
+/* Algorithm 1 steps 3-4: collocation sweeps with source iteration.    */
+/* ------------------------------------------------------------------ */
+
+/* psi0_j(x) = sum_k L0_k(Om^(j)) X0_k(x) (step 3); then the fixed-point
+ * iteration of Eq. (steady state collocation): with phi = beta^T What^{-1}
+ * Psi, sweep every chosen angle against
+ *   src_j = sigma_s phi / (4 pi) + q + psi0_j / (c dt)
+ * and repeat until max|phi_new - phi| <= tol max|phi_new| (reading R7);
+ * phi starts from the old state at the chosen angles.  With fixed > 0,
+ * exactly `fixed` iterations.  Psi is the last sweep's output. */
+static int collocation_si(const oracle_problem *p, int r, const double *X0,
+                          const double *L0, const int *idx, const double *WLU,
+                          const int *wpiv, const double *beta, const double *ox,
+                          const double *oy, const double *sig_t,
+                          const double *sig_s, const double *q, double tol,
+                          int max_iter, int fixed, double *Psi, int *iters_out) {
+  int Nx = p->nx * p->ny;
+  double inv_cdt = 1.0 / (p->c * p->dt);
+  double *Psi0 = (double *)malloc(sizeof(double) * Nx * r);
+  double *phi = (double *)malloc(sizeof(double) * Nx);
+  double *phin = (double *)malloc(sizeof(double) * Nx);
+  double *src = (double *)malloc(sizeof(double) * Nx);
+  double *Kc = (double *)malloc(sizeof(double) * r);
+  for (int j = 0; j < r; j++)
+    for (int c = 0; c < Nx; c++) {
+      double t = 0;
+      for (int k = 0; k < r; k++) t += L0[k + r * idx[j]] * X0[c + (size_t)Nx * k];
+      Psi0[c + (size_t)Nx * j] = t;
+    }
+  for (int c = 0; c < Nx; c++) {
+    for (int j = 0; j < r; j++) Kc[j] = Psi0[c + (size_t)Nx * j];
+    lu_solve_inplace(r, WLU, wpiv, Kc);
+    double t = 0;
+    for (int j = 0; j < r; j++) t += beta[j] * Kc[j];
+    phi[c] = t;
+  }
+  int cap = fixed > 0 ? fixed : max_iter;
+  int iters = 0, converged = 0;
+  while (iters < cap) {
+    for (int j = 0; j < r; j++) {
+      for (int c = 0; c < Nx; c++)
+        src[c] = sig_s[c] * phi[c] / (4.0 * ORACLE_PI) + q[c] +
+                 inv_cdt * Psi0[c + (size_t)Nx * j];
+      oracle_sweep(p, ox[idx[j]], oy[idx[j]], sig_t, src, Psi + (size_t)Nx * j);
+    }
+    iters++;
+    double dmax = 0, pmax = 0;
+    for (int c = 0; c < Nx; c++) {
+      for (int j = 0; j < r; j++) Kc[j] = Psi[c + (size_t)Nx * j];
+      lu_solve_inplace(r, WLU, wpiv, Kc);
+      double t = 0;
+      for (int j = 0; j < r; j++) t += beta[j] * Kc[j];
+      phin[c] = t;
+      if (fabs(t - phi[c]) > dmax) dmax = fabs(t - phi[c]);
+      if (fabs(t) > pmax) pmax = fabs(t);
+    }
+    memcpy(phi, phin, sizeof(double) * Nx);
+    if (fixed <= 0 && dmax <= tol * pmax) { converged = 1; break; }
+  }
+  *iters_out = iters;
+  free(Psi0); free(phi); free(phin); free(src); free(Kc);
+  return (fixed <= 0 && !converged) ? -2 : 0;
+}
+
+int oracle_collocation(const oracle_problem *p, int r, const double *X0,
+                       const double *S0, const double *W0, const double *T0,
+                       const int *idx, double tol, int max_iter, int fixed,
+                       double *Psi, int *iters) {
+  int Nx = p->nx * p->ny, NOm = p->n_polar * p->n_azim;
+  double *ox = (double *)malloc(sizeof(double) * NOm);
+  double *oy = (double *)malloc(sizeof(double) * NOm);
+  double *oz = (double *)malloc(sizeof(double) * NOm);
+  double *w = (double *)malloc(sizeof(double) * NOm);
+  double *sig_s = (double *)malloc(sizeof(double) * Nx);
+  double *q = (double *)malloc(sizeof(double) * Nx);
+  double *sig_t = (double *)malloc(sizeof(double) * Nx);
+  double *WLU = (double *)malloc(sizeof(double) * r * r);
+  int *wpiv = (int *)malloc(sizeof(int) * r);
+  double *beta = (double *)calloc(r, sizeof(double));
+  double *L0 = (double *)malloc(sizeof(double) * r * NOm);
+  oracle_quadrature(p->n_polar, p->n_azim, ox, oy, oz, w);
+  oracle_coefficients(p, T0, sig_s, q, NULL, NULL);
+  for (int c = 0; c < Nx; c++) sig_t[c] = p->sigma[c] + 1.0 / (p->c * p->dt);
+  for (int i = 0; i < r; i++)
+    for (int j = 0; j < r; j++) WLU[i + r * j] = W0[idx[i] + (size_t)NOm * j];
+  for (int j = 0; j < r; j++)
+    for (int k = 0; k < NOm; k++) beta[j] += w[k] * W0[k + (size_t)NOm * j];
+  for (int i = 0; i < r; i++)
+    for (int k = 0; k < NOm; k++) {
+      double t = 0;
+      for (int l = 0; l < r; l++) t += S0[i + r * l] * W0[k + (size_t)NOm * l];
+      L0[i + r * k] = t;
+    }
+  int rc = lu_factor(r, WLU, wpiv);
+  if (rc == 0)
+    rc = collocation_si(p, r, X0, L0, idx, WLU, wpiv, beta, ox, oy, sig_t, sig_s, q,
+                        tol, max_iter, fixed, Psi, iters);
+  free(ox); free(oy); free(oz); free(w); free(sig_s); free(q); free(sig_t);
+  free(WLU); free(wpiv); free(beta); free(L0);
+  return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Algorithm 1: one SN-like DLR time step.                             */
+/* ------------------------------------------------------------------ */
+
+int oracle_dlr_step(const oracle_problem *p, int r, double *X, double *S,
+                    double *W, double *T, const oracle_dlr_opts *opt,
+                    int *idx_out, double *phi_out, oracle_dlr_diag *diag) {
+  int nx = p->nx, ny = p->ny, Nx = nx * ny, NOm = p->n_polar * p->n_azim;
+  double hx = p->lx / nx, hy = p->ly / ny, h2 = hx * hy, h = sqrt(h2);
+  double inv_cdt = 1.0 / (p->c * p->dt);
+  if (r < 1 || r > Nx || r > NOm) return -1;
+  int rc = 0;
+
+  double *ox = (double *)malloc(sizeof(double) * NOm);
+  double *oy = (double *)malloc(sizeof(double) * NOm);
+  double *oz = (double *)malloc(sizeof(double) * NOm);
+  double *w = (double *)malloc(sizeof(double) * NOm);
+  oracle_quadrature(p->n_polar, p->n_azim, ox, oy, oz, w);
+
+  double *phi0 = (double *)malloc(sizeof(double) * Nx);
+  phi_from_factors(Nx, NOm, r, X, S, W, w, phi0);
+  double E_before = energy(p, T, phi0);
+
+  /* Step 1: effective scattering and source from T0 (Eqs. effective
+   * scattering / effective source, reading R1). */
+  double *sig_s = (double *)malloc(sizeof(double) * Nx);
+  double *q = (double *)malloc(sizeof(double) * Nx);
+  double *B0 = (double *)malloc(sizeof(double) * Nx);
+  double *D = (double *)malloc(sizeof(double) * Nx);
+  double *sig_t = (double *)malloc(sizeof(double) * Nx);
+  oracle_coefficients(p, T, sig_s, q, B0, D);
+  for (int c = 0; c < Nx; c++) sig_t[c] = p->sigma[c] + inv_cdt;
+
+  /* Step 2: select r angles from W0 (Section 4.2; reading R8). */
+  int *idx = (int *)malloc(sizeof(int) * r);
+  if (opt && opt->forced_idx) memcpy(idx, opt->forced_idx, sizeof(int) * r);
+  else if (opt && opt->selection == 1) rc = oracle_deim(NOm, r, W, idx);
+  else rc = oracle_qdeim(NOm, r, W, idx);
+  if (idx_out) memcpy(idx_out, idx, sizeof(int) * r);
+
+  /* What_ij = W0_j(Om^(i)), beta_j = int W0_j (Section 4.1) */
+  double *What = (double *)malloc(sizeof(double) * r * r);
+  double *WLU = (double *)malloc(sizeof(double) * r * r);
+  int *wpiv = (int *)malloc(sizeof(int) * r);
+  double *beta = (double *)calloc(r, sizeof(double));
+  for (int i = 0; i < r; i++)
+    for (int j = 0; j < r; j++) What[i + r * j] = W[idx[i] + (size_t)NOm * j];
+  for (int j = 0; j < r; j++)
+    for (int k = 0; k < NOm; k++) beta[j] += w[k] * W[k + (size_t)NOm * j];
+  memcpy(WLU, What, sizeof(double) * r * r);
+  if (rc == 0 && lu_factor(r, WLU, wpiv) != 0) rc = -1;
+
+  /* Steps 3-4: initial condition at the chosen angles and source
+   * iteration on the collocation system. */
+  double *L0 = (double *)malloc(sizeof(double) * r * NOm);
+  for (int i = 0; i < r; i++)
+    for (int k = 0; k < NOm; k++) {
+      double t = 0;
+      for (int l = 0; l < r; l++) t += S[i + r * l] * W[k + (size_t)NOm * l];
+      L0[i + r * k] = t;
+    }
+  double *Psi = (double *)malloc(sizeof(double) * Nx * r);
+  int iters = 0;
+  if (rc == 0) {
+    int fixed = opt ? opt->si_fixed_iters : 0;
+    rc = collocation_si(p, r, X, L0, idx, WLU, wpiv, beta, ox, oy, sig_t, sig_s, q,
+                        opt ? opt->si_tol : 1e-13, opt ? opt->si_max_iter : 1000,
+                        fixed, Psi, &iters);
+  }
+
+  /* Step 5: Psi = X R with h^2 X^T X = I (Householder QR of h Psi). */
+  double *Xn = (double *)malloc(sizeof(double) * Nx * r);
+  double *R = (double *)malloc(sizeof(double) * r * r);
+  double *A = (double *)malloc(sizeof(double) * Nx * r);
+  double rdr = 0;
+  if (rc == 0) {
+    for (size_t e = 0; e < (size_t)Nx * r; e++) A[e] = h * Psi[e];
+    oracle_householder_qr(Nx, r, A, Xn, R);
+    for (size_t e = 0; e < (size_t)Nx * r; e++) Xn[e] /= h;
+    double rmin = INFINITY, rmax = 0;
+    for (int j = 0; j < r; j++) {
+      double d = fabs(R[j + r * j]);
+      if (d < rmin) rmin = d;
+      if (d > rmax) rmax = d;
+    }
+    rdr = rmax > 0 ? rmin / rmax : 0;
+  }
+
+  /* Step 6: Lt0 = <psi0, X_j> = P L0, P_ji = h^2 <X_j, X0_i>. */
+  double *P = (double *)malloc(sizeof(double) * r * r);
+  double *Lt0 = (double *)malloc(sizeof(double) * r * NOm);
+  if (rc == 0) {
+    for (int jj = 0; jj < r; jj++)
+      for (int i = 0; i < r; i++) {
+        double t = 0;
+        for (int c = 0; c < Nx; c++) t += Xn[c + (size_t)Nx * jj] * X[c + (size_t)Nx * i];
+        P[jj + r * i] = h2 * t;
+      }
+    for (int jj = 0; jj < r; jj++)
+      for (int k = 0; k < NOm; k++) {
+        double t = 0;
+        for (int i = 0; i < r; i++) t += P[jj + r * i] * L0[i + r * k];
+        Lt0[jj + r * k] = t;
+      }
+  }
+
+  /* Step 7: L-step (Eq. L step). */
+  double *L = (double *)malloc(sizeof(double) * r * NOm);
+  if (rc == 0) rc = oracle_lstep(p, r, Xn, sig_t, sig_s, q, Lt0, L);
+
+  /* Step 8: L = S W^T with sum_k w_k W_ki W_kj = delta: Householder QR of
+   * diag(sqrt w) L^T = Q R, W = diag(1/sqrt w) Q, S = R^T; then optionally
+   * S = U Sigma V^T -> X U, Sigma, W V (signs: max-|.| entry of W_j > 0). */
+  double *Wn = (double *)malloc(sizeof(double) * NOm * r);
+  double *Sn = (double *)malloc(sizeof(double) * r * r);
+  if (rc == 0) {
+    double *M = (double *)malloc(sizeof(double) * NOm * r);
+    double *Qm = (double *)malloc(sizeof(double) * NOm * r);
+    double *Rm = (double *)malloc(sizeof(double) * r * r);
+    for (int j = 0; j < r; j++)
+      for (int k = 0; k < NOm; k++) M[k + (size_t)NOm * j] = sqrt(w[k]) * L[j + r * k];
+    oracle_householder_qr(NOm, r, M, Qm, Rm);
+    for (int j = 0; j < r; j++)
+      for (int k = 0; k < NOm; k++) Wn[k + (size_t)NOm * j] = Qm[k + (size_t)NOm * j] / sqrt(w[k]);
+    for (int i = 0; i < r; i++)
+      for (int j = 0; j < r; j++) Sn[i + r * j] = Rm[j + r * i];
+    if (!opt || opt->canonicalize) {
+      double *U = (double *)malloc(sizeof(double) * r * r);
+      double *V = (double *)malloc(sizeof(double) * r * r);
+      double *sv = (double *)malloc(sizeof(double) * r);
+      oracle_jacobi_svd(r, Sn, U, sv, V);
+      double *Xr = (double *)malloc(sizeof(double) * Nx * r);
+      double *Wr = (double *)malloc(sizeof(double) * NOm * r);
+      double *absw = (double *)malloc(sizeof(double) * NOm);
+      for (int j = 0; j < r; j++) {
+        for (int c = 0; c < Nx; c++) {
+          double t = 0;
+          for (int i = 0; i < r; i++) t += Xn[c + (size_t)Nx * i] * U[i + r * j];
+          Xr[c + (size_t)Nx * j] = t;
+        }
+        for (int k = 0; k < NOm; k++) {
+          double t = 0;
+          for (int i = 0; i < r; i++) t += Wn[k + (size_t)NOm * i] * V[i + r * j];
+          Wr[k + (size_t)NOm * j] = t;
+        }
+        /* sign: the entry of largest magnitude (tie rule R8) is > 0 */
+        for (int k = 0; k < NOm; k++) absw[k] = fabs(Wr[k + (size_t)NOm * j]);
+        int am = argmax_tie(NOm, absw, NULL);
+        if (Wr[am + (size_t)NOm * j] < 0) {
+          for (int k = 0; k < NOm; k++) Wr[k + (size_t)NOm * j] = -Wr[k + (size_t)NOm * j];
+          for (int c = 0; c < Nx; c++) Xr[c + (size_t)Nx * j] = -Xr[c + (size_t)Nx * j];
+        }
+      }
+      memcpy(Xn, Xr, sizeof(double) * Nx * r);
+      memcpy(Wn, Wr, sizeof(double) * NOm * r);
+      for (int e = 0; e < r * r; e++) Sn[e] = 0.0;
+      for (int j = 0; j < r; j++) Sn[j + r * j] = sv[j];
+      free(U); free(V); free(sv); free(Xr); free(Wr); free(absw);
+    }
+    free(M); free(Qm); free(Rm);
+  }
+
+  /* Step 9: temperature update (Eq. temperature update, reading R1/R12). */
+  if (rc == 0) {
+    double *phin2 = (double *)malloc(sizeof(double) * Nx);
+    phi_from_factors(Nx, NOm, r, Xn, Sn, Wn, w, phin2);
+    double *Tn = (double *)malloc(sizeof(double) * Nx);
+    double minT = INFINITY, minphi = INFINITY;
+    for (int c = 0; c < Nx; c++) {
+      Tn[c] = T[c] + p->dt * p->sigma[c] * (phin2[c] - 4.0 * ORACLE_PI * B0[c]) / D[c];
+      if (Tn[c] < minT) minT = Tn[c];
+      if (phin2[c] < minphi) minphi = phin2[c];
+    }
+    if (diag) {
+      xl_ctx g = {Xn, NULL, Nx, r};
+      double *Lc = (double *)malloc(sizeof(double) * r * NOm);
+      for (int i = 0; i < r; i++)
+        for (int k = 0; k < NOm; k++) {
+          double t = 0;
+          for (int j = 0; j < r; j++) t += Sn[i + r * j] * Wn[k + (size_t)NOm * j];
+          Lc[i + r * k] = t;
+        }
+      g.L = Lc;
+      double out, in;
+      boundary_rates(p, ox, oy, w, get_xl, &g, &out, &in);
+      free(Lc);
+      diag->iters = iters;
+      diag->E_before = E_before;
+      diag->E_after = energy(p, Tn, phin2);
+      diag->outflow = out;
+      diag->inflow = in;
+      diag->residual = diag->E_after - E_before + p->dt * (out - in);
+      diag->min_T = minT;
+      diag->min_phi = minphi;
+      diag->R_diag_ratio = rdr;
+      /* 1-norm condition of What from its explicit inverse */
+      double *Wi = (double *)malloc(sizeof(double) * r * r);
+      double *I_r = (double *)calloc(r * r, sizeof(double));
+      for (int i = 0; i < r; i++) I_r[i + r * i] = 1.0;
+      oracle_lu_solve(r, What, r, I_r, Wi);
+      double n1 = 0, n2 = 0;
+      for (int j = 0; j < r; j++) {
+        double a = 0, b = 0;
+        for (int i = 0; i < r; i++) { a += fabs(What[i + r * j]); b += fabs(Wi[i + r * j]); }
+        if (a > n1) n1 = a;
+        if (b > n2) n2 = b;
+      }
+      diag->What_cond1 = n1 * n2;
+      free(Wi); free(I_r);
+    }
+    if (phi_out) memcpy(phi_out, phin2, sizeof(double) * Nx);
+    memcpy(X, Xn, sizeof(double) * Nx * r);
+    memcpy(S, Sn, sizeof(double) * r * r);
+    memcpy(W, Wn, sizeof(double) * NOm * r);
+    memcpy(T, Tn, sizeof(double) * Nx);
+    free(phin2);
+    free(Tn);
+  } else if (diag) {
+    diag->iters = iters;
+  }
+
+  free(ox); free(oy); free(oz); free(w); free(phi0); free(sig_s); free(q);
+  free(B0); free(D); free(sig_t); free(idx); free(What); free(WLU);
+  free(wpiv); free(beta); free(L0); free(Psi); free(Xn); free(R); free(A); free(P);
+  free(Lt0); free(L); free(Wn); free(Sn);
+  return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Full-rank SN step (the comparison method of Section 5).            */
+/* ------------------------------------------------------------------ */
+
+int oracle_sn_step(const oracle_problem *p, double *psi, double *T,
+                   double si_tol, int si_max_iter, double *phi_out,
+                   double *outflow, double *inflow) {
+  int Nx = p->nx * p->ny, NOm = p->n_polar * p->n_azim;
+  double inv_cdt = 1.0 / (p->c * p->dt);
+  double *ox = (double *)malloc(sizeof(double) * NOm);
+  double *oy = (double *)malloc(sizeof(double) * NOm);
+  double *oz = (double *)malloc(sizeof(double) * NOm);
+  double *w = (double *)malloc(sizeof(double) * NOm);
+  oracle_quadrature(p->n_polar, p->n_azim, ox, oy, oz, w);
+  double *sig_s = (double *)malloc(sizeof(double) * Nx);
+  double *q = (double *)malloc(sizeof(double) * Nx);
+  double *B0 = (double *)malloc(sizeof(double) * Nx);
+  double *D = (double *)malloc(sizeof(double) * Nx);
+  double *sig_t = (double *)malloc(sizeof(double) * Nx);
+  double *phi = (double *)calloc(Nx, sizeof(double));
+  double *phin = (double *)malloc(sizeof(double) * Nx);
+  double *src = (double *)malloc(sizeof(double) * Nx);
+  double *psi0 = (double *)malloc(sizeof(double) * Nx * NOm);
+  memcpy(psi0, psi, sizeof(double) * Nx * NOm);
+  oracle_coefficients(p, T, sig_s, q, B0, D);
+  for (int c = 0; c < Nx; c++) sig_t[c] = p->sigma[c] + inv_cdt;
+  for (int k = 0; k < NOm; k++)
+    for (int c = 0; c < Nx; c++) phi[c] += w[k] * psi0[c + (size_t)Nx * k];
+  int iters = 0, converged = 0;
+  while (iters < si_max_iter) {
+    for (int c = 0; c < Nx; c++) phin[c] = 0;
+    for (int k = 0; k < NOm; k++) {
+      for (int c = 0; c < Nx; c++)
+        src[c] = sig_s[c] * phi[c] / (4.0 * ORACLE_PI) + q[c] + inv_cdt * psi0[c + (size_t)Nx * k];
+      oracle_sweep(p, ox[k], oy[k], sig_t, src, psi + (size_t)Nx * k);
+      for (int c = 0; c < Nx; c++) phin[c] += w[k] * psi[c + (size_t)Nx * k];
+    }
+    iters++;
+    double dmax = 0, pmax = 0;
+    for (int c = 0; c < Nx; c++) {
+      if (fabs(phin[c] - phi[c]) > dmax) dmax = fabs(phin[c] - phi[c]);
+      if (fabs(phin[c]) > pmax) pmax = fabs(phin[c]);
+    }
+    memcpy(phi, phin, sizeof(double) * Nx);
+    if (dmax <= si_tol * pmax) { converged = 1; break; }
+  }
+  for (int c = 0; c < Nx; c++)
+    T[c] = T[c] + p->dt * p->sigma[c] * (phi[c] - 4.0 * ORACLE_PI * B0[c]) / D[c];
+  if (phi_out) memcpy(phi_out, phi, sizeof(double) * Nx);
+  if (outflow && inflow) {
+    full_ctx g = {psi, Nx};
+    boundary_rates(p, ox, oy, w, get_full, &g, outflow, inflow);
+  }
+  free(ox); free(oy); free(oz); free(w); free(sig_s); free(q); free(B0);
+  free(D); free(sig_t); free(phi); free(phin); free(src); free(psi0);
+  return converged ? iters : -2;
+}

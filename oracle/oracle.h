@@ -1,0 +1,118 @@
+/*
+ * oracle.h -- plain FP64 CPU reference of the SN-like dynamic-low-rank (DLR)
+ * time step for gray thermal radiative transfer in 2-D (Haut et al.,
+ * "Efficient SN-like and PN-like Dynamic Low Rank methods for Thermal
+ * Radiative Transfer", Section 4 and Algorithm 1).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or
+ * calls this code; only the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark do.  It shares no code, header, table or helper with the CUDA
+ * path.
+ *
+ * Conventions (all arrays FP64, caller-owned):
+ *   cells      c = iy*nx + ix, cell centres ((ix+1/2)hx, (iy+1/2)hy)
+ *   angles     k = p*n_azim + a  (Gauss-Legendre polar index p, azimuth a)
+ *   matrices   column-major: X[c + Nx*i] (Nx x r), W[k + NOm*j] (NOm x r),
+ *              S[i + r*j] (r x r), L[i + r*k] (r x NOm)
+ *   edges      0 = left (x=0), 1 = right (x=lx), 2 = bottom (y=0), 3 = top
+ *   orthonormality  hx*hy*sum_c X_ci X_cj = delta_ij,
+ *                   sum_k w_k W_ki W_kj = delta_ij
+ */
+#ifndef DLR_ORACLE_H
+#define DLR_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  int nx, ny;          /* cells */
+  double lx, ly;       /* domain [0,lx] x [0,ly] */
+  int n_polar, n_azim; /* product quadrature, NOm = n_polar*n_azim */
+  double dt, c, a_rad; /* time step, speed of light, radiation constant */
+  const double *sigma;  /* Nx absorption opacity */
+  const double *rho_cv; /* Nx heat capacity */
+  double psi_edge[4];  /* isotropic inflow value of psi per edge; 0 = vacuum */
+} oracle_problem;
+
+typedef struct {
+  int selection;          /* 0 = pivoted-QR (Q-DEIM) angle choice, 1 = DEIM */
+  const int *forced_idx;  /* if non-NULL: use these r angle indices */
+  double si_tol;          /* relative sup-norm stopping tolerance */
+  int si_max_iter;        /* iteration cap (returns -2 if reached) */
+  int si_fixed_iters;     /* > 0: run exactly this many iterations */
+  int canonicalize;       /* 1: rotate factors to the SVD of S */
+} oracle_dlr_opts;
+
+typedef struct {
+  int iters;              /* source iterations taken */
+  double E_before, E_after;  /* sum_c h^2 (rho_cv T + phi/c) */
+  double outflow, inflow;    /* boundary energy rates of the new psi */
+  double residual;        /* E_after - E_before + dt (outflow - inflow) */
+  double min_T, min_phi;
+  double What_cond1;      /* 1-norm condition estimate of What (explicit inverse) */
+  double R_diag_ratio;    /* min_j |R_jj| / max_j |R_jj| of the Psi = X R factor */
+} oracle_dlr_diag;
+
+/* Planck function B(T) = a c T^4 / (4 pi) (reading of the undefined B). */
+double oracle_planck(double a_rad, double c, double T);
+
+/* Product quadrature: Gauss-Legendre mu ascending x equispaced azimuths. */
+void oracle_quadrature(int n_polar, int n_azim, double *ox, double *oy,
+                       double *oz, double *w);
+
+/* Linearised coefficients of Section 2.2 (reading R1): sigma_s, q, B0, D. */
+void oracle_coefficients(const oracle_problem *p, const double *T0,
+                         double *sigma_s, double *q, double *B0, double *D);
+
+/* One DG0 upwind transport sweep in direction (ox, oy):
+ * (ox d/dx + oy d/dy + sigma_t) psi = src, with the problem's edge inflow. */
+void oracle_sweep(const oracle_problem *p, double ox, double oy,
+                  const double *sigma_t, const double *src, double *psi);
+
+/* Dense linear algebra building blocks. */
+int oracle_lu_solve(int n, const double *A, int nrhs, const double *B,
+                    double *Xout);
+void oracle_householder_qr(int m, int n, const double *A, double *Q,
+                           double *R);
+int oracle_jacobi_svd(int n, const double *A, double *U, double *s,
+                      double *V);
+int oracle_qdeim(int n, int r, const double *W, int *idx);
+int oracle_deim(int n, int r, const double *W, int *idx);
+
+/* Deterministic rank-r initial factors for psi0(x, Om) = B(T0(x)). */
+int oracle_initial_factors(const oracle_problem *p, const double *T0, int r,
+                           double *X0, double *S0, double *W0);
+
+/* L-step of Algorithm 1 step 7 for given X (new space basis), coefficient
+ * fields and projected old state Lt0 (r x NOm).  Writes L (r x NOm). */
+int oracle_lstep(const oracle_problem *p, int r, const double *X,
+                 const double *sigma_t, const double *sigma_s,
+                 const double *q, const double *Lt0, double *L);
+
+/* Steps 1-4 of Algorithm 1 at the given angle indices: coefficients from
+ * T0, psi0 at the chosen angles, source iteration of the collocation system.
+ * Writes Psi (Nx x r); returns 0, -1 (singular What), -2 (SI cap). */
+int oracle_collocation(const oracle_problem *p, int r, const double *X0,
+                       const double *S0, const double *W0, const double *T0,
+                       const int *idx, double tol, int max_iter, int fixed,
+                       double *Psi, int *iters);
+
+/* One SN-like DLR step (Algorithm 1).  X (Nx x r), S (r x r), W (NOm x r)
+ * and T (Nx) are read as the state at t0 and overwritten with the state at
+ * t0 + dt.  idx_out (r), phi_out (Nx) and diag may be NULL.
+ * Returns 0, -1 on bad input / singular matrix, -2 if SI hit its cap. */
+int oracle_dlr_step(const oracle_problem *p, int r, double *X, double *S,
+                    double *W, double *T, const oracle_dlr_opts *opt,
+                    int *idx_out, double *phi_out, oracle_dlr_diag *diag);
+
+/* One full-rank SN step with source iteration.  psi (Nx x NOm, column k is
+ * angle k) and T are overwritten.  Returns iterations, or -2 at the cap. */
+int oracle_sn_step(const oracle_problem *p, double *psi, double *T,
+                   double si_tol, int si_max_iter, double *phi_out,
+                   double *outflow, double *inflow);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
