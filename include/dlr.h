@@ -1,0 +1,199 @@
+/*
+ * dlr.h -- C ABI of the GB300 SN-like dynamic-low-rank (DLR) solver for gray
+ * thermal radiative transfer in two space dimensions.
+ *
+ * Method: Haut, Loffeld, Einkemmer, Guthrey, Brunner, Schill, "Efficient
+ * SN-like and PN-like Dynamic Low Rank methods for Thermal Radiative
+ * Transfer", Section 4 (SN-like DLR scheme) and Algorithm 1 (one implicit time
+ * step).  The problem statement follows Section 2: Eqs. (TRT psi), (TRT
+ * inflow), (TRT T) with the backward-Euler / Newton linearisation of Section
+ * 2.2.  The state is the rank-r factorisation psi(x, Om) = sum_ij X_i(x) S_ij
+ * W_j(Om) of Eq. (low rank) plus the material temperature T(x).
+ *
+ * Discretisation (fixed by this library): nx x ny Cartesian cells on
+ * [0,lx] x [0,ly], piecewise-constant (DG0) upwind transport; a product
+ * angular quadrature of n_polar Gauss-Legendre cosines mu (ascending) times
+ * n_azim equispaced azimuths (a + 1/2) 2 pi / n_azim; angle index
+ * k = p * n_azim + a.  Cells are indexed c = iy * nx + ix.  B(T) = a c T^4 /
+ * (4 pi).  An edge with a non-negative temperature T_b has isotropic inflow
+ * B(T_b) for directions entering it; a negative value means vacuum.
+ *
+ * Memory and ownership.  dlr_create copies every host input it is given; the
+ * library owns all device state of a handle (allocated through the caller's
+ * allocator callback when one is given, else cudaMalloc) until dlr_destroy.
+ * Output buffers always belong to the caller.  "on_device" arguments say
+ * whether a caller pointer is device memory (1) or host memory (0).
+ *
+ * Streams.  All device work of a handle is enqueued on runtime.stream (0 =
+ * the legacy default stream).  dlr_step and dlr_step_batch return after
+ * enqueueing; getters synchronise the stream.
+ *
+ * Errors.  Every function returning int returns DLR_OK (0) or a negative
+ * DLR_E* code and records a message readable with dlr_last_error() (per
+ * thread).  A device-side failure (no convergence, singular matrix, timeout
+ * of a bounded wait, non-positive temperature) is sticky on the handle: it is
+ * reported by the next synchronising call and by every later dlr_step.
+ * Nothing crosses the ABI as a C++ exception.  There is no CPU fallback: on a
+ * machine without a usable sm_103 GPU, dlr_create fails with DLR_ECUDA.
+ */
+#ifndef DLR_GB300_H
+#define DLR_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DLR_OK 0
+#define DLR_EINVAL (-1)     /* bad argument or size */
+#define DLR_ENOMEM (-2)     /* allocation failed or HBM budget exceeded */
+#define DLR_ENOTCONV (-3)   /* source iteration hit si_max_iter */
+#define DLR_ESINGULAR (-4)  /* singular collocation or L-step matrix */
+#define DLR_ETIMEOUT (-5)   /* a bounded device-side wait ran out */
+#define DLR_ENONPOS (-6)    /* temperature became non-positive */
+#define DLR_ECUDA (-7)      /* CUDA runtime error */
+
+#define DLR_FP64 0   /* every kernel in FP64 */
+#define DLR_MIXED 1  /* FP32 sweeps and projections, FP64 small linear algebra and T */
+
+#define DLR_SEL_QDEIM 0  /* angles = first r pivots of column-pivoted QR of W^T */
+#define DLR_SEL_DEIM 1   /* greedy DEIM of Section 4.2 */
+
+/* Problem statement (Section 2.1-2.2, Algorithm 1 inputs). */
+typedef struct dlr_problem {
+  int32_t nx, ny;        /* cells per side, >= 1 */
+  double lx, ly;         /* domain size, > 0 */
+  int32_t n_polar;       /* Gauss-Legendre polar cosines, >= 1 */
+  int32_t n_azim;        /* azimuths, >= 1 */
+  int32_t rank;          /* r0: 1 <= r0 <= min(64, nx*ny, n_polar*n_azim) */
+  double dt;             /* time step, > 0 */
+  double c;              /* speed of light, > 0 */
+  double a_rad;          /* radiation constant, >= 0 */
+  const double *sigma;   /* host, nx*ny absorption opacities, >= 0 (copied) */
+  const double *rho_cv;  /* host, nx*ny heat capacities rho*c_v, > 0 (copied) */
+  const double *T0;      /* host, nx*ny initial temperatures, > 0 (copied) */
+  double T_edge[4];      /* inflow temperature per edge: left, right, bottom,
+                            top; < 0 = vacuum */
+  int32_t precision;     /* DLR_FP64 or DLR_MIXED */
+  int32_t selection;     /* DLR_SEL_QDEIM or DLR_SEL_DEIM */
+  int32_t augment;       /* must be 0 (Algorithm 1 as printed) */
+  double si_tol;         /* source-iteration tolerance; stop when
+                            max|phi_new - phi| <= si_tol * max|phi_new|;
+                            <= 0 selects 1e-13 (FP64) or 1e-7 (mixed) */
+  int32_t si_max_iter;   /* iteration cap (<= 0 selects 1000) */
+  int32_t si_fixed_iters;/* > 0: run exactly this many iterations (testing) */
+} dlr_problem;
+
+/* Device memory and stream supplied by the caller (e.g. PyTorch). */
+typedef struct dlr_runtime {
+  void *stream;                                 /* cudaStream_t, 0 = default */
+  void *(*alloc)(size_t bytes, void *ctx);      /* NULL: cudaMalloc */
+  void (*free)(void *ptr, void *ctx);           /* NULL: cudaFree */
+  void *ctx;                                    /* passed to alloc / free */
+  size_t hbm_budget;  /* if > 0: dlr_create fails with DLR_ENOMEM when the
+                         handle's footprint exceeds it */
+} dlr_runtime;
+
+typedef struct dlr_handle dlr_handle;
+
+/* Statistics of a handle (all counters since creation). */
+typedef struct dlr_stats {
+  int64_t steps;             /* completed time steps */
+  int64_t si_iters_total;    /* source iterations over all steps */
+  int64_t cell_angle_updates;/* sum over steps of nx*ny*r*iterations */
+  int32_t si_iters_last;     /* iterations of the last step */
+  int32_t status;            /* sticky device status (DLR_OK or DLR_E*) */
+  double ms_si_total;        /* device time of the source-iteration kernel,
+                                when timing is enabled (else 0) */
+  double ms_step_total;      /* device time of whole steps when timing is on */
+  int64_t si_launches;       /* timed source-iteration launches */
+} dlr_stats;
+
+/* Creates a solver: validates sizes, builds the quadrature and the initial
+ * rank-r factors of psi0(x, Om) = B(T0(x)) (X0 = B(T0) then cosine modes,
+ * W0 = Om_x^a Om_y^b monomials then Om_z times them, both orthonormalised,
+ * S0 = diag(s0, 0, ...)), copies sigma, rho_cv and T0 to the device.  On
+ * success *out owns the device state.  Returns DLR_EINVAL, DLR_ENOMEM or
+ * DLR_ECUDA on failure (then *out is NULL). */
+int dlr_create(const dlr_problem *problem, const dlr_runtime *runtime,
+               dlr_handle **out);
+
+/* Enqueues nsteps implicit time steps (Algorithm 1, steps 1-9) on the
+ * handle's stream; asynchronous.  Returns a sticky error if an earlier step
+ * failed on the device. */
+int dlr_step(dlr_handle *h, int32_t nsteps);
+
+/* Enqueues nsteps steps of n independent handles as one batch: each kernel
+ * launch covers all handles (one persistent source-iteration launch per step
+ * for all of them).  All handles must share precision, selection and the
+ * stream of hs[0].  Results equal those of dlr_step on each handle alone. */
+int dlr_step_batch(dlr_handle *const *hs, int32_t n, int32_t nsteps);
+
+/* Copies T (nx*ny FP64) into out; synchronises. */
+int dlr_get_T(dlr_handle *h, double *out, int32_t out_on_device);
+
+/* Replaces T (nx*ny FP64) with in; enqueued on the stream (host input is
+ * copied before return). */
+int dlr_set_T(dlr_handle *h, const double *in, int32_t in_on_device);
+
+/* Copies the factors: X (nx*ny x r, column-major, hx*hy*X^T X = I), S (r x
+ * r, column-major), W (NOm x r, column-major, sum_k w_k W_ki W_kj = d_ij), all
+ * FP64 (X is widened in mixed precision); *r_out = r.  Any pointer may be
+ * NULL.  Synchronises. */
+int dlr_get_factors(dlr_handle *h, double *X, double *S, double *W,
+                    int32_t *r_out, int32_t out_on_device);
+
+/* Replaces the factors (same layouts as dlr_get_factors).  Used to start
+ * from a given state. */
+int dlr_set_factors(dlr_handle *h, const double *X, const double *S,
+                    const double *W, int32_t in_on_device);
+
+/* Copies the quadrature: omega_xyz (NOm x 3 row-major: Om_x, Om_y, Om_z per
+ * angle) and weights w (NOm, summing to 4 pi).  Either may be NULL. */
+int dlr_get_quadrature(dlr_handle *h, double *omega_xyz, double *w);
+
+/* The r angle indices chosen in the last step (Algorithm 1 step 2), or -1
+ * before the first step.  Synchronises. */
+int dlr_get_selected(dlr_handle *h, int32_t *idx);
+
+/* Statistics; synchronises. */
+int dlr_get_stats(dlr_handle *h, dlr_stats *out);
+
+/* Enables (1) or disables (0) CUDA-event timing of the source-iteration
+ * kernel and of whole steps (read back through dlr_get_stats). */
+int dlr_set_timing(dlr_handle *h, int32_t enable);
+
+/* Sets the isotropic inflow value psi_iso (>= 0, a value of psi, not a
+ * temperature) of one edge (0 left, 1 right, 2 bottom, 3 top) for the
+ * following steps. */
+int dlr_set_edge_inflow(dlr_handle *h, int32_t edge, double psi_iso);
+
+/* Device bytes a handle for this problem would hold (no allocation). */
+size_t dlr_footprint_bytes(const dlr_problem *problem);
+
+/* Releases the handle and its device state (synchronises its stream). */
+void dlr_destroy(dlr_handle *h);
+
+/* Message of the last error on this thread ("" if none). */
+const char *dlr_last_error(void);
+
+/* Hot-kernel entry point (the DG0 upwind sweep of Section 4.4 used by
+ * Algorithm 1 step 4), for testing the sweep alone.  For each of n_dir
+ * directions d with in-plane components dirs[2d], dirs[2d+1] (host), solves
+ *   |ox|/hx (psi_c - psi_west) + |oy|/hy (psi_c - psi_south) + sigma_t,c psi_c
+ *     = src[d*N + c]
+ * in upwind order, with edge inflow psi_edge[4] (host; left, right, bottom,
+ * top).  sigma_t (N), src (n_dir*N) and psi (n_dir*N, output) are device
+ * arrays of double (precision DLR_FP64) or float (DLR_MIXED), N = nx*ny.
+ * Synchronous on stream.  Returns DLR_EINVAL, DLR_ETIMEOUT or DLR_ECUDA on
+ * failure. */
+int dlr_sweep(int32_t nx, int32_t ny, double lx, double ly, int32_t n_dir,
+              const double *dirs, const double *psi_edge, int32_t precision,
+              const void *sigma_t, const void *src, void *psi, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

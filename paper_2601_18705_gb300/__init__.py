@@ -1,0 +1,248 @@
+"""GB300-native SN-like dynamic-low-rank (DLR) solver for gray thermal
+radiative transfer in 2-D (Haut et al., Section 4 and Algorithm 1).
+
+The Python layer marshals arguments for the C ABI of include/dlr.h; every
+step of the method runs in the CUDA kernels of libdlr_gb300.so.  PyTorch
+supplies device memory (through the allocator callback) and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib
+from ._lib import (DLR_FP64, DLR_MIXED, DLR_SEL_DEIM, DLR_SEL_QDEIM, DlrError,  # noqa: F401
+                   check, load)
+
+__all__ = ["Solver", "step_batch", "sweep", "footprint_bytes", "DlrError", "DLR_FP64",
+           "DLR_MIXED", "DLR_SEL_QDEIM", "DLR_SEL_DEIM", "problem_from_case"]
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
+
+
+@dataclass
+class ProblemSpec:
+    nx: int
+    ny: int
+    n_polar: int
+    n_azim: int
+    rank: int
+    sigma: np.ndarray
+    rho_cv: np.ndarray
+    T0: np.ndarray
+    T_edge: tuple = (-1.0, -1.0, -1.0, -1.0)
+    lx: float = 1.0
+    ly: float = 1.0
+    dt: float = 1e-3
+    c: float = 299.792458
+    a_rad: float = 0.01372
+    precision: int = DLR_FP64
+    selection: int = DLR_SEL_QDEIM
+    si_tol: float = 0.0
+    si_max_iter: int = 0
+    si_fixed_iters: int = 0
+
+    def cstruct(self):
+        keep = [_f64(self.sigma), _f64(self.rho_cv), _f64(self.T0)]
+        N = self.nx * self.ny
+        for a in keep:
+            if a.size != N:
+                raise ValueError("field size does not match nx*ny")
+        p = _lib.DlrProblem()
+        p.nx, p.ny, p.lx, p.ly = self.nx, self.ny, self.lx, self.ly
+        p.n_polar, p.n_azim, p.rank = self.n_polar, self.n_azim, self.rank
+        p.dt, p.c, p.a_rad = self.dt, self.c, self.a_rad
+        dp = C.POINTER(C.c_double)
+        p.sigma, p.rho_cv, p.T0 = (a.ctypes.data_as(dp) for a in keep)
+        for e in range(4):
+            p.T_edge[e] = float(self.T_edge[e])
+        p.precision, p.selection, p.augment = self.precision, self.selection, 0
+        p.si_tol, p.si_max_iter, p.si_fixed_iters = self.si_tol, self.si_max_iter, self.si_fixed_iters
+        return p, keep
+
+
+def problem_from_case(case: dict, precision=None, **kw) -> ProblemSpec:
+    """ProblemSpec of a workloads case dict."""
+    prec = case.get("precision", "fp64") if precision is None else precision
+    if isinstance(prec, str):
+        prec = DLR_MIXED if prec == "mixed" else DLR_FP64
+    spec = ProblemSpec(nx=case["nx"], ny=case["ny"], n_polar=case["n_polar"],
+                       n_azim=case["n_azim"], rank=case["r"], sigma=case["sigma"],
+                       rho_cv=case["rho_cv"], T0=case["T0"], T_edge=tuple(case["T_edge"]),
+                       lx=case.get("lx", 1.0), ly=case.get("ly", 1.0), dt=case["dt"],
+                       c=case["c"], a_rad=case["a_rad"], precision=prec)
+    for k, v in kw.items():
+        setattr(spec, k, v)
+    return spec
+
+
+def footprint_bytes(spec: ProblemSpec) -> int:
+    p, keep = spec.cstruct()
+    return int(load().dlr_footprint_bytes(C.byref(p)))
+
+
+class _TorchArena:
+    """Device memory for a handle from PyTorch's caching allocator."""
+
+    def __init__(self, device, stream):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.stream = stream
+        self.blocks = {}
+        self._alloc = _lib.ALLOC_FN(self.alloc)
+        self._free = _lib.FREE_FN(self.free)
+
+    def alloc(self, nbytes, ctx):
+        try:
+            with self.torch.cuda.stream(self.stream):
+                t = self.torch.empty(int(nbytes), dtype=self.torch.uint8, device=self.device)
+        except Exception:
+            return None
+        ptr = t.data_ptr()
+        self.blocks[ptr] = t
+        return ptr
+
+    def free(self, ptr, ctx):
+        self.blocks.pop(ptr, None)
+
+
+class Solver:
+    """One SN-like DLR instance resident on the GPU.
+
+    spec: ProblemSpec; use_torch_memory: allocate device state from PyTorch
+    (else cudaMalloc); stream: a torch.cuda.Stream (a new one by default);
+    hbm_budget: reject problems whose footprint exceeds it (bytes, 0 = none).
+    """
+
+    def __init__(self, spec: ProblemSpec, *, use_torch_memory: bool = True, stream=None,
+                 hbm_budget: int = 0):
+        import torch
+        L = load()
+        self.spec = spec
+        self.N = spec.nx * spec.ny
+        self.K = spec.n_polar * spec.n_azim
+        self.r = spec.rank
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        rt = _lib.DlrRuntime()
+        rt.stream = C.c_void_p(self.stream.cuda_stream)
+        self._arena = None
+        if use_torch_memory:
+            self._arena = _TorchArena(torch.device("cuda", torch.cuda.current_device()), self.stream)
+            rt.alloc, rt.free = self._arena._alloc, self._arena._free
+        rt.hbm_budget = int(hbm_budget)
+        p, keep = spec.cstruct()
+        h = C.c_void_p()
+        check(L.dlr_create(C.byref(p), C.byref(rt), C.byref(h)))
+        self._rt = rt
+        self.h = h
+
+    # -- lifetime --
+    def close(self) -> None:
+        if getattr(self, "h", None) is not None and self.h.value:
+            load().dlr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- stepping --
+    def step(self, nsteps: int = 1) -> None:
+        check(load().dlr_step(self.h, int(nsteps)))
+
+    # -- state --
+    def T(self) -> np.ndarray:
+        out = np.empty(self.N)
+        check(load().dlr_get_T(self.h, out.ctypes.data, 0))
+        return out
+
+    def T_into(self, tensor) -> None:
+        check(load().dlr_get_T(self.h, C.c_void_p(tensor.data_ptr()), 1 if tensor.is_cuda else 0))
+
+    def set_T(self, T) -> None:
+        if hasattr(T, "data_ptr"):
+            check(load().dlr_set_T(self.h, C.c_void_p(T.data_ptr()), 1 if T.is_cuda else 0))
+        else:
+            a = _f64(T)
+            check(load().dlr_set_T(self.h, a.ctypes.data, 0))
+
+    def factors(self):
+        X = np.empty((self.N, self.r), order="F")
+        S = np.empty((self.r, self.r), order="F")
+        W = np.empty((self.K, self.r), order="F")
+        r = C.c_int32()
+        check(load().dlr_get_factors(self.h, X.ctypes.data, S.ctypes.data, W.ctypes.data,
+                                     C.byref(r), 0))
+        return X, S, W
+
+    def set_factors(self, X, S, W) -> None:
+        X = np.asfortranarray(X, dtype=np.float64)
+        S = np.asfortranarray(S, dtype=np.float64)
+        W = np.asfortranarray(W, dtype=np.float64)
+        assert X.shape == (self.N, self.r) and S.shape == (self.r, self.r) and W.shape == (self.K, self.r)
+        check(load().dlr_set_factors(self.h, X.ctypes.data, S.ctypes.data, W.ctypes.data, 0))
+
+    def psi(self) -> np.ndarray:
+        """psi = X S W^T (Nx x NOm) from the current factors."""
+        X, S, W = self.factors()
+        return X @ S @ W.T
+
+    def quadrature(self):
+        om = np.empty((self.K, 3))
+        w = np.empty(self.K)
+        dp = C.POINTER(C.c_double)
+        check(load().dlr_get_quadrature(self.h, om.ctypes.data_as(dp), w.ctypes.data_as(dp)))
+        return om, w
+
+    def selected(self) -> np.ndarray:
+        idx = np.empty(self.r, dtype=np.int32)
+        check(load().dlr_get_selected(self.h, idx.ctypes.data_as(C.POINTER(C.c_int32))))
+        return idx
+
+    def stats(self) -> dict:
+        s = _lib.DlrStats()
+        check(load().dlr_get_stats(self.h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in _lib.DlrStats._fields_}
+
+    def set_timing(self, on: bool) -> None:
+        check(load().dlr_set_timing(self.h, 1 if on else 0))
+
+    def set_edge_inflow(self, edge: int, psi_iso: float) -> None:
+        check(load().dlr_set_edge_inflow(self.h, int(edge), float(psi_iso)))
+
+
+def step_batch(solvers, nsteps: int = 1) -> None:
+    """Steps several solvers as one batch (shared launches)."""
+    arr = (C.c_void_p * len(solvers))(*[s.h.value for s in solvers])
+    check(load().dlr_step_batch(arr, len(solvers), int(nsteps)))
+
+
+def sweep(nx, ny, dirs, psi_edge, sigma_t, src, *, lx=1.0, ly=1.0, stream=None):
+    """DG0 upwind sweeps of the hot kernel for n_dir directions.  sigma_t (N)
+    and src (n_dir*N) are CUDA tensors of float64 (FP64) or float32 (mixed);
+    returns psi (n_dir*N) of the same dtype."""
+    import torch
+    dirs = _f64(dirs)
+    n_dir = dirs.size // 2
+    edge = _f64(psi_edge)
+    prec = DLR_MIXED if sigma_t.dtype == torch.float32 else DLR_FP64
+    psi = torch.empty(n_dir * nx * ny, dtype=sigma_t.dtype, device=sigma_t.device)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    dp = C.POINTER(C.c_double)
+    check(load().dlr_sweep(nx, ny, lx, ly, n_dir, dirs.ctypes.data_as(dp), edge.ctypes.data_as(dp),
+                           prec, C.c_void_p(sigma_t.data_ptr()), C.c_void_p(src.data_ptr()),
+                           C.c_void_p(psi.data_ptr()), C.c_void_p(st.cuda_stream)))
+    return psi

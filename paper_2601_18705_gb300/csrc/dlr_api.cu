@@ -1,0 +1,1102 @@
+// dlr_api.cu -- the C ABI of include/dlr.h: handle lifetime, the initial
+// factors, batch plans (device-side work descriptors for all instances of a
+// batch) and the launch sequence of one SN-like DLR step (Algorithm 1 of
+// Haut et al.):
+//   graph "pre":  select angles (step 2), coefficients + psi0 (steps 1, 3),
+//                 source-iteration control reset
+//   direct:       cooperative source-iteration kernel (step 4)
+//   graph "post": CholeskyQR of Psi (step 5), projections (steps 6, 7),
+//                 L-step (step 7), CholeskyQR + SVD of L (step 8),
+//                 temperature update and factor rotation (step 9)
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/dlr.h"
+#include "dlr_internal.cuh"
+
+namespace dlr {
+// launchers defined in the kernel translation units
+template <typename real> cudaError_t launch_si(const Inst *, const SiCtl &, int, cudaStream_t);
+template <typename real> int si_max_grid(int, int, int);
+template <typename real> size_t si_smem_bytes(int, int, int);
+template <typename real>
+cudaError_t launch_sweep_dirs(int, int, double, double, int, const double *, const double *,
+                              const real *, const real *, real *, int *, cudaStream_t);
+template <typename real> cudaError_t launch_coeff_recon(const Inst *, int, int, int, cudaStream_t);
+template <typename real> cudaError_t launch_tsgram(const GramJob *, int, int, cudaStream_t);
+template <typename rin, typename rout>
+cudaError_t launch_apply(const ApplyJob *, int, int, int, cudaStream_t);
+template <typename real> cudaError_t launch_project(const Inst *, int, int, cudaStream_t);
+cudaError_t launch_reduce(const ReduceJob *, int, int, cudaStream_t);
+template <typename real> cudaError_t launch_tupdate(const Inst *, int, int, int, cudaStream_t);
+cudaError_t launch_select(const Inst *, int, int, cudaStream_t);
+cudaError_t launch_chol(const CholJob *, const Inst *, int, cudaStream_t);
+cudaError_t launch_proj_post(const Inst *, int, cudaStream_t);
+size_t lstep_angle_smem(int);
+cudaError_t launch_lstep(const Inst *, int, int, int, cudaStream_t);
+cudaError_t launch_svd(const Inst *, int, cudaStream_t);
+cudaError_t launch_sign(const Inst *, int, int, cudaStream_t);
+cudaError_t launch_si_prep(const Inst *, int, SiCtl, cudaStream_t);
+cudaError_t prepare_small(int, int);
+}  // namespace dlr
+
+using namespace dlr;
+
+// FP32 <-> FP64 column copies of X
+__global__ void k_widen(const float *a, double *b, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    b[i] = a[i];
+}
+__global__ void k_narrow(const double *a, float *b, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+
+// ------------------------------------------------------------------
+// errors
+// ------------------------------------------------------------------
+static thread_local std::string g_err;
+
+static int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return fail(DLR_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),  \
+                  __FILE__, __LINE__);                                                \
+  } while (0)
+
+static const char *status_name(int s) {
+  switch (s) {
+    case DLR_ENOTCONV: return "source iteration did not converge within si_max_iter";
+    case DLR_ESINGULAR: return "singular collocation or L-step matrix";
+    case DLR_ETIMEOUT: return "a bounded device-side wait ran out";
+    case DLR_ENONPOS: return "temperature became non-positive";
+    default: return "device error";
+  }
+}
+
+// ------------------------------------------------------------------
+// handle and batch plan
+// ------------------------------------------------------------------
+struct Batch;
+
+struct dlr_handle {
+  dlr_problem prob{};
+  int N = 0, K = 0, r = 0;
+  bool mixed = false;
+  size_t rs = 8;  // sizeof(real)
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  dlr_runtime rt{};
+  std::vector<void *> allocs;
+  Inst inst{};
+  unsigned version = 0;  // bumped whenever inst changes on the host
+  std::vector<double> ox, oy, oz, w;
+  int pb = 1;    // partial blocks of the cell reductions
+  int pbl = 1;   // partial blocks of the angle reductions
+  int lb = 1;    // blocks of the per-angle L-step
+  // device counters: [0] total SI iterations
+  long long *d_iters_total = nullptr;
+  int *h_status = nullptr;  // pinned mirror of the device status
+  int64_t steps = 0;
+  bool timing = false;
+  double ms_si = 0, ms_step = 0;
+  int64_t si_launches = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::array<cudaEvent_t, 4>> ev_pending;
+  Batch *own_batch = nullptr;
+};
+
+struct Batch {
+  std::vector<dlr_handle *> hs;
+  std::vector<unsigned> versions;  // handle versions of the uploaded copies
+  int n = 0;
+  bool mixed = false;
+  cudaStream_t st = nullptr;
+  Inst *d_insts = nullptr;   // contiguous copies of the instances
+  void *d_mem = nullptr;     // jobs, units, control
+  int maxN = 0, maxK = 0, rmax = 0, pbmax = 1, pblmax = 1, lbmax = 1;
+  int nx_max = 0, bands_max = 0, si_grid = 0;
+  SiCtl ctl{};
+  GramJob *g_psi1, *g_x, *g_l1, *g_w;
+  ApplyJob *a_psi, *a_x2, *a_x3, *a_l1, *a_w2, *a_w3, *a_wv;
+  CholJob *c_p1, *c_p2, *c_p3, *c_l1, *c_l2, *c_l3;
+  ReduceJob *r_proj;
+  cudaGraphExec_t pre = nullptr, post = nullptr;
+};
+
+static void *dev_alloc(dlr_handle *h, size_t bytes) {
+  bytes = (bytes + 255) & ~size_t(255);
+  void *p = nullptr;
+  if (h->rt.alloc) {
+    p = h->rt.alloc(bytes, h->rt.ctx);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    p = nullptr;
+  }
+  if (p) h->allocs.push_back(p);
+  return p;
+}
+
+static void dev_free_all(dlr_handle *h) {
+  for (void *p : h->allocs) {
+    if (h->rt.free) h->rt.free(p, h->rt.ctx);
+    else if (!h->rt.alloc) cudaFree(p);
+  }
+  h->allocs.clear();
+}
+
+// ------------------------------------------------------------------
+// quadrature and initial factors (host, FP64)
+// ------------------------------------------------------------------
+static void gl_nodes(int n, std::vector<double> &x, std::vector<double> &wt) {
+  // roots of P_n by Newton from cos(pi (i + 3/4) / (n + 1/2)); weights
+  // 2 / ((1 - x^2) P_n'(x)^2); ascending
+  x.assign(n, 0.0);
+  wt.assign(n, 0.0);
+  auto pn = [n](double z, double &d) {
+    double p0 = 1.0, p1 = z;
+    if (n == 0) { d = 0.0; return 1.0; }
+    for (int k = 2; k <= n; ++k) {
+      double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    d = n * (z * p1 - p0) / (z * z - 1.0);
+    return p1;
+  };
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(kPi * (i + 0.75) / (n + 0.5)), d = 0.0;
+    for (int it = 0; it < 200; ++it) {
+      double p = pn(z, d);
+      double dz = p / d;
+      z -= dz;
+      if (std::fabs(dz) < 1e-15) {
+        p = pn(z, d);
+        z -= p / d;
+        break;
+      }
+    }
+    pn(z, d);
+    x[n - 1 - i] = z;
+    wt[n - 1 - i] = 2.0 / ((1.0 - z * z) * d * d);
+  }
+}
+
+static void build_quadrature(dlr_handle *h) {
+  const int np = h->prob.n_polar, na = h->prob.n_azim;
+  std::vector<double> mu, wp;
+  gl_nodes(np, mu, wp);
+  h->ox.resize(h->K);
+  h->oy.resize(h->K);
+  h->oz.resize(h->K);
+  h->w.resize(h->K);
+  for (int p = 0; p < np; ++p) {
+    const double s = std::sqrt(1.0 - mu[p] * mu[p]);
+    for (int a = 0; a < na; ++a) {
+      const double ph = (a + 0.5) * 2.0 * kPi / na;
+      const int k = p * na + a;
+      h->ox[k] = s * std::cos(ph);
+      h->oy[k] = s * std::sin(ph);
+      h->oz[k] = mu[p];
+      h->w[k] = wp[p] * 2.0 * kPi / na;
+    }
+  }
+}
+
+// W0: monomials Om_x^a Om_y^b by total degree (a descending), then the same
+// times Om_z, orthonormalised in sum_k w_k (two modified Gram-Schmidt
+// passes, candidates with < 1e-8 surviving are skipped).  Returns false if
+// fewer than r independent candidates exist.
+static bool build_W0(const dlr_handle *h, std::vector<double> &W) {
+  const int K = h->K, r = h->r;
+  W.assign((size_t)K * r, 0.0);
+  std::vector<double> v(K);
+  int cnt = 0;
+  for (int e = 0; e <= 1 && cnt < r; ++e)
+    for (int d = 0; d <= 12 && cnt < r; ++d)
+      for (int a = d; a >= 0 && cnt < r; --a) {
+        const int b = d - a;
+        double n0 = 0.0;
+        for (int k = 0; k < K; ++k) {
+          v[k] = std::pow(h->ox[k], a) * std::pow(h->oy[k], b) * (e ? h->oz[k] : 1.0);
+          n0 += h->w[k] * v[k] * v[k];
+        }
+        n0 = std::sqrt(n0);
+        if (n0 == 0.0) continue;
+        for (int pass = 0; pass < 2; ++pass)
+          for (int l = 0; l < cnt; ++l) {
+            double dd = 0.0;
+            for (int k = 0; k < K; ++k) dd += h->w[k] * W[k + (size_t)K * l] * v[k];
+            for (int k = 0; k < K; ++k) v[k] -= dd * W[k + (size_t)K * l];
+          }
+        double n1 = 0.0;
+        for (int k = 0; k < K; ++k) n1 += h->w[k] * v[k] * v[k];
+        n1 = std::sqrt(n1);
+        if (n1 > 1e-8 * n0) {
+          for (int k = 0; k < K; ++k) W[k + (size_t)K * cnt] = v[k] / n1;
+          ++cnt;
+        }
+      }
+  return cnt == r;
+}
+
+// X0: first column f / |f| with f = B(T0) (the only column that carries
+// psi0, since S0 = diag(s0, 0, ...)); the others are the DCT modes
+// cos(pi k x^) cos(pi l y^), (k, l) != (0, 0) in (k + l, k) order, reflected
+// by the Householder map that swaps the constant mode and f / |f|, which
+// keeps them orthonormal and orthogonal to f.  All in the h^2 inner product.
+static bool build_X0(const dlr_handle *h, const double *T0, std::vector<double> &X, double &fn) {
+  const int nx = h->prob.nx, ny = h->prob.ny, N = h->N, r = h->r;
+  const double hx = h->prob.lx / nx, hy = h->prob.ly / ny, h2 = hx * hy;
+  X.assign((size_t)N * r, 0.0);
+  std::vector<double> f(N), u(N, 1.0 / std::sqrt(h->prob.lx * h->prob.ly)), v(N);
+  fn = 0.0;
+  for (int c = 0; c < N; ++c) {
+    f[c] = h->prob.a_rad * h->prob.c * std::pow(T0[c], 4) / (4.0 * kPi);
+    fn += h2 * f[c] * f[c];
+  }
+  fn = std::sqrt(fn);
+  std::vector<double> fh(N);
+  for (int c = 0; c < N; ++c) fh[c] = fn > 0 ? f[c] / fn : u[c];
+  double vv = 0.0;
+  for (int c = 0; c < N; ++c) {
+    v[c] = u[c] - fh[c];
+    vv += h2 * v[c] * v[c];
+  }
+  auto reflect = [&](std::vector<double> &m) {
+    if (vv <= 0.0) return;
+    double d = 0.0;
+    for (int c = 0; c < N; ++c) d += h2 * v[c] * m[c];
+    for (int c = 0; c < N; ++c) m[c] -= 2.0 * d / vv * v[c];
+  };
+  for (int c = 0; c < N; ++c) X[c] = fh[c];
+  int cnt = 1;
+  std::vector<double> m(N);
+  for (int d = 1; d <= nx + ny - 2 && cnt < r; ++d)
+    for (int k = 0; k <= d && cnt < r; ++k) {
+      const int l = d - k;
+      if (k >= nx || l >= ny) continue;
+      const double ck = std::sqrt((k == 0 ? 1.0 : 2.0) / h->prob.lx);
+      const double cl = std::sqrt((l == 0 ? 1.0 : 2.0) / h->prob.ly);
+      for (int iy = 0; iy < ny; ++iy)
+        for (int ix = 0; ix < nx; ++ix)
+          m[iy * nx + ix] = ck * cl * std::cos(kPi * k * (ix + 0.5) / nx) *
+                            std::cos(kPi * l * (iy + 0.5) / ny);
+      reflect(m);
+      for (int c = 0; c < N; ++c) X[c + (size_t)N * cnt] = m[c];
+      ++cnt;
+    }
+  return cnt == r;
+}
+
+// ------------------------------------------------------------------
+// footprint
+// ------------------------------------------------------------------
+struct Sizes {
+  int N, K, r, pb, pbl, lb;
+  size_t rs;
+  size_t partial_doubles;
+  size_t total;
+};
+
+static int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+      sms = 152;
+  }
+  return sms;
+}
+
+static Sizes sizes_of(const dlr_problem *p, int sms) {
+  Sizes s;
+  s.N = p->nx * p->ny;
+  s.K = p->n_polar * p->n_azim;
+  s.r = p->rank;
+  s.rs = p->precision == DLR_MIXED ? 4 : 8;
+  s.pb = std::max(1, std::min(2 * sms, (s.N + 2047) / 2048));
+  s.pbl = std::max(1, std::min(64, (s.K + 511) / 512));
+  s.lb = std::max(1, std::min(2 * sms, (s.K + 31) / 32));
+  const size_t r = s.r;
+  s.partial_doubles = std::max({(size_t)s.pb * proj_count(s.r), (size_t)s.pb * r * r,
+                                (size_t)s.pbl * r * r, (size_t)s.lb * (r * r + r)});
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  size_t t = 0;
+  t += 5 * al((size_t)s.N * 8);                 // sigma, rho_cv, T, B0, D
+  t += 6 * al((size_t)s.N * s.rs);              // sig_t, ss4, q, phi0, phi1, sphi
+  t += 4 * al((size_t)s.N * r * s.rs);          // X0, X, Psi, s0
+  t += 3 * al((size_t)s.K * 8);                 // ox, oy, w
+  t += 2 * al((size_t)s.K * r * 8);             // W0, L
+  t += al(r * r * 8) + al(r * 4);               // S0, idx
+  t += al((size_t)small_layout(s.r).total * 8); // small
+  t += al((size_t)s.K * r * r * 8) + al((size_t)s.K * r * 4);  // lu, piv
+  t += al(s.partial_doubles * 8);
+  t += al(64) * 4 + al(sizeof(Inst));           // status, iters, conv, totals, inst
+  s.total = t;
+  return s;
+}
+
+size_t dlr_footprint_bytes(const dlr_problem *p) {
+  if (!p || p->nx < 1 || p->ny < 1 || p->rank < 1 || p->n_polar < 1 || p->n_azim < 1) return 0;
+  return sizes_of(p, num_sms()).total;
+}
+
+const char *dlr_last_error(void) { return g_err.c_str(); }
+
+// ------------------------------------------------------------------
+// create / destroy
+// ------------------------------------------------------------------
+static int validate(const dlr_problem *p) {
+  if (!p) return fail(DLR_EINVAL, "problem is NULL");
+  if (p->nx < 1 || p->ny < 1) return fail(DLR_EINVAL, "nx, ny must be >= 1");
+  if (!(p->lx > 0) || !(p->ly > 0)) return fail(DLR_EINVAL, "lx, ly must be > 0");
+  if (p->n_polar < 1 || p->n_azim < 1) return fail(DLR_EINVAL, "n_polar, n_azim must be >= 1");
+  const long long N = (long long)p->nx * p->ny, K = (long long)p->n_polar * p->n_azim;
+  if (N > (1ll << 30) || K > 8192) return fail(DLR_EINVAL, "mesh or quadrature too large");
+  if (p->rank < 1 || p->rank > kMaxRank || p->rank > N || p->rank > K)
+    return fail(DLR_EINVAL, "rank must satisfy 1 <= r <= min(%d, nx*ny, NOm)", kMaxRank);
+  if (!(p->dt > 0) || !(p->c > 0) || !(p->a_rad >= 0)) return fail(DLR_EINVAL, "dt, c must be > 0, a_rad >= 0");
+  if (p->precision != DLR_FP64 && p->precision != DLR_MIXED) return fail(DLR_EINVAL, "bad precision");
+  if (p->selection != DLR_SEL_QDEIM && p->selection != DLR_SEL_DEIM) return fail(DLR_EINVAL, "bad selection");
+  if (p->augment != 0) return fail(DLR_EINVAL, "augment must be 0");
+  if (!p->sigma || !p->rho_cv || !p->T0) return fail(DLR_EINVAL, "sigma, rho_cv, T0 must be given");
+  for (long long c = 0; c < N; ++c) {
+    if (!(p->sigma[c] >= 0) || !std::isfinite(p->sigma[c])) return fail(DLR_EINVAL, "sigma[%lld] invalid", c);
+    if (!(p->rho_cv[c] > 0) || !std::isfinite(p->rho_cv[c])) return fail(DLR_EINVAL, "rho_cv[%lld] invalid", c);
+    if (!(p->T0[c] > 0) || !std::isfinite(p->T0[c])) return fail(DLR_EINVAL, "T0[%lld] invalid", c);
+  }
+  // shared memory of the sweep for this mesh
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const size_t need = p->precision == DLR_MIXED ? si_smem_bytes<float>(p->nx, (p->ny + 31) / 32, 256)
+                                                : si_smem_bytes<double>(p->nx, (p->ny + 31) / 32, 256);
+  if (optin > 0 && need > (size_t)optin) return fail(DLR_EINVAL, "nx = %d too large for the sweep's shared memory", p->nx);
+  return DLR_OK;
+}
+
+static double planck(double a, double c, double T) { return a * c * T * T * T * T / (4.0 * kPi); }
+
+static void destroy_batch(Batch *b);
+static void purge_batches(dlr_handle *h);
+
+int dlr_create(const dlr_problem *problem, const dlr_runtime *runtime, dlr_handle **out) {
+  if (!out) return fail(DLR_EINVAL, "out is NULL");
+  *out = nullptr;
+  int rc = validate(problem);
+  if (rc) return rc;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(DLR_ECUDA, "no CUDA device");
+  {
+    // the kernels are built for sm_103a only: fail loudly on anything else
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, k_widen);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(DLR_ECUDA, "kernels cannot run on this GPU: %s", cudaGetErrorString(e));
+    }
+  }
+  dlr_handle *h = new dlr_handle();
+  h->prob = *problem;
+  h->prob.sigma = h->prob.rho_cv = h->prob.T0 = nullptr;
+  h->mixed = problem->precision == DLR_MIXED;
+  h->rs = h->mixed ? 4 : 8;
+  h->N = problem->nx * problem->ny;
+  h->K = problem->n_polar * problem->n_azim;
+  h->r = problem->rank;
+  if (runtime) h->rt = *runtime;
+  h->st = (cudaStream_t)h->rt.stream;
+  if (!h->st) {  // graphs cannot be captured on the legacy stream
+    if (cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking) != cudaSuccess) {
+      delete h;
+      return fail(DLR_ECUDA, "stream creation failed");
+    }
+    h->own_stream = true;
+  }
+  const Sizes sz = sizes_of(problem, num_sms());
+  if (h->rt.hbm_budget && sz.total > h->rt.hbm_budget) {
+    if (h->own_stream) cudaStreamDestroy(h->st);
+    delete h;
+    return fail(DLR_ENOMEM, "footprint %zu bytes exceeds the HBM budget %zu", sz.total, h->rt.hbm_budget);
+  }
+  h->pb = sz.pb;
+  h->pbl = sz.pbl;
+  h->lb = sz.lb;
+  build_quadrature(h);
+  std::vector<double> X0, W0;
+  double fn = 0.0;
+  if (!build_W0(h, W0) || !build_X0(h, problem->T0, X0, fn)) {
+    delete h;
+    return fail(DLR_EINVAL, "rank %d exceeds the independent initial basis functions", h->r);
+  }
+  const int N = h->N, K = h->K, r = h->r;
+  const size_t rs = h->rs;
+  Inst &I = h->inst;
+  I.nx = problem->nx;
+  I.ny = problem->ny;
+  I.N = N;
+  I.r = r;
+  I.K = K;
+  I.precision = problem->precision;
+  I.selection = problem->selection;
+  I.fixed_iters = problem->si_fixed_iters > 0 ? problem->si_fixed_iters : 0;
+  I.max_iter = problem->si_max_iter > 0 ? problem->si_max_iter : 1000;
+  I.hx = problem->lx / problem->nx;
+  I.hy = problem->ly / problem->ny;
+  I.h2 = I.hx * I.hy;
+  I.dt = problem->dt;
+  I.c = problem->c;
+  I.a_rad = problem->a_rad;
+  I.inv_cdt = 1.0 / (problem->c * problem->dt);
+  I.si_tol = problem->si_tol > 0 ? problem->si_tol : (h->mixed ? 1e-7 : 1e-13);
+  for (int e = 0; e < 4; ++e)
+    I.psi_edge[e] = problem->T_edge[e] >= 0 ? planck(problem->a_rad, problem->c, problem->T_edge[e]) : 0.0;
+  I.lay = small_layout(r);
+  bool ok = true;
+  auto A = [&](size_t bytes) {
+    void *p = dev_alloc(h, bytes);
+    ok = ok && p;
+    return p;
+  };
+  double *sigma = (double *)A((size_t)N * 8);
+  double *rho = (double *)A((size_t)N * 8);
+  I.T = (double *)A((size_t)N * 8);
+  I.B0 = (double *)A((size_t)N * 8);
+  I.D = (double *)A((size_t)N * 8);
+  I.sigma = sigma;
+  I.rho_cv = rho;
+  I.sig_t = A((size_t)N * rs);
+  I.ss4 = A((size_t)N * rs);
+  I.q = A((size_t)N * rs);
+  I.phi0 = A((size_t)N * rs);
+  I.phi1 = A((size_t)N * rs);
+  I.sphi = A((size_t)N * rs);
+  I.X0 = A((size_t)N * r * rs);
+  I.X = A((size_t)N * r * rs);
+  I.Psi = A((size_t)N * r * rs);
+  I.s0 = A((size_t)N * r * rs);
+  double *dox = (double *)A((size_t)K * 8), *doy = (double *)A((size_t)K * 8), *dw = (double *)A((size_t)K * 8);
+  I.ox = dox;
+  I.oy = doy;
+  I.w = dw;
+  I.W0 = (double *)A((size_t)K * r * 8);
+  I.L = (double *)A((size_t)K * r * 8);
+  I.S0 = (double *)A((size_t)r * r * 8);
+  I.idx = (int *)A((size_t)r * 4);
+  I.small = (double *)A((size_t)I.lay.total * 8);
+  I.lu = (double *)A((size_t)K * r * r * 8);
+  I.piv = (int *)A((size_t)K * r * 4);
+  I.partials = (double *)A(sz.partial_doubles * 8);
+  I.partial_blocks = h->pb;
+  I.lstep_blocks = h->lb;
+  I.status = (int *)A(64);
+  I.iters = (int *)A(64);
+  I.conv = (unsigned long long *)A(64);
+  h->d_iters_total = (long long *)A(64);
+  I.iters_total = (unsigned long long *)h->d_iters_total;
+  if (!ok) {
+    dev_free_all(h);
+    delete h;
+    return fail(DLR_ENOMEM, "device allocation failed");
+  }
+  if (cudaMallocHost(&h->h_status, sizeof(int)) != cudaSuccess) {
+    dev_free_all(h);
+    delete h;
+    return fail(DLR_ENOMEM, "pinned allocation failed");
+  }
+  *h->h_status = 0;
+  // host -> device
+  std::vector<double> S0(r * r, 0.0);
+  S0[0] = fn * std::sqrt(4.0 * kPi);
+  auto up = [&](void *dst, const void *src, size_t bytes) {
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, h->st);
+  };
+  cudaError_t e = cudaSuccess;
+  auto chain = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+  chain(up(sigma, problem->sigma, (size_t)N * 8));
+  chain(up(rho, problem->rho_cv, (size_t)N * 8));
+  chain(up(I.T, problem->T0, (size_t)N * 8));
+  chain(up(dox, h->ox.data(), (size_t)K * 8));
+  chain(up(doy, h->oy.data(), (size_t)K * 8));
+  chain(up(dw, h->w.data(), (size_t)K * 8));
+  chain(up(I.W0, W0.data(), (size_t)K * r * 8));
+  chain(up(I.S0, S0.data(), (size_t)r * r * 8));
+  if (h->mixed) {
+    std::vector<float> Xf(X0.begin(), X0.end());
+    chain(up(I.X0, Xf.data(), Xf.size() * 4));
+  } else {
+    chain(up(I.X0, X0.data(), X0.size() * 8));
+  }
+  chain(cudaMemsetAsync(I.status, 0, 64, h->st));
+  chain(cudaMemsetAsync(I.iters, 0, 64, h->st));
+  chain(cudaMemsetAsync(h->d_iters_total, 0, 64, h->st));
+  chain(cudaMemsetAsync(I.idx, 0xff, (size_t)r * 4, h->st));
+  chain(cudaMemsetAsync(I.small, 0, (size_t)I.lay.total * 8, h->st));
+  // the host vectors above are released on return: wait for the copies
+  chain(cudaStreamSynchronize(h->st));
+  if (e != cudaSuccess) {
+    std::string msg = cudaGetErrorString(e);
+    cudaFreeHost(h->h_status);
+    dev_free_all(h);
+    if (h->own_stream) cudaStreamDestroy(h->st);
+    delete h;
+    return fail(DLR_ECUDA, "upload failed: %s", msg.c_str());
+  }
+  *out = h;
+  return DLR_OK;
+}
+
+void dlr_destroy(dlr_handle *h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->st);
+  purge_batches(h);
+  if (h->own_batch) destroy_batch(h->own_batch);
+  for (auto &p : h->ev_pending)
+    for (auto ev : p) cudaEventDestroy(ev);
+  for (auto ev : h->ev_pool) cudaEventDestroy(ev);
+  if (h->h_status) cudaFreeHost(h->h_status);
+  dev_free_all(h);
+  if (h->own_stream) cudaStreamDestroy(h->st);
+  delete h;
+}
+
+// ------------------------------------------------------------------
+// batch plans
+// ------------------------------------------------------------------
+static void destroy_batch(Batch *b) {
+  if (!b) return;
+  if (b->pre) cudaGraphExecDestroy(b->pre);
+  if (b->post) cudaGraphExecDestroy(b->post);
+  if (b->d_mem) cudaFree(b->d_mem);
+  delete b;
+}
+
+template <typename T>
+static T *carve(char *&cur, size_t count) {
+  T *p = reinterpret_cast<T *>(cur);
+  cur += (count * sizeof(T) + 255) & ~size_t(255);
+  return p;
+}
+
+static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
+  Batch *b = new Batch();
+  b->hs.assign(hs, hs + n);
+  for (int i = 0; i < n; ++i) b->versions.push_back(hs[i]->version);
+  b->n = n;
+  b->mixed = hs[0]->mixed;
+  b->st = hs[0]->st;
+  for (int i = 0; i < n; ++i) {
+    const dlr_handle *h = hs[i];
+    b->maxN = std::max(b->maxN, h->N);
+    b->maxK = std::max(b->maxK, h->K);
+    b->rmax = std::max(b->rmax, h->r);
+    b->pbmax = std::max(b->pbmax, h->pb);
+    b->pblmax = std::max(b->pblmax, h->pbl);
+    b->lbmax = std::max(b->lbmax, h->lb);
+    b->nx_max = std::max(b->nx_max, h->prob.nx);
+    b->bands_max = std::max(b->bands_max, (h->prob.ny + 31) / 32);
+  }
+  // units: (instance, angle), instances with the most cells first
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return hs[a]->N > hs[c]->N; });
+  std::vector<int2> units;
+  for (int i : order)
+    for (int j = 0; j < hs[i]->r; ++j) units.push_back(make_int2(i, j));
+  // one device block for the batch's tables
+  size_t bytes = 0;
+  auto sz = [](size_t s) { return (s + 255) & ~size_t(255); };
+  bytes += sz(sizeof(Inst) * n);
+  bytes += 4 * sz(sizeof(GramJob) * n) + 7 * sz(sizeof(ApplyJob) * n) + 6 * sz(sizeof(CholJob) * n) +
+           sz(sizeof(ReduceJob) * n);
+  bytes += sz(sizeof(int2) * units.size()) + sz(64) * 3;
+  if (cudaMalloc(&b->d_mem, bytes) != cudaSuccess) {
+    delete b;
+    return fail(DLR_ENOMEM, "batch table allocation failed");
+  }
+  char *cur = (char *)b->d_mem;
+  b->d_insts = carve<Inst>(cur, n);
+  b->g_psi1 = carve<GramJob>(cur, n);
+  b->g_x = carve<GramJob>(cur, n);
+  b->g_l1 = carve<GramJob>(cur, n);
+  b->g_w = carve<GramJob>(cur, n);
+  b->a_psi = carve<ApplyJob>(cur, n);
+  b->a_x2 = carve<ApplyJob>(cur, n);
+  b->a_x3 = carve<ApplyJob>(cur, n);
+  b->a_l1 = carve<ApplyJob>(cur, n);
+  b->a_w2 = carve<ApplyJob>(cur, n);
+  b->a_w3 = carve<ApplyJob>(cur, n);
+  b->a_wv = carve<ApplyJob>(cur, n);
+  b->c_p1 = carve<CholJob>(cur, n);
+  b->c_p2 = carve<CholJob>(cur, n);
+  b->c_p3 = carve<CholJob>(cur, n);
+  b->c_l1 = carve<CholJob>(cur, n);
+  b->c_l2 = carve<CholJob>(cur, n);
+  b->c_l3 = carve<CholJob>(cur, n);
+  b->r_proj = carve<ReduceJob>(cur, n);
+  int2 *d_units = carve<int2>(cur, units.size());
+  b->ctl.bar = carve<unsigned>(cur, 16);
+  b->ctl.work = carve<unsigned>(cur, 16);
+  b->ctl.abort_flag = carve<int>(cur, 16);
+  b->ctl.units = d_units;
+  b->ctl.n_units = (int)units.size();
+  b->ctl.n_inst = n;
+  b->ctl.nx_max = b->nx_max;
+  b->ctl.bands_max = b->bands_max;
+  // host copies of the job tables
+  std::vector<Inst> insts(n);
+  std::vector<GramJob> gp1(n), gx(n), gl1(n), gw(n);
+  std::vector<ApplyJob> ap(n), ax2(n), ax3(n), al1(n), aw2(n), aw3(n), awv(n);
+  std::vector<CholJob> cp1(n), cp2(n), cp3(n), cl1(n), cl2(n), cl3(n);
+  std::vector<ReduceJob> rp(n);
+  for (int i = 0; i < n; ++i) {
+    const dlr_handle *h = hs[i];
+    const Inst &I = h->inst;
+    insts[i] = I;
+    const int N = h->N, K = h->K, r = h->r;
+    double *sm = I.small;
+    const SmallLayout &L = I.lay;
+    int *flag = reinterpret_cast<int *>(sm + L.qr_flag);
+    auto gram = [&](const void *A, const double *wt, int m, int lda, int layout, int nb, const int *run_if) {
+      GramJob g{};
+      g.A = A; g.wt = wt; g.m = m; g.r = r; g.lda = lda; g.layout = layout;
+      g.out = I.partials; g.nblocks = nb; g.run_if = run_if;
+      return g;
+    };
+    gp1[i] = gram(I.Psi, nullptr, N, N, 0, h->pb, nullptr);
+    gx[i] = gram(I.X, nullptr, N, N, 0, h->pb, nullptr);
+    gl1[i] = gram(I.L, I.w, K, r, 1, h->pbl, nullptr);
+    gw[i] = gram(I.W0, nullptr, K, K, 0, h->pbl, nullptr);
+    auto apply = [&](const void *A, int layout, int lda, const double *s_in, int sq_in, const double *T,
+                     void *outp, int ldo, const double *s_out, int inv_sq, int m, const int *run_if) {
+      ApplyJob a{};
+      a.A = A; a.in_layout = layout; a.lda = lda; a.s_in = s_in; a.sq_in = sq_in; a.T = T;
+      a.out = outp; a.ldo = ldo; a.s_out = s_out; a.inv_sq_out = inv_sq; a.m = m; a.r = r;
+      a.run_if = run_if;
+      return a;
+    };
+    ap[i] = apply(I.Psi, 0, N, nullptr, 0, sm + L.R1i, I.X, N, nullptr, 0, N, nullptr);
+    ax2[i] = apply(I.X, 0, N, nullptr, 0, sm + L.R2i, I.X, N, nullptr, 0, N, nullptr);
+    ax3[i] = apply(I.X, 0, N, nullptr, 0, sm + L.R3i, I.X, N, nullptr, 0, N, flag);
+    al1[i] = apply(I.L, 1, r, I.w, 1, sm + L.R1i, I.W0, K, nullptr, 0, K, nullptr);
+    aw2[i] = apply(I.W0, 0, K, nullptr, 0, sm + L.R2i, I.W0, K, nullptr, 0, K, nullptr);
+    aw3[i] = apply(I.W0, 0, K, nullptr, 0, sm + L.R3i, I.W0, K, nullptr, 0, K, flag);
+    awv[i] = apply(I.W0, 0, K, nullptr, 0, sm + L.V, I.W0, K, I.w, 1, K, nullptr);
+    auto chol = [&](int nb, double scale, double *R, double *Ri, int pass, double m) {
+      CholJob c{};
+      c.part = I.partials; c.nblocks = nb; c.scale = scale; c.R = R; c.Ri = Ri;
+      c.flag = flag; c.r = r; c.pass = pass; c.m_rows = m;
+      return c;
+    };
+    cp1[i] = chol(h->pb, I.h2, sm + L.R1, sm + L.R1i, 1, N);
+    cp2[i] = chol(h->pb, I.h2, sm + L.R2, sm + L.R2i, 2, N);
+    cp3[i] = chol(h->pb, I.h2, sm + L.R3, sm + L.R3i, 3, N);
+    cl1[i] = chol(h->pbl, 1.0, sm + L.R1, sm + L.R1i, 1, K);
+    cl2[i] = chol(h->pbl, 1.0, sm + L.R2, sm + L.R2i, 2, K);
+    cl3[i] = chol(h->pbl, 1.0, sm + L.R3, sm + L.R3i, 3, K);
+    ReduceJob red{};
+    red.part = I.partials; red.nblocks = h->pb; red.stride = proj_count(r);
+    red.count = proj_count(r); red.out = sm + L.G; red.scale = 1.0;
+    rp[i] = red;
+  }
+  auto upv = [&](void *dst, const void *src, size_t bytes) {
+    return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+  };
+  cudaError_t e = cudaSuccess;
+  auto chain = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+  cudaStreamSynchronize(b->st);
+  chain(upv(b->d_insts, insts.data(), sizeof(Inst) * n));
+  chain(upv(b->g_psi1, gp1.data(), sizeof(GramJob) * n));
+  chain(upv(b->g_x, gx.data(), sizeof(GramJob) * n));
+  chain(upv(b->g_l1, gl1.data(), sizeof(GramJob) * n));
+  chain(upv(b->g_w, gw.data(), sizeof(GramJob) * n));
+  chain(upv(b->a_psi, ap.data(), sizeof(ApplyJob) * n));
+  chain(upv(b->a_x2, ax2.data(), sizeof(ApplyJob) * n));
+  chain(upv(b->a_x3, ax3.data(), sizeof(ApplyJob) * n));
+  chain(upv(b->a_l1, al1.data(), sizeof(ApplyJob) * n));
+  chain(upv(b->a_w2, aw2.data(), sizeof(ApplyJob) * n));
+  chain(upv(b->a_w3, aw3.data(), sizeof(ApplyJob) * n));
+  chain(upv(b->a_wv, awv.data(), sizeof(ApplyJob) * n));
+  chain(upv(b->c_p1, cp1.data(), sizeof(CholJob) * n));
+  chain(upv(b->c_p2, cp2.data(), sizeof(CholJob) * n));
+  chain(upv(b->c_p3, cp3.data(), sizeof(CholJob) * n));
+  chain(upv(b->c_l1, cl1.data(), sizeof(CholJob) * n));
+  chain(upv(b->c_l2, cl2.data(), sizeof(CholJob) * n));
+  chain(upv(b->c_l3, cl3.data(), sizeof(CholJob) * n));
+  chain(upv(b->r_proj, rp.data(), sizeof(ReduceJob) * n));
+  chain(upv(d_units, units.data(), sizeof(int2) * units.size()));
+  if (e != cudaSuccess) {
+    destroy_batch(b);
+    return fail(DLR_ECUDA, "batch table upload failed: %s", cudaGetErrorString(e));
+  }
+  const int gmax = b->mixed ? si_max_grid<float>(b->nx_max, b->bands_max, n)
+                            : si_max_grid<double>(b->nx_max, b->bands_max, n);
+  if (gmax <= 0) {
+    destroy_batch(b);
+    return fail(DLR_ECUDA, "the source-iteration kernel does not fit on this GPU");
+  }
+  b->si_grid = gmax;
+  if ((e = prepare_small(b->maxK, b->rmax)) != cudaSuccess) {
+    destroy_batch(b);
+    return fail(DLR_ECUDA, "kernel attribute setup failed: %s", cudaGetErrorString(e));
+  }
+  *out = b;
+  return DLR_OK;
+}
+
+// refresh the batch's instance copies of handles changed since the upload
+// (pageable sources are consumed before cudaMemcpyAsync returns)
+static int refresh_batch(Batch *b) {
+  for (int i = 0; i < b->n; ++i)
+    if (b->versions[i] != b->hs[i]->version) {
+      CK(cudaMemcpyAsync(b->d_insts + i, &b->hs[i]->inst, sizeof(Inst), cudaMemcpyHostToDevice, b->st));
+      b->versions[i] = b->hs[i]->version;
+    }
+  return DLR_OK;
+}
+
+template <typename real>
+static int enqueue_pre(Batch *b) {
+  const Inst *d = b->d_insts;
+  const int n = b->n;
+  CK(launch_select(d, n, b->maxK, b->st));
+  CK(launch_coeff_recon<real>(d, n, b->maxN, b->rmax, b->st));
+  CK(launch_si_prep(d, n, b->ctl, b->st));
+  return DLR_OK;
+}
+
+template <typename real>
+static int enqueue_post(Batch *b) {
+  const Inst *d = b->d_insts;
+  const int n = b->n;
+  cudaStream_t st = b->st;
+  // step 5: CholeskyQR of Psi (two passes, a third when pass 1 was shifted)
+  CK(launch_tsgram<real>(b->g_psi1, n, b->pbmax, st));
+  CK(launch_chol(b->c_p1, d, n, st));
+  CK((launch_apply<real, real>(b->a_psi, n, b->maxN, b->rmax, st)));
+  CK(launch_tsgram<real>(b->g_x, n, b->pbmax, st));
+  CK(launch_chol(b->c_p2, d, n, st));
+  CK((launch_apply<real, real>(b->a_x2, n, b->maxN, b->rmax, st)));
+  CK(launch_tsgram<real>(b->g_x, n, b->pbmax, st));
+  CK(launch_chol(b->c_p3, d, n, st));
+  CK((launch_apply<real, real>(b->a_x3, n, b->maxN, b->rmax, st)));
+  // steps 6-7: projections and the L-step
+  CK(launch_project<real>(d, n, b->pbmax, st));
+  CK(launch_reduce(b->r_proj, n, proj_count(b->rmax), st));
+  CK(launch_proj_post(d, n, st));
+  CK(launch_lstep(d, n, b->rmax, b->lbmax, st));
+  // step 8: CholeskyQR of diag(sqrt w) L^T into W0, SVD of S, W0 <- W V
+  CK(launch_tsgram<double>(b->g_l1, n, b->pblmax, st));
+  CK(launch_chol(b->c_l1, d, n, st));
+  CK((launch_apply<double, double>(b->a_l1, n, b->maxK, b->rmax, st)));
+  CK(launch_tsgram<double>(b->g_w, n, b->pblmax, st));
+  CK(launch_chol(b->c_l2, d, n, st));
+  CK((launch_apply<double, double>(b->a_w2, n, b->maxK, b->rmax, st)));
+  CK(launch_tsgram<double>(b->g_w, n, b->pblmax, st));
+  CK(launch_chol(b->c_l3, d, n, st));
+  CK((launch_apply<double, double>(b->a_w3, n, b->maxK, b->rmax, st)));
+  CK(launch_svd(d, n, st));
+  CK((launch_apply<double, double>(b->a_wv, n, b->maxK, b->rmax, st)));
+  CK(launch_sign(d, n, b->maxK, st));
+  // step 9
+  CK(launch_tupdate<real>(d, n, b->maxN, b->rmax, st));
+  return DLR_OK;
+}
+
+static int capture(Batch *b, bool pre, cudaGraphExec_t *exec) {
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+  int rc = pre ? (b->mixed ? enqueue_pre<float>(b) : enqueue_pre<double>(b))
+               : (b->mixed ? enqueue_post<float>(b) : enqueue_post<double>(b));
+  cudaError_t e = cudaStreamEndCapture(b->st, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(DLR_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(DLR_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+  return DLR_OK;
+}
+
+static cudaEvent_t pool_event(dlr_handle *h) {
+  if (!h->ev_pool.empty()) {
+    cudaEvent_t e = h->ev_pool.back();
+    h->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+static int run_steps(Batch *b, int nsteps) {
+  int rc = refresh_batch(b);
+  if (rc) return rc;
+  if (!b->pre && (rc = capture(b, true, &b->pre))) return rc;
+  if (!b->post && (rc = capture(b, false, &b->post))) return rc;
+  dlr_handle *h0 = b->hs[0];
+  for (int s = 0; s < nsteps; ++s) {
+    std::array<cudaEvent_t, 4> ev{};
+    const bool timing = h0->timing && b->n == 1;
+    if (timing) {
+      for (auto &x : ev) x = pool_event(h0);
+      CK(cudaEventRecord(ev[0], b->st));
+    }
+    CK(cudaGraphLaunch(b->pre, b->st));
+    if (timing) CK(cudaEventRecord(ev[1], b->st));
+    CK(b->mixed ? launch_si<float>(b->d_insts, b->ctl, b->si_grid, b->st)
+                : launch_si<double>(b->d_insts, b->ctl, b->si_grid, b->st));
+    if (timing) CK(cudaEventRecord(ev[2], b->st));
+    CK(cudaGraphLaunch(b->post, b->st));
+    if (timing) {
+      CK(cudaEventRecord(ev[3], b->st));
+      h0->ev_pending.push_back(ev);
+    }
+  }
+  for (auto *h : b->hs) {
+    h->steps += nsteps;
+    CK(cudaMemcpyAsync(h->h_status, h->inst.status, sizeof(int), cudaMemcpyDeviceToHost, b->st));
+  }
+  return DLR_OK;
+}
+
+int dlr_step(dlr_handle *h, int32_t nsteps) {
+  if (!h) return fail(DLR_EINVAL, "handle is NULL");
+  return dlr_step_batch(&h, 1, nsteps);
+}
+
+static std::map<std::vector<dlr_handle *>, Batch *> &batch_cache() {
+  static std::map<std::vector<dlr_handle *>, Batch *> m;
+  return m;
+}
+
+static void purge_batches(dlr_handle *h) {
+  auto &m = batch_cache();
+  for (auto it = m.begin(); it != m.end();) {
+    if (std::find(it->first.begin(), it->first.end(), h) != it->first.end()) {
+      destroy_batch(it->second);
+      it = m.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
+int dlr_step_batch(dlr_handle *const *hs, int32_t n, int32_t nsteps) {
+  if (!hs || n < 1) return fail(DLR_EINVAL, "no handles");
+  if (nsteps < 0) return fail(DLR_EINVAL, "nsteps < 0");
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i]) return fail(DLR_EINVAL, "handle %d is NULL", i);
+    if (hs[i]->mixed != hs[0]->mixed) return fail(DLR_EINVAL, "mixed precisions in one batch");
+    if (hs[i]->st != hs[0]->st) return fail(DLR_EINVAL, "handles on different streams");
+    const int s = *hs[i]->h_status;
+    if (s != DLR_OK) return fail(s, "handle %d: %s", i, status_name(s));
+  }
+  if (nsteps == 0) return DLR_OK;
+  Batch *b = nullptr;
+  int rc;
+  if (n == 1) {
+    if (!hs[0]->own_batch && (rc = build_batch(hs, 1, &hs[0]->own_batch))) return rc;
+    b = hs[0]->own_batch;
+  } else {
+    std::vector<dlr_handle *> key(hs, hs + n);
+    auto &m = batch_cache();
+    auto it = m.find(key);
+    if (it == m.end()) {
+      if ((rc = build_batch(hs, n, &b))) return rc;
+      m[key] = b;
+    } else {
+      b = it->second;
+    }
+  }
+  return run_steps(b, nsteps);
+}
+
+// ------------------------------------------------------------------
+// getters / setters
+// ------------------------------------------------------------------
+static int sync_status(dlr_handle *h) {
+  CK(cudaStreamSynchronize(h->st));
+  int s = 0;
+  CK(cudaMemcpy(&s, h->inst.status, sizeof(int), cudaMemcpyDeviceToHost));
+  *h->h_status = s;
+  if (s != DLR_OK) return fail(s, "%s", status_name(s));
+  return DLR_OK;
+}
+
+int dlr_get_T(dlr_handle *h, double *out, int32_t out_on_device) {
+  if (!h || !out) return fail(DLR_EINVAL, "NULL argument");
+  CK(cudaMemcpyAsync(out, h->inst.T, (size_t)h->N * 8,
+                     out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
+  return sync_status(h);
+}
+
+int dlr_set_T(dlr_handle *h, const double *in, int32_t in_on_device) {
+  if (!h || !in) return fail(DLR_EINVAL, "NULL argument");
+  CK(cudaMemcpyAsync(h->inst.T, in, (size_t)h->N * 8,
+                     in_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+  return DLR_OK;
+}
+
+int dlr_get_factors(dlr_handle *h, double *X, double *S, double *W, int32_t *r_out, int32_t out_on_device) {
+  if (!h) return fail(DLR_EINVAL, "NULL handle");
+  const size_t nX = (size_t)h->N * h->r;
+  const cudaMemcpyKind k = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (r_out) *r_out = h->r;
+  if (X) {
+    if (!h->mixed) {
+      CK(cudaMemcpyAsync(X, h->inst.X0, nX * 8, k, h->st));
+    } else if (out_on_device) {
+      k_widen<<<1024, 256, 0, h->st>>>((const float *)h->inst.X0, X, nX);
+      CK(cudaGetLastError());
+    } else {
+      std::vector<float> tmp(nX);
+      CK(cudaMemcpyAsync(tmp.data(), h->inst.X0, nX * 4, cudaMemcpyDeviceToHost, h->st));
+      CK(cudaStreamSynchronize(h->st));
+      for (size_t i = 0; i < nX; ++i) X[i] = tmp[i];
+    }
+  }
+  if (S) CK(cudaMemcpyAsync(S, h->inst.S0, (size_t)h->r * h->r * 8, k, h->st));
+  if (W) CK(cudaMemcpyAsync(W, h->inst.W0, (size_t)h->K * h->r * 8, k, h->st));
+  return sync_status(h);
+}
+
+int dlr_set_factors(dlr_handle *h, const double *X, const double *S, const double *W, int32_t in_on_device) {
+  if (!h || !X || !S || !W) return fail(DLR_EINVAL, "NULL argument");
+  const size_t nX = (size_t)h->N * h->r;
+  const cudaMemcpyKind k = in_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (!h->mixed) {
+    CK(cudaMemcpyAsync(h->inst.X0, X, nX * 8, k, h->st));
+  } else if (in_on_device) {
+    k_narrow<<<1024, 256, 0, h->st>>>(X, (float *)h->inst.X0, nX);
+    CK(cudaGetLastError());
+  } else {
+    std::vector<float> tmp(X, X + nX);
+    CK(cudaMemcpyAsync(h->inst.X0, tmp.data(), nX * 4, cudaMemcpyHostToDevice, h->st));
+    CK(cudaStreamSynchronize(h->st));
+  }
+  CK(cudaMemcpyAsync(h->inst.S0, S, (size_t)h->r * h->r * 8, k, h->st));
+  CK(cudaMemcpyAsync(h->inst.W0, W, (size_t)h->K * h->r * 8, k, h->st));
+  if (!in_on_device) CK(cudaStreamSynchronize(h->st));
+  return DLR_OK;
+}
+
+int dlr_get_quadrature(dlr_handle *h, double *omega_xyz, double *w) {
+  if (!h) return fail(DLR_EINVAL, "NULL handle");
+  for (int k = 0; k < h->K; ++k) {
+    if (omega_xyz) {
+      omega_xyz[3 * k] = h->ox[k];
+      omega_xyz[3 * k + 1] = h->oy[k];
+      omega_xyz[3 * k + 2] = h->oz[k];
+    }
+    if (w) w[k] = h->w[k];
+  }
+  return DLR_OK;
+}
+
+int dlr_get_selected(dlr_handle *h, int32_t *idx) {
+  if (!h || !idx) return fail(DLR_EINVAL, "NULL argument");
+  CK(cudaMemcpyAsync(idx, h->inst.idx, (size_t)h->r * 4, cudaMemcpyDeviceToHost, h->st));
+  return sync_status(h);
+}
+
+int dlr_get_stats(dlr_handle *h, dlr_stats *out) {
+  if (!h || !out) return fail(DLR_EINVAL, "NULL argument");
+  CK(cudaStreamSynchronize(h->st));
+  long long tot = 0;
+  int last = 0, s = 0;
+  CK(cudaMemcpy(&tot, h->d_iters_total, sizeof tot, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&last, h->inst.iters, sizeof last, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&s, h->inst.status, sizeof s, cudaMemcpyDeviceToHost));
+  for (auto &ev : h->ev_pending) {
+    float a = 0, b2 = 0;
+    cudaEventElapsedTime(&a, ev[1], ev[2]);
+    cudaEventElapsedTime(&b2, ev[0], ev[3]);
+    h->ms_si += a;
+    h->ms_step += b2;
+    h->si_launches += 1;
+    for (auto e : ev) h->ev_pool.push_back(e);
+  }
+  h->ev_pending.clear();
+  out->steps = h->steps;
+  out->si_iters_total = tot;
+  out->cell_angle_updates = tot * (long long)h->N * h->r;
+  out->si_iters_last = last;
+  out->status = s;
+  out->ms_si_total = h->ms_si;
+  out->ms_step_total = h->ms_step;
+  out->si_launches = h->si_launches;
+  *h->h_status = s;
+  return DLR_OK;
+}
+
+int dlr_set_timing(dlr_handle *h, int32_t enable) {
+  if (!h) return fail(DLR_EINVAL, "NULL handle");
+  h->timing = enable != 0;
+  return DLR_OK;
+}
+
+int dlr_set_edge_inflow(dlr_handle *h, int32_t edge, double psi_iso) {
+  if (!h || edge < 0 || edge > 3 || !(psi_iso >= 0) || !std::isfinite(psi_iso))
+    return fail(DLR_EINVAL, "bad edge or inflow value");
+  h->inst.psi_edge[edge] = psi_iso;
+  ++h->version;
+  return DLR_OK;
+}
+
+int dlr_sweep(int32_t nx, int32_t ny, double lx, double ly, int32_t n_dir, const double *dirs,
+              const double *psi_edge, int32_t precision, const void *sigma_t, const void *src,
+              void *psi, void *stream) {
+  if (nx < 1 || ny < 1 || n_dir < 1 || !dirs || !psi_edge || !sigma_t || !src || !psi || !(lx > 0) ||
+      !(ly > 0) || (precision != DLR_FP64 && precision != DLR_MIXED))
+    return fail(DLR_EINVAL, "bad argument to dlr_sweep");
+  cudaStream_t st = (cudaStream_t)stream;
+  double *d_dirs = nullptr, *d_edge = nullptr;
+  int *d_abort = nullptr;
+  CK(cudaMallocAsync(&d_dirs, (size_t)n_dir * 2 * 8, st));
+  CK(cudaMallocAsync(&d_edge, 4 * 8, st));
+  CK(cudaMallocAsync(&d_abort, sizeof(int), st));
+  CK(cudaMemcpyAsync(d_dirs, dirs, (size_t)n_dir * 2 * 8, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_edge, psi_edge, 4 * 8, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(d_abort, 0, sizeof(int), st));
+  const double hx = lx / nx, hy = ly / ny;
+  cudaError_t e = precision == DLR_MIXED
+                      ? launch_sweep_dirs<float>(nx, ny, hx, hy, n_dir, d_dirs, d_edge, (const float *)sigma_t,
+                                                 (const float *)src, (float *)psi, d_abort, st)
+                      : launch_sweep_dirs<double>(nx, ny, hx, hy, n_dir, d_dirs, d_edge,
+                                                  (const double *)sigma_t, (const double *)src, (double *)psi,
+                                                  d_abort, st);
+  if (e != cudaSuccess) return fail(DLR_ECUDA, "sweep launch failed: %s", cudaGetErrorString(e));
+  int ab = 0;
+  CK(cudaMemcpyAsync(&ab, d_abort, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaFreeAsync(d_dirs, st));
+  CK(cudaFreeAsync(d_edge, st));
+  CK(cudaFreeAsync(d_abort, st));
+  CK(cudaStreamSynchronize(st));
+  if (ab) return fail(DLR_ETIMEOUT, "a sweep wait timed out");
+  return DLR_OK;
+}

@@ -1,0 +1,213 @@
+// dlr_internal.cuh -- device-side data layout and helpers shared by the
+// kernels of the SN-like DLR step (Algorithm 1 of Haut et al.).
+//
+// Layout of one instance in HBM (r = rank, N = nx*ny cells, K = angles):
+//   real  X0[N*r], X[N*r], Psi[N*r], s0[N*r]   column-major (cell fastest)
+//   real  sig_t[N], ss4[N] (= sigma_s / 4pi), q[N], phi[2][N], sphi[N]
+//   f64   T[N], B0[N], D[N], sigma[N], rho_cv[N]
+//   f64   W0[K*r] (column-major), S0[r*r], L[r*K] (angle-major rows of r)
+//   f64   small[]   r x r work matrices (offsets in SmallLayout)
+//   f64   lu[K*r*r], int piv[K*r]  per-angle LU factors of B_k
+//   f64   partials[] per-block partial sums of the tall-skinny reductions
+// "real" is float in mixed precision and double in FP64 mode.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dlr {
+
+constexpr int kMaxRank = 32;
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kTieRel = 1e-12;  // angle-selection tie window
+
+// status codes mirror include/dlr.h
+constexpr int kOk = 0;
+constexpr int kENotConv = -3;
+constexpr int kESingular = -4;
+constexpr int kETimeout = -5;
+constexpr int kENonPos = -6;
+
+// Offsets (in doubles) of the r x r work matrices inside Inst::small.
+struct SmallLayout {
+  int What, WLU, beta, gamma, C0;      // angle selection
+  int R1, R1i, R2, R2i, R3, R3i;       // CholeskyQR factors / inverses
+  int qr_flag;                         // 1 if a third CholeskyQR pass runs
+  int G, Nx, Ny, Mt, Ms, P, vec;       // projections (vec: qh, bL, bR, bB, bT)
+  int Axp, Axm, Ayp, Aym, PS0;         // L-step operators
+  int Cbar, zeta, Lbar, tvec;          // C-bar device
+  int U, V, sv, vphi, Sn, Tr;          // SVD of S and temperature vector
+  int total;
+};
+
+inline SmallLayout small_layout(int r) {
+  SmallLayout s;
+  int o = 0;
+  auto m = [&](int n) { int at = o; o += n; return at; };
+  s.What = m(r * r); s.WLU = m(r * r); s.beta = m(r); s.gamma = m(r); s.C0 = m(r * r);
+  s.R1 = m(r * r); s.R1i = m(r * r); s.R2 = m(r * r); s.R2i = m(r * r);
+  s.R3 = m(r * r); s.R3i = m(r * r); s.qr_flag = m(2);
+  s.G = m(r * r); s.Nx = m(r * r); s.Ny = m(r * r); s.Mt = m(r * r); s.Ms = m(r * r);
+  s.P = m(r * r); s.vec = m(5 * r);
+  s.Axp = m(r * r); s.Axm = m(r * r); s.Ayp = m(r * r); s.Aym = m(r * r); s.PS0 = m(r * r);
+  s.Cbar = m(r * r); s.zeta = m(r); s.Lbar = m(r); s.tvec = m(r);
+  s.U = m(r * r); s.V = m(r * r); s.sv = m(r); s.vphi = m(r); s.Sn = m(r * r); s.Tr = m(r * r);
+  s.total = o;
+  return s;
+}
+
+// Number of doubles one block writes for each reduction kind.
+// (six r x r matrices G, Nx, Ny, Mt, Ms, P and five r-vectors per block)
+__host__ __device__ inline int proj_count(int r) { return 6 * r * r + 5 * r; }
+
+struct Inst {
+  int nx, ny, N, r, K;
+  int precision, selection, fixed_iters, max_iter;
+  double hx, hy, h2, dt, c, a_rad, inv_cdt, si_tol;
+  double psi_edge[4];
+  // per cell, FP64
+  const double *sigma, *rho_cv;
+  double *T, *B0, *D;
+  // per cell, real
+  void *sig_t, *ss4, *q, *phi0, *phi1, *sphi;
+  // N x r, real
+  void *X0, *X, *Psi, *s0;
+  // quadrature, FP64
+  const double *ox, *oy, *w;
+  // factors, FP64
+  double *W0, *S0, *L;
+  // angle selection
+  int *idx;
+  // r x r work space and per-angle LU
+  double *small;
+  SmallLayout lay;
+  double *lu;
+  int *piv;
+  // partial sums of block reductions (partial_stride doubles per block)
+  double *partials;
+  int partial_blocks;      // blocks of the cell reductions (project, Gram)
+  int lstep_blocks;        // blocks of the per-angle L-step
+  // status and iteration bookkeeping
+  int *status;            // sticky device status
+  int *iters;             // iterations of the last source-iteration solve
+  unsigned long long *iters_total;  // iterations summed over all steps
+  unsigned long long *conv;  // [2 parities][2]: max |dphi|, max |phi| (bits)
+};
+
+// Work descriptors of the batched kernels (one entry per instance).
+// A tall-skinny Gram: m x r matrix A, layout 0 column-major A[row + lda*i],
+// layout 1 rows of r contiguous A[i + r*row]; optional row weights.
+struct GramJob {
+  const void *A;
+  const double *wt;
+  int m, r, lda, layout;
+  double *out;      // partial sums
+  int nblocks;      // blocks used for this job
+  const int *run_if;  // optional: skip unless *run_if != 0
+};
+
+// out = diag(s_out) (diag(s_in) A) T for a small r x r T (FP64).
+struct ApplyJob {
+  const void *A;        // input (real_in)
+  int in_layout;        // 0: column-major (lda), 1: rows of r contiguous
+  int lda;
+  const double *s_in;   // optional per-row scale (sqrt applied if sq_in)
+  int sq_in;
+  const double *T;      // r x r column-major FP64
+  void *out;            // column-major, leading dimension ldo
+  int ldo;
+  const double *s_out;  // optional per-row scale
+  int inv_sq_out;       // 1: multiply by 1/sqrt(s_out)
+  int m, r;
+  const int *run_if;  // optional: skip unless *run_if != 0
+};
+
+struct ReduceJob {
+  const double *part;
+  int nblocks, stride, count;
+  double *out;
+  double scale;
+};
+
+struct CholJob {
+  const double *part;
+  int nblocks;
+  double scale;
+  double *R, *Ri;
+  int *flag;
+  int r;
+  int pass;
+  double m_rows;   // rows of the tall matrix (for the shift size)
+};
+
+struct SiCtl {
+  unsigned *bar;        // [0] arrivals, [1] generation
+  unsigned *work;       // [2] unit counters by iteration parity
+  int *abort_flag;
+  const int2 *units;    // (instance, angle), largest first
+  int n_units;
+  int n_inst;
+  int nx_max, bands_max;
+};
+
+template <typename real> struct Real2;
+template <> struct Real2<float> { using type = float2; };
+template <> struct Real2<double> { using type = double2; };
+
+template <typename T>
+__device__ __forceinline__ T *as(void *p) { return reinterpret_cast<T *>(p); }
+template <typename T>
+__device__ __forceinline__ const T *as_c(const void *p) { return reinterpret_cast<const T *>(p); }
+
+// First error wins; later ones are dropped.
+__device__ __forceinline__ void set_status(int *status, int code) {
+  atomicCAS(status, 0, code);
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Non-negative doubles order like their bit patterns.
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long *addr, double v) {
+  atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block-wide sum; every thread gets the result.  scratch >= 32 entries.
+template <typename T>
+__device__ T block_sum(T v, T *scratch) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) scratch[wid] = v;
+  __syncthreads();
+  T t = lane < nw ? scratch[lane] : T(0);
+  t = warp_sum(t);
+  return t;
+}
+template <typename T>
+__device__ T block_max(T v, T *scratch) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_max(v);
+  __syncthreads();
+  if (lane == 0) scratch[wid] = v;
+  __syncthreads();
+  T t = lane < nw ? scratch[lane] : T(-1e308);
+  t = warp_max(t);
+  return t;
+}
+
+}  // namespace dlr

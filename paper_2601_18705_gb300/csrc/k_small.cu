@@ -1,0 +1,850 @@
+// k_small.cu -- FP64 small dense linear algebra of the SN-like DLR step
+// (Algorithm 1 of Haut et al.):
+//   k_select       step 2: angle choice (column-pivoted Householder QR of W0^T,
+//                  or the greedy DEIM of Section 4.2), What, beta, gamma =
+//                  What^{-T} beta, C0 = S0 What^T
+//   k_chol         Cholesky of a reduced Gram (one CholeskyQR pass of steps 5
+//                  and 8), shifted when the Gram is numerically singular
+//   k_proj_post    step 7 Galerkin operators from the reduced projections
+//   k_lstep_angle  step 7 per angle: B_k = |ox| A_x + |oy| A_y + M_t, LU with
+//                  partial pivoting (one warp per angle, one lane per column),
+//                  B_k^{-1} and B_k^{-1} Q_k summed with weights w_k (the
+//                  C-bar device of Section 3.3)
+//   k_lstep_mid    (I - Cbar M_s / 4pi) Lbar = zeta
+//   k_lstep_back   L_k = B_k^{-1} (Q_k + M_s Lbar / 4pi)
+//   k_svd          step 8: S = R^T, one-sided Jacobi SVD S = U Sigma V^T
+//   k_sign         sign of each W column: its largest-magnitude entry > 0
+#include "dlr_internal.cuh"
+
+namespace dlr {
+
+constexpr unsigned kFullMask = 0xffffffffu;
+
+// ------------------------------------------------------------------
+// small parallel LU with partial pivoting on an n x n column-major matrix
+// in shared memory (one CTA).  Returns false if a pivot is exactly zero.
+// ------------------------------------------------------------------
+__device__ bool block_lu(double *A, int n, int *piv) {
+  __shared__ int pr_s;
+  __shared__ int bad_s;
+  if (threadIdx.x == 0) bad_s = 0;
+  __syncthreads();
+  for (int p = 0; p < n; ++p) {
+    if (threadIdx.x == 0) {
+      int pr = p;
+      double best = fabs(A[p + n * p]);
+      for (int i = p + 1; i < n; ++i)
+        if (fabs(A[i + n * p]) > best) { best = fabs(A[i + n * p]); pr = i; }
+      pr_s = pr;
+      piv[p] = pr;
+      if (best == 0.0) bad_s = 1;
+    }
+    __syncthreads();
+    if (bad_s) return false;
+    const int pr = pr_s;
+    if (pr != p)
+      for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        double t = A[p + n * k]; A[p + n * k] = A[pr + n * k]; A[pr + n * k] = t;
+      }
+    __syncthreads();
+    for (int i = p + 1 + threadIdx.x; i < n; i += blockDim.x) A[i + n * p] /= A[p + n * p];
+    __syncthreads();
+    const int m = n - p - 1;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int i = p + 1 + e % m, k = p + 1 + e / m;
+      A[i + n * k] -= A[i + n * p] * A[p + n * k];
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+// solve with the factors of block_lu (thread 0; n <= 32)
+__device__ void lu_solve_serial(const double *A, int n, const int *piv, double *b) {
+  for (int i = 0; i < n; ++i) { double t = b[i]; b[i] = b[piv[i]]; b[piv[i]] = t; }
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < i; ++k) b[i] -= A[i + n * k] * b[k];
+  for (int i = n - 1; i >= 0; --i) {
+    for (int k = i + 1; k < n; ++k) b[i] -= A[i + n * k] * b[k];
+    b[i] /= A[i + n * i];
+  }
+}
+
+// Block argmax with the tie rule: the lowest index whose value is within a
+// relative kTieRel of the maximum.  val < 0 marks excluded entries.
+__device__ int block_argmax_tie(const double *val, int n) {
+  __shared__ double red_d[32];
+  __shared__ int red_i[32];
+  double m = -1.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) m = fmax(m, val[k]);
+  m = block_max(m, red_d);
+  const double thr = m * (1.0 - kTieRel);
+  int best = 0x7fffffff;
+  for (int k = threadIdx.x; k < n; k += blockDim.x)
+    if (val[k] >= 0.0 && val[k] >= thr) best = min(best, k);
+  for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(kFullMask, best, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red_i[threadIdx.x >> 5] = best;
+  __syncthreads();
+  int b = 0x7fffffff;
+  const int nw = (blockDim.x + 31) >> 5;
+  for (int w = 0; w < nw; ++w) b = min(b, red_i[w]);
+  __syncthreads();
+  return b;
+}
+
+// ------------------------------------------------------------------
+// step 2
+// ------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_select(const Inst *__restrict__ insts) {
+  const Inst &I = insts[blockIdx.x];
+  if (*I.status != kOk) return;
+  extern __shared__ double sh[];
+  const int r = I.r, K = I.K;
+  double *val = sh;            // K
+  double *v = val + K;         // r
+  double *M = v + 32;          // r*r
+  double *rhs = M + 32 * 32;   // 32
+  __shared__ int used_dummy;
+  (void)used_dummy;
+  __shared__ int ipiv[32];
+  __shared__ int sel[32];
+  __shared__ double vv_s, alpha_s;
+  double *A = I.L;  // r x K work copy of W0^T
+  const double *W = I.W0;
+  for (int e = threadIdx.x; e < r * K; e += blockDim.x) {
+    const int k = e / r, i = e % r;
+    A[i + r * k] = W[k + (size_t)K * i];
+  }
+  __syncthreads();
+  if (I.selection == 0) {
+    // column-pivoted Householder QR of A = W0^T (Businger-Golub)
+    for (int s = 0; s < r; ++s) {
+      for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        bool u = false;
+        for (int q = 0; q < s; ++q) u |= (sel[q] == k);
+        double t = 0.0;
+        for (int i = s; i < r; ++i) t += A[i + r * k] * A[i + r * k];
+        val[k] = u ? -1.0 : sqrt(t);
+      }
+      __syncthreads();
+      const int p = block_argmax_tie(val, K);
+      if (threadIdx.x == 0) {
+        sel[s] = p;
+        const double nrm = val[p];
+        const double a = A[s + r * p] >= 0 ? -nrm : nrm;
+        double vv = 0.0;
+        for (int i = s; i < r; ++i) {
+          v[i] = A[i + r * p];
+          if (i == s) v[i] -= a;
+          vv += v[i] * v[i];
+        }
+        vv_s = vv;
+        alpha_s = a;
+      }
+      __syncthreads();
+      const double vv = vv_s;
+      if (vv > 0.0)
+        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+          double d = 0.0;
+          for (int i = s; i < r; ++i) d += v[i] * A[i + r * k];
+          const double f = 2.0 * d / vv;
+          for (int i = s; i < r; ++i) A[i + r * k] -= f * v[i];
+        }
+      __syncthreads();
+    }
+  } else {
+    // greedy DEIM: residual of W_j after interpolation on earlier points
+    for (int j = 0; j < r; ++j) {
+      if (threadIdx.x == 0 && j > 0) {
+        for (int i = 0; i < j; ++i) {
+          rhs[i] = W[sel[i] + (size_t)K * j];
+          for (int l = 0; l < j; ++l) M[i + j * l] = W[sel[i] + (size_t)K * l];
+        }
+        // Gaussian elimination with partial pivoting, j x j
+        for (int p = 0; p < j; ++p) {
+          int pr = p;
+          for (int i = p + 1; i < j; ++i) if (fabs(M[i + j * p]) > fabs(M[pr + j * p])) pr = i;
+          if (pr != p) {
+            for (int l = 0; l < j; ++l) { double t = M[p + j * l]; M[p + j * l] = M[pr + j * l]; M[pr + j * l] = t; }
+            double t = rhs[p]; rhs[p] = rhs[pr]; rhs[pr] = t;
+          }
+          for (int i = p + 1; i < j; ++i) {
+            const double f = M[i + j * p] / M[p + j * p];
+            for (int l = p; l < j; ++l) M[i + j * l] -= f * M[p + j * l];
+            rhs[i] -= f * rhs[p];
+          }
+        }
+        for (int i = j - 1; i >= 0; --i) {
+          for (int l = i + 1; l < j; ++l) rhs[i] -= M[i + j * l] * rhs[l];
+          rhs[i] /= M[i + j * i];
+        }
+      }
+      __syncthreads();
+      for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        bool u = false;
+        for (int q = 0; q < j; ++q) u |= (sel[q] == k);
+        double res = W[k + (size_t)K * j];
+        for (int l = 0; l < j; ++l) res -= rhs[l] * W[k + (size_t)K * l];
+        val[k] = u ? -1.0 : fabs(res);
+      }
+      __syncthreads();
+      const int p = block_argmax_tie(val, K);
+      if (threadIdx.x == 0) sel[j] = p;
+      __syncthreads();
+    }
+  }
+  // What_ij = W0_j(Om^(i)), beta_j = sum_k w_k W0_kj
+  double *What = I.small + I.lay.What;
+  double *beta = I.small + I.lay.beta;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int i = e % r, j = e / r;
+    What[e] = W[sel[i] + (size_t)K * j];
+  }
+  for (int i = threadIdx.x; i < r; i += blockDim.x) I.idx[i] = sel[i];
+  {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = wid; j < r; j += nw) {
+      double s = 0.0;
+      for (int k = lane; k < K; k += 32) s += I.w[k] * W[k + (size_t)K * j];
+      s = warp_sum(s);
+      if (lane == 0) beta[j] = s;
+    }
+  }
+  __syncthreads();
+  // gamma = What^{-T} beta (LU of What^T)
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int i = e % r, j = e / r;
+    M[i + r * j] = What[j + r * i];
+  }
+  __syncthreads();
+  const bool ok = block_lu(M, r, ipiv);
+  if (!ok) {
+    if (threadIdx.x == 0) set_status(I.status, kESingular);
+    return;
+  }
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < r; ++i) rhs[i] = beta[i];
+    lu_solve_serial(M, r, ipiv, rhs);
+    for (int i = 0; i < r; ++i) I.small[I.lay.gamma + i] = rhs[i];
+  }
+  // C0 = S0 What^T: C0_kj = sum_l S0_kl What_jl
+  double *C0 = I.small + I.lay.C0;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int k = e % r, j = e / r;
+    double s = 0.0;
+    for (int l = 0; l < r; ++l) s += I.S0[k + r * l] * What[j + r * l];
+    C0[e] = s;
+  }
+}
+
+// ------------------------------------------------------------------
+// Cholesky of G = scale * sum_b part[b] (r x r): R upper with R^T R = G
+// (+ shift), Ri = R^{-1}.  pass: 1, 2 or 3.  *flag is cleared by pass 1 and
+// set when pass 1 or 2 needed a shift; pass 3 runs only if *flag (else it
+// writes R = Ri = I and the pass-3 apply kernels skip).
+// ------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_chol(const CholJob *__restrict__ jobs,
+                                              const Inst *__restrict__ insts) {
+  const CholJob J = jobs[blockIdx.x];
+  const Inst &I = insts[blockIdx.x];
+  if (*I.status != kOk) return;
+  __shared__ double G[32 * 32], C[32 * 32];
+  __shared__ int fail_s;
+  const int r = J.r;
+  if (J.pass == 3 && *J.flag == 0) {
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+      const double d = (e % r == e / r) ? 1.0 : 0.0;
+      J.R[e] = d;
+      J.Ri[e] = d;
+    }
+    return;
+  }
+  if (J.pass == 1 && threadIdx.x == 0) *J.flag = 0;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < J.nblocks; ++b) s += J.part[(size_t)b * r * r + e];
+    G[e] = J.scale * s;
+  }
+  __syncthreads();
+  // symmetrise (the partial sums fill both triangles)
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int i = e % r, j = e / r;
+    if (i < j) {
+      const double a = 0.5 * (G[i + r * j] + G[j + r * i]);
+      C[i + r * j] = a;
+      C[j + r * i] = a;
+    } else if (i == j) {
+      C[e] = G[e];
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) G[e] = C[e];
+  __syncthreads();
+  double tr = 0.0;
+  for (int i = 0; i < r; ++i) tr += G[i + r * i];
+  double shift = 0.0;
+  for (int attempt = 0; attempt < 6; ++attempt) {
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x)
+      C[e] = G[e] + ((e % r == e / r) ? shift : 0.0);
+    if (threadIdx.x == 0) fail_s = 0;
+    __syncthreads();
+    for (int p = 0; p < r; ++p) {
+      if (threadIdx.x == 0) {
+        const double d = C[p + r * p];
+        if (!(d > 1e-15 * tr)) fail_s = 1;
+        C[p + r * p] = sqrt(fmax(d, 1e-300));
+      }
+      __syncthreads();
+      if (fail_s) break;
+      const double dp = C[p + r * p];
+      for (int j = p + 1 + threadIdx.x; j < r; j += blockDim.x) C[p + r * j] /= dp;
+      __syncthreads();
+      const int m = r - p - 1;
+      for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        const int i = p + 1 + e % m, j = p + 1 + e / m;
+        if (i <= j) C[i + r * j] -= C[p + r * i] * C[p + r * j];
+      }
+      __syncthreads();
+    }
+    if (!fail_s) break;
+    // shifted Cholesky QR: s = 11 (m r + r (r+1)) u ||A||^2
+    shift = shift == 0.0 ? 11.0 * (J.m_rows * r + r * (r + 1.0)) * 1.1102230246251565e-16 * tr
+                         : shift * 100.0;
+    if (J.pass <= 2 && threadIdx.x == 0) *J.flag = 1;
+    __syncthreads();
+  }
+  // R = upper triangle of C
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int i = e % r, j = e / r;
+    J.R[e] = i <= j ? C[e] : 0.0;
+  }
+  // Ri: column j solves R x = e_j (back substitution)
+  for (int j = threadIdx.x; j < r; j += blockDim.x) {
+    for (int i = r - 1; i >= 0; --i) {
+      double s = (i == j) ? 1.0 : 0.0;
+      for (int k = i + 1; k <= j; ++k) s -= C[i + r * k] * J.Ri[k + r * j];
+      J.Ri[i + r * j] = i <= j ? s / C[i + r * i] : 0.0;
+    }
+  }
+}
+
+// ------------------------------------------------------------------
+// step 7 operators from the reduced sums (unscaled) in small[G .. vec]
+// ------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_proj_post(const Inst *__restrict__ insts) {
+  const Inst &I = insts[blockIdx.x];
+  if (*I.status != kOk) return;
+  const int r = I.r;
+  double *s = I.small;
+  const SmallLayout &L = I.lay;
+  const double h2 = I.h2;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int i = e % r, j = e / r;
+    const double g = s[L.G + e];
+    s[L.Axp + e] = h2 / I.hx * (g - s[L.Nx + e]);
+    s[L.Axm + e] = h2 / I.hx * (g - s[L.Nx + j + r * i]);
+    s[L.Ayp + e] = h2 / I.hy * (g - s[L.Ny + e]);
+    s[L.Aym + e] = h2 / I.hy * (g - s[L.Ny + j + r * i]);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    s[L.Mt + e] *= h2;
+    s[L.Ms + e] *= h2;
+    s[L.P + e] *= h2;
+  }
+  for (int i = threadIdx.x; i < r; i += blockDim.x) {
+    s[L.vec + i] *= h2;                 // qh
+    s[L.vec + r + i] *= I.hy;           // left edge
+    s[L.vec + 2 * r + i] *= I.hy;       // right edge
+    s[L.vec + 3 * r + i] *= I.hx;       // bottom edge
+    s[L.vec + 4 * r + i] *= I.hx;       // top edge
+  }
+  __syncthreads();
+  // PS0 = P S0
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int i = e % r, j = e / r;
+    double t = 0.0;
+    for (int l = 0; l < r; ++l) t += s[L.P + i + r * l] * I.S0[l + r * j];
+    s[L.PS0 + e] = t;
+  }
+}
+
+// ------------------------------------------------------------------
+// step 7, per angle (one warp per angle; lane j owns column j)
+// ------------------------------------------------------------------
+struct AngleOps {
+  const double *Ax, *Ay, *bx, *by;
+  double aox, aoy, px, py;
+};
+
+__device__ __forceinline__ AngleOps angle_ops(const Inst &I, const double *sm, int k) {
+  const SmallLayout &L = I.lay;
+  const int r = I.r;
+  AngleOps o;
+  const double ox = I.ox[k], oy = I.oy[k];
+  o.Ax = sm + (ox > 0 ? 0 : r * r);          // smem copy: Axp, Axm, Ayp, Aym, ...
+  o.Ay = sm + (oy > 0 ? 2 * r * r : 3 * r * r);
+  const double *vec = sm + 6 * r * r;        // qh, bL, bR, bB, bT
+  o.bx = vec + (ox > 0 ? r : 2 * r);
+  o.by = vec + (oy > 0 ? 3 * r : 4 * r);
+  o.aox = fabs(ox);
+  o.aoy = fabs(oy);
+  o.px = ox > 0 ? I.psi_edge[0] : (ox < 0 ? I.psi_edge[1] : 0.0);
+  o.py = oy > 0 ? I.psi_edge[2] : (oy < 0 ? I.psi_edge[3] : 0.0);
+  (void)L;
+  return o;
+}
+
+// Q_k[i] = qh_i + (P S0 W0_k)_i / (c dt) + |ox| psi_x bx_i + |oy| psi_y by_i
+__device__ __forceinline__ double angle_q(const Inst &I, const double *sm, const AngleOps &o,
+                                          int k, int i) {
+  const int r = I.r;
+  const double *PS0 = sm + 5 * r * r;
+  const double *qh = sm + 6 * r * r;
+  double t = 0.0;
+  for (int l = 0; l < r; ++l) t += PS0[i + r * l] * I.W0[k + (size_t)I.K * l];
+  return qh[i] + I.inv_cdt * t + o.aox * o.px * o.bx[i] + o.aoy * o.py * o.by[i];
+}
+
+// stage Axp, Axm, Ayp, Aym, Mt, PS0 (r x r each) and vec (5r) in smem
+__device__ void stage_ops(const Inst &I, double *sm) {
+  const int r = I.r;
+  const SmallLayout &L = I.lay;
+  const int offs[6] = {L.Axp, L.Axm, L.Ayp, L.Aym, L.Mt, L.PS0};
+  for (int a = 0; a < 6; ++a)
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) sm[a * r * r + e] = I.small[offs[a] + e];
+  for (int e = threadIdx.x; e < 5 * r; e += blockDim.x) sm[6 * r * r + e] = I.small[L.vec + e];
+  __syncthreads();
+}
+
+constexpr int kLsWarps = 8;
+
+__global__ void __launch_bounds__(kLsWarps * 32) k_lstep_angle(const Inst *__restrict__ insts,
+                                                               int blocks_per_inst) {
+  const Inst &I = insts[blockIdx.y];
+  blocks_per_inst = I.lstep_blocks;
+  if ((int)blockIdx.x >= blocks_per_inst || *I.status != kOk) return;
+  extern __shared__ double sh[];
+  const int r = I.r, K = I.K;
+  double *sm = sh;                                   // 6 r^2 + 5 r
+  double *wlu = sh + 6 * r * r + 5 * r;              // kLsWarps x r^2
+  double *red = wlu + (size_t)kLsWarps * r * r;      // kLsWarps x (r^2 + r)
+  stage_ops(I, sm);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double *lu_w = wlu + (size_t)wid * r * r;
+  // per-warp accumulators: lane j owns column j of sum_k w_k B_k^{-1} and
+  // entry j of sum_k w_k B_k^{-1} Q_k
+  double *mine = red + (size_t)wid * (r * r + r);
+  for (int e = lane; e < r * r + r; e += 32) mine[e] = 0.0;
+  __syncwarp();
+  bool bad = false;
+  const int gw = blockIdx.x * kLsWarps + wid, nwarps = blocks_per_inst * kLsWarps;
+  for (int k = gw; k < K; k += nwarps) {
+    const AngleOps o = angle_ops(I, sm, k);
+    const double *Mt = sm + 4 * r * r;
+    double col[kMaxRank];
+#pragma unroll
+    for (int i = 0; i < kMaxRank; ++i)
+      col[i] = (i < r && lane < r)
+                   ? o.aox * o.Ax[i + r * lane] + o.aoy * o.Ay[i + r * lane] + Mt[i + r * lane]
+                   : 0.0;
+    const double qk = lane < r ? angle_q(I, sm, o, k, lane) : 0.0;
+    int mypiv = 0;
+    bool singular = false;
+    for (int p = 0; p < r; ++p) {
+      int pr = p;
+      if (lane == p) {
+        double best = -1.0;
+#pragma unroll
+        for (int i = 0; i < kMaxRank; ++i)
+          if (i >= p && i < r && fabs(col[i]) > best) { best = fabs(col[i]); pr = i; }
+        if (best == 0.0) pr = -1;
+      }
+      pr = __shfl_sync(kFullMask, pr, p);
+      if (pr < 0) { singular = true; break; }
+      if (lane == p) mypiv = pr;
+      if (pr != p) {
+        double a = 0.0, b = 0.0;
+#pragma unroll
+        for (int i = 0; i < kMaxRank; ++i) { if (i == p) a = col[i]; if (i == pr) b = col[i]; }
+#pragma unroll
+        for (int i = 0; i < kMaxRank; ++i) { if (i == p) col[i] = b; if (i == pr) col[i] = a; }
+      }
+      double dpp = 0.0;
+#pragma unroll
+      for (int i = 0; i < kMaxRank; ++i) if (i == p) dpp = col[i];
+      dpp = __shfl_sync(kFullMask, dpp, p);
+      if (lane == p) {
+#pragma unroll
+        for (int i = 0; i < kMaxRank; ++i) if (i > p && i < r) col[i] /= dpp;
+      }
+      double cp = 0.0;  // this lane's entry in row p
+#pragma unroll
+      for (int i = 0; i < kMaxRank; ++i) if (i == p) cp = col[i];
+#pragma unroll
+      for (int i = 0; i < kMaxRank; ++i) {
+        if (i > p && i < r) {
+          const double li = __shfl_sync(kFullMask, col[i], p);
+          if (lane > p && lane < r) col[i] -= li * cp;
+        }
+      }
+    }
+    if (singular) {
+      if (lane == 0) set_status(I.status, kESingular);
+      bad = true;
+      break;
+    }
+    // factors to global (for the back-solve) and to this warp's smem
+    if (lane < r) {
+#pragma unroll
+      for (int i = 0; i < kMaxRank; ++i)
+        if (i < r) {
+          I.lu[((size_t)k * r + lane) * r + i] = col[i];
+          lu_w[lane * r + i] = col[i];
+        }
+      I.piv[(size_t)k * r + lane] = mypiv;
+    }
+    __syncwarp();
+    // lane j: column j of B^{-1} = U^{-1} L^{-1} P e_j
+    double y[kMaxRank];
+#pragma unroll
+    for (int i = 0; i < kMaxRank; ++i) y[i] = (i == lane) ? 1.0 : 0.0;
+    for (int p = 0; p < r; ++p) {
+      const int pr = __shfl_sync(kFullMask, mypiv, p);
+      if (pr != p) {
+        double a = 0.0, b = 0.0;
+#pragma unroll
+        for (int i = 0; i < kMaxRank; ++i) { if (i == p) a = y[i]; if (i == pr) b = y[i]; }
+#pragma unroll
+        for (int i = 0; i < kMaxRank; ++i) { if (i == p) y[i] = b; if (i == pr) y[i] = a; }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kMaxRank; ++i) {
+      if (i < r) {
+#pragma unroll
+        for (int m = 0; m < kMaxRank; ++m)
+          if (m < i) y[i] -= lu_w[m * r + i] * y[m];
+      }
+    }
+#pragma unroll
+    for (int ii = kMaxRank - 1; ii >= 0; --ii) {
+      if (ii < r) {
+#pragma unroll
+        for (int m = 0; m < kMaxRank; ++m)
+          if (m > ii && m < r) y[ii] -= lu_w[m * r + ii] * y[m];
+        y[ii] /= lu_w[ii * r + ii];
+      }
+    }
+    // (B^{-1} Q)_i = sum_j (B^{-1})_ij Q_j ; lane j holds column j and Q_j
+    const double wk = I.w[k];
+#pragma unroll
+    for (int i = 0; i < kMaxRank; ++i) {
+      if (i < r) {
+        const double z = warp_sum(lane < r ? y[i] * qk : 0.0);
+        if (lane == i) mine[r * r + i] += wk * z;
+        if (lane < r) mine[i + r * lane] += wk * y[i];
+      }
+    }
+    __syncwarp();
+  }
+  (void)bad;
+  // CTA reduction (fixed order) -> partials[blockIdx.x]
+  __syncthreads();
+  double *out = I.partials + (size_t)blockIdx.x * (r * r + r);
+  for (int e = threadIdx.x; e < r * r + r; e += blockDim.x) {
+    double s = 0.0;
+    for (int w = 0; w < kLsWarps; ++w) s += red[(size_t)w * (r * r + r) + e];
+    out[e] = s;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_lstep_mid(const Inst *__restrict__ insts,
+                                                   int blocks_per_inst) {
+  const Inst &I = insts[blockIdx.x];
+  if (*I.status != kOk) return;
+  blocks_per_inst = I.lstep_blocks;
+  __shared__ double M[32 * 32], Cb[32 * 32], z[32], Lb[32];
+  __shared__ int ipiv[32];
+  const int r = I.r;
+  const SmallLayout &L = I.lay;
+  for (int e = threadIdx.x; e < r * r + r; e += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < blocks_per_inst; ++b) s += I.partials[(size_t)b * (r * r + r) + e];
+    if (e < r * r) Cb[e] = s; else z[e - r * r] = s;
+  }
+  __syncthreads();
+  const double *Ms = I.small + L.Ms;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int i = e % r, j = e / r;
+    double t = 0.0;
+    for (int l = 0; l < r; ++l) t += Cb[i + r * l] * Ms[l + r * j];
+    M[e] = (i == j ? 1.0 : 0.0) - t / (4.0 * kPi);
+  }
+  __syncthreads();
+  if (!block_lu(M, r, ipiv)) {
+    if (threadIdx.x == 0) set_status(I.status, kESingular);
+    return;
+  }
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < r; ++i) Lb[i] = z[i];
+    lu_solve_serial(M, r, ipiv, Lb);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < r; i += blockDim.x) {
+    double t = 0.0;
+    for (int l = 0; l < r; ++l) t += Ms[i + r * l] * Lb[l];
+    I.small[L.tvec + i] = t / (4.0 * kPi);
+    I.small[L.Lbar + i] = Lb[i];
+  }
+}
+
+__global__ void __launch_bounds__(kLsWarps * 32) k_lstep_back(const Inst *__restrict__ insts,
+                                                              int blocks_per_inst) {
+  const Inst &I = insts[blockIdx.y];
+  blocks_per_inst = I.lstep_blocks;
+  if ((int)blockIdx.x >= blocks_per_inst || *I.status != kOk) return;
+  extern __shared__ double sh[];
+  const int r = I.r, K = I.K;
+  double *sm = sh;
+  stage_ops(I, sm);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const double tv = lane < r ? I.small[I.lay.tvec + lane] : 0.0;
+  const int gw = blockIdx.x * kLsWarps + wid, nwarps = blocks_per_inst * kLsWarps;
+  for (int k = gw; k < K; k += nwarps) {
+    const AngleOps o = angle_ops(I, sm, k);
+    double b = lane < r ? angle_q(I, sm, o, k, lane) + tv : 0.0;  // lane i holds b_i
+    const double *LU = I.lu + (size_t)k * r * r;
+    const int *pv = I.piv + (size_t)k * r;
+    for (int p = 0; p < r; ++p) {
+      const int pr = pv[p];
+      if (pr != p) {
+        const double bp = __shfl_sync(kFullMask, b, p), bq = __shfl_sync(kFullMask, b, pr);
+        if (lane == p) b = bq;
+        if (lane == pr) b = bp;
+      }
+    }
+    for (int m = 0; m < r; ++m) {  // forward: unit lower
+      const double ym = __shfl_sync(kFullMask, b, m);
+      if (lane > m && lane < r) b -= LU[m * r + lane] * ym;
+    }
+    for (int m = r - 1; m >= 0; --m) {  // backward: upper
+      double xm = 0.0;
+      if (lane == m) { b /= LU[m * r + m]; xm = b; }
+      xm = __shfl_sync(kFullMask, xm, m);
+      if (lane < m) b -= LU[m * r + lane] * xm;
+    }
+    if (lane < r) I.L[(size_t)r * k + lane] = b;
+  }
+}
+
+// ------------------------------------------------------------------
+// step 8: S = R^T with R = R3 R2 R1 (CholeskyQR of diag(sqrt w) L^T),
+// one-sided Jacobi SVD S = U Sigma V^T (descending), S0 <- Sigma, V and U
+// kept for W <- W V and X <- X U, vphi = L w.
+// ------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_svd(const Inst *__restrict__ insts) {
+  const Inst &I = insts[blockIdx.x];
+  if (*I.status != kOk) return;
+  __shared__ double Rm[32 * 32], Tm[32 * 32], Uw[32 * 32], Vw[32 * 32], sv[32];
+  __shared__ int ord[32];
+  __shared__ int rot_s;
+  const int r = I.r;
+  const SmallLayout &L = I.lay;
+  // R = R3 R2 R1 : R1, R2 in small[R1], small[R2]; R3 in small[Tr]
+  const double *R1 = I.small + L.R1, *R2 = I.small + L.R2, *R3 = I.small + L.R3;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int i = e % r, j = e / r;
+    double t = 0.0;
+    for (int l = 0; l < r; ++l) t += R2[i + r * l] * R1[l + r * j];
+    Tm[e] = t;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int i = e % r, j = e / r;
+    double t = 0.0;
+    for (int l = 0; l < r; ++l) t += R3[i + r * l] * Tm[l + r * j];
+    Rm[e] = t;
+  }
+  __syncthreads();
+  // U := S = R^T, V := I
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int i = e % r, j = e / r;
+    Uw[e] = Rm[j + r * i];
+    Vw[e] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  // one-sided Jacobi; each sweep visits all pairs in n-1 rounds of n/2
+  // disjoint pairs (circle method), one warp per pair
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int n = (r + 1) & ~1;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    if (threadIdx.x == 0) rot_s = 0;
+    __syncthreads();
+    for (int round = 0; round < n - 1; ++round) {
+      for (int pr = wid; pr < n / 2; pr += nw) {
+        // positions pr and n-1-pr of [0, rotate(1..n-1, round)]
+        auto player = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + round) % (n - 1); };
+        int i = player(pr), j = player(n - 1 - pr);
+        if (i > j) { const int t = i; i = j; j = t; }
+        if (j >= r) continue;
+        const double ui = lane < r ? Uw[lane + r * i] : 0.0;
+        const double uj = lane < r ? Uw[lane + r * j] : 0.0;
+        const double al = warp_sum(ui * ui), be = warp_sum(uj * uj), ga = warp_sum(ui * uj);
+        if (ga == 0.0 || fabs(ga) <= 1e-15 * sqrt(al * be)) continue;
+        if (lane == 0) rot_s = 1;
+        const double zeta = (be - al) / (2.0 * ga);
+        const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+        if (lane < r) {
+          Uw[lane + r * i] = cs * ui - sn * uj;
+          Uw[lane + r * j] = sn * ui + cs * uj;
+          const double vi = Vw[lane + r * i], vj = Vw[lane + r * j];
+          Vw[lane + r * i] = cs * vi - sn * vj;
+          Vw[lane + r * j] = sn * vi + cs * vj;
+        }
+      }
+      __syncthreads();
+    }
+    if (!rot_s) break;
+  }
+  if (threadIdx.x == 0) {
+    for (int j = 0; j < r; ++j) {
+      double t = 0.0;
+      for (int k = 0; k < r; ++k) t += Uw[k + r * j] * Uw[k + r * j];
+      sv[j] = sqrt(t);
+      ord[j] = j;
+    }
+    for (int a = 1; a < r; ++a) {  // stable insertion sort, descending
+      const int key = ord[a];
+      int b = a - 1;
+      while (b >= 0 && sv[ord[b]] < sv[key]) { ord[b + 1] = ord[b]; --b; }
+      ord[b + 1] = key;
+    }
+  }
+  __syncthreads();
+  const double smax = sv[ord[0]];
+  double *U = I.small + L.U, *V = I.small + L.V;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int k = e % r, j = e / r, o = ord[j];
+    const double s = sv[o];
+    V[k + r * j] = Vw[k + r * o];
+    U[k + r * j] = (s > 1e-300 && s > 1e-15 * smax) ? Uw[k + r * o] / s : 0.0;
+  }
+  __syncthreads();
+  // complete U columns of zero singular values (Gram-Schmidt on unit vectors)
+  if (threadIdx.x == 0) {
+    for (int j = 0; j < r; ++j) {
+      double t = 0.0;
+      for (int k = 0; k < r; ++k) t += U[k + r * j] * U[k + r * j];
+      if (t > 0.5) continue;
+      for (int e = 0; e < r; ++e) {
+        double u[32];
+        for (int k = 0; k < r; ++k) u[k] = k == e ? 1.0 : 0.0;
+        for (int pass = 0; pass < 2; ++pass)
+          for (int l = 0; l < r; ++l) {
+            if (l == j) continue;
+            double d = 0.0, ll = 0.0;
+            for (int k = 0; k < r; ++k) { d += U[k + r * l] * u[k]; ll += U[k + r * l] * U[k + r * l]; }
+            if (ll < 0.5) continue;
+            for (int k = 0; k < r; ++k) u[k] -= d * U[k + r * l];
+          }
+        double nn = 0.0;
+        for (int k = 0; k < r; ++k) nn += u[k] * u[k];
+        if (nn > 1e-2) {
+          nn = sqrt(nn);
+          for (int k = 0; k < r; ++k) U[k + r * j] = u[k] / nn;
+          break;
+        }
+      }
+    }
+  }
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int i = e % r, j = e / r;
+    I.S0[e] = (i == j) ? sv[ord[j]] : 0.0;
+  }
+  // vphi_i = sum_k w_k L_ik  (phi = X L w)
+  {
+    for (int i = wid; i < r; i += nw) {
+      double s = 0.0;
+      for (int k = lane; k < I.K; k += 32) s += I.w[k] * I.L[(size_t)r * k + i];
+      s = warp_sum(s);
+      if (lane == 0) I.small[L.vphi + i] = s;
+    }
+  }
+}
+
+// Sign of W columns: the entry of largest magnitude (tie rule) made positive;
+// the same flip is applied to U (and so to X in the temperature kernel).
+__global__ void __launch_bounds__(256) k_sign(const Inst *__restrict__ insts) {
+  const Inst &I = insts[blockIdx.x];
+  if (*I.status != kOk) return;
+  extern __shared__ double val[];
+  const int r = I.r, K = I.K;
+  for (int j = 0; j < r; ++j) {
+    for (int k = threadIdx.x; k < K; k += blockDim.x) val[k] = fabs(I.W0[k + (size_t)K * j]);
+    __syncthreads();
+    const int am = block_argmax_tie(val, K);
+    const bool flip = I.W0[am + (size_t)K * j] < 0.0;
+    if (flip) {
+      for (int k = threadIdx.x; k < K; k += blockDim.x) I.W0[k + (size_t)K * j] = -I.W0[k + (size_t)K * j];
+      for (int i = threadIdx.x; i < r; i += blockDim.x) I.small[I.lay.U + i + r * j] *= -1.0;
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------
+// host launchers (kernel attributes are set by prepare_small before any
+// launch is captured into a graph)
+// ------------------------------------------------------------------
+static size_t select_smem(int maxK) { return (size_t)(maxK + 32 + 32 * 32 + 32) * sizeof(double); }
+size_t lstep_angle_smem(int r) {
+  return (size_t)(6 * r * r + 5 * r + kLsWarps * r * r + kLsWarps * (r * r + r)) * sizeof(double);
+}
+static size_t lstep_back_smem(int r) { return (size_t)(6 * r * r + 5 * r) * sizeof(double); }
+
+cudaError_t prepare_small(int maxK, int rmax) {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)select_smem(maxK))) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_lstep_angle, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)lstep_angle_smem(rmax))) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_lstep_back, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)lstep_back_smem(rmax))) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_sign, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(maxK * sizeof(double)));
+}
+cudaError_t launch_select(const Inst *d, int n, int maxK, cudaStream_t st) {
+  k_select<<<n, 256, select_smem(maxK), st>>>(d);
+  return cudaGetLastError();
+}
+cudaError_t launch_chol(const CholJob *dj, const Inst *d, int n, cudaStream_t st) {
+  k_chol<<<n, 256, 0, st>>>(dj, d);
+  return cudaGetLastError();
+}
+cudaError_t launch_proj_post(const Inst *d, int n, cudaStream_t st) {
+  k_proj_post<<<n, 256, 0, st>>>(d);
+  return cudaGetLastError();
+}
+cudaError_t launch_lstep(const Inst *d, int n, int r_max, int blocks, cudaStream_t st) {
+  k_lstep_angle<<<dim3(blocks, n), kLsWarps * 32, lstep_angle_smem(r_max), st>>>(d, blocks);
+  cudaError_t e;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_lstep_mid<<<n, 256, 0, st>>>(d, blocks);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_lstep_back<<<dim3(blocks, n), kLsWarps * 32, lstep_back_smem(r_max), st>>>(d, blocks);
+  return cudaGetLastError();
+}
+cudaError_t launch_svd(const Inst *d, int n, cudaStream_t st) {
+  k_svd<<<n, 256, 0, st>>>(d);
+  return cudaGetLastError();
+}
+cudaError_t launch_sign(const Inst *d, int n, int maxK, cudaStream_t st) {
+  k_sign<<<n, 256, (size_t)maxK * sizeof(double), st>>>(d);
+  return cudaGetLastError();
+}
+
+}  // namespace dlr

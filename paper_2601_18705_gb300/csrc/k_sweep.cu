@@ -1,0 +1,486 @@
+// k_sweep.cu -- the hot path of Algorithm 1 step 4: DG0 upwind transport
+// sweeps at the r collocation angles with source iteration on
+//   Om^(j).grad psi_j + (sigma + 1/(c dt)) psi_j
+//       = sigma_s/(4 pi) beta^T What^{-1} Psi + q + psi0_j / (c dt)
+// (Eq. steady state collocation of Haut et al.; phi = beta^T What^{-1} Psi is
+// evaluated as gamma^T Psi with gamma = What^{-T} beta).
+//
+// Sweep organisation (one CTA per (instance, angle) unit):
+//   * cells are visited in sweep coordinates (u, v): x and y are mirrored so
+//     that the direction points to +u, +v;
+//   * rows are grouped in bands of 32; lane i of a warp owns row 32b+i and at
+//     step t updates column u = t - i (an anti-diagonal wavefront); the value
+//     of the cell below arrives from lane i-1 by a warp shuffle, the value of
+//     the cell to the left stays in a register;
+//   * inputs of a 32x32 chunk are loaded with coalesced row loads into a
+//     per-warp shared-memory tile (source and 1/(sigma_t + ax + ay)), which
+//     the diagonal then reads without bank conflicts (row stride 32, the
+//     diagonal index 31 i + const hits distinct banks);
+//   * the top row of a band is handed to the next band (another warp) through
+//     a shared-memory ring of row buffers, guarded by a per-band progress
+//     counter published every kSub steps; every wait is bounded in time.
+// The source-iteration loop runs inside one cooperative launch per step for
+// all instances: sweep phase, grid barrier, scalar-flux phase
+// phi = sum_j gamma_j psi_j with the convergence test, grid barrier.
+#include "dlr_internal.cuh"
+
+namespace dlr {
+
+template <typename real> struct SweepCfg;
+template <> struct SweepCfg<float> { static constexpr int NW = 8; };
+template <> struct SweepCfg<double> { static constexpr int NW = 4; };
+
+constexpr int kSub = 8;                        // progress granularity (steps)
+constexpr uint64_t kWaitNs = 4000000000ull;    // bound of any single wait
+constexpr unsigned kFull = 0xffffffffu;
+
+template <typename real>
+struct SweepArgs {
+  int nx, ny;
+  bool flipx, flipy;
+  real ax, ay, in_x, in_y;
+  const real *sig_t;  // N
+  const real *src;    // N: the angle's fixed source
+  const real *sphi;   // N or nullptr: sigma_s phi / (4 pi), added to src
+  real *psi;          // N: output
+};
+
+struct SweepSmem {
+  void *tiles;    // NW warps x 2 x 32 x 32 real2
+  void *edge;     // (NW + 1) x nx_max real
+  int *prog;      // bands_max
+  int nx_max;
+};
+
+// Bounded spin of lane 0 until *flag >= need.  Returns false on timeout or
+// abort (the warp then leaves the unit).
+__device__ __forceinline__ bool wait_progress(volatile int *flag, int need,
+                                              volatile int *abort_flag) {
+  bool ok = true;
+  if ((threadIdx.x & 31) == 0) {
+    if (*flag < need) {
+      uint64_t t0 = global_ns();
+      unsigned spins = 0;
+      while (*flag < need) {
+        if ((++spins & 255u) == 0) {
+          if (*abort_flag || global_ns() - t0 > kWaitNs) { ok = false; break; }
+        }
+      }
+    }
+    __threadfence_block();
+  }
+  ok = __shfl_sync(kFull, ok, 0);
+  __syncwarp();
+  return ok;
+}
+
+// One band of 32 rows of one angle, swept by one warp.
+template <typename real, int NW>
+__device__ bool sweep_band(int b, const SweepArgs<real> &A, const SweepSmem &S,
+                           volatile int *abort_flag) {
+  using real2 = typename Real2<real>::type;
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  real2 *tiles = reinterpret_cast<real2 *>(S.tiles) + wid * 2048;
+  real *edge = reinterpret_cast<real *>(S.edge);
+  real *edge_out = edge + (b % (NW + 1)) * S.nx_max;
+  volatile real *edge_in = edge + ((b + NW) % (NW + 1)) * S.nx_max;
+  volatile int *prog = S.prog;
+  const int nx = A.nx, ny = A.ny;
+  const int v = 32 * b + lane;
+  const bool row_ok = v < ny;
+  const int nch = (nx + 31) >> 5;
+  real psi_left = A.in_x, psi_prev = real(0);
+
+  for (int k = 0; k <= nch; ++k) {
+    real2 *tk = tiles + (k & 1) * 1024;        // chunk k
+    real2 *tp = tiles + ((k + 1) & 1) * 1024;  // chunk k-1
+    if (k < nch) {
+      const int u = 32 * k + lane;
+      const int ix = A.flipx ? nx - 1 - u : u;
+#pragma unroll 4
+      for (int ii = 0; ii < 32; ++ii) {
+        const int vv = 32 * b + ii;
+        real2 e;
+        e.x = real(0);
+        e.y = real(0);
+        if (u < nx && vv < ny) {
+          const int iy = A.flipy ? ny - 1 - vv : vv;
+          const int c = iy * nx + ix;
+          real s = A.src[c];
+          if (A.sphi) s += A.sphi[c];
+          e.x = s;
+          e.y = real(1) / (A.sig_t[c] + A.ax + A.ay);
+        }
+        tk[ii * 32 + lane] = e;
+      }
+    }
+    __syncwarp();
+#pragma unroll 1
+    for (int tau = 0; tau < 32; tau += kSub) {
+      const int t0 = 32 * k + tau;
+      if (b > 0 && t0 < nx) {
+        if (!wait_progress(prog + b - 1, min(nx, t0 + kSub), abort_flag)) return false;
+      }
+#pragma unroll
+      for (int s = 0; s < kSub; ++s) {
+        const int t = t0 + s;
+        const int u = t - lane;
+        real down = __shfl_up_sync(kFull, psi_prev, 1);
+        const bool active = row_ok && u >= 0 && u < nx;
+        if (lane == 0) down = (b == 0) ? A.in_y : (active ? edge_in[u] : real(0));
+        if (active) {
+          real2 *slot = (u >= 32 * k ? tk : tp) + lane * 32 + (u & 31);
+          const real2 e = *slot;
+          const real psi = (e.x + A.ax * psi_left + A.ay * down) * e.y;
+          slot->x = psi;
+          psi_left = psi;
+          psi_prev = psi;
+          if (lane == 31) edge_out[u] = psi;
+        }
+      }
+      if (lane == 31 && row_ok) {
+        __threadfence_block();
+        const int done = min(nx, max(0, t0 + kSub - 31));
+        prog[b] = done;
+      }
+    }
+    __syncwarp();
+    if (k >= 1) {  // chunk k-1 is complete: write it out
+      const int u = 32 * (k - 1) + lane;
+      if (u < nx) {
+        const int ix = A.flipx ? nx - 1 - u : u;
+#pragma unroll 4
+        for (int ii = 0; ii < 32; ++ii) {
+          const int vv = 32 * b + ii;
+          if (vv < ny) {
+            const int iy = A.flipy ? ny - 1 - vv : vv;
+            A.psi[iy * nx + ix] = tp[ii * 32 + lane].x;
+          }
+        }
+      }
+    }
+    __syncwarp();
+  }
+  return true;
+}
+
+// Whole sweep of one angle by one CTA.  Returns false if a wait gave up.
+template <typename real, int NW>
+__device__ bool sweep_unit(const SweepArgs<real> &A, const SweepSmem &S,
+                           volatile int *abort_flag) {
+  const int nb = (A.ny + 31) >> 5;
+  __syncthreads();
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) S.prog[i] = 0;
+  __syncthreads();
+  bool ok = true;
+  const int wid = threadIdx.x >> 5;
+  for (int b = wid; b < nb && ok; b += NW) ok = sweep_band<real, NW>(b, A, S, abort_flag);
+  if (!ok) *abort_flag = 1;
+  __syncthreads();
+  return ok;
+}
+
+template <typename real>
+__device__ SweepArgs<real> unit_args(const Inst &I, int j) {
+  SweepArgs<real> A;
+  const int k = I.idx[j];
+  const double ox = I.ox[k], oy = I.oy[k];
+  A.nx = I.nx;
+  A.ny = I.ny;
+  A.flipx = ox < 0;
+  A.flipy = oy < 0;
+  A.ax = real(fabs(ox) / I.hx);
+  A.ay = real(fabs(oy) / I.hy);
+  A.in_x = real(ox > 0 ? I.psi_edge[0] : (ox < 0 ? I.psi_edge[1] : 0.0));
+  A.in_y = real(oy > 0 ? I.psi_edge[2] : (oy < 0 ? I.psi_edge[3] : 0.0));
+  A.sig_t = as_c<real>(I.sig_t);
+  A.src = as_c<real>(I.s0) + (size_t)I.N * j;
+  A.sphi = as_c<real>(I.sphi);
+  A.psi = as<real>(I.Psi) + (size_t)I.N * j;
+  return A;
+}
+
+
+// Sense-reversing grid barrier with a bounded wait (co-residency of all
+// CTAs is guaranteed by the cooperative launch).
+__device__ bool grid_barrier(unsigned *bar, volatile int *abort_flag) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u);
+    int ok = 1;
+    if (arrived == gridDim.x - 1) {
+      bar[0] = 0;
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      uint64_t t0 = global_ns();
+      unsigned spins = 0;
+      while (*gen == g) {
+        if ((++spins & 63u) == 0) {
+          __nanosleep(64);
+          if (*abort_flag || global_ns() - t0 > kWaitNs) { ok = 0; break; }
+        }
+      }
+    }
+    __threadfence();
+    ok_s = ok && !*abort_flag;
+  }
+  __syncthreads();
+  return ok_s;
+}
+
+template <typename real>
+__global__ void __launch_bounds__(SweepCfg<real>::NW * 32)
+k_si(const Inst *__restrict__ insts, SiCtl ctl) {
+  constexpr int NW = SweepCfg<real>::NW;
+  extern __shared__ __align__(16) unsigned char smem[];
+  using real2 = typename Real2<real>::type;
+  SweepSmem S;
+  S.tiles = smem;
+  size_t off = (size_t)NW * 2048 * sizeof(real2);
+  S.edge = smem + off;
+  off += (size_t)(NW + 1) * ctl.nx_max * sizeof(real);
+  S.prog = reinterpret_cast<int *>(smem + off);
+  off += (size_t)ctl.bands_max * sizeof(int);
+  int *active = reinterpret_cast<int *>(smem + off);
+  S.nx_max = ctl.nx_max;
+  __shared__ int unit_s, n_active_s;
+  volatile int *abort_flag = ctl.abort_flag;
+
+  for (int i = threadIdx.x; i < ctl.n_inst; i += blockDim.x)
+    active[i] = (*insts[i].status == kOk) ? 1 : 0;
+  __syncthreads();
+
+  for (int it = 0;; ++it) {
+    if (threadIdx.x == 0) {
+      int n = 0;
+      for (int i = 0; i < ctl.n_inst; ++i) n += active[i];
+      n_active_s = n;
+    }
+    __syncthreads();
+    if (n_active_s == 0) break;
+
+    // ---- phase A: sweeps of all active (instance, angle) units ----
+    for (;;) {
+      if (threadIdx.x == 0) unit_s = (int)atomicAdd(ctl.work + (it & 1), 1u);
+      __syncthreads();
+      const int u = unit_s;
+      __syncthreads();
+      if (u >= ctl.n_units) break;
+      const int2 ij = ctl.units[u];
+      if (!active[ij.x]) continue;
+      const SweepArgs<real> A = unit_args<real>(insts[ij.x], ij.y);
+      if (!sweep_unit<real, NW>(A, S, abort_flag)) break;
+    }
+    if (!grid_barrier(ctl.bar, abort_flag)) break;
+
+    // ---- phase B: phi_new = sum_j gamma_j psi_j, convergence maxima ----
+    if (blockIdx.x == 0) {
+      for (int i = threadIdx.x; i < ctl.n_inst; i += blockDim.x) {
+        insts[i].conv[((it + 1) & 1) * 2 + 0] = 0ull;
+        insts[i].conv[((it + 1) & 1) * 2 + 1] = 0ull;
+      }
+      if (threadIdx.x == 0) ctl.work[(it + 1) & 1] = 0u;
+    }
+    for (int i = 0; i < ctl.n_inst; ++i) {
+      if (!active[i]) continue;
+      const Inst &I = insts[i];
+      const real *psi = as_c<real>(I.Psi);
+      const real *ss4 = as_c<real>(I.ss4);
+      const real *pold = as_c<real>((it & 1) ? I.phi1 : I.phi0);
+      real *pnew = as<real>((it & 1) ? I.phi0 : I.phi1);
+      real *sphi = as<real>(I.sphi);
+      const double *gamma = I.small + I.lay.gamma;
+      double dmax = 0.0, pmax = 0.0;
+      for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < I.N; c += gridDim.x * blockDim.x) {
+        real acc = real(0);
+        for (int j = 0; j < I.r; ++j) acc += real(gamma[j]) * psi[(size_t)I.N * j + c];
+        pnew[c] = acc;
+        sphi[c] = ss4[c] * acc;
+        dmax = fmax(dmax, fabs((double)acc - (double)pold[c]));
+        pmax = fmax(pmax, fabs((double)acc));
+      }
+      dmax = warp_max(dmax);
+      pmax = warp_max(pmax);
+      if ((threadIdx.x & 31) == 0) {
+        atomic_max_nonneg(I.conv + (it & 1) * 2 + 0, dmax);
+        atomic_max_nonneg(I.conv + (it & 1) * 2 + 1, pmax);
+      }
+    }
+    if (!grid_barrier(ctl.bar, abort_flag)) break;
+
+    // ---- phase C: every CTA takes the same decision per instance ----
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int i = 0; i < ctl.n_inst; ++i) {
+        if (!active[i]) continue;
+        const Inst &I = insts[i];
+        volatile unsigned long long *cv = I.conv + (it & 1) * 2;
+        const double d = __longlong_as_double((long long)cv[0]);
+        const double m = __longlong_as_double((long long)cv[1]);
+        const int done_iters = it + 1;
+        bool done;
+        if (I.fixed_iters > 0) {
+          done = done_iters >= I.fixed_iters;
+        } else {
+          done = d <= I.si_tol * m;
+          if (!done && done_iters >= I.max_iter) {
+            done = true;
+            if (blockIdx.x == 0) set_status(I.status, kENotConv);
+          }
+        }
+        if (done) {
+          active[i] = 0;
+          if (blockIdx.x == 0) {
+            *I.iters = done_iters;
+            atomicAdd(I.iters_total, (unsigned long long)done_iters);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // a wait that gave up marks every still-active instance
+  if (*abort_flag && blockIdx.x == 0 && threadIdx.x == 0) {
+    for (int i = 0; i < ctl.n_inst; ++i)
+      if (active[i]) set_status(insts[i].status, kETimeout);
+  }
+}
+
+// Resets the barrier, the unit counters and the convergence maxima of
+// iteration 0 before each source-iteration launch.
+__global__ void k_si_prep(const Inst *__restrict__ insts, int n, SiCtl ctl) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0) {
+    ctl.bar[0] = 0u;
+    ctl.work[0] = 0u;
+    ctl.work[1] = 0u;
+    *ctl.abort_flag = 0;
+  }
+  if (t < n) {
+    insts[t].conv[0] = 0ull;
+    insts[t].conv[1] = 0ull;
+  }
+}
+
+// Standalone sweeps (dlr_sweep): one CTA per direction.
+template <typename real>
+__global__ void __launch_bounds__(SweepCfg<real>::NW * 32)
+k_sweep_dirs(int nx, int ny, double hx, double hy, const double *dirs,
+             const double *psi_edge, const real *sig_t, const real *src, real *psi,
+             int nx_max, int *abort_flag) {
+  constexpr int NW = SweepCfg<real>::NW;
+  extern __shared__ __align__(16) unsigned char smem[];
+  using real2 = typename Real2<real>::type;
+  SweepSmem S;
+  S.tiles = smem;
+  size_t off = (size_t)NW * 2048 * sizeof(real2);
+  S.edge = smem + off;
+  off += (size_t)(NW + 1) * nx_max * sizeof(real);
+  S.prog = reinterpret_cast<int *>(smem + off);
+  S.nx_max = nx_max;
+  const int d = blockIdx.x;
+  const double ox = dirs[2 * d], oy = dirs[2 * d + 1];
+  SweepArgs<real> A;
+  A.nx = nx;
+  A.ny = ny;
+  A.flipx = ox < 0;
+  A.flipy = oy < 0;
+  A.ax = real(fabs(ox) / hx);
+  A.ay = real(fabs(oy) / hy);
+  A.in_x = real(ox > 0 ? psi_edge[0] : (ox < 0 ? psi_edge[1] : 0.0));
+  A.in_y = real(oy > 0 ? psi_edge[2] : (oy < 0 ? psi_edge[3] : 0.0));
+  A.sig_t = sig_t;
+  A.src = src + (size_t)nx * ny * d;
+  A.sphi = nullptr;
+  A.psi = psi + (size_t)nx * ny * d;
+  sweep_unit<real, NW>(A, S, abort_flag);
+}
+
+// ------------------------------------------------------------------
+// host-side launch helpers
+// ------------------------------------------------------------------
+
+cudaError_t launch_si_prep(const Inst *d, int n, SiCtl ctl, cudaStream_t st) {
+  k_si_prep<<<(n + 255) / 256, 256, 0, st>>>(d, n, ctl);
+  return cudaGetLastError();
+}
+
+template <typename real>
+size_t si_smem_bytes(int nx_max, int bands_max, int n_inst) {
+  constexpr int NW = SweepCfg<real>::NW;
+  using real2 = typename Real2<real>::type;
+  return (size_t)NW * 2048 * sizeof(real2) + (size_t)(NW + 1) * nx_max * sizeof(real) +
+         (size_t)bands_max * sizeof(int) + (size_t)n_inst * sizeof(int);
+}
+
+template <typename real>
+cudaError_t launch_si(const Inst *d_insts, const SiCtl &ctl, int grid, cudaStream_t st) {
+  constexpr int NW = SweepCfg<real>::NW;
+  size_t smem = si_smem_bytes<real>(ctl.nx_max, ctl.bands_max, ctl.n_inst);
+  cudaError_t e = cudaFuncSetAttribute(k_si<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(NW * 32);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_si<real>, d_insts, ctl);
+}
+
+template <typename real>
+int si_max_grid(int nx_max, int bands_max, int n_inst) {
+  constexpr int NW = SweepCfg<real>::NW;
+  size_t smem = si_smem_bytes<real>(nx_max, bands_max, n_inst);
+  if (cudaFuncSetAttribute(k_si<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return 0;
+  int per_sm = 0, dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_si<real>, NW * 32, smem) !=
+      cudaSuccess)
+    return 0;
+  return per_sm * sms;
+}
+
+template <typename real>
+cudaError_t launch_sweep_dirs(int nx, int ny, double hx, double hy, int n_dir,
+                              const double *d_dirs, const double *d_edge, const real *sig_t,
+                              const real *src, real *psi, int *d_abort, cudaStream_t st) {
+  constexpr int NW = SweepCfg<real>::NW;
+  const int bands = (ny + 31) / 32;
+  size_t smem = si_smem_bytes<real>(nx, bands, 0);
+  cudaError_t e = cudaFuncSetAttribute(k_sweep_dirs<real>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_sweep_dirs<real><<<n_dir, NW * 32, smem, st>>>(nx, ny, hx, hy, d_dirs, d_edge, sig_t, src,
+                                                   psi, nx, d_abort);
+  return cudaGetLastError();
+}
+
+template size_t si_smem_bytes<float>(int, int, int);
+template size_t si_smem_bytes<double>(int, int, int);
+template cudaError_t launch_si<float>(const Inst *, const SiCtl &, int, cudaStream_t);
+template cudaError_t launch_si<double>(const Inst *, const SiCtl &, int, cudaStream_t);
+template int si_max_grid<float>(int, int, int);
+template int si_max_grid<double>(int, int, int);
+template cudaError_t launch_sweep_dirs<float>(int, int, double, double, int, const double *,
+                                              const double *, const float *, const float *,
+                                              float *, int *, cudaStream_t);
+template cudaError_t launch_sweep_dirs<double>(int, int, double, double, int, const double *,
+                                               const double *, const double *, const double *,
+                                               double *, int *, cudaStream_t);
+
+}  // namespace dlr
