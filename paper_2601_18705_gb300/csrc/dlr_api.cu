@@ -33,6 +33,7 @@ cudaError_t launch_sweep_dirs(int, int, double, double, int, const double *, con
                               const real *, const real *, real *, int *, cudaStream_t);
 template <typename real> cudaError_t launch_coeff_recon(const Inst *, int, int, int, cudaStream_t);
 template <typename real> cudaError_t launch_tsgram(const GramJob *, int, int, cudaStream_t);
+template <typename real> cudaError_t launch_fill(const FillJob *, int, int, cudaStream_t);
 template <typename rin, typename rout>
 cudaError_t launch_apply(const ApplyJob *, int, int, int, cudaStream_t);
 template <typename real> cudaError_t launch_project(const Inst *, int, int, cudaStream_t);
@@ -138,9 +139,10 @@ struct Batch {
   int maxN = 0, maxK = 0, rmax = 0, pbmax = 1, pblmax = 1, lbmax = 1;
   int nx_max = 0, bands_max = 0, si_grid = 0;
   SiCtl ctl{};
-  GramJob *g_psi1, *g_x, *g_l1, *g_w;
+  GramJob *g_psi1, *g_psire, *g_x, *g_x3, *g_l1, *g_lf, *g_w, *g_w3, *g_cross;
+  FillJob *f_psi, *f_l;
   ApplyJob *a_psi, *a_x2, *a_x3, *a_l1, *a_w2, *a_w3, *a_wv;
-  CholJob *c_p1, *c_p2, *c_p3, *c_l1, *c_l2, *c_l3;
+  CholJob *c_p1, *c_p1b, *c_p2, *c_p3, *c_l1, *c_l1b, *c_l2, *c_l3;
   ReduceJob *r_proj;
   cudaGraphExec_t pre = nullptr, post = nullptr;
 };
@@ -348,7 +350,7 @@ static Sizes sizes_of(const dlr_problem *p, int sms) {
   t += 6 * al((size_t)s.N * s.rs);              // sig_t, ss4, q, phi0, phi1, sphi
   t += 4 * al((size_t)s.N * r * s.rs);          // X0, X, Psi, s0
   t += 3 * al((size_t)s.K * 8);                 // ox, oy, w
-  t += 2 * al((size_t)s.K * r * 8);             // W0, L
+  t += 3 * al((size_t)s.K * r * 8);             // W0, L, Lf
   t += al(r * r * 8) + al(r * 4);               // S0, idx
   t += al((size_t)small_layout(s.r).total * 8); // small
   t += al((size_t)s.K * r * r * 8) + al((size_t)s.K * r * 4);  // lu, piv
@@ -503,6 +505,7 @@ int dlr_create(const dlr_problem *problem, const dlr_runtime *runtime, dlr_handl
   I.w = dw;
   I.W0 = (double *)A((size_t)K * r * 8);
   I.L = (double *)A((size_t)K * r * 8);
+  I.Lf = (double *)A((size_t)K * r * 8);
   I.S0 = (double *)A((size_t)r * r * 8);
   I.idx = (int *)A((size_t)r * 4);
   I.small = (double *)A((size_t)I.lay.total * 8);
@@ -510,6 +513,7 @@ int dlr_create(const dlr_problem *problem, const dlr_runtime *runtime, dlr_handl
   I.piv = (int *)A((size_t)K * r * 4);
   I.partials = (double *)A(sz.partial_doubles * 8);
   I.partial_blocks = h->pb;
+  I.angle_blocks = h->pbl;
   I.lstep_blocks = h->lb;
   I.status = (int *)A(64);
   I.iters = (int *)A(64);
@@ -629,8 +633,8 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   size_t bytes = 0;
   auto sz = [](size_t s) { return (s + 255) & ~size_t(255); };
   bytes += sz(sizeof(Inst) * n);
-  bytes += 4 * sz(sizeof(GramJob) * n) + 7 * sz(sizeof(ApplyJob) * n) + 6 * sz(sizeof(CholJob) * n) +
-           sz(sizeof(ReduceJob) * n);
+  bytes += 9 * sz(sizeof(GramJob) * n) + 2 * sz(sizeof(FillJob) * n) + 7 * sz(sizeof(ApplyJob) * n) +
+           8 * sz(sizeof(CholJob) * n) + sz(sizeof(ReduceJob) * n);
   bytes += sz(sizeof(int2) * units.size()) + sz(64) * 3;
   if (cudaMalloc(&b->d_mem, bytes) != cudaSuccess) {
     delete b;
@@ -639,9 +643,16 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   char *cur = (char *)b->d_mem;
   b->d_insts = carve<Inst>(cur, n);
   b->g_psi1 = carve<GramJob>(cur, n);
+  b->g_psire = carve<GramJob>(cur, n);
   b->g_x = carve<GramJob>(cur, n);
+  b->g_x3 = carve<GramJob>(cur, n);
   b->g_l1 = carve<GramJob>(cur, n);
+  b->g_lf = carve<GramJob>(cur, n);
   b->g_w = carve<GramJob>(cur, n);
+  b->g_w3 = carve<GramJob>(cur, n);
+  b->g_cross = carve<GramJob>(cur, n);
+  b->f_psi = carve<FillJob>(cur, n);
+  b->f_l = carve<FillJob>(cur, n);
   b->a_psi = carve<ApplyJob>(cur, n);
   b->a_x2 = carve<ApplyJob>(cur, n);
   b->a_x3 = carve<ApplyJob>(cur, n);
@@ -650,9 +661,11 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   b->a_w3 = carve<ApplyJob>(cur, n);
   b->a_wv = carve<ApplyJob>(cur, n);
   b->c_p1 = carve<CholJob>(cur, n);
+  b->c_p1b = carve<CholJob>(cur, n);
   b->c_p2 = carve<CholJob>(cur, n);
   b->c_p3 = carve<CholJob>(cur, n);
   b->c_l1 = carve<CholJob>(cur, n);
+  b->c_l1b = carve<CholJob>(cur, n);
   b->c_l2 = carve<CholJob>(cur, n);
   b->c_l3 = carve<CholJob>(cur, n);
   b->r_proj = carve<ReduceJob>(cur, n);
@@ -667,9 +680,10 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   b->ctl.bands_max = b->bands_max;
   // host copies of the job tables
   std::vector<Inst> insts(n);
-  std::vector<GramJob> gp1(n), gx(n), gl1(n), gw(n);
+  std::vector<GramJob> gp1(n), gpre(n), gx(n), gx3(n), gl1(n), glf(n), gw(n), gw3(n), gcr(n);
+  std::vector<FillJob> fp(n), fl(n);
   std::vector<ApplyJob> ap(n), ax2(n), ax3(n), al1(n), aw2(n), aw3(n), awv(n);
-  std::vector<CholJob> cp1(n), cp2(n), cp3(n), cl1(n), cl2(n), cl3(n);
+  std::vector<CholJob> cp1(n), cp1b(n), cp2(n), cp3(n), cl1(n), cl1b(n), cl2(n), cl3(n);
   std::vector<ReduceJob> rp(n);
   for (int i = 0; i < n; ++i) {
     const dlr_handle *h = hs[i];
@@ -686,9 +700,25 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
       return g;
     };
     gp1[i] = gram(I.Psi, nullptr, N, N, 0, h->pb, nullptr);
+    gpre[i] = gram(I.Psi, nullptr, N, N, 0, h->pb, flag + 1);
     gx[i] = gram(I.X, nullptr, N, N, 0, h->pb, nullptr);
     gl1[i] = gram(I.L, I.w, K, r, 1, h->pbl, nullptr);
+    glf[i] = gram(I.Lf, I.w, K, r, 1, h->pbl, flag + 1);
     gw[i] = gram(I.W0, nullptr, K, K, 0, h->pbl, nullptr);
+    gcr[i] = gram(I.L, I.w, K, r, 1, h->pbl, nullptr);
+    gcr[i].B = I.W0;
+    gcr[i].ldb = K;
+    gcr[i].sqrt_wt = 1;
+    // the third-pass Grams run only when the first passes were shifted
+    gx3[i] = gram(I.X, nullptr, N, N, 0, h->pb, flag);
+    gw3[i] = gram(I.W0, nullptr, K, K, 0, h->pbl, flag);
+    auto fill = [&](void *A, const void *src, int m, int lda, int layout) {
+      FillJob f{};
+      f.A = A; f.src = src; f.m = m; f.r = r; f.lda = lda; f.layout = layout; f.flag = flag;
+      return f;
+    };
+    fp[i] = fill(I.Psi, nullptr, N, N, 0);
+    fl[i] = fill(I.Lf, I.L, K, r, 1);
     auto apply = [&](const void *A, int layout, int lda, const double *s_in, int sq_in, const double *T,
                      void *outp, int ldo, const double *s_out, int inv_sq, int m, const int *run_if) {
       ApplyJob a{};
@@ -700,22 +730,25 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
     ap[i] = apply(I.Psi, 0, N, nullptr, 0, sm + L.R1i, I.X, N, nullptr, 0, N, nullptr);
     ax2[i] = apply(I.X, 0, N, nullptr, 0, sm + L.R2i, I.X, N, nullptr, 0, N, nullptr);
     ax3[i] = apply(I.X, 0, N, nullptr, 0, sm + L.R3i, I.X, N, nullptr, 0, N, flag);
-    al1[i] = apply(I.L, 1, r, I.w, 1, sm + L.R1i, I.W0, K, nullptr, 0, K, nullptr);
+    al1[i] = apply(I.Lf, 1, r, I.w, 1, sm + L.R1i, I.W0, K, nullptr, 0, K, nullptr);
     aw2[i] = apply(I.W0, 0, K, nullptr, 0, sm + L.R2i, I.W0, K, nullptr, 0, K, nullptr);
     aw3[i] = apply(I.W0, 0, K, nullptr, 0, sm + L.R3i, I.W0, K, nullptr, 0, K, flag);
     awv[i] = apply(I.W0, 0, K, nullptr, 0, sm + L.V, I.W0, K, I.w, 1, K, nullptr);
-    auto chol = [&](int nb, double scale, double *R, double *Ri, int pass, double m) {
+    const double u = h->mixed ? 1e-7 : 1e-15, tau = h->mixed ? 1e-10 : 1e-24;
+    auto chol = [&](int nb, double scale, double *R, double *Ri, int mode) {
       CholJob c{};
       c.part = I.partials; c.nblocks = nb; c.scale = scale; c.R = R; c.Ri = Ri;
-      c.flag = flag; c.r = r; c.pass = pass; c.m_rows = m;
+      c.flag = flag; c.r = r; c.mode = mode; c.u = u; c.tau_dep = tau;
       return c;
     };
-    cp1[i] = chol(h->pb, I.h2, sm + L.R1, sm + L.R1i, 1, N);
-    cp2[i] = chol(h->pb, I.h2, sm + L.R2, sm + L.R2i, 2, N);
-    cp3[i] = chol(h->pb, I.h2, sm + L.R3, sm + L.R3i, 3, N);
-    cl1[i] = chol(h->pbl, 1.0, sm + L.R1, sm + L.R1i, 1, K);
-    cl2[i] = chol(h->pbl, 1.0, sm + L.R2, sm + L.R2i, 2, K);
-    cl3[i] = chol(h->pbl, 1.0, sm + L.R3, sm + L.R3i, 3, K);
+    cp1[i] = chol(h->pb, I.h2, sm + L.R1, sm + L.R1i, 1);
+    cp1b[i] = chol(h->pb, I.h2, sm + L.R1, sm + L.R1i, 4);
+    cp2[i] = chol(h->pb, I.h2, sm + L.R2, sm + L.R2i, 2);
+    cp3[i] = chol(h->pb, I.h2, sm + L.R3, sm + L.R3i, 3);
+    cl1[i] = chol(h->pbl, 1.0, sm + L.R1, sm + L.R1i, 1);
+    cl1b[i] = chol(h->pbl, 1.0, sm + L.R1, sm + L.R1i, 4);
+    cl2[i] = chol(h->pbl, 1.0, sm + L.R2, sm + L.R2i, 2);
+    cl3[i] = chol(h->pbl, 1.0, sm + L.R3, sm + L.R3i, 3);
     ReduceJob red{};
     red.part = I.partials; red.nblocks = h->pb; red.stride = proj_count(r);
     red.count = proj_count(r); red.out = sm + L.G; red.scale = 1.0;
@@ -729,9 +762,16 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   cudaStreamSynchronize(b->st);
   chain(upv(b->d_insts, insts.data(), sizeof(Inst) * n));
   chain(upv(b->g_psi1, gp1.data(), sizeof(GramJob) * n));
+  chain(upv(b->g_psire, gpre.data(), sizeof(GramJob) * n));
   chain(upv(b->g_x, gx.data(), sizeof(GramJob) * n));
+  chain(upv(b->g_x3, gx3.data(), sizeof(GramJob) * n));
   chain(upv(b->g_l1, gl1.data(), sizeof(GramJob) * n));
+  chain(upv(b->g_lf, glf.data(), sizeof(GramJob) * n));
   chain(upv(b->g_w, gw.data(), sizeof(GramJob) * n));
+  chain(upv(b->g_w3, gw3.data(), sizeof(GramJob) * n));
+  chain(upv(b->g_cross, gcr.data(), sizeof(GramJob) * n));
+  chain(upv(b->f_psi, fp.data(), sizeof(FillJob) * n));
+  chain(upv(b->f_l, fl.data(), sizeof(FillJob) * n));
   chain(upv(b->a_psi, ap.data(), sizeof(ApplyJob) * n));
   chain(upv(b->a_x2, ax2.data(), sizeof(ApplyJob) * n));
   chain(upv(b->a_x3, ax3.data(), sizeof(ApplyJob) * n));
@@ -740,9 +780,11 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   chain(upv(b->a_w3, aw3.data(), sizeof(ApplyJob) * n));
   chain(upv(b->a_wv, awv.data(), sizeof(ApplyJob) * n));
   chain(upv(b->c_p1, cp1.data(), sizeof(CholJob) * n));
+  chain(upv(b->c_p1b, cp1b.data(), sizeof(CholJob) * n));
   chain(upv(b->c_p2, cp2.data(), sizeof(CholJob) * n));
   chain(upv(b->c_p3, cp3.data(), sizeof(CholJob) * n));
   chain(upv(b->c_l1, cl1.data(), sizeof(CholJob) * n));
+  chain(upv(b->c_l1b, cl1b.data(), sizeof(CholJob) * n));
   chain(upv(b->c_l2, cl2.data(), sizeof(CholJob) * n));
   chain(upv(b->c_l3, cl3.data(), sizeof(CholJob) * n));
   chain(upv(b->r_proj, rp.data(), sizeof(ReduceJob) * n));
@@ -792,14 +834,19 @@ static int enqueue_post(Batch *b) {
   const Inst *d = b->d_insts;
   const int n = b->n;
   cudaStream_t st = b->st;
-  // step 5: CholeskyQR of Psi (two passes, a third when pass 1 was shifted)
+  // step 5: CholeskyQR of Psi; dependent columns are replaced by
+  // pseudo-random ones (orthonormal completion) and the pass redone; a third
+  // pass runs when a Cholesky needed a shift
   CK(launch_tsgram<real>(b->g_psi1, n, b->pbmax, st));
   CK(launch_chol(b->c_p1, d, n, st));
+  CK(launch_fill<real>(b->f_psi, n, b->maxN, st));
+  CK(launch_tsgram<real>(b->g_psire, n, b->pbmax, st));
+  CK(launch_chol(b->c_p1b, d, n, st));
   CK((launch_apply<real, real>(b->a_psi, n, b->maxN, b->rmax, st)));
   CK(launch_tsgram<real>(b->g_x, n, b->pbmax, st));
   CK(launch_chol(b->c_p2, d, n, st));
   CK((launch_apply<real, real>(b->a_x2, n, b->maxN, b->rmax, st)));
-  CK(launch_tsgram<real>(b->g_x, n, b->pbmax, st));
+  CK(launch_tsgram<real>(b->g_x3, n, b->pbmax, st));
   CK(launch_chol(b->c_p3, d, n, st));
   CK((launch_apply<real, real>(b->a_x3, n, b->maxN, b->rmax, st)));
   // steps 6-7: projections and the L-step
@@ -807,16 +854,21 @@ static int enqueue_post(Batch *b) {
   CK(launch_reduce(b->r_proj, n, proj_count(b->rmax), st));
   CK(launch_proj_post(d, n, st));
   CK(launch_lstep(d, n, b->rmax, b->lbmax, st));
-  // step 8: CholeskyQR of diag(sqrt w) L^T into W0, SVD of S, W0 <- W V
+  // step 8: CholeskyQR of M = diag(sqrt w) L^T into Q (held in W0), S = M^T Q,
+  // SVD of S, W0 <- diag(1/sqrt w) Q V
   CK(launch_tsgram<double>(b->g_l1, n, b->pblmax, st));
   CK(launch_chol(b->c_l1, d, n, st));
+  CK(launch_fill<double>(b->f_l, n, b->maxK, st));
+  CK(launch_tsgram<double>(b->g_lf, n, b->pblmax, st));
+  CK(launch_chol(b->c_l1b, d, n, st));
   CK((launch_apply<double, double>(b->a_l1, n, b->maxK, b->rmax, st)));
   CK(launch_tsgram<double>(b->g_w, n, b->pblmax, st));
   CK(launch_chol(b->c_l2, d, n, st));
   CK((launch_apply<double, double>(b->a_w2, n, b->maxK, b->rmax, st)));
-  CK(launch_tsgram<double>(b->g_w, n, b->pblmax, st));
+  CK(launch_tsgram<double>(b->g_w3, n, b->pblmax, st));
   CK(launch_chol(b->c_l3, d, n, st));
   CK((launch_apply<double, double>(b->a_w3, n, b->maxK, b->rmax, st)));
+  CK(launch_tsgram<double>(b->g_cross, n, b->pblmax, st));
   CK(launch_svd(d, n, st));
   CK((launch_apply<double, double>(b->a_wv, n, b->maxK, b->rmax, st)));
   CK(launch_sign(d, n, b->maxK, st));

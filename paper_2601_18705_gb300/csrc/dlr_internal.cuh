@@ -32,7 +32,7 @@ constexpr int kENonPos = -6;
 struct SmallLayout {
   int What, WLU, beta, gamma, C0;      // angle selection
   int R1, R1i, R2, R2i, R3, R3i;       // CholeskyQR factors / inverses
-  int qr_flag;                         // 1 if a third CholeskyQR pass runs
+  int qr_flag;    // ints: [0] third pass needed, [1] filled columns, [2..] mask
   int G, Nx, Ny, Mt, Ms, P, vec;       // projections (vec: qh, bL, bR, bB, bT)
   int Axp, Axm, Ayp, Aym, PS0;         // L-step operators
   int Cbar, zeta, Lbar, tvec;          // C-bar device
@@ -46,7 +46,7 @@ inline SmallLayout small_layout(int r) {
   auto m = [&](int n) { int at = o; o += n; return at; };
   s.What = m(r * r); s.WLU = m(r * r); s.beta = m(r); s.gamma = m(r); s.C0 = m(r * r);
   s.R1 = m(r * r); s.R1i = m(r * r); s.R2 = m(r * r); s.R2i = m(r * r);
-  s.R3 = m(r * r); s.R3i = m(r * r); s.qr_flag = m(2);
+  s.R3 = m(r * r); s.R3i = m(r * r); s.qr_flag = m(20);
   s.G = m(r * r); s.Nx = m(r * r); s.Ny = m(r * r); s.Mt = m(r * r); s.Ms = m(r * r);
   s.P = m(r * r); s.vec = m(5 * r);
   s.Axp = m(r * r); s.Axm = m(r * r); s.Ayp = m(r * r); s.Aym = m(r * r); s.PS0 = m(r * r);
@@ -76,6 +76,7 @@ struct Inst {
   const double *ox, *oy, *w;
   // factors, FP64
   double *W0, *S0, *L;
+  double *Lf;              // L with dependent rows replaced (QR input)
   // angle selection
   int *idx;
   // r x r work space and per-angle LU
@@ -86,6 +87,7 @@ struct Inst {
   // partial sums of block reductions (partial_stride doubles per block)
   double *partials;
   int partial_blocks;      // blocks of the cell reductions (project, Gram)
+  int angle_blocks;        // blocks of the angle reductions (Grams of L)
   int lstep_blocks;        // blocks of the per-angle L-step
   // status and iteration bookkeeping
   int *status;            // sticky device status
@@ -101,6 +103,9 @@ struct GramJob {
   const void *A;
   const double *wt;
   int m, r, lda, layout;
+  const void *B;    // optional: cross Gram sum wt a b^T with B (layout 0, ldb)
+  int ldb;
+  int sqrt_wt;      // 1: weight sqrt(wt) instead of wt
   double *out;      // partial sums
   int nblocks;      // blocks used for this job
   const int *run_if;  // optional: skip unless *run_if != 0
@@ -134,10 +139,20 @@ struct CholJob {
   int nblocks;
   double scale;
   double *R, *Ri;
-  int *flag;
+  int *flag;        // ints: [0] third pass needed, [1] filled columns, [2..] mask
   int r;
-  int pass;
-  double m_rows;   // rows of the tall matrix (for the shift size)
+  int mode;         // 1 detect, 2 plain, 3 only if flag[0], 4 only if flag[1]
+  double u;         // relative size of the shift (data precision)
+  double tau_dep;   // a column whose residual^2 falls below tau_dep |col|^2 is dependent
+};
+
+// Copies a tall-skinny matrix (optionally) and replaces the columns marked
+// dependent by deterministic pseudo-random ones (orthonormal completion).
+struct FillJob {
+  void *A;          // matrix to fill (layout as in GramJob)
+  const void *src;  // if non-null: copy src into A first (same layout)
+  int m, r, lda, layout;
+  const int *flag;  // CholJob flag block
 };
 
 struct SiCtl {

@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(kTB) k_tsgram(const GramJob *__restrict__ jobs
   const GramJob J = jobs[blockIdx.y];
   if ((int)blockIdx.x >= J.nblocks || (J.run_if && *J.run_if == 0)) return;
   __shared__ real tile[kChunk / 8][33];  // 32 rows x r columns
+  __shared__ real tileb[kChunk / 8][33];
   __shared__ real wts[kChunk / 8];
   const int r = J.r;
   const int t = threadIdx.x;
@@ -107,9 +108,18 @@ __global__ void __launch_bounds__(kTB) k_tsgram(const GramJob *__restrict__ jobs
         if (row < J.m) v = J.layout == 0 ? A[(size_t)J.lda * i + row] : A[(size_t)r * row + i];
         tile[rr][i] = v;
       }
+      if (J.B) {
+        const real *Bm = as_c<real>(J.B);
+        for (int e = t; e < 32 * r; e += blockDim.x) {
+          const int rr = e & 31, i = e >> 5, row = row0 + rr;
+          tileb[rr][i] = row < J.m ? Bm[(size_t)J.ldb * i + row] : real(0);
+        }
+      }
       if (t < 32) {
         const int row = row0 + t;
-        wts[t] = (row < J.m) ? (J.wt ? real(J.wt[row]) : real(1)) : real(0);
+        double wv = (row < J.m) ? (J.wt ? J.wt[row] : 1.0) : 0.0;
+        if (J.sqrt_wt) wv = sqrt(wv);
+        wts[t] = real(wv);
       }
       __syncthreads();
       if (own) {
@@ -117,7 +127,8 @@ __global__ void __launch_bounds__(kTB) k_tsgram(const GramJob *__restrict__ jobs
         for (int rr = 0; rr < 32; ++rr) {
           const real w = wts[rr];
           const real a0 = tile[rr][ti] * w, a1 = tile[rr][ti + 1] * w;
-          const real b0 = tile[rr][tj], b1 = tile[rr][tj + 1];
+          const real b0 = J.B ? tileb[rr][tj] : tile[rr][tj];
+          const real b1 = J.B ? tileb[rr][tj + 1] : tile[rr][tj + 1];
           s[0] += a0 * b0; s[1] += a1 * b0; s[2] += a0 * b1; s[3] += a1 * b1;
         }
       }
@@ -131,6 +142,33 @@ __global__ void __launch_bounds__(kTB) k_tsgram(const GramJob *__restrict__ jobs
     if (ti + 1 < r && tj < r) o[ti + 1 + r * tj] = acc[1];
     if (ti < r && tj + 1 < r) o[ti + r * (tj + 1)] = acc[2];
     if (ti + 1 < r && tj + 1 < r) o[ti + 1 + r * (tj + 1)] = acc[3];
+  }
+}
+
+// ------------------------------------------------------------------
+// orthonormal completion: dependent columns replaced by pseudo-random ones
+// ------------------------------------------------------------------
+__device__ __forceinline__ double hash_uniform(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  x ^= x >> 31;
+  return (double)(x >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+template <typename real>
+__global__ void __launch_bounds__(256) k_fill(const FillJob *__restrict__ jobs) {
+  const FillJob J = jobs[blockIdx.y];
+  const int nfill = J.flag[1];
+  if (!J.src && nfill == 0) return;
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= J.m) return;
+  real *A = as<real>(J.A);
+  const real *S = as_c<real>(J.src);
+  for (int j = 0; j < J.r; ++j) {
+    const size_t at = J.layout == 0 ? (size_t)J.lda * j + row : (size_t)J.r * row + j;
+    if (nfill && J.flag[2 + j]) A[at] = real(hash_uniform(((unsigned long long)j << 40) ^ (unsigned long long)row));
+    else if (S) A[at] = S[at];
   }
 }
 
@@ -366,6 +404,12 @@ cudaError_t launch_tsgram(const GramJob *d_jobs, int n, int maxblocks, cudaStrea
   return cudaGetLastError();
 }
 
+template <typename real>
+cudaError_t launch_fill(const FillJob *d_jobs, int n, int maxm, cudaStream_t st) {
+  k_fill<real><<<dim3((maxm + 255) / 256, n), 256, 0, st>>>(d_jobs);
+  return cudaGetLastError();
+}
+
 template <typename rin, typename rout>
 cudaError_t launch_apply(const ApplyJob *d_jobs, int n, int maxm, int r, cudaStream_t st) {
   dim3 g((maxm + 127) / 128, n);
@@ -399,6 +443,8 @@ template cudaError_t launch_coeff_recon<float>(const Inst *, int, int, int, cuda
 template cudaError_t launch_coeff_recon<double>(const Inst *, int, int, int, cudaStream_t);
 template cudaError_t launch_tsgram<float>(const GramJob *, int, int, cudaStream_t);
 template cudaError_t launch_tsgram<double>(const GramJob *, int, int, cudaStream_t);
+template cudaError_t launch_fill<float>(const FillJob *, int, int, cudaStream_t);
+template cudaError_t launch_fill<double>(const FillJob *, int, int, cudaStream_t);
 template cudaError_t launch_apply<float, float>(const ApplyJob *, int, int, int, cudaStream_t);
 template cudaError_t launch_apply<double, double>(const ApplyJob *, int, int, int, cudaStream_t);
 template cudaError_t launch_project<float>(const Inst *, int, int, cudaStream_t);

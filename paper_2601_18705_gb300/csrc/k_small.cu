@@ -4,7 +4,7 @@
 //                  or the greedy DEIM of Section 4.2), What, beta, gamma =
 //                  What^{-T} beta, C0 = S0 What^T
 //   k_chol         Cholesky of a reduced Gram (one CholeskyQR pass of steps 5
-//                  and 8), shifted when the Gram is numerically singular
+//                  and 8); detects dependent columns, shifts when needed
 //   k_proj_post    step 7 Galerkin operators from the reduced projections
 //   k_lstep_angle  step 7 per angle: B_k = |ox| A_x + |oy| A_y + M_t, LU with
 //                  partial pivoting (one warp per angle, one lane per column),
@@ -12,7 +12,7 @@
 //                  C-bar device of Section 3.3)
 //   k_lstep_mid    (I - Cbar M_s / 4pi) Lbar = zeta
 //   k_lstep_back   L_k = B_k^{-1} (Q_k + M_s Lbar / 4pi)
-//   k_svd          step 8: S = R^T, one-sided Jacobi SVD S = U Sigma V^T
+//   k_svd          step 8: S = M^T Q, one-sided Jacobi SVD S = U Sigma V^T
 //   k_sign         sign of each W column: its largest-magnitude entry > 0
 #include "dlr_internal.cuh"
 
@@ -239,29 +239,39 @@ __global__ void __launch_bounds__(256) k_select(const Inst *__restrict__ insts) 
 }
 
 // ------------------------------------------------------------------
-// Cholesky of G = scale * sum_b part[b] (r x r): R upper with R^T R = G
-// (+ shift), Ri = R^{-1}.  pass: 1, 2 or 3.  *flag is cleared by pass 1 and
-// set when pass 1 or 2 needed a shift; pass 3 runs only if *flag (else it
-// writes R = Ri = I and the pass-3 apply kernels skip).
+// One CholeskyQR pass on G = scale * sum_b part[b] (r x r): R upper with
+// R^T R = G (+ shift), Ri = R^{-1}.  Modes:
+//   1 first pass: unshifted Cholesky that also detects dependent columns
+//     (residual^2 < tau_dep |column|^2).  Dependent columns are marked in
+//     flag[2 + j] and counted in flag[1] (they are then replaced by
+//     pseudo-random columns and the pass is redone in mode 4).  Without
+//     dependent columns a failed pivot falls back to a shifted Cholesky
+//     (shifted CholeskyQR) and sets flag[0] (a third pass is needed).
+//   2 always: Cholesky, shifted if needed (sets flag[0] when shifted)
+//   3 only if flag[0]; otherwise R = Ri = I
+//   4 only if flag[1] (after the fill); as mode 2
 // ------------------------------------------------------------------
-
 __global__ void __launch_bounds__(256) k_chol(const CholJob *__restrict__ jobs,
                                               const Inst *__restrict__ insts) {
   const CholJob J = jobs[blockIdx.x];
   const Inst &I = insts[blockIdx.x];
   if (*I.status != kOk) return;
   __shared__ double G[32 * 32], C[32 * 32];
-  __shared__ int fail_s;
+  __shared__ int fail_s, ndep_s;
+  __shared__ int dep[32];
   const int r = J.r;
-  if (J.pass == 3 && *J.flag == 0) {
-    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-      const double d = (e % r == e / r) ? 1.0 : 0.0;
-      J.R[e] = d;
-      J.Ri[e] = d;
-    }
+  int *flag = J.flag;
+  const bool run = J.mode == 1 || J.mode == 2 || (J.mode == 3 && flag[0] != 0) ||
+                   (J.mode == 4 && flag[1] != 0);
+  if (!run) {
+    if (J.mode == 3)
+      for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+        const double d = (e % r == e / r) ? 1.0 : 0.0;
+        J.R[e] = d;
+        J.Ri[e] = d;
+      }
     return;
   }
-  if (J.pass == 1 && threadIdx.x == 0) *J.flag = 0;
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     double s = 0.0;
     for (int b = 0; b < J.nblocks; ++b) s += J.part[(size_t)b * r * r + e];
@@ -271,33 +281,47 @@ __global__ void __launch_bounds__(256) k_chol(const CholJob *__restrict__ jobs,
   // symmetrise (the partial sums fill both triangles)
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     const int i = e % r, j = e / r;
-    if (i < j) {
-      const double a = 0.5 * (G[i + r * j] + G[j + r * i]);
-      C[i + r * j] = a;
-      C[j + r * i] = a;
-    } else if (i == j) {
-      C[e] = G[e];
-    }
+    C[e] = (i == j) ? G[e] : 0.5 * (G[i + r * j] + G[j + r * i]);
   }
   __syncthreads();
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) G[e] = C[e];
+  if (J.mode == 1 && threadIdx.x == 0) {
+    flag[0] = 0;
+    flag[1] = 0;
+  }
+  if (J.mode == 1 && threadIdx.x < 32) flag[2 + threadIdx.x] = 0;
   __syncthreads();
   double tr = 0.0;
   for (int i = 0; i < r; ++i) tr += G[i + r * i];
   double shift = 0.0;
-  for (int attempt = 0; attempt < 6; ++attempt) {
+  bool shifted = false;
+  for (int attempt = 0; attempt < 8; ++attempt) {
     for (int e = threadIdx.x; e < r * r; e += blockDim.x)
       C[e] = G[e] + ((e % r == e / r) ? shift : 0.0);
-    if (threadIdx.x == 0) fail_s = 0;
+    if (threadIdx.x < 32) dep[threadIdx.x] = 0;
+    if (threadIdx.x == 0) { fail_s = 0; ndep_s = 0; }
     __syncthreads();
+    const bool detect = J.mode == 1 && shift == 0.0;
     for (int p = 0; p < r; ++p) {
       if (threadIdx.x == 0) {
         const double d = C[p + r * p];
-        if (!(d > 1e-15 * tr)) fail_s = 1;
-        C[p + r * p] = sqrt(fmax(d, 1e-300));
+        if (detect && d <= J.tau_dep * G[p + r * p]) {
+          dep[p] = 1;
+          ++ndep_s;
+          C[p + r * p] = 1.0;
+        } else if (!(d > J.u * tr)) {
+          fail_s = 1;
+        } else {
+          C[p + r * p] = sqrt(d);
+        }
       }
       __syncthreads();
       if (fail_s) break;
+      if (dep[p]) {  // a dependent column: row p of R is e_p
+        for (int j = p + 1 + threadIdx.x; j < r; j += blockDim.x) C[p + r * j] = 0.0;
+        __syncthreads();
+        continue;
+      }
       const double dp = C[p + r * p];
       for (int j = p + 1 + threadIdx.x; j < r; j += blockDim.x) C[p + r * j] /= dp;
       __syncthreads();
@@ -308,13 +332,18 @@ __global__ void __launch_bounds__(256) k_chol(const CholJob *__restrict__ jobs,
       }
       __syncthreads();
     }
+    if (detect && ndep_s > 0) {
+      // mark the dependent columns; the pass is redone after the fill
+      if (threadIdx.x == 0) flag[1] = ndep_s;
+      if (threadIdx.x < r) flag[2 + threadIdx.x] = dep[threadIdx.x];
+      return;
+    }
     if (!fail_s) break;
-    // shifted Cholesky QR: s = 11 (m r + r (r+1)) u ||A||^2
-    shift = shift == 0.0 ? 11.0 * (J.m_rows * r + r * (r + 1.0)) * 1.1102230246251565e-16 * tr
-                         : shift * 100.0;
-    if (J.pass <= 2 && threadIdx.x == 0) *J.flag = 1;
+    shift = shift == 0.0 ? J.u * tr : shift * 100.0;
+    shifted = true;
     __syncthreads();
   }
+  if (shifted && threadIdx.x == 0) flag[0] = 1;
   // R = upper triangle of C
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     const int i = e % r, j = e / r;
@@ -641,39 +670,24 @@ __global__ void __launch_bounds__(kLsWarps * 32) k_lstep_back(const Inst *__rest
 }
 
 // ------------------------------------------------------------------
-// step 8: S = R^T with R = R3 R2 R1 (CholeskyQR of diag(sqrt w) L^T),
-// one-sided Jacobi SVD S = U Sigma V^T (descending), S0 <- Sigma, V and U
-// kept for W <- W V and X <- X U, vphi = L w.
+// step 8: with Q (in W0) the orthonormal factor of M = diag(sqrt w) L^T,
+// S = M^T Q (summed from the cross-Gram partials), so that L = S W^T with
+// W = diag(1/sqrt w) Q; one-sided Jacobi SVD S = U Sigma V^T (descending),
+// S0 <- Sigma, V and U kept for W <- W V and X <- X U, vphi = L w.
 // ------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_svd(const Inst *__restrict__ insts) {
   const Inst &I = insts[blockIdx.x];
   if (*I.status != kOk) return;
-  __shared__ double Rm[32 * 32], Tm[32 * 32], Uw[32 * 32], Vw[32 * 32], sv[32];
+  __shared__ double Uw[32 * 32], Vw[32 * 32], sv[32];
   __shared__ int ord[32];
   __shared__ int rot_s;
   const int r = I.r;
   const SmallLayout &L = I.lay;
-  // R = R3 R2 R1 : R1, R2 in small[R1], small[R2]; R3 in small[Tr]
-  const double *R1 = I.small + L.R1, *R2 = I.small + L.R2, *R3 = I.small + L.R3;
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-    const int i = e % r, j = e / r;
     double t = 0.0;
-    for (int l = 0; l < r; ++l) t += R2[i + r * l] * R1[l + r * j];
-    Tm[e] = t;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-    const int i = e % r, j = e / r;
-    double t = 0.0;
-    for (int l = 0; l < r; ++l) t += R3[i + r * l] * Tm[l + r * j];
-    Rm[e] = t;
-  }
-  __syncthreads();
-  // U := S = R^T, V := I
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-    const int i = e % r, j = e / r;
-    Uw[e] = Rm[j + r * i];
-    Vw[e] = (i == j) ? 1.0 : 0.0;
+    for (int b = 0; b < I.angle_blocks; ++b) t += I.partials[(size_t)b * r * r + e];
+    Uw[e] = t;  // S_ij = sum_k sqrt(w_k) L_ik Q_kj
+    Vw[e] = (e % r == e / r) ? 1.0 : 0.0;
   }
   __syncthreads();
   // one-sided Jacobi; each sweep visits all pairs in n-1 rounds of n/2
