@@ -1,0 +1,334 @@
+#!/usr/bin/env python3
+"""Benchmark of the SN-like DLR time step (Algorithm 1 of Haut et al.) on GB300.
+
+One "step" is one implicit DLR time step of the checker256 workload (256 x
+256 cells, 8x8 thick/thin opacity blocks, rank 16, 16 x 32 angles, left-edge
+inflow at T = 1): angle selection, collocation sweeps with source iteration,
+QR of Psi, projections, L-step, QR + SVD of L, temperature update, all in the
+library's kernels with the state resident in HBM.
+
+Printed JSON line (rank 0): cell-angle updates per second over the timed
+steps (whole job for N GPUs; each rank steps its own replica, weak scaling),
+the same measured through the public API with host buffers (e2e), DLR steps/s,
+the all-FP64 GPU path on the same steps, the roofline of the
+source-iteration kernel, the FP64 CPU oracle on a bounded sample, and SM
+clocks sampled during the timed region.  L2 is flushed between timed steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+METRIC = "cell-angle updates/s"
+WORKLOAD = "checker256"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="dlr", choices=["dlr", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="CPU work of the oracle sample")
+    return ap.parse_args()
+
+
+def case_config(case, precision):
+    return {"workload": f"{case['name']}: {case['nx']}x{case['ny']} cells, rank {case['r']}, "
+                        f"{case['n_polar']}x{case['n_azim']} angles, dt {case['dt']}",
+            "nx": case["nx"], "ny": case["ny"], "rank": case["r"],
+            "n_omega": case["n_polar"] * case["n_azim"], "precision": precision,
+            "l2": "flushed between timed steps (256 MiB write)",
+            "inputs": "resident in HBM (value); host buffers each step (e2e)"}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (every 50 ms) with host timestamps."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.samples = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(device), "-lms", "50"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.perf_counter(), [x.strip() for x in line.split(",")]))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        win = [s for t, s in self.samples if t0 <= t <= t1] or [s for _, s in self.samples[-3:]]
+        if not win:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(s[1]) for s in win if num(s[1]) is not None]
+        mx = [num(s[2]) for s in win if num(s[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in win for i in range(4)
+                          if len(s) > 5 + i and s[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(win)}
+
+
+# ---------------------------------------------------------------- CPU
+def oracle_rate(case, seconds: float, steps=None):
+    """FP64 CPU oracle, single thread: (updates/s, steps run, seconds)."""
+    import oracle
+    p = oracle.Problem(case["nx"], case["ny"], case["n_polar"], case["n_azim"], case["sigma"],
+                       case["rho_cv"], dt=case["dt"], c=case["c"], a_rad=case["a_rad"])
+    p.set_edge_temperatures(case["T_edge"])
+    T = case["T0"].reshape(-1).copy()
+    X, S, W = oracle.initial_factors(p, T, case["r"])
+    upd, n, t0 = 0, 0, time.perf_counter()
+    while True:
+        X, S, W, T, res = oracle.dlr_step(p, X, S, W, T)
+        upd += p.Nx * case["r"] * res.iters
+        n += 1
+        el = time.perf_counter() - t0
+        if (steps is not None and n >= steps) or (steps is None and el >= seconds):
+            break
+    return upd / el, n, el
+
+
+def run_reference(args):
+    """The oracle, as it stands, on the host cores (the base contract's
+    reference arm): W untimed steps, then K timed steps."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    case = workloads.checker256()
+    import oracle
+    p = oracle.Problem(case["nx"], case["ny"], case["n_polar"], case["n_azim"], case["sigma"],
+                       case["rho_cv"], dt=case["dt"], c=case["c"], a_rad=case["a_rad"])
+    p.set_edge_temperatures(case["T_edge"])
+    T = case["T0"].reshape(-1).copy()
+    X, S, W = oracle.initial_factors(p, T, case["r"])
+    for _ in range(args.warmup):
+        X, S, W, T, res = oracle.dlr_step(p, X, S, W, T)
+    upd, t0 = 0, time.perf_counter()
+    for _ in range(args.steps):
+        X, S, W, T, res = oracle.dlr_step(p, X, S, W, T)
+        upd += p.Nx * case["r"] * res.iters
+    el = time.perf_counter() - t0
+    v = upd / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": case_config(case, "fp64 (CPU oracle)"),
+            "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} DLR steps after {args.warmup} warm-up steps"},
+            "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------- GPU
+def timed_steps(dlr, torch, solver, K, flush):
+    """K steps, each timed with CUDA events on the solver's stream, L2 flushed
+    before each.  Returns (ms list)."""
+    st = solver.stream
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    for a, b in ev:
+        with torch.cuda.stream(st):
+            flush.fill_(1)
+        a.record(st)
+        solver.step(1)
+        b.record(st)
+    st.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def run_gpu(args):
+    import torch
+    import paper_2601_18705_gb300 as dlr
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    case = workloads.checker256()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    # ---- main (mixed precision) ----
+    solver = dlr.Solver(dlr.problem_from_case(case, precision=dlr.DLR_MIXED, allow_nonpositive=1))
+    solver.step(args.warmup)
+    solver.stream.synchronize()
+    s0 = solver.stats()
+    solver.set_timing(True)
+    clk = ClockSampler(local) if rank == 0 else None
+    time.sleep(0.15)
+    barrier()
+    tw0 = time.perf_counter()
+    ms = timed_steps(dlr, torch, solver, args.steps, flush)
+    barrier()
+    tw1 = time.perf_counter()
+    s1 = solver.stats()
+    total_ms = float(sum(ms))
+    updates = s1["cell_angle_updates"] - s0["cell_angle_updates"]
+    iters = s1["si_iters_total"] - s0["si_iters_total"]
+    si_ms = s1["ms_si_total"] - s0["ms_si_total"]
+    si_launch = s1["si_launches"] - s0["si_launches"]
+    launches = s1["kernel_launches"] - s0["kernel_launches"]
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        u = torch.tensor([float(updates)], device="cuda")
+        dist.all_reduce(u)
+        updates_all = float(u.item())
+    else:
+        updates_all = float(updates)
+    if clk:
+        time.sleep(0.1)
+        clk.stop()
+    value = updates_all / (total_ms / 1e3)
+    T_mixed = solver.T()
+    nonpos = solver.stats()["nonpositive_cells"]
+    solver.close()
+
+    # ---- e2e: public API with host buffers, copies inside the timed region ----
+    e2e = None
+    if not args.no_e2e:
+        s2 = dlr.Solver(dlr.problem_from_case(case, precision=dlr.DLR_MIXED, allow_nonpositive=1))
+        s2.step(args.warmup)
+        hostT = torch.empty(s2.N, dtype=torch.float64, pin_memory=True)
+        s2.T_into(hostT)
+        e0 = s2.stats()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            s2.set_T(hostT)          # H2D of the step's input temperature
+            s2.step(1)
+            s2.T_into(hostT)         # D2H of the step's result (synchronises)
+        barrier()
+        el = time.perf_counter() - t0
+        e1 = s2.stats()
+        s2.close()
+        eu = float(e1["cell_angle_updates"] - e0["cell_angle_updates"]) * world
+        e2e = {"value": eu / el, "unit": METRIC, "h2d_bytes_per_step": 8 * case["nx"] * case["ny"],
+               "d2h_bytes_per_step": 8 * case["nx"] * case["ny"]}
+
+    # ---- the all-FP64 GPU path on the same steps ----
+    fp64 = None
+    if not args.no_fp64 and rank == 0:
+        s3 = dlr.Solver(dlr.problem_from_case(case, precision=dlr.DLR_FP64, allow_nonpositive=1))
+        s3.step(args.warmup)
+        s3.stream.synchronize()
+        f0 = s3.stats()
+        ms64 = timed_steps(dlr, torch, s3, args.steps, flush)
+        f1 = s3.stats()
+        T64 = s3.T()
+        s3.close()
+        u64 = f1["cell_angle_updates"] - f0["cell_angle_updates"]
+        t64 = sum(ms64)
+        fp64 = {"value": u64 / (t64 / 1e3), "unit": METRIC, "ms_per_step": t64 / args.steps,
+                "dlr_steps_per_s": args.steps / (t64 / 1e3),
+                "mixed_vs_fp64_rel_l2_T": float(np.linalg.norm(T_mixed - T64) / np.linalg.norm(T64))}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    hbm, kind = peaks()
+    r = case["r"]
+    bytes_per_update = 4.0 + 16.0 / r  # fixed-source read + amortised per-cell terms (FP32)
+    per_launch_ms = si_ms / max(si_launch, 1)
+    per_launch_updates = updates / max(si_launch, 1)
+    achieved = per_launch_updates * bytes_per_update / (per_launch_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "kernel": "k_si<float>",
+                "peak_kind": kind, "bytes_per_update": bytes_per_update,
+                "avg_launch_ms": per_launch_ms}
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        v, n, el = oracle_rate(case, args.cpu_seconds)
+        cpu = {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
+               "sample": f"first {n} DLR steps of {WORKLOAD} ({el:.1f} s, single thread)"}
+    clocks = clk.summary(tw0, tw1) if clk else None
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic", "config": case_config(case, "mixed: FP32 sweeps/projections, FP64 small LA and T"),
+            "dlr_steps_per_s": world * args.steps / (total_ms / 1e3),
+            "si_iters_per_step": iters / args.steps,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fp64_gpu": fp64,
+            "clocks": clocks, "gpu_launches": int(launches),
+            "nonpositive_cells_at_end": int(nonpos)}
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

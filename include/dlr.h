@@ -24,9 +24,11 @@
  * Output buffers always belong to the caller.  "on_device" arguments say
  * whether a caller pointer is device memory (1) or host memory (0).
  *
- * Streams.  All device work of a handle is enqueued on runtime.stream (0 =
- * the legacy default stream).  dlr_step and dlr_step_batch return after
- * enqueueing; getters synchronise the stream.
+ * Streams.  All device work of a handle is enqueued on runtime.stream; when
+ * it is 0 the handle creates and owns a non-blocking stream (the step is
+ * replayed as CUDA graphs, which cannot be captured on the legacy stream).
+ * dlr_step and dlr_step_batch return after enqueueing; getters synchronise
+ * the stream.
  *
  * Errors.  Every function returning int returns DLR_OK (0) or a negative
  * DLR_E* code and records a message readable with dlr_last_error() (per
@@ -67,7 +69,7 @@ typedef struct dlr_problem {
   double lx, ly;         /* domain size, > 0 */
   int32_t n_polar;       /* Gauss-Legendre polar cosines, >= 1 */
   int32_t n_azim;        /* azimuths, >= 1 */
-  int32_t rank;          /* r0: 1 <= r0 <= min(64, nx*ny, n_polar*n_azim) */
+  int32_t rank;          /* r0: 1 <= r0 <= min(32, nx*ny, n_polar*n_azim) */
   double dt;             /* time step, > 0 */
   double c;              /* speed of light, > 0 */
   double a_rad;          /* radiation constant, >= 0 */
@@ -84,11 +86,16 @@ typedef struct dlr_problem {
                             <= 0 selects 1e-13 (FP64) or 1e-7 (mixed) */
   int32_t si_max_iter;   /* iteration cap (<= 0 selects 1000) */
   int32_t si_fixed_iters;/* > 0: run exactly this many iterations (testing) */
+  int32_t allow_nonpositive; /* 0: a non-positive temperature is the sticky
+                                error DLR_ENONPOS; 1: it is only counted
+                                (dlr_stats.nonpositive_cells).  Algorithm 1
+                                does not preserve positivity: a low-rank psi
+                                can turn negative ahead of a steep front */
 } dlr_problem;
 
 /* Device memory and stream supplied by the caller (e.g. PyTorch). */
 typedef struct dlr_runtime {
-  void *stream;                                 /* cudaStream_t, 0 = default */
+  void *stream;                                 /* cudaStream_t, 0 = own stream */
   void *(*alloc)(size_t bytes, void *ctx);      /* NULL: cudaMalloc */
   void (*free)(void *ptr, void *ctx);           /* NULL: cudaFree */
   void *ctx;                                    /* passed to alloc / free */
@@ -109,6 +116,8 @@ typedef struct dlr_stats {
                                 when timing is enabled (else 0) */
   double ms_step_total;      /* device time of whole steps when timing is on */
   int64_t si_launches;       /* timed source-iteration launches */
+  int64_t kernel_launches;   /* kernels this handle's steps launched */
+  int64_t nonpositive_cells; /* cells with T <= 0 after the last step */
 } dlr_stats;
 
 /* Creates a solver: validates sizes, builds the quadrature and the initial
@@ -134,8 +143,9 @@ int dlr_step_batch(dlr_handle *const *hs, int32_t n, int32_t nsteps);
 /* Copies T (nx*ny FP64) into out; synchronises. */
 int dlr_get_T(dlr_handle *h, double *out, int32_t out_on_device);
 
-/* Replaces T (nx*ny FP64) with in; enqueued on the stream (host input is
- * copied before return). */
+/* Replaces T (nx*ny FP64) with in; enqueued on the stream.  A pageable host
+ * buffer is consumed before return; a pinned one must stay unchanged until
+ * the stream has executed the copy. */
 int dlr_set_T(dlr_handle *h, const double *in, int32_t in_on_device);
 
 /* Copies the factors: X (nx*ny x r, column-major, hx*hy*X^T X = I), S (r x

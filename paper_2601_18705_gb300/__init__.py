@@ -45,6 +45,7 @@ class ProblemSpec:
     si_tol: float = 0.0
     si_max_iter: int = 0
     si_fixed_iters: int = 0
+    allow_nonpositive: int = 0
 
     def cstruct(self):
         keep = [_f64(self.sigma), _f64(self.rho_cv), _f64(self.T0)]
@@ -62,6 +63,7 @@ class ProblemSpec:
             p.T_edge[e] = float(self.T_edge[e])
         p.precision, p.selection, p.augment = self.precision, self.selection, 0
         p.si_tol, p.si_max_iter, p.si_fixed_iters = self.si_tol, self.si_max_iter, self.si_fixed_iters
+        p.allow_nonpositive = 1 if self.allow_nonpositive else 0
         return p, keep
 
 
@@ -74,7 +76,8 @@ def problem_from_case(case: dict, precision=None, **kw) -> ProblemSpec:
                        n_azim=case["n_azim"], rank=case["r"], sigma=case["sigma"],
                        rho_cv=case["rho_cv"], T0=case["T0"], T_edge=tuple(case["T_edge"]),
                        lx=case.get("lx", 1.0), ly=case.get("ly", 1.0), dt=case["dt"],
-                       c=case["c"], a_rad=case["a_rad"], precision=prec)
+                       c=case["c"], a_rad=case["a_rad"], precision=prec,
+                       si_max_iter=case.get("si_max_iter", 0))
     for k, v in kw.items():
         setattr(spec, k, v)
     return spec

@@ -31,7 +31,8 @@ class DlrProblem(C.Structure):
                 ("sigma", C.POINTER(C.c_double)), ("rho_cv", C.POINTER(C.c_double)),
                 ("T0", C.POINTER(C.c_double)), ("T_edge", C.c_double * 4),
                 ("precision", C.c_int32), ("selection", C.c_int32), ("augment", C.c_int32),
-                ("si_tol", C.c_double), ("si_max_iter", C.c_int32), ("si_fixed_iters", C.c_int32)]
+                ("si_tol", C.c_double), ("si_max_iter", C.c_int32), ("si_fixed_iters", C.c_int32),
+                ("allow_nonpositive", C.c_int32)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -47,7 +48,8 @@ class DlrStats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("si_iters_total", C.c_int64),
                 ("cell_angle_updates", C.c_int64), ("si_iters_last", C.c_int32),
                 ("status", C.c_int32), ("ms_si_total", C.c_double), ("ms_step_total", C.c_double),
-                ("si_launches", C.c_int64)]
+                ("si_launches", C.c_int64), ("kernel_launches", C.c_int64),
+                ("nonpositive_cells", C.c_int64)]
 
 
 _lib = None

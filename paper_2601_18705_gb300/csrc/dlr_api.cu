@@ -44,7 +44,7 @@ cudaError_t launch_chol(const CholJob *, const Inst *, int, cudaStream_t);
 cudaError_t launch_proj_post(const Inst *, int, cudaStream_t);
 size_t lstep_angle_smem(int);
 cudaError_t launch_lstep(const Inst *, int, int, int, cudaStream_t);
-cudaError_t launch_svd(const Inst *, int, cudaStream_t);
+cudaError_t launch_svd(const Inst *, int, int, cudaStream_t);
 cudaError_t launch_sign(const Inst *, int, int, cudaStream_t);
 cudaError_t launch_si_prep(const Inst *, int, SiCtl, cudaStream_t);
 cudaError_t prepare_small(int, int);
@@ -123,9 +123,11 @@ struct dlr_handle {
   bool timing = false;
   double ms_si = 0, ms_step = 0;
   int64_t si_launches = 0;
+  int64_t kernel_launches = 0;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::array<cudaEvent_t, 4>> ev_pending;
   Batch *own_batch = nullptr;
+  bool canonical = true;  // S0 diagonal (SVD basis) since the last step
 };
 
 struct Batch {
@@ -141,10 +143,13 @@ struct Batch {
   SiCtl ctl{};
   GramJob *g_psi1, *g_psire, *g_x, *g_x3, *g_l1, *g_lf, *g_w, *g_w3, *g_cross;
   FillJob *f_psi, *f_l;
-  ApplyJob *a_psi, *a_x2, *a_x3, *a_l1, *a_w2, *a_w3, *a_wv;
+  ApplyJob *a_psi, *a_x2, *a_x3, *a_l1, *a_w2, *a_w3, *a_wv, *a_cw, *a_cx;
+  int svd_mode = 0;  // 0: S kept general (pivoted-QR selection), 1: SVD every step (DEIM)
   CholJob *c_p1, *c_p1b, *c_p2, *c_p3, *c_l1, *c_l1b, *c_l2, *c_l3;
   ReduceJob *r_proj;
   cudaGraphExec_t pre = nullptr, post = nullptr;
+  int kernels_per_step = 0;  // kernel launches of one step (graphs + direct)
+  int kcount = 0;            // counter used while capturing
 };
 
 static void *dev_alloc(dlr_handle *h, size_t bytes) {
@@ -338,9 +343,9 @@ static Sizes sizes_of(const dlr_problem *p, int sms) {
   s.K = p->n_polar * p->n_azim;
   s.r = p->rank;
   s.rs = p->precision == DLR_MIXED ? 4 : 8;
-  s.pb = std::max(1, std::min(2 * sms, (s.N + 2047) / 2048));
-  s.pbl = std::max(1, std::min(64, (s.K + 511) / 512));
-  s.lb = std::max(1, std::min(2 * sms, (s.K + 31) / 32));
+  s.pb = std::max(1, std::min(2 * sms, (s.N + 511) / 512));      // >= 2 chunks of 256 cells
+  s.pbl = std::max(1, std::min(2 * sms, (s.K + 63) / 64));       // >= 2 chunks of 32 angles
+  s.lb = std::max(1, std::min(2 * sms, (s.K + 15) / 16));        // 4 warps x 4 angles
   const size_t r = s.r;
   s.partial_doubles = std::max({(size_t)s.pb * proj_count(s.r), (size_t)s.pb * r * r,
                                 (size_t)s.pbl * r * r, (size_t)s.lb * (r * r + r)});
@@ -516,6 +521,8 @@ int dlr_create(const dlr_problem *problem, const dlr_runtime *runtime, dlr_handl
   I.angle_blocks = h->pbl;
   I.lstep_blocks = h->lb;
   I.status = (int *)A(64);
+  I.nonpos = (int *)A(64);
+  I.allow_nonpos = problem->allow_nonpositive ? 1 : 0;
   I.iters = (int *)A(64);
   I.conv = (unsigned long long *)A(64);
   h->d_iters_total = (long long *)A(64);
@@ -554,6 +561,7 @@ int dlr_create(const dlr_problem *problem, const dlr_runtime *runtime, dlr_handl
     chain(up(I.X0, X0.data(), X0.size() * 8));
   }
   chain(cudaMemsetAsync(I.status, 0, 64, h->st));
+  chain(cudaMemsetAsync(I.nonpos, 0, 64, h->st));
   chain(cudaMemsetAsync(I.iters, 0, 64, h->st));
   chain(cudaMemsetAsync(h->d_iters_total, 0, 64, h->st));
   chain(cudaMemsetAsync(I.idx, 0xff, (size_t)r * 4, h->st));
@@ -611,6 +619,7 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   b->n = n;
   b->mixed = hs[0]->mixed;
   b->st = hs[0]->st;
+  b->svd_mode = hs[0]->prob.selection == DLR_SEL_DEIM ? 1 : 0;
   for (int i = 0; i < n; ++i) {
     const dlr_handle *h = hs[i];
     b->maxN = std::max(b->maxN, h->N);
@@ -633,7 +642,7 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   size_t bytes = 0;
   auto sz = [](size_t s) { return (s + 255) & ~size_t(255); };
   bytes += sz(sizeof(Inst) * n);
-  bytes += 9 * sz(sizeof(GramJob) * n) + 2 * sz(sizeof(FillJob) * n) + 7 * sz(sizeof(ApplyJob) * n) +
+  bytes += 9 * sz(sizeof(GramJob) * n) + 2 * sz(sizeof(FillJob) * n) + 9 * sz(sizeof(ApplyJob) * n) +
            8 * sz(sizeof(CholJob) * n) + sz(sizeof(ReduceJob) * n);
   bytes += sz(sizeof(int2) * units.size()) + sz(64) * 3;
   if (cudaMalloc(&b->d_mem, bytes) != cudaSuccess) {
@@ -660,6 +669,8 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   b->a_w2 = carve<ApplyJob>(cur, n);
   b->a_w3 = carve<ApplyJob>(cur, n);
   b->a_wv = carve<ApplyJob>(cur, n);
+  b->a_cw = carve<ApplyJob>(cur, n);
+  b->a_cx = carve<ApplyJob>(cur, n);
   b->c_p1 = carve<CholJob>(cur, n);
   b->c_p1b = carve<CholJob>(cur, n);
   b->c_p2 = carve<CholJob>(cur, n);
@@ -682,7 +693,7 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   std::vector<Inst> insts(n);
   std::vector<GramJob> gp1(n), gpre(n), gx(n), gx3(n), gl1(n), glf(n), gw(n), gw3(n), gcr(n);
   std::vector<FillJob> fp(n), fl(n);
-  std::vector<ApplyJob> ap(n), ax2(n), ax3(n), al1(n), aw2(n), aw3(n), awv(n);
+  std::vector<ApplyJob> ap(n), ax2(n), ax3(n), al1(n), aw2(n), aw3(n), awv(n), acw(n), acx(n);
   std::vector<CholJob> cp1(n), cp1b(n), cp2(n), cp3(n), cl1(n), cl1b(n), cl2(n), cl3(n);
   std::vector<ReduceJob> rp(n);
   for (int i = 0; i < n; ++i) {
@@ -697,6 +708,7 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
       GramJob g{};
       g.A = A; g.wt = wt; g.m = m; g.r = r; g.lda = lda; g.layout = layout;
       g.out = I.partials; g.nblocks = nb; g.run_if = run_if;
+      g.chunk = (m == N) ? 256 : 32;  // cells: 256-row FP32 chunks; angles (FP64): 32
       return g;
     };
     gp1[i] = gram(I.Psi, nullptr, N, N, 0, h->pb, nullptr);
@@ -734,6 +746,8 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
     aw2[i] = apply(I.W0, 0, K, nullptr, 0, sm + L.R2i, I.W0, K, nullptr, 0, K, nullptr);
     aw3[i] = apply(I.W0, 0, K, nullptr, 0, sm + L.R3i, I.W0, K, nullptr, 0, K, flag);
     awv[i] = apply(I.W0, 0, K, nullptr, 0, sm + L.V, I.W0, K, I.w, 1, K, nullptr);
+    acw[i] = apply(I.W0, 0, K, nullptr, 0, sm + L.V, I.W0, K, nullptr, 0, K, nullptr);
+    acx[i] = apply(I.X0, 0, N, nullptr, 0, sm + L.U, I.X0, N, nullptr, 0, N, nullptr);
     const double u = h->mixed ? 1e-7 : 1e-15, tau = h->mixed ? 1e-10 : 1e-24;
     auto chol = [&](int nb, double scale, double *R, double *Ri, int mode) {
       CholJob c{};
@@ -779,6 +793,8 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   chain(upv(b->a_w2, aw2.data(), sizeof(ApplyJob) * n));
   chain(upv(b->a_w3, aw3.data(), sizeof(ApplyJob) * n));
   chain(upv(b->a_wv, awv.data(), sizeof(ApplyJob) * n));
+  chain(upv(b->a_cw, acw.data(), sizeof(ApplyJob) * n));
+  chain(upv(b->a_cx, acx.data(), sizeof(ApplyJob) * n));
   chain(upv(b->c_p1, cp1.data(), sizeof(CholJob) * n));
   chain(upv(b->c_p1b, cp1b.data(), sizeof(CholJob) * n));
   chain(upv(b->c_p2, cp2.data(), sizeof(CholJob) * n));
@@ -819,13 +835,19 @@ static int refresh_batch(Batch *b) {
   return DLR_OK;
 }
 
+#define LK(call) \
+  do {             \
+    CK(call);      \
+    ++b->kcount;   \
+  } while (0)
+
 template <typename real>
 static int enqueue_pre(Batch *b) {
   const Inst *d = b->d_insts;
   const int n = b->n;
-  CK(launch_select(d, n, b->maxK, b->st));
-  CK(launch_coeff_recon<real>(d, n, b->maxN, b->rmax, b->st));
-  CK(launch_si_prep(d, n, b->ctl, b->st));
+  LK(launch_select(d, n, b->maxK, b->st));
+  LK(launch_coeff_recon<real>(d, n, b->maxN, b->rmax, b->st));
+  LK(launch_si_prep(d, n, b->ctl, b->st));
   return DLR_OK;
 }
 
@@ -837,43 +859,44 @@ static int enqueue_post(Batch *b) {
   // step 5: CholeskyQR of Psi; dependent columns are replaced by
   // pseudo-random ones (orthonormal completion) and the pass redone; a third
   // pass runs when a Cholesky needed a shift
-  CK(launch_tsgram<real>(b->g_psi1, n, b->pbmax, st));
-  CK(launch_chol(b->c_p1, d, n, st));
-  CK(launch_fill<real>(b->f_psi, n, b->maxN, st));
-  CK(launch_tsgram<real>(b->g_psire, n, b->pbmax, st));
-  CK(launch_chol(b->c_p1b, d, n, st));
-  CK((launch_apply<real, real>(b->a_psi, n, b->maxN, b->rmax, st)));
-  CK(launch_tsgram<real>(b->g_x, n, b->pbmax, st));
-  CK(launch_chol(b->c_p2, d, n, st));
-  CK((launch_apply<real, real>(b->a_x2, n, b->maxN, b->rmax, st)));
-  CK(launch_tsgram<real>(b->g_x3, n, b->pbmax, st));
-  CK(launch_chol(b->c_p3, d, n, st));
-  CK((launch_apply<real, real>(b->a_x3, n, b->maxN, b->rmax, st)));
+  LK(launch_tsgram<real>(b->g_psi1, n, b->pbmax, st));
+  LK(launch_chol(b->c_p1, d, n, st));
+  LK(launch_fill<real>(b->f_psi, n, b->maxN, st));
+  LK(launch_tsgram<real>(b->g_psire, n, b->pbmax, st));
+  LK(launch_chol(b->c_p1b, d, n, st));
+  LK((launch_apply<real, real>(b->a_psi, n, b->maxN, b->rmax, st)));
+  LK(launch_tsgram<real>(b->g_x, n, b->pbmax, st));
+  LK(launch_chol(b->c_p2, d, n, st));
+  LK((launch_apply<real, real>(b->a_x2, n, b->maxN, b->rmax, st)));
+  LK(launch_tsgram<real>(b->g_x3, n, b->pbmax, st));
+  LK(launch_chol(b->c_p3, d, n, st));
+  LK((launch_apply<real, real>(b->a_x3, n, b->maxN, b->rmax, st)));
   // steps 6-7: projections and the L-step
-  CK(launch_project<real>(d, n, b->pbmax, st));
-  CK(launch_reduce(b->r_proj, n, proj_count(b->rmax), st));
-  CK(launch_proj_post(d, n, st));
-  CK(launch_lstep(d, n, b->rmax, b->lbmax, st));
+  LK(launch_project<real>(d, n, b->pbmax, st));
+  LK(launch_reduce(b->r_proj, n, proj_count(b->rmax), st));
+  LK(launch_proj_post(d, n, st));
+  LK(launch_lstep(d, n, b->rmax, b->lbmax, st));
+  b->kcount += 2;  // three kernels
   // step 8: CholeskyQR of M = diag(sqrt w) L^T into Q (held in W0), S = M^T Q,
   // SVD of S, W0 <- diag(1/sqrt w) Q V
-  CK(launch_tsgram<double>(b->g_l1, n, b->pblmax, st));
-  CK(launch_chol(b->c_l1, d, n, st));
-  CK(launch_fill<double>(b->f_l, n, b->maxK, st));
-  CK(launch_tsgram<double>(b->g_lf, n, b->pblmax, st));
-  CK(launch_chol(b->c_l1b, d, n, st));
-  CK((launch_apply<double, double>(b->a_l1, n, b->maxK, b->rmax, st)));
-  CK(launch_tsgram<double>(b->g_w, n, b->pblmax, st));
-  CK(launch_chol(b->c_l2, d, n, st));
-  CK((launch_apply<double, double>(b->a_w2, n, b->maxK, b->rmax, st)));
-  CK(launch_tsgram<double>(b->g_w3, n, b->pblmax, st));
-  CK(launch_chol(b->c_l3, d, n, st));
-  CK((launch_apply<double, double>(b->a_w3, n, b->maxK, b->rmax, st)));
-  CK(launch_tsgram<double>(b->g_cross, n, b->pblmax, st));
-  CK(launch_svd(d, n, st));
-  CK((launch_apply<double, double>(b->a_wv, n, b->maxK, b->rmax, st)));
-  CK(launch_sign(d, n, b->maxK, st));
+  LK(launch_tsgram<double>(b->g_l1, n, b->pblmax, st));
+  LK(launch_chol(b->c_l1, d, n, st));
+  LK(launch_fill<double>(b->f_l, n, b->maxK, st));
+  LK(launch_tsgram<double>(b->g_lf, n, b->pblmax, st));
+  LK(launch_chol(b->c_l1b, d, n, st));
+  LK((launch_apply<double, double>(b->a_l1, n, b->maxK, b->rmax, st)));
+  LK(launch_tsgram<double>(b->g_w, n, b->pblmax, st));
+  LK(launch_chol(b->c_l2, d, n, st));
+  LK((launch_apply<double, double>(b->a_w2, n, b->maxK, b->rmax, st)));
+  LK(launch_tsgram<double>(b->g_w3, n, b->pblmax, st));
+  LK(launch_chol(b->c_l3, d, n, st));
+  LK((launch_apply<double, double>(b->a_w3, n, b->maxK, b->rmax, st)));
+  LK(launch_tsgram<double>(b->g_cross, n, b->pblmax, st));
+  LK(launch_svd(d, n, b->svd_mode, st));
+  LK((launch_apply<double, double>(b->a_wv, n, b->maxK, b->rmax, st)));
+  if (b->svd_mode == 1) LK(launch_sign(d, n, b->maxK, st));
   // step 9
-  CK(launch_tupdate<real>(d, n, b->maxN, b->rmax, st));
+  LK(launch_tupdate<real>(d, n, b->maxN, b->rmax, st));
   return DLR_OK;
 }
 
@@ -908,8 +931,12 @@ static cudaEvent_t pool_event(dlr_handle *h) {
 static int run_steps(Batch *b, int nsteps) {
   int rc = refresh_batch(b);
   if (rc) return rc;
-  if (!b->pre && (rc = capture(b, true, &b->pre))) return rc;
-  if (!b->post && (rc = capture(b, false, &b->post))) return rc;
+  if (!b->pre) {
+    b->kcount = 0;
+    if ((rc = capture(b, true, &b->pre))) return rc;
+    if ((rc = capture(b, false, &b->post))) return rc;
+    b->kernels_per_step = b->kcount + 1;  // + the source-iteration kernel
+  }
   dlr_handle *h0 = b->hs[0];
   for (int s = 0; s < nsteps; ++s) {
     std::array<cudaEvent_t, 4> ev{};
@@ -931,6 +958,8 @@ static int run_steps(Batch *b, int nsteps) {
   }
   for (auto *h : b->hs) {
     h->steps += nsteps;
+    h->canonical = b->svd_mode == 1;
+    h->kernel_launches += (int64_t)nsteps * b->kernels_per_step;
     CK(cudaMemcpyAsync(h->h_status, h->inst.status, sizeof(int), cudaMemcpyDeviceToHost, b->st));
   }
   return DLR_OK;
@@ -1014,8 +1043,32 @@ int dlr_set_T(dlr_handle *h, const double *in, int32_t in_on_device) {
   return DLR_OK;
 }
 
+// Rotates the stored factors to the SVD basis of S (X0 <- X0 U, S0 <- Sigma,
+// W0 <- W0 V, signs: largest-magnitude entry of each W column > 0); psi is
+// unchanged.  Steps with pivoted-QR selection keep S general, because that
+// selection depends only on span W.
+static int canonicalize(dlr_handle *h) {
+  if (h->canonical) return DLR_OK;
+  int rc;
+  if (!h->own_batch && (rc = build_batch(&h, 1, &h->own_batch))) return rc;
+  Batch *b = h->own_batch;
+  rc = refresh_batch(b);
+  if (rc) return rc;
+  CK(launch_svd(b->d_insts, 1, 2, h->st));
+  CK((launch_apply<double, double>(b->a_cw, 1, h->K, h->r, h->st)));
+  CK(launch_sign(b->d_insts, 1, h->K, h->st));
+  if (h->mixed) CK((launch_apply<float, float>(b->a_cx, 1, h->N, h->r, h->st)));
+  else CK((launch_apply<double, double>(b->a_cx, 1, h->N, h->r, h->st)));
+  h->canonical = true;
+  return DLR_OK;
+}
+
 int dlr_get_factors(dlr_handle *h, double *X, double *S, double *W, int32_t *r_out, int32_t out_on_device) {
   if (!h) return fail(DLR_EINVAL, "NULL handle");
+  {
+    int rc = canonicalize(h);
+    if (rc) return rc;
+  }
   const size_t nX = (size_t)h->N * h->r;
   const cudaMemcpyKind k = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (r_out) *r_out = h->r;
@@ -1039,6 +1092,7 @@ int dlr_get_factors(dlr_handle *h, double *X, double *S, double *W, int32_t *r_o
 
 int dlr_set_factors(dlr_handle *h, const double *X, const double *S, const double *W, int32_t in_on_device) {
   if (!h || !X || !S || !W) return fail(DLR_EINVAL, "NULL argument");
+  h->canonical = false;
   const size_t nX = (size_t)h->N * h->r;
   const cudaMemcpyKind k = in_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   if (!h->mixed) {
@@ -1080,7 +1134,8 @@ int dlr_get_stats(dlr_handle *h, dlr_stats *out) {
   if (!h || !out) return fail(DLR_EINVAL, "NULL argument");
   CK(cudaStreamSynchronize(h->st));
   long long tot = 0;
-  int last = 0, s = 0;
+  int last = 0, s = 0, np = 0;
+  CK(cudaMemcpy(&np, h->inst.nonpos, sizeof np, cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(&tot, h->d_iters_total, sizeof tot, cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(&last, h->inst.iters, sizeof last, cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(&s, h->inst.status, sizeof s, cudaMemcpyDeviceToHost));
@@ -1102,6 +1157,8 @@ int dlr_get_stats(dlr_handle *h, dlr_stats *out) {
   out->ms_si_total = h->ms_si;
   out->ms_step_total = h->ms_step;
   out->si_launches = h->si_launches;
+  out->kernel_launches = h->kernel_launches;
+  out->nonpositive_cells = np;
   *h->h_status = s;
   return DLR_OK;
 }

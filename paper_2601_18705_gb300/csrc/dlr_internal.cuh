@@ -91,6 +91,8 @@ struct Inst {
   int lstep_blocks;        // blocks of the per-angle L-step
   // status and iteration bookkeeping
   int *status;            // sticky device status
+  int *nonpos;            // cells with T <= 0 after the last step
+  int allow_nonpos;       // 1: count non-positive T instead of failing
   int *iters;             // iterations of the last source-iteration solve
   unsigned long long *iters_total;  // iterations summed over all steps
   unsigned long long *conv;  // [2 parities][2]: max |dphi|, max |phi| (bits)
@@ -106,6 +108,7 @@ struct GramJob {
   const void *B;    // optional: cross Gram sum wt a b^T with B (layout 0, ldb)
   int ldb;
   int sqrt_wt;      // 1: weight sqrt(wt) instead of wt
+  int chunk;        // rows per FP32 partial sum (multiple of 32)
   double *out;      // partial sums
   int nblocks;      // blocks used for this job
   const int *run_if;  // optional: skip unless *run_if != 0

@@ -93,11 +93,12 @@ __global__ void __launch_bounds__(kTB) k_tsgram(const GramJob *__restrict__ jobs
   const bool own = ti < r && tj < r;
   double acc[4] = {0, 0, 0, 0};
   const real *A = as_c<real>(J.A);
-  const int nchunks = (J.m + kChunk - 1) / kChunk;
+  const int chunk = J.chunk;
+  const int nchunks = (J.m + chunk - 1) / chunk;
   for (int ch = blockIdx.x; ch < nchunks; ch += J.nblocks) {
     real s[4] = {0, 0, 0, 0};
-    for (int sub = 0; sub < kChunk; sub += 32) {
-      const int row0 = ch * kChunk + sub;
+    for (int sub = 0; sub < chunk; sub += 32) {
+      const int row0 = ch * chunk + sub;
       __syncthreads();
       for (int e = t; e < 32 * r; e += blockDim.x) {
         int rr, i;
@@ -380,7 +381,10 @@ __global__ void __launch_bounds__(128) k_tupdate(const Inst *__restrict__ insts)
   const double T0 = I.T[c];
   const double T = T0 + I.dt * I.sigma[c] * ((double)phi - 4.0 * kPi * I.B0[c]) / I.D[c];
   I.T[c] = T;
-  if (!(T > 0.0)) set_status(I.status, kENonPos);
+  if (!(T > 0.0)) {
+    atomicAdd(I.nonpos, 1);
+    if (!I.allow_nonpos) set_status(I.status, kENonPos);
+  }
 }
 
 // ------------------------------------------------------------------

@@ -448,8 +448,12 @@ __device__ void stage_ops(const Inst &I, double *sm) {
   __syncthreads();
 }
 
-constexpr int kLsWarps = 8;
+constexpr int kLsWarps = 4;
 
+// One warp per angle; lane j owns column j of B_k padded to RB x RB with an
+// identity block (so every loop has a compile-time bound).  The per-CTA
+// sums of w_k B_k^{-1} and w_k B_k^{-1} Q_k go to partials[blockIdx.x].
+template <int RB>
 __global__ void __launch_bounds__(kLsWarps * 32) k_lstep_angle(const Inst *__restrict__ insts,
                                                                int blocks_per_inst) {
   const Inst &I = insts[blockIdx.y];
@@ -458,119 +462,110 @@ __global__ void __launch_bounds__(kLsWarps * 32) k_lstep_angle(const Inst *__res
   extern __shared__ double sh[];
   const int r = I.r, K = I.K;
   double *sm = sh;                                   // 6 r^2 + 5 r
-  double *wlu = sh + 6 * r * r + 5 * r;              // kLsWarps x r^2
-  double *red = wlu + (size_t)kLsWarps * r * r;      // kLsWarps x (r^2 + r)
+  double *wlu = sh + 6 * r * r + 5 * r;              // kLsWarps x RB^2
+  double *red = wlu + (size_t)kLsWarps * RB * RB;    // kLsWarps x (r^2 + r)
   stage_ops(I, sm);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  double *lu_w = wlu + (size_t)wid * r * r;
-  // per-warp accumulators: lane j owns column j of sum_k w_k B_k^{-1} and
-  // entry j of sum_k w_k B_k^{-1} Q_k
+  double *lu_w = wlu + (size_t)wid * RB * RB;
   double *mine = red + (size_t)wid * (r * r + r);
   for (int e = lane; e < r * r + r; e += 32) mine[e] = 0.0;
   __syncwarp();
-  bool bad = false;
+  const bool on = lane < RB;
   const int gw = blockIdx.x * kLsWarps + wid, nwarps = blocks_per_inst * kLsWarps;
   for (int k = gw; k < K; k += nwarps) {
     const AngleOps o = angle_ops(I, sm, k);
     const double *Mt = sm + 4 * r * r;
-    double col[kMaxRank];
+    double col[RB];
 #pragma unroll
-    for (int i = 0; i < kMaxRank; ++i)
-      col[i] = (i < r && lane < r)
-                   ? o.aox * o.Ax[i + r * lane] + o.aoy * o.Ay[i + r * lane] + Mt[i + r * lane]
-                   : 0.0;
+    for (int i = 0; i < RB; ++i) {
+      double v = (i == lane) ? 1.0 : 0.0;  // identity padding
+      if (lane < r && i < r)
+        v = o.aox * o.Ax[i + r * lane] + o.aoy * o.Ay[i + r * lane] + Mt[i + r * lane];
+      col[i] = v;
+    }
     const double qk = lane < r ? angle_q(I, sm, o, k, lane) : 0.0;
-    int mypiv = 0;
+    int mypiv = lane;
     bool singular = false;
-    for (int p = 0; p < r; ++p) {
+#pragma unroll
+    for (int p = 0; p < RB; ++p) {
       int pr = p;
       if (lane == p) {
         double best = -1.0;
 #pragma unroll
-        for (int i = 0; i < kMaxRank; ++i)
-          if (i >= p && i < r && fabs(col[i]) > best) { best = fabs(col[i]); pr = i; }
+        for (int i = p; i < RB; ++i)
+          if (fabs(col[i]) > best) { best = fabs(col[i]); pr = i; }
         if (best == 0.0) pr = -1;
       }
       pr = __shfl_sync(kFullMask, pr, p);
       if (pr < 0) { singular = true; break; }
       if (lane == p) mypiv = pr;
       if (pr != p) {
-        double a = 0.0, b = 0.0;
+        double a = col[p], b = col[p];
 #pragma unroll
-        for (int i = 0; i < kMaxRank; ++i) { if (i == p) a = col[i]; if (i == pr) b = col[i]; }
+        for (int i = p + 1; i < RB; ++i) if (i == pr) b = col[i];
+        col[p] = b;
 #pragma unroll
-        for (int i = 0; i < kMaxRank; ++i) { if (i == p) col[i] = b; if (i == pr) col[i] = a; }
+        for (int i = p + 1; i < RB; ++i) if (i == pr) col[i] = a;
       }
-      double dpp = 0.0;
-#pragma unroll
-      for (int i = 0; i < kMaxRank; ++i) if (i == p) dpp = col[i];
-      dpp = __shfl_sync(kFullMask, dpp, p);
+      const double dpp = __shfl_sync(kFullMask, col[p], p);
       if (lane == p) {
+        const double inv = 1.0 / dpp;
 #pragma unroll
-        for (int i = 0; i < kMaxRank; ++i) if (i > p && i < r) col[i] /= dpp;
+        for (int i = p + 1; i < RB; ++i) col[i] *= inv;
       }
-      double cp = 0.0;  // this lane's entry in row p
+      const double cp = col[p];
 #pragma unroll
-      for (int i = 0; i < kMaxRank; ++i) if (i == p) cp = col[i];
-#pragma unroll
-      for (int i = 0; i < kMaxRank; ++i) {
-        if (i > p && i < r) {
-          const double li = __shfl_sync(kFullMask, col[i], p);
-          if (lane > p && lane < r) col[i] -= li * cp;
-        }
+      for (int i = p + 1; i < RB; ++i) {
+        const double li = __shfl_sync(kFullMask, col[i], p);
+        if (lane > p) col[i] -= li * cp;
       }
     }
     if (singular) {
       if (lane == 0) set_status(I.status, kESingular);
-      bad = true;
       break;
     }
-    // factors to global (for the back-solve) and to this warp's smem
+    if (on) {
+#pragma unroll
+      for (int i = 0; i < RB; ++i) lu_w[lane * RB + i] = col[i];
+    }
     if (lane < r) {
 #pragma unroll
-      for (int i = 0; i < kMaxRank; ++i)
-        if (i < r) {
-          I.lu[((size_t)k * r + lane) * r + i] = col[i];
-          lu_w[lane * r + i] = col[i];
-        }
+      for (int i = 0; i < RB; ++i)
+        if (i < r) I.lu[((size_t)k * r + lane) * r + i] = col[i];
       I.piv[(size_t)k * r + lane] = mypiv;
     }
     __syncwarp();
-    // lane j: column j of B^{-1} = U^{-1} L^{-1} P e_j
-    double y[kMaxRank];
+    // lane j: column j of B^{-1} = U^{-1} L^{-1} P e_j (rows swapped in order)
+    double y[RB];
 #pragma unroll
-    for (int i = 0; i < kMaxRank; ++i) y[i] = (i == lane) ? 1.0 : 0.0;
-    for (int p = 0; p < r; ++p) {
+    for (int i = 0; i < RB; ++i) y[i] = (i == lane) ? 1.0 : 0.0;
+#pragma unroll
+    for (int p = 0; p < RB; ++p) {
       const int pr = __shfl_sync(kFullMask, mypiv, p);
       if (pr != p) {
-        double a = 0.0, b = 0.0;
+        double a = y[p], b = y[p];
 #pragma unroll
-        for (int i = 0; i < kMaxRank; ++i) { if (i == p) a = y[i]; if (i == pr) b = y[i]; }
+        for (int i = p + 1; i < RB; ++i) if (i == pr) b = y[i];
+        y[p] = b;
 #pragma unroll
-        for (int i = 0; i < kMaxRank; ++i) { if (i == p) y[i] = b; if (i == pr) y[i] = a; }
+        for (int i = p + 1; i < RB; ++i) if (i == pr) y[i] = a;
       }
     }
 #pragma unroll
-    for (int i = 0; i < kMaxRank; ++i) {
-      if (i < r) {
+    for (int i = 1; i < RB; ++i) {
 #pragma unroll
-        for (int m = 0; m < kMaxRank; ++m)
-          if (m < i) y[i] -= lu_w[m * r + i] * y[m];
-      }
+      for (int m = 0; m < i; ++m) y[i] -= lu_w[m * RB + i] * y[m];
     }
 #pragma unroll
-    for (int ii = kMaxRank - 1; ii >= 0; --ii) {
-      if (ii < r) {
+    for (int ii = RB - 1; ii >= 0; --ii) {
 #pragma unroll
-        for (int m = 0; m < kMaxRank; ++m)
-          if (m > ii && m < r) y[ii] -= lu_w[m * r + ii] * y[m];
-        y[ii] /= lu_w[ii * r + ii];
-      }
+      for (int m = ii + 1; m < RB; ++m) y[ii] -= lu_w[m * RB + ii] * y[m];
+      y[ii] /= lu_w[ii * RB + ii];
     }
     // (B^{-1} Q)_i = sum_j (B^{-1})_ij Q_j ; lane j holds column j and Q_j
     const double wk = I.w[k];
 #pragma unroll
-    for (int i = 0; i < kMaxRank; ++i) {
+    for (int i = 0; i < RB; ++i) {
       if (i < r) {
         const double z = warp_sum(lane < r ? y[i] * qk : 0.0);
         if (lane == i) mine[r * r + i] += wk * z;
@@ -579,8 +574,6 @@ __global__ void __launch_bounds__(kLsWarps * 32) k_lstep_angle(const Inst *__res
     }
     __syncwarp();
   }
-  (void)bad;
-  // CTA reduction (fixed order) -> partials[blockIdx.x]
   __syncthreads();
   double *out = I.partials + (size_t)blockIdx.x * (r * r + r);
   for (int e = threadIdx.x; e < r * r + r; e += blockDim.x) {
@@ -675,7 +668,9 @@ __global__ void __launch_bounds__(kLsWarps * 32) k_lstep_back(const Inst *__rest
 // W = diag(1/sqrt w) Q; one-sided Jacobi SVD S = U Sigma V^T (descending),
 // S0 <- Sigma, V and U kept for W <- W V and X <- X U, vphi = L w.
 // ------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_svd(const Inst *__restrict__ insts) {
+// mode 0: S0 <- S (no SVD; U = V = I), vphi; mode 1: SVD as well;
+// mode 2: SVD of the stored S0 (canonical factors on request).
+__global__ void __launch_bounds__(256) k_svd(const Inst *__restrict__ insts, int mode) {
   const Inst &I = insts[blockIdx.x];
   if (*I.status != kOk) return;
   __shared__ double Uw[32 * 32], Vw[32 * 32], sv[32];
@@ -685,16 +680,39 @@ __global__ void __launch_bounds__(256) k_svd(const Inst *__restrict__ insts) {
   const SmallLayout &L = I.lay;
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     double t = 0.0;
-    for (int b = 0; b < I.angle_blocks; ++b) t += I.partials[(size_t)b * r * r + e];
+    if (mode == 2) {
+      t = I.S0[e];
+    } else {
+      for (int b = 0; b < I.angle_blocks; ++b) t += I.partials[(size_t)b * r * r + e];
+    }
     Uw[e] = t;  // S_ij = sum_k sqrt(w_k) L_ik Q_kj
     Vw[e] = (e % r == e / r) ? 1.0 : 0.0;
   }
   __syncthreads();
+  if (mode != 2) {  // vphi_i = sum_k w_k L_ik  (phi = X L w)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = wid; i < r; i += nw) {
+      double s = 0.0;
+      for (int k = lane; k < I.K; k += 32) s += I.w[k] * I.L[(size_t)r * k + i];
+      s = warp_sum(s);
+      if (lane == 0) I.small[L.vphi + i] = s;
+    }
+  }
+  if (mode == 0) {
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+      I.S0[e] = Uw[e];
+      const double d = (e % r == e / r) ? 1.0 : 0.0;
+      I.small[L.U + e] = d;
+      I.small[L.V + e] = d;
+    }
+    return;
+  }
   // one-sided Jacobi; each sweep visits all pairs in n-1 rounds of n/2
   // disjoint pairs (circle method), one warp per pair
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int n = (r + 1) & ~1;
-  for (int sweep = 0; sweep < 60; ++sweep) {
+  (void)lane;
+  for (int sweep = 0; sweep < 30; ++sweep) {
     if (threadIdx.x == 0) rot_s = 0;
     __syncthreads();
     for (int round = 0; round < n - 1; ++round) {
@@ -707,7 +725,7 @@ __global__ void __launch_bounds__(256) k_svd(const Inst *__restrict__ insts) {
         const double ui = lane < r ? Uw[lane + r * i] : 0.0;
         const double uj = lane < r ? Uw[lane + r * j] : 0.0;
         const double al = warp_sum(ui * ui), be = warp_sum(uj * uj), ga = warp_sum(ui * uj);
-        if (ga == 0.0 || fabs(ga) <= 1e-15 * sqrt(al * be)) continue;
+        if (ga == 0.0 || fabs(ga) <= 1e-14 * sqrt(al * be)) continue;
         if (lane == 0) rot_s = 1;
         const double zeta = (be - al) / (2.0 * ga);
         const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
@@ -779,15 +797,6 @@ __global__ void __launch_bounds__(256) k_svd(const Inst *__restrict__ insts) {
     const int i = e % r, j = e / r;
     I.S0[e] = (i == j) ? sv[ord[j]] : 0.0;
   }
-  // vphi_i = sum_k w_k L_ik  (phi = X L w)
-  {
-    for (int i = wid; i < r; i += nw) {
-      double s = 0.0;
-      for (int k = lane; k < I.K; k += 32) s += I.w[k] * I.L[(size_t)r * k + i];
-      s = warp_sum(s);
-      if (lane == 0) I.small[L.vphi + i] = s;
-    }
-  }
 }
 
 // Sign of W columns: the entry of largest magnitude (tie rule) made positive;
@@ -815,8 +824,10 @@ __global__ void __launch_bounds__(256) k_sign(const Inst *__restrict__ insts) {
 // launch is captured into a graph)
 // ------------------------------------------------------------------
 static size_t select_smem(int maxK) { return (size_t)(maxK + 32 + 32 * 32 + 32) * sizeof(double); }
+static int rank_bucket(int r) { return r <= 8 ? 8 : r <= 16 ? 16 : 32; }
 size_t lstep_angle_smem(int r) {
-  return (size_t)(6 * r * r + 5 * r + kLsWarps * r * r + kLsWarps * (r * r + r)) * sizeof(double);
+  const int RB = rank_bucket(r);
+  return (size_t)(6 * r * r + 5 * r + kLsWarps * RB * RB + kLsWarps * (r * r + r)) * sizeof(double);
 }
 static size_t lstep_back_smem(int r) { return (size_t)(6 * r * r + 5 * r) * sizeof(double); }
 
@@ -824,7 +835,11 @@ cudaError_t prepare_small(int maxK, int rmax) {
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)select_smem(maxK))) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_lstep_angle, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if ((e = cudaFuncSetAttribute(k_lstep_angle<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)lstep_angle_smem(rmax))) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_lstep_angle<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)lstep_angle_smem(rmax))) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_lstep_angle<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)lstep_angle_smem(rmax))) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_lstep_back, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)lstep_back_smem(rmax))) != cudaSuccess) return e;
@@ -844,7 +859,13 @@ cudaError_t launch_proj_post(const Inst *d, int n, cudaStream_t st) {
   return cudaGetLastError();
 }
 cudaError_t launch_lstep(const Inst *d, int n, int r_max, int blocks, cudaStream_t st) {
-  k_lstep_angle<<<dim3(blocks, n), kLsWarps * 32, lstep_angle_smem(r_max), st>>>(d, blocks);
+  const dim3 g(blocks, n);
+  const size_t sm = lstep_angle_smem(r_max);
+  switch (rank_bucket(r_max)) {
+    case 8: k_lstep_angle<8><<<g, kLsWarps * 32, sm, st>>>(d, blocks); break;
+    case 16: k_lstep_angle<16><<<g, kLsWarps * 32, sm, st>>>(d, blocks); break;
+    default: k_lstep_angle<32><<<g, kLsWarps * 32, sm, st>>>(d, blocks); break;
+  }
   cudaError_t e;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_lstep_mid<<<n, 256, 0, st>>>(d, blocks);
@@ -852,8 +873,8 @@ cudaError_t launch_lstep(const Inst *d, int n, int r_max, int blocks, cudaStream
   k_lstep_back<<<dim3(blocks, n), kLsWarps * 32, lstep_back_smem(r_max), st>>>(d, blocks);
   return cudaGetLastError();
 }
-cudaError_t launch_svd(const Inst *d, int n, cudaStream_t st) {
-  k_svd<<<n, 256, 0, st>>>(d);
+cudaError_t launch_svd(const Inst *d, int n, int mode, cudaStream_t st) {
+  k_svd<<<n, 256, 0, st>>>(d, mode);
   return cudaGetLastError();
 }
 cudaError_t launch_sign(const Inst *d, int n, int maxK, cudaStream_t st) {

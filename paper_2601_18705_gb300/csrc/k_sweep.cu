@@ -365,6 +365,7 @@ __global__ void k_si_prep(const Inst *__restrict__ insts, int n, SiCtl ctl) {
   if (t < n) {
     insts[t].conv[0] = 0ull;
     insts[t].conv[1] = 0ull;
+    *insts[t].nonpos = 0;
   }
 }
 

@@ -9,7 +9,7 @@ def rel_l2(a, b) -> float:
 
 
 def run_pair(case, precision, steps, *, orc, dlr, forced=None, si_fixed_iters=0, si_tol=None,
-             selection=0, start=None):
+             selection=0, start=None, allow_nonpositive=0):
     """Runs the oracle and the GPU solver side by side from the same state.
     Returns per-step (T error, psi error, oracle idx, gpu idx) and both states.
     When the GPU picks different angles than the oracle (a near-tie), the
@@ -19,7 +19,8 @@ def run_pair(case, precision, steps, *, orc, dlr, forced=None, si_fixed_iters=0,
     kw = {}
     if si_fixed_iters:
         kw["si_fixed_iters"] = si_fixed_iters
-    spec = dlr.problem_from_case(case, precision=precision, selection=selection, **kw)
+    spec = dlr.problem_from_case(case, precision=precision, selection=selection,
+                                 allow_nonpositive=allow_nonpositive, **kw)
     if si_tol is not None:
         spec.si_tol = si_tol
     T = case["T0"].reshape(-1).copy()

@@ -115,7 +115,9 @@ def test_batch_equals_alone(dlr):
             with dlr.Solver(dlr.problem_from_case(cs, precision=prec)) as s:
                 s.step(3)
                 alone.append(s.T())
-        solvers = [dlr.Solver(dlr.problem_from_case(cs, precision=prec)) for cs in cases]
+        import torch
+        st = torch.cuda.Stream()
+        solvers = [dlr.Solver(dlr.problem_from_case(cs, precision=prec), stream=st) for cs in cases]
         dlr.step_batch(solvers, 3)
         for s, Ta in zip(solvers, alone):
             assert np.array_equal(s.T(), Ta)
