@@ -83,7 +83,8 @@ typedef struct dlr_problem {
   int32_t augment;       /* must be 0 (Algorithm 1 as printed) */
   double si_tol;         /* source-iteration tolerance; stop when
                             max|phi_new - phi| <= si_tol * max|phi_new|;
-                            <= 0 selects 1e-13 (FP64) or 1e-7 (mixed) */
+                            <= 0 selects 1e-13 (FP64) or 1e-6 (mixed; the
+                            FP32 iterates stall at a few 1e-7 of max|phi|) */
   int32_t si_max_iter;   /* iteration cap (<= 0 selects 1000) */
   int32_t si_fixed_iters;/* > 0: run exactly this many iterations (testing) */
   int32_t allow_nonpositive; /* 0: a non-positive temperature is the sticky

@@ -477,7 +477,7 @@ int dlr_create(const dlr_problem *problem, const dlr_runtime *runtime, dlr_handl
   I.c = problem->c;
   I.a_rad = problem->a_rad;
   I.inv_cdt = 1.0 / (problem->c * problem->dt);
-  I.si_tol = problem->si_tol > 0 ? problem->si_tol : (h->mixed ? 1e-7 : 1e-13);
+  I.si_tol = problem->si_tol > 0 ? problem->si_tol : (h->mixed ? 1e-6 : 1e-13);
   for (int e = 0; e < 4; ++e)
     I.psi_edge[e] = problem->T_edge[e] >= 0 ? planck(problem->a_rad, problem->c, problem->T_edge[e]) : 0.0;
   I.lay = small_layout(r);

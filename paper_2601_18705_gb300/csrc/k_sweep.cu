@@ -74,6 +74,48 @@ __device__ __forceinline__ bool wait_progress(volatile int *flag, int need,
   return ok;
 }
 
+// Raw inputs of one 32 x 32 chunk of a band, prefetched into registers
+// (lane = column) one chunk ahead of the wavefront so that the global-load
+// latency overlaps the sweep of the previous chunk.
+template <typename real>
+struct ChunkRegs {
+  real src[32], st[32];
+};
+
+template <typename real>
+__device__ __forceinline__ void load_chunk(const SweepArgs<real> &A, int b, int k, ChunkRegs<real> &R) {
+  const int lane = threadIdx.x & 31;
+  const int u = 32 * k + lane;
+  const bool col_ok = u < A.nx;
+  const int ix = A.flipx ? A.nx - 1 - u : u;
+#pragma unroll
+  for (int ii = 0; ii < 32; ++ii) {
+    const int vv = 32 * b + ii;
+    const bool ok = col_ok && vv < A.ny;
+    const int iy = A.flipy ? A.ny - 1 - vv : vv;
+    const int c = ok ? iy * A.nx + ix : 0;
+    real s = A.src[c];
+    if (A.sphi) s += A.sphi[c];
+    R.src[ii] = ok ? s : real(0);
+    R.st[ii] = ok ? A.sig_t[c] : real(1);
+  }
+}
+
+// (source, 1 / (sigma_t + ax + ay)) of a prefetched chunk into a tile.
+template <typename real>
+__device__ __forceinline__ void store_chunk(const SweepArgs<real> &A, const ChunkRegs<real> &R,
+                                            typename Real2<real>::type *tile) {
+  const int lane = threadIdx.x & 31;
+  const real axy = A.ax + A.ay;
+#pragma unroll
+  for (int ii = 0; ii < 32; ++ii) {
+    typename Real2<real>::type e;
+    e.x = R.src[ii];
+    e.y = real(1) / (R.st[ii] + axy);
+    tile[ii * 32 + lane] = e;
+  }
+}
+
 // One band of 32 rows of one angle, swept by one warp.
 template <typename real, int NW>
 __device__ bool sweep_band(int b, const SweepArgs<real> &A, const SweepSmem &S,
@@ -91,31 +133,15 @@ __device__ bool sweep_band(int b, const SweepArgs<real> &A, const SweepSmem &S,
   const bool row_ok = v < ny;
   const int nch = (nx + 31) >> 5;
   real psi_left = A.in_x, psi_prev = real(0);
+  ChunkRegs<real> R;
+  load_chunk(A, b, 0, R);
 
   for (int k = 0; k <= nch; ++k) {
     real2 *tk = tiles + (k & 1) * 1024;        // chunk k
     real2 *tp = tiles + ((k + 1) & 1) * 1024;  // chunk k-1
-    if (k < nch) {
-      const int u = 32 * k + lane;
-      const int ix = A.flipx ? nx - 1 - u : u;
-#pragma unroll 4
-      for (int ii = 0; ii < 32; ++ii) {
-        const int vv = 32 * b + ii;
-        real2 e;
-        e.x = real(0);
-        e.y = real(0);
-        if (u < nx && vv < ny) {
-          const int iy = A.flipy ? ny - 1 - vv : vv;
-          const int c = iy * nx + ix;
-          real s = A.src[c];
-          if (A.sphi) s += A.sphi[c];
-          e.x = s;
-          e.y = real(1) / (A.sig_t[c] + A.ax + A.ay);
-        }
-        tk[ii * 32 + lane] = e;
-      }
-    }
+    if (k < nch) store_chunk(A, R, tk);
     __syncwarp();
+    if (k + 1 < nch) load_chunk(A, b, k + 1, R);  // in flight during the sweep below
 #pragma unroll 1
     for (int tau = 0; tau < 32; tau += kSub) {
       const int t0 = 32 * k + tau;
@@ -150,7 +176,7 @@ __device__ bool sweep_band(int b, const SweepArgs<real> &A, const SweepSmem &S,
       const int u = 32 * (k - 1) + lane;
       if (u < nx) {
         const int ix = A.flipx ? nx - 1 - u : u;
-#pragma unroll 4
+#pragma unroll 8
         for (int ii = 0; ii < 32; ++ii) {
           const int vv = 32 * b + ii;
           if (vv < ny) {
