@@ -204,6 +204,32 @@ int dlr_sweep(int32_t nx, int32_t ny, double lx, double ly, int32_t n_dir,
               const double *dirs, const double *psi_edge, int32_t precision,
               const void *sigma_t, const void *src, void *psi, void *stream);
 
+/* Allocation-free variant of dlr_sweep.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory, for
+ * example an application whose device memory is entirely held by another
+ * allocator (a framework's caching allocator that reserved the pool, so a
+ * fresh cudaMalloc fails or fragments it), or a latency-critical loop in
+ * which cudaMalloc / cudaFree, which may synchronise the device, are not
+ * allowed.  dlr_sweep allocates its small scratch (the directions, the edge
+ * inflow values and a wait flag) stream-ordered on every call; this variant
+ * keeps that scratch in one fixed array compiled into the library instead
+ * (about 64 KB, held on every GPU that loads the library until the process
+ * exits) and calls no allocating routine.
+ *
+ * Arguments, layouts and results are those of dlr_sweep; inputs and outputs
+ * stay the caller's.  n_dir may not exceed DLR_SWEEP_NOALLOC_MAX_DIRS
+ * (DLR_EINVAL otherwise).  The first call on a device looks up the array's
+ * device address for that device (the device current at the call); make
+ * that first call before any stream capture.  All calls share the one array,
+ * which keeps the last call's contents (the wait flag is cleared on every
+ * call): calls that overlap on the GPU, from several streams or threads at
+ * once, race on it and must be serialised by the caller.  Synchronous on
+ * stream.  Returns DLR_OK, DLR_EINVAL, DLR_ETIMEOUT or DLR_ECUDA. */
+#define DLR_SWEEP_NOALLOC_MAX_DIRS 4096
+int dlr_sweep_noalloc(int32_t nx, int32_t ny, double lx, double ly, int32_t n_dir,
+                      const double *dirs, const double *psi_edge, int32_t precision,
+                      const void *sigma_t, const void *src, void *psi, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -78,6 +78,14 @@ static int fail(int code, const char *fmt, ...) {
   return code;
 }
 
+namespace dlr {
+// lets other translation units report through dlr_last_error()
+int record_error(int code, const char *msg) {
+  g_err = msg ? msg : "";
+  return code;
+}
+}  // namespace dlr
+
 #define CK(call)                                                                      \
   do {                                                                                \
     cudaError_t e_ = (call);                                                          \
