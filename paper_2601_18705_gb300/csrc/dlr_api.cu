@@ -39,7 +39,8 @@ cudaError_t launch_apply(const ApplyJob *, int, int, int, cudaStream_t);
 template <typename real> cudaError_t launch_project(const Inst *, int, int, cudaStream_t);
 cudaError_t launch_reduce(const ReduceJob *, int, int, cudaStream_t);
 template <typename real> cudaError_t launch_tupdate(const Inst *, int, int, int, cudaStream_t);
-cudaError_t launch_select(const Inst *, int, int, cudaStream_t);
+cudaError_t launch_select(const Inst *, const SelCtl &, int, cudaStream_t);
+int select_max_grid(int);
 cudaError_t launch_chol(const CholJob *, const Inst *, int, cudaStream_t);
 cudaError_t launch_proj_post(const Inst *, int, cudaStream_t);
 size_t lstep_angle_smem(int);
@@ -47,7 +48,7 @@ cudaError_t launch_lstep(const Inst *, int, int, int, cudaStream_t);
 cudaError_t launch_svd(const Inst *, int, int, cudaStream_t);
 cudaError_t launch_sign(const Inst *, int, int, cudaStream_t);
 cudaError_t launch_si_prep(const Inst *, int, SiCtl, cudaStream_t);
-cudaError_t prepare_small(int, int);
+cudaError_t prepare_small(int, int, int);
 }  // namespace dlr
 
 using namespace dlr;
@@ -149,6 +150,9 @@ struct Batch {
   int maxN = 0, maxK = 0, rmax = 0, pbmax = 1, pblmax = 1, lbmax = 1;
   int nx_max = 0, bands_max = 0, si_grid = 0;
   SiCtl ctl{};
+  SelCtl sel{};
+  int sel_grid = 0;
+  void *sel_reset = nullptr;  // barrier words of the selection kernel (zeroed per launch)
   GramJob *g_psi1, *g_psire, *g_x, *g_x3, *g_l1, *g_lf, *g_w, *g_w3, *g_cross;
   FillJob *f_psi, *f_l;
   ApplyJob *a_psi, *a_x2, *a_x3, *a_l1, *a_w2, *a_w3, *a_wv, *a_cw, *a_cx;
@@ -356,7 +360,8 @@ static Sizes sizes_of(const dlr_problem *p, int sms) {
   s.lb = std::max(1, std::min(2 * sms, (s.K + 15) / 16));        // 4 warps x 4 angles
   const size_t r = s.r;
   s.partial_doubles = std::max({(size_t)s.pb * proj_count(s.r), (size_t)s.pb * r * r,
-                                (size_t)s.pbl * r * r, (size_t)s.lb * (r * r + r)});
+                                (size_t)s.pbl * r * r, (size_t)s.lb * (r * r + r),
+                                (size_t)(128 + 2 * 64 * 32)});  // angle-selection scratch
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
   size_t t = 0;
   t += 5 * al((size_t)s.N * 8);                 // sigma, rho_cv, T, B0, D
@@ -652,7 +657,7 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   bytes += sz(sizeof(Inst) * n);
   bytes += 9 * sz(sizeof(GramJob) * n) + 2 * sz(sizeof(FillJob) * n) + 9 * sz(sizeof(ApplyJob) * n) +
            8 * sz(sizeof(CholJob) * n) + sz(sizeof(ReduceJob) * n);
-  bytes += sz(sizeof(int2) * units.size()) + sz(64) * 3;
+  bytes += sz(sizeof(int2) * units.size()) + sz(64) * 4 + sz(sizeof(int) * (n + 1));
   if (cudaMalloc(&b->d_mem, bytes) != cudaSuccess) {
     delete b;
     return fail(DLR_ENOMEM, "batch table allocation failed");
@@ -692,6 +697,11 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   b->ctl.bar = carve<unsigned>(cur, 16);
   b->ctl.work = carve<unsigned>(cur, 16);
   b->ctl.abort_flag = carve<int>(cur, 16);
+  unsigned *sel_words = carve<unsigned>(cur, 16);
+  int *d_cta_begin = carve<int>(cur, n + 1);
+  b->sel_reset = sel_words;
+  b->sel.bar = sel_words;
+  b->sel.abort_flag = reinterpret_cast<int *>(sel_words + 2);
   b->ctl.units = d_units;
   b->ctl.n_units = (int)units.size();
   b->ctl.n_inst = n;
@@ -813,6 +823,29 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   chain(upv(b->c_l3, cl3.data(), sizeof(CholJob) * n));
   chain(upv(b->r_proj, rp.data(), sizeof(ReduceJob) * n));
   chain(upv(d_units, units.data(), sizeof(int2) * units.size()));
+  // angle selection: up to 64 CTAs per instance, 32+ angles each, all
+  // co-resident (cooperative launch)
+  {
+    std::vector<int> G(n), begin(n + 1, 0);
+    int slice_max = 1;
+    for (int i = 0; i < n; ++i) G[i] = std::max(1, std::min(64, hs[i]->K / 32));
+    for (int attempt = 0; attempt < 8; ++attempt) {
+      slice_max = 1;
+      for (int i = 0; i < n; ++i) slice_max = std::max(slice_max, (hs[i]->K + G[i] - 1) / G[i]);
+      long tot = 0;
+      for (int i = 0; i < n; ++i) tot += G[i];
+      const int cap = select_max_grid(slice_max);
+      if (cap > 0 && tot <= cap) break;
+      for (int i = 0; i < n; ++i) G[i] = std::max(1, G[i] / 2);
+    }
+    for (int i = 0; i < n; ++i) begin[i + 1] = begin[i] + G[i];
+    b->sel_grid = begin[n];
+    b->sel.cta_begin = d_cta_begin;
+    b->sel.n_inst = n;
+    b->sel.rmax = b->rmax;
+    b->sel.slice_max = slice_max;
+    chain(upv(d_cta_begin, begin.data(), sizeof(int) * (n + 1)));
+  }
   if (e != cudaSuccess) {
     destroy_batch(b);
     return fail(DLR_ECUDA, "batch table upload failed: %s", cudaGetErrorString(e));
@@ -824,7 +857,7 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
     return fail(DLR_ECUDA, "the source-iteration kernel does not fit on this GPU");
   }
   b->si_grid = gmax;
-  if ((e = prepare_small(b->maxK, b->rmax)) != cudaSuccess) {
+  if ((e = prepare_small(b->sel.slice_max, b->maxK, b->rmax)) != cudaSuccess) {
     destroy_batch(b);
     return fail(DLR_ECUDA, "kernel attribute setup failed: %s", cudaGetErrorString(e));
   }
@@ -853,7 +886,6 @@ template <typename real>
 static int enqueue_pre(Batch *b) {
   const Inst *d = b->d_insts;
   const int n = b->n;
-  LK(launch_select(d, n, b->maxK, b->st));
   LK(launch_coeff_recon<real>(d, n, b->maxN, b->rmax, b->st));
   LK(launch_si_prep(d, n, b->ctl, b->st));
   return DLR_OK;
@@ -943,7 +975,7 @@ static int run_steps(Batch *b, int nsteps) {
     b->kcount = 0;
     if ((rc = capture(b, true, &b->pre))) return rc;
     if ((rc = capture(b, false, &b->post))) return rc;
-    b->kernels_per_step = b->kcount + 1;  // + the source-iteration kernel
+    b->kernels_per_step = b->kcount + 2;  // + angle selection + source iteration
   }
   dlr_handle *h0 = b->hs[0];
   for (int s = 0; s < nsteps; ++s) {
@@ -953,6 +985,8 @@ static int run_steps(Batch *b, int nsteps) {
       for (auto &x : ev) x = pool_event(h0);
       CK(cudaEventRecord(ev[0], b->st));
     }
+    CK(cudaMemsetAsync(b->sel_reset, 0, 16, b->st));
+    CK(launch_select(b->d_insts, b->sel, b->sel_grid, b->st));
     CK(cudaGraphLaunch(b->pre, b->st));
     if (timing) CK(cudaEventRecord(ev[1], b->st));
     CK(b->mixed ? launch_si<float>(b->d_insts, b->ctl, b->si_grid, b->st)

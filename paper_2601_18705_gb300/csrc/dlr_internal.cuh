@@ -168,6 +168,17 @@ struct SiCtl {
   int nx_max, bands_max;
 };
 
+// Cooperative angle selection: CTAs [cta_begin[i], cta_begin[i+1]) serve
+// instance i; every CTA passes the same 2 * rmax grid barriers.
+struct SelCtl {
+  unsigned *bar;        // [0] arrivals, [1] generation
+  int *abort_flag;
+  const int *cta_begin; // n_inst + 1 prefix counts
+  int n_inst;
+  int rmax;
+  int slice_max;        // most angles a CTA owns
+};
+
 template <typename real> struct Real2;
 template <> struct Real2<float> { using type = float2; };
 template <> struct Real2<double> { using type = double2; };
@@ -204,6 +215,21 @@ __device__ __forceinline__ T warp_max(T v) {
   return v;
 }
 
+// sum_b part[b * stride + e] for b < nb with eight independent partial sums
+// (loads in flight together; the order of the additions is fixed, so the
+// result is deterministic).
+__device__ __forceinline__ double sum_partials(const double *__restrict__ part, int nb,
+                                               size_t stride, size_t e) {
+  double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int b = 0;
+  for (; b + 8 <= nb; b += 8) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) a[q] += part[(size_t)(b + q) * stride + e];
+  }
+  for (int q = 0; b + q < nb; ++q) a[q] += part[(size_t)(b + q) * stride + e];
+  return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+}
+
 // Block-wide sum; every thread gets the result.  scratch >= 32 entries.
 template <typename T>
 __device__ T block_sum(T v, T *scratch) {
@@ -226,6 +252,40 @@ __device__ T block_max(T v, T *scratch) {
   T t = lane < nw ? scratch[lane] : T(-1e308);
   t = warp_max(t);
   return t;
+}
+
+constexpr uint64_t kGridWaitNs = 4000000000ull;  // bound of a grid-barrier wait
+
+// Sense-reversing grid barrier with a bounded wait (co-residency of all
+// CTAs is guaranteed by the cooperative launch).
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, volatile int *abort_flag) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u);
+    int ok = 1;
+    if (arrived == gridDim.x - 1) {
+      bar[0] = 0;
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      uint64_t t0 = global_ns();
+      unsigned spins = 0;
+      while (*gen == g) {
+        if ((++spins & 63u) == 0) {
+          __nanosleep(64);
+          if (*abort_flag || global_ns() - t0 > kGridWaitNs) { ok = 0; break; }
+        }
+      }
+    }
+    __threadfence();
+    ok_s = ok && !*abort_flag;
+  }
+  __syncthreads();
+  return ok_s;
 }
 
 }  // namespace dlr

@@ -89,10 +89,15 @@ __global__ void __launch_bounds__(kTB) k_tsgram(const GramJob *__restrict__ jobs
   __shared__ real wts[kChunk / 8];
   const int r = J.r;
   const int t = threadIdx.x;
-  const int ti = (t & 15) * 2, tj = (t >> 4) * 2;  // 2x2 tile of G
-  const bool own = ti < r && tj < r;
+  // 2x2 tiles of G; for small r, G groups of threads split the rows
+  const int side = (r + 1) / 2, ntile = side * side;
+  const int ngroup = max(1, (int)blockDim.x / ntile);
+  const int grp = t / ntile, tt = t % ntile;
+  const int ti = (tt % side) * 2, tj = (tt / side) * 2;
+  const bool own = grp < ngroup;
   double acc[4] = {0, 0, 0, 0};
   const real *A = as_c<real>(J.A);
+  __shared__ double gsum[256 * 4];
   const int chunk = J.chunk;
   const int nchunks = (J.m + chunk - 1) / chunk;
   for (int ch = blockIdx.x; ch < nchunks; ch += J.nblocks) {
@@ -124,8 +129,7 @@ __global__ void __launch_bounds__(kTB) k_tsgram(const GramJob *__restrict__ jobs
       }
       __syncthreads();
       if (own) {
-#pragma unroll 8
-        for (int rr = 0; rr < 32; ++rr) {
+        for (int rr = grp; rr < 32; rr += ngroup) {
           const real w = wts[rr];
           const real a0 = tile[rr][ti] * w, a1 = tile[rr][ti + 1] * w;
           const real b0 = J.B ? tileb[rr][tj] : tile[rr][tj];
@@ -137,7 +141,14 @@ __global__ void __launch_bounds__(kTB) k_tsgram(const GramJob *__restrict__ jobs
 #pragma unroll
     for (int e = 0; e < 4; ++e) acc[e] += (double)s[e];
   }
-  if (own) {
+  // combine the groups in a fixed order
+  __syncthreads();
+  if (own && grp > 0)
+    for (int e = 0; e < 4; ++e) gsum[((grp - 1) * ntile + tt) * 4 + e] = acc[e];
+  __syncthreads();
+  if (own && grp == 0) {
+    for (int g = 1; g < ngroup; ++g)
+      for (int e = 0; e < 4; ++e) acc[e] += gsum[((g - 1) * ntile + tt) * 4 + e];
     double *o = J.out + (size_t)blockIdx.x * r * r;
     if (ti < r && tj < r) o[ti + r * tj] = acc[0];
     if (ti + 1 < r && tj < r) o[ti + 1 + r * tj] = acc[1];
@@ -229,8 +240,11 @@ __global__ void __launch_bounds__(kTB) k_project(const Inst *__restrict__ insts)
   __shared__ int ixs[CR], iys[CR];
   const int r = I.r, N = I.N, nx = I.nx;
   const int t = threadIdx.x;
-  const int ti = (t & 15) * 2, tj = (t >> 4) * 2;
-  const bool own = ti < r && tj < r;
+  const int side = (r + 1) / 2, ntile = side * side;
+  const int ngroup = ntile <= 64 ? (int)blockDim.x / ntile : 1;  // groups split the cells
+  const int grp = t / ntile, tt = t % ntile;
+  const int ti = (tt % side) * 2, tj = (tt / side) * 2;
+  const bool own = grp < ngroup;
   const real *X = as_c<real>(I.X), *X0 = as_c<real>(I.X0);
   const real *sig_t = as_c<real>(I.sig_t), *ss4 = as_c<real>(I.ss4), *qv = as_c<real>(I.q);
   double acc[6][4];
@@ -273,8 +287,7 @@ __global__ void __launch_bounds__(kTB) k_project(const Inst *__restrict__ insts)
       }
       __syncthreads();
       if (own) {
-#pragma unroll 4
-        for (int cc = 0; cc < CR; ++cc) {
+        for (int cc = grp; cc < CR; cc += ngroup) {
           const int ix = ixs[cc], iy = iys[cc];
           if (ix < 0) break;
           const real a0 = xs[cc + 1][ti], a1 = xs[cc + 1][ti + 1];
@@ -317,8 +330,19 @@ __global__ void __launch_bounds__(kTB) k_project(const Inst *__restrict__ insts)
     for (int e = 0; e < 5; ++e) vacc[e] += (double)vs[e];
   }
   double *o = I.partials + (size_t)blockIdx.x * proj_count(r);
-  if (own) {
-#pragma unroll
+  // combine the groups in a fixed order (stage through the partial slot)
+  __shared__ double gsum[6 * 4 * 64];
+  for (int g = 1; g < ngroup; ++g) {
+    __syncthreads();
+    if (own && grp == g && tt < 64)
+      for (int a = 0; a < 6; ++a)
+        for (int e = 0; e < 4; ++e) gsum[(a * 4 + e) * 64 + tt] = acc[a][e];
+    __syncthreads();
+    if (own && grp == 0 && tt < 64)
+      for (int a = 0; a < 6; ++a)
+        for (int e = 0; e < 4; ++e) acc[a][e] += gsum[(a * 4 + e) * 64 + tt];
+  }
+  if (own && grp == 0) {
     for (int a = 0; a < 6; ++a) {
       double *m = o + (size_t)a * r * r;
       if (ti < r && tj < r) m[ti + r * tj] = acc[a][0];
@@ -338,9 +362,7 @@ __global__ void __launch_bounds__(256) k_reduce(const ReduceJob *__restrict__ jo
   const ReduceJob J = jobs[blockIdx.y];
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= J.count) return;
-  double s = 0.0;
-  for (int b = 0; b < J.nblocks; ++b) s += J.part[(size_t)b * J.stride + e];
-  J.out[e] = J.scale * s;
+  J.out[e] = J.scale * sum_partials(J.part, J.nblocks, J.stride, e);
 }
 
 // ------------------------------------------------------------------

@@ -94,125 +94,193 @@ __device__ int block_argmax_tie(const double *val, int n) {
 }
 
 // ------------------------------------------------------------------
-// step 2
+// step 2: angle choice, cooperative over several CTAs per instance.  CTA g
+// of an instance owns angles [g*slice, (g+1)*slice) as columns of A = W0^T
+// in shared memory.  Per pivot step: (1) every CTA publishes the largest
+// remaining column norm it owns; grid barrier; (2) with the global maximum m
+// known everywhere, every CTA publishes its lowest angle with norm >=
+// m (1 - 1e-12) and that column; grid barrier; (3) every CTA takes the
+// lowest published angle and applies the same Householder reflection (the
+// column-pivoted QR of W0^T, reading R8).  DEIM (Section 4.2) uses the same
+// two-barrier argmax on the interpolation residual.  CTA 0 then forms What,
+// beta, gamma = What^{-T} beta and C0 = S0 What^T.
+// Scratch (in the instance's partials): lmax[64], lmin[64], cand[64][32],
+// bpart[64][32].
 // ------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_select(const Inst *__restrict__ insts) {
-  const Inst &I = insts[blockIdx.x];
-  if (*I.status != kOk) return;
-  extern __shared__ double sh[];
+__global__ void __launch_bounds__(256) k_select(const Inst *__restrict__ insts, SelCtl ctl) {
+  int inst = 0;
+  while (inst + 1 < ctl.n_inst && (int)blockIdx.x >= ctl.cta_begin[inst + 1]) ++inst;
+  const Inst &I = insts[inst];
+  const int G = ctl.cta_begin[inst + 1] - ctl.cta_begin[inst];
+  const int g = blockIdx.x - ctl.cta_begin[inst];
+  const bool active = *I.status == kOk;
   const int r = I.r, K = I.K;
-  double *val = sh;            // K
-  double *v = val + K;         // r
-  double *M = v + 32;          // r*r
-  double *rhs = M + 32 * 32;   // 32
-  __shared__ int used_dummy;
-  (void)used_dummy;
-  __shared__ int ipiv[32];
-  __shared__ int sel[32];
-  __shared__ double vv_s, alpha_s;
-  double *A = I.L;  // r x K work copy of W0^T
+  const int slice = (K + G - 1) / G, k0 = min(K, g * slice), k1 = min(K, k0 + slice), ns = k1 - k0;
+  extern __shared__ double sh[];
+  double *A = sh;                       // r x slice_max
+  double *nrm = A + 32 * ctl.slice_max; // slice_max
+  __shared__ double v[32], col[32], M[32 * 32], rhs[32];
+  __shared__ int sel[32], ipiv[32];
+  __shared__ double red_d[32];
+  __shared__ int red_i[32];
+  __shared__ int piv_s;
+  double *lmax = I.partials;
+  int *lmin = reinterpret_cast<int *>(I.partials + 64);
+  double *cand = I.partials + 128;          // 64 x 32
+  double *bpart = I.partials + 128 + 2048;  // 64 x 32
   const double *W = I.W0;
-  for (int e = threadIdx.x; e < r * K; e += blockDim.x) {
-    const int k = e / r, i = e % r;
-    A[i + r * k] = W[k + (size_t)K * i];
+  volatile int *abort_flag = ctl.abort_flag;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (active) {
+    for (int e = threadIdx.x; e < r * ns; e += blockDim.x) {
+      const int c = e / r, i = e % r;
+      A[i + r * c] = W[(k0 + c) + (size_t)K * i];
+    }
+    // this CTA's share of beta_j = sum_k w_k W0_kj
+    for (int j = wid; j < r; j += nw) {
+      double s = 0.0;
+      for (int k = k0 + lane; k < k1; k += 32) s += I.w[k] * W[k + (size_t)K * j];
+      s = warp_sum(s);
+      if (lane == 0) bpart[g * 32 + j] = s;
+    }
   }
   __syncthreads();
-  if (I.selection == 0) {
-    // column-pivoted Householder QR of A = W0^T (Businger-Golub)
-    for (int s = 0; s < r; ++s) {
-      for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        bool u = false;
-        for (int q = 0; q < s; ++q) u |= (sel[q] == k);
-        double t = 0.0;
-        for (int i = s; i < r; ++i) t += A[i + r * k] * A[i + r * k];
-        val[k] = u ? -1.0 : sqrt(t);
+  for (int s = 0; s < ctl.rmax; ++s) {
+    const bool work = active && s < r;
+    // (1) norms (or interpolation residuals) of the owned columns
+    if (work) {
+      if (I.selection == 0) {
+        for (int c = threadIdx.x; c < ns; c += blockDim.x) {
+          bool u = false;
+          for (int q = 0; q < s; ++q) u |= (sel[q] == k0 + c);
+          double t = 0.0;
+          for (int i = s; i < r; ++i) t += A[i + r * c] * A[i + r * c];
+          nrm[c] = u ? -1.0 : sqrt(t);
+        }
+      } else {
+        if (threadIdx.x == 0 && s > 0) {  // interpolation coefficients on the s chosen points
+          for (int i = 0; i < s; ++i) {
+            rhs[i] = W[sel[i] + (size_t)K * s];
+            for (int l = 0; l < s; ++l) M[i + s * l] = W[sel[i] + (size_t)K * l];
+          }
+          for (int p = 0; p < s; ++p) {
+            int pr = p;
+            for (int i = p + 1; i < s; ++i) if (fabs(M[i + s * p]) > fabs(M[pr + s * p])) pr = i;
+            if (pr != p) {
+              for (int l = 0; l < s; ++l) { double t = M[p + s * l]; M[p + s * l] = M[pr + s * l]; M[pr + s * l] = t; }
+              double t = rhs[p]; rhs[p] = rhs[pr]; rhs[pr] = t;
+            }
+            for (int i = p + 1; i < s; ++i) {
+              const double f = M[i + s * p] / M[p + s * p];
+              for (int l = p; l < s; ++l) M[i + s * l] -= f * M[p + s * l];
+              rhs[i] -= f * rhs[p];
+            }
+          }
+          for (int i = s - 1; i >= 0; --i) {
+            for (int l = i + 1; l < s; ++l) rhs[i] -= M[i + s * l] * rhs[l];
+            rhs[i] /= M[i + s * i];
+          }
+        }
+        __syncthreads();
+        for (int c = threadIdx.x; c < ns; c += blockDim.x) {
+          bool u = false;
+          for (int q = 0; q < s; ++q) u |= (sel[q] == k0 + c);
+          double res = A[s + r * c];
+          for (int l = 0; l < s; ++l) res -= rhs[l] * A[l + r * c];
+          nrm[c] = u ? -1.0 : fabs(res);
+        }
       }
       __syncthreads();
-      const int p = block_argmax_tie(val, K);
-      if (threadIdx.x == 0) {
-        sel[s] = p;
-        const double nrm = val[p];
-        const double a = A[s + r * p] >= 0 ? -nrm : nrm;
-        double vv = 0.0;
-        for (int i = s; i < r; ++i) {
-          v[i] = A[i + r * p];
-          if (i == s) v[i] -= a;
-          vv += v[i] * v[i];
-        }
-        vv_s = vv;
-        alpha_s = a;
-      }
-      __syncthreads();
-      const double vv = vv_s;
-      if (vv > 0.0)
-        for (int k = threadIdx.x; k < K; k += blockDim.x) {
-          double d = 0.0;
-          for (int i = s; i < r; ++i) d += v[i] * A[i + r * k];
-          const double f = 2.0 * d / vv;
-          for (int i = s; i < r; ++i) A[i + r * k] -= f * v[i];
-        }
-      __syncthreads();
+      double m = -1.0;
+      for (int c = threadIdx.x; c < ns; c += blockDim.x) m = fmax(m, nrm[c]);
+      m = block_max(m, red_d);
+      if (threadIdx.x == 0) lmax[g] = m;
     }
-  } else {
-    // greedy DEIM: residual of W_j after interpolation on earlier points
-    for (int j = 0; j < r; ++j) {
-      if (threadIdx.x == 0 && j > 0) {
-        for (int i = 0; i < j; ++i) {
-          rhs[i] = W[sel[i] + (size_t)K * j];
-          for (int l = 0; l < j; ++l) M[i + j * l] = W[sel[i] + (size_t)K * l];
-        }
-        // Gaussian elimination with partial pivoting, j x j
-        for (int p = 0; p < j; ++p) {
-          int pr = p;
-          for (int i = p + 1; i < j; ++i) if (fabs(M[i + j * p]) > fabs(M[pr + j * p])) pr = i;
-          if (pr != p) {
-            for (int l = 0; l < j; ++l) { double t = M[p + j * l]; M[p + j * l] = M[pr + j * l]; M[pr + j * l] = t; }
-            double t = rhs[p]; rhs[p] = rhs[pr]; rhs[pr] = t;
-          }
-          for (int i = p + 1; i < j; ++i) {
-            const double f = M[i + j * p] / M[p + j * p];
-            for (int l = p; l < j; ++l) M[i + j * l] -= f * M[p + j * l];
-            rhs[i] -= f * rhs[p];
-          }
-        }
-        for (int i = j - 1; i >= 0; --i) {
-          for (int l = i + 1; l < j; ++l) rhs[i] -= M[i + j * l] * rhs[l];
-          rhs[i] /= M[i + j * i];
-        }
+    if (!grid_barrier(ctl.bar, abort_flag)) {
+      if (threadIdx.x == 0 && g == 0) set_status(I.status, kETimeout);
+      return;
+    }
+    // (2) lowest owned angle within the tie window of the global maximum
+    if (work) {
+      double m = -1.0;
+      for (int q = 0; q < G; ++q) m = fmax(m, ((volatile double *)lmax)[q]);
+      const double thr = m * (1.0 - kTieRel);
+      int best = 0x7fffffff;
+      for (int c = threadIdx.x; c < ns; c += blockDim.x)
+        if (nrm[c] >= 0.0 && nrm[c] >= thr) best = min(best, c);
+      for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(kFullMask, best, o));
+      __syncthreads();
+      if (lane == 0) red_i[wid] = best;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int bb = 0x7fffffff;
+        for (int q = 0; q < nw; ++q) bb = min(bb, red_i[q]);
+        lmin[g] = bb == 0x7fffffff ? 0x7fffffff : k0 + bb;
+        piv_s = bb;
       }
       __syncthreads();
-      for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        bool u = false;
-        for (int q = 0; q < j; ++q) u |= (sel[q] == k);
-        double res = W[k + (size_t)K * j];
-        for (int l = 0; l < j; ++l) res -= rhs[l] * W[k + (size_t)K * l];
-        val[k] = u ? -1.0 : fabs(res);
+      if (piv_s != 0x7fffffff && threadIdx.x < r) cand[g * 32 + threadIdx.x] = A[threadIdx.x + r * piv_s];
+    }
+    if (!grid_barrier(ctl.bar, abort_flag)) {
+      if (threadIdx.x == 0 && g == 0) set_status(I.status, kETimeout);
+      return;
+    }
+    // (3) the pivot and (pivoted QR) the reflection of the owned columns
+    if (work) {
+      if (threadIdx.x == 0) {
+        int p = 0x7fffffff, owner = 0;
+        for (int q = 0; q < G; ++q) {
+          const int x = ((volatile int *)lmin)[q];
+          if (x < p) { p = x; owner = q; }
+        }
+        sel[s] = p;
+        piv_s = owner;
       }
       __syncthreads();
-      const int p = block_argmax_tie(val, K);
-      if (threadIdx.x == 0) sel[j] = p;
+      if (I.selection == 0) {
+        if (threadIdx.x < r) col[threadIdx.x] = ((volatile double *)cand)[piv_s * 32 + threadIdx.x];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          double t = 0.0;
+          for (int i = s; i < r; ++i) t += col[i] * col[i];
+          const double nrm_p = sqrt(t);
+          const double a = col[s] >= 0 ? -nrm_p : nrm_p;
+          double vv = 0.0;
+          for (int i = s; i < r; ++i) {
+            v[i] = col[i];
+            if (i == s) v[i] -= a;
+            vv += v[i] * v[i];
+          }
+          red_d[0] = vv;
+        }
+        __syncthreads();
+        const double vv = red_d[0];
+        if (vv > 0.0)
+          for (int c = threadIdx.x; c < ns; c += blockDim.x) {
+            double d = 0.0;
+            for (int i = s; i < r; ++i) d += v[i] * A[i + r * c];
+            const double f = 2.0 * d / vv;
+            for (int i = s; i < r; ++i) A[i + r * c] -= f * v[i];
+          }
+      }
       __syncthreads();
     }
   }
-  // What_ij = W0_j(Om^(i)), beta_j = sum_k w_k W0_kj
+  if (!active || g != 0) return;
+  // What_ij = W0_j(Om^(i)), beta, gamma = What^{-T} beta, C0 = S0 What^T
   double *What = I.small + I.lay.What;
   double *beta = I.small + I.lay.beta;
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     const int i = e % r, j = e / r;
     What[e] = W[sel[i] + (size_t)K * j];
   }
-  for (int i = threadIdx.x; i < r; i += blockDim.x) I.idx[i] = sel[i];
-  {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int j = wid; j < r; j += nw) {
-      double s = 0.0;
-      for (int k = lane; k < K; k += 32) s += I.w[k] * W[k + (size_t)K * j];
-      s = warp_sum(s);
-      if (lane == 0) beta[j] = s;
-    }
+  for (int i = threadIdx.x; i < r; i += blockDim.x) {
+    I.idx[i] = sel[i];
+    double t = 0.0;
+    for (int q = 0; q < G; ++q) t += ((volatile double *)bpart)[q * 32 + i];
+    beta[i] = t;
   }
   __syncthreads();
-  // gamma = What^{-T} beta (LU of What^T)
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     const int i = e % r, j = e / r;
     M[i + r * j] = What[j + r * i];
@@ -228,7 +296,6 @@ __global__ void __launch_bounds__(256) k_select(const Inst *__restrict__ insts) 
     lu_solve_serial(M, r, ipiv, rhs);
     for (int i = 0; i < r; ++i) I.small[I.lay.gamma + i] = rhs[i];
   }
-  // C0 = S0 What^T: C0_kj = sum_l S0_kl What_jl
   double *C0 = I.small + I.lay.C0;
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     const int k = e % r, j = e / r;
@@ -272,11 +339,8 @@ __global__ void __launch_bounds__(256) k_chol(const CholJob *__restrict__ jobs,
       }
     return;
   }
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < J.nblocks; ++b) s += J.part[(size_t)b * r * r + e];
-    G[e] = J.scale * s;
-  }
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x)
+    G[e] = J.scale * sum_partials(J.part, J.nblocks, (size_t)r * r, e);
   __syncthreads();
   // symmetrise (the partial sums fill both triangles)
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
@@ -468,8 +532,10 @@ __global__ void __launch_bounds__(kLsWarps * 32) k_lstep_angle(const Inst *__res
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   double *lu_w = wlu + (size_t)wid * RB * RB;
   double *mine = red + (size_t)wid * (r * r + r);
-  for (int e = lane; e < r * r + r; e += 32) mine[e] = 0.0;
-  __syncwarp();
+  double accC[RB];   // lane j: column j of sum_k w_k B_k^{-1}
+  double accZ = 0.0; // lane i: entry i of sum_k w_k B_k^{-1} Q_k
+#pragma unroll
+  for (int i = 0; i < RB; ++i) accC[i] = 0.0;
   const bool on = lane < RB;
   const int gw = blockIdx.x * kLsWarps + wid, nwarps = blocks_per_inst * kLsWarps;
   for (int k = gw; k < K; k += nwarps) {
@@ -568,11 +634,17 @@ __global__ void __launch_bounds__(kLsWarps * 32) k_lstep_angle(const Inst *__res
     for (int i = 0; i < RB; ++i) {
       if (i < r) {
         const double z = warp_sum(lane < r ? y[i] * qk : 0.0);
-        if (lane == i) mine[r * r + i] += wk * z;
-        if (lane < r) mine[i + r * lane] += wk * y[i];
+        if (lane == i) accZ += wk * z;
       }
+      accC[i] += wk * y[i];
     }
     __syncwarp();
+  }
+  if (lane < r) {
+#pragma unroll
+    for (int i = 0; i < RB; ++i)
+      if (i < r) mine[i + r * lane] = accC[i];
+    mine[r * r + lane] = accZ;
   }
   __syncthreads();
   double *out = I.partials + (size_t)blockIdx.x * (r * r + r);
@@ -593,8 +665,7 @@ __global__ void __launch_bounds__(256) k_lstep_mid(const Inst *__restrict__ inst
   const int r = I.r;
   const SmallLayout &L = I.lay;
   for (int e = threadIdx.x; e < r * r + r; e += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < blocks_per_inst; ++b) s += I.partials[(size_t)b * (r * r + r) + e];
+    const double s = sum_partials(I.partials, blocks_per_inst, (size_t)(r * r + r), e);
     if (e < r * r) Cb[e] = s; else z[e - r * r] = s;
   }
   __syncthreads();
@@ -640,23 +711,33 @@ __global__ void __launch_bounds__(kLsWarps * 32) k_lstep_back(const Inst *__rest
     double b = lane < r ? angle_q(I, sm, o, k, lane) + tv : 0.0;  // lane i holds b_i
     const double *LU = I.lu + (size_t)k * r * r;
     const int *pv = I.piv + (size_t)k * r;
+    double row[kMaxRank];  // lane i: row i of the LU factors (entry m = column m)
+#pragma unroll
+    for (int m = 0; m < kMaxRank; ++m) row[m] = (m < r && lane < r) ? LU[m * r + lane] : 0.0;
+    const int mypv = lane < r ? pv[lane] : lane;
     for (int p = 0; p < r; ++p) {
-      const int pr = pv[p];
+      const int pr = __shfl_sync(kFullMask, mypv, p);
       if (pr != p) {
         const double bp = __shfl_sync(kFullMask, b, p), bq = __shfl_sync(kFullMask, b, pr);
         if (lane == p) b = bq;
         if (lane == pr) b = bp;
       }
     }
-    for (int m = 0; m < r; ++m) {  // forward: unit lower
-      const double ym = __shfl_sync(kFullMask, b, m);
-      if (lane > m && lane < r) b -= LU[m * r + lane] * ym;
+#pragma unroll
+    for (int m = 0; m < kMaxRank; ++m) {  // forward: unit lower
+      if (m < r) {
+        const double ym = __shfl_sync(kFullMask, b, m);
+        if (lane > m && lane < r) b -= row[m] * ym;
+      }
     }
-    for (int m = r - 1; m >= 0; --m) {  // backward: upper
-      double xm = 0.0;
-      if (lane == m) { b /= LU[m * r + m]; xm = b; }
-      xm = __shfl_sync(kFullMask, xm, m);
-      if (lane < m) b -= LU[m * r + lane] * xm;
+#pragma unroll
+    for (int m = kMaxRank - 1; m >= 0; --m) {  // backward: upper
+      if (m < r) {
+        double xm = 0.0;
+        if (lane == m) { b /= row[m]; xm = b; }
+        xm = __shfl_sync(kFullMask, xm, m);
+        if (lane < m) b -= row[m] * xm;
+      }
     }
     if (lane < r) I.L[(size_t)r * k + lane] = b;
   }
@@ -680,11 +761,8 @@ __global__ void __launch_bounds__(256) k_svd(const Inst *__restrict__ insts, int
   const SmallLayout &L = I.lay;
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     double t = 0.0;
-    if (mode == 2) {
-      t = I.S0[e];
-    } else {
-      for (int b = 0; b < I.angle_blocks; ++b) t += I.partials[(size_t)b * r * r + e];
-    }
+    if (mode == 2) t = I.S0[e];
+    else t = sum_partials(I.partials, I.angle_blocks, (size_t)r * r, e);
     Uw[e] = t;  // S_ij = sum_k sqrt(w_k) L_ik Q_kj
     Vw[e] = (e % r == e / r) ? 1.0 : 0.0;
   }
@@ -823,7 +901,7 @@ __global__ void __launch_bounds__(256) k_sign(const Inst *__restrict__ insts) {
 // host launchers (kernel attributes are set by prepare_small before any
 // launch is captured into a graph)
 // ------------------------------------------------------------------
-static size_t select_smem(int maxK) { return (size_t)(maxK + 32 + 32 * 32 + 32) * sizeof(double); }
+static size_t select_smem(int slice_max) { return (size_t)(33 * slice_max) * sizeof(double); }
 static int rank_bucket(int r) { return r <= 8 ? 8 : r <= 16 ? 16 : 32; }
 size_t lstep_angle_smem(int r) {
   const int RB = rank_bucket(r);
@@ -831,10 +909,10 @@ size_t lstep_angle_smem(int r) {
 }
 static size_t lstep_back_smem(int r) { return (size_t)(6 * r * r + 5 * r) * sizeof(double); }
 
-cudaError_t prepare_small(int maxK, int rmax) {
+cudaError_t prepare_small(int slice_max, int maxK, int rmax) {
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)select_smem(maxK))) != cudaSuccess) return e;
+                                (int)select_smem(slice_max))) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_lstep_angle<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)lstep_angle_smem(rmax))) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_lstep_angle<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -846,9 +924,27 @@ cudaError_t prepare_small(int maxK, int rmax) {
   return cudaFuncSetAttribute(k_sign, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)(maxK * sizeof(double)));
 }
-cudaError_t launch_select(const Inst *d, int n, int maxK, cudaStream_t st) {
-  k_select<<<n, 256, select_smem(maxK), st>>>(d);
-  return cudaGetLastError();
+cudaError_t launch_select(const Inst *d, const SelCtl &ctl, int grid, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = select_smem(ctl.slice_max);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_select, d, ctl);
+}
+int select_max_grid(int slice_max) {
+  int per_sm = 0, dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_select, 256, select_smem(slice_max)) !=
+      cudaSuccess)
+    return 0;
+  return per_sm * sms;
 }
 cudaError_t launch_chol(const CholJob *dj, const Inst *d, int n, cudaStream_t st) {
   k_chol<<<n, 256, 0, st>>>(dj, d);

@@ -148,18 +148,27 @@ __device__ bool sweep_band(int b, const SweepArgs<real> &A, const SweepSmem &S,
       if (b > 0 && t0 < nx) {
         if (!wait_progress(prog + b - 1, min(nx, t0 + kSub), abort_flag)) return false;
       }
+      // operands of the next kSub steps, loaded before the dependent chain
+      real2 ev[kSub];
+      real ed[kSub];
+#pragma unroll
+      for (int s = 0; s < kSub; ++s) {
+        const int u = t0 + s - lane;
+        const bool active = row_ok && u >= 0 && u < nx;
+        real2 *slot = (u >= 32 * k ? tk : tp) + lane * 32 + (u & 31);
+        ev[s] = active ? *slot : real2{real(0), real(0)};
+        ed[s] = (lane == 0 && b > 0 && active) ? edge_in[u] : A.in_y;
+      }
 #pragma unroll
       for (int s = 0; s < kSub; ++s) {
         const int t = t0 + s;
         const int u = t - lane;
         real down = __shfl_up_sync(kFull, psi_prev, 1);
         const bool active = row_ok && u >= 0 && u < nx;
-        if (lane == 0) down = (b == 0) ? A.in_y : (active ? edge_in[u] : real(0));
+        if (lane == 0) down = ed[s];
         if (active) {
-          real2 *slot = (u >= 32 * k ? tk : tp) + lane * 32 + (u & 31);
-          const real2 e = *slot;
-          const real psi = (e.x + A.ax * psi_left + A.ay * down) * e.y;
-          slot->x = psi;
+          const real psi = (ev[s].x + A.ax * psi_left + A.ay * down) * ev[s].y;
+          (u >= 32 * k ? tk : tp)[lane * 32 + (u & 31)].x = psi;
           psi_left = psi;
           psi_prev = psi;
           if (lane == 31) edge_out[u] = psi;
@@ -227,38 +236,6 @@ __device__ SweepArgs<real> unit_args(const Inst &I, int j) {
   return A;
 }
 
-
-// Sense-reversing grid barrier with a bounded wait (co-residency of all
-// CTAs is guaranteed by the cooperative launch).
-__device__ bool grid_barrier(unsigned *bar, volatile int *abort_flag) {
-  __shared__ int ok_s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned *gen = bar + 1;
-    const unsigned g = *gen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(bar, 1u);
-    int ok = 1;
-    if (arrived == gridDim.x - 1) {
-      bar[0] = 0;
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      uint64_t t0 = global_ns();
-      unsigned spins = 0;
-      while (*gen == g) {
-        if ((++spins & 63u) == 0) {
-          __nanosleep(64);
-          if (*abort_flag || global_ns() - t0 > kWaitNs) { ok = 0; break; }
-        }
-      }
-    }
-    __threadfence();
-    ok_s = ok && !*abort_flag;
-  }
-  __syncthreads();
-  return ok_s;
-}
 
 template <typename real>
 __global__ void __launch_bounds__(SweepCfg<real>::NW * 32)
