@@ -233,6 +233,10 @@ __global__ void __launch_bounds__(256) k_select(const Inst *__restrict__ insts, 
           const int x = ((volatile int *)lmin)[q];
           if (x < p) { p = x; owner = q; }
         }
+        if (p < 0 || p >= K) {  // no finite candidate (NaN input)
+          set_status(I.status, kESingular);
+          p = 0;
+        }
         sel[s] = p;
         piv_s = owner;
       }
