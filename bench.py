@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="CPU work of the oracle sample")
+    ap.add_argument("--kernel", default=None, choices=["sweep"],
+                    help="time one kernel alone instead of the DLR step")
+    ap.add_argument("--workload", default=WORKLOAD, choices=["lattice32", "checker256", "lognormal1024"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     return ap.parse_args()
 
 
@@ -322,8 +326,48 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_kernel_sweep(args):
+    """The hot kernel alone: r DG0 upwind sweeps (dlr_sweep) on the workload's
+    mesh, directions of its quadrature, random sources; one CTA per direction."""
+    import torch
+    import paper_2601_18705_gb300 as dlr
+    case = workloads.CONFIGS[args.workload]()
+    nx, ny, r = case["nx"], case["ny"], case["r"]
+    N = nx * ny
+    td = torch.float32 if args.precision == "mixed" else torch.float64
+    rng = np.random.default_rng(0)
+    K = case["n_polar"] * case["n_azim"]
+    k = rng.choice(K, r, replace=False)
+    mu, wp = np.polynomial.legendre.leggauss(case["n_polar"])
+    p, a = k // case["n_azim"], k % case["n_azim"]
+    phi = (a + 0.5) * 2 * np.pi / case["n_azim"]
+    s = np.sqrt(1 - mu[p] ** 2)
+    dirs = np.stack([s * np.cos(phi), s * np.sin(phi)], 1)
+    sig_t = torch.tensor(case["sigma"].reshape(-1) + 1 / (case["c"] * case["dt"]), dtype=td, device="cuda")
+    src = torch.rand(r * N, dtype=td, device="cuda")
+    for _ in range(args.warmup):
+        dlr.sweep(nx, ny, dirs, [1, 0, 0, 0], sig_t, src)
+    torch.cuda.synchronize()
+    t = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        dlr.sweep(nx, ny, dirs, [1, 0, 0, 0], sig_t, src)
+        e1.record()
+        torch.cuda.synchronize()
+        t.append(e0.elapsed_time(e1))
+    ms = statistics.median(t)
+    print(json.dumps({"kernel": "sweep", "workload": args.workload, "precision": args.precision,
+                      "directions": r, "cells": N, "ms_median": ms,
+                      "cell_angle_updates_per_s": r * N / (ms / 1e3),
+                      "ns_per_wavefront_step": ms * 1e6 / (nx + 1.25 * ny)}))
+
+
 def main():
     args = parse()
+    if args.kernel == "sweep":
+        run_kernel_sweep(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
