@@ -357,7 +357,7 @@ static Sizes sizes_of(const dlr_problem *p, int sms) {
   s.rs = p->precision == DLR_MIXED ? 4 : 8;
   s.pb = std::max(1, std::min(2 * sms, (s.N + 511) / 512));      // >= 2 chunks of 256 cells
   s.pbl = std::max(1, std::min(2 * sms, (s.K + 63) / 64));       // >= 2 chunks of 32 angles
-  s.lb = std::max(1, std::min(2 * sms, (s.K + 15) / 16));        // 4 warps x 4 angles
+  s.lb = std::max(1, std::min(2 * sms, (s.K + 7) / 8));          // 4 warps x 2 angles
   const size_t r = s.r;
   s.partial_doubles = std::max({(size_t)s.pb * proj_count(s.r), (size_t)s.pb * r * r,
                                 (size_t)s.pbl * r * r, (size_t)s.lb * (r * r + r),

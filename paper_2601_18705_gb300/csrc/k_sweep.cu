@@ -82,18 +82,26 @@ struct ChunkRegs {
   real src[32], st[32];
 };
 
+// 1 / x: IEEE division in FP64; in FP32 the hardware reciprocal (about one
+// ulp), well inside the mixed-precision error budget.
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+
+// Cell (sweep row vv, sweep column u) -> index iy * nx + ix; rows advance by
+// row_step (+-nx) from row0 (the cell of sweep row 0 in this column).
 template <typename real>
 __device__ __forceinline__ void load_chunk(const SweepArgs<real> &A, int b, int k, ChunkRegs<real> &R) {
   const int lane = threadIdx.x & 31;
   const int u = 32 * k + lane;
   const bool col_ok = u < A.nx;
   const int ix = A.flipx ? A.nx - 1 - u : u;
+  const int row_step = A.flipy ? -A.nx : A.nx;
+  const int c0 = (A.flipy ? (A.ny - 1 - 32 * b) * A.nx : 32 * b * A.nx) + ix;
+  const int rows = min(32, A.ny - 32 * b);
 #pragma unroll
   for (int ii = 0; ii < 32; ++ii) {
-    const int vv = 32 * b + ii;
-    const bool ok = col_ok && vv < A.ny;
-    const int iy = A.flipy ? A.ny - 1 - vv : vv;
-    const int c = ok ? iy * A.nx + ix : 0;
+    const bool ok = col_ok && ii < rows;
+    const int c = ok ? c0 + ii * row_step : 0;
     real s = A.src[c];
     if (A.sphi) s += A.sphi[c];
     R.src[ii] = ok ? s : real(0);
@@ -111,7 +119,7 @@ __device__ __forceinline__ void store_chunk(const SweepArgs<real> &A, const Chun
   for (int ii = 0; ii < 32; ++ii) {
     typename Real2<real>::type e;
     e.x = R.src[ii];
-    e.y = real(1) / (R.st[ii] + axy);
+    e.y = recip(R.st[ii] + axy);
     tile[ii * 32 + lane] = e;
   }
 }
@@ -129,8 +137,8 @@ __device__ bool sweep_band(int b, const SweepArgs<real> &A, const SweepSmem &S,
   volatile real *edge_in = edge + ((b + NW) % (NW + 1)) * S.nx_max;
   volatile int *prog = S.prog;
   const int nx = A.nx, ny = A.ny;
-  const int v = 32 * b + lane;
-  const bool row_ok = v < ny;
+  const bool row_ok = 32 * b + lane < ny;
+  const bool top = lane == 31 && row_ok;
   const int nch = (nx + 31) >> 5;
   real psi_left = A.in_x, psi_prev = real(0);
   ChunkRegs<real> R;
@@ -148,36 +156,34 @@ __device__ bool sweep_band(int b, const SweepArgs<real> &A, const SweepSmem &S,
       if (b > 0 && t0 < nx) {
         if (!wait_progress(prog + b - 1, min(nx, t0 + kSub), abort_flag)) return false;
       }
-      // operands of the next kSub steps, loaded before the dependent chain
+      // operands of the next kSub steps, loaded before the dependent chain;
+      // step s of lane i touches column u = t0 + s - i, in chunk k or k-1
       real2 ev[kSub];
       real ed[kSub];
+      bool act[kSub];
 #pragma unroll
       for (int s = 0; s < kSub; ++s) {
         const int u = t0 + s - lane;
-        const bool active = row_ok && u >= 0 && u < nx;
-        real2 *slot = (u >= 32 * k ? tk : tp) + lane * 32 + (u & 31);
-        ev[s] = active ? *slot : real2{real(0), real(0)};
-        ed[s] = (lane == 0 && b > 0 && active) ? edge_in[u] : A.in_y;
+        act[s] = row_ok && u >= 0 && u < nx;
+        const int tau_u = tau + s - lane;  // column inside chunk k (negative: chunk k-1)
+        real2 *slot = (tau_u >= 0 ? tk + tau_u : tp + 32 + tau_u) + lane * 32;
+        ev[s] = *slot;
+        ed[s] = (b > 0 && act[s]) ? edge_in[max(u, 0)] : A.in_y;
       }
 #pragma unroll
       for (int s = 0; s < kSub; ++s) {
-        const int t = t0 + s;
-        const int u = t - lane;
         real down = __shfl_up_sync(kFull, psi_prev, 1);
-        const bool active = row_ok && u >= 0 && u < nx;
         if (lane == 0) down = ed[s];
-        if (active) {
-          const real psi = (ev[s].x + A.ax * psi_left + A.ay * down) * ev[s].y;
-          (u >= 32 * k ? tk : tp)[lane * 32 + (u & 31)].x = psi;
-          psi_left = psi;
-          psi_prev = psi;
-          if (lane == 31) edge_out[u] = psi;
-        }
+        const real psi = (ev[s].x + A.ax * psi_left + A.ay * down) * ev[s].y;
+        psi_left = act[s] ? psi : psi_left;
+        psi_prev = act[s] ? psi : psi_prev;
+        const int tau_u = tau + s - lane;
+        if (act[s]) (tau_u >= 0 ? tk + tau_u : tp + 32 + tau_u)[lane * 32].x = psi;
+        if (top && act[s]) edge_out[t0 + s - 31] = psi;
       }
-      if (lane == 31 && row_ok) {
+      if (top) {
         __threadfence_block();
-        const int done = min(nx, max(0, t0 + kSub - 31));
-        prog[b] = done;
+        prog[b] = min(nx, max(0, t0 + kSub - 31));
       }
     }
     __syncwarp();
@@ -185,14 +191,12 @@ __device__ bool sweep_band(int b, const SweepArgs<real> &A, const SweepSmem &S,
       const int u = 32 * (k - 1) + lane;
       if (u < nx) {
         const int ix = A.flipx ? nx - 1 - u : u;
+        const int row_step = A.flipy ? -nx : nx;
+        const int c0 = (A.flipy ? (ny - 1 - 32 * b) * nx : 32 * b * nx) + ix;
+        const int rows = min(32, ny - 32 * b);
 #pragma unroll 8
-        for (int ii = 0; ii < 32; ++ii) {
-          const int vv = 32 * b + ii;
-          if (vv < ny) {
-            const int iy = A.flipy ? ny - 1 - vv : vv;
-            A.psi[iy * nx + ix] = tp[ii * 32 + lane].x;
-          }
-        }
+        for (int ii = 0; ii < 32; ++ii)
+          if (ii < rows) A.psi[c0 + ii * row_step] = tp[ii * 32 + lane].x;
       }
     }
     __syncwarp();
