@@ -52,7 +52,10 @@ def parse():
                     help="CPU work of the oracle sample")
     ap.add_argument("--kernel", default=None, choices=["sweep"],
                     help="time one kernel alone instead of the DLR step")
-    ap.add_argument("--workload", default=WORKLOAD, choices=["lattice32", "checker256", "lognormal1024"])
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=["lattice32", "checker256", "lognormal1024", "batch64", "served"])
+    ap.add_argument("--requests", type=int, default=200, help="served: number of requests")
+    ap.add_argument("--hbm-budget-gb", type=float, default=0.0, help="served: admission budget")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     return ap.parse_args()
 
@@ -177,6 +180,22 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+# ---------------------------------------------------------------- ranks
+def reduce_over_ranks(total_ms: float, updates: float, dist=None):
+    """Whole-job aggregate of a replicated run (each rank steps its own
+    instance; no data-path collective): the slowest rank's time and the sum of
+    all ranks' updates."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(total_ms), float(updates)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=dev)
+    u = torch.tensor([float(updates)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 # ---------------------------------------------------------------- GPU
 def timed_steps(dlr, torch, solver, K, flush):
     """K steps, each timed with CUDA events on the solver's stream, L2 flushed
@@ -212,7 +231,7 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    case = workloads.checker256()
+    case = workloads.CONFIGS[args.workload]()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     # ---- main (mixed precision) ----
@@ -235,15 +254,7 @@ def run_gpu(args):
     si_ms = s1["ms_si_total"] - s0["ms_si_total"]
     si_launch = s1["si_launches"] - s0["si_launches"]
     launches = s1["kernel_launches"] - s0["kernel_launches"]
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        u = torch.tensor([float(updates)], device="cuda")
-        dist.all_reduce(u)
-        updates_all = float(u.item())
-    else:
-        updates_all = float(updates)
+    total_ms, updates_all = reduce_over_ranks(total_ms, updates, dist)
     if clk:
         time.sleep(0.1)
         clk.stop()
@@ -270,7 +281,8 @@ def run_gpu(args):
         el = time.perf_counter() - t0
         e1 = s2.stats()
         s2.close()
-        eu = float(e1["cell_angle_updates"] - e0["cell_angle_updates"]) * world
+        el_ms, eu = reduce_over_ranks(1e3 * el, e1["cell_angle_updates"] - e0["cell_angle_updates"], dist)
+        el = el_ms / 1e3
         e2e = {"value": eu / el, "unit": METRIC, "h2d_bytes_per_step": 8 * case["nx"] * case["ny"],
                "d2h_bytes_per_step": 8 * case["nx"] * case["ny"]}
 
@@ -363,10 +375,92 @@ def run_kernel_sweep(args):
                       "ns_per_wavefront_step": ms * 1e6 / (nx + 1.25 * ny)}))
 
 
+def run_batch64(args):
+    """64 independent instances stepped as one batch (one launch per kernel
+    per step for all of them), against the plain FP64 path run one instance
+    at a time on the same steps."""
+    import torch
+    import paper_2601_18705_gb300 as dlr
+    cases = workloads.batch64(steps=args.warmup + args.steps)
+    st = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    solvers = [dlr.Solver(dlr.problem_from_case(c, precision=dlr.DLR_MIXED, allow_nonpositive=1),
+                          stream=st) for c in cases]
+    dlr.step_batch(solvers, args.warmup)
+    st.synchronize()
+    u0 = sum(s.stats()["cell_angle_updates"] for s in solvers)
+    ms = 0.0
+    for _ in range(args.steps):
+        with torch.cuda.stream(st):
+            flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        dlr.step_batch(solvers, 1)
+        e1.record(st)
+        st.synchronize()
+        ms += e0.elapsed_time(e1)
+    u1 = sum(s.stats()["cell_angle_updates"] for s in solvers)
+    for s in solvers:
+        s.close()
+    value = (u1 - u0) / (ms / 1e3)
+    # plain FP64, one instance at a time, same steps
+    fp_ms, fp_upd = 0.0, 0
+    if not args.no_fp64:
+        for c in cases:
+            with dlr.Solver(dlr.problem_from_case(c, precision=dlr.DLR_FP64, allow_nonpositive=1)) as s:
+                s.step(args.warmup)
+                a = s.stats()["cell_angle_updates"]
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s.stream)
+                s.step(args.steps)
+                e1.record(s.stream)
+                s.stream.synchronize()
+                fp_ms += e0.elapsed_time(e1)
+                fp_upd += s.stats()["cell_angle_updates"] - a
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "batch64: 64 instances, sides {64..512}, ranks {8..32}, "
+                                   "128..1024 angles, one launch per kernel per step",
+                       "precision": "mixed", "l2": "flushed between timed steps"},
+            "dlr_steps_per_s": 64 * args.steps / (ms / 1e3),
+            "fp64_one_at_a_time": None if args.no_fp64 else {
+                "value": fp_upd / (fp_ms / 1e3), "dlr_steps_per_s": 64 * args.steps / (fp_ms / 1e3),
+                "ms_total": fp_ms}}
+    print(json.dumps(line))
+
+
+def run_served(args):
+    """Poisson arrivals (mean gap 50 ms); continuous batching with admission
+    by HBM footprint; latency = completion - arrival."""
+    import paper_2601_18705_gb300 as dlr  # noqa: F401
+    from paper_2601_18705_gb300 import server
+    reqs = [server.Request(rid=q["id"], arrival=t, case=workloads.materialize(q), steps=q["steps"])
+            for t, q in workloads.served_requests(n=args.requests)]
+    srv = server.Server(max_active=48, hbm_budget=int(args.hbm_budget_gb * 2 ** 30))
+    rep = srv.run(reqs, realtime=True)
+    s = rep.summary()
+    line = {"metric": METRIC, "value": s["cell_angle_updates_per_s"], "unit": METRIC, "n_gpus": 1,
+            "steps": s["ticks"], "warmup": 0, "ms_per_step": 1e3 * s["wall_s"] / max(s["ticks"], 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": f"served: {args.requests} requests, Poisson 20/s, sides "
+                                   "U{128..1024}, ranks {8,16,32}, 50-200 steps, 16x32 angles",
+                       "precision": "mixed", "hbm_budget_gb": args.hbm_budget_gb},
+            "served": s}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.kernel == "sweep":
         run_kernel_sweep(args)
+        return
+    if args.workload == "batch64" and args.impl != "reference":
+        run_batch64(args)
+        return
+    if args.workload == "served" and args.impl != "reference":
+        run_served(args)
         return
     if args.impl == "reference":
         run_reference(args)

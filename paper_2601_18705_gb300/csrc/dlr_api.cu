@@ -310,17 +310,19 @@ static bool build_X0(const dlr_handle *h, const double *T0, std::vector<double> 
   };
   for (int c = 0; c < N; ++c) X[c] = fh[c];
   int cnt = 1;
-  std::vector<double> m(N);
+  std::vector<double> m(N), cx, cy;
   for (int d = 1; d <= nx + ny - 2 && cnt < r; ++d)
     for (int k = 0; k <= d && cnt < r; ++k) {
       const int l = d - k;
       if (k >= nx || l >= ny) continue;
       const double ck = std::sqrt((k == 0 ? 1.0 : 2.0) / h->prob.lx);
       const double cl = std::sqrt((l == 0 ? 1.0 : 2.0) / h->prob.ly);
+      cx.resize(nx);
+      cy.resize(ny);
+      for (int ix = 0; ix < nx; ++ix) cx[ix] = ck * std::cos(kPi * k * (ix + 0.5) / nx);
+      for (int iy = 0; iy < ny; ++iy) cy[iy] = cl * std::cos(kPi * l * (iy + 0.5) / ny);
       for (int iy = 0; iy < ny; ++iy)
-        for (int ix = 0; ix < nx; ++ix)
-          m[iy * nx + ix] = ck * cl * std::cos(kPi * k * (ix + 0.5) / nx) *
-                            std::cos(kPi * l * (iy + 0.5) / ny);
+        for (int ix = 0; ix < nx; ++ix) m[iy * nx + ix] = cx[ix] * cy[iy];
       reflect(m);
       for (int c = 0; c < N; ++c) X[c + (size_t)N * cnt] = m[c];
       ++cnt;
