@@ -44,6 +44,7 @@ class ServeReport:
     ticks: int = 0
     max_active: int = 0
     admission_waits: int = 0
+    peak_bytes: int = 0
 
     def summary(self) -> dict:
         lat = np.array(self.latencies) if self.latencies else np.zeros(1)
@@ -52,7 +53,7 @@ class ServeReport:
                 "mean_latency_s": float(lat.mean()), "steps_per_s": self.steps_total / self.wall,
                 "cell_angle_updates_per_s": self.updates_total / self.wall,
                 "wall_s": self.wall, "ticks": self.ticks, "max_active": self.max_active,
-                "admission_waits": self.admission_waits}
+                "admission_waits": self.admission_waits, "peak_bytes": self.peak_bytes}
 
 
 class Server:
@@ -94,6 +95,7 @@ class Server:
                 q.solver = Solver(q.spec, stream=self.stream)
                 q.admitted = now
                 used += q.footprint
+                rep.peak_bytes = max(rep.peak_bytes, used)
                 active.append(q)
             if not active:
                 if pending and realtime:

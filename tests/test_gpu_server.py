@@ -47,6 +47,7 @@ def test_small_budget_serialises_admission():
     biggest = max(dlr.footprint_bytes(dlr.problem_from_case(q.case, precision=q.precision)) for q in reqs)
     srv = server.Server(max_active=8, hbm_budget=biggest, keep_results=True)
     rep = srv.run(reqs, realtime=False)
-    assert rep.max_active == 1 and len(rep.latencies) == 4
+    assert len(rep.latencies) == 4 and rep.admission_waits > 0
+    assert rep.peak_bytes <= biggest and rep.max_active < 4
     for q in reqs:
         assert np.linalg.norm(q.result_T - _alone(dlr, q)) <= 2e-5 * np.linalg.norm(q.result_T)
