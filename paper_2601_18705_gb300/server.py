@@ -16,7 +16,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import DLR_MIXED, Solver, footprint_bytes, problem_from_case, step_batch
+from . import DLR_MIXED, DlrError, Solver, footprint_bytes, problem_from_case, step_batch
 
 
 @dataclass
@@ -45,6 +45,7 @@ class ServeReport:
     max_active: int = 0
     admission_waits: int = 0
     peak_bytes: int = 0
+    failures: list = field(default_factory=list)  # (request id, step, status)
 
     def summary(self) -> dict:
         lat = np.array(self.latencies) if self.latencies else np.zeros(1)
@@ -53,7 +54,8 @@ class ServeReport:
                 "mean_latency_s": float(lat.mean()), "steps_per_s": self.steps_total / self.wall,
                 "cell_angle_updates_per_s": self.updates_total / self.wall,
                 "wall_s": self.wall, "ticks": self.ticks, "max_active": self.max_active,
-                "admission_waits": self.admission_waits, "peak_bytes": self.peak_bytes}
+                "admission_waits": self.admission_waits, "peak_bytes": self.peak_bytes,
+                "failed": len(self.failures)}
 
 
 class Server:
@@ -102,8 +104,25 @@ class Server:
                     time.sleep(max(0.0, min(0.002, pending[0].arrival - (self.clock() - t0))))
                 continue
             rep.max_active = max(rep.max_active, len(active))
-            step_batch([q.solver for q in active], 1)
-            self.stream.synchronize()  # one tick at a time: admission and latency follow the GPU
+            try:
+                step_batch([q.solver for q in active], 1)
+                self.stream.synchronize()  # one tick at a time: admission and latency follow the GPU
+            except DlrError:
+                # a request failed on the device (sticky status): drop it, keep serving the rest
+                keep = []
+                for q in active:
+                    status = q.solver.stats()["status"]
+                    if status != 0:
+                        rep.failures.append((q.rid, q.done_steps, status))
+                        q.solver.close()
+                        q.solver = None
+                        used -= q.footprint
+                    else:
+                        keep.append(q)
+                if len(keep) == len(active):
+                    raise
+                active = keep
+                continue
             rep.ticks += 1
             for q in active:
                 q.done_steps += 1
