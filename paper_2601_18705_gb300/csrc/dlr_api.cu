@@ -36,11 +36,11 @@ template <typename real> cudaError_t launch_tsgram(const GramJob *, int, int, cu
 template <typename real> cudaError_t launch_fill(const FillJob *, int, int, cudaStream_t);
 template <typename rin, typename rout>
 cudaError_t launch_apply(const ApplyJob *, int, int, int, cudaStream_t);
-template <typename real> cudaError_t launch_project(const Inst *, int, int, cudaStream_t);
+template <typename real> cudaError_t launch_project(const Inst *, int, int, int, cudaStream_t);
+cudaError_t prepare_dense(int);
 cudaError_t launch_reduce(const ReduceJob *, int, int, cudaStream_t);
 template <typename real> cudaError_t launch_tupdate(const Inst *, int, int, int, cudaStream_t);
-cudaError_t launch_select(const Inst *, const SelCtl &, int, cudaStream_t);
-int select_max_grid(int);
+cudaError_t launch_select(const Inst *, int, int, cudaStream_t);
 cudaError_t launch_chol(const CholJob *, const Inst *, int, cudaStream_t);
 cudaError_t launch_proj_post(const Inst *, int, cudaStream_t);
 size_t lstep_angle_smem(int);
@@ -150,9 +150,7 @@ struct Batch {
   int maxN = 0, maxK = 0, rmax = 0, pbmax = 1, pblmax = 1, lbmax = 1;
   int nx_max = 0, bands_max = 0, si_grid = 0;
   SiCtl ctl{};
-  SelCtl sel{};
-  int sel_grid = 0;
-  void *sel_reset = nullptr;  // barrier words of the selection kernel (zeroed per launch)
+  int sel_slice_max = 1;      // most angles one CTA of the selection cluster owns
   GramJob *g_psi1, *g_psire, *g_x, *g_x3, *g_l1, *g_lf, *g_w, *g_w3, *g_cross;
   FillJob *f_psi, *f_l;
   ApplyJob *a_psi, *a_x2, *a_x3, *a_l1, *a_w2, *a_w3, *a_wv, *a_cw, *a_cx;
@@ -357,13 +355,15 @@ static Sizes sizes_of(const dlr_problem *p, int sms) {
   s.K = p->n_polar * p->n_azim;
   s.r = p->rank;
   s.rs = p->precision == DLR_MIXED ? 4 : 8;
-  s.pb = std::max(1, std::min(2 * sms, (s.N + 511) / 512));      // >= 2 chunks of 256 cells
-  s.pbl = std::max(1, std::min(2 * sms, (s.K + 63) / 64));       // >= 2 chunks of 32 angles
+  // CTAs of the cell and angle reductions: whole clusters of kCl CTAs,
+  // about 512 cells or 16 angles per CTA
+  auto clusters = [](int x) { return (x + kCl - 1) / kCl * kCl; };
+  s.pb = clusters(std::max(1, std::min(2 * sms, (s.N + 511) / 512)));
+  s.pbl = clusters(std::max(1, std::min(2 * sms, (s.K + 15) / 16)));
   s.lb = std::max(1, std::min(2 * sms, (s.K + 7) / 8));          // 4 warps x 2 angles
   const size_t r = s.r;
-  s.partial_doubles = std::max({(size_t)s.pb * proj_count(s.r), (size_t)s.pb * r * r,
-                                (size_t)s.pbl * r * r, (size_t)s.lb * (r * r + r),
-                                (size_t)(128 + 2 * 64 * 32)});  // angle-selection scratch
+  s.partial_doubles = std::max({(size_t)(s.pb / kCl) * proj_count(s.r), (size_t)(s.pb / kCl) * r * r,
+                                (size_t)(s.pbl / kCl) * r * r, (size_t)s.lb * (r * r + r)});
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
   size_t t = 0;
   t += 5 * al((size_t)s.N * 8);                 // sigma, rho_cv, T, B0, D
@@ -659,7 +659,7 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   bytes += sz(sizeof(Inst) * n);
   bytes += 9 * sz(sizeof(GramJob) * n) + 2 * sz(sizeof(FillJob) * n) + 9 * sz(sizeof(ApplyJob) * n) +
            8 * sz(sizeof(CholJob) * n) + sz(sizeof(ReduceJob) * n);
-  bytes += sz(sizeof(int2) * units.size()) + sz(64) * 4 + sz(sizeof(int) * (n + 1));
+  bytes += sz(sizeof(int2) * units.size()) + sz(64) * 3;
   if (cudaMalloc(&b->d_mem, bytes) != cudaSuccess) {
     delete b;
     return fail(DLR_ENOMEM, "batch table allocation failed");
@@ -699,11 +699,6 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   b->ctl.bar = carve<unsigned>(cur, 16);
   b->ctl.work = carve<unsigned>(cur, 16);
   b->ctl.abort_flag = carve<int>(cur, 16);
-  unsigned *sel_words = carve<unsigned>(cur, 16);
-  int *d_cta_begin = carve<int>(cur, n + 1);
-  b->sel_reset = sel_words;
-  b->sel.bar = sel_words;
-  b->sel.abort_flag = reinterpret_cast<int *>(sel_words + 2);
   b->ctl.units = d_units;
   b->ctl.n_units = (int)units.size();
   b->ctl.n_inst = n;
@@ -728,7 +723,6 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
       GramJob g{};
       g.A = A; g.wt = wt; g.m = m; g.r = r; g.lda = lda; g.layout = layout;
       g.out = I.partials; g.nblocks = nb; g.run_if = run_if;
-      g.chunk = (m == N) ? 256 : 32;  // cells: 256-row FP32 chunks; angles (FP64): 32
       return g;
     };
     gp1[i] = gram(I.Psi, nullptr, N, N, 0, h->pb, nullptr);
@@ -759,32 +753,40 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
       a.run_if = run_if;
       return a;
     };
-    ap[i] = apply(I.Psi, 0, N, nullptr, 0, sm + L.R1i, I.X, N, nullptr, 0, N, nullptr);
-    ax2[i] = apply(I.X, 0, N, nullptr, 0, sm + L.R2i, I.X, N, nullptr, 0, N, nullptr);
-    ax3[i] = apply(I.X, 0, N, nullptr, 0, sm + L.R3i, I.X, N, nullptr, 0, N, flag);
-    al1[i] = apply(I.Lf, 1, r, I.w, 1, sm + L.R1i, I.W0, K, nullptr, 0, K, nullptr);
-    aw2[i] = apply(I.W0, 0, K, nullptr, 0, sm + L.R2i, I.W0, K, nullptr, 0, K, nullptr);
-    aw3[i] = apply(I.W0, 0, K, nullptr, 0, sm + L.R3i, I.W0, K, nullptr, 0, K, flag);
+    // CholeskyQR passes: Q = A R^{-1} by forward substitution
+    auto solve = [&](const void *A, int layout, int lda, const double *s_in, const double *R,
+                     void *outp, int ldo, int m, const int *run_if) {
+      ApplyJob a = apply(A, layout, lda, s_in, s_in ? 1 : 0, R, outp, ldo, nullptr, 0, m, run_if);
+      a.tri = 1;
+      return a;
+    };
+    ap[i] = solve(I.Psi, 0, N, nullptr, sm + L.R1, I.X, N, N, nullptr);
+    ax2[i] = solve(I.X, 0, N, nullptr, sm + L.R2, I.X, N, N, nullptr);
+    ax3[i] = solve(I.X, 0, N, nullptr, sm + L.R3, I.X, N, N, flag);
+    al1[i] = solve(I.Lf, 1, r, I.w, sm + L.R1, I.W0, K, K, nullptr);
+    aw2[i] = solve(I.W0, 0, K, nullptr, sm + L.R2, I.W0, K, K, nullptr);
+    aw3[i] = solve(I.W0, 0, K, nullptr, sm + L.R3, I.W0, K, K, flag);
     awv[i] = apply(I.W0, 0, K, nullptr, 0, sm + L.V, I.W0, K, I.w, 1, K, nullptr);
     acw[i] = apply(I.W0, 0, K, nullptr, 0, sm + L.V, I.W0, K, nullptr, 0, K, nullptr);
     acx[i] = apply(I.X0, 0, N, nullptr, 0, sm + L.U, I.X0, N, nullptr, 0, N, nullptr);
     const double u = h->mixed ? 1e-7 : 1e-15, tau = h->mixed ? 1e-10 : 1e-24;
-    auto chol = [&](int nb, double scale, double *R, double *Ri, int mode) {
+    auto chol = [&](int nparts, double scale, double *R, int mode) {
       CholJob c{};
-      c.part = I.partials; c.nblocks = nb; c.scale = scale; c.R = R; c.Ri = Ri;
+      c.part = I.partials; c.nblocks = nparts; c.scale = scale; c.R = R;
       c.flag = flag; c.r = r; c.mode = mode; c.u = u; c.tau_dep = tau;
       return c;
     };
-    cp1[i] = chol(h->pb, I.h2, sm + L.R1, sm + L.R1i, 1);
-    cp1b[i] = chol(h->pb, I.h2, sm + L.R1, sm + L.R1i, 4);
-    cp2[i] = chol(h->pb, I.h2, sm + L.R2, sm + L.R2i, 2);
-    cp3[i] = chol(h->pb, I.h2, sm + L.R3, sm + L.R3i, 3);
-    cl1[i] = chol(h->pbl, 1.0, sm + L.R1, sm + L.R1i, 1);
-    cl1b[i] = chol(h->pbl, 1.0, sm + L.R1, sm + L.R1i, 4);
-    cl2[i] = chol(h->pbl, 1.0, sm + L.R2, sm + L.R2i, 2);
-    cl3[i] = chol(h->pbl, 1.0, sm + L.R3, sm + L.R3i, 3);
+    const int pc = h->pb / kCl, pcl = h->pbl / kCl;  // partials: one per cluster
+    cp1[i] = chol(pc, I.h2, sm + L.R1, 1);
+    cp1b[i] = chol(pc, I.h2, sm + L.R1, 4);
+    cp2[i] = chol(pc, I.h2, sm + L.R2, 2);
+    cp3[i] = chol(pc, I.h2, sm + L.R3, 3);
+    cl1[i] = chol(pcl, 1.0, sm + L.R1, 1);
+    cl1b[i] = chol(pcl, 1.0, sm + L.R1, 4);
+    cl2[i] = chol(pcl, 1.0, sm + L.R2, 2);
+    cl3[i] = chol(pcl, 1.0, sm + L.R3, 3);
     ReduceJob red{};
-    red.part = I.partials; red.nblocks = h->pb; red.stride = proj_count(r);
+    red.part = I.partials; red.nblocks = pc; red.stride = proj_count(r);
     red.count = proj_count(r); red.out = sm + L.G; red.scale = 1.0;
     rp[i] = red;
   }
@@ -825,29 +827,8 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   chain(upv(b->c_l3, cl3.data(), sizeof(CholJob) * n));
   chain(upv(b->r_proj, rp.data(), sizeof(ReduceJob) * n));
   chain(upv(d_units, units.data(), sizeof(int2) * units.size()));
-  // angle selection: up to 64 CTAs per instance, 32+ angles each, all
-  // co-resident (cooperative launch)
-  {
-    std::vector<int> G(n), begin(n + 1, 0);
-    int slice_max = 1;
-    for (int i = 0; i < n; ++i) G[i] = std::max(1, std::min(64, hs[i]->K / 32));
-    for (int attempt = 0; attempt < 8; ++attempt) {
-      slice_max = 1;
-      for (int i = 0; i < n; ++i) slice_max = std::max(slice_max, (hs[i]->K + G[i] - 1) / G[i]);
-      long tot = 0;
-      for (int i = 0; i < n; ++i) tot += G[i];
-      const int cap = select_max_grid(slice_max);
-      if (cap > 0 && tot <= cap) break;
-      for (int i = 0; i < n; ++i) G[i] = std::max(1, G[i] / 2);
-    }
-    for (int i = 0; i < n; ++i) begin[i + 1] = begin[i] + G[i];
-    b->sel_grid = begin[n];
-    b->sel.cta_begin = d_cta_begin;
-    b->sel.n_inst = n;
-    b->sel.rmax = b->rmax;
-    b->sel.slice_max = slice_max;
-    chain(upv(d_cta_begin, begin.data(), sizeof(int) * (n + 1)));
-  }
+  // angle selection: one cluster of kCl CTAs per instance
+  b->sel_slice_max = std::max(1, (b->maxK + kCl - 1) / kCl);
   if (e != cudaSuccess) {
     destroy_batch(b);
     return fail(DLR_ECUDA, "batch table upload failed: %s", cudaGetErrorString(e));
@@ -859,7 +840,8 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
     return fail(DLR_ECUDA, "the source-iteration kernel does not fit on this GPU");
   }
   b->si_grid = gmax;
-  if ((e = prepare_small(b->sel.slice_max, b->maxK, b->rmax)) != cudaSuccess) {
+  if ((e = prepare_small(b->sel_slice_max, b->maxK, b->rmax)) != cudaSuccess ||
+      (e = prepare_dense(b->rmax)) != cudaSuccess) {
     destroy_batch(b);
     return fail(DLR_ECUDA, "kernel attribute setup failed: %s", cudaGetErrorString(e));
   }
@@ -888,6 +870,7 @@ template <typename real>
 static int enqueue_pre(Batch *b) {
   const Inst *d = b->d_insts;
   const int n = b->n;
+  LK(launch_select(d, n, b->sel_slice_max, b->st));
   LK(launch_coeff_recon<real>(d, n, b->maxN, b->rmax, b->st));
   LK(launch_si_prep(d, n, b->ctl, b->st));
   return DLR_OK;
@@ -914,7 +897,7 @@ static int enqueue_post(Batch *b) {
   LK(launch_chol(b->c_p3, d, n, st));
   LK((launch_apply<real, real>(b->a_x3, n, b->maxN, b->rmax, st)));
   // steps 6-7: projections and the L-step
-  LK(launch_project<real>(d, n, b->pbmax, st));
+  LK(launch_project<real>(d, n, b->pbmax, b->rmax, st));
   LK(launch_reduce(b->r_proj, n, proj_count(b->rmax), st));
   LK(launch_proj_post(d, n, st));
   LK(launch_lstep(d, n, b->rmax, b->lbmax, st));
@@ -977,7 +960,7 @@ static int run_steps(Batch *b, int nsteps) {
     b->kcount = 0;
     if ((rc = capture(b, true, &b->pre))) return rc;
     if ((rc = capture(b, false, &b->post))) return rc;
-    b->kernels_per_step = b->kcount + 2;  // + angle selection + source iteration
+    b->kernels_per_step = b->kcount + 1;  // + source iteration
   }
   dlr_handle *h0 = b->hs[0];
   for (int s = 0; s < nsteps; ++s) {
@@ -987,8 +970,6 @@ static int run_steps(Batch *b, int nsteps) {
       for (auto &x : ev) x = pool_event(h0);
       CK(cudaEventRecord(ev[0], b->st));
     }
-    CK(cudaMemsetAsync(b->sel_reset, 0, 16, b->st));
-    CK(launch_select(b->d_insts, b->sel, b->sel_grid, b->st));
     CK(cudaGraphLaunch(b->pre, b->st));
     if (timing) CK(cudaEventRecord(ev[1], b->st));
     CK(b->mixed ? launch_si<float>(b->d_insts, b->ctl, b->si_grid, b->st)

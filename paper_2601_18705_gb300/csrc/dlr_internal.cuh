@@ -8,16 +8,23 @@
 //   f64   W0[K*r] (column-major), S0[r*r], L[r*K] (angle-major rows of r)
 //   f64   small[]   r x r work matrices (offsets in SmallLayout)
 //   f64   lu[K*r*r], int piv[K*r]  per-angle LU factors of B_k
-//   f64   partials[] per-block partial sums of the tall-skinny reductions
+//   f64   partials[] per-cluster partial sums of the tall-skinny reductions
 // "real" is float in mixed precision and double in FP64 mode.
 #pragma once
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace dlr {
 
+namespace cg = cooperative_groups;
+
 constexpr int kMaxRank = 32;
+// CTAs per thread-block cluster of the tall-skinny reductions: the CTAs of a
+// cluster sum their partials through distributed shared memory, so one
+// partial per cluster reaches global memory.
+constexpr int kCl = 8;
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kTieRel = 1e-12;  // angle-selection tie window
 
@@ -31,7 +38,7 @@ constexpr int kENonPos = -6;
 // Offsets (in doubles) of the r x r work matrices inside Inst::small.
 struct SmallLayout {
   int What, WLU, beta, gamma, C0;      // angle selection
-  int R1, R1i, R2, R2i, R3, R3i;       // CholeskyQR factors / inverses
+  int R1, R2, R3;                      // CholeskyQR factors
   int qr_flag;    // ints: [0] third pass needed, [1] filled columns, [2..] mask
   int G, Nx, Ny, Mt, Ms, P, vec;       // projections (vec: qh, bL, bR, bB, bT)
   int Axp, Axm, Ayp, Aym, PS0;         // L-step operators
@@ -45,8 +52,7 @@ inline SmallLayout small_layout(int r) {
   int o = 0;
   auto m = [&](int n) { int at = o; o += n; return at; };
   s.What = m(r * r); s.WLU = m(r * r); s.beta = m(r); s.gamma = m(r); s.C0 = m(r * r);
-  s.R1 = m(r * r); s.R1i = m(r * r); s.R2 = m(r * r); s.R2i = m(r * r);
-  s.R3 = m(r * r); s.R3i = m(r * r); s.qr_flag = m(20);
+  s.R1 = m(r * r); s.R2 = m(r * r); s.R3 = m(r * r); s.qr_flag = m(20);
   s.G = m(r * r); s.Nx = m(r * r); s.Ny = m(r * r); s.Mt = m(r * r); s.Ms = m(r * r);
   s.P = m(r * r); s.vec = m(5 * r);
   s.Axp = m(r * r); s.Axm = m(r * r); s.Ayp = m(r * r); s.Aym = m(r * r); s.PS0 = m(r * r);
@@ -86,8 +92,8 @@ struct Inst {
   int *piv;
   // partial sums of block reductions (partial_stride doubles per block)
   double *partials;
-  int partial_blocks;      // blocks of the cell reductions (project, Gram)
-  int angle_blocks;        // blocks of the angle reductions (Grams of L)
+  int partial_blocks;      // CTAs of the cell reductions (project, Gram; whole clusters)
+  int angle_blocks;        // CTAs of the angle reductions (Grams of L; whole clusters)
   int lstep_blocks;        // blocks of the per-angle L-step
   // status and iteration bookkeeping
   int *status;            // sticky device status
@@ -108,13 +114,14 @@ struct GramJob {
   const void *B;    // optional: cross Gram sum wt a b^T with B (layout 0, ldb)
   int ldb;
   int sqrt_wt;      // 1: weight sqrt(wt) instead of wt
-  int chunk;        // rows per FP32 partial sum (multiple of 32)
-  double *out;      // partial sums
-  int nblocks;      // blocks used for this job
+  double *out;      // partial sums, one r x r block per cluster
+  int nblocks;      // CTAs used for this job (a multiple of kCl)
   const int *run_if;  // optional: skip unless *run_if != 0
 };
 
-// out = diag(s_out) (diag(s_in) A) T for a small r x r T (FP64).
+// out = diag(s_out) (diag(s_in) A) T for a small r x r T (FP64); with tri
+// set, T holds an upper-triangular R and out = diag(s_out) (diag(s_in) A) R^-1
+// (forward substitution per row).
 struct ApplyJob {
   const void *A;        // input (real_in)
   int in_layout;        // 0: column-major (lda), 1: rows of r contiguous
@@ -127,6 +134,7 @@ struct ApplyJob {
   const double *s_out;  // optional per-row scale
   int inv_sq_out;       // 1: multiply by 1/sqrt(s_out)
   int m, r;
+  int tri;              // 1: T is upper triangular, apply its inverse
   const int *run_if;  // optional: skip unless *run_if != 0
 };
 
@@ -139,9 +147,9 @@ struct ReduceJob {
 
 struct CholJob {
   const double *part;
-  int nblocks;
+  int nblocks;      // partials (clusters) to sum
   double scale;
-  double *R, *Ri;
+  double *R;        // upper-triangular factor (applied by forward substitution)
   int *flag;        // ints: [0] third pass needed, [1] filled columns, [2..] mask
   int r;
   int mode;         // 1 detect, 2 plain, 3 only if flag[0], 4 only if flag[1]
@@ -168,16 +176,8 @@ struct SiCtl {
   int nx_max, bands_max;
 };
 
-// Cooperative angle selection: CTAs [cta_begin[i], cta_begin[i+1]) serve
-// instance i; every CTA passes the same 2 * rmax grid barriers.
-struct SelCtl {
-  unsigned *bar;        // [0] arrivals, [1] generation
-  int *abort_flag;
-  const int *cta_begin; // n_inst + 1 prefix counts
-  int n_inst;
-  int rmax;
-  int slice_max;        // most angles a CTA owns
-};
+// Four consecutive elements, aligned for one vector shared-memory access.
+template <typename real> struct alignas(4 * sizeof(real)) Quad { real v[4]; };
 
 template <typename real> struct Real2;
 template <> struct Real2<float> { using type = float2; };
@@ -226,7 +226,9 @@ __device__ __forceinline__ double sum_partials(const double *__restrict__ part, 
 #pragma unroll
     for (int q = 0; q < 8; ++q) a[q] += part[(size_t)(b + q) * stride + e];
   }
-  for (int q = 0; b + q < nb; ++q) a[q] += part[(size_t)(b + q) * stride + e];
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    if (b + q < nb) a[q] += part[(size_t)(b + q) * stride + e];
   return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
 }
 

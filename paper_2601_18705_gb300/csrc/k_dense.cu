@@ -6,19 +6,19 @@
 //                  and the starting scalar flux gamma^T Psi0
 //   k_tsgram       G = sum_c wt_c a_c a_c^T for a tall-skinny matrix (step 5
 //                  CholeskyQR Grams of Psi and step 8 Grams of L)
-//   k_apply        out = diag(s_out) (diag(s_in) A) T for a small dense T
+//   k_apply        out = diag(s_out) (diag(s_in) A) T for a small dense T, or
+//                  A R^{-1} for a CholeskyQR factor R (forward substitution)
 //   k_project      step 6 P = <X, X0> and the step 7 Galerkin operators:
 //                  Gram, x/y neighbour Grams, <sigma_t X, X>, <sigma_s X, X>,
 //                  <q, X> and the four edge sums
 //   k_tupdate      step 9 temperature update (Eq. temperature update, Newton
 //                  form) with phi = X (L w), fused with the rotation X0 <- X U
-// Mixed precision: products and sums over a chunk of kChunk cells in FP32,
-// chunk sums accumulated in FP64.
+// Mixed precision: products and sums over one staging round (at most 128
+// rows) in FP32, round sums accumulated in FP64.
 #include "dlr_internal.cuh"
 
 namespace dlr {
 
-constexpr int kChunk = 256;   // cells per FP32 partial sum
 constexpr int kTB = 256;      // threads per block of the reduction kernels
 
 // ------------------------------------------------------------------
@@ -74,87 +74,156 @@ __global__ void __launch_bounds__(256) k_coeff_recon(const Inst *__restrict__ in
 }
 
 // ------------------------------------------------------------------
-// tall-skinny Gram with 2x2 register tiles per thread (r <= 32)
+// tall-skinny Gram, one thread-block cluster per slice of rows (r <= 32)
 // ------------------------------------------------------------------
 // A is m x r; layout 0: column-major A[row + lda*i]; layout 1: rows of r
-// contiguous A[i + r*row].  wt: per-row weight or nullptr.  Each block
-// writes its partial r x r sum (FP64, column-major) to out + blockIdx.x*r*r.
+// contiguous A[i + r*row].  wt: per-row weight or nullptr.  The CTAs of a
+// job split the rows evenly; each stages GR rows per round in shared memory
+// (column-major, the next round prefetched into registers while the current
+// one is multiplied) and every thread accumulates a 4 x 4 tile of G over the
+// rows of its group.  FP32 tiles are added to FP64 accumulators after every
+// round.  The CTA partial is summed over the cluster through distributed
+// shared memory (fixed order); cluster c writes its r x r sum (FP64,
+// column-major) to out + c*r*r.
+template <typename real> struct GramCfg;
+template <> struct GramCfg<float> { static constexpr int GR = 128; };
+template <> struct GramCfg<double> { static constexpr int GR = 64; };
 
 template <typename real>
-__global__ void __launch_bounds__(kTB) k_tsgram(const GramJob *__restrict__ jobs) {
-  const GramJob J = jobs[blockIdx.y];
+constexpr int gram_smem_bytes() {
+  constexpr int GR = GramCfg<real>::GR;
+  constexpr int tiles = (2 * 32 * (GR + 4) + GR) * (int)sizeof(real);
+  constexpr int red = (kTB * 16 + 32 * 32) * 8;
+  return tiles > red ? tiles : red;
+}
+
+template <typename real>
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kTB)
+k_tsgram(const GramJob *__restrict__ jobs) {
+  constexpr int GR = GramCfg<real>::GR, LD = GR + 4;
+  constexpr int PF = GR * 32 / kTB;  // prefetched elements per thread and matrix
+  const GramJob &J = jobs[blockIdx.y];
+  // nblocks is a multiple of the cluster size and run_if is per job, so
+  // whole clusters leave together
   if ((int)blockIdx.x >= J.nblocks || (J.run_if && *J.run_if == 0)) return;
-  __shared__ real tile[kChunk / 8][33];  // 32 rows x r columns
-  __shared__ real tileb[kChunk / 8][33];
-  __shared__ real wts[kChunk / 8];
-  const int r = J.r;
-  const int t = threadIdx.x;
-  // 2x2 tiles of G; for small r, G groups of threads split the rows
-  const int side = (r + 1) / 2, ntile = side * side;
-  const int ngroup = max(1, (int)blockDim.x / ntile);
-  const int grp = t / ntile, tt = t % ntile;
-  const int ti = (tt % side) * 2, tj = (tt / side) * 2;
-  const bool own = grp < ngroup;
-  double acc[4] = {0, 0, 0, 0};
-  const real *A = as_c<real>(J.A);
-  __shared__ double gsum[256 * 4];
-  const int chunk = J.chunk;
-  const int nchunks = (J.m + chunk - 1) / chunk;
-  for (int ch = blockIdx.x; ch < nchunks; ch += J.nblocks) {
-    real s[4] = {0, 0, 0, 0};
-    for (int sub = 0; sub < chunk; sub += 32) {
-      const int row0 = ch * chunk + sub;
-      __syncthreads();
-      for (int e = t; e < 32 * r; e += blockDim.x) {
-        int rr, i;
-        if (J.layout == 0) { rr = e & 31; i = e >> 5; }
-        else { i = e % r; rr = e / r; }
-        const int row = row0 + rr;
-        real v = real(0);
-        if (row < J.m) v = J.layout == 0 ? A[(size_t)J.lda * i + row] : A[(size_t)r * row + i];
-        tile[rr][i] = v;
+  cg::cluster_group cluster = cg::this_cluster();
+  __shared__ __align__(32) unsigned char raw[gram_smem_bytes<real>()];
+  real *As = reinterpret_cast<real *>(raw);
+  real *Bs = As + 32 * LD;
+  real *ws = Bs + 32 * LD;
+  const int r = J.r, t = threadIdx.x, lay = J.layout;
+  const int side = (r + 3) >> 2, ntile = side * side;
+  const int ngroup = kTB / ntile;
+  const int grp = t / ntile, tt = t - grp * ntile;
+  const int ti = 4 * (tt % side), tj = 4 * (tt / side);
+  const bool cross = J.B != nullptr;
+  // a symmetric Gram needs the tiles on and above the diagonal only
+  const bool own = grp < ngroup && (cross || tj >= ti);
+  const real *A = as_c<real>(J.A), *Bm = as_c<real>(J.B);
+  const int per = (J.m + J.nblocks - 1) / J.nblocks;
+  const int row0 = min(J.m, (int)blockIdx.x * per), row1 = min(J.m, row0 + per);
+  const int nround = (row1 - row0 + GR - 1) / GR;
+  real pa[PF], pbv[PF], pw = real(0);
+  auto prefetch = [&](int rd) {
+    const int base = row0 + rd * GR;
+#pragma unroll
+    for (int k = 0; k < PF; ++k) {
+      const int e = t + kTB * k;
+      const int rr = lay == 0 ? e % GR : e / r, i = lay == 0 ? e / GR : e % r;
+      const bool ok = rr < GR && i < r && base + rr < row1;
+      const size_t at = lay == 0 ? (size_t)J.lda * i + base + rr : (size_t)r * (base + rr) + i;
+      pa[k] = ok ? A[at] : real(0);
+      if (cross) pbv[k] = ok ? Bm[(size_t)J.ldb * i + base + rr] : real(0);
+    }
+    if (t < GR) {
+      const int row = base + t;
+      double w = 0.0;
+      if (row < row1) {
+        w = J.wt ? J.wt[row] : 1.0;
+        if (J.sqrt_wt) w = sqrt(w);
       }
-      if (J.B) {
-        const real *Bm = as_c<real>(J.B);
-        for (int e = t; e < 32 * r; e += blockDim.x) {
-          const int rr = e & 31, i = e >> 5, row = row0 + rr;
-          tileb[rr][i] = row < J.m ? Bm[(size_t)J.ldb * i + row] : real(0);
-        }
-      }
-      if (t < 32) {
-        const int row = row0 + t;
-        double wv = (row < J.m) ? (J.wt ? J.wt[row] : 1.0) : 0.0;
-        if (J.sqrt_wt) wv = sqrt(wv);
-        wts[t] = real(wv);
-      }
-      __syncthreads();
-      if (own) {
-        for (int rr = grp; rr < 32; rr += ngroup) {
-          const real w = wts[rr];
-          const real a0 = tile[rr][ti] * w, a1 = tile[rr][ti + 1] * w;
-          const real b0 = J.B ? tileb[rr][tj] : tile[rr][tj];
-          const real b1 = J.B ? tileb[rr][tj + 1] : tile[rr][tj + 1];
-          s[0] += a0 * b0; s[1] += a1 * b0; s[2] += a0 * b1; s[3] += a1 * b1;
-        }
+      pw = real(w);
+    }
+  };
+  real s[16];
+  double acc[16];
+#pragma unroll
+  for (int e = 0; e < 16; ++e) { s[e] = real(0); acc[e] = 0.0; }
+  if (nround > 0) prefetch(0);
+  for (int rd = 0; rd < nround; ++rd) {
+    __syncthreads();  // the previous round's products are done
+#pragma unroll
+    for (int k = 0; k < PF; ++k) {
+      const int e = t + kTB * k;
+      const int rr = lay == 0 ? e % GR : e / r, i = lay == 0 ? e / GR : e % r;
+      if (rr < GR && i < r) {
+        As[i * LD + rr] = pa[k];
+        if (cross) Bs[i * LD + rr] = pbv[k];
       }
     }
+    if (t < GR) ws[t] = pw;
+    __syncthreads();
+    if (rd + 1 < nround) prefetch(rd + 1);  // in flight during the products below
+    if (own) {
+      const real *Bsrc = cross ? Bs : As;
+      const int nq = (min(GR, row1 - row0 - rd * GR) + 3) >> 2;  // quads holding rows
+      for (int q = grp; q < nq; q += ngroup) {
+        Quad<real> a[4], b[4];
+        const Quad<real> w = *reinterpret_cast<const Quad<real> *>(ws + 4 * q);
 #pragma unroll
-    for (int e = 0; e < 4; ++e) acc[e] += (double)s[e];
+        for (int k = 0; k < 4; ++k) {
+          a[k] = *reinterpret_cast<const Quad<real> *>(As + (ti + k) * LD + 4 * q);
+          b[k] = *reinterpret_cast<const Quad<real> *>(Bsrc + (tj + k) * LD + 4 * q);
+#pragma unroll
+          for (int m = 0; m < 4; ++m) a[k].v[m] *= w.v[m];
+        }
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int m = 0; m < 4; ++m) s[kk * 4 + k] += a[kk].v[m] * b[k].v[m];
+      }
+      if (sizeof(real) == 4) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) { acc[e] += (double)s[e]; s[e] = real(0); }
+      }
+    }
   }
-  // combine the groups in a fixed order
-  __syncthreads();
-  if (own && grp > 0)
-    for (int e = 0; e < 4; ++e) gsum[((grp - 1) * ntile + tt) * 4 + e] = acc[e];
-  __syncthreads();
-  if (own && grp == 0) {
-    for (int g = 1; g < ngroup; ++g)
-      for (int e = 0; e < 4; ++e) acc[e] += gsum[((g - 1) * ntile + tt) * 4 + e];
-    double *o = J.out + (size_t)blockIdx.x * r * r;
-    if (ti < r && tj < r) o[ti + r * tj] = acc[0];
-    if (ti + 1 < r && tj < r) o[ti + 1 + r * tj] = acc[1];
-    if (ti < r && tj + 1 < r) o[ti + r * (tj + 1)] = acc[2];
-    if (ti + 1 < r && tj + 1 < r) o[ti + 1 + r * (tj + 1)] = acc[3];
+  if (sizeof(real) != 4) {
+#pragma unroll
+    for (int e = 0; e < 16; ++e) acc[e] = (double)s[e];
   }
+  // groups -> CTA partial (fixed order), tile entries of the lower triangle
+  // of a symmetric Gram mirrored from the upper one
+  __syncthreads();
+  double *buf = reinterpret_cast<double *>(raw);
+  double *part_s = buf + kTB * 16;
+  if (grp < ngroup) {
+#pragma unroll
+    for (int e = 0; e < 16; ++e) buf[t * 16 + e] = acc[e];
+  }
+  __syncthreads();
+  for (int e = t; e < r * r; e += kTB) {
+    int i = e % r, j = e / r;
+    if (!cross && i > j) { const int x = i; i = j; j = x; }
+    const int tl = (i >> 2) + side * (j >> 2), comp = (i & 3) * 4 + (j & 3);
+    double v = 0.0;
+    for (int g = 0; g < ngroup; ++g) v += buf[(g * ntile + tl) * 16 + comp];
+    part_s[e] = v;
+  }
+  cluster.sync();
+  // this CTA's share of the cluster sum, CTA partials added in rank order
+  const int rank = (int)cluster.block_rank();
+  const int rr2 = r * r, share = (rr2 + kCl - 1) / kCl;
+  double *out = J.out + (size_t)(blockIdx.x / kCl) * rr2;
+  for (int e = rank * share + t; e < min(rr2, (rank + 1) * share); e += kTB) {
+    double v = 0.0;
+#pragma unroll
+    for (int q = 0; q < kCl; ++q) v += cluster.map_shared_rank(part_s, q)[e];
+    out[e] = v;
+  }
+  cluster.sync();  // peers' shared memory stays valid until every read is done
 }
 
 // ------------------------------------------------------------------
@@ -193,11 +262,14 @@ __global__ void __launch_bounds__(128) k_apply(const ApplyJob *__restrict__ jobs
   const ApplyJob J = jobs[blockIdx.y];
   if (J.run_if && *J.run_if == 0) return;
   __shared__ rout Ts[RB * RB];
+  __shared__ rout dg[RB];
   const int r = J.r;
   for (int e = threadIdx.x; e < RB * RB; e += blockDim.x) {
     const int i = e % RB, j = e / RB;
-    Ts[e] = (i < r && j < r) ? rout(J.T[i + r * j]) : rout(0);
+    Ts[e] = (i < r && j < r) ? rout(J.T[i + r * j]) : rout(i == j && J.tri ? 1 : 0);
   }
+  if (J.tri)
+    for (int j = threadIdx.x; j < RB; j += blockDim.x) dg[j] = j < r ? rout(1.0 / J.T[j + r * j]) : rout(1);
   __syncthreads();
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= J.m) return;
@@ -212,6 +284,20 @@ __global__ void __launch_bounds__(128) k_apply(const ApplyJob *__restrict__ jobs
   rout so = rout(1);
   if (J.s_out) so = rout(J.inv_sq_out ? 1.0 / sqrt(J.s_out[row]) : J.s_out[row]);
   rout *O = as<rout>(J.out);
+  if (J.tri) {
+    // x R = a by forward substitution (R upper triangular), x in place of a
+#pragma unroll
+    for (int j = 0; j < RB; ++j) {
+      rout v = a[j];
+#pragma unroll
+      for (int i = 0; i < j; ++i) v -= a[i] * Ts[j * RB + i];
+      a[j] = v * dg[j];
+    }
+#pragma unroll
+    for (int j = 0; j < RB; ++j)
+      if (j < r) O[(size_t)J.ldo * j + row] = so * a[j];
+    return;
+  }
   for (int j = 0; j < r; ++j) {
     rout v = rout(0);
 #pragma unroll
@@ -221,140 +307,239 @@ __global__ void __launch_bounds__(128) k_apply(const ApplyJob *__restrict__ jobs
 }
 
 // ------------------------------------------------------------------
-// step 6 / step 7 projections.  Per block partial (FP64) layout, r x r
-// column-major each: G, Nx, Ny, Mt, Ms, P, then vec[5r]: qh, bL, bR, bB, bT.
+// step 6 / step 7 projections, one thread-block cluster per slice of cells.
+// Per-cluster partial (FP64) layout, r x r column-major each: G, Nx, Ny,
+// Mt, Ms, P, then vec[5r]: qh, bL, bR, bB, bT.
 //   G_ij  = sum_c X_ci X_cj            Mt_ij = sum_c sig_t X_ci X_cj
 //   Ms_ij = sum_c sigma_s X_ci X_cj    P_ij  = sum_c X_ci X0_cj
 //   Nx_ij = sum_{ix>=1} X_ci X_{c-1,j} Ny_ij = sum_{iy>=1} X_ci X_{c-nx,j}
-// (all without the h^2 factor, applied in the reduction)
+//   qh_i  = sum_c q_c X_ci             bL_i  = sum_{ix=0} X_ci, ...
+// (all without the h^2 factor, applied in the reduction).  Threads come in
+// two kinds over 4 x 2 tiles of the r x r outputs: kind 0 accumulates G,
+// Mt, Ms (and qh), kind 1 Nx, Ny, P (and the four edge sums).  Staging,
+// prefetch, FP32-round/FP64-total accumulation and the cluster sum are as in
+// k_tsgram.
 // ------------------------------------------------------------------
+template <typename real> struct ProjCfg;
+template <> struct ProjCfg<float> { static constexpr int GP = 64; };
+template <> struct ProjCfg<double> { static constexpr int GP = 32; };
+
 template <typename real>
-__global__ void __launch_bounds__(kTB) k_project(const Inst *__restrict__ insts) {
+constexpr int proj_tile_bytes() {
+  return (4 * 32 * (ProjCfg<real>::GP + 4) + 9 * ProjCfg<real>::GP) * (int)sizeof(real);
+}
+inline int proj_smem_bytes(int r, int rs) {
+  const int tiles = rs == 4 ? proj_tile_bytes<float>() : proj_tile_bytes<double>();
+  const int red = (kTB * 16 + proj_count(r)) * 8;
+  return tiles > red ? tiles : red;
+}
+
+template <typename real>
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kTB)
+k_project(const Inst *__restrict__ insts) {
+  constexpr int GP = ProjCfg<real>::GP, LD = GP + 4;
+  constexpr int PF = GP * 32 / kTB;
   const Inst &I = insts[blockIdx.y];
-  if ((int)blockIdx.x >= I.partial_blocks) return;
-  constexpr int CR = 32;  // cells per staging round
-  __shared__ real xs[CR + 1][33];   // cells c0-1 .. c0+31
-  __shared__ real xb[CR][33];       // cells c0-nx .. c0-nx+31
-  __shared__ real x0s[CR][33];
-  __shared__ real sts[CR], sss[CR], qs[CR];
-  __shared__ int ixs[CR], iys[CR];
-  const int r = I.r, N = I.N, nx = I.nx;
-  const int t = threadIdx.x;
-  const int side = (r + 1) / 2, ntile = side * side;
-  const int ngroup = ntile <= 64 ? (int)blockDim.x / ntile : 1;  // groups split the cells
-  const int grp = t / ntile, tt = t % ntile;
-  const int ti = (tt % side) * 2, tj = (tt / side) * 2;
+  if ((int)blockIdx.x >= I.partial_blocks) return;  // whole clusters
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(32) unsigned char dyn[];
+  real *Xs = reinterpret_cast<real *>(dyn);
+  real *XLs = Xs + 32 * LD, *XBs = XLs + 32 * LD, *X0s = XBs + 32 * LD;
+  real *vs = X0s + 32 * LD;  // 9 x GP: sig_t, sigma_s, q, mL, mB, eL, eR, eB, eT
+  const int r = I.r, N = I.N, nx = I.nx, ny = I.ny, t = threadIdx.x;
+  const int s4 = (r + 3) >> 2, s2 = (r + 1) >> 1, ntile = s4 * s2;
+  const int gsz = 2 * ntile, ngroup = kTB / gsz;
+  const int grp = t / gsz, l = t - grp * gsz;
+  const int kind = l / ntile, tt = l - kind * ntile;
+  const int ti = 4 * (tt % s4), tj = 2 * (tt / s4);
   const bool own = grp < ngroup;
+  const bool vec_owner = own && tj == 0;
   const real *X = as_c<real>(I.X), *X0 = as_c<real>(I.X0);
   const real *sig_t = as_c<real>(I.sig_t), *ss4 = as_c<real>(I.ss4), *qv = as_c<real>(I.q);
-  double acc[6][4];
+  const int per = (N + I.partial_blocks - 1) / I.partial_blocks;
+  const int c0 = min(N, (int)blockIdx.x * per), c1 = min(N, c0 + per);
+  const int nround = (c1 - c0 + GP - 1) / GP;
+  real px[PF], pl[PF], pd[PF], p0[PF], pv[3];
+  int pix = -1, piy = -1;
+  auto prefetch = [&](int rd) {
+    const int base = c0 + rd * GP;
 #pragma unroll
-  for (int a = 0; a < 6; ++a)
+    for (int k = 0; k < PF; ++k) {
+      const int e = t + kTB * k, rr = e % GP, i = e / GP;
+      const int c = base + rr;
+      const bool ok = i < r && c < c1;
+      const size_t col = (size_t)N * i;
+      px[k] = ok ? X[col + c] : real(0);
+      pl[k] = ok && c >= 1 ? X[col + c - 1] : real(0);
+      pd[k] = ok && c >= nx ? X[col + c - nx] : real(0);
+      p0[k] = ok ? X0[col + c] : real(0);
+    }
+    if (t < GP) {
+      const int c = base + t;
+      const bool ok = c < c1;
+      pv[0] = ok ? sig_t[c] : real(0);
+      pv[1] = ok ? ss4[c] * real(4.0 * kPi) : real(0);
+      pv[2] = ok ? qv[c] : real(0);
+      pix = ok ? c % nx : -1;
+      piy = ok ? c / nx : -1;
+    }
+  };
+  real sm[24], sv[16];
+  double am[24], av[16];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) acc[a][e] = 0.0;
-  double vacc[5] = {0, 0, 0, 0, 0};  // thread t < r: qh, bL, bR, bB, bT for index t
-  const real four_pi = real(4.0 * kPi);
-  const int nchunks = (N + kChunk - 1) / kChunk;
-  for (int ch = blockIdx.x; ch < nchunks; ch += I.partial_blocks) {
-    real s[6][4];
+  for (int e = 0; e < 24; ++e) { sm[e] = real(0); am[e] = 0.0; }
 #pragma unroll
-    for (int a = 0; a < 6; ++a)
+  for (int e = 0; e < 16; ++e) { sv[e] = real(0); av[e] = 0.0; }
+  if (nround > 0) prefetch(0);
+  for (int rd = 0; rd < nround; ++rd) {
+    __syncthreads();
 #pragma unroll
-      for (int e = 0; e < 4; ++e) s[a][e] = real(0);
-    real vs[5] = {0, 0, 0, 0, 0};
-    for (int sub = 0; sub < kChunk; sub += CR) {
-      const int c0 = ch * kChunk + sub;
-      __syncthreads();
-      for (int e = t; e < (CR + 1) * r; e += blockDim.x) {
-        const int cc = e % (CR + 1), i = e / (CR + 1);
-        const int c = c0 - 1 + cc;
-        xs[cc][i] = (c >= 0 && c < N) ? X[(size_t)N * i + c] : real(0);
-      }
-      for (int e = t; e < CR * r; e += blockDim.x) {
-        const int cc = e & (CR - 1), i = e / CR;
-        const int c = c0 + cc, cb = c - nx;
-        xb[cc][i] = (cb >= 0 && c < N) ? X[(size_t)N * i + cb] : real(0);
-        x0s[cc][i] = (c < N) ? X0[(size_t)N * i + c] : real(0);
-      }
-      if (t < CR) {
-        const int c = c0 + t;
-        const bool in = c < N;
-        sts[t] = in ? sig_t[c] : real(0);
-        sss[t] = in ? ss4[c] * four_pi : real(0);
-        qs[t] = in ? qv[c] : real(0);
-        ixs[t] = in ? c % nx : -1;
-        iys[t] = in ? c / nx : -1;
-      }
-      __syncthreads();
-      if (own) {
-        for (int cc = grp; cc < CR; cc += ngroup) {
-          const int ix = ixs[cc], iy = iys[cc];
-          if (ix < 0) break;
-          const real a0 = xs[cc + 1][ti], a1 = xs[cc + 1][ti + 1];
-          const real b0 = xs[cc + 1][tj], b1 = xs[cc + 1][tj + 1];
-          const real st = sts[cc], sg = sss[cc];
-          const real p00 = a0 * b0, p10 = a1 * b0, p01 = a0 * b1, p11 = a1 * b1;
-          s[0][0] += p00; s[0][1] += p10; s[0][2] += p01; s[0][3] += p11;
-          s[3][0] += st * p00; s[3][1] += st * p10; s[3][2] += st * p01; s[3][3] += st * p11;
-          s[4][0] += sg * p00; s[4][1] += sg * p10; s[4][2] += sg * p01; s[4][3] += sg * p11;
-          if (ix >= 1) {
-            const real l0 = xs[cc][tj], l1 = xs[cc][tj + 1];
-            s[1][0] += a0 * l0; s[1][1] += a1 * l0; s[1][2] += a0 * l1; s[1][3] += a1 * l1;
-          }
-          if (iy >= 1) {
-            const real d0 = xb[cc][tj], d1 = xb[cc][tj + 1];
-            s[2][0] += a0 * d0; s[2][1] += a1 * d0; s[2][2] += a0 * d1; s[2][3] += a1 * d1;
-          }
-          const real o0 = x0s[cc][tj], o1 = x0s[cc][tj + 1];
-          s[5][0] += a0 * o0; s[5][1] += a1 * o0; s[5][2] += a0 * o1; s[5][3] += a1 * o1;
-        }
-      }
-      if (t < r) {
-        for (int cc = 0; cc < CR; ++cc) {
-          const int ix = ixs[cc], iy = iys[cc];
-          if (ix < 0) break;
-          const real x = xs[cc + 1][t];
-          vs[0] += qs[cc] * x;
-          if (ix == 0) vs[1] += x;
-          if (ix == nx - 1) vs[2] += x;
-          if (iy == 0) vs[3] += x;
-          if (iy == I.ny - 1) vs[4] += x;
-        }
+    for (int k = 0; k < PF; ++k) {
+      const int e = t + kTB * k, rr = e % GP, i = e / GP;
+      if (i < r) {
+        Xs[i * LD + rr] = px[k];
+        XLs[i * LD + rr] = pl[k];
+        XBs[i * LD + rr] = pd[k];
+        X0s[i * LD + rr] = p0[k];
       }
     }
-#pragma unroll
-    for (int a = 0; a < 6; ++a)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[a][e] += (double)s[a][e];
-#pragma unroll
-    for (int e = 0; e < 5; ++e) vacc[e] += (double)vs[e];
-  }
-  double *o = I.partials + (size_t)blockIdx.x * proj_count(r);
-  // combine the groups in a fixed order (stage through the partial slot)
-  __shared__ double gsum[6 * 4 * 64];
-  for (int g = 1; g < ngroup; ++g) {
+    if (t < GP) {
+      const bool ok = pix >= 0;
+      vs[0 * GP + t] = pv[0];
+      vs[1 * GP + t] = pv[1];
+      vs[2 * GP + t] = pv[2];
+      vs[3 * GP + t] = real(ok && pix >= 1);
+      vs[4 * GP + t] = real(ok && piy >= 1);
+      vs[5 * GP + t] = real(ok && pix == 0);
+      vs[6 * GP + t] = real(ok && pix == nx - 1);
+      vs[7 * GP + t] = real(ok && piy == 0);
+      vs[8 * GP + t] = real(ok && piy == ny - 1);
+    }
     __syncthreads();
-    if (own && grp == g && tt < 64)
-      for (int a = 0; a < 6; ++a)
-        for (int e = 0; e < 4; ++e) gsum[(a * 4 + e) * 64 + tt] = acc[a][e];
-    __syncthreads();
-    if (own && grp == 0 && tt < 64)
-      for (int a = 0; a < 6; ++a)
-        for (int e = 0; e < 4; ++e) acc[a][e] += gsum[(a * 4 + e) * 64 + tt];
-  }
-  if (own && grp == 0) {
-    for (int a = 0; a < 6; ++a) {
-      double *m = o + (size_t)a * r * r;
-      if (ti < r && tj < r) m[ti + r * tj] = acc[a][0];
-      if (ti + 1 < r && tj < r) m[ti + 1 + r * tj] = acc[a][1];
-      if (ti < r && tj + 1 < r) m[ti + r * (tj + 1)] = acc[a][2];
-      if (ti + 1 < r && tj + 1 < r) m[ti + 1 + r * (tj + 1)] = acc[a][3];
+    if (rd + 1 < nround) prefetch(rd + 1);
+    if (own) {
+      const int nq = (min(GP, c1 - c0 - rd * GP) + 3) >> 2;  // quads holding cells
+      for (int q = grp; q < nq; q += ngroup) {
+        Quad<real> a[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a[k] = *reinterpret_cast<const Quad<real> *>(Xs + (ti + k) * LD + 4 * q);
+        if (kind == 0) {
+          Quad<real> b[2];
+#pragma unroll
+          for (int k = 0; k < 2; ++k) b[k] = *reinterpret_cast<const Quad<real> *>(Xs + (tj + k) * LD + 4 * q);
+          const Quad<real> st = *reinterpret_cast<const Quad<real> *>(vs + 4 * q);
+          const Quad<real> ss = *reinterpret_cast<const Quad<real> *>(vs + GP + 4 * q);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+              for (int m = 0; m < 4; ++m) {
+                const real p = a[kk].v[m] * b[k].v[m];
+                sm[kk * 2 + k] += p;
+                sm[8 + kk * 2 + k] += st.v[m] * p;
+                sm[16 + kk * 2 + k] += ss.v[m] * p;
+              }
+          if (vec_owner) {
+            const Quad<real> qq = *reinterpret_cast<const Quad<real> *>(vs + 2 * GP + 4 * q);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+              for (int m = 0; m < 4; ++m) sv[kk] += qq.v[m] * a[kk].v[m];
+          }
+        } else {
+          Quad<real> bl[2], bd[2], b0[2];
+          const Quad<real> ml = *reinterpret_cast<const Quad<real> *>(vs + 3 * GP + 4 * q);
+          const Quad<real> mb = *reinterpret_cast<const Quad<real> *>(vs + 4 * GP + 4 * q);
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            bl[k] = *reinterpret_cast<const Quad<real> *>(XLs + (tj + k) * LD + 4 * q);
+            bd[k] = *reinterpret_cast<const Quad<real> *>(XBs + (tj + k) * LD + 4 * q);
+            b0[k] = *reinterpret_cast<const Quad<real> *>(X0s + (tj + k) * LD + 4 * q);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) { bl[k].v[m] *= ml.v[m]; bd[k].v[m] *= mb.v[m]; }
+          }
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+              for (int m = 0; m < 4; ++m) {
+                sm[kk * 2 + k] += a[kk].v[m] * bl[k].v[m];
+                sm[8 + kk * 2 + k] += a[kk].v[m] * bd[k].v[m];
+                sm[16 + kk * 2 + k] += a[kk].v[m] * b0[k].v[m];
+              }
+          if (vec_owner) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+              const Quad<real> ev = *reinterpret_cast<const Quad<real> *>(vs + (5 + v) * GP + 4 * q);
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+                for (int m = 0; m < 4; ++m) sv[v * 4 + kk] += ev.v[m] * a[kk].v[m];
+            }
+          }
+        }
+      }
+      if (sizeof(real) == 4) {
+#pragma unroll
+        for (int e = 0; e < 24; ++e) { am[e] += (double)sm[e]; sm[e] = real(0); }
+#pragma unroll
+        for (int e = 0; e < 16; ++e) { av[e] += (double)sv[e]; sv[e] = real(0); }
+      }
     }
   }
-  if (t < r) {
-    double *v = o + 6 * r * r;
-    for (int e = 0; e < 5; ++e) v[e * r + t] = vacc[e];
+  if (sizeof(real) != 4) {
+#pragma unroll
+    for (int e = 0; e < 24; ++e) am[e] = (double)sm[e];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) av[e] = (double)sv[e];
   }
+  // groups -> CTA partial in a fixed order, one output slot at a time
+  double *buf = reinterpret_cast<double *>(dyn);
+  double *part_s = buf + kTB * 16;
+  const int rr2 = r * r;
+  for (int slot = 0; slot < 3; ++slot) {
+    __syncthreads();
+    if (own) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) buf[t * 8 + e] = am[slot * 8 + e];
+    }
+    __syncthreads();
+    for (int e = t; e < 2 * rr2; e += kTB) {
+      const int kd = e / rr2, ij = e - kd * rr2, i = ij % r, j = ij / r;
+      const int lt = kd * ntile + (i >> 2) + s4 * (j >> 1), comp = (i & 3) * 2 + (j & 1);
+      double v = 0.0;
+      for (int g = 0; g < ngroup; ++g) v += buf[(g * gsz + lt) * 8 + comp];
+      // kind 0 holds G, Mt, Ms (blocks 0, 3, 4); kind 1 Nx, Ny, P (1, 2, 5)
+      const int mat = kd == 0 ? (slot == 0 ? 0 : slot + 2) : (slot == 2 ? 5 : slot + 1);
+      part_s[mat * rr2 + ij] = v;
+    }
+  }
+  __syncthreads();
+  if (own) {
+#pragma unroll
+    for (int e = 0; e < 16; ++e) buf[t * 16 + e] = av[e];
+  }
+  __syncthreads();
+  for (int e = t; e < 5 * r; e += kTB) {
+    const int v = e / r, i = e - v * r;
+    const int lt = (v == 0 ? 0 : ntile) + (i >> 2), comp = (v == 0 ? 0 : (v - 1) * 4) + (i & 3);
+    double x = 0.0;
+    for (int g = 0; g < ngroup; ++g) x += buf[(g * gsz + lt) * 16 + comp];
+    part_s[6 * rr2 + e] = x;
+  }
+  cluster.sync();
+  const int rank = (int)cluster.block_rank();
+  const int cnt = proj_count(r), share = (cnt + kCl - 1) / kCl;
+  double *out = I.partials + (size_t)(blockIdx.x / kCl) * cnt;
+  for (int e = rank * share + t; e < min(cnt, (rank + 1) * share); e += kTB) {
+    double v = 0.0;
+#pragma unroll
+    for (int q = 0; q < kCl; ++q) v += cluster.map_shared_rank(part_s, q)[e];
+    out[e] = v;
+  }
+  cluster.sync();
 }
 
 // Sum of per-block partials: out[e] = scale * sum_b part[b*stride + e].
@@ -446,9 +631,18 @@ cudaError_t launch_apply(const ApplyJob *d_jobs, int n, int maxm, int r, cudaStr
 }
 
 template <typename real>
-cudaError_t launch_project(const Inst *d, int n, int maxblocks, cudaStream_t st) {
-  k_project<real><<<dim3(maxblocks, n), kTB, 0, st>>>(d);
+cudaError_t launch_project(const Inst *d, int n, int maxblocks, int rmax, cudaStream_t st) {
+  k_project<real><<<dim3(maxblocks, n), kTB, proj_smem_bytes(rmax, sizeof(real)), st>>>(d);
   return cudaGetLastError();
+}
+
+// Kernel attributes, set before any launch is captured into a graph.
+cudaError_t prepare_dense(int rmax) {
+  cudaError_t e = cudaFuncSetAttribute(k_project<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       proj_smem_bytes(rmax, 4));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_project<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              proj_smem_bytes(rmax, 8));
 }
 
 cudaError_t launch_reduce(const ReduceJob *d_jobs, int n, int maxcount, cudaStream_t st) {
@@ -473,8 +667,8 @@ template cudaError_t launch_fill<float>(const FillJob *, int, int, cudaStream_t)
 template cudaError_t launch_fill<double>(const FillJob *, int, int, cudaStream_t);
 template cudaError_t launch_apply<float, float>(const ApplyJob *, int, int, int, cudaStream_t);
 template cudaError_t launch_apply<double, double>(const ApplyJob *, int, int, int, cudaStream_t);
-template cudaError_t launch_project<float>(const Inst *, int, int, cudaStream_t);
-template cudaError_t launch_project<double>(const Inst *, int, int, cudaStream_t);
+template cudaError_t launch_project<float>(const Inst *, int, int, int, cudaStream_t);
+template cudaError_t launch_project<double>(const Inst *, int, int, int, cudaStream_t);
 template cudaError_t launch_tupdate<float>(const Inst *, int, int, int, cudaStream_t);
 template cudaError_t launch_tupdate<double>(const Inst *, int, int, int, cudaStream_t);
 

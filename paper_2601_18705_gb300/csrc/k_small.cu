@@ -1,8 +1,9 @@
 // k_small.cu -- FP64 small dense linear algebra of the SN-like DLR step
 // (Algorithm 1 of Haut et al.):
 //   k_select       step 2: angle choice (column-pivoted Householder QR of W0^T,
-//                  or the greedy DEIM of Section 4.2), What, beta, gamma =
-//                  What^{-T} beta, C0 = S0 What^T
+//                  or the greedy DEIM of Section 4.2) by one thread-block
+//                  cluster per instance, What, beta, gamma = What^{-T} beta,
+//                  C0 = S0 What^T
 //   k_chol         Cholesky of a reduced Gram (one CholeskyQR pass of steps 5
 //                  and 8); detects dependent columns, shifts when needed
 //   k_proj_post    step 7 Galerkin operators from the reduced projections
@@ -94,182 +95,161 @@ __device__ int block_argmax_tie(const double *val, int n) {
 }
 
 // ------------------------------------------------------------------
-// step 2: angle choice, cooperative over several CTAs per instance.  CTA g
-// of an instance owns angles [g*slice, (g+1)*slice) as columns of A = W0^T
-// in shared memory.  Per pivot step: (1) every CTA publishes the largest
-// remaining column norm it owns; grid barrier; (2) with the global maximum m
-// known everywhere, every CTA publishes its lowest angle with norm >=
-// m (1 - 1e-12) and that column; grid barrier; (3) every CTA takes the
-// lowest published angle and applies the same Householder reflection (the
-// column-pivoted QR of W0^T, reading R8).  DEIM (Section 4.2) uses the same
-// two-barrier argmax on the interpolation residual.  CTA 0 then forms What,
-// beta, gamma = What^{-T} beta and C0 = S0 What^T.
-// Scratch (in the instance's partials): lmax[64], lmin[64], cand[64][32],
-// bpart[64][32].
+// step 2: angle choice, one thread-block cluster per instance.  CTA g of the
+// cluster owns angles [g*slice, (g+1)*slice) as columns of A = W0^T in its
+// shared memory.  Per pivot step: (1) every CTA computes the remaining norm
+// (or DEIM interpolation residual) of its unused columns and its largest
+// one; cluster barrier; (2) every CTA reads the CTAs' maxima and then all
+// norms through distributed shared memory and takes the same pivot: the
+// lowest angle within a relative 1e-12 of the maximum (reading R8); (3) in
+// pivoted-QR mode every CTA reads the pivot column from its owner and
+// applies the same Householder reflection to its unused columns.  Norms and
+// maxima alternate between two buffers by step parity and chosen columns are
+// never written again, so one cluster barrier per step suffices.  CTA 0 then
+// forms What, beta, gamma = What^{-T} beta and C0 = S0 What^T.
 // ------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_select(const Inst *__restrict__ insts, SelCtl ctl) {
-  int inst = 0;
-  while (inst + 1 < ctl.n_inst && (int)blockIdx.x >= ctl.cta_begin[inst + 1]) ++inst;
-  const Inst &I = insts[inst];
-  const int G = ctl.cta_begin[inst + 1] - ctl.cta_begin[inst];
-  const int g = blockIdx.x - ctl.cta_begin[inst];
-  const bool active = *I.status == kOk;
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(256)
+k_select(const Inst *__restrict__ insts, int slice_max) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int g = (int)cluster.block_rank();
+  const Inst &I = insts[blockIdx.x / kCl];
+  const bool active = *I.status == kOk;  // read before the first barrier
   const int r = I.r, K = I.K;
-  const int slice = (K + G - 1) / G, k0 = min(K, g * slice), k1 = min(K, k0 + slice), ns = k1 - k0;
+  const int slice = (K + kCl - 1) / kCl, k0 = min(K, g * slice), k1 = min(K, k0 + slice);
+  const int ns = k1 - k0;
   extern __shared__ double sh[];
-  double *A = sh;                       // r x slice_max
-  double *nrm = A + 32 * ctl.slice_max; // slice_max
-  __shared__ double v[32], col[32], M[32 * 32], rhs[32];
+  double *A = sh;                          // r x slice_max, column c at A + r*c
+  double *nrm = A + 32 * slice_max;        // [2][slice_max]
+  unsigned char *used = reinterpret_cast<unsigned char *>(nrm + 2 * slice_max);
+  __shared__ double v[32], col[32], M[32 * 32], rhs[32], bpart[32], lmax[2];
   __shared__ int sel[32], ipiv[32];
   __shared__ double red_d[32];
   __shared__ int red_i[32];
-  __shared__ int piv_s;
-  double *lmax = I.partials;
-  int *lmin = reinterpret_cast<int *>(I.partials + 64);
-  double *cand = I.partials + 128;          // 64 x 32
-  double *bpart = I.partials + 128 + 2048;  // 64 x 32
+  __shared__ double vv_s, gmax_s;
   const double *W = I.W0;
-  volatile int *abort_flag = ctl.abort_flag;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (active) {
-    for (int e = threadIdx.x; e < r * ns; e += blockDim.x) {
-      const int c = e / r, i = e % r;
-      A[i + r * c] = W[(k0 + c) + (size_t)K * i];
-    }
-    // this CTA's share of beta_j = sum_k w_k W0_kj
-    for (int j = wid; j < r; j += nw) {
-      double s = 0.0;
+  for (int e = threadIdx.x; e < r * ns; e += blockDim.x) {
+    const int c = e / r, i = e % r;
+    A[i + r * c] = active ? W[(k0 + c) + (size_t)K * i] : 0.0;
+  }
+  for (int c = threadIdx.x; c < ns; c += blockDim.x) used[c] = 0;
+  // this CTA's share of beta_j = sum_k w_k W0_kj
+  for (int j = wid; j < r; j += nw) {
+    double s = 0.0;
+    if (active)
       for (int k = k0 + lane; k < k1; k += 32) s += I.w[k] * W[k + (size_t)K * j];
-      s = warp_sum(s);
-      if (lane == 0) bpart[g * 32 + j] = s;
-    }
+    s = warp_sum(s);
+    if (lane == 0) bpart[j] = s;
   }
   __syncthreads();
-  for (int s = 0; s < ctl.rmax; ++s) {
-    const bool work = active && s < r;
-    // (1) norms (or interpolation residuals) of the owned columns
-    if (work) {
-      if (I.selection == 0) {
+  for (int s = 0; s < r; ++s) {
+    const int par = s & 1;
+    double *nr = nrm + par * slice_max;
+    // (1) norms (or interpolation residuals) of the unused owned columns
+    if (I.selection == 0) {
+      for (int c = threadIdx.x; c < ns; c += blockDim.x) {
+        double t = 0.0;
+        for (int i = s; i < r; ++i) t += A[i + r * c] * A[i + r * c];
+        nr[c] = used[c] ? -1.0 : sqrt(t);
+      }
+    } else {
+      if (threadIdx.x == 0 && s > 0 && active) {  // interpolation coefficients on the s chosen points
+        for (int i = 0; i < s; ++i) {
+          rhs[i] = W[sel[i] + (size_t)K * s];
+          for (int l = 0; l < s; ++l) M[i + s * l] = W[sel[i] + (size_t)K * l];
+        }
+        for (int p = 0; p < s; ++p) {
+          int pr = p;
+          for (int i = p + 1; i < s; ++i) if (fabs(M[i + s * p]) > fabs(M[pr + s * p])) pr = i;
+          if (pr != p) {
+            for (int l = 0; l < s; ++l) { double t = M[p + s * l]; M[p + s * l] = M[pr + s * l]; M[pr + s * l] = t; }
+            double t = rhs[p]; rhs[p] = rhs[pr]; rhs[pr] = t;
+          }
+          for (int i = p + 1; i < s; ++i) {
+            const double f = M[i + s * p] / M[p + s * p];
+            for (int l = p; l < s; ++l) M[i + s * l] -= f * M[p + s * l];
+            rhs[i] -= f * rhs[p];
+          }
+        }
+        for (int i = s - 1; i >= 0; --i) {
+          for (int l = i + 1; l < s; ++l) rhs[i] -= M[i + s * l] * rhs[l];
+          rhs[i] /= M[i + s * i];
+        }
+      }
+      __syncthreads();
+      for (int c = threadIdx.x; c < ns; c += blockDim.x) {
+        double res = A[s + r * c];
+        for (int l = 0; l < s; ++l) res -= rhs[l] * A[l + r * c];
+        nr[c] = used[c] ? -1.0 : fabs(res);
+      }
+    }
+    __syncthreads();
+    double m = -1.0;
+    for (int c = threadIdx.x; c < ns; c += blockDim.x) m = fmax(m, nr[c]);
+    m = block_max(m, red_d);
+    if (threadIdx.x == 0) lmax[par] = m;
+    cluster.sync();
+    // (2) the same pivot in every CTA
+    if (wid == 0) {
+      double x = lane < kCl ? cluster.map_shared_rank(lmax, lane)[par] : -1.0;
+      x = warp_max(x);
+      if (lane == 0) gmax_s = x;
+    }
+    __syncthreads();
+    const double thr = gmax_s * (1.0 - kTieRel);
+    int best = 0x7fffffff;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+      const int o = k / slice;
+      const double x = cluster.map_shared_rank(nrm, o)[par * slice_max + (k - o * slice)];
+      if (x >= 0.0 && x >= thr) best = min(best, k);
+    }
+    for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(kFullMask, best, o));
+    if (lane == 0) red_i[wid] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int p = 0x7fffffff;
+      for (int q = 0; q < nw; ++q) p = min(p, red_i[q]);
+      if (p < 0 || p >= K) {  // no finite candidate (NaN input)
+        if (active && g == 0) set_status(I.status, kESingular);
+        p = 0;
+      }
+      sel[s] = p;
+    }
+    __syncthreads();
+    const int p = sel[s], owner = p / slice, pl = p - owner * slice;
+    if (owner == g && threadIdx.x == 0) used[pl] = 1;  // never written again
+    if (I.selection == 0) {
+      if (threadIdx.x < r) col[threadIdx.x] = cluster.map_shared_rank(A, owner)[threadIdx.x + r * pl];
+      __syncthreads();
+      if (wid == 0) {  // Householder vector of col[s..r)
+        const double ci = (lane >= s && lane < r) ? col[lane] : 0.0;
+        const double nrm_p = sqrt(warp_sum(ci * ci));
+        const double a = col[s] >= 0 ? -nrm_p : nrm_p;
+        const double vi = lane == s ? ci - a : ci;
+        const double vv = warp_sum(vi * vi);
+        if (lane < 32) v[lane] = vi;
+        if (lane == 0) vv_s = vv;
+      }
+      __syncthreads();
+      const double vv = vv_s;
+      if (vv > 0.0)
         for (int c = threadIdx.x; c < ns; c += blockDim.x) {
-          bool u = false;
-          for (int q = 0; q < s; ++q) u |= (sel[q] == k0 + c);
-          double t = 0.0;
-          for (int i = s; i < r; ++i) t += A[i + r * c] * A[i + r * c];
-          nrm[c] = u ? -1.0 : sqrt(t);
+          if (used[c]) continue;
+          double d = 0.0;
+          for (int i = s; i < r; ++i) d += v[i] * A[i + r * c];
+          const double f = 2.0 * d / vv;
+          for (int i = s; i < r; ++i) A[i + r * c] -= f * v[i];
         }
-      } else {
-        if (threadIdx.x == 0 && s > 0) {  // interpolation coefficients on the s chosen points
-          for (int i = 0; i < s; ++i) {
-            rhs[i] = W[sel[i] + (size_t)K * s];
-            for (int l = 0; l < s; ++l) M[i + s * l] = W[sel[i] + (size_t)K * l];
-          }
-          for (int p = 0; p < s; ++p) {
-            int pr = p;
-            for (int i = p + 1; i < s; ++i) if (fabs(M[i + s * p]) > fabs(M[pr + s * p])) pr = i;
-            if (pr != p) {
-              for (int l = 0; l < s; ++l) { double t = M[p + s * l]; M[p + s * l] = M[pr + s * l]; M[pr + s * l] = t; }
-              double t = rhs[p]; rhs[p] = rhs[pr]; rhs[pr] = t;
-            }
-            for (int i = p + 1; i < s; ++i) {
-              const double f = M[i + s * p] / M[p + s * p];
-              for (int l = p; l < s; ++l) M[i + s * l] -= f * M[p + s * l];
-              rhs[i] -= f * rhs[p];
-            }
-          }
-          for (int i = s - 1; i >= 0; --i) {
-            for (int l = i + 1; l < s; ++l) rhs[i] -= M[i + s * l] * rhs[l];
-            rhs[i] /= M[i + s * i];
-          }
-        }
-        __syncthreads();
-        for (int c = threadIdx.x; c < ns; c += blockDim.x) {
-          bool u = false;
-          for (int q = 0; q < s; ++q) u |= (sel[q] == k0 + c);
-          double res = A[s + r * c];
-          for (int l = 0; l < s; ++l) res -= rhs[l] * A[l + r * c];
-          nrm[c] = u ? -1.0 : fabs(res);
-        }
-      }
-      __syncthreads();
-      double m = -1.0;
-      for (int c = threadIdx.x; c < ns; c += blockDim.x) m = fmax(m, nrm[c]);
-      m = block_max(m, red_d);
-      if (threadIdx.x == 0) lmax[g] = m;
     }
-    if (!grid_barrier(ctl.bar, abort_flag)) {
-      if (threadIdx.x == 0 && g == 0) set_status(I.status, kETimeout);
-      return;
-    }
-    // (2) lowest owned angle within the tie window of the global maximum
-    if (work) {
-      double m = -1.0;
-      for (int q = 0; q < G; ++q) m = fmax(m, ((volatile double *)lmax)[q]);
-      const double thr = m * (1.0 - kTieRel);
-      int best = 0x7fffffff;
-      for (int c = threadIdx.x; c < ns; c += blockDim.x)
-        if (nrm[c] >= 0.0 && nrm[c] >= thr) best = min(best, c);
-      for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(kFullMask, best, o));
-      __syncthreads();
-      if (lane == 0) red_i[wid] = best;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        int bb = 0x7fffffff;
-        for (int q = 0; q < nw; ++q) bb = min(bb, red_i[q]);
-        lmin[g] = bb == 0x7fffffff ? 0x7fffffff : k0 + bb;
-        piv_s = bb;
-      }
-      __syncthreads();
-      if (piv_s != 0x7fffffff && threadIdx.x < r) cand[g * 32 + threadIdx.x] = A[threadIdx.x + r * piv_s];
-    }
-    if (!grid_barrier(ctl.bar, abort_flag)) {
-      if (threadIdx.x == 0 && g == 0) set_status(I.status, kETimeout);
-      return;
-    }
-    // (3) the pivot and (pivoted QR) the reflection of the owned columns
-    if (work) {
-      if (threadIdx.x == 0) {
-        int p = 0x7fffffff, owner = 0;
-        for (int q = 0; q < G; ++q) {
-          const int x = ((volatile int *)lmin)[q];
-          if (x < p) { p = x; owner = q; }
-        }
-        if (p < 0 || p >= K) {  // no finite candidate (NaN input)
-          set_status(I.status, kESingular);
-          p = 0;
-        }
-        sel[s] = p;
-        piv_s = owner;
-      }
-      __syncthreads();
-      if (I.selection == 0) {
-        if (threadIdx.x < r) col[threadIdx.x] = ((volatile double *)cand)[piv_s * 32 + threadIdx.x];
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          double t = 0.0;
-          for (int i = s; i < r; ++i) t += col[i] * col[i];
-          const double nrm_p = sqrt(t);
-          const double a = col[s] >= 0 ? -nrm_p : nrm_p;
-          double vv = 0.0;
-          for (int i = s; i < r; ++i) {
-            v[i] = col[i];
-            if (i == s) v[i] -= a;
-            vv += v[i] * v[i];
-          }
-          red_d[0] = vv;
-        }
-        __syncthreads();
-        const double vv = red_d[0];
-        if (vv > 0.0)
-          for (int c = threadIdx.x; c < ns; c += blockDim.x) {
-            double d = 0.0;
-            for (int i = s; i < r; ++i) d += v[i] * A[i + r * c];
-            const double f = 2.0 * d / vv;
-            for (int i = s; i < r; ++i) A[i + r * c] -= f * v[i];
-          }
-      }
-      __syncthreads();
-    }
+    __syncthreads();
   }
+  cluster.sync();  // every CTA's beta share is final
+  if (g == 0 && active && threadIdx.x < r) {
+    double t = 0.0;
+    for (int q = 0; q < kCl; ++q) t += cluster.map_shared_rank(bpart, q)[threadIdx.x];
+    rhs[threadIdx.x] = t;
+  }
+  cluster.sync();  // peers' shared memory stays valid until CTA 0 has read it
   if (!active || g != 0) return;
   // What_ij = W0_j(Om^(i)), beta, gamma = What^{-T} beta, C0 = S0 What^T
   double *What = I.small + I.lay.What;
@@ -280,9 +260,7 @@ __global__ void __launch_bounds__(256) k_select(const Inst *__restrict__ insts, 
   }
   for (int i = threadIdx.x; i < r; i += blockDim.x) {
     I.idx[i] = sel[i];
-    double t = 0.0;
-    for (int q = 0; q < G; ++q) t += ((volatile double *)bpart)[q * 32 + i];
-    beta[i] = t;
+    beta[i] = rhs[i];
   }
   __syncthreads();
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
@@ -296,7 +274,6 @@ __global__ void __launch_bounds__(256) k_select(const Inst *__restrict__ insts, 
     return;
   }
   if (threadIdx.x == 0) {
-    for (int i = 0; i < r; ++i) rhs[i] = beta[i];
     lu_solve_serial(M, r, ipiv, rhs);
     for (int i = 0; i < r; ++i) I.small[I.lay.gamma + i] = rhs[i];
   }
@@ -310,8 +287,10 @@ __global__ void __launch_bounds__(256) k_select(const Inst *__restrict__ insts, 
 }
 
 // ------------------------------------------------------------------
-// One CholeskyQR pass on G = scale * sum_b part[b] (r x r): R upper with
-// R^T R = G (+ shift), Ri = R^{-1}.  Modes:
+// One CholeskyQR pass on G = scale * sum_c part[c] (r x r, c over the
+// cluster partials): R upper triangular with R^T R = G (+ shift).  The
+// elimination keeps the unscaled pivot rows (C_ij -= C_pi C_pj / C_pp, one
+// barrier per pivot) and scales row p by 1/sqrt(C_pp) at the end.  Modes:
 //   1 first pass: unshifted Cholesky that also detects dependent columns
 //     (residual^2 < tau_dep |column|^2).  Dependent columns are marked in
 //     flag[2 + j] and counted in flag[1] (they are then replaced by
@@ -319,7 +298,7 @@ __global__ void __launch_bounds__(256) k_select(const Inst *__restrict__ insts, 
 //     dependent columns a failed pivot falls back to a shifted Cholesky
 //     (shifted CholeskyQR) and sets flag[0] (a third pass is needed).
 //   2 always: Cholesky, shifted if needed (sets flag[0] when shifted)
-//   3 only if flag[0]; otherwise R = Ri = I
+//   3 only if flag[0]; otherwise R = I
 //   4 only if flag[1] (after the fill); as mode 2
 // ------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_chol(const CholJob *__restrict__ jobs,
@@ -328,102 +307,88 @@ __global__ void __launch_bounds__(256) k_chol(const CholJob *__restrict__ jobs,
   const Inst &I = insts[blockIdx.x];
   if (*I.status != kOk) return;
   __shared__ double G[32 * 32], C[32 * 32];
-  __shared__ int fail_s, ndep_s;
+  __shared__ double dinv[32];
   __shared__ int dep[32];
-  const int r = J.r;
+  __shared__ int ndep_s;
+  const int r = J.r, t = threadIdx.x;
   int *flag = J.flag;
   const bool run = J.mode == 1 || J.mode == 2 || (J.mode == 3 && flag[0] != 0) ||
                    (J.mode == 4 && flag[1] != 0);
   if (!run) {
     if (J.mode == 3)
-      for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-        const double d = (e % r == e / r) ? 1.0 : 0.0;
-        J.R[e] = d;
-        J.Ri[e] = d;
-      }
+      for (int e = t; e < r * r; e += blockDim.x) J.R[e] = (e % r == e / r) ? 1.0 : 0.0;
     return;
   }
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x)
-    G[e] = J.scale * sum_partials(J.part, J.nblocks, (size_t)r * r, e);
+  for (int e = t; e < r * r; e += blockDim.x)
+    C[e] = J.scale * sum_partials(J.part, J.nblocks, (size_t)r * r, e);
   __syncthreads();
-  // symmetrise (the partial sums fill both triangles)
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+  // symmetrise (both triangles hold the same sums up to rounding order)
+  for (int e = t; e < r * r; e += blockDim.x) {
     const int i = e % r, j = e / r;
-    C[e] = (i == j) ? G[e] : 0.5 * (G[i + r * j] + G[j + r * i]);
+    G[e] = (i == j) ? C[e] : 0.5 * (C[i + r * j] + C[j + r * i]);
   }
-  __syncthreads();
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) G[e] = C[e];
-  if (J.mode == 1 && threadIdx.x == 0) {
+  if (J.mode == 1 && t == 0) {
     flag[0] = 0;
     flag[1] = 0;
   }
-  if (J.mode == 1 && threadIdx.x < 32) flag[2 + threadIdx.x] = 0;
+  if (J.mode == 1 && t < 32) flag[2 + t] = 0;
   __syncthreads();
   double tr = 0.0;
   for (int i = 0; i < r; ++i) tr += G[i + r * i];
   double shift = 0.0;
-  bool shifted = false;
+  bool shifted = false, failed = false;
   for (int attempt = 0; attempt < 8; ++attempt) {
-    for (int e = threadIdx.x; e < r * r; e += blockDim.x)
-      C[e] = G[e] + ((e % r == e / r) ? shift : 0.0);
-    if (threadIdx.x < 32) dep[threadIdx.x] = 0;
-    if (threadIdx.x == 0) { fail_s = 0; ndep_s = 0; }
+    for (int e = t; e < r * r; e += blockDim.x) C[e] = G[e] + ((e % r == e / r) ? shift : 0.0);
+    if (t < 32) dep[t] = 0;
+    if (t == 0) ndep_s = 0;
+    __syncthreads();
+    if (t == 0) dinv[0] = 1.0 / C[0];
     __syncthreads();
     const bool detect = J.mode == 1 && shift == 0.0;
+    failed = false;
     for (int p = 0; p < r; ++p) {
-      if (threadIdx.x == 0) {
-        const double d = C[p + r * p];
-        if (detect && d <= J.tau_dep * G[p + r * p]) {
-          dep[p] = 1;
-          ++ndep_s;
-          C[p + r * p] = 1.0;
-        } else if (!(d > J.u * tr)) {
-          fail_s = 1;
-        } else {
-          C[p + r * p] = sqrt(d);
-        }
-      }
-      __syncthreads();
-      if (fail_s) break;
-      if (dep[p]) {  // a dependent column: row p of R is e_p
-        for (int j = p + 1 + threadIdx.x; j < r; j += blockDim.x) C[p + r * j] = 0.0;
+      // the same decision in every thread (C_pp is final after the last barrier)
+      const double d = C[p + r * p];
+      const bool is_dep = detect && d <= J.tau_dep * G[p + r * p];
+      if (!is_dep && !(d > J.u * tr)) { failed = true; break; }
+      if (is_dep) {  // a dependent column: row p of R becomes e_p
+        if (t == 0) { dep[p] = 1; ++ndep_s; }
+        if (p + 1 < r && t == 0) dinv[p + 1] = 1.0 / C[(p + 1) + r * (p + 1)];
         __syncthreads();
         continue;
       }
-      const double dp = C[p + r * p];
-      for (int j = p + 1 + threadIdx.x; j < r; j += blockDim.x) C[p + r * j] /= dp;
-      __syncthreads();
-      const int m = r - p - 1;
-      for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-        const int i = p + 1 + e % m, j = p + 1 + e / m;
-        if (i <= j) C[i + r * j] -= C[p + r * i] * C[p + r * j];
+      const double inv = dinv[p];
+      for (int e = t; e < r * r; e += blockDim.x) {
+        const int i = e % r, j = e / r;
+        if (i > p && i <= j) {
+          const double x = C[i + r * j] - C[p + r * i] * inv * C[p + r * j];
+          C[i + r * j] = x;
+          if (i == p + 1 && j == p + 1) dinv[p + 1] = 1.0 / x;
+        }
       }
       __syncthreads();
     }
     if (detect && ndep_s > 0) {
       // mark the dependent columns; the pass is redone after the fill
-      if (threadIdx.x == 0) flag[1] = ndep_s;
-      if (threadIdx.x < r) flag[2 + threadIdx.x] = dep[threadIdx.x];
+      if (t == 0) flag[1] = ndep_s;
+      if (t < r) flag[2 + t] = dep[t];
       return;
     }
-    if (!fail_s) break;
+    if (!failed) break;
     shift = shift == 0.0 ? J.u * tr : shift * 100.0;
     shifted = true;
     __syncthreads();
   }
-  if (shifted && threadIdx.x == 0) flag[0] = 1;
-  // R = upper triangle of C
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+  if (shifted && t == 0) flag[0] = 1;
+  // R_pj = C_pj / sqrt(C_pp) (rows of dependent columns: e_p)
+  if (t < r) dinv[t] = dep[t] ? 0.0 : sqrt(dinv[t]);
+  __syncthreads();
+  for (int e = t; e < r * r; e += blockDim.x) {
     const int i = e % r, j = e / r;
-    J.R[e] = i <= j ? C[e] : 0.0;
-  }
-  // Ri: column j solves R x = e_j (back substitution)
-  for (int j = threadIdx.x; j < r; j += blockDim.x) {
-    for (int i = r - 1; i >= 0; --i) {
-      double s = (i == j) ? 1.0 : 0.0;
-      for (int k = i + 1; k <= j; ++k) s -= C[i + r * k] * J.Ri[k + r * j];
-      J.Ri[i + r * j] = i <= j ? s / C[i + r * i] : 0.0;
-    }
+    double x = 0.0;
+    if (dep[i]) x = (i == j) ? 1.0 : 0.0;
+    else if (i <= j) x = C[e] * dinv[i];
+    J.R[e] = x;
   }
 }
 
@@ -766,7 +731,7 @@ __global__ void __launch_bounds__(256) k_svd(const Inst *__restrict__ insts, int
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     double t = 0.0;
     if (mode == 2) t = I.S0[e];
-    else t = sum_partials(I.partials, I.angle_blocks, (size_t)r * r, e);
+    else t = sum_partials(I.partials, I.angle_blocks / kCl, (size_t)r * r, e);  // one partial per cluster
     Uw[e] = t;  // S_ij = sum_k sqrt(w_k) L_ik Q_kj
     Vw[e] = (e % r == e / r) ? 1.0 : 0.0;
   }
@@ -905,7 +870,9 @@ __global__ void __launch_bounds__(256) k_sign(const Inst *__restrict__ insts) {
 // host launchers (kernel attributes are set by prepare_small before any
 // launch is captured into a graph)
 // ------------------------------------------------------------------
-static size_t select_smem(int slice_max) { return (size_t)(33 * slice_max) * sizeof(double); }
+static size_t select_smem(int slice_max) {
+  return (size_t)(34 * slice_max) * sizeof(double) + (size_t)slice_max;
+}
 static int rank_bucket(int r) { return r <= 8 ? 8 : r <= 16 ? 16 : 32; }
 size_t lstep_angle_smem(int r) {
   const int RB = rank_bucket(r);
@@ -928,27 +895,9 @@ cudaError_t prepare_small(int slice_max, int maxK, int rmax) {
   return cudaFuncSetAttribute(k_sign, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)(maxK * sizeof(double)));
 }
-cudaError_t launch_select(const Inst *d, const SelCtl &ctl, int grid, cudaStream_t st) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(256);
-  cfg.dynamicSmemBytes = select_smem(ctl.slice_max);
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_select, d, ctl);
-}
-int select_max_grid(int slice_max) {
-  int per_sm = 0, dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_select, 256, select_smem(slice_max)) !=
-      cudaSuccess)
-    return 0;
-  return per_sm * sms;
+cudaError_t launch_select(const Inst *d, int n, int slice_max, cudaStream_t st) {
+  k_select<<<n * kCl, 256, select_smem(slice_max), st>>>(d, slice_max);
+  return cudaGetLastError();
 }
 cudaError_t launch_chol(const CholJob *dj, const Inst *d, int n, cudaStream_t st) {
   k_chol<<<n, 256, 0, st>>>(dj, d);
