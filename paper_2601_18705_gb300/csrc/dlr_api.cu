@@ -32,12 +32,13 @@ template <typename real>
 cudaError_t launch_sweep_dirs(int, int, double, double, int, const double *, const double *,
                               const real *, const real *, real *, int *, cudaStream_t);
 template <typename real> cudaError_t launch_coeff_recon(const Inst *, int, int, int, cudaStream_t);
-template <typename real> cudaError_t launch_tsgram(const GramJob *, int, int, cudaStream_t);
+template <typename real> cudaError_t launch_tsgram(const GramJob *, int, int, int, cudaStream_t);
 template <typename real> cudaError_t launch_fill(const FillJob *, int, int, cudaStream_t);
 template <typename rin, typename rout>
 cudaError_t launch_apply(const ApplyJob *, int, int, int, cudaStream_t);
 template <typename real> cudaError_t launch_project(const Inst *, int, int, int, cudaStream_t);
 cudaError_t prepare_dense(int);
+int reduce_cluster_cap();
 cudaError_t launch_reduce(const ReduceJob *, int, int, cudaStream_t);
 template <typename real> cudaError_t launch_tupdate(const Inst *, int, int, int, cudaStream_t);
 cudaError_t launch_select(const Inst *, int, int, cudaStream_t);
@@ -349,6 +350,16 @@ static int num_sms() {
   return sms;
 }
 
+// CTAs a reduction may use: whole clusters, all resident at once
+static int reduce_cta_cap() {
+  static int cap = 0;
+  if (!cap) {
+    const int c = reduce_cluster_cap();
+    cap = c > 0 ? c * kCl : 15 * kCl;
+  }
+  return cap;
+}
+
 static Sizes sizes_of(const dlr_problem *p, int sms) {
   Sizes s;
   s.N = p->nx * p->ny;
@@ -357,9 +368,10 @@ static Sizes sizes_of(const dlr_problem *p, int sms) {
   s.rs = p->precision == DLR_MIXED ? 4 : 8;
   // CTAs of the cell and angle reductions: whole clusters of kCl CTAs,
   // about 512 cells or 16 angles per CTA
-  auto clusters = [](int x) { return (x + kCl - 1) / kCl * kCl; };
-  s.pb = clusters(std::max(1, std::min(2 * sms, (s.N + 511) / 512)));
-  s.pbl = clusters(std::max(1, std::min(2 * sms, (s.K + 15) / 16)));
+  const int cap = std::min(reduce_cta_cap(), 2 * sms / kCl * kCl);
+  auto clusters = [&](int x) { return std::min(cap, (x + kCl - 1) / kCl * kCl); };
+  s.pb = clusters(std::max(1, (s.N + 511) / 512));
+  s.pbl = clusters(std::max(1, (s.K + 15) / 16));
   s.lb = std::max(1, std::min(2 * sms, (s.K + 7) / 8));          // 4 warps x 2 angles
   const size_t r = s.r;
   s.partial_doubles = std::max({(size_t)(s.pb / kCl) * proj_count(s.r), (size_t)(s.pb / kCl) * r * r,
@@ -884,16 +896,16 @@ static int enqueue_post(Batch *b) {
   // step 5: CholeskyQR of Psi; dependent columns are replaced by
   // pseudo-random ones (orthonormal completion) and the pass redone; a third
   // pass runs when a Cholesky needed a shift
-  LK(launch_tsgram<real>(b->g_psi1, n, b->pbmax, st));
+  LK(launch_tsgram<real>(b->g_psi1, n, b->pbmax, 0, st));
   LK(launch_chol(b->c_p1, d, n, st));
   LK(launch_fill<real>(b->f_psi, n, b->maxN, st));
-  LK(launch_tsgram<real>(b->g_psire, n, b->pbmax, st));
+  LK(launch_tsgram<real>(b->g_psire, n, b->pbmax, 0, st));
   LK(launch_chol(b->c_p1b, d, n, st));
   LK((launch_apply<real, real>(b->a_psi, n, b->maxN, b->rmax, st)));
-  LK(launch_tsgram<real>(b->g_x, n, b->pbmax, st));
+  LK(launch_tsgram<real>(b->g_x, n, b->pbmax, 0, st));
   LK(launch_chol(b->c_p2, d, n, st));
   LK((launch_apply<real, real>(b->a_x2, n, b->maxN, b->rmax, st)));
-  LK(launch_tsgram<real>(b->g_x3, n, b->pbmax, st));
+  LK(launch_tsgram<real>(b->g_x3, n, b->pbmax, 0, st));
   LK(launch_chol(b->c_p3, d, n, st));
   LK((launch_apply<real, real>(b->a_x3, n, b->maxN, b->rmax, st)));
   // steps 6-7: projections and the L-step
@@ -904,19 +916,19 @@ static int enqueue_post(Batch *b) {
   b->kcount += 2;  // three kernels
   // step 8: CholeskyQR of M = diag(sqrt w) L^T into Q (held in W0), S = M^T Q,
   // SVD of S, W0 <- diag(1/sqrt w) Q V
-  LK(launch_tsgram<double>(b->g_l1, n, b->pblmax, st));
+  LK(launch_tsgram<double>(b->g_l1, n, b->pblmax, 1, st));
   LK(launch_chol(b->c_l1, d, n, st));
   LK(launch_fill<double>(b->f_l, n, b->maxK, st));
-  LK(launch_tsgram<double>(b->g_lf, n, b->pblmax, st));
+  LK(launch_tsgram<double>(b->g_lf, n, b->pblmax, 1, st));
   LK(launch_chol(b->c_l1b, d, n, st));
   LK((launch_apply<double, double>(b->a_l1, n, b->maxK, b->rmax, st)));
-  LK(launch_tsgram<double>(b->g_w, n, b->pblmax, st));
+  LK(launch_tsgram<double>(b->g_w, n, b->pblmax, 0, st));
   LK(launch_chol(b->c_l2, d, n, st));
   LK((launch_apply<double, double>(b->a_w2, n, b->maxK, b->rmax, st)));
-  LK(launch_tsgram<double>(b->g_w3, n, b->pblmax, st));
+  LK(launch_tsgram<double>(b->g_w3, n, b->pblmax, 0, st));
   LK(launch_chol(b->c_l3, d, n, st));
   LK((launch_apply<double, double>(b->a_w3, n, b->maxK, b->rmax, st)));
-  LK(launch_tsgram<double>(b->g_cross, n, b->pblmax, st));
+  LK(launch_tsgram<double>(b->g_cross, n, b->pblmax, 1, st));
   LK(launch_svd(d, n, b->svd_mode, st));
   LK((launch_apply<double, double>(b->a_wv, n, b->maxK, b->rmax, st)));
   if (b->svd_mode == 1) LK(launch_sign(d, n, b->maxK, st));

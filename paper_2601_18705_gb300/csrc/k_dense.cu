@@ -15,6 +15,8 @@
 //                  form) with phi = X (L w), fused with the rotation X0 <- X U
 // Mixed precision: products and sums over one staging round (at most 128
 // rows) in FP32, round sums accumulated in FP64.
+#include <algorithm>
+
 #include "dlr_internal.cuh"
 
 namespace dlr {
@@ -97,12 +99,12 @@ constexpr int gram_smem_bytes() {
   return tiles > red ? tiles : red;
 }
 
-template <typename real>
+template <typename real, int LAY>
 __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kTB)
 k_tsgram(const GramJob *__restrict__ jobs) {
   constexpr int GR = GramCfg<real>::GR, LD = GR + 4;
   constexpr int PF = GR * 32 / kTB;  // prefetched elements per thread and matrix
-  const GramJob &J = jobs[blockIdx.y];
+  const GramJob J = jobs[blockIdx.y];
   // nblocks is a multiple of the cluster size and run_if is per job, so
   // whole clusters leave together
   if ((int)blockIdx.x >= J.nblocks || (J.run_if && *J.run_if == 0)) return;
@@ -111,7 +113,7 @@ k_tsgram(const GramJob *__restrict__ jobs) {
   real *As = reinterpret_cast<real *>(raw);
   real *Bs = As + 32 * LD;
   real *ws = Bs + 32 * LD;
-  const int r = J.r, t = threadIdx.x, lay = J.layout;
+  const int r = J.r, t = threadIdx.x;
   const int side = (r + 3) >> 2, ntile = side * side;
   const int ngroup = kTB / ntile;
   const int grp = t / ntile, tt = t - grp * ntile;
@@ -123,27 +125,32 @@ k_tsgram(const GramJob *__restrict__ jobs) {
   const int per = (J.m + J.nblocks - 1) / J.nblocks;
   const int row0 = min(J.m, (int)blockIdx.x * per), row1 = min(J.m, row0 + per);
   const int nround = (row1 - row0 + GR - 1) / GR;
-  real pa[PF], pbv[PF], pw = real(0);
+  // (row, column) of the elements this thread stages, fixed for all rounds
+  int erow[PF], ecol[PF];
+#pragma unroll
+  for (int k = 0; k < PF; ++k) {
+    const int e = t + kTB * k;
+    erow[k] = LAY == 0 ? e % GR : e / r;
+    ecol[k] = LAY == 0 ? e / GR : e % r;
+    if (erow[k] >= GR || ecol[k] >= r) ecol[k] = 32;  // not staged
+  }
+  // rounds per FP32 partial: about 64 rows per thread before the FP64 add
+  const int flush_every = max(1, 64 * ngroup / GR);
+  // The prefetch issues plain loads from clamped (always valid) addresses
+  // and keeps the raw values: no arithmetic touches them until they are
+  // staged, so the loads stay in flight during the products.
+  real pa[PF], pbv[PF];
+  double pw = 0.0;
   auto prefetch = [&](int rd) {
     const int base = row0 + rd * GR;
 #pragma unroll
     for (int k = 0; k < PF; ++k) {
-      const int e = t + kTB * k;
-      const int rr = lay == 0 ? e % GR : e / r, i = lay == 0 ? e / GR : e % r;
-      const bool ok = rr < GR && i < r && base + rr < row1;
-      const size_t at = lay == 0 ? (size_t)J.lda * i + base + rr : (size_t)r * (base + rr) + i;
-      pa[k] = ok ? A[at] : real(0);
-      if (cross) pbv[k] = ok ? Bm[(size_t)J.ldb * i + base + rr] : real(0);
+      const int row = min(base + erow[k], row1 - 1), i = min(ecol[k], r - 1);
+      const size_t at = LAY == 0 ? (size_t)J.lda * i + row : (size_t)r * row + i;
+      pa[k] = A[at];
+      if (cross) pbv[k] = Bm[(size_t)J.ldb * i + row];
     }
-    if (t < GR) {
-      const int row = base + t;
-      double w = 0.0;
-      if (row < row1) {
-        w = J.wt ? J.wt[row] : 1.0;
-        if (J.sqrt_wt) w = sqrt(w);
-      }
-      pw = real(w);
-    }
+    if (t < GR && J.wt) pw = J.wt[min(base + t, row1 - 1)];
   };
   real s[16];
   double acc[16];
@@ -152,16 +159,21 @@ k_tsgram(const GramJob *__restrict__ jobs) {
   if (nround > 0) prefetch(0);
   for (int rd = 0; rd < nround; ++rd) {
     __syncthreads();  // the previous round's products are done
+    const int base = row0 + rd * GR;
 #pragma unroll
     for (int k = 0; k < PF; ++k) {
-      const int e = t + kTB * k;
-      const int rr = lay == 0 ? e % GR : e / r, i = lay == 0 ? e / GR : e % r;
-      if (rr < GR && i < r) {
-        As[i * LD + rr] = pa[k];
-        if (cross) Bs[i * LD + rr] = pbv[k];
+      const int rr = erow[k], i = ecol[k];
+      if (i < 32) {
+        const bool ok = base + rr < row1;
+        As[i * LD + rr] = ok ? pa[k] : real(0);
+        if (cross) Bs[i * LD + rr] = ok ? pbv[k] : real(0);
       }
     }
-    if (t < GR) ws[t] = pw;
+    if (t < GR) {
+      double w = base + t < row1 ? (J.wt ? pw : 1.0) : 0.0;
+      if (J.sqrt_wt) w = sqrt(w);
+      ws[t] = real(w);
+    }
     __syncthreads();
     if (rd + 1 < nround) prefetch(rd + 1);  // in flight during the products below
     if (own) {
@@ -184,7 +196,7 @@ k_tsgram(const GramJob *__restrict__ jobs) {
 #pragma unroll
             for (int m = 0; m < 4; ++m) s[kk * 4 + k] += a[kk].v[m] * b[k].v[m];
       }
-      if (sizeof(real) == 4) {
+      if (sizeof(real) == 4 && ((rd + 1) % flush_every == 0 || rd + 1 == nround)) {
 #pragma unroll
         for (int e = 0; e < 16; ++e) { acc[e] += (double)s[e]; s[e] = real(0); }
       }
@@ -340,7 +352,8 @@ k_project(const Inst *__restrict__ insts) {
   constexpr int GP = ProjCfg<real>::GP, LD = GP + 4;
   constexpr int PF = GP * 32 / kTB;
   const Inst &I = insts[blockIdx.y];
-  if ((int)blockIdx.x >= I.partial_blocks) return;  // whole clusters
+  const int nblk = I.partial_blocks;
+  if ((int)blockIdx.x >= nblk) return;  // whole clusters
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ __align__(32) unsigned char dyn[];
   real *Xs = reinterpret_cast<real *>(dyn);
@@ -354,34 +367,38 @@ k_project(const Inst *__restrict__ insts) {
   const int ti = 4 * (tt % s4), tj = 2 * (tt / s4);
   const bool own = grp < ngroup;
   const bool vec_owner = own && tj == 0;
-  const real *X = as_c<real>(I.X), *X0 = as_c<real>(I.X0);
-  const real *sig_t = as_c<real>(I.sig_t), *ss4 = as_c<real>(I.ss4), *qv = as_c<real>(I.q);
-  const int per = (N + I.partial_blocks - 1) / I.partial_blocks;
+  const real *__restrict__ X = as_c<real>(I.X);
+  const real *__restrict__ X0 = as_c<real>(I.X0);
+  const real *__restrict__ sig_t = as_c<real>(I.sig_t);
+  const real *__restrict__ ss4 = as_c<real>(I.ss4);
+  const real *__restrict__ qv = as_c<real>(I.q);
+  double *const partials = I.partials;
+  const int per = (N + nblk - 1) / nblk;
+  // rounds per FP32 partial: about 64 cells per thread before the FP64 add
+  const int flush_every = max(1, 64 * ngroup / GP);
   const int c0 = min(N, (int)blockIdx.x * per), c1 = min(N, c0 + per);
   const int nround = (c1 - c0 + GP - 1) / GP;
+  // raw loads from clamped addresses (masks applied when staging), as in
+  // k_tsgram; the left and lower neighbours of cells on the first column or
+  // row are masked by mL and mB in the products
   real px[PF], pl[PF], pd[PF], p0[PF], pv[3];
-  int pix = -1, piy = -1;
   auto prefetch = [&](int rd) {
     const int base = c0 + rd * GP;
 #pragma unroll
     for (int k = 0; k < PF; ++k) {
-      const int e = t + kTB * k, rr = e % GP, i = e / GP;
-      const int c = base + rr;
-      const bool ok = i < r && c < c1;
+      const int e = t + kTB * k, rr = e % GP, i = min(e / GP, r - 1);
+      const int c = min(base + rr, c1 - 1);
       const size_t col = (size_t)N * i;
-      px[k] = ok ? X[col + c] : real(0);
-      pl[k] = ok && c >= 1 ? X[col + c - 1] : real(0);
-      pd[k] = ok && c >= nx ? X[col + c - nx] : real(0);
-      p0[k] = ok ? X0[col + c] : real(0);
+      px[k] = X[col + c];
+      pl[k] = X[col + max(c - 1, 0)];
+      pd[k] = X[col + max(c - nx, 0)];
+      p0[k] = X0[col + c];
     }
     if (t < GP) {
-      const int c = base + t;
-      const bool ok = c < c1;
-      pv[0] = ok ? sig_t[c] : real(0);
-      pv[1] = ok ? ss4[c] * real(4.0 * kPi) : real(0);
-      pv[2] = ok ? qv[c] : real(0);
-      pix = ok ? c % nx : -1;
-      piy = ok ? c / nx : -1;
+      const int c = min(base + t, c1 - 1);
+      pv[0] = sig_t[c];
+      pv[1] = ss4[c];
+      pv[2] = qv[c];
     }
   };
   real sm[24], sv[16];
@@ -393,21 +410,25 @@ k_project(const Inst *__restrict__ insts) {
   if (nround > 0) prefetch(0);
   for (int rd = 0; rd < nround; ++rd) {
     __syncthreads();
+    const int base = c0 + rd * GP;
 #pragma unroll
     for (int k = 0; k < PF; ++k) {
       const int e = t + kTB * k, rr = e % GP, i = e / GP;
       if (i < r) {
-        Xs[i * LD + rr] = px[k];
-        XLs[i * LD + rr] = pl[k];
-        XBs[i * LD + rr] = pd[k];
-        X0s[i * LD + rr] = p0[k];
+        const bool ok = base + rr < c1;
+        Xs[i * LD + rr] = ok ? px[k] : real(0);
+        XLs[i * LD + rr] = ok ? pl[k] : real(0);
+        XBs[i * LD + rr] = ok ? pd[k] : real(0);
+        X0s[i * LD + rr] = ok ? p0[k] : real(0);
       }
     }
     if (t < GP) {
-      const bool ok = pix >= 0;
-      vs[0 * GP + t] = pv[0];
-      vs[1 * GP + t] = pv[1];
-      vs[2 * GP + t] = pv[2];
+      const int c = base + t;
+      const bool ok = c < c1;
+      const int pix = ok ? c % nx : -1, piy = ok ? c / nx : -1;
+      vs[0 * GP + t] = ok ? pv[0] : real(0);
+      vs[1 * GP + t] = ok ? pv[1] * real(4.0 * kPi) : real(0);
+      vs[2 * GP + t] = ok ? pv[2] : real(0);
       vs[3 * GP + t] = real(ok && pix >= 1);
       vs[4 * GP + t] = real(ok && piy >= 1);
       vs[5 * GP + t] = real(ok && pix == 0);
@@ -481,7 +502,7 @@ k_project(const Inst *__restrict__ insts) {
           }
         }
       }
-      if (sizeof(real) == 4) {
+      if (sizeof(real) == 4 && ((rd + 1) % flush_every == 0 || rd + 1 == nround)) {
 #pragma unroll
         for (int e = 0; e < 24; ++e) { am[e] += (double)sm[e]; sm[e] = real(0); }
 #pragma unroll
@@ -532,7 +553,7 @@ k_project(const Inst *__restrict__ insts) {
   cluster.sync();
   const int rank = (int)cluster.block_rank();
   const int cnt = proj_count(r), share = (cnt + kCl - 1) / kCl;
-  double *out = I.partials + (size_t)(blockIdx.x / kCl) * cnt;
+  double *out = partials + (size_t)(blockIdx.x / kCl) * cnt;
   for (int e = rank * share + t; e < min(cnt, (rank + 1) * share); e += kTB) {
     double v = 0.0;
 #pragma unroll
@@ -609,9 +630,11 @@ cudaError_t launch_coeff_recon(const Inst *d, int n, int maxN, int r, cudaStream
   return cudaGetLastError();
 }
 
+// layout: the (common) layout of the batch's matrices
 template <typename real>
-cudaError_t launch_tsgram(const GramJob *d_jobs, int n, int maxblocks, cudaStream_t st) {
-  k_tsgram<real><<<dim3(maxblocks, n), kTB, 0, st>>>(d_jobs);
+cudaError_t launch_tsgram(const GramJob *d_jobs, int n, int maxblocks, int layout, cudaStream_t st) {
+  if (layout == 0) k_tsgram<real, 0><<<dim3(maxblocks, n), kTB, 0, st>>>(d_jobs);
+  else k_tsgram<real, 1><<<dim3(maxblocks, n), kTB, 0, st>>>(d_jobs);
   return cudaGetLastError();
 }
 
@@ -634,6 +657,41 @@ template <typename real>
 cudaError_t launch_project(const Inst *d, int n, int maxblocks, int rmax, cudaStream_t st) {
   k_project<real><<<dim3(maxblocks, n), kTB, proj_smem_bytes(rmax, sizeof(real)), st>>>(d);
   return cudaGetLastError();
+}
+
+cudaError_t prepare_dense(int rmax);
+
+// Clusters of the reduction kernels that can be resident at once (the CTA
+// count of a reduction is kept to that many clusters, so it runs in one
+// wave); 0 if it cannot be determined.
+int reduce_cluster_cap() {
+  auto cap = [](const void *fn, size_t smem) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kCl);
+    cfg.blockDim = dim3(kTB);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = kCl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return n;
+  };
+  int c = cap((const void *)k_tsgram<float, 0>, 0);
+  c = std::min(c, cap((const void *)k_tsgram<double, 0>, 0));
+  c = std::min(c, cap((const void *)k_tsgram<double, 1>, 0));
+  if (prepare_dense(kMaxRank) == cudaSuccess) {
+    c = std::min(c, cap((const void *)k_project<float>, proj_smem_bytes(kMaxRank, 4)));
+    c = std::min(c, cap((const void *)k_project<double>, proj_smem_bytes(kMaxRank, 8)));
+  }
+  return c;
 }
 
 // Kernel attributes, set before any launch is captured into a graph.
@@ -661,8 +719,8 @@ cudaError_t launch_tupdate(const Inst *d, int n, int maxN, int r, cudaStream_t s
 
 template cudaError_t launch_coeff_recon<float>(const Inst *, int, int, int, cudaStream_t);
 template cudaError_t launch_coeff_recon<double>(const Inst *, int, int, int, cudaStream_t);
-template cudaError_t launch_tsgram<float>(const GramJob *, int, int, cudaStream_t);
-template cudaError_t launch_tsgram<double>(const GramJob *, int, int, cudaStream_t);
+template cudaError_t launch_tsgram<float>(const GramJob *, int, int, int, cudaStream_t);
+template cudaError_t launch_tsgram<double>(const GramJob *, int, int, int, cudaStream_t);
 template cudaError_t launch_fill<float>(const FillJob *, int, int, cudaStream_t);
 template cudaError_t launch_fill<double>(const FillJob *, int, int, cudaStream_t);
 template cudaError_t launch_apply<float, float>(const ApplyJob *, int, int, int, cudaStream_t);

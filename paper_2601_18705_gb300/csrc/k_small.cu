@@ -22,53 +22,65 @@ namespace dlr {
 constexpr unsigned kFullMask = 0xffffffffu;
 
 // ------------------------------------------------------------------
-// small parallel LU with partial pivoting on an n x n column-major matrix
-// in shared memory (one CTA).  Returns false if a pivot is exactly zero.
+// Solve M x = b (n x n, column-major, n <= 32, in shared memory) by Gaussian
+// elimination with partial pivoting, all threads of the CTA; M and b are
+// overwritten, x is left in b.  The pivot is the largest magnitude in the
+// column (lowest row on exact ties).  Returns false (in every thread) if a
+// pivot is exactly zero.
 // ------------------------------------------------------------------
-__device__ bool block_lu(double *A, int n, int *piv) {
-  __shared__ int pr_s;
-  __shared__ int bad_s;
-  if (threadIdx.x == 0) bad_s = 0;
-  __syncthreads();
+__device__ bool block_solve(double *M, double *b, int n) {
+  __shared__ int piv_s;
+  __shared__ double inv_s;
+  const int t = threadIdx.x, lane = t & 31;
   for (int p = 0; p < n; ++p) {
-    if (threadIdx.x == 0) {
-      int pr = p;
-      double best = fabs(A[p + n * p]);
-      for (int i = p + 1; i < n; ++i)
-        if (fabs(A[i + n * p]) > best) { best = fabs(A[i + n * p]); pr = i; }
-      pr_s = pr;
-      piv[p] = pr;
-      if (best == 0.0) bad_s = 1;
-    }
-    __syncthreads();
-    if (bad_s) return false;
-    const int pr = pr_s;
-    if (pr != p)
-      for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        double t = A[p + n * k]; A[p + n * k] = A[pr + n * k]; A[pr + n * k] = t;
+    if (t < 32) {  // warp 0: pivot row (lanes = rows)
+      double v = (lane >= p && lane < n) ? fabs(M[lane + n * p]) : -1.0;
+      int row = lane;
+      for (int o = 16; o > 0; o >>= 1) {
+        const double v2 = __shfl_xor_sync(kFullMask, v, o);
+        const int r2 = __shfl_xor_sync(kFullMask, row, o);
+        if (v2 > v || (v2 == v && r2 < row)) { v = v2; row = r2; }
       }
+      if (lane == 0) {
+        piv_s = row;
+        const double d = M[row + n * p];
+        inv_s = d != 0.0 ? 1.0 / d : 0.0;
+      }
+    }
     __syncthreads();
-    for (int i = p + 1 + threadIdx.x; i < n; i += blockDim.x) A[i + n * p] /= A[p + n * p];
-    __syncthreads();
+    const int pr = piv_s;
+    const double inv = inv_s;
+    if (inv == 0.0) return false;
+    if (pr != p) {
+      for (int j = p + t; j <= n; j += blockDim.x) {
+        double *a = j < n ? M + n * j : b;
+        const double x = a[p];
+        a[p] = a[pr];
+        a[pr] = x;
+      }
+      __syncthreads();
+    }
+    // rows below p: a_ij -= (a_ip / a_pp) a_pj for j > p and for b
     const int m = n - p - 1;
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-      const int i = p + 1 + e % m, k = p + 1 + e / m;
-      A[i + n * k] -= A[i + n * p] * A[p + n * k];
+    for (int e = t; e < m * (m + 1); e += blockDim.x) {
+      const int i = p + 1 + e % m, j = p + 1 + e / m;  // j == n: the right-hand side
+      double *col = j < n ? M + n * j : b;
+      col[i] -= M[i + n * p] * inv * col[p];
     }
     __syncthreads();
   }
-  return true;
-}
-
-// solve with the factors of block_lu (thread 0; n <= 32)
-__device__ void lu_solve_serial(const double *A, int n, const int *piv, double *b) {
-  for (int i = 0; i < n; ++i) { double t = b[i]; b[i] = b[piv[i]]; b[piv[i]] = t; }
-  for (int i = 0; i < n; ++i)
-    for (int k = 0; k < i; ++k) b[i] -= A[i + n * k] * b[k];
-  for (int i = n - 1; i >= 0; --i) {
-    for (int k = i + 1; k < n; ++k) b[i] -= A[i + n * k] * b[k];
-    b[i] /= A[i + n * i];
+  if (t < 32) {  // back substitution, lanes = rows
+    double x = lane < n ? b[lane] : 0.0;
+    for (int k = n - 1; k >= 0; --k) {
+      double xk = __shfl_sync(kFullMask, x, k);
+      xk = xk / M[k + n * k];
+      if (lane == k) x = xk;
+      if (lane < k) x -= M[lane + n * k] * xk;
+    }
+    if (lane < n) b[lane] = x;
   }
+  __syncthreads();
+  return true;
 }
 
 // Block argmax with the tie rule: the lowest index whose value is within a
@@ -97,16 +109,19 @@ __device__ int block_argmax_tie(const double *val, int n) {
 // ------------------------------------------------------------------
 // step 2: angle choice, one thread-block cluster per instance.  CTA g of the
 // cluster owns angles [g*slice, (g+1)*slice) as columns of A = W0^T in its
-// shared memory.  Per pivot step: (1) every CTA computes the remaining norm
-// (or DEIM interpolation residual) of its unused columns and its largest
-// one; cluster barrier; (2) every CTA reads the CTAs' maxima and then all
-// norms through distributed shared memory and takes the same pivot: the
-// lowest angle within a relative 1e-12 of the maximum (reading R8); (3) in
-// pivoted-QR mode every CTA reads the pivot column from its owner and
-// applies the same Householder reflection to its unused columns.  Norms and
-// maxima alternate between two buffers by step parity and chosen columns are
-// never written again, so one cluster barrier per step suffices.  CTA 0 then
-// forms What, beta, gamma = What^{-T} beta and C0 = S0 What^T.
+// shared memory (row i of A at A + i*slice_max), each column worked on by a
+// team of T threads (T a power of two, rows split by i mod T).  Per pivot
+// step: (1) every CTA computes the remaining squared norm (or the squared
+// DEIM interpolation residual) of its unused columns and its largest one;
+// cluster barrier; (2) every CTA reads the CTAs' maxima and then all
+// squared norms through distributed shared memory and takes the same pivot:
+// the lowest angle whose norm is within a relative 1e-12 of the largest
+// (reading R8); (3) in pivoted-QR mode every CTA reads the pivot column from
+// its owner and applies the same Householder reflection to its unused
+// columns.  Norms and maxima alternate between two buffers by step parity
+// and chosen columns are never written again, so one cluster barrier per
+// step suffices.  CTA 0 then forms What, beta, gamma = What^{-T} beta and
+// C0 = S0 What^T.
 // ------------------------------------------------------------------
 __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(256)
 k_select(const Inst *__restrict__ insts, int slice_max) {
@@ -118,21 +133,25 @@ k_select(const Inst *__restrict__ insts, int slice_max) {
   const int slice = (K + kCl - 1) / kCl, k0 = min(K, g * slice), k1 = min(K, k0 + slice);
   const int ns = k1 - k0;
   extern __shared__ double sh[];
-  double *A = sh;                          // r x slice_max, column c at A + r*c
-  double *nrm = A + 32 * slice_max;        // [2][slice_max]
+  double *A = sh;                          // r x slice_max, A[i*slice_max + c]
+  double *nrm = A + 32 * slice_max;        // [2][slice_max] squared norms
   unsigned char *used = reinterpret_cast<unsigned char *>(nrm + 2 * slice_max);
   __shared__ double v[32], col[32], M[32 * 32], rhs[32], bpart[32], lmax[2];
-  __shared__ int sel[32], ipiv[32];
+  __shared__ int sel[32];
   __shared__ double red_d[32];
   __shared__ int red_i[32];
-  __shared__ double vv_s, gmax_s;
+  __shared__ double hh_s, gmax_s;
   const double *W = I.W0;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int e = threadIdx.x; e < r * ns; e += blockDim.x) {
-    const int c = e / r, i = e % r;
-    A[i + r * c] = active ? W[(k0 + c) + (size_t)K * i] : 0.0;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
+  // column teams: T threads per column, rows i = m, m + T, ...
+  int T = 1;
+  while (T < 32 && 2 * T * max(ns, 1) <= (int)blockDim.x) T *= 2;
+  const int m = t & (T - 1), c_first = t / T, c_step = (int)blockDim.x / T;
+  for (int e = t; e < r * ns; e += blockDim.x) {
+    const int i = e / ns, c = e - i * ns;
+    A[i * slice_max + c] = active ? W[(k0 + c) + (size_t)K * i] : 0.0;
   }
-  for (int c = threadIdx.x; c < ns; c += blockDim.x) used[c] = 0;
+  for (int c = t; c < ns; c += blockDim.x) used[c] = 0;
   // this CTA's share of beta_j = sum_k w_k W0_kj
   for (int j = wid; j < r; j += nw) {
     double s = 0.0;
@@ -145,49 +164,42 @@ k_select(const Inst *__restrict__ insts, int slice_max) {
   for (int s = 0; s < r; ++s) {
     const int par = s & 1;
     double *nr = nrm + par * slice_max;
-    // (1) norms (or interpolation residuals) of the unused owned columns
-    if (I.selection == 0) {
-      for (int c = threadIdx.x; c < ns; c += blockDim.x) {
-        double t = 0.0;
-        for (int i = s; i < r; ++i) t += A[i + r * c] * A[i + r * c];
-        nr[c] = used[c] ? -1.0 : sqrt(t);
+    // (1) squared norms (or residuals) of the unused owned columns
+    if (I.selection == 1 && s > 0) {
+      // DEIM: interpolation coefficients on the s chosen points,
+      // W0[sel, 0:s] c = W0[sel, s]
+      for (int e = t; e < s * s; e += blockDim.x) {
+        const int i = e % s, l = e / s;
+        M[e] = active ? W[sel[i] + (size_t)K * l] : (i == l ? 1.0 : 0.0);
       }
-    } else {
-      if (threadIdx.x == 0 && s > 0 && active) {  // interpolation coefficients on the s chosen points
-        for (int i = 0; i < s; ++i) {
-          rhs[i] = W[sel[i] + (size_t)K * s];
-          for (int l = 0; l < s; ++l) M[i + s * l] = W[sel[i] + (size_t)K * l];
-        }
-        for (int p = 0; p < s; ++p) {
-          int pr = p;
-          for (int i = p + 1; i < s; ++i) if (fabs(M[i + s * p]) > fabs(M[pr + s * p])) pr = i;
-          if (pr != p) {
-            for (int l = 0; l < s; ++l) { double t = M[p + s * l]; M[p + s * l] = M[pr + s * l]; M[pr + s * l] = t; }
-            double t = rhs[p]; rhs[p] = rhs[pr]; rhs[pr] = t;
-          }
-          for (int i = p + 1; i < s; ++i) {
-            const double f = M[i + s * p] / M[p + s * p];
-            for (int l = p; l < s; ++l) M[i + s * l] -= f * M[p + s * l];
-            rhs[i] -= f * rhs[p];
-          }
-        }
-        for (int i = s - 1; i >= 0; --i) {
-          for (int l = i + 1; l < s; ++l) rhs[i] -= M[i + s * l] * rhs[l];
-          rhs[i] /= M[i + s * i];
-        }
-      }
+      for (int i = t; i < s; i += blockDim.x) rhs[i] = active ? W[sel[i] + (size_t)K * s] : 0.0;
       __syncthreads();
-      for (int c = threadIdx.x; c < ns; c += blockDim.x) {
-        double res = A[s + r * c];
-        for (int l = 0; l < s; ++l) res -= rhs[l] * A[l + r * c];
-        nr[c] = used[c] ? -1.0 : fabs(res);
+      block_solve(M, rhs, s);  // a singular system leaves rhs partly reduced; the step goes on
+    }
+    for (int base = 0; base < ns; base += c_step) {  // the same trip count in every thread
+      const int c = base + c_first < ns ? base + c_first : -1;
+      double x = 0.0;
+      if (c >= 0) {
+        if (I.selection == 0) {
+          for (int i = s + ((m - s) & (T - 1)); i < r; i += T) {
+            const double a = A[i * slice_max + c];
+            x += a * a;
+          }
+        } else {
+          for (int i = m; i <= s; i += T) {
+            const double a = A[i * slice_max + c];
+            x += i == s ? a : -rhs[i] * a;
+          }
+        }
       }
+      for (int o = T >> 1; o > 0; o >>= 1) x += __shfl_xor_sync(kFullMask, x, o);
+      if (c >= 0 && m == 0) nr[c] = used[c] ? -1.0 : (I.selection == 0 ? x : x * x);
     }
     __syncthreads();
-    double m = -1.0;
-    for (int c = threadIdx.x; c < ns; c += blockDim.x) m = fmax(m, nr[c]);
-    m = block_max(m, red_d);
-    if (threadIdx.x == 0) lmax[par] = m;
+    double mx = -1.0;
+    for (int c = t; c < ns; c += blockDim.x) mx = fmax(mx, nr[c]);
+    mx = block_max(mx, red_d);
+    if (t == 0) lmax[par] = mx;
     cluster.sync();
     // (2) the same pivot in every CTA
     if (wid == 0) {
@@ -196,9 +208,9 @@ k_select(const Inst *__restrict__ insts, int slice_max) {
       if (lane == 0) gmax_s = x;
     }
     __syncthreads();
-    const double thr = gmax_s * (1.0 - kTieRel);
+    const double thr = gmax_s * ((1.0 - kTieRel) * (1.0 - kTieRel));  // on squared norms
     int best = 0x7fffffff;
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    for (int k = t; k < K; k += blockDim.x) {
       const int o = k / slice;
       const double x = cluster.map_shared_rank(nrm, o)[par * slice_max + (k - o * slice)];
       if (x >= 0.0 && x >= thr) best = min(best, k);
@@ -206,7 +218,7 @@ k_select(const Inst *__restrict__ insts, int slice_max) {
     for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(kFullMask, best, o));
     if (lane == 0) red_i[wid] = best;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (t == 0) {
       int p = 0x7fffffff;
       for (int q = 0; q < nw; ++q) p = min(p, red_i[q]);
       if (p < 0 || p >= K) {  // no finite candidate (NaN input)
@@ -217,72 +229,70 @@ k_select(const Inst *__restrict__ insts, int slice_max) {
     }
     __syncthreads();
     const int p = sel[s], owner = p / slice, pl = p - owner * slice;
-    if (owner == g && threadIdx.x == 0) used[pl] = 1;  // never written again
+    if (owner == g && t == 0) used[pl] = 1;  // never written again
     if (I.selection == 0) {
-      if (threadIdx.x < r) col[threadIdx.x] = cluster.map_shared_rank(A, owner)[threadIdx.x + r * pl];
+      if (t < r) col[t] = cluster.map_shared_rank(A, owner)[t * slice_max + pl];
       __syncthreads();
-      if (wid == 0) {  // Householder vector of col[s..r)
+      if (wid == 0) {  // Householder vector v of col[s..r), hh = 2 / v^T v
         const double ci = (lane >= s && lane < r) ? col[lane] : 0.0;
         const double nrm_p = sqrt(warp_sum(ci * ci));
         const double a = col[s] >= 0 ? -nrm_p : nrm_p;
         const double vi = lane == s ? ci - a : ci;
         const double vv = warp_sum(vi * vi);
-        if (lane < 32) v[lane] = vi;
-        if (lane == 0) vv_s = vv;
+        v[lane] = vi;
+        if (lane == 0) hh_s = vv > 0.0 ? 2.0 / vv : 0.0;
       }
       __syncthreads();
-      const double vv = vv_s;
-      if (vv > 0.0)
-        for (int c = threadIdx.x; c < ns; c += blockDim.x) {
-          if (used[c]) continue;
-          double d = 0.0;
-          for (int i = s; i < r; ++i) d += v[i] * A[i + r * c];
-          const double f = 2.0 * d / vv;
-          for (int i = s; i < r; ++i) A[i + r * c] -= f * v[i];
+      const double hh = hh_s;
+      for (int base = 0; base < ns; base += c_step) {
+        const int c0 = base + c_first;
+        const int c = (c0 < ns && hh != 0.0 && !used[min(c0, ns - 1)]) ? c0 : -1;
+        const int i0 = s + ((m - s) & (T - 1));
+        double d = 0.0;
+        if (c >= 0)
+          for (int i = i0; i < r; i += T) d += v[i] * A[i * slice_max + c];
+        for (int o = T >> 1; o > 0; o >>= 1) d += __shfl_xor_sync(kFullMask, d, o);
+        if (c >= 0) {
+          const double f = d * hh;
+          for (int i = i0; i < r; i += T) A[i * slice_max + c] -= f * v[i];
         }
+      }
     }
     __syncthreads();
   }
   cluster.sync();  // every CTA's beta share is final
-  if (g == 0 && active && threadIdx.x < r) {
-    double t = 0.0;
-    for (int q = 0; q < kCl; ++q) t += cluster.map_shared_rank(bpart, q)[threadIdx.x];
-    rhs[threadIdx.x] = t;
+  if (g == 0 && active && t < r) {
+    double x = 0.0;
+    for (int q = 0; q < kCl; ++q) x += cluster.map_shared_rank(bpart, q)[t];
+    rhs[t] = x;
   }
   cluster.sync();  // peers' shared memory stays valid until CTA 0 has read it
   if (!active || g != 0) return;
   // What_ij = W0_j(Om^(i)), beta, gamma = What^{-T} beta, C0 = S0 What^T
   double *What = I.small + I.lay.What;
   double *beta = I.small + I.lay.beta;
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+  for (int e = t; e < r * r; e += blockDim.x) {
     const int i = e % r, j = e / r;
-    What[e] = W[sel[i] + (size_t)K * j];
+    const double x = W[sel[i] + (size_t)K * j];
+    What[e] = x;
+    M[j + r * i] = x;  // What^T
   }
-  for (int i = threadIdx.x; i < r; i += blockDim.x) {
+  for (int i = t; i < r; i += blockDim.x) {
     I.idx[i] = sel[i];
     beta[i] = rhs[i];
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-    const int i = e % r, j = e / r;
-    M[i + r * j] = What[j + r * i];
-  }
-  __syncthreads();
-  const bool ok = block_lu(M, r, ipiv);
-  if (!ok) {
-    if (threadIdx.x == 0) set_status(I.status, kESingular);
+  if (!block_solve(M, rhs, r)) {
+    if (t == 0) set_status(I.status, kESingular);
     return;
   }
-  if (threadIdx.x == 0) {
-    lu_solve_serial(M, r, ipiv, rhs);
-    for (int i = 0; i < r; ++i) I.small[I.lay.gamma + i] = rhs[i];
-  }
+  for (int i = t; i < r; i += blockDim.x) I.small[I.lay.gamma + i] = rhs[i];
   double *C0 = I.small + I.lay.C0;
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+  for (int e = t; e < r * r; e += blockDim.x) {
     const int k = e % r, j = e / r;
-    double s = 0.0;
-    for (int l = 0; l < r; ++l) s += I.S0[k + r * l] * What[j + r * l];
-    C0[e] = s;
+    double x = 0.0;
+    for (int l = 0; l < r; ++l) x += I.S0[k + r * l] * What[j + r * l];
+    C0[e] = x;
   }
 }
 
@@ -630,7 +640,6 @@ __global__ void __launch_bounds__(256) k_lstep_mid(const Inst *__restrict__ inst
   if (*I.status != kOk) return;
   blocks_per_inst = I.lstep_blocks;
   __shared__ double M[32 * 32], Cb[32 * 32], z[32], Lb[32];
-  __shared__ int ipiv[32];
   const int r = I.r;
   const SmallLayout &L = I.lay;
   for (int e = threadIdx.x; e < r * r + r; e += blockDim.x) {
@@ -646,15 +655,12 @@ __global__ void __launch_bounds__(256) k_lstep_mid(const Inst *__restrict__ inst
     M[e] = (i == j ? 1.0 : 0.0) - t / (4.0 * kPi);
   }
   __syncthreads();
-  if (!block_lu(M, r, ipiv)) {
+  for (int i = threadIdx.x; i < r; i += blockDim.x) Lb[i] = z[i];
+  __syncthreads();
+  if (!block_solve(M, Lb, r)) {
     if (threadIdx.x == 0) set_status(I.status, kESingular);
     return;
   }
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < r; ++i) Lb[i] = z[i];
-    lu_solve_serial(M, r, ipiv, Lb);
-  }
-  __syncthreads();
   for (int i = threadIdx.x; i < r; i += blockDim.x) {
     double t = 0.0;
     for (int l = 0; l < r; ++l) t += Ms[i + r * l] * Lb[l];
