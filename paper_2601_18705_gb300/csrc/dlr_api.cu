@@ -45,7 +45,7 @@ cudaError_t launch_select(const Inst *, int, int, cudaStream_t);
 cudaError_t launch_chol(const CholJob *, const Inst *, int, cudaStream_t);
 cudaError_t launch_proj_post(const Inst *, int, cudaStream_t);
 size_t lstep_angle_smem(int);
-cudaError_t launch_lstep(const Inst *, int, int, int, cudaStream_t);
+cudaError_t launch_lstep(const Inst *, int, int, int, int, cudaStream_t);
 cudaError_t launch_svd(const Inst *, int, int, cudaStream_t);
 cudaError_t launch_sign(const Inst *, int, int, cudaStream_t);
 cudaError_t launch_si_prep(const Inst *, int, SiCtl, cudaStream_t);
@@ -372,10 +372,10 @@ static Sizes sizes_of(const dlr_problem *p, int sms) {
   auto clusters = [&](int x) { return std::min(cap, (x + kCl - 1) / kCl * kCl); };
   s.pb = clusters(std::max(1, (s.N + 511) / 512));
   s.pbl = clusters(std::max(1, (s.K + 15) / 16));
-  s.lb = std::max(1, std::min(2 * sms, (s.K + 7) / 8));          // 4 warps x 2 angles
+  s.lb = std::min(2 * sms / kCl * kCl, (std::max(1, (s.K + 3) / 4) + kCl - 1) / kCl * kCl);  // 4 warps, one angle each
   const size_t r = s.r;
   s.partial_doubles = std::max({(size_t)(s.pb / kCl) * proj_count(s.r), (size_t)(s.pb / kCl) * r * r,
-                                (size_t)(s.pbl / kCl) * r * r, (size_t)s.lb * (r * r + r)});
+                                (size_t)(s.pbl / kCl) * r * r, (size_t)(s.lb / kCl) * (r * r + r)});
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
   size_t t = 0;
   t += 5 * al((size_t)s.N * 8);                 // sigma, rho_cv, T, B0, D
@@ -912,7 +912,7 @@ static int enqueue_post(Batch *b) {
   LK(launch_project<real>(d, n, b->pbmax, b->rmax, st));
   LK(launch_reduce(b->r_proj, n, proj_count(b->rmax), st));
   LK(launch_proj_post(d, n, st));
-  LK(launch_lstep(d, n, b->rmax, b->lbmax, st));
+  LK(launch_lstep(d, n, b->rmax, b->lbmax, b->maxK, st));
   b->kcount += 2;  // three kernels
   // step 8: CholeskyQR of M = diag(sqrt w) L^T into Q (held in W0), S = M^T Q,
   // SVD of S, W0 <- diag(1/sqrt w) Q V

@@ -7,12 +7,13 @@
 //   k_chol         Cholesky of a reduced Gram (one CholeskyQR pass of steps 5
 //                  and 8); detects dependent columns, shifts when needed
 //   k_proj_post    step 7 Galerkin operators from the reduced projections
-//   k_lstep_angle  step 7 per angle: B_k = |ox| A_x + |oy| A_y + M_t, LU with
-//                  partial pivoting (one warp per angle, one lane per column),
-//                  B_k^{-1} and B_k^{-1} Q_k summed with weights w_k (the
-//                  C-bar device of Section 3.3)
+//   k_lstep_angle  step 7 per angle: B_k = |ox| A_x + |oy| A_y + M_t,
+//                  Gauss-Jordan with partial pivoting on [B_k | I] (one warp
+//                  per angle, one lane per column), B_k^{-1} kept, y_k =
+//                  B_k^{-1} Q_k, both summed with weights w_k (the C-bar
+//                  device of Section 3.3)
 //   k_lstep_mid    (I - Cbar M_s / 4pi) Lbar = zeta
-//   k_lstep_back   L_k = B_k^{-1} (Q_k + M_s Lbar / 4pi)
+//   k_lstep_back   L_k = y_k + B_k^{-1} M_s Lbar / 4pi
 //   k_svd          step 8: S = M^T Q, one-sided Jacobi SVD S = U Sigma V^T
 //   k_sign         sign of each W column: its largest-magnitude entry > 0
 #include "dlr_internal.cuh"
@@ -493,168 +494,169 @@ __device__ void stage_ops(const Inst &I, double *sm) {
 
 constexpr int kLsWarps = 4;
 
-// One warp per angle; lane j owns column j of B_k padded to RB x RB with an
-// identity block (so every loop has a compile-time bound).  The per-CTA
-// sums of w_k B_k^{-1} and w_k B_k^{-1} Q_k go to partials[blockIdx.x].
+// |x| as an integer that orders like |x| (non-negative doubles order like
+// their bit patterns); integer compares stay off the FP64 pipe.
+__device__ __forceinline__ long long abs_bits(double x) {
+  return __double_as_longlong(x) & 0x7fffffffffffffffll;
+}
+
+// step 7, per angle.  One warp per angle runs Gauss-Jordan elimination with
+// partial pivoting on [B_k | I] (lane = column, two columns per lane when
+// RB = 32; B_k padded to RB x RB with an identity block).  The identity half
+// ends as B_k^{-1}: it is kept in lu for the last part of the L-step, y_k =
+// B_k^{-1} Q_k goes to L, and the CTA accumulates sum w_k B_k^{-1} and
+// sum w_k y_k (the C-bar device of Section 3.3).  CTA sums are added over
+// the cluster through distributed shared memory; cluster c writes its
+// partial (r^2 + r doubles) to partials + c*(r^2 + r).
 template <int RB>
-__global__ void __launch_bounds__(kLsWarps * 32) k_lstep_angle(const Inst *__restrict__ insts,
-                                                               int blocks_per_inst) {
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kLsWarps * 32)
+k_lstep_angle(const Inst *__restrict__ insts) {
+  constexpr int CPL = RB == 32 ? 2 : 1;  // columns per lane
   const Inst &I = insts[blockIdx.y];
-  blocks_per_inst = I.lstep_blocks;
-  if ((int)blockIdx.x >= blocks_per_inst || *I.status != kOk) return;
+  const int nblk = I.lstep_blocks;
+  if ((int)blockIdx.x >= nblk) return;  // whole clusters (nblk is a multiple of kCl)
+  cg::cluster_group cluster = cg::this_cluster();
+  const bool active = *I.status == kOk;
   extern __shared__ double sh[];
-  const int r = I.r, K = I.K;
-  double *sm = sh;                                   // 6 r^2 + 5 r
-  double *wlu = sh + 6 * r * r + 5 * r;              // kLsWarps x RB^2
-  double *red = wlu + (size_t)kLsWarps * RB * RB;    // kLsWarps x (r^2 + r)
+  const int r = I.r, K = I.K, rq = r * r + r;
+  double *sm = sh;                              // staged operators, 6 r^2 + 5 r
+  double *acc = sm + 6 * r * r + 5 * r;         // kLsWarps x (r^2 + r)
+  double *binv = acc + kLsWarps * rq;           // kLsWarps x r^2
+  double *part_s = binv + kLsWarps * r * r;     // r^2 + r
   stage_ops(I, sm);
+  for (int e = threadIdx.x; e < kLsWarps * rq; e += blockDim.x) acc[e] = 0.0;
+  __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  double *lu_w = wlu + (size_t)wid * RB * RB;
-  double *mine = red + (size_t)wid * (r * r + r);
-  double accC[RB];   // lane j: column j of sum_k w_k B_k^{-1}
-  double accZ = 0.0; // lane i: entry i of sum_k w_k B_k^{-1} Q_k
-#pragma unroll
-  for (int i = 0; i < RB; ++i) accC[i] = 0.0;
-  const bool on = lane < RB;
-  const int gw = blockIdx.x * kLsWarps + wid, nwarps = blocks_per_inst * kLsWarps;
-  for (int k = gw; k < K; k += nwarps) {
+  double *myacc = acc + wid * rq, *myb = binv + wid * r * r;
+  const double *Mt = sm + 4 * r * r;
+  const int gw = blockIdx.x * kLsWarps + wid, nwarps = nblk * kLsWarps;
+  for (int k = gw; active && k < K; k += nwarps) {
     const AngleOps o = angle_ops(I, sm, k);
-    const double *Mt = sm + 4 * r * r;
-    double col[RB];
+    double m[CPL][RB];
 #pragma unroll
-    for (int i = 0; i < RB; ++i) {
-      double v = (i == lane) ? 1.0 : 0.0;  // identity padding
-      if (lane < r && i < r)
-        v = o.aox * o.Ax[i + r * lane] + o.aoy * o.Ay[i + r * lane] + Mt[i + r * lane];
-      col[i] = v;
+    for (int s = 0; s < CPL; ++s) {
+      const int c = lane + 32 * s;
+#pragma unroll
+      for (int i = 0; i < RB; ++i) {
+        double v = 0.0;
+        if (c < RB) {
+          if (c < r && i < r) v = o.aox * o.Ax[i + r * c] + o.aoy * o.Ay[i + r * c] + Mt[i + r * c];
+          else v = (i == c) ? 1.0 : 0.0;
+        } else if (c < 2 * RB) {
+          v = (i == c - RB) ? 1.0 : 0.0;
+        }
+        m[s][i] = v;
+      }
     }
-    const double qk = lane < r ? angle_q(I, sm, o, k, lane) : 0.0;
-    int mypiv = lane;
     bool singular = false;
 #pragma unroll
     for (int p = 0; p < RB; ++p) {
       int pr = p;
-      if (lane == p) {
-        double best = -1.0;
+      if (lane == p) {  // column p: set 0 of lane p
+        long long best = -1;
 #pragma unroll
-        for (int i = p; i < RB; ++i)
-          if (fabs(col[i]) > best) { best = fabs(col[i]); pr = i; }
-        if (best == 0.0) pr = -1;
+        for (int i = p; i < RB; ++i) {
+          const long long a = abs_bits(m[0][i]);
+          if (a > best) { best = a; pr = i; }
+        }
+        if (best == 0) pr = -1;
       }
       pr = __shfl_sync(kFullMask, pr, p);
       if (pr < 0) { singular = true; break; }
-      if (lane == p) mypiv = pr;
       if (pr != p) {
-        double a = col[p], b = col[p];
 #pragma unroll
-        for (int i = p + 1; i < RB; ++i) if (i == pr) b = col[i];
-        col[p] = b;
+        for (int s = 0; s < CPL; ++s)
 #pragma unroll
-        for (int i = p + 1; i < RB; ++i) if (i == pr) col[i] = a;
+          for (int i = p + 1; i < RB; ++i)
+            if (i == pr) { const double x = m[s][p]; m[s][p] = m[s][i]; m[s][i] = x; }
       }
-      const double dpp = __shfl_sync(kFullMask, col[p], p);
-      if (lane == p) {
-        const double inv = 1.0 / dpp;
+      const double inv = 1.0 / __shfl_sync(kFullMask, m[0][p], p);
 #pragma unroll
-        for (int i = p + 1; i < RB; ++i) col[i] *= inv;
-      }
-      const double cp = col[p];
+      for (int s = 0; s < CPL; ++s) m[s][p] *= inv;
 #pragma unroll
-      for (int i = p + 1; i < RB; ++i) {
-        const double li = __shfl_sync(kFullMask, col[i], p);
-        if (lane > p) col[i] -= li * cp;
+      for (int i = 0; i < RB; ++i) {
+        if (i == p) continue;
+        const double f = __shfl_sync(kFullMask, m[0][i], p);  // before lane p updates it
+#pragma unroll
+        for (int s = 0; s < CPL; ++s) m[s][i] -= f * m[s][p];
       }
     }
     if (singular) {
       if (lane == 0) set_status(I.status, kESingular);
       break;
     }
-    if (on) {
-#pragma unroll
-      for (int i = 0; i < RB; ++i) lu_w[lane * RB + i] = col[i];
-    }
-    if (lane < r) {
+    // B_k^{-1} column j: lane RB + j (RB <= 16) or the second column of lane j
+    const int j = RB <= 16 ? lane - RB : lane;
+    if (j >= 0 && j < r) {
 #pragma unroll
       for (int i = 0; i < RB; ++i)
-        if (i < r) I.lu[((size_t)k * r + lane) * r + i] = col[i];
-      I.piv[(size_t)k * r + lane] = mypiv;
+        if (i < r) myb[i + r * j] = m[CPL - 1][i];
     }
     __syncwarp();
-    // lane j: column j of B^{-1} = U^{-1} L^{-1} P e_j (rows swapped in order)
-    double y[RB];
+    const double qk = lane < r ? angle_q(I, sm, o, k, lane) : 0.0;
+    double y0 = 0.0, y1 = 0.0;
 #pragma unroll
-    for (int i = 0; i < RB; ++i) y[i] = (i == lane) ? 1.0 : 0.0;
-#pragma unroll
-    for (int p = 0; p < RB; ++p) {
-      const int pr = __shfl_sync(kFullMask, mypiv, p);
-      if (pr != p) {
-        double a = y[p], b = y[p];
-#pragma unroll
-        for (int i = p + 1; i < RB; ++i) if (i == pr) b = y[i];
-        y[p] = b;
-#pragma unroll
-        for (int i = p + 1; i < RB; ++i) if (i == pr) y[i] = a;
+    for (int jj = 0; jj < RB; ++jj) {
+      if (jj < r) {
+        const double qj = __shfl_sync(kFullMask, qk, jj);
+        if (lane < r) {
+          const double t = myb[lane + r * jj] * qj;
+          if (jj & 1) y1 += t; else y0 += t;
+        }
       }
     }
-#pragma unroll
-    for (int i = 1; i < RB; ++i) {
-#pragma unroll
-      for (int m = 0; m < i; ++m) y[i] -= lu_w[m * RB + i] * y[m];
-    }
-#pragma unroll
-    for (int ii = RB - 1; ii >= 0; --ii) {
-#pragma unroll
-      for (int m = ii + 1; m < RB; ++m) y[ii] -= lu_w[m * RB + ii] * y[m];
-      y[ii] /= lu_w[ii * RB + ii];
-    }
-    // (B^{-1} Q)_i = sum_j (B^{-1})_ij Q_j ; lane j holds column j and Q_j
     const double wk = I.w[k];
-#pragma unroll
-    for (int i = 0; i < RB; ++i) {
-      if (i < r) {
-        const double z = warp_sum(lane < r ? y[i] * qk : 0.0);
-        if (lane == i) accZ += wk * z;
-      }
-      accC[i] += wk * y[i];
+    if (lane < r) {
+      const double y = y0 + y1;
+      I.L[(size_t)r * k + lane] = y;
+      myacc[r * r + lane] += wk * y;
+      for (int jj = 0; jj < r; ++jj) myacc[lane + r * jj] += wk * myb[lane + r * jj];
     }
+    double *B = I.lu + (size_t)k * r * r;
+    for (int e = lane; e < r * r; e += 32) B[e] = myb[e];
     __syncwarp();
-  }
-  if (lane < r) {
-#pragma unroll
-    for (int i = 0; i < RB; ++i)
-      if (i < r) mine[i + r * lane] = accC[i];
-    mine[r * r + lane] = accZ;
   }
   __syncthreads();
-  double *out = I.partials + (size_t)blockIdx.x * (r * r + r);
-  for (int e = threadIdx.x; e < r * r + r; e += blockDim.x) {
+  for (int e = threadIdx.x; e < rq; e += blockDim.x) {
     double s = 0.0;
-    for (int w = 0; w < kLsWarps; ++w) s += red[(size_t)w * (r * r + r) + e];
+    for (int w = 0; w < kLsWarps; ++w) s += acc[w * rq + e];
+    part_s[e] = s;
+  }
+  cluster.sync();
+  const int rank = (int)cluster.block_rank(), share = (rq + kCl - 1) / kCl;
+  double *out = I.partials + (size_t)(blockIdx.x / kCl) * rq;
+  for (int e = rank * share + threadIdx.x; e < min(rq, (rank + 1) * share); e += blockDim.x) {
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < kCl; ++q) s += cluster.map_shared_rank(part_s, q)[e];
     out[e] = s;
   }
+  cluster.sync();
 }
 
-__global__ void __launch_bounds__(256) k_lstep_mid(const Inst *__restrict__ insts,
-                                                   int blocks_per_inst) {
+// (I - Cbar M_s / 4pi) Lbar = zeta, tvec = M_s Lbar / 4pi
+__global__ void __launch_bounds__(256) k_lstep_mid(const Inst *__restrict__ insts) {
   const Inst &I = insts[blockIdx.x];
   if (*I.status != kOk) return;
-  blocks_per_inst = I.lstep_blocks;
+  const int nparts = I.lstep_blocks / kCl;
   __shared__ double M[32 * 32], Cb[32 * 32], z[32], Lb[32];
   const int r = I.r;
   const SmallLayout &L = I.lay;
   for (int e = threadIdx.x; e < r * r + r; e += blockDim.x) {
-    const double s = sum_partials(I.partials, blocks_per_inst, (size_t)(r * r + r), e);
+    const double s = sum_partials(I.partials, nparts, (size_t)(r * r + r), e);
     if (e < r * r) Cb[e] = s; else z[e - r * r] = s;
   }
   __syncthreads();
   const double *Ms = I.small + L.Ms;
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     const int i = e % r, j = e / r;
-    double t = 0.0;
-    for (int l = 0; l < r; ++l) t += Cb[i + r * l] * Ms[l + r * j];
-    M[e] = (i == j ? 1.0 : 0.0) - t / (4.0 * kPi);
+    double t0 = 0.0, t1 = 0.0;
+    for (int l = 0; l < r; l += 2) {
+      t0 += Cb[i + r * l] * Ms[l + r * j];
+      if (l + 1 < r) t1 += Cb[i + r * (l + 1)] * Ms[(l + 1) + r * j];
+    }
+    M[e] = (i == j ? 1.0 : 0.0) - (t0 + t1) / (4.0 * kPi);
   }
-  __syncthreads();
   for (int i = threadIdx.x; i < r; i += blockDim.x) Lb[i] = z[i];
   __syncthreads();
   if (!block_solve(M, Lb, r)) {
@@ -669,53 +671,24 @@ __global__ void __launch_bounds__(256) k_lstep_mid(const Inst *__restrict__ inst
   }
 }
 
-__global__ void __launch_bounds__(kLsWarps * 32) k_lstep_back(const Inst *__restrict__ insts,
-                                                              int blocks_per_inst) {
+// L_k = B_k^{-1} (Q_k + M_s Lbar / 4pi) = y_k + B_k^{-1} tvec, one thread per
+// entry (k, i) of L (angle-major rows of r)
+__global__ void __launch_bounds__(256) k_lstep_back(const Inst *__restrict__ insts) {
   const Inst &I = insts[blockIdx.y];
-  blocks_per_inst = I.lstep_blocks;
-  if ((int)blockIdx.x >= blocks_per_inst || *I.status != kOk) return;
-  extern __shared__ double sh[];
   const int r = I.r, K = I.K;
-  double *sm = sh;
-  stage_ops(I, sm);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const double tv = lane < r ? I.small[I.lay.tvec + lane] : 0.0;
-  const int gw = blockIdx.x * kLsWarps + wid, nwarps = blocks_per_inst * kLsWarps;
-  for (int k = gw; k < K; k += nwarps) {
-    const AngleOps o = angle_ops(I, sm, k);
-    double b = lane < r ? angle_q(I, sm, o, k, lane) + tv : 0.0;  // lane i holds b_i
-    const double *LU = I.lu + (size_t)k * r * r;
-    const int *pv = I.piv + (size_t)k * r;
-    double row[kMaxRank];  // lane i: row i of the LU factors (entry m = column m)
-#pragma unroll
-    for (int m = 0; m < kMaxRank; ++m) row[m] = (m < r && lane < r) ? LU[m * r + lane] : 0.0;
-    const int mypv = lane < r ? pv[lane] : lane;
-    for (int p = 0; p < r; ++p) {
-      const int pr = __shfl_sync(kFullMask, mypv, p);
-      if (pr != p) {
-        const double bp = __shfl_sync(kFullMask, b, p), bq = __shfl_sync(kFullMask, b, pr);
-        if (lane == p) b = bq;
-        if (lane == pr) b = bp;
-      }
-    }
-#pragma unroll
-    for (int m = 0; m < kMaxRank; ++m) {  // forward: unit lower
-      if (m < r) {
-        const double ym = __shfl_sync(kFullMask, b, m);
-        if (lane > m && lane < r) b -= row[m] * ym;
-      }
-    }
-#pragma unroll
-    for (int m = kMaxRank - 1; m >= 0; --m) {  // backward: upper
-      if (m < r) {
-        double xm = 0.0;
-        if (lane == m) { b /= row[m]; xm = b; }
-        xm = __shfl_sync(kFullMask, xm, m);
-        if (lane < m) b -= row[m] * xm;
-      }
-    }
-    if (lane < r) I.L[(size_t)r * k + lane] = b;
+  __shared__ double tv[32];
+  if (threadIdx.x < r) tv[threadIdx.x] = I.small[I.lay.tvec + threadIdx.x];
+  __syncthreads();
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (*I.status != kOk || e >= K * r) return;
+  const int k = e / r, i = e - k * r;
+  const double *B = I.lu + (size_t)k * r * r;
+  double s0 = 0.0, s1 = 0.0;
+  for (int j = 0; j < r; j += 2) {
+    s0 += B[i + r * j] * tv[j];
+    if (j + 1 < r) s1 += B[i + r * (j + 1)] * tv[j + 1];
   }
+  I.L[e] += s0 + s1;
 }
 
 // ------------------------------------------------------------------
@@ -881,10 +854,8 @@ static size_t select_smem(int slice_max) {
 }
 static int rank_bucket(int r) { return r <= 8 ? 8 : r <= 16 ? 16 : 32; }
 size_t lstep_angle_smem(int r) {
-  const int RB = rank_bucket(r);
-  return (size_t)(6 * r * r + 5 * r + kLsWarps * RB * RB + kLsWarps * (r * r + r)) * sizeof(double);
+  return (size_t)(6 * r * r + 5 * r + kLsWarps * (r * r + r) + kLsWarps * r * r + r * r + r) * sizeof(double);
 }
-static size_t lstep_back_smem(int r) { return (size_t)(6 * r * r + 5 * r) * sizeof(double); }
 
 cudaError_t prepare_small(int slice_max, int maxK, int rmax) {
   cudaError_t e;
@@ -896,8 +867,6 @@ cudaError_t prepare_small(int slice_max, int maxK, int rmax) {
                                 (int)lstep_angle_smem(rmax))) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_lstep_angle<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)lstep_angle_smem(rmax))) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_lstep_back, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)lstep_back_smem(rmax))) != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_sign, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)(maxK * sizeof(double)));
 }
@@ -913,19 +882,20 @@ cudaError_t launch_proj_post(const Inst *d, int n, cudaStream_t st) {
   k_proj_post<<<n, 256, 0, st>>>(d);
   return cudaGetLastError();
 }
-cudaError_t launch_lstep(const Inst *d, int n, int r_max, int blocks, cudaStream_t st) {
+// blocks: CTAs of the per-angle kernel (a multiple of kCl); maxK: most angles
+cudaError_t launch_lstep(const Inst *d, int n, int r_max, int blocks, int maxK, cudaStream_t st) {
   const dim3 g(blocks, n);
   const size_t sm = lstep_angle_smem(r_max);
   switch (rank_bucket(r_max)) {
-    case 8: k_lstep_angle<8><<<g, kLsWarps * 32, sm, st>>>(d, blocks); break;
-    case 16: k_lstep_angle<16><<<g, kLsWarps * 32, sm, st>>>(d, blocks); break;
-    default: k_lstep_angle<32><<<g, kLsWarps * 32, sm, st>>>(d, blocks); break;
+    case 8: k_lstep_angle<8><<<g, kLsWarps * 32, sm, st>>>(d); break;
+    case 16: k_lstep_angle<16><<<g, kLsWarps * 32, sm, st>>>(d); break;
+    default: k_lstep_angle<32><<<g, kLsWarps * 32, sm, st>>>(d); break;
   }
   cudaError_t e;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_lstep_mid<<<n, 256, 0, st>>>(d, blocks);
+  k_lstep_mid<<<n, 256, 0, st>>>(d);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_lstep_back<<<dim3(blocks, n), kLsWarps * 32, lstep_back_smem(r_max), st>>>(d, blocks);
+  k_lstep_back<<<dim3((maxK * r_max + 255) / 256, n), 256, 0, st>>>(d);
   return cudaGetLastError();
 }
 cudaError_t launch_svd(const Inst *d, int n, int mode, cudaStream_t st) {
