@@ -183,6 +183,11 @@ template <typename real> struct Real2;
 template <> struct Real2<float> { using type = float2; };
 template <> struct Real2<double> { using type = double2; };
 
+// fused multiply-add in the precision of the arguments (a plain fma() call
+// with float arguments would be evaluated in FP64)
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 template <typename T>
 __device__ __forceinline__ T *as(void *p) { return reinterpret_cast<T *>(p); }
 template <typename T>

@@ -22,36 +22,46 @@ namespace dlr {
 
 constexpr unsigned kFullMask = 0xffffffffu;
 
+// |x| as an integer that orders like |x| (non-negative doubles order like
+// their bit patterns); integer compares stay off the FP64 pipe.
+__device__ __forceinline__ long long abs_bits(double x) {
+  return __double_as_longlong(x) & 0x7fffffffffffffffll;
+}
+
+// 2^-e for the binary exponent e of a normal x > 0 (x 2^-e in [1, 2))
+__device__ __forceinline__ double inv_pow2_exponent(double x) {
+  const int e = (int)((__double_as_longlong(x) >> 52) & 0x7ff) - 1023;
+  return __longlong_as_double((long long)(1023 - e) << 52);
+}
+
 // ------------------------------------------------------------------
 // Solve M x = b (n x n, column-major, n <= 32, in shared memory) by Gaussian
 // elimination with partial pivoting, all threads of the CTA; M and b are
 // overwritten, x is left in b.  The pivot is the largest magnitude in the
-// column (lowest row on exact ties).  Returns false (in every thread) if a
-// pivot is exactly zero.
+// column (lowest row on exact ties).  The elimination is division-free
+// (rows below the pivot become (d a_ij - a_ip a_pj) 2^-e, a uniform scale
+// per row), so the FP64 divides happen once per row in the back
+// substitution, all at once.  Returns false (in every thread) if a pivot is
+// exactly zero.
 // ------------------------------------------------------------------
 __device__ bool block_solve(double *M, double *b, int n) {
   __shared__ int piv_s;
-  __shared__ double inv_s;
+  __shared__ double rdiag[32];
   const int t = threadIdx.x, lane = t & 31;
   for (int p = 0; p < n; ++p) {
-    if (t < 32) {  // warp 0: pivot row (lanes = rows)
-      double v = (lane >= p && lane < n) ? fabs(M[lane + n * p]) : -1.0;
+    if (t < 32) {  // warp 0: pivot row (lanes = rows), integer compares of |a|
+      long long v = (lane >= p && lane < n) ? abs_bits(M[lane + n * p]) : -1;
       int row = lane;
       for (int o = 16; o > 0; o >>= 1) {
-        const double v2 = __shfl_xor_sync(kFullMask, v, o);
+        const long long v2 = __shfl_xor_sync(kFullMask, v, o);
         const int r2 = __shfl_xor_sync(kFullMask, row, o);
         if (v2 > v || (v2 == v && r2 < row)) { v = v2; row = r2; }
       }
-      if (lane == 0) {
-        piv_s = row;
-        const double d = M[row + n * p];
-        inv_s = d != 0.0 ? 1.0 / d : 0.0;
-      }
+      if (lane == 0) piv_s = v > 0 ? row : -1;
     }
     __syncthreads();
     const int pr = piv_s;
-    const double inv = inv_s;
-    if (inv == 0.0) return false;
+    if (pr < 0) return false;
     if (pr != p) {
       for (int j = p + t; j <= n; j += blockDim.x) {
         double *a = j < n ? M + n * j : b;
@@ -61,20 +71,22 @@ __device__ bool block_solve(double *M, double *b, int n) {
       }
       __syncthreads();
     }
-    // rows below p: a_ij -= (a_ip / a_pp) a_pj for j > p and for b
+    const double d = M[p + n * p];
+    const double sc = inv_pow2_exponent(fabs(d));
     const int m = n - p - 1;
     for (int e = t; e < m * (m + 1); e += blockDim.x) {
       const int i = p + 1 + e % m, j = p + 1 + e / m;  // j == n: the right-hand side
       double *col = j < n ? M + n * j : b;
-      col[i] -= M[i + n * p] * inv * col[p];
+      col[i] = (d * col[i] - M[i + n * p] * col[p]) * sc;
     }
     __syncthreads();
   }
+  for (int k = t; k < n; k += blockDim.x) rdiag[k] = 1.0 / M[k + n * k];
+  __syncthreads();
   if (t < 32) {  // back substitution, lanes = rows
     double x = lane < n ? b[lane] : 0.0;
     for (int k = n - 1; k >= 0; --k) {
-      double xk = __shfl_sync(kFullMask, x, k);
-      xk = xk / M[k + n * k];
+      const double xk = __shfl_sync(kFullMask, x, k) * rdiag[k];
       if (lane == k) x = xk;
       if (lane < k) x -= M[lane + n * k] * xk;
     }
@@ -137,11 +149,12 @@ k_select(const Inst *__restrict__ insts, int slice_max) {
   double *A = sh;                          // r x slice_max, A[i*slice_max + c]
   double *nrm = A + 32 * slice_max;        // [2][slice_max] squared norms
   unsigned char *used = reinterpret_cast<unsigned char *>(nrm + 2 * slice_max);
-  __shared__ double v[32], col[32], M[32 * 32], rhs[32], bpart[32], lmax[2];
+  __shared__ double v[32], col[32], M[32 * 32], rhs[32], bpart[32];
+  __shared__ long long lmax[2], red_l[32];  // maxima as bit patterns
   __shared__ int sel[32];
-  __shared__ double red_d[32];
   __shared__ int red_i[32];
-  __shared__ double hh_s, gmax_s;
+  __shared__ double hh_s;
+  __shared__ long long thr_s;
   const double *W = I.W0;
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
   // column teams: T threads per column, rows i = m, m + T, ...
@@ -197,24 +210,35 @@ k_select(const Inst *__restrict__ insts, int slice_max) {
       if (c >= 0 && m == 0) nr[c] = used[c] ? -1.0 : (I.selection == 0 ? x : x * x);
     }
     __syncthreads();
-    double mx = -1.0;
-    for (int c = t; c < ns; c += blockDim.x) mx = fmax(mx, nr[c]);
-    mx = block_max(mx, red_d);
-    if (t == 0) lmax[par] = mx;
+    // maxima on the bit patterns (squared norms are >= 0, unused columns
+    // hold -1 and so a negative pattern): integer compares only
+    long long mx = -1;
+    for (int c = t; c < ns; c += blockDim.x) mx = max(mx, __double_as_longlong(nr[c]));
+    mx = warp_max(mx);
+    if (lane == 0) red_l[wid] = mx;
+    __syncthreads();
+    if (t == 0) {
+      long long x = -1;
+      for (int q = 0; q < nw; ++q) x = max(x, red_l[q]);
+      lmax[par] = x;
+    }
     cluster.sync();
     // (2) the same pivot in every CTA
     if (wid == 0) {
-      double x = lane < kCl ? cluster.map_shared_rank(lmax, lane)[par] : -1.0;
+      long long x = lane < kCl ? cluster.map_shared_rank(lmax, lane)[par] : -1;
       x = warp_max(x);
-      if (lane == 0) gmax_s = x;
+      if (lane == 0) {
+        const double g2 = x >= 0 ? __longlong_as_double(x) : -1.0;
+        thr_s = __double_as_longlong(g2 * ((1.0 - kTieRel) * (1.0 - kTieRel)));  // on squared norms
+      }
     }
     __syncthreads();
-    const double thr = gmax_s * ((1.0 - kTieRel) * (1.0 - kTieRel));  // on squared norms
+    const long long thr = thr_s;
     int best = 0x7fffffff;
     for (int k = t; k < K; k += blockDim.x) {
       const int o = k / slice;
       const double x = cluster.map_shared_rank(nrm, o)[par * slice_max + (k - o * slice)];
-      if (x >= 0.0 && x >= thr) best = min(best, k);
+      if (thr >= 0 && __double_as_longlong(x) >= thr) best = min(best, k);
     }
     for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(kFullMask, best, o));
     if (lane == 0) red_i[wid] = best;
@@ -234,14 +258,14 @@ k_select(const Inst *__restrict__ insts, int slice_max) {
     if (I.selection == 0) {
       if (t < r) col[t] = cluster.map_shared_rank(A, owner)[t * slice_max + pl];
       __syncthreads();
-      if (wid == 0) {  // Householder vector v of col[s..r), hh = 2 / v^T v
+      if (wid == 0) {  // Householder vector v of x = col[s..r), hh = 2 / v^T v
         const double ci = (lane >= s && lane < r) ? col[lane] : 0.0;
-        const double nrm_p = sqrt(warp_sum(ci * ci));
+        const double ss = warp_sum(ci * ci);
+        const double nrm_p = sqrt(ss);
         const double a = col[s] >= 0 ? -nrm_p : nrm_p;
-        const double vi = lane == s ? ci - a : ci;
-        const double vv = warp_sum(vi * vi);
-        v[lane] = vi;
-        if (lane == 0) hh_s = vv > 0.0 ? 2.0 / vv : 0.0;
+        v[lane] = lane == s ? ci - a : ci;
+        // v^T v = 2 (|x|^2 + |x_s| |x|)
+        if (lane == 0) hh_s = ss > 0.0 ? 1.0 / fma(fabs(col[s]), nrm_p, ss) : 0.0;
       }
       __syncthreads();
       const double hh = hh_s;
@@ -299,9 +323,14 @@ k_select(const Inst *__restrict__ insts, int slice_max) {
 
 // ------------------------------------------------------------------
 // One CholeskyQR pass on G = scale * sum_c part[c] (r x r, c over the
-// cluster partials): R upper triangular with R^T R = G (+ shift).  The
-// elimination keeps the unscaled pivot rows (C_ij -= C_pi C_pj / C_pp, one
-// barrier per pivot) and scales row p by 1/sqrt(C_pp) at the end.  Modes:
+// cluster partials): R upper triangular with R^T R = G (+ shift).
+// The elimination is division-free: with d the pivot of step p and 2^-e its
+// binary exponent, the trailing block becomes (d C_ij - C_pi C_pj) 2^-e,
+// i.e. the Schur complement of the usual elimination times a known scale
+// sigma (sigma_{p+1} = sigma_p d 2^-e, always in [1, 2^p)).  Only the final
+// normalisation R_pj = C_pj / sqrt(sigma_p d_p) divides (once per row, all
+// rows at once), which keeps the FP64 divide and square root off the
+// per-pivot chain.  Modes:
 //   1 first pass: unshifted Cholesky that also detects dependent columns
 //     (residual^2 < tau_dep |column|^2).  Dependent columns are marked in
 //     flag[2 + j] and counted in flag[1] (they are then replaced by
@@ -318,9 +347,10 @@ __global__ void __launch_bounds__(256) k_chol(const CholJob *__restrict__ jobs,
   const Inst &I = insts[blockIdx.x];
   if (*I.status != kOk) return;
   __shared__ double G[32 * 32], C[32 * 32];
-  __shared__ double dinv[32];
+  __shared__ double sig[33], thr_dep[33], thr_fail[33], rho[32];
   __shared__ int dep[32];
   __shared__ int ndep_s;
+  __shared__ double tr_s;
   const int r = J.r, t = threadIdx.x;
   int *flag = J.flag;
   const bool run = J.mode == 1 || J.mode == 2 || (J.mode == 3 && flag[0] != 0) ||
@@ -344,37 +374,48 @@ __global__ void __launch_bounds__(256) k_chol(const CholJob *__restrict__ jobs,
   }
   if (J.mode == 1 && t < 32) flag[2 + t] = 0;
   __syncthreads();
-  double tr = 0.0;
-  for (int i = 0; i < r; ++i) tr += G[i + r * i];
+  if (t < 32) {
+    const double x = warp_sum(t < r ? G[t + r * t] : 0.0);
+    if (t == 0) tr_s = x;
+  }
+  __syncthreads();
+  const double tr = tr_s;
   double shift = 0.0;
   bool shifted = false, failed = false;
   for (int attempt = 0; attempt < 8; ++attempt) {
+    const bool detect = J.mode == 1 && shift == 0.0;
     for (int e = t; e < r * r; e += blockDim.x) C[e] = G[e] + ((e % r == e / r) ? shift : 0.0);
     if (t < 32) dep[t] = 0;
-    if (t == 0) ndep_s = 0;
+    if (t == 0) {
+      ndep_s = 0;
+      sig[0] = 1.0;
+      thr_dep[0] = J.tau_dep * G[0];
+      thr_fail[0] = J.u * tr;
+    }
     __syncthreads();
-    if (t == 0) dinv[0] = 1.0 / C[0];
-    __syncthreads();
-    const bool detect = J.mode == 1 && shift == 0.0;
     failed = false;
     for (int p = 0; p < r; ++p) {
-      // the same decision in every thread (C_pp is final after the last barrier)
+      // the same decision in every thread, on the scaled pivot
       const double d = C[p + r * p];
-      const bool is_dep = detect && d <= J.tau_dep * G[p + r * p];
-      if (!is_dep && !(d > J.u * tr)) { failed = true; break; }
-      if (is_dep) {  // a dependent column: row p of R becomes e_p
-        if (t == 0) { dep[p] = 1; ++ndep_s; }
-        if (p + 1 < r && t == 0) dinv[p + 1] = 1.0 / C[(p + 1) + r * (p + 1)];
-        __syncthreads();
-        continue;
+      const bool is_dep = detect && d <= thr_dep[p];
+      if (!is_dep && !(d > thr_fail[p])) { failed = true; break; }
+      const double sc = is_dep ? 1.0 : inv_pow2_exponent(d);
+      if (t == 0) {  // scale and thresholds of the next step
+        const double s1 = is_dep ? sig[p] : sig[p] * (d * sc);
+        sig[p + 1] = s1;
+        if (p + 1 < r) {
+          thr_dep[p + 1] = J.tau_dep * G[(p + 1) * (r + 1)] * s1;
+          thr_fail[p + 1] = J.u * tr * s1;
+        }
+        if (is_dep) { dep[p] = 1; ++ndep_s; }
       }
-      const double inv = dinv[p];
-      for (int e = t; e < r * r; e += blockDim.x) {
-        const int i = e % r, j = e / r;
-        if (i > p && i <= j) {
-          const double x = C[i + r * j] - C[p + r * i] * inv * C[p + r * j];
-          C[i + r * j] = x;
-          if (i == p + 1 && j == p + 1) dinv[p + 1] = 1.0 / x;
+      if (!is_dep) {
+        for (int e = t; e < r * r; e += blockDim.x) {
+          const int i = e % r, j = e / r;
+          // both products rounded on their own (no fused multiply-add), so
+          // that exactly repeated columns cancel to an exact zero pivot
+          if (i > p && i <= j)
+            C[i + r * j] = __dmul_rn(__dsub_rn(__dmul_rn(d, C[i + r * j]), __dmul_rn(C[p + r * i], C[p + r * j])), sc);
         }
       }
       __syncthreads();
@@ -391,14 +432,14 @@ __global__ void __launch_bounds__(256) k_chol(const CholJob *__restrict__ jobs,
     __syncthreads();
   }
   if (shifted && t == 0) flag[0] = 1;
-  // R_pj = C_pj / sqrt(C_pp) (rows of dependent columns: e_p)
-  if (t < r) dinv[t] = dep[t] ? 0.0 : sqrt(dinv[t]);
+  // R_pj = C_pj / sqrt(sigma_p C_pp) (rows of dependent columns: e_p)
+  if (t < r) rho[t] = dep[t] ? 0.0 : 1.0 / sqrt(sig[t] * C[t * (r + 1)]);
   __syncthreads();
   for (int e = t; e < r * r; e += blockDim.x) {
     const int i = e % r, j = e / r;
     double x = 0.0;
     if (dep[i]) x = (i == j) ? 1.0 : 0.0;
-    else if (i <= j) x = C[e] * dinv[i];
+    else if (i <= j) x = C[e] * rho[i];
     J.R[e] = x;
   }
 }
@@ -493,12 +534,6 @@ __device__ void stage_ops(const Inst &I, double *sm) {
 }
 
 constexpr int kLsWarps = 4;
-
-// |x| as an integer that orders like |x| (non-negative doubles order like
-// their bit patterns); integer compares stay off the FP64 pipe.
-__device__ __forceinline__ long long abs_bits(double x) {
-  return __double_as_longlong(x) & 0x7fffffffffffffffll;
-}
 
 // step 7, per angle.  One warp per angle runs Gauss-Jordan elimination with
 // partial pivoting on [B_k | I] (lane = column, two columns per lane when

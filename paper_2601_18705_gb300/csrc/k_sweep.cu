@@ -12,10 +12,17 @@
 //     step t updates column u = t - i (an anti-diagonal wavefront); the value
 //     of the cell below arrives from lane i-1 by a warp shuffle, the value of
 //     the cell to the left stays in a register;
-//   * inputs of a 32x32 chunk are loaded with coalesced row loads into a
-//     per-warp shared-memory tile (source and 1/(sigma_t + ax + ay)), which
-//     the diagonal then reads without bank conflicts (row stride 32, the
-//     diagonal index 31 i + const hits distinct banks);
+//   * the inputs of each 32 x 32 chunk (lane = column) are prefetched into
+//     registers one chunk ahead and staged as (source, 1/(sigma_t + ax +
+//     ay)) in a per-warp ring of 64 diagonal slots: cell (row i, column u)
+//     goes to slot (u + i) mod 64, so at step t every lane reads slot
+//     t mod 64 (a compile-time offset inside an unrolled window of 32
+//     steps) and writes its result back there; rows of a slot are padded to
+//     33 entries, which keeps staging and stepping free of bank conflicts;
+//     a chunk's results are written out when its slots are reused;
+//   * only the first window and the last ones need per-lane masks; the
+//     others run a mask-free step of two loads, one shuffle, three FP
+//     operations and two stores;
 //   * the top row of a band is handed to the next band (another warp) through
 //     a shared-memory ring of row buffers, guarded by a per-band progress
 //     counter published every kSub steps; every wait is bounded in time.
@@ -45,24 +52,54 @@ struct SweepArgs {
   real *psi;          // N: output
 };
 
-struct SweepSmem {
-  void *tiles;    // NW warps x 2 x 32 x 32 real2
-  void *edge;     // (NW + 1) x nx_max real
-  int *prog;      // bands_max
-  int nx_max;
+constexpr int kRing = 64;    // diagonal slots per warp
+constexpr int kRingLd = 33;  // entries per slot (32 lanes, padded)
+
+// Edge rows (a band's top row for the next band) hold column u at index
+// u + kEdgePad; the padding absorbs the writes of columns -31..-1 and
+// nx..nx+31 that the mask-free steps produce, and the vector reads of
+// kSub columns past nx.
+constexpr int kEdgePad = 32;
+__host__ __device__ inline int edge_ld(int nx_max) { return (nx_max + 3) / 4 * 4 + 2 * kEdgePad; }
+
+template <typename real> struct Real4;
+template <> struct Real4<float> {
+  using type = float4;
+  static constexpr int kN = 4;
+  __device__ static void unpack(const volatile float4 &v, float *o) {
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  }
+};
+template <> struct Real4<double> {
+  using type = double2;
+  static constexpr int kN = 2;
+  __device__ static void unpack(const volatile double2 &v, double *o) {
+    o[0] = v.x; o[1] = v.y;
+  }
 };
 
-// Bounded spin of lane 0 until *flag >= need.  Returns false on timeout or
-// abort (the warp then leaves the unit).
+struct SweepSmem {
+  void *tiles;    // NW warps x kRing x kRingLd real2
+  void *edge;     // (NW + 1) x edge_ld(nx_max) real
+  int *prog;      // bands_max
+  int edge_ld;
+};
+
+// Bounded wait of lane 0 until *flag >= need.  The polls back off with
+// __nanosleep, so a waiting warp takes (almost) no issue slots from the
+// warps that are sweeping on the same scheduler.  Returns false on timeout
+// or abort (the warp then leaves the unit).
 __device__ __forceinline__ bool wait_progress(volatile int *flag, int need,
                                               volatile int *abort_flag) {
   bool ok = true;
   if ((threadIdx.x & 31) == 0) {
     if (*flag < need) {
       uint64_t t0 = global_ns();
-      unsigned spins = 0;
+      unsigned spins = 0, nap = 16;
       while (*flag < need) {
-        if ((++spins & 255u) == 0) {
+        __nanosleep(nap);
+        nap = min(nap * 2, 128u);
+        if ((++spins & 63u) == 0) {
           if (*abort_flag || global_ns() - t0 > kWaitNs) { ok = false; break; }
         }
       }
@@ -75,11 +112,20 @@ __device__ __forceinline__ bool wait_progress(volatile int *flag, int need,
 }
 
 // Raw inputs of one 32 x 32 chunk of a band, prefetched into registers
-// (lane = column) one chunk ahead of the wavefront so that the global-load
-// latency overlaps the sweep of the previous chunk.
-template <typename real>
-struct ChunkRegs {
-  real src[32], st[32];
+// (lane = column) one chunk ahead of the wavefront.  The loads use clamped,
+// always valid addresses and nothing consumes their values until the chunk
+// is staged, so their latency overlaps the sweep of the previous chunk.  In
+// FP32 the scalar-flux source is kept apart (added when staging); in FP64 it
+// is added at once to stay within the register budget.
+template <typename real> struct ChunkRegs;
+template <> struct ChunkRegs<float> {
+  static constexpr bool kRaw = true;
+  float src[32], sp[32], st[32];
+};
+template <> struct ChunkRegs<double> {
+  static constexpr bool kRaw = false;
+  double src[32], st[32];
+  double sp[1];
 };
 
 // 1 / x: IEEE division in FP64; in FP32 the hardware reciprocal (about one
@@ -87,41 +133,132 @@ struct ChunkRegs {
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 
-// Cell (sweep row vv, sweep column u) -> index iy * nx + ix; rows advance by
-// row_step (+-nx) from row0 (the cell of sweep row 0 in this column).
+// Cell of the band's first row in sweep column u (index iy * nx + ix); the
+// band's rows follow at multiples of row_step = +-nx.
+template <typename real>
+__device__ __forceinline__ int chunk_cell0(const SweepArgs<real> &A, int b, int u) {
+  const int ix = A.flipx ? A.nx - 1 - u : u;
+  return (A.flipy ? (A.ny - 1 - 32 * b) * A.nx : 32 * b * A.nx) + ix;
+}
+
 template <typename real>
 __device__ __forceinline__ void load_chunk(const SweepArgs<real> &A, int b, int k, ChunkRegs<real> &R) {
   const int lane = threadIdx.x & 31;
-  const int u = 32 * k + lane;
-  const bool col_ok = u < A.nx;
-  const int ix = A.flipx ? A.nx - 1 - u : u;
-  const int row_step = A.flipy ? -A.nx : A.nx;
-  const int c0 = (A.flipy ? (A.ny - 1 - 32 * b) * A.nx : 32 * b * A.nx) + ix;
-  const int rows = min(32, A.ny - 32 * b);
+  const int c0 = chunk_cell0(A, b, min(32 * k + lane, A.nx - 1));
+  const int rs = A.flipy ? -A.nx : A.nx;
+  const int last = min(32, A.ny - 32 * b) - 1;
+  const real *__restrict__ ps = A.src + c0;
+  const real *__restrict__ pt = A.sig_t + c0;
+  const real *__restrict__ pp = A.sphi ? A.sphi + c0 : nullptr;
 #pragma unroll
   for (int ii = 0; ii < 32; ++ii) {
-    const bool ok = col_ok && ii < rows;
-    const int c = ok ? c0 + ii * row_step : 0;
-    real s = A.src[c];
-    if (A.sphi) s += A.sphi[c];
-    R.src[ii] = ok ? s : real(0);
-    R.st[ii] = ok ? A.sig_t[c] : real(1);
+    const int off = min(ii, last) * rs;
+    R.src[ii] = ps[off];
+    R.st[ii] = pt[off];
+    if (ChunkRegs<real>::kRaw) {
+      if (pp) R.sp[ChunkRegs<real>::kRaw ? ii : 0] = pp[off];
+    } else if (pp) {
+      R.src[ii] += pp[off];
+    }
   }
 }
 
-// (source, 1 / (sigma_t + ax + ay)) of a prefetched chunk into a tile.
+// (source, 1 / (sigma_t + ax + ay)) of a prefetched chunk into its diagonal
+// slots: cell (row i, column u) -> slot (u + i) mod 64, entry i.  Cells
+// outside the mesh get a zero source and sigma_t = 1.
 template <typename real>
-__device__ __forceinline__ void store_chunk(const SweepArgs<real> &A, const ChunkRegs<real> &R,
-                                            typename Real2<real>::type *tile) {
+__device__ __forceinline__ void stage_chunk(const SweepArgs<real> &A, const ChunkRegs<real> &R, int b,
+                                            int k, typename Real2<real>::type *ring) {
   const int lane = threadIdx.x & 31;
   const real axy = A.ax + A.ay;
+  const int u = 32 * k + lane;
+  const bool col_ok = u < A.nx;
+  const int rows = min(32, A.ny - 32 * b);
+  typename Real2<real>::type *col = ring + (u & (kRing - 1)) * kRingLd;
+  typename Real2<real>::type *const wrap = ring + kRing * kRingLd;
 #pragma unroll
   for (int ii = 0; ii < 32; ++ii) {
+    const bool ok = col_ok && ii < rows;
+    real src = R.src[ii];
+    if (ChunkRegs<real>::kRaw && A.sphi) src += R.sp[ChunkRegs<real>::kRaw ? ii : 0];
     typename Real2<real>::type e;
-    e.x = R.src[ii];
-    e.y = recip(R.st[ii] + axy);
-    tile[ii * 32 + lane] = e;
+    e.x = ok ? src : real(0);
+    e.y = recip((ok ? R.st[ii] : real(1)) + axy);
+    col[ii] = e;
+    col += kRingLd;
+    if (col == wrap) col = ring;
   }
+}
+
+// results of chunk k (complete) from their diagonal slots to psi
+template <typename real>
+__device__ __forceinline__ void write_chunk(const SweepArgs<real> &A, int b, int k,
+                                            const typename Real2<real>::type *ring) {
+  const int lane = threadIdx.x & 31;
+  const int u = 32 * k + lane;
+  if (u >= A.nx) return;
+  real *__restrict__ out = A.psi + chunk_cell0(A, b, u);
+  const int rs = A.flipy ? -A.nx : A.nx;
+  const int rows = min(32, A.ny - 32 * b);
+  const typename Real2<real>::type *col = ring + (u & (kRing - 1)) * kRingLd;
+  const typename Real2<real>::type *const wrap = ring + kRing * kRingLd;
+#pragma unroll
+  for (int ii = 0; ii < 32; ++ii) {
+    if (ii < rows) out[ii * rs] = col[ii].x;
+    col += kRingLd;
+    if (col == wrap) col = ring;
+  }
+}
+
+// The 32 steps t = 32k + tau of window k (OFF = 32 (k mod 2): slot t mod 64
+// = OFF + tau).  Lane i updates column u = t - i.  FIRST (window 0): lanes
+// whose column is still negative keep their inflow value; in later windows
+// every column is >= 0, and columns >= nx only touch slots and edge entries
+// that nobody reads, so no lane needs a mask.
+template <typename real, int NW, int OFF, bool FIRST>
+__device__ __forceinline__ bool sweep_window(int b, int k, const SweepArgs<real> &A,
+                                             typename Real2<real>::type *mine, real &psi,
+                                             const real *edge_in, real *edge_out,
+                                             volatile int *prog, volatile int *abort_flag) {
+  const int lane = threadIdx.x & 31;
+  const int nx = A.nx;
+  const real ax = A.ax, ay = A.ay;
+#pragma unroll
+  for (int sb = 0; sb < 32; sb += kSub) {
+    const int t0 = 32 * k + sb;
+    if (b > 0 && t0 < nx) {
+      if (!wait_progress(prog + b - 1, min(nx, t0 + kSub), abort_flag)) return false;
+    }
+    // lane 0's lower neighbours (the previous band's top row) for the next
+    // kSub columns, read as vectors
+    real ed[kSub];
+    if (b > 0 && t0 < nx) {
+      const volatile typename Real4<real>::type *e4 =
+          reinterpret_cast<const volatile typename Real4<real>::type *>(edge_in + t0);
+#pragma unroll
+      for (int q = 0; q < kSub / Real4<real>::kN; ++q) Real4<real>::unpack(e4[q], ed + q * Real4<real>::kN);
+    } else {
+#pragma unroll
+      for (int s = 0; s < kSub; ++s) ed[s] = A.in_y;
+    }
+#pragma unroll
+    for (int s = 0; s < kSub; ++s) {
+      const int slot = (OFF + sb + s) * kRingLd;
+      const typename Real2<real>::type v = mine[slot];
+      real down = __shfl_up_sync(kFull, psi, 1);
+      if (lane == 0) down = ed[s];
+      real p = fmadd(ay, down, fmadd(ax, psi, v.x)) * v.y;
+      if (FIRST && t0 + s < lane) p = psi;
+      psi = p;
+      mine[slot].x = p;
+      if (lane == 31) edge_out[t0 + s - 31] = p;
+    }
+    if (lane == 31) {
+      __threadfence_block();
+      prog[b] = min(nx, max(0, t0 + kSub - 31));
+    }
+  }
+  return true;
 }
 
 // One band of 32 rows of one angle, swept by one warp.
@@ -131,76 +268,36 @@ __device__ bool sweep_band(int b, const SweepArgs<real> &A, const SweepSmem &S,
   using real2 = typename Real2<real>::type;
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
-  real2 *tiles = reinterpret_cast<real2 *>(S.tiles) + wid * 2048;
+  real2 *ring = reinterpret_cast<real2 *>(S.tiles) + wid * (kRing * kRingLd);
+  real2 *mine = ring + lane;
+  // edge rows: column u at index u + kEdgePad (columns -31 .. nx + 31 fit)
   real *edge = reinterpret_cast<real *>(S.edge);
-  real *edge_out = edge + (b % (NW + 1)) * S.nx_max;
-  volatile real *edge_in = edge + ((b + NW) % (NW + 1)) * S.nx_max;
+  real *edge_out = edge + (b % (NW + 1)) * S.edge_ld + kEdgePad;
+  const real *edge_in = edge + ((b + NW) % (NW + 1)) * S.edge_ld + kEdgePad;
   volatile int *prog = S.prog;
-  const int nx = A.nx, ny = A.ny;
-  const bool row_ok = 32 * b + lane < ny;
-  const bool top = lane == 31 && row_ok;
+  const int nx = A.nx;
   const int nch = (nx + 31) >> 5;
-  real psi_left = A.in_x, psi_prev = real(0);
+  real psi = A.in_x;  // this lane's last value: the left neighbour of its next cell
   ChunkRegs<real> R;
   load_chunk(A, b, 0, R);
-
   for (int k = 0; k <= nch; ++k) {
-    real2 *tk = tiles + (k & 1) * 1024;        // chunk k
-    real2 *tp = tiles + ((k + 1) & 1) * 1024;  // chunk k-1
-    if (k < nch) store_chunk(A, R, tk);
+    if (k >= 2) write_chunk(A, b, k - 2, ring);  // its slots are reused by chunk k
     __syncwarp();
-    if (k + 1 < nch) load_chunk(A, b, k + 1, R);  // in flight during the sweep below
-#pragma unroll 1
-    for (int tau = 0; tau < 32; tau += kSub) {
-      const int t0 = 32 * k + tau;
-      if (b > 0 && t0 < nx) {
-        if (!wait_progress(prog + b - 1, min(nx, t0 + kSub), abort_flag)) return false;
-      }
-      // operands of the next kSub steps, loaded before the dependent chain;
-      // step s of lane i touches column u = t0 + s - i, in chunk k or k-1
-      real2 ev[kSub];
-      real ed[kSub];
-      bool act[kSub];
-#pragma unroll
-      for (int s = 0; s < kSub; ++s) {
-        const int u = t0 + s - lane;
-        act[s] = row_ok && u >= 0 && u < nx;
-        const int tau_u = tau + s - lane;  // column inside chunk k (negative: chunk k-1)
-        real2 *slot = (tau_u >= 0 ? tk + tau_u : tp + 32 + tau_u) + lane * 32;
-        ev[s] = *slot;
-        ed[s] = (b > 0 && act[s]) ? edge_in[max(u, 0)] : A.in_y;
-      }
-#pragma unroll
-      for (int s = 0; s < kSub; ++s) {
-        real down = __shfl_up_sync(kFull, psi_prev, 1);
-        if (lane == 0) down = ed[s];
-        const real psi = (ev[s].x + A.ax * psi_left + A.ay * down) * ev[s].y;
-        psi_left = act[s] ? psi : psi_left;
-        psi_prev = act[s] ? psi : psi_prev;
-        const int tau_u = tau + s - lane;
-        if (act[s]) (tau_u >= 0 ? tk + tau_u : tp + 32 + tau_u)[lane * 32].x = psi;
-        if (top && act[s]) edge_out[t0 + s - 31] = psi;
-      }
-      if (top) {
-        __threadfence_block();
-        prog[b] = min(nx, max(0, t0 + kSub - 31));
-      }
-    }
+    if (k < nch) stage_chunk(A, R, b, k, ring);
     __syncwarp();
-    if (k >= 1) {  // chunk k-1 is complete: write it out
-      const int u = 32 * (k - 1) + lane;
-      if (u < nx) {
-        const int ix = A.flipx ? nx - 1 - u : u;
-        const int row_step = A.flipy ? -nx : nx;
-        const int c0 = (A.flipy ? (ny - 1 - 32 * b) * nx : 32 * b * nx) + ix;
-        const int rows = min(32, ny - 32 * b);
-#pragma unroll 8
-        for (int ii = 0; ii < 32; ++ii)
-          if (ii < rows) A.psi[c0 + ii * row_step] = tp[ii * 32 + lane].x;
-      }
-    }
-    __syncwarp();
+    if (k + 1 < nch) load_chunk(A, b, k + 1, R);  // in flight during the steps below
+    bool ok;
+    if (k == 0)
+      ok = sweep_window<real, NW, 0, true>(b, k, A, mine, psi, edge_in, edge_out, prog, abort_flag);
+    else if (k & 1)
+      ok = sweep_window<real, NW, 32, false>(b, k, A, mine, psi, edge_in, edge_out, prog, abort_flag);
+    else
+      ok = sweep_window<real, NW, 0, false>(b, k, A, mine, psi, edge_in, edge_out, prog, abort_flag);
+    if (!ok) return false;
   }
+  __syncwarp();
+  write_chunk(A, b, nch - 1, ring);
+  __syncwarp();
   return true;
 }
 
@@ -249,14 +346,15 @@ k_si(const Inst *__restrict__ insts, SiCtl ctl) {
   using real2 = typename Real2<real>::type;
   SweepSmem S;
   S.tiles = smem;
-  size_t off = (size_t)NW * 2048 * sizeof(real2);
+  size_t off = (size_t)NW * kRing * kRingLd * sizeof(real2);
   S.edge = smem + off;
-  off += (size_t)(NW + 1) * ctl.nx_max * sizeof(real);
+  off += (size_t)(NW + 1) * edge_ld(ctl.nx_max) * sizeof(real);
   S.prog = reinterpret_cast<int *>(smem + off);
   off += (size_t)ctl.bands_max * sizeof(int);
   int *active = reinterpret_cast<int *>(smem + off);
-  S.nx_max = ctl.nx_max;
+  S.edge_ld = edge_ld(ctl.nx_max);
   __shared__ int unit_s, n_active_s;
+  __shared__ real gam[kMaxRank];
   volatile int *abort_flag = ctl.abort_flag;
 
   for (int i = threadIdx.x; i < ctl.n_inst; i += blockDim.x)
@@ -297,26 +395,29 @@ k_si(const Inst *__restrict__ insts, SiCtl ctl) {
     for (int i = 0; i < ctl.n_inst; ++i) {
       if (!active[i]) continue;
       const Inst &I = insts[i];
+      const int N = I.N, r = I.r;
       const real *psi = as_c<real>(I.Psi);
       const real *ss4 = as_c<real>(I.ss4);
       const real *pold = as_c<real>((it & 1) ? I.phi1 : I.phi0);
       real *pnew = as<real>((it & 1) ? I.phi0 : I.phi1);
       real *sphi = as<real>(I.sphi);
-      const double *gamma = I.small + I.lay.gamma;
-      double dmax = 0.0, pmax = 0.0;
-      for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < I.N; c += gridDim.x * blockDim.x) {
+      __syncthreads();
+      if (threadIdx.x < r) gam[threadIdx.x] = real(I.small[I.lay.gamma + threadIdx.x]);
+      __syncthreads();
+      real dmax = real(0), pmax = real(0);  // |differences| and |phi| in the working precision
+      for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
         real acc = real(0);
-        for (int j = 0; j < I.r; ++j) acc += real(gamma[j]) * psi[(size_t)I.N * j + c];
+        for (int j = 0; j < r; ++j) acc = fmadd(gam[j], psi[(size_t)N * j + c], acc);
         pnew[c] = acc;
         sphi[c] = ss4[c] * acc;
-        dmax = fmax(dmax, fabs((double)acc - (double)pold[c]));
-        pmax = fmax(pmax, fabs((double)acc));
+        dmax = max(dmax, abs(acc - pold[c]));
+        pmax = max(pmax, abs(acc));
       }
       dmax = warp_max(dmax);
       pmax = warp_max(pmax);
       if ((threadIdx.x & 31) == 0) {
-        atomic_max_nonneg(I.conv + (it & 1) * 2 + 0, dmax);
-        atomic_max_nonneg(I.conv + (it & 1) * 2 + 1, pmax);
+        atomic_max_nonneg(I.conv + (it & 1) * 2 + 0, (double)dmax);
+        atomic_max_nonneg(I.conv + (it & 1) * 2 + 1, (double)pmax);
       }
     }
     if (!grid_barrier(ctl.bar, abort_flag)) break;
@@ -387,11 +488,11 @@ k_sweep_dirs(int nx, int ny, double hx, double hy, const double *dirs,
   using real2 = typename Real2<real>::type;
   SweepSmem S;
   S.tiles = smem;
-  size_t off = (size_t)NW * 2048 * sizeof(real2);
+  size_t off = (size_t)NW * kRing * kRingLd * sizeof(real2);
   S.edge = smem + off;
-  off += (size_t)(NW + 1) * nx_max * sizeof(real);
+  off += (size_t)(NW + 1) * edge_ld(nx_max) * sizeof(real);
   S.prog = reinterpret_cast<int *>(smem + off);
-  S.nx_max = nx_max;
+  S.edge_ld = edge_ld(nx_max);
   const int d = blockIdx.x;
   const double ox = dirs[2 * d], oy = dirs[2 * d + 1];
   SweepArgs<real> A;
@@ -423,7 +524,7 @@ template <typename real>
 size_t si_smem_bytes(int nx_max, int bands_max, int n_inst) {
   constexpr int NW = SweepCfg<real>::NW;
   using real2 = typename Real2<real>::type;
-  return (size_t)NW * 2048 * sizeof(real2) + (size_t)(NW + 1) * nx_max * sizeof(real) +
+  return (size_t)NW * kRing * kRingLd * sizeof(real2) + (size_t)(NW + 1) * edge_ld(nx_max) * sizeof(real) +
          (size_t)bands_max * sizeof(int) + (size_t)n_inst * sizeof(int);
 }
 
