@@ -129,6 +129,26 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- CPU
+
+def si_traffic(iters_per_launch):
+    """DRAM bytes (read + write) per k_si launch from the committed ncu capture
+    (profiles/k_si_traffic.json), scaled by this run's source iterations per
+    launch; None when the kernel sources changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_si_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        h = hashlib.sha256()
+        for src in rec["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+        if h.hexdigest() != rec["source_sha256"]:
+            return None
+        return rec["dram_bytes_per_si_iteration"] * iters_per_launch
+    except (OSError, KeyError, ValueError):
+        return None
+
 def oracle_rate(case, seconds: float, steps=None):
     """FP64 CPU oracle, single thread: (updates/s, steps run, seconds)."""
     import oracle
@@ -309,13 +329,14 @@ def run_gpu(args):
         return
 
     hbm, kind = peaks()
+    traffic = si_traffic(iters / max(si_launch, 1)) if args.workload == WORKLOAD else None
     r = case["r"]
     bytes_per_update = 4.0 + 16.0 / r  # fixed-source read + amortised per-cell terms (FP32)
     per_launch_ms = si_ms / max(si_launch, 1)
     per_launch_updates = updates / max(si_launch, 1)
     achieved = per_launch_updates * bytes_per_update / (per_launch_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None, "kernel": "k_si<float>",
+                "frac": achieved / hbm, "traffic": traffic, "kernel": "k_si<float>",
                 "peak_kind": kind, "bytes_per_update": bytes_per_update,
                 "avg_launch_ms": per_launch_ms}
     cpu = None
