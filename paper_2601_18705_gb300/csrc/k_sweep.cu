@@ -128,10 +128,16 @@ template <> struct ChunkRegs<double> {
   double sp[1];
 };
 
-// 1 / x: IEEE division in FP64; in FP32 the hardware reciprocal (about one
-// ulp), well inside the mixed-precision error budget.
+// 1 / x: IEEE division in FP64; in FP32 the approximate reciprocal of the
+// special-function unit (one instruction, relative error about 2^-23),
+// inside the mixed-precision error budget (x = sigma_t + ax + ay >= 1 is
+// never subnormal).
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
-__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ float recip(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
 // Cell of the band's first row in sweep column u (index iy * nx + ix); the
 // band's rows follow at multiples of row_step = +-nx.
@@ -141,72 +147,118 @@ __device__ __forceinline__ int chunk_cell0(const SweepArgs<real> &A, int b, int 
   return (A.flipy ? (A.ny - 1 - 32 * b) * A.nx : 32 * b * A.nx) + ix;
 }
 
-template <typename real>
-__device__ __forceinline__ void load_chunk(const SweepArgs<real> &A, int b, int k, ChunkRegs<real> &R) {
+// FULL: the chunk is whole (32 rows and 32 columns inside the mesh), so no
+// clamps or masks are needed; SP: a scalar-flux source is present.
+template <typename real, bool FULL, bool SP>
+__device__ __forceinline__ void load_chunk_t(const SweepArgs<real> &A, int b, int k, ChunkRegs<real> &R) {
   const int lane = threadIdx.x & 31;
-  const int c0 = chunk_cell0(A, b, min(32 * k + lane, A.nx - 1));
+  const int c0 = chunk_cell0(A, b, FULL ? 32 * k + lane : min(32 * k + lane, A.nx - 1));
   const int rs = A.flipy ? -A.nx : A.nx;
-  const int last = min(32, A.ny - 32 * b) - 1;
+  const int last = FULL ? 31 : min(32, A.ny - 32 * b) - 1;
   const real *__restrict__ ps = A.src + c0;
   const real *__restrict__ pt = A.sig_t + c0;
-  const real *__restrict__ pp = A.sphi ? A.sphi + c0 : nullptr;
+  const real *__restrict__ pp = SP ? A.sphi + c0 : nullptr;
 #pragma unroll
   for (int ii = 0; ii < 32; ++ii) {
-    const int off = min(ii, last) * rs;
+    const int off = (FULL ? ii : min(ii, last)) * rs;
     R.src[ii] = ps[off];
     R.st[ii] = pt[off];
-    if (ChunkRegs<real>::kRaw) {
-      if (pp) R.sp[ChunkRegs<real>::kRaw ? ii : 0] = pp[off];
-    } else if (pp) {
-      R.src[ii] += pp[off];
+    if (SP) {
+      if (ChunkRegs<real>::kRaw) R.sp[ChunkRegs<real>::kRaw ? ii : 0] = pp[off];
+      else R.src[ii] += pp[off];
     }
   }
 }
 
-// (source, 1 / (sigma_t + ax + ay)) of a prefetched chunk into its diagonal
-// slots: cell (row i, column u) -> slot (u + i) mod 64, entry i.  Cells
-// outside the mesh get a zero source and sigma_t = 1.
 template <typename real>
-__device__ __forceinline__ void stage_chunk(const SweepArgs<real> &A, const ChunkRegs<real> &R, int b,
-                                            int k, typename Real2<real>::type *ring) {
-  const int lane = threadIdx.x & 31;
-  const real axy = A.ax + A.ay;
-  const int u = 32 * k + lane;
-  const bool col_ok = u < A.nx;
-  const int rows = min(32, A.ny - 32 * b);
-  typename Real2<real>::type *col = ring + (u & (kRing - 1)) * kRingLd;
-  typename Real2<real>::type *const wrap = ring + kRing * kRingLd;
-#pragma unroll
-  for (int ii = 0; ii < 32; ++ii) {
-    const bool ok = col_ok && ii < rows;
-    real src = R.src[ii];
-    if (ChunkRegs<real>::kRaw && A.sphi) src += R.sp[ChunkRegs<real>::kRaw ? ii : 0];
-    typename Real2<real>::type e;
-    e.x = ok ? src : real(0);
-    e.y = recip((ok ? R.st[ii] : real(1)) + axy);
-    col[ii] = e;
-    col += kRingLd;
-    if (col == wrap) col = ring;
+__device__ __forceinline__ bool chunk_full(const SweepArgs<real> &A, int b, int k) {
+  return 32 * b + 32 <= A.ny && 32 * k + 32 <= A.nx;
+}
+
+template <typename real>
+__device__ __forceinline__ void load_chunk(const SweepArgs<real> &A, int b, int k, ChunkRegs<real> &R) {
+  const bool full = chunk_full(A, b, k);
+  if (A.sphi) {
+    if (full) load_chunk_t<real, true, true>(A, b, k, R);
+    else load_chunk_t<real, false, true>(A, b, k, R);
+  } else {
+    if (full) load_chunk_t<real, true, false>(A, b, k, R);
+    else load_chunk_t<real, false, false>(A, b, k, R);
   }
 }
 
+// Ring entry of (row ii, column u = 32k + lane): slot (u + ii) mod 64, entry
+// ii, i.e. ring + (32 PAR + lane) * 33 + 34 ii for PAR = k mod 2, minus one
+// ring length once 32 PAR + lane + ii reaches 64 (odd chunks only).
+template <int PAR>
+__device__ __forceinline__ int ring_entry(int lane, int ii) {
+  int e = (32 * PAR + lane) * kRingLd + (kRingLd + 1) * ii;
+  if (PAR == 1 && ii >= 32 - lane) e -= kRing * kRingLd;
+  return e;
+}
+
+// (source, 1 / (sigma_t + ax + ay)) of a prefetched chunk into its diagonal
+// slots.  Cells outside the mesh get a zero source and sigma_t = 1.
+template <typename real, bool FULL, bool SP, int PAR>
+__device__ __forceinline__ void stage_chunk_t(const SweepArgs<real> &A, const ChunkRegs<real> &R, int b,
+                                              int k, typename Real2<real>::type *ring) {
+  const int lane = threadIdx.x & 31;
+  const real axy = A.ax + A.ay;
+  const bool col_ok = FULL || 32 * k + lane < A.nx;
+  const int rows = FULL ? 32 : min(32, A.ny - 32 * b);
+#pragma unroll
+  for (int ii = 0; ii < 32; ++ii) {
+    const bool ok = FULL || (col_ok && ii < rows);
+    real src = R.src[ii];
+    if (SP && ChunkRegs<real>::kRaw) src += R.sp[ChunkRegs<real>::kRaw ? ii : 0];
+    typename Real2<real>::type e;
+    e.x = ok ? src : real(0);
+    e.y = recip((ok ? R.st[ii] : real(1)) + axy);
+    ring[ring_entry<PAR>(lane, ii)] = e;
+  }
+}
+
+template <typename real>
+__device__ __forceinline__ void stage_chunk(const SweepArgs<real> &A, const ChunkRegs<real> &R, int b,
+                                            int k, typename Real2<real>::type *ring) {
+  const bool full = chunk_full(A, b, k), sp = A.sphi != nullptr;
+#define DLR_STAGE(F, S)                                                 \
+  do {                                                                  \
+    if (k & 1) stage_chunk_t<real, F, S, 1>(A, R, b, k, ring);          \
+    else stage_chunk_t<real, F, S, 0>(A, R, b, k, ring);                \
+  } while (0)
+  if (full) {
+    if (sp) DLR_STAGE(true, true); else DLR_STAGE(true, false);
+  } else {
+    if (sp) DLR_STAGE(false, true); else DLR_STAGE(false, false);
+  }
+#undef DLR_STAGE
+}
+
 // results of chunk k (complete) from their diagonal slots to psi
+template <typename real, bool FULL, int PAR>
+__device__ __forceinline__ void write_chunk_t(const SweepArgs<real> &A, int b, int k,
+                                              const typename Real2<real>::type *ring) {
+  const int lane = threadIdx.x & 31;
+  const int u = 32 * k + lane;
+  if (!FULL && u >= A.nx) return;
+  real *__restrict__ out = A.psi + chunk_cell0(A, b, u);
+  const int rs = A.flipy ? -A.nx : A.nx;
+  const int rows = FULL ? 32 : min(32, A.ny - 32 * b);
+#pragma unroll
+  for (int ii = 0; ii < 32; ++ii)
+    if (FULL || ii < rows) out[ii * rs] = ring[ring_entry<PAR>(lane, ii)].x;
+}
+
 template <typename real>
 __device__ __forceinline__ void write_chunk(const SweepArgs<real> &A, int b, int k,
                                             const typename Real2<real>::type *ring) {
-  const int lane = threadIdx.x & 31;
-  const int u = 32 * k + lane;
-  if (u >= A.nx) return;
-  real *__restrict__ out = A.psi + chunk_cell0(A, b, u);
-  const int rs = A.flipy ? -A.nx : A.nx;
-  const int rows = min(32, A.ny - 32 * b);
-  const typename Real2<real>::type *col = ring + (u & (kRing - 1)) * kRingLd;
-  const typename Real2<real>::type *const wrap = ring + kRing * kRingLd;
-#pragma unroll
-  for (int ii = 0; ii < 32; ++ii) {
-    if (ii < rows) out[ii * rs] = col[ii].x;
-    col += kRingLd;
-    if (col == wrap) col = ring;
+  if (chunk_full(A, b, k)) {
+    if (k & 1) write_chunk_t<real, true, 1>(A, b, k, ring);
+    else write_chunk_t<real, true, 0>(A, b, k, ring);
+  } else {
+    if (k & 1) write_chunk_t<real, false, 1>(A, b, k, ring);
+    else write_chunk_t<real, false, 0>(A, b, k, ring);
   }
 }
 
