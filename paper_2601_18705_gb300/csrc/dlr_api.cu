@@ -38,6 +38,8 @@ template <typename rin, typename rout>
 cudaError_t launch_apply(const ApplyJob *, int, int, int, cudaStream_t);
 template <typename real> cudaError_t launch_project(const Inst *, int, int, int, cudaStream_t);
 cudaError_t prepare_dense(int);
+cudaError_t prepare_lside(int, int);
+cudaError_t launch_lside(const Inst *, int, int, int, cudaStream_t);
 int reduce_cluster_cap();
 cudaError_t launch_reduce(const ReduceJob *, int, int, cudaStream_t);
 template <typename real> cudaError_t launch_tupdate(const Inst *, int, int, int, cudaStream_t);
@@ -152,6 +154,7 @@ struct Batch {
   int nx_max = 0, bands_max = 0, si_grid = 0;
   SiCtl ctl{};
   int sel_slice_max = 1;      // most angles one CTA of the selection cluster owns
+  bool lside_fused = false;   // step 8 by the one-cluster kernel (pivoted-QR choice, K <= 1024)
   GramJob *g_psi1, *g_psire, *g_x, *g_x3, *g_l1, *g_lf, *g_w, *g_w3, *g_cross;
   FillJob *f_psi, *f_l;
   ApplyJob *a_psi, *a_x2, *a_x3, *a_l1, *a_w2, *a_w3, *a_wv, *a_cw, *a_cx;
@@ -841,6 +844,8 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   chain(upv(d_units, units.data(), sizeof(int2) * units.size()));
   // angle selection: one cluster of kCl CTAs per instance
   b->sel_slice_max = std::max(1, (b->maxK + kCl - 1) / kCl);
+  // step 8 in one cluster kernel when the angles fit its shared memory
+  b->lside_fused = b->svd_mode == 0 && b->maxK <= 1024;
   if (e != cudaSuccess) {
     destroy_batch(b);
     return fail(DLR_ECUDA, "batch table upload failed: %s", cudaGetErrorString(e));
@@ -853,7 +858,8 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   }
   b->si_grid = gmax;
   if ((e = prepare_small(b->sel_slice_max, b->maxK, b->rmax)) != cudaSuccess ||
-      (e = prepare_dense(b->rmax)) != cudaSuccess) {
+      (e = prepare_dense(b->rmax)) != cudaSuccess ||
+      (b->lside_fused && (e = prepare_lside(b->sel_slice_max, b->rmax)) != cudaSuccess)) {
     destroy_batch(b);
     return fail(DLR_ECUDA, "kernel attribute setup failed: %s", cudaGetErrorString(e));
   }
@@ -916,22 +922,26 @@ static int enqueue_post(Batch *b) {
   b->kcount += 2;  // three kernels
   // step 8: CholeskyQR of M = diag(sqrt w) L^T into Q (held in W0), S = M^T Q,
   // SVD of S, W0 <- diag(1/sqrt w) Q V
-  LK(launch_tsgram<double>(b->g_l1, n, b->pblmax, 1, st));
-  LK(launch_chol(b->c_l1, d, n, st));
-  LK(launch_fill<double>(b->f_l, n, b->maxK, st));
-  LK(launch_tsgram<double>(b->g_lf, n, b->pblmax, 1, st));
-  LK(launch_chol(b->c_l1b, d, n, st));
-  LK((launch_apply<double, double>(b->a_l1, n, b->maxK, b->rmax, st)));
-  LK(launch_tsgram<double>(b->g_w, n, b->pblmax, 0, st));
-  LK(launch_chol(b->c_l2, d, n, st));
-  LK((launch_apply<double, double>(b->a_w2, n, b->maxK, b->rmax, st)));
-  LK(launch_tsgram<double>(b->g_w3, n, b->pblmax, 0, st));
-  LK(launch_chol(b->c_l3, d, n, st));
-  LK((launch_apply<double, double>(b->a_w3, n, b->maxK, b->rmax, st)));
-  LK(launch_tsgram<double>(b->g_cross, n, b->pblmax, 1, st));
-  LK(launch_svd(d, n, b->svd_mode, st));
-  LK((launch_apply<double, double>(b->a_wv, n, b->maxK, b->rmax, st)));
-  if (b->svd_mode == 1) LK(launch_sign(d, n, b->maxK, st));
+  if (b->lside_fused) {
+    LK(launch_lside(d, n, b->sel_slice_max, b->rmax, st));
+  } else {
+    LK(launch_tsgram<double>(b->g_l1, n, b->pblmax, 1, st));
+    LK(launch_chol(b->c_l1, d, n, st));
+    LK(launch_fill<double>(b->f_l, n, b->maxK, st));
+    LK(launch_tsgram<double>(b->g_lf, n, b->pblmax, 1, st));
+    LK(launch_chol(b->c_l1b, d, n, st));
+    LK((launch_apply<double, double>(b->a_l1, n, b->maxK, b->rmax, st)));
+    LK(launch_tsgram<double>(b->g_w, n, b->pblmax, 0, st));
+    LK(launch_chol(b->c_l2, d, n, st));
+    LK((launch_apply<double, double>(b->a_w2, n, b->maxK, b->rmax, st)));
+    LK(launch_tsgram<double>(b->g_w3, n, b->pblmax, 0, st));
+    LK(launch_chol(b->c_l3, d, n, st));
+    LK((launch_apply<double, double>(b->a_w3, n, b->maxK, b->rmax, st)));
+    LK(launch_tsgram<double>(b->g_cross, n, b->pblmax, 1, st));
+    LK(launch_svd(d, n, b->svd_mode, st));
+    LK((launch_apply<double, double>(b->a_wv, n, b->maxK, b->rmax, st)));
+    if (b->svd_mode == 1) LK(launch_sign(d, n, b->maxK, st));
+  }
   // step 9
   LK(launch_tupdate<real>(d, n, b->maxN, b->rmax, st));
   return DLR_OK;

@@ -188,6 +188,17 @@ template <> struct Real2<double> { using type = double2; };
 __device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
 
+// Deterministic pseudo-random value in [-1, 1) from a 64-bit key (the
+// SplitMix64 finaliser); used for the orthonormal completion of dependent
+// columns.
+__device__ __forceinline__ double hash_uniform(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  x ^= x >> 31;
+  return (double)(x >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
 template <typename T>
 __device__ __forceinline__ T *as(void *p) { return reinterpret_cast<T *>(p); }
 template <typename T>

@@ -241,13 +241,6 @@ k_tsgram(const GramJob *__restrict__ jobs) {
 // ------------------------------------------------------------------
 // orthonormal completion: dependent columns replaced by pseudo-random ones
 // ------------------------------------------------------------------
-__device__ __forceinline__ double hash_uniform(unsigned long long x) {
-  x += 0x9E3779B97F4A7C15ull;
-  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
-  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
-  x ^= x >> 31;
-  return (double)(x >> 11) * (2.0 / 9007199254740992.0) - 1.0;
-}
 
 template <typename real>
 __global__ void __launch_bounds__(256) k_fill(const FillJob *__restrict__ jobs) {

@@ -16,6 +16,7 @@
 //   k_lstep_back   L_k = y_k + B_k^{-1} M_s Lbar / 4pi
 //   k_svd          step 8: S = M^T Q, one-sided Jacobi SVD S = U Sigma V^T
 //   k_sign         sign of each W column: its largest-magnitude entry > 0
+#include "chol_core.cuh"
 #include "dlr_internal.cuh"
 
 namespace dlr {
@@ -28,11 +29,6 @@ __device__ __forceinline__ long long abs_bits(double x) {
   return __double_as_longlong(x) & 0x7fffffffffffffffll;
 }
 
-// 2^-e for the binary exponent e of a normal x > 0 (x 2^-e in [1, 2))
-__device__ __forceinline__ double inv_pow2_exponent(double x) {
-  const int e = (int)((__double_as_longlong(x) >> 52) & 0x7ff) - 1023;
-  return __longlong_as_double((long long)(1023 - e) << 52);
-}
 
 // ------------------------------------------------------------------
 // Solve M x = b (n x n, column-major, n <= 32, in shared memory) by Gaussian
@@ -323,14 +319,8 @@ k_select(const Inst *__restrict__ insts, int slice_max) {
 
 // ------------------------------------------------------------------
 // One CholeskyQR pass on G = scale * sum_c part[c] (r x r, c over the
-// cluster partials): R upper triangular with R^T R = G (+ shift).
-// The elimination is division-free: with d the pivot of step p and 2^-e its
-// binary exponent, the trailing block becomes (d C_ij - C_pi C_pj) 2^-e,
-// i.e. the Schur complement of the usual elimination times a known scale
-// sigma (sigma_{p+1} = sigma_p d 2^-e, always in [1, 2^p)).  Only the final
-// normalisation R_pj = C_pj / sqrt(sigma_p d_p) divides (once per row, all
-// rows at once), which keeps the FP64 divide and square root off the
-// per-pivot chain.  Modes:
+// cluster partials): R upper triangular with R^T R = G (+ shift), by the
+// division-free elimination of chol_core.cuh.  Modes:
 //   1 first pass: unshifted Cholesky that also detects dependent columns
 //     (residual^2 < tau_dep |column|^2).  Dependent columns are marked in
 //     flag[2 + j] and counted in flag[1] (they are then replaced by
@@ -346,11 +336,8 @@ __global__ void __launch_bounds__(256) k_chol(const CholJob *__restrict__ jobs,
   const CholJob J = jobs[blockIdx.x];
   const Inst &I = insts[blockIdx.x];
   if (*I.status != kOk) return;
-  __shared__ double G[32 * 32], C[32 * 32];
-  __shared__ double sig[33], thr_dep[33], thr_fail[33], rho[32];
-  __shared__ int dep[32];
-  __shared__ int ndep_s;
-  __shared__ double tr_s;
+  __shared__ double G[32 * 32];
+  __shared__ CholScratch S;
   const int r = J.r, t = threadIdx.x;
   int *flag = J.flag;
   const bool run = J.mode == 1 || J.mode == 2 || (J.mode == 3 && flag[0] != 0) ||
@@ -361,12 +348,12 @@ __global__ void __launch_bounds__(256) k_chol(const CholJob *__restrict__ jobs,
     return;
   }
   for (int e = t; e < r * r; e += blockDim.x)
-    C[e] = J.scale * sum_partials(J.part, J.nblocks, (size_t)r * r, e);
+    S.C[e] = J.scale * sum_partials(J.part, J.nblocks, (size_t)r * r, e);
   __syncthreads();
   // symmetrise (both triangles hold the same sums up to rounding order)
   for (int e = t; e < r * r; e += blockDim.x) {
     const int i = e % r, j = e / r;
-    G[e] = (i == j) ? C[e] : 0.5 * (C[i + r * j] + C[j + r * i]);
+    G[e] = (i == j) ? S.C[e] : 0.5 * (S.C[i + r * j] + S.C[j + r * i]);
   }
   if (J.mode == 1 && t == 0) {
     flag[0] = 0;
@@ -374,74 +361,16 @@ __global__ void __launch_bounds__(256) k_chol(const CholJob *__restrict__ jobs,
   }
   if (J.mode == 1 && t < 32) flag[2 + t] = 0;
   __syncthreads();
-  if (t < 32) {
-    const double x = warp_sum(t < r ? G[t + r * t] : 0.0);
-    if (t == 0) tr_s = x;
-  }
-  __syncthreads();
-  const double tr = tr_s;
-  double shift = 0.0;
-  bool shifted = false, failed = false;
-  for (int attempt = 0; attempt < 8; ++attempt) {
-    const bool detect = J.mode == 1 && shift == 0.0;
-    for (int e = t; e < r * r; e += blockDim.x) C[e] = G[e] + ((e % r == e / r) ? shift : 0.0);
-    if (t < 32) dep[t] = 0;
-    if (t == 0) {
-      ndep_s = 0;
-      sig[0] = 1.0;
-      thr_dep[0] = J.tau_dep * G[0];
-      thr_fail[0] = J.u * tr;
-    }
-    __syncthreads();
-    failed = false;
-    for (int p = 0; p < r; ++p) {
-      // the same decision in every thread, on the scaled pivot
-      const double d = C[p + r * p];
-      const bool is_dep = detect && d <= thr_dep[p];
-      if (!is_dep && !(d > thr_fail[p])) { failed = true; break; }
-      const double sc = is_dep ? 1.0 : inv_pow2_exponent(d);
-      if (t == 0) {  // scale and thresholds of the next step
-        const double s1 = is_dep ? sig[p] : sig[p] * (d * sc);
-        sig[p + 1] = s1;
-        if (p + 1 < r) {
-          thr_dep[p + 1] = J.tau_dep * G[(p + 1) * (r + 1)] * s1;
-          thr_fail[p + 1] = J.u * tr * s1;
-        }
-        if (is_dep) { dep[p] = 1; ++ndep_s; }
-      }
-      if (!is_dep) {
-        for (int e = t; e < r * r; e += blockDim.x) {
-          const int i = e % r, j = e / r;
-          // both products rounded on their own (no fused multiply-add), so
-          // that exactly repeated columns cancel to an exact zero pivot
-          if (i > p && i <= j)
-            C[i + r * j] = __dmul_rn(__dsub_rn(__dmul_rn(d, C[i + r * j]), __dmul_rn(C[p + r * i], C[p + r * j])), sc);
-        }
-      }
-      __syncthreads();
-    }
-    if (detect && ndep_s > 0) {
-      // mark the dependent columns; the pass is redone after the fill
-      if (t == 0) flag[1] = ndep_s;
-      if (t < r) flag[2 + t] = dep[t];
-      return;
-    }
-    if (!failed) break;
-    shift = shift == 0.0 ? J.u * tr : shift * 100.0;
-    shifted = true;
-    __syncthreads();
+  int ndep;
+  bool shifted;
+  chol_core(G, r, J.mode == 1, J.u, J.tau_dep, J.R, S, &ndep, &shifted);
+  if (ndep > 0) {
+    // mark the dependent columns; the pass is redone after the fill
+    if (t == 0) flag[1] = ndep;
+    if (t < r) flag[2 + t] = S.dep[t];
+    return;
   }
   if (shifted && t == 0) flag[0] = 1;
-  // R_pj = C_pj / sqrt(sigma_p C_pp) (rows of dependent columns: e_p)
-  if (t < r) rho[t] = dep[t] ? 0.0 : 1.0 / sqrt(sig[t] * C[t * (r + 1)]);
-  __syncthreads();
-  for (int e = t; e < r * r; e += blockDim.x) {
-    const int i = e % r, j = e / r;
-    double x = 0.0;
-    if (dep[i]) x = (i == j) ? 1.0 : 0.0;
-    else if (i <= j) x = C[e] * rho[i];
-    J.R[e] = x;
-  }
 }
 
 // ------------------------------------------------------------------
