@@ -36,7 +36,16 @@ struct CholScratch {
   int dep[32];
   int ndep;
   double tr;
+  // upper-triangle entries (i, j), i <= j, ordered by i from r-1 down, so
+  // that the entries a pivot step updates (i > p) form a prefix
+  unsigned short tri[32 * 33 / 2];
 };
+
+// x > thr for thr >= 0, compared as integers (non-negative doubles order
+// like their bit patterns; a negative x has a negative pattern)
+__device__ __forceinline__ bool above(double x, double thr) {
+  return __double_as_longlong(x) > __double_as_longlong(thr);
+}
 
 __device__ __forceinline__ void chol_core(const double *G, int r, bool detect_first, double u, double tau, double *R,
                                           CholScratch &S, int *ndep_out, bool *shifted_out) {
@@ -45,6 +54,10 @@ __device__ __forceinline__ void chol_core(const double *G, int r, bool detect_fi
   if (t < 32) {
     const double x = warp_sum(t < r ? G[t + r * t] : 0.0);
     if (t == 0) S.tr = x;
+  }
+  for (int i = t; i < r; i += blockDim.x) {  // row i of the table: offset of rows r-1 .. i+1
+    const int above_rows = (r - 1 - i) * (r - i) / 2;  // entries of rows > i
+    for (int j = i; j < r; ++j) S.tri[above_rows + (j - i)] = (unsigned short)(i | (j << 8));
   }
   __syncthreads();
   const double tr = S.tr;
@@ -65,8 +78,8 @@ __device__ __forceinline__ void chol_core(const double *G, int r, bool detect_fi
     for (int p = 0; p < r; ++p) {
       // the same decision in every thread, on the scaled pivot
       const double d = C[p + r * p];
-      const bool is_dep = detect && d <= S.thr_dep[p];
-      if (!is_dep && !(d > S.thr_fail[p])) { failed = true; break; }
+      const bool is_dep = detect && !above(d, S.thr_dep[p]);
+      if (!is_dep && !above(d, S.thr_fail[p])) { failed = true; break; }
       const double sc = is_dep ? 1.0 : inv_pow2_exponent(d);
       if (t == 0) {  // scale and thresholds of the next step
         const double s1 = is_dep ? S.sig[p] : S.sig[p] * (d * sc);
@@ -78,10 +91,10 @@ __device__ __forceinline__ void chol_core(const double *G, int r, bool detect_fi
         if (is_dep) { S.dep[p] = 1; ++S.ndep; }
       }
       if (!is_dep) {
-        for (int e = t; e < r * r; e += blockDim.x) {
-          const int i = e % r, j = e / r;
-          if (i > p && i <= j)
-            C[i + r * j] = __dmul_rn(__dsub_rn(__dmul_rn(d, C[i + r * j]), __dmul_rn(C[p + r * i], C[p + r * j])), sc);
+        const int na = (r - 1 - p) * (r - p) / 2;  // entries with i > p
+        for (int e = t; e < na; e += blockDim.x) {
+          const int i = S.tri[e] & 0xff, j = S.tri[e] >> 8;
+          C[i + r * j] = __dmul_rn(__dsub_rn(__dmul_rn(d, C[i + r * j]), __dmul_rn(C[p + r * i], C[p + r * j])), sc);
         }
       }
       __syncthreads();

@@ -78,9 +78,11 @@ k_lside(const Inst *__restrict__ insts, int slice_max) {
     Q[e] = v;
   }
   __syncthreads();
-  // forward substitution teams: T threads per row (a power of two <= 32)
+  // forward substitution teams: T threads per row (a power of two <= 32),
+  // enough to give the four schedulers a warp each; a thread updates every
+  // T-th column, so each FP64 instruction has all its lanes busy
   int T = 1;
-  while (T < 32 && 2 * T * max(ns, 1) <= (int)blockDim.x) T *= 2;
+  while (T < 32 && 2 * T * max(ns, 1) <= 128) T *= 2;
   const int m = t & (T - 1), rows_per_pass = blockDim.x / T;
   bool shifted_any = false;
   for (int pass = 1; pass <= 3; ++pass) {
@@ -119,8 +121,7 @@ k_lside(const Inst *__restrict__ insts, int slice_max) {
         }
         x = __shfl_sync(0xffffffffu, x, (lane & ~(T - 1)) + (j & (T - 1)));
         if (own)
-          for (int k = j + 1; k < r; ++k)
-            if ((k & (T - 1)) == m) row[k] -= x * R[j + r * k];
+          for (int k = j + 1 + ((m - j - 1) & (T - 1)); k < r; k += T) row[k] -= x * R[j + r * k];
       }
     }
     __syncthreads();
