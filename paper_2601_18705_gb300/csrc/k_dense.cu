@@ -367,8 +367,6 @@ k_project(const Inst *__restrict__ insts) {
   const real *__restrict__ qv = as_c<real>(I.q);
   double *const partials = I.partials;
   const int per = (N + nblk - 1) / nblk;
-  // rounds per FP32 partial: about 64 cells per thread before the FP64 add
-  const int flush_every = max(1, 64 * ngroup / GP);
   const int c0 = min(N, (int)blockIdx.x * per), c1 = min(N, c0 + per);
   const int nround = (c1 - c0 + GP - 1) / GP;
   // raw loads from clamped addresses (masks applied when staging), as in
@@ -394,12 +392,16 @@ k_project(const Inst *__restrict__ insts) {
       pv[2] = qv[c];
     }
   };
-  real sm[24], sv[16];
+  // three levels of sums in the working precision (a round, up to eight
+  // rounds, all rounds), converted to FP64 once at the end: the FP64 pipe
+  // stays out of the loop, and no FP32 sum runs over more than about 64
+  // terms
+  real sm[24], sv[16], m2[24], v2[16], m3[24], v3[16];
   double am[24], av[16];
 #pragma unroll
-  for (int e = 0; e < 24; ++e) { sm[e] = real(0); am[e] = 0.0; }
+  for (int e = 0; e < 24; ++e) { sm[e] = real(0); m2[e] = real(0); m3[e] = real(0); }
 #pragma unroll
-  for (int e = 0; e < 16; ++e) { sv[e] = real(0); av[e] = 0.0; }
+  for (int e = 0; e < 16; ++e) { sv[e] = real(0); v2[e] = real(0); v3[e] = real(0); }
   if (nround > 0) prefetch(0);
   for (int rd = 0; rd < nround; ++rd) {
     __syncthreads();
@@ -495,20 +497,24 @@ k_project(const Inst *__restrict__ insts) {
           }
         }
       }
-      if (sizeof(real) == 4 && ((rd + 1) % flush_every == 0 || rd + 1 == nround)) {
+      if (sizeof(real) == 4) {
 #pragma unroll
-        for (int e = 0; e < 24; ++e) { am[e] += (double)sm[e]; sm[e] = real(0); }
+        for (int e = 0; e < 24; ++e) { m2[e] += sm[e]; sm[e] = real(0); }
 #pragma unroll
-        for (int e = 0; e < 16; ++e) { av[e] += (double)sv[e]; sv[e] = real(0); }
+        for (int e = 0; e < 16; ++e) { v2[e] += sv[e]; sv[e] = real(0); }
+        if ((rd + 1) % 8 == 0) {
+#pragma unroll
+          for (int e = 0; e < 24; ++e) { m3[e] += m2[e]; m2[e] = real(0); }
+#pragma unroll
+          for (int e = 0; e < 16; ++e) { v3[e] += v2[e]; v2[e] = real(0); }
+        }
       }
     }
   }
-  if (sizeof(real) != 4) {
 #pragma unroll
-    for (int e = 0; e < 24; ++e) am[e] = (double)sm[e];
+  for (int e = 0; e < 24; ++e) am[e] = (double)sm[e] + ((double)m2[e] + (double)m3[e]);
 #pragma unroll
-    for (int e = 0; e < 16; ++e) av[e] = (double)sv[e];
-  }
+  for (int e = 0; e < 16; ++e) av[e] = (double)sv[e] + ((double)v2[e] + (double)v3[e]);
   // groups -> CTA partial in a fixed order, one output slot at a time
   double *buf = reinterpret_cast<double *>(dyn);
   double *part_s = buf + kTB * 16;

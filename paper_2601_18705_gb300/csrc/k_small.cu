@@ -465,17 +465,20 @@ __device__ void stage_ops(const Inst &I, double *sm) {
 constexpr int kLsWarps = 4;
 
 // step 7, per angle.  One warp per angle runs Gauss-Jordan elimination with
-// partial pivoting on [B_k | I] (lane = column, two columns per lane when
-// RB = 32; B_k padded to RB x RB with an identity block).  The identity half
-// ends as B_k^{-1}: it is kept in lu for the last part of the L-step, y_k =
-// B_k^{-1} Q_k goes to L, and the CTA accumulates sum w_k B_k^{-1} and
-// sum w_k y_k (the C-bar device of Section 3.3).  CTA sums are added over
-// the cluster through distributed shared memory; cluster c writes its
-// partial (r^2 + r doubles) to partials + c*(r^2 + r).
+// partial pivoting on [B_k | I] (B_k padded to RB x RB with an identity
+// block).  The 2 RB columns live in the warp's shared memory (column c at
+// cols + c (RB + 1)); lane l updates columns l and l + 32, so every FP64
+// instruction keeps the lanes busy, and the pivot steps form a run-time loop
+// over an unrolled row update (small code, no instruction-cache misses).
+// The identity half ends as B_k^{-1}: it is kept in lu for the last part of
+// the L-step, y_k = B_k^{-1} Q_k goes to L, and the CTA accumulates
+// sum w_k B_k^{-1} and sum w_k y_k (the C-bar device of Section 3.3).  CTA
+// sums are added over the cluster through distributed shared memory;
+// cluster c writes its partial (r^2 + r doubles) to partials + c*(r^2 + r).
 template <int RB>
 __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kLsWarps * 32)
 k_lstep_angle(const Inst *__restrict__ insts) {
-  constexpr int CPL = RB == 32 ? 2 : 1;  // columns per lane
+  constexpr int NC = 2 * RB, LDC = RB + 1;
   const Inst &I = insts[blockIdx.y];
   const int nblk = I.lstep_blocks;
   if ((int)blockIdx.x >= nblk) return;  // whole clusters (nblk is a multiple of kCl)
@@ -485,78 +488,70 @@ k_lstep_angle(const Inst *__restrict__ insts) {
   const int r = I.r, K = I.K, rq = r * r + r;
   double *sm = sh;                              // staged operators, 6 r^2 + 5 r
   double *acc = sm + 6 * r * r + 5 * r;         // kLsWarps x (r^2 + r)
-  double *binv = acc + kLsWarps * rq;           // kLsWarps x r^2
-  double *part_s = binv + kLsWarps * r * r;     // r^2 + r
+  double *colsw = acc + kLsWarps * rq;          // kLsWarps x NC x LDC
+  double *part_s = colsw + kLsWarps * NC * LDC; // r^2 + r
   stage_ops(I, sm);
   for (int e = threadIdx.x; e < kLsWarps * rq; e += blockDim.x) acc[e] = 0.0;
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  double *myacc = acc + wid * rq, *myb = binv + wid * r * r;
+  double *myacc = acc + wid * rq;
+  double *cols = colsw + wid * NC * LDC;
   const double *Mt = sm + 4 * r * r;
   const int gw = blockIdx.x * kLsWarps + wid, nwarps = nblk * kLsWarps;
   for (int k = gw; active && k < K; k += nwarps) {
     const AngleOps o = angle_ops(I, sm, k);
-    double m[CPL][RB];
-#pragma unroll
-    for (int s = 0; s < CPL; ++s) {
-      const int c = lane + 32 * s;
+    for (int c = lane; c < NC; c += 32) {
 #pragma unroll
       for (int i = 0; i < RB; ++i) {
-        double v = 0.0;
+        double v;
         if (c < RB) {
           if (c < r && i < r) v = o.aox * o.Ax[i + r * c] + o.aoy * o.Ay[i + r * c] + Mt[i + r * c];
           else v = (i == c) ? 1.0 : 0.0;
-        } else if (c < 2 * RB) {
+        } else {
           v = (i == c - RB) ? 1.0 : 0.0;
         }
-        m[s][i] = v;
+        cols[c * LDC + i] = v;
       }
     }
+    __syncwarp();
     bool singular = false;
-#pragma unroll
     for (int p = 0; p < RB; ++p) {
-      int pr = p;
-      if (lane == p) {  // column p: set 0 of lane p
-        long long best = -1;
-#pragma unroll
-        for (int i = p; i < RB; ++i) {
-          const long long a = abs_bits(m[0][i]);
-          if (a > best) { best = a; pr = i; }
+      // pivot row: the largest |B_ip|, i >= p (integer compares, lowest row on ties)
+      long long best = (lane >= p && lane < RB) ? abs_bits(cols[p * LDC + lane]) : -1;
+      int pr = lane;
+      for (int off = 16; off > 0; off >>= 1) {
+        const long long b2 = __shfl_xor_sync(kFullMask, best, off);
+        const int r2 = __shfl_xor_sync(kFullMask, pr, off);
+        if (b2 > best || (b2 == best && r2 < pr)) { best = b2; pr = r2; }
+      }
+      if (best <= 0) { singular = true; break; }
+      if (pr != p)
+        for (int c = lane; c < NC; c += 32) {
+          const double x = cols[c * LDC + p];
+          cols[c * LDC + p] = cols[c * LDC + pr];
+          cols[c * LDC + pr] = x;
         }
-        if (best == 0) pr = -1;
+      __syncwarp();
+      const double inv = 1.0 / cols[p * LDC + p];
+      // row p scaled, the other rows eliminated; column p itself is not
+      // needed any more and is left as it is
+      for (int c = lane; c < NC; c += 32) {
+        if (c == p) continue;
+        double *col = cols + c * LDC;
+        const double x = col[p] * inv;
+#pragma unroll
+        for (int i = 0; i < RB; ++i)
+          if (i != p) col[i] -= cols[p * LDC + i] * x;
+        col[p] = x;
       }
-      pr = __shfl_sync(kFullMask, pr, p);
-      if (pr < 0) { singular = true; break; }
-      if (pr != p) {
-#pragma unroll
-        for (int s = 0; s < CPL; ++s)
-#pragma unroll
-          for (int i = p + 1; i < RB; ++i)
-            if (i == pr) { const double x = m[s][p]; m[s][p] = m[s][i]; m[s][i] = x; }
-      }
-      const double inv = 1.0 / __shfl_sync(kFullMask, m[0][p], p);
-#pragma unroll
-      for (int s = 0; s < CPL; ++s) m[s][p] *= inv;
-#pragma unroll
-      for (int i = 0; i < RB; ++i) {
-        if (i == p) continue;
-        const double f = __shfl_sync(kFullMask, m[0][i], p);  // before lane p updates it
-#pragma unroll
-        for (int s = 0; s < CPL; ++s) m[s][i] -= f * m[s][p];
-      }
+      __syncwarp();
     }
     if (singular) {
       if (lane == 0) set_status(I.status, kESingular);
       break;
     }
-    // B_k^{-1} column j: lane RB + j (RB <= 16) or the second column of lane j
-    const int j = RB <= 16 ? lane - RB : lane;
-    if (j >= 0 && j < r) {
-#pragma unroll
-      for (int i = 0; i < RB; ++i)
-        if (i < r) myb[i + r * j] = m[CPL - 1][i];
-    }
-    __syncwarp();
+    // B_k^{-1} column j is cols column RB + j
+    const double *binv = cols + RB * LDC;
     const double qk = lane < r ? angle_q(I, sm, o, k, lane) : 0.0;
     double y0 = 0.0, y1 = 0.0;
 #pragma unroll
@@ -564,7 +559,7 @@ k_lstep_angle(const Inst *__restrict__ insts) {
       if (jj < r) {
         const double qj = __shfl_sync(kFullMask, qk, jj);
         if (lane < r) {
-          const double t = myb[lane + r * jj] * qj;
+          const double t = binv[jj * LDC + lane] * qj;
           if (jj & 1) y1 += t; else y0 += t;
         }
       }
@@ -574,10 +569,10 @@ k_lstep_angle(const Inst *__restrict__ insts) {
       const double y = y0 + y1;
       I.L[(size_t)r * k + lane] = y;
       myacc[r * r + lane] += wk * y;
-      for (int jj = 0; jj < r; ++jj) myacc[lane + r * jj] += wk * myb[lane + r * jj];
+      for (int jj = 0; jj < r; ++jj) myacc[lane + r * jj] += wk * binv[jj * LDC + lane];
     }
     double *B = I.lu + (size_t)k * r * r;
-    for (int e = lane; e < r * r; e += 32) B[e] = myb[e];
+    for (int e = lane; e < r * r; e += 32) B[e] = binv[(e / r) * LDC + (e % r)];
     __syncwarp();
   }
   __syncthreads();
@@ -818,7 +813,9 @@ static size_t select_smem(int slice_max) {
 }
 static int rank_bucket(int r) { return r <= 8 ? 8 : r <= 16 ? 16 : 32; }
 size_t lstep_angle_smem(int r) {
-  return (size_t)(6 * r * r + 5 * r + kLsWarps * (r * r + r) + kLsWarps * r * r + r * r + r) * sizeof(double);
+  const int RB = rank_bucket(r);
+  return (size_t)(6 * r * r + 5 * r + kLsWarps * (r * r + r) + kLsWarps * 2 * RB * (RB + 1) + r * r + r) *
+         sizeof(double);
 }
 
 cudaError_t prepare_small(int slice_max, int maxK, int rmax) {
