@@ -204,6 +204,30 @@ __device__ __forceinline__ T *as(void *p) { return reinterpret_cast<T *>(p); }
 template <typename T>
 __device__ __forceinline__ const T *as_c(const void *p) { return reinterpret_cast<const T *>(p); }
 
+// Programmatic dependent launch (launch_pdl): a kernel may be scheduled while
+// its predecessor in the stream (or graph) is still running, which hides the
+// launch gap between the many short kernels of a step.  Every such kernel
+// calls pdl_wait() before it reads anything a predecessor writes, and
+// pdl_trigger() to let its own successor be scheduled.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // First error wins; later ones are dropped.
 __device__ __forceinline__ void set_status(int *status, int code) {
   atomicCAS(status, 0, code);

@@ -28,6 +28,8 @@ constexpr int kTB = 256;      // threads per block of the reduction kernels
 // ------------------------------------------------------------------
 template <typename real, int RB>
 __global__ void __launch_bounds__(256) k_coeff_recon(const Inst *__restrict__ insts) {
+  pdl_wait();
+  pdl_trigger();
   const Inst &I = insts[blockIdx.y];
   __shared__ real C0s[RB * RB];
   __shared__ real gam[RB];
@@ -102,6 +104,8 @@ constexpr int gram_smem_bytes() {
 template <typename real, int LAY>
 __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kTB)
 k_tsgram(const GramJob *__restrict__ jobs) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int GR = GramCfg<real>::GR, LD = GR + 4;
   constexpr int PF = GR * 32 / kTB;  // prefetched elements per thread and matrix
   const GramJob J = jobs[blockIdx.y];
@@ -244,6 +248,8 @@ k_tsgram(const GramJob *__restrict__ jobs) {
 
 template <typename real>
 __global__ void __launch_bounds__(256) k_fill(const FillJob *__restrict__ jobs) {
+  pdl_wait();
+  pdl_trigger();
   const FillJob J = jobs[blockIdx.y];
   const int nfill = J.flag[1];
   if (!J.src && nfill == 0) return;
@@ -264,6 +270,8 @@ __global__ void __launch_bounds__(256) k_fill(const FillJob *__restrict__ jobs) 
 
 template <typename rin, typename rout, int RB>
 __global__ void __launch_bounds__(128) k_apply(const ApplyJob *__restrict__ jobs) {
+  pdl_wait();
+  pdl_trigger();
   const ApplyJob J = jobs[blockIdx.y];
   if (J.run_if && *J.run_if == 0) return;
   __shared__ rout Ts[RB * RB];
@@ -342,6 +350,8 @@ inline int proj_smem_bytes(int r, int rs) {
 template <typename real>
 __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kTB)
 k_project(const Inst *__restrict__ insts) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int GP = ProjCfg<real>::GP, LD = GP + 4;
   constexpr int PF = GP * 32 / kTB;
   const Inst &I = insts[blockIdx.y];
@@ -564,6 +574,8 @@ k_project(const Inst *__restrict__ insts) {
 
 // Sum of per-block partials: out[e] = scale * sum_b part[b*stride + e].
 __global__ void __launch_bounds__(256) k_reduce(const ReduceJob *__restrict__ jobs) {
+  pdl_wait();
+  pdl_trigger();
   const ReduceJob J = jobs[blockIdx.y];
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= J.count) return;
@@ -576,6 +588,8 @@ __global__ void __launch_bounds__(256) k_reduce(const ReduceJob *__restrict__ jo
 // ------------------------------------------------------------------
 template <typename real, int RB>
 __global__ void __launch_bounds__(128) k_tupdate(const Inst *__restrict__ insts) {
+  pdl_wait();
+  pdl_trigger();
   const Inst &I = insts[blockIdx.y];
   __shared__ real Us[RB * RB];
   __shared__ real vp[RB];
@@ -623,39 +637,38 @@ __global__ void __launch_bounds__(128) k_tupdate(const Inst *__restrict__ insts)
 template <typename real>
 cudaError_t launch_coeff_recon(const Inst *d, int n, int maxN, int r, cudaStream_t st) {
   dim3 g((maxN + 255) / 256, n);
-#define L_(RB) (k_coeff_recon<real, RB><<<g, 256, 0, st>>>(d), 0)
+#define L_(RB) (e = launch_pdl(k_coeff_recon<real, RB>, g, dim3(256), 0, st, d))
+  cudaError_t e = cudaSuccess;
   DLR_RB_DISPATCH(r, L_);
 #undef L_
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // layout: the (common) layout of the batch's matrices
 template <typename real>
 cudaError_t launch_tsgram(const GramJob *d_jobs, int n, int maxblocks, int layout, cudaStream_t st) {
-  if (layout == 0) k_tsgram<real, 0><<<dim3(maxblocks, n), kTB, 0, st>>>(d_jobs);
-  else k_tsgram<real, 1><<<dim3(maxblocks, n), kTB, 0, st>>>(d_jobs);
-  return cudaGetLastError();
+  if (layout == 0) return launch_pdl(k_tsgram<real, 0>, dim3(maxblocks, n), dim3(kTB), 0, st, d_jobs);
+  return launch_pdl(k_tsgram<real, 1>, dim3(maxblocks, n), dim3(kTB), 0, st, d_jobs);
 }
 
 template <typename real>
 cudaError_t launch_fill(const FillJob *d_jobs, int n, int maxm, cudaStream_t st) {
-  k_fill<real><<<dim3((maxm + 255) / 256, n), 256, 0, st>>>(d_jobs);
-  return cudaGetLastError();
+  return launch_pdl(k_fill<real>, dim3((maxm + 255) / 256, n), dim3(256), 0, st, d_jobs);
 }
 
 template <typename rin, typename rout>
 cudaError_t launch_apply(const ApplyJob *d_jobs, int n, int maxm, int r, cudaStream_t st) {
   dim3 g((maxm + 127) / 128, n);
-#define L_(RB) (k_apply<rin, rout, RB><<<g, 128, 0, st>>>(d_jobs), 0)
+#define L_(RB) (e = launch_pdl(k_apply<rin, rout, RB>, g, dim3(128), 0, st, d_jobs))
+  cudaError_t e = cudaSuccess;
   DLR_RB_DISPATCH(r, L_);
 #undef L_
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <typename real>
 cudaError_t launch_project(const Inst *d, int n, int maxblocks, int rmax, cudaStream_t st) {
-  k_project<real><<<dim3(maxblocks, n), kTB, proj_smem_bytes(rmax, sizeof(real)), st>>>(d);
-  return cudaGetLastError();
+  return launch_pdl(k_project<real>, dim3(maxblocks, n), dim3(kTB), proj_smem_bytes(rmax, sizeof(real)), st, d);
 }
 
 cudaError_t prepare_dense(int rmax);
@@ -703,17 +716,17 @@ cudaError_t prepare_dense(int rmax) {
 }
 
 cudaError_t launch_reduce(const ReduceJob *d_jobs, int n, int maxcount, cudaStream_t st) {
-  k_reduce<<<dim3((maxcount + 255) / 256, n), 256, 0, st>>>(d_jobs);
-  return cudaGetLastError();
+  return launch_pdl(k_reduce, dim3((maxcount + 255) / 256, n), dim3(256), 0, st, d_jobs);
 }
 
 template <typename real>
 cudaError_t launch_tupdate(const Inst *d, int n, int maxN, int r, cudaStream_t st) {
   dim3 g((maxN + 127) / 128, n);
-#define L_(RB) (k_tupdate<real, RB><<<g, 128, 0, st>>>(d), 0)
+#define L_(RB) (e = launch_pdl(k_tupdate<real, RB>, g, dim3(128), 0, st, d))
+  cudaError_t e = cudaSuccess;
   DLR_RB_DISPATCH(r, L_);
 #undef L_
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template cudaError_t launch_coeff_recon<float>(const Inst *, int, int, int, cudaStream_t);

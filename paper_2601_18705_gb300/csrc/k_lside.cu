@@ -54,6 +54,8 @@ __device__ __forceinline__ void local_gram(const double *A, const double *B, int
 
 __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(256)
 k_lside(const Inst *__restrict__ insts, int slice_max) {
+  pdl_wait();
+  pdl_trigger();
   cg::cluster_group cl = cg::this_cluster();
   const int g = (int)cl.block_rank();
   const Inst &I = insts[blockIdx.x / kCl];
@@ -160,8 +162,7 @@ cudaError_t prepare_lside(int slice_max, int rmax) {
 }
 
 cudaError_t launch_lside(const Inst *d, int n, int slice_max, int rmax, cudaStream_t st) {
-  k_lside<<<n * kCl, 256, lside_smem_bytes(slice_max, rmax), st>>>(d, slice_max);
-  return cudaGetLastError();
+  return launch_pdl(k_lside, dim3(n * kCl), dim3(256), lside_smem_bytes(slice_max, rmax), st, d, slice_max);
 }
 
 }  // namespace dlr

@@ -134,6 +134,8 @@ __device__ int block_argmax_tie(const double *val, int n) {
 // ------------------------------------------------------------------
 __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(256)
 k_select(const Inst *__restrict__ insts, int slice_max) {
+  pdl_wait();
+  pdl_trigger();
   cg::cluster_group cluster = cg::this_cluster();
   const int g = (int)cluster.block_rank();
   const Inst &I = insts[blockIdx.x / kCl];
@@ -333,6 +335,8 @@ k_select(const Inst *__restrict__ insts, int slice_max) {
 // ------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_chol(const CholJob *__restrict__ jobs,
                                               const Inst *__restrict__ insts) {
+  pdl_wait();
+  pdl_trigger();
   const CholJob J = jobs[blockIdx.x];
   const Inst &I = insts[blockIdx.x];
   if (*I.status != kOk) return;
@@ -377,6 +381,8 @@ __global__ void __launch_bounds__(256) k_chol(const CholJob *__restrict__ jobs,
 // step 7 operators from the reduced sums (unscaled) in small[G .. vec]
 // ------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_proj_post(const Inst *__restrict__ insts) {
+  pdl_wait();
+  pdl_trigger();
   const Inst &I = insts[blockIdx.x];
   if (*I.status != kOk) return;
   const int r = I.r;
@@ -478,6 +484,8 @@ constexpr int kLsWarps = 4;
 template <int RB>
 __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kLsWarps * 32)
 k_lstep_angle(const Inst *__restrict__ insts) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int NC = 2 * RB, LDC = RB + 1;
   const Inst &I = insts[blockIdx.y];
   const int nblk = I.lstep_blocks;
@@ -595,6 +603,8 @@ k_lstep_angle(const Inst *__restrict__ insts) {
 
 // (I - Cbar M_s / 4pi) Lbar = zeta, tvec = M_s Lbar / 4pi
 __global__ void __launch_bounds__(256) k_lstep_mid(const Inst *__restrict__ insts) {
+  pdl_wait();
+  pdl_trigger();
   const Inst &I = insts[blockIdx.x];
   if (*I.status != kOk) return;
   const int nparts = I.lstep_blocks / kCl;
@@ -633,6 +643,8 @@ __global__ void __launch_bounds__(256) k_lstep_mid(const Inst *__restrict__ inst
 // L_k = B_k^{-1} (Q_k + M_s Lbar / 4pi) = y_k + B_k^{-1} tvec, one thread per
 // entry (k, i) of L (angle-major rows of r)
 __global__ void __launch_bounds__(256) k_lstep_back(const Inst *__restrict__ insts) {
+  pdl_wait();
+  pdl_trigger();
   const Inst &I = insts[blockIdx.y];
   const int r = I.r, K = I.K;
   __shared__ double tv[32];
@@ -659,6 +671,8 @@ __global__ void __launch_bounds__(256) k_lstep_back(const Inst *__restrict__ ins
 // mode 0: S0 <- S (no SVD; U = V = I), vphi; mode 1: SVD as well;
 // mode 2: SVD of the stored S0 (canonical factors on request).
 __global__ void __launch_bounds__(256) k_svd(const Inst *__restrict__ insts, int mode) {
+  pdl_wait();
+  pdl_trigger();
   const Inst &I = insts[blockIdx.x];
   if (*I.status != kOk) return;
   __shared__ double Uw[32 * 32], Vw[32 * 32], sv[32];
@@ -787,6 +801,8 @@ __global__ void __launch_bounds__(256) k_svd(const Inst *__restrict__ insts, int
 // Sign of W columns: the entry of largest magnitude (tie rule) made positive;
 // the same flip is applied to U (and so to X in the temperature kernel).
 __global__ void __launch_bounds__(256) k_sign(const Inst *__restrict__ insts) {
+  pdl_wait();
+  pdl_trigger();
   const Inst &I = insts[blockIdx.x];
   if (*I.status != kOk) return;
   extern __shared__ double val[];
@@ -832,40 +848,33 @@ cudaError_t prepare_small(int slice_max, int maxK, int rmax) {
                               (int)(maxK * sizeof(double)));
 }
 cudaError_t launch_select(const Inst *d, int n, int slice_max, cudaStream_t st) {
-  k_select<<<n * kCl, 256, select_smem(slice_max), st>>>(d, slice_max);
-  return cudaGetLastError();
+  return launch_pdl(k_select, dim3(n * kCl), dim3(256), select_smem(slice_max), st, d, slice_max);
 }
 cudaError_t launch_chol(const CholJob *dj, const Inst *d, int n, cudaStream_t st) {
-  k_chol<<<n, 256, 0, st>>>(dj, d);
-  return cudaGetLastError();
+  return launch_pdl(k_chol, dim3(n), dim3(256), 0, st, dj, d);
 }
 cudaError_t launch_proj_post(const Inst *d, int n, cudaStream_t st) {
-  k_proj_post<<<n, 256, 0, st>>>(d);
-  return cudaGetLastError();
+  return launch_pdl(k_proj_post, dim3(n), dim3(256), 0, st, d);
 }
 // blocks: CTAs of the per-angle kernel (a multiple of kCl); maxK: most angles
 cudaError_t launch_lstep(const Inst *d, int n, int r_max, int blocks, int maxK, cudaStream_t st) {
   const dim3 g(blocks, n);
   const size_t sm = lstep_angle_smem(r_max);
-  switch (rank_bucket(r_max)) {
-    case 8: k_lstep_angle<8><<<g, kLsWarps * 32, sm, st>>>(d); break;
-    case 16: k_lstep_angle<16><<<g, kLsWarps * 32, sm, st>>>(d); break;
-    default: k_lstep_angle<32><<<g, kLsWarps * 32, sm, st>>>(d); break;
-  }
   cudaError_t e;
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_lstep_mid<<<n, 256, 0, st>>>(d);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_lstep_back<<<dim3((maxK * r_max + 255) / 256, n), 256, 0, st>>>(d);
-  return cudaGetLastError();
+  switch (rank_bucket(r_max)) {
+    case 8: e = launch_pdl(k_lstep_angle<8>, g, dim3(kLsWarps * 32), sm, st, d); break;
+    case 16: e = launch_pdl(k_lstep_angle<16>, g, dim3(kLsWarps * 32), sm, st, d); break;
+    default: e = launch_pdl(k_lstep_angle<32>, g, dim3(kLsWarps * 32), sm, st, d); break;
+  }
+  if (e != cudaSuccess) return e;
+  if ((e = launch_pdl(k_lstep_mid, dim3(n), dim3(256), 0, st, d)) != cudaSuccess) return e;
+  return launch_pdl(k_lstep_back, dim3((maxK * r_max + 255) / 256, n), dim3(256), 0, st, d);
 }
 cudaError_t launch_svd(const Inst *d, int n, int mode, cudaStream_t st) {
-  k_svd<<<n, 256, 0, st>>>(d, mode);
-  return cudaGetLastError();
+  return launch_pdl(k_svd, dim3(n), dim3(256), 0, st, d, mode);
 }
 cudaError_t launch_sign(const Inst *d, int n, int maxK, cudaStream_t st) {
-  k_sign<<<n, 256, (size_t)maxK * sizeof(double), st>>>(d);
-  return cudaGetLastError();
+  return launch_pdl(k_sign, dim3(n), dim3(256), (size_t)maxK * sizeof(double), st, d);
 }
 
 }  // namespace dlr

@@ -515,6 +515,8 @@ k_si(const Inst *__restrict__ insts, SiCtl ctl) {
 // Resets the barrier, the unit counters and the convergence maxima of
 // iteration 0 before each source-iteration launch.
 __global__ void k_si_prep(const Inst *__restrict__ insts, int n, SiCtl ctl) {
+  pdl_wait();
+  pdl_trigger();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t == 0) {
     ctl.bar[0] = 0u;
@@ -568,8 +570,7 @@ k_sweep_dirs(int nx, int ny, double hx, double hy, const double *dirs,
 // ------------------------------------------------------------------
 
 cudaError_t launch_si_prep(const Inst *d, int n, SiCtl ctl, cudaStream_t st) {
-  k_si_prep<<<(n + 255) / 256, 256, 0, st>>>(d, n, ctl);
-  return cudaGetLastError();
+  return launch_pdl(k_si_prep, dim3((n + 255) / 256), dim3(256), 0, st, d, n, ctl);
 }
 
 template <typename real>
