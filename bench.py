@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--requests", type=int, default=200, help="served: number of requests")
     ap.add_argument("--hbm-budget-gb", type=float, default=0.0, help="served: admission budget")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the sweep-plan autotuner (default plan: splitting threshold 1)")
     return ap.parse_args()
 
 
@@ -256,6 +258,7 @@ def run_gpu(args):
 
     # ---- main (mixed precision) ----
     solver = dlr.Solver(dlr.problem_from_case(case, precision=dlr.DLR_MIXED, allow_nonpositive=1))
+    tuned = None if args.no_tune else dlr.autotune([solver])  # also applies to later solvers of this shape
     solver.step(args.warmup)
     solver.stream.synchronize()
     s0 = solver.stats()
@@ -353,7 +356,7 @@ def run_gpu(args):
             "si_iters_per_step": iters / args.steps,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fp64_gpu": fp64,
             "clocks": clocks, "gpu_launches": int(launches),
-            "nonpositive_cells_at_end": int(nonpos)}
+            "nonpositive_cells_at_end": int(nonpos), "sweep_plan": tuned}
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
@@ -407,6 +410,7 @@ def run_batch64(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     solvers = [dlr.Solver(dlr.problem_from_case(c, precision=dlr.DLR_MIXED, allow_nonpositive=1),
                           stream=st) for c in cases]
+    tuned = None if args.no_tune else dlr.autotune(solvers)
     dlr.step_batch(solvers, args.warmup)
     st.synchronize()
     u0 = sum(s.stats()["cell_angle_updates"] for s in solvers)
@@ -447,7 +451,8 @@ def run_batch64(args):
             "dlr_steps_per_s": 64 * args.steps / (ms / 1e3),
             "fp64_one_at_a_time": None if args.no_fp64 else {
                 "value": fp_upd / (fp_ms / 1e3), "dlr_steps_per_s": 64 * args.steps / (fp_ms / 1e3),
-                "ms_total": fp_ms}}
+                "ms_total": fp_ms},
+            "sweep_plan": tuned}
     print(json.dumps(line))
 
 

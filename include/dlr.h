@@ -141,6 +141,29 @@ int dlr_step(dlr_handle *h, int32_t nsteps);
  * stream of hs[0].  Results equal those of dlr_step on each handle alone. */
 int dlr_step_batch(dlr_handle *const *hs, int32_t n, int32_t nsteps);
 
+/* Autotuner of the sweep work plan of a batch (the same handles, in the same
+ * order, as later dlr_step_batch calls; n = 1 for dlr_step).  The sweeps of
+ * Algorithm 1 step 4 run as units of consecutive 32-row bands of one angle,
+ * one CTA per unit; an angle split over several units hands its band edges
+ * from unit to unit through global memory.  Candidate plans (no split, and
+ * splitting thresholds 2, 1 and 0.5: an instance's units are halved while
+ * the longest is longer than threshold x the average load of one resident
+ * CTA) are timed on the device, each as reps source-iteration launches of
+ * exactly iters iterations on the state the next step starts from, and the
+ * fastest is kept for this handle set and for later batches of the same
+ * shape (sorted nx, ny, r, precision).  Nothing the next step reads is
+ * changed.  *chosen (may be NULL) receives the chosen threshold (0 = no
+ * split); ms (NULL or 4 entries) the milliseconds per launch of each
+ * candidate in the order above.  Synchronises.  Without tuning, a batch uses
+ * threshold 1. */
+int dlr_autotune(dlr_handle *const *hs, int32_t n, int32_t iters, int32_t reps,
+                 double *chosen, double *ms);
+
+/* Sets the splitting threshold of the sweep work plan of a batch (as in
+ * dlr_autotune; 0 = one unit per angle) without timing.  Results do not
+ * depend on the plan.  Synchronises.  DLR_EINVAL unless 0 <= split <= 1e9. */
+int dlr_set_split(dlr_handle *const *hs, int32_t n, double split);
+
 /* Copies T (nx*ny FP64) into out; synchronises. */
 int dlr_get_T(dlr_handle *h, double *out, int32_t out_on_device);
 

@@ -16,7 +16,7 @@ from . import _lib
 from ._lib import (DLR_FP64, DLR_MIXED, DLR_SEL_DEIM, DLR_SEL_QDEIM, DlrError,  # noqa: F401
                    check, load)
 
-__all__ = ["Solver", "step_batch", "sweep", "footprint_bytes", "DlrError", "DLR_FP64",
+__all__ = ["Solver", "step_batch", "autotune", "set_split", "sweep", "footprint_bytes", "DlrError", "DLR_FP64",
            "DLR_MIXED", "DLR_SEL_QDEIM", "DLR_SEL_DEIM", "problem_from_case"]
 
 
@@ -231,6 +231,29 @@ def step_batch(solvers, nsteps: int = 1) -> None:
     """Steps several solvers as one batch (shared launches)."""
     arr = (C.c_void_p * len(solvers))(*[s.h.value for s in solvers])
     check(load().dlr_step_batch(arr, len(solvers), int(nsteps)))
+
+
+AUTOTUNE_CANDIDATES = (0.0, 2.0, 1.0, 0.5)  # splitting thresholds, in dlr_autotune's order
+
+
+def autotune(solvers, *, iters: int = 2, reps: int = 3) -> dict:
+    """Autotunes the sweep work plan of the batch `solvers` (the same list
+    later passed to step_batch; one solver for Solver.step): times each
+    candidate splitting threshold on the device and keeps the fastest.
+    Returns {"split": chosen threshold (0 = no split), "ms": {threshold:
+    milliseconds per source-iteration launch}}."""
+    arr = (C.c_void_p * len(solvers))(*[s.h.value for s in solvers])
+    chosen = C.c_double(0.0)
+    ms = (C.c_double * len(AUTOTUNE_CANDIDATES))()
+    check(load().dlr_autotune(arr, len(solvers), int(iters), int(reps), C.byref(chosen), ms))
+    return {"split": chosen.value, "ms": dict(zip(AUTOTUNE_CANDIDATES, list(ms)))}
+
+
+def set_split(solvers, split: float) -> None:
+    """Sets the splitting threshold of the sweep work plan of the batch
+    `solvers` (0 = one work unit per angle) without timing."""
+    arr = (C.c_void_p * len(solvers))(*[s.h.value for s in solvers])
+    check(load().dlr_set_split(arr, len(solvers), float(split)))
 
 
 def sweep(nx, ny, dirs, psi_edge, sigma_t, src, *, lx=1.0, ly=1.0, stream=None):

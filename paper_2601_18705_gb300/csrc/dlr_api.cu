@@ -27,6 +27,7 @@ namespace dlr {
 // launchers defined in the kernel translation units
 template <typename real> cudaError_t launch_si(const Inst *, const SiCtl &, int, cudaStream_t);
 template <typename real> int si_max_grid(int, int, int);
+int si_sweep_warps(bool mixed);
 template <typename real> size_t si_smem_bytes(int, int, int);
 template <typename real>
 cudaError_t launch_sweep_dirs(int, int, double, double, int, const double *, const double *,
@@ -153,6 +154,9 @@ struct Batch {
   int maxN = 0, maxK = 0, rmax = 0, pbmax = 1, pblmax = 1, lbmax = 1;
   int nx_max = 0, bands_max = 0, si_grid = 0;
   SiCtl ctl{};
+  SiUnit *d_units = nullptr;  // capacity units_cap
+  int units_cap = 0;
+  double split = 0;           // splitting threshold of the unit plan (<= 0: no split)
   int sel_slice_max = 1;      // most angles one CTA of the selection cluster owns
   bool lside_fused = false;   // step 8 by the one-cluster kernel (pivoted-QR choice, K <= 1024)
   GramJob *g_psi1, *g_psire, *g_x, *g_x3, *g_l1, *g_lf, *g_w, *g_w3, *g_cross;
@@ -642,6 +646,85 @@ static T *carve(char *&cur, size_t count) {
   return p;
 }
 
+// ------------------------------------------------------------------
+// sweep work units and their autotuning
+// ------------------------------------------------------------------
+
+// Modelled wavefront steps of one unit of p bands (32 rows each) on an
+// nx-column mesh swept by nw warps: each warp sweeps ceil(p / nw) bands one
+// after the other, and the warps start one band lag (about 40 steps) apart.
+static double unit_steps(int nx, int p, int nw) {
+  return (double)((p + nw - 1) / nw) * (nx + 31) + (std::min(p, nw) - 1) * 40.0;
+}
+
+// Splits angles into units of consecutive bands.  Starting from one unit per
+// (instance, angle), the instance with the longest unit is split (bands per
+// unit halved, kept a multiple of nw) while its unit takes longer than
+// `split` times the average load of one of the `ctas` resident CTAs; split <= 0
+// keeps one unit per angle.  Units are ordered by modelled length, longest
+// first, and the units of one angle bottom-up, so that a unit's predecessor
+// is always claimed before it.  Returns the number of edge rows used.
+static int plan_units(dlr_handle *const *hs, int n, int nw, int ctas, double split,
+                      std::vector<SiUnit> &units) {
+  std::vector<int> nb(n), bpu(n);
+  for (int i = 0; i < n; ++i) bpu[i] = nb[i] = (hs[i]->prob.ny + 31) / 32;
+  while (split > 0) {
+    double total = 0, tmax = 0;
+    int imax = -1;
+    for (int i = 0; i < n; ++i) {
+      const int g = (nb[i] + bpu[i] - 1) / bpu[i];
+      const double t = unit_steps(hs[i]->prob.nx, bpu[i], nw);
+      total += (double)hs[i]->r * g * t;
+      if (bpu[i] > nw && t > tmax) {
+        tmax = t;
+        imax = i;
+      }
+    }
+    if (imax < 0 || tmax <= split * total / ctas) break;
+    const int half = (bpu[imax] + 1) / 2;
+    bpu[imax] = std::max(nw, (half + nw - 1) / nw * nw);
+  }
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+    return unit_steps(hs[a]->prob.nx, bpu[a], nw) > unit_steps(hs[c]->prob.nx, bpu[c], nw);
+  });
+  units.clear();
+  int rows = 0;
+  for (int i : order) {
+    const int g = (nb[i] + bpu[i] - 1) / bpu[i];
+    for (int j = 0; j < hs[i]->r; ++j) {
+      for (int q = 0; q < g; ++q) {
+        SiUnit u;
+        u.inst = i;
+        u.angle = j;
+        u.b0 = q * bpu[i];
+        u.nb = std::min(bpu[i], nb[i] - q * bpu[i]);
+        u.in_row = q > 0 ? rows + q - 1 : -1;
+        u.out_row = q + 1 < g ? rows + q : -1;
+        units.push_back(u);
+      }
+      rows += g - 1;
+    }
+  }
+  return rows;
+}
+
+// Autotuned splitting thresholds by batch shape: the sorted (nx, ny, r,
+// precision) of its instances.
+static std::map<std::vector<std::array<int, 4>>, double> &tune_table() {
+  static std::map<std::vector<std::array<int, 4>>, double> m;
+  return m;
+}
+static std::vector<std::array<int, 4>> batch_shape(dlr_handle *const *hs, int n);
+constexpr double kDefaultSplit = 1.0;
+
+static double tuned_split(dlr_handle *const *hs, int n) {
+  auto &m = tune_table();
+  auto it = m.find(batch_shape(hs, n));
+  return it == m.end() ? kDefaultSplit : it->second;
+}
+
 static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   Batch *b = new Batch();
   b->hs.assign(hs, hs + n);
@@ -661,23 +744,45 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
     b->nx_max = std::max(b->nx_max, h->prob.nx);
     b->bands_max = std::max(b->bands_max, (h->prob.ny + 31) / 32);
   }
-  // units: (instance, angle), instances with the most cells first
-  std::vector<int> order(n);
-  for (int i = 0; i < n; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return hs[a]->N > hs[c]->N; });
-  std::vector<int2> units;
-  for (int i : order)
-    for (int j = 0; j < hs[i]->r; ++j) units.push_back(make_int2(i, j));
+  const int gmax = b->mixed ? si_max_grid<float>(b->nx_max, b->bands_max, n)
+                            : si_max_grid<double>(b->nx_max, b->bands_max, n);
+  if (gmax <= 0) {
+    delete b;
+    return fail(DLR_ECUDA, "the source-iteration kernel does not fit on this GPU");
+  }
+  b->si_grid = gmax;
+  // capacity of the unit and edge tables: the finest split (one unit per
+  // NW bands, or per band when an angle has fewer bands than warps)
+  const int nw = si_sweep_warps(b->mixed);
+  int rows_cap = 0;
+  for (int i = 0; i < n; ++i) {
+    const int nb = (hs[i]->prob.ny + 31) / 32;
+    const int g = (nb + std::min(nb, nw) - 1) / std::min(nb, nw);
+    b->units_cap += hs[i]->r * g;
+    rows_cap += hs[i]->r * (g - 1);
+  }
+  b->split = tuned_split(hs, n);
+  std::vector<SiUnit> units;
+  plan_units(hs, n, nw, gmax, b->split, units);
   // one device block for the batch's tables
   size_t bytes = 0;
   auto sz = [](size_t s) { return (s + 255) & ~size_t(255); };
   bytes += sz(sizeof(Inst) * n);
   bytes += 9 * sz(sizeof(GramJob) * n) + 2 * sz(sizeof(FillJob) * n) + 9 * sz(sizeof(ApplyJob) * n) +
            8 * sz(sizeof(CholJob) * n) + sz(sizeof(ReduceJob) * n);
-  bytes += sz(sizeof(int2) * units.size()) + sz(64) * 3;
+  const int gedge_ld = (b->nx_max + 3) / 4 * 4 * (b->mixed ? 1 : 2);  // 64-bit words
+  bytes += sz(sizeof(SiUnit) * b->units_cap) + sz(64) * 4;
+  bytes += sz(sizeof(unsigned long long) * gedge_ld * std::max(1, rows_cap));
   if (cudaMalloc(&b->d_mem, bytes) != cudaSuccess) {
     delete b;
     return fail(DLR_ENOMEM, "batch table allocation failed");
+  }
+  // zeroed once: the launch counter, and edge words that can never carry a
+  // valid tag (tags are nonzero)
+  if (cudaMemsetAsync(b->d_mem, 0, bytes, hs[0]->st) != cudaSuccess) {
+    cudaFree(b->d_mem);
+    delete b;
+    return fail(DLR_ECUDA, "batch table initialisation failed");
   }
   char *cur = (char *)b->d_mem;
   b->d_insts = carve<Inst>(cur, n);
@@ -710,11 +815,16 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   b->c_l2 = carve<CholJob>(cur, n);
   b->c_l3 = carve<CholJob>(cur, n);
   b->r_proj = carve<ReduceJob>(cur, n);
-  int2 *d_units = carve<int2>(cur, units.size());
+  b->d_units = carve<SiUnit>(cur, b->units_cap);
   b->ctl.bar = carve<unsigned>(cur, 16);
   b->ctl.work = carve<unsigned>(cur, 16);
   b->ctl.abort_flag = carve<int>(cur, 16);
-  b->ctl.units = d_units;
+  b->ctl.epoch = carve<unsigned>(cur, 16);
+  b->ctl.gedge = carve<unsigned long long>(cur, (size_t)gedge_ld * std::max(1, rows_cap));
+  b->ctl.n_rows = rows_cap;
+  b->ctl.gedge_ld = gedge_ld;
+  b->ctl.force_iters = 0;
+  b->ctl.units = b->d_units;
   b->ctl.n_units = (int)units.size();
   b->ctl.n_inst = n;
   b->ctl.nx_max = b->nx_max;
@@ -841,7 +951,7 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   chain(upv(b->c_l2, cl2.data(), sizeof(CholJob) * n));
   chain(upv(b->c_l3, cl3.data(), sizeof(CholJob) * n));
   chain(upv(b->r_proj, rp.data(), sizeof(ReduceJob) * n));
-  chain(upv(d_units, units.data(), sizeof(int2) * units.size()));
+  chain(upv(b->d_units, units.data(), sizeof(SiUnit) * units.size()));
   // angle selection: one cluster of kCl CTAs per instance
   b->sel_slice_max = std::max(1, (b->maxK + kCl - 1) / kCl);
   // step 8 in one cluster kernel when the angles fit its shared memory
@@ -850,13 +960,6 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
     destroy_batch(b);
     return fail(DLR_ECUDA, "batch table upload failed: %s", cudaGetErrorString(e));
   }
-  const int gmax = b->mixed ? si_max_grid<float>(b->nx_max, b->bands_max, n)
-                            : si_max_grid<double>(b->nx_max, b->bands_max, n);
-  if (gmax <= 0) {
-    destroy_batch(b);
-    return fail(DLR_ECUDA, "the source-iteration kernel does not fit on this GPU");
-  }
-  b->si_grid = gmax;
   if ((e = prepare_small(b->sel_slice_max, b->maxK, b->rmax)) != cudaSuccess ||
       (e = prepare_dense(b->rmax)) != cudaSuccess ||
       (b->lside_fused && (e = prepare_lside(b->sel_slice_max, b->rmax)) != cudaSuccess)) {
@@ -1034,9 +1137,16 @@ static void purge_batches(dlr_handle *h) {
   }
 }
 
-int dlr_step_batch(dlr_handle *const *hs, int32_t n, int32_t nsteps) {
+static std::vector<std::array<int, 4>> batch_shape(dlr_handle *const *hs, int n) {
+  std::vector<std::array<int, 4>> v;
+  for (int i = 0; i < n; ++i)
+    v.push_back({hs[i]->prob.nx, hs[i]->prob.ny, hs[i]->r, hs[i]->mixed ? 1 : 0});
+  std::sort(v.begin(), v.end());
+  return v;
+}
+
+static int check_handles(dlr_handle *const *hs, int n) {
   if (!hs || n < 1) return fail(DLR_EINVAL, "no handles");
-  if (nsteps < 0) return fail(DLR_EINVAL, "nsteps < 0");
   for (int i = 0; i < n; ++i) {
     if (!hs[i]) return fail(DLR_EINVAL, "handle %d is NULL", i);
     if (hs[i]->mixed != hs[0]->mixed) return fail(DLR_EINVAL, "mixed precisions in one batch");
@@ -1044,24 +1154,141 @@ int dlr_step_batch(dlr_handle *const *hs, int32_t n, int32_t nsteps) {
     const int s = *hs[i]->h_status;
     if (s != DLR_OK) return fail(s, "handle %d: %s", i, status_name(s));
   }
-  if (nsteps == 0) return DLR_OK;
-  Batch *b = nullptr;
+  return DLR_OK;
+}
+
+// the batch plan of a handle set (built on first use, then cached)
+static int get_batch(dlr_handle *const *hs, int n, Batch **out) {
   int rc;
   if (n == 1) {
     if (!hs[0]->own_batch && (rc = build_batch(hs, 1, &hs[0]->own_batch))) return rc;
-    b = hs[0]->own_batch;
+    *out = hs[0]->own_batch;
+    return DLR_OK;
+  }
+  std::vector<dlr_handle *> key(hs, hs + n);
+  auto &m = batch_cache();
+  auto it = m.find(key);
+  if (it == m.end()) {
+    Batch *b = nullptr;
+    if ((rc = build_batch(hs, n, &b))) return rc;
+    m[key] = b;
+    *out = b;
   } else {
-    std::vector<dlr_handle *> key(hs, hs + n);
-    auto &m = batch_cache();
-    auto it = m.find(key);
-    if (it == m.end()) {
-      if ((rc = build_batch(hs, n, &b))) return rc;
-      m[key] = b;
-    } else {
-      b = it->second;
+    *out = it->second;
+  }
+  return DLR_OK;
+}
+
+int dlr_step_batch(dlr_handle *const *hs, int32_t n, int32_t nsteps) {
+  int rc = check_handles(hs, n);
+  if (rc) return rc;
+  if (nsteps < 0) return fail(DLR_EINVAL, "nsteps < 0");
+  if (nsteps == 0) return DLR_OK;
+  Batch *b = nullptr;
+  if ((rc = get_batch(hs, n, &b))) return rc;
+  return run_steps(b, nsteps);
+}
+
+// Re-plans the batch's sweep units with splitting threshold `split`.
+static int set_plan(Batch *b, double split) {
+  std::vector<SiUnit> units;
+  plan_units(b->hs.data(), b->n, si_sweep_warps(b->mixed), b->si_grid, split, units);
+  if ((int)units.size() > b->units_cap) return fail(DLR_EINVAL, "unit plan exceeds its table");
+  CK(cudaMemcpyAsync(b->d_units, units.data(), sizeof(SiUnit) * units.size(), cudaMemcpyHostToDevice,
+                     b->st));
+  CK(cudaStreamSynchronize(b->st));  // the host vector dies here
+  b->ctl.n_units = (int)units.size();
+  b->split = split;
+  return DLR_OK;
+}
+
+int dlr_set_split(dlr_handle *const *hs, int32_t n, double split) {
+  int rc = check_handles(hs, n);
+  if (rc) return rc;
+  if (!(split >= 0) || split > 1e9) return fail(DLR_EINVAL, "split must be in [0, 1e9]");
+  Batch *b = nullptr;
+  if ((rc = get_batch(hs, n, &b))) return rc;
+  return set_plan(b, split);
+}
+
+// Times the source-iteration launch of the batch for each candidate unit
+// plan (exactly `iters` iterations, `reps` launches after one untimed one)
+// and keeps the fastest.  The sweeps run on the state the next step starts
+// from (the "pre" graph is replayed first); everything they write is
+// recomputed by that step, and the iteration counters are left alone.
+int dlr_autotune(dlr_handle *const *hs, int32_t n, int32_t iters, int32_t reps, double *chosen,
+                 double *ms_out) {
+  int rc = check_handles(hs, n);
+  if (rc) return rc;
+  if (iters < 1 || reps < 1) return fail(DLR_EINVAL, "iters and reps must be >= 1");
+  Batch *b = nullptr;
+  if ((rc = get_batch(hs, n, &b))) return rc;
+  if ((rc = refresh_batch(b))) return rc;
+  if (!b->pre) {
+    b->kcount = 0;
+    if ((rc = capture(b, true, &b->pre))) return rc;
+    if ((rc = capture(b, false, &b->post))) return rc;
+    b->kernels_per_step = b->kcount + 1;
+  }
+  CK(cudaGraphLaunch(b->pre, b->st));
+  const double cand[] = {0.0, 2.0, 1.0, 0.5};
+  const int nc = (int)(sizeof(cand) / sizeof(cand[0]));
+  const int nw = si_sweep_warps(b->mixed);
+  std::vector<std::vector<SiUnit>> plans(nc);
+  for (int c = 0; c < nc; ++c) plan_units(b->hs.data(), n, nw, b->si_grid, cand[c], plans[c]);
+  auto same = [](const std::vector<SiUnit> &x, const std::vector<SiUnit> &y) {
+    return x.size() == y.size() && std::memcmp(x.data(), y.data(), x.size() * sizeof(SiUnit)) == 0;
+  };
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  std::vector<double> ms(nc, -1.0);
+  int best = -1;
+  SiCtl c = b->ctl;
+  c.force_iters = iters;
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < nc && e == cudaSuccess; ++k) {
+    int dup = -1;
+    for (int q = 0; q < k; ++q)
+      if (same(plans[q], plans[k])) dup = q;
+    if (dup >= 0) {
+      ms[k] = ms[dup];
+      continue;
+    }
+    e = cudaMemcpyAsync(b->d_units, plans[k].data(), sizeof(SiUnit) * plans[k].size(),
+                        cudaMemcpyHostToDevice, b->st);
+    c.n_units = (int)plans[k].size();
+    for (int rep = 0; rep <= reps && e == cudaSuccess; ++rep) {
+      if (rep == 1) e = cudaEventRecord(e0, b->st);
+      if (e == cudaSuccess) e = launch_si_prep(b->d_insts, n, c, b->st);
+      if (e == cudaSuccess)
+        e = b->mixed ? launch_si<float>(b->d_insts, c, b->si_grid, b->st)
+                     : launch_si<double>(b->d_insts, c, b->si_grid, b->st);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, b->st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    ms[k] = t / reps;
+    if (best < 0 || ms[k] < ms[best]) best = k;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return fail(DLR_ECUDA, "autotune: %s", cudaGetErrorString(e));
+  if ((rc = set_plan(b, cand[best]))) return rc;
+  tune_table()[batch_shape(hs, n)] = cand[best];
+  for (auto *h : b->hs) {
+    int s = 0;
+    CK(cudaMemcpy(&s, h->inst.status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (s != DLR_OK) {
+      *h->h_status = s;
+      return fail(s, "autotune: %s", status_name(s));
     }
   }
-  return run_steps(b, nsteps);
+  if (chosen) *chosen = cand[best];
+  if (ms_out)
+    for (int k = 0; k < nc; ++k) ms_out[k] = ms[k];
+  return DLR_OK;
 }
 
 // ------------------------------------------------------------------

@@ -166,14 +166,28 @@ struct FillJob {
   const int *flag;  // CholJob flag block
 };
 
+// One unit of sweep work: bands b0 .. b0 + nb - 1 (32 rows each) of one
+// angle of one instance.  An angle whose bands are split over several units
+// hands the top row of each unit's last band to the next unit through a row
+// of a global edge table (in_row / out_row, -1 if none).
+struct SiUnit {
+  int inst, angle, b0, nb, in_row, out_row;
+};
+
 struct SiCtl {
   unsigned *bar;        // [0] arrivals, [1] generation
   unsigned *work;       // [2] unit counters by iteration parity
   int *abort_flag;
-  const int2 *units;    // (instance, angle), largest first
+  const SiUnit *units;  // in claiming order: a unit's predecessor comes first
   int n_units;
   int n_inst;
   int nx_max, bands_max;
+  unsigned long long *gedge;   // edge rows between units: n_rows x gedge_ld words, each
+                               // column one (FP32) or two (FP64) words tag << 32 | bits
+  unsigned *epoch;             // launch counter (tags of the edge words)
+  int n_rows, gedge_ld;
+  int force_iters;             // > 0: every instance runs exactly this many iterations
+                               // and its iteration counters are left alone (timing runs)
 };
 
 // Four consecutive elements, aligned for one vector shared-memory access.

@@ -262,29 +262,130 @@ __device__ __forceinline__ void write_chunk(const SweepArgs<real> &A, int b, int
   }
 }
 
+// Edge rows between units of one angle (an angle whose bands are split over
+// several CTAs) live in global memory as tagged words: column c of the row
+// is one (FP32) or two (FP64) 64-bit words tag << 32 | 32 bits of the value,
+// each written and read as a single relaxed access, so a reader that sees
+// the expected tag (launch epoch, iteration) also sees the value, with no
+// fence or flag on either side.  The producer is the unit's last band, which
+// copies the kSub top-row values of each sub-window from its shared edge row
+// (kSub lanes, one store each, outside the step loop); the consumer is the
+// unit's first band, which loads the words of the next kSub columns one
+// sub-window ahead and checks their tags.
+struct EdgeLink {
+  int b0, nb;                        // the unit's bands
+  const unsigned long long *g_in;    // words of band b0 - 1's top row (nullptr: none)
+  unsigned long long *g_out;         // words of band b0 + nb - 1's top row (nullptr: none)
+  unsigned tag;
+};
+
+template <typename real> struct EdgeWords;
+template <> struct EdgeWords<float> {
+  static constexpr int kW = 1;
+  __device__ static float decode(const unsigned long long *w) { return __uint_as_float((unsigned)w[0]); }
+  __device__ static void encode(float v, unsigned long long tag, unsigned long long *w) {
+    w[0] = tag | __float_as_uint(v);
+  }
+};
+template <> struct EdgeWords<double> {
+  static constexpr int kW = 2;
+  __device__ static double decode(const unsigned long long *w) {
+    return __hiloint2double((int)(unsigned)w[1], (int)(unsigned)w[0]);
+  }
+  __device__ static void encode(double v, unsigned long long tag, unsigned long long *w) {
+    w[0] = tag | (unsigned)__double2loint(v);
+    w[1] = tag | (unsigned)__double2hiint(v);
+  }
+};
+
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v));
+}
+
+template <typename real>
+__device__ __forceinline__ void edge_load(const unsigned long long *g, int t0, int nx,
+                                          unsigned long long (&w)[EdgeWords<real>::kW]) {
+  const int lane = threadIdx.x & 31, c = t0 + lane;
+  if (lane < kSub && c < nx) {
+#pragma unroll
+    for (int q = 0; q < EdgeWords<real>::kW; ++q) w[q] = ld_relaxed(g + (size_t)c * EdgeWords<real>::kW + q);
+  }
+}
+
+// Lane 0's lower neighbours for columns t0 .. t0 + kSub - 1 from the tagged
+// words prefetched in w (reloaded until every tag matches, bounded in time),
+// then the prefetch of the next sub-window.
+template <typename real>
+__device__ __forceinline__ bool edge_take(const unsigned long long *g, int t0, int nx, unsigned tag,
+                                          unsigned long long (&w)[EdgeWords<real>::kW],
+                                          real (&ed)[kSub], volatile int *abort_flag) {
+  constexpr int kW = EdgeWords<real>::kW;
+  const int lane = threadIdx.x & 31;
+  const bool mine = lane < kSub && t0 + lane < nx;
+  auto valid = [&]() {
+    bool ok = true;
+#pragma unroll
+    for (int q = 0; q < kW; ++q) ok = ok && (unsigned)(w[q] >> 32) == tag;
+    return !mine || ok;
+  };
+  if (!__all_sync(kFull, valid())) {
+    const uint64_t ts = global_ns();
+    unsigned nap = 32, spins = 0;
+    do {
+      __nanosleep(nap);
+      nap = min(nap * 2, 256u);
+      edge_load<real>(g, t0, nx, w);
+      if ((++spins & 15u) == 0) {
+        bool stop = false;
+        if (lane == 0) stop = *abort_flag || global_ns() - ts > kWaitNs;
+        if (__shfl_sync(kFull, stop, 0)) return false;
+      }
+    } while (!__all_sync(kFull, valid()));
+  }
+  const real v = EdgeWords<real>::decode(w);
+#pragma unroll
+  for (int s = 0; s < kSub; ++s) ed[s] = __shfl_sync(kFull, v, s);
+  edge_load<real>(g, t0 + kSub, nx, w);
+  return true;
+}
+
 // The 32 steps t = 32k + tau of window k (OFF = 32 (k mod 2): slot t mod 64
 // = OFF + tau).  Lane i updates column u = t - i.  FIRST (window 0): lanes
 // whose column is still negative keep their inflow value; in later windows
 // every column is >= 0, and columns >= nx only touch slots and edge entries
 // that nobody reads, so no lane needs a mask.
-template <typename real, int NW, int OFF, bool FIRST>
+template <typename real, int NW, int OFF, bool FIRST, bool GIN>
 __device__ __forceinline__ bool sweep_window(int b, int k, const SweepArgs<real> &A,
                                              typename Real2<real>::type *mine, real &psi,
                                              const real *edge_in, real *edge_out,
-                                             volatile int *prog, volatile int *abort_flag) {
+                                             volatile int *prog, volatile int *abort_flag,
+                                             const unsigned long long *g_in,
+                                             unsigned long long *g_out, unsigned tag,
+                                             unsigned long long (&gw)[EdgeWords<real>::kW]) {
   const int lane = threadIdx.x & 31;
   const int nx = A.nx;
   const real ax = A.ax, ay = A.ay;
 #pragma unroll
   for (int sb = 0; sb < 32; sb += kSub) {
     const int t0 = 32 * k + sb;
-    if (b > 0 && t0 < nx) {
-      if (!wait_progress(prog + b - 1, min(nx, t0 + kSub), abort_flag)) return false;
-    }
-    // lane 0's lower neighbours (the previous band's top row) for the next
-    // kSub columns, read as vectors
+    // the sub-window's staged (source, 1 / diagonal) entries, loaded before
+    // the wait: the steps below only overwrite entries already read
+    typename Real2<real>::type vv[kSub];
+#pragma unroll
+    for (int s = 0; s < kSub; ++s) vv[s] = mine[(OFF + sb + s) * kRingLd];
     real ed[kSub];
-    if (b > 0 && t0 < nx) {
+    if (GIN && t0 < nx) {
+      // the previous band belongs to another CTA
+      if (!edge_take<real>(g_in, t0, nx, tag, gw, ed, abort_flag)) return false;
+    } else if (b > 0 && t0 < nx) {
+      if (!wait_progress(prog + b - 1, min(nx, t0 + kSub), abort_flag)) return false;
+      // lane 0's lower neighbours (the previous band's top row) for the next
+      // kSub columns, read as vectors
       const volatile typename Real4<real>::type *e4 =
           reinterpret_cast<const volatile typename Real4<real>::type *>(edge_in + t0);
 #pragma unroll
@@ -296,7 +397,7 @@ __device__ __forceinline__ bool sweep_window(int b, int k, const SweepArgs<real>
 #pragma unroll
     for (int s = 0; s < kSub; ++s) {
       const int slot = (OFF + sb + s) * kRingLd;
-      const typename Real2<real>::type v = mine[slot];
+      const typename Real2<real>::type v = vv[s];
       real down = __shfl_up_sync(kFull, psi, 1);
       if (lane == 0) down = ed[s];
       real p = fmadd(ay, down, fmadd(ax, psi, v.x)) * v.y;
@@ -309,13 +410,27 @@ __device__ __forceinline__ bool sweep_window(int b, int k, const SweepArgs<real>
       __threadfence_block();
       prog[b] = min(nx, max(0, t0 + kSub - 31));
     }
+    if (g_out) {
+      // the unit's last band: the kSub columns of its top row finished in
+      // this sub-window go to the next unit's CTA as tagged words
+      __syncwarp();
+      const int c = t0 - 31 + lane;
+      if (lane < kSub && (unsigned)c < (unsigned)nx) {
+        unsigned long long w[EdgeWords<real>::kW];
+        EdgeWords<real>::encode(edge_out[c], (unsigned long long)tag << 32, w);
+#pragma unroll
+        for (int q = 0; q < EdgeWords<real>::kW; ++q)
+          st_relaxed(g_out + (size_t)c * EdgeWords<real>::kW + q, w[q]);
+      }
+    }
   }
   return true;
 }
 
-// One band of 32 rows of one angle, swept by one warp.
-template <typename real, int NW>
-__device__ bool sweep_band(int b, const SweepArgs<real> &A, const SweepSmem &S,
+// One band of 32 rows of one angle, swept by one warp.  GIN: the band below
+// belongs to another CTA (the first band of a unit with an incoming edge row).
+template <typename real, int NW, bool GIN>
+__device__ bool sweep_band(int b, const SweepArgs<real> &A, const SweepSmem &S, const EdgeLink &L,
                            volatile int *abort_flag) {
   using real2 = typename Real2<real>::type;
   const int lane = threadIdx.x & 31;
@@ -330,6 +445,14 @@ __device__ bool sweep_band(int b, const SweepArgs<real> &A, const SweepSmem &S,
   const int nx = A.nx;
   const int nch = (nx + 31) >> 5;
   real psi = A.in_x;  // this lane's last value: the left neighbour of its next cell
+  // a neighbouring band in another CTA: the unit's first band reads, its
+  // last band writes, the tagged edge words
+  const unsigned long long *g_in = GIN ? L.g_in : nullptr;
+  unsigned long long *g_out = b == L.b0 + L.nb - 1 ? L.g_out : nullptr;
+  unsigned long long gw[EdgeWords<real>::kW];
+#pragma unroll
+  for (int q = 0; q < EdgeWords<real>::kW; ++q) gw[q] = 0ull;
+  if (GIN) edge_load<real>(g_in, 0, nx, gw);
   ChunkRegs<real> R;
   load_chunk(A, b, 0, R);
   for (int k = 0; k <= nch; ++k) {
@@ -340,11 +463,14 @@ __device__ bool sweep_band(int b, const SweepArgs<real> &A, const SweepSmem &S,
     if (k + 1 < nch) load_chunk(A, b, k + 1, R);  // in flight during the steps below
     bool ok;
     if (k == 0)
-      ok = sweep_window<real, NW, 0, true>(b, k, A, mine, psi, edge_in, edge_out, prog, abort_flag);
+      ok = sweep_window<real, NW, 0, true, GIN>(b, k, A, mine, psi, edge_in, edge_out, prog,
+                                                   abort_flag, g_in, g_out, L.tag, gw);
     else if (k & 1)
-      ok = sweep_window<real, NW, 32, false>(b, k, A, mine, psi, edge_in, edge_out, prog, abort_flag);
+      ok = sweep_window<real, NW, 32, false, GIN>(b, k, A, mine, psi, edge_in, edge_out, prog,
+                                                   abort_flag, g_in, g_out, L.tag, gw);
     else
-      ok = sweep_window<real, NW, 0, false>(b, k, A, mine, psi, edge_in, edge_out, prog, abort_flag);
+      ok = sweep_window<real, NW, 0, false, GIN>(b, k, A, mine, psi, edge_in, edge_out, prog,
+                                                   abort_flag, g_in, g_out, L.tag, gw);
     if (!ok) return false;
   }
   __syncwarp();
@@ -353,17 +479,21 @@ __device__ bool sweep_band(int b, const SweepArgs<real> &A, const SweepSmem &S,
   return true;
 }
 
-// Whole sweep of one angle by one CTA.  Returns false if a wait gave up.
+// Bands b0 .. b0 + nb - 1 of one angle by one CTA: warp w sweeps bands
+// b0 + w, b0 + w + NW, ...  Returns false if a wait gave up.
 template <typename real, int NW>
-__device__ bool sweep_unit(const SweepArgs<real> &A, const SweepSmem &S,
+__device__ bool sweep_unit(const SweepArgs<real> &A, const SweepSmem &S, const EdgeLink &L,
                            volatile int *abort_flag) {
-  const int nb = (A.ny + 31) >> 5;
   __syncthreads();
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) S.prog[i] = 0;
+  for (int i = L.b0 + threadIdx.x; i < L.b0 + L.nb; i += blockDim.x) S.prog[i] = 0;
   __syncthreads();
   bool ok = true;
   const int wid = threadIdx.x >> 5;
-  for (int b = wid; b < nb && ok; b += NW) ok = sweep_band<real, NW>(b, A, S, abort_flag);
+  for (int b = L.b0 + wid; b < L.b0 + L.nb && ok; b += NW) {
+    const bool gin = b == L.b0 && L.g_in;
+    ok = gin ? sweep_band<real, NW, true>(b, A, S, L, abort_flag)
+             : sweep_band<real, NW, false>(b, A, S, L, abort_flag);
+  }
   if (!ok) *abort_flag = 1;
   __syncthreads();
   return ok;
@@ -411,6 +541,8 @@ k_si(const Inst *__restrict__ insts, SiCtl ctl) {
 
   for (int i = threadIdx.x; i < ctl.n_inst; i += blockDim.x)
     active[i] = (*insts[i].status == kOk) ? 1 : 0;
+  // tags of the edge words: 20 bits of the launch counter, 12 of the iteration
+  const unsigned epoch_tag = (*(volatile unsigned *)ctl.epoch & 0xfffffu) << 12;
   __syncthreads();
 
   for (int it = 0;; ++it) {
@@ -429,10 +561,16 @@ k_si(const Inst *__restrict__ insts, SiCtl ctl) {
       const int u = unit_s;
       __syncthreads();
       if (u >= ctl.n_units) break;
-      const int2 ij = ctl.units[u];
-      if (!active[ij.x]) continue;
-      const SweepArgs<real> A = unit_args<real>(insts[ij.x], ij.y);
-      if (!sweep_unit<real, NW>(A, S, abort_flag)) break;
+      const SiUnit U = ctl.units[u];
+      if (!active[U.inst]) continue;
+      const SweepArgs<real> A = unit_args<real>(insts[U.inst], U.angle);
+      EdgeLink L;
+      L.b0 = U.b0;
+      L.nb = U.nb;
+      L.g_in = U.in_row >= 0 ? ctl.gedge + (size_t)U.in_row * ctl.gedge_ld : nullptr;
+      L.g_out = U.out_row >= 0 ? ctl.gedge + (size_t)U.out_row * ctl.gedge_ld : nullptr;
+      L.tag = epoch_tag | ((unsigned)(it + 1) & 0xfffu);
+      if (!sweep_unit<real, NW>(A, S, L, abort_flag)) break;
     }
     if (!grid_barrier(ctl.bar, abort_flag)) break;
 
@@ -485,6 +623,11 @@ k_si(const Inst *__restrict__ insts, SiCtl ctl) {
         const double m = __longlong_as_double((long long)cv[1]);
         const int done_iters = it + 1;
         bool done;
+        if (ctl.force_iters > 0) {
+          done = done_iters >= ctl.force_iters;
+          if (done) active[i] = 0;
+          continue;
+        }
         if (I.fixed_iters > 0) {
           done = done_iters >= I.fixed_iters;
         } else {
@@ -523,6 +666,7 @@ __global__ void k_si_prep(const Inst *__restrict__ insts, int n, SiCtl ctl) {
     ctl.work[0] = 0u;
     ctl.work[1] = 0u;
     *ctl.abort_flag = 0;
+    *ctl.epoch += 1u;  // stale edge words of earlier launches never match
   }
   if (t < n) {
     insts[t].conv[0] = 0ull;
@@ -562,7 +706,10 @@ k_sweep_dirs(int nx, int ny, double hx, double hy, const double *dirs,
   A.src = src + (size_t)nx * ny * d;
   A.sphi = nullptr;
   A.psi = psi + (size_t)nx * ny * d;
-  sweep_unit<real, NW>(A, S, abort_flag);
+  EdgeLink L{};
+  L.b0 = 0;
+  L.nb = (ny + 31) >> 5;
+  sweep_unit<real, NW>(A, S, L, abort_flag);
 }
 
 // ------------------------------------------------------------------
@@ -631,6 +778,8 @@ cudaError_t launch_sweep_dirs(int nx, int ny, double hx, double hy, int n_dir,
                                                    psi, nx, d_abort);
   return cudaGetLastError();
 }
+
+int si_sweep_warps(bool mixed) { return mixed ? SweepCfg<float>::NW : SweepCfg<double>::NW; }
 
 template size_t si_smem_bytes<float>(int, int, int);
 template size_t si_smem_bytes<double>(int, int, int);

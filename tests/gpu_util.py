@@ -9,7 +9,7 @@ def rel_l2(a, b) -> float:
 
 
 def run_pair(case, precision, steps, *, orc, dlr, forced=None, si_fixed_iters=0, si_tol=None,
-             selection=0, start=None, allow_nonpositive=0):
+             selection=0, start=None, allow_nonpositive=0, split=None):
     """Runs the oracle and the GPU solver side by side from the same state.
     Returns per-step (T error, psi error, oracle idx, gpu idx) and both states.
     When the GPU picks different angles than the oracle (a near-tie), the
@@ -32,6 +32,8 @@ def run_pair(case, precision, steps, *, orc, dlr, forced=None, si_fixed_iters=0,
     out = []
     with dlr.Solver(spec) as s:
         s.set_factors(X, S, W)
+        if split is not None:
+            dlr.set_split([s], split)
         for _ in range(steps):
             X1, S1, W1, T1, res = orc.dlr_step(p, X, S, W, T, selection=selection,
                                                si_fixed_iters=si_fixed_iters, si_tol=tol_o)
