@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sn", action="store_true", help="skip the full-rank SN comparator")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="CPU work of the oracle sample")
     ap.add_argument("--kernel", default=None, choices=["sweep"],
@@ -326,6 +327,26 @@ def run_gpu(args):
                 "dlr_steps_per_s": args.steps / (t64 / 1e3),
                 "mixed_vs_fp64_rel_l2_T": float(np.linalg.norm(T_mixed - T64) / np.linalg.norm(T64))}
 
+    # ---- the full-rank SN step it approximates (all NOm angles), same steps ----
+    sn = None
+    if not args.no_sn and rank == 0:
+        s4 = dlr.Solver(dlr.problem_from_case(case, precision=dlr.DLR_MIXED, allow_nonpositive=1,
+                                              method=dlr.DLR_METHOD_SN))
+        s4.step(args.warmup)
+        s4.stream.synchronize()
+        g0 = s4.stats()
+        ms_sn = timed_steps(dlr, torch, s4, args.steps, flush)
+        g1 = s4.stats()
+        T_sn = s4.T()
+        s4.close()
+        usn = g1["cell_angle_updates"] - g0["cell_angle_updates"]
+        tsn = sum(ms_sn)
+        sn = {"method": f"full-rank SN over all {case['n_polar'] * case['n_azim']} angles, mixed",
+              "value": usn / (tsn / 1e3), "unit": METRIC, "ms_per_step": tsn / args.steps,
+              "dlr_steps_per_s": args.steps / (tsn / 1e3),
+              "si_iters_per_step": (g1["si_iters_total"] - g0["si_iters_total"]) / args.steps,
+              "T_rel_l2_dlr_vs_sn": float(np.linalg.norm(T_mixed - T_sn) / np.linalg.norm(T_sn))}
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -354,7 +375,7 @@ def run_gpu(args):
             "data": "synthetic", "config": case_config(case, "mixed: FP32 sweeps/projections, FP64 small LA and T"),
             "dlr_steps_per_s": world * args.steps / (total_ms / 1e3),
             "si_iters_per_step": iters / args.steps,
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fp64_gpu": fp64,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fp64_gpu": fp64, "sn_gpu": sn,
             "clocks": clocks, "gpu_launches": int(launches),
             "nonpositive_cells_at_end": int(nonpos), "sweep_plan": tuned}
     print(json.dumps(line))

@@ -63,6 +63,12 @@ extern "C" {
 #define DLR_SEL_QDEIM 0  /* angles = first r pivots of column-pivoted QR of W^T */
 #define DLR_SEL_DEIM 1   /* greedy DEIM of Section 4.2 */
 
+/* dlr_problem.method */
+#define DLR_METHOD_DLR 0 /* the SN-like DLR step, Algorithm 1 */
+#define DLR_METHOD_SN 1  /* the full-rank SN step it approximates (Section 2.2
+                            discretised like Algorithm 1 step 4, over all
+                            n_polar * n_azim angles with phi = sum_k w_k psi_k) */
+
 /* Problem statement (Section 2.1-2.2, Algorithm 1 inputs). */
 typedef struct dlr_problem {
   int32_t nx, ny;        /* cells per side, >= 1 */
@@ -92,6 +98,10 @@ typedef struct dlr_problem {
                                 (dlr_stats.nonpositive_cells).  Algorithm 1
                                 does not preserve positivity: a low-rank psi
                                 can turn negative ahead of a steep front */
+  int32_t method;        /* DLR_METHOD_DLR (rank, selection used) or
+                            DLR_METHOD_SN (rank and selection ignored; the
+                            state is psi at every cell and angle, starting
+                            from the isotropic equilibrium psi = B(T0)) */
 } dlr_problem;
 
 /* Device memory and stream supplied by the caller (e.g. PyTorch). */
@@ -191,6 +201,14 @@ int dlr_get_quadrature(dlr_handle *h, double *omega_xyz, double *w);
 /* The r angle indices chosen in the last step (Algorithm 1 step 2), or -1
  * before the first step.  Synchronises. */
 int dlr_get_selected(dlr_handle *h, int32_t *idx);
+
+/* Full-rank SN handles only (DLR_METHOD_SN; DLR_EINVAL otherwise): copy the
+ * angular flux psi (nx*ny x NOm, column-major: psi[c + nx*ny*k] for cell c and
+ * angle k of dlr_get_quadrature, FP64; widened from FP32 in mixed precision)
+ * out of / into the handle.  dlr_get_psi synchronises; dlr_set_psi is
+ * enqueued (a pageable host buffer is consumed before return). */
+int dlr_get_psi(dlr_handle *h, double *out, int32_t out_on_device);
+int dlr_set_psi(dlr_handle *h, const double *in, int32_t in_on_device);
 
 /* Statistics; synchronises. */
 int dlr_get_stats(dlr_handle *h, dlr_stats *out);

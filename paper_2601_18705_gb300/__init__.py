@@ -13,11 +13,13 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import _lib
-from ._lib import (DLR_FP64, DLR_MIXED, DLR_SEL_DEIM, DLR_SEL_QDEIM, DlrError,  # noqa: F401
+from ._lib import (DLR_FP64, DLR_METHOD_DLR, DLR_METHOD_SN, DLR_MIXED, DLR_SEL_DEIM,  # noqa: F401
+                   DLR_SEL_QDEIM, DlrError,
                    check, load)
 
 __all__ = ["Solver", "step_batch", "autotune", "set_split", "sweep", "footprint_bytes", "DlrError", "DLR_FP64",
-           "DLR_MIXED", "DLR_SEL_QDEIM", "DLR_SEL_DEIM", "problem_from_case"]
+           "DLR_MIXED", "DLR_SEL_QDEIM", "DLR_SEL_DEIM", "DLR_METHOD_DLR", "DLR_METHOD_SN",
+           "problem_from_case"]
 
 
 def _f64(a) -> np.ndarray:
@@ -46,6 +48,7 @@ class ProblemSpec:
     si_max_iter: int = 0
     si_fixed_iters: int = 0
     allow_nonpositive: int = 0
+    method: int = DLR_METHOD_DLR
 
     def cstruct(self):
         keep = [_f64(self.sigma), _f64(self.rho_cv), _f64(self.T0)]
@@ -64,6 +67,7 @@ class ProblemSpec:
         p.precision, p.selection, p.augment = self.precision, self.selection, 0
         p.si_tol, p.si_max_iter, p.si_fixed_iters = self.si_tol, self.si_max_iter, self.si_fixed_iters
         p.allow_nonpositive = 1 if self.allow_nonpositive else 0
+        p.method = self.method
         return p, keep
 
 
@@ -115,7 +119,8 @@ class _TorchArena:
 
 
 class Solver:
-    """One SN-like DLR instance resident on the GPU.
+    """One SN-like DLR instance (or, with spec.method = DLR_METHOD_SN, one
+    full-rank SN instance) resident on the GPU.
 
     spec: ProblemSpec; use_torch_memory: allocate device state from PyTorch
     (else cudaMalloc); stream: a torch.cuda.Stream (a new one by default);
@@ -129,7 +134,8 @@ class Solver:
         self.spec = spec
         self.N = spec.nx * spec.ny
         self.K = spec.n_polar * spec.n_azim
-        self.r = spec.rank
+        self.sn = spec.method == DLR_METHOD_SN
+        self.r = self.K if self.sn else spec.rank
         self.stream = stream if stream is not None else torch.cuda.Stream()
         rt = _lib.DlrRuntime()
         rt.stream = C.c_void_p(self.stream.cuda_stream)
@@ -199,9 +205,20 @@ class Solver:
         check(load().dlr_set_factors(self.h, X.ctypes.data, S.ctypes.data, W.ctypes.data, 0))
 
     def psi(self) -> np.ndarray:
-        """psi = X S W^T (Nx x NOm) from the current factors."""
+        """psi (Nx x NOm): the full-rank state of an SN instance, or X S W^T
+        from the current factors of a DLR instance."""
+        if self.sn:
+            out = np.empty((self.N, self.K), order="F")
+            check(load().dlr_get_psi(self.h, out.ctypes.data, 0))
+            return out
         X, S, W = self.factors()
         return X @ S @ W.T
+
+    def set_psi(self, psi) -> None:
+        """Replaces the angular flux of an SN instance (Nx x NOm)."""
+        a = np.asfortranarray(psi, dtype=np.float64)
+        assert a.shape == (self.N, self.K)
+        check(load().dlr_set_psi(self.h, a.ctypes.data, 0))
 
     def quadrature(self):
         om = np.empty((self.K, 3))

@@ -12,6 +12,7 @@ DLR_OK, DLR_EINVAL, DLR_ENOMEM, DLR_ENOTCONV = 0, -1, -2, -3
 DLR_ESINGULAR, DLR_ETIMEOUT, DLR_ENONPOS, DLR_ECUDA = -4, -5, -6, -7
 DLR_FP64, DLR_MIXED = 0, 1
 DLR_SEL_QDEIM, DLR_SEL_DEIM = 0, 1
+DLR_METHOD_DLR, DLR_METHOD_SN = 0, 1
 
 ERROR_NAMES = {DLR_EINVAL: "EINVAL", DLR_ENOMEM: "ENOMEM", DLR_ENOTCONV: "ENOTCONV",
                DLR_ESINGULAR: "ESINGULAR", DLR_ETIMEOUT: "ETIMEOUT",
@@ -20,6 +21,7 @@ ERROR_NAMES = {DLR_EINVAL: "EINVAL", DLR_ENOMEM: "ENOMEM", DLR_ENOTCONV: "ENOTCO
 # every entry point declared in include/dlr.h
 SYMBOLS = ["dlr_create", "dlr_step", "dlr_step_batch", "dlr_autotune", "dlr_set_split",
            "dlr_get_T", "dlr_set_T", "dlr_get_factors", "dlr_set_factors", "dlr_get_quadrature", "dlr_get_selected",
+           "dlr_get_psi", "dlr_set_psi",
            "dlr_get_stats", "dlr_set_timing", "dlr_set_edge_inflow", "dlr_footprint_bytes",
            "dlr_destroy", "dlr_last_error", "dlr_sweep", "dlr_sweep_noalloc"]
 
@@ -32,7 +34,7 @@ class DlrProblem(C.Structure):
                 ("T0", C.POINTER(C.c_double)), ("T_edge", C.c_double * 4),
                 ("precision", C.c_int32), ("selection", C.c_int32), ("augment", C.c_int32),
                 ("si_tol", C.c_double), ("si_max_iter", C.c_int32), ("si_fixed_iters", C.c_int32),
-                ("allow_nonpositive", C.c_int32)]
+                ("allow_nonpositive", C.c_int32), ("method", C.c_int32)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -78,6 +80,8 @@ def load() -> C.CDLL:
     L.dlr_set_factors.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]
     L.dlr_get_quadrature.argtypes = [H, dp, dp]
     L.dlr_get_selected.argtypes = [H, C.POINTER(C.c_int32)]
+    L.dlr_get_psi.argtypes = [H, C.c_void_p, C.c_int32]
+    L.dlr_set_psi.argtypes = [H, C.c_void_p, C.c_int32]
     L.dlr_get_stats.argtypes = [H, C.POINTER(DlrStats)]
     L.dlr_set_timing.argtypes = [H, C.c_int32]
     L.dlr_set_edge_inflow.argtypes = [H, C.c_int32, C.c_double]

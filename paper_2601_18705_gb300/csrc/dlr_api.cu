@@ -26,9 +26,12 @@
 namespace dlr {
 // launchers defined in the kernel translation units
 template <typename real> cudaError_t launch_si(const Inst *, const SiCtl &, int, cudaStream_t);
-template <typename real> int si_max_grid(int, int, int);
+template <typename real> int si_max_grid(int, int, int, int);
 int si_sweep_warps(bool mixed);
-template <typename real> size_t si_smem_bytes(int, int, int);
+template <typename real> size_t si_smem_bytes(int, int, int, int);
+template <typename real> cudaError_t launch_sn_init(void *, const double *, int, int, double, double, cudaStream_t);
+template <typename real> cudaError_t launch_sn_prep(const Inst *, int, int, cudaStream_t);
+template <typename real> cudaError_t launch_sn_tupdate(const Inst *, int, int, cudaStream_t);
 template <typename real>
 cudaError_t launch_sweep_dirs(int, int, double, double, int, const double *, const double *,
                               const real *, const real *, real *, int *, cudaStream_t);
@@ -141,6 +144,7 @@ struct dlr_handle {
   std::vector<std::array<cudaEvent_t, 4>> ev_pending;
   Batch *own_batch = nullptr;
   bool canonical = true;  // S0 diagonal (SVD basis) since the last step
+  bool sn = false;        // full-rank SN instance (r = K swept angles)
 };
 
 struct Batch {
@@ -157,6 +161,7 @@ struct Batch {
   SiUnit *d_units = nullptr;  // capacity units_cap
   int units_cap = 0;
   double split = 0;           // splitting threshold of the unit plan (<= 0: no split)
+  bool sn = false;            // a batch of full-rank SN instances
   int sel_slice_max = 1;      // most angles one CTA of the selection cluster owns
   bool lside_fused = false;   // step 8 by the one-cluster kernel (pivoted-QR choice, K <= 1024)
   GramJob *g_psi1, *g_psire, *g_x, *g_x3, *g_l1, *g_lf, *g_w, *g_w3, *g_cross;
@@ -373,6 +378,15 @@ static Sizes sizes_of(const dlr_problem *p, int sms) {
   s.K = p->n_polar * p->n_azim;
   s.r = p->rank;
   s.rs = p->precision == DLR_MIXED ? 4 : 8;
+  if (p->method == DLR_METHOD_SN) {
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    s.r = s.K;
+    s.pb = s.pbl = s.lb = kCl;
+    s.partial_doubles = 0;
+    s.total = 5 * al((size_t)s.N * 8) + 6 * al((size_t)s.N * s.rs) + 2 * al((size_t)s.N * s.K * s.rs) +
+              3 * al((size_t)s.K * 8) + al((size_t)s.K * 4) + al(64) * 4 + al(sizeof(Inst));
+    return s;
+  }
   // CTAs of the cell and angle reductions: whole clusters of kCl CTAs,
   // about 512 cells or 16 angles per CTA
   const int cap = std::min(reduce_cta_cap(), 2 * sms / kCl * kCl);
@@ -416,7 +430,10 @@ static int validate(const dlr_problem *p) {
   if (p->n_polar < 1 || p->n_azim < 1) return fail(DLR_EINVAL, "n_polar, n_azim must be >= 1");
   const long long N = (long long)p->nx * p->ny, K = (long long)p->n_polar * p->n_azim;
   if (N > (1ll << 30) || K > 8192) return fail(DLR_EINVAL, "mesh or quadrature too large");
-  if (p->rank < 1 || p->rank > kMaxRank || p->rank > N || p->rank > K)
+  if (p->method != DLR_METHOD_DLR && p->method != DLR_METHOD_SN) return fail(DLR_EINVAL, "bad method");
+  const bool sn = p->method == DLR_METHOD_SN;
+  if (sn && N * K > (1ll << 34)) return fail(DLR_EINVAL, "nx*ny*NOm too large for a full-rank state");
+  if (!sn && (p->rank < 1 || p->rank > kMaxRank || p->rank > N || p->rank > K))
     return fail(DLR_EINVAL, "rank must satisfy 1 <= r <= min(%d, nx*ny, NOm)", kMaxRank);
   if (!(p->dt > 0) || !(p->c > 0) || !(p->a_rad >= 0)) return fail(DLR_EINVAL, "dt, c must be > 0, a_rad >= 0");
   if (p->precision != DLR_FP64 && p->precision != DLR_MIXED) return fail(DLR_EINVAL, "bad precision");
@@ -432,8 +449,9 @@ static int validate(const dlr_problem *p) {
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const size_t need = p->precision == DLR_MIXED ? si_smem_bytes<float>(p->nx, (p->ny + 31) / 32, 256)
-                                                : si_smem_bytes<double>(p->nx, (p->ny + 31) / 32, 256);
+  const int gam = sn ? (int)K : kMaxRank;
+  const size_t need = p->precision == DLR_MIXED ? si_smem_bytes<float>(p->nx, (p->ny + 31) / 32, 256, gam)
+                                                : si_smem_bytes<double>(p->nx, (p->ny + 31) / 32, 256, gam);
   if (optin > 0 && need > (size_t)optin) return fail(DLR_EINVAL, "nx = %d too large for the sweep's shared memory", p->nx);
   return DLR_OK;
 }
@@ -442,6 +460,123 @@ static double planck(double a, double c, double T) { return a * c * T * T * T * 
 
 static void destroy_batch(Batch *b);
 static void purge_batches(dlr_handle *h);
+
+static void fill_common(dlr_handle *h, const dlr_problem *problem) {
+  Inst &I = h->inst;
+  I.nx = problem->nx;
+  I.ny = problem->ny;
+  I.N = h->N;
+  I.r = h->r;
+  I.K = h->K;
+  I.precision = problem->precision;
+  I.selection = problem->selection;
+  I.fixed_iters = problem->si_fixed_iters > 0 ? problem->si_fixed_iters : 0;
+  I.max_iter = problem->si_max_iter > 0 ? problem->si_max_iter : 1000;
+  I.hx = problem->lx / problem->nx;
+  I.hy = problem->ly / problem->ny;
+  I.h2 = I.hx * I.hy;
+  I.dt = problem->dt;
+  I.c = problem->c;
+  I.a_rad = problem->a_rad;
+  I.inv_cdt = 1.0 / (problem->c * problem->dt);
+  I.si_tol = problem->si_tol > 0 ? problem->si_tol : (h->mixed ? 1e-6 : 1e-13);
+  for (int e = 0; e < 4; ++e)
+    I.psi_edge[e] = problem->T_edge[e] >= 0 ? planck(problem->a_rad, problem->c, problem->T_edge[e]) : 0.0;
+  I.method = problem->method;
+  I.gamma_ext = nullptr;
+}
+
+// Full-rank SN handle: the per-cell state of Algorithm 1's sweeps, psi and
+// its fixed sources at every angle (N x K each), the quadrature, and the
+// identity as the "selected" angles; psi starts at B(T0).
+static int create_sn(dlr_handle *h, const dlr_problem *problem, dlr_handle **out) {
+  h->sn = true;
+  h->r = h->K;
+  fill_common(h, problem);
+  const int N = h->N, K = h->K;
+  const size_t rs = h->rs;
+  Inst &I = h->inst;
+  I.lay = SmallLayout{};
+  bool ok = true;
+  auto A = [&](size_t bytes) {
+    void *p = dev_alloc(h, bytes);
+    ok = ok && p;
+    return p;
+  };
+  double *sigma = (double *)A((size_t)N * 8);
+  double *rho = (double *)A((size_t)N * 8);
+  I.T = (double *)A((size_t)N * 8);
+  I.B0 = (double *)A((size_t)N * 8);
+  I.D = (double *)A((size_t)N * 8);
+  I.sigma = sigma;
+  I.rho_cv = rho;
+  I.sig_t = A((size_t)N * rs);
+  I.ss4 = A((size_t)N * rs);
+  I.q = A((size_t)N * rs);
+  I.phi0 = A((size_t)N * rs);
+  I.phi1 = A((size_t)N * rs);
+  I.sphi = A((size_t)N * rs);
+  I.Psi = A((size_t)N * K * rs);
+  I.s0 = A((size_t)N * K * rs);
+  double *dox = (double *)A((size_t)K * 8), *doy = (double *)A((size_t)K * 8), *dw = (double *)A((size_t)K * 8);
+  I.ox = dox;
+  I.oy = doy;
+  I.w = dw;
+  I.gamma_ext = dw;
+  I.idx = (int *)A((size_t)K * 4);
+  I.status = (int *)A(64);
+  I.nonpos = (int *)A(64);
+  I.allow_nonpos = problem->allow_nonpositive ? 1 : 0;
+  I.iters = (int *)A(64);
+  I.conv = (unsigned long long *)A(64);
+  h->d_iters_total = (long long *)A(64);
+  I.iters_total = (unsigned long long *)h->d_iters_total;
+  if (!ok) {
+    dev_free_all(h);
+    if (h->own_stream) cudaStreamDestroy(h->st);
+    delete h;
+    return fail(DLR_ENOMEM, "device allocation failed");
+  }
+  if (cudaMallocHost(&h->h_status, sizeof(int)) != cudaSuccess) {
+    dev_free_all(h);
+    if (h->own_stream) cudaStreamDestroy(h->st);
+    delete h;
+    return fail(DLR_ENOMEM, "pinned allocation failed");
+  }
+  *h->h_status = 0;
+  std::vector<int> ident(K);
+  for (int k = 0; k < K; ++k) ident[k] = k;
+  auto up = [&](void *dst, const void *src, size_t bytes) {
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, h->st);
+  };
+  cudaError_t e = cudaSuccess;
+  auto chain = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+  chain(up(sigma, problem->sigma, (size_t)N * 8));
+  chain(up(rho, problem->rho_cv, (size_t)N * 8));
+  chain(up(I.T, problem->T0, (size_t)N * 8));
+  chain(up(dox, h->ox.data(), (size_t)K * 8));
+  chain(up(doy, h->oy.data(), (size_t)K * 8));
+  chain(up(dw, h->w.data(), (size_t)K * 8));
+  chain(up(I.idx, ident.data(), (size_t)K * 4));
+  chain(cudaMemsetAsync(I.status, 0, 64, h->st));
+  chain(cudaMemsetAsync(I.nonpos, 0, 64, h->st));
+  chain(cudaMemsetAsync(I.iters, 0, 64, h->st));
+  chain(cudaMemsetAsync(h->d_iters_total, 0, 64, h->st));
+  if (e == cudaSuccess)
+    e = h->mixed ? launch_sn_init<float>(I.Psi, I.T, N, K, problem->a_rad, problem->c, h->st)
+                 : launch_sn_init<double>(I.Psi, I.T, N, K, problem->a_rad, problem->c, h->st);
+  chain(cudaStreamSynchronize(h->st));
+  if (e != cudaSuccess) {
+    std::string msg = cudaGetErrorString(e);
+    cudaFreeHost(h->h_status);
+    dev_free_all(h);
+    if (h->own_stream) cudaStreamDestroy(h->st);
+    delete h;
+    return fail(DLR_ECUDA, "upload failed: %s", msg.c_str());
+  }
+  *out = h;
+  return DLR_OK;
+}
 
 int dlr_create(const dlr_problem *problem, const dlr_runtime *runtime, dlr_handle **out) {
   if (!out) return fail(DLR_EINVAL, "out is NULL");
@@ -486,6 +621,7 @@ int dlr_create(const dlr_problem *problem, const dlr_runtime *runtime, dlr_handl
   h->pbl = sz.pbl;
   h->lb = sz.lb;
   build_quadrature(h);
+  if (problem->method == DLR_METHOD_SN) return create_sn(h, problem, out);
   std::vector<double> X0, W0;
   double fn = 0.0;
   if (!build_W0(h, W0) || !build_X0(h, problem->T0, X0, fn)) {
@@ -495,25 +631,7 @@ int dlr_create(const dlr_problem *problem, const dlr_runtime *runtime, dlr_handl
   const int N = h->N, K = h->K, r = h->r;
   const size_t rs = h->rs;
   Inst &I = h->inst;
-  I.nx = problem->nx;
-  I.ny = problem->ny;
-  I.N = N;
-  I.r = r;
-  I.K = K;
-  I.precision = problem->precision;
-  I.selection = problem->selection;
-  I.fixed_iters = problem->si_fixed_iters > 0 ? problem->si_fixed_iters : 0;
-  I.max_iter = problem->si_max_iter > 0 ? problem->si_max_iter : 1000;
-  I.hx = problem->lx / problem->nx;
-  I.hy = problem->ly / problem->ny;
-  I.h2 = I.hx * I.hy;
-  I.dt = problem->dt;
-  I.c = problem->c;
-  I.a_rad = problem->a_rad;
-  I.inv_cdt = 1.0 / (problem->c * problem->dt);
-  I.si_tol = problem->si_tol > 0 ? problem->si_tol : (h->mixed ? 1e-6 : 1e-13);
-  for (int e = 0; e < 4; ++e)
-    I.psi_edge[e] = problem->T_edge[e] >= 0 ? planck(problem->a_rad, problem->c, problem->T_edge[e]) : 0.0;
+  fill_common(h, problem);
   I.lay = small_layout(r);
   bool ok = true;
   auto A = [&](size_t bytes) {
@@ -733,6 +851,7 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   b->mixed = hs[0]->mixed;
   b->st = hs[0]->st;
   b->svd_mode = hs[0]->prob.selection == DLR_SEL_DEIM ? 1 : 0;
+  b->sn = hs[0]->sn;
   for (int i = 0; i < n; ++i) {
     const dlr_handle *h = hs[i];
     b->maxN = std::max(b->maxN, h->N);
@@ -744,8 +863,9 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
     b->nx_max = std::max(b->nx_max, h->prob.nx);
     b->bands_max = std::max(b->bands_max, (h->prob.ny + 31) / 32);
   }
-  const int gmax = b->mixed ? si_max_grid<float>(b->nx_max, b->bands_max, n)
-                            : si_max_grid<double>(b->nx_max, b->bands_max, n);
+  const int gam_max = b->sn ? b->rmax : kMaxRank;  // scalar-flux weights of k_si
+  const int gmax = b->mixed ? si_max_grid<float>(b->nx_max, b->bands_max, n, gam_max)
+                            : si_max_grid<double>(b->nx_max, b->bands_max, n, gam_max);
   if (gmax <= 0) {
     delete b;
     return fail(DLR_ECUDA, "the source-iteration kernel does not fit on this GPU");
@@ -829,6 +949,7 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   b->ctl.n_inst = n;
   b->ctl.nx_max = b->nx_max;
   b->ctl.bands_max = b->bands_max;
+  b->ctl.gam_max = gam_max;
   // host copies of the job tables
   std::vector<Inst> insts(n);
   std::vector<GramJob> gp1(n), gpre(n), gx(n), gx3(n), gl1(n), glf(n), gw(n), gw3(n), gcr(n);
@@ -840,6 +961,7 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
     const dlr_handle *h = hs[i];
     const Inst &I = h->inst;
     insts[i] = I;
+    if (b->sn) continue;  // the SN step uses no job tables
     const int N = h->N, K = h->K, r = h->r;
     double *sm = I.small;
     const SmallLayout &L = I.lay;
@@ -960,9 +1082,9 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
     destroy_batch(b);
     return fail(DLR_ECUDA, "batch table upload failed: %s", cudaGetErrorString(e));
   }
-  if ((e = prepare_small(b->sel_slice_max, b->maxK, b->rmax)) != cudaSuccess ||
-      (e = prepare_dense(b->rmax)) != cudaSuccess ||
-      (b->lside_fused && (e = prepare_lside(b->sel_slice_max, b->rmax)) != cudaSuccess)) {
+  if (!b->sn && ((e = prepare_small(b->sel_slice_max, b->maxK, b->rmax)) != cudaSuccess ||
+                  (e = prepare_dense(b->rmax)) != cudaSuccess ||
+                  (b->lside_fused && (e = prepare_lside(b->sel_slice_max, b->rmax)) != cudaSuccess))) {
     destroy_batch(b);
     return fail(DLR_ECUDA, "kernel attribute setup failed: %s", cudaGetErrorString(e));
   }
@@ -991,6 +1113,11 @@ template <typename real>
 static int enqueue_pre(Batch *b) {
   const Inst *d = b->d_insts;
   const int n = b->n;
+  if (b->sn) {  // full-rank SN: coefficients, fixed sources, starting phi
+    LK(launch_sn_prep<real>(d, n, b->maxN, b->st));
+    LK(launch_si_prep(d, n, b->ctl, b->st));
+    return DLR_OK;
+  }
   LK(launch_select(d, n, b->sel_slice_max, b->st));
   LK(launch_coeff_recon<real>(d, n, b->maxN, b->rmax, b->st));
   LK(launch_si_prep(d, n, b->ctl, b->st));
@@ -1002,6 +1129,10 @@ static int enqueue_post(Batch *b) {
   const Inst *d = b->d_insts;
   const int n = b->n;
   cudaStream_t st = b->st;
+  if (b->sn) {
+    LK(launch_sn_tupdate<real>(d, n, b->maxN, st));
+    return DLR_OK;
+  }
   // step 5: CholeskyQR of Psi; dependent columns are replaced by
   // pseudo-random ones (orthonormal completion) and the pass redone; a third
   // pass runs when a Cholesky needed a shift
@@ -1151,6 +1282,7 @@ static int check_handles(dlr_handle *const *hs, int n) {
     if (!hs[i]) return fail(DLR_EINVAL, "handle %d is NULL", i);
     if (hs[i]->mixed != hs[0]->mixed) return fail(DLR_EINVAL, "mixed precisions in one batch");
     if (hs[i]->st != hs[0]->st) return fail(DLR_EINVAL, "handles on different streams");
+    if (hs[i]->sn != hs[0]->sn) return fail(DLR_EINVAL, "SN and DLR handles in one batch");
     const int s = *hs[i]->h_status;
     if (s != DLR_OK) return fail(s, "handle %d: %s", i, status_name(s));
   }
@@ -1339,6 +1471,7 @@ static int canonicalize(dlr_handle *h) {
 
 int dlr_get_factors(dlr_handle *h, double *X, double *S, double *W, int32_t *r_out, int32_t out_on_device) {
   if (!h) return fail(DLR_EINVAL, "NULL handle");
+  if (h->sn) return fail(DLR_EINVAL, "a full-rank SN handle has no factors (dlr_get_psi)");
   {
     int rc = canonicalize(h);
     if (rc) return rc;
@@ -1366,6 +1499,7 @@ int dlr_get_factors(dlr_handle *h, double *X, double *S, double *W, int32_t *r_o
 
 int dlr_set_factors(dlr_handle *h, const double *X, const double *S, const double *W, int32_t in_on_device) {
   if (!h || !X || !S || !W) return fail(DLR_EINVAL, "NULL argument");
+  if (h->sn) return fail(DLR_EINVAL, "a full-rank SN handle has no factors (dlr_set_psi)");
   h->canonical = false;
   const size_t nX = (size_t)h->N * h->r;
   const cudaMemcpyKind k = in_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -1400,8 +1534,47 @@ int dlr_get_quadrature(dlr_handle *h, double *omega_xyz, double *w) {
 
 int dlr_get_selected(dlr_handle *h, int32_t *idx) {
   if (!h || !idx) return fail(DLR_EINVAL, "NULL argument");
+  if (h->sn) return fail(DLR_EINVAL, "a full-rank SN handle selects no angles");
   CK(cudaMemcpyAsync(idx, h->inst.idx, (size_t)h->r * 4, cudaMemcpyDeviceToHost, h->st));
   return sync_status(h);
+}
+
+int dlr_get_psi(dlr_handle *h, double *out, int32_t out_on_device) {
+  if (!h || !out) return fail(DLR_EINVAL, "NULL argument");
+  if (!h->sn) return fail(DLR_EINVAL, "dlr_get_psi needs a full-rank SN handle (dlr_get_factors)");
+  const size_t n = (size_t)h->N * h->K;
+  if (!h->mixed) {
+    CK(cudaMemcpyAsync(out, h->inst.Psi, n * 8, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       h->st));
+  } else if (out_on_device) {
+    k_widen<<<1024, 256, 0, h->st>>>((const float *)h->inst.Psi, out, n);
+    CK(cudaGetLastError());
+  } else {
+    std::vector<float> tmp(n);
+    CK(cudaMemcpyAsync(tmp.data(), h->inst.Psi, n * 4, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    for (size_t i = 0; i < n; ++i) out[i] = tmp[i];
+  }
+  return sync_status(h);
+}
+
+int dlr_set_psi(dlr_handle *h, const double *in, int32_t in_on_device) {
+  if (!h || !in) return fail(DLR_EINVAL, "NULL argument");
+  if (!h->sn) return fail(DLR_EINVAL, "dlr_set_psi needs a full-rank SN handle (dlr_set_factors)");
+  const size_t n = (size_t)h->N * h->K;
+  if (!h->mixed) {
+    CK(cudaMemcpyAsync(h->inst.Psi, in, n * 8, in_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       h->st));
+    if (!in_on_device) CK(cudaStreamSynchronize(h->st));
+  } else if (in_on_device) {
+    k_narrow<<<1024, 256, 0, h->st>>>(in, (float *)h->inst.Psi, n);
+    CK(cudaGetLastError());
+  } else {
+    std::vector<float> tmp(in, in + n);
+    CK(cudaMemcpyAsync(h->inst.Psi, tmp.data(), n * 4, cudaMemcpyHostToDevice, h->st));
+    CK(cudaStreamSynchronize(h->st));
+  }
+  return DLR_OK;
 }
 
 int dlr_get_stats(dlr_handle *h, dlr_stats *out) {

@@ -102,7 +102,31 @@ struct Inst {
   int *iters;             // iterations of the last source-iteration solve
   unsigned long long *iters_total;  // iterations summed over all steps
   unsigned long long *conv;  // [2 parities][2]: max |dphi|, max |phi| (bits)
+  // full-rank SN instances: r = K swept angles, idx the identity, and the
+  // scalar-flux weights gamma = w read from here (nullptr: the DLR gamma in
+  // small)
+  int method;
+  const double *gamma_ext;
 };
+
+// Per-cell coefficients of the Newton-linearised step (Section 2.2, in the
+// backward-Euler form: D = rho c_v + 4 pi dt sigma B'(T0), effective
+// scattering sigma_s = sigma 4 pi dt sigma B' / D, effective source
+// q = sigma B0 - sigma B' 4 pi dt sigma B0 / D, with B = a c T^4 / (4 pi)).
+struct CellCoef {
+  double B, D, ss, q;
+};
+__device__ __forceinline__ CellCoef cell_coefficients(const Inst &I, int c) {
+  const double T0 = I.T[c], sig = I.sigma[c], rho = I.rho_cv[c];
+  CellCoef k;
+  k.B = I.a_rad * I.c * T0 * T0 * T0 * T0 / (4.0 * kPi);
+  const double dB = I.a_rad * I.c * T0 * T0 * T0 / kPi;
+  const double g = 4.0 * kPi * I.dt * sig * dB;
+  k.D = rho + g;
+  k.ss = sig * g / k.D;
+  k.q = sig * k.B - sig * dB * (4.0 * kPi * I.dt * sig * k.B) / k.D;
+  return k;
+}
 
 // Work descriptors of the batched kernels (one entry per instance).
 // A tall-skinny Gram: m x r matrix A, layout 0 column-major A[row + lda*i],
@@ -182,6 +206,7 @@ struct SiCtl {
   int n_units;
   int n_inst;
   int nx_max, bands_max;
+  int gam_max;                 // largest r of the batch (scalar-flux weights in shared memory)
   unsigned long long *gedge;   // edge rows between units: n_rows x gedge_ld words, each
                                // column one (FP32) or two (FP64) words tag << 32 | bits
   unsigned *epoch;             // launch counter (tags of the edge words)

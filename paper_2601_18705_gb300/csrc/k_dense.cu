@@ -45,17 +45,12 @@ __global__ void __launch_bounds__(256) k_coeff_recon(const Inst *__restrict__ in
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= I.N) return;
   // Section 2.2 (Newton linearisation, B = a c T^4 / 4pi)
-  const double T0 = I.T[c], sig = I.sigma[c], rho = I.rho_cv[c];
-  const double B = I.a_rad * I.c * T0 * T0 * T0 * T0 / (4.0 * kPi);
-  const double dB = I.a_rad * I.c * T0 * T0 * T0 / kPi;
-  const double g = 4.0 * kPi * I.dt * sig * dB;
-  const double D = rho + g;
-  const double ss = sig * g / D;
-  const double q = sig * B - sig * dB * (4.0 * kPi * I.dt * sig * B) / D;
-  I.B0[c] = B;
-  I.D[c] = D;
-  as<real>(I.sig_t)[c] = real(sig + I.inv_cdt);
-  const real ss4 = real(ss / (4.0 * kPi));
+  const CellCoef cf = cell_coefficients(I, c);
+  const double q = cf.q;
+  I.B0[c] = cf.B;
+  I.D[c] = cf.D;
+  as<real>(I.sig_t)[c] = real(I.sigma[c] + I.inv_cdt);
+  const real ss4 = real(cf.ss / (4.0 * kPi));
   as<real>(I.ss4)[c] = ss4;
   as<real>(I.q)[c] = real(q);
   // psi0 at the chosen angles: Psi0[c, j] = sum_k X0[c, k] C0[k, j]

@@ -532,11 +532,12 @@ k_si(const Inst *__restrict__ insts, SiCtl ctl) {
   S.edge = smem + off;
   off += (size_t)(NW + 1) * edge_ld(ctl.nx_max) * sizeof(real);
   S.prog = reinterpret_cast<int *>(smem + off);
-  off += (size_t)ctl.bands_max * sizeof(int);
+  off += (size_t)(ctl.bands_max + 3) / 4 * 4 * sizeof(int);
   int *active = reinterpret_cast<int *>(smem + off);
+  off += (size_t)(ctl.n_inst + 3) / 4 * 4 * sizeof(int);
+  real *gam = reinterpret_cast<real *>(smem + off);  // gam_max scalar-flux weights
   S.edge_ld = edge_ld(ctl.nx_max);
   __shared__ int unit_s, n_active_s;
-  __shared__ real gam[kMaxRank];
   volatile int *abort_flag = ctl.abort_flag;
 
   for (int i = threadIdx.x; i < ctl.n_inst; i += blockDim.x)
@@ -592,7 +593,8 @@ k_si(const Inst *__restrict__ insts, SiCtl ctl) {
       real *pnew = as<real>((it & 1) ? I.phi0 : I.phi1);
       real *sphi = as<real>(I.sphi);
       __syncthreads();
-      if (threadIdx.x < r) gam[threadIdx.x] = real(I.small[I.lay.gamma + threadIdx.x]);
+      for (int j = threadIdx.x; j < r; j += blockDim.x)
+        gam[j] = real(I.gamma_ext ? I.gamma_ext[j] : I.small[I.lay.gamma + j]);
       __syncthreads();
       real dmax = real(0), pmax = real(0);  // |differences| and |phi| in the working precision
       for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
@@ -721,17 +723,18 @@ cudaError_t launch_si_prep(const Inst *d, int n, SiCtl ctl, cudaStream_t st) {
 }
 
 template <typename real>
-size_t si_smem_bytes(int nx_max, int bands_max, int n_inst) {
+size_t si_smem_bytes(int nx_max, int bands_max, int n_inst, int gam_max) {
   constexpr int NW = SweepCfg<real>::NW;
   using real2 = typename Real2<real>::type;
   return (size_t)NW * kRing * kRingLd * sizeof(real2) + (size_t)(NW + 1) * edge_ld(nx_max) * sizeof(real) +
-         (size_t)bands_max * sizeof(int) + (size_t)n_inst * sizeof(int);
+         (size_t)(bands_max + 3) / 4 * 4 * sizeof(int) + (size_t)(n_inst + 3) / 4 * 4 * sizeof(int) +
+         (size_t)gam_max * sizeof(real);
 }
 
 template <typename real>
 cudaError_t launch_si(const Inst *d_insts, const SiCtl &ctl, int grid, cudaStream_t st) {
   constexpr int NW = SweepCfg<real>::NW;
-  size_t smem = si_smem_bytes<real>(ctl.nx_max, ctl.bands_max, ctl.n_inst);
+  size_t smem = si_smem_bytes<real>(ctl.nx_max, ctl.bands_max, ctl.n_inst, ctl.gam_max);
   cudaError_t e = cudaFuncSetAttribute(k_si<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
@@ -749,9 +752,9 @@ cudaError_t launch_si(const Inst *d_insts, const SiCtl &ctl, int grid, cudaStrea
 }
 
 template <typename real>
-int si_max_grid(int nx_max, int bands_max, int n_inst) {
+int si_max_grid(int nx_max, int bands_max, int n_inst, int gam_max) {
   constexpr int NW = SweepCfg<real>::NW;
-  size_t smem = si_smem_bytes<real>(nx_max, bands_max, n_inst);
+  size_t smem = si_smem_bytes<real>(nx_max, bands_max, n_inst, gam_max);
   if (cudaFuncSetAttribute(k_si<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return 0;
@@ -770,7 +773,7 @@ cudaError_t launch_sweep_dirs(int nx, int ny, double hx, double hy, int n_dir,
                               const real *src, real *psi, int *d_abort, cudaStream_t st) {
   constexpr int NW = SweepCfg<real>::NW;
   const int bands = (ny + 31) / 32;
-  size_t smem = si_smem_bytes<real>(nx, bands, 0);
+  size_t smem = si_smem_bytes<real>(nx, bands, 0, 0);
   cudaError_t e = cudaFuncSetAttribute(k_sweep_dirs<real>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -781,12 +784,12 @@ cudaError_t launch_sweep_dirs(int nx, int ny, double hx, double hy, int n_dir,
 
 int si_sweep_warps(bool mixed) { return mixed ? SweepCfg<float>::NW : SweepCfg<double>::NW; }
 
-template size_t si_smem_bytes<float>(int, int, int);
-template size_t si_smem_bytes<double>(int, int, int);
+template size_t si_smem_bytes<float>(int, int, int, int);
+template size_t si_smem_bytes<double>(int, int, int, int);
 template cudaError_t launch_si<float>(const Inst *, const SiCtl &, int, cudaStream_t);
 template cudaError_t launch_si<double>(const Inst *, const SiCtl &, int, cudaStream_t);
-template int si_max_grid<float>(int, int, int);
-template int si_max_grid<double>(int, int, int);
+template int si_max_grid<float>(int, int, int, int);
+template int si_max_grid<double>(int, int, int, int);
 template cudaError_t launch_sweep_dirs<float>(int, int, double, double, int, const double *,
                                               const double *, const float *, const float *,
                                               float *, int *, cudaStream_t);
