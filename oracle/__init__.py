@@ -62,7 +62,8 @@ class _Problem(C.Structure):
 class _Opts(C.Structure):
     _fields_ = [("selection", C.c_int), ("forced_idx", _ip),
                 ("si_tol", C.c_double), ("si_max_iter", C.c_int),
-                ("si_fixed_iters", C.c_int), ("canonicalize", C.c_int)]
+                ("si_fixed_iters", C.c_int), ("canonicalize", C.c_int),
+                ("augment", C.c_int)]
 
 
 class _Diag(C.Structure):
@@ -267,8 +268,9 @@ class StepResult:
 
 def dlr_step(p: Problem, X, S, W, T, *, selection: int = 0, forced_idx=None,
              si_tol: float = 1e-13, si_max_iter: int = 1000,
-             si_fixed_iters: int = 0, canonicalize: int = 1):
-    """One SN-like DLR step.  Returns new (X, S, W, T) copies and a
+             si_fixed_iters: int = 0, canonicalize: int = 1, augment: int = 0):
+    """One SN-like DLR step (augment=1: the augmented rank-2r step truncated
+    back to rank r, reading R15).  Returns new (X, S, W, T) copies and a
     StepResult; the inputs are not modified."""
     X = _fortran(X).copy(order="F")
     S = _fortran(S).copy(order="F")
@@ -277,7 +279,7 @@ def dlr_step(p: Problem, X, S, W, T, *, selection: int = 0, forced_idx=None,
     r = X.shape[1]
     o = _Opts()
     o.selection, o.si_tol, o.si_max_iter = selection, si_tol, si_max_iter
-    o.si_fixed_iters, o.canonicalize = si_fixed_iters, canonicalize
+    o.si_fixed_iters, o.canonicalize, o.augment = si_fixed_iters, canonicalize, augment
     fi = None
     if forced_idx is not None:
         fi = np.ascontiguousarray(forced_idx, dtype=np.int32)

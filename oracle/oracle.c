@@ -23,6 +23,13 @@
  *   R10 What_ij = W_j(Om^(i)); Psi = What K; phi = beta^T What^{-1} Psi.
  *   R11 initial factors: psi0(x, Om) = B(T0(x)), S0 = diag(s0, 0, ...).
  *   R12 the temperature update uses phi of the final factors, X S beta.
+ *   R15 augmented step (optional; Algorithm 1 never forms rank 2r): the
+ *       rank-2r rounding the paper gives for its PN-like method (Section 3)
+ *       carried over to the SN-like step -- the new basis is
+ *       orth([Psi, X0]) (2r columns, h^2 inner product), steps 6-8 run at
+ *       rank 2r (P = <X^, X0> is 2r x r), and the 2r x 2r S = U Sigma V^T is
+ *       truncated to its r largest singular values (X = X^ U_r, S = Sigma_r,
+ *       W = W V_r, signs as in the canonical form) before step 9.
  */
 #include "oracle.h"
 
@@ -863,6 +870,10 @@ int oracle_dlr_step(const oracle_problem *p, int r, double *X, double *S,
   double hx = p->lx / nx, hy = p->ly / ny, h2 = hx * hy, h = sqrt(h2);
   double inv_cdt = 1.0 / (p->c * p->dt);
   if (r < 1 || r > Nx || r > NOm) return -1;
+  const int aug = opt && opt->augment;
+  /* rank of steps 5-8: 2r for the augmented step (R15) */
+  const int m = aug ? 2 * r : r;
+  if (m > Nx || m > NOm) return -1;
   int rc = 0;
 
   double *ox = (double *)malloc(sizeof(double) * NOm);
@@ -922,79 +933,84 @@ int oracle_dlr_step(const oracle_problem *p, int r, double *X, double *S,
                         fixed, Psi, &iters);
   }
 
-  /* Step 5: Psi = X R with h^2 X^T X = I (Householder QR of h Psi). */
-  double *Xn = (double *)malloc(sizeof(double) * Nx * r);
-  double *R = (double *)malloc(sizeof(double) * r * r);
-  double *A = (double *)malloc(sizeof(double) * Nx * r);
+  /* Step 5: Psi = X R with h^2 X^T X = I (Householder QR of h Psi); the
+   * augmented step (R15) factors h [Psi, X0] instead. */
+  double *Xn = (double *)malloc(sizeof(double) * Nx * m);
+  double *R = (double *)malloc(sizeof(double) * m * m);
+  double *A = (double *)malloc(sizeof(double) * Nx * m);
   double rdr = 0;
   if (rc == 0) {
     for (size_t e = 0; e < (size_t)Nx * r; e++) A[e] = h * Psi[e];
-    oracle_householder_qr(Nx, r, A, Xn, R);
-    for (size_t e = 0; e < (size_t)Nx * r; e++) Xn[e] /= h;
+    if (aug)
+      for (size_t e = 0; e < (size_t)Nx * r; e++) A[(size_t)Nx * r + e] = h * X[e];
+    oracle_householder_qr(Nx, m, A, Xn, R);
+    for (size_t e = 0; e < (size_t)Nx * m; e++) Xn[e] /= h;
     double rmin = INFINITY, rmax = 0;
-    for (int j = 0; j < r; j++) {
-      double d = fabs(R[j + r * j]);
+    for (int j = 0; j < m; j++) {
+      double d = fabs(R[j + m * j]);
       if (d < rmin) rmin = d;
       if (d > rmax) rmax = d;
     }
     rdr = rmax > 0 ? rmin / rmax : 0;
   }
 
-  /* Step 6: Lt0 = <psi0, X_j> = P L0, P_ji = h^2 <X_j, X0_i>. */
-  double *P = (double *)malloc(sizeof(double) * r * r);
-  double *Lt0 = (double *)malloc(sizeof(double) * r * NOm);
+  /* Step 6: Lt0 = <psi0, X_j> = P L0, P_ji = h^2 <X_j, X0_i> (m x r). */
+  double *P = (double *)malloc(sizeof(double) * m * r);
+  double *Lt0 = (double *)malloc(sizeof(double) * m * NOm);
   if (rc == 0) {
-    for (int jj = 0; jj < r; jj++)
+    for (int jj = 0; jj < m; jj++)
       for (int i = 0; i < r; i++) {
         double t = 0;
         for (int c = 0; c < Nx; c++) t += Xn[c + (size_t)Nx * jj] * X[c + (size_t)Nx * i];
-        P[jj + r * i] = h2 * t;
+        P[jj + m * i] = h2 * t;
       }
-    for (int jj = 0; jj < r; jj++)
+    for (int jj = 0; jj < m; jj++)
       for (int k = 0; k < NOm; k++) {
         double t = 0;
-        for (int i = 0; i < r; i++) t += P[jj + r * i] * L0[i + r * k];
-        Lt0[jj + r * k] = t;
+        for (int i = 0; i < r; i++) t += P[jj + m * i] * L0[i + r * k];
+        Lt0[jj + m * k] = t;
       }
   }
 
-  /* Step 7: L-step (Eq. L step). */
-  double *L = (double *)malloc(sizeof(double) * r * NOm);
-  if (rc == 0) rc = oracle_lstep(p, r, Xn, sig_t, sig_s, q, Lt0, L);
+  /* Step 7: L-step (Eq. L step) on the m basis functions. */
+  double *L = (double *)malloc(sizeof(double) * m * NOm);
+  if (rc == 0) rc = oracle_lstep(p, m, Xn, sig_t, sig_s, q, Lt0, L);
 
   /* Step 8: L = S W^T with sum_k w_k W_ki W_kj = delta: Householder QR of
    * diag(sqrt w) L^T = Q R, W = diag(1/sqrt w) Q, S = R^T; then optionally
-   * S = U Sigma V^T -> X U, Sigma, W V (signs: max-|.| entry of W_j > 0). */
-  double *Wn = (double *)malloc(sizeof(double) * NOm * r);
-  double *Sn = (double *)malloc(sizeof(double) * r * r);
+   * S = U Sigma V^T -> X U, Sigma, W V (signs: max-|.| entry of W_j > 0).
+   * The augmented step (R15) works at rank m = 2r here and keeps the r
+   * largest singular values (always canonical). */
+  double *Wn = (double *)malloc(sizeof(double) * NOm * m);
+  double *Sn = (double *)malloc(sizeof(double) * m * m);
   if (rc == 0) {
-    double *M = (double *)malloc(sizeof(double) * NOm * r);
-    double *Qm = (double *)malloc(sizeof(double) * NOm * r);
-    double *Rm = (double *)malloc(sizeof(double) * r * r);
-    for (int j = 0; j < r; j++)
-      for (int k = 0; k < NOm; k++) M[k + (size_t)NOm * j] = sqrt(w[k]) * L[j + r * k];
-    oracle_householder_qr(NOm, r, M, Qm, Rm);
-    for (int j = 0; j < r; j++)
+    double *M = (double *)malloc(sizeof(double) * NOm * m);
+    double *Qm = (double *)malloc(sizeof(double) * NOm * m);
+    double *Rm = (double *)malloc(sizeof(double) * m * m);
+    for (int j = 0; j < m; j++)
+      for (int k = 0; k < NOm; k++) M[k + (size_t)NOm * j] = sqrt(w[k]) * L[j + m * k];
+    oracle_householder_qr(NOm, m, M, Qm, Rm);
+    for (int j = 0; j < m; j++)
       for (int k = 0; k < NOm; k++) Wn[k + (size_t)NOm * j] = Qm[k + (size_t)NOm * j] / sqrt(w[k]);
-    for (int i = 0; i < r; i++)
-      for (int j = 0; j < r; j++) Sn[i + r * j] = Rm[j + r * i];
-    if (!opt || opt->canonicalize) {
-      double *U = (double *)malloc(sizeof(double) * r * r);
-      double *V = (double *)malloc(sizeof(double) * r * r);
-      double *sv = (double *)malloc(sizeof(double) * r);
-      oracle_jacobi_svd(r, Sn, U, sv, V);
+    for (int i = 0; i < m; i++)
+      for (int j = 0; j < m; j++) Sn[i + m * j] = Rm[j + m * i];
+    if (aug || !opt || opt->canonicalize) {
+      double *U = (double *)malloc(sizeof(double) * m * m);
+      double *V = (double *)malloc(sizeof(double) * m * m);
+      double *sv = (double *)malloc(sizeof(double) * m);
+      oracle_jacobi_svd(m, Sn, U, sv, V);
       double *Xr = (double *)malloc(sizeof(double) * Nx * r);
       double *Wr = (double *)malloc(sizeof(double) * NOm * r);
       double *absw = (double *)malloc(sizeof(double) * NOm);
       for (int j = 0; j < r; j++) {
         for (int c = 0; c < Nx; c++) {
           double t = 0;
-          for (int i = 0; i < r; i++) t += Xn[c + (size_t)Nx * i] * U[i + r * j];
+          for (int i = 0; i < m; i++) t += Xn[c + (size_t)Nx * i] * U[i + m * j];
           Xr[c + (size_t)Nx * j] = t;
         }
         for (int k = 0; k < NOm; k++) {
           double t = 0;
-          for (int i = 0; i < r; i++) t += Wn[k + (size_t)NOm * i] * V[i + r * j];
+          for (int i = 0; i < m; i++) t += Wn[k + (size_t)NOm * i] * V[i + m * j];
           Wr[k + (size_t)NOm * j] = t;
         }
         /* sign: the entry of largest magnitude (tie rule R8) is > 0 */

@@ -42,6 +42,9 @@ typedef struct {
   int si_max_iter;        /* iteration cap (returns -2 if reached) */
   int si_fixed_iters;     /* > 0: run exactly this many iterations */
   int canonicalize;       /* 1: rotate factors to the SVD of S */
+  int augment;            /* 1: augmented step (reading R15): steps 5-8 on
+                             orth([Psi, X0]) at rank 2r, then the SVD of the
+                             2r x 2r S truncated back to rank r */
 } oracle_dlr_opts;
 
 typedef struct {

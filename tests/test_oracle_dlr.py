@@ -219,3 +219,45 @@ def test_fixed_iterations_and_cap(orc):
     assert res.rc == 0 and res.iters == 2
     *_, res = orc.dlr_step(p, X, S, W, T, si_tol=1e-30, si_max_iter=3)
     assert res.rc == -2
+
+
+def _weighted_truncation(psi, h2, w, r):
+    """Best rank-r approximation of psi in the norm sum_c sum_k h2 w_k psi^2
+    (numpy SVD of the weighted matrix) and the weighted singular values."""
+    sw = np.sqrt(w)[None, :]
+    U, s, Vt = np.linalg.svd(np.sqrt(h2) * psi * sw, full_matrices=False)
+    return (U[:, :r] * s[:r]) @ Vt[:r] / np.sqrt(h2) / sw, s
+
+
+@pytest.mark.parametrize("nx,ny,r,npol,naz", [(2, 3, 3, 2, 8), (4, 2, 4, 2, 8), (3, 4, 6, 4, 4)])
+def test_augmented_step_on_the_full_space_is_the_truncated_sn_step(orc, nx, ny, r, npol, naz):
+    """Augmented step (reading R15) with 2r = Nx: orth([Psi, X0]) spans all of
+    R^Nx, so its L-step is the full SN step (a Galerkin projection on the
+    whole space), and the truncation of the 2r x 2r S keeps the best rank-r
+    part of that SN solution in the (h^2, w) norm."""
+    c = workloads.small_case(nx, ny, r, npol, naz, seed=nx + 5 * ny, T0=0.5)
+    p = oracle_problem(c)
+    h2 = (1.0 / nx) * (1.0 / ny)
+    _, _, _, w = orc.quadrature(npol, naz)
+    T = c["T0"].reshape(-1).copy()
+    X, S, W = orc.initial_factors(p, T, r)
+    for _ in range(3):
+        psi_sn, *_ = orc.sn_step(p, X @ S @ W.T, T, si_tol=1e-15)
+        X, S, W, T, res = orc.dlr_step(p, X, S, W, T, augment=1)
+        assert res.rc == 0
+        target, sv = _weighted_truncation(psi_sn, h2, w, r)
+        assert sv[r - 1] - sv[r] > 1e-6 * sv[0]  # a gap: the truncation is unique
+        np.testing.assert_allclose(X @ S @ W.T, target, rtol=0, atol=1e-10 * np.abs(target).max())
+        np.testing.assert_allclose(h2 * X.T @ X, np.eye(r), atol=1e-12)
+        np.testing.assert_allclose(W.T @ (w[:, None] * W), np.eye(r), atol=1e-12)
+        # canonical: S is diagonal with the leading singular values
+        np.testing.assert_allclose(S, np.diag(sv[:r]), rtol=0, atol=1e-10 * sv[0])
+
+
+def test_augmented_step_rejects_2r_above_nx(orc):
+    c = workloads.small_case(2, 2, 3, 2, 4, seed=1, T0=0.5)
+    p = oracle_problem(c)
+    T = c["T0"].reshape(-1).copy()
+    X, S, W = orc.initial_factors(p, T, 3)
+    *_, res = orc.dlr_step(p, X, S, W, T, augment=1)
+    assert res.rc == -1
