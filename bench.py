@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sn", action="store_true", help="skip the full-rank SN comparator")
+    ap.add_argument("--no-aug", action="store_true", help="skip the augmented (rank-2r) step")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="CPU work of the oracle sample")
     ap.add_argument("--kernel", default=None, choices=["sweep"],
@@ -347,6 +348,26 @@ def run_gpu(args):
               "si_iters_per_step": (g1["si_iters_total"] - g0["si_iters_total"]) / args.steps,
               "T_rel_l2_dlr_vs_sn": float(np.linalg.norm(T_mixed - T_sn) / np.linalg.norm(T_sn))}
 
+    # ---- the augmented step (rank-2r basis truncated to r), same steps ----
+    aug = None
+    if not args.no_aug and rank == 0 and 2 * case["r"] <= 32 and case["n_polar"] * case["n_azim"] <= 1024:
+        s5 = dlr.Solver(dlr.problem_from_case(case, precision=dlr.DLR_MIXED, allow_nonpositive=1, augment=1))
+        s5.step(args.warmup)
+        s5.stream.synchronize()
+        a0 = s5.stats()
+        ms_aug = timed_steps(dlr, torch, s5, args.steps, flush)
+        a1 = s5.stats()
+        T_aug = s5.T()
+        s5.close()
+        ua = a1["cell_angle_updates"] - a0["cell_angle_updates"]
+        ta = sum(ms_aug)
+        aug = {"method": f"augmented step, rank {2 * case['r']} basis truncated to {case['r']}, mixed",
+               "value": ua / (ta / 1e3), "unit": METRIC, "ms_per_step": ta / args.steps,
+               "dlr_steps_per_s": args.steps / (ta / 1e3),
+               "si_iters_per_step": (a1["si_iters_total"] - a0["si_iters_total"]) / args.steps}
+        if sn is not None:
+            aug["T_rel_l2_vs_sn"] = float(np.linalg.norm(T_aug - T_sn) / np.linalg.norm(T_sn))
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -375,7 +396,7 @@ def run_gpu(args):
             "data": "synthetic", "config": case_config(case, "mixed: FP32 sweeps/projections, FP64 small LA and T"),
             "dlr_steps_per_s": world * args.steps / (total_ms / 1e3),
             "si_iters_per_step": iters / args.steps,
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fp64_gpu": fp64, "sn_gpu": sn,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fp64_gpu": fp64, "sn_gpu": sn, "augmented_gpu": aug,
             "clocks": clocks, "gpu_launches": int(launches),
             "nonpositive_cells_at_end": int(nonpos), "sweep_plan": tuned}
     print(json.dumps(line))

@@ -86,7 +86,13 @@ typedef struct dlr_problem {
                             top; < 0 = vacuum */
   int32_t precision;     /* DLR_FP64 or DLR_MIXED */
   int32_t selection;     /* DLR_SEL_QDEIM or DLR_SEL_DEIM */
-  int32_t augment;       /* must be 0 (Algorithm 1 as printed) */
+  int32_t augment;       /* 0: Algorithm 1 as printed; 1: augmented step --
+                            step 5 factors [Psi, X0] (2r columns), steps 6-8
+                            run at rank 2r, and the SVD of the 2r x 2r S is
+                            truncated back to rank r before step 9 (the
+                            rank-2r rounding of Section 3 carried over to the
+                            SN-like step).  Needs 2r <= min(32, nx*ny, NOm),
+                            NOm <= 1024 and DLR_SEL_QDEIM */
   double si_tol;         /* source-iteration tolerance; stop when
                             max|phi_new - phi| <= si_tol * max|phi_new|;
                             <= 0 selects 1e-13 (FP64) or 1e-6 (mixed; the

@@ -49,6 +49,7 @@ class ProblemSpec:
     si_fixed_iters: int = 0
     allow_nonpositive: int = 0
     method: int = DLR_METHOD_DLR
+    augment: int = 0     # 1: augmented step (rank-2r basis truncated back to rank r)
 
     def cstruct(self):
         keep = [_f64(self.sigma), _f64(self.rho_cv), _f64(self.T0)]
@@ -64,7 +65,7 @@ class ProblemSpec:
         p.sigma, p.rho_cv, p.T0 = (a.ctypes.data_as(dp) for a in keep)
         for e in range(4):
             p.T_edge[e] = float(self.T_edge[e])
-        p.precision, p.selection, p.augment = self.precision, self.selection, 0
+        p.precision, p.selection, p.augment = self.precision, self.selection, int(self.augment)
         p.si_tol, p.si_max_iter, p.si_fixed_iters = self.si_tol, self.si_max_iter, self.si_fixed_iters
         p.allow_nonpositive = 1 if self.allow_nonpositive else 0
         p.method = self.method

@@ -56,6 +56,8 @@ cudaError_t launch_svd(const Inst *, int, int, cudaStream_t);
 cudaError_t launch_sign(const Inst *, int, int, cudaStream_t);
 cudaError_t launch_si_prep(const Inst *, int, SiCtl, cudaStream_t);
 cudaError_t prepare_small(int, int, int);
+cudaError_t launch_aug_pad(const Inst *, int, cudaStream_t);
+cudaError_t launch_aug_trunc(const Inst *, int, cudaStream_t);
 }  // namespace dlr
 
 using namespace dlr;
@@ -145,6 +147,8 @@ struct dlr_handle {
   Batch *own_batch = nullptr;
   bool canonical = true;  // S0 diagonal (SVD basis) since the last step
   bool sn = false;        // full-rank SN instance (r = K swept angles)
+  bool aug = false;       // augmented step: steps 5-10 on inst2 at rank 2r
+  Inst inst2{};
 };
 
 struct Batch {
@@ -162,6 +166,8 @@ struct Batch {
   int units_cap = 0;
   double split = 0;           // splitting threshold of the unit plan (<= 0: no split)
   bool sn = false;            // a batch of full-rank SN instances
+  bool aug = false;           // a batch of augmented instances (steps 5-10 on d_insts2)
+  Inst *d_insts2 = nullptr;   // the instances of steps 5-10 (rank 2r when augmented)
   int sel_slice_max = 1;      // most angles one CTA of the selection cluster owns
   bool lside_fused = false;   // step 8 by the one-cluster kernel (pivoted-QR choice, K <= 1024)
   GramJob *g_psi1, *g_psire, *g_x, *g_x3, *g_l1, *g_lf, *g_w, *g_w3, *g_cross;
@@ -394,18 +400,21 @@ static Sizes sizes_of(const dlr_problem *p, int sms) {
   s.pb = clusters(std::max(1, (s.N + 511) / 512));
   s.pbl = clusters(std::max(1, (s.K + 15) / 16));
   s.lb = std::min(2 * sms / kCl * kCl, (std::max(1, (s.K + 3) / 4) + kCl - 1) / kCl * kCl);  // 4 warps, one angle each
-  const size_t r = s.r;
-  s.partial_doubles = std::max({(size_t)(s.pb / kCl) * proj_count(s.r), (size_t)(s.pb / kCl) * r * r,
+  const size_t r1 = s.r;
+  const size_t r = p->augment ? 2 * r1 : r1;    // rank of steps 5-10
+  s.partial_doubles = std::max({(size_t)(s.pb / kCl) * proj_count((int)r), (size_t)(s.pb / kCl) * r * r,
                                 (size_t)(s.pbl / kCl) * r * r, (size_t)(s.lb / kCl) * (r * r + r)});
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
   size_t t = 0;
   t += 5 * al((size_t)s.N * 8);                 // sigma, rho_cv, T, B0, D
   t += 6 * al((size_t)s.N * s.rs);              // sig_t, ss4, q, phi0, phi1, sphi
-  t += 4 * al((size_t)s.N * r * s.rs);          // X0, X, Psi, s0
+  t += 3 * al((size_t)s.N * r * s.rs);          // X0, X, Psi (with X0 beside it when augmented)
+  t += al((size_t)s.N * r1 * s.rs);             // s0
   t += 3 * al((size_t)s.K * 8);                 // ox, oy, w
   t += 3 * al((size_t)s.K * r * 8);             // W0, L, Lf
   t += al(r * r * 8) + al(r * 4);               // S0, idx
-  t += al((size_t)small_layout(s.r).total * 8); // small
+  t += al((size_t)small_layout((int)r).total * 8); // small
+  if (p->augment) t += al(r1 * r1 * 8) + al((size_t)small_layout((int)r1).total * 8);  // rank-r S0, small
   t += al((size_t)s.K * r * r * 8) + al((size_t)s.K * r * 4);  // lu, piv
   t += al(s.partial_doubles * 8);
   t += al(64) * 4 + al(sizeof(Inst));           // status, iters, conv, totals, inst
@@ -438,7 +447,14 @@ static int validate(const dlr_problem *p) {
   if (!(p->dt > 0) || !(p->c > 0) || !(p->a_rad >= 0)) return fail(DLR_EINVAL, "dt, c must be > 0, a_rad >= 0");
   if (p->precision != DLR_FP64 && p->precision != DLR_MIXED) return fail(DLR_EINVAL, "bad precision");
   if (p->selection != DLR_SEL_QDEIM && p->selection != DLR_SEL_DEIM) return fail(DLR_EINVAL, "bad selection");
-  if (p->augment != 0) return fail(DLR_EINVAL, "augment must be 0");
+  if (p->augment != 0 && p->augment != 1) return fail(DLR_EINVAL, "augment must be 0 or 1");
+  if (p->augment == 1) {
+    if (sn) return fail(DLR_EINVAL, "the augmented step is a DLR mode");
+    if (2 * p->rank > kMaxRank || 2 * p->rank > N || 2 * p->rank > K)
+      return fail(DLR_EINVAL, "augmented step: 2r must be <= min(%d, nx*ny, NOm)", kMaxRank);
+    if (K > 1024 || p->selection != DLR_SEL_QDEIM)
+      return fail(DLR_EINVAL, "augmented step: needs NOm <= 1024 and the pivoted-QR angle choice");
+  }
   if (!p->sigma || !p->rho_cv || !p->T0) return fail(DLR_EINVAL, "sigma, rho_cv, T0 must be given");
   for (long long c = 0; c < N; ++c) {
     if (!(p->sigma[c] >= 0) || !std::isfinite(p->sigma[c])) return fail(DLR_EINVAL, "sigma[%lld] invalid", c);
@@ -652,22 +668,30 @@ int dlr_create(const dlr_problem *problem, const dlr_runtime *runtime, dlr_handl
   I.phi0 = A((size_t)N * rs);
   I.phi1 = A((size_t)N * rs);
   I.sphi = A((size_t)N * rs);
-  I.X0 = A((size_t)N * r * rs);
-  I.X = A((size_t)N * r * rs);
-  I.Psi = A((size_t)N * r * rs);
+  // the augmented step keeps X0, W0 with m = 2r columns (the last r zero
+  // between steps) and runs steps 5-10 on a rank-2r copy of the instance
+  const bool aug = problem->augment == 1;
+  const int m = aug ? 2 * r : r;
+  h->aug = aug;
+  I.X0 = A((size_t)N * m * rs);
+  I.X = A((size_t)N * m * rs);
+  I.Psi = A((size_t)N * m * rs);
   I.s0 = A((size_t)N * r * rs);
   double *dox = (double *)A((size_t)K * 8), *doy = (double *)A((size_t)K * 8), *dw = (double *)A((size_t)K * 8);
   I.ox = dox;
   I.oy = doy;
   I.w = dw;
-  I.W0 = (double *)A((size_t)K * r * 8);
-  I.L = (double *)A((size_t)K * r * 8);
-  I.Lf = (double *)A((size_t)K * r * 8);
+  I.W0 = (double *)A((size_t)K * m * 8);
+  I.L = (double *)A((size_t)K * m * 8);
+  I.Lf = (double *)A((size_t)K * m * 8);
   I.S0 = (double *)A((size_t)r * r * 8);
   I.idx = (int *)A((size_t)r * 4);
   I.small = (double *)A((size_t)I.lay.total * 8);
-  I.lu = (double *)A((size_t)K * r * r * 8);
-  I.piv = (int *)A((size_t)K * r * 4);
+  I.lu = (double *)A((size_t)K * m * m * 8);
+  I.piv = (int *)A((size_t)K * m * 4);
+  const SmallLayout lay2 = small_layout(m);
+  double *S0m = aug ? (double *)A((size_t)m * m * 8) : nullptr;
+  double *small2 = aug ? (double *)A((size_t)lay2.total * 8) : nullptr;
   I.partials = (double *)A(sz.partial_doubles * 8);
   I.partial_blocks = h->pb;
   I.angle_blocks = h->pbl;
@@ -704,6 +728,12 @@ int dlr_create(const dlr_problem *problem, const dlr_runtime *runtime, dlr_handl
   chain(up(dox, h->ox.data(), (size_t)K * 8));
   chain(up(doy, h->oy.data(), (size_t)K * 8));
   chain(up(dw, h->w.data(), (size_t)K * 8));
+  if (aug) {  // zero the extra columns of X0 and W0 (and the rank-2r work space)
+    chain(cudaMemsetAsync(I.X0, 0, (size_t)N * m * rs, h->st));
+    chain(cudaMemsetAsync(I.W0, 0, (size_t)K * m * 8, h->st));
+    chain(cudaMemsetAsync(S0m, 0, (size_t)m * m * 8, h->st));
+    chain(cudaMemsetAsync(small2, 0, (size_t)lay2.total * 8, h->st));
+  }
   chain(up(I.W0, W0.data(), (size_t)K * r * 8));
   chain(up(I.S0, S0.data(), (size_t)r * r * 8));
   if (h->mixed) {
@@ -727,6 +757,20 @@ int dlr_create(const dlr_problem *problem, const dlr_runtime *runtime, dlr_handl
     if (h->own_stream) cudaStreamDestroy(h->st);
     delete h;
     return fail(DLR_ECUDA, "upload failed: %s", msg.c_str());
+  }
+  if (aug) {
+    // steps 1-4 sweep Psi into the first r columns of the step-5 input and
+    // copy X0 beside it; steps 5-10 see the instance at rank m = 2r
+    I.aug_x0 = static_cast<char *>(I.Psi) + (size_t)N * r * rs;
+    Inst &J = h->inst2;
+    J = I;
+    J.r = m;
+    J.lay = lay2;
+    J.small = small2;
+    J.S0 = S0m;
+    J.aug_r = r;
+    J.S0_r = I.S0;
+    J.aug_x0 = nullptr;
   }
   *out = h;
   return DLR_OK;
@@ -852,11 +896,12 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   b->st = hs[0]->st;
   b->svd_mode = hs[0]->prob.selection == DLR_SEL_DEIM ? 1 : 0;
   b->sn = hs[0]->sn;
+  b->aug = hs[0]->aug;
   for (int i = 0; i < n; ++i) {
     const dlr_handle *h = hs[i];
     b->maxN = std::max(b->maxN, h->N);
     b->maxK = std::max(b->maxK, h->K);
-    b->rmax = std::max(b->rmax, h->r);
+    b->rmax = std::max(b->rmax, h->aug ? 2 * h->r : h->r);  // rank of steps 5-10
     b->pbmax = std::max(b->pbmax, h->pb);
     b->pblmax = std::max(b->pblmax, h->pbl);
     b->lbmax = std::max(b->lbmax, h->lb);
@@ -887,7 +932,7 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   // one device block for the batch's tables
   size_t bytes = 0;
   auto sz = [](size_t s) { return (s + 255) & ~size_t(255); };
-  bytes += sz(sizeof(Inst) * n);
+  bytes += 2 * sz(sizeof(Inst) * n);
   bytes += 9 * sz(sizeof(GramJob) * n) + 2 * sz(sizeof(FillJob) * n) + 9 * sz(sizeof(ApplyJob) * n) +
            8 * sz(sizeof(CholJob) * n) + sz(sizeof(ReduceJob) * n);
   const int gedge_ld = (b->nx_max + 3) / 4 * 4 * (b->mixed ? 1 : 2);  // 64-bit words
@@ -906,6 +951,7 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   }
   char *cur = (char *)b->d_mem;
   b->d_insts = carve<Inst>(cur, n);
+  b->d_insts2 = carve<Inst>(cur, n);
   b->g_psi1 = carve<GramJob>(cur, n);
   b->g_psire = carve<GramJob>(cur, n);
   b->g_x = carve<GramJob>(cur, n);
@@ -951,7 +997,7 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   b->ctl.bands_max = b->bands_max;
   b->ctl.gam_max = gam_max;
   // host copies of the job tables
-  std::vector<Inst> insts(n);
+  std::vector<Inst> insts(n), insts2(n);
   std::vector<GramJob> gp1(n), gpre(n), gx(n), gx3(n), gl1(n), glf(n), gw(n), gw3(n), gcr(n);
   std::vector<FillJob> fp(n), fl(n);
   std::vector<ApplyJob> ap(n), ax2(n), ax3(n), al1(n), aw2(n), aw3(n), awv(n), acw(n), acx(n);
@@ -959,10 +1005,12 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   std::vector<ReduceJob> rp(n);
   for (int i = 0; i < n; ++i) {
     const dlr_handle *h = hs[i];
-    const Inst &I = h->inst;
-    insts[i] = I;
+    insts[i] = h->inst;
+    insts2[i] = h->aug ? h->inst2 : h->inst;
     if (b->sn) continue;  // the SN step uses no job tables
-    const int N = h->N, K = h->K, r = h->r;
+    // the jobs of steps 5-10 (rank 2r when augmented)
+    const Inst &I = insts2[i];
+    const int N = h->N, K = h->K, r = I.r;
     double *sm = I.small;
     const SmallLayout &L = I.lay;
     int *flag = reinterpret_cast<int *>(sm + L.qr_flag);
@@ -1044,6 +1092,7 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   auto chain = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
   cudaStreamSynchronize(b->st);
   chain(upv(b->d_insts, insts.data(), sizeof(Inst) * n));
+  chain(upv(b->d_insts2, insts2.data(), sizeof(Inst) * n));
   chain(upv(b->g_psi1, gp1.data(), sizeof(GramJob) * n));
   chain(upv(b->g_psire, gpre.data(), sizeof(GramJob) * n));
   chain(upv(b->g_x, gx.data(), sizeof(GramJob) * n));
@@ -1098,6 +1147,8 @@ static int refresh_batch(Batch *b) {
   for (int i = 0; i < b->n; ++i)
     if (b->versions[i] != b->hs[i]->version) {
       CK(cudaMemcpyAsync(b->d_insts + i, &b->hs[i]->inst, sizeof(Inst), cudaMemcpyHostToDevice, b->st));
+      const Inst *j2 = b->hs[i]->aug ? &b->hs[i]->inst2 : &b->hs[i]->inst;
+      CK(cudaMemcpyAsync(b->d_insts2 + i, j2, sizeof(Inst), cudaMemcpyHostToDevice, b->st));
       b->versions[i] = b->hs[i]->version;
     }
   return DLR_OK;
@@ -1126,7 +1177,7 @@ static int enqueue_pre(Batch *b) {
 
 template <typename real>
 static int enqueue_post(Batch *b) {
-  const Inst *d = b->d_insts;
+  const Inst *d = b->d_insts2;  // steps 5-10 (rank 2r when augmented)
   const int n = b->n;
   cudaStream_t st = b->st;
   if (b->sn) {
@@ -1135,7 +1186,9 @@ static int enqueue_post(Batch *b) {
   }
   // step 5: CholeskyQR of Psi; dependent columns are replaced by
   // pseudo-random ones (orthonormal completion) and the pass redone; a third
-  // pass runs when a Cholesky needed a shift
+  // pass runs when a Cholesky needed a shift.  The augmented step factors
+  // [Psi, X0] at rank 2r against the old factors padded to 2r columns.
+  if (b->aug) LK(launch_aug_pad(d, n, st));
   LK(launch_tsgram<real>(b->g_psi1, n, b->pbmax, 0, st));
   LK(launch_chol(b->c_p1, d, n, st));
   LK(launch_fill<real>(b->f_psi, n, b->maxN, st));
@@ -1175,6 +1228,13 @@ static int enqueue_post(Batch *b) {
     LK(launch_svd(d, n, b->svd_mode, st));
     LK((launch_apply<double, double>(b->a_wv, n, b->maxK, b->rmax, st)));
     if (b->svd_mode == 1) LK(launch_sign(d, n, b->maxK, st));
+  }
+  if (b->aug) {
+    // SVD of the 2r x 2r S, truncation to the r largest singular values,
+    // W0 <- W V (the last r columns zero); X0 <- X^ U in step 9
+    LK(launch_svd(d, n, 2, st));
+    LK(launch_aug_trunc(d, n, st));
+    LK((launch_apply<double, double>(b->a_cw, n, b->maxK, b->rmax, st)));
   }
   // step 9
   LK(launch_tupdate<real>(d, n, b->maxN, b->rmax, st));
@@ -1239,7 +1299,7 @@ static int run_steps(Batch *b, int nsteps) {
   }
   for (auto *h : b->hs) {
     h->steps += nsteps;
-    h->canonical = b->svd_mode == 1;
+    h->canonical = b->svd_mode == 1 || b->aug;  // the augmented step ends on the SVD of S
     h->kernel_launches += (int64_t)nsteps * b->kernels_per_step;
     CK(cudaMemcpyAsync(h->h_status, h->inst.status, sizeof(int), cudaMemcpyDeviceToHost, b->st));
   }
@@ -1283,6 +1343,7 @@ static int check_handles(dlr_handle *const *hs, int n) {
     if (hs[i]->mixed != hs[0]->mixed) return fail(DLR_EINVAL, "mixed precisions in one batch");
     if (hs[i]->st != hs[0]->st) return fail(DLR_EINVAL, "handles on different streams");
     if (hs[i]->sn != hs[0]->sn) return fail(DLR_EINVAL, "SN and DLR handles in one batch");
+    if (hs[i]->aug != hs[0]->aug) return fail(DLR_EINVAL, "augmented and plain handles in one batch");
     const int s = *hs[i]->h_status;
     if (s != DLR_OK) return fail(s, "handle %d: %s", i, status_name(s));
   }
@@ -1454,7 +1515,7 @@ int dlr_set_T(dlr_handle *h, const double *in, int32_t in_on_device) {
 // unchanged.  Steps with pivoted-QR selection keep S general, because that
 // selection depends only on span W.
 static int canonicalize(dlr_handle *h) {
-  if (h->canonical) return DLR_OK;
+  if (h->canonical || h->aug) return DLR_OK;  // augmented factors are canonical after a step
   int rc;
   if (!h->own_batch && (rc = build_batch(&h, 1, &h->own_batch))) return rc;
   Batch *b = h->own_batch;

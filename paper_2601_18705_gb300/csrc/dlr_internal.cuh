@@ -107,6 +107,13 @@ struct Inst {
   // small)
   int method;
   const double *gamma_ext;
+  // augmented step (rank-2r basis truncated back to rank r): in the rank-r
+  // instance aug_x0 is where step 3 copies X0 (the second half of the
+  // [Psi, X0] input of step 5); in the rank-2r instance aug_r = r and S0_r is
+  // the rank-r S0 that the truncation writes
+  int aug_r;
+  void *aug_x0;
+  double *S0_r;
 };
 
 // Per-cell coefficients of the Newton-linearised step (Section 2.2, in the

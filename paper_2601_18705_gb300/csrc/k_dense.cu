@@ -68,6 +68,12 @@ __global__ void __launch_bounds__(256) k_coeff_recon(const Inst *__restrict__ in
     s0[(size_t)I.N * j + c] = qr + icdt * p;
     phi += gam[j] * p;
   }
+  if (I.aug_x0) {  // augmented step: X0 beside Psi as the input of step 5
+    real *xa = as<real>(I.aug_x0);
+#pragma unroll
+    for (int k = 0; k < RB; ++k)
+      if (k < r) xa[(size_t)I.N * k + c] = x[k];
+  }
   as<real>(I.phi0)[c] = phi;
   as<real>(I.sphi)[c] = ss4 * phi;
 }

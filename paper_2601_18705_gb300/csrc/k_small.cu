@@ -798,6 +798,71 @@ __global__ void __launch_bounds__(256) k_svd(const Inst *__restrict__ insts, int
   }
 }
 
+// ------------------------------------------------------------------
+// augmented step (rank-2r basis truncated back to rank r)
+// ------------------------------------------------------------------
+// Before the rank-2r steps: S0 (2r x 2r) = [[S0_r, 0], [0, 0]] (X0 and W0 are
+// stored with 2r columns whose last r stay zero).
+__global__ void __launch_bounds__(256) k_aug_pad(const Inst *__restrict__ insts) {
+  pdl_wait();
+  pdl_trigger();
+  const Inst &I = insts[blockIdx.x];
+  const int m = I.r, r = I.aug_r;
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int i = e % m, j = e / m;
+    I.S0[e] = (i < r && j < r) ? I.S0_r[i + r * j] : 0.0;
+  }
+}
+
+// After the SVD S = U Sigma V^T of the 2r x 2r S (k_svd mode 2): keep the r
+// largest singular values.  With b = W^T w (W the step-8 angular basis),
+// phi of the truncated factors is X^ (U_r Sigma_r V_r^T b): that vector goes
+// to vphi for the temperature kernel; the columns r..2r-1 of U and V are
+// zeroed, so the rotations X0 <- X^ U and W0 <- W V leave them zero; S0 and
+// S0_r become diag(Sigma_r).
+__global__ void __launch_bounds__(256) k_aug_trunc(const Inst *__restrict__ insts) {
+  pdl_wait();
+  pdl_trigger();
+  const Inst &I = insts[blockIdx.x];
+  if (*I.status != kOk) return;
+  const int m = I.r, r = I.aug_r, K = I.K;
+  __shared__ double b[32], y[32], sg[32];
+  double *U = I.small + I.lay.U, *V = I.small + I.lay.V;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = wid; j < m; j += nw) {
+    double t = 0.0;
+    for (int k = lane; k < K; k += 32) t += I.W0[(size_t)K * j + k] * I.w[k];
+    t = warp_sum(t);
+    if (lane == 0) b[j] = t;
+  }
+  if (threadIdx.x < m) sg[threadIdx.x] = I.S0[threadIdx.x * (m + 1)];
+  __syncthreads();
+  if (threadIdx.x < r) {
+    double t = 0.0;
+    for (int j = 0; j < m; ++j) t += V[j + m * threadIdx.x] * b[j];
+    y[threadIdx.x] = sg[threadIdx.x] * t;
+  }
+  __syncthreads();
+  if (threadIdx.x < m) {
+    double t = 0.0;
+    for (int i = 0; i < r; ++i) t += U[threadIdx.x + m * i] * y[i];
+    I.small[I.lay.vphi + threadIdx.x] = t;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int i = e % m, j = e / m;
+    if (j >= r) {
+      U[e] = 0.0;
+      V[e] = 0.0;
+    }
+    I.S0[e] = (i == j && i < r) ? sg[i] : 0.0;
+  }
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int i = e % r, j = e / r;
+    I.S0_r[e] = (i == j) ? sg[i] : 0.0;
+  }
+}
+
 // Sign of W columns: the entry of largest magnitude (tie rule) made positive;
 // the same flip is applied to U (and so to X in the temperature kernel).
 __global__ void __launch_bounds__(256) k_sign(const Inst *__restrict__ insts) {
@@ -875,6 +940,14 @@ cudaError_t launch_svd(const Inst *d, int n, int mode, cudaStream_t st) {
 }
 cudaError_t launch_sign(const Inst *d, int n, int maxK, cudaStream_t st) {
   return launch_pdl(k_sign, dim3(n), dim3(256), (size_t)maxK * sizeof(double), st, d);
+}
+
+cudaError_t launch_aug_pad(const Inst *d, int n, cudaStream_t st) {
+  return launch_pdl(k_aug_pad, dim3(n), dim3(256), 0, st, d);
+}
+
+cudaError_t launch_aug_trunc(const Inst *d, int n, cudaStream_t st) {
+  return launch_pdl(k_aug_trunc, dim3(n), dim3(256), 0, st, d);
 }
 
 }  // namespace dlr

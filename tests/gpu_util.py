@@ -9,7 +9,7 @@ def rel_l2(a, b) -> float:
 
 
 def run_pair(case, precision, steps, *, orc, dlr, forced=None, si_fixed_iters=0, si_tol=None,
-             selection=0, start=None, allow_nonpositive=0, split=None):
+             selection=0, start=None, allow_nonpositive=0, split=None, augment=0):
     """Runs the oracle and the GPU solver side by side from the same state.
     Returns per-step (T error, psi error, oracle idx, gpu idx) and both states.
     When the GPU picks different angles than the oracle (a near-tie), the
@@ -20,7 +20,7 @@ def run_pair(case, precision, steps, *, orc, dlr, forced=None, si_fixed_iters=0,
     if si_fixed_iters:
         kw["si_fixed_iters"] = si_fixed_iters
     spec = dlr.problem_from_case(case, precision=precision, selection=selection,
-                                 allow_nonpositive=allow_nonpositive, **kw)
+                                 allow_nonpositive=allow_nonpositive, augment=augment, **kw)
     if si_tol is not None:
         spec.si_tol = si_tol
     T = case["T0"].reshape(-1).copy()
@@ -36,13 +36,15 @@ def run_pair(case, precision, steps, *, orc, dlr, forced=None, si_fixed_iters=0,
             dlr.set_split([s], split)
         for _ in range(steps):
             X1, S1, W1, T1, res = orc.dlr_step(p, X, S, W, T, selection=selection,
-                                               si_fixed_iters=si_fixed_iters, si_tol=tol_o)
+                                               si_fixed_iters=si_fixed_iters, si_tol=tol_o,
+                                               augment=augment)
             assert res.rc == 0, res
             s.step(1)
             gidx = s.selected()
             if sorted(gidx.tolist()) != sorted(res.idx.tolist()):
                 X1, S1, W1, T1, res2 = orc.dlr_step(p, X, S, W, T, forced_idx=gidx,
-                                                    si_fixed_iters=si_fixed_iters, si_tol=tol_o)
+                                                    si_fixed_iters=si_fixed_iters, si_tol=tol_o,
+                                                    augment=augment)
                 assert res2.rc == 0
             X, S, W, T = X1, S1, W1, T1
             Tg = s.T()
