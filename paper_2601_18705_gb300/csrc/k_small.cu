@@ -670,7 +670,7 @@ __global__ void __launch_bounds__(256) k_lstep_back(const Inst *__restrict__ ins
 // ------------------------------------------------------------------
 // mode 0: S0 <- S (no SVD; U = V = I), vphi; mode 1: SVD as well;
 // mode 2: SVD of the stored S0 (canonical factors on request).
-__global__ void __launch_bounds__(256) k_svd(const Inst *__restrict__ insts, int mode) {
+__global__ void __launch_bounds__(512) k_svd(const Inst *__restrict__ insts, int mode) {
   pdl_wait();
   pdl_trigger();
   const Inst &I = insts[blockIdx.x];
@@ -707,9 +707,15 @@ __global__ void __launch_bounds__(256) k_svd(const Inst *__restrict__ insts, int
     return;
   }
   // one-sided Jacobi; each sweep visits all pairs in n-1 rounds of n/2
-  // disjoint pairs (circle method), one warp per pair
+  // disjoint pairs (circle method), one warp per pair.  A pair counts as
+  // converged when |ga| <= 1e-14 sqrt(al be) or |ga| <= 1e-16 ||S||_F^2 (the
+  // second keeps columns at rounding-noise level from rotating forever).
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int n = (r + 1) & ~1;
+  __shared__ double red[32];
+  double f2 = 0.0;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) f2 += Uw[e] * Uw[e];
+  const double floor_ga = 1e-16 * block_sum(f2, red);
   (void)lane;
   for (int sweep = 0; sweep < 30; ++sweep) {
     if (threadIdx.x == 0) rot_s = 0;
@@ -724,11 +730,17 @@ __global__ void __launch_bounds__(256) k_svd(const Inst *__restrict__ insts, int
         const double ui = lane < r ? Uw[lane + r * i] : 0.0;
         const double uj = lane < r ? Uw[lane + r * j] : 0.0;
         const double al = warp_sum(ui * ui), be = warp_sum(uj * uj), ga = warp_sum(ui * uj);
-        if (ga == 0.0 || fabs(ga) <= 1e-14 * sqrt(al * be)) continue;
+        // converged pair: |ga| <= 1e-14 sqrt(al be), tested on squares
+        if (fabs(ga) <= floor_ga || ga * ga <= 1e-28 * (al * be)) continue;
         if (lane == 0) rot_s = 1;
-        const double zeta = (be - al) / (2.0 * ga);
-        const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+        // t = tan(theta), the smaller root of ga t^2 + (be - al) t - ga = 0,
+        // written with one square root and one division (each several
+        // hundred cycles in FP64 on this GPU), cos(theta) by a reciprocal
+        // square root; t = 1 when be = al
+        const double d = be - al;
+        const double t = d == 0.0 ? 1.0
+                                  : (d > 0.0 ? 2.0 * ga : -2.0 * ga) / (fabs(d) + sqrt(d * d + 4.0 * ga * ga));
+        const double cs = rsqrt(1.0 + t * t), sn = cs * t;
         if (lane < r) {
           Uw[lane + r * i] = cs * ui - sn * uj;
           Uw[lane + r * j] = sn * ui + cs * uj;
@@ -765,9 +777,11 @@ __global__ void __launch_bounds__(256) k_svd(const Inst *__restrict__ insts, int
     U[k + r * j] = (s > 1e-300 && s > 1e-15 * smax) ? Uw[k + r * o] / s : 0.0;
   }
   __syncthreads();
-  // complete U columns of zero singular values (Gram-Schmidt on unit vectors)
+  // complete U columns of zero singular values (Gram-Schmidt on unit
+  // vectors); the augmented step drops the columns from aug_r on
   if (threadIdx.x == 0) {
-    for (int j = 0; j < r; ++j) {
+    const int keep = I.aug_r > 0 ? I.aug_r : r;
+    for (int j = 0; j < keep; ++j) {
       double t = 0.0;
       for (int k = 0; k < r; ++k) t += U[k + r * j] * U[k + r * j];
       if (t > 0.5) continue;
@@ -936,7 +950,7 @@ cudaError_t launch_lstep(const Inst *d, int n, int r_max, int blocks, int maxK, 
   return launch_pdl(k_lstep_back, dim3((maxK * r_max + 255) / 256, n), dim3(256), 0, st, d);
 }
 cudaError_t launch_svd(const Inst *d, int n, int mode, cudaStream_t st) {
-  return launch_pdl(k_svd, dim3(n), dim3(256), 0, st, d, mode);
+  return launch_pdl(k_svd, dim3(n), dim3(512), 0, st, d, mode);
 }
 cudaError_t launch_sign(const Inst *d, int n, int maxK, cudaStream_t st) {
   return launch_pdl(k_sign, dim3(n), dim3(256), (size_t)maxK * sizeof(double), st, d);
