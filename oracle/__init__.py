@@ -56,7 +56,8 @@ class _Problem(C.Structure):
                 ("ly", C.c_double), ("n_polar", C.c_int), ("n_azim", C.c_int),
                 ("dt", C.c_double), ("c", C.c_double), ("a_rad", C.c_double),
                 ("sigma", _dp), ("rho_cv", _dp),
-                ("psi_edge", C.c_double * 4)]
+                ("psi_edge", C.c_double * 4), ("sigma_texp", C.c_double),
+                ("cv_texp", C.c_double), ("T_ref", C.c_double)]
 
 
 class _Opts(C.Structure):
@@ -137,6 +138,9 @@ class Problem:
     lx: float = 1.0
     ly: float = 1.0
     psi_edge: tuple = (0.0, 0.0, 0.0, 0.0)
+    sigma_texp: float = 0.0   # sigma(T) = sigma (T/T_ref)^-sigma_texp (reading R16)
+    cv_texp: float = 0.0      # rho c_v(T) = rho_cv (T/T_ref)^cv_texp
+    T_ref: float = 1.0
     _keep: list = field(default_factory=list, repr=False)
 
     @property
@@ -163,6 +167,7 @@ class Problem:
         s.n_polar, s.n_azim = self.n_polar, self.n_azim
         s.dt, s.c, s.a_rad = self.dt, self.c, self.a_rad
         s.sigma, s.rho_cv = _ptr(sig), _ptr(rho)
+        s.sigma_texp, s.cv_texp, s.T_ref = self.sigma_texp, self.cv_texp, self.T_ref
         for e in range(4):
             s.psi_edge[e] = float(self.psi_edge[e])
         return s

@@ -30,6 +30,10 @@
  *       rank 2r (P = <X^, X0> is 2r x r), and the 2r x 2r S = U Sigma V^T is
  *       truncated to its r largest singular values (X = X^ U_r, S = Sigma_r,
  *       W = W V_r, signs as in the canonical form) before step 9.
+ *   R16 temperature-dependent materials (no law is given): per-cell power
+ *       laws sigma(T) = sigma (T/T_ref)^-n_s, rho c_v(T) = rho_cv (T/T_ref)^n_c,
+ *       taken at the step's T0 as Eq. (T, backward Euler) prescribes (the
+ *       transport opacity too: sigma_t = sigma(T0) + 1/(c dt)).
  */
 #include "oracle.h"
 
@@ -53,6 +57,18 @@ static double planck_deriv(double a_rad, double c, double T) {
   return a_rad * c * T * T * T / ORACLE_PI;
 }
 
+/* sigma(T0) and rho c_v(T0) of cell c (Section 2.1, taken explicitly at
+ * T0 as in Eq. T backward Euler; reading R16 for the law). */
+static double tref(const oracle_problem *p) { return p->T_ref > 0 ? p->T_ref : 1.0; }
+double oracle_sigma_at(const oracle_problem *p, int c, double T0) {
+  if (p->sigma_texp == 0.0) return p->sigma[c];
+  return p->sigma[c] * pow(T0 / tref(p), -p->sigma_texp);
+}
+double oracle_rhocv_at(const oracle_problem *p, int c, double T0) {
+  if (p->cv_texp == 0.0) return p->rho_cv[c];
+  return p->rho_cv[c] * pow(T0 / tref(p), p->cv_texp);
+}
+
 /* Section 2.2: Newton linearisation of the backward-Euler temperature
  * equation about T0 gives the pseudo-scattering sigma_s (Eq. effective
  * scattering) and the source q (Eq. effective source; reading R1). */
@@ -60,10 +76,10 @@ void oracle_coefficients(const oracle_problem *p, const double *T0,
                          double *sigma_s, double *q, double *B0, double *D) {
   int Nx = p->nx * p->ny;
   for (int c = 0; c < Nx; c++) {
-    double sig = p->sigma[c];
+    double sig = oracle_sigma_at(p, c, T0[c]);
     double B = oracle_planck(p->a_rad, p->c, T0[c]);
     double dB = planck_deriv(p->a_rad, p->c, T0[c]);
-    double Dc = p->rho_cv[c] + 4.0 * ORACLE_PI * p->dt * sig * dB;
+    double Dc = oracle_rhocv_at(p, c, T0[c]) + 4.0 * ORACLE_PI * p->dt * sig * dB;
     sigma_s[c] = sig * (4.0 * ORACLE_PI * p->dt * sig * dB) / Dc;
     q[c] = sig * B - sig * dB * (4.0 * ORACLE_PI * p->dt * sig * B) / Dc;
     if (B0) B0[c] = B;
@@ -839,7 +855,7 @@ int oracle_collocation(const oracle_problem *p, int r, const double *X0,
   double *L0 = (double *)malloc(sizeof(double) * r * NOm);
   oracle_quadrature(p->n_polar, p->n_azim, ox, oy, oz, w);
   oracle_coefficients(p, T0, sig_s, q, NULL, NULL);
-  for (int c = 0; c < Nx; c++) sig_t[c] = p->sigma[c] + 1.0 / (p->c * p->dt);
+  for (int c = 0; c < Nx; c++) sig_t[c] = oracle_sigma_at(p, c, T0[c]) + 1.0 / (p->c * p->dt);
   for (int i = 0; i < r; i++)
     for (int j = 0; j < r; j++) WLU[i + r * j] = W0[idx[i] + (size_t)NOm * j];
   for (int j = 0; j < r; j++)
@@ -894,7 +910,7 @@ int oracle_dlr_step(const oracle_problem *p, int r, double *X, double *S,
   double *D = (double *)malloc(sizeof(double) * Nx);
   double *sig_t = (double *)malloc(sizeof(double) * Nx);
   oracle_coefficients(p, T, sig_s, q, B0, D);
-  for (int c = 0; c < Nx; c++) sig_t[c] = p->sigma[c] + inv_cdt;
+  for (int c = 0; c < Nx; c++) sig_t[c] = oracle_sigma_at(p, c, T[c]) + inv_cdt;
 
   /* Step 2: select r angles from W0 (Section 4.2; reading R8). */
   int *idx = (int *)malloc(sizeof(int) * r);
@@ -1037,7 +1053,7 @@ int oracle_dlr_step(const oracle_problem *p, int r, double *X, double *S,
     double *Tn = (double *)malloc(sizeof(double) * Nx);
     double minT = INFINITY, minphi = INFINITY;
     for (int c = 0; c < Nx; c++) {
-      Tn[c] = T[c] + p->dt * p->sigma[c] * (phin2[c] - 4.0 * ORACLE_PI * B0[c]) / D[c];
+      Tn[c] = T[c] + p->dt * oracle_sigma_at(p, c, T[c]) * (phin2[c] - 4.0 * ORACLE_PI * B0[c]) / D[c];
       if (Tn[c] < minT) minT = Tn[c];
       if (phin2[c] < minphi) minphi = phin2[c];
     }
@@ -1121,7 +1137,7 @@ int oracle_sn_step(const oracle_problem *p, double *psi, double *T,
   double *psi0 = (double *)malloc(sizeof(double) * Nx * NOm);
   memcpy(psi0, psi, sizeof(double) * Nx * NOm);
   oracle_coefficients(p, T, sig_s, q, B0, D);
-  for (int c = 0; c < Nx; c++) sig_t[c] = p->sigma[c] + inv_cdt;
+  for (int c = 0; c < Nx; c++) sig_t[c] = oracle_sigma_at(p, c, T[c]) + inv_cdt;
   for (int k = 0; k < NOm; k++)
     for (int c = 0; c < Nx; c++) phi[c] += w[k] * psi0[c + (size_t)Nx * k];
   int iters = 0, converged = 0;
@@ -1143,7 +1159,7 @@ int oracle_sn_step(const oracle_problem *p, double *psi, double *T,
     if (dmax <= si_tol * pmax) { converged = 1; break; }
   }
   for (int c = 0; c < Nx; c++)
-    T[c] = T[c] + p->dt * p->sigma[c] * (phi[c] - 4.0 * ORACLE_PI * B0[c]) / D[c];
+    T[c] = T[c] + p->dt * oracle_sigma_at(p, c, T[c]) * (phi[c] - 4.0 * ORACLE_PI * B0[c]) / D[c];
   if (phi_out) memcpy(phi_out, phi, sizeof(double) * Nx);
   if (outflow && inflow) {
     full_ctx g = {psi, Nx};

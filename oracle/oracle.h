@@ -33,6 +33,11 @@ typedef struct {
   const double *sigma;  /* Nx absorption opacity */
   const double *rho_cv; /* Nx heat capacity */
   double psi_edge[4];  /* isotropic inflow value of psi per edge; 0 = vacuum */
+  /* temperature dependence (reading R16): sigma(T) = sigma (T/T_ref)^-sigma_texp,
+   * rho c_v(T) = rho_cv (T/T_ref)^cv_texp, both taken at the step's T0
+   * (explicit, Eq. T backward Euler); exponents 0 = constant; T_ref <= 0
+   * means 1 */
+  double sigma_texp, cv_texp, T_ref;
 } oracle_problem;
 
 typedef struct {
@@ -59,6 +64,10 @@ typedef struct {
 
 /* Planck function B(T) = a c T^4 / (4 pi) (reading of the undefined B). */
 double oracle_planck(double a_rad, double c, double T);
+
+/* sigma(T0) and rho c_v(T0) of cell c (reading R16). */
+double oracle_sigma_at(const oracle_problem *p, int c, double T0);
+double oracle_rhocv_at(const oracle_problem *p, int c, double T0);
 
 /* Product quadrature: Gauss-Legendre mu ascending x equispaced azimuths. */
 void oracle_quadrature(int n_polar, int n_azim, double *ox, double *oy,

@@ -158,6 +158,36 @@ def test_infinite_medium_recurrence_and_equilibrium(orc, r):
     assert abs(rho * Tz + phiz / p.c - E0) < 1e-13 * E0
 
 
+@pytest.mark.parametrize("n_s,n_c", [(3.0, 0.0), (2.0, 1.0)])
+def test_infinite_medium_with_temperature_dependent_materials(orc, n_s, n_c):
+    """Reading R16: sigma(T) = sigma (T/T_ref)^-n_s and rho c_v(T) = rho_cv
+    (T/T_ref)^n_c taken at the step's T0 everywhere (coefficients, sweep
+    opacity, temperature update): the uniform medium follows the 0-D
+    backward-Euler recurrence with the materials of each step's T0."""
+    nx, ny, sig0, rho0, T0, dt, Tr = 5, 4, 10.0, 0.5, 0.5, 0.02, 0.8
+    p = orc.Problem(nx, ny, 4, 8, np.full(nx * ny, sig0), np.full(nx * ny, rho0), dt=dt,
+                    sigma_texp=n_s, cv_texp=n_c, T_ref=Tr)
+    X, S, W = orc.initial_factors(p, np.full(nx * ny, T0), 2)
+    T = np.full(nx * ny, T0)
+    Tz, phiz = T0, 4 * np.pi * orc.planck(p.a_rad, p.c, T0)
+    for step in range(40):
+        sig, rho = sig0 * (Tz / Tr) ** -n_s, rho0 * (Tz / Tr) ** n_c
+        Tz, phiz = _zero_d_step(Tz, phiz, sig, rho, dt, p.c, p.a_rad)
+        p.psi_edge = (phiz / (4 * np.pi),) * 4
+        X, S, W, T, res = orc.dlr_step(p, X, S, W, T)
+        assert res.rc == 0
+        np.testing.assert_allclose(T, Tz, rtol=1e-12)
+        np.testing.assert_allclose(res.phi, phiz, rtol=1e-12)
+    # the same law with zero exponents is the constant-material step
+    q = orc.Problem(nx, ny, 4, 8, np.full(nx * ny, sig0), np.full(nx * ny, rho0), dt=dt,
+                    sigma_texp=0.0, cv_texp=0.0, T_ref=Tr)
+    r = orc.Problem(nx, ny, 4, 8, np.full(nx * ny, sig0), np.full(nx * ny, rho0), dt=dt)
+    q.psi_edge = r.psi_edge = p.psi_edge
+    a = orc.dlr_step(q, X, S, W, T)
+    b = orc.dlr_step(r, X, S, W, T)
+    assert np.array_equal(a[3], b[3])
+
+
 def test_equilibrium_preserved(orc):
     c = workloads.small_case(8, 6, 4, 4, 8, seed=2, T0=0.7)
     p = oracle_problem(c, psi_edge=[0] * 4)
