@@ -108,6 +108,11 @@ typedef struct dlr_problem {
                             DLR_METHOD_SN (rank and selection ignored; the
                             state is psi at every cell and angle, starting
                             from the isotropic equilibrium psi = B(T0)) */
+  double sigma_texp;     /* temperature-dependent materials, taken at the */
+  double cv_texp;        /* step's T0 (Eq. T backward Euler; explicit):    */
+  double T_ref;          /* sigma(T) = sigma (T/T_ref)^-sigma_texp and
+                            rho c_v(T) = rho_cv (T/T_ref)^cv_texp; exponents
+                            0 = constant materials; T_ref <= 0 means 1 */
 } dlr_problem;
 
 /* Device memory and stream supplied by the caller (e.g. PyTorch). */

@@ -50,6 +50,9 @@ class ProblemSpec:
     allow_nonpositive: int = 0
     method: int = DLR_METHOD_DLR
     augment: int = 0     # 1: augmented step (rank-2r basis truncated back to rank r)
+    sigma_texp: float = 0.0  # sigma(T) = sigma (T/T_ref)^-sigma_texp, at each step's T0
+    cv_texp: float = 0.0     # rho c_v(T) = rho_cv (T/T_ref)^cv_texp
+    T_ref: float = 1.0
 
     def cstruct(self):
         keep = [_f64(self.sigma), _f64(self.rho_cv), _f64(self.T0)]
@@ -69,6 +72,7 @@ class ProblemSpec:
         p.si_tol, p.si_max_iter, p.si_fixed_iters = self.si_tol, self.si_max_iter, self.si_fixed_iters
         p.allow_nonpositive = 1 if self.allow_nonpositive else 0
         p.method = self.method
+        p.sigma_texp, p.cv_texp, p.T_ref = self.sigma_texp, self.cv_texp, self.T_ref
         return p, keep
 
 
@@ -82,7 +86,9 @@ def problem_from_case(case: dict, precision=None, **kw) -> ProblemSpec:
                        rho_cv=case["rho_cv"], T0=case["T0"], T_edge=tuple(case["T_edge"]),
                        lx=case.get("lx", 1.0), ly=case.get("ly", 1.0), dt=case["dt"],
                        c=case["c"], a_rad=case["a_rad"], precision=prec,
-                       si_max_iter=case.get("si_max_iter", 0))
+                       si_max_iter=case.get("si_max_iter", 0),
+                       sigma_texp=case.get("sigma_texp", 0.0), cv_texp=case.get("cv_texp", 0.0),
+                       T_ref=case.get("T_ref", 1.0))
     for k, v in kw.items():
         setattr(spec, k, v)
     return spec

@@ -34,7 +34,8 @@ class DlrProblem(C.Structure):
                 ("T0", C.POINTER(C.c_double)), ("T_edge", C.c_double * 4),
                 ("precision", C.c_int32), ("selection", C.c_int32), ("augment", C.c_int32),
                 ("si_tol", C.c_double), ("si_max_iter", C.c_int32), ("si_fixed_iters", C.c_int32),
-                ("allow_nonpositive", C.c_int32), ("method", C.c_int32)]
+                ("allow_nonpositive", C.c_int32), ("method", C.c_int32),
+                ("sigma_texp", C.c_double), ("cv_texp", C.c_double), ("T_ref", C.c_double)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)

@@ -440,6 +440,8 @@ static int validate(const dlr_problem *p) {
   const long long N = (long long)p->nx * p->ny, K = (long long)p->n_polar * p->n_azim;
   if (N > (1ll << 30) || K > 8192) return fail(DLR_EINVAL, "mesh or quadrature too large");
   if (p->method != DLR_METHOD_DLR && p->method != DLR_METHOD_SN) return fail(DLR_EINVAL, "bad method");
+  if (!std::isfinite(p->sigma_texp) || !std::isfinite(p->cv_texp) || !std::isfinite(p->T_ref))
+    return fail(DLR_EINVAL, "material exponents and T_ref must be finite");
   const bool sn = p->method == DLR_METHOD_SN;
   if (sn && N * K > (1ll << 34)) return fail(DLR_EINVAL, "nx*ny*NOm too large for a full-rank state");
   if (!sn && (p->rank < 1 || p->rank > kMaxRank || p->rank > N || p->rank > K))
@@ -500,6 +502,9 @@ static void fill_common(dlr_handle *h, const dlr_problem *problem) {
     I.psi_edge[e] = problem->T_edge[e] >= 0 ? planck(problem->a_rad, problem->c, problem->T_edge[e]) : 0.0;
   I.method = problem->method;
   I.gamma_ext = nullptr;
+  I.sig_texp = problem->sigma_texp;
+  I.cv_texp = problem->cv_texp;
+  I.T_ref = problem->T_ref > 0 ? problem->T_ref : 1.0;
 }
 
 // Full-rank SN handle: the per-cell state of Algorithm 1's sweeps, psi and

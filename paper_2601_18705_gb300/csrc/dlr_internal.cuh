@@ -114,18 +114,29 @@ struct Inst {
   int aug_r;
   void *aug_x0;
   double *S0_r;
+  // temperature-dependent materials, taken at the step's T0:
+  // sigma(T) = sigma (T/T_ref)^-sig_texp, rho c_v(T) = rho_cv (T/T_ref)^cv_texp
+  double sig_texp, cv_texp, T_ref;
 };
+
+__device__ __forceinline__ double sigma_at(const Inst &I, int c, double T0) {
+  return I.sig_texp == 0.0 ? I.sigma[c] : I.sigma[c] * pow(T0 / I.T_ref, -I.sig_texp);
+}
+__device__ __forceinline__ double rhocv_at(const Inst &I, int c, double T0) {
+  return I.cv_texp == 0.0 ? I.rho_cv[c] : I.rho_cv[c] * pow(T0 / I.T_ref, I.cv_texp);
+}
 
 // Per-cell coefficients of the Newton-linearised step (Section 2.2, in the
 // backward-Euler form: D = rho c_v + 4 pi dt sigma B'(T0), effective
 // scattering sigma_s = sigma 4 pi dt sigma B' / D, effective source
 // q = sigma B0 - sigma B' 4 pi dt sigma B0 / D, with B = a c T^4 / (4 pi)).
 struct CellCoef {
-  double B, D, ss, q;
+  double B, D, ss, q, sig;  // sig = sigma(T0)
 };
 __device__ __forceinline__ CellCoef cell_coefficients(const Inst &I, int c) {
-  const double T0 = I.T[c], sig = I.sigma[c], rho = I.rho_cv[c];
+  const double T0 = I.T[c], sig = sigma_at(I, c, T0), rho = rhocv_at(I, c, T0);
   CellCoef k;
+  k.sig = sig;
   k.B = I.a_rad * I.c * T0 * T0 * T0 * T0 / (4.0 * kPi);
   const double dB = I.a_rad * I.c * T0 * T0 * T0 / kPi;
   const double g = 4.0 * kPi * I.dt * sig * dB;

@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(256) k_coeff_recon(const Inst *__restrict__ in
   const double q = cf.q;
   I.B0[c] = cf.B;
   I.D[c] = cf.D;
-  as<real>(I.sig_t)[c] = real(I.sigma[c] + I.inv_cdt);
+  as<real>(I.sig_t)[c] = real(cf.sig + I.inv_cdt);
   const real ss4 = real(cf.ss / (4.0 * kPi));
   as<real>(I.ss4)[c] = ss4;
   as<real>(I.q)[c] = real(q);
@@ -621,7 +621,7 @@ __global__ void __launch_bounds__(128) k_tupdate(const Inst *__restrict__ insts)
     X0[(size_t)I.N * j + c] = v;
   }
   const double T0 = I.T[c];
-  const double T = T0 + I.dt * I.sigma[c] * ((double)phi - 4.0 * kPi * I.B0[c]) / I.D[c];
+  const double T = T0 + I.dt * sigma_at(I, c, T0) * ((double)phi - 4.0 * kPi * I.B0[c]) / I.D[c];
   I.T[c] = T;
   if (!(T > 0.0)) {
     atomicAdd(I.nonpos, 1);

@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(256) k_sn_prep(const Inst *__restrict__ insts)
   const CellCoef cf = cell_coefficients(I, c);
   I.B0[c] = cf.B;
   I.D[c] = cf.D;
-  as<real>(I.sig_t)[c] = real(I.sigma[c] + I.inv_cdt);
+  as<real>(I.sig_t)[c] = real(cf.sig + I.inv_cdt);
   const real ss4 = real(cf.ss / (4.0 * kPi));
   as<real>(I.ss4)[c] = ss4;
   as<real>(I.q)[c] = real(cf.q);
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(256) k_sn_tupdate(const Inst *__restrict__ ins
   const int last = *I.iters - 1;
   const real *phi = as_c<real>((last & 1) ? I.phi0 : I.phi1);
   const double T0 = I.T[c];
-  const double T = T0 + I.dt * I.sigma[c] * ((double)phi[c] - 4.0 * kPi * I.B0[c]) / I.D[c];
+  const double T = T0 + I.dt * sigma_at(I, c, T0) * ((double)phi[c] - 4.0 * kPi * I.B0[c]) / I.D[c];
   I.T[c] = T;
   if (!(T > 0.0)) {
     atomicAdd(I.nonpos, 1);

@@ -17,7 +17,9 @@ def oracle_problem(case, psi_edge=None):
     import oracle
     p = oracle.Problem(case["nx"], case["ny"], case["n_polar"], case["n_azim"],
                        case["sigma"], case["rho_cv"], dt=case["dt"], c=case["c"],
-                       a_rad=case["a_rad"], lx=case.get("lx", 1.0), ly=case.get("ly", 1.0))
+                       a_rad=case["a_rad"], lx=case.get("lx", 1.0), ly=case.get("ly", 1.0),
+                       sigma_texp=case.get("sigma_texp", 0.0), cv_texp=case.get("cv_texp", 0.0),
+                       T_ref=case.get("T_ref", 1.0))
     if psi_edge is not None:
         p.psi_edge = tuple(psi_edge)
     else:
