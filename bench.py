@@ -58,6 +58,7 @@ def parse():
                     choices=["lattice32", "checker256", "lognormal1024", "batch64", "served"])
     ap.add_argument("--requests", type=int, default=200, help="served: number of requests")
     ap.add_argument("--hbm-budget-gb", type=float, default=0.0, help="served: admission budget")
+    ap.add_argument("--max-active", type=int, default=48, help="served: requests stepped together")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the sweep-plan autotuner (default plan: splitting threshold 1)")
@@ -505,7 +506,7 @@ def run_served(args):
     from paper_2601_18705_gb300 import server
     reqs = [server.Request(rid=q["id"], arrival=t, case=workloads.materialize(q), steps=q["steps"])
             for t, q in workloads.served_requests(n=args.requests)]
-    srv = server.Server(max_active=48, hbm_budget=int(args.hbm_budget_gb * 2 ** 30))
+    srv = server.Server(max_active=args.max_active, hbm_budget=int(args.hbm_budget_gb * 2 ** 30))
     rep = srv.run(reqs, realtime=True)
     s = rep.summary()
     line = {"metric": METRIC, "value": s["cell_angle_updates_per_s"], "unit": METRIC, "n_gpus": 1,
@@ -514,7 +515,8 @@ def run_served(args):
             "data": "synthetic",
             "config": {"workload": f"served: {args.requests} requests, Poisson 20/s, sides "
                                    "U{128..1024}, ranks {8,16,32}, 50-200 steps, 16x32 angles",
-                       "precision": "mixed", "hbm_budget_gb": args.hbm_budget_gb},
+                       "precision": "mixed", "hbm_budget_gb": args.hbm_budget_gb,
+                       "max_active": args.max_active},
             "served": s}
     print(json.dumps(line))
 
