@@ -51,7 +51,7 @@ cudaError_t launch_select(const Inst *, int, int, cudaStream_t);
 cudaError_t launch_chol(const CholJob *, const Inst *, int, cudaStream_t);
 cudaError_t launch_proj_post(const Inst *, int, cudaStream_t);
 size_t lstep_angle_smem(int);
-cudaError_t launch_lstep(const Inst *, int, int, int, int, cudaStream_t);
+cudaError_t launch_lstep(const Inst *, int, int, int, int, int, cudaStream_t);
 cudaError_t launch_svd(const Inst *, int, int, cudaStream_t);
 cudaError_t launch_sign(const Inst *, int, int, cudaStream_t);
 cudaError_t launch_si_prep(const Inst *, int, SiCtl, cudaStream_t);
@@ -160,6 +160,7 @@ struct Batch {
   Inst *d_insts = nullptr;   // contiguous copies of the instances
   void *d_mem = nullptr;     // jobs, units, control
   int maxN = 0, maxK = 0, rmax = 0, pbmax = 1, pblmax = 1, lbmax = 1;
+  int rmask_pre = 0, rmask = 0;  // rank classes of steps 1-4 and of steps 5-10
   int nx_max = 0, bands_max = 0, si_grid = 0;
   SiCtl ctl{};
   SiUnit *d_units = nullptr;  // capacity units_cap
@@ -907,6 +908,8 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
     b->maxN = std::max(b->maxN, h->N);
     b->maxK = std::max(b->maxK, h->K);
     b->rmax = std::max(b->rmax, h->aug ? 2 * h->r : h->r);  // rank of steps 5-10
+    b->rmask |= rank_mask(h->aug ? 2 * h->r : h->r);
+    b->rmask_pre |= rank_mask(h->r);
     b->pbmax = std::max(b->pbmax, h->pb);
     b->pblmax = std::max(b->pblmax, h->pbl);
     b->lbmax = std::max(b->lbmax, h->lb);
@@ -1164,6 +1167,12 @@ static int refresh_batch(Batch *b) {
     CK(call);      \
     ++b->kcount;   \
   } while (0)
+// a launcher that launches one kernel per rank class in mask
+#define LKM(call, mask)                      \
+  do {                                       \
+    CK(call);                                \
+    b->kcount += __builtin_popcount(mask);   \
+  } while (0)
 
 template <typename real>
 static int enqueue_pre(Batch *b) {
@@ -1175,7 +1184,7 @@ static int enqueue_pre(Batch *b) {
     return DLR_OK;
   }
   LK(launch_select(d, n, b->sel_slice_max, b->st));
-  LK(launch_coeff_recon<real>(d, n, b->maxN, b->rmax, b->st));
+  LKM(launch_coeff_recon<real>(d, n, b->maxN, b->rmask_pre, b->st), b->rmask_pre);
   LK(launch_si_prep(d, n, b->ctl, b->st));
   return DLR_OK;
 }
@@ -1199,19 +1208,19 @@ static int enqueue_post(Batch *b) {
   LK(launch_fill<real>(b->f_psi, n, b->maxN, st));
   LK(launch_tsgram<real>(b->g_psire, n, b->pbmax, 0, st));
   LK(launch_chol(b->c_p1b, d, n, st));
-  LK((launch_apply<real, real>(b->a_psi, n, b->maxN, b->rmax, st)));
+  LKM((launch_apply<real, real>(b->a_psi, n, b->maxN, b->rmask, st)), b->rmask);
   LK(launch_tsgram<real>(b->g_x, n, b->pbmax, 0, st));
   LK(launch_chol(b->c_p2, d, n, st));
-  LK((launch_apply<real, real>(b->a_x2, n, b->maxN, b->rmax, st)));
+  LKM((launch_apply<real, real>(b->a_x2, n, b->maxN, b->rmask, st)), b->rmask);
   LK(launch_tsgram<real>(b->g_x3, n, b->pbmax, 0, st));
   LK(launch_chol(b->c_p3, d, n, st));
-  LK((launch_apply<real, real>(b->a_x3, n, b->maxN, b->rmax, st)));
+  LKM((launch_apply<real, real>(b->a_x3, n, b->maxN, b->rmask, st)), b->rmask);
   // steps 6-7: projections and the L-step
   LK(launch_project<real>(d, n, b->pbmax, b->rmax, st));
   LK(launch_reduce(b->r_proj, n, proj_count(b->rmax), st));
   LK(launch_proj_post(d, n, st));
-  LK(launch_lstep(d, n, b->rmax, b->lbmax, b->maxK, st));
-  b->kcount += 2;  // three kernels
+  LKM(launch_lstep(d, n, b->rmax, b->rmask, b->lbmax, b->maxK, st), b->rmask);
+  b->kcount += 2;  // and two more kernels
   // step 8: CholeskyQR of M = diag(sqrt w) L^T into Q (held in W0), S = M^T Q,
   // SVD of S, W0 <- diag(1/sqrt w) Q V
   if (b->lside_fused) {
@@ -1222,16 +1231,16 @@ static int enqueue_post(Batch *b) {
     LK(launch_fill<double>(b->f_l, n, b->maxK, st));
     LK(launch_tsgram<double>(b->g_lf, n, b->pblmax, 1, st));
     LK(launch_chol(b->c_l1b, d, n, st));
-    LK((launch_apply<double, double>(b->a_l1, n, b->maxK, b->rmax, st)));
+    LKM((launch_apply<double, double>(b->a_l1, n, b->maxK, b->rmask, st)), b->rmask);
     LK(launch_tsgram<double>(b->g_w, n, b->pblmax, 0, st));
     LK(launch_chol(b->c_l2, d, n, st));
-    LK((launch_apply<double, double>(b->a_w2, n, b->maxK, b->rmax, st)));
+    LKM((launch_apply<double, double>(b->a_w2, n, b->maxK, b->rmask, st)), b->rmask);
     LK(launch_tsgram<double>(b->g_w3, n, b->pblmax, 0, st));
     LK(launch_chol(b->c_l3, d, n, st));
-    LK((launch_apply<double, double>(b->a_w3, n, b->maxK, b->rmax, st)));
+    LKM((launch_apply<double, double>(b->a_w3, n, b->maxK, b->rmask, st)), b->rmask);
     LK(launch_tsgram<double>(b->g_cross, n, b->pblmax, 1, st));
     LK(launch_svd(d, n, b->svd_mode, st));
-    LK((launch_apply<double, double>(b->a_wv, n, b->maxK, b->rmax, st)));
+    LKM((launch_apply<double, double>(b->a_wv, n, b->maxK, b->rmask, st)), b->rmask);
     if (b->svd_mode == 1) LK(launch_sign(d, n, b->maxK, st));
   }
   if (b->aug) {
@@ -1239,10 +1248,10 @@ static int enqueue_post(Batch *b) {
     // W0 <- W V (the last r columns zero); X0 <- X^ U in step 9
     LK(launch_svd(d, n, 2, st));
     LK(launch_aug_trunc(d, n, st));
-    LK((launch_apply<double, double>(b->a_cw, n, b->maxK, b->rmax, st)));
+    LKM((launch_apply<double, double>(b->a_cw, n, b->maxK, b->rmask, st)), b->rmask);
   }
   // step 9
-  LK(launch_tupdate<real>(d, n, b->maxN, b->rmax, st));
+  LKM(launch_tupdate<real>(d, n, b->maxN, b->rmask, st), b->rmask);
   return DLR_OK;
 }
 
@@ -1527,10 +1536,10 @@ static int canonicalize(dlr_handle *h) {
   rc = refresh_batch(b);
   if (rc) return rc;
   CK(launch_svd(b->d_insts, 1, 2, h->st));
-  CK((launch_apply<double, double>(b->a_cw, 1, h->K, h->r, h->st)));
+  CK((launch_apply<double, double>(b->a_cw, 1, h->K, rank_mask(h->r), h->st)));
   CK(launch_sign(b->d_insts, 1, h->K, h->st));
-  if (h->mixed) CK((launch_apply<float, float>(b->a_cx, 1, h->N, h->r, h->st)));
-  else CK((launch_apply<double, double>(b->a_cx, 1, h->N, h->r, h->st)));
+  if (h->mixed) CK((launch_apply<float, float>(b->a_cx, 1, h->N, rank_mask(h->r), h->st)));
+  else CK((launch_apply<double, double>(b->a_cx, 1, h->N, rank_mask(h->r), h->st)));
   h->canonical = true;
   return DLR_OK;
 }

@@ -126,6 +126,12 @@ __device__ __forceinline__ double rhocv_at(const Inst &I, int c, double T0) {
   return I.cv_texp == 0.0 ? I.rho_cv[c] : I.rho_cv[c] * pow(T0 / I.T_ref, I.cv_texp);
 }
 
+// Rank classes of the kernels unrolled over RB = 8, 16 or 32 columns: a
+// batch launches one kernel per class present, each skipping the other
+// instances, so an instance's work follows its own rank.
+__host__ __device__ inline int rank_class(int r) { return r <= 8 ? 8 : r <= 16 ? 16 : 32; }
+__host__ __device__ inline int rank_mask(int r) { return r <= 8 ? 1 : r <= 16 ? 2 : 4; }
+
 // Per-cell coefficients of the Newton-linearised step (Section 2.2, in the
 // backward-Euler form: D = rho c_v + 4 pi dt sigma B'(T0), effective
 // scattering sigma_s = sigma 4 pi dt sigma B' / D, effective source

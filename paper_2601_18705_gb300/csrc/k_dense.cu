@@ -31,6 +31,7 @@ __global__ void __launch_bounds__(256) k_coeff_recon(const Inst *__restrict__ in
   pdl_wait();
   pdl_trigger();
   const Inst &I = insts[blockIdx.y];
+  if (rank_class(I.r) != RB) return;
   __shared__ real C0s[RB * RB];
   __shared__ real gam[RB];
   const int r = I.r;
@@ -274,7 +275,7 @@ __global__ void __launch_bounds__(128) k_apply(const ApplyJob *__restrict__ jobs
   pdl_wait();
   pdl_trigger();
   const ApplyJob J = jobs[blockIdx.y];
-  if (J.run_if && *J.run_if == 0) return;
+  if (rank_class(J.r) != RB || (J.run_if && *J.run_if == 0)) return;
   __shared__ rout Ts[RB * RB];
   __shared__ rout dg[RB];
   const int r = J.r;
@@ -592,6 +593,7 @@ __global__ void __launch_bounds__(128) k_tupdate(const Inst *__restrict__ insts)
   pdl_wait();
   pdl_trigger();
   const Inst &I = insts[blockIdx.y];
+  if (rank_class(I.r) != RB) return;
   __shared__ real Us[RB * RB];
   __shared__ real vp[RB];
   const int r = I.r;
@@ -632,15 +634,20 @@ __global__ void __launch_bounds__(128) k_tupdate(const Inst *__restrict__ insts)
 // ------------------------------------------------------------------
 // host launchers
 // ------------------------------------------------------------------
-#define DLR_RB_DISPATCH(r, MACRO) \
-  ((r) <= 8 ? MACRO(8) : (r) <= 16 ? MACRO(16) : MACRO(32))
+// one launch per rank class in mask (bits: 8, 16, 32)
+#define DLR_RB_DISPATCH(mask, MACRO)                   \
+  do {                                                 \
+    if ((mask) & 1) MACRO(8);                          \
+    if (e == cudaSuccess && ((mask) & 2)) MACRO(16);   \
+    if (e == cudaSuccess && ((mask) & 4)) MACRO(32);   \
+  } while (0)
 
 template <typename real>
-cudaError_t launch_coeff_recon(const Inst *d, int n, int maxN, int r, cudaStream_t st) {
+cudaError_t launch_coeff_recon(const Inst *d, int n, int maxN, int rmask, cudaStream_t st) {
   dim3 g((maxN + 255) / 256, n);
 #define L_(RB) (e = launch_pdl(k_coeff_recon<real, RB>, g, dim3(256), 0, st, d))
   cudaError_t e = cudaSuccess;
-  DLR_RB_DISPATCH(r, L_);
+  DLR_RB_DISPATCH(rmask, L_);
 #undef L_
   return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -658,11 +665,11 @@ cudaError_t launch_fill(const FillJob *d_jobs, int n, int maxm, cudaStream_t st)
 }
 
 template <typename rin, typename rout>
-cudaError_t launch_apply(const ApplyJob *d_jobs, int n, int maxm, int r, cudaStream_t st) {
+cudaError_t launch_apply(const ApplyJob *d_jobs, int n, int maxm, int rmask, cudaStream_t st) {
   dim3 g((maxm + 127) / 128, n);
 #define L_(RB) (e = launch_pdl(k_apply<rin, rout, RB>, g, dim3(128), 0, st, d_jobs))
   cudaError_t e = cudaSuccess;
-  DLR_RB_DISPATCH(r, L_);
+  DLR_RB_DISPATCH(rmask, L_);
 #undef L_
   return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -721,11 +728,11 @@ cudaError_t launch_reduce(const ReduceJob *d_jobs, int n, int maxcount, cudaStre
 }
 
 template <typename real>
-cudaError_t launch_tupdate(const Inst *d, int n, int maxN, int r, cudaStream_t st) {
+cudaError_t launch_tupdate(const Inst *d, int n, int maxN, int rmask, cudaStream_t st) {
   dim3 g((maxN + 127) / 128, n);
 #define L_(RB) (e = launch_pdl(k_tupdate<real, RB>, g, dim3(128), 0, st, d))
   cudaError_t e = cudaSuccess;
-  DLR_RB_DISPATCH(r, L_);
+  DLR_RB_DISPATCH(rmask, L_);
 #undef L_
   return e != cudaSuccess ? e : cudaGetLastError();
 }

@@ -488,6 +488,7 @@ k_lstep_angle(const Inst *__restrict__ insts) {
   pdl_trigger();
   constexpr int NC = 2 * RB, LDC = RB + 1;
   const Inst &I = insts[blockIdx.y];
+  if (rank_class(I.r) != RB) return;  // another launch serves this rank class
   const int nblk = I.lstep_blocks;
   if ((int)blockIdx.x >= nblk) return;  // whole clusters (nblk is a multiple of kCl)
   cg::cluster_group cluster = cg::this_cluster();
@@ -936,15 +937,14 @@ cudaError_t launch_proj_post(const Inst *d, int n, cudaStream_t st) {
   return launch_pdl(k_proj_post, dim3(n), dim3(256), 0, st, d);
 }
 // blocks: CTAs of the per-angle kernel (a multiple of kCl); maxK: most angles
-cudaError_t launch_lstep(const Inst *d, int n, int r_max, int blocks, int maxK, cudaStream_t st) {
+// rmask: the rank classes present (one launch of the per-angle kernel each)
+cudaError_t launch_lstep(const Inst *d, int n, int r_max, int rmask, int blocks, int maxK, cudaStream_t st) {
   const dim3 g(blocks, n);
   const size_t sm = lstep_angle_smem(r_max);
-  cudaError_t e;
-  switch (rank_bucket(r_max)) {
-    case 8: e = launch_pdl(k_lstep_angle<8>, g, dim3(kLsWarps * 32), sm, st, d); break;
-    case 16: e = launch_pdl(k_lstep_angle<16>, g, dim3(kLsWarps * 32), sm, st, d); break;
-    default: e = launch_pdl(k_lstep_angle<32>, g, dim3(kLsWarps * 32), sm, st, d); break;
-  }
+  cudaError_t e = cudaSuccess;
+  if (rmask & 1) e = launch_pdl(k_lstep_angle<8>, g, dim3(kLsWarps * 32), sm, st, d);
+  if (e == cudaSuccess && (rmask & 2)) e = launch_pdl(k_lstep_angle<16>, g, dim3(kLsWarps * 32), sm, st, d);
+  if (e == cudaSuccess && (rmask & 4)) e = launch_pdl(k_lstep_angle<32>, g, dim3(kLsWarps * 32), sm, st, d);
   if (e != cudaSuccess) return e;
   if ((e = launch_pdl(k_lstep_mid, dim3(n), dim3(256), 0, st, d)) != cudaSuccess) return e;
   return launch_pdl(k_lstep_back, dim3((maxK * r_max + 255) / 256, n), dim3(256), 0, st, d);
