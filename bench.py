@@ -336,6 +336,7 @@ def run_gpu(args):
                                               method=dlr.DLR_METHOD_SN))
         s4.step(args.warmup)
         s4.stream.synchronize()
+        s4.set_timing(True)
         g0 = s4.stats()
         ms_sn = timed_steps(dlr, torch, s4, args.steps, flush)
         g1 = s4.stats()
@@ -348,6 +349,18 @@ def run_gpu(args):
               "dlr_steps_per_s": args.steps / (tsn / 1e3),
               "si_iters_per_step": (g1["si_iters_total"] - g0["si_iters_total"]) / args.steps,
               "T_rel_l2_dlr_vs_sn": float(np.linalg.norm(T_mixed - T_sn) / np.linalg.norm(T_sn))}
+        # the same source-iteration kernel over all angles: per update it reads
+        # the fixed source and writes psi (4 + 4 B), the scalar-flux phase
+        # reads psi again (4 B), plus per-cell terms amortised over NOm angles
+        K = case["n_polar"] * case["n_azim"]
+        bpu = 12.0 + 16.0 / K
+        nl = max(g1["si_launches"] - g0["si_launches"], 1)
+        l_ms = (g1["ms_si_total"] - g0["ms_si_total"]) / nl
+        ach = usn / nl * bpu / (l_ms / 1e3) / 1e9
+        hbm_pk, pk_kind = peaks()
+        sn["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm_pk, "unit": "GB/s",
+                          "frac": ach / hbm_pk, "kernel": "k_si<float>", "peak_kind": pk_kind,
+                          "bytes_per_update": bpu, "avg_launch_ms": l_ms}
 
     # ---- the augmented step (rank-2r basis truncated to r), same steps ----
     aug = None
