@@ -1705,6 +1705,16 @@ int dlr_sweep(int32_t nx, int32_t ny, double lx, double ly, int32_t n_dir, const
   if (nx < 1 || ny < 1 || n_dir < 1 || !dirs || !psi_edge || !sigma_t || !src || !psi || !(lx > 0) ||
       !(ly > 0) || (precision != DLR_FP64 && precision != DLR_MIXED))
     return fail(DLR_EINVAL, "bad argument to dlr_sweep");
+  {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int bands = (ny + 31) / 32;
+    const size_t need = precision == DLR_MIXED ? si_smem_bytes<float>(nx, bands, 0, 0)
+                                               : si_smem_bytes<double>(nx, bands, 0, 0);
+    if (optin > 0 && need > (size_t)optin)
+      return fail(DLR_EINVAL, "nx = %d too large for the sweep's shared memory", nx);
+  }
   cudaStream_t st = (cudaStream_t)stream;
   double *d_dirs = nullptr, *d_edge = nullptr;
   int *d_abort = nullptr;
