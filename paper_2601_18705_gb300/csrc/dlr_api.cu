@@ -28,6 +28,7 @@ namespace dlr {
 template <typename real> cudaError_t launch_si(const Inst *, const SiCtl &, int, cudaStream_t);
 template <typename real> int si_max_grid(int, int, int, int);
 int si_sweep_warps(bool mixed);
+int si_sweep_lag(bool mixed);
 template <typename real> size_t si_smem_bytes(int, int, int, int);
 template <typename real> cudaError_t launch_sn_init(void *, const double *, int, int, double, double, cudaStream_t);
 template <typename real> cudaError_t launch_sn_prep(const Inst *, int, int, cudaStream_t);
@@ -820,9 +821,10 @@ static T *carve(char *&cur, size_t count) {
 
 // Modelled wavefront steps of one unit of p bands (32 rows each) on an
 // nx-column mesh swept by nw warps: each warp sweeps ceil(p / nw) bands one
-// after the other, and the warps start one band lag (about 40 steps) apart.
-static double unit_steps(int nx, int p, int nw) {
-  return (double)((p + nw - 1) / nw) * (nx + 31) + (std::min(p, nw) - 1) * 40.0;
+// after the other, and the warps start one band lag apart (the 31-step skew
+// of a band plus its progress granularity: `lag` steps).
+static double unit_steps(int nx, int p, int nw, int lag) {
+  return (double)((p + nw - 1) / nw) * (nx + 31) + (std::min(p, nw) - 1) * (double)lag;
 }
 
 // Splits angles into units of consecutive bands.  Starting from one unit per
@@ -832,8 +834,9 @@ static double unit_steps(int nx, int p, int nw) {
 // keeps one unit per angle.  Units are ordered by modelled length, longest
 // first, and the units of one angle bottom-up, so that a unit's predecessor
 // is always claimed before it.  Returns the number of edge rows used.
-static int plan_units(dlr_handle *const *hs, int n, int nw, int ctas, double split,
+static int plan_units(dlr_handle *const *hs, int n, bool mixed, int ctas, double split,
                       std::vector<SiUnit> &units) {
+  const int nw = si_sweep_warps(mixed), lag = si_sweep_lag(mixed);
   std::vector<int> nb(n), bpu(n);
   for (int i = 0; i < n; ++i) bpu[i] = nb[i] = (hs[i]->prob.ny + 31) / 32;
   while (split > 0) {
@@ -841,7 +844,7 @@ static int plan_units(dlr_handle *const *hs, int n, int nw, int ctas, double spl
     int imax = -1;
     for (int i = 0; i < n; ++i) {
       const int g = (nb[i] + bpu[i] - 1) / bpu[i];
-      const double t = unit_steps(hs[i]->prob.nx, bpu[i], nw);
+      const double t = unit_steps(hs[i]->prob.nx, bpu[i], nw, lag);
       total += (double)hs[i]->r * g * t;
       if (bpu[i] > nw && t > tmax) {
         tmax = t;
@@ -855,7 +858,7 @@ static int plan_units(dlr_handle *const *hs, int n, int nw, int ctas, double spl
   std::vector<int> order(n);
   for (int i = 0; i < n; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
-    return unit_steps(hs[a]->prob.nx, bpu[a], nw) > unit_steps(hs[c]->prob.nx, bpu[c], nw);
+    return unit_steps(hs[a]->prob.nx, bpu[a], nw, lag) > unit_steps(hs[c]->prob.nx, bpu[c], nw, lag);
   });
   units.clear();
   int rows = 0;
@@ -936,7 +939,7 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   }
   b->split = tuned_split(hs, n);
   std::vector<SiUnit> units;
-  plan_units(hs, n, nw, gmax, b->split, units);
+  plan_units(hs, n, b->mixed, gmax, b->split, units);
   // one device block for the batch's tables
   size_t bytes = 0;
   auto sz = [](size_t s) { return (s + 255) & ~size_t(255); };
@@ -1399,7 +1402,7 @@ int dlr_step_batch(dlr_handle *const *hs, int32_t n, int32_t nsteps) {
 // Re-plans the batch's sweep units with splitting threshold `split`.
 static int set_plan(Batch *b, double split) {
   std::vector<SiUnit> units;
-  plan_units(b->hs.data(), b->n, si_sweep_warps(b->mixed), b->si_grid, split, units);
+  plan_units(b->hs.data(), b->n, b->mixed, b->si_grid, split, units);
   if ((int)units.size() > b->units_cap) return fail(DLR_EINVAL, "unit plan exceeds its table");
   CK(cudaMemcpyAsync(b->d_units, units.data(), sizeof(SiUnit) * units.size(), cudaMemcpyHostToDevice,
                      b->st));
@@ -1440,9 +1443,8 @@ int dlr_autotune(dlr_handle *const *hs, int32_t n, int32_t iters, int32_t reps, 
   CK(cudaGraphLaunch(b->pre, b->st));
   const double cand[] = {0.0, 2.0, 1.0, 0.5};
   const int nc = (int)(sizeof(cand) / sizeof(cand[0]));
-  const int nw = si_sweep_warps(b->mixed);
   std::vector<std::vector<SiUnit>> plans(nc);
-  for (int c = 0; c < nc; ++c) plan_units(b->hs.data(), n, nw, b->si_grid, cand[c], plans[c]);
+  for (int c = 0; c < nc; ++c) plan_units(b->hs.data(), n, b->mixed, b->si_grid, cand[c], plans[c]);
   auto same = [](const std::vector<SiUnit> &x, const std::vector<SiUnit> &y) {
     return x.size() == y.size() && std::memcmp(x.data(), y.data(), x.size() * sizeof(SiUnit)) == 0;
   };

@@ -33,11 +33,16 @@
 
 namespace dlr {
 
+// NW: sweeping warps per CTA.  kSub: progress granularity (steps).  Finer
+// steps shorten the lag between bands (31 + kSub steps) but their waits, edge
+// reads and progress stores cost more than the lag saves: in FP32 a whole
+// window (measured: 8 -> 32 cut lognormal1024 from 23.2 to 16.4 ms per
+// step).  In FP64 the kSub staged (source, 1/diagonal) pairs held across a
+// sub-window cost 4 registers each: at 16 or 32 the kernel spills kilobytes
+// (measured at 32: checker256 FP64 5.2 -> 5.8 ms per step), so it keeps 8.
 template <typename real> struct SweepCfg;
-template <> struct SweepCfg<float> { static constexpr int NW = 8; };
-template <> struct SweepCfg<double> { static constexpr int NW = 4; };
-
-constexpr int kSub = 8;                        // progress granularity (steps)
+template <> struct SweepCfg<float> { static constexpr int NW = 8, kSub = 32; };
+template <> struct SweepCfg<double> { static constexpr int NW = 4, kSub = 8; };
 constexpr uint64_t kWaitNs = 4000000000ull;    // bound of any single wait
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -310,6 +315,7 @@ __device__ __forceinline__ void st_relaxed(unsigned long long *p, unsigned long 
 template <typename real>
 __device__ __forceinline__ void edge_load(const unsigned long long *g, int t0, int nx,
                                           unsigned long long (&w)[EdgeWords<real>::kW]) {
+  constexpr int kSub = SweepCfg<real>::kSub;
   const int lane = threadIdx.x & 31, c = t0 + lane;
   if (lane < kSub && c < nx) {
 #pragma unroll
@@ -323,8 +329,8 @@ __device__ __forceinline__ void edge_load(const unsigned long long *g, int t0, i
 template <typename real>
 __device__ __forceinline__ bool edge_take(const unsigned long long *g, int t0, int nx, unsigned tag,
                                           unsigned long long (&w)[EdgeWords<real>::kW],
-                                          real (&ed)[kSub], volatile int *abort_flag) {
-  constexpr int kW = EdgeWords<real>::kW;
+                                          real (&ed)[SweepCfg<real>::kSub], volatile int *abort_flag) {
+  constexpr int kW = EdgeWords<real>::kW, kSub = SweepCfg<real>::kSub;
   const int lane = threadIdx.x & 31;
   const bool mine = lane < kSub && t0 + lane < nx;
   auto valid = [&]() {
@@ -367,6 +373,7 @@ __device__ __forceinline__ bool sweep_window(int b, int k, const SweepArgs<real>
                                              const unsigned long long *g_in,
                                              unsigned long long *g_out, unsigned tag,
                                              unsigned long long (&gw)[EdgeWords<real>::kW]) {
+  constexpr int kSub = SweepCfg<real>::kSub;
   const int lane = threadIdx.x & 31;
   const int nx = A.nx;
   const real ax = A.ax, ay = A.ay;
@@ -783,6 +790,7 @@ cudaError_t launch_sweep_dirs(int nx, int ny, double hx, double hy, int n_dir,
 }
 
 int si_sweep_warps(bool mixed) { return mixed ? SweepCfg<float>::NW : SweepCfg<double>::NW; }
+int si_sweep_lag(bool mixed) { return 32 + (mixed ? SweepCfg<float>::kSub : SweepCfg<double>::kSub); }
 
 template size_t si_smem_bytes<float>(int, int, int, int);
 template size_t si_smem_bytes<double>(int, int, int, int);
