@@ -57,7 +57,8 @@ class _Problem(C.Structure):
                 ("dt", C.c_double), ("c", C.c_double), ("a_rad", C.c_double),
                 ("sigma", _dp), ("rho_cv", _dp),
                 ("psi_edge", C.c_double * 4), ("sigma_texp", C.c_double),
-                ("cv_texp", C.c_double), ("T_ref", C.c_double)]
+                ("cv_texp", C.c_double), ("T_ref", C.c_double),
+                ("dsa", C.c_int), ("dsa_tol", C.c_double), ("dsa_max_iter", C.c_int)]
 
 
 class _Opts(C.Structure):
@@ -68,7 +69,7 @@ class _Opts(C.Structure):
 
 
 class _Diag(C.Structure):
-    _fields_ = [("iters", C.c_int), ("E_before", C.c_double),
+    _fields_ = [("iters", C.c_int), ("dsa_iters", C.c_int), ("E_before", C.c_double),
                 ("E_after", C.c_double), ("outflow", C.c_double),
                 ("inflow", C.c_double), ("residual", C.c_double),
                 ("min_T", C.c_double), ("min_phi", C.c_double),
@@ -97,6 +98,12 @@ def lib() -> C.CDLL:
                                          C.c_double, C.c_int, C.c_int, _dp, _ip]
         L.oracle_sn_step.argtypes = [C.POINTER(_Problem), _dp, _dp, C.c_double, C.c_int,
                                      _dp, _dp, _dp]
+        L.oracle_dsa_kappa.restype = C.c_double
+        L.oracle_dsa_kappa.argtypes = [C.c_int, C.c_int, C.c_int]
+        L.oracle_dsa_apply.argtypes = [C.POINTER(_Problem), _dp, _dp, _dp, _dp]
+        L.oracle_dsa_diag.argtypes = [C.POINTER(_Problem), _dp, _dp, _dp]
+        L.oracle_dsa_solve.argtypes = [C.POINTER(_Problem), _dp, _dp, _dp, C.c_double,
+                                       C.c_int, _dp]
         _lib = L
     return _lib
 
@@ -141,6 +148,9 @@ class Problem:
     sigma_texp: float = 0.0   # sigma(T) = sigma (T/T_ref)^-sigma_texp (reading R16)
     cv_texp: float = 0.0      # rho c_v(T) = rho_cv (T/T_ref)^cv_texp
     T_ref: float = 1.0
+    dsa: int = 0              # diffusion synthetic acceleration (Section 4.5, reading R17)
+    dsa_tol: float = 1e-6     # CG stop: ||r||_2 <= dsa_tol ||b||_2
+    dsa_max_iter: int = 1000
     _keep: list = field(default_factory=list, repr=False)
 
     @property
@@ -168,6 +178,7 @@ class Problem:
         s.dt, s.c, s.a_rad = self.dt, self.c, self.a_rad
         s.sigma, s.rho_cv = _ptr(sig), _ptr(rho)
         s.sigma_texp, s.cv_texp, s.T_ref = self.sigma_texp, self.cv_texp, self.T_ref
+        s.dsa, s.dsa_tol, s.dsa_max_iter = int(self.dsa), float(self.dsa_tol), int(self.dsa_max_iter)
         for e in range(4):
             s.psi_edge[e] = float(self.psi_edge[e])
         return s
@@ -193,6 +204,33 @@ def sweep(p: Problem, ox: float, oy: float, sigma_t, src) -> np.ndarray:
     psi = np.zeros(p.Nx)
     lib().oracle_sweep(C.byref(p.cstruct()), float(ox), float(oy), _ptr(st), _ptr(s), _ptr(psi))
     return psi
+
+
+def dsa_kappa(n_polar: int, n_azim: int, axis: int) -> float:
+    return lib().oracle_dsa_kappa(n_polar, n_azim, axis)
+
+
+def dsa_apply(p: Problem, sigma_t, sigma_a, u) -> np.ndarray:
+    st, sa, uu = (_f64(a).reshape(-1) for a in (sigma_t, sigma_a, u))
+    out = np.zeros(p.Nx)
+    lib().oracle_dsa_apply(C.byref(p.cstruct()), _ptr(st), _ptr(sa), _ptr(uu), _ptr(out))
+    return out
+
+
+def dsa_diag(p: Problem, sigma_t, sigma_a) -> np.ndarray:
+    st, sa = (_f64(a).reshape(-1) for a in (sigma_t, sigma_a))
+    d = np.zeros(p.Nx)
+    lib().oracle_dsa_diag(C.byref(p.cstruct()), _ptr(st), _ptr(sa), _ptr(d))
+    return d
+
+
+def dsa_solve(p: Problem, sigma_t, sigma_a, b, tol: float = 1e-12, max_iter: int = 10000):
+    """Jacobi-PCG solve of the DSA system A x = b; returns (x, iterations)."""
+    st, sa, bb = (_f64(a).reshape(-1) for a in (sigma_t, sigma_a, b))
+    x = np.zeros(p.Nx)
+    it = lib().oracle_dsa_solve(C.byref(p.cstruct()), _ptr(st), _ptr(sa), _ptr(bb), float(tol),
+                                int(max_iter), _ptr(x))
+    return x, it
 
 
 def lu_solve(A, B) -> np.ndarray:

@@ -34,6 +34,16 @@
  *       laws sigma(T) = sigma (T/T_ref)^-n_s, rho c_v(T) = rho_cv (T/T_ref)^n_c,
  *       taken at the step's T0 as Eq. (T, backward Euler) prescribes (the
  *       transport opacity too: sigma_t = sigma(T0) + 1/(c dt)).
+ *   R17 DSA (Section 4.5) on DG0 cells: the volume terms G_j vanish on
+ *       piecewise constants, faces on the domain boundary see a zero
+ *       exterior trace (the vacuum error equation), and the penalty F0 uses
+ *       the full-quadrature coefficient (1/4 pi)(1/2) sum_k w_k |Om_k . n|,
+ *       the traditional consistent-DSA penalty the paper's experiments use,
+ *       in place of the collocation weights beta^T What^{-1}.  The DSA
+ *       system A delta = M_s (phi^{l+1/2} - phi^l) is solved by
+ *       Jacobi-preconditioned CG to ||r||_2 <= dsa_tol ||b||_2 (at most
+ *       dsa_max_iter iterations), and phi^{l+1} = phi^{l+1/2} + delta; the
+ *       SI stopping test of R7 compares phi^{l+1} with phi^l.
  */
 #include "oracle.h"
 
@@ -182,6 +192,172 @@ void oracle_sweep(const oracle_problem *p, double ox, double oy,
       psi[c] = (src[c] + ax * up_x + ay * up_y) / (sigma_t[c] + ax + ay);
     }
   }
+}
+
+/* ------------------------------------------------------------------ */
+/* Diffusion synthetic acceleration (Section 4.5; reading R17).        */
+/* ------------------------------------------------------------------ */
+
+/* Penalty coefficient of F0 on faces whose normal is along x (axis 0) or y
+ * (axis 1): (1/4 pi) (1/2) sum_k w_k |Om_k . n|. */
+double oracle_dsa_kappa(int n_polar, int n_azim, int axis) {
+  int NOm = n_polar * n_azim;
+  double *ox = (double *)malloc(sizeof(double) * NOm);
+  double *oy = (double *)malloc(sizeof(double) * NOm);
+  double *oz = (double *)malloc(sizeof(double) * NOm);
+  double *w = (double *)malloc(sizeof(double) * NOm);
+  oracle_quadrature(n_polar, n_azim, ox, oy, oz, w);
+  double t = 0;
+  for (int k = 0; k < NOm; k++) t += w[k] * fabs(axis == 0 ? ox[k] : oy[k]);
+  free(ox); free(oy); free(oz); free(w);
+  return t / (8.0 * ORACLE_PI);
+}
+
+/* The faces normal to `axis`: face f of line l (f = 0 .. n, n cells along
+ * the axis) lies between cell f-1 (lo) and cell f (hi); -1 = outside. */
+static void face_cells(const oracle_problem *p, int axis, int l, int f, int *lo, int *hi) {
+  int nx = p->nx, ny = p->ny;
+  int n = axis == 0 ? nx : ny;
+  int c_lo = axis == 0 ? l * nx + (f - 1) : (f - 1) * nx + l;
+  int c_hi = axis == 0 ? l * nx + f : f * nx + l;
+  *lo = f > 0 ? c_lo : -1;
+  *hi = f < n ? c_hi : -1;
+}
+
+/* out = A u with A = (1/3) sum_j Fbar_j^T M_t^{-1} Fbar_j + F0 + M_a, the
+ * DG0 form of the diffusion operator of Section 4.5 (G_j = 0):
+ *   v^T Fbar_j u = sum_faces int [[u]]_j {v},
+ *   v^T F0 u     = sum_faces kappa [[u]] [[v]],
+ *   M_t = h^2 diag(sigma_t), M_a = h^2 diag(sigma_a),
+ * with [[u]] = u_lo - u_hi across a face (normal from lo to hi), {v} the
+ * mean of the two traces, and a zero trace outside the domain. */
+void oracle_dsa_apply(const oracle_problem *p, const double *sig_t,
+                      const double *sig_a, const double *u, double *out) {
+  int nx = p->nx, ny = p->ny, N = nx * ny;
+  double hx = p->lx / nx, hy = p->ly / ny, h2 = hx * hy;
+  double *g = (double *)malloc(sizeof(double) * N);
+  double *z = (double *)malloc(sizeof(double) * N);
+  for (int c = 0; c < N; c++) out[c] = h2 * sig_a[c] * u[c];
+  for (int axis = 0; axis < 2; axis++) {
+    int n = axis == 0 ? nx : ny, lines = axis == 0 ? ny : nx;
+    double hf = axis == 0 ? hy : hx;  /* face length */
+    double kap = oracle_dsa_kappa(p->n_polar, p->n_azim, axis);
+    /* g = Fbar u */
+    for (int c = 0; c < N; c++) g[c] = 0;
+    for (int l = 0; l < lines; l++)
+      for (int f = 0; f <= n; f++) {
+        int lo, hi;
+        face_cells(p, axis, l, f, &lo, &hi);
+        double jump = (lo >= 0 ? u[lo] : 0.0) - (hi >= 0 ? u[hi] : 0.0);
+        if (lo >= 0) g[lo] += hf * jump * 0.5;
+        if (hi >= 0) g[hi] += hf * jump * 0.5;
+      }
+    /* z = M_t^{-1} g, then out += (1/3) Fbar^T z (the face loop transposed) */
+    for (int c = 0; c < N; c++) z[c] = g[c] / (h2 * sig_t[c]);
+    for (int l = 0; l < lines; l++)
+      for (int f = 0; f <= n; f++) {
+        int lo, hi;
+        face_cells(p, axis, l, f, &lo, &hi);
+        double zs = hf * 0.5 * ((lo >= 0 ? z[lo] : 0.0) + (hi >= 0 ? z[hi] : 0.0));
+        if (lo >= 0) out[lo] += zs / 3.0;
+        if (hi >= 0) out[hi] -= zs / 3.0;
+      }
+    /* F0 */
+    for (int l = 0; l < lines; l++)
+      for (int f = 0; f <= n; f++) {
+        int lo, hi;
+        face_cells(p, axis, l, f, &lo, &hi);
+        double jump = (lo >= 0 ? u[lo] : 0.0) - (hi >= 0 ? u[hi] : 0.0);
+        if (lo >= 0) out[lo] += kap * hf * jump;
+        if (hi >= 0) out[hi] -= kap * hf * jump;
+      }
+  }
+  free(g); free(z);
+}
+
+/* The diagonal of A by probing: A couples a cell only with cells at most two
+ * apart along x or along y, so applying A to the indicator of the cells
+ * with (ix mod 5, iy mod 5) fixed reads A_cc for every cell of that class. */
+void oracle_dsa_diag(const oracle_problem *p, const double *sig_t,
+                     const double *sig_a, double *d) {
+  int nx = p->nx, ny = p->ny, N = nx * ny;
+  double *e = (double *)malloc(sizeof(double) * N);
+  double *Ae = (double *)malloc(sizeof(double) * N);
+  for (int a = 0; a < 5; a++)
+    for (int b = 0; b < 5; b++) {
+      for (int c = 0; c < N; c++) e[c] = ((c % nx) % 5 == a && (c / nx) % 5 == b) ? 1.0 : 0.0;
+      oracle_dsa_apply(p, sig_t, sig_a, e, Ae);
+      for (int c = 0; c < N; c++)
+        if (e[c] != 0.0) d[c] = Ae[c];
+    }
+  free(e); free(Ae);
+}
+
+static double dot(int n, const double *a, const double *b) {
+  double t = 0;
+  for (int i = 0; i < n; i++) t += a[i] * b[i];
+  return t;
+}
+
+/* Jacobi-preconditioned conjugate gradients for A x = b (x starts at 0),
+ * stopping when ||r||_2 <= tol ||b||_2 or after max_iter iterations.
+ * Returns the iterations taken. */
+int oracle_dsa_solve(const oracle_problem *p, const double *sig_t,
+                     const double *sig_a, const double *b, double tol,
+                     int max_iter, double *x) {
+  int N = p->nx * p->ny;
+  double *d = (double *)malloc(sizeof(double) * N);
+  double *r = (double *)malloc(sizeof(double) * N);
+  double *z = (double *)malloc(sizeof(double) * N);
+  double *pp = (double *)malloc(sizeof(double) * N);
+  double *q = (double *)malloc(sizeof(double) * N);
+  oracle_dsa_diag(p, sig_t, sig_a, d);
+  for (int c = 0; c < N; c++) {
+    x[c] = 0;
+    r[c] = b[c];
+    z[c] = r[c] / d[c];
+    pp[c] = z[c];
+  }
+  double bb = dot(N, b, b), rz = dot(N, r, z);
+  int it = 0;
+  while (bb > 0 && it < max_iter) {
+    oracle_dsa_apply(p, sig_t, sig_a, pp, q);
+    double alpha = rz / dot(N, pp, q);
+    for (int c = 0; c < N; c++) {
+      x[c] += alpha * pp[c];
+      r[c] -= alpha * q[c];
+    }
+    it++;
+    if (dot(N, r, r) <= tol * tol * bb) break;
+    for (int c = 0; c < N; c++) z[c] = r[c] / d[c];
+    double rz_new = dot(N, r, z);
+    double beta = rz_new / rz;
+    rz = rz_new;
+    for (int c = 0; c < N; c++) pp[c] = z[c] + beta * pp[c];
+  }
+  free(d); free(r); free(z); free(pp); free(q);
+  return it;
+}
+
+/* The DSA step between source iterations: phi_half (the scalar flux of the
+ * sweeps at phi_old) becomes phi_half + delta with
+ * A delta = M_s (phi_half - phi_old).  Returns the CG iterations. */
+static int dsa_correct(const oracle_problem *p, const double *sig_t,
+                       const double *sig_s, const double *phi_old,
+                       double *phi_half) {
+  int N = p->nx * p->ny;
+  double h2 = (p->lx / p->nx) * (p->ly / p->ny);
+  double *sig_a = (double *)malloc(sizeof(double) * N);
+  double *b = (double *)malloc(sizeof(double) * N);
+  double *delta = (double *)malloc(sizeof(double) * N);
+  for (int c = 0; c < N; c++) {
+    sig_a[c] = sig_t[c] - sig_s[c];
+    b[c] = h2 * sig_s[c] * (phi_half[c] - phi_old[c]);
+  }
+  int it = oracle_dsa_solve(p, sig_t, sig_a, b, p->dsa_tol, p->dsa_max_iter, delta);
+  for (int c = 0; c < N; c++) phi_half[c] += delta[c];
+  free(sig_a); free(b); free(delta);
+  return it;
 }
 
 /* ------------------------------------------------------------------ */
@@ -788,7 +964,8 @@ static int collocation_si(const oracle_problem *p, int r, const double *X0,
                           const int *wpiv, const double *beta, const double *ox,
                           const double *oy, const double *sig_t,
                           const double *sig_s, const double *q, double tol,
-                          int max_iter, int fixed, double *Psi, int *iters_out) {
+                          int max_iter, int fixed, double *Psi, int *iters_out,
+                          int *dsa_iters_out) {
   int Nx = p->nx * p->ny;
   double inv_cdt = 1.0 / (p->c * p->dt);
   double *Psi0 = (double *)malloc(sizeof(double) * Nx * r);
@@ -810,7 +987,7 @@ static int collocation_si(const oracle_problem *p, int r, const double *X0,
     phi[c] = t;
   }
   int cap = fixed > 0 ? fixed : max_iter;
-  int iters = 0, converged = 0;
+  int iters = 0, converged = 0, dsa_iters = 0;
   while (iters < cap) {
     for (int j = 0; j < r; j++) {
       for (int c = 0; c < Nx; c++)
@@ -826,13 +1003,17 @@ static int collocation_si(const oracle_problem *p, int r, const double *X0,
       double t = 0;
       for (int j = 0; j < r; j++) t += beta[j] * Kc[j];
       phin[c] = t;
-      if (fabs(t - phi[c]) > dmax) dmax = fabs(t - phi[c]);
-      if (fabs(t) > pmax) pmax = fabs(t);
+    }
+    if (p->dsa) dsa_iters += dsa_correct(p, sig_t, sig_s, phi, phin);
+    for (int c = 0; c < Nx; c++) {
+      if (fabs(phin[c] - phi[c]) > dmax) dmax = fabs(phin[c] - phi[c]);
+      if (fabs(phin[c]) > pmax) pmax = fabs(phin[c]);
     }
     memcpy(phi, phin, sizeof(double) * Nx);
     if (fixed <= 0 && dmax <= tol * pmax) { converged = 1; break; }
   }
   *iters_out = iters;
+  if (dsa_iters_out) *dsa_iters_out = dsa_iters;
   free(Psi0); free(phi); free(phin); free(src); free(Kc);
   return (fixed <= 0 && !converged) ? -2 : 0;
 }
@@ -869,7 +1050,7 @@ int oracle_collocation(const oracle_problem *p, int r, const double *X0,
   int rc = lu_factor(r, WLU, wpiv);
   if (rc == 0)
     rc = collocation_si(p, r, X0, L0, idx, WLU, wpiv, beta, ox, oy, sig_t, sig_s, q,
-                        tol, max_iter, fixed, Psi, iters);
+                        tol, max_iter, fixed, Psi, iters, NULL);
   free(ox); free(oy); free(oz); free(w); free(sig_s); free(q); free(sig_t);
   free(WLU); free(wpiv); free(beta); free(L0);
   return rc;
@@ -941,12 +1122,12 @@ int oracle_dlr_step(const oracle_problem *p, int r, double *X, double *S,
       L0[i + r * k] = t;
     }
   double *Psi = (double *)malloc(sizeof(double) * Nx * r);
-  int iters = 0;
+  int iters = 0, dsa_iters = 0;
   if (rc == 0) {
     int fixed = opt ? opt->si_fixed_iters : 0;
     rc = collocation_si(p, r, X, L0, idx, WLU, wpiv, beta, ox, oy, sig_t, sig_s, q,
                         opt ? opt->si_tol : 1e-13, opt ? opt->si_max_iter : 1000,
-                        fixed, Psi, &iters);
+                        fixed, Psi, &iters, &dsa_iters);
   }
 
   /* Step 5: Psi = X R with h^2 X^T X = I (Householder QR of h Psi); the
@@ -1071,6 +1252,7 @@ int oracle_dlr_step(const oracle_problem *p, int r, double *X, double *S,
       boundary_rates(p, ox, oy, w, get_xl, &g, &out, &in);
       free(Lc);
       diag->iters = iters;
+      diag->dsa_iters = dsa_iters;
       diag->E_before = E_before;
       diag->E_after = energy(p, Tn, phin2);
       diag->outflow = out;
@@ -1103,6 +1285,7 @@ int oracle_dlr_step(const oracle_problem *p, int r, double *X, double *S,
     free(Tn);
   } else if (diag) {
     diag->iters = iters;
+    diag->dsa_iters = dsa_iters;
   }
 
   free(ox); free(oy); free(oz); free(w); free(phi0); free(sig_s); free(q);
@@ -1149,6 +1332,7 @@ int oracle_sn_step(const oracle_problem *p, double *psi, double *T,
       oracle_sweep(p, ox[k], oy[k], sig_t, src, psi + (size_t)Nx * k);
       for (int c = 0; c < Nx; c++) phin[c] += w[k] * psi[c + (size_t)Nx * k];
     }
+    if (p->dsa) dsa_correct(p, sig_t, sig_s, phi, phin);
     iters++;
     double dmax = 0, pmax = 0;
     for (int c = 0; c < Nx; c++) {

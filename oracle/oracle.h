@@ -38,6 +38,12 @@ typedef struct {
    * (explicit, Eq. T backward Euler); exponents 0 = constant; T_ref <= 0
    * means 1 */
   double sigma_texp, cv_texp, T_ref;
+  /* diffusion synthetic acceleration of the source iteration (Section 4.5,
+   * reading R17): dsa = 1 turns it on; the CG solve of each DSA step stops
+   * at ||r||_2 <= dsa_tol ||b||_2 or after dsa_max_iter iterations */
+  int dsa;
+  double dsa_tol;
+  int dsa_max_iter;
 } oracle_problem;
 
 typedef struct {
@@ -54,6 +60,7 @@ typedef struct {
 
 typedef struct {
   int iters;              /* source iterations taken */
+  int dsa_iters;          /* CG iterations of all DSA solves of the step */
   double E_before, E_after;  /* sum_c h^2 (rho_cv T + phi/c) */
   double outflow, inflow;    /* boundary energy rates of the new psi */
   double residual;        /* E_after - E_before + dt (outflow - inflow) */
@@ -81,6 +88,19 @@ void oracle_coefficients(const oracle_problem *p, const double *T0,
  * (ox d/dx + oy d/dy + sigma_t) psi = src, with the problem's edge inflow. */
 void oracle_sweep(const oracle_problem *p, double ox, double oy,
                   const double *sigma_t, const double *src, double *psi);
+
+/* DSA (Section 4.5, reading R17): the penalty coefficient of faces normal
+ * to x (axis 0) or y (axis 1); out = A u for the DG0 diffusion operator
+ * A = (1/3) sum_j Fbar_j^T M_t^{-1} Fbar_j + F0 + M_a; its diagonal; and
+ * Jacobi-preconditioned CG for A x = b (returns the iterations). */
+double oracle_dsa_kappa(int n_polar, int n_azim, int axis);
+void oracle_dsa_apply(const oracle_problem *p, const double *sig_t,
+                      const double *sig_a, const double *u, double *out);
+void oracle_dsa_diag(const oracle_problem *p, const double *sig_t,
+                     const double *sig_a, double *d);
+int oracle_dsa_solve(const oracle_problem *p, const double *sig_t,
+                     const double *sig_a, const double *b, double tol,
+                     int max_iter, double *x);
 
 /* Dense linear algebra building blocks. */
 int oracle_lu_solve(int n, const double *A, int nrhs, const double *B,
