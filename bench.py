@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sn", action="store_true", help="skip the full-rank SN comparator")
     ap.add_argument("--no-aug", action="store_true", help="skip the augmented (rank-2r) step")
+    ap.add_argument("--no-dsa", action="store_true", help="skip the DSA-accelerated step")
+    ap.add_argument("--dsa", action="store_true", help="served: every request with DSA")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="CPU work of the oracle sample")
     ap.add_argument("--kernel", default=None, choices=["sweep"],
@@ -382,6 +384,28 @@ def run_gpu(args):
         if sn is not None:
             aug["T_rel_l2_vs_sn"] = float(np.linalg.norm(T_aug - T_sn) / np.linalg.norm(T_sn))
 
+    # ---- the same steps with DSA-accelerated source iteration (Section 4.5) ----
+    dsa = None
+    if not args.no_dsa and rank == 0:
+        s6 = dlr.Solver(dlr.problem_from_case(case, precision=dlr.DLR_MIXED, allow_nonpositive=1, dsa=1))
+        s6.step(args.warmup)
+        s6.stream.synchronize()
+        d0 = s6.stats()
+        ms_dsa = timed_steps(dlr, torch, s6, args.steps, flush)
+        d1 = s6.stats()
+        T_dsa = s6.T()
+        s6.close()
+        ud = d1["cell_angle_updates"] - d0["cell_angle_updates"]
+        td = sum(ms_dsa)
+        si_d = d1["si_iters_total"] - d0["si_iters_total"]
+        dsa = {"method": "DSA-accelerated source iteration (Jacobi-PCG, dsa_tol 0.1), mixed",
+               "ms_per_step": td / args.steps, "dlr_steps_per_s": args.steps / (td / 1e3),
+               "si_iters_per_step": si_d / args.steps,
+               "cg_iters_per_si_iter": (d1["dsa_iters_total"] - d0["dsa_iters_total"]) / max(si_d, 1),
+               "step_speedup_vs_plain": (total_ms / args.steps) / (td / args.steps),
+               "T_rel_l2_vs_plain": float(np.linalg.norm(T_dsa - T_mixed) / np.linalg.norm(T_mixed)),
+               "cell_angle_updates_per_s": ud / (td / 1e3)}
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -410,7 +434,7 @@ def run_gpu(args):
             "data": "synthetic", "config": case_config(case, "mixed: FP32 sweeps/projections, FP64 small LA and T"),
             "dlr_steps_per_s": world * args.steps / (total_ms / 1e3),
             "si_iters_per_step": iters / args.steps,
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fp64_gpu": fp64, "sn_gpu": sn, "augmented_gpu": aug,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fp64_gpu": fp64, "sn_gpu": sn, "augmented_gpu": aug, "dsa_gpu": dsa,
             "clocks": clocks, "gpu_launches": int(launches),
             "nonpositive_cells_at_end": int(nonpos), "sweep_plan": tuned}
     print(json.dumps(line))
@@ -515,10 +539,13 @@ def run_batch64(args):
 def run_served(args):
     """Poisson arrivals (mean gap 50 ms); continuous batching with admission
     by HBM footprint; latency = completion - arrival."""
-    import paper_2601_18705_gb300 as dlr  # noqa: F401
+    import paper_2601_18705_gb300 as dlr
     from paper_2601_18705_gb300 import server
     reqs = [server.Request(rid=q["id"], arrival=t, case=workloads.materialize(q), steps=q["steps"])
             for t, q in workloads.served_requests(n=args.requests)]
+    if args.dsa:
+        for q in reqs:
+            q.spec = dlr.problem_from_case(q.case, precision=q.precision, allow_nonpositive=1, dsa=1)
     srv = server.Server(max_active=args.max_active, hbm_budget=int(args.hbm_budget_gb * 2 ** 30))
     rep = srv.run(reqs, realtime=True)
     s = rep.summary()
@@ -529,7 +556,7 @@ def run_served(args):
             "config": {"workload": f"served: {args.requests} requests, Poisson 20/s, sides "
                                    "U{128..1024}, ranks {8,16,32}, 50-200 steps, 16x32 angles",
                        "precision": "mixed", "hbm_budget_gb": args.hbm_budget_gb,
-                       "max_active": args.max_active},
+                       "max_active": args.max_active, "dsa": int(args.dsa)},
             "served": s}
     print(json.dumps(line))
 

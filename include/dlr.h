@@ -113,6 +113,21 @@ typedef struct dlr_problem {
   double T_ref;          /* sigma(T) = sigma (T/T_ref)^-sigma_texp and
                             rho c_v(T) = rho_cv (T/T_ref)^cv_texp; exponents
                             0 = constant materials; T_ref <= 0 means 1 */
+  int32_t dsa;           /* 1: diffusion synthetic acceleration of the source
+                            iteration (Section 4.5): after each round of
+                            sweeps the scalar flux is corrected by delta,
+                            A delta = M_s (phi^{l+1/2} - phi^l), with A the
+                            consistent DG0 diffusion operator (the face
+                            penalty (1/8 pi) sum_k w_k |Om_k . n|), solved by
+                            Jacobi-preconditioned CG.  The converged step is
+                            the same; only the iteration count changes.  The
+                            stopping test (si_tol) still measures each round
+                            of sweeps' change of phi.  Either method; 0 = off */
+  double dsa_tol;        /* CG stop: ||r||_2 <= dsa_tol ||b||_2 (<= 0: 0.1;
+                            must be < 1) */
+  int32_t dsa_max_iter;  /* CG iteration cap per solve (<= 0: 500); reaching
+                            it is not an error (the correction only
+                            accelerates the iteration) */
 } dlr_problem;
 
 /* Device memory and stream supplied by the caller (e.g. PyTorch). */
@@ -140,6 +155,7 @@ typedef struct dlr_stats {
   int64_t si_launches;       /* timed source-iteration launches */
   int64_t kernel_launches;   /* kernels this handle's steps launched */
   int64_t nonpositive_cells; /* cells with T <= 0 after the last step */
+  int64_t dsa_iters_total;   /* CG iterations of all DSA solves (dsa = 1) */
 } dlr_stats;
 
 /* Creates a solver: validates sizes, builds the quadrature and the initial

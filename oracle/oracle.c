@@ -42,8 +42,12 @@
  *       in place of the collocation weights beta^T What^{-1}.  The DSA
  *       system A delta = M_s (phi^{l+1/2} - phi^l) is solved by
  *       Jacobi-preconditioned CG to ||r||_2 <= dsa_tol ||b||_2 (at most
- *       dsa_max_iter iterations), and phi^{l+1} = phi^{l+1/2} + delta; the
- *       SI stopping test of R7 compares phi^{l+1} with phi^l.
+ *       dsa_max_iter iterations), and phi^{l+1} = phi^{l+1/2} + delta.
+ *       The stopping test of R7 is applied to the sweep's change,
+ *       phi^{l+1/2} - phi^l (what it measures without DSA): the
+ *       correction multiplies rounding noise by up to sigma_s / sigma_a in
+ *       thick scattering cells, so phi^{l+1} - phi^l would stall above a
+ *       tolerance near the working precision.
  */
 #include "oracle.h"
 
@@ -1003,12 +1007,10 @@ static int collocation_si(const oracle_problem *p, int r, const double *X0,
       double t = 0;
       for (int j = 0; j < r; j++) t += beta[j] * Kc[j];
       phin[c] = t;
+      if (fabs(t - phi[c]) > dmax) dmax = fabs(t - phi[c]);
+      if (fabs(t) > pmax) pmax = fabs(t);
     }
     if (p->dsa) dsa_iters += dsa_correct(p, sig_t, sig_s, phi, phin);
-    for (int c = 0; c < Nx; c++) {
-      if (fabs(phin[c] - phi[c]) > dmax) dmax = fabs(phin[c] - phi[c]);
-      if (fabs(phin[c]) > pmax) pmax = fabs(phin[c]);
-    }
     memcpy(phi, phin, sizeof(double) * Nx);
     if (fixed <= 0 && dmax <= tol * pmax) { converged = 1; break; }
   }
@@ -1332,13 +1334,13 @@ int oracle_sn_step(const oracle_problem *p, double *psi, double *T,
       oracle_sweep(p, ox[k], oy[k], sig_t, src, psi + (size_t)Nx * k);
       for (int c = 0; c < Nx; c++) phin[c] += w[k] * psi[c + (size_t)Nx * k];
     }
-    if (p->dsa) dsa_correct(p, sig_t, sig_s, phi, phin);
     iters++;
     double dmax = 0, pmax = 0;
     for (int c = 0; c < Nx; c++) {
       if (fabs(phin[c] - phi[c]) > dmax) dmax = fabs(phin[c] - phi[c]);
       if (fabs(phin[c]) > pmax) pmax = fabs(phin[c]);
     }
+    if (p->dsa) dsa_correct(p, sig_t, sig_s, phi, phin);
     memcpy(phi, phin, sizeof(double) * Nx);
     if (dmax <= si_tol * pmax) { converged = 1; break; }
   }

@@ -53,6 +53,9 @@ class ProblemSpec:
     sigma_texp: float = 0.0  # sigma(T) = sigma (T/T_ref)^-sigma_texp, at each step's T0
     cv_texp: float = 0.0     # rho c_v(T) = rho_cv (T/T_ref)^cv_texp
     T_ref: float = 1.0
+    dsa: int = 0             # 1: diffusion synthetic acceleration of the source iteration
+    dsa_tol: float = 0.0     # CG stop ||r|| <= dsa_tol ||b|| (0: 0.1)
+    dsa_max_iter: int = 0    # CG cap per solve (0: 500)
 
     def cstruct(self):
         keep = [_f64(self.sigma), _f64(self.rho_cv), _f64(self.T0)]
@@ -73,6 +76,7 @@ class ProblemSpec:
         p.allow_nonpositive = 1 if self.allow_nonpositive else 0
         p.method = self.method
         p.sigma_texp, p.cv_texp, p.T_ref = self.sigma_texp, self.cv_texp, self.T_ref
+        p.dsa, p.dsa_tol, p.dsa_max_iter = int(self.dsa), float(self.dsa_tol), int(self.dsa_max_iter)
         return p, keep
 
 

@@ -35,7 +35,8 @@ class DlrProblem(C.Structure):
                 ("precision", C.c_int32), ("selection", C.c_int32), ("augment", C.c_int32),
                 ("si_tol", C.c_double), ("si_max_iter", C.c_int32), ("si_fixed_iters", C.c_int32),
                 ("allow_nonpositive", C.c_int32), ("method", C.c_int32),
-                ("sigma_texp", C.c_double), ("cv_texp", C.c_double), ("T_ref", C.c_double)]
+                ("sigma_texp", C.c_double), ("cv_texp", C.c_double), ("T_ref", C.c_double),
+                ("dsa", C.c_int32), ("dsa_tol", C.c_double), ("dsa_max_iter", C.c_int32)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -52,7 +53,7 @@ class DlrStats(C.Structure):
                 ("cell_angle_updates", C.c_int64), ("si_iters_last", C.c_int32),
                 ("status", C.c_int32), ("ms_si_total", C.c_double), ("ms_step_total", C.c_double),
                 ("si_launches", C.c_int64), ("kernel_launches", C.c_int64),
-                ("nonpositive_cells", C.c_int64)]
+                ("nonpositive_cells", C.c_int64), ("dsa_iters_total", C.c_int64)]
 
 
 _lib = None

@@ -26,10 +26,10 @@
 namespace dlr {
 // launchers defined in the kernel translation units
 template <typename real> cudaError_t launch_si(const Inst *, const SiCtl &, int, cudaStream_t);
-template <typename real> int si_max_grid(int, int, int, int);
+template <typename real> int si_max_grid(int, int, int, int, int);
 int si_sweep_warps(bool mixed);
 int si_sweep_lag(bool mixed);
-template <typename real> size_t si_smem_bytes(int, int, int, int);
+template <typename real> size_t si_smem_bytes(int, int, int, int, int);
 template <typename real> cudaError_t launch_sn_init(void *, const double *, int, int, double, double, cudaStream_t);
 template <typename real> cudaError_t launch_sn_prep(const Inst *, int, int, cudaStream_t);
 template <typename real> cudaError_t launch_sn_tupdate(const Inst *, int, int, cudaStream_t);
@@ -137,6 +137,7 @@ struct dlr_handle {
   int lb = 1;    // blocks of the per-angle L-step
   // device counters: [0] total SI iterations
   long long *d_iters_total = nullptr;
+  long long *d_dsa_iters_total = nullptr;  // CG iterations of the DSA solves
   int *h_status = nullptr;  // pinned mirror of the device status
   int64_t steps = 0;
   bool timing = false;
@@ -393,6 +394,7 @@ static Sizes sizes_of(const dlr_problem *p, int sms) {
     s.partial_doubles = 0;
     s.total = 5 * al((size_t)s.N * 8) + 6 * al((size_t)s.N * s.rs) + 2 * al((size_t)s.N * s.K * s.rs) +
               3 * al((size_t)s.K * 8) + al((size_t)s.K * 4) + al(64) * 4 + al(sizeof(Inst));
+    if (p->dsa) s.total += kDsaArrays * al((size_t)s.N * s.rs) + al(64);
     return s;
   }
   // CTAs of the cell and angle reductions: whole clusters of kCl CTAs,
@@ -420,6 +422,7 @@ static Sizes sizes_of(const dlr_problem *p, int sms) {
   t += al((size_t)s.K * r * r * 8) + al((size_t)s.K * r * 4);  // lu, piv
   t += al(s.partial_doubles * 8);
   t += al(64) * 4 + al(sizeof(Inst));           // status, iters, conv, totals, inst
+  if (p->dsa) t += kDsaArrays * al((size_t)s.N * s.rs) + al(64);  // DSA coefficients, CG vectors
   s.total = t;
   return s;
 }
@@ -459,6 +462,8 @@ static int validate(const dlr_problem *p) {
     if (K > 1024 || p->selection != DLR_SEL_QDEIM)
       return fail(DLR_EINVAL, "augmented step: needs NOm <= 1024 and the pivoted-QR angle choice");
   }
+  if (p->dsa != 0 && p->dsa != 1) return fail(DLR_EINVAL, "dsa must be 0 or 1");
+  if (!std::isfinite(p->dsa_tol) || p->dsa_tol >= 1.0) return fail(DLR_EINVAL, "dsa_tol must be finite and < 1");
   if (!p->sigma || !p->rho_cv || !p->T0) return fail(DLR_EINVAL, "sigma, rho_cv, T0 must be given");
   for (long long c = 0; c < N; ++c) {
     if (!(p->sigma[c] >= 0) || !std::isfinite(p->sigma[c])) return fail(DLR_EINVAL, "sigma[%lld] invalid", c);
@@ -470,8 +475,8 @@ static int validate(const dlr_problem *p) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const int gam = sn ? (int)K : kMaxRank;
-  const size_t need = p->precision == DLR_MIXED ? si_smem_bytes<float>(p->nx, (p->ny + 31) / 32, 256, gam)
-                                                : si_smem_bytes<double>(p->nx, (p->ny + 31) / 32, 256, gam);
+  const size_t need = p->precision == DLR_MIXED ? si_smem_bytes<float>(p->nx, (p->ny + 31) / 32, 256, gam, p->dsa)
+                                                : si_smem_bytes<double>(p->nx, (p->ny + 31) / 32, 256, gam, p->dsa);
   if (optin > 0 && need > (size_t)optin) return fail(DLR_EINVAL, "nx = %d too large for the sweep's shared memory", p->nx);
   return DLR_OK;
 }
@@ -507,6 +512,38 @@ static void fill_common(dlr_handle *h, const dlr_problem *problem) {
   I.sig_texp = problem->sigma_texp;
   I.cv_texp = problem->cv_texp;
   I.T_ref = problem->T_ref > 0 ? problem->T_ref : 1.0;
+  // DSA (Section 4.5): penalty kappa = (1/8 pi) sum_k w_k |Om_k . n| per face
+  // orientation; the stencil coefficients are scaled by 1/h^2
+  I.dsa = problem->dsa;
+  I.dsa_tol = problem->dsa_tol > 0 ? problem->dsa_tol : 0.1;
+  I.dsa_max_iter = problem->dsa_max_iter > 0 ? problem->dsa_max_iter : 500;
+  double kx = 0, ky = 0;
+  for (int k = 0; k < h->K; ++k) {
+    kx += h->w[k] * std::fabs(h->ox[k]);
+    ky += h->w[k] * std::fabs(h->oy[k]);
+  }
+  kx /= 8.0 * kPi;
+  ky /= 8.0 * kPi;
+  I.dsa_cx = 1.0 / (12.0 * I.hx * I.hx);
+  I.dsa_cy = 1.0 / (12.0 * I.hy * I.hy);
+  I.dsa_kx = kx / I.hx;
+  I.dsa_ky = ky / I.hy;
+  I.dsa_ist = I.dsa_dg = I.dsa_dinv = I.dsa_x = I.dsa_r = I.dsa_z = I.dsa_p0 = I.dsa_p1 = I.dsa_q = nullptr;
+  I.dsa_iters_total = nullptr;
+}
+
+// Device arrays of the DSA solve (N each, working precision): 1/sigma_t,
+// the diagonal and its inverse, x, r, z, two search directions, q.
+template <typename Alloc>
+static void alloc_dsa(dlr_handle *h, Alloc &A) {
+  Inst &I = h->inst;
+  if (!I.dsa) return;
+  const size_t b = (size_t)h->N * h->rs;
+  void **v[kDsaArrays] = {&I.dsa_ist, &I.dsa_dg, &I.dsa_dinv, &I.dsa_x, &I.dsa_r,
+                          &I.dsa_z, &I.dsa_p0, &I.dsa_p1, &I.dsa_q};
+  for (int k = 0; k < kDsaArrays; ++k) *v[k] = A(b);
+  I.dsa_iters_total = (unsigned long long *)A(64);
+  h->d_dsa_iters_total = (long long *)I.dsa_iters_total;
 }
 
 // Full-rank SN handle: the per-cell state of Algorithm 1's sweeps, psi and
@@ -554,6 +591,7 @@ static int create_sn(dlr_handle *h, const dlr_problem *problem, dlr_handle **out
   I.conv = (unsigned long long *)A(64);
   h->d_iters_total = (long long *)A(64);
   I.iters_total = (unsigned long long *)h->d_iters_total;
+  alloc_dsa(h, A);
   if (!ok) {
     dev_free_all(h);
     if (h->own_stream) cudaStreamDestroy(h->st);
@@ -585,6 +623,7 @@ static int create_sn(dlr_handle *h, const dlr_problem *problem, dlr_handle **out
   chain(cudaMemsetAsync(I.nonpos, 0, 64, h->st));
   chain(cudaMemsetAsync(I.iters, 0, 64, h->st));
   chain(cudaMemsetAsync(h->d_iters_total, 0, 64, h->st));
+  if (h->d_dsa_iters_total) chain(cudaMemsetAsync(h->d_dsa_iters_total, 0, 64, h->st));
   if (e == cudaSuccess)
     e = h->mixed ? launch_sn_init<float>(I.Psi, I.T, N, K, problem->a_rad, problem->c, h->st)
                  : launch_sn_init<double>(I.Psi, I.T, N, K, problem->a_rad, problem->c, h->st);
@@ -710,6 +749,7 @@ int dlr_create(const dlr_problem *problem, const dlr_runtime *runtime, dlr_handl
   I.conv = (unsigned long long *)A(64);
   h->d_iters_total = (long long *)A(64);
   I.iters_total = (unsigned long long *)h->d_iters_total;
+  alloc_dsa(h, A);
   if (!ok) {
     dev_free_all(h);
     delete h;
@@ -753,6 +793,7 @@ int dlr_create(const dlr_problem *problem, const dlr_runtime *runtime, dlr_handl
   chain(cudaMemsetAsync(I.nonpos, 0, 64, h->st));
   chain(cudaMemsetAsync(I.iters, 0, 64, h->st));
   chain(cudaMemsetAsync(h->d_iters_total, 0, 64, h->st));
+  if (h->d_dsa_iters_total) chain(cudaMemsetAsync(h->d_dsa_iters_total, 0, 64, h->st));
   chain(cudaMemsetAsync(I.idx, 0xff, (size_t)r * 4, h->st));
   chain(cudaMemsetAsync(I.small, 0, (size_t)I.lay.total * 8, h->st));
   // the host vectors above are released on return: wait for the copies
@@ -920,8 +961,10 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
     b->bands_max = std::max(b->bands_max, (h->prob.ny + 31) / 32);
   }
   const int gam_max = b->sn ? b->rmax : kMaxRank;  // scalar-flux weights of k_si
-  const int gmax = b->mixed ? si_max_grid<float>(b->nx_max, b->bands_max, n, gam_max)
-                            : si_max_grid<double>(b->nx_max, b->bands_max, n, gam_max);
+  int any_dsa = 0;
+  for (int i = 0; i < n; ++i) any_dsa |= hs[i]->inst.dsa ? 1 : 0;
+  const int gmax = b->mixed ? si_max_grid<float>(b->nx_max, b->bands_max, n, gam_max, any_dsa)
+                            : si_max_grid<double>(b->nx_max, b->bands_max, n, gam_max, any_dsa);
   if (gmax <= 0) {
     delete b;
     return fail(DLR_ECUDA, "the source-iteration kernel does not fit on this GPU");
@@ -949,6 +992,8 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   const int gedge_ld = (b->nx_max + 3) / 4 * 4 * (b->mixed ? 1 : 2);  // 64-bit words
   bytes += sz(sizeof(SiUnit) * b->units_cap) + sz(64) * 4;
   bytes += sz(sizeof(unsigned long long) * gedge_ld * std::max(1, rows_cap));
+  const size_t dsa_part = any_dsa ? (size_t)n * kDsaSlots * gmax : 0;  // per-CTA CG partials
+  bytes += sz(sizeof(double) * std::max<size_t>(1, dsa_part));
   if (cudaMalloc(&b->d_mem, bytes) != cudaSuccess) {
     delete b;
     return fail(DLR_ENOMEM, "batch table allocation failed");
@@ -1000,6 +1045,8 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   b->ctl.gedge = carve<unsigned long long>(cur, (size_t)gedge_ld * std::max(1, rows_cap));
   b->ctl.n_rows = rows_cap;
   b->ctl.gedge_ld = gedge_ld;
+  b->ctl.dsa_part = carve<double>(cur, std::max<size_t>(1, dsa_part));
+  b->ctl.any_dsa = any_dsa;
   b->ctl.force_iters = 0;
   b->ctl.units = b->d_units;
   b->ctl.n_units = (int)units.size();
@@ -1673,6 +1720,9 @@ int dlr_get_stats(dlr_handle *h, dlr_stats *out) {
     for (auto e : ev) h->ev_pool.push_back(e);
   }
   h->ev_pending.clear();
+  long long dsa_tot = 0;
+  if (h->d_dsa_iters_total) CK(cudaMemcpy(&dsa_tot, h->d_dsa_iters_total, sizeof dsa_tot, cudaMemcpyDeviceToHost));
+  out->dsa_iters_total = dsa_tot;
   out->steps = h->steps;
   out->si_iters_total = tot;
   out->cell_angle_updates = tot * (long long)h->N * h->r;
@@ -1712,8 +1762,8 @@ int dlr_sweep(int32_t nx, int32_t ny, double lx, double ly, int32_t n_dir, const
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int bands = (ny + 31) / 32;
-    const size_t need = precision == DLR_MIXED ? si_smem_bytes<float>(nx, bands, 0, 0)
-                                               : si_smem_bytes<double>(nx, bands, 0, 0);
+    const size_t need = precision == DLR_MIXED ? si_smem_bytes<float>(nx, bands, 0, 0, 0)
+                                               : si_smem_bytes<double>(nx, bands, 0, 0, 0);
     if (optin > 0 && need > (size_t)optin)
       return fail(DLR_EINVAL, "nx = %d too large for the sweep's shared memory", nx);
   }

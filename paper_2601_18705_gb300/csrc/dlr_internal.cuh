@@ -117,6 +117,14 @@ struct Inst {
   // temperature-dependent materials, taken at the step's T0:
   // sigma(T) = sigma (T/T_ref)^-sig_texp, rho c_v(T) = rho_cv (T/T_ref)^cv_texp
   double sig_texp, cv_texp, T_ref;
+  // diffusion synthetic acceleration of the source iteration (Section 4.5;
+  // dsa = 0: off).  Per cell (real): 1/sigma_t, the diagonal of the DSA
+  // operator and its inverse, and the CG vectors.  dsa_cx = 1/(12 hx^2),
+  // dsa_kx = kappa_x / hx (likewise in y): the stencil scaled by 1/h^2.
+  int dsa, dsa_max_iter;
+  double dsa_tol, dsa_cx, dsa_cy, dsa_kx, dsa_ky;
+  void *dsa_ist, *dsa_dg, *dsa_dinv, *dsa_x, *dsa_r, *dsa_z, *dsa_p0, *dsa_p1, *dsa_q;
+  unsigned long long *dsa_iters_total;  // CG iterations summed over all steps
 };
 
 __device__ __forceinline__ double sigma_at(const Inst &I, int c, double T0) {
@@ -237,7 +245,15 @@ struct SiCtl {
   int n_rows, gedge_ld;
   int force_iters;             // > 0: every instance runs exactly this many iterations
                                // and its iteration counters are left alone (timing runs)
+  int any_dsa;                 // some instance accelerates its iteration (Section 4.5)
+  double *dsa_part;            // per-CTA partial sums of the DSA CG: n_inst x kDsaSlots x grid
 };
+
+// partial sums of one DSA CG iteration: p.q, r.z, r.r, and b.b of the
+// right-hand side
+constexpr int kDsaSlots = 4;
+// per-cell device arrays of the DSA solve
+constexpr int kDsaArrays = 9;
 
 // Four consecutive elements, aligned for one vector shared-memory access.
 template <typename real> struct alignas(4 * sizeof(real)) Quad { real v[4]; };

@@ -30,6 +30,7 @@
 // all instances: sweep phase, grid barrier, scalar-flux phase
 // phi = sum_j gamma_j psi_j with the convergence test, grid barrier.
 #include "dlr_internal.cuh"
+#include "k_dsa.cuh"
 
 namespace dlr {
 
@@ -542,6 +543,9 @@ k_si(const Inst *__restrict__ insts, SiCtl ctl) {
   off += (size_t)(ctl.bands_max + 3) / 4 * 4 * sizeof(int);
   int *active = reinterpret_cast<int *>(smem + off);
   off += (size_t)(ctl.n_inst + 3) / 4 * 4 * sizeof(int);
+  double *dsa_sc = reinterpret_cast<double *>(smem + off);  // CG scalars (DSA)
+  int *dsa_on = reinterpret_cast<int *>(smem + off + dsa_scalar_bytes(ctl.n_inst, ctl.any_dsa));
+  off += dsa_smem_bytes(ctl.n_inst, ctl.any_dsa);
   real *gam = reinterpret_cast<real *>(smem + off);  // gam_max scalar-flux weights
   S.edge_ld = edge_ld(ctl.nx_max);
   __shared__ int unit_s, n_active_s;
@@ -552,6 +556,11 @@ k_si(const Inst *__restrict__ insts, SiCtl ctl) {
   // tags of the edge words: 20 bits of the launch counter, 12 of the iteration
   const unsigned epoch_tag = (*(volatile unsigned *)ctl.epoch & 0xfffffu) << 12;
   __syncthreads();
+  if (ctl.any_dsa) {
+    // DSA coefficients of this step (read after the first grid barrier)
+    for (int i = 0; i < ctl.n_inst; ++i)
+      if (active[i] && insts[i].dsa) dsa_setup<real>(insts[i]);
+  }
 
   for (int it = 0;; ++it) {
     if (threadIdx.x == 0) {
@@ -603,14 +612,39 @@ k_si(const Inst *__restrict__ insts, SiCtl ctl) {
       for (int j = threadIdx.x; j < r; j += blockDim.x)
         gam[j] = real(I.gamma_ext ? I.gamma_ext[j] : I.small[I.lay.gamma + j]);
       __syncthreads();
+      // the convergence test measures the sweeps' change phi^{l+1/2} - phi^l,
+      // with or without DSA (the DSA correction multiplies rounding noise by
+      // up to sigma_s / sigma_a, so phi^{l+1} - phi^l would stall above a
+      // tolerance near the working precision)
       real dmax = real(0), pmax = real(0);  // |differences| and |phi| in the working precision
-      for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-        real acc = real(0);
-        for (int j = 0; j < r; ++j) acc = fmadd(gam[j], psi[(size_t)N * j + c], acc);
-        pnew[c] = acc;
-        sphi[c] = ss4[c] * acc;
-        dmax = max(dmax, abs(acc - pold[c]));
-        pmax = max(pmax, abs(acc));
+      if (I.dsa) {
+        // phi^{l+1/2}, and the right-hand side of its DSA correction
+        double rz = 0, bb = 0;
+        for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+          real acc = real(0);
+          for (int j = 0; j < r; ++j) acc = fmadd(gam[j], psi[(size_t)N * j + c], acc);
+          pnew[c] = acc;
+          const real po = pold[c];
+          dsa_rhs<real>(I, c, acc, po, rz, bb);
+          dmax = max(dmax, abs(acc - po));
+          pmax = max(pmax, abs(acc));
+        }
+        __shared__ double red[32];
+        rz = block_sum(rz, red);
+        bb = block_sum(bb, red);
+        if (threadIdx.x == 0) {
+          dsa_slot(ctl, i, kDsaRz)[blockIdx.x] = rz;
+          dsa_slot(ctl, i, kDsaBb)[blockIdx.x] = bb;
+        }
+      } else {
+        for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+          real acc = real(0);
+          for (int j = 0; j < r; ++j) acc = fmadd(gam[j], psi[(size_t)N * j + c], acc);
+          pnew[c] = acc;
+          sphi[c] = ss4[c] * acc;
+          dmax = max(dmax, abs(acc - pold[c]));
+          pmax = max(pmax, abs(acc));
+        }
       }
       dmax = warp_max(dmax);
       pmax = warp_max(pmax);
@@ -620,6 +654,29 @@ k_si(const Inst *__restrict__ insts, SiCtl ctl) {
       }
     }
     if (!grid_barrier(ctl.bar, abort_flag)) break;
+
+    if (ctl.any_dsa) {
+      // ---- DSA: delta from A delta = sigma_s (phi^{l+1/2} - phi^l), then
+      // phi^{l+1} = phi^{l+1/2} + delta feeds the next sweeps ----
+      for (int i = threadIdx.x; i < ctl.n_inst; i += blockDim.x)
+        dsa_on[i] = active[i] && insts[i].dsa;
+      __syncthreads();
+      if (!dsa_solve<real>(insts, ctl, dsa_on, dsa_sc, abort_flag)) break;
+      for (int i = 0; i < ctl.n_inst; ++i) {
+        if (!active[i] || !insts[i].dsa) continue;
+        const Inst &I = insts[i];
+        const int N = I.N;
+        const real *ss4 = as_c<real>(I.ss4), *x = as_c<real>(I.dsa_x);
+        real *pnew = as<real>((it & 1) ? I.phi0 : I.phi1);
+        real *sphi = as<real>(I.sphi);
+        for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+          const real v = pnew[c] + x[c];
+          pnew[c] = v;
+          sphi[c] = ss4[c] * v;
+        }
+      }
+      if (!grid_barrier(ctl.bar, abort_flag)) break;
+    }
 
     // ---- phase C: every CTA takes the same decision per instance ----
     __syncthreads();
@@ -730,18 +787,18 @@ cudaError_t launch_si_prep(const Inst *d, int n, SiCtl ctl, cudaStream_t st) {
 }
 
 template <typename real>
-size_t si_smem_bytes(int nx_max, int bands_max, int n_inst, int gam_max) {
+size_t si_smem_bytes(int nx_max, int bands_max, int n_inst, int gam_max, int dsa) {
   constexpr int NW = SweepCfg<real>::NW;
   using real2 = typename Real2<real>::type;
   return (size_t)NW * kRing * kRingLd * sizeof(real2) + (size_t)(NW + 1) * edge_ld(nx_max) * sizeof(real) +
          (size_t)(bands_max + 3) / 4 * 4 * sizeof(int) + (size_t)(n_inst + 3) / 4 * 4 * sizeof(int) +
-         (size_t)gam_max * sizeof(real);
+         dsa_smem_bytes(n_inst, dsa) + (size_t)gam_max * sizeof(real);
 }
 
 template <typename real>
 cudaError_t launch_si(const Inst *d_insts, const SiCtl &ctl, int grid, cudaStream_t st) {
   constexpr int NW = SweepCfg<real>::NW;
-  size_t smem = si_smem_bytes<real>(ctl.nx_max, ctl.bands_max, ctl.n_inst, ctl.gam_max);
+  size_t smem = si_smem_bytes<real>(ctl.nx_max, ctl.bands_max, ctl.n_inst, ctl.gam_max, ctl.any_dsa);
   cudaError_t e = cudaFuncSetAttribute(k_si<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
@@ -759,9 +816,9 @@ cudaError_t launch_si(const Inst *d_insts, const SiCtl &ctl, int grid, cudaStrea
 }
 
 template <typename real>
-int si_max_grid(int nx_max, int bands_max, int n_inst, int gam_max) {
+int si_max_grid(int nx_max, int bands_max, int n_inst, int gam_max, int dsa) {
   constexpr int NW = SweepCfg<real>::NW;
-  size_t smem = si_smem_bytes<real>(nx_max, bands_max, n_inst, gam_max);
+  size_t smem = si_smem_bytes<real>(nx_max, bands_max, n_inst, gam_max, dsa);
   if (cudaFuncSetAttribute(k_si<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return 0;
@@ -780,7 +837,7 @@ cudaError_t launch_sweep_dirs(int nx, int ny, double hx, double hy, int n_dir,
                               const real *src, real *psi, int *d_abort, cudaStream_t st) {
   constexpr int NW = SweepCfg<real>::NW;
   const int bands = (ny + 31) / 32;
-  size_t smem = si_smem_bytes<real>(nx, bands, 0, 0);
+  size_t smem = si_smem_bytes<real>(nx, bands, 0, 0, 0);
   cudaError_t e = cudaFuncSetAttribute(k_sweep_dirs<real>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -792,12 +849,12 @@ cudaError_t launch_sweep_dirs(int nx, int ny, double hx, double hy, int n_dir,
 int si_sweep_warps(bool mixed) { return mixed ? SweepCfg<float>::NW : SweepCfg<double>::NW; }
 int si_sweep_lag(bool mixed) { return 32 + (mixed ? SweepCfg<float>::kSub : SweepCfg<double>::kSub); }
 
-template size_t si_smem_bytes<float>(int, int, int, int);
-template size_t si_smem_bytes<double>(int, int, int, int);
+template size_t si_smem_bytes<float>(int, int, int, int, int);
+template size_t si_smem_bytes<double>(int, int, int, int, int);
 template cudaError_t launch_si<float>(const Inst *, const SiCtl &, int, cudaStream_t);
 template cudaError_t launch_si<double>(const Inst *, const SiCtl &, int, cudaStream_t);
-template int si_max_grid<float>(int, int, int, int);
-template int si_max_grid<double>(int, int, int, int);
+template int si_max_grid<float>(int, int, int, int, int);
+template int si_max_grid<double>(int, int, int, int, int);
 template cudaError_t launch_sweep_dirs<float>(int, int, double, double, int, const double *,
                                               const double *, const float *, const float *,
                                               float *, int *, cudaStream_t);

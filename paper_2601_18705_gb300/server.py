@@ -55,7 +55,8 @@ class ServeReport:
                 "cell_angle_updates_per_s": self.updates_total / self.wall,
                 "wall_s": self.wall, "ticks": self.ticks, "max_active": self.max_active,
                 "admission_waits": self.admission_waits, "peak_bytes": self.peak_bytes,
-                "failed": len(self.failures)}
+                "failed": len(self.failures),
+                "failures": [list(f) for f in self.failures]}
 
 
 class Server:

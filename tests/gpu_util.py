@@ -9,18 +9,21 @@ def rel_l2(a, b) -> float:
 
 
 def run_pair(case, precision, steps, *, orc, dlr, forced=None, si_fixed_iters=0, si_tol=None,
-             selection=0, start=None, allow_nonpositive=0, split=None, augment=0):
+             selection=0, start=None, allow_nonpositive=0, split=None, augment=0, dsa=0,
+             dsa_tol=0.1, dsa_max_iter=500, iters_out=None):
     """Runs the oracle and the GPU solver side by side from the same state.
     Returns per-step (T error, psi error, oracle idx, gpu idx) and both states.
     When the GPU picks different angles than the oracle (a near-tie), the
     oracle step is repeated with the GPU's indices."""
     from conftest import oracle_problem
     p = oracle_problem(case)
+    p.dsa, p.dsa_tol, p.dsa_max_iter = dsa, dsa_tol, dsa_max_iter
     kw = {}
     if si_fixed_iters:
         kw["si_fixed_iters"] = si_fixed_iters
     spec = dlr.problem_from_case(case, precision=precision, selection=selection,
-                                 allow_nonpositive=allow_nonpositive, augment=augment, **kw)
+                                 allow_nonpositive=allow_nonpositive, augment=augment, dsa=dsa,
+                                 dsa_tol=dsa_tol, dsa_max_iter=dsa_max_iter, **kw)
     if si_tol is not None:
         spec.si_tol = si_tol
     T = case["T0"].reshape(-1).copy()
@@ -47,6 +50,8 @@ def run_pair(case, precision, steps, *, orc, dlr, forced=None, si_fixed_iters=0,
                                                     augment=augment)
                 assert res2.rc == 0
             X, S, W, T = X1, S1, W1, T1
+            if iters_out is not None:
+                iters_out.append((res.iters, s.stats()["si_iters_last"], res.diag["dsa_iters"]))
             Tg = s.T()
             psig = s.psi()
             out.append((rel_l2(Tg, T), rel_l2(psig, X @ S @ W.T), res.idx.copy(), gidx.copy()))

@@ -74,3 +74,31 @@ def test_oracle_and_product_are_independent():
         if f.endswith((".py", ".c", ".h")):
             txt = open(os.path.join(ROOT, "oracle", f)).read()
             assert "paper_2601_18705_gb300" not in txt and "dlr.h" not in txt, f
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    # the ctypes mirrors of the public structs against the C compiler's layout
+    import shutil
+    import subprocess
+    from paper_2601_18705_gb300 import _lib
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"dlr_problem": _lib.DlrProblem, "dlr_stats": _lib.DlrStats,
+               "dlr_runtime": _lib.DlrRuntime}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dlr.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                       text=True).stdout.splitlines())
+    for cname, py in structs.items():
+        assert int(got[cname]) == C.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(got[f"{cname}.{f}"]) == getattr(py, f).offset, f"{cname}.{f}"
