@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-aug", action="store_true", help="skip the augmented (rank-2r) step")
     ap.add_argument("--no-dsa", action="store_true", help="skip the DSA-accelerated step")
     ap.add_argument("--dsa", action="store_true", help="served: every request with DSA")
+    ap.add_argument("--dsa-max-iter", type=int, default=0, help="CG cap per DSA solve (0: the library's)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="CPU work of the oracle sample")
     ap.add_argument("--kernel", default=None, choices=["sweep"],
@@ -387,7 +388,8 @@ def run_gpu(args):
     # ---- the same steps with DSA-accelerated source iteration (Section 4.5) ----
     dsa = None
     if not args.no_dsa and rank == 0:
-        s6 = dlr.Solver(dlr.problem_from_case(case, precision=dlr.DLR_MIXED, allow_nonpositive=1, dsa=1))
+        s6 = dlr.Solver(dlr.problem_from_case(case, precision=dlr.DLR_MIXED, allow_nonpositive=1, dsa=1,
+                                              dsa_max_iter=args.dsa_max_iter))
         s6.step(args.warmup)
         s6.stream.synchronize()
         d0 = s6.stats()
@@ -398,7 +400,8 @@ def run_gpu(args):
         ud = d1["cell_angle_updates"] - d0["cell_angle_updates"]
         td = sum(ms_dsa)
         si_d = d1["si_iters_total"] - d0["si_iters_total"]
-        dsa = {"method": "DSA-accelerated source iteration (Jacobi-PCG, dsa_tol 0.1), mixed",
+        dsa = {"method": "DSA-accelerated source iteration (Jacobi-PCG, dsa_tol 0.1, at most "
+                         f"{args.dsa_max_iter or 3} CG iterations per solve), mixed",
                "ms_per_step": td / args.steps, "dlr_steps_per_s": args.steps / (td / 1e3),
                "si_iters_per_step": si_d / args.steps,
                "cg_iters_per_si_iter": (d1["dsa_iters_total"] - d0["dsa_iters_total"]) / max(si_d, 1),
@@ -545,7 +548,8 @@ def run_served(args):
             for t, q in workloads.served_requests(n=args.requests)]
     if args.dsa:
         for q in reqs:
-            q.spec = dlr.problem_from_case(q.case, precision=q.precision, allow_nonpositive=1, dsa=1)
+            q.spec = dlr.problem_from_case(q.case, precision=q.precision, allow_nonpositive=1, dsa=1,
+                                           dsa_max_iter=args.dsa_max_iter)
     srv = server.Server(max_active=args.max_active, hbm_budget=int(args.hbm_budget_gb * 2 ** 30))
     rep = srv.run(reqs, realtime=True)
     s = rep.summary()

@@ -125,9 +125,11 @@ typedef struct dlr_problem {
                             of sweeps' change of phi.  Either method; 0 = off */
   double dsa_tol;        /* CG stop: ||r||_2 <= dsa_tol ||b||_2 (<= 0: 0.1;
                             must be < 1) */
-  int32_t dsa_max_iter;  /* CG iteration cap per solve (<= 0: 500); reaching
+  int32_t dsa_max_iter;  /* CG iteration cap per solve (<= 0: 3); reaching
                             it is not an error (the correction only
-                            accelerates the iteration) */
+                            accelerates the iteration, and a few CG
+                            iterations already remove most source
+                            iterations) */
 } dlr_problem;
 
 /* Device memory and stream supplied by the caller (e.g. PyTorch). */

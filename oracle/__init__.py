@@ -149,8 +149,8 @@ class Problem:
     cv_texp: float = 0.0      # rho c_v(T) = rho_cv (T/T_ref)^cv_texp
     T_ref: float = 1.0
     dsa: int = 0              # diffusion synthetic acceleration (Section 4.5, reading R17)
-    dsa_tol: float = 1e-6     # CG stop: ||r||_2 <= dsa_tol ||b||_2
-    dsa_max_iter: int = 1000
+    dsa_tol: float = 0.1      # CG stop: ||r||_2 <= dsa_tol ||b||_2
+    dsa_max_iter: int = 3
     _keep: list = field(default_factory=list, repr=False)
 
     @property

@@ -55,7 +55,7 @@ class ProblemSpec:
     T_ref: float = 1.0
     dsa: int = 0             # 1: diffusion synthetic acceleration of the source iteration
     dsa_tol: float = 0.0     # CG stop ||r|| <= dsa_tol ||b|| (0: 0.1)
-    dsa_max_iter: int = 0    # CG cap per solve (0: 500)
+    dsa_max_iter: int = 0    # CG cap per solve (0: 3)
 
     def cstruct(self):
         keep = [_f64(self.sigma), _f64(self.rho_cv), _f64(self.T0)]

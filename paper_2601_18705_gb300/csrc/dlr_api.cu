@@ -516,7 +516,7 @@ static void fill_common(dlr_handle *h, const dlr_problem *problem) {
   // orientation; the stencil coefficients are scaled by 1/h^2
   I.dsa = problem->dsa;
   I.dsa_tol = problem->dsa_tol > 0 ? problem->dsa_tol : 0.1;
-  I.dsa_max_iter = problem->dsa_max_iter > 0 ? problem->dsa_max_iter : 500;
+  I.dsa_max_iter = problem->dsa_max_iter > 0 ? problem->dsa_max_iter : 3;
   double kx = 0, ky = 0;
   for (int k = 0; k < h->K; ++k) {
     kx += h->w[k] * std::fabs(h->ox[k]);

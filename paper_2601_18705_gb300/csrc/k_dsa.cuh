@@ -55,6 +55,7 @@ template <typename real>
 __device__ void dsa_setup(const Inst &I) {
   const real *st = as_c<real>(I.sig_t), *ss4 = as_c<real>(I.ss4);
   real *ist = as<real>(I.dsa_ist), *dg = as<real>(I.dsa_dg), *dinv = as<real>(I.dsa_dinv);
+  real *p1 = as<real>(I.dsa_p1);
   const int nx = I.nx, ny = I.ny, N = I.N;
   const real cx = real(I.dsa_cx), cy = real(I.dsa_cy);
   const real k2 = real(2.0 * (I.dsa_kx + I.dsa_ky));
@@ -68,6 +69,7 @@ __device__ void dsa_setup(const Inst &I) {
     ist[c] = real(1) / st[c];
     dg[c] = d;
     dinv[c] = real(1) / d;
+    p1[c] = real(0);  // p_old of the first CG iteration (beta = 0 there)
   }
 }
 
@@ -94,10 +96,22 @@ __device__ __forceinline__ void dsa_sum2(const SiCtl &ctl, const int *on, int s0
   for (int i = wid; i < ctl.n_inst; i += nw) {
     if (!on[i]) continue;
     const double *p0 = dsa_slot(ctl, i, s0), *p1 = dsa_slot(ctl, i, s1);
+    // up to 8 partials per lane per round, all loads issued before the adds
     double v0 = 0, v1 = 0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) {
-      v0 += p0[b];
-      v1 += p1[b];
+    for (int b0 = 0; b0 < (int)gridDim.x; b0 += 256) {
+      double a0[8], a1[8];
+#pragma unroll
+      for (int g = 0; g < 8; ++g) {
+        const int b = b0 + g * 32 + lane;
+        const bool ok = b < (int)gridDim.x;
+        a0[g] = ok ? p0[b] : 0.0;
+        a1[g] = ok ? p1[b] : 0.0;
+      }
+#pragma unroll
+      for (int g = 0; g < 8; ++g) {
+        v0 += a0[g];
+        v1 += a1[g];
+      }
     }
     v0 = warp_sum(v0);
     v1 = warp_sum(v1);
@@ -109,10 +123,131 @@ __device__ __forceinline__ void dsa_sum2(const SiCtl &ctl, const int *on, int s0
   __syncthreads();
 }
 
-// z + beta p_old at cell c (the first iteration has p = z)
+// P1 of one instance: u = z + beta p_old (u = z in the first iteration),
+// then q = A u, p = u.  A warp takes 32 cells of one row (lane = x offset):
+// the x-neighbours come from its lanes by shuffles plus a halo of four cells
+// (x0 - 2, x0 - 1, x0 + 32, x0 + 33) loaded by lanes 0-3, the y-neighbours
+// from the rows above and below; a cell outside the mesh counts as 0 (u and
+// 1/sigma_t), which drops exactly the terms the stencil drops.
 template <typename real>
-__device__ __forceinline__ real dsa_dir(const real *z, const real *po, real beta, bool first, int c) {
-  return first ? z[c] : fmadd(beta, po[c], z[c]);
+struct DsaP1 {
+  const real *__restrict__ z;
+  const real *__restrict__ po;
+  const real *__restrict__ ist;
+  const real *__restrict__ dg;
+  real *__restrict__ pn;
+  real *__restrict__ q;
+  int nx, ny;
+  real beta, cx, cy, kx, ky;
+
+  // The values one lane loads for one 32-cell segment (row iy, cells x0 ..
+  // x0 + 31), gathered before any of them is used so that the loads of
+  // several segments are in flight together.
+  struct Seg {
+    int c;       // this lane's cell (valid only if in)
+    bool in;     // this lane's cell is inside the mesh
+    real uc, ic, uh, ih, un1, un2, us1, us2, in1, is1, dc;
+  };
+  // u = z + beta p_old at cell c if ok, else 0 (p_old is zero before the
+  // first iteration, where beta = 0)
+  __device__ __forceinline__ real u(bool ok, int c) const {
+    return ok ? fmadd(beta, po[c], z[c]) : real(0);
+  }
+  __device__ __forceinline__ void load(Seg &S, int iy, int x0) const {
+    const int lane = threadIdx.x & 31, ix = x0 + lane;
+    // row tests are the same for the whole warp
+    const bool r0 = (unsigned)iy < (unsigned)ny;
+    const bool rn1 = r0 && iy >= 1, rn2 = r0 && iy >= 2;
+    const bool rs1 = r0 && iy + 1 < ny, rs2 = r0 && iy + 2 < ny;
+    const bool col = ix < nx;
+    const int c = iy * nx + ix;
+    // halo cells of lanes 0-3: x0 - 2, x0 - 1, x0 + 32, x0 + 33
+    const int hd = lane < 2 ? -2 : 30;  // offset of the halo cell from ix
+    const int hx = ix + hd;
+    const bool hok = r0 && lane < 4 && (unsigned)hx < (unsigned)nx;
+    S.c = c;
+    S.in = r0 && col;
+    S.uc = u(S.in, c);
+    S.ic = S.in ? ist[c] : real(0);
+    S.uh = u(hok, c + hd);
+    S.ih = hok ? ist[c + hd] : real(0);
+    S.un1 = u(rn1 && col, c - nx);
+    S.un2 = u(rn2 && col, c - 2 * nx);
+    S.us1 = u(rs1 && col, c + nx);
+    S.us2 = u(rs2 && col, c + 2 * nx);
+    S.in1 = rn1 && col ? ist[c - nx] : real(0);
+    S.is1 = rs1 && col ? ist[c + nx] : real(0);
+    S.dc = S.in ? dg[c] : real(0);
+  }
+  // q = A u and p = u for the segment; returns this lane's u q (0 outside)
+  __device__ __forceinline__ double finish(const Seg &S) const {
+    const int lane = threadIdx.x & 31;
+    real um1 = __shfl_up_sync(0xffffffffu, S.uc, 1), um2 = __shfl_up_sync(0xffffffffu, S.uc, 2);
+    real up1 = __shfl_down_sync(0xffffffffu, S.uc, 1), up2 = __shfl_down_sync(0xffffffffu, S.uc, 2);
+    real im1 = __shfl_up_sync(0xffffffffu, S.ic, 1), ip1 = __shfl_down_sync(0xffffffffu, S.ic, 1);
+    const real h0 = __shfl_sync(0xffffffffu, S.uh, 0), h1 = __shfl_sync(0xffffffffu, S.uh, 1);
+    const real h2 = __shfl_sync(0xffffffffu, S.uh, 2), h3 = __shfl_sync(0xffffffffu, S.uh, 3);
+    const real g1 = __shfl_sync(0xffffffffu, S.ih, 1), g2 = __shfl_sync(0xffffffffu, S.ih, 2);
+    if (lane == 0) {
+      um1 = h1;
+      um2 = h0;
+      im1 = g1;
+    }
+    if (lane == 1) um2 = h1;
+    if (lane == 30) up2 = h2;
+    if (lane == 31) {
+      up1 = h2;
+      up2 = h3;
+      ip1 = g2;
+    }
+    real off = kx * (up1 + um1);
+    off = fmadd(cx, fmadd(ip1, up2, im1 * um2), off);
+    off = fmadd(ky, S.us1 + S.un1, off);
+    off = fmadd(cy, fmadd(S.is1, S.us2, S.in1 * S.un2), off);
+    const real Au = fmadd(S.dc, S.uc, -off);
+    if (S.in) {
+      pn[S.c] = S.uc;
+      q[S.c] = Au;
+    }
+    return (double)S.uc * (double)Au;
+  }
+};
+
+// Block-wide sums of two values at once (one pair of barriers); every
+// thread gets both.  scratch >= 64 entries.
+__device__ __forceinline__ void block_sum2(double &a, double &b, double *scratch) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  a = warp_sum(a);
+  b = warp_sum(b);
+  __syncthreads();
+  if (lane == 0) {
+    scratch[wid] = a;
+    scratch[32 + wid] = b;
+  }
+  __syncthreads();
+  a = warp_sum(lane < nw ? scratch[lane] : 0.0);
+  b = warp_sum(lane < nw ? scratch[32 + lane] : 0.0);
+}
+
+template <typename real> struct DsaVec;
+template <> struct DsaVec<float> {
+  using type = float4;
+  static constexpr int kN = 4;
+};
+template <> struct DsaVec<double> {
+  using type = double2;
+  static constexpr int kN = 2;
+};
+
+// P2 on elements [0, n): x += a p, r -= a q, z = r dinv; accumulates r.z and r.r
+template <typename real>
+__device__ __forceinline__ void dsa_p2_elem(real a, real p, real qq, real &x, real &r, real &z,
+                                            real dinv, double &rz, double &rr) {
+  x = fmadd(a, p, x);
+  r = fmadd(-a, qq, r);
+  z = r * dinv;
+  rz += (double)r * (double)z;
+  rr += (double)r * (double)r;
 }
 
 // The CG solves of all instances with on[i] (set by the caller: active, DSA
@@ -122,7 +257,7 @@ __device__ __forceinline__ real dsa_dir(const real *z, const real *po, real beta
 template <typename real>
 __device__ __noinline__ bool dsa_solve(const Inst *__restrict__ insts, const SiCtl &ctl, int *on,
                                        double *sc, volatile int *abort_flag) {
-  __shared__ double red[32];
+  __shared__ double red[64];
   const int n = ctl.n_inst;
   double *rz = sc, *beta = sc + n, *alpha = sc + 2 * n, *bb = sc + 3 * n, *t0 = sc + 4 * n,
          *t1 = sc + 5 * n;
@@ -139,42 +274,41 @@ __device__ __noinline__ bool dsa_solve(const Inst *__restrict__ insts, const SiC
     if (!__syncthreads_or(any)) break;
 
     // P1: p = z + beta p_old, q = A p
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     for (int i = 0; i < n; ++i) {
       if (!on[i]) continue;
       const Inst &I = insts[i];
-      const int nx = I.nx, ny = I.ny, N = I.N;
-      const real *z = as_c<real>(I.dsa_z), *ist = as_c<real>(I.dsa_ist), *dg = as_c<real>(I.dsa_dg);
-      const real *po = as_c<real>((k & 1) ? I.dsa_p0 : I.dsa_p1);
-      real *pn = as<real>((k & 1) ? I.dsa_p1 : I.dsa_p0);
-      real *q = as<real>(I.dsa_q);
-      const real b = real(beta[i]);
-      const bool first = k == 0;
-      const real cx = real(I.dsa_cx), cy = real(I.dsa_cy), kx = real(I.dsa_kx), ky = real(I.dsa_ky);
+      DsaP1<real> P;
+      P.z = as_c<real>(I.dsa_z);
+      P.po = as_c<real>((k & 1) ? I.dsa_p0 : I.dsa_p1);
+      P.ist = as_c<real>(I.dsa_ist);
+      P.dg = as_c<real>(I.dsa_dg);
+      P.pn = as<real>((k & 1) ? I.dsa_p1 : I.dsa_p0);
+      P.q = as<real>(I.dsa_q);
+      P.nx = I.nx;
+      P.ny = I.ny;
+      P.beta = k == 0 ? real(0) : real(beta[i]);
+      P.cx = real(I.dsa_cx);
+      P.cy = real(I.dsa_cy);
+      P.kx = real(I.dsa_kx);
+      P.ky = real(I.dsa_ky);
+      const int nxb = (I.nx + 31) >> 5, items = I.ny * nxb;
       double pq = 0;
-      for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-        const int ix = c % nx, iy = c / nx;
-        const real uc = dsa_dir(z, po, b, first, c);
-        real off = real(0);
-        if (ix + 1 < nx) {
-          off = fmadd(kx, dsa_dir(z, po, b, first, c + 1), off);
-          if (ix + 2 < nx) off = fmadd(cx * ist[c + 1], dsa_dir(z, po, b, first, c + 2), off);
+      // kSegs row segments per warp and round, all loads before any use (8 in
+      // FP32; FP64 spills at 8)
+      constexpr int kSegs = sizeof(real) == 4 ? 8 : 4;
+      for (int t = gw; t < items; t += kSegs * warps) {
+        typename DsaP1<real>::Seg S[kSegs];
+#pragma unroll
+        for (int g = 0; g < kSegs; ++g) {
+          const int tg = t + g * warps;
+          const int iy = tg / nxb;
+          // a segment past the end loads nothing (its row is outside the mesh)
+          P.load(S[g], tg < items ? iy : -8, (tg - iy * nxb) << 5);
         }
-        if (ix >= 1) {
-          off = fmadd(kx, dsa_dir(z, po, b, first, c - 1), off);
-          if (ix >= 2) off = fmadd(cx * ist[c - 1], dsa_dir(z, po, b, first, c - 2), off);
-        }
-        if (iy + 1 < ny) {
-          off = fmadd(ky, dsa_dir(z, po, b, first, c + nx), off);
-          if (iy + 2 < ny) off = fmadd(cy * ist[c + nx], dsa_dir(z, po, b, first, c + 2 * nx), off);
-        }
-        if (iy >= 1) {
-          off = fmadd(ky, dsa_dir(z, po, b, first, c - nx), off);
-          if (iy >= 2) off = fmadd(cy * ist[c - nx], dsa_dir(z, po, b, first, c - 2 * nx), off);
-        }
-        const real Au = fmadd(dg[c], uc, -off);
-        pn[c] = uc;
-        q[c] = Au;
-        pq += (double)uc * (double)Au;
+#pragma unroll
+        for (int g = 0; g < kSegs; ++g) pq += P.finish(S[g]);
       }
       pq = block_sum(pq, red);
       if (threadIdx.x == 0) dsa_slot(ctl, i, kDsaPq)[blockIdx.x] = pq;
@@ -195,17 +329,47 @@ __device__ __noinline__ bool dsa_solve(const Inst *__restrict__ insts, const SiC
       real *x = as<real>(I.dsa_x), *r = as<real>(I.dsa_r), *z = as<real>(I.dsa_z);
       const real a = real(alpha[i]);
       double prz = 0, prr = 0;
-      for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-        x[c] = fmadd(a, pn[c], x[c]);
-        const real rc = fmadd(-a, q[c], r[c]);
-        const real zc = rc * dinv[c];
+      // vectors of kN elements (the arrays are separate allocations, aligned),
+      // then the tail
+      using V = typename DsaVec<real>::type;
+      constexpr int kN = DsaVec<real>::kN;
+      const int nv = N / kN, t0 = blockIdx.x * blockDim.x + threadIdx.x, ts = gridDim.x * blockDim.x;
+      // two vectors per thread and round, loads first
+      for (int t = t0; t < nv; t += 2 * ts) {
+        V pv[2], qv[2], dv[2], xv[2], rv[2], zv[2];
+        const bool two = t + ts < nv;
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+          const int tg = (g == 0 || two) ? t + g * ts : t;
+          pv[g] = reinterpret_cast<const V *>(pn)[tg];
+          qv[g] = reinterpret_cast<const V *>(q)[tg];
+          dv[g] = reinterpret_cast<const V *>(dinv)[tg];
+          xv[g] = reinterpret_cast<const V *>(x)[tg];
+          rv[g] = reinterpret_cast<const V *>(r)[tg];
+        }
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+          if (g == 1 && !two) break;
+          dsa_p2_elem(a, pv[g].x, qv[g].x, xv[g].x, rv[g].x, zv[g].x, dv[g].x, prz, prr);
+          dsa_p2_elem(a, pv[g].y, qv[g].y, xv[g].y, rv[g].y, zv[g].y, dv[g].y, prz, prr);
+          if constexpr (kN == 4) {
+            dsa_p2_elem(a, pv[g].z, qv[g].z, xv[g].z, rv[g].z, zv[g].z, dv[g].z, prz, prr);
+            dsa_p2_elem(a, pv[g].w, qv[g].w, xv[g].w, rv[g].w, zv[g].w, dv[g].w, prz, prr);
+          }
+          const int tg = t + g * ts;
+          reinterpret_cast<V *>(x)[tg] = xv[g];
+          reinterpret_cast<V *>(r)[tg] = rv[g];
+          reinterpret_cast<V *>(z)[tg] = zv[g];
+        }
+      }
+      for (int c = nv * kN + t0; c < N; c += ts) {
+        real xc = x[c], rc = r[c], zc;
+        dsa_p2_elem(a, pn[c], q[c], xc, rc, zc, dinv[c], prz, prr);
+        x[c] = xc;
         r[c] = rc;
         z[c] = zc;
-        prz += (double)rc * (double)zc;
-        prr += (double)rc * (double)rc;
       }
-      prz = block_sum(prz, red);
-      prr = block_sum(prr, red);
+      block_sum2(prz, prr, red);
       if (threadIdx.x == 0) {
         dsa_slot(ctl, i, kDsaRz)[blockIdx.x] = prz;
         dsa_slot(ctl, i, kDsaRr)[blockIdx.x] = prr;

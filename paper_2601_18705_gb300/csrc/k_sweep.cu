@@ -629,9 +629,8 @@ k_si(const Inst *__restrict__ insts, SiCtl ctl) {
           dmax = max(dmax, abs(acc - po));
           pmax = max(pmax, abs(acc));
         }
-        __shared__ double red[32];
-        rz = block_sum(rz, red);
-        bb = block_sum(bb, red);
+        __shared__ double red[64];
+        block_sum2(rz, bb, red);
         if (threadIdx.x == 0) {
           dsa_slot(ctl, i, kDsaRz)[blockIdx.x] = rz;
           dsa_slot(ctl, i, kDsaBb)[blockIdx.x] = bb;
