@@ -365,6 +365,27 @@ def run_gpu(args):
                           "frac": ach / hbm_pk, "kernel": "k_si<float>", "peak_kind": pk_kind,
                           "bytes_per_update": bpu, "avg_launch_ms": l_ms}
 
+    # ---- the same SN step with DSA-accelerated source iteration ----
+    sn_dsa = None
+    if not args.no_sn and not args.no_dsa and rank == 0:
+        s7 = dlr.Solver(dlr.problem_from_case(case, precision=dlr.DLR_MIXED, allow_nonpositive=1,
+                                              method=dlr.DLR_METHOD_SN, dsa=1,
+                                              dsa_max_iter=args.dsa_max_iter))
+        s7.step(args.warmup)
+        s7.stream.synchronize()
+        h0 = s7.stats()
+        ms_snd = timed_steps(dlr, torch, s7, args.steps, flush)
+        h1 = s7.stats()
+        T_snd = s7.T()
+        s7.close()
+        si_s = h1["si_iters_total"] - h0["si_iters_total"]
+        tsd = sum(ms_snd)
+        sn_dsa = {"method": f"full-rank SN, DSA (at most {args.dsa_max_iter or 3} CG iterations per solve), mixed",
+                  "ms_per_step": tsd / args.steps, "si_iters_per_step": si_s / args.steps,
+                  "cg_iters_per_si_iter": (h1["dsa_iters_total"] - h0["dsa_iters_total"]) / max(si_s, 1),
+                  "step_speedup_vs_sn": (sn["ms_per_step"] / (tsd / args.steps)) if sn else None,
+                  "T_rel_l2_vs_sn": float(np.linalg.norm(T_snd - T_sn) / np.linalg.norm(T_sn)) if sn else None}
+
     # ---- the augmented step (rank-2r basis truncated to r), same steps ----
     aug = None
     if not args.no_aug and rank == 0 and 2 * case["r"] <= 32 and case["n_polar"] * case["n_azim"] <= 1024:
@@ -437,7 +458,7 @@ def run_gpu(args):
             "data": "synthetic", "config": case_config(case, "mixed: FP32 sweeps/projections, FP64 small LA and T"),
             "dlr_steps_per_s": world * args.steps / (total_ms / 1e3),
             "si_iters_per_step": iters / args.steps,
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fp64_gpu": fp64, "sn_gpu": sn, "augmented_gpu": aug, "dsa_gpu": dsa,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fp64_gpu": fp64, "sn_gpu": sn, "sn_dsa_gpu": sn_dsa, "augmented_gpu": aug, "dsa_gpu": dsa,
             "clocks": clocks, "gpu_launches": int(launches),
             "nonpositive_cells_at_end": int(nonpos), "sweep_plan": tuned}
     print(json.dumps(line))

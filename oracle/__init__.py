@@ -58,7 +58,8 @@ class _Problem(C.Structure):
                 ("sigma", _dp), ("rho_cv", _dp),
                 ("psi_edge", C.c_double * 4), ("sigma_texp", C.c_double),
                 ("cv_texp", C.c_double), ("T_ref", C.c_double),
-                ("dsa", C.c_int), ("dsa_tol", C.c_double), ("dsa_max_iter", C.c_int)]
+                ("dsa", C.c_int), ("dsa_tol", C.c_double), ("dsa_max_iter", C.c_int),
+                ("reflect", C.c_int * 4)]
 
 
 class _Opts(C.Structure):
@@ -98,6 +99,9 @@ def lib() -> C.CDLL:
                                          C.c_double, C.c_int, C.c_int, _dp, _ip]
         L.oracle_sn_step.argtypes = [C.POINTER(_Problem), _dp, _dp, C.c_double, C.c_int,
                                      _dp, _dp, _dp]
+        L.oracle_sweep_in.argtypes = [C.POINTER(_Problem), C.c_double, C.c_double, _dp, _dp, _dp,
+                                      _dp, _dp]
+        L.oracle_reflect_index.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
         L.oracle_dsa_kappa.restype = C.c_double
         L.oracle_dsa_kappa.argtypes = [C.c_int, C.c_int, C.c_int]
         L.oracle_dsa_apply.argtypes = [C.POINTER(_Problem), _dp, _dp, _dp, _dp]
@@ -151,6 +155,7 @@ class Problem:
     dsa: int = 0              # diffusion synthetic acceleration (Section 4.5, reading R17)
     dsa_tol: float = 0.1      # CG stop: ||r||_2 <= dsa_tol ||b||_2
     dsa_max_iter: int = 3
+    reflect: tuple = (0, 0, 0, 0)  # reflective edges L, R, B, T (reading R18, SN only)
     _keep: list = field(default_factory=list, repr=False)
 
     @property
@@ -180,6 +185,8 @@ class Problem:
         s.sigma_texp, s.cv_texp, s.T_ref = self.sigma_texp, self.cv_texp, self.T_ref
         s.dsa, s.dsa_tol, s.dsa_max_iter = int(self.dsa), float(self.dsa_tol), int(self.dsa_max_iter)
         for e in range(4):
+            s.reflect[e] = int(self.reflect[e])
+        for e in range(4):
             s.psi_edge[e] = float(self.psi_edge[e])
         return s
 
@@ -204,6 +211,18 @@ def sweep(p: Problem, ox: float, oy: float, sigma_t, src) -> np.ndarray:
     psi = np.zeros(p.Nx)
     lib().oracle_sweep(C.byref(p.cstruct()), float(ox), float(oy), _ptr(st), _ptr(s), _ptr(psi))
     return psi
+
+
+def sweep_in(p: Problem, ox: float, oy: float, sigma_t, src, in_x, in_y) -> np.ndarray:
+    st, s, ix, iy = (_f64(a).reshape(-1) for a in (sigma_t, src, in_x, in_y))
+    psi = np.zeros(p.Nx)
+    lib().oracle_sweep_in(C.byref(p.cstruct()), float(ox), float(oy), _ptr(st), _ptr(s), _ptr(ix),
+                          _ptr(iy), _ptr(psi))
+    return psi
+
+
+def reflect_index(n_polar: int, n_azim: int, k: int, axis: int) -> int:
+    return lib().oracle_reflect_index(n_polar, n_azim, k, axis)
 
 
 def dsa_kappa(n_polar: int, n_azim: int, axis: int) -> float:

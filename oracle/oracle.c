@@ -48,6 +48,13 @@
  *       correction multiplies rounding noise by up to sigma_s / sigma_a in
  *       thick scattering cells, so phi^{l+1} - phi^l would stall above a
  *       tolerance near the working precision.
+ *   R18 reflective edges (full-rank SN only): a direction entering through a
+ *       reflective edge takes as inflow, row by row, the boundary cell value
+ *       of its mirror image (the direction with the normal component
+ *       negated), from the previous source iteration (from psi^n in the
+ *       first); the product quadrature maps onto itself (x mirror: azimuth
+ *       a -> n_azim/2 - 1 - a, needs n_azim even; y mirror: a -> n_azim - 1
+ *       - a).
  */
 #include "oracle.h"
 
@@ -179,21 +186,59 @@ static double inflow_y(const oracle_problem *p, double oy) {
  *       + sigma_t,c psi_c = src_c,
  * where west/south are the upwind neighbours (or the edge inflow).  The
  * sweep solves this lower-triangular system cell by cell in upwind order. */
-void oracle_sweep(const oracle_problem *p, double ox, double oy,
-                  const double *sigma_t, const double *src, double *psi) {
+void oracle_sweep_in(const oracle_problem *p, double ox, double oy,
+                     const double *sigma_t, const double *src,
+                     const double *in_x, const double *in_y, double *psi) {
   int nx = p->nx, ny = p->ny;
   double hx = p->lx / nx, hy = p->ly / ny;
   double ax = fabs(ox) / hx, ay = fabs(oy) / hy;
   int sx = ox >= 0 ? 1 : -1, sy = oy >= 0 ? 1 : -1;
-  double in_x = inflow_x(p, ox), in_y = inflow_y(p, oy);
   for (int jj = 0; jj < ny; jj++) {
     int iy = sy > 0 ? jj : ny - 1 - jj;
     for (int ii = 0; ii < nx; ii++) {
       int ix = sx > 0 ? ii : nx - 1 - ii;
       int c = iy * nx + ix;
-      double up_x = ii == 0 ? in_x : psi[iy * nx + (ix - sx)];
-      double up_y = jj == 0 ? in_y : psi[(iy - sy) * nx + ix];
+      double up_x = ii == 0 ? in_x[iy] : psi[iy * nx + (ix - sx)];
+      double up_y = jj == 0 ? in_y[ix] : psi[(iy - sy) * nx + ix];
       psi[c] = (src[c] + ax * up_x + ay * up_y) / (sigma_t[c] + ax + ay);
+    }
+  }
+}
+
+void oracle_sweep(const oracle_problem *p, double ox, double oy,
+                  const double *sigma_t, const double *src, double *psi) {
+  double *in_x = (double *)malloc(sizeof(double) * p->ny);
+  double *in_y = (double *)malloc(sizeof(double) * p->nx);
+  for (int iy = 0; iy < p->ny; iy++) in_x[iy] = inflow_x(p, ox);
+  for (int ix = 0; ix < p->nx; ix++) in_y[ix] = inflow_y(p, oy);
+  oracle_sweep_in(p, ox, oy, sigma_t, src, in_x, in_y, psi);
+  free(in_x); free(in_y);
+}
+
+/* Reflection maps of the product quadrature (reading R18). */
+int oracle_reflect_index(int n_polar, int n_azim, int k, int axis) {
+  int pp = k / n_azim, a = k % n_azim;
+  int b = axis == 0 ? ((n_azim / 2 - 1 - a) % n_azim + n_azim) % n_azim : n_azim - 1 - a;
+  (void)n_polar;
+  return pp * n_azim + b;
+}
+
+/* Inflow of every angle through the edges it enters (reading R4; R18 on
+ * reflective edges, from psi, Nx x NOm): in_x[k ny + iy], in_y[k nx + ix]. */
+static void sn_inflow(const oracle_problem *p, const double *ox, const double *oy,
+                      const double *psi, double *in_x, double *in_y) {
+  int nx = p->nx, ny = p->ny, Nx = nx * ny, NOm = p->n_polar * p->n_azim;
+  for (int k = 0; k < NOm; k++) {
+    int ex = ox[k] > 0 ? 0 : 1, ey = oy[k] > 0 ? 2 : 3;
+    int kx = oracle_reflect_index(p->n_polar, p->n_azim, k, 0);
+    int ky = oracle_reflect_index(p->n_polar, p->n_azim, k, 1);
+    for (int iy = 0; iy < ny; iy++) {
+      int c = iy * nx + (ex == 0 ? 0 : nx - 1);
+      in_x[k * ny + iy] = p->reflect[ex] ? psi[c + (size_t)Nx * kx] : inflow_x(p, ox[k]);
+    }
+    for (int ix = 0; ix < nx; ix++) {
+      int c = (ey == 2 ? 0 : ny - 1) * nx + ix;
+      in_y[k * nx + ix] = p->reflect[ey] ? psi[c + (size_t)Nx * ky] : inflow_y(p, oy[k]);
     }
   }
 }
@@ -927,11 +972,6 @@ static double get_xl(const void *ctx, int c, int k) {
   for (int i = 0; i < g->r; i++) t += g->X[c + (size_t)g->Nx * i] * g->L[i + g->r * k];
   return t;
 }
-typedef struct { const double *psi; int Nx; } full_ctx;
-static double get_full(const void *ctx, int c, int k) {
-  const full_ctx *g = (const full_ctx *)ctx;
-  return g->psi[c + (size_t)g->Nx * k];
-}
 
 /* phi_c = sum_k w_k psi(c, Om_k) = sum_ij X_ci S_ij beta_j, beta_j = sum_k w_k W_kj */
 static void phi_from_factors(int Nx, int NOm, int r, const double *X,
@@ -1069,6 +1109,7 @@ int oracle_dlr_step(const oracle_problem *p, int r, double *X, double *S,
   double hx = p->lx / nx, hy = p->ly / ny, h2 = hx * hy, h = sqrt(h2);
   double inv_cdt = 1.0 / (p->c * p->dt);
   if (r < 1 || r > Nx || r > NOm) return -1;
+  if (p->reflect[0] || p->reflect[1] || p->reflect[2] || p->reflect[3]) return -1;  /* R18: SN only */
   const int aug = opt && opt->augment;
   /* rank of steps 5-8: 2r for the augmented step (R15) */
   const int m = aug ? 2 * r : r;
@@ -1325,13 +1366,18 @@ int oracle_sn_step(const oracle_problem *p, double *psi, double *T,
   for (int c = 0; c < Nx; c++) sig_t[c] = oracle_sigma_at(p, c, T[c]) + inv_cdt;
   for (int k = 0; k < NOm; k++)
     for (int c = 0; c < Nx; c++) phi[c] += w[k] * psi0[c + (size_t)Nx * k];
+  /* inflow per angle and boundary row; reflective edges lag one iteration */
+  double *in_x = (double *)malloc(sizeof(double) * NOm * p->ny);
+  double *in_y = (double *)malloc(sizeof(double) * NOm * p->nx);
   int iters = 0, converged = 0;
   while (iters < si_max_iter) {
+    sn_inflow(p, ox, oy, iters == 0 ? psi0 : psi, in_x, in_y);
     for (int c = 0; c < Nx; c++) phin[c] = 0;
     for (int k = 0; k < NOm; k++) {
       for (int c = 0; c < Nx; c++)
         src[c] = sig_s[c] * phi[c] / (4.0 * ORACLE_PI) + q[c] + inv_cdt * psi0[c + (size_t)Nx * k];
-      oracle_sweep(p, ox[k], oy[k], sig_t, src, psi + (size_t)Nx * k);
+      oracle_sweep_in(p, ox[k], oy[k], sig_t, src, in_x + (size_t)k * p->ny,
+                      in_y + (size_t)k * p->nx, psi + (size_t)Nx * k);
       for (int c = 0; c < Nx; c++) phin[c] += w[k] * psi[c + (size_t)Nx * k];
     }
     iters++;
@@ -1348,10 +1394,25 @@ int oracle_sn_step(const oracle_problem *p, double *psi, double *T,
     T[c] = T[c] + p->dt * oracle_sigma_at(p, c, T[c]) * (phi[c] - 4.0 * ORACLE_PI * B0[c]) / D[c];
   if (phi_out) memcpy(phi_out, phi, sizeof(double) * Nx);
   if (outflow && inflow) {
-    full_ctx g = {psi, Nx};
-    boundary_rates(p, ox, oy, w, get_full, &g, outflow, inflow);
+    /* outflow from the last sweep; inflow as that sweep took it */
+    int nx = p->nx, ny = p->ny;
+    double hx = p->lx / nx, hy = p->ly / ny, o = 0, i_ = 0;
+    for (int k = 0; k < NOm; k++) {
+      const double *pk = psi + (size_t)Nx * k;
+      for (int iy = 0; iy < ny; iy++) {
+        o += w[k] * fabs(ox[k]) * hy * pk[iy * nx + (ox[k] < 0 ? 0 : nx - 1)];
+        i_ += w[k] * fabs(ox[k]) * hy * in_x[(size_t)k * ny + iy];
+      }
+      for (int ix = 0; ix < nx; ix++) {
+        o += w[k] * fabs(oy[k]) * hx * pk[(oy[k] < 0 ? 0 : ny - 1) * nx + ix];
+        i_ += w[k] * fabs(oy[k]) * hx * in_y[(size_t)k * nx + ix];
+      }
+    }
+    *outflow = o;
+    *inflow = i_;
   }
   free(ox); free(oy); free(oz); free(w); free(sig_s); free(q); free(B0);
   free(D); free(sig_t); free(phi); free(phin); free(src); free(psi0);
+  free(in_x); free(in_y);
   return converged ? iters : -2;
 }

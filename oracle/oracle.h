@@ -44,6 +44,9 @@ typedef struct {
   int dsa;
   double dsa_tol;
   int dsa_max_iter;
+  /* reflective edges (left, right, bottom, top; reading R18, full-rank SN
+   * only): 1 = the edge mirrors the angular flux, 0 = psi_edge inflow */
+  int reflect[4];
 } oracle_problem;
 
 typedef struct {
@@ -101,6 +104,17 @@ void oracle_dsa_diag(const oracle_problem *p, const double *sig_t,
 int oracle_dsa_solve(const oracle_problem *p, const double *sig_t,
                      const double *sig_a, const double *b, double tol,
                      int max_iter, double *x);
+
+/* The sweep with an inflow value per boundary row and column:
+ * in_x[iy] enters the upwind x-face of row iy, in_y[ix] the upwind y-face of
+ * column ix. */
+void oracle_sweep_in(const oracle_problem *p, double ox, double oy,
+                     const double *sigma_t, const double *src,
+                     const double *in_x, const double *in_y, double *psi);
+
+/* Index of the mirror image of quadrature angle k (axis 0: x component
+ * negated, needs n_azim even; axis 1: y component negated), reading R18. */
+int oracle_reflect_index(int n_polar, int n_azim, int k, int axis);
 
 /* Dense linear algebra building blocks. */
 int oracle_lu_solve(int n, const double *A, int nrhs, const double *B,
