@@ -130,6 +130,14 @@ typedef struct dlr_problem {
                             accelerates the iteration, and a few CG
                             iterations already remove most source
                             iterations) */
+  int32_t reflect[4];    /* reflective edges, left, right, bottom, top (1 =
+                            reflective; T_edge of that edge is ignored).  A
+                            direction entering a reflective edge takes, row by
+                            row, the boundary value of its mirror direction
+                            (normal component negated) from the previous
+                            source iteration.  DLR_METHOD_SN only; a
+                            reflective left or right edge needs n_azim even
+                            (the quadrature's mirror map) */
 } dlr_problem;
 
 /* Device memory and stream supplied by the caller (e.g. PyTorch). */

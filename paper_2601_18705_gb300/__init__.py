@@ -56,6 +56,7 @@ class ProblemSpec:
     dsa: int = 0             # 1: diffusion synthetic acceleration of the source iteration
     dsa_tol: float = 0.0     # CG stop ||r|| <= dsa_tol ||b|| (0: 0.1)
     dsa_max_iter: int = 0    # CG cap per solve (0: 3)
+    reflect: tuple = (0, 0, 0, 0)  # reflective edges L, R, B, T (full-rank SN only)
 
     def cstruct(self):
         keep = [_f64(self.sigma), _f64(self.rho_cv), _f64(self.T0)]
@@ -77,6 +78,8 @@ class ProblemSpec:
         p.method = self.method
         p.sigma_texp, p.cv_texp, p.T_ref = self.sigma_texp, self.cv_texp, self.T_ref
         p.dsa, p.dsa_tol, p.dsa_max_iter = int(self.dsa), float(self.dsa_tol), int(self.dsa_max_iter)
+        for e in range(4):
+            p.reflect[e] = int(self.reflect[e])
         return p, keep
 
 

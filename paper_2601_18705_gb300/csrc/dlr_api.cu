@@ -395,6 +395,8 @@ static Sizes sizes_of(const dlr_problem *p, int sms) {
     s.total = 5 * al((size_t)s.N * 8) + 6 * al((size_t)s.N * s.rs) + 2 * al((size_t)s.N * s.K * s.rs) +
               3 * al((size_t)s.K * 8) + al((size_t)s.K * 4) + al(64) * 4 + al(sizeof(Inst));
     if (p->dsa) s.total += kDsaArrays * al((size_t)s.N * s.rs) + al(64);
+    if (p->reflect[0] || p->reflect[1] || p->reflect[2] || p->reflect[3])
+      s.total += al((size_t)s.K * (p->nx + p->ny) * s.rs);  // boundary sources of reflective edges
     return s;
   }
   // CTAs of the cell and angle reductions: whole clusters of kCl CTAs,
@@ -463,6 +465,13 @@ static int validate(const dlr_problem *p) {
       return fail(DLR_EINVAL, "augmented step: needs NOm <= 1024 and the pivoted-QR angle choice");
   }
   if (p->dsa != 0 && p->dsa != 1) return fail(DLR_EINVAL, "dsa must be 0 or 1");
+  for (int e = 0; e < 4; ++e)
+    if (p->reflect[e] != 0 && p->reflect[e] != 1) return fail(DLR_EINVAL, "reflect[%d] must be 0 or 1", e);
+  if (p->reflect[0] || p->reflect[1] || p->reflect[2] || p->reflect[3]) {
+    if (!sn) return fail(DLR_EINVAL, "reflective edges are built for DLR_METHOD_SN only");
+    if ((p->reflect[0] || p->reflect[1]) && p->n_azim % 2)
+      return fail(DLR_EINVAL, "a reflective left or right edge needs an even n_azim");
+  }
   if (!std::isfinite(p->dsa_tol) || p->dsa_tol >= 1.0) return fail(DLR_EINVAL, "dsa_tol must be finite and < 1");
   if (!p->sigma || !p->rho_cv || !p->T0) return fail(DLR_EINVAL, "sigma, rho_cv, T0 must be given");
   for (long long c = 0; c < N; ++c) {
@@ -530,6 +539,9 @@ static void fill_common(dlr_handle *h, const dlr_problem *problem) {
   I.dsa_ky = ky / I.hy;
   I.dsa_ist = I.dsa_dg = I.dsa_dinv = I.dsa_x = I.dsa_r = I.dsa_z = I.dsa_p0 = I.dsa_p1 = I.dsa_q = nullptr;
   I.dsa_iters_total = nullptr;
+  for (int e = 0; e < 4; ++e) I.reflect[e] = problem->reflect[e];
+  I.n_azim = problem->n_azim;
+  I.refl_base = nullptr;
 }
 
 // Device arrays of the DSA solve (N each, working precision): 1/sigma_t,
@@ -578,6 +590,8 @@ static int create_sn(dlr_handle *h, const dlr_problem *problem, dlr_handle **out
   I.sphi = A((size_t)N * rs);
   I.Psi = A((size_t)N * K * rs);
   I.s0 = A((size_t)N * K * rs);
+  if (I.reflect[0] || I.reflect[1] || I.reflect[2] || I.reflect[3])
+    I.refl_base = A((size_t)K * (problem->nx + problem->ny) * rs);
   double *dox = (double *)A((size_t)K * 8), *doy = (double *)A((size_t)K * 8), *dw = (double *)A((size_t)K * 8);
   I.ox = dox;
   I.oy = doy;

@@ -125,7 +125,28 @@ struct Inst {
   double dsa_tol, dsa_cx, dsa_cy, dsa_kx, dsa_ky;
   void *dsa_ist, *dsa_dg, *dsa_dinv, *dsa_x, *dsa_r, *dsa_z, *dsa_p0, *dsa_p1, *dsa_q;
   unsigned long long *dsa_iters_total;  // CG iterations summed over all steps
+  // reflective edges (full-rank SN; left, right, bottom, top): a direction
+  // entering a reflective edge takes, row by row, its mirror direction's
+  // boundary value from the previous source iteration.  The sweep sees that
+  // inflow as a source: the scalar inflow of the edge is 0 and the upwind
+  // term (|Om_x|/hx) psi_in is added to the angle's fixed source s0 in the
+  // boundary cells.  refl_base (real, K x (ny + nx), nullptr without
+  // reflective edges) keeps those cells' own fixed source: entry
+  // k (ny + nx) + o for boundary row o (o < ny) of the x-edge angle k enters,
+  // and for boundary column o - ny of its y-edge
+  int reflect[4];
+  int n_azim;
+  void *refl_base;
 };
+
+// Mirror image of quadrature angle k = p n_azim + a of the product
+// quadrature: axis 0 negates the x component (azimuth a -> n_azim/2 - 1 - a,
+// n_azim even), axis 1 the y component (a -> n_azim - 1 - a).
+__host__ __device__ inline int mirror_angle(int k, int n_azim, int axis) {
+  const int p = k / n_azim, a = k - p * n_azim;
+  const int b = axis == 0 ? (n_azim / 2 - 1 - a + n_azim) % n_azim : n_azim - 1 - a;
+  return p * n_azim + b;
+}
 
 __device__ __forceinline__ double sigma_at(const Inst &I, int c, double T0) {
   return I.sig_texp == 0.0 ? I.sigma[c] : I.sigma[c] * pow(T0 / I.T_ref, -I.sig_texp);
@@ -373,6 +394,50 @@ __device__ T block_max(T v, T *scratch) {
   T t = lane < nw ? scratch[lane] : T(-1e308);
   t = warp_max(t);
   return t;
+}
+
+// The boundary-cell geometry of angle k: the x-edge and y-edge it enters
+// (0 left, 1 right, 2 bottom, 3 top), the boundary column and row, and the
+// upwind coefficients |Om_x|/hx, |Om_y|/hy in the working precision.
+template <typename real>
+struct ReflGeom {
+  int ex, ey, bx, by;
+  bool rx, ry;
+  real ax, ay;
+  __device__ __forceinline__ ReflGeom(const Inst &I, int k) {
+    ex = I.ox[k] > 0 ? 0 : 1;
+    ey = I.oy[k] > 0 ? 2 : 3;
+    bx = ex == 0 ? 0 : I.nx - 1;
+    by = ey == 2 ? 0 : I.ny - 1;
+    rx = I.reflect[ex] != 0;
+    ry = I.reflect[ey] != 0;
+    ax = real(fabs(I.ox[k]) / I.hx);
+    ay = real(fabs(I.oy[k]) / I.hy);
+  }
+};
+
+// Entry e of refl_base (see Inst): the fixed source of its boundary cell
+// plus the reflected inflow term(s) from psi (N x K) of the mirror
+// directions, written to s0.  The corner cell of two reflective edges is
+// written by its x-edge entry only.
+template <typename real>
+__device__ __forceinline__ void refl_inject(const Inst &I, const real *psi, int e) {
+  const int L = I.ny + I.nx, k = e / L, o = e - k * L;
+  const ReflGeom<real> G(I, k);
+  const real *base = as_c<real>(I.refl_base) + (size_t)k * L;
+  real *s0 = as<real>(I.s0) + (size_t)I.N * k;
+  if (o < I.ny) {
+    if (!G.rx) return;
+    const int c = o * I.nx + G.bx;
+    real v = fmadd(G.ax, psi[(size_t)I.N * mirror_angle(k, I.n_azim, 0) + c], base[o]);
+    if (G.ry && o == G.by) v = fmadd(G.ay, psi[(size_t)I.N * mirror_angle(k, I.n_azim, 1) + c], v);
+    s0[c] = v;
+  } else {
+    const int ix = o - I.ny;
+    if (!G.ry || (G.rx && ix == G.bx)) return;
+    const int c = G.by * I.nx + ix;
+    s0[c] = fmadd(G.ay, psi[(size_t)I.N * mirror_angle(k, I.n_azim, 1) + c], base[o]);
+  }
 }
 
 constexpr uint64_t kGridWaitNs = 4000000000ull;  // bound of a grid-barrier wait

@@ -46,9 +46,26 @@ __global__ void __launch_bounds__(256) k_sn_prep(const Inst *__restrict__ insts)
   real *s0 = as<real>(I.s0);
   const real qr = real(cf.q), icdt = real(I.inv_cdt);
   real phi = real(0);
+  const int ix = c % I.nx, iy = c / I.nx, L = I.nx + I.ny;
   for (int k = 0; k < I.K; ++k) {
     const real p = psi[(size_t)I.N * k + c];
-    s0[(size_t)I.N * k + c] = fmadd(icdt, p, qr);
+    real v = fmadd(icdt, p, qr);
+    if (I.refl_base) {
+      // reflective edges: keep the boundary cell's own source and add the
+      // inflow of the first iteration, from psi^n of the mirror directions
+      const ReflGeom<real> G(I, k);
+      real *base = as<real>(I.refl_base) + (size_t)k * L;
+      const real f = v;
+      if (G.rx && ix == G.bx) {
+        base[iy] = f;
+        v = fmadd(G.ax, psi[(size_t)I.N * mirror_angle(k, I.n_azim, 0) + c], v);
+      }
+      if (G.ry && iy == G.by) {
+        base[I.ny + ix] = f;
+        v = fmadd(G.ay, psi[(size_t)I.N * mirror_angle(k, I.n_azim, 1) + c], v);
+      }
+    }
+    s0[(size_t)I.N * k + c] = v;
     phi = fmadd(real(I.w[k]), p, phi);
   }
   as<real>(I.phi0)[c] = phi;

@@ -520,6 +520,10 @@ __device__ SweepArgs<real> unit_args(const Inst &I, int j) {
   A.ay = real(fabs(oy) / I.hy);
   A.in_x = real(ox > 0 ? I.psi_edge[0] : (ox < 0 ? I.psi_edge[1] : 0.0));
   A.in_y = real(oy > 0 ? I.psi_edge[2] : (oy < 0 ? I.psi_edge[3] : 0.0));
+  if (I.refl_base) {  // a reflective edge's inflow is in the fixed source
+    if (I.reflect[ox > 0 ? 0 : 1]) A.in_x = real(0);
+    if (I.reflect[oy > 0 ? 2 : 3]) A.in_y = real(0);
+  }
   A.sig_t = as_c<real>(I.sig_t);
   A.src = as_c<real>(I.s0) + (size_t)I.N * j;
   A.sphi = as_c<real>(I.sphi);
@@ -650,6 +654,12 @@ k_si(const Inst *__restrict__ insts, SiCtl ctl) {
       if ((threadIdx.x & 31) == 0) {
         atomic_max_nonneg(I.conv + (it & 1) * 2 + 0, (double)dmax);
         atomic_max_nonneg(I.conv + (it & 1) * 2 + 1, (double)pmax);
+      }
+      if (I.refl_base) {
+        // reflective edges: the next sweeps' inflow from these sweeps
+        const int ne = I.K * (I.ny + I.nx);
+        for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x)
+          refl_inject<real>(I, psi, e);
       }
     }
     if (!grid_barrier(ctl.bar, abort_flag)) break;
