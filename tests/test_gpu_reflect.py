@@ -114,3 +114,25 @@ def test_reflective_refusals(dlr):
     with dlr.Solver(dlr.problem_from_case(case, precision=0, method=dlr.DLR_METHOD_SN,
                                           reflect=(0, 0, 1, 1))) as s:  # y mirror: any count
         s.step(1)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_sn_reflective_with_dsa_matches_oracle(orc, dlr, prec):
+    from conftest import oracle_problem
+    case = workloads.small_case(23, 19, 1, 2, 8, seed=8, T0=1.0)
+    case["sigma"] = case["sigma"] * 10.0
+    reflect = (1, 0, 1, 0)
+    p = oracle_problem(case)
+    p.reflect = reflect
+    p.dsa, p.dsa_tol, p.dsa_max_iter = 1, 0.1, 3
+    T = case["T0"].reshape(-1).copy()
+    psi = _planck_psi(case, 16)
+    spec = dlr.problem_from_case(case, precision=prec, method=dlr.DLR_METHOD_SN,
+                                 si_tol=1e-13 if prec == 0 else 0.0, reflect=reflect, dsa=1)
+    with dlr.Solver(spec) as s:
+        for _ in range(2):
+            psi, T, phi, it, *_ = orc.sn_step(p, psi, T, si_tol=1e-13, si_max_iter=20000)
+            s.step(1)
+            assert rel_l2(s.T(), T) < TOL[prec]
+            assert rel_l2(s.psi(), psi) < TOL[prec]
+        assert s.stats()["dsa_iters_total"] > 0

@@ -123,3 +123,22 @@ def test_dlr_refuses_reflective_edges(orc):
     X, S, W = orc.initial_factors(p, T, 2)
     *_, res = orc.dlr_step(p, X, S, W, T)
     assert res.rc == -1
+
+
+def test_dsa_with_reflective_edges_keeps_the_step(orc):
+    # DSA (reading R17: vacuum traces in the diffusion operator) only changes
+    # how the iteration gets there, also behind reflective edges
+    c = workloads.small_case(8, 6, 1, 2, 8, seed=6, T0=1.0)
+    c["sigma"] = c["sigma"] * 10.0
+    res = []
+    for dsa in (0, 1):
+        p = oracle_problem(c)
+        p.reflect = (1, 0, 1, 0)
+        p.dsa, p.dsa_tol, p.dsa_max_iter = dsa, 0.1, 3
+        T = c["T0"].reshape(-1).copy()
+        psi = np.repeat((p.a_rad * p.c * T ** 4 / (4 * np.pi))[:, None], 16, axis=1)
+        psi, T, phi, it, *_ = orc.sn_step(p, psi, T, si_tol=1e-13, si_max_iter=20000)
+        res.append((T, psi, it))
+    assert np.linalg.norm(res[1][0] - res[0][0]) <= 1e-10 * np.linalg.norm(res[0][0])
+    assert np.linalg.norm(res[1][1] - res[0][1]) <= 1e-10 * np.linalg.norm(res[0][1])
+    assert res[1][2] < res[0][2]
