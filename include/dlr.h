@@ -211,6 +211,16 @@ int dlr_autotune(dlr_handle *const *hs, int32_t n, int32_t iters, int32_t reps,
  * depend on the plan.  Synchronises.  DLR_EINVAL unless 0 <= split <= 1e9. */
 int dlr_set_split(dlr_handle *const *hs, int32_t n, double split);
 
+/* Testing aid for failure detection (no paper counterpart): gives the batch
+ * of these handles its finest sweep work plan, with one unit whose bands
+ * wait for the top row of the band below it in another CTA pointed at an
+ * edge row that nothing writes.  The next step's wait for that row gives up
+ * after its time bound (4 s), every instance of the batch reports the sticky
+ * DLR_ETIMEOUT, and the GPU context stays usable (nothing faults or hangs).
+ * DLR_EINVAL if no angle spans more than one unit (ny <= 32 x sweep warps).
+ * Synchronises. */
+int dlr_debug_lose_edge(dlr_handle *const *hs, int32_t n);
+
 /* Copies T (nx*ny FP64) into out; synchronises. */
 int dlr_get_T(dlr_handle *h, double *out, int32_t out_on_device);
 

@@ -280,6 +280,13 @@ def autotune(solvers, *, iters: int = 2, reps: int = 3) -> dict:
     return {"split": chosen.value, "ms": dict(zip(AUTOTUNE_CANDIDATES, list(ms)))}
 
 
+def debug_lose_edge(solvers) -> None:
+    """Testing aid: the next step of the batch `solvers` waits for an edge row
+    that nothing writes, gives up after its time bound and reports ETIMEOUT."""
+    arr = (C.c_void_p * len(solvers))(*[s.h.value for s in solvers])
+    check(load().dlr_debug_lose_edge(arr, len(solvers)))
+
+
 def set_split(solvers, split: float) -> None:
     """Sets the splitting threshold of the sweep work plan of the batch
     `solvers` (0 = one work unit per angle) without timing."""

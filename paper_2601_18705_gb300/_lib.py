@@ -19,7 +19,7 @@ ERROR_NAMES = {DLR_EINVAL: "EINVAL", DLR_ENOMEM: "ENOMEM", DLR_ENOTCONV: "ENOTCO
                DLR_ENONPOS: "ENONPOS", DLR_ECUDA: "ECUDA"}
 
 # every entry point declared in include/dlr.h
-SYMBOLS = ["dlr_create", "dlr_step", "dlr_step_batch", "dlr_autotune", "dlr_set_split",
+SYMBOLS = ["dlr_create", "dlr_step", "dlr_step_batch", "dlr_autotune", "dlr_set_split", "dlr_debug_lose_edge",
            "dlr_get_T", "dlr_set_T", "dlr_get_factors", "dlr_set_factors", "dlr_get_quadrature", "dlr_get_selected",
            "dlr_get_psi", "dlr_set_psi",
            "dlr_get_stats", "dlr_set_timing", "dlr_set_edge_inflow", "dlr_footprint_bytes",
@@ -77,6 +77,7 @@ def load() -> C.CDLL:
     L.dlr_step_batch.argtypes = [C.POINTER(H), C.c_int32, C.c_int32]
     L.dlr_autotune.argtypes = [C.POINTER(H), C.c_int32, C.c_int32, C.c_int32, dp, dp]
     L.dlr_set_split.argtypes = [C.POINTER(H), C.c_int32, C.c_double]
+    L.dlr_debug_lose_edge.argtypes = [C.POINTER(H), C.c_int32]
     L.dlr_get_T.argtypes = [H, C.c_void_p, C.c_int32]
     L.dlr_set_T.argtypes = [H, C.c_void_p, C.c_int32]
     L.dlr_get_factors.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32), C.c_int32]

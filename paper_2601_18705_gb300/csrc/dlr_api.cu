@@ -166,6 +166,7 @@ struct Batch {
   int nx_max = 0, bands_max = 0, si_grid = 0;
   SiCtl ctl{};
   SiUnit *d_units = nullptr;  // capacity units_cap
+  int spare_row = 0;          // an edge row no unit writes (dlr_debug_lose_edge)
   int units_cap = 0;
   double split = 0;           // splitting threshold of the unit plan (<= 0: no split)
   bool sn = false;            // a batch of full-rank SN instances
@@ -1005,7 +1006,9 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
            8 * sz(sizeof(CholJob) * n) + sz(sizeof(ReduceJob) * n);
   const int gedge_ld = (b->nx_max + 3) / 4 * 4 * (b->mixed ? 1 : 2);  // 64-bit words
   bytes += sz(sizeof(SiUnit) * b->units_cap) + sz(64) * 4;
-  bytes += sz(sizeof(unsigned long long) * gedge_ld * std::max(1, rows_cap));
+  // one row more than any plan uses: zeroed below and never written (tags
+  // are nonzero), the row dlr_debug_lose_edge points a unit at
+  bytes += sz(sizeof(unsigned long long) * gedge_ld * (rows_cap + 1));
   const size_t dsa_part = any_dsa ? (size_t)n * kDsaSlots * gmax : 0;  // per-CTA CG partials
   bytes += sz(sizeof(double) * std::max<size_t>(1, dsa_part));
   if (cudaMalloc(&b->d_mem, bytes) != cudaSuccess) {
@@ -1056,8 +1059,9 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   b->ctl.work = carve<unsigned>(cur, 16);
   b->ctl.abort_flag = carve<int>(cur, 16);
   b->ctl.epoch = carve<unsigned>(cur, 16);
-  b->ctl.gedge = carve<unsigned long long>(cur, (size_t)gedge_ld * std::max(1, rows_cap));
+  b->ctl.gedge = carve<unsigned long long>(cur, (size_t)gedge_ld * (rows_cap + 1));
   b->ctl.n_rows = rows_cap;
+  b->spare_row = rows_cap;
   b->ctl.gedge_ld = gedge_ld;
   b->ctl.dsa_part = carve<double>(cur, std::max<size_t>(1, dsa_part));
   b->ctl.any_dsa = any_dsa;
@@ -1470,6 +1474,28 @@ static int set_plan(Batch *b, double split) {
   CK(cudaStreamSynchronize(b->st));  // the host vector dies here
   b->ctl.n_units = (int)units.size();
   b->split = split;
+  return DLR_OK;
+}
+
+// Testing aid for the bounded waits: the finest plan, with the first unit
+// that has an incoming edge row reading the spare row instead, which nothing
+// writes.  The next step's wait for it gives up after its time bound and the
+// instances report DLR_ETIMEOUT; nothing faults.
+int dlr_debug_lose_edge(dlr_handle *const *hs, int32_t n) {
+  int rc = check_handles(hs, n);
+  if (rc) return rc;
+  Batch *b = nullptr;
+  if ((rc = get_batch(hs, n, &b))) return rc;
+  std::vector<SiUnit> units;
+  plan_units(b->hs.data(), b->n, b->mixed, b->si_grid, 1e-9, units);
+  auto it = std::find_if(units.begin(), units.end(), [](const SiUnit &u) { return u.in_row >= 0; });
+  if (it == units.end()) return fail(DLR_EINVAL, "no angle spans more than one sweep unit");
+  if ((int)units.size() > b->units_cap) return fail(DLR_EINVAL, "unit plan exceeds its table");
+  it->in_row = b->spare_row;
+  CK(cudaMemcpyAsync(b->d_units, units.data(), sizeof(SiUnit) * units.size(), cudaMemcpyHostToDevice,
+                     b->st));
+  CK(cudaStreamSynchronize(b->st));
+  b->ctl.n_units = (int)units.size();
   return DLR_OK;
 }
 
