@@ -443,7 +443,9 @@ __device__ __forceinline__ void refl_inject(const Inst &I, const real *psi, int 
 constexpr uint64_t kGridWaitNs = 4000000000ull;  // bound of a grid-barrier wait
 
 // Sense-reversing grid barrier with a bounded wait (co-residency of all
-// CTAs is guaranteed by the cooperative launch).
+// CTAs is guaranteed by the cooperative launch).  A wait that runs out sets
+// the abort flag, so that every CTA leaves at its next wait and the launch
+// reports the timeout.
 __device__ __forceinline__ bool grid_barrier(unsigned *bar, volatile int *abort_flag) {
   __shared__ int ok_s;
   __syncthreads();
@@ -463,7 +465,12 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, volatile int *abort_
       while (*gen == g) {
         if ((++spins & 63u) == 0) {
           __nanosleep(64);
-          if (*abort_flag || global_ns() - t0 > kGridWaitNs) { ok = 0; break; }
+          if (*abort_flag) { ok = 0; break; }
+          if (global_ns() - t0 > kGridWaitNs) {
+            *abort_flag = 1;
+            ok = 0;
+            break;
+          }
         }
       }
     }

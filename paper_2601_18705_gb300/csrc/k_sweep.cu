@@ -488,7 +488,9 @@ __device__ bool sweep_band(int b, const SweepArgs<real> &A, const SweepSmem &S, 
 }
 
 // Bands b0 .. b0 + nb - 1 of one angle by one CTA: warp w sweeps bands
-// b0 + w, b0 + w + NW, ...  Returns false if a wait gave up.
+// b0 + w, b0 + w + NW, ...  Returns, in every thread of the CTA, false if a
+// wait of any warp gave up (a per-warp result would split the CTA between
+// the caller's branches).
 template <typename real, int NW>
 __device__ bool sweep_unit(const SweepArgs<real> &A, const SweepSmem &S, const EdgeLink &L,
                            volatile int *abort_flag) {
@@ -503,8 +505,7 @@ __device__ bool sweep_unit(const SweepArgs<real> &A, const SweepSmem &S, const E
              : sweep_band<real, NW, false>(b, A, S, L, abort_flag);
   }
   if (!ok) *abort_flag = 1;
-  __syncthreads();
-  return ok;
+  return __syncthreads_and(ok) != 0;
 }
 
 template <typename real>
