@@ -102,6 +102,8 @@ def lib() -> C.CDLL:
         L.oracle_sweep_in.argtypes = [C.POINTER(_Problem), C.c_double, C.c_double, _dp, _dp, _dp,
                                       _dp, _dp]
         L.oracle_reflect_index.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
+        L.oracle_sweep_q1.argtypes = [C.POINTER(_Problem), C.c_double, C.c_double, _dp, _dp, _dp,
+                                      _dp, _dp]
         L.oracle_dsa_kappa.restype = C.c_double
         L.oracle_dsa_kappa.argtypes = [C.c_int, C.c_int, C.c_int]
         L.oracle_dsa_apply.argtypes = [C.POINTER(_Problem), _dp, _dp, _dp, _dp]
@@ -219,6 +221,18 @@ def sweep_in(p: Problem, ox: float, oy: float, sigma_t, src, in_x, in_y) -> np.n
     lib().oracle_sweep_in(C.byref(p.cstruct()), float(ox), float(oy), _ptr(st), _ptr(s), _ptr(ix),
                           _ptr(iy), _ptr(psi))
     return psi
+
+
+def sweep_q1(p: Problem, ox: float, oy: float, sigma_t, src, in_x, in_y) -> np.ndarray:
+    """Q1 DG sweep: src (Nx, 4) Legendre coefficients per cell, in_x (ny, 2),
+    in_y (nx, 2) inflow traces; returns psi (Nx, 4)."""
+    st = _f64(sigma_t).reshape(-1)
+    s, ix, iy = (_f64(a).reshape(-1) for a in (src, in_x, in_y))
+    assert s.size == 4 * p.Nx and ix.size == 2 * p.ny and iy.size == 2 * p.nx
+    psi = np.zeros(4 * p.Nx)
+    lib().oracle_sweep_q1(C.byref(p.cstruct()), float(ox), float(oy), _ptr(st), _ptr(s), _ptr(ix),
+                          _ptr(iy), _ptr(psi))
+    return psi.reshape(p.Nx, 4)
 
 
 def reflect_index(n_polar: int, n_azim: int, k: int, axis: int) -> int:

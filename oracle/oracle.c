@@ -244,6 +244,117 @@ static void sn_inflow(const oracle_problem *p, const double *ox, const double *o
 }
 
 /* ------------------------------------------------------------------ */
+/* Bilinear (Q1) upwind DG sweep (Section 4.4 with bilinear elements). */
+/* ------------------------------------------------------------------ */
+
+/* On cell [xc - a, xc + a] x [yc - b, yc + b] (a = hx/2, b = hy/2) a Q1
+ * function is u = u0 + u1 xi + u2 eta + u3 xi eta in the reference
+ * coordinates xi = (x - xc)/a, eta = (y - yc)/b.  The cell equations are
+ * the upwind DG weak form of Section 4.4 (the volume term of G_j and the
+ * face matrix F_d): for every basis function v,
+ *   -int_K u (Om . grad v) + sum_faces int (Om . n) u^ v + int_K sigma_t u v
+ *       = int_K src v,
+ * with u^ the own trace on outflow faces and the upwind trace (the
+ * neighbour's, or the inflow) on inflow faces.  The inflow on a boundary
+ * face is a linear function along it: in[0] + in[1] s, s in [-1, 1] the
+ * reference coordinate along the face (eta on x-faces, xi on y-faces).
+ * src and psi hold 4 coefficients per cell (cell-major); in_x[2 iy + m]
+ * is the inflow of row iy through the upwind x-face, in_y[2 ix + m] that
+ * of column ix through the upwind y-face. */
+
+static int lu_factor(int n, double *A, int *piv);
+static void lu_solve_inplace(int n, const double *LU, const int *piv, double *b);
+
+/* int_{-1}^{1} of the products of two face traces, each trace written as
+ * (c + d s) with (c, d) = (t0, t1): the face trace of basis function i is
+ * tr[i][0] + tr[i][1] s. */
+static double face_prod(const double *ti, const double *tj) {
+  return 2.0 * ti[0] * tj[0] + (2.0 / 3.0) * ti[1] * tj[1];
+}
+
+void oracle_sweep_q1(const oracle_problem *p, double ox, double oy,
+                     const double *sigma_t, const double *src,
+                     const double *in_x, const double *in_y, double *psi) {
+  int nx = p->nx, ny = p->ny;
+  double hx = p->lx / nx, hy = p->ly / ny, a = 0.5 * hx, b = 0.5 * hy;
+  int sx = ox >= 0 ? 1 : -1, sy = oy >= 0 ? 1 : -1;
+  /* face traces (constant, slope along the face) of 1, xi, eta, xi eta:
+   * x-faces xi = +-1 (slope in eta), y-faces eta = +-1 (slope in xi) */
+  double trR[4][2] = {{1, 0}, {1, 0}, {0, 1}, {0, 1}};
+  double trL[4][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1}};
+  double trT[4][2] = {{1, 0}, {0, 1}, {1, 0}, {0, 1}};
+  double trB[4][2] = {{1, 0}, {0, 1}, {-1, 0}, {0, -1}};
+  /* upwind (inflow) and downwind (outflow) faces of this direction */
+  double (*tin_x)[2] = sx > 0 ? trL : trR, (*tout_x)[2] = sx > 0 ? trR : trL;
+  double (*tin_y)[2] = sy > 0 ? trB : trT, (*tout_y)[2] = sy > 0 ? trT : trB;
+  const double mass[4] = {4.0, 4.0 / 3.0, 4.0 / 3.0, 4.0 / 9.0};
+  double A[16], rhs[4], sol[4];
+  int piv[4];
+  for (int jj = 0; jj < ny; jj++) {
+    int iy = sy > 0 ? jj : ny - 1 - jj;
+    for (int ii = 0; ii < nx; ii++) {
+      int ix = sx > 0 ? ii : nx - 1 - ii;
+      int c = iy * nx + ix;
+      /* A[i + 4 j]: column-major 4 x 4 */
+      for (int e = 0; e < 16; e++) A[e] = 0.0;
+      /* volume: -int u (Om . grad v) = -(ox b D1 + oy a D2), with
+       * int int (d v_i / d xi) v_j: (1,0) -> 4, (3,2) -> 4/3 and
+       * int int (d v_i / d eta) v_j: (2,0) -> 4, (3,1) -> 4/3 */
+      A[1 + 4 * 0] -= ox * b * 4.0;
+      A[3 + 4 * 2] -= ox * b * 4.0 / 3.0;
+      A[2 + 4 * 0] -= oy * a * 4.0;
+      A[3 + 4 * 1] -= oy * a * 4.0 / 3.0;
+      /* outflow faces: |Om . n| (face length / 2) int trace_i trace_j */
+      for (int i = 0; i < 4; i++)
+        for (int j = 0; j < 4; j++)
+          A[i + 4 * j] += fabs(ox) * b * face_prod(tout_x[i], tout_x[j]) +
+                          fabs(oy) * a * face_prod(tout_y[i], tout_y[j]);
+      /* reaction and source (the Legendre mass matrix is diagonal) */
+      for (int i = 0; i < 4; i++) {
+        A[i + 4 * i] += sigma_t[c] * a * b * mass[i];
+        rhs[i] = a * b * mass[i] * src[4 * c + i];
+      }
+      /* inflow faces: + |Om . n| (length / 2) int u^_upwind trace_i */
+      double ux[2], uy[2];
+      if (ii == 0) {
+        ux[0] = in_x[2 * iy];
+        ux[1] = in_x[2 * iy + 1];
+      } else {
+        const double *un = psi + 4 * (iy * nx + ix - sx);
+        /* the upwind neighbour's trace on the shared face, as (const, slope in eta) */
+        double (*tn)[2] = sx > 0 ? trR : trL;
+        ux[0] = ux[1] = 0;
+        for (int j = 0; j < 4; j++) {
+          ux[0] += un[j] * tn[j][0];
+          ux[1] += un[j] * tn[j][1];
+        }
+      }
+      if (jj == 0) {
+        uy[0] = in_y[2 * ix];
+        uy[1] = in_y[2 * ix + 1];
+      } else {
+        const double *un = psi + 4 * ((iy - sy) * nx + ix);
+        double (*tn)[2] = sy > 0 ? trT : trB;
+        uy[0] = uy[1] = 0;
+        for (int j = 0; j < 4; j++) {
+          uy[0] += un[j] * tn[j][0];
+          uy[1] += un[j] * tn[j][1];
+        }
+      }
+      for (int i = 0; i < 4; i++)
+        rhs[i] += fabs(ox) * b * face_prod(tin_x[i], ux) + fabs(oy) * a * face_prod(tin_y[i], uy);
+      if (lu_factor(4, A, piv) != 0) {
+        for (int i = 0; i < 4; i++) psi[4 * c + i] = NAN;
+        continue;
+      }
+      memcpy(sol, rhs, sizeof sol);
+      lu_solve_inplace(4, A, piv, sol);
+      memcpy(psi + 4 * c, sol, sizeof sol);
+    }
+  }
+}
+
+/* ------------------------------------------------------------------ */
 /* Diffusion synthetic acceleration (Section 4.5; reading R17).        */
 /* ------------------------------------------------------------------ */
 

@@ -112,6 +112,15 @@ void oracle_sweep_in(const oracle_problem *p, double ox, double oy,
                      const double *sigma_t, const double *src,
                      const double *in_x, const double *in_y, double *psi);
 
+/* Bilinear (Q1) upwind DG sweep of Section 4.4 in direction (ox, oy): per
+ * cell the coefficients of 1, xi, eta, xi eta (reference coordinates of the
+ * cell), 4 per cell in src and psi; in_x[2 iy + m] and in_y[2 ix + m] the
+ * inflow through the upwind x-face of row iy and y-face of column ix as
+ * constant (m = 0) and slope (m = 1) along the face. */
+void oracle_sweep_q1(const oracle_problem *p, double ox, double oy,
+                     const double *sigma_t, const double *src,
+                     const double *in_x, const double *in_y, double *psi);
+
 /* Index of the mirror image of quadrature angle k (axis 0: x component
  * negated, needs n_azim even; axis 1: y component negated), reading R18. */
 int oracle_reflect_index(int n_polar, int n_azim, int k, int axis);

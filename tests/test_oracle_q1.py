@@ -1,0 +1,122 @@
+"""Pins of the oracle's bilinear (Q1) upwind DG sweep (Section 4.4 with the
+paper's bilinear elements): a globally bilinear solution is reproduced
+exactly, a smooth one converges at second order in the cell averages (DG0
+at first), and the cell equations with the test function 1 add up to the
+global balance."""
+import numpy as np
+import pytest
+
+
+def _problem(orc, nx, ny, lx=1.0, ly=1.0):
+    return orc.Problem(nx, ny, 2, 4, np.ones(nx * ny), np.ones(nx * ny), lx=lx, ly=ly)
+
+
+def _centres(p):
+    hx, hy = p.lx / p.nx, p.ly / p.ny
+    xc = (np.arange(p.nx) + 0.5) * hx
+    yc = (np.arange(p.ny) + 0.5) * hy
+    return np.meshgrid(xc, yc), hx / 2, hy / 2
+
+
+def _gauss(n=4):
+    return np.polynomial.legendre.leggauss(n)
+
+
+def _project(p, f):
+    """Legendre coefficients (1, xi, eta, xi eta) per cell of f(x, y), by
+    4 x 4 Gauss quadrature (exact for the polynomial degrees used)."""
+    (X, Y), a, b = _centres(p)
+    g, w = _gauss()
+    out = np.zeros((p.ny, p.nx, 4))
+    norm = np.array([4.0, 4.0 / 3.0, 4.0 / 3.0, 4.0 / 9.0])
+    for gi, wi in zip(g, w):
+        for gj, wj in zip(g, w):
+            val = f(X + a * gi, Y + b * gj)
+            basis = (1.0, gi, gj, gi * gj)
+            for k in range(4):
+                out[:, :, k] += wi * wj * val * basis[k]
+    return (out / norm).reshape(-1, 4)
+
+
+def _inflow(p, f, ox, oy):
+    """Traces of f on the upwind boundary faces as (constant, slope)."""
+    (X, Y), a, b = _centres(p)
+    g, w = _gauss()
+    xb = 0.0 if ox > 0 else p.lx
+    yb = 0.0 if oy > 0 else p.ly
+    in_x = np.zeros((p.ny, 2))
+    in_y = np.zeros((p.nx, 2))
+    for gi, wi in zip(g, w):
+        in_x[:, 0] += wi * f(xb, Y[:, 0] + b * gi) / 2
+        in_x[:, 1] += wi * f(xb, Y[:, 0] + b * gi) * gi / (2 / 3)
+        in_y[:, 0] += wi * f(X[0, :] + a * gi, yb) / 2
+        in_y[:, 1] += wi * f(X[0, :] + a * gi, yb) * gi / (2 / 3)
+    return in_x, in_y
+
+
+@pytest.mark.parametrize("ox,oy", [(0.6, 0.3), (-0.5, 0.7), (0.2, -0.9), (-0.8, -0.4)])
+def test_bilinear_solution_is_exact(orc, ox, oy):
+    p = _problem(orc, 7, 5, lx=1.3, ly=0.7)
+    al, be, ga, de, st = 0.7, -0.4, 1.1, 0.9, 2.5
+    u = lambda x, y: al + be * x + ga * y + de * x * y
+    q = lambda x, y: ox * (be + de * y) + oy * (ga + de * x) + st * u(x, y)
+    in_x, in_y = _inflow(p, u, ox, oy)
+    psi = orc.sweep_q1(p, ox, oy, np.full(p.Nx, st), _project(p, q), in_x, in_y)
+    np.testing.assert_allclose(psi, _project(p, u), rtol=0, atol=1e-12)
+
+
+def _smooth_error(orc, n, ox, oy, st):
+    p = _problem(orc, n, n)
+    u = lambda x, y: 2.0 + np.sin(np.pi * x) * np.cos(0.5 * np.pi * y)
+    ux = lambda x, y: np.pi * np.cos(np.pi * x) * np.cos(0.5 * np.pi * y)
+    uy = lambda x, y: -0.5 * np.pi * np.sin(np.pi * x) * np.sin(0.5 * np.pi * y)
+    q = lambda x, y: ox * ux(x, y) + oy * uy(x, y) + st * u(x, y)
+    in_x, in_y = _inflow(p, u, ox, oy)
+    psi = orc.sweep_q1(p, ox, oy, np.full(p.Nx, st), _project(p, q), in_x, in_y)
+    exact = _project(p, u)
+    e_q1 = np.sqrt(np.mean((psi[:, 0] - exact[:, 0]) ** 2))
+    # DG0 on the same problem: cell-average source, constant inflow
+    orc_p = _problem(orc, n, n)
+    orc_p.psi_edge = (0.0,) * 4
+    in0x, in0y = in_x[:, 0].copy(), in_y[:, 0].copy()
+    psi0 = orc.sweep_in(orc_p, ox, oy, np.full(p.Nx, st), _project(p, q)[:, 0], in0x, in0y)
+    e_dg0 = np.sqrt(np.mean((psi0 - exact[:, 0]) ** 2))
+    return e_q1, e_dg0
+
+
+def test_second_order_convergence(orc):
+    errs = [_smooth_error(orc, n, 0.6, 0.45, 1.5) for n in (8, 16, 32)]
+    q1 = [e[0] for e in errs]
+    dg0 = [e[1] for e in errs]
+    rates_q1 = np.log2(np.array(q1[:-1]) / np.array(q1[1:]))
+    rates_dg0 = np.log2(np.array(dg0[:-1]) / np.array(dg0[1:]))
+    assert np.all(rates_q1 > 1.8), rates_q1
+    assert np.all(rates_dg0 < 1.3), rates_dg0
+    assert q1[-1] < 0.05 * dg0[-1]
+
+
+def test_global_balance(orc):
+    # the cell equations with v = 1 summed over the mesh: the interior faces
+    # cancel, leaving outflow - inflow + int sigma_t u = int src
+    p = _problem(orc, 6, 9, lx=0.8, ly=1.1)
+    rng = np.random.default_rng(3)
+    ox, oy = -0.55, 0.35
+    st = rng.uniform(0.5, 20.0, p.Nx)
+    src = rng.uniform(0.0, 2.0, (p.Nx, 4))
+    in_x = rng.uniform(0.0, 1.0, (p.ny, 2))
+    in_y = rng.uniform(0.0, 1.0, (p.nx, 2))
+    psi = orc.sweep_q1(p, ox, oy, st, src, in_x, in_y)
+    hx, hy = p.lx / p.nx, p.ly / p.ny
+    area = hx * hy
+    U = psi.reshape(p.ny, p.nx, 4)
+    # outflow through the downwind faces (face means: the constant part of the trace)
+    ix_out = 0 if ox < 0 else p.nx - 1
+    iy_out = 0 if oy < 0 else p.ny - 1
+    sgn_x = 1.0 if ox > 0 else -1.0
+    sgn_y = 1.0 if oy > 0 else -1.0
+    out = abs(ox) * hy * np.sum(U[:, ix_out, 0] + sgn_x * U[:, ix_out, 1])
+    out += abs(oy) * hx * np.sum(U[iy_out, :, 0] + sgn_y * U[iy_out, :, 2])
+    inn = abs(ox) * hy * np.sum(in_x[:, 0]) + abs(oy) * hx * np.sum(in_y[:, 0])
+    lhs = out - inn + area * np.sum(st * psi[:, 0])
+    rhs = area * np.sum(src[:, 0])
+    assert abs(lhs - rhs) < 1e-12 * rhs
