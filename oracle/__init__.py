@@ -102,6 +102,8 @@ def lib() -> C.CDLL:
         L.oracle_sweep_in.argtypes = [C.POINTER(_Problem), C.c_double, C.c_double, _dp, _dp, _dp,
                                       _dp, _dp]
         L.oracle_reflect_index.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
+        L.oracle_sn_step_q1.argtypes = [C.POINTER(_Problem), _dp, _dp, C.c_double, C.c_int,
+                                        _dp, _dp, _dp]
         L.oracle_sweep_q1.argtypes = [C.POINTER(_Problem), C.c_double, C.c_double, _dp, _dp, _dp,
                                       _dp, _dp]
         L.oracle_dsa_kappa.restype = C.c_double
@@ -233,6 +235,19 @@ def sweep_q1(p: Problem, ox: float, oy: float, sigma_t, src, in_x, in_y) -> np.n
     lib().oracle_sweep_q1(C.byref(p.cstruct()), float(ox), float(oy), _ptr(st), _ptr(s), _ptr(ix),
                           _ptr(iy), _ptr(psi))
     return psi.reshape(p.Nx, 4)
+
+
+def sn_step_q1(p: Problem, psi, T, *, si_tol: float = 1e-14, si_max_iter: int = 5000):
+    """One full-rank SN step on Q1 elements.  psi is (NOm, Nx, 4); returns
+    new copies (psi, T, phi (Nx, 4), iterations, outflow, inflow)."""
+    psi = _f64(psi).reshape(-1).copy()
+    assert psi.size == 4 * p.Nx * p.NOm
+    T = _f64(T).reshape(-1).copy()
+    phi = np.zeros(4 * p.Nx)
+    out, inn = C.c_double(), C.c_double()
+    it = lib().oracle_sn_step_q1(C.byref(p.cstruct()), _ptr(psi), _ptr(T), si_tol, si_max_iter,
+                                 _ptr(phi), C.byref(out), C.byref(inn))
+    return psi.reshape(p.NOm, p.Nx, 4), T, phi.reshape(p.Nx, 4), it, out.value, inn.value
 
 
 def reflect_index(n_polar: int, n_azim: int, k: int, axis: int) -> int:

@@ -354,6 +354,89 @@ void oracle_sweep_q1(const oracle_problem *p, double ox, double oy,
   }
 }
 
+/* Full-rank SN step on Q1 elements (Section 2.2 with the sweep above):
+ * psi holds 4 Legendre coefficients per cell for every angle,
+ * psi[4 (k Nx + c) + m]; the materials and T stay per cell (the emission q
+ * is constant on a cell), and the temperature update takes the cell
+ * average of phi (its constant coefficient).  Returns the source
+ * iterations, or -2 at the cap. */
+int oracle_sn_step_q1(const oracle_problem *p, double *psi, double *T,
+                      double si_tol, int si_max_iter, double *phi_out,
+                      double *outflow, double *inflow) {
+  int nx = p->nx, ny = p->ny, Nx = nx * ny, NOm = p->n_polar * p->n_azim;
+  double hx = p->lx / nx, hy = p->ly / ny, inv_cdt = 1.0 / (p->c * p->dt);
+  double *ox = (double *)malloc(sizeof(double) * NOm);
+  double *oy = (double *)malloc(sizeof(double) * NOm);
+  double *oz = (double *)malloc(sizeof(double) * NOm);
+  double *w = (double *)malloc(sizeof(double) * NOm);
+  oracle_quadrature(p->n_polar, p->n_azim, ox, oy, oz, w);
+  double *sig_s = (double *)malloc(sizeof(double) * Nx);
+  double *q = (double *)malloc(sizeof(double) * Nx);
+  double *B0 = (double *)malloc(sizeof(double) * Nx);
+  double *D = (double *)malloc(sizeof(double) * Nx);
+  double *sig_t = (double *)malloc(sizeof(double) * Nx);
+  double *phi = (double *)calloc(4 * (size_t)Nx, sizeof(double));
+  double *phin = (double *)malloc(sizeof(double) * 4 * Nx);
+  double *src = (double *)malloc(sizeof(double) * 4 * Nx);
+  double *psi0 = (double *)malloc(sizeof(double) * 4 * (size_t)Nx * NOm);
+  double *in_x = (double *)malloc(sizeof(double) * 2 * ny);
+  double *in_y = (double *)malloc(sizeof(double) * 2 * nx);
+  memcpy(psi0, psi, sizeof(double) * 4 * (size_t)Nx * NOm);
+  oracle_coefficients(p, T, sig_s, q, B0, D);
+  for (int c = 0; c < Nx; c++) sig_t[c] = oracle_sigma_at(p, c, T[c]) + inv_cdt;
+  for (int k = 0; k < NOm; k++)
+    for (size_t e = 0; e < 4 * (size_t)Nx; e++) phi[e] += w[k] * psi0[4 * (size_t)Nx * k + e];
+  int iters = 0, converged = 0;
+  while (iters < si_max_iter) {
+    for (size_t e = 0; e < 4 * (size_t)Nx; e++) phin[e] = 0;
+    for (int k = 0; k < NOm; k++) {
+      for (int c = 0; c < Nx; c++)
+        for (int m = 0; m < 4; m++)
+          src[4 * c + m] = sig_s[c] * phi[4 * c + m] / (4.0 * ORACLE_PI) + (m == 0 ? q[c] : 0.0) +
+                           inv_cdt * psi0[4 * ((size_t)Nx * k + c) + m];
+      for (int iy = 0; iy < ny; iy++) { in_x[2 * iy] = inflow_x(p, ox[k]); in_x[2 * iy + 1] = 0; }
+      for (int ix = 0; ix < nx; ix++) { in_y[2 * ix] = inflow_y(p, oy[k]); in_y[2 * ix + 1] = 0; }
+      double *pk = psi + 4 * (size_t)Nx * k;
+      oracle_sweep_q1(p, ox[k], oy[k], sig_t, src, in_x, in_y, pk);
+      for (size_t e = 0; e < 4 * (size_t)Nx; e++) phin[e] += w[k] * pk[e];
+    }
+    iters++;
+    double dmax = 0, pmax = 0;
+    for (size_t e = 0; e < 4 * (size_t)Nx; e++) {
+      if (fabs(phin[e] - phi[e]) > dmax) dmax = fabs(phin[e] - phi[e]);
+      if (fabs(phin[e]) > pmax) pmax = fabs(phin[e]);
+    }
+    memcpy(phi, phin, sizeof(double) * 4 * Nx);
+    if (dmax <= si_tol * pmax) { converged = 1; break; }
+  }
+  for (int c = 0; c < Nx; c++)
+    T[c] = T[c] + p->dt * oracle_sigma_at(p, c, T[c]) * (phi[4 * c] - 4.0 * ORACLE_PI * B0[c]) / D[c];
+  if (phi_out) memcpy(phi_out, phi, sizeof(double) * 4 * Nx);
+  if (outflow && inflow) {
+    /* face means of the traces: right u0 + u1, left u0 - u1, top u0 + u2,
+     * bottom u0 - u2 */
+    double o = 0, i_ = 0;
+    for (int k = 0; k < NOm; k++) {
+      const double *pk = psi + 4 * (size_t)Nx * k;
+      for (int iy = 0; iy < ny; iy++) {
+        const double *u = pk + 4 * (iy * nx + (ox[k] < 0 ? 0 : nx - 1));
+        o += w[k] * fabs(ox[k]) * hy * (u[0] + (ox[k] < 0 ? -u[1] : u[1]));
+        i_ += w[k] * fabs(ox[k]) * hy * inflow_x(p, ox[k]);
+      }
+      for (int ix = 0; ix < nx; ix++) {
+        const double *u = pk + 4 * ((oy[k] < 0 ? 0 : ny - 1) * nx + ix);
+        o += w[k] * fabs(oy[k]) * hx * (u[0] + (oy[k] < 0 ? -u[2] : u[2]));
+        i_ += w[k] * fabs(oy[k]) * hx * inflow_y(p, oy[k]);
+      }
+    }
+    *outflow = o;
+    *inflow = i_;
+  }
+  free(ox); free(oy); free(oz); free(w); free(sig_s); free(q); free(B0); free(D);
+  free(sig_t); free(phi); free(phin); free(src); free(psi0); free(in_x); free(in_y);
+  return converged ? iters : -2;
+}
+
 /* ------------------------------------------------------------------ */
 /* Diffusion synthetic acceleration (Section 4.5; reading R17).        */
 /* ------------------------------------------------------------------ */

@@ -121,6 +121,13 @@ void oracle_sweep_q1(const oracle_problem *p, double ox, double oy,
                      const double *sigma_t, const double *src,
                      const double *in_x, const double *in_y, double *psi);
 
+/* Full-rank SN step on Q1 elements: psi[4 (k Nx + c) + m] (coefficients of
+ * 1, xi, eta, xi eta), T per cell, phi_out 4 Nx; the temperature update uses
+ * the cell average of phi.  Returns iterations, or -2 at the cap. */
+int oracle_sn_step_q1(const oracle_problem *p, double *psi, double *T,
+                      double si_tol, int si_max_iter, double *phi_out,
+                      double *outflow, double *inflow);
+
 /* Index of the mirror image of quadrature angle k (axis 0: x component
  * negated, needs n_azim even; axis 1: y component negated), reading R18. */
 int oracle_reflect_index(int n_polar, int n_azim, int k, int axis);

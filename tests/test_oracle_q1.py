@@ -120,3 +120,65 @@ def test_global_balance(orc):
     lhs = out - inn + area * np.sum(st * psi[:, 0])
     rhs = area * np.sum(src[:, 0])
     assert abs(lhs - rhs) < 1e-12 * rhs
+
+
+# ---- the full-rank SN step on Q1 elements ----
+
+from test_oracle_dlr import _zero_d_step  # noqa: E402
+import workloads  # noqa: E402
+from conftest import oracle_problem  # noqa: E402
+
+
+def _q1_planck(p, T):
+    B = p.a_rad * p.c * np.asarray(T) ** 4 / (4 * np.pi)
+    psi = np.zeros((p.NOm, p.Nx, 4))
+    psi[:, :, 0] = B[None, :]
+    return psi
+
+
+def test_sn_q1_infinite_medium_recurrence(orc):
+    nx, ny, sig, rho, T0, dt = 5, 4, 10.0, 0.5, 0.5, 0.02
+    p = orc.Problem(nx, ny, 2, 8, np.full(nx * ny, sig), np.full(nx * ny, rho), dt=dt)
+    T = np.full(nx * ny, T0)
+    psi = _q1_planck(p, T)
+    Tz, phiz = T0, 4 * np.pi * orc.planck(p.a_rad, p.c, T0)
+    for _ in range(10):
+        Tz, phiz = _zero_d_step(Tz, phiz, sig, rho, dt, p.c, p.a_rad)
+        p.psi_edge = (phiz / (4 * np.pi),) * 4
+        psi, T, phi, it, *_ = orc.sn_step_q1(p, psi, T, si_tol=1e-15)
+        np.testing.assert_allclose(T, Tz, rtol=1e-12)
+        np.testing.assert_allclose(phi[:, 0], phiz, rtol=1e-12)
+        np.testing.assert_allclose(phi[:, 1:], 0.0, atol=1e-12 * phiz)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_sn_q1_energy_balance(orc, seed):
+    c = workloads.small_case(7, 5, 1, 4, 8, seed=seed, T0=0.6)
+    p = oracle_problem(c)
+    p.psi_edge = (0.3, 0.0, 0.05, 0.0)
+    ox, oy, oz, w = orc.quadrature(4, 8)
+    T = c["T0"].reshape(-1).copy()
+    T[:6] = 1.0
+    psi = _q1_planck(p, T)
+    h2 = (p.lx / p.nx) * (p.ly / p.ny)
+    rho = np.asarray(p.rho_cv).reshape(-1)
+    for _ in range(3):
+        phi0 = np.tensordot(w, psi, axes=(0, 0))[:, 0]
+        E0 = h2 * np.sum(rho * T + phi0 / p.c)
+        psi, T, phi, it, out, inn = orc.sn_step_q1(p, psi, T, si_tol=1e-15, si_max_iter=20000)
+        assert it > 0
+        E1 = h2 * np.sum(rho * T + phi[:, 0] / p.c)
+        assert abs(E1 - E0 + p.dt * (out - inn)) < 1e-12 * E1
+
+
+def test_sn_q1_equilibrium_preserved(orc):
+    c = workloads.small_case(6, 6, 1, 4, 8, T0=0.7)
+    p = oracle_problem(c, psi_edge=[0] * 4)
+    p.set_edge_temperatures([0.7] * 4)
+    T = np.full(p.Nx, 0.7)
+    psi = _q1_planck(p, T)
+    for _ in range(2):
+        psi, T, phi, it, *_ = orc.sn_step_q1(p, psi, T, si_tol=1e-15)
+    np.testing.assert_allclose(T, 0.7, rtol=1e-13)
+    np.testing.assert_allclose(psi[:, :, 0], psi[0, 0, 0], rtol=1e-12)
+    np.testing.assert_allclose(psi[:, :, 1:], 0.0, atol=1e-12 * psi[0, 0, 0])
