@@ -104,6 +104,8 @@ def lib() -> C.CDLL:
         L.oracle_reflect_index.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
         L.oracle_sn_step_q1.argtypes = [C.POINTER(_Problem), _dp, _dp, C.c_double, C.c_int,
                                         _dp, _dp, _dp]
+        L.oracle_dlr_step_q1.argtypes = [C.POINTER(_Problem), C.c_int, _dp, _dp, _dp, _dp,
+                                         C.c_double, C.c_int, _ip, _dp]
         L.oracle_sweep_q1.argtypes = [C.POINTER(_Problem), C.c_double, C.c_double, _dp, _dp, _dp,
                                       _dp, _dp]
         L.oracle_dsa_kappa.restype = C.c_double
@@ -248,6 +250,22 @@ def sn_step_q1(p: Problem, psi, T, *, si_tol: float = 1e-14, si_max_iter: int = 
     it = lib().oracle_sn_step_q1(C.byref(p.cstruct()), _ptr(psi), _ptr(T), si_tol, si_max_iter,
                                  _ptr(phi), C.byref(out), C.byref(inn))
     return psi.reshape(p.NOm, p.Nx, 4), T, phi.reshape(p.Nx, 4), it, out.value, inn.value
+
+
+def dlr_step_q1(p: Problem, X, S, W, T, *, si_tol: float = 1e-13, si_max_iter: int = 5000):
+    """One SN-like DLR step on Q1 elements.  X (4 Nx, r) Q1 coefficients,
+    S (r, r), W (NOm, r), T (Nx).  Returns new copies (X, S, W, T, phi
+    (Nx, 4), iterations, rc)."""
+    X = _fortran(X).copy(order="F")
+    S = _fortran(S).copy(order="F")
+    W = _fortran(W).copy(order="F")
+    T = _f64(T).reshape(-1).copy()
+    r = X.shape[1]
+    phi = np.zeros(4 * p.Nx)
+    it = C.c_int(0)
+    rc = lib().oracle_dlr_step_q1(C.byref(p.cstruct()), r, _fptr(X), _fptr(S), _fptr(W), _ptr(T),
+                                  si_tol, si_max_iter, C.byref(it), _ptr(phi))
+    return X, S, W, T, phi.reshape(p.Nx, 4), it.value, rc
 
 
 def reflect_index(n_polar: int, n_azim: int, k: int, axis: int) -> int:

@@ -264,6 +264,9 @@ static void sn_inflow(const oracle_problem *p, const double *ox, const double *o
 
 static int lu_factor(int n, double *A, int *piv);
 static void lu_solve_inplace(int n, const double *LU, const int *piv, double *b);
+static int lstep_solve(const oracle_problem *p, int r, double *const *Ax, double *const *Ay,
+                       const double *Mt, const double *Ms, const double *qh,
+                       double *const *bE, const double *Lt0, double *L);
 
 /* int_{-1}^{1} of the products of two face traces, each trace written as
  * (c + d s) with (c, d) = (t0, t1): the face trace of basis function i is
@@ -272,86 +275,124 @@ static double face_prod(const double *ti, const double *tj) {
   return 2.0 * ti[0] * tj[0] + (2.0 / 3.0) * ti[1] * tj[1];
 }
 
+/* Face traces (constant, slope along the face) of 1, xi, eta, xi eta:
+ * x-faces xi = +-1 (slope in eta), y-faces eta = +-1 (slope in xi). */
+static const double Q1_TR_R[4][2] = {{1, 0}, {1, 0}, {0, 1}, {0, 1}};
+static const double Q1_TR_L[4][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1}};
+static const double Q1_TR_T[4][2] = {{1, 0}, {0, 1}, {1, 0}, {0, 1}};
+static const double Q1_TR_B[4][2] = {{1, 0}, {0, 1}, {-1, 0}, {0, -1}};
+static const double Q1_MASS[4] = {4.0, 4.0 / 3.0, 4.0 / 3.0, 4.0 / 9.0};
+
+/* The transport part of the cell matrix (volume term and outflow faces) of
+ * direction (ox, oy) on a cell of half-widths a, b: A[i + 4 j]. */
+static void q1_local(double ox, double oy, double a, double b, double *A) {
+  const double (*tout_x)[2] = ox >= 0 ? Q1_TR_R : Q1_TR_L;
+  const double (*tout_y)[2] = oy >= 0 ? Q1_TR_T : Q1_TR_B;
+  for (int e = 0; e < 16; e++) A[e] = 0.0;
+  /* volume: -int u (Om . grad v) = -(ox b D1 + oy a D2), with
+   * int int (d v_i / d xi) v_j: (1,0) -> 4, (3,2) -> 4/3 and
+   * int int (d v_i / d eta) v_j: (2,0) -> 4, (3,1) -> 4/3 */
+  A[1 + 4 * 0] -= ox * b * 4.0;
+  A[3 + 4 * 2] -= ox * b * 4.0 / 3.0;
+  A[2 + 4 * 0] -= oy * a * 4.0;
+  A[3 + 4 * 1] -= oy * a * 4.0 / 3.0;
+  /* outflow faces: |Om . n| (face length / 2) int trace_i trace_j */
+  for (int i = 0; i < 4; i++)
+    for (int j = 0; j < 4; j++)
+      A[i + 4 * j] += fabs(ox) * b * face_prod(tout_x[i], tout_x[j]) +
+                      fabs(oy) * a * face_prod(tout_y[i], tout_y[j]);
+}
+
+/* The trace, on the shared face, of the upwind neighbour's coefficients un
+ * (axis 0: the neighbour across the x-face the direction enters, s = sign
+ * of ox; axis 1 likewise in y), as (constant, slope). */
+static void q1_upwind_trace(const double *un, int axis, int s, double *tr) {
+  const double (*tn)[2] = axis == 0 ? (s > 0 ? Q1_TR_R : Q1_TR_L) : (s > 0 ? Q1_TR_T : Q1_TR_B);
+  tr[0] = tr[1] = 0.0;
+  for (int j = 0; j < 4; j++) {
+    tr[0] += un[j] * tn[j][0];
+    tr[1] += un[j] * tn[j][1];
+  }
+}
+
+/* The inflow-face terms |Om . n| (length / 2) int u^ trace_i of the traces
+ * ux, uy entering through the upwind x- and y-faces, added to r. */
+static void q1_inflow_terms(double ox, double oy, double a, double b, const double *ux,
+                            const double *uy, double *r) {
+  const double (*tin_x)[2] = ox >= 0 ? Q1_TR_L : Q1_TR_R;
+  const double (*tin_y)[2] = oy >= 0 ? Q1_TR_B : Q1_TR_T;
+  for (int i = 0; i < 4; i++)
+    r[i] += fabs(ox) * b * face_prod(tin_x[i], ux) + fabs(oy) * a * face_prod(tin_y[i], uy);
+}
+
 void oracle_sweep_q1(const oracle_problem *p, double ox, double oy,
                      const double *sigma_t, const double *src,
                      const double *in_x, const double *in_y, double *psi) {
   int nx = p->nx, ny = p->ny;
   double hx = p->lx / nx, hy = p->ly / ny, a = 0.5 * hx, b = 0.5 * hy;
   int sx = ox >= 0 ? 1 : -1, sy = oy >= 0 ? 1 : -1;
-  /* face traces (constant, slope along the face) of 1, xi, eta, xi eta:
-   * x-faces xi = +-1 (slope in eta), y-faces eta = +-1 (slope in xi) */
-  double trR[4][2] = {{1, 0}, {1, 0}, {0, 1}, {0, 1}};
-  double trL[4][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1}};
-  double trT[4][2] = {{1, 0}, {0, 1}, {1, 0}, {0, 1}};
-  double trB[4][2] = {{1, 0}, {0, 1}, {-1, 0}, {0, -1}};
-  /* upwind (inflow) and downwind (outflow) faces of this direction */
-  double (*tin_x)[2] = sx > 0 ? trL : trR, (*tout_x)[2] = sx > 0 ? trR : trL;
-  double (*tin_y)[2] = sy > 0 ? trB : trT, (*tout_y)[2] = sy > 0 ? trT : trB;
-  const double mass[4] = {4.0, 4.0 / 3.0, 4.0 / 3.0, 4.0 / 9.0};
-  double A[16], rhs[4], sol[4];
+  double A[16], rhs[4], ux[2], uy[2];
   int piv[4];
   for (int jj = 0; jj < ny; jj++) {
     int iy = sy > 0 ? jj : ny - 1 - jj;
     for (int ii = 0; ii < nx; ii++) {
       int ix = sx > 0 ? ii : nx - 1 - ii;
       int c = iy * nx + ix;
-      /* A[i + 4 j]: column-major 4 x 4 */
-      for (int e = 0; e < 16; e++) A[e] = 0.0;
-      /* volume: -int u (Om . grad v) = -(ox b D1 + oy a D2), with
-       * int int (d v_i / d xi) v_j: (1,0) -> 4, (3,2) -> 4/3 and
-       * int int (d v_i / d eta) v_j: (2,0) -> 4, (3,1) -> 4/3 */
-      A[1 + 4 * 0] -= ox * b * 4.0;
-      A[3 + 4 * 2] -= ox * b * 4.0 / 3.0;
-      A[2 + 4 * 0] -= oy * a * 4.0;
-      A[3 + 4 * 1] -= oy * a * 4.0 / 3.0;
-      /* outflow faces: |Om . n| (face length / 2) int trace_i trace_j */
-      for (int i = 0; i < 4; i++)
-        for (int j = 0; j < 4; j++)
-          A[i + 4 * j] += fabs(ox) * b * face_prod(tout_x[i], tout_x[j]) +
-                          fabs(oy) * a * face_prod(tout_y[i], tout_y[j]);
+      q1_local(ox, oy, a, b, A);
       /* reaction and source (the Legendre mass matrix is diagonal) */
       for (int i = 0; i < 4; i++) {
-        A[i + 4 * i] += sigma_t[c] * a * b * mass[i];
-        rhs[i] = a * b * mass[i] * src[4 * c + i];
+        A[i + 4 * i] += sigma_t[c] * a * b * Q1_MASS[i];
+        rhs[i] = a * b * Q1_MASS[i] * src[4 * c + i];
       }
-      /* inflow faces: + |Om . n| (length / 2) int u^_upwind trace_i */
-      double ux[2], uy[2];
       if (ii == 0) {
         ux[0] = in_x[2 * iy];
         ux[1] = in_x[2 * iy + 1];
       } else {
-        const double *un = psi + 4 * (iy * nx + ix - sx);
-        /* the upwind neighbour's trace on the shared face, as (const, slope in eta) */
-        double (*tn)[2] = sx > 0 ? trR : trL;
-        ux[0] = ux[1] = 0;
-        for (int j = 0; j < 4; j++) {
-          ux[0] += un[j] * tn[j][0];
-          ux[1] += un[j] * tn[j][1];
-        }
+        q1_upwind_trace(psi + 4 * (iy * nx + ix - sx), 0, sx, ux);
       }
       if (jj == 0) {
         uy[0] = in_y[2 * ix];
         uy[1] = in_y[2 * ix + 1];
       } else {
-        const double *un = psi + 4 * ((iy - sy) * nx + ix);
-        double (*tn)[2] = sy > 0 ? trT : trB;
-        uy[0] = uy[1] = 0;
-        for (int j = 0; j < 4; j++) {
-          uy[0] += un[j] * tn[j][0];
-          uy[1] += un[j] * tn[j][1];
-        }
+        q1_upwind_trace(psi + 4 * ((iy - sy) * nx + ix), 1, sy, uy);
       }
-      for (int i = 0; i < 4; i++)
-        rhs[i] += fabs(ox) * b * face_prod(tin_x[i], ux) + fabs(oy) * a * face_prod(tin_y[i], uy);
+      q1_inflow_terms(ox, oy, a, b, ux, uy, rhs);
       if (lu_factor(4, A, piv) != 0) {
         for (int i = 0; i < 4; i++) psi[4 * c + i] = NAN;
         continue;
       }
-      memcpy(sol, rhs, sizeof sol);
-      lu_solve_inplace(4, A, piv, sol);
-      memcpy(psi + 4 * c, sol, sizeof sol);
+      lu_solve_inplace(4, A, piv, rhs);
+      memcpy(psi + 4 * c, rhs, sizeof rhs);
     }
   }
+}
+
+/* The transport operator of direction (ox, oy) on Q1 fields, without
+ * sigma and with zero boundary inflow: out = the left-hand side of the cell
+ * equations of the sweep (tested against every basis function) for u. */
+static void q1_transport_apply(const oracle_problem *p, double ox, double oy, const double *u,
+                               double *out) {
+  int nx = p->nx, ny = p->ny;
+  double a = 0.5 * p->lx / nx, b = 0.5 * p->ly / ny;
+  int sx = ox >= 0 ? 1 : -1, sy = oy >= 0 ? 1 : -1;
+  double A[16], ux[2], uy[2], inr[4];
+  q1_local(ox, oy, a, b, A);
+  for (int iy = 0; iy < ny; iy++)
+    for (int ix = 0; ix < nx; ix++) {
+      int c = iy * nx + ix;
+      for (int i = 0; i < 4; i++) {
+        double t = 0;
+        for (int j = 0; j < 4; j++) t += A[i + 4 * j] * u[4 * c + j];
+        out[4 * c + i] = t;
+      }
+      int jx = ix - sx, jy = iy - sy;
+      ux[0] = ux[1] = uy[0] = uy[1] = 0.0;
+      if (jx >= 0 && jx < nx) q1_upwind_trace(u + 4 * (iy * nx + jx), 0, sx, ux);
+      if (jy >= 0 && jy < ny) q1_upwind_trace(u + 4 * (jy * nx + ix), 1, sy, uy);
+      for (int i = 0; i < 4; i++) inr[i] = 0.0;
+      q1_inflow_terms(ox, oy, a, b, ux, uy, inr);
+      for (int i = 0; i < 4; i++) out[4 * c + i] -= inr[i];
+    }
 }
 
 /* Full-rank SN step on Q1 elements (Section 2.2 with the sweep above):
@@ -435,6 +476,247 @@ int oracle_sn_step_q1(const oracle_problem *p, double *psi, double *T,
   free(ox); free(oy); free(oz); free(w); free(sig_s); free(q); free(B0); free(D);
   free(sig_t); free(phi); free(phin); free(src); free(psi0); free(in_x); free(in_y);
   return converged ? iters : -2;
+}
+
+/* One SN-like DLR step (Algorithm 1) on Q1 elements, steps 2-9 in the
+ * order of Algorithm 1 with the Q1 sweep in step 4 and the Q1 transport
+ * operator in step 7.  X (4 Nx x r) holds Q1 coefficients, orthonormal in
+ * the L2 inner product of Q1 fields, int_K u v = sum_m wq_m u_m v_m with
+ * wq = hx hy (1, 1/3, 1/3, 1/9); S, W as for DG0; T per cell (its update
+ * takes the cell average of phi).  Angle choice by pivoted QR; no
+ * canonical rotation of the factors.  Returns 0, -1 (bad input, singular
+ * matrix) or -2 (SI cap); iters_out and phi_out (4 Nx) may be NULL. */
+int oracle_dlr_step_q1(const oracle_problem *p, int r, double *X, double *S, double *W,
+                       double *T, double si_tol, int si_max_iter, int *iters_out,
+                       double *phi_out) {
+  int nx = p->nx, ny = p->ny, Nx = nx * ny, M4 = 4 * Nx, NOm = p->n_polar * p->n_azim;
+  double hx = p->lx / nx, hy = p->ly / ny, inv_cdt = 1.0 / (p->c * p->dt);
+  if (r < 1 || r > M4 || r > NOm) return -1;
+  int rc = 0;
+  double *ox = (double *)malloc(sizeof(double) * NOm);
+  double *oy = (double *)malloc(sizeof(double) * NOm);
+  double *oz = (double *)malloc(sizeof(double) * NOm);
+  double *w = (double *)malloc(sizeof(double) * NOm);
+  oracle_quadrature(p->n_polar, p->n_azim, ox, oy, oz, w);
+  double *wq = (double *)malloc(sizeof(double) * M4);
+  for (int c = 0; c < Nx; c++)
+    for (int m = 0; m < 4; m++) wq[4 * c + m] = hx * hy * Q1_MASS[m] / 4.0;
+
+  /* step 1: coefficients from T0 */
+  double *sig_s = (double *)malloc(sizeof(double) * Nx);
+  double *q = (double *)malloc(sizeof(double) * Nx);
+  double *B0 = (double *)malloc(sizeof(double) * Nx);
+  double *D = (double *)malloc(sizeof(double) * Nx);
+  double *sig_t = (double *)malloc(sizeof(double) * Nx);
+  oracle_coefficients(p, T, sig_s, q, B0, D);
+  for (int c = 0; c < Nx; c++) sig_t[c] = oracle_sigma_at(p, c, T[c]) + inv_cdt;
+
+  /* step 2: angles, What, beta */
+  int *idx = (int *)malloc(sizeof(int) * r);
+  double *WLU = (double *)malloc(sizeof(double) * r * r);
+  int *wpiv = (int *)malloc(sizeof(int) * r);
+  double *beta = (double *)calloc(r, sizeof(double));
+  if (oracle_qdeim(NOm, r, W, idx) != 0) rc = -1;
+  for (int i = 0; i < r; i++)
+    for (int j = 0; j < r; j++) WLU[i + r * j] = W[idx[i] + (size_t)NOm * j];
+  for (int j = 0; j < r; j++)
+    for (int k = 0; k < NOm; k++) beta[j] += w[k] * W[k + (size_t)NOm * j];
+  if (rc == 0 && lu_factor(r, WLU, wpiv) != 0) rc = -1;
+
+  /* step 3: psi0 at the chosen angles, Psi0_j = X L0[:, idx_j], L0 = S W^T */
+  double *L0 = (double *)malloc(sizeof(double) * r * NOm);
+  for (int i = 0; i < r; i++)
+    for (int k = 0; k < NOm; k++) {
+      double t = 0;
+      for (int l = 0; l < r; l++) t += S[i + r * l] * W[k + (size_t)NOm * l];
+      L0[i + r * k] = t;
+    }
+  double *Psi0 = (double *)malloc(sizeof(double) * M4 * r);
+  double *Psi = (double *)malloc(sizeof(double) * M4 * r);
+  for (int j = 0; j < r; j++)
+    for (int e = 0; e < M4; e++) {
+      double t = 0;
+      for (int i = 0; i < r; i++) t += X[e + (size_t)M4 * i] * L0[i + r * idx[j]];
+      Psi0[e + (size_t)M4 * j] = t;
+    }
+
+  /* step 4: source iteration; phi = beta^T What^-1 Psi per coefficient */
+  double *phi = (double *)malloc(sizeof(double) * M4);
+  double *phin = (double *)malloc(sizeof(double) * M4);
+  double *src = (double *)malloc(sizeof(double) * M4);
+  double *Kc = (double *)malloc(sizeof(double) * r);
+  double *in_x = (double *)malloc(sizeof(double) * 2 * ny);
+  double *in_y = (double *)malloc(sizeof(double) * 2 * nx);
+  int iters = 0;
+  if (rc == 0) {
+    for (int e = 0; e < M4; e++) {
+      for (int j = 0; j < r; j++) Kc[j] = Psi0[e + (size_t)M4 * j];
+      lu_solve_inplace(r, WLU, wpiv, Kc);
+      double t = 0;
+      for (int j = 0; j < r; j++) t += beta[j] * Kc[j];
+      phi[e] = t;
+    }
+    int converged = 0;
+    while (iters < si_max_iter) {
+      for (int j = 0; j < r; j++) {
+        int k = idx[j];
+        for (int c = 0; c < Nx; c++)
+          for (int m = 0; m < 4; m++)
+            src[4 * c + m] = sig_s[c] * phi[4 * c + m] / (4.0 * ORACLE_PI) + (m == 0 ? q[c] : 0.0) +
+                             inv_cdt * Psi0[4 * c + m + (size_t)M4 * j];
+        for (int iy = 0; iy < ny; iy++) { in_x[2 * iy] = inflow_x(p, ox[k]); in_x[2 * iy + 1] = 0; }
+        for (int ix = 0; ix < nx; ix++) { in_y[2 * ix] = inflow_y(p, oy[k]); in_y[2 * ix + 1] = 0; }
+        oracle_sweep_q1(p, ox[k], oy[k], sig_t, src, in_x, in_y, Psi + (size_t)M4 * j);
+      }
+      iters++;
+      double dmax = 0, pmax = 0;
+      for (int e = 0; e < M4; e++) {
+        for (int j = 0; j < r; j++) Kc[j] = Psi[e + (size_t)M4 * j];
+        lu_solve_inplace(r, WLU, wpiv, Kc);
+        double t = 0;
+        for (int j = 0; j < r; j++) t += beta[j] * Kc[j];
+        phin[e] = t;
+        if (fabs(t - phi[e]) > dmax) dmax = fabs(t - phi[e]);
+        if (fabs(t) > pmax) pmax = fabs(t);
+      }
+      memcpy(phi, phin, sizeof(double) * M4);
+      if (dmax <= si_tol * pmax) { converged = 1; break; }
+    }
+    if (!converged) rc = -2;
+  }
+  if (iters_out) *iters_out = iters;
+
+  /* step 5: Psi = X R, X orthonormal in the Q1 inner product */
+  double *Xn = (double *)malloc(sizeof(double) * M4 * r);
+  double *R = (double *)malloc(sizeof(double) * r * r);
+  double *A = (double *)malloc(sizeof(double) * M4 * r);
+  if (rc == 0) {
+    for (int j = 0; j < r; j++)
+      for (int e = 0; e < M4; e++) A[e + (size_t)M4 * j] = sqrt(wq[e]) * Psi[e + (size_t)M4 * j];
+    oracle_householder_qr(M4, r, A, Xn, R);
+    for (int j = 0; j < r; j++)
+      for (int e = 0; e < M4; e++) Xn[e + (size_t)M4 * j] /= sqrt(wq[e]);
+  }
+
+  /* step 6: Lt0 = P L0, P = <X_new, X_old> */
+  double *Lt0 = (double *)malloc(sizeof(double) * r * NOm);
+  double *P = (double *)malloc(sizeof(double) * r * r);
+  if (rc == 0) {
+    for (int jj = 0; jj < r; jj++)
+      for (int i = 0; i < r; i++) {
+        double t = 0;
+        for (int e = 0; e < M4; e++) t += Xn[e + (size_t)M4 * jj] * wq[e] * X[e + (size_t)M4 * i];
+        P[jj + r * i] = t;
+      }
+    for (int jj = 0; jj < r; jj++)
+      for (int k = 0; k < NOm; k++) {
+        double t = 0;
+        for (int i = 0; i < r; i++) t += P[jj + r * i] * L0[i + r * k];
+        Lt0[jj + r * k] = t;
+      }
+  }
+
+  /* step 7: the L-step with the Q1 Galerkin operators
+   * A_x^+- = X^T T(+-1, 0) X, A_y^+- = X^T T(0, +-1) X (T the Q1 transport
+   * operator of the sweep), M_t, M_s, q^ in the Q1 inner product, and the
+   * inflow vectors of a unit inflow on each edge */
+  double *L = (double *)malloc(sizeof(double) * r * NOm);
+  if (rc == 0) {
+    double *Ax[2], *Ay[2], *bE[4];
+    for (int sgn = 0; sgn < 2; sgn++) {
+      Ax[sgn] = (double *)calloc(r * r, sizeof(double));
+      Ay[sgn] = (double *)calloc(r * r, sizeof(double));
+    }
+    for (int e = 0; e < 4; e++) bE[e] = (double *)calloc(r, sizeof(double));
+    double *Mt = (double *)calloc(r * r, sizeof(double));
+    double *Ms = (double *)calloc(r * r, sizeof(double));
+    double *qh = (double *)calloc(r, sizeof(double));
+    double *Tu = (double *)malloc(sizeof(double) * M4);
+    for (int j = 0; j < r; j++) {
+      const double *Xj = Xn + (size_t)M4 * j;
+      for (int sgn = 0; sgn < 2; sgn++) {
+        const double o = sgn == 0 ? 1.0 : -1.0;
+        q1_transport_apply(p, o, 0.0, Xj, Tu);
+        for (int i = 0; i < r; i++) {
+          double t = 0;
+          for (int e = 0; e < M4; e++) t += Xn[e + (size_t)M4 * i] * Tu[e];
+          Ax[sgn][i + r * j] = t;
+        }
+        q1_transport_apply(p, 0.0, o, Xj, Tu);
+        for (int i = 0; i < r; i++) {
+          double t = 0;
+          for (int e = 0; e < M4; e++) t += Xn[e + (size_t)M4 * i] * Tu[e];
+          Ay[sgn][i + r * j] = t;
+        }
+      }
+      for (int i = 0; i < r; i++) {
+        double tt = 0, ts = 0;
+        for (int e = 0; e < M4; e++) {
+          double xx = Xn[e + (size_t)M4 * i] * wq[e] * Xj[e];
+          tt += sig_t[e / 4] * xx;
+          ts += sig_s[e / 4] * xx;
+        }
+        Mt[i + r * j] = tt;
+        Ms[i + r * j] = ts;
+      }
+      double tq = 0;
+      for (int c = 0; c < Nx; c++) tq += q[c] * wq[4 * c] * Xj[4 * c];
+      qh[j] = tq;
+      /* a unit inflow through a boundary face: (length / 2) int trace_i = length trace_i(const) */
+      for (int iy = 0; iy < ny; iy++)
+        for (int i = 0; i < 4; i++) {
+          bE[0][j] += hy * Q1_TR_L[i][0] * Xj[4 * (iy * nx) + i];
+          bE[1][j] += hy * Q1_TR_R[i][0] * Xj[4 * (iy * nx + nx - 1) + i];
+        }
+      for (int ix = 0; ix < nx; ix++)
+        for (int i = 0; i < 4; i++) {
+          bE[2][j] += hx * Q1_TR_B[i][0] * Xj[4 * ix + i];
+          bE[3][j] += hx * Q1_TR_T[i][0] * Xj[4 * ((ny - 1) * nx + ix) + i];
+        }
+    }
+    rc = lstep_solve(p, r, Ax, Ay, Mt, Ms, qh, bE, Lt0, L);
+    for (int sgn = 0; sgn < 2; sgn++) { free(Ax[sgn]); free(Ay[sgn]); }
+    for (int e = 0; e < 4; e++) free(bE[e]);
+    free(Mt); free(Ms); free(qh); free(Tu);
+  }
+
+  /* step 8: L = S W^T (Householder QR of diag(sqrt w) L^T) */
+  if (rc == 0) {
+    double *Mq = (double *)malloc(sizeof(double) * NOm * r);
+    double *Qm = (double *)malloc(sizeof(double) * NOm * r);
+    double *Rm = (double *)malloc(sizeof(double) * r * r);
+    for (int j = 0; j < r; j++)
+      for (int k = 0; k < NOm; k++) Mq[k + (size_t)NOm * j] = sqrt(w[k]) * L[j + r * k];
+    oracle_householder_qr(NOm, r, Mq, Qm, Rm);
+    for (int j = 0; j < r; j++)
+      for (int k = 0; k < NOm; k++) W[k + (size_t)NOm * j] = Qm[k + (size_t)NOm * j] / sqrt(w[k]);
+    for (int i = 0; i < r; i++)
+      for (int j = 0; j < r; j++) S[i + r * j] = Rm[j + r * i];
+    memcpy(X, Xn, sizeof(double) * M4 * r);
+    free(Mq); free(Qm); free(Rm);
+
+    /* step 9: phi of the new factors, T from its cell average */
+    double *bn = (double *)calloc(r, sizeof(double));
+    double *Sb = (double *)calloc(r, sizeof(double));
+    for (int j = 0; j < r; j++)
+      for (int k = 0; k < NOm; k++) bn[j] += w[k] * W[k + (size_t)NOm * j];
+    for (int i = 0; i < r; i++)
+      for (int j = 0; j < r; j++) Sb[i] += S[i + r * j] * bn[j];
+    for (int e = 0; e < M4; e++) {
+      double t = 0;
+      for (int i = 0; i < r; i++) t += X[e + (size_t)M4 * i] * Sb[i];
+      phin[e] = t;
+    }
+    for (int c = 0; c < Nx; c++)
+      T[c] = T[c] + p->dt * oracle_sigma_at(p, c, T[c]) * (phin[4 * c] - 4.0 * ORACLE_PI * B0[c]) / D[c];
+    if (phi_out) memcpy(phi_out, phin, sizeof(double) * M4);
+    free(bn); free(Sb);
+  }
+  free(ox); free(oy); free(oz); free(w); free(wq); free(sig_s); free(q); free(B0); free(D);
+  free(sig_t); free(idx); free(WLU); free(wpiv); free(beta); free(L0); free(Psi0); free(Psi);
+  free(phi); free(phin); free(src); free(Kc); free(in_x); free(in_y); free(Xn); free(R); free(A);
+  free(Lt0); free(P); free(L);
+  return rc;
 }
 
 /* ------------------------------------------------------------------ */
@@ -1060,8 +1342,27 @@ int oracle_lstep(const oracle_problem *p, int r, const double *X,
     }
   }
 
-  /* per angle: B_k = |ox| Ax^s + |oy| Ay^s + M_t, Q_k = q^ + Lt0_k/(c dt)
-   * + inflow terms; Cbar = sum w B^-1, zeta = sum w B^-1 Q */
+  int rc = lstep_solve(p, r, Ax, Ay, Mt, Ms, qh, bE, Lt0, L);
+  for (int s = 0; s < 2; s++) { free(Ax[s]); free(Ay[s]); }
+  for (int e = 0; e < 4; e++) free(bE[e]);
+  free(Mt); free(Ms); free(qh); free(Du); free(ox); free(oy); free(oz); free(w);
+  return rc;
+}
+
+/* The solve of step 7 (Eq. L step) from the Galerkin operators: per angle
+ * B_k = |ox| Ax^s + |oy| Ay^s + M_t, Q_k = q^ + Lt0_k/(c dt) + the inflow
+ * terms; Cbar = sum_k w_k B_k^-1, zeta = sum_k w_k B_k^-1 Q_k;
+ * (I - Cbar M_s / 4 pi) Lbar = zeta; L_k = B_k^-1 (Q_k + M_s Lbar / 4 pi)
+ * (the C-bar device of Section 3.3). */
+static int lstep_solve(const oracle_problem *p, int r, double *const *Ax, double *const *Ay,
+                       const double *Mt, const double *Ms, const double *qh,
+                       double *const *bE, const double *Lt0, double *L) {
+  int NOm = p->n_polar * p->n_azim;
+  double *ox = (double *)malloc(sizeof(double) * NOm);
+  double *oy = (double *)malloc(sizeof(double) * NOm);
+  double *oz = (double *)malloc(sizeof(double) * NOm);
+  double *w = (double *)malloc(sizeof(double) * NOm);
+  oracle_quadrature(p->n_polar, p->n_azim, ox, oy, oz, w);
   double inv_cdt = 1.0 / (p->c * p->dt);
   double *Bk = (double *)malloc(sizeof(double) * r * r * NOm);
   double *Qk = (double *)malloc(sizeof(double) * r * NOm);
@@ -1112,11 +1413,8 @@ int oracle_lstep(const oracle_problem *p, int r, const double *X,
     }
     rc = oracle_lu_solve(r, Bk + (size_t)r * r * k, 1, rhs, L + (size_t)r * k);
   }
-  for (int s = 0; s < 2; s++) { free(Ax[s]); free(Ay[s]); }
-  for (int e = 0; e < 4; e++) free(bE[e]);
-  free(Mt); free(Ms); free(qh); free(Du); free(Bk); free(Qk); free(Cbar);
-  free(zeta); free(I_r); free(Binv); free(BQ); free(Msys); free(Lbar);
-  free(rhs); free(ox); free(oy); free(oz); free(w);
+  free(Bk); free(Qk); free(Cbar); free(zeta); free(I_r); free(Binv); free(BQ); free(Msys);
+  free(Lbar); free(rhs); free(ox); free(oy); free(oz); free(w);
   return rc;
 }
 

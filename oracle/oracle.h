@@ -128,6 +128,14 @@ int oracle_sn_step_q1(const oracle_problem *p, double *psi, double *T,
                       double si_tol, int si_max_iter, double *phi_out,
                       double *outflow, double *inflow);
 
+/* One SN-like DLR step (Algorithm 1) on Q1 elements: X (4 Nx x r) holds Q1
+ * coefficients per cell, orthonormal in the L2 inner product of Q1 fields;
+ * S (r x r), W (NOm x r), T (Nx) as for DG0.  Pivoted-QR angle choice, no
+ * canonical rotation.  Returns 0, -1 or -2 (SI cap). */
+int oracle_dlr_step_q1(const oracle_problem *p, int r, double *X, double *S, double *W,
+                       double *T, double si_tol, int si_max_iter, int *iters_out,
+                       double *phi_out);
+
 /* Index of the mirror image of quadrature angle k (axis 0: x component
  * negated, needs n_azim even; axis 1: y component negated), reading R18. */
 int oracle_reflect_index(int n_polar, int n_azim, int k, int axis);

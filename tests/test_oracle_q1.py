@@ -182,3 +182,60 @@ def test_sn_q1_equilibrium_preserved(orc):
     np.testing.assert_allclose(T, 0.7, rtol=1e-13)
     np.testing.assert_allclose(psi[:, :, 0], psi[0, 0, 0], rtol=1e-12)
     np.testing.assert_allclose(psi[:, :, 1:], 0.0, atol=1e-12 * psi[0, 0, 0])
+
+
+# ---- the SN-like DLR step on Q1 elements ----
+
+def _q1_weights(p):
+    hx, hy = p.lx / p.nx, p.ly / p.ny
+    return np.tile(hx * hy * np.array([1.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 9.0]), p.Nx)
+
+
+def _factors_of(p, w, psi_full, r):
+    """X, S, W with X S W^T = psi_full (4 Nx x NOm) at rank r = 4 Nx: X the
+    scaled unit basis (orthonormal in the Q1 inner product), S W^T its
+    coefficients, factored by a w-weighted QR."""
+    wq = _q1_weights(p)
+    X = np.diag(1.0 / np.sqrt(wq))[:, :r]
+    C = (np.sqrt(wq)[:, None] * psi_full)[:r]
+    Q, R = np.linalg.qr(np.sqrt(w)[:, None] * C.T)
+    return X, R.T.copy(), Q / np.sqrt(w)[:, None]
+
+
+def test_full_rank_dlr_q1_equals_sn_q1(orc):
+    c = workloads.small_case(2, 2, 16, 2, 8, seed=4, T0=0.5)
+    p = oracle_problem(c)
+    p.psi_edge = (0.2, 0.0, 0.1, 0.05)
+    ox, oy, oz, w = orc.quadrature(2, 8)
+    T = c["T0"].reshape(-1).copy()
+    T[0] = 0.9
+    psi = _q1_planck(p, T)                        # (NOm, Nx, 4)
+    X, S, W = _factors_of(p, w, psi.reshape(p.NOm, -1).T, 16)
+    np.testing.assert_allclose(X @ S @ W.T, psi.reshape(p.NOm, -1).T, atol=1e-14)
+    Td = T.copy()
+    for _ in range(2):
+        X, S, W, Td, phid, itd, rc = orc.dlr_step_q1(p, X, S, W, Td, si_tol=1e-14)
+        assert rc == 0 and itd > 0
+        psi, T, phi, it, *_ = orc.sn_step_q1(p, psi, T, si_tol=1e-14)
+        np.testing.assert_allclose(Td, T, rtol=1e-11)
+        full = psi.reshape(p.NOm, -1).T
+        np.testing.assert_allclose(X @ S @ W.T, full, rtol=0, atol=1e-11 * np.abs(full).max())
+        np.testing.assert_allclose(phid, phi, rtol=0, atol=1e-11 * np.abs(phi).max())
+
+
+def test_dlr_q1_infinite_medium_recurrence(orc):
+    nx, ny, sig, rho, T0, dt = 4, 3, 10.0, 0.5, 0.5, 0.02
+    p = orc.Problem(nx, ny, 2, 8, np.full(nx * ny, sig), np.full(nx * ny, rho), dt=dt)
+    X = np.zeros((4 * p.Nx, 1))
+    X[0::4, 0] = 1.0                      # the constant, orthonormal on the unit square
+    W = np.full((p.NOm, 1), 1.0 / np.sqrt(4 * np.pi))
+    S = np.array([[orc.planck(p.a_rad, p.c, T0) * np.sqrt(4 * np.pi)]])
+    T = np.full(p.Nx, T0)
+    Tz, phiz = T0, 4 * np.pi * orc.planck(p.a_rad, p.c, T0)
+    for _ in range(10):
+        Tz, phiz = _zero_d_step(Tz, phiz, sig, rho, dt, p.c, p.a_rad)
+        p.psi_edge = (phiz / (4 * np.pi),) * 4
+        X, S, W, T, phi, it, rc = orc.dlr_step_q1(p, X, S, W, T, si_tol=1e-15)
+        assert rc == 0
+        np.testing.assert_allclose(T, Tz, rtol=1e-12)
+        np.testing.assert_allclose(phi[:, 0], phiz, rtol=1e-12)
