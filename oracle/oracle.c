@@ -55,6 +55,12 @@
  *       first); the product quadrature maps onto itself (x mirror: azimuth
  *       a -> n_azim/2 - 1 - a, needs n_azim even; y mirror: a -> n_azim - 1
  *       - a).
+ *   R19 reflective edges in the DLR step: the collocation sweeps take the
+ *       mirror direction's boundary value interpolated through the chosen
+ *       angles (W0(Om_R)^T What^-1 Psi) from the previous source
+ *       iteration; the L-step's reflected inflow X(c) L_R(k) is implicit and
+ *       solved by a fixed point on the boundary values (per-angle L-steps
+ *       with the current values as extra inflow).
  */
 #include "oracle.h"
 
@@ -266,7 +272,7 @@ static int lu_factor(int n, double *A, int *piv);
 static void lu_solve_inplace(int n, const double *LU, const int *piv, double *b);
 static int lstep_solve(const oracle_problem *p, int r, double *const *Ax, double *const *Ay,
                        const double *Mt, const double *Ms, const double *qh,
-                       double *const *bE, const double *Lt0, double *L);
+                       double *const *bE, const double *Lt0, const double *gext, double *L);
 
 /* int_{-1}^{1} of the products of two face traces, each trace written as
  * (c + d s) with (c, d) = (t0, t1): the face trace of basis function i is
@@ -674,7 +680,7 @@ int oracle_dlr_step_q1(const oracle_problem *p, int r, double *X, double *S, dou
           bE[3][j] += hx * Q1_TR_T[i][0] * Xj[4 * ((ny - 1) * nx + ix) + i];
         }
     }
-    rc = lstep_solve(p, r, Ax, Ay, Mt, Ms, qh, bE, Lt0, L);
+    rc = lstep_solve(p, r, Ax, Ay, Mt, Ms, qh, bE, Lt0, NULL, L);
     for (int sgn = 0; sgn < 2; sgn++) { free(Ax[sgn]); free(Ay[sgn]); }
     for (int e = 0; e < 4; e++) free(bE[e]);
     free(Mt); free(Ms); free(qh); free(Tu);
@@ -1283,6 +1289,13 @@ static void upwind_diff(const oracle_problem *p, int axis, int dir,
 int oracle_lstep(const oracle_problem *p, int r, const double *X,
                  const double *sigma_t, const double *sigma_s,
                  const double *q, const double *Lt0, double *L) {
+  return oracle_lstep_g(p, r, X, sigma_t, sigma_s, q, Lt0, NULL, L);
+}
+
+/* The L-step with an extra inflow vector per angle, gext (r x NOm; NULL: none). */
+int oracle_lstep_g(const oracle_problem *p, int r, const double *X,
+                   const double *sigma_t, const double *sigma_s,
+                   const double *q, const double *Lt0, const double *gext, double *L) {
   int nx = p->nx, ny = p->ny, Nx = nx * ny, NOm = p->n_polar * p->n_azim;
   double hx = p->lx / nx, hy = p->ly / ny, h2 = hx * hy;
   double *ox = (double *)malloc(sizeof(double) * NOm);
@@ -1342,7 +1355,7 @@ int oracle_lstep(const oracle_problem *p, int r, const double *X,
     }
   }
 
-  int rc = lstep_solve(p, r, Ax, Ay, Mt, Ms, qh, bE, Lt0, L);
+  int rc = lstep_solve(p, r, Ax, Ay, Mt, Ms, qh, bE, Lt0, gext, L);
   for (int s = 0; s < 2; s++) { free(Ax[s]); free(Ay[s]); }
   for (int e = 0; e < 4; e++) free(bE[e]);
   free(Mt); free(Ms); free(qh); free(Du); free(ox); free(oy); free(oz); free(w);
@@ -1356,7 +1369,7 @@ int oracle_lstep(const oracle_problem *p, int r, const double *X,
  * (the C-bar device of Section 3.3). */
 static int lstep_solve(const oracle_problem *p, int r, double *const *Ax, double *const *Ay,
                        const double *Mt, const double *Ms, const double *qh,
-                       double *const *bE, const double *Lt0, double *L) {
+                       double *const *bE, const double *Lt0, const double *gext, double *L) {
   int NOm = p->n_polar * p->n_azim;
   double *ox = (double *)malloc(sizeof(double) * NOm);
   double *oy = (double *)malloc(sizeof(double) * NOm);
@@ -1379,13 +1392,16 @@ static int lstep_solve(const oracle_problem *p, int r, double *const *Ax, double
     for (int e = 0; e < r * r; e++)
       B[e] = fabs(ox[k]) * Ax[sx][e] + fabs(oy[k]) * Ay[sy][e] + Mt[e];
     double *Q = Qk + (size_t)r * k;
-    double psx = ox[k] > 0 ? p->psi_edge[0] : p->psi_edge[1];
-    double psy = oy[k] > 0 ? p->psi_edge[2] : p->psi_edge[3];
+    /* a reflective edge's inflow comes in through gext (reading R19) */
+    int ex = ox[k] > 0 ? 0 : 1, ey = oy[k] > 0 ? 2 : 3;
+    double psx = p->reflect[ex] ? 0.0 : p->psi_edge[ex];
+    double psy = p->reflect[ey] ? 0.0 : p->psi_edge[ey];
     const double *bx = ox[k] > 0 ? bE[0] : bE[1];
     const double *by = oy[k] > 0 ? bE[2] : bE[3];
     for (int i = 0; i < r; i++)
       Q[i] = qh[i] + inv_cdt * Lt0[i + r * k] + fabs(ox[k]) * psx * bx[i] +
-             fabs(oy[k]) * psy * by[i];
+             fabs(oy[k]) * psy * by[i] +
+             (gext ? gext[i + (size_t)r * k] : 0.0);
     rc = oracle_lu_solve(r, B, r, I_r, Binv);
     if (rc) break;
     rc = oracle_lu_solve(r, B, 1, Q, BQ);
@@ -1495,15 +1511,51 @@ static void phi_from_factors(int Nx, int NOm, int r, const double *X,
  * and repeat until max|phi_new - phi| <= tol max|phi_new| (reading R7);
  * phi starts from the old state at the chosen angles.  With fixed > 0,
  * exactly `fixed` iterations.  Psi is the last sweep's output. */
+/* For boundary cell c with kappa = What^-1 Psi(c) (the coefficients of
+ * psi(c, .) in W0): the inflow of every chosen angle entering a reflective
+ * edge through c, psi(c, Om_R) = sum_m W0[R, m] kappa_m with R the mirror
+ * angle (reading R19). */
+static void reflected_inflow(const oracle_problem *p, int r, const int *idx, const double *ox,
+                             const double *oy, const double *W, int NOm, int c,
+                             const double *kappa, double *in_x, double *in_y) {
+  int nx = p->nx, ny = p->ny, ix = c % nx, iy = c / nx;
+  for (int j = 0; j < r; j++) {
+    int k = idx[j], ex = ox[k] > 0 ? 0 : 1, ey = oy[k] > 0 ? 2 : 3;
+    if (p->reflect[ex] && ix == (ex == 0 ? 0 : nx - 1)) {
+      int km = oracle_reflect_index(p->n_polar, p->n_azim, k, 0);
+      double t = 0;
+      for (int m = 0; m < r; m++) t += W[km + (size_t)NOm * m] * kappa[m];
+      in_x[j * ny + iy] = t;
+    }
+    if (p->reflect[ey] && iy == (ey == 2 ? 0 : ny - 1)) {
+      int km = oracle_reflect_index(p->n_polar, p->n_azim, k, 1);
+      double t = 0;
+      for (int m = 0; m < r; m++) t += W[km + (size_t)NOm * m] * kappa[m];
+      in_y[j * nx + ix] = t;
+    }
+  }
+}
+
 static int collocation_si(const oracle_problem *p, int r, const double *X0,
                           const double *L0, const int *idx, const double *WLU,
                           const int *wpiv, const double *beta, const double *ox,
                           const double *oy, const double *sig_t,
                           const double *sig_s, const double *q, double tol,
                           int max_iter, int fixed, double *Psi, int *iters_out,
-                          int *dsa_iters_out) {
-  int Nx = p->nx * p->ny;
+                          int *dsa_iters_out, const double *W) {
+  int nx = p->nx, ny = p->ny, Nx = nx * ny, NOm = p->n_polar * p->n_azim;
   double inv_cdt = 1.0 / (p->c * p->dt);
+  /* inflow per chosen angle and boundary row (x-edge) or column (y-edge);
+   * on a reflective edge (reading R19) the mirror direction's value
+   * W0(Om_R)^T What^-1 Psi in the boundary cell, from the previous
+   * iteration (psi0 in the first) */
+  const int refl = p->reflect[0] || p->reflect[1] || p->reflect[2] || p->reflect[3];
+  double *in_x = (double *)malloc(sizeof(double) * r * ny);
+  double *in_y = (double *)malloc(sizeof(double) * r * nx);
+  for (int j = 0; j < r; j++) {
+    for (int iy = 0; iy < ny; iy++) in_x[j * ny + iy] = inflow_x(p, ox[idx[j]]);
+    for (int ix = 0; ix < nx; ix++) in_y[j * nx + ix] = inflow_y(p, oy[idx[j]]);
+  }
   double *Psi0 = (double *)malloc(sizeof(double) * Nx * r);
   double *phi = (double *)malloc(sizeof(double) * Nx);
   double *phin = (double *)malloc(sizeof(double) * Nx);
@@ -1521,6 +1573,7 @@ static int collocation_si(const oracle_problem *p, int r, const double *X0,
     double t = 0;
     for (int j = 0; j < r; j++) t += beta[j] * Kc[j];
     phi[c] = t;
+    if (refl) reflected_inflow(p, r, idx, ox, oy, W, NOm, c, Kc, in_x, in_y);
   }
   int cap = fixed > 0 ? fixed : max_iter;
   int iters = 0, converged = 0, dsa_iters = 0;
@@ -1529,7 +1582,8 @@ static int collocation_si(const oracle_problem *p, int r, const double *X0,
       for (int c = 0; c < Nx; c++)
         src[c] = sig_s[c] * phi[c] / (4.0 * ORACLE_PI) + q[c] +
                  inv_cdt * Psi0[c + (size_t)Nx * j];
-      oracle_sweep(p, ox[idx[j]], oy[idx[j]], sig_t, src, Psi + (size_t)Nx * j);
+      oracle_sweep_in(p, ox[idx[j]], oy[idx[j]], sig_t, src, in_x + (size_t)j * ny,
+                      in_y + (size_t)j * nx, Psi + (size_t)Nx * j);
     }
     iters++;
     double dmax = 0, pmax = 0;
@@ -1539,6 +1593,7 @@ static int collocation_si(const oracle_problem *p, int r, const double *X0,
       double t = 0;
       for (int j = 0; j < r; j++) t += beta[j] * Kc[j];
       phin[c] = t;
+      if (refl) reflected_inflow(p, r, idx, ox, oy, W, NOm, c, Kc, in_x, in_y);
       if (fabs(t - phi[c]) > dmax) dmax = fabs(t - phi[c]);
       if (fabs(t) > pmax) pmax = fabs(t);
     }
@@ -1548,7 +1603,7 @@ static int collocation_si(const oracle_problem *p, int r, const double *X0,
   }
   *iters_out = iters;
   if (dsa_iters_out) *dsa_iters_out = dsa_iters;
-  free(Psi0); free(phi); free(phin); free(src); free(Kc);
+  free(Psi0); free(phi); free(phin); free(src); free(Kc); free(in_x); free(in_y);
   return (fixed <= 0 && !converged) ? -2 : 0;
 }
 
@@ -1584,9 +1639,91 @@ int oracle_collocation(const oracle_problem *p, int r, const double *X0,
   int rc = lu_factor(r, WLU, wpiv);
   if (rc == 0)
     rc = collocation_si(p, r, X0, L0, idx, WLU, wpiv, beta, ox, oy, sig_t, sig_s, q,
-                        tol, max_iter, fixed, Psi, iters, NULL);
+                        tol, max_iter, fixed, Psi, iters, NULL, W0);
   free(ox); free(oy); free(oz); free(w); free(sig_s); free(q); free(sig_t);
   free(WLU); free(wpiv); free(beta); free(L0);
+  return rc;
+}
+
+/* Step 7 with reflective edges (reading R19).  The inflow of angle k
+ * through a reflective edge is the value of its mirror angle R(k) in the
+ * same boundary cell, which the L-step determines itself: a fixed point on
+ * those boundary values, started from the collocation fluxes interpolated
+ * to the mirror angles (W0(Om_R)^T What^-1 Psi), each pass an L-step with
+ * the current values as an extra inflow vector, the values then taken from
+ * its solution (psi(c, Om_R) = X(c) L_R), until they change by at most
+ * 1e-14 relative to their size (at most 5000 passes; -2 otherwise). */
+static int lstep_reflective(const oracle_problem *p, int r, const double *X,
+                            const double *sig_t, const double *sig_s, const double *q,
+                            const double *Lt0, const double *Psi, const double *WLU,
+                            const int *wpiv, const double *W0, double *L) {
+  int nx = p->nx, ny = p->ny, Nx = nx * ny, NOm = p->n_polar * p->n_azim, LB = nx + ny;
+  double hx = p->lx / nx, hy = p->ly / ny;
+  double *ox = (double *)malloc(sizeof(double) * NOm);
+  double *oy = (double *)malloc(sizeof(double) * NOm);
+  double *oz = (double *)malloc(sizeof(double) * NOm);
+  double *w = (double *)malloc(sizeof(double) * NOm);
+  oracle_quadrature(p->n_polar, p->n_azim, ox, oy, oz, w);
+  /* data[k LB + o]: o < ny the x-edge row o angle k enters, o >= ny the y-edge column */
+  double *data = (double *)calloc((size_t)NOm * LB, sizeof(double));
+  double *gext = (double *)malloc(sizeof(double) * r * NOm);
+  double *kap = (double *)malloc(sizeof(double) * r);
+  int rc = -2;
+  /* boundary cell of entry o of angle k, and whether that edge is reflective */
+#define REFL_CELL(k, o, c, on)                                                     \
+  do {                                                                             \
+    if ((o) < ny) {                                                                \
+      int ex_ = ox[k] > 0 ? 0 : 1;                                                 \
+      (on) = p->reflect[ex_];                                                      \
+      (c) = (o) * nx + (ex_ == 0 ? 0 : nx - 1);                                    \
+    } else {                                                                       \
+      int ey_ = oy[k] > 0 ? 2 : 3;                                                 \
+      (on) = p->reflect[ey_];                                                      \
+      (c) = (ey_ == 2 ? 0 : ny - 1) * nx + ((o) - ny);                             \
+    }                                                                              \
+  } while (0)
+  for (int k = 0; k < NOm; k++)
+    for (int o = 0; o < LB; o++) {
+      int c, on;
+      REFL_CELL(k, o, c, on);
+      if (!on) continue;
+      for (int m = 0; m < r; m++) kap[m] = Psi[c + (size_t)Nx * m];
+      lu_solve_inplace(r, WLU, wpiv, kap);
+      int km = oracle_reflect_index(p->n_polar, p->n_azim, k, o < ny ? 0 : 1);
+      double t = 0;
+      for (int m = 0; m < r; m++) t += W0[km + (size_t)NOm * m] * kap[m];
+      data[(size_t)k * LB + o] = t;
+    }
+  for (int pass = 0; pass < 5000; pass++) {
+    for (size_t e = 0; e < (size_t)r * NOm; e++) gext[e] = 0.0;
+    for (int k = 0; k < NOm; k++)
+      for (int o = 0; o < LB; o++) {
+        int c, on;
+        REFL_CELL(k, o, c, on);
+        if (!on) continue;
+        double f = o < ny ? fabs(ox[k]) * hy : fabs(oy[k]) * hx;
+        for (int i = 0; i < r; i++) gext[i + (size_t)r * k] += f * X[c + (size_t)Nx * i] * data[(size_t)k * LB + o];
+      }
+    int lrc = oracle_lstep_g(p, r, X, sig_t, sig_s, q, Lt0, gext, L);
+    if (lrc) { rc = lrc; break; }
+    double dmax = 0, vmax = 0;
+    for (int k = 0; k < NOm; k++)
+      for (int o = 0; o < LB; o++) {
+        int c, on;
+        REFL_CELL(k, o, c, on);
+        if (!on) continue;
+        int km = oracle_reflect_index(p->n_polar, p->n_azim, k, o < ny ? 0 : 1);
+        double t = 0;
+        for (int i = 0; i < r; i++) t += X[c + (size_t)Nx * i] * L[i + (size_t)r * km];
+        double d = fabs(t - data[(size_t)k * LB + o]);
+        if (d > dmax) dmax = d;
+        if (fabs(t) > vmax) vmax = fabs(t);
+        data[(size_t)k * LB + o] = t;
+      }
+    if (dmax <= 1e-14 * vmax) { rc = 0; break; }
+  }
+#undef REFL_CELL
+  free(ox); free(oy); free(oz); free(w); free(data); free(gext); free(kap);
   return rc;
 }
 
@@ -1601,8 +1738,8 @@ int oracle_dlr_step(const oracle_problem *p, int r, double *X, double *S,
   double hx = p->lx / nx, hy = p->ly / ny, h2 = hx * hy, h = sqrt(h2);
   double inv_cdt = 1.0 / (p->c * p->dt);
   if (r < 1 || r > Nx || r > NOm) return -1;
-  if (p->reflect[0] || p->reflect[1] || p->reflect[2] || p->reflect[3]) return -1;  /* R18: SN only */
   const int aug = opt && opt->augment;
+  if (aug && (p->reflect[0] || p->reflect[1] || p->reflect[2] || p->reflect[3])) return -1;
   /* rank of steps 5-8: 2r for the augmented step (R15) */
   const int m = aug ? 2 * r : r;
   if (m > Nx || m > NOm) return -1;
@@ -1662,7 +1799,7 @@ int oracle_dlr_step(const oracle_problem *p, int r, double *X, double *S,
     int fixed = opt ? opt->si_fixed_iters : 0;
     rc = collocation_si(p, r, X, L0, idx, WLU, wpiv, beta, ox, oy, sig_t, sig_s, q,
                         opt ? opt->si_tol : 1e-13, opt ? opt->si_max_iter : 1000,
-                        fixed, Psi, &iters, &dsa_iters);
+                        fixed, Psi, &iters, &dsa_iters, W);
   }
 
   /* Step 5: Psi = X R with h^2 X^T X = I (Householder QR of h Psi); the
@@ -1706,7 +1843,12 @@ int oracle_dlr_step(const oracle_problem *p, int r, double *X, double *S,
 
   /* Step 7: L-step (Eq. L step) on the m basis functions. */
   double *L = (double *)malloc(sizeof(double) * m * NOm);
-  if (rc == 0) rc = oracle_lstep(p, m, Xn, sig_t, sig_s, q, Lt0, L);
+  if (rc == 0) {
+    if (p->reflect[0] || p->reflect[1] || p->reflect[2] || p->reflect[3])
+      rc = lstep_reflective(p, m, Xn, sig_t, sig_s, q, Lt0, Psi, WLU, wpiv, W, L);
+    else
+      rc = oracle_lstep(p, m, Xn, sig_t, sig_s, q, Lt0, L);
+  }
 
   /* Step 8: L = S W^T with sum_k w_k W_ki W_kj = delta: Householder QR of
    * diag(sqrt w) L^T = Q R, W = diag(1/sqrt w) Q, S = R^T; then optionally

@@ -159,6 +159,11 @@ int oracle_initial_factors(const oracle_problem *p, const double *T0, int r,
 int oracle_lstep(const oracle_problem *p, int r, const double *X,
                  const double *sigma_t, const double *sigma_s,
                  const double *q, const double *Lt0, double *L);
+/* The same with an extra inflow vector per angle added to Q_k, gext
+ * (r x NOm, NULL: none); a reflective edge adds no constant inflow. */
+int oracle_lstep_g(const oracle_problem *p, int r, const double *X,
+                   const double *sigma_t, const double *sigma_s,
+                   const double *q, const double *Lt0, const double *gext, double *L);
 
 /* Steps 1-4 of Algorithm 1 at the given angle indices: coefficients from
  * T0, psi0 at the chosen angles, source iteration of the collocation system.

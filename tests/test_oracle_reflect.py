@@ -1,7 +1,9 @@
-"""Pins of reflective edges in the oracle's full-rank SN step (reading R18):
-the mirror maps of the quadrature, the lagged source iteration against a
-dense solve with the reflection coupled in, a mirror-doubled domain, the 0-D
-recurrence of an all-reflective uniform medium, and energy conservation."""
+"""Pins of reflective edges in the oracle (readings R18 for the SN step, R19
+for the DLR step): the mirror maps of the quadrature, the lagged source
+iteration against a dense solve with the reflection coupled in, a
+mirror-doubled domain, the 0-D recurrence of an all-reflective uniform
+medium, energy conservation, and the full-rank DLR step equal to the SN
+step with reflective edges."""
 import numpy as np
 import pytest
 
@@ -115,14 +117,42 @@ def test_all_reflective_conserves_energy(orc):
         assert abs(E1 - E0) < 1e-11 * E1
 
 
-def test_dlr_refuses_reflective_edges(orc):
-    c = workloads.small_case(6, 5, 2, 2, 8, seed=4)
+@pytest.mark.parametrize("n,reflect", [(2, (1, 0, 0, 0)), (3, (0, 1, 1, 0)), (3, (1, 1, 1, 1))])
+def test_full_rank_dlr_with_reflective_edges_equals_sn(orc, n, reflect):
+    # reading R19: the L-step's reflected inflow is implicit (a fixed point on
+    # the boundary values), so at full rank the DLR step is the SN step
+    c = workloads.small_case(n, n, n * n, 2, 8, seed=n + 7, T0=0.5)
     p = oracle_problem(c)
-    p.reflect = (1, 0, 0, 0)
-    T = c["T0"].reshape(-1)
-    X, S, W = orc.initial_factors(p, T, 2)
-    *_, res = orc.dlr_step(p, X, S, W, T)
-    assert res.rc == -1
+    p.psi_edge = (0.2, 0.1, 0.05, 0.0)
+    p.reflect = reflect
+    r = n * n
+    T = c["T0"].reshape(-1).copy()
+    T[0] = 0.9
+    X, S, W = orc.initial_factors(p, T, r)
+    psi = X @ S @ W.T
+    Tsn = T.copy()
+    for _ in range(2):
+        X, S, W, T, res = orc.dlr_step(p, X, S, W, T, si_tol=1e-14, si_max_iter=20000)
+        assert res.rc == 0
+        psi, Tsn, phi, it, *_ = orc.sn_step(p, psi, Tsn, si_tol=1e-14, si_max_iter=20000)
+        np.testing.assert_allclose(T, Tsn, rtol=1e-10)
+        np.testing.assert_allclose(X @ S @ W.T, psi, rtol=0, atol=1e-10 * np.abs(psi).max())
+
+
+@pytest.mark.parametrize("r", [1, 3])
+def test_dlr_all_reflective_uniform_medium_is_the_zero_d_recurrence(orc, r):
+    nx, ny, sig, rho, T0, dt = 6, 5, 10.0, 0.5, 0.5, 0.02
+    p = orc.Problem(nx, ny, 4, 8, np.full(nx * ny, sig), np.full(nx * ny, rho), dt=dt)
+    p.reflect = (1, 1, 1, 1)
+    X, S, W = orc.initial_factors(p, np.full(nx * ny, T0), r)
+    T = np.full(nx * ny, T0)
+    Tz, phiz = T0, 4 * np.pi * orc.planck(p.a_rad, p.c, T0)
+    for _ in range(15):
+        Tz, phiz = _zero_d_step(Tz, phiz, sig, rho, dt, p.c, p.a_rad)
+        X, S, W, T, res = orc.dlr_step(p, X, S, W, T, si_tol=1e-14)
+        assert res.rc == 0
+        np.testing.assert_allclose(T, Tz, rtol=1e-12)
+        np.testing.assert_allclose(res.phi, phiz, rtol=1e-12)
 
 
 def test_dsa_with_reflective_edges_keeps_the_step(orc):
@@ -142,3 +172,21 @@ def test_dsa_with_reflective_edges_keeps_the_step(orc):
     assert np.linalg.norm(res[1][0] - res[0][0]) <= 1e-10 * np.linalg.norm(res[0][0])
     assert np.linalg.norm(res[1][1] - res[0][1]) <= 1e-10 * np.linalg.norm(res[0][1])
     assert res[1][2] < res[0][2]
+
+
+def test_collocation_at_every_angle_is_the_sn_iteration(orc):
+    # steps 1-4 at r = NOm chosen angles: the interpolation through What is
+    # exact, so the lagged reflected inflow of the collocation sweeps is the
+    # SN one and the collocation fluxes are the SN angular flux
+    c = workloads.small_case(4, 4, 16, 2, 8, seed=17, T0=0.5)
+    p = oracle_problem(c)
+    p.psi_edge = (0.2, 0.0, 0.05, 0.1)
+    p.reflect = (1, 0, 0, 1)
+    T = c["T0"].reshape(-1).copy()
+    T[3] = 0.9
+    X, S, W = orc.initial_factors(p, T, 16)
+    idx = np.arange(16)[::-1].copy()
+    Psi, it, rc = orc.collocation(p, X, S, W, T, idx, si_tol=1e-14, si_max_iter=20000)
+    assert rc == 0 and it > 0
+    psi, *_ = orc.sn_step(p, X @ S @ W.T, T, si_tol=1e-14, si_max_iter=20000)
+    np.testing.assert_allclose(Psi, psi[:, idx], rtol=0, atol=1e-11 * np.abs(psi).max())
