@@ -48,7 +48,7 @@
  *       correction multiplies rounding noise by up to sigma_s / sigma_a in
  *       thick scattering cells, so phi^{l+1} - phi^l would stall above a
  *       tolerance near the working precision.
- *   R18 reflective edges (full-rank SN only): a direction entering through a
+ *   R18 reflective edges (full-rank SN): a direction entering through a
  *       reflective edge takes as inflow, row by row, the boundary cell value
  *       of its mirror image (the direction with the normal component
  *       negated), from the previous source iteration (from psi^n in the
