@@ -1524,7 +1524,7 @@ static void reflected_inflow(const oracle_problem *p, int r, const int *idx, con
     if (p->reflect[ex] && ix == (ex == 0 ? 0 : nx - 1)) {
       int km = oracle_reflect_index(p->n_polar, p->n_azim, k, 0);
       double t = 0;
-      for (int m = 0; m < r; m++) t += W[km + (size_t)NOm * m] * kappa[m];
+      for (int m = 0; m < r; m++) t += W[k + (size_t)NOm * m] * kappa[m];
       in_x[j * ny + iy] = t;
     }
     if (p->reflect[ey] && iy == (ey == 2 ? 0 : ny - 1)) {
@@ -1645,6 +1645,21 @@ int oracle_collocation(const oracle_problem *p, int r, const double *X0,
   return rc;
 }
 
+/* Boundary entry o of a direction (ox, oy): o < ny the row of the x-edge it
+ * enters, o >= ny the column of its y-edge.  Sets *c to the boundary cell
+ * and returns whether that edge is reflective. */
+static int refl_entry(const oracle_problem *p, double ox, double oy, int o, int *c) {
+  int nx = p->nx, ny = p->ny;
+  if (o < ny) {
+    int ex = ox > 0 ? 0 : 1;
+    *c = o * nx + (ex == 0 ? 0 : nx - 1);
+    return p->reflect[ex];
+  }
+  int ey = oy > 0 ? 2 : 3;
+  *c = (ey == 2 ? 0 : ny - 1) * nx + (o - ny);
+  return p->reflect[ey];
+}
+
 /* Step 7 with reflective edges (reading R19).  The inflow of angle k
  * through a reflective edge is the value of its mirror angle R(k) in the
  * same boundary cell, which the L-step determines itself: a fixed point on
@@ -1669,24 +1684,10 @@ static int lstep_reflective(const oracle_problem *p, int r, const double *X,
   double *gext = (double *)malloc(sizeof(double) * r * NOm);
   double *kap = (double *)malloc(sizeof(double) * r);
   int rc = -2;
-  /* boundary cell of entry o of angle k, and whether that edge is reflective */
-#define REFL_CELL(k, o, c, on)                                                     \
-  do {                                                                             \
-    if ((o) < ny) {                                                                \
-      int ex_ = ox[k] > 0 ? 0 : 1;                                                 \
-      (on) = p->reflect[ex_];                                                      \
-      (c) = (o) * nx + (ex_ == 0 ? 0 : nx - 1);                                    \
-    } else {                                                                       \
-      int ey_ = oy[k] > 0 ? 2 : 3;                                                 \
-      (on) = p->reflect[ey_];                                                      \
-      (c) = (ey_ == 2 ? 0 : ny - 1) * nx + ((o) - ny);                             \
-    }                                                                              \
-  } while (0)
   for (int k = 0; k < NOm; k++)
     for (int o = 0; o < LB; o++) {
-      int c, on;
-      REFL_CELL(k, o, c, on);
-      if (!on) continue;
+      int c;
+      if (!refl_entry(p, ox[k], oy[k], o, &c)) continue;
       for (int m = 0; m < r; m++) kap[m] = Psi[c + (size_t)Nx * m];
       lu_solve_inplace(r, WLU, wpiv, kap);
       int km = oracle_reflect_index(p->n_polar, p->n_azim, k, o < ny ? 0 : 1);
@@ -1698,9 +1699,8 @@ static int lstep_reflective(const oracle_problem *p, int r, const double *X,
     for (size_t e = 0; e < (size_t)r * NOm; e++) gext[e] = 0.0;
     for (int k = 0; k < NOm; k++)
       for (int o = 0; o < LB; o++) {
-        int c, on;
-        REFL_CELL(k, o, c, on);
-        if (!on) continue;
+        int c;
+        if (!refl_entry(p, ox[k], oy[k], o, &c)) continue;
         double f = o < ny ? fabs(ox[k]) * hy : fabs(oy[k]) * hx;
         for (int i = 0; i < r; i++) gext[i + (size_t)r * k] += f * X[c + (size_t)Nx * i] * data[(size_t)k * LB + o];
       }
@@ -1709,9 +1709,8 @@ static int lstep_reflective(const oracle_problem *p, int r, const double *X,
     double dmax = 0, vmax = 0;
     for (int k = 0; k < NOm; k++)
       for (int o = 0; o < LB; o++) {
-        int c, on;
-        REFL_CELL(k, o, c, on);
-        if (!on) continue;
+        int c;
+        if (!refl_entry(p, ox[k], oy[k], o, &c)) continue;
         int km = oracle_reflect_index(p->n_polar, p->n_azim, k, o < ny ? 0 : 1);
         double t = 0;
         for (int i = 0; i < r; i++) t += X[c + (size_t)Nx * i] * L[i + (size_t)r * km];
@@ -1722,7 +1721,6 @@ static int lstep_reflective(const oracle_problem *p, int r, const double *X,
       }
     if (dmax <= 1e-14 * vmax) { rc = 0; break; }
   }
-#undef REFL_CELL
   free(ox); free(oy); free(oz); free(w); free(data); free(gext); free(kap);
   return rc;
 }
