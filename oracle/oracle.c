@@ -1524,7 +1524,7 @@ static void reflected_inflow(const oracle_problem *p, int r, const int *idx, con
     if (p->reflect[ex] && ix == (ex == 0 ? 0 : nx - 1)) {
       int km = oracle_reflect_index(p->n_polar, p->n_azim, k, 0);
       double t = 0;
-      for (int m = 0; m < r; m++) t += W[k + (size_t)NOm * m] * kappa[m];
+      for (int m = 0; m < r; m++) t += W[km + (size_t)NOm * m] * kappa[m];
       in_x[j * ny + iy] = t;
     }
     if (p->reflect[ey] && iy == (ey == 2 ? 0 : ny - 1)) {
