@@ -106,6 +106,8 @@ def lib() -> C.CDLL:
                                         _dp, _dp, _dp]
         L.oracle_dlr_step_q1.argtypes = [C.POINTER(_Problem), C.c_int, _dp, _dp, _dp, _dp,
                                          C.c_double, C.c_int, _ip, _dp]
+        L.oracle_q1_deriv.argtypes = [C.POINTER(_Problem), C.c_int, _dp]
+        L.oracle_dsa_matrix_q1.argtypes = [C.POINTER(_Problem), _dp, _dp, _dp]
         L.oracle_sweep_q1.argtypes = [C.POINTER(_Problem), C.c_double, C.c_double, _dp, _dp, _dp,
                                       _dp, _dp]
         L.oracle_dsa_kappa.restype = C.c_double
@@ -266,6 +268,22 @@ def dlr_step_q1(p: Problem, X, S, W, T, *, si_tol: float = 1e-13, si_max_iter: i
     rc = lib().oracle_dlr_step_q1(C.byref(p.cstruct()), r, _fptr(X), _fptr(S), _fptr(W), _ptr(T),
                                   si_tol, si_max_iter, C.byref(it), _ptr(phi))
     return X, S, W, T, phi.reshape(p.Nx, 4), it.value, rc
+
+
+def q1_deriv(p: Problem, axis: int) -> np.ndarray:
+    """The Q1 DG derivative D_j as a dense (4 Nx, 4 Nx) matrix (reading R20)."""
+    n = 4 * p.Nx
+    D = np.zeros(n * n)
+    lib().oracle_q1_deriv(C.byref(p.cstruct()), int(axis), _ptr(D))
+    return D.reshape(n, n).T.copy()
+
+
+def dsa_matrix_q1(p: Problem, sigma_t, sigma_a) -> np.ndarray:
+    n = 4 * p.Nx
+    st, sa = (_f64(a).reshape(-1) for a in (sigma_t, sigma_a))
+    A = np.zeros(n * n)
+    lib().oracle_dsa_matrix_q1(C.byref(p.cstruct()), _ptr(st), _ptr(sa), _ptr(A))
+    return A.reshape(n, n).T.copy()
 
 
 def reflect_index(n_polar: int, n_azim: int, k: int, axis: int) -> int:

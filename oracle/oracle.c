@@ -55,6 +55,13 @@
  *       first); the product quadrature maps onto itself (x mirror: azimuth
  *       a -> n_azim/2 - 1 - a, needs n_azim even; y mirror: a -> n_azim - 1
  *       - a).
+ *   R20 DSA on Q1 elements: the DG derivative is
+ *       v^T D_j u = -sum_K int_K u dv/dx_j + sum_faces int {u} [[v]]_j
+ *       (the volume term G_j of Section 4.4 with the face term in the form
+ *       that makes D_j exact for continuous fields, which on piecewise
+ *       constants is the centred difference of R17), M_t and M_a the Q1
+ *       mass matrices weighted by sigma_t and sigma_a, F0 the face-jump
+ *       penalty of R17 on the Q1 traces, zero traces outside.
  *   R19 reflective edges in the DLR step: the collocation sweeps take the
  *       mirror direction's boundary value interpolated through the chosen
  *       angles (W0(Om_R)^T What^-1 Psi) from the previous source
@@ -273,6 +280,8 @@ static void lu_solve_inplace(int n, const double *LU, const int *piv, double *b)
 static int lstep_solve(const oracle_problem *p, int r, double *const *Ax, double *const *Ay,
                        const double *Mt, const double *Ms, const double *qh,
                        double *const *bE, const double *Lt0, const double *gext, double *L);
+static int dsa_correct_q1(const oracle_problem *p, const double *sig_t, const double *sig_s,
+                          const double *phi_old, double *phi_half);
 
 /* int_{-1}^{1} of the products of two face traces, each trace written as
  * (c + d s) with (c, d) = (t0, t1): the face trace of basis function i is
@@ -453,6 +462,7 @@ int oracle_sn_step_q1(const oracle_problem *p, double *psi, double *T,
       if (fabs(phin[e] - phi[e]) > dmax) dmax = fabs(phin[e] - phi[e]);
       if (fabs(phin[e]) > pmax) pmax = fabs(phin[e]);
     }
+    if (p->dsa) dsa_correct_q1(p, sig_t, sig_s, phi, phin);  /* R17, R20 */
     memcpy(phi, phin, sizeof(double) * 4 * Nx);
     if (dmax <= si_tol * pmax) { converged = 1; break; }
   }
@@ -888,6 +898,153 @@ static int dsa_correct(const oracle_problem *p, const double *sig_t,
   int it = oracle_dsa_solve(p, sig_t, sig_a, b, p->dsa_tol, p->dsa_max_iter, delta);
   for (int c = 0; c < N; c++) phi_half[c] += delta[c];
   free(sig_a); free(b); free(delta);
+  return it;
+}
+
+/* ------------------------------------------------------------------ */
+/* DSA on Q1 elements (Section 4.5 with the bilinear elements; R20).   */
+/* ------------------------------------------------------------------ */
+
+/* The DG derivative D_j (axis 0: x, 1: y) on Q1 fields as a dense n x n
+ * matrix (n = 4 Nx, row 4 c + i tests basis function i of cell c), column
+ * major: v^T D_j u = -sum_K int_K u dv/dx_j + sum_faces int {u} [[v]]_j,
+ * with [[v]]_j = v_lo - v_hi across a face normal to axis j and a zero
+ * trace outside the domain. */
+void oracle_q1_deriv(const oracle_problem *p, int axis, double *Dm) {
+  int nx = p->nx, ny = p->ny, Nx = nx * ny;
+  size_t n = 4 * (size_t)Nx;
+  double hx = p->lx / nx, hy = p->ly / ny;
+  double hf = axis == 0 ? hy : hx;  /* face length */
+  const double (*tlo)[2] = axis == 0 ? Q1_TR_R : Q1_TR_T;  /* traces on the face, lo side */
+  const double (*thi)[2] = axis == 0 ? Q1_TR_L : Q1_TR_B;  /* hi side */
+  for (size_t e = 0; e < n * n; e++) Dm[e] = 0.0;
+#define DM(row, col) Dm[(size_t)(row) + n * (size_t)(col)]
+  for (int c = 0; c < Nx; c++) {
+    /* volume: -int_K u dv/dx_j = -(hf / 2) int int u dv/dxi_j */
+    if (axis == 0) {
+      DM(4 * c + 1, 4 * c + 0) -= 0.5 * hf * 4.0;
+      DM(4 * c + 3, 4 * c + 2) -= 0.5 * hf * 4.0 / 3.0;
+    } else {
+      DM(4 * c + 2, 4 * c + 0) -= 0.5 * hf * 4.0;
+      DM(4 * c + 3, 4 * c + 1) -= 0.5 * hf * 4.0 / 3.0;
+    }
+  }
+  int nl = axis == 0 ? nx : ny, lines = axis == 0 ? ny : nx;
+  for (int l = 0; l < lines; l++)
+    for (int f = 0; f <= nl; f++) {
+      int lo, hi;
+      face_cells(p, axis, l, f, &lo, &hi);
+      /* (hf / 2) int {u} [[v]]: {u} = (u_lo + u_hi) / 2, [[v]] = v_lo - v_hi */
+      for (int i = 0; i < 4; i++)
+        for (int m = 0; m < 4; m++) {
+          if (lo >= 0) {
+            DM(4 * lo + i, 4 * lo + m) += 0.25 * hf * face_prod(tlo[i], tlo[m]);
+            if (hi >= 0) DM(4 * lo + i, 4 * hi + m) += 0.25 * hf * face_prod(tlo[i], thi[m]);
+          }
+          if (hi >= 0) {
+            if (lo >= 0) DM(4 * hi + i, 4 * lo + m) -= 0.25 * hf * face_prod(thi[i], tlo[m]);
+            DM(4 * hi + i, 4 * hi + m) -= 0.25 * hf * face_prod(thi[i], thi[m]);
+          }
+        }
+    }
+#undef DM
+}
+
+/* The DSA operator on Q1 fields as a dense matrix, column major:
+ * A = (1/3) sum_j D_j^T M_t^{-1} D_j + F0 + M_a (R20). */
+void oracle_dsa_matrix_q1(const oracle_problem *p, const double *sig_t, const double *sig_a,
+                          double *A) {
+  int nx = p->nx, ny = p->ny, Nx = nx * ny;
+  size_t n = 4 * (size_t)Nx;
+  double hx = p->lx / nx, hy = p->ly / ny;
+  double *Dm = (double *)malloc(sizeof(double) * n * n);
+  for (size_t e = 0; e < n * n; e++) A[e] = 0.0;
+  for (int axis = 0; axis < 2; axis++) {
+    oracle_q1_deriv(p, axis, Dm);
+    /* (1/3) D^T M_t^{-1} D, M_t = diag(sigma_t wq) in the Legendre basis */
+    for (size_t a = 0; a < n; a++)
+      for (size_t b = 0; b < n; b++) {
+        double t = 0;
+        for (size_t k = 0; k < n; k++) {
+          double mt = sig_t[k / 4] * hx * hy * Q1_MASS[k % 4] / 4.0;
+          t += Dm[k + n * a] * Dm[k + n * b] / mt;
+        }
+        A[a + n * b] += t / 3.0;
+      }
+    /* F0: kappa (hf / 2) int [[u]] [[v]] on every face */
+    double kap = oracle_dsa_kappa(p->n_polar, p->n_azim, axis);
+    double hf = axis == 0 ? hy : hx;
+    const double (*tlo)[2] = axis == 0 ? Q1_TR_R : Q1_TR_T;
+    const double (*thi)[2] = axis == 0 ? Q1_TR_L : Q1_TR_B;
+    int nl = axis == 0 ? nx : ny, lines = axis == 0 ? ny : nx;
+    for (int l = 0; l < lines; l++)
+      for (int f = 0; f <= nl; f++) {
+        int lo, hi;
+        face_cells(p, axis, l, f, &lo, &hi);
+        for (int i = 0; i < 4; i++)
+          for (int m = 0; m < 4; m++) {
+            double k2 = kap * 0.5 * hf;
+            if (lo >= 0) A[(4 * lo + i) + n * (4 * lo + m)] += k2 * face_prod(tlo[i], tlo[m]);
+            if (hi >= 0) A[(4 * hi + i) + n * (4 * hi + m)] += k2 * face_prod(thi[i], thi[m]);
+            if (lo >= 0 && hi >= 0) {
+              A[(4 * lo + i) + n * (4 * hi + m)] -= k2 * face_prod(tlo[i], thi[m]);
+              A[(4 * hi + i) + n * (4 * lo + m)] -= k2 * face_prod(thi[i], tlo[m]);
+            }
+          }
+      }
+  }
+  /* M_a */
+  for (size_t k = 0; k < n; k++) A[k + n * k] += sig_a[k / 4] * hx * hy * Q1_MASS[k % 4] / 4.0;
+  free(Dm);
+}
+
+/* The DSA step of the Q1 SN step: phi_half += delta,
+ * A delta = M_s (phi_half - phi_old), by Jacobi-preconditioned CG as in
+ * R17 (dsa_tol, dsa_max_iter).  Returns the CG iterations. */
+static int dsa_correct_q1(const oracle_problem *p, const double *sig_t, const double *sig_s,
+                          const double *phi_old, double *phi_half) {
+  int Nx = p->nx * p->ny;
+  size_t n = 4 * (size_t)Nx;
+  double hx = p->lx / p->nx, hy = p->ly / p->ny;
+  double *sig_a = (double *)malloc(sizeof(double) * Nx);
+  for (int c = 0; c < Nx; c++) sig_a[c] = sig_t[c] - sig_s[c];
+  double *A = (double *)malloc(sizeof(double) * n * n);
+  oracle_dsa_matrix_q1(p, sig_t, sig_a, A);
+  double *b = (double *)malloc(sizeof(double) * n);
+  double *x = (double *)calloc(n, sizeof(double));
+  double *r = (double *)malloc(sizeof(double) * n);
+  double *z = (double *)malloc(sizeof(double) * n);
+  double *pp = (double *)malloc(sizeof(double) * n);
+  double *q = (double *)malloc(sizeof(double) * n);
+  for (size_t k = 0; k < n; k++) {
+    b[k] = sig_s[k / 4] * hx * hy * Q1_MASS[k % 4] / 4.0 * (phi_half[k] - phi_old[k]);
+    r[k] = b[k];
+    z[k] = r[k] / A[k + n * k];
+    pp[k] = z[k];
+  }
+  double bb = dot((int)n, b, b), rz = dot((int)n, r, z);
+  int it = 0;
+  while (bb > 0 && it < p->dsa_max_iter) {
+    for (size_t a = 0; a < n; a++) {
+      double t = 0;
+      for (size_t k = 0; k < n; k++) t += A[a + n * k] * pp[k];
+      q[a] = t;
+    }
+    double alpha = rz / dot((int)n, pp, q);
+    for (size_t k = 0; k < n; k++) {
+      x[k] += alpha * pp[k];
+      r[k] -= alpha * q[k];
+    }
+    it++;
+    if (dot((int)n, r, r) <= p->dsa_tol * p->dsa_tol * bb) break;
+    for (size_t k = 0; k < n; k++) z[k] = r[k] / A[k + n * k];
+    double rz_new = dot((int)n, r, z);
+    double beta = rz_new / rz;
+    rz = rz_new;
+    for (size_t k = 0; k < n; k++) pp[k] = z[k] + beta * pp[k];
+  }
+  for (size_t k = 0; k < n; k++) phi_half[k] += x[k];
+  free(sig_a); free(A); free(b); free(x); free(r); free(z); free(pp); free(q);
   return it;
 }
 

@@ -136,6 +136,13 @@ int oracle_dlr_step_q1(const oracle_problem *p, int r, double *X, double *S, dou
                        double *T, double si_tol, int si_max_iter, int *iters_out,
                        double *phi_out);
 
+/* DSA on Q1 elements (reading R20), dense (4 Nx x 4 Nx, column major): the
+ * DG derivative D_j (axis 0: x, 1: y) and the operator
+ * A = (1/3) sum_j D_j^T M_t^{-1} D_j + F0 + M_a. */
+void oracle_q1_deriv(const oracle_problem *p, int axis, double *Dm);
+void oracle_dsa_matrix_q1(const oracle_problem *p, const double *sig_t, const double *sig_a,
+                          double *A);
+
 /* Index of the mirror image of quadrature angle k (axis 0: x component
  * negated, needs n_azim even; axis 1: y component negated), reading R18. */
 int oracle_reflect_index(int n_polar, int n_azim, int k, int axis);

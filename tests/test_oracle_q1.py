@@ -239,3 +239,104 @@ def test_dlr_q1_infinite_medium_recurrence(orc):
         assert rc == 0
         np.testing.assert_allclose(T, Tz, rtol=1e-12)
         np.testing.assert_allclose(phi[:, 0], phiz, rtol=1e-12)
+
+
+# ---- DSA on Q1 elements (reading R20) ----
+
+def _q1_coeffs_of(p, f):
+    return _project(p, f)                       # (Nx, 4), exact for bilinear f
+
+
+def test_q1_derivative_is_exact_on_continuous_bilinear_fields(orc):
+    p = _problem(orc, 6, 5, lx=1.2, ly=0.9)
+    hx, hy = p.lx / p.nx, p.ly / p.ny
+    (X, Y), a, b = _centres(p)
+    Dx, Dy = orc.q1_deriv(p, 0), orc.q1_deriv(p, 1)
+    inner = np.zeros((p.ny, p.nx), bool)
+    inner[1:-1, 1:-1] = True
+    inner = inner.reshape(-1)
+    for f, dfx, dfy in [(lambda x, y: x, lambda x, y: 1.0 + 0 * x, lambda x, y: 0 * x),
+                        (lambda x, y: x * y, lambda x, y: y, lambda x, y: x),
+                        (lambda x, y: 2 - y + 0.5 * x * y, lambda x, y: 0.5 * y, lambda x, y: -1 + 0.5 * x)]:
+        u = _q1_coeffs_of(p, f).reshape(-1)
+        # int_K v d f / dx_j for every basis function v: the Q1 mass times the projection
+        wq = np.tile(hx * hy * np.array([1.0, 1 / 3, 1 / 3, 1 / 9]), p.Nx)
+        for D, df in ((Dx, dfx), (Dy, dfy)):
+            expect = wq * _q1_coeffs_of(p, df).reshape(-1)
+            got = D @ u
+            np.testing.assert_allclose(got.reshape(-1, 4)[inner], expect.reshape(-1, 4)[inner],
+                                       rtol=0, atol=1e-13)
+
+
+def test_q1_derivative_on_constants_is_the_centred_difference(orc):
+    p = _problem(orc, 5, 4, lx=1.1, ly=0.8)
+    hy = p.ly / p.ny
+    u0 = np.random.default_rng(5).uniform(0.5, 2.0, p.Nx)
+    u = np.zeros((p.Nx, 4))
+    u[:, 0] = u0
+    got = (orc.q1_deriv(p, 0) @ u.reshape(-1)).reshape(-1, 4)[:, 0].reshape(p.ny, p.nx)
+    g = np.pad(u0.reshape(p.ny, p.nx), ((0, 0), (1, 1)))      # zero traces outside
+    np.testing.assert_allclose(got, 0.5 * hy * (g[:, 2:] - g[:, :-2]), rtol=0, atol=1e-14)
+
+
+def test_q1_dsa_operator_is_spd(orc):
+    p = _problem(orc, 4, 3, lx=0.9, ly=1.3)
+    st = 10.0 ** (2.0 * np.random.default_rng(7).uniform(size=p.Nx))
+    sa = st * np.random.default_rng(8).uniform(0.01, 0.5, p.Nx)
+    A = orc.dsa_matrix_q1(p, st, sa)
+    assert np.max(np.abs(A - A.T)) <= 1e-13 * np.max(np.abs(A))
+    assert np.linalg.eigvalsh(A).min() > 0
+
+
+def test_q1_sn_dsa_keeps_the_step_and_cuts_iterations(orc):
+    c = workloads.small_case(5, 4, 1, 2, 8, seed=9, T0=1.0)
+    c["sigma"] = np.full((4, 5), 1e3)
+    res = []
+    for dsa in (0, 1):
+        p = oracle_problem(c)
+        p.dsa, p.dsa_tol, p.dsa_max_iter = dsa, 0.1, 3
+        T = c["T0"].reshape(-1).copy()
+        psi = _q1_planck(p, T)
+        psi, T, phi, it, *_ = orc.sn_step_q1(p, psi, T, si_tol=1e-12, si_max_iter=20000)
+        res.append((T, psi, it))
+    assert np.linalg.norm(res[1][0] - res[0][0]) <= 1e-9 * np.linalg.norm(res[0][0])
+    assert np.linalg.norm(res[1][1] - res[0][1]) <= 1e-9 * np.linalg.norm(res[0][1])
+    assert res[0][2] > 100 and res[1][2] * 5 < res[0][2], (res[0][2], res[1][2])
+
+
+def _q1_mass_by_quadrature(p, coef):
+    """int_K coef phi_i phi_j over each cell by 4 x 4 Gauss quadrature (the
+    Legendre basis 1, xi, eta, xi eta), as a dense block-diagonal matrix."""
+    hx, hy = p.lx / p.nx, p.ly / p.ny
+    g, w = _gauss()
+    M = np.zeros((4 * p.Nx, 4 * p.Nx))
+    for c in range(p.Nx):
+        B = np.zeros((4, 4))
+        for gi, wi in zip(g, w):
+            for gj, wj in zip(g, w):
+                ph = np.array([1.0, gi, gj, gi * gj])
+                B += wi * wj * np.outer(ph, ph) * hx * hy / 4
+        M[4 * c:4 * c + 4, 4 * c:4 * c + 4] = coef[c] * B
+    return M
+
+
+def test_q1_dsa_operator_parts(orc):
+    p = _problem(orc, 4, 5, lx=1.0, ly=1.2)
+    rng = np.random.default_rng(11)
+    st = rng.uniform(1.0, 30.0, p.Nx)
+    sa = rng.uniform(0.1, 1.0, p.Nx)
+    D = [orc.q1_deriv(p, 0), orc.q1_deriv(p, 1)]
+    # M_a: the sigma_a-weighted Q1 mass matrix
+    Ma = orc.dsa_matrix_q1(p, st, sa) - orc.dsa_matrix_q1(p, st, 0 * sa)
+    np.testing.assert_allclose(Ma, _q1_mass_by_quadrature(p, sa), rtol=0, atol=1e-13)
+    # (1/3) sum_j D_j^T M_t^-1 D_j: halving it by doubling sigma_t
+    diff = orc.dsa_matrix_q1(p, st, sa) - orc.dsa_matrix_q1(p, 2 * st, sa)
+    Mt_inv = np.linalg.inv(_q1_mass_by_quadrature(p, st))
+    expect = sum(Dj.T @ Mt_inv @ Dj for Dj in D) / 6.0
+    np.testing.assert_allclose(diff, expect, rtol=0, atol=1e-12 * np.abs(expect).max())
+    # F0 penalises jumps only: zero on a continuous field away from the boundary
+    F0 = orc.dsa_matrix_q1(p, np.full(p.Nx, 1e300), 0 * sa)
+    u = _project(p, lambda x, y: 1 + x - 2 * y + x * y).reshape(-1)
+    inner = np.zeros((p.ny, p.nx), bool)
+    inner[1:-1, 1:-1] = True
+    np.testing.assert_allclose((F0 @ u).reshape(-1, 4)[inner.reshape(-1)], 0.0, atol=1e-13)
