@@ -500,7 +500,7 @@ int oracle_sn_step_q1(const oracle_problem *p, double *psi, double *T,
  * the L2 inner product of Q1 fields, int_K u v = sum_m wq_m u_m v_m with
  * wq = hx hy (1, 1/3, 1/3, 1/9); S, W as for DG0; T per cell (its update
  * takes the cell average of phi).  Angle choice by pivoted QR; no
- * canonical rotation of the factors.  Returns 0, -1 (bad input, singular
+ * canonical rotation of the factors; DSA (R17, R20) when p->dsa.  Returns 0, -1 (bad input, singular
  * matrix) or -2 (SI cap); iters_out and phi_out (4 Nx) may be NULL. */
 int oracle_dlr_step_q1(const oracle_problem *p, int r, double *X, double *S, double *W,
                        double *T, double si_tol, int si_max_iter, int *iters_out,
@@ -595,6 +595,7 @@ int oracle_dlr_step_q1(const oracle_problem *p, int r, double *X, double *S, dou
         if (fabs(t - phi[e]) > dmax) dmax = fabs(t - phi[e]);
         if (fabs(t) > pmax) pmax = fabs(t);
       }
+      if (p->dsa) dsa_correct_q1(p, sig_t, sig_s, phi, phin);  /* R17, R20 */
       memcpy(phi, phin, sizeof(double) * M4);
       if (dmax <= si_tol * pmax) { converged = 1; break; }
     }

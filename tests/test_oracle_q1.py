@@ -340,3 +340,24 @@ def test_q1_dsa_operator_parts(orc):
     inner = np.zeros((p.ny, p.nx), bool)
     inner[1:-1, 1:-1] = True
     np.testing.assert_allclose((F0 @ u).reshape(-1, 4)[inner.reshape(-1)], 0.0, atol=1e-13)
+
+
+def test_dlr_q1_dsa_keeps_the_step_and_cuts_iterations(orc):
+    c = workloads.small_case(5, 4, 4, 2, 8, seed=10, T0=1.0)
+    c["sigma"] = np.full((4, 5), 1e3)
+    res = []
+    for dsa in (0, 1):
+        p = oracle_problem(c)
+        p.dsa, p.dsa_tol, p.dsa_max_iter = dsa, 0.1, 3
+        X = np.zeros((4 * p.Nx, 1))
+        X[0::4, 0] = 1.0
+        W = np.full((p.NOm, 1), 1.0 / np.sqrt(4 * np.pi))
+        S = np.array([[orc.planck(p.a_rad, p.c, 1.0) * np.sqrt(4 * np.pi)]])
+        T = c["T0"].reshape(-1).copy()
+        T[:5] = 0.6                              # a cooler bottom row: not a 0-D problem
+        X, S, W, T, phi, it, rc = orc.dlr_step_q1(p, X, S, W, T, si_tol=1e-12, si_max_iter=20000)
+        assert rc == 0
+        res.append((T, X @ S @ W.T, it))
+    assert np.linalg.norm(res[1][0] - res[0][0]) <= 1e-9 * np.linalg.norm(res[0][0])
+    assert np.linalg.norm(res[1][1] - res[0][1]) <= 1e-9 * np.linalg.norm(res[0][1])
+    assert res[0][2] > 50 and res[1][2] * 3 < res[0][2], (res[0][2], res[1][2])
