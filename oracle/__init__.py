@@ -41,10 +41,21 @@ def build(force: bool = False) -> str:
         os.path.getmtime(_SRC), os.path.getmtime(_HDR)) > os.path.getmtime(_OUT)
     if force or stale:
         tmp = _OUT + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared",
-                               _SRC, "-o", tmp, "-lm"])
+        base = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+        # OpenMP where the compiler has it (same results with any thread count)
+        if subprocess.call(base + ["-fopenmp"], stderr=subprocess.DEVNULL) != 0:
+            subprocess.check_call(base)
         os.replace(tmp, _OUT)
     return _OUT
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops (n <= 0: all processors)."""
+    lib().oracle_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().oracle_get_threads())
 
 
 _dp = C.POINTER(C.c_double)
@@ -110,6 +121,8 @@ def lib() -> C.CDLL:
         L.oracle_dsa_matrix_q1.argtypes = [C.POINTER(_Problem), _dp, _dp, _dp]
         L.oracle_sweep_q1.argtypes = [C.POINTER(_Problem), C.c_double, C.c_double, _dp, _dp, _dp,
                                       _dp, _dp]
+        L.oracle_set_threads.argtypes = [C.c_int]
+        L.oracle_get_threads.restype = C.c_int
         L.oracle_dsa_kappa.restype = C.c_double
         L.oracle_dsa_kappa.argtypes = [C.c_int, C.c_int, C.c_int]
         L.oracle_dsa_apply.argtypes = [C.POINTER(_Problem), _dp, _dp, _dp, _dp]

@@ -74,6 +74,30 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads: where OpenMP is available, loops whose iterations are independent
+ * (angles of one round of sweeps, cells of the scalar flux, columns of a
+ * reflector application, entries of a projection, angles of the L-step)
+ * run in parallel.  Every sum keeps its serial order inside one iteration
+ * and no iteration writes what another reads, so the results are bitwise
+ * those of one thread. */
+void oracle_set_threads(int n) {
+#ifdef _OPENMP
+  omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+#else
+  (void)n;
+#endif
+}
+int oracle_get_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 #define ORACLE_PI 3.14159265358979323846
 #define TIE_REL 1e-12
@@ -1125,6 +1149,7 @@ void oracle_householder_qr(int m, int n, const double *A, double *Q,
     for (int i = j; i < m; i++) vv += H[i + m * j] * H[i + m * j];
     hn[j] = vv;
     if (vv > 0) {
+#pragma omp parallel for schedule(static) if ((size_t)m * (n - j) > 65536)
       for (int k = j; k < n; k++) {
         double d = 0;
         for (int i = j; i < m; i++) d += H[i + m * j] * V[i + m * k];
@@ -1140,6 +1165,7 @@ void oracle_householder_qr(int m, int n, const double *A, double *Q,
     for (int i = 0; i < m; i++) Q[i + m * j] = i == j ? 1.0 : 0.0;
   for (int j = n - 1; j >= 0; j--) {
     if (hn[j] == 0) continue;
+#pragma omp parallel for schedule(static) if ((size_t)m * n > 65536)
     for (int k = 0; k < n; k++) {
       double d = 0;
       for (int i = j; i < m; i++) d += H[i + m * j] * Q[i + m * k];
@@ -1473,7 +1499,10 @@ int oracle_lstep_g(const oracle_problem *p, int r, const double *X,
   double *qh = (double *)calloc(r, sizeof(double));
   double *bE[4];
   for (int e = 0; e < 4; e++) bE[e] = (double *)calloc(r, sizeof(double));
+#pragma omp parallel if ((size_t)Nx * r > 65536)
+  {
   double *Du = (double *)malloc(sizeof(double) * Nx);
+#pragma omp for schedule(dynamic, 1)
   for (int j = 0; j < r; j++) {
     const double *Xj = X + (size_t)Nx * j;
     for (int s = 0; s < 2; s++) {
@@ -1512,11 +1541,13 @@ int oracle_lstep_g(const oracle_problem *p, int r, const double *X,
       bE[3][j] += hx * Xj[(ny - 1) * nx + ix];
     }
   }
+  free(Du);
+  }
 
   int rc = lstep_solve(p, r, Ax, Ay, Mt, Ms, qh, bE, Lt0, gext, L);
   for (int s = 0; s < 2; s++) { free(Ax[s]); free(Ay[s]); }
   for (int e = 0; e < 4; e++) free(bE[e]);
-  free(Mt); free(Ms); free(qh); free(Du); free(ox); free(oy); free(oz); free(w);
+  free(Mt); free(Ms); free(qh); free(ox); free(oy); free(oz); free(w);
   return rc;
 }
 
@@ -1540,11 +1571,15 @@ static int lstep_solve(const oracle_problem *p, int r, double *const *Ax, double
   double *Cbar = (double *)calloc(r * r, sizeof(double));
   double *zeta = (double *)calloc(r, sizeof(double));
   double *I_r = (double *)calloc(r * r, sizeof(double));
-  double *Binv = (double *)malloc(sizeof(double) * r * r);
-  double *BQ = (double *)malloc(sizeof(double) * r);
+  /* B_k^-1 and B_k^-1 Q_k of every angle first (independent per angle),
+   * then the sums over angles in angle order */
+  double *Binv_all = (double *)malloc(sizeof(double) * r * r * NOm);
+  double *BQ_all = (double *)malloc(sizeof(double) * r * NOm);
+  int *rck = (int *)calloc(NOm, sizeof(int));
   for (int i = 0; i < r; i++) I_r[i + r * i] = 1.0;
   int rc = 0;
-  for (int k = 0; k < NOm && rc == 0; k++) {
+#pragma omp parallel for schedule(dynamic, 8) if (NOm * r * r > 65536)
+  for (int k = 0; k < NOm; k++) {
     int sx = ox[k] > 0 ? 0 : 1, sy = oy[k] > 0 ? 0 : 1;
     double *B = Bk + (size_t)r * r * k;
     for (int e = 0; e < r * r; e++)
@@ -1560,9 +1595,14 @@ static int lstep_solve(const oracle_problem *p, int r, double *const *Ax, double
       Q[i] = qh[i] + inv_cdt * Lt0[i + r * k] + fabs(ox[k]) * psx * bx[i] +
              fabs(oy[k]) * psy * by[i] +
              (gext ? gext[i + (size_t)r * k] : 0.0);
-    rc = oracle_lu_solve(r, B, r, I_r, Binv);
+    double *Binv = Binv_all + (size_t)r * r * k, *BQ = BQ_all + (size_t)r * k;
+    rck[k] = oracle_lu_solve(r, B, r, I_r, Binv);
+    if (rck[k] == 0) rck[k] = oracle_lu_solve(r, B, 1, Q, BQ);
+  }
+  for (int k = 0; k < NOm && rc == 0; k++) {
+    rc = rck[k];
     if (rc) break;
-    rc = oracle_lu_solve(r, B, 1, Q, BQ);
+    const double *Binv = Binv_all + (size_t)r * r * k, *BQ = BQ_all + (size_t)r * k;
     for (int e = 0; e < r * r; e++) Cbar[e] += w[k] * Binv[e];
     for (int i = 0; i < r; i++) zeta[i] += w[k] * BQ[i];
   }
@@ -1579,16 +1619,24 @@ static int lstep_solve(const oracle_problem *p, int r, double *const *Ax, double
       }
     rc = oracle_lu_solve(r, Msys, 1, zeta, Lbar);
   }
-  for (int k = 0; k < NOm && rc == 0; k++) {
+  if (rc == 0) {
+    /* M_s Lbar / 4 pi is the same for every angle */
     for (int i = 0; i < r; i++) {
       double t = 0;
       for (int l = 0; l < r; l++) t += Ms[i + r * l] * Lbar[l];
-      rhs[i] = Qk[i + (size_t)r * k] + t / (4.0 * ORACLE_PI);
+      rhs[i] = t / (4.0 * ORACLE_PI);
     }
-    rc = oracle_lu_solve(r, Bk + (size_t)r * r * k, 1, rhs, L + (size_t)r * k);
+#pragma omp parallel for schedule(dynamic, 8) if (NOm * r * r > 65536)
+    for (int k = 0; k < NOm; k++) {
+      double *rk = (double *)malloc(sizeof(double) * r);
+      for (int i = 0; i < r; i++) rk[i] = Qk[i + (size_t)r * k] + rhs[i];
+      rck[k] = oracle_lu_solve(r, Bk + (size_t)r * r * k, 1, rk, L + (size_t)r * k);
+      free(rk);
+    }
+    for (int k = 0; k < NOm && rc == 0; k++) rc = rck[k];
   }
-  free(Bk); free(Qk); free(Cbar); free(zeta); free(I_r); free(Binv); free(BQ); free(Msys);
-  free(Lbar); free(rhs); free(ox); free(oy); free(oz); free(w);
+  free(Bk); free(Qk); free(Cbar); free(zeta); free(I_r); free(Binv_all); free(BQ_all); free(rck);
+  free(Msys); free(Lbar); free(rhs); free(ox); free(oy); free(oz); free(w);
   return rc;
 }
 
@@ -1649,6 +1697,7 @@ static void phi_from_factors(int Nx, int NOm, int r, const double *X,
     for (int k = 0; k < NOm; k++) beta[j] += w[k] * W[k + (size_t)NOm * j];
   for (int i = 0; i < r; i++)
     for (int j = 0; j < r; j++) Sb[i] += S[i + r * j] * beta[j];
+#pragma omp parallel for schedule(static) if (Nx > 16384)
   for (int c = 0; c < Nx; c++) {
     double t = 0;
     for (int i = 0; i < r; i++) t += X[c + (size_t)Nx * i] * Sb[i];
@@ -1718,42 +1767,61 @@ static int collocation_si(const oracle_problem *p, int r, const double *X0,
   double *phi = (double *)malloc(sizeof(double) * Nx);
   double *phin = (double *)malloc(sizeof(double) * Nx);
   double *src = (double *)malloc(sizeof(double) * Nx);
-  double *Kc = (double *)malloc(sizeof(double) * r);
+  const int par = (size_t)Nx * r > 65536;
+#pragma omp parallel for schedule(static) if (par)
   for (int j = 0; j < r; j++)
     for (int c = 0; c < Nx; c++) {
       double t = 0;
       for (int k = 0; k < r; k++) t += L0[k + r * idx[j]] * X0[c + (size_t)Nx * k];
       Psi0[c + (size_t)Nx * j] = t;
     }
-  for (int c = 0; c < Nx; c++) {
-    for (int j = 0; j < r; j++) Kc[j] = Psi0[c + (size_t)Nx * j];
-    lu_solve_inplace(r, WLU, wpiv, Kc);
-    double t = 0;
-    for (int j = 0; j < r; j++) t += beta[j] * Kc[j];
-    phi[c] = t;
-    if (refl) reflected_inflow(p, r, idx, ox, oy, W, NOm, c, Kc, in_x, in_y);
+#pragma omp parallel if (par && !refl)
+  {
+    double *Kc = (double *)malloc(sizeof(double) * r);
+#pragma omp for schedule(static)
+    for (int c = 0; c < Nx; c++) {
+      for (int j = 0; j < r; j++) Kc[j] = Psi0[c + (size_t)Nx * j];
+      lu_solve_inplace(r, WLU, wpiv, Kc);
+      double t = 0;
+      for (int j = 0; j < r; j++) t += beta[j] * Kc[j];
+      phi[c] = t;
+      if (refl) reflected_inflow(p, r, idx, ox, oy, W, NOm, c, Kc, in_x, in_y);
+    }
+    free(Kc);
   }
   int cap = fixed > 0 ? fixed : max_iter;
   int iters = 0, converged = 0, dsa_iters = 0;
   while (iters < cap) {
-    for (int j = 0; j < r; j++) {
-      for (int c = 0; c < Nx; c++)
-        src[c] = sig_s[c] * phi[c] / (4.0 * ORACLE_PI) + q[c] +
-                 inv_cdt * Psi0[c + (size_t)Nx * j];
-      oracle_sweep_in(p, ox[idx[j]], oy[idx[j]], sig_t, src, in_x + (size_t)j * ny,
-                      in_y + (size_t)j * nx, Psi + (size_t)Nx * j);
+#pragma omp parallel if (par)
+    {
+      double *srcj = (double *)malloc(sizeof(double) * Nx);
+#pragma omp for schedule(dynamic, 1)
+      for (int j = 0; j < r; j++) {
+        for (int c = 0; c < Nx; c++)
+          srcj[c] = sig_s[c] * phi[c] / (4.0 * ORACLE_PI) + q[c] +
+                    inv_cdt * Psi0[c + (size_t)Nx * j];
+        oracle_sweep_in(p, ox[idx[j]], oy[idx[j]], sig_t, srcj, in_x + (size_t)j * ny,
+                        in_y + (size_t)j * nx, Psi + (size_t)Nx * j);
+      }
+      free(srcj);
     }
     iters++;
     double dmax = 0, pmax = 0;
-    for (int c = 0; c < Nx; c++) {
-      for (int j = 0; j < r; j++) Kc[j] = Psi[c + (size_t)Nx * j];
-      lu_solve_inplace(r, WLU, wpiv, Kc);
-      double t = 0;
-      for (int j = 0; j < r; j++) t += beta[j] * Kc[j];
-      phin[c] = t;
-      if (refl) reflected_inflow(p, r, idx, ox, oy, W, NOm, c, Kc, in_x, in_y);
-      if (fabs(t - phi[c]) > dmax) dmax = fabs(t - phi[c]);
-      if (fabs(t) > pmax) pmax = fabs(t);
+#pragma omp parallel if (par && !refl) reduction(max : dmax, pmax)
+    {
+      double *Kc = (double *)malloc(sizeof(double) * r);
+#pragma omp for schedule(static)
+      for (int c = 0; c < Nx; c++) {
+        for (int j = 0; j < r; j++) Kc[j] = Psi[c + (size_t)Nx * j];
+        lu_solve_inplace(r, WLU, wpiv, Kc);
+        double t = 0;
+        for (int j = 0; j < r; j++) t += beta[j] * Kc[j];
+        phin[c] = t;
+        if (refl) reflected_inflow(p, r, idx, ox, oy, W, NOm, c, Kc, in_x, in_y);
+        if (fabs(t - phi[c]) > dmax) dmax = fabs(t - phi[c]);
+        if (fabs(t) > pmax) pmax = fabs(t);
+      }
+      free(Kc);
     }
     if (p->dsa) dsa_iters += dsa_correct(p, sig_t, sig_s, phi, phin);
     memcpy(phi, phin, sizeof(double) * Nx);
@@ -1761,7 +1829,7 @@ static int collocation_si(const oracle_problem *p, int r, const double *X0,
   }
   *iters_out = iters;
   if (dsa_iters_out) *dsa_iters_out = dsa_iters;
-  free(Psi0); free(phi); free(phin); free(src); free(Kc); free(in_x); free(in_y);
+  free(Psi0); free(phi); free(phin); free(src); free(in_x); free(in_y);
   return (fixed <= 0 && !converged) ? -2 : 0;
 }
 
@@ -1983,6 +2051,7 @@ int oracle_dlr_step(const oracle_problem *p, int r, double *X, double *S,
   double *P = (double *)malloc(sizeof(double) * m * r);
   double *Lt0 = (double *)malloc(sizeof(double) * m * NOm);
   if (rc == 0) {
+#pragma omp parallel for collapse(2) schedule(dynamic, 1) if ((size_t)Nx * m > 65536)
     for (int jj = 0; jj < m; jj++)
       for (int i = 0; i < r; i++) {
         double t = 0;
@@ -2033,6 +2102,7 @@ int oracle_dlr_step(const oracle_problem *p, int r, double *X, double *S,
       double *Wr = (double *)malloc(sizeof(double) * NOm * r);
       double *absw = (double *)malloc(sizeof(double) * NOm);
       for (int j = 0; j < r; j++) {
+#pragma omp parallel for schedule(static) if (Nx > 16384)
         for (int c = 0; c < Nx; c++) {
           double t = 0;
           for (int i = 0; i < m; i++) t += Xn[c + (size_t)Nx * i] * U[i + m * j];

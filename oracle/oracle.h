@@ -73,6 +73,11 @@ typedef struct {
 } oracle_dlr_diag;
 
 /* Planck function B(T) = a c T^4 / (4 pi) (reading of the undefined B). */
+/* Threads of the OpenMP loops (n <= 0: all processors); results do not
+ * depend on the count.  Without OpenMP the oracle runs on one thread. */
+void oracle_set_threads(int n);
+int oracle_get_threads(void);
+
 double oracle_planck(double a_rad, double c, double T);
 
 /* sigma(T0) and rho c_v(T0) of cell c (reading R16). */

@@ -291,3 +291,26 @@ def test_augmented_step_rejects_2r_above_nx(orc):
     X, S, W = orc.initial_factors(p, T, 3)
     *_, res = orc.dlr_step(p, X, S, W, T, augment=1)
     assert res.rc == -1
+
+
+def test_threads_do_not_change_results(orc):
+    """The oracle's parallel loops (angles, cells, reflector columns, L-step
+    angles) keep every sum in its serial order: one thread and several give
+    bitwise the same step.  The mesh is above the size where the loops go
+    parallel."""
+    c = workloads.small_case(96, 90, 8, 4, 8, seed=21, T0=0.5)
+    p = oracle_problem(c)
+    out = []
+    try:
+        for th in (1, 4):
+            orc.set_threads(th)
+            T = c["T0"].reshape(-1).copy()
+            X, S, W = orc.initial_factors(p, T, 8)
+            for _ in range(2):
+                X, S, W, T, res = orc.dlr_step(p, X, S, W, T)
+                assert res.rc == 0
+            out.append((X, S, W, T))
+    finally:
+        orc.set_threads(0)
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
