@@ -1,18 +1,21 @@
 #!/usr/bin/env python3
 """Benchmark of the SN-like DLR time step (Algorithm 1 of Haut et al.) on GB300.
 
-One "step" is one implicit DLR time step of the checker256 workload (256 x
-256 cells, 8x8 thick/thin opacity blocks, rank 16, 16 x 32 angles, left-edge
-inflow at T = 1): angle selection, collocation sweeps with source iteration,
-QR of Psi, projections, L-step, QR + SVD of L, temperature update, all in the
+One "step" is one implicit DLR time step of the lognormal1024 workload (1024
+x 1024 cells, log-normal opacity smoothed over 16 cells, central hot square
+at T = 1, vacuum edges, rank 32, 32 x 64 angles), the largest single-GPU
+configuration: angle selection, collocation sweeps with source iteration, QR
+of Psi, projections, L-step, QR + SVD of L, temperature update, all in the
 library's kernels with the state resident in HBM.
 
 Printed JSON line (rank 0): cell-angle updates per second over the timed
 steps (whole job for N GPUs; each rank steps its own replica, weak scaling),
 the same measured through the public API with host buffers (e2e), DLR steps/s,
 the all-FP64 GPU path on the same steps, the roofline of the
-source-iteration kernel, the FP64 CPU oracle on a bounded sample, and SM
-clocks sampled during the timed region.  L2 is flushed between timed steps.
+source-iteration kernel, the FP64 CPU oracle on all host cores on a bounded
+sample (the first step) with the GPU paths' errors against it, and SM clocks
+sampled during the timed region.  L2 is flushed between timed steps (value
+and e2e alike).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -36,14 +39,14 @@ import numpy as np  # noqa: E402
 import workloads  # noqa: E402
 
 METRIC = "cell-angle updates/s"
-WORKLOAD = "checker256"
+WORKLOAD = "lognormal1024"
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="dlr", choices=["dlr", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -54,7 +57,9 @@ def parse():
     ap.add_argument("--dsa", action="store_true", help="served: every request with DSA")
     ap.add_argument("--dsa-max-iter", type=int, default=0, help="CG cap per DSA solve (0: the library's)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
-                    help="CPU work of the oracle sample")
+                    help="CPU work of the oracle sample (checker256 and smaller)")
+    ap.add_argument("--cpu-1thread", action="store_true",
+                    help="also time the oracle sample on one thread")
     ap.add_argument("--kernel", default=None, choices=["sweep"],
                     help="time one kernel alone instead of the DLR step")
     ap.add_argument("--workload", default=WORKLOAD,
@@ -73,7 +78,7 @@ def case_config(case, precision):
                         f"{case['n_polar']}x{case['n_azim']} angles, dt {case['dt']}",
             "nx": case["nx"], "ny": case["ny"], "rank": case["r"],
             "n_omega": case["n_polar"] * case["n_azim"], "precision": precision,
-            "l2": "flushed between timed steps (256 MiB write)",
+            "l2": "flushed between timed steps (256 MiB write), value and e2e alike",
             "inputs": "resident in HBM (value); host buffers each step (e2e)"}
 
 
@@ -138,15 +143,18 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- CPU
 
-def si_traffic(iters_per_launch):
+def si_traffic(workload, iters_per_launch):
     """DRAM bytes (read + write) per k_si launch from the committed ncu capture
     (profiles/k_si_traffic.json), scaled by this run's source iterations per
-    launch; None when the kernel sources changed since the capture."""
+    launch; None when the capture is of another workload or the kernel
+    sources changed since the capture."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "k_si_traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
+        if rec.get("workload") != workload:
+            return None
         h = hashlib.sha256()
         for src in rec["sources"]:
             with open(os.path.join(ROOT, src), "rb") as f:
@@ -157,12 +165,46 @@ def si_traffic(iters_per_launch):
     except (OSError, KeyError, ValueError):
         return None
 
-def oracle_rate(case, seconds: float, steps=None):
-    """FP64 CPU oracle, single thread: (updates/s, steps run, seconds)."""
+
+def _oracle_problem(case):
     import oracle
     p = oracle.Problem(case["nx"], case["ny"], case["n_polar"], case["n_azim"], case["sigma"],
                        case["rho_cv"], dt=case["dt"], c=case["c"], a_rad=case["a_rad"])
     p.set_edge_temperatures(case["T_edge"])
+    return p
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_first_step(case, si_iters: int, threads: int):
+    """The CPU baseline's sample: the FP64 oracle's first DLR step from the
+    initial state with the source iteration fixed at si_iters (the count the
+    GPU path took), on `threads` host threads.  Returns (updates/s, seconds,
+    state after the step)."""
+    import oracle
+    oracle.set_threads(threads)
+    p = _oracle_problem(case)
+    T = case["T0"].reshape(-1).copy()
+    X, S, W = oracle.initial_factors(p, T, case["r"])
+    t0 = time.perf_counter()
+    X, S, W, T, res = oracle.dlr_step(p, X, S, W, T, si_fixed_iters=si_iters)
+    el = time.perf_counter() - t0
+    if res.rc != 0:
+        raise RuntimeError(f"oracle step failed: rc {res.rc}")
+    return p.Nx * case["r"] * res.iters / el, el, (X, S, W, T, res.idx.copy())
+
+
+def oracle_rate(case, seconds: float, steps=None, threads: int = 1):
+    """FP64 CPU oracle: (updates/s, steps run, seconds) over whole steps from
+    the initial state until `seconds` (or `steps`) are reached."""
+    import oracle
+    oracle.set_threads(threads)
+    p = _oracle_problem(case)
     T = case["T0"].reshape(-1).copy()
     X, S, W = oracle.initial_factors(p, T, case["r"])
     upd, n, t0 = 0, 0, time.perf_counter()
@@ -176,24 +218,40 @@ def oracle_rate(case, seconds: float, steps=None):
     return upd / el, n, el
 
 
+def psi_sample(X, S, W, ncols: int = 64):
+    """psi = X S W^T at ncols evenly spaced angles (the full N x NOm array of
+    the large workloads does not fit comfortably in host memory)."""
+    cols = np.linspace(0, W.shape[0] - 1, ncols).astype(int)
+    return X @ (S @ W[cols].T)
+
+
+def rel_l2(a, b) -> float:
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+MIXED_SI_TOL = 1e-6  # the library's default stopping tolerance of the mixed path
+
+
 def run_reference(args):
-    """The oracle, as it stands, on the host cores (the base contract's
-    reference arm): W untimed steps, then K timed steps."""
+    """The oracle, as it stands, on all host cores (the base contract's
+    reference arm): W untimed steps, then K timed steps of the same workload
+    with the mixed path's stopping rule (max |d phi| <= 1e-6 max |phi|)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    case = workloads.checker256()
+    case = workloads.CONFIGS[args.workload]()
     import oracle
-    p = oracle.Problem(case["nx"], case["ny"], case["n_polar"], case["n_azim"], case["sigma"],
-                       case["rho_cv"], dt=case["dt"], c=case["c"], a_rad=case["a_rad"])
-    p.set_edge_temperatures(case["T_edge"])
+    cores = host_cores()
+    oracle.set_threads(cores)
+    p = _oracle_problem(case)
     T = case["T0"].reshape(-1).copy()
     X, S, W = oracle.initial_factors(p, T, case["r"])
+    kw = dict(si_tol=MIXED_SI_TOL, si_max_iter=case.get("si_max_iter", 1000))
     for _ in range(args.warmup):
-        X, S, W, T, res = oracle.dlr_step(p, X, S, W, T)
+        X, S, W, T, res = oracle.dlr_step(p, X, S, W, T, **kw)
     upd, t0 = 0, time.perf_counter()
     for _ in range(args.steps):
-        X, S, W, T, res = oracle.dlr_step(p, X, S, W, T)
+        X, S, W, T, res = oracle.dlr_step(p, X, S, W, T, **kw)
         upd += p.Nx * case["r"] * res.iters
     el = time.perf_counter() - t0
     v = upd / el
@@ -202,8 +260,10 @@ def run_reference(args):
             "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": case_config(case, "fp64 (CPU oracle)"),
-            "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} DLR steps after {args.warmup} warm-up steps"},
+            "cpu_baseline": {"value": v, "unit": METRIC, "cores": oracle.get_threads(), "kind": "oracle",
+                             "sample": f"{args.steps} whole DLR steps of {case['name']} after "
+                                       f"{args.warmup} warm-up steps, source iteration to "
+                                       f"{MIXED_SI_TOL:g}, {oracle.get_threads()} threads"},
             "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -239,6 +299,48 @@ def timed_steps(dlr, torch, solver, K, flush):
         b.record(st)
     st.synchronize()
     return [a.elapsed_time(b) for a, b in ev]
+
+
+def cpu_leg(args, dlr, case):
+    """The CPU baseline and the GPU paths' errors against the FP64 oracle.
+
+    Large workloads (beyond checker256): the sample is the first DLR step
+    from the initial state.  Fresh GPU solvers (the library's own initial
+    factors) take that step in mixed precision with the default stopping
+    rule, then in FP64 with the same source-iteration count; the oracle
+    takes it with that count on all host cores (timed: the baseline), and
+    both GPU results are compared with it (T and psi on 64 sampled angles).
+    Smaller workloads: whole oracle steps for about --cpu-seconds."""
+    cores = host_cores()
+    if case["nx"] * case["ny"] <= 256 * 256:
+        v, n, el = oracle_rate(case, args.cpu_seconds, threads=cores)
+        cpu = {"value": v, "unit": METRIC, "cores": cores, "kind": "oracle",
+               "sample": f"first {n} DLR steps of {case['name']} ({el:.1f} s, {cores} threads)"}
+        return cpu, None
+    gpu = {}
+    with dlr.Solver(dlr.problem_from_case(case, precision=dlr.DLR_MIXED)) as s:
+        s.step(1)
+        n1 = s.stats()["si_iters_last"]
+        X, S, W = s.factors()
+        gpu["mixed"] = (s.T(), psi_sample(X, S, W), s.selected())
+    with dlr.Solver(dlr.problem_from_case(case, precision=dlr.DLR_FP64, si_fixed_iters=n1)) as s:
+        s.step(1)
+        X, S, W = s.factors()
+        gpu["fp64"] = (s.T(), psi_sample(X, S, W), s.selected())
+    v, el, (Xo, So, Wo, To, idx) = oracle_first_step(case, n1, cores)
+    po = psi_sample(Xo, So, Wo)
+    cpu = {"value": v, "unit": METRIC, "cores": cores, "kind": "oracle",
+           "sample": f"first DLR step of {case['name']} from the initial state, source iteration "
+                     f"fixed at the GPU's {n1} iterations ({el:.1f} s on {cores} threads)"}
+    if args.cpu_1thread:
+        v1, el1, _ = oracle_first_step(case, n1, 1)
+        cpu["one_thread"] = {"value": v1, "seconds": el1}
+    vs = {"sample": "first step from the library's own initial factors vs the oracle's, same "
+                    f"source-iteration count ({n1}); psi = X S W^T at 64 sampled angles"}
+    for k, (T, ps, sel) in gpu.items():
+        vs[k] = {"rel_l2_T": rel_l2(T, To), "rel_l2_psi": rel_l2(ps, po),
+                 "same_angles": sorted(sel.tolist()) == sorted(idx.tolist())}
+    return cpu, vs
 
 
 def run_gpu(args):
@@ -292,7 +394,9 @@ def run_gpu(args):
     nonpos = solver.stats()["nonpositive_cells"]
     solver.close()
 
-    # ---- e2e: public API with host buffers, copies inside the timed region ----
+    # ---- e2e: public API with host buffers, copies inside the timed region,
+    # timed like value (CUDA events on the solver's stream, L2 flushed
+    # before each step) ----
     e2e = None
     if not args.no_e2e:
         s2 = dlr.Solver(dlr.problem_from_case(case, precision=dlr.DLR_MIXED, allow_nonpositive=1))
@@ -300,20 +404,27 @@ def run_gpu(args):
         hostT = torch.empty(s2.N, dtype=torch.float64, pin_memory=True)
         s2.T_into(hostT)
         e0 = s2.stats()
+        st2 = s2.stream
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
         barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            s2.set_T(hostT)          # H2D of the step's input temperature
+        for a, b in ev:
+            with torch.cuda.stream(st2):
+                flush.fill_(1)
+            a.record(st2)
+            s2.set_T(hostT)          # H2D of the step's input temperature (pinned host)
             s2.step(1)
             s2.T_into(hostT)         # D2H of the step's result (synchronises)
+            b.record(st2)
+        st2.synchronize()
         barrier()
-        el = time.perf_counter() - t0
+        el_ms = float(sum(a.elapsed_time(b) for a, b in ev))
         e1 = s2.stats()
         s2.close()
-        el_ms, eu = reduce_over_ranks(1e3 * el, e1["cell_angle_updates"] - e0["cell_angle_updates"], dist)
-        el = el_ms / 1e3
-        e2e = {"value": eu / el, "unit": METRIC, "h2d_bytes_per_step": 8 * case["nx"] * case["ny"],
-               "d2h_bytes_per_step": 8 * case["nx"] * case["ny"]}
+        el_ms, eu = reduce_over_ranks(el_ms, e1["cell_angle_updates"] - e0["cell_angle_updates"], dist)
+        e2e = {"value": eu / (el_ms / 1e3), "unit": METRIC, "h2d_bytes_per_step": 8 * case["nx"] * case["ny"],
+               "d2h_bytes_per_step": 8 * case["nx"] * case["ny"], "ms_per_step": el_ms / args.steps,
+               "timing": "CUDA events on the solver's stream around H2D + step + D2H, L2 flushed before each step"}
 
     # ---- the all-FP64 GPU path on the same steps ----
     fp64 = None
@@ -436,7 +547,7 @@ def run_gpu(args):
         return
 
     hbm, kind = peaks()
-    traffic = si_traffic(iters / max(si_launch, 1)) if args.workload == WORKLOAD else None
+    traffic = si_traffic(args.workload, iters / max(si_launch, 1))
     r = case["r"]
     bytes_per_update = 4.0 + 16.0 / r  # fixed-source read + amortised per-cell terms (FP32)
     per_launch_ms = si_ms / max(si_launch, 1)
@@ -445,12 +556,12 @@ def run_gpu(args):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": traffic, "kernel": "k_si<float>",
                 "peak_kind": kind, "bytes_per_update": bytes_per_update,
-                "avg_launch_ms": per_launch_ms}
-    cpu = None
+                "avg_launch_ms": per_launch_ms,
+                "traffic_note": "DRAM bytes per launch from profiles/k_si_traffic.json (ncu capture of the "
+                                "same kernel sources), scaled by this run's iterations per launch"}
+    cpu, vs_oracle = None, None
     if not args.no_cpu_baseline and world == 1:
-        v, n, el = oracle_rate(case, args.cpu_seconds)
-        cpu = {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
-               "sample": f"first {n} DLR steps of {WORKLOAD} ({el:.1f} s, single thread)"}
+        cpu, vs_oracle = cpu_leg(args, dlr, case)
     clocks = clk.summary(tw0, tw1) if clk else None
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -458,7 +569,7 @@ def run_gpu(args):
             "data": "synthetic", "config": case_config(case, "mixed: FP32 sweeps/projections, FP64 small LA and T"),
             "dlr_steps_per_s": world * args.steps / (total_ms / 1e3),
             "si_iters_per_step": iters / args.steps,
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fp64_gpu": fp64, "sn_gpu": sn, "sn_dsa_gpu": sn_dsa, "augmented_gpu": aug, "dsa_gpu": dsa,
+            "roofline": roofline, "cpu_baseline": cpu, "vs_oracle": vs_oracle, "e2e": e2e, "fp64_gpu": fp64, "sn_gpu": sn, "sn_dsa_gpu": sn_dsa, "augmented_gpu": aug, "dsa_gpu": dsa,
             "clocks": clocks, "gpu_launches": int(launches),
             "nonpositive_cells_at_end": int(nonpos), "sweep_plan": tuned}
     print(json.dumps(line))

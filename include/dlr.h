@@ -306,9 +306,11 @@ int dlr_sweep(int32_t nx, int32_t ny, double lx, double ly, int32_t n_dir,
  *
  * Arguments, layouts and results are those of dlr_sweep; inputs and outputs
  * stay the caller's.  n_dir may not exceed DLR_SWEEP_NOALLOC_MAX_DIRS
- * (DLR_EINVAL otherwise).  The first call on a device looks up the array's
- * device address for that device (the device current at the call); make
- * that first call before any stream capture.  All calls share the one array,
+ * (DLR_EINVAL otherwise), and the mesh-width limit of dlr_sweep applies
+ * (DLR_EINVAL).  Every call looks up the array's device address on the
+ * device current at the call (no cached address can go stale after a
+ * context teardown); the first lookup on a device may load the library's
+ * device code there, so make the first call before any stream capture.  All calls share the one array,
  * which keeps the last call's contents (the wait flag is cleared on every
  * call): calls that overlap on the GPU, from several streams or threads at
  * once, race on it and must be serialised by the caller.  Synchronous on

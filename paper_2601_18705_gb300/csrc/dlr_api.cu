@@ -1791,22 +1791,34 @@ int dlr_set_edge_inflow(dlr_handle *h, int32_t edge, double psi_iso) {
   return DLR_OK;
 }
 
+namespace dlr {
+// The standalone sweep keeps a band's top row in shared memory, so the mesh
+// width is bounded by the device's opt-in shared memory per block: DLR_OK,
+// or DLR_EINVAL (with its message) for a mesh too wide.  Checked before any
+// work is enqueued, so a refused call leaves no runtime error behind.
+int sweep_width_check(int nx, int ny, int precision) {
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(DLR_ECUDA, "no usable current device");
+  }
+  const int bands = (ny + 31) / 32;
+  const size_t need = precision == DLR_MIXED ? si_smem_bytes<float>(nx, bands, 0, 0, 0)
+                                             : si_smem_bytes<double>(nx, bands, 0, 0, 0);
+  if (optin > 0 && need > (size_t)optin)
+    return fail(DLR_EINVAL, "nx = %d too large for the sweep's shared memory", nx);
+  return DLR_OK;
+}
+}  // namespace dlr
+
 int dlr_sweep(int32_t nx, int32_t ny, double lx, double ly, int32_t n_dir, const double *dirs,
               const double *psi_edge, int32_t precision, const void *sigma_t, const void *src,
               void *psi, void *stream) {
   if (nx < 1 || ny < 1 || n_dir < 1 || !dirs || !psi_edge || !sigma_t || !src || !psi || !(lx > 0) ||
       !(ly > 0) || (precision != DLR_FP64 && precision != DLR_MIXED))
     return fail(DLR_EINVAL, "bad argument to dlr_sweep");
-  {
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const int bands = (ny + 31) / 32;
-    const size_t need = precision == DLR_MIXED ? si_smem_bytes<float>(nx, bands, 0, 0, 0)
-                                               : si_smem_bytes<double>(nx, bands, 0, 0, 0);
-    if (optin > 0 && need > (size_t)optin)
-      return fail(DLR_EINVAL, "nx = %d too large for the sweep's shared memory", nx);
-  }
+  if (int rc = sweep_width_check(nx, ny, precision)) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   double *d_dirs = nullptr, *d_edge = nullptr;
   int *d_abort = nullptr;

@@ -4,8 +4,6 @@
 // this file instead of stream-ordered allocations.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "../../include/dlr.h"
 #include "dlr_internal.cuh"
 
@@ -14,6 +12,7 @@ template <typename real>
 cudaError_t launch_sweep_dirs(int, int, double, double, int, const double *, const double *,
                               const real *, const real *, real *, int *, cudaStream_t);
 int record_error(int code, const char *msg);  // message for dlr_last_error()
+int sweep_width_check(int nx, int ny, int precision);  // DLR_EINVAL for a mesh too wide
 }
 
 namespace {
@@ -24,12 +23,6 @@ namespace {
 constexpr int kMaxDirs = DLR_SWEEP_NOALLOC_MAX_DIRS;
 constexpr int kScratchDoubles = 2 * kMaxDirs + 4 + 4;
 __device__ __align__(256) double g_sweep_scratch[kScratchDoubles];
-
-// Device address of the array, looked up once per device (the array's name
-// in host code is only a host-side stand-in, not a device address).
-constexpr int kMaxDevices = 64;
-double *g_addr[kMaxDevices] = {};
-std::mutex g_lock;
 
 int err(int code, const char *m) { return dlr::record_error(code, m); }
 
@@ -42,20 +35,23 @@ extern "C" int dlr_sweep_noalloc(int32_t nx, int32_t ny, double lx, double ly, i
       !(lx > 0) || !(ly > 0) || (precision != DLR_FP64 && precision != DLR_MIXED))
     return err(DLR_EINVAL, "bad argument to dlr_sweep_noalloc");
   if (n_dir > kMaxDirs) return err(DLR_EINVAL, "n_dir exceeds DLR_SWEEP_NOALLOC_MAX_DIRS");
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-    return err(DLR_ECUDA, "no usable current device");
-  double *base;
+  // the same mesh-width limit as dlr_sweep, checked before anything is enqueued
+  if (int rc = dlr::sweep_width_check(nx, ny, precision)) return rc;
+  // The device address of the array on the current device.  In host code
+  // the array's name is only a host-side stand-in, not a device address, so
+  // it is looked up on every call (cheap, allocates nothing, and never stale
+  // after a context teardown); the first lookup on a device may load the
+  // library's device code there, so make the first call before any stream
+  // capture.
+  void *addr = nullptr;
   {
-    std::lock_guard<std::mutex> g(g_lock);
-    if (!g_addr[dev]) {
-      void *p = nullptr;
-      cudaError_t e = cudaGetSymbolAddress(&p, g_sweep_scratch);
-      if (e != cudaSuccess || !p) return err(DLR_ECUDA, cudaGetErrorString(e));
-      g_addr[dev] = static_cast<double *>(p);
+    cudaError_t e = cudaGetSymbolAddress(&addr, g_sweep_scratch);
+    if (e != cudaSuccess || !addr) {
+      cudaGetLastError();
+      return err(DLR_ECUDA, cudaGetErrorString(e));
     }
-    base = g_addr[dev];
   }
+  double *base = static_cast<double *>(addr);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   double *d_dirs = base;
   double *d_edge = base + 2 * kMaxDirs;

@@ -1,0 +1,114 @@
+"""GPU parity at the shape of the lognormal1024 workload: rank 32 and
+32 x 64 = 2048 angles, so every kernel runs at rank class 32 and step 8
+takes its unfused path (more than 1024 angles), on meshes the oracle steps
+in seconds; one full-size lognormal1024 step against the oracle; and the
+library's own initial factors (dlr_create without set_factors) against the
+oracle's (reading R11), including the first step taken from them.
+Tolerances: relative L2 on T and psi = X S W^T of 1e-10 (FP64 path) and
+2e-5 (mixed path)."""
+import numpy as np
+import pytest
+
+import workloads
+from conftest import oracle_problem
+from gpu_util import rel_l2, run_pair
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-10, 1: 2e-5}
+
+
+@pytest.fixture(scope="module")
+def dlr():
+    import paper_2601_18705_gb300 as m
+    return m
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("shape", [(64, None), (72, 56), (96, None)])
+def test_rank32_2048_angles(orc, dlr, prec, shape):
+    case = workloads.lognormal_small(shape[0], ny=shape[1])
+    out, stats = run_pair(case, prec, 3, orc=orc, dlr=dlr)
+    for k, (eT, ep, oi, gi) in enumerate(out):
+        assert eT < TOL[prec] and ep < TOL[prec], (k, eT, ep)
+    assert stats["status"] == 0
+
+
+def _own_start(dlr, case, precision):
+    """Factors of a fresh solver built by dlr_create from the case alone."""
+    s = dlr.Solver(dlr.problem_from_case(case, precision=precision))
+    return s, s.factors()
+
+
+def _check_initial(orc, case, X, S, W):
+    p = oracle_problem(case)
+    T = case["T0"].reshape(-1).copy()
+    Xo, So, Wo = orc.initial_factors(p, T, case["r"])
+    # the same initial state psi0 = B(T0) (isotropic)
+    assert rel_l2(X @ S @ W.T, Xo @ So @ Wo.T) < 1e-12
+    # the same angular span: W^T diag(w) W_o is orthogonal
+    _, _, _, w = orc.quadrature(case["n_polar"], case["n_azim"])
+    sv = np.linalg.svd(W.T @ (w[:, None] * Wo), compute_uv=False)
+    np.testing.assert_allclose(sv, 1.0, atol=1e-10)
+    return p, T, (Xo, So, Wo)
+
+
+@pytest.mark.parametrize("make", [lambda: workloads.lognormal_small(64),
+                                  lambda: workloads.lognormal_small(72, ny=56),
+                                  workloads.lattice32,
+                                  lambda: workloads.small_case(33, 70, 12, 8, 16, seed=5, T0=0.35)])
+def test_initial_factors_and_first_step(orc, dlr, make):
+    """W0's span decides the angle choice, so a difference there would change
+    every later step; X0's columns past the first never enter step 1 (S0 has
+    one nonzero entry)."""
+    case = make()
+    s, (X, S, W) = _own_start(dlr, case, 0)
+    with s:
+        p, T, (Xo, So, Wo) = _check_initial(orc, case, X, S, W)
+        for _ in range(2):
+            Xo, So, Wo, T, res = orc.dlr_step(p, Xo, So, Wo, T)
+            assert res.rc == 0
+            s.step(1)
+            assert sorted(s.selected().tolist()) == sorted(res.idx.tolist())
+            Xg, Sg, Wg = s.factors()
+            assert rel_l2(s.T(), T) < 1e-10
+            assert rel_l2(Xg @ Sg @ Wg.T, Xo @ So @ Wo.T) < 1e-10
+
+
+@pytest.fixture(scope="module")
+def lognormal1024_oracle(orc):
+    """One oracle step of lognormal1024 from its initial factors, with the
+    source iteration fixed at 12 iterations (the thick hot cells converge
+    slowly; both sides run the same iterations)."""
+    case = workloads.lognormal1024()
+    p = oracle_problem(case)
+    T = case["T0"].reshape(-1).copy()
+    X, S, W = orc.initial_factors(p, T, case["r"])
+    start = (X.copy(), S.copy(), W.copy())
+    X, S, W, T, res = orc.dlr_step(p, X, S, W, T, si_fixed_iters=12)
+    assert res.rc == 0
+    return case, start, (X, S, W, T, res.idx.copy())
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_lognormal1024_one_step_vs_oracle(dlr, lognormal1024_oracle, prec):
+    """Full size (1024^2 cells, rank 32, 2048 angles).  The FP64 run starts
+    from the oracle's factors; the mixed run from the library's own, whose
+    initial state is compared first."""
+    case, start, (Xo, So, Wo, To, idx) = lognormal1024_oracle
+    spec = dlr.problem_from_case(case, precision=prec, si_fixed_iters=12)
+    with dlr.Solver(spec) as s:
+        if prec == 0:
+            s.set_factors(*start)
+        else:
+            X, S, W = s.factors()
+            assert rel_l2(X @ S @ W.T[:, :64], start[0] @ start[1] @ start[2].T[:, :64]) < 1e-12
+        s.step(1)
+        assert sorted(s.selected().tolist()) == sorted(idx.tolist())
+        Tg = s.T()
+        Xg, Sg, Wg = s.factors()
+    assert rel_l2(Tg, To) < TOL[prec]
+    # psi = X S W^T compared on a sample of 64 angles (the full N x 2048
+    # array is 17 GB): the relative L2 error over those columns
+    cols = np.linspace(0, Wo.shape[0] - 1, 64).astype(int)
+    assert rel_l2(Xg @ (Sg @ Wg[cols].T), Xo @ (So @ Wo[cols].T)) < TOL[prec]

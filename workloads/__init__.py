@@ -152,6 +152,26 @@ def lognormal1024():
     return c
 
 
+def lognormal_small(side: int = 64, seed: int = 2, r: int = 32, n_polar: int = 32,
+                    n_azim: int = 64, ny: int = None):
+    """lognormal1024's shape at a mesh the oracle steps in seconds: the same
+    opacity law (smoothing window scaled with the side, at least 2 cells),
+    a central hot square of 1/8 of the side at T = 1, vacuum edges, rank 32
+    and 32 x 64 angles by default; ny != side gives a ragged mesh (the field
+    is cut from a side x side draw)."""
+    ny = side if ny is None else ny
+    big = max(side, ny)
+    sig = lognormal_sigma(big, seed, width=max(2, big // 64))[:ny, :side]
+    T0 = np.full((ny, side), 0.01)
+    hx, hy = max(1, side // 8), max(1, ny // 8)
+    T0[ny // 2 - hy // 2:ny // 2 - hy // 2 + hy, side // 2 - hx // 2:side // 2 - hx // 2 + hx] = 1.0
+    c = _case(f"lognormal{side}x{ny}", side, sig, r, n_polar, n_azim, 1, VACUUM, T0=T0,
+              precision="mixed")
+    c.update(ny=ny, rho_cv=np.ones((ny, side)))
+    c["si_max_iter"] = 20000
+    return c
+
+
 ANGLE_SETS = [(8, 16), (8, 32), (16, 32), (16, 64)]
 
 
