@@ -554,7 +554,7 @@ def run_gpu(args):
     per_launch_updates = updates / max(si_launch, 1)
     achieved = per_launch_updates * bytes_per_update / (per_launch_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": traffic, "kernel": "k_si<float>",
+                "frac": achieved / hbm, "traffic": traffic, "kernel": "k_si_grp",
                 "peak_kind": kind, "bytes_per_update": bytes_per_update,
                 "avg_launch_ms": per_launch_ms,
                 "traffic_note": "DRAM bytes per launch from profiles/k_si_traffic.json (ncu capture of the "

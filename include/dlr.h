@@ -138,6 +138,17 @@ typedef struct dlr_problem {
                             source iteration.  DLR_METHOD_SN only; a
                             reflective left or right edge needs n_azim even
                             (the quadrature's mirror map) */
+  int32_t sweep_mode;    /* source-iteration kernel of mixed-precision DLR
+                            steps (Algorithm 1 step 4): 0 = grouped -- each
+                            warp sweeps 2 chosen angles of one quadrant at
+                            once, the scalar flux is summed from per-group
+                            partials, and psi is written once, by a last
+                            sweep after the iteration stops (used when the
+                            problem has no DSA, no reflective edge and no
+                            augmented step, and for a batch only when all
+                            its instances qualify); 1 = one angle per warp
+                            (the kernel of every other case).  Both give the
+                            same step to FP32 rounding */
 } dlr_problem;
 
 /* Device memory and stream supplied by the caller (e.g. PyTorch). */

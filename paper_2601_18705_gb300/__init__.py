@@ -57,6 +57,7 @@ class ProblemSpec:
     dsa_tol: float = 0.0     # CG stop ||r|| <= dsa_tol ||b|| (0: 0.1)
     dsa_max_iter: int = 0    # CG cap per solve (0: 3)
     reflect: tuple = (0, 0, 0, 0)  # reflective edges L, R, B, T (full-rank SN only)
+    sweep_mode: int = 0      # mixed DLR source iteration: 0 grouped angles, 1 one angle per warp
 
     def cstruct(self):
         keep = [_f64(self.sigma), _f64(self.rho_cv), _f64(self.T0)]
@@ -80,6 +81,7 @@ class ProblemSpec:
         p.dsa, p.dsa_tol, p.dsa_max_iter = int(self.dsa), float(self.dsa_tol), int(self.dsa_max_iter)
         for e in range(4):
             p.reflect[e] = int(self.reflect[e])
+        p.sweep_mode = int(self.sweep_mode)
         return p, keep
 
 

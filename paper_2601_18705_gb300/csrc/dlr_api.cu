@@ -29,6 +29,11 @@ template <typename real> cudaError_t launch_si(const Inst *, const SiCtl &, int,
 template <typename real> int si_max_grid(int, int, int, int, int);
 int si_sweep_warps(bool mixed);
 int si_sweep_lag(bool mixed);
+cudaError_t launch_si_grp(const Inst *, const SiCtl &, int grid, int stages, cudaStream_t);
+int si_grp_stages(int nx_max, int bands_max, int n_inst);
+int si_grp_max_grid(int nx_max, int bands_max, int n_inst, int stages);
+int si_grp_warps();
+int si_grp_lag();
 template <typename real> size_t si_smem_bytes(int, int, int, int, int);
 template <typename real> cudaError_t launch_sn_init(void *, const double *, int, int, double, double, cudaStream_t);
 template <typename real> cudaError_t launch_sn_prep(const Inst *, int, int, cudaStream_t);
@@ -36,7 +41,7 @@ template <typename real> cudaError_t launch_sn_tupdate(const Inst *, int, int, c
 template <typename real>
 cudaError_t launch_sweep_dirs(int, int, double, double, int, const double *, const double *,
                               const real *, const real *, real *, int *, cudaStream_t);
-template <typename real> cudaError_t launch_coeff_recon(const Inst *, int, int, int, cudaStream_t);
+template <typename real> cudaError_t launch_coeff_recon(const Inst *, int, int, int, int, cudaStream_t);
 template <typename real> cudaError_t launch_tsgram(const GramJob *, int, int, int, cudaStream_t);
 template <typename real> cudaError_t launch_fill(const FillJob *, int, int, cudaStream_t);
 template <typename rin, typename rout>
@@ -174,6 +179,8 @@ struct Batch {
   Inst *d_insts2 = nullptr;   // the instances of steps 5-10 (rank 2r when augmented)
   int sel_slice_max = 1;      // most angles one CTA of the selection cluster owns
   bool lside_fused = false;   // step 8 by the one-cluster kernel (pivoted-QR choice, K <= 1024)
+  bool grp = false;           // every instance takes the grouped sweep (k_si_grp)
+  int grp_stages = 0;         // shared-memory stages per warp of k_si_grp
   GramJob *g_psi1, *g_psire, *g_x, *g_x3, *g_l1, *g_lf, *g_w, *g_w3, *g_cross;
   FillJob *f_psi, *f_l;
   ApplyJob *a_psi, *a_x2, *a_x3, *a_l1, *a_w2, *a_w3, *a_wv, *a_cw, *a_cx;
@@ -382,6 +389,14 @@ static int reduce_cta_cap() {
   return cap;
 }
 
+// The grouped sweep (k_sweepg.cu) serves mixed-precision DLR steps without
+// DSA, reflective edges or the augmented step, unless sweep_mode asks for
+// the per-angle kernel.
+static bool grp_eligible(const dlr_problem *p) {
+  return p->precision == DLR_MIXED && p->method == DLR_METHOD_DLR && !p->dsa && !p->augment &&
+         !(p->reflect[0] || p->reflect[1] || p->reflect[2] || p->reflect[3]) && p->sweep_mode == 0;
+}
+
 static Sizes sizes_of(const dlr_problem *p, int sms) {
   Sizes s;
   s.N = p->nx * p->ny;
@@ -426,6 +441,11 @@ static Sizes sizes_of(const dlr_problem *p, int sms) {
   t += al(s.partial_doubles * 8);
   t += al(64) * 4 + al(sizeof(Inst));           // status, iters, conv, totals, inst
   if (p->dsa) t += kDsaArrays * al((size_t)s.N * s.rs) + al(64);  // DSA coefficients, CG vectors
+  if (grp_eligible(p)) {  // skewed inputs and partials of the grouped sweep
+    const size_t L = grp_lay(p->nx, p->ny) * 4;
+    const size_t ng = grp_count((int)r1);
+    t += al(ng * (kGA + 1) * L) + al(8 * L) + al(ng * L) + al(4 * L) + al(ng * kGrpRec * 4);
+  }
   s.total = t;
   return s;
 }
@@ -468,6 +488,7 @@ static int validate(const dlr_problem *p) {
   if (p->dsa != 0 && p->dsa != 1) return fail(DLR_EINVAL, "dsa must be 0 or 1");
   for (int e = 0; e < 4; ++e)
     if (p->reflect[e] != 0 && p->reflect[e] != 1) return fail(DLR_EINVAL, "reflect[%d] must be 0 or 1", e);
+  if (p->sweep_mode != 0 && p->sweep_mode != 1) return fail(DLR_EINVAL, "sweep_mode must be 0 or 1");
   if (p->reflect[0] || p->reflect[1] || p->reflect[2] || p->reflect[3]) {
     if (!sn) return fail(DLR_EINVAL, "reflective edges are built for DLR_METHOD_SN only");
     if ((p->reflect[0] || p->reflect[1]) && p->n_azim % 2)
@@ -543,6 +564,10 @@ static void fill_common(dlr_handle *h, const dlr_problem *problem) {
   for (int e = 0; e < 4; ++e) I.reflect[e] = problem->reflect[e];
   I.n_azim = problem->n_azim;
   I.refl_base = nullptr;
+  I.grp = 0;
+  I.grp_ng = 0;
+  I.grp_tab = nullptr;
+  I.sgk = I.spk = I.part = I.qsum = nullptr;
 }
 
 // Device arrays of the DSA solve (N each, working precision): 1/sigma_t,
@@ -765,6 +790,20 @@ int dlr_create(const dlr_problem *problem, const dlr_runtime *runtime, dlr_handl
   h->d_iters_total = (long long *)A(64);
   I.iters_total = (unsigned long long *)h->d_iters_total;
   alloc_dsa(h, A);
+  I.grp = grp_eligible(problem) ? 1 : 0;
+  I.grp_tab = nullptr;
+  I.sgk = I.spk = I.part = I.qsum = nullptr;
+  if (I.grp) {
+    I.grp_ng = grp_count(r);
+    I.nwin = grp_nwin(problem->nx);
+    I.nbands = (problem->ny + 31) / 32;
+    I.glay = grp_lay(problem->nx, problem->ny);
+    I.grp_tab = (int *)A((size_t)I.grp_ng * kGrpRec * 4);
+    I.sgk = (float *)A((size_t)I.grp_ng * (kGA + 1) * I.glay * 4);
+    I.spk = (float *)A(8 * I.glay * 4);
+    I.part = (float *)A((size_t)I.grp_ng * I.glay * 4);
+    I.qsum = (float *)A(4 * I.glay * 4);
+  }
   if (!ok) {
     dev_free_all(h);
     delete h;
@@ -798,6 +837,10 @@ int dlr_create(const dlr_problem *problem, const dlr_runtime *runtime, dlr_handl
   }
   chain(up(I.W0, W0.data(), (size_t)K * r * 8));
   chain(up(I.S0, S0.data(), (size_t)r * r * 8));
+  if (I.grp) {  // the padding of the skewed layouts stays zero
+    chain(cudaMemsetAsync(I.sgk, 0, (size_t)I.grp_ng * (kGA + 1) * I.glay * 4, h->st));
+    chain(cudaMemsetAsync(I.spk, 0, 8 * I.glay * 4, h->st));
+  }
   if (h->mixed) {
     std::vector<float> Xf(X0.begin(), X0.end());
     chain(up(I.X0, Xf.data(), Xf.size() * 4));
@@ -890,9 +933,14 @@ static double unit_steps(int nx, int p, int nw, int lag) {
 // keeps one unit per angle.  Units are ordered by modelled length, longest
 // first, and the units of one angle bottom-up, so that a unit's predecessor
 // is always claimed before it.  Returns the number of edge rows used.
-static int plan_units(dlr_handle *const *hs, int n, bool mixed, int ctas, double split,
+// Sweep items per instance: its r angles (per-angle kernel) or its groups
+// of angles (grouped kernel; a unit's `angle` is then the group index).
+static int sweep_items(const dlr_handle *h, bool grp) { return grp ? h->inst.grp_ng : h->r; }
+
+static int plan_units(dlr_handle *const *hs, int n, bool mixed, bool grp, int ctas, double split,
                       std::vector<SiUnit> &units) {
-  const int nw = si_sweep_warps(mixed), lag = si_sweep_lag(mixed);
+  const int nw = grp ? si_grp_warps() : si_sweep_warps(mixed);
+  const int lag = grp ? si_grp_lag() : si_sweep_lag(mixed);
   std::vector<int> nb(n), bpu(n);
   for (int i = 0; i < n; ++i) bpu[i] = nb[i] = (hs[i]->prob.ny + 31) / 32;
   while (split > 0) {
@@ -901,7 +949,7 @@ static int plan_units(dlr_handle *const *hs, int n, bool mixed, int ctas, double
     for (int i = 0; i < n; ++i) {
       const int g = (nb[i] + bpu[i] - 1) / bpu[i];
       const double t = unit_steps(hs[i]->prob.nx, bpu[i], nw, lag);
-      total += (double)hs[i]->r * g * t;
+      total += (double)sweep_items(hs[i], grp) * g * t;
       if (bpu[i] > nw && t > tmax) {
         tmax = t;
         imax = i;
@@ -920,7 +968,7 @@ static int plan_units(dlr_handle *const *hs, int n, bool mixed, int ctas, double
   int rows = 0;
   for (int i : order) {
     const int g = (nb[i] + bpu[i] - 1) / bpu[i];
-    for (int j = 0; j < hs[i]->r; ++j) {
+    for (int j = 0; j < sweep_items(hs[i], grp); ++j) {
       for (int q = 0; q < g; ++q) {
         SiUnit u;
         u.inst = i;
@@ -977,8 +1025,17 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   }
   const int gam_max = b->sn ? b->rmax : kMaxRank;  // scalar-flux weights of k_si
   int any_dsa = 0;
-  for (int i = 0; i < n; ++i) any_dsa |= hs[i]->inst.dsa ? 1 : 0;
-  const int gmax = b->mixed ? si_max_grid<float>(b->nx_max, b->bands_max, n, gam_max, any_dsa)
+  b->grp = true;
+  for (int i = 0; i < n; ++i) {
+    any_dsa |= hs[i]->inst.dsa ? 1 : 0;
+    b->grp = b->grp && hs[i]->inst.grp;
+  }
+  if (b->grp) {
+    b->grp_stages = si_grp_stages(b->nx_max, b->bands_max, n);
+    if (b->grp_stages == 0) b->grp = false;  // too wide for its shared memory: the per-angle kernel
+  }
+  const int gmax = b->grp ? si_grp_max_grid(b->nx_max, b->bands_max, n, b->grp_stages)
+                 : b->mixed ? si_max_grid<float>(b->nx_max, b->bands_max, n, gam_max, any_dsa)
                             : si_max_grid<double>(b->nx_max, b->bands_max, n, gam_max, any_dsa);
   if (gmax <= 0) {
     delete b;
@@ -987,24 +1044,26 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   b->si_grid = gmax;
   // capacity of the unit and edge tables: the finest split (one unit per
   // NW bands, or per band when an angle has fewer bands than warps)
-  const int nw = si_sweep_warps(b->mixed);
+  const int nw = b->grp ? si_grp_warps() : si_sweep_warps(b->mixed);
   int rows_cap = 0;
   for (int i = 0; i < n; ++i) {
     const int nb = (hs[i]->prob.ny + 31) / 32;
     const int g = (nb + std::min(nb, nw) - 1) / std::min(nb, nw);
-    b->units_cap += hs[i]->r * g;
-    rows_cap += hs[i]->r * (g - 1);
+    b->units_cap += sweep_items(hs[i], b->grp) * g;
+    rows_cap += sweep_items(hs[i], b->grp) * (g - 1);
   }
   b->split = tuned_split(hs, n);
   std::vector<SiUnit> units;
-  plan_units(hs, n, b->mixed, gmax, b->split, units);
+  plan_units(hs, n, b->mixed, b->grp, gmax, b->split, units);
   // one device block for the batch's tables
   size_t bytes = 0;
   auto sz = [](size_t s) { return (s + 255) & ~size_t(255); };
   bytes += 2 * sz(sizeof(Inst) * n);
   bytes += 9 * sz(sizeof(GramJob) * n) + 2 * sz(sizeof(FillJob) * n) + 9 * sz(sizeof(ApplyJob) * n) +
            8 * sz(sizeof(CholJob) * n) + sz(sizeof(ReduceJob) * n);
-  const int gedge_ld = (b->nx_max + 3) / 4 * 4 * (b->mixed ? 1 : 2);  // 64-bit words
+  // 64-bit words per edge row: one per column and value (two per FP64 value;
+  // kGA values per column in the grouped sweep)
+  const int gedge_ld = (b->nx_max + 3) / 4 * 4 * (b->grp ? kGA : b->mixed ? 1 : 2);
   bytes += sz(sizeof(SiUnit) * b->units_cap) + sz(64) * 4;
   // one row more than any plan uses: zeroed below and never written (tags
   // are nonzero), the row dlr_debug_lose_edge points a unit at
@@ -1252,7 +1311,7 @@ static int enqueue_pre(Batch *b) {
     return DLR_OK;
   }
   LK(launch_select(d, n, b->sel_slice_max, b->st));
-  LKM(launch_coeff_recon<real>(d, n, b->maxN, b->rmask_pre, b->st), b->rmask_pre);
+  LKM(launch_coeff_recon<real>(d, n, b->maxN, b->rmask_pre, b->grp ? 1 : 0, b->st), b->rmask_pre);
   LK(launch_si_prep(d, n, b->ctl, b->st));
   return DLR_OK;
 }
@@ -1351,6 +1410,13 @@ static cudaEvent_t pool_event(dlr_handle *h) {
   return e;
 }
 
+// The source-iteration launch of the batch with control block c.
+static cudaError_t launch_si_batch(const Batch *b, const SiCtl &c) {
+  if (b->grp) return launch_si_grp(b->d_insts, c, b->si_grid, b->grp_stages, b->st);
+  return b->mixed ? launch_si<float>(b->d_insts, c, b->si_grid, b->st)
+                  : launch_si<double>(b->d_insts, c, b->si_grid, b->st);
+}
+
 static int run_steps(Batch *b, int nsteps) {
   int rc = refresh_batch(b);
   if (rc) return rc;
@@ -1370,8 +1436,7 @@ static int run_steps(Batch *b, int nsteps) {
     }
     CK(cudaGraphLaunch(b->pre, b->st));
     if (timing) CK(cudaEventRecord(ev[1], b->st));
-    CK(b->mixed ? launch_si<float>(b->d_insts, b->ctl, b->si_grid, b->st)
-                : launch_si<double>(b->d_insts, b->ctl, b->si_grid, b->st));
+    CK(launch_si_batch(b, b->ctl));
     if (timing) CK(cudaEventRecord(ev[2], b->st));
     CK(cudaGraphLaunch(b->post, b->st));
     if (timing) {
@@ -1467,7 +1532,7 @@ int dlr_step_batch(dlr_handle *const *hs, int32_t n, int32_t nsteps) {
 // Re-plans the batch's sweep units with splitting threshold `split`.
 static int set_plan(Batch *b, double split) {
   std::vector<SiUnit> units;
-  plan_units(b->hs.data(), b->n, b->mixed, b->si_grid, split, units);
+  plan_units(b->hs.data(), b->n, b->mixed, b->grp, b->si_grid, split, units);
   if ((int)units.size() > b->units_cap) return fail(DLR_EINVAL, "unit plan exceeds its table");
   CK(cudaMemcpyAsync(b->d_units, units.data(), sizeof(SiUnit) * units.size(), cudaMemcpyHostToDevice,
                      b->st));
@@ -1487,7 +1552,7 @@ int dlr_debug_lose_edge(dlr_handle *const *hs, int32_t n) {
   Batch *b = nullptr;
   if ((rc = get_batch(hs, n, &b))) return rc;
   std::vector<SiUnit> units;
-  plan_units(b->hs.data(), b->n, b->mixed, b->si_grid, 1e-9, units);
+  plan_units(b->hs.data(), b->n, b->mixed, b->grp, b->si_grid, 1e-9, units);
   auto it = std::find_if(units.begin(), units.end(), [](const SiUnit &u) { return u.in_row >= 0; });
   if (it == units.end()) return fail(DLR_EINVAL, "no angle spans more than one sweep unit");
   if ((int)units.size() > b->units_cap) return fail(DLR_EINVAL, "unit plan exceeds its table");
@@ -1531,7 +1596,7 @@ int dlr_autotune(dlr_handle *const *hs, int32_t n, int32_t iters, int32_t reps, 
   const double cand[] = {0.0, 2.0, 1.0, 0.5};
   const int nc = (int)(sizeof(cand) / sizeof(cand[0]));
   std::vector<std::vector<SiUnit>> plans(nc);
-  for (int c = 0; c < nc; ++c) plan_units(b->hs.data(), n, b->mixed, b->si_grid, cand[c], plans[c]);
+  for (int c = 0; c < nc; ++c) plan_units(b->hs.data(), n, b->mixed, b->grp, b->si_grid, cand[c], plans[c]);
   auto same = [](const std::vector<SiUnit> &x, const std::vector<SiUnit> &y) {
     return x.size() == y.size() && std::memcmp(x.data(), y.data(), x.size() * sizeof(SiUnit)) == 0;
   };
@@ -1558,8 +1623,7 @@ int dlr_autotune(dlr_handle *const *hs, int32_t n, int32_t iters, int32_t reps, 
       if (rep == 1) e = cudaEventRecord(e0, b->st);
       if (e == cudaSuccess) e = launch_si_prep(b->d_insts, n, c, b->st);
       if (e == cudaSuccess)
-        e = b->mixed ? launch_si<float>(b->d_insts, c, b->si_grid, b->st)
-                     : launch_si<double>(b->d_insts, c, b->si_grid, b->st);
+        e = launch_si_batch(b, c);
     }
     if (e == cudaSuccess) e = cudaEventRecord(e1, b->st);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);

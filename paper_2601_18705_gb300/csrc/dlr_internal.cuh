@@ -137,7 +137,57 @@ struct Inst {
   int reflect[4];
   int n_azim;
   void *refl_base;
+  // grouped-angle sweep (mixed-precision DLR instances without DSA or
+  // reflective edges, grp = 1): the chosen angles are grouped by quadrant
+  // (kGA per group, table grp_tab of grp_ng records, ordered by quadrant),
+  // and the sweep's inputs and outputs live in the skewed band layout of
+  // grp_off (glay floats per layout, glay / 1024 blocks): sgk holds per
+  // group and block the kGA angles' fixed sources and sigma_t of the
+  // group's quadrant, (kGA + 1) x 1024 floats together (grp_sgk); spk
+  // sigma_s phi / 4 pi in the four quadrant layouts, two sets for the
+  // iteration parity; part per group the sum over its angles of
+  // gamma_j psi_j; qsum per quadrant the sum of its groups' part
+  int grp, grp_ng, nwin, nbands;
+  size_t glay;
+  int *grp_tab;
+  float *sgk, *spk, *part, *qsum;
 };
+
+// Angles per group of the grouped sweep, and the ints of one group record:
+// quadrant, number of angles, the angles' indices j.
+constexpr int kGA = 2;
+constexpr int kGrpRec = 2 + kGA;
+// Groups needed for r angles in any split over the four quadrants.
+__host__ __device__ inline int grp_count(int r) { return (r + 4 * (kGA - 1)) / kGA; }
+
+// Skewed band layout of the grouped sweep.  Quadrant quad = (Om_x < 0) +
+// 2 (Om_y < 0) mirrors the mesh so that its directions point to +u, +v
+// (u = x or nx-1-x, v = y or ny-1-y).  Rows are grouped in bands of 32
+// (lane i = v mod 32 of band b = v / 32); lane i reaches column u at
+// wavefront step t = u + i, and step t belongs to window k = t / 32.  One
+// (band, window) block holds 32 lanes x 32 steps, lane-major (a lane's 32
+// steps in one 128-byte row), the 4-step groups of a row permuted by
+// XOR with i mod 8 so that the lanes' 16-byte reads of one step group fall
+// in distinct banks.  Blocks are 4 KB and ordered (band, window); nwin =
+// (nx + 62) / 32 windows cover t = 0 .. nx + 30.  Positions outside the
+// mesh are padding.
+__host__ __device__ inline int grp_nwin(int nx) { return (nx + 62) >> 5; }
+__host__ __device__ inline size_t grp_lay(int nx, int ny) {
+  return (size_t)((ny + 31) >> 5) * grp_nwin(nx) * 1024;
+}
+__device__ __forceinline__ size_t grp_off(int quad, int nx, int ny, int nwin, int x, int y) {
+  const int u = (quad & 1) ? nx - 1 - x : x;
+  const int v = (quad & 2) ? ny - 1 - y : y;
+  const int i = v & 31, t = u + i;
+  const int s = t & 31;
+  return ((size_t)((v >> 5) * nwin + (t >> 5)) << 10) + (i << 5) + ((((s >> 2) ^ (i & 7)) << 2) | (s & 3));
+}
+__device__ __forceinline__ int quad_of(double ox, double oy) { return (ox < 0 ? 1 : 0) | (oy < 0 ? 2 : 0); }
+// Position in sgk of slot `slot` (0 .. kGA-1: the group's angles, kGA:
+// sigma_t) of group g at layout offset o (block o / 1024, entry o % 1024).
+__host__ __device__ inline size_t grp_sgk(size_t glay, int g, int slot, size_t o) {
+  return ((((size_t)g * (glay >> 10) + (o >> 10)) * (kGA + 1) + slot) << 10) + (o & 1023);
+}
 
 // Mirror image of quadrature angle k = p n_azim + a of the product
 // quadrature: axis 0 negates the x component (azimuth a -> n_azim/2 - 1 - a,

@@ -26,22 +26,63 @@ constexpr int kTB = 256;      // threads per block of the reduction kernels
 // ------------------------------------------------------------------
 // step 1 + step 3
 // ------------------------------------------------------------------
+// grp_mode = 1 (a batch of grouped-sweep instances, mixed precision): the
+// fixed sources, sigma_t and the starting sigma_s phi / 4 pi go to the
+// skewed layouts of the grouped sweep (each angle in its quadrant's layout;
+// sigma_t and sigma_s phi / 4 pi in all four), and block 0 of each instance
+// writes the group table (the chosen angles by quadrant, then by index, kGA
+// per group); otherwise they go to the plain cell-major arrays.
 template <typename real, int RB>
-__global__ void __launch_bounds__(256) k_coeff_recon(const Inst *__restrict__ insts) {
+__global__ void __launch_bounds__(256) k_coeff_recon(const Inst *__restrict__ insts, int grp_mode) {
   pdl_wait();
   pdl_trigger();
   const Inst &I = insts[blockIdx.y];
   if (rank_class(I.r) != RB) return;
   __shared__ real C0s[RB * RB];
   __shared__ real gam[RB];
+  __shared__ int quadj[RB], grpj[RB], slotj[RB];
+  __shared__ int grpq[RB + 4], ngrp;
   const int r = I.r;
   const double *C0 = I.small + I.lay.C0;
   for (int e = threadIdx.x; e < RB * RB; e += blockDim.x) {
     const int k = e % RB, j = e / RB;  // C0s[j*RB + k] = C0[k, j]
     C0s[e] = (k < r && j < r) ? real(C0[k + r * j]) : real(0);
   }
-  for (int e = threadIdx.x; e < RB; e += blockDim.x)
+  for (int e = threadIdx.x; e < RB; e += blockDim.x) {
     gam[e] = e < r ? real(I.small[I.lay.gamma + e]) : real(0);
+    if (grp_mode && e < r) quadj[e] = quad_of(I.ox[I.idx[e]], I.oy[I.idx[e]]);
+  }
+  __syncthreads();
+  if (grp_mode && threadIdx.x == 0) {
+    // groups: the chosen angles by quadrant, then by index, kGA per group
+    // (every block forms the same table; block 0 stores it)
+    const bool store = blockIdx.x == 0;
+    int g = 0;
+    for (int q = 0; q < 4; ++q) {
+      int na = 0;
+      for (int j = 0; j < r; ++j) {
+        if (quadj[j] != q) continue;
+        grpj[j] = g;
+        slotj[j] = na;
+        grpq[g] = q;
+        if (store) {
+          int *rec = I.grp_tab + g * kGrpRec;
+          rec[0] = q;
+          rec[2 + na] = j;
+          rec[1] = na + 1;
+        }
+        if (++na == kGA) { ++g; na = 0; }
+      }
+      if (na) ++g;
+    }
+    ngrp = g;
+    for (; store && g < I.grp_ng; ++g) {
+      int *rec = I.grp_tab + g * kGrpRec;
+      rec[0] = 0;
+      rec[1] = 0;
+      for (int a = 0; a < kGA; ++a) rec[2 + a] = 0;
+    }
+  }
   __syncthreads();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= I.N) return;
@@ -50,8 +91,19 @@ __global__ void __launch_bounds__(256) k_coeff_recon(const Inst *__restrict__ in
   const double q = cf.q;
   I.B0[c] = cf.B;
   I.D[c] = cf.D;
-  as<real>(I.sig_t)[c] = real(cf.sig + I.inv_cdt);
+  const real sig_t = real(cf.sig + I.inv_cdt);
+  as<real>(I.sig_t)[c] = sig_t;
   const real ss4 = real(cf.ss / (4.0 * kPi));
+  // skewed positions of this cell in the four quadrant layouts (grp_mode)
+  size_t go[4] = {0, 0, 0, 0};
+  if (grp_mode) {
+    const int y = c / I.nx, xx = c - y * I.nx;
+#pragma unroll
+    for (int qd = 0; qd < 4; ++qd) go[qd] = grp_off(qd, I.nx, I.ny, I.nwin, xx, y);
+    // sigma_t beside each group's fixed sources, in the group's quadrant layout
+    for (int g = 0; g < ngrp; ++g)
+      I.sgk[grp_sgk(I.glay, g, kGA, go[grpq[g]])] = float(sig_t);
+  }
   as<real>(I.ss4)[c] = ss4;
   as<real>(I.q)[c] = real(q);
   // psi0 at the chosen angles: Psi0[c, j] = sum_k X0[c, k] C0[k, j]
@@ -66,7 +118,8 @@ __global__ void __launch_bounds__(256) k_coeff_recon(const Inst *__restrict__ in
     real p = real(0);
 #pragma unroll
     for (int k = 0; k < RB; ++k) p += x[k] * C0s[j * RB + k];
-    s0[(size_t)I.N * j + c] = qr + icdt * p;
+    if (grp_mode) I.sgk[grp_sgk(I.glay, grpj[j], slotj[j], go[quadj[j]])] = float(qr + icdt * p);
+    else s0[(size_t)I.N * j + c] = qr + icdt * p;
     phi += gam[j] * p;
   }
   if (I.aug_x0) {  // augmented step: X0 beside Psi as the input of step 5
@@ -76,7 +129,12 @@ __global__ void __launch_bounds__(256) k_coeff_recon(const Inst *__restrict__ in
       if (k < r) xa[(size_t)I.N * k + c] = x[k];
   }
   as<real>(I.phi0)[c] = phi;
-  as<real>(I.sphi)[c] = ss4 * phi;
+  if (grp_mode) {
+#pragma unroll
+    for (int qd = 0; qd < 4; ++qd) I.spk[(size_t)qd * I.glay + go[qd]] = float(ss4 * phi);
+  } else {
+    as<real>(I.sphi)[c] = ss4 * phi;
+  }
 }
 
 // ------------------------------------------------------------------
@@ -643,9 +701,9 @@ __global__ void __launch_bounds__(128) k_tupdate(const Inst *__restrict__ insts)
   } while (0)
 
 template <typename real>
-cudaError_t launch_coeff_recon(const Inst *d, int n, int maxN, int rmask, cudaStream_t st) {
+cudaError_t launch_coeff_recon(const Inst *d, int n, int maxN, int rmask, int grp_mode, cudaStream_t st) {
   dim3 g((maxN + 255) / 256, n);
-#define L_(RB) (e = launch_pdl(k_coeff_recon<real, RB>, g, dim3(256), 0, st, d))
+#define L_(RB) (e = launch_pdl(k_coeff_recon<real, RB>, g, dim3(256), 0, st, d, grp_mode))
   cudaError_t e = cudaSuccess;
   DLR_RB_DISPATCH(rmask, L_);
 #undef L_
@@ -737,8 +795,8 @@ cudaError_t launch_tupdate(const Inst *d, int n, int maxN, int rmask, cudaStream
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-template cudaError_t launch_coeff_recon<float>(const Inst *, int, int, int, cudaStream_t);
-template cudaError_t launch_coeff_recon<double>(const Inst *, int, int, int, cudaStream_t);
+template cudaError_t launch_coeff_recon<float>(const Inst *, int, int, int, int, cudaStream_t);
+template cudaError_t launch_coeff_recon<double>(const Inst *, int, int, int, int, cudaStream_t);
 template cudaError_t launch_tsgram<float>(const GramJob *, int, int, int, cudaStream_t);
 template cudaError_t launch_tsgram<double>(const GramJob *, int, int, int, cudaStream_t);
 template cudaError_t launch_fill<float>(const FillJob *, int, int, cudaStream_t);
