@@ -29,7 +29,10 @@ template <typename real> cudaError_t launch_si(const Inst *, const SiCtl &, int,
 template <typename real> int si_max_grid(int, int, int, int, int);
 int si_sweep_warps(bool mixed);
 int si_sweep_lag(bool mixed);
-cudaError_t launch_si_grp(const Inst *, const SiCtl &, int grid, int stages, cudaStream_t);
+cudaError_t launch_grp_prep(const Inst *, int, const SiCtl &, GrpSi *, cudaStream_t);
+cudaError_t launch_grp_iteration(const Inst *, int, const SiCtl &, GrpSi *, int grid, int stages,
+                                 cudaGraphConditionalHandle loop, cudaStream_t);
+cudaError_t launch_grp_final(const Inst *, const SiCtl &, GrpSi *, int grid, int stages, cudaStream_t);
 int si_grp_stages(int nx_max, int bands_max, int n_inst);
 int si_grp_max_grid(int nx_max, int bands_max, int n_inst, int stages);
 int si_grp_warps();
@@ -179,8 +182,10 @@ struct Batch {
   Inst *d_insts2 = nullptr;   // the instances of steps 5-10 (rank 2r when augmented)
   int sel_slice_max = 1;      // most angles one CTA of the selection cluster owns
   bool lside_fused = false;   // step 8 by the one-cluster kernel (pivoted-QR choice, K <= 1024)
-  bool grp = false;           // every instance takes the grouped sweep (k_si_grp)
-  int grp_stages = 0;         // shared-memory stages per warp of k_si_grp
+  bool grp = false;           // every instance takes the grouped sweep (k_sweepg.cu)
+  int grp_stages = 0;         // shared-memory stages per warp of the grouped sweep
+  GrpSi *gs = nullptr;        // its loop state (device)
+  cudaGraphExec_t si = nullptr;  // its source iteration: a while node and the last sweep
   GramJob *g_psi1, *g_psire, *g_x, *g_x3, *g_l1, *g_lf, *g_w, *g_w3, *g_cross;
   FillJob *f_psi, *f_l;
   ApplyJob *a_psi, *a_x2, *a_x3, *a_l1, *a_w2, *a_w3, *a_wv, *a_cw, *a_cx;
@@ -903,6 +908,7 @@ static void destroy_batch(Batch *b) {
   if (!b) return;
   if (b->pre) cudaGraphExecDestroy(b->pre);
   if (b->post) cudaGraphExecDestroy(b->post);
+  if (b->si) cudaGraphExecDestroy(b->si);
   if (b->d_mem) cudaFree(b->d_mem);
   delete b;
 }
@@ -1070,6 +1076,7 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   bytes += sz(sizeof(unsigned long long) * gedge_ld * (rows_cap + 1));
   const size_t dsa_part = any_dsa ? (size_t)n * kDsaSlots * gmax : 0;  // per-CTA CG partials
   bytes += sz(sizeof(double) * std::max<size_t>(1, dsa_part));
+  bytes += sz(sizeof(GrpSi)) + 2 * sz(sizeof(int) * n);  // loop state of the grouped sweep
   if (cudaMalloc(&b->d_mem, bytes) != cudaSuccess) {
     delete b;
     return fail(DLR_ENOMEM, "batch table allocation failed");
@@ -1127,6 +1134,19 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   b->ctl.force_iters = 0;
   b->ctl.units = b->d_units;
   b->ctl.n_units = (int)units.size();
+  b->gs = carve<GrpSi>(cur, 1);
+  {
+    GrpSi g{};
+    g.n_units = b->ctl.n_units;
+    g.active = carve<int>(cur, n);
+    g.par_of = carve<int>(cur, n);
+    if (cudaMemcpyAsync(b->gs, &g, sizeof g, cudaMemcpyHostToDevice, hs[0]->st) != cudaSuccess ||
+        cudaStreamSynchronize(hs[0]->st) != cudaSuccess) {
+      cudaFree(b->d_mem);
+      delete b;
+      return fail(DLR_ECUDA, "batch table initialisation failed");
+    }
+  }
   b->ctl.n_inst = n;
   b->ctl.nx_max = b->nx_max;
   b->ctl.bands_max = b->bands_max;
@@ -1312,7 +1332,8 @@ static int enqueue_pre(Batch *b) {
   }
   LK(launch_select(d, n, b->sel_slice_max, b->st));
   LKM(launch_coeff_recon<real>(d, n, b->maxN, b->rmask_pre, b->grp ? 1 : 0, b->st), b->rmask_pre);
-  LK(launch_si_prep(d, n, b->ctl, b->st));
+  if (b->grp) LK(launch_grp_prep(d, n, b->ctl, b->gs, b->st));
+  else LK(launch_si_prep(d, n, b->ctl, b->st));
   return DLR_OK;
 }
 
@@ -1410,9 +1431,61 @@ static cudaEvent_t pool_event(dlr_handle *h) {
   return e;
 }
 
-// The source-iteration launch of the batch with control block c.
+// The grouped source iteration as a graph: a while node whose body is one
+// iteration (sweeps, quadrant sums, scalar flux and decision; the decision
+// kernel ends the loop) and, after it, the last sweep that writes Psi.
+static int capture_si(Batch *b) {
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle loop;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&loop, g, 1, cudaGraphCondAssignDefault);
+  cudaGraphNode_t wn = nullptr;
+  if (e == cudaSuccess) {
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = loop;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(&wn, g, nullptr, nullptr, 0, &cp);
+    if (e == cudaSuccess) {
+      cudaGraph_t body = cp.conditional.phGraph_out[0];
+      e = cudaStreamBeginCaptureToGraph(b->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        cudaError_t e1 = launch_grp_iteration(b->d_insts, b->n, b->ctl, b->gs, b->si_grid, b->grp_stages,
+                                              loop, b->st);
+        e = cudaStreamEndCapture(b->st, &body);
+        if (e == cudaSuccess) e = e1;
+      }
+    }
+  }
+  if (e == cudaSuccess) {
+    e = cudaStreamBeginCaptureToGraph(b->st, g, &wn, nullptr, 1, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e1 = launch_grp_final(b->d_insts, b->ctl, b->gs, b->si_grid, b->grp_stages, b->st);
+      e = cudaStreamEndCapture(b->st, &g);
+      if (e == cudaSuccess) e = e1;
+    }
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->si, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(DLR_ECUDA, "source-iteration graph: %s", cudaGetErrorString(e));
+  }
+  return DLR_OK;
+}
+
+// The source-iteration launch of the batch with control block c (for the
+// grouped sweep: its graph, after the loop state's forced iteration count
+// is set to c.force_iters).
 static cudaError_t launch_si_batch(const Batch *b, const SiCtl &c) {
-  if (b->grp) return launch_si_grp(b->d_insts, c, b->si_grid, b->grp_stages, b->st);
+  if (b->grp) {
+    cudaError_t e = cudaMemcpyAsync(&b->gs->force_iters, &c.force_iters, sizeof(int), cudaMemcpyHostToDevice,
+                                    b->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&b->gs->n_units, &c.n_units, sizeof(int), cudaMemcpyHostToDevice,
+                                              b->st);
+    return e == cudaSuccess ? cudaGraphLaunch(b->si, b->st) : e;
+  }
   return b->mixed ? launch_si<float>(b->d_insts, c, b->si_grid, b->st)
                   : launch_si<double>(b->d_insts, c, b->si_grid, b->st);
 }
@@ -1424,7 +1497,8 @@ static int run_steps(Batch *b, int nsteps) {
     b->kcount = 0;
     if ((rc = capture(b, true, &b->pre))) return rc;
     if ((rc = capture(b, false, &b->post))) return rc;
-    b->kernels_per_step = b->kcount + 1;  // + source iteration
+    if (b->grp && (rc = capture_si(b))) return rc;
+    b->kernels_per_step = b->kcount + 1;  // + source iteration (the last sweep of the grouped one)
   }
   dlr_handle *h0 = b->hs[0];
   for (int s = 0; s < nsteps; ++s) {
@@ -1436,7 +1510,7 @@ static int run_steps(Batch *b, int nsteps) {
     }
     CK(cudaGraphLaunch(b->pre, b->st));
     if (timing) CK(cudaEventRecord(ev[1], b->st));
-    CK(launch_si_batch(b, b->ctl));
+    CK(b->grp ? cudaGraphLaunch(b->si, b->st) : launch_si_batch(b, b->ctl));
     if (timing) CK(cudaEventRecord(ev[2], b->st));
     CK(cudaGraphLaunch(b->post, b->st));
     if (timing) {
@@ -1536,8 +1610,11 @@ static int set_plan(Batch *b, double split) {
   if ((int)units.size() > b->units_cap) return fail(DLR_EINVAL, "unit plan exceeds its table");
   CK(cudaMemcpyAsync(b->d_units, units.data(), sizeof(SiUnit) * units.size(), cudaMemcpyHostToDevice,
                      b->st));
-  CK(cudaStreamSynchronize(b->st));  // the host vector dies here
   b->ctl.n_units = (int)units.size();
+  const int no_force = 0;  // timing runs of the autotuner leave a forced count behind
+  CK(cudaMemcpyAsync(&b->gs->n_units, &b->ctl.n_units, sizeof(int), cudaMemcpyHostToDevice, b->st));
+  CK(cudaMemcpyAsync(&b->gs->force_iters, &no_force, sizeof(int), cudaMemcpyHostToDevice, b->st));
+  CK(cudaStreamSynchronize(b->st));  // the host values die here
   b->split = split;
   return DLR_OK;
 }
@@ -1559,8 +1636,9 @@ int dlr_debug_lose_edge(dlr_handle *const *hs, int32_t n) {
   it->in_row = b->spare_row;
   CK(cudaMemcpyAsync(b->d_units, units.data(), sizeof(SiUnit) * units.size(), cudaMemcpyHostToDevice,
                      b->st));
-  CK(cudaStreamSynchronize(b->st));
   b->ctl.n_units = (int)units.size();
+  CK(cudaMemcpyAsync(&b->gs->n_units, &b->ctl.n_units, sizeof(int), cudaMemcpyHostToDevice, b->st));
+  CK(cudaStreamSynchronize(b->st));
   return DLR_OK;
 }
 
@@ -1590,6 +1668,7 @@ int dlr_autotune(dlr_handle *const *hs, int32_t n, int32_t iters, int32_t reps, 
     b->kcount = 0;
     if ((rc = capture(b, true, &b->pre))) return rc;
     if ((rc = capture(b, false, &b->post))) return rc;
+    if (b->grp && (rc = capture_si(b))) return rc;
     b->kernels_per_step = b->kcount + 1;
   }
   CK(cudaGraphLaunch(b->pre, b->st));
@@ -1621,7 +1700,8 @@ int dlr_autotune(dlr_handle *const *hs, int32_t n, int32_t iters, int32_t reps, 
     c.n_units = (int)plans[k].size();
     for (int rep = 0; rep <= reps && e == cudaSuccess; ++rep) {
       if (rep == 1) e = cudaEventRecord(e0, b->st);
-      if (e == cudaSuccess) e = launch_si_prep(b->d_insts, n, c, b->st);
+      if (e == cudaSuccess)
+        e = b->grp ? launch_grp_prep(b->d_insts, n, c, b->gs, b->st) : launch_si_prep(b->d_insts, n, c, b->st);
       if (e == cudaSuccess)
         e = launch_si_batch(b, c);
     }
@@ -1835,7 +1915,8 @@ int dlr_get_stats(dlr_handle *h, dlr_stats *out) {
   out->ms_si_total = h->ms_si;
   out->ms_step_total = h->ms_step;
   out->si_launches = h->si_launches;
-  out->kernel_launches = h->kernel_launches;
+  // the grouped source iteration launches three kernels per iteration
+  out->kernel_launches = h->kernel_launches + (h->inst.grp ? 3 * tot : 0);
   out->nonpositive_cells = np;
   *h->h_status = s;
   return DLR_OK;

@@ -320,6 +320,20 @@ struct SiCtl {
   double *dsa_part;            // per-CTA partial sums of the DSA CG: n_inst x kDsaSlots x grid
 };
 
+// Loop state of the grouped source iteration (one per batch, device
+// memory): the iteration index, the blocks of the scalar-flux kernel that
+// have finished, a forced iteration count (timing runs), the number of
+// sweep units, and per instance whether it is still iterating and the
+// parity of its last sweep's sigma_s phi (-1: not swept in this step).
+struct GrpSi {
+  int it;
+  unsigned done;
+  int force_iters;
+  int n_units;
+  int *active;
+  int *par_of;
+};
+
 // partial sums of one DSA CG iteration: p.q, r.z, r.r, and b.b of the
 // right-hand side
 constexpr int kDsaSlots = 4;

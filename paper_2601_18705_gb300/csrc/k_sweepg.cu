@@ -6,7 +6,8 @@
 // (Eq. steady state collocation of Haut et al., phi = beta^T What^{-1} Psi =
 // gamma^T Psi with gamma = What^{-T} beta), DG0 upwind cells.
 //
-// Organisation (one cooperative launch per step for every instance):
+// Organisation (one loop of kernels per step for every instance of a batch,
+// see the section "The source iteration as a loop of kernels" below):
 //   * a warp sweeps one band of 32 rows for the kGA angles of its group at
 //     once (lane i = row i, anti-diagonal wavefront: lane i reaches column u
 //     at step t = u + i; the lower neighbour comes from lane i - 1 by a
@@ -16,11 +17,12 @@
 //     are stored in the skewed band layout of grp_off, where one
 //     (band, 32-step window) block is 4 KB contiguous: a warp streams them
 //     into shared memory with bulk asynchronous copies (cp.async.bulk, one
-//     mbarrier per stage), prefetches later windows into L2, and reads 4
-//     steps per lane with one conflict-free 16-byte load;
+//     mbarrier per stage; the fixed sources with an L2 evict-first policy)
+//     and reads 4 steps per lane with one conflict-free 16-byte load;
 //   * instead of psi the sweep writes, per group, sum_j gamma_j psi_j in the
-//     same skewed layout (16-byte stores of 4 steps per lane); the
-//     scalar-flux phase sums the groups' partials per cell;
+//     same skewed layout (in place of the stage's sigma_s phi values, then
+//     one bulk store per window); the scalar-flux kernels sum the groups'
+//     partials per quadrant, then the four quadrant sums per cell;
 //   * psi itself is written only once, by one more sweep after the source
 //     iteration has stopped, with the sigma_s phi of the last iteration
 //     (the same inputs and arithmetic, so the same psi bit for bit);
@@ -35,10 +37,6 @@ namespace dlr {
 namespace {
 
 constexpr int kNWg = 4;                  // sweeping warps per CTA (one band each at a time)
-// warps per CTA (warps past the sweeping ones would only take part in the
-// scalar-flux phases: measured with 8 and 16, they sped those phases up but
-// slowed the sweeps by more)
-constexpr int kNWt = kNWg;
 constexpr int kSubG = 16;                // progress granularity (steps)
 constexpr int kEdgePadG = 32;            // edge row padding (columns -31 .. -1)
 constexpr uint64_t kWaitNsG = 4000000000ull;
@@ -560,7 +558,7 @@ __device__ bool grp_unit(const Inst &I, const SiUnit &U, int par, const GrpSmem 
 // Phase A of one iteration (or the final sweep): every unit of the active
 // instances.  Returns false when a wait gave up.
 template <bool FINAL>
-__device__ bool grp_sweeps(const Inst *__restrict__ insts, const SiCtl &ctl, const int *active,
+__device__ bool grp_sweeps(const Inst *__restrict__ insts, const SiCtl &ctl, int n_units, const int *active,
                            const int *par_of, unsigned ctr, unsigned tag, const GrpSmem &S, Pipe &P,
                            volatile int *abort_flag) {
   __shared__ int unit_g;
@@ -569,7 +567,7 @@ __device__ bool grp_sweeps(const Inst *__restrict__ insts, const SiCtl &ctl, con
     __syncthreads();
     const int u = unit_g;
     __syncthreads();
-    if (u >= ctl.n_units) return true;
+    if (u >= n_units) return true;
     const SiUnit U = ctl.units[u];
     if (!active[U.inst]) continue;
     const unsigned long long *g_in = U.in_row >= 0 ? ctl.gedge + (size_t)U.in_row * ctl.gedge_ld : nullptr;
@@ -580,13 +578,42 @@ __device__ bool grp_sweeps(const Inst *__restrict__ insts, const SiCtl &ctl, con
 
 }  // namespace
 
-// Source iteration of a batch of grouped (mixed-precision DLR) instances in
-// one cooperative launch: sweeps of all groups, grid barrier, scalar flux
-// phi = sum over groups of the partials with the convergence test and the
-// next sigma_s phi / 4 pi (in the four quadrant layouts), grid barrier,
-// until every instance has converged (or run its fixed iterations); then
-// one more sweep per instance with its last sigma_s phi writes Psi.
-__global__ void __launch_bounds__(kNWt * 32) k_si_grp(const Inst *__restrict__ insts, SiCtl ctl, int stages) {
+// ------------------------------------------------------------------
+// The source iteration as a loop of kernels (a while node of the step's
+// CUDA graph): k_grp_sweep (the sweeps of all active groups), k_grp_qsum
+// (per quadrant, the sum of its groups' partials), k_grp_phi (phi, the next
+// sigma_s phi / 4 pi, the convergence test; its last block decides per
+// instance and ends the loop); after the loop k_grp_sweep<true> writes Psi
+// from each instance's last sigma_s phi.  The sweep needs no co-resident
+// grid: a unit is claimed only by a running CTA, after the unit it waits
+// on.  The scalar-flux kernels run at full occupancy.
+// ------------------------------------------------------------------
+
+// Resets the loop state before a step's source iteration.
+__global__ void k_grp_prep(const Inst *__restrict__ insts, int n, SiCtl ctl, GrpSi *gs) {
+  pdl_wait();
+  pdl_trigger();
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0) {
+    ctl.work[0] = 0u;
+    ctl.work[1] = 0u;
+    *ctl.abort_flag = 0;
+    *ctl.epoch += 1u;  // stale edge words of earlier launches never match
+    gs->it = 0;
+    gs->done = 0u;
+  }
+  if (t < n) {
+    insts[t].conv[0] = 0ull;
+    insts[t].conv[1] = 0ull;
+    *insts[t].nonpos = 0;
+    gs->active[t] = *insts[t].status == kOk ? 1 : 0;
+    gs->par_of[t] = -1;
+  }
+}
+
+template <bool FINAL>
+__global__ void __launch_bounds__(kNWg * 32)
+k_grp_sweep(const Inst *__restrict__ insts, SiCtl ctl, GrpSi *gs, int stages) {
   extern __shared__ __align__(128) unsigned char smem[];
   GrpSmem S;
   S.S = stages;
@@ -600,202 +627,168 @@ __global__ void __launch_bounds__(kNWt * 32) k_si_grp(const Inst *__restrict__ i
   off += (size_t)(kNWg + 1) * kGA * S.edge_ld * 4;
   S.prog = reinterpret_cast<int *>(smem + off);
   off += (size_t)(ctl.bands_max + 3) / 4 * 4 * 4;
-  int *active = reinterpret_cast<int *>(smem + off);
+  int *act = reinterpret_cast<int *>(smem + off);
   off += (size_t)(ctl.n_inst + 3) / 4 * 4 * 4;
-  int *par_of = reinterpret_cast<int *>(smem + off);  // parity of each instance's last sweep
+  int *par = reinterpret_cast<int *>(smem + off);
   volatile int *abort_flag = ctl.abort_flag;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-
-  if (lane == 0 && wid < kNWg)
+  if (lane == 0)
     for (int s = 0; s < stages; ++s) mbar_init(S.mbar + wid * stages + s, 1);
   for (int i = threadIdx.x; i < (kNWg + 1) * kGA * S.edge_ld; i += blockDim.x) S.edge[i] = 0.f;
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  const int it = *(volatile int *)&gs->it;
   for (int i = threadIdx.x; i < ctl.n_inst; i += blockDim.x) {
-    active[i] = (*insts[i].status == kOk) ? 1 : 0;
-    par_of[i] = -1;  // set by the instance's sweeps in this launch
+    if (FINAL) {
+      // instances swept in this step's iteration, unless a wait gave up
+      const int st = *insts[i].status;
+      act[i] = gs->par_of[i] >= 0 && (st == kOk || st == kENotConv);
+      par[i] = gs->par_of[i];
+    } else {
+      act[i] = gs->active[i];
+      par[i] = it & 1;
+    }
   }
   __syncthreads();
+  if (*abort_flag) return;
   Pipe P;
   P.parity = 0u;
-  const unsigned epoch_tag = (*(volatile unsigned *)ctl.epoch & 0xfffffu) << 12;
-  int it = 0;
-  bool failed = false;
-  for (;; ++it) {
-    __shared__ int n_active_s;
-    if (threadIdx.x == 0) {
-      int n = 0;
-      for (int i = 0; i < ctl.n_inst; ++i) n += active[i];
-      n_active_s = n;
-    }
-    __syncthreads();
-    if (n_active_s == 0) break;
-    for (int i = threadIdx.x; i < ctl.n_inst; i += blockDim.x)
-      if (active[i]) par_of[i] = it & 1;
-    __syncthreads();
+  const unsigned tag = ((*(volatile unsigned *)ctl.epoch & 0xfffffu) << 12) |
+                       ((unsigned)(it + (FINAL ? 2 : 1)) & 0xfffu);
+  grp_sweeps<FINAL>(insts, ctl, gs->n_units, act, par, it & 1, tag, S, P, abort_flag);
+}
 
-    // ---- phase A: sweeps of all active groups ----
-    const unsigned tag = epoch_tag | ((unsigned)(it + 1) & 0xfffu);
-    if (!grp_sweeps<false>(insts, ctl, active, par_of, it & 1, tag, S, P, abort_flag)) { failed = true; break; }
-    if (!grid_barrier(ctl.bar, abort_flag)) { failed = true; break; }
-
-    // ---- phase B: phi = sum of the group partials, sigma_s phi / 4 pi of
-    // the next iteration in the four quadrant layouts, convergence maxima ----
-    if (blockIdx.x == 0) {
-      for (int i = threadIdx.x; i < ctl.n_inst; i += blockDim.x) {
-        insts[i].conv[((it + 1) & 1) * 2 + 0] = 0ull;
-        insts[i].conv[((it + 1) & 1) * 2 + 1] = 0ull;
+// Per quadrant of each active instance, the sum of its groups' partials
+// (the groups are ordered by quadrant; each sum in group order), 16 bytes
+// at a time.
+__global__ void __launch_bounds__(256) k_grp_qsum(const Inst *__restrict__ insts, int n, const GrpSi *gs) {
+  for (int i = 0; i < n; ++i) {
+    if (!gs->active[i]) continue;
+    const Inst &I = insts[i];
+    const size_t n4 = I.glay / 4;
+    int lo = 0;
+    for (int q = 0; q < 4; ++q) {
+      int hi = lo;
+      while (hi < I.grp_ng && I.grp_tab[hi * kGrpRec + 1] > 0 && I.grp_tab[hi * kGrpRec] == q) ++hi;
+      if (hi > lo) {
+        const float4 *src = reinterpret_cast<const float4 *>(I.part);
+        float4 *dst = reinterpret_cast<float4 *>(I.qsum + (size_t)q * I.glay);
+        for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n4;
+             e += (size_t)gridDim.x * blockDim.x) {
+          float4 acc = src[(size_t)lo * n4 + e];
+          for (int g = lo + 1; g < hi; ++g) {
+            const float4 v = src[(size_t)g * n4 + e];
+            acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+          }
+          dst[e] = acc;
+        }
       }
-      if (threadIdx.x == 0) ctl.work[(it + 1) & 1] = 0u;
+      lo = hi;
     }
-    // B1: per quadrant, the sum of its groups' partials (the groups are
-    // ordered by quadrant; each sum in group order), 16 bytes at a time
-    for (int i = 0; i < ctl.n_inst; ++i) {
-      if (!active[i]) continue;
-      const Inst &I = insts[i];
-      const size_t n4 = I.glay / 4;
-      int lo = 0;
+  }
+}
+
+// phi = the quadrant sums at each cell, sigma_s phi / 4 pi of the next
+// iteration in the four quadrant layouts, the convergence maxima; the last
+// block to finish takes every instance's decision (as the per-angle
+// kernel's), resets the counters of the next iteration and, when no
+// instance is left (or a wait gave up), ends the loop.
+__global__ void __launch_bounds__(256) k_grp_phi(const Inst *__restrict__ insts, int n, SiCtl ctl, GrpSi *gs,
+                                                 cudaGraphConditionalHandle loop) {
+  const int it = gs->it;
+  const int lane = threadIdx.x & 31;
+  for (int i = 0; i < n; ++i) {
+    if (!gs->active[i]) continue;
+    const Inst &I = insts[i];
+    const int nx = I.nx, ny = I.ny, N = I.N, nwin = I.nwin;
+    int qmask = 0;  // quadrants with a group
+    for (int g = 0; g < I.grp_ng; ++g)
+      if (I.grp_tab[g * kGrpRec + 1] > 0) qmask |= 1 << I.grp_tab[g * kGrpRec];
+    const float *qs = I.qsum;
+    const float *ss4 = as_c<float>(I.ss4);
+    const float *pold = as_c<float>((it & 1) ? I.phi1 : I.phi0);
+    float *pnew = as<float>((it & 1) ? I.phi0 : I.phi1);
+    float *spn = I.spk + (size_t)((it + 1) & 1) * 4 * I.glay;
+    float dmax = 0.f, pmax = 0.f;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+      const int y = c / nx, x = c - y * nx;
+      unsigned o[4];
+      float v[4];
+#pragma unroll
       for (int q = 0; q < 4; ++q) {
-        int hi = lo;
-        while (hi < I.grp_ng && I.grp_tab[hi * kGrpRec + 1] > 0 && I.grp_tab[hi * kGrpRec] == q) ++hi;
-        if (hi > lo) {
-          const float4 *src = reinterpret_cast<const float4 *>(I.part);
-          float4 *dst = reinterpret_cast<float4 *>(I.qsum + (size_t)q * I.glay);
-          // kP1 positions per thread, up to kG1 groups' loads of each in
-          // flight before they are added
-          constexpr int kP1 = 4, kG1 = 5;
-          const size_t nt = (size_t)gridDim.x * blockDim.x;
-          for (size_t e0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e0 < n4; e0 += kP1 * nt) {
-            float4 acc[kP1];
+        o[q] = (unsigned)grp_off(q, nx, ny, nwin, x, y);
+        v[q] = (qmask >> q) & 1 ? qs[(size_t)q * I.glay + o[q]] : 0.f;
+      }
+      const float acc = ((v[0] + v[1]) + v[2]) + v[3];
+      pnew[c] = acc;
+      const float sp = ss4[c] * acc;
 #pragma unroll
-            for (int j = 0; j < kP1; ++j) acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int g0 = lo; g0 < hi; g0 += kG1) {
-              float4 v[kG1][kP1];
-#pragma unroll
-              for (int h = 0; h < kG1; ++h)
-#pragma unroll
-                for (int j = 0; j < kP1; ++j)
-                  if (g0 + h < hi && e0 + j * nt < n4) v[h][j] = src[(size_t)(g0 + h) * n4 + e0 + j * nt];
-#pragma unroll
-              for (int h = 0; h < kG1; ++h)
-#pragma unroll
-                for (int j = 0; j < kP1; ++j)
-                  if (g0 + h < hi) {
-                    acc[j].x += v[h][j].x; acc[j].y += v[h][j].y; acc[j].z += v[h][j].z; acc[j].w += v[h][j].w;
-                  }
-            }
-#pragma unroll
-            for (int j = 0; j < kP1; ++j)
-              if (e0 + j * nt < n4) dst[e0 + j * nt] = acc[j];
-          }
-        }
-        lo = hi;
+      for (int q = 0; q < 4; ++q) spn[(size_t)q * I.glay + o[q]] = sp;
+      dmax = fmaxf(dmax, fabsf(acc - pold[c]));
+      pmax = fmaxf(pmax, fabsf(acc));
+    }
+    dmax = warp_max(dmax);
+    pmax = warp_max(pmax);
+    if (lane == 0) {
+      atomic_max_nonneg(I.conv + (it & 1) * 2 + 0, (double)dmax);
+      atomic_max_nonneg(I.conv + (it & 1) * 2 + 1, (double)pmax);
+    }
+  }
+  // the last block to finish decides
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&gs->done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  const bool aborted = *(volatile int *)ctl.abort_flag != 0;
+  int left = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!gs->active[i]) continue;
+    const Inst &I = insts[i];
+    gs->par_of[i] = it & 1;  // the parity of this instance's last sweep so far
+    if (aborted) {
+      set_status(I.status, kETimeout);
+      gs->active[i] = 0;
+      continue;
+    }
+    volatile unsigned long long *cv = I.conv + (it & 1) * 2;
+    const double d = __longlong_as_double((long long)cv[0]);
+    const double m = __longlong_as_double((long long)cv[1]);
+    const int done_iters = it + 1;
+    bool done;
+    if (gs->force_iters > 0) {
+      done = done_iters >= gs->force_iters;
+      if (done) gs->active[i] = 0;
+      else ++left;
+      I.conv[((it + 1) & 1) * 2 + 0] = 0ull;
+      I.conv[((it + 1) & 1) * 2 + 1] = 0ull;
+      continue;
+    }
+    if (I.fixed_iters > 0) {
+      done = done_iters >= I.fixed_iters;
+    } else {
+      done = d <= I.si_tol * m;
+      if (!done && done_iters >= I.max_iter) {
+        done = true;
+        set_status(I.status, kENotConv);
       }
     }
-    if (!grid_barrier(ctl.bar, abort_flag)) { failed = true; break; }
-    // B2: phi = the quadrant sums at each cell, sigma_s phi / 4 pi of the
-    // next iteration in the four quadrant layouts, convergence maxima
-    for (int i = 0; i < ctl.n_inst; ++i) {
-      if (!active[i]) continue;
-      const Inst &I = insts[i];
-      const int nx = I.nx, ny = I.ny, N = I.N, nwin = I.nwin;
-      int qmask = 0;  // quadrants with a group
-      for (int g = 0; g < I.grp_ng; ++g)
-        if (I.grp_tab[g * kGrpRec + 1] > 0) qmask |= 1 << I.grp_tab[g * kGrpRec];
-      const float *qs = I.qsum;
-      const float *ss4 = as_c<float>(I.ss4);
-      const float *pold = as_c<float>((it & 1) ? I.phi1 : I.phi0);
-      float *pnew = as<float>((it & 1) ? I.phi0 : I.phi1);
-      float *spn = I.spk + (size_t)((it + 1) & 1) * 4 * I.glay;
-      float dmax = 0.f, pmax = 0.f;
-      constexpr int kPB = 8;  // cells per thread at a time, loads issued together
-      const int nthr = gridDim.x * blockDim.x;
-      for (int c0 = blockIdx.x * blockDim.x + threadIdx.x; c0 < N; c0 += kPB * nthr) {
-        unsigned o[kPB][4];
-        float v[kPB][4];
-#pragma unroll
-        for (int j = 0; j < kPB; ++j) {
-          const int c = min(c0 + j * nthr, N - 1);
-          const int y = c / nx, x = c - y * nx;
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            o[j][q] = (unsigned)grp_off(q, nx, ny, nwin, x, y);
-            v[j][q] = (qmask >> q) & 1 ? qs[(size_t)q * I.glay + o[j][q]] : 0.f;
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < kPB; ++j) {
-          const int c = c0 + j * nthr;
-          if (c >= N) continue;
-          const float acc = ((v[j][0] + v[j][1]) + v[j][2]) + v[j][3];
-          pnew[c] = acc;
-          const float sp = ss4[c] * acc;
-#pragma unroll
-          for (int q = 0; q < 4; ++q) spn[(size_t)q * I.glay + o[j][q]] = sp;
-          dmax = fmaxf(dmax, fabsf(acc - pold[c]));
-          pmax = fmaxf(pmax, fabsf(acc));
-        }
-      }
-      dmax = warp_max(dmax);
-      pmax = warp_max(pmax);
-      if (lane == 0) {
-        atomic_max_nonneg(I.conv + (it & 1) * 2 + 0, (double)dmax);
-        atomic_max_nonneg(I.conv + (it & 1) * 2 + 1, (double)pmax);
-      }
+    if (done) {
+      gs->active[i] = 0;
+      *I.iters = done_iters;
+      atomicAdd(I.iters_total, (unsigned long long)done_iters);
+    } else {
+      ++left;
     }
-    if (!grid_barrier(ctl.bar, abort_flag)) { failed = true; break; }
-    // the next sweeps read phase B's sigma_s phi through bulk copies (the
-    // asynchronous proxy)
-    asm volatile("fence.proxy.async.global;" ::: "memory");
-
-    // ---- phase C: every CTA takes the same decision per instance ----
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int i = 0; i < ctl.n_inst; ++i) {
-        if (!active[i]) continue;
-        const Inst &I = insts[i];
-        volatile unsigned long long *cv = I.conv + (it & 1) * 2;
-        const double d = __longlong_as_double((long long)cv[0]);
-        const double m = __longlong_as_double((long long)cv[1]);
-        const int done_iters = it + 1;
-        bool done;
-        if (ctl.force_iters > 0) {
-          if (done_iters >= ctl.force_iters) active[i] = 0;
-          continue;
-        }
-        if (I.fixed_iters > 0) {
-          done = done_iters >= I.fixed_iters;
-        } else {
-          done = d <= I.si_tol * m;
-          if (!done && done_iters >= I.max_iter) {
-            done = true;
-            if (blockIdx.x == 0) set_status(I.status, kENotConv);
-          }
-        }
-        if (done) {
-          active[i] = 0;
-          if (blockIdx.x == 0) {
-            *I.iters = done_iters;
-            atomicAdd(I.iters_total, (unsigned long long)done_iters);
-          }
-        }
-      }
-    }
-    __syncthreads();
+    I.conv[((it + 1) & 1) * 2 + 0] = 0ull;
+    I.conv[((it + 1) & 1) * 2 + 1] = 0ull;
   }
-
-  if (!failed) {
-    // ---- the final sweep: Psi from each instance's last sigma_s phi ----
-    for (int i = threadIdx.x; i < ctl.n_inst; i += blockDim.x)
-      active[i] = par_of[i] >= 0 && (*insts[i].status == kOk || *insts[i].status == kENotConv) ? 1 : 0;
-    __syncthreads();
-    const unsigned tag = epoch_tag | ((unsigned)(it + 2) & 0xfffu);
-    // the unit counter of this parity was reset by the last phase B
-    if (!grp_sweeps<true>(insts, ctl, active, par_of, it & 1, tag, S, P, abort_flag)) failed = true;
-  }
-  // a wait that gave up marks every instance of the launch
-  if (*abort_flag && blockIdx.x == 0 && threadIdx.x == 0) {
-    for (int i = 0; i < ctl.n_inst; ++i) set_status(insts[i].status, kETimeout);
-  }
+  ctl.work[(it + 1) & 1] = 0u;
+  gs->done = 0u;
+  gs->it = it + 1;
+  __threadfence();
+  if (left == 0) cudaGraphSetConditional(loop, 0);
 }
 
 // ------------------------------------------------------------------
@@ -818,33 +811,45 @@ int si_grp_stages(int nx_max, int bands_max, int n_inst) {
   return 0;
 }
 
+// CTAs of the sweep kernel: as many as fit at once (they claim units).
 int si_grp_max_grid(int nx_max, int bands_max, int n_inst, int stages) {
   const size_t smem = si_grp_smem_bytes(nx_max, bands_max, n_inst, stages);
-  if (cudaFuncSetAttribute(k_si_grp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return 0;
+  for (auto fn : {k_grp_sweep<false>, k_grp_sweep<true>})
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return 0;
   int per_sm = 0, dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_si_grp, kNWt * 32, smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grp_sweep<false>, kNWg * 32, smem) != cudaSuccess)
     return 0;
   return per_sm * sms;
 }
 
-cudaError_t launch_si_grp(const Inst *d_insts, const SiCtl &ctl, int grid, int stages, cudaStream_t st) {
+cudaError_t launch_grp_prep(const Inst *d, int n, const SiCtl &ctl, GrpSi *gs, cudaStream_t st) {
+  return launch_pdl(k_grp_prep, dim3((n + 255) / 256), dim3(256), 0, st, d, n, ctl, gs);
+}
+
+// The body of the loop (three kernels) on stream st: used to fill the while
+// node's body graph by stream capture.
+cudaError_t launch_grp_iteration(const Inst *d, int n, const SiCtl &ctl, GrpSi *gs, int grid, int stages,
+                                 cudaGraphConditionalHandle loop, cudaStream_t st) {
   const size_t smem = si_grp_smem_bytes(ctl.nx_max, ctl.bands_max, ctl.n_inst, stages);
-  cudaError_t e = cudaFuncSetAttribute(k_si_grp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_grp_sweep<false><<<grid, kNWg * 32, smem, st>>>(d, ctl, gs, stages);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kNWt * 32);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_si_grp, d_insts, ctl, stages);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  k_grp_qsum<<<4 * sms, 256, 0, st>>>(d, n, gs);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_grp_phi<<<4 * sms, 256, 0, st>>>(d, n, ctl, gs, loop);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grp_final(const Inst *d, const SiCtl &ctl, GrpSi *gs, int grid, int stages, cudaStream_t st) {
+  const size_t smem = si_grp_smem_bytes(ctl.nx_max, ctl.bands_max, ctl.n_inst, stages);
+  k_grp_sweep<true><<<grid, kNWg * 32, smem, st>>>(d, ctl, gs, stages);
+  return cudaGetLastError();
 }
 
 int si_grp_warps() { return kNWg; }
