@@ -139,16 +139,20 @@ typedef struct dlr_problem {
                             reflective left or right edge needs n_azim even
                             (the quadrature's mirror map) */
   int32_t sweep_mode;    /* source-iteration kernel of mixed-precision DLR
-                            steps (Algorithm 1 step 4): 0 = grouped -- each
-                            warp sweeps 2 chosen angles of one quadrant at
-                            once, the scalar flux is summed from per-group
-                            partials, and psi is written once, by a last
-                            sweep after the iteration stops (used when the
-                            problem has no DSA, no reflective edge and no
-                            augmented step, and for a batch only when all
-                            its instances qualify); 1 = one angle per warp
-                            (the kernel of every other case).  Both give the
-                            same step to FP32 rounding */
+                            steps (Algorithm 1 step 4).  The grouped kernel
+                            sweeps 2 chosen angles of one quadrant per warp,
+                            sums the scalar flux from per-group partials,
+                            writes psi once, by a last sweep after the
+                            iteration stops, and runs as a loop inside the
+                            step's CUDA graph; it serves problems without
+                            DSA, reflective edges or the augmented step, and
+                            a batch only when all its instances qualify.
+                            The per-angle kernel sweeps one angle per warp
+                            (every other case).  0 = chosen by dlr_autotune
+                            (untuned: grouped for meshes of 2^19 cells or
+                            more); 1 = per-angle; 2 = grouped where the
+                            problem qualifies.  Both give the same step to
+                            FP32 rounding */
 } dlr_problem;
 
 /* Device memory and stream supplied by the caller (e.g. PyTorch). */
@@ -177,6 +181,9 @@ typedef struct dlr_stats {
   int64_t kernel_launches;   /* kernels this handle's steps launched */
   int64_t nonpositive_cells; /* cells with T <= 0 after the last step */
   int64_t dsa_iters_total;   /* CG iterations of all DSA solves (dsa = 1) */
+  int32_t sweep_grouped;     /* 1: the last step's source iteration swept two
+                                angles of one quadrant per warp (the grouped
+                                kernel, see sweep_mode); 0: one per warp */
 } dlr_stats;
 
 /* Creates a solver: validates sizes, builds the quadrature and the initial
@@ -201,19 +208,26 @@ int dlr_step_batch(dlr_handle *const *hs, int32_t n, int32_t nsteps);
 
 /* Autotuner of the sweep work plan of a batch (the same handles, in the same
  * order, as later dlr_step_batch calls; n = 1 for dlr_step).  The sweeps of
- * Algorithm 1 step 4 run as units of consecutive 32-row bands of one angle,
- * one CTA per unit; an angle split over several units hands its band edges
- * from unit to unit through global memory.  Candidate plans (no split, and
- * splitting thresholds 2, 1 and 0.5: an instance's units are halved while
- * the longest is longer than threshold x the average load of one resident
- * CTA) are timed on the device, each as reps source-iteration launches of
- * exactly iters iterations on the state the next step starts from, and the
- * fastest is kept for this handle set and for later batches of the same
- * shape (sorted nx, ny, r, precision).  Nothing the next step reads is
- * changed.  *chosen (may be NULL) receives the chosen threshold (0 = no
- * split); ms (NULL or 4 entries) the milliseconds per launch of each
- * candidate in the order above.  Synchronises.  Without tuning, a batch uses
- * threshold 1. */
+ * Algorithm 1 step 4 run as units of consecutive 32-row bands of one angle
+ * (the per-angle kernel) or of one group of two angles of a quadrant (the
+ * grouped kernel, for batches that qualify: see sweep_mode), one CTA per
+ * unit; an angle split over several units hands its band edges from unit to
+ * unit through global memory.  Candidate plans -- the two kernels, each with
+ * no split and with splitting thresholds 2, 1 and 0.5 (an instance's units
+ * are halved while the longest is longer than threshold x the average load
+ * of one resident CTA) -- are timed on the device, each as reps
+ * source-iteration launches of exactly iters iterations on the state the
+ * next step starts from, and the fastest is kept for this handle set and
+ * for later batches of the same shape (sorted nx, ny, r, precision).
+ * Nothing the next step reads is changed.  *chosen (may be NULL) receives
+ * the chosen threshold (0 = no split; dlr_stats.sweep_grouped tells the
+ * kernel after the next step); ms (NULL or DLR_AUTOTUNE_CANDIDATES entries)
+ * the milliseconds per launch of each candidate: the four thresholds above
+ * with the per-angle kernel, then with the grouped one (-1 where the batch
+ * cannot take it).  Synchronises.  Without tuning, a batch uses threshold 1
+ * and the grouped kernel when it qualifies and its largest mesh has at
+ * least 2^19 cells. */
+#define DLR_AUTOTUNE_CANDIDATES 8
 int dlr_autotune(dlr_handle *const *hs, int32_t n, int32_t iters, int32_t reps,
                  double *chosen, double *ms);
 

@@ -57,7 +57,7 @@ class ProblemSpec:
     dsa_tol: float = 0.0     # CG stop ||r|| <= dsa_tol ||b|| (0: 0.1)
     dsa_max_iter: int = 0    # CG cap per solve (0: 3)
     reflect: tuple = (0, 0, 0, 0)  # reflective edges L, R, B, T (full-rank SN only)
-    sweep_mode: int = 0      # mixed DLR source iteration: 0 grouped angles, 1 one angle per warp
+    sweep_mode: int = 0      # mixed DLR source iteration: 0 autotuned, 1 one angle per warp, 2 grouped
 
     def cstruct(self):
         keep = [_f64(self.sigma), _f64(self.rho_cv), _f64(self.T0)]
@@ -272,14 +272,22 @@ AUTOTUNE_CANDIDATES = (0.0, 2.0, 1.0, 0.5)  # splitting thresholds, in dlr_autot
 def autotune(solvers, *, iters: int = 2, reps: int = 3) -> dict:
     """Autotunes the sweep work plan of the batch `solvers` (the same list
     later passed to step_batch; one solver for Solver.step): times each
-    candidate splitting threshold on the device and keeps the fastest.
-    Returns {"split": chosen threshold (0 = no split), "ms": {threshold:
-    milliseconds per source-iteration launch}}."""
+    candidate -- the per-angle and the grouped source-iteration kernel, each
+    with every splitting threshold -- on the device and keeps the fastest.
+    Returns {"split": chosen threshold (0 = no split), "grouped": whether
+    the grouped kernel was chosen, "ms": {threshold: ms per launch} of the
+    per-angle kernel, "ms_grouped": the same for the grouped kernel (-1:
+    the batch cannot take it)}."""
     arr = (C.c_void_p * len(solvers))(*[s.h.value for s in solvers])
     chosen = C.c_double(0.0)
-    ms = (C.c_double * len(AUTOTUNE_CANDIDATES))()
+    nc = len(AUTOTUNE_CANDIDATES)
+    ms = (C.c_double * (2 * nc))()
     check(load().dlr_autotune(arr, len(solvers), int(iters), int(reps), C.byref(chosen), ms))
-    return {"split": chosen.value, "ms": dict(zip(AUTOTUNE_CANDIDATES, list(ms)))}
+    ms = list(ms)
+    grouped = min(ms[nc:]) >= 0 and min(ms[nc:]) < min(ms[:nc])
+    return {"split": chosen.value, "grouped": bool(grouped),
+            "ms": dict(zip(AUTOTUNE_CANDIDATES, ms[:nc])),
+            "ms_grouped": dict(zip(AUTOTUNE_CANDIDATES, ms[nc:]))}
 
 
 def debug_lose_edge(solvers) -> None:

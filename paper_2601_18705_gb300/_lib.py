@@ -54,7 +54,8 @@ class DlrStats(C.Structure):
                 ("cell_angle_updates", C.c_int64), ("si_iters_last", C.c_int32),
                 ("status", C.c_int32), ("ms_si_total", C.c_double), ("ms_step_total", C.c_double),
                 ("si_launches", C.c_int64), ("kernel_launches", C.c_int64),
-                ("nonpositive_cells", C.c_int64), ("dsa_iters_total", C.c_int64)]
+                ("nonpositive_cells", C.c_int64), ("dsa_iters_total", C.c_int64),
+                ("sweep_grouped", C.c_int32)]
 
 
 _lib = None

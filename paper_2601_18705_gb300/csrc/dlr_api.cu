@@ -157,6 +157,7 @@ struct dlr_handle {
   Batch *own_batch = nullptr;
   bool canonical = true;  // S0 diagonal (SVD basis) since the last step
   bool sn = false;        // full-rank SN instance (r = K swept angles)
+  bool grp_loop = false;  // the last step took the grouped source iteration
   bool aug = false;       // augmented step: steps 5-10 on inst2 at rank 2r
   Inst inst2{};
 };
@@ -182,7 +183,9 @@ struct Batch {
   Inst *d_insts2 = nullptr;   // the instances of steps 5-10 (rank 2r when augmented)
   int sel_slice_max = 1;      // most angles one CTA of the selection cluster owns
   bool lside_fused = false;   // step 8 by the one-cluster kernel (pivoted-QR choice, K <= 1024)
-  bool grp = false;           // every instance takes the grouped sweep (k_sweepg.cu)
+  bool grp_ok = false;        // every instance can take the grouped sweep (k_sweepg.cu)
+  bool grp = false;           // ... and the batch takes it
+  int grid_angle = 0, grid_grp = 0;  // CTAs of the per-angle and the grouped sweep
   int grp_stages = 0;         // shared-memory stages per warp of the grouped sweep
   GrpSi *gs = nullptr;        // its loop state (device)
   cudaGraphExec_t si = nullptr;  // its source iteration: a while node and the last sweep
@@ -399,7 +402,7 @@ static int reduce_cta_cap() {
 // the per-angle kernel.
 static bool grp_eligible(const dlr_problem *p) {
   return p->precision == DLR_MIXED && p->method == DLR_METHOD_DLR && !p->dsa && !p->augment &&
-         !(p->reflect[0] || p->reflect[1] || p->reflect[2] || p->reflect[3]) && p->sweep_mode == 0;
+         !(p->reflect[0] || p->reflect[1] || p->reflect[2] || p->reflect[3]) && p->sweep_mode != 1;
 }
 
 static Sizes sizes_of(const dlr_problem *p, int sms) {
@@ -493,7 +496,7 @@ static int validate(const dlr_problem *p) {
   if (p->dsa != 0 && p->dsa != 1) return fail(DLR_EINVAL, "dsa must be 0 or 1");
   for (int e = 0; e < 4; ++e)
     if (p->reflect[e] != 0 && p->reflect[e] != 1) return fail(DLR_EINVAL, "reflect[%d] must be 0 or 1", e);
-  if (p->sweep_mode != 0 && p->sweep_mode != 1) return fail(DLR_EINVAL, "sweep_mode must be 0 or 1");
+  if (p->sweep_mode < 0 || p->sweep_mode > 2) return fail(DLR_EINVAL, "sweep_mode must be 0, 1 or 2");
   if (p->reflect[0] || p->reflect[1] || p->reflect[2] || p->reflect[3]) {
     if (!sn) return fail(DLR_EINVAL, "reflective edges are built for DLR_METHOD_SN only");
     if ((p->reflect[0] || p->reflect[1]) && p->n_azim % 2)
@@ -991,19 +994,35 @@ static int plan_units(dlr_handle *const *hs, int n, bool mixed, bool grp, int ct
   return rows;
 }
 
-// Autotuned splitting thresholds by batch shape: the sorted (nx, ny, r,
-// precision) of its instances.
-static std::map<std::vector<std::array<int, 4>>, double> &tune_table() {
-  static std::map<std::vector<std::array<int, 4>>, double> m;
+// Autotuned sweep plans by batch shape (the sorted (nx, ny, r, precision)
+// of its instances): the splitting threshold and the source-iteration
+// kernel (grouped: two angles per warp; or one angle per warp).
+struct TunedPlan {
+  double split;
+  int grouped;
+};
+static std::map<std::vector<std::array<int, 4>>, TunedPlan> &tune_table() {
+  static std::map<std::vector<std::array<int, 4>>, TunedPlan> m;
   return m;
 }
 static std::vector<std::array<int, 4>> batch_shape(dlr_handle *const *hs, int n);
 constexpr double kDefaultSplit = 1.0;
+// Untuned, the grouped kernel serves batches whose largest mesh has at least
+// this many cells (measured: it is 1.3x faster per source iteration on
+// 1024^2 cells, 1.3x slower on 256^2, and even on a batch of 64^2-512^2
+// meshes).
+constexpr long long kGroupedMinCells = 1ll << 19;
 
-static double tuned_split(dlr_handle *const *hs, int n) {
+static TunedPlan tuned_plan(dlr_handle *const *hs, int n) {
+  bool forced = true;  // sweep_mode 2 on every instance: the grouped kernel
+  for (int i = 0; i < n; ++i) forced = forced && hs[i]->prob.sweep_mode == 2;
   auto &m = tune_table();
   auto it = m.find(batch_shape(hs, n));
-  return it == m.end() ? kDefaultSplit : it->second;
+  if (forced) return TunedPlan{it != m.end() ? it->second.split : kDefaultSplit, 1};
+  if (it != m.end()) return it->second;
+  long long cmax = 0;
+  for (int i = 0; i < n; ++i) cmax = std::max(cmax, (long long)hs[i]->N);
+  return TunedPlan{kDefaultSplit, cmax >= kGroupedMinCells ? 1 : 0};
 }
 
 static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
@@ -1031,34 +1050,45 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   }
   const int gam_max = b->sn ? b->rmax : kMaxRank;  // scalar-flux weights of k_si
   int any_dsa = 0;
-  b->grp = true;
+  b->grp_ok = true;
   for (int i = 0; i < n; ++i) {
     any_dsa |= hs[i]->inst.dsa ? 1 : 0;
-    b->grp = b->grp && hs[i]->inst.grp;
+    b->grp_ok = b->grp_ok && hs[i]->inst.grp;
   }
-  if (b->grp) {
+  if (b->grp_ok) {
     b->grp_stages = si_grp_stages(b->nx_max, b->bands_max, n);
-    if (b->grp_stages == 0) b->grp = false;  // too wide for its shared memory: the per-angle kernel
+    if (b->grp_stages == 0) b->grp_ok = false;  // too wide for its shared memory: the per-angle kernel
   }
-  const int gmax = b->grp ? si_grp_max_grid(b->nx_max, b->bands_max, n, b->grp_stages)
-                 : b->mixed ? si_max_grid<float>(b->nx_max, b->bands_max, n, gam_max, any_dsa)
-                            : si_max_grid<double>(b->nx_max, b->bands_max, n, gam_max, any_dsa);
-  if (gmax <= 0) {
+  b->grid_angle = b->mixed ? si_max_grid<float>(b->nx_max, b->bands_max, n, gam_max, any_dsa)
+                           : si_max_grid<double>(b->nx_max, b->bands_max, n, gam_max, any_dsa);
+  b->grid_grp = b->grp_ok ? si_grp_max_grid(b->nx_max, b->bands_max, n, b->grp_stages) : 0;
+  if (b->grp_ok && b->grid_grp <= 0) b->grp_ok = false;
+  if (b->grid_angle <= 0) {
     delete b;
     return fail(DLR_ECUDA, "the source-iteration kernel does not fit on this GPU");
   }
-  b->si_grid = gmax;
+  const TunedPlan tp = tuned_plan(hs, n);
+  b->grp = b->grp_ok && tp.grouped;
+  b->si_grid = b->grp ? b->grid_grp : b->grid_angle;
+  const int gmax = b->si_grid;
   // capacity of the unit and edge tables: the finest split (one unit per
-  // NW bands, or per band when an angle has fewer bands than warps)
-  const int nw = b->grp ? si_grp_warps() : si_sweep_warps(b->mixed);
+  // NW bands, or per band when an angle has fewer bands than warps), for
+  // either kernel
   int rows_cap = 0;
-  for (int i = 0; i < n; ++i) {
-    const int nb = (hs[i]->prob.ny + 31) / 32;
-    const int g = (nb + std::min(nb, nw) - 1) / std::min(nb, nw);
-    b->units_cap += sweep_items(hs[i], b->grp) * g;
-    rows_cap += sweep_items(hs[i], b->grp) * (g - 1);
+  for (int kind = 0; kind < (b->grp_ok ? 2 : 1); ++kind) {
+    const bool g1 = kind == 1;
+    const int nw = g1 ? si_grp_warps() : si_sweep_warps(b->mixed);
+    int units = 0, rows = 0;
+    for (int i = 0; i < n; ++i) {
+      const int nb = (hs[i]->prob.ny + 31) / 32;
+      const int g = (nb + std::min(nb, nw) - 1) / std::min(nb, nw);
+      units += sweep_items(hs[i], g1) * g;
+      rows += sweep_items(hs[i], g1) * (g - 1);
+    }
+    b->units_cap = std::max(b->units_cap, units);
+    rows_cap = std::max(rows_cap, rows);
   }
-  b->split = tuned_split(hs, n);
+  b->split = tp.split;
   std::vector<SiUnit> units;
   plan_units(hs, n, b->mixed, b->grp, gmax, b->split, units);
   // one device block for the batch's tables
@@ -1069,7 +1099,7 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
            8 * sz(sizeof(CholJob) * n) + sz(sizeof(ReduceJob) * n);
   // 64-bit words per edge row: one per column and value (two per FP64 value;
   // kGA values per column in the grouped sweep)
-  const int gedge_ld = (b->nx_max + 3) / 4 * 4 * (b->grp ? kGA : b->mixed ? 1 : 2);
+  const int gedge_ld = (b->nx_max + 3) / 4 * 4 * (b->grp_ok ? kGA : b->mixed ? 1 : 2);
   bytes += sz(sizeof(SiUnit) * b->units_cap) + sz(64) * 4;
   // one row more than any plan uses: zeroed below and never written (tags
   // are nonzero), the row dlr_debug_lose_edge points a unit at
@@ -1490,16 +1520,12 @@ static cudaError_t launch_si_batch(const Batch *b, const SiCtl &c) {
                   : launch_si<double>(b->d_insts, c, b->si_grid, b->st);
 }
 
+static int ensure_graphs(Batch *b);
+
 static int run_steps(Batch *b, int nsteps) {
   int rc = refresh_batch(b);
   if (rc) return rc;
-  if (!b->pre) {
-    b->kcount = 0;
-    if ((rc = capture(b, true, &b->pre))) return rc;
-    if ((rc = capture(b, false, &b->post))) return rc;
-    if (b->grp && (rc = capture_si(b))) return rc;
-    b->kernels_per_step = b->kcount + 1;  // + source iteration (the last sweep of the grouped one)
-  }
+  if ((rc = ensure_graphs(b))) return rc;
   dlr_handle *h0 = b->hs[0];
   for (int s = 0; s < nsteps; ++s) {
     std::array<cudaEvent_t, 4> ev{};
@@ -1520,6 +1546,7 @@ static int run_steps(Batch *b, int nsteps) {
   }
   for (auto *h : b->hs) {
     h->steps += nsteps;
+    h->grp_loop = b->grp;
     h->canonical = b->svd_mode == 1 || b->aug;  // the augmented step ends on the SVD of S
     h->kernel_launches += (int64_t)nsteps * b->kernels_per_step;
     CK(cudaMemcpyAsync(h->h_status, h->inst.status, sizeof(int), cudaMemcpyDeviceToHost, b->st));
@@ -1651,10 +1678,42 @@ int dlr_set_split(dlr_handle *const *hs, int32_t n, double split) {
   return set_plan(b, split);
 }
 
-// Times the source-iteration launch of the batch for each candidate unit
-// plan (exactly `iters` iterations, `reps` launches after one untimed one)
-// and keeps the fastest.  The sweeps run on the state the next step starts
-// from (the "pre" graph is replayed first); everything they write is
+// The step's graphs of the batch (captured on first use, or after the
+// source-iteration kernel was switched).
+static int ensure_graphs(Batch *b) {
+  int rc;
+  if (!b->pre) {
+    b->kcount = 0;
+    if ((rc = capture(b, true, &b->pre))) return rc;
+    if ((rc = capture(b, false, &b->post))) return rc;
+    if (b->grp && (rc = capture_si(b))) return rc;
+    b->kernels_per_step = b->kcount + 1;  // + source iteration (the last sweep of the grouped one)
+  }
+  return DLR_OK;
+}
+
+// Switches the batch between the grouped and the per-angle source-iteration
+// kernel: the step's graphs are captured again (the coefficients go to the
+// other kernel's layout) and the unit plan is redone for the kernel's items.
+static int select_kernel(Batch *b, bool grp) {
+  if (grp == b->grp) return DLR_OK;
+  CK(cudaStreamSynchronize(b->st));
+  for (cudaGraphExec_t *g : {&b->pre, &b->post, &b->si})
+    if (*g) {
+      cudaGraphExecDestroy(*g);
+      *g = nullptr;
+    }
+  b->grp = grp;
+  b->si_grid = grp ? b->grid_grp : b->grid_angle;
+  return set_plan(b, b->split);
+}
+
+// Times the source-iteration launch of the batch for each candidate sweep
+// plan -- the splitting thresholds with the per-angle kernel, and again
+// with the grouped kernel where the batch can take it (exactly `iters`
+// iterations, `reps` launches after one untimed one) -- and keeps the
+// fastest.  The sweeps run on the state the next step starts from (the
+// "pre" graph of each kernel is replayed first); everything they write is
 // recomputed by that step, and the iteration counters are left alone.
 int dlr_autotune(dlr_handle *const *hs, int32_t n, int32_t iters, int32_t reps, double *chosen,
                  double *ms_out) {
@@ -1664,59 +1723,63 @@ int dlr_autotune(dlr_handle *const *hs, int32_t n, int32_t iters, int32_t reps, 
   Batch *b = nullptr;
   if ((rc = get_batch(hs, n, &b))) return rc;
   if ((rc = refresh_batch(b))) return rc;
-  if (!b->pre) {
-    b->kcount = 0;
-    if ((rc = capture(b, true, &b->pre))) return rc;
-    if ((rc = capture(b, false, &b->post))) return rc;
-    if (b->grp && (rc = capture_si(b))) return rc;
-    b->kernels_per_step = b->kcount + 1;
-  }
-  CK(cudaGraphLaunch(b->pre, b->st));
   const double cand[] = {0.0, 2.0, 1.0, 0.5};
   const int nc = (int)(sizeof(cand) / sizeof(cand[0]));
-  std::vector<std::vector<SiUnit>> plans(nc);
-  for (int c = 0; c < nc; ++c) plan_units(b->hs.data(), n, b->mixed, b->grp, b->si_grid, cand[c], plans[c]);
   auto same = [](const std::vector<SiUnit> &x, const std::vector<SiUnit> &y) {
     return x.size() == y.size() && std::memcmp(x.data(), y.data(), x.size() * sizeof(SiUnit)) == 0;
   };
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  std::vector<double> ms(nc, -1.0);
+  std::vector<double> ms(2 * nc, -1.0);  // per-angle kernel, then grouped
   int best = -1;
-  SiCtl c = b->ctl;
-  c.force_iters = iters;
   cudaError_t e = cudaSuccess;
-  for (int k = 0; k < nc && e == cudaSuccess; ++k) {
-    int dup = -1;
-    for (int q = 0; q < k; ++q)
-      if (same(plans[q], plans[k])) dup = q;
-    if (dup >= 0) {
-      ms[k] = ms[dup];
-      continue;
+  for (int kind = 0; kind < 2 && e == cudaSuccess; ++kind) {
+    if (kind == 1 && !b->grp_ok) break;
+    if ((rc = select_kernel(b, kind == 1)) || (rc = ensure_graphs(b))) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return rc;
     }
-    e = cudaMemcpyAsync(b->d_units, plans[k].data(), sizeof(SiUnit) * plans[k].size(),
-                        cudaMemcpyHostToDevice, b->st);
-    c.n_units = (int)plans[k].size();
-    for (int rep = 0; rep <= reps && e == cudaSuccess; ++rep) {
-      if (rep == 1) e = cudaEventRecord(e0, b->st);
-      if (e == cudaSuccess)
-        e = b->grp ? launch_grp_prep(b->d_insts, n, c, b->gs, b->st) : launch_si_prep(b->d_insts, n, c, b->st);
-      if (e == cudaSuccess)
-        e = launch_si_batch(b, c);
+    e = cudaGraphLaunch(b->pre, b->st);
+    std::vector<std::vector<SiUnit>> plans(nc);
+    for (int c = 0; c < nc; ++c) plan_units(b->hs.data(), n, b->mixed, b->grp, b->si_grid, cand[c], plans[c]);
+    SiCtl c = b->ctl;
+    c.force_iters = iters;
+    for (int k = 0; k < nc && e == cudaSuccess; ++k) {
+      const int slot = kind * nc + k;
+      int dup = -1;
+      for (int q = 0; q < k; ++q)
+        if (same(plans[q], plans[k])) dup = q;
+      if (dup >= 0) {
+        ms[slot] = ms[kind * nc + dup];
+        continue;
+      }
+      e = cudaMemcpyAsync(b->d_units, plans[k].data(), sizeof(SiUnit) * plans[k].size(),
+                          cudaMemcpyHostToDevice, b->st);
+      c.n_units = (int)plans[k].size();
+      for (int rep = 0; rep <= reps && e == cudaSuccess; ++rep) {
+        if (rep == 1) e = cudaEventRecord(e0, b->st);
+        if (e == cudaSuccess)
+          e = b->grp ? launch_grp_prep(b->d_insts, n, c, b->gs, b->st) : launch_si_prep(b->d_insts, n, c, b->st);
+        if (e == cudaSuccess) e = launch_si_batch(b, c);
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(e1, b->st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float t = 0;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+      ms[slot] = t / reps;
+      if (best < 0 || ms[slot] < ms[best]) best = slot;
     }
-    if (e == cudaSuccess) e = cudaEventRecord(e1, b->st);
-    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-    float t = 0;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
-    ms[k] = t / reps;
-    if (best < 0 || ms[k] < ms[best]) best = k;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (e != cudaSuccess) return fail(DLR_ECUDA, "autotune: %s", cudaGetErrorString(e));
-  if ((rc = set_plan(b, cand[best]))) return rc;
-  tune_table()[batch_shape(hs, n)] = cand[best];
+  const bool grp_best = best >= nc;
+  b->split = cand[best % nc];
+  if ((rc = select_kernel(b, grp_best))) return rc;
+  if ((rc = set_plan(b, cand[best % nc]))) return rc;
+  tune_table()[batch_shape(hs, n)] = TunedPlan{cand[best % nc], grp_best ? 1 : 0};
   for (auto *h : b->hs) {
     int s = 0;
     CK(cudaMemcpy(&s, h->inst.status, sizeof(int), cudaMemcpyDeviceToHost));
@@ -1725,9 +1788,9 @@ int dlr_autotune(dlr_handle *const *hs, int32_t n, int32_t iters, int32_t reps, 
       return fail(s, "autotune: %s", status_name(s));
     }
   }
-  if (chosen) *chosen = cand[best];
+  if (chosen) *chosen = cand[best % nc];
   if (ms_out)
-    for (int k = 0; k < nc; ++k) ms_out[k] = ms[k];
+    for (int k = 0; k < 2 * nc; ++k) ms_out[k] = ms[k];
   return DLR_OK;
 }
 
@@ -1916,7 +1979,8 @@ int dlr_get_stats(dlr_handle *h, dlr_stats *out) {
   out->ms_step_total = h->ms_step;
   out->si_launches = h->si_launches;
   // the grouped source iteration launches three kernels per iteration
-  out->kernel_launches = h->kernel_launches + (h->inst.grp ? 3 * tot : 0);
+  out->kernel_launches = h->kernel_launches + (h->grp_loop ? 3 * tot : 0);
+  out->sweep_grouped = h->grp_loop ? 1 : 0;
   out->nonpositive_cells = np;
   *h->h_status = s;
   return DLR_OK;

@@ -10,7 +10,7 @@ def rel_l2(a, b) -> float:
 
 def run_pair(case, precision, steps, *, orc, dlr, forced=None, si_fixed_iters=0, si_tol=None,
              selection=0, start=None, allow_nonpositive=0, split=None, augment=0, dsa=0,
-             dsa_tol=0.1, dsa_max_iter=500, iters_out=None):
+             dsa_tol=0.1, dsa_max_iter=500, iters_out=None, sweep_mode=0):
     """Runs the oracle and the GPU solver side by side from the same state.
     Returns per-step (T error, psi error, oracle idx, gpu idx) and both states.
     When the GPU picks different angles than the oracle (a near-tie), the
@@ -23,7 +23,7 @@ def run_pair(case, precision, steps, *, orc, dlr, forced=None, si_fixed_iters=0,
         kw["si_fixed_iters"] = si_fixed_iters
     spec = dlr.problem_from_case(case, precision=precision, selection=selection,
                                  allow_nonpositive=allow_nonpositive, augment=augment, dsa=dsa,
-                                 dsa_tol=dsa_tol, dsa_max_iter=dsa_max_iter, **kw)
+                                 dsa_tol=dsa_tol, dsa_max_iter=dsa_max_iter, sweep_mode=sweep_mode, **kw)
     if si_tol is not None:
         spec.si_tol = si_tol
     T = case["T0"].reshape(-1).copy()

@@ -26,7 +26,9 @@ def _run(dlr, case, mode, steps, split=None, fixed=0):
             dlr.set_split([s], split)
         s.step(steps)
         X, S, W = s.factors()
-        return s.T(), X @ S @ W.T, s.stats()
+        st = s.stats()
+        assert st["sweep_grouped"] == (1 if mode == 2 else 0)
+        return s.T(), X @ S @ W.T, st
 
 
 @pytest.mark.parametrize("shape", [(40, 36, 7, 4, 8), (67, 33, 5, 4, 8), (33, 70, 12, 8, 16),
@@ -35,7 +37,7 @@ def _run(dlr, case, mode, steps, split=None, fixed=0):
 def test_grouped_vs_per_angle_kernel(dlr, shape):
     nx, ny, r, npol, naz = shape
     case = workloads.small_case(nx, ny, r, npol, naz, seed=nx + 7 * ny, T0=0.4)
-    Tg, pg, sg = _run(dlr, case, 0, 3, fixed=6)
+    Tg, pg, sg = _run(dlr, case, 2, 3, fixed=6)
     Ta, pa, sa = _run(dlr, case, 1, 3, fixed=6)
     assert sg["si_iters_total"] == sa["si_iters_total"] == 18
     assert rel_l2(Tg, Ta) < 2e-6 and rel_l2(pg, pa) < 2e-6
@@ -46,8 +48,8 @@ def test_grouped_split_plans_bitwise(dlr, split):
     """A plan only changes which CTA sweeps a band: the results are the same
     bit for bit with and without splitting an angle group's bands."""
     case = workloads.lognormal_small(160, ny=200)
-    ref = _run(dlr, case, 0, 2, split=1e9)
-    got = _run(dlr, case, 0, 2, split=split)
+    ref = _run(dlr, case, 2, 2, split=1e9)
+    got = _run(dlr, case, 2, 2, split=split)
     assert np.array_equal(ref[0], got[0]) and np.array_equal(ref[1], got[1])
 
 
@@ -56,9 +58,10 @@ def test_grouped_batch_equals_alone(dlr):
              workloads.lognormal_small(64),
              workloads.small_case(33, 70, 12, 8, 16, seed=3, T0=0.3)]
     import torch
-    alone = [_run(dlr, c, 0, 2) for c in cases]
+    alone = [_run(dlr, c, 2, 2) for c in cases]
     st = torch.cuda.Stream()
-    ss = [dlr.Solver(dlr.problem_from_case(c, precision=dlr.DLR_MIXED), stream=st) for c in cases]
+    ss = [dlr.Solver(dlr.problem_from_case(c, precision=dlr.DLR_MIXED, sweep_mode=2), stream=st)
+          for c in cases]
     try:
         dlr.step_batch(ss, 2)
         for s, (T, p, _) in zip(ss, alone):
@@ -75,6 +78,17 @@ def test_grouped_batch_equals_alone(dlr):
 @pytest.mark.parametrize("shape", [(64, None), (72, 56)])
 def test_grouped_rank32_vs_oracle(orc, dlr, shape):
     case = workloads.lognormal_small(shape[0], ny=shape[1])
-    out, stats = run_pair(case, 1, 3, orc=orc, dlr=dlr)
+    out, stats = run_pair(case, 1, 3, orc=orc, dlr=dlr, sweep_mode=2)
     for k, (eT, ep, oi, gi) in enumerate(out):
         assert eT < 2e-5 and ep < 2e-5, (k, eT, ep)
+
+
+def test_autotune_chooses_between_kernels(dlr):
+    """The autotuner times both source-iteration kernels with every splitting
+    threshold and keeps the fastest; the next step uses its choice."""
+    case = workloads.lognormal_small(160, ny=200)
+    with dlr.Solver(dlr.problem_from_case(case, precision=dlr.DLR_MIXED)) as s:
+        tuned = dlr.autotune([s], iters=2, reps=1)
+        assert all(v > 0 for v in tuned["ms"].values()) and all(v > 0 for v in tuned["ms_grouped"].values())
+        s.step(1)
+        assert s.stats()["sweep_grouped"] == int(tuned["grouped"])
