@@ -144,10 +144,11 @@ class ClockSampler:
 # ---------------------------------------------------------------- CPU
 
 def si_traffic(workload, iters_per_launch):
-    """DRAM bytes (read + write) per k_si launch from the committed ncu capture
-    (profiles/k_si_traffic.json), scaled by this run's source iterations per
-    launch; None when the capture is of another workload or the kernel
-    sources changed since the capture."""
+    """DRAM bytes (read + write) per source-iteration launch from the
+    committed ncu captures (profiles/k_si_traffic.json): bytes per iteration
+    x this run's iterations per launch + the launch's fixed bytes; None when
+    the capture is of another workload or the kernel sources changed since
+    the capture."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "k_si_traffic.json")
     try:
@@ -161,7 +162,7 @@ def si_traffic(workload, iters_per_launch):
                 h.update(f.read())
         if h.hexdigest() != rec["source_sha256"]:
             return None
-        return rec["dram_bytes_per_si_iteration"] * iters_per_launch
+        return rec["dram_bytes_per_si_iteration"] * iters_per_launch + rec.get("dram_bytes_per_launch_fixed", 0.0)
     except (OSError, KeyError, ValueError):
         return None
 
@@ -385,6 +386,7 @@ def run_gpu(args):
     si_ms = s1["ms_si_total"] - s0["ms_si_total"]
     si_launch = s1["si_launches"] - s0["si_launches"]
     launches = s1["kernel_launches"] - s0["kernel_launches"]
+    grouped = bool(s1["sweep_grouped"])
     total_ms, updates_all = reduce_over_ranks(total_ms, updates, dist)
     if clk:
         time.sleep(0.1)
@@ -547,18 +549,21 @@ def run_gpu(args):
         return
 
     hbm, kind = peaks()
-    traffic = si_traffic(args.workload, iters / max(si_launch, 1))
+    si_kernel = ("grouped source iteration (graph loop of k_grp_sweep, k_grp_qsum, k_grp_phi + last sweep)"
+                 if grouped else "k_si<float> (per-angle source iteration)")
+    traffic = si_traffic(args.workload, iters / max(si_launch, 1)) if grouped else None
     r = case["r"]
     bytes_per_update = 4.0 + 16.0 / r  # fixed-source read + amortised per-cell terms (FP32)
     per_launch_ms = si_ms / max(si_launch, 1)
     per_launch_updates = updates / max(si_launch, 1)
     achieved = per_launch_updates * bytes_per_update / (per_launch_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": traffic, "kernel": "k_si_grp",
+                "frac": achieved / hbm, "traffic": traffic, "kernel": si_kernel,
                 "peak_kind": kind, "bytes_per_update": bytes_per_update,
                 "avg_launch_ms": per_launch_ms,
-                "traffic_note": "DRAM bytes per launch from profiles/k_si_traffic.json (ncu capture of the "
-                                "same kernel sources), scaled by this run's iterations per launch"}
+                "traffic_note": "DRAM bytes per launch from profiles/k_si_traffic.json (ncu graph-level "
+                                "captures of the same kernel sources at 2 and 6 iterations), at this "
+                                "run's iterations per launch"}
     cpu, vs_oracle = None, None
     if not args.no_cpu_baseline and world == 1:
         cpu, vs_oracle = cpu_leg(args, dlr, case)
