@@ -60,8 +60,10 @@ def parse():
                     help="CPU work of the oracle sample (checker256 and smaller)")
     ap.add_argument("--cpu-1thread", action="store_true",
                     help="also time the oracle sample on one thread")
-    ap.add_argument("--kernel", default=None, choices=["sweep"],
-                    help="time one kernel alone instead of the DLR step")
+    ap.add_argument("--kernel", default=None, choices=["sweep", "si"],
+                    help="sweep: the hot kernel alone; si: two steps of the workload with the source "
+                         "iteration fixed at --si-iters (a short run for profilers)")
+    ap.add_argument("--si-iters", type=int, default=4, help="--kernel si: source iterations per step")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=["lattice32", "checker256", "lognormal1024", "batch64", "served"])
     ap.add_argument("--requests", type=int, default=200, help="served: number of requests")
@@ -619,6 +621,22 @@ def run_kernel_sweep(args):
                       "ns_per_wavefront_step": ms * 1e6 / (nx + 1.25 * ny)}))
 
 
+def run_kernel_si(args):
+    """Two DLR steps of the workload (mixed precision, splitting threshold 2)
+    with the source iteration fixed at --si-iters iterations: a short,
+    repeatable run for profilers (e.g. ncu --graph-profiling graph)."""
+    import paper_2601_18705_gb300 as dlr
+    case = workloads.CONFIGS[args.workload]()
+    spec = dlr.problem_from_case(case, precision=dlr.DLR_MIXED, si_fixed_iters=args.si_iters)
+    with dlr.Solver(spec) as s:
+        dlr.set_split([s], 2.0)
+        s.step(2)
+        st = s.stats()
+        print(json.dumps({"kernel": "si", "workload": args.workload, "si_iters_per_step": args.si_iters,
+                          "steps": st["steps"], "sweep_grouped": st["sweep_grouped"],
+                          "T_min": float(s.T().min())}))
+
+
 def run_batch64(args):
     """64 independent instances stepped as one batch (one launch per kernel
     per step for all of them), against the plain FP64 path run one instance
@@ -706,6 +724,9 @@ def main():
     args = parse()
     if args.kernel == "sweep":
         run_kernel_sweep(args)
+        return
+    if args.kernel == "si":
+        run_kernel_si(args)
         return
     if args.workload == "batch64" and args.impl != "reference":
         run_batch64(args)
