@@ -45,6 +45,8 @@ template <typename real>
 cudaError_t launch_sweep_dirs(int, int, double, double, int, const double *, const double *,
                               const real *, const real *, real *, int *, cudaStream_t);
 template <typename real> cudaError_t launch_coeff_recon(const Inst *, int, int, int, int, cudaStream_t);
+cudaError_t launch_gram32(const GramJob *, int, int maxblocks, cudaStream_t);
+int gram32_cta_cap();
 template <typename real> cudaError_t launch_tsgram(const GramJob *, int, int, int, cudaStream_t);
 template <typename real> cudaError_t launch_fill(const FillJob *, int, int, cudaStream_t);
 template <typename rin, typename rout>
@@ -141,6 +143,7 @@ struct dlr_handle {
   unsigned version = 0;  // bumped whenever inst changes on the host
   std::vector<double> ox, oy, oz, w;
   int pb = 1;    // partial blocks of the cell reductions
+  int pbg = 1;   // CTAs of the FP32 Grams of step 5
   int pbl = 1;   // partial blocks of the angle reductions
   int lb = 1;    // blocks of the per-angle L-step
   // device counters: [0] total SI iterations
@@ -170,7 +173,7 @@ struct Batch {
   cudaStream_t st = nullptr;
   Inst *d_insts = nullptr;   // contiguous copies of the instances
   void *d_mem = nullptr;     // jobs, units, control
-  int maxN = 0, maxK = 0, rmax = 0, pbmax = 1, pblmax = 1, lbmax = 1;
+  int maxN = 0, maxK = 0, rmax = 0, pbmax = 1, pblmax = 1, lbmax = 1, pbgmax = 1;
   int rmask_pre = 0, rmask = 0;  // rank classes of steps 1-4 and of steps 5-10
   int nx_max = 0, bands_max = 0, si_grid = 0;
   SiCtl ctl{};
@@ -371,6 +374,7 @@ static bool build_X0(const dlr_handle *h, const double *T0, std::vector<double> 
 // ------------------------------------------------------------------
 struct Sizes {
   int N, K, r, pb, pbl, lb;
+  int pbg;  // CTAs (and partials) of the FP32 Grams of step 5 (k_gram32; mixed precision)
   size_t rs;
   size_t partial_doubles;
   size_t total;
@@ -415,6 +419,7 @@ static Sizes sizes_of(const dlr_problem *p, int sms) {
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     s.r = s.K;
     s.pb = s.pbl = s.lb = kCl;
+    s.pbg = 1;
     s.partial_doubles = 0;
     s.total = 5 * al((size_t)s.N * 8) + 6 * al((size_t)s.N * s.rs) + 2 * al((size_t)s.N * s.K * s.rs) +
               3 * al((size_t)s.K * 8) + al((size_t)s.K * 4) + al(64) * 4 + al(sizeof(Inst));
@@ -432,8 +437,16 @@ static Sizes sizes_of(const dlr_problem *p, int sms) {
   s.lb = std::min(2 * sms / kCl * kCl, (std::max(1, (s.K + 3) / 4) + kCl - 1) / kCl * kCl);  // 4 warps, one angle each
   const size_t r1 = s.r;
   const size_t r = p->augment ? 2 * r1 : r1;    // rank of steps 5-10
+  // the FP32 Grams (k_gram32): whole clusters, all resident at once (two
+  // CTAs per SM), at least 2048 rows per CTA
+  {
+    static int gcap = 0;
+    if (!gcap) gcap = std::max(kCl, gram32_cta_cap());
+    s.pbg = std::min(gcap, std::max(kCl, (s.N / 2048) / kCl * kCl));
+  }
   s.partial_doubles = std::max({(size_t)(s.pb / kCl) * proj_count((int)r), (size_t)(s.pb / kCl) * r * r,
-                                (size_t)(s.pbl / kCl) * r * r, (size_t)(s.lb / kCl) * (r * r + r)});
+                                (size_t)(s.pbl / kCl) * r * r, (size_t)(s.lb / kCl) * (r * r + r),
+                                (size_t)(s.pbg / kCl) * r * r});
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
   size_t t = 0;
   t += 5 * al((size_t)s.N * 8);                 // sigma, rho_cv, T, B0, D
@@ -730,6 +743,7 @@ int dlr_create(const dlr_problem *problem, const dlr_runtime *runtime, dlr_handl
   h->pb = sz.pb;
   h->pbl = sz.pbl;
   h->lb = sz.lb;
+  h->pbg = sz.pbg;
   build_quadrature(h);
   if (problem->method == DLR_METHOD_SN) return create_sn(h, problem, out);
   std::vector<double> X0, W0;
@@ -1043,6 +1057,7 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
     b->rmask |= rank_mask(h->aug ? 2 * h->r : h->r);
     b->rmask_pre |= rank_mask(h->r);
     b->pbmax = std::max(b->pbmax, h->pb);
+    b->pbgmax = std::max(b->pbgmax, h->pbg);
     b->pblmax = std::max(b->pblmax, h->pbl);
     b->lbmax = std::max(b->lbmax, h->lb);
     b->nx_max = std::max(b->nx_max, h->prob.nx);
@@ -1205,9 +1220,12 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
       g.out = I.partials; g.nblocks = nb; g.run_if = run_if;
       return g;
     };
-    gp1[i] = gram(I.Psi, nullptr, N, N, 0, h->pb, nullptr);
-    gpre[i] = gram(I.Psi, nullptr, N, N, 0, h->pb, flag + 1);
-    gx[i] = gram(I.X, nullptr, N, N, 0, h->pb, nullptr);
+    // the Grams of step 5: k_gram32 in mixed precision, k_tsgram in FP64
+    // (one partial per cluster either way)
+    const int pbx = h->mixed ? h->pbg : h->pb;
+    gp1[i] = gram(I.Psi, nullptr, N, N, 0, pbx, nullptr);
+    gpre[i] = gram(I.Psi, nullptr, N, N, 0, pbx, flag + 1);
+    gx[i] = gram(I.X, nullptr, N, N, 0, pbx, nullptr);
     gl1[i] = gram(I.L, I.w, K, r, 1, h->pbl, nullptr);
     glf[i] = gram(I.Lf, I.w, K, r, 1, h->pbl, flag + 1);
     gw[i] = gram(I.W0, nullptr, K, K, 0, h->pbl, nullptr);
@@ -1216,7 +1234,7 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
     gcr[i].ldb = K;
     gcr[i].sqrt_wt = 1;
     // the third-pass Grams run only when the first passes were shifted
-    gx3[i] = gram(I.X, nullptr, N, N, 0, h->pb, flag);
+    gx3[i] = gram(I.X, nullptr, N, N, 0, pbx, flag);
     gw3[i] = gram(I.W0, nullptr, K, K, 0, h->pbl, flag);
     auto fill = [&](void *A, const void *src, int m, int lda, int layout) {
       FillJob f{};
@@ -1257,10 +1275,11 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
       return c;
     };
     const int pc = h->pb / kCl, pcl = h->pbl / kCl;  // partials: one per cluster
-    cp1[i] = chol(pc, I.h2, sm + L.R1, 1);
-    cp1b[i] = chol(pc, I.h2, sm + L.R1, 4);
-    cp2[i] = chol(pc, I.h2, sm + L.R2, 2);
-    cp3[i] = chol(pc, I.h2, sm + L.R3, 3);
+    const int pcx = h->mixed ? h->pbg / kCl : pc;      // (k_gram32 in mixed precision)
+    cp1[i] = chol(pcx, I.h2, sm + L.R1, 1);
+    cp1b[i] = chol(pcx, I.h2, sm + L.R1, 4);
+    cp2[i] = chol(pcx, I.h2, sm + L.R2, 2);
+    cp3[i] = chol(pcx, I.h2, sm + L.R3, 3);
     cl1[i] = chol(pcl, 1.0, sm + L.R1, 1);
     cl1b[i] = chol(pcl, 1.0, sm + L.R1, 4);
     cl2[i] = chol(pcl, 1.0, sm + L.R2, 2);
@@ -1381,16 +1400,20 @@ static int enqueue_post(Batch *b) {
   // pass runs when a Cholesky needed a shift.  The augmented step factors
   // [Psi, X0] at rank 2r against the old factors padded to 2r columns.
   if (b->aug) LK(launch_aug_pad(d, n, st));
-  LK(launch_tsgram<real>(b->g_psi1, n, b->pbmax, 0, st));
+  // Grams of step 5 (FP32: k_gram32)
+  auto gram5 = [&](const GramJob *g) {
+    return b->mixed ? launch_gram32(g, n, b->pbgmax, st) : launch_tsgram<real>(g, n, b->pbmax, 0, st);
+  };
+  LK(gram5(b->g_psi1));
   LK(launch_chol(b->c_p1, d, n, st));
   LK(launch_fill<real>(b->f_psi, n, b->maxN, st));
-  LK(launch_tsgram<real>(b->g_psire, n, b->pbmax, 0, st));
+  LK(gram5(b->g_psire));
   LK(launch_chol(b->c_p1b, d, n, st));
   LKM((launch_apply<real, real>(b->a_psi, n, b->maxN, b->rmask, st)), b->rmask);
-  LK(launch_tsgram<real>(b->g_x, n, b->pbmax, 0, st));
+  LK(gram5(b->g_x));
   LK(launch_chol(b->c_p2, d, n, st));
   LKM((launch_apply<real, real>(b->a_x2, n, b->maxN, b->rmask, st)), b->rmask);
-  LK(launch_tsgram<real>(b->g_x3, n, b->pbmax, 0, st));
+  LK(gram5(b->g_x3));
   LK(launch_chol(b->c_p3, d, n, st));
   LKM((launch_apply<real, real>(b->a_x3, n, b->maxN, b->rmask, st)), b->rmask);
   // steps 6-7: projections and the L-step

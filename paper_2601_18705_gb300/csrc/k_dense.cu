@@ -710,6 +710,196 @@ cudaError_t launch_coeff_recon(const Inst *d, int n, int maxN, int rmask, int gr
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
+// ------------------------------------------------------------------
+// Gram of an FP32 column-major m x r matrix (r <= 32, no weights), for the
+// CholeskyQR passes of step 5 in mixed precision: G = sum over rows of
+// a a^T, one FP64 partial per thread-block cluster (both triangles).  Rows stream through a
+// ring of kGS shared-memory stages of kGR rows filled by cp.async (16-byte
+// chunks when lda is a multiple of 4, else 4-byte ones; rows past the CTA's
+// slice are zero-filled), so several rounds are in flight per CTA and two
+// CTAs share an SM.  A stage holds column c at c kGR, its rows rotated by
+// 4 (c / 4 mod 8) so that the 16-byte reads of the eight column quads of a
+// tile row fall in distinct banks.  Products as in k_tsgram: 4 x 4 register
+// tiles on and above the diagonal, FP32 over about 64 rows per thread, then
+// FP64; the CTA's row groups, then the cluster's CTAs (through distributed
+// shared memory, rank order) are summed in a fixed order.  The tiles are
+// packed so that every lane of a warp owns one (a square grid of tiles
+// left the warps below the diagonal two-thirds idle).
+// ------------------------------------------------------------------
+constexpr int kGR = 128, kGS = 4;
+constexpr int gram32_smem_bytes() { return kGS * 32 * kGR * 4; }
+// position of (column c, row q) of a stage
+__device__ __forceinline__ int g32_at(int c, int q) { return c * kGR + ((q + 4 * ((c >> 2) & 7)) & (kGR - 1)); }
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kTB, 2) k_gram32(const GramJob *__restrict__ jobs) {
+  pdl_wait();
+  pdl_trigger();
+  const GramJob J = jobs[blockIdx.y];
+  // nblocks is a multiple of the cluster size and run_if is per job, so
+  // whole clusters leave together
+  if ((int)blockIdx.x >= J.nblocks || (J.run_if && *J.run_if == 0)) return;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char gsm[];
+  float *ring = reinterpret_cast<float *>(gsm);
+  const float *A = as_c<float>(J.A);
+  const int r = J.r, t = threadIdx.x, lda = J.lda;
+  // the 4 x 4 tiles on and above the diagonal, packed: tile u = bj (bj + 1)
+  // / 2 + bi (bi <= bj); kTB / ntile groups of threads split the rows
+  const int side = (r + 3) >> 2, ntile = side * (side + 1) / 2;
+  const int ngroup = kTB / ntile;
+  const int grp = t / ntile, tt = t - grp * ntile;
+  int bj = 0;
+  while ((bj + 1) * (bj + 2) / 2 <= tt) ++bj;
+  const int ti = 4 * (tt - bj * (bj + 1) / 2), tj = 4 * bj;
+  const bool own = grp < ngroup;
+  // slices of a multiple of 4 rows: with lda a multiple of 4 every 16-byte
+  // chunk of a stage starts 16-byte aligned
+  const int per = ((J.m + J.nblocks - 1) / J.nblocks + 3) & ~3;
+  const int row0 = min(J.m, (int)blockIdx.x * per), row1 = min(J.m, row0 + per);
+  const int nround = (row1 - row0 + kGR - 1) / kGR;
+  const bool vec = (lda & 3) == 0 && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
+  auto load = [&](int rd) {
+    float *st = ring + (size_t)(rd % kGS) * 32 * kGR;
+    const int base = row0 + rd * kGR;
+    if (vec) {
+      for (int c = t; c < r * (kGR / 4); c += kTB) {
+        const int i = c / (kGR / 4), q = c - i * (kGR / 4);
+        const int row = base + 4 * q;
+        const int n_ok = max(0, min(4, row1 - row));  // rows of the chunk in the slice
+        // a chunk past the slice reads nothing (zero-filled) from an aligned
+        // address inside the matrix
+        cp_async16(st + g32_at(i, 4 * q), A + (size_t)lda * i + (n_ok > 0 ? row : row0), 4 * n_ok);
+      }
+    } else {
+      for (int c = t; c < r * kGR; c += kTB) {
+        const int i = c / kGR, q = c - i * kGR;
+        const int row = base + q;
+        const bool ok = row < row1;
+        cp_async4(st + g32_at(i, q), A + (size_t)lda * i + (ok ? row : row1 - 1), ok ? 4 : 0);
+      }
+    }
+  };
+  const int flush_every = max(1, 64 * ngroup / kGR);
+  float s[16];
+  double acc[16];
+#pragma unroll
+  for (int e = 0; e < 16; ++e) { s[e] = 0.f; acc[e] = 0.0; }
+#pragma unroll
+  for (int p = 0; p < kGS - 1; ++p) {
+    if (p < nround) load(p);
+    cp_async_commit();
+  }
+  for (int rd = 0; rd < nround; ++rd) {
+    cp_async_wait<kGS - 2>();
+    __syncthreads();  // stage rd has landed; stage rd - 1 is no longer read
+    if (rd + kGS - 1 < nround) load(rd + kGS - 1);
+    cp_async_commit();
+    const float *st = ring + (size_t)(rd % kGS) * 32 * kGR;
+    if (own) {
+      const int nq = (min(kGR, row1 - row0 - rd * kGR) + 3) >> 2;  // quads holding rows
+      for (int q = grp; q < nq; q += ngroup) {
+        Quad<float> a[4], b[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          // columns past r (r not a multiple of 4) read a valid column;
+          // those tile entries are never written out
+          a[k] = *reinterpret_cast<const Quad<float> *>(st + g32_at(min(ti + k, r - 1), 4 * q));
+          b[k] = *reinterpret_cast<const Quad<float> *>(st + g32_at(min(tj + k, r - 1), 4 * q));
+        }
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int m = 0; m < 4; ++m) s[kk * 4 + k] += a[kk].v[m] * b[k].v[m];
+      }
+      if ((rd + 1) % flush_every == 0 || rd + 1 == nround) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) { acc[e] += (double)s[e]; s[e] = 0.f; }
+      }
+    }
+  }
+  cp_async_wait<0>();
+  // groups -> CTA partial in a fixed order, the lower triangle mirrored
+  __syncthreads();
+  double *buf = reinterpret_cast<double *>(gsm);
+  double *part_s = buf + kTB * 16;
+  if (grp < ngroup) {
+#pragma unroll
+    for (int e = 0; e < 16; ++e) buf[t * 16 + e] = acc[e];
+  }
+  __syncthreads();
+  for (int e = t; e < r * r; e += kTB) {
+    int i = e % r, j = e / r;
+    if (i > j) { const int x = i; i = j; j = x; }
+    const int tl = (j >> 2) * ((j >> 2) + 1) / 2 + (i >> 2), comp = (i & 3) * 4 + (j & 3);
+    double v = 0.0;
+    for (int g = 0; g < ngroup; ++g) v += buf[(g * ntile + tl) * 16 + comp];
+    part_s[e] = v;
+  }
+  cluster.sync();
+  // this CTA's share of the cluster sum, CTA partials added in rank order
+  const int rank = (int)cluster.block_rank();
+  const int rr2 = r * r, share = (rr2 + kCl - 1) / kCl;
+  double *out = J.out + (size_t)(blockIdx.x / kCl) * rr2;
+  for (int e = rank * share + t; e < min(rr2, (rank + 1) * share); e += kTB) {
+    double v = 0.0;
+#pragma unroll
+    for (int q = 0; q < kCl; ++q) v += cluster.map_shared_rank(part_s, q)[e];
+    out[e] = v;
+  }
+  cluster.sync();  // peers' shared memory stays valid until every read is done
+}
+
+cudaError_t launch_gram32(const GramJob *d_jobs, int n, int maxblocks, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_gram32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         gram32_smem_bytes());
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  return launch_pdl(k_gram32, dim3(maxblocks, n), dim3(kTB), gram32_smem_bytes(), st, d_jobs);
+}
+
+// CTAs of k_gram32 that can be resident at once (whole clusters), or 0.
+int gram32_cta_cap() {
+  if (cudaFuncSetAttribute(k_gram32, cudaFuncAttributeMaxDynamicSharedMemorySize, gram32_smem_bytes()) !=
+      cudaSuccess)
+    return 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kCl);
+  cfg.blockDim = dim3(kTB);
+  cfg.dynamicSmemBytes = gram32_smem_bytes();
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = kCl;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int c = 0;
+  if (cudaOccupancyMaxActiveClusters(&c, k_gram32, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return c * kCl;
+}
+
 // layout: the (common) layout of the batch's matrices
 template <typename real>
 cudaError_t launch_tsgram(const GramJob *d_jobs, int n, int maxblocks, int layout, cudaStream_t st) {
