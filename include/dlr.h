@@ -134,8 +134,14 @@ typedef struct dlr_problem {
                             reflective; T_edge of that edge is ignored).  A
                             direction entering a reflective edge takes, row by
                             row, the boundary value of its mirror direction
-                            (normal component negated) from the previous
-                            source iteration.  DLR_METHOD_SN only; a
+                            (normal component negated; Section 2.1's general
+                            boundary conditions).  SN: from the previous
+                            source iteration.  DLR: in step 4 the mirror
+                            value interpolated through the chosen angles,
+                            W0(Om_R) What^-1 Psi, from the previous source
+                            iteration; in step 7 the L-step's own boundary
+                            values, by a fixed point (at most 5000 passes,
+                            else DLR_ENOTCONV).  Not with augment = 1; a
                             reflective left or right edge needs n_azim even
                             (the quadrature's mirror map) */
   int32_t sweep_mode;    /* source-iteration kernel of mixed-precision DLR
@@ -184,6 +190,8 @@ typedef struct dlr_stats {
   int32_t sweep_grouped;     /* 1: the last step's source iteration swept two
                                 angles of one quadrant per warp (the grouped
                                 kernel, see sweep_mode); 0: one per warp */
+  int32_t refl_passes_last;  /* fixed-point passes of the last step's L-step
+                                with reflective edges (DLR; else 0) */
 } dlr_stats;
 
 /* Creates a solver: validates sizes, builds the quadrature and the initial

@@ -55,7 +55,8 @@ class DlrStats(C.Structure):
                 ("status", C.c_int32), ("ms_si_total", C.c_double), ("ms_step_total", C.c_double),
                 ("si_launches", C.c_int64), ("kernel_launches", C.c_int64),
                 ("nonpositive_cells", C.c_int64), ("dsa_iters_total", C.c_int64),
-                ("sweep_grouped", C.c_int32)]
+                ("sweep_grouped", C.c_int32),
+                ("refl_passes_last", C.c_int32)]
 
 
 _lib = None

@@ -69,6 +69,9 @@ cudaError_t launch_si_prep(const Inst *, int, SiCtl, cudaStream_t);
 cudaError_t prepare_small(int, int, int);
 cudaError_t launch_aug_pad(const Inst *, int, cudaStream_t);
 cudaError_t launch_aug_trunc(const Inst *, int, cudaStream_t);
+template <typename real> cudaError_t launch_refl_pre(const Inst *, int, int, int, cudaStream_t);
+template <typename real> cudaError_t launch_refl_kap(const Inst *, int, int, int, cudaStream_t);
+template <typename real> cudaError_t launch_refl_lstep(const Inst *, int, cudaStream_t);
 }  // namespace dlr
 
 using namespace dlr;
@@ -186,6 +189,8 @@ struct Batch {
   Inst *d_insts2 = nullptr;   // the instances of steps 5-10 (rank 2r when augmented)
   int sel_slice_max = 1;      // most angles one CTA of the selection cluster owns
   bool lside_fused = false;   // step 8 by the one-cluster kernel (pivoted-QR choice, K <= 1024)
+  bool refl = false;          // some DLR instance has reflective edges (k_reflect.cu)
+  int maxL = 0;               // most boundary entries nx + ny
   bool grp_ok = false;        // every instance can take the grouped sweep (k_sweepg.cu)
   bool grp = false;           // ... and the batch takes it
   int grid_angle = 0, grid_grp = 0;  // CTAs of the per-angle and the grouped sweep
@@ -462,6 +467,11 @@ static Sizes sizes_of(const dlr_problem *p, int sms) {
   t += al(s.partial_doubles * 8);
   t += al(64) * 4 + al(sizeof(Inst));           // status, iters, conv, totals, inst
   if (p->dsa) t += kDsaArrays * al((size_t)s.N * s.rs) + al(64);  // DSA coefficients, CG vectors
+  if (p->reflect[0] || p->reflect[1] || p->reflect[2] || p->reflect[3]) {
+    const size_t LB = (size_t)p->nx + p->ny;
+    t += al(r1 * LB * s.rs) + al(2 * LB * r1 * 8) + al((size_t)s.K * LB * 8) + 2 * al((size_t)s.K * r1 * 8) +
+         al(64);  // boundary sources, What^-1 Psi, boundary values, y_k, u_k, passes
+  }
   if (grp_eligible(p)) {  // skewed inputs and partials of the grouped sweep
     const size_t L = grp_lay(p->nx, p->ny) * 4;
     const size_t ng = grp_count((int)r1);
@@ -511,7 +521,7 @@ static int validate(const dlr_problem *p) {
     if (p->reflect[e] != 0 && p->reflect[e] != 1) return fail(DLR_EINVAL, "reflect[%d] must be 0 or 1", e);
   if (p->sweep_mode < 0 || p->sweep_mode > 2) return fail(DLR_EINVAL, "sweep_mode must be 0, 1 or 2");
   if (p->reflect[0] || p->reflect[1] || p->reflect[2] || p->reflect[3]) {
-    if (!sn) return fail(DLR_EINVAL, "reflective edges are built for DLR_METHOD_SN only");
+    if (p->augment) return fail(DLR_EINVAL, "reflective edges are not built for the augmented step");
     if ((p->reflect[0] || p->reflect[1]) && p->n_azim % 2)
       return fail(DLR_EINVAL, "a reflective left or right edge needs an even n_azim");
   }
@@ -585,6 +595,8 @@ static void fill_common(dlr_handle *h, const dlr_problem *problem) {
   for (int e = 0; e < 4; ++e) I.reflect[e] = problem->reflect[e];
   I.n_azim = problem->n_azim;
   I.refl_base = nullptr;
+  I.refl_kap = I.refl_data = I.refl_y = I.refl_u = nullptr;
+  I.refl_passes = nullptr;
   I.grp = 0;
   I.grp_ng = 0;
   I.grp_tab = nullptr;
@@ -812,6 +824,15 @@ int dlr_create(const dlr_problem *problem, const dlr_runtime *runtime, dlr_handl
   h->d_iters_total = (long long *)A(64);
   I.iters_total = (unsigned long long *)h->d_iters_total;
   alloc_dsa(h, A);
+  if (problem->reflect[0] || problem->reflect[1] || problem->reflect[2] || problem->reflect[3]) {
+    const size_t LB = (size_t)problem->nx + problem->ny;
+    I.refl_base = A((size_t)r * LB * rs);
+    I.refl_kap = (double *)A(2 * LB * r * 8);
+    I.refl_data = (double *)A((size_t)K * LB * 8);
+    I.refl_y = (double *)A((size_t)K * r * 8);
+    I.refl_u = (double *)A((size_t)K * r * 8);
+    I.refl_passes = (int *)A(64);
+  }
   I.grp = grp_eligible(problem) ? 1 : 0;
   I.grp_tab = nullptr;
   I.sgk = I.spk = I.part = I.qsum = nullptr;
@@ -876,6 +897,7 @@ int dlr_create(const dlr_problem *problem, const dlr_runtime *runtime, dlr_handl
   if (h->d_dsa_iters_total) chain(cudaMemsetAsync(h->d_dsa_iters_total, 0, 64, h->st));
   chain(cudaMemsetAsync(I.idx, 0xff, (size_t)r * 4, h->st));
   chain(cudaMemsetAsync(I.small, 0, (size_t)I.lay.total * 8, h->st));
+  if (I.refl_passes) chain(cudaMemsetAsync(I.refl_passes, 0, 64, h->st));
   // the host vectors above are released on return: wait for the copies
   chain(cudaStreamSynchronize(h->st));
   if (e != cudaSuccess) {
@@ -1061,6 +1083,8 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
     b->pblmax = std::max(b->pblmax, h->pbl);
     b->lbmax = std::max(b->lbmax, h->lb);
     b->nx_max = std::max(b->nx_max, h->prob.nx);
+    b->maxL = std::max(b->maxL, h->prob.nx + h->prob.ny);
+    b->refl = b->refl || h->inst.refl_kap != nullptr;
     b->bands_max = std::max(b->bands_max, (h->prob.ny + 31) / 32);
   }
   const int gam_max = b->sn ? b->rmax : kMaxRank;  // scalar-flux weights of k_si
@@ -1267,7 +1291,7 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
     awv[i] = apply(I.W0, 0, K, nullptr, 0, sm + L.V, I.W0, K, I.w, 1, K, nullptr);
     acw[i] = apply(I.W0, 0, K, nullptr, 0, sm + L.V, I.W0, K, nullptr, 0, K, nullptr);
     acx[i] = apply(I.X0, 0, N, nullptr, 0, sm + L.U, I.X0, N, nullptr, 0, N, nullptr);
-    const double u = h->mixed ? 1e-7 : 1e-15, tau = h->mixed ? 1e-10 : 1e-24;
+    const double u = chol_u(h->mixed), tau = chol_tau(h->mixed);
     auto chol = [&](int nparts, double scale, double *R, int mode) {
       CholJob c{};
       c.part = I.partials; c.nblocks = nparts; c.scale = scale; c.R = R;
@@ -1381,6 +1405,10 @@ static int enqueue_pre(Batch *b) {
   }
   LK(launch_select(d, n, b->sel_slice_max, b->st));
   LKM(launch_coeff_recon<real>(d, n, b->maxN, b->rmask_pre, b->grp ? 1 : 0, b->st), b->rmask_pre);
+  if (b->refl) {  // reflective edges: G, H and the first sweeps' inflow (two kernels)
+    LK(launch_refl_pre<real>(d, n, b->rmax, b->maxL, b->st));
+    ++b->kcount;
+  }
   if (b->grp) LK(launch_grp_prep(d, n, b->ctl, b->gs, b->st));
   else LK(launch_si_prep(d, n, b->ctl, b->st));
   return DLR_OK;
@@ -1400,6 +1428,7 @@ static int enqueue_post(Batch *b) {
   // pass runs when a Cholesky needed a shift.  The augmented step factors
   // [Psi, X0] at rank 2r against the old factors padded to 2r columns.
   if (b->aug) LK(launch_aug_pad(d, n, st));
+  if (b->refl) LK(launch_refl_kap<real>(d, n, b->rmax, b->maxL, st));  // What^-1 Psi at reflective edges
   // Grams of step 5 (FP32: k_gram32)
   auto gram5 = [&](const GramJob *g) {
     return b->mixed ? launch_gram32(g, n, b->pbgmax, st) : launch_tsgram<real>(g, n, b->pbmax, 0, st);
@@ -1422,6 +1451,7 @@ static int enqueue_post(Batch *b) {
   LK(launch_proj_post(d, n, st));
   LKM(launch_lstep(d, n, b->rmax, b->rmask, b->lbmax, b->maxK, st), b->rmask);
   b->kcount += 2;  // and two more kernels
+  if (b->refl) LK(launch_refl_lstep<real>(d, n, st));  // the reflected inflow's fixed point
   // step 8: CholeskyQR of M = diag(sqrt w) L^T into Q (held in W0), S = M^T Q,
   // SVD of S, W0 <- diag(1/sqrt w) Q V
   if (b->lside_fused) {
@@ -2005,6 +2035,9 @@ int dlr_get_stats(dlr_handle *h, dlr_stats *out) {
   out->kernel_launches = h->kernel_launches + (h->grp_loop ? 3 * tot : 0);
   out->sweep_grouped = h->grp_loop ? 1 : 0;
   out->nonpositive_cells = np;
+  int rp = 0;
+  if (h->inst.refl_passes) CK(cudaMemcpy(&rp, h->inst.refl_passes, sizeof rp, cudaMemcpyDeviceToHost));
+  out->refl_passes_last = rp;
   *h->h_status = s;
   return DLR_OK;
 }

@@ -37,12 +37,13 @@ constexpr int kENonPos = -6;
 
 // Offsets (in doubles) of the r x r work matrices inside Inst::small.
 struct SmallLayout {
-  int What, WLU, beta, gamma, C0;      // angle selection
+  int What, Winv, beta, gamma, C0;     // angle selection
   int R1, R2, R3;                      // CholeskyQR factors
   int qr_flag;    // ints: [0] third pass needed, [1] filled columns, [2..] mask
   int G, Nx, Ny, Mt, Ms, P, vec;       // projections (vec: qh, bL, bR, bB, bT)
   int Axp, Axm, Ayp, Aym, PS0;         // L-step operators
   int Cbar, zeta, Lbar, tvec;          // C-bar device
+  int RGx, RGy, RHx, RHy;              // reflective edges (DLR)
   int U, V, sv, vphi, Sn, Tr;          // SVD of S and temperature vector
   int total;
 };
@@ -51,16 +52,29 @@ inline SmallLayout small_layout(int r) {
   SmallLayout s;
   int o = 0;
   auto m = [&](int n) { int at = o; o += n; return at; };
-  s.What = m(r * r); s.WLU = m(r * r); s.beta = m(r); s.gamma = m(r); s.C0 = m(r * r);
+  s.What = m(r * r); s.Winv = m(r * r); s.beta = m(r); s.gamma = m(r); s.C0 = m(r * r);
   s.R1 = m(r * r); s.R2 = m(r * r); s.R3 = m(r * r); s.qr_flag = m(20);
   s.G = m(r * r); s.Nx = m(r * r); s.Ny = m(r * r); s.Mt = m(r * r); s.Ms = m(r * r);
   s.P = m(r * r); s.vec = m(5 * r);
   s.Axp = m(r * r); s.Axm = m(r * r); s.Ayp = m(r * r); s.Aym = m(r * r); s.PS0 = m(r * r);
   s.Cbar = m(r * r); s.zeta = m(r); s.Lbar = m(r); s.tvec = m(r);
+  s.RGx = m(r * r); s.RGy = m(r * r); s.RHx = m(r * r); s.RHy = m(r * r);
   s.U = m(r * r); s.V = m(r * r); s.sv = m(r); s.vphi = m(r); s.Sn = m(r * r); s.Tr = m(r * r);
   s.total = o;
   return s;
 }
+
+// Thresholds of the CholeskyQR passes (chol_core.cuh).  u: a pivot below
+// u tr(G) needs a shift.  tau: in the first pass, a column whose residual^2
+// is below tau |column|^2 is dependent and replaced by an orthonormal
+// completion.  The Gram resolves a residual^2 only to a few ulps of
+// |column|^2, so in FP64 tau sits above that level (1e-14, about 45 ulps: a
+// column within about 1e-7 of the span of the previous ones, e.g. the
+// collocation fluxes of an exactly isotropic state, counts as dependent).  In
+// mixed precision the FP32 Grams resolve only about 1e-6, which would also
+// catch genuine columns at rank 32; tau stays at 1e-10 there.
+__host__ __device__ inline double chol_u(bool mixed) { return mixed ? 1e-7 : 1e-15; }
+__host__ __device__ inline double chol_tau(bool mixed) { return mixed ? 1e-10 : 1e-14; }
 
 // Number of doubles one block writes for each reduction kind.
 // (six r x r matrices G, Nx, Ny, Mt, Ms, P and five r-vectors per block)
@@ -137,6 +151,19 @@ struct Inst {
   int reflect[4];
   int n_azim;
   void *refl_base;
+  // reflective edges of a DLR instance (reading R19; refl_base then holds
+  // r x (ny + nx) entries, one per chosen angle j).  In the source iteration
+  // the inflow of chosen angle j through a reflective edge is its mirror
+  // angle's value interpolated through the chosen angles, G Psi(c) with
+  // G = W0(Om_R(idx)) What^{-1} (small: RGx, RGy; RHx, RHy = C0 G^T give it
+  // from X0 in the first sweeps).  Step 7 solves its reflected inflow by a
+  // fixed point on the boundary values: refl_kap (FP64, (2 ny + 2 nx) x r)
+  // What^{-1} Psi(c) of the boundary cells (left, right, bottom, top),
+  // refl_data (FP64, K x (ny + nx)) the boundary value of each (angle,
+  // entry), refl_y and refl_u (FP64, K x r) B_k^{-1} Q_k and B_k^{-1}
+  // g_k, refl_passes the fixed-point passes of the last step.
+  double *refl_kap, *refl_data, *refl_y, *refl_u;
+  int *refl_passes;
   // grouped-angle sweep (mixed-precision DLR instances without DSA or
   // reflective edges, grp = 1): the chosen angles are grouped by quadrant
   // (kGA per group, table grp_tab of grp_ng records, ordered by quadrant),
@@ -480,27 +507,42 @@ struct ReflGeom {
   }
 };
 
+// The reflected inflow of swept angle j (quadrature angle k) in boundary
+// cell c through its x-edge (axis 0) or y-edge (axis 1), from the sweeps'
+// output psi (N x r): full-rank SN takes the mirror direction's own value
+// (reading R18); DLR interpolates the mirror angle through the chosen ones,
+// sum_m G_jm Psi(c, m) with G = RGx or RGy (reading R19).
+template <typename real>
+__device__ __forceinline__ real refl_in(const Inst &I, const real *psi, int j, int k, int c, int axis) {
+  if (!I.refl_kap) return psi[(size_t)I.N * mirror_angle(k, I.n_azim, axis) + c];
+  const double *G = I.small + (axis == 0 ? I.lay.RGx : I.lay.RGy);
+  real v = real(0);
+  for (int m = 0; m < I.r; ++m) v = fmadd(real(G[j + I.r * m]), psi[(size_t)I.N * m + c], v);
+  return v;
+}
+
 // Entry e of refl_base (see Inst): the fixed source of its boundary cell
-// plus the reflected inflow term(s) from psi (N x K) of the mirror
-// directions, written to s0.  The corner cell of two reflective edges is
-// written by its x-edge entry only.
+// plus the reflected inflow term(s) from psi (N x r) of the swept angles,
+// written to s0.  The corner cell of two reflective edges is written by its
+// x-edge entry only.
 template <typename real>
 __device__ __forceinline__ void refl_inject(const Inst &I, const real *psi, int e) {
-  const int L = I.ny + I.nx, k = e / L, o = e - k * L;
+  const int L = I.ny + I.nx, j = e / L, o = e - j * L;
+  const int k = I.refl_kap ? I.idx[j] : j;
   const ReflGeom<real> G(I, k);
-  const real *base = as_c<real>(I.refl_base) + (size_t)k * L;
-  real *s0 = as<real>(I.s0) + (size_t)I.N * k;
+  const real *base = as_c<real>(I.refl_base) + (size_t)j * L;
+  real *s0 = as<real>(I.s0) + (size_t)I.N * j;
   if (o < I.ny) {
     if (!G.rx) return;
     const int c = o * I.nx + G.bx;
-    real v = fmadd(G.ax, psi[(size_t)I.N * mirror_angle(k, I.n_azim, 0) + c], base[o]);
-    if (G.ry && o == G.by) v = fmadd(G.ay, psi[(size_t)I.N * mirror_angle(k, I.n_azim, 1) + c], v);
+    real v = fmadd(G.ax, refl_in<real>(I, psi, j, k, c, 0), base[o]);
+    if (G.ry && o == G.by) v = fmadd(G.ay, refl_in<real>(I, psi, j, k, c, 1), v);
     s0[c] = v;
   } else {
     const int ix = o - I.ny;
     if (!G.ry || (G.rx && ix == G.bx)) return;
     const int c = G.by * I.nx + ix;
-    s0[c] = fmadd(G.ay, psi[(size_t)I.N * mirror_angle(k, I.n_azim, 1) + c], base[o]);
+    s0[c] = fmadd(G.ay, refl_in<real>(I, psi, j, k, c, 1), base[o]);
   }
 }
 

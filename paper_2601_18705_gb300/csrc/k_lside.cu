@@ -70,7 +70,7 @@ k_lside(const Inst *__restrict__ insts, int slice_max) {
   double *sw = Q + slice_max * r;   // sqrt(w_k)
   __shared__ double part[32 * 32 + 32], G[32 * 32 + 32], R[32 * 32], dg[32];
   __shared__ CholScratch cs;
-  const double u = I.precision == 1 ? 1e-7 : 1e-15, tau = I.precision == 1 ? 1e-10 : 1e-24;
+  const double u = chol_u(I.precision == 1), tau = chol_tau(I.precision == 1);
   for (int c = t; c < ns; c += blockDim.x) sw[c] = sqrt(I.w[k0 + c]);
   __syncthreads();
   for (int e = t; e < ns * r; e += blockDim.x) {

@@ -442,6 +442,10 @@ __device__ __forceinline__ AngleOps angle_ops(const Inst &I, const double *sm, i
   o.aoy = fabs(oy);
   o.px = ox > 0 ? I.psi_edge[0] : (ox < 0 ? I.psi_edge[1] : 0.0);
   o.py = oy > 0 ? I.psi_edge[2] : (oy < 0 ? I.psi_edge[3] : 0.0);
+  // a reflective edge's inflow is not prescribed: it enters through the
+  // fixed point of k_refl_lstep (reading R19)
+  if (I.reflect[ox > 0 ? 0 : 1]) o.px = 0.0;
+  if (I.reflect[oy > 0 ? 2 : 3]) o.py = 0.0;
   (void)L;
   return o;
 }
@@ -647,6 +651,7 @@ __global__ void __launch_bounds__(256) k_lstep_back(const Inst *__restrict__ ins
   pdl_wait();
   pdl_trigger();
   const Inst &I = insts[blockIdx.y];
+  if (I.refl_kap) return;  // reflective edges: k_refl_lstep forms L
   const int r = I.r, K = I.K;
   __shared__ double tv[32];
   if (threadIdx.x < r) tv[threadIdx.x] = I.small[I.lay.tvec + threadIdx.x];

@@ -658,7 +658,7 @@ k_si(const Inst *__restrict__ insts, SiCtl ctl) {
       }
       if (I.refl_base) {
         // reflective edges: the next sweeps' inflow from these sweeps
-        const int ne = I.K * (I.ny + I.nx);
+        const int ne = I.r * (I.ny + I.nx);
         for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x)
           refl_inject<real>(I, psi, e);
       }

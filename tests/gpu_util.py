@@ -10,7 +10,7 @@ def rel_l2(a, b) -> float:
 
 def run_pair(case, precision, steps, *, orc, dlr, forced=None, si_fixed_iters=0, si_tol=None,
              selection=0, start=None, allow_nonpositive=0, split=None, augment=0, dsa=0,
-             dsa_tol=0.1, dsa_max_iter=500, iters_out=None, sweep_mode=0):
+             dsa_tol=0.1, dsa_max_iter=500, iters_out=None, sweep_mode=0, reflect=None):
     """Runs the oracle and the GPU solver side by side from the same state.
     Returns per-step (T error, psi error, oracle idx, gpu idx) and both states.
     When the GPU picks different angles than the oracle (a near-tie), the
@@ -19,6 +19,9 @@ def run_pair(case, precision, steps, *, orc, dlr, forced=None, si_fixed_iters=0,
     p = oracle_problem(case)
     p.dsa, p.dsa_tol, p.dsa_max_iter = dsa, dsa_tol, dsa_max_iter
     kw = {}
+    if reflect is not None:
+        p.reflect = reflect
+        kw["reflect"] = reflect
     if si_fixed_iters:
         kw["si_fixed_iters"] = si_fixed_iters
     spec = dlr.problem_from_case(case, precision=precision, selection=selection,
