@@ -159,6 +159,16 @@ typedef struct dlr_problem {
                             more); 1 = per-angle; 2 = grouped where the
                             problem qualifies.  Both give the same step to
                             FP32 rounding */
+  int32_t element;       /* spatial elements (Section 4.4).  0 = piecewise
+                            constant (DG0) cells; 1 = bilinear (Q1) upwind
+                            DG with the Legendre basis 1, xi, eta, xi eta per
+                            cell: psi, X and phi then have 4 coefficients per
+                            cell (X is 4 nx ny x r, row 4 c + m, orthonormal
+                            in the Q1 L2 inner product), T and the materials
+                            stay per cell and the temperature update takes
+                            the cell average.  Q1 needs precision = DLR_FP64,
+                            the pivoted-QR angle choice, and neither DSA,
+                            reflective edges nor the augmented step */
 } dlr_problem;
 
 /* Device memory and stream supplied by the caller (e.g. PyTorch). */

@@ -58,6 +58,7 @@ class ProblemSpec:
     dsa_max_iter: int = 0    # CG cap per solve (0: 3)
     reflect: tuple = (0, 0, 0, 0)  # reflective edges L, R, B, T (full-rank SN only)
     sweep_mode: int = 0      # mixed DLR source iteration: 0 autotuned, 1 one angle per warp, 2 grouped
+    element: int = 0         # 0 DG0 cells, 1 bilinear (Q1) elements (4 coefficients per cell)
 
     def cstruct(self):
         keep = [_f64(self.sigma), _f64(self.rho_cv), _f64(self.T0)]
@@ -82,6 +83,7 @@ class ProblemSpec:
         for e in range(4):
             p.reflect[e] = int(self.reflect[e])
         p.sweep_mode = int(self.sweep_mode)
+        p.element = int(self.element)
         return p, keep
 
 
@@ -152,6 +154,8 @@ class Solver:
         self.K = spec.n_polar * spec.n_azim
         self.sn = spec.method == DLR_METHOD_SN
         self.r = self.K if self.sn else spec.rank
+        # rows of X and psi: one per cell, four (Legendre coefficients) on bilinear elements
+        self.rows = self.N * (4 if getattr(spec, "element", 0) == 1 else 1)
         self.stream = stream if stream is not None else torch.cuda.Stream()
         rt = _lib.DlrRuntime()
         rt.stream = C.c_void_p(self.stream.cuda_stream)
@@ -205,7 +209,7 @@ class Solver:
             check(load().dlr_set_T(self.h, a.ctypes.data, 0))
 
     def factors(self):
-        X = np.empty((self.N, self.r), order="F")
+        X = np.empty((self.rows, self.r), order="F")
         S = np.empty((self.r, self.r), order="F")
         W = np.empty((self.K, self.r), order="F")
         r = C.c_int32()
@@ -217,23 +221,24 @@ class Solver:
         X = np.asfortranarray(X, dtype=np.float64)
         S = np.asfortranarray(S, dtype=np.float64)
         W = np.asfortranarray(W, dtype=np.float64)
-        assert X.shape == (self.N, self.r) and S.shape == (self.r, self.r) and W.shape == (self.K, self.r)
+        assert X.shape == (self.rows, self.r) and S.shape == (self.r, self.r) and W.shape == (self.K, self.r)
         check(load().dlr_set_factors(self.h, X.ctypes.data, S.ctypes.data, W.ctypes.data, 0))
 
     def psi(self) -> np.ndarray:
-        """psi (Nx x NOm): the full-rank state of an SN instance, or X S W^T
+        """psi (rows x NOm; rows = Nx, or 4 Nx Legendre coefficients on
+        bilinear elements): the full-rank state of an SN instance, or X S W^T
         from the current factors of a DLR instance."""
         if self.sn:
-            out = np.empty((self.N, self.K), order="F")
+            out = np.empty((self.rows, self.K), order="F")
             check(load().dlr_get_psi(self.h, out.ctypes.data, 0))
             return out
         X, S, W = self.factors()
         return X @ S @ W.T
 
     def set_psi(self, psi) -> None:
-        """Replaces the angular flux of an SN instance (Nx x NOm)."""
+        """Replaces the angular flux of an SN instance (rows x NOm)."""
         a = np.asfortranarray(psi, dtype=np.float64)
-        assert a.shape == (self.N, self.K)
+        assert a.shape == (self.rows, self.K)
         check(load().dlr_set_psi(self.h, a.ctypes.data, 0))
 
     def quadrature(self):

@@ -37,7 +37,8 @@ class DlrProblem(C.Structure):
                 ("allow_nonpositive", C.c_int32), ("method", C.c_int32),
                 ("sigma_texp", C.c_double), ("cv_texp", C.c_double), ("T_ref", C.c_double),
                 ("dsa", C.c_int32), ("dsa_tol", C.c_double), ("dsa_max_iter", C.c_int32),
-                ("reflect", C.c_int32 * 4), ("sweep_mode", C.c_int32)]
+                ("reflect", C.c_int32 * 4), ("sweep_mode", C.c_int32),
+                ("element", C.c_int32)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)

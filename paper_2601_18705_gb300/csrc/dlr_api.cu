@@ -72,6 +72,14 @@ cudaError_t launch_aug_trunc(const Inst *, int, cudaStream_t);
 template <typename real> cudaError_t launch_refl_pre(const Inst *, int, int, int, cudaStream_t);
 template <typename real> cudaError_t launch_refl_kap(const Inst *, int, int, int, cudaStream_t);
 template <typename real> cudaError_t launch_refl_lstep(const Inst *, int, cudaStream_t);
+cudaError_t launch_q1_coeff(const Inst *, int, int, bool, cudaStream_t);
+size_t q1_si_smem(int, int, int, int);
+int q1_si_max_grid(int, int, int, int);
+cudaError_t launch_q1_si(const Inst *, const SiCtl &, int, cudaStream_t);
+cudaError_t launch_q1_transport(const Inst *, int, int, int, cudaStream_t);
+cudaError_t launch_q1_vec(const Inst *, int, cudaStream_t);
+cudaError_t launch_q1_tupdate(const Inst *, int, int, bool, cudaStream_t);
+cudaError_t launch_q1_rescale(double *, size_t, int, int, cudaStream_t);
 }  // namespace dlr
 
 using namespace dlr;
@@ -190,6 +198,10 @@ struct Batch {
   int sel_slice_max = 1;      // most angles one CTA of the selection cluster owns
   bool lside_fused = false;   // step 8 by the one-cluster kernel (pivoted-QR choice, K <= 1024)
   bool refl = false;          // some DLR instance has reflective edges (k_reflect.cu)
+  bool q1 = false;            // a batch of bilinear-element instances (k_q1.cu)
+  int maxRows = 0;            // most rows of X (4 N with Q1 elements)
+  GramJob *g_q1t = nullptr;   // Q1: X^T (T X) per axis direction (4 n), then M_t, M_s, P (3 n)
+  ReduceJob *r_q1 = nullptr;  // Q1: the seven reductions (7 n)
   int maxL = 0;               // most boundary entries nx + ny
   bool grp_ok = false;        // every instance can take the grouped sweep (k_sweepg.cu)
   bool grp = false;           // ... and the batch takes it
@@ -328,8 +340,9 @@ static bool build_W0(const dlr_handle *h, std::vector<double> &W) {
 // cos(pi k x^) cos(pi l y^), (k, l) != (0, 0) in (k + l, k) order, reflected
 // by the Householder map that swaps the constant mode and f / |f|, which
 // keeps them orthonormal and orthogonal to f.  All in the h^2 inner product.
-static bool build_X0(const dlr_handle *h, const double *T0, std::vector<double> &X, double &fn) {
-  const int nx = h->prob.nx, ny = h->prob.ny, N = h->N, r = h->r;
+// r columns (at most N).
+static bool build_X0(const dlr_handle *h, const double *T0, int r, std::vector<double> &X, double &fn) {
+  const int nx = h->prob.nx, ny = h->prob.ny, N = h->N;
   const double hx = h->prob.lx / nx, hy = h->prob.ly / ny, h2 = hx * hy;
   X.assign((size_t)N * r, 0.0);
   std::vector<double> f(N), u(N, 1.0 / std::sqrt(h->prob.lx * h->prob.ly)), v(N);
@@ -431,6 +444,8 @@ static Sizes sizes_of(const dlr_problem *p, int sms) {
     if (p->dsa) s.total += kDsaArrays * al((size_t)s.N * s.rs) + al(64);
     if (p->reflect[0] || p->reflect[1] || p->reflect[2] || p->reflect[3])
       s.total += al((size_t)s.K * (p->nx + p->ny) * s.rs);  // boundary sources of reflective edges
+    if (p->element == 1)  // Q1: psi, s0 and phi with 4 coefficients per cell
+      s.total += 2 * al((size_t)3 * s.N * s.K * 8) + 2 * al((size_t)3 * s.N * 8);
     return s;
   }
   // CTAs of the cell and angle reductions: whole clusters of kCl CTAs,
@@ -451,7 +466,8 @@ static Sizes sizes_of(const dlr_problem *p, int sms) {
   }
   s.partial_doubles = std::max({(size_t)(s.pb / kCl) * proj_count((int)r), (size_t)(s.pb / kCl) * r * r,
                                 (size_t)(s.pbl / kCl) * r * r, (size_t)(s.lb / kCl) * (r * r + r),
-                                (size_t)(s.pbg / kCl) * r * r});
+                                (size_t)(s.pbg / kCl) * r * r,
+                                p->element == 1 ? (size_t)7 * (s.pb / kCl) * r * r : (size_t)0});
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
   size_t t = 0;
   t += 5 * al((size_t)s.N * 8);                 // sigma, rho_cv, T, B0, D
@@ -467,6 +483,9 @@ static Sizes sizes_of(const dlr_problem *p, int sms) {
   t += al(s.partial_doubles * 8);
   t += al(64) * 4 + al(sizeof(Inst));           // status, iters, conv, totals, inst
   if (p->dsa) t += kDsaArrays * al((size_t)s.N * s.rs) + al(64);  // DSA coefficients, CG vectors
+  if (p->element == 1)  // Q1: X0, X, Psi, s0, phi with 4 rows per cell, Gram weights, T X
+    t += 3 * al((size_t)3 * s.N * r * 8) + al((size_t)3 * s.N * r1 * 8) + 2 * al((size_t)3 * s.N * 8) +
+         2 * al((size_t)4 * s.N * 8) + al((size_t)4 * s.N * r * 8);
   if (p->reflect[0] || p->reflect[1] || p->reflect[2] || p->reflect[3]) {
     const size_t LB = (size_t)p->nx + p->ny;
     t += al(r1 * LB * s.rs) + al(2 * LB * r1 * 8) + al((size_t)s.K * LB * 8) + 2 * al((size_t)s.K * r1 * 8) +
@@ -503,8 +522,9 @@ static int validate(const dlr_problem *p) {
     return fail(DLR_EINVAL, "material exponents and T_ref must be finite");
   const bool sn = p->method == DLR_METHOD_SN;
   if (sn && N * K > (1ll << 34)) return fail(DLR_EINVAL, "nx*ny*NOm too large for a full-rank state");
-  if (!sn && (p->rank < 1 || p->rank > kMaxRank || p->rank > N || p->rank > K))
-    return fail(DLR_EINVAL, "rank must satisfy 1 <= r <= min(%d, nx*ny, NOm)", kMaxRank);
+  const long long rows = p->element == 1 ? 4 * N : N;  // rows of X (Q1: 4 coefficients per cell)
+  if (!sn && (p->rank < 1 || p->rank > kMaxRank || p->rank > rows || p->rank > K))
+    return fail(DLR_EINVAL, "rank must satisfy 1 <= r <= min(%d, rows of X, NOm)", kMaxRank);
   if (!(p->dt > 0) || !(p->c > 0) || !(p->a_rad >= 0)) return fail(DLR_EINVAL, "dt, c must be > 0, a_rad >= 0");
   if (p->precision != DLR_FP64 && p->precision != DLR_MIXED) return fail(DLR_EINVAL, "bad precision");
   if (p->selection != DLR_SEL_QDEIM && p->selection != DLR_SEL_DEIM) return fail(DLR_EINVAL, "bad selection");
@@ -520,6 +540,14 @@ static int validate(const dlr_problem *p) {
   for (int e = 0; e < 4; ++e)
     if (p->reflect[e] != 0 && p->reflect[e] != 1) return fail(DLR_EINVAL, "reflect[%d] must be 0 or 1", e);
   if (p->sweep_mode < 0 || p->sweep_mode > 2) return fail(DLR_EINVAL, "sweep_mode must be 0, 1 or 2");
+  if (p->element != 0 && p->element != 1) return fail(DLR_EINVAL, "element must be 0 or 1");
+  if (p->element == 1) {
+    if (p->precision != DLR_FP64) return fail(DLR_EINVAL, "bilinear elements need precision DLR_FP64");
+    if (p->dsa || p->augment || p->reflect[0] || p->reflect[1] || p->reflect[2] || p->reflect[3])
+      return fail(DLR_EINVAL, "bilinear elements: no DSA, augmented step or reflective edges");
+    if (!sn && p->selection != DLR_SEL_QDEIM)
+      return fail(DLR_EINVAL, "bilinear elements need the pivoted-QR angle choice");
+  }
   if (p->reflect[0] || p->reflect[1] || p->reflect[2] || p->reflect[3]) {
     if (p->augment) return fail(DLR_EINVAL, "reflective edges are not built for the augmented step");
     if ((p->reflect[0] || p->reflect[1]) && p->n_azim % 2)
@@ -540,6 +568,8 @@ static int validate(const dlr_problem *p) {
   const size_t need = p->precision == DLR_MIXED ? si_smem_bytes<float>(p->nx, (p->ny + 31) / 32, 256, gam, p->dsa)
                                                 : si_smem_bytes<double>(p->nx, (p->ny + 31) / 32, 256, gam, p->dsa);
   if (optin > 0 && need > (size_t)optin) return fail(DLR_EINVAL, "nx = %d too large for the sweep's shared memory", p->nx);
+  if (p->element == 1 && optin > 0 && q1_si_smem(p->nx, (p->ny + 31) / 32, 256, gam) > (size_t)optin)
+    return fail(DLR_EINVAL, "nx = %d too large for the bilinear sweep's shared memory", p->nx);
   return DLR_OK;
 }
 
@@ -597,6 +627,8 @@ static void fill_common(dlr_handle *h, const dlr_problem *problem) {
   I.refl_base = nullptr;
   I.refl_kap = I.refl_data = I.refl_y = I.refl_u = nullptr;
   I.refl_passes = nullptr;
+  I.q1 = problem->element == 1 ? 1 : 0;
+  I.q1_wt = I.q1_ws = I.q1_v = nullptr;
   I.grp = 0;
   I.grp_ng = 0;
   I.grp_tab = nullptr;
@@ -644,11 +676,12 @@ static int create_sn(dlr_handle *h, const dlr_problem *problem, dlr_handle **out
   I.sig_t = A((size_t)N * rs);
   I.ss4 = A((size_t)N * rs);
   I.q = A((size_t)N * rs);
-  I.phi0 = A((size_t)N * rs);
-  I.phi1 = A((size_t)N * rs);
+  const size_t rowsN = I.q1 ? (size_t)4 * N : (size_t)N;  // Q1: 4 coefficients per cell
+  I.phi0 = A(rowsN * rs);
+  I.phi1 = A(rowsN * rs);
   I.sphi = A((size_t)N * rs);
-  I.Psi = A((size_t)N * K * rs);
-  I.s0 = A((size_t)N * K * rs);
+  I.Psi = A(rowsN * K * rs);
+  I.s0 = A(rowsN * K * rs);
   if (I.reflect[0] || I.reflect[1] || I.reflect[2] || I.reflect[3])
     I.refl_base = A((size_t)K * (problem->nx + problem->ny) * rs);
   double *dox = (double *)A((size_t)K * 8), *doy = (double *)A((size_t)K * 8), *dw = (double *)A((size_t)K * 8);
@@ -697,9 +730,18 @@ static int create_sn(dlr_handle *h, const dlr_problem *problem, dlr_handle **out
   chain(cudaMemsetAsync(I.iters, 0, 64, h->st));
   chain(cudaMemsetAsync(h->d_iters_total, 0, 64, h->st));
   if (h->d_dsa_iters_total) chain(cudaMemsetAsync(h->d_dsa_iters_total, 0, 64, h->st));
-  if (e == cudaSuccess)
+  std::vector<double> psi_q1;
+  if (I.q1) {
+    // psi0 = B(T0) isotropic: each cell's constant coefficient, slopes zero
+    psi_q1.assign(rowsN * K, 0.0);
+    for (int k = 0; k < K; ++k)
+      for (int c = 0; c < N; ++c)
+        psi_q1[(size_t)4 * c + rowsN * k] = planck(problem->a_rad, problem->c, problem->T0[c]);
+    chain(up(I.Psi, psi_q1.data(), psi_q1.size() * 8));
+  } else if (e == cudaSuccess) {
     e = h->mixed ? launch_sn_init<float>(I.Psi, I.T, N, K, problem->a_rad, problem->c, h->st)
                  : launch_sn_init<double>(I.Psi, I.T, N, K, problem->a_rad, problem->c, h->st);
+  }
   chain(cudaStreamSynchronize(h->st));
   if (e != cudaSuccess) {
     std::string msg = cudaGetErrorString(e);
@@ -760,7 +802,9 @@ int dlr_create(const dlr_problem *problem, const dlr_runtime *runtime, dlr_handl
   if (problem->method == DLR_METHOD_SN) return create_sn(h, problem, out);
   std::vector<double> X0, W0;
   double fn = 0.0;
-  if (!build_W0(h, W0) || !build_X0(h, problem->T0, X0, fn)) {
+  // bilinear elements: at most N DG0 modes, the rest of X0 on the slopes
+  const int rx = problem->element == 1 ? std::min(h->r, h->N) : h->r;
+  if (!build_W0(h, W0) || !build_X0(h, problem->T0, rx, X0, fn)) {
     delete h;
     return fail(DLR_EINVAL, "rank %d exceeds the independent initial basis functions", h->r);
   }
@@ -793,10 +837,18 @@ int dlr_create(const dlr_problem *problem, const dlr_runtime *runtime, dlr_handl
   const bool aug = problem->augment == 1;
   const int m = aug ? 2 * r : r;
   h->aug = aug;
-  I.X0 = A((size_t)N * m * rs);
-  I.X = A((size_t)N * m * rs);
-  I.Psi = A((size_t)N * m * rs);
-  I.s0 = A((size_t)N * r * rs);
+  const size_t rowsN = I.q1 ? (size_t)4 * N : (size_t)N;  // rows of X (Q1: 4 per cell)
+  if (I.q1) {
+    I.phi0 = A(rowsN * rs);
+    I.phi1 = A(rowsN * rs);
+    I.q1_wt = (double *)A(rowsN * 8);
+    I.q1_ws = (double *)A(rowsN * 8);
+    I.q1_v = (double *)A(rowsN * r * 8);
+  }
+  I.X0 = A(rowsN * m * rs);
+  I.X = A(rowsN * m * rs);
+  I.Psi = A(rowsN * m * rs);
+  I.s0 = A(rowsN * r * rs);
   double *dox = (double *)A((size_t)K * 8), *doy = (double *)A((size_t)K * 8), *dw = (double *)A((size_t)K * 8);
   I.ox = dox;
   I.oy = doy;
@@ -884,9 +936,25 @@ int dlr_create(const dlr_problem *problem, const dlr_runtime *runtime, dlr_handl
     chain(cudaMemsetAsync(I.sgk, 0, (size_t)I.grp_ng * (kGA + 1) * I.glay * 4, h->st));
     chain(cudaMemsetAsync(I.spk, 0, 8 * I.glay * 4, h->st));
   }
+  std::vector<double> X0q;
+  if (I.q1) {
+    // the DG0 basis as Q1 fields: each cell's constant coefficient (stored
+    // scale 1), slopes zero; still orthonormal in the h^2 inner product
+    X0q.assign((size_t)4 * N * r, 0.0);
+    for (int l = 0; l < rx; ++l)
+      for (int c = 0; c < N; ++c) X0q[(size_t)4 * c + (size_t)4 * N * l] = X0[c + (size_t)N * l];
+    // columns beyond the N cell constants (r > N on tiny meshes): one slope
+    // coefficient each, scaled to unit h^2 norm (they carry no psi0)
+    for (int l = rx; l < r; ++l) {
+      const int q = l - rx, c = q / 3, m = 1 + q % 3;
+      X0q[(size_t)4 * c + m + (size_t)4 * N * l] = 1.0 / std::sqrt(I.h2);
+    }
+  }
   if (h->mixed) {
     std::vector<float> Xf(X0.begin(), X0.end());
     chain(up(I.X0, Xf.data(), Xf.size() * 4));
+  } else if (I.q1) {
+    chain(up(I.X0, X0q.data(), X0q.size() * 8));
   } else {
     chain(up(I.X0, X0.data(), X0.size() * 8));
   }
@@ -984,6 +1052,12 @@ static int sweep_items(const dlr_handle *h, bool grp) { return grp ? h->inst.grp
 
 static int plan_units(dlr_handle *const *hs, int n, bool mixed, bool grp, int ctas, double split,
                       std::vector<SiUnit> &units) {
+  if (hs[0]->inst.q1) {  // the bilinear sweep takes a whole angle per unit
+    units.clear();
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < hs[i]->r; ++j) units.push_back(SiUnit{i, j, 0, (hs[i]->prob.ny + 31) / 32, -1, -1});
+    return (int)units.size();
+  }
   const int nw = grp ? si_grp_warps() : si_sweep_warps(mixed);
   const int lag = grp ? si_grp_lag() : si_sweep_lag(mixed);
   std::vector<int> nb(n), bpu(n);
@@ -1071,6 +1145,7 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   b->svd_mode = hs[0]->prob.selection == DLR_SEL_DEIM ? 1 : 0;
   b->sn = hs[0]->sn;
   b->aug = hs[0]->aug;
+  b->q1 = hs[0]->inst.q1 != 0;
   for (int i = 0; i < n; ++i) {
     const dlr_handle *h = hs[i];
     b->maxN = std::max(b->maxN, h->N);
@@ -1084,6 +1159,7 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
     b->lbmax = std::max(b->lbmax, h->lb);
     b->nx_max = std::max(b->nx_max, h->prob.nx);
     b->maxL = std::max(b->maxL, h->prob.nx + h->prob.ny);
+    b->maxRows = std::max(b->maxRows, h->inst.q1 ? 4 * h->N : h->N);
     b->refl = b->refl || h->inst.refl_kap != nullptr;
     b->bands_max = std::max(b->bands_max, (h->prob.ny + 31) / 32);
   }
@@ -1102,6 +1178,7 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
                            : si_max_grid<double>(b->nx_max, b->bands_max, n, gam_max, any_dsa);
   b->grid_grp = b->grp_ok ? si_grp_max_grid(b->nx_max, b->bands_max, n, b->grp_stages) : 0;
   if (b->grp_ok && b->grid_grp <= 0) b->grp_ok = false;
+  if (b->q1) b->grid_angle = q1_si_max_grid(b->nx_max, b->bands_max, n, gam_max);
   if (b->grid_angle <= 0) {
     delete b;
     return fail(DLR_ECUDA, "the source-iteration kernel does not fit on this GPU");
@@ -1136,6 +1213,7 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   bytes += 2 * sz(sizeof(Inst) * n);
   bytes += 9 * sz(sizeof(GramJob) * n) + 2 * sz(sizeof(FillJob) * n) + 9 * sz(sizeof(ApplyJob) * n) +
            8 * sz(sizeof(CholJob) * n) + sz(sizeof(ReduceJob) * n);
+  bytes += sz(sizeof(GramJob) * 7 * n) + sz(sizeof(ReduceJob) * 7 * n);  // bilinear elements
   // 64-bit words per edge row: one per column and value (two per FP64 value;
   // kGA values per column in the grouped sweep)
   const int gedge_ld = (b->nx_max + 3) / 4 * 4 * (b->grp_ok ? kGA : b->mixed ? 1 : 2);
@@ -1189,6 +1267,8 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   b->c_l2 = carve<CholJob>(cur, n);
   b->c_l3 = carve<CholJob>(cur, n);
   b->r_proj = carve<ReduceJob>(cur, n);
+  b->g_q1t = carve<GramJob>(cur, 7 * n);
+  b->r_q1 = carve<ReduceJob>(cur, 7 * n);
   b->d_units = carve<SiUnit>(cur, b->units_cap);
   b->ctl.bar = carve<unsigned>(cur, 16);
   b->ctl.work = carve<unsigned>(cur, 16);
@@ -1227,6 +1307,8 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   std::vector<ApplyJob> ap(n), ax2(n), ax3(n), al1(n), aw2(n), aw3(n), awv(n), acw(n), acx(n);
   std::vector<CholJob> cp1(n), cp1b(n), cp2(n), cp3(n), cl1(n), cl1b(n), cl2(n), cl3(n);
   std::vector<ReduceJob> rp(n);
+  std::vector<GramJob> gq(7 * n);
+  std::vector<ReduceJob> rq(7 * n);
   for (int i = 0; i < n; ++i) {
     const dlr_handle *h = hs[i];
     insts[i] = h->inst;
@@ -1247,9 +1329,10 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
     // the Grams of step 5: k_gram32 in mixed precision, k_tsgram in FP64
     // (one partial per cluster either way)
     const int pbx = h->mixed ? h->pbg : h->pb;
-    gp1[i] = gram(I.Psi, nullptr, N, N, 0, pbx, nullptr);
-    gpre[i] = gram(I.Psi, nullptr, N, N, 0, pbx, flag + 1);
-    gx[i] = gram(I.X, nullptr, N, N, 0, pbx, nullptr);
+    const int NR = I.q1 ? 4 * N : N;  // rows of Psi and X (Q1: 4 coefficients per cell)
+    gp1[i] = gram(I.Psi, nullptr, NR, NR, 0, pbx, nullptr);
+    gpre[i] = gram(I.Psi, nullptr, NR, NR, 0, pbx, flag + 1);
+    gx[i] = gram(I.X, nullptr, NR, NR, 0, pbx, nullptr);
     gl1[i] = gram(I.L, I.w, K, r, 1, h->pbl, nullptr);
     glf[i] = gram(I.Lf, I.w, K, r, 1, h->pbl, flag + 1);
     gw[i] = gram(I.W0, nullptr, K, K, 0, h->pbl, nullptr);
@@ -1258,14 +1341,14 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
     gcr[i].ldb = K;
     gcr[i].sqrt_wt = 1;
     // the third-pass Grams run only when the first passes were shifted
-    gx3[i] = gram(I.X, nullptr, N, N, 0, pbx, flag);
+    gx3[i] = gram(I.X, nullptr, NR, NR, 0, pbx, flag);
     gw3[i] = gram(I.W0, nullptr, K, K, 0, h->pbl, flag);
     auto fill = [&](void *A, const void *src, int m, int lda, int layout) {
       FillJob f{};
       f.A = A; f.src = src; f.m = m; f.r = r; f.lda = lda; f.layout = layout; f.flag = flag;
       return f;
     };
-    fp[i] = fill(I.Psi, nullptr, N, N, 0);
+    fp[i] = fill(I.Psi, nullptr, NR, NR, 0);
     fl[i] = fill(I.Lf, I.L, K, r, 1);
     auto apply = [&](const void *A, int layout, int lda, const double *s_in, int sq_in, const double *T,
                      void *outp, int ldo, const double *s_out, int inv_sq, int m, const int *run_if) {
@@ -1282,15 +1365,15 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
       a.tri = 1;
       return a;
     };
-    ap[i] = solve(I.Psi, 0, N, nullptr, sm + L.R1, I.X, N, N, nullptr);
-    ax2[i] = solve(I.X, 0, N, nullptr, sm + L.R2, I.X, N, N, nullptr);
-    ax3[i] = solve(I.X, 0, N, nullptr, sm + L.R3, I.X, N, N, flag);
+    ap[i] = solve(I.Psi, 0, NR, nullptr, sm + L.R1, I.X, NR, NR, nullptr);
+    ax2[i] = solve(I.X, 0, NR, nullptr, sm + L.R2, I.X, NR, NR, nullptr);
+    ax3[i] = solve(I.X, 0, NR, nullptr, sm + L.R3, I.X, NR, NR, flag);
     al1[i] = solve(I.Lf, 1, r, I.w, sm + L.R1, I.W0, K, K, nullptr);
     aw2[i] = solve(I.W0, 0, K, nullptr, sm + L.R2, I.W0, K, K, nullptr);
     aw3[i] = solve(I.W0, 0, K, nullptr, sm + L.R3, I.W0, K, K, flag);
     awv[i] = apply(I.W0, 0, K, nullptr, 0, sm + L.V, I.W0, K, I.w, 1, K, nullptr);
     acw[i] = apply(I.W0, 0, K, nullptr, 0, sm + L.V, I.W0, K, nullptr, 0, K, nullptr);
-    acx[i] = apply(I.X0, 0, N, nullptr, 0, sm + L.U, I.X0, N, nullptr, 0, N, nullptr);
+    acx[i] = apply(I.X0, 0, NR, nullptr, 0, sm + L.U, I.X0, NR, nullptr, 0, NR, nullptr);
     const double u = chol_u(h->mixed), tau = chol_tau(h->mixed);
     auto chol = [&](int nparts, double scale, double *R, int mode) {
       CholJob c{};
@@ -1312,6 +1395,27 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
     red.part = I.partials; red.nblocks = pc; red.stride = proj_count(r);
     red.count = proj_count(r); red.out = sm + L.G; red.scale = 1.0;
     rp[i] = red;
+    if (I.q1) {
+      // step 7 on bilinear elements: A_x+, A_x-, A_y+, A_y- = X^T (T X)
+      // (cross Grams with the transport buffer, filled one direction at a
+      // time), M_t, M_s (row weights sigma_t, sigma_s) and P = <X, X0>, each
+      // into its own block of partials, then reduced into the small slots
+      const int slots[7] = {L.Axp, L.Axm, L.Ayp, L.Aym, L.Mt, L.Ms, L.P};
+      for (int g = 0; g < 7; ++g) {
+        double *part = I.partials + (size_t)g * pc * r * r;
+        GramJob q = gram(I.X, nullptr, NR, NR, 0, h->pb, nullptr);
+        q.out = part;
+        if (g < 4) { q.B = I.q1_v; q.ldb = NR; }
+        if (g == 4) q.wt = I.q1_wt;
+        if (g == 5) q.wt = I.q1_ws;
+        if (g == 6) { q.B = I.X0; q.ldb = NR; }
+        gq[(size_t)g * n + i] = q;
+        ReduceJob rj{};
+        rj.part = part; rj.nblocks = pc; rj.stride = r * r; rj.count = r * r;
+        rj.out = sm + slots[g]; rj.scale = g < 4 ? 1.0 : I.h2;
+        rq[(size_t)g * n + i] = rj;
+      }
+    }
   }
   auto upv = [&](void *dst, const void *src, size_t bytes) {
     return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
@@ -1350,6 +1454,8 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   chain(upv(b->c_l2, cl2.data(), sizeof(CholJob) * n));
   chain(upv(b->c_l3, cl3.data(), sizeof(CholJob) * n));
   chain(upv(b->r_proj, rp.data(), sizeof(ReduceJob) * n));
+  chain(upv(b->g_q1t, gq.data(), sizeof(GramJob) * 7 * n));
+  chain(upv(b->r_q1, rq.data(), sizeof(ReduceJob) * 7 * n));
   chain(upv(b->d_units, units.data(), sizeof(SiUnit) * units.size()));
   // angle selection: one cluster of kCl CTAs per instance
   b->sel_slice_max = std::max(1, (b->maxK + kCl - 1) / kCl);
@@ -1399,11 +1505,17 @@ static int enqueue_pre(Batch *b) {
   const Inst *d = b->d_insts;
   const int n = b->n;
   if (b->sn) {  // full-rank SN: coefficients, fixed sources, starting phi
-    LK(launch_sn_prep<real>(d, n, b->maxN, b->st));
+    if (b->q1) LK(launch_q1_coeff(d, n, b->maxN, true, b->st));
+    else LK(launch_sn_prep<real>(d, n, b->maxN, b->st));
     LK(launch_si_prep(d, n, b->ctl, b->st));
     return DLR_OK;
   }
   LK(launch_select(d, n, b->sel_slice_max, b->st));
+  if (b->q1) {  // bilinear elements: coefficients, psi0, fixed sources, starting phi
+    LK(launch_q1_coeff(d, n, b->maxN, false, b->st));
+    LK(launch_si_prep(d, n, b->ctl, b->st));
+    return DLR_OK;
+  }
   LKM(launch_coeff_recon<real>(d, n, b->maxN, b->rmask_pre, b->grp ? 1 : 0, b->st), b->rmask_pre);
   if (b->refl) {  // reflective edges: G, H and the first sweeps' inflow (two kernels)
     LK(launch_refl_pre<real>(d, n, b->rmax, b->maxL, b->st));
@@ -1420,7 +1532,8 @@ static int enqueue_post(Batch *b) {
   const int n = b->n;
   cudaStream_t st = b->st;
   if (b->sn) {
-    LK(launch_sn_tupdate<real>(d, n, b->maxN, st));
+    if (b->q1) LK(launch_q1_tupdate(d, n, b->maxN, true, st));
+    else LK(launch_sn_tupdate<real>(d, n, b->maxN, st));
     return DLR_OK;
   }
   // step 5: CholeskyQR of Psi; dependent columns are replaced by
@@ -1435,20 +1548,33 @@ static int enqueue_post(Batch *b) {
   };
   LK(gram5(b->g_psi1));
   LK(launch_chol(b->c_p1, d, n, st));
-  LK(launch_fill<real>(b->f_psi, n, b->maxN, st));
+  LK(launch_fill<real>(b->f_psi, n, b->maxRows, st));
   LK(gram5(b->g_psire));
   LK(launch_chol(b->c_p1b, d, n, st));
-  LKM((launch_apply<real, real>(b->a_psi, n, b->maxN, b->rmask, st)), b->rmask);
+  LKM((launch_apply<real, real>(b->a_psi, n, b->maxRows, b->rmask, st)), b->rmask);
   LK(gram5(b->g_x));
   LK(launch_chol(b->c_p2, d, n, st));
-  LKM((launch_apply<real, real>(b->a_x2, n, b->maxN, b->rmask, st)), b->rmask);
+  LKM((launch_apply<real, real>(b->a_x2, n, b->maxRows, b->rmask, st)), b->rmask);
   LK(gram5(b->g_x3));
   LK(launch_chol(b->c_p3, d, n, st));
-  LKM((launch_apply<real, real>(b->a_x3, n, b->maxN, b->rmask, st)), b->rmask);
+  LKM((launch_apply<real, real>(b->a_x3, n, b->maxRows, b->rmask, st)), b->rmask);
   // steps 6-7: projections and the L-step
-  LK(launch_project<real>(d, n, b->pbmax, b->rmax, st));
-  LK(launch_reduce(b->r_proj, n, proj_count(b->rmax), st));
-  LK(launch_proj_post(d, n, st));
+  if (b->q1) {
+    // bilinear elements: X^T (T X) per axis direction (the transport buffer
+    // refilled for each), M_t, M_s, P, the seven reductions, q^, the edge
+    // vectors and P S0
+    for (int dir = 0; dir < 4; ++dir) {
+      LK(launch_q1_transport(d, n, b->maxN, dir, st));
+      LK(launch_tsgram<double>(b->g_q1t + (size_t)dir * n, n, b->pbmax, 0, st));
+    }
+    LK(launch_tsgram<double>(b->g_q1t + (size_t)4 * n, 3 * n, b->pbmax, 0, st));
+    LK(launch_reduce(b->r_q1, 7 * n, b->rmax * b->rmax, st));
+    LK(launch_q1_vec(d, n, st));
+  } else {
+    LK(launch_project<real>(d, n, b->pbmax, b->rmax, st));
+    LK(launch_reduce(b->r_proj, n, proj_count(b->rmax), st));
+    LK(launch_proj_post(d, n, st));
+  }
   LKM(launch_lstep(d, n, b->rmax, b->rmask, b->lbmax, b->maxK, st), b->rmask);
   b->kcount += 2;  // and two more kernels
   if (b->refl) LK(launch_refl_lstep<real>(d, n, st));  // the reflected inflow's fixed point
@@ -1482,7 +1608,8 @@ static int enqueue_post(Batch *b) {
     LKM((launch_apply<double, double>(b->a_cw, n, b->maxK, b->rmask, st)), b->rmask);
   }
   // step 9
-  LKM(launch_tupdate<real>(d, n, b->maxN, b->rmask, st), b->rmask);
+  if (b->q1) LK(launch_q1_tupdate(d, n, b->maxN, false, st));
+  else LKM(launch_tupdate<real>(d, n, b->maxN, b->rmask, st), b->rmask);
   return DLR_OK;
 }
 
@@ -1569,6 +1696,7 @@ static cudaError_t launch_si_batch(const Batch *b, const SiCtl &c) {
                                               b->st);
     return e == cudaSuccess ? cudaGraphLaunch(b->si, b->st) : e;
   }
+  if (b->q1) return launch_q1_si(b->d_insts, c, b->si_grid, b->st);
   return b->mixed ? launch_si<float>(b->d_insts, c, b->si_grid, b->st)
                   : launch_si<double>(b->d_insts, c, b->si_grid, b->st);
 }
@@ -1645,6 +1773,7 @@ static int check_handles(dlr_handle *const *hs, int n) {
     if (hs[i]->st != hs[0]->st) return fail(DLR_EINVAL, "handles on different streams");
     if (hs[i]->sn != hs[0]->sn) return fail(DLR_EINVAL, "SN and DLR handles in one batch");
     if (hs[i]->aug != hs[0]->aug) return fail(DLR_EINVAL, "augmented and plain handles in one batch");
+    if (hs[i]->inst.q1 != hs[0]->inst.q1) return fail(DLR_EINVAL, "DG0 and bilinear handles in one batch");
     const int s = *hs[i]->h_status;
     if (s != DLR_OK) return fail(s, "handle %d: %s", i, status_name(s));
   }
@@ -1888,7 +2017,7 @@ static int canonicalize(dlr_handle *h) {
   CK((launch_apply<double, double>(b->a_cw, 1, h->K, rank_mask(h->r), h->st)));
   CK(launch_sign(b->d_insts, 1, h->K, h->st));
   if (h->mixed) CK((launch_apply<float, float>(b->a_cx, 1, h->N, rank_mask(h->r), h->st)));
-  else CK((launch_apply<double, double>(b->a_cx, 1, h->N, rank_mask(h->r), h->st)));
+  else CK((launch_apply<double, double>(b->a_cx, 1, h->inst.q1 ? 4 * h->N : h->N, rank_mask(h->r), h->st)));
   h->canonical = true;
   return DLR_OK;
 }
@@ -1900,11 +2029,20 @@ int dlr_get_factors(dlr_handle *h, double *X, double *S, double *W, int32_t *r_o
     int rc = canonicalize(h);
     if (rc) return rc;
   }
-  const size_t nX = (size_t)h->N * h->r;
+  const size_t rowsX = h->inst.q1 ? (size_t)4 * h->N : (size_t)h->N;
+  const size_t nX = rowsX * h->r;
   const cudaMemcpyKind k = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (r_out) *r_out = h->r;
   if (X) {
-    if (!h->mixed) {
+    if (h->inst.q1) {  // plain Legendre coefficients out (stored scaled)
+      CK(cudaMemcpyAsync(X, h->inst.X0, nX * 8, k, h->st));
+      if (out_on_device) {
+        CK(launch_q1_rescale(X, rowsX, h->r, 1, h->st));
+      } else {
+        CK(cudaStreamSynchronize(h->st));
+        for (size_t e = 0; e < nX; ++e) X[e] *= q1_unscale((int)((e % rowsX) & 3));
+      }
+    } else if (!h->mixed) {
       CK(cudaMemcpyAsync(X, h->inst.X0, nX * 8, k, h->st));
     } else if (out_on_device) {
       k_widen<<<1024, 256, 0, h->st>>>((const float *)h->inst.X0, X, nX);
@@ -1925,9 +2063,20 @@ int dlr_set_factors(dlr_handle *h, const double *X, const double *S, const doubl
   if (!h || !X || !S || !W) return fail(DLR_EINVAL, "NULL argument");
   if (h->sn) return fail(DLR_EINVAL, "a full-rank SN handle has no factors (dlr_set_psi)");
   h->canonical = false;
-  const size_t nX = (size_t)h->N * h->r;
+  const size_t rowsX = h->inst.q1 ? (size_t)4 * h->N : (size_t)h->N;
+  const size_t nX = rowsX * h->r;
   const cudaMemcpyKind k = in_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  if (!h->mixed) {
+  if (h->inst.q1) {  // plain Legendre coefficients in, stored scaled
+    if (in_on_device) {
+      CK(cudaMemcpyAsync(h->inst.X0, X, nX * 8, k, h->st));
+      CK(launch_q1_rescale((double *)h->inst.X0, rowsX, h->r, 0, h->st));
+    } else {
+      std::vector<double> tmp(X, X + nX);
+      for (size_t e = 0; e < nX; ++e) tmp[e] *= q1_scale((int)((e % rowsX) & 3));
+      CK(cudaMemcpyAsync(h->inst.X0, tmp.data(), nX * 8, cudaMemcpyHostToDevice, h->st));
+      CK(cudaStreamSynchronize(h->st));
+    }
+  } else if (!h->mixed) {
     CK(cudaMemcpyAsync(h->inst.X0, X, nX * 8, k, h->st));
   } else if (in_on_device) {
     k_narrow<<<1024, 256, 0, h->st>>>(X, (float *)h->inst.X0, nX);
@@ -1966,8 +2115,18 @@ int dlr_get_selected(dlr_handle *h, int32_t *idx) {
 int dlr_get_psi(dlr_handle *h, double *out, int32_t out_on_device) {
   if (!h || !out) return fail(DLR_EINVAL, "NULL argument");
   if (!h->sn) return fail(DLR_EINVAL, "dlr_get_psi needs a full-rank SN handle (dlr_get_factors)");
-  const size_t n = (size_t)h->N * h->K;
-  if (!h->mixed) {
+  const size_t rows = h->inst.q1 ? (size_t)4 * h->N : (size_t)h->N;
+  const size_t n = rows * h->K;
+  if (h->inst.q1) {  // plain Legendre coefficients out (stored scaled)
+    CK(cudaMemcpyAsync(out, h->inst.Psi, n * 8, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       h->st));
+    if (out_on_device) {
+      CK(launch_q1_rescale(out, rows, h->K, 1, h->st));
+    } else {
+      CK(cudaStreamSynchronize(h->st));
+      for (size_t e = 0; e < n; ++e) out[e] *= q1_unscale((int)((e % rows) & 3));
+    }
+  } else if (!h->mixed) {
     CK(cudaMemcpyAsync(out, h->inst.Psi, n * 8, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                        h->st));
   } else if (out_on_device) {
@@ -1985,8 +2144,19 @@ int dlr_get_psi(dlr_handle *h, double *out, int32_t out_on_device) {
 int dlr_set_psi(dlr_handle *h, const double *in, int32_t in_on_device) {
   if (!h || !in) return fail(DLR_EINVAL, "NULL argument");
   if (!h->sn) return fail(DLR_EINVAL, "dlr_set_psi needs a full-rank SN handle (dlr_set_factors)");
-  const size_t n = (size_t)h->N * h->K;
-  if (!h->mixed) {
+  const size_t rows = h->inst.q1 ? (size_t)4 * h->N : (size_t)h->N;
+  const size_t n = rows * h->K;
+  if (h->inst.q1) {  // plain Legendre coefficients in, stored scaled
+    if (in_on_device) {
+      CK(cudaMemcpyAsync(h->inst.Psi, in, n * 8, cudaMemcpyDeviceToDevice, h->st));
+      CK(launch_q1_rescale((double *)h->inst.Psi, rows, h->K, 0, h->st));
+    } else {
+      std::vector<double> tmp(in, in + n);
+      for (size_t e = 0; e < n; ++e) tmp[e] *= q1_scale((int)((e % rows) & 3));
+      CK(cudaMemcpyAsync(h->inst.Psi, tmp.data(), n * 8, cudaMemcpyHostToDevice, h->st));
+      CK(cudaStreamSynchronize(h->st));
+    }
+  } else if (!h->mixed) {
     CK(cudaMemcpyAsync(h->inst.Psi, in, n * 8, in_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                        h->st));
     if (!in_on_device) CK(cudaStreamSynchronize(h->st));

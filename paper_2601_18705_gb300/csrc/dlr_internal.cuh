@@ -164,6 +164,12 @@ struct Inst {
   // g_k, refl_passes the fixed-point passes of the last step.
   double *refl_kap, *refl_data, *refl_y, *refl_u;
   int *refl_passes;
+  // bilinear (Q1) elements (k_q1.cu; FP64): X0, X, Psi, s0 are 4 N x r,
+  // phi0, phi1 4 N, rows e = 4 c + m scaled by (1, 1/sqrt3, 1/sqrt3, 1/3);
+  // q1_wt, q1_ws (4 N) the row weights sigma_t, sigma_s of the step-7 mass
+  // Grams, q1_v (4 N x r) the transport operator applied to X
+  int q1;
+  double *q1_wt, *q1_ws, *q1_v;
   // grouped-angle sweep (mixed-precision DLR instances without DSA or
   // reflective edges, grp = 1): the chosen angles are grouped by quadrant
   // (kGA per group, table grp_tab of grp_ng records, ordered by quadrant),
@@ -179,6 +185,12 @@ struct Inst {
   int *grp_tab;
   float *sgk, *spk, *part, *qsum;
 };
+
+// Bilinear (Q1) coefficients are stored scaled by s = (1, 1/sqrt3, 1/sqrt3,
+// 1/3) (k_q1.cu): q1_scale(m) = s_m, q1_unscale(m) = 1/s_m.
+constexpr double kQ1Sqrt3 = 1.7320508075688772935;
+__host__ __device__ inline double q1_scale(int m) { return m == 0 ? 1.0 : (m == 3 ? 1.0 / 3.0 : 1.0 / kQ1Sqrt3); }
+__host__ __device__ inline double q1_unscale(int m) { return m == 0 ? 1.0 : (m == 3 ? 3.0 : kQ1Sqrt3); }
 
 // Angles per group of the grouped sweep, and the ints of one group record:
 // quadrant, number of angles, the angles' indices j.

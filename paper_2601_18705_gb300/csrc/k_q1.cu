@@ -1,0 +1,717 @@
+// k_q1.cu -- the SN-like DLR step (Algorithm 1) and the full-rank SN step on
+// bilinear (Q1) elements: upwind DG with the Legendre basis 1, xi, eta,
+// xi eta on each cell (Section 4.4's volume term G_j and face matrices F_d
+// with the paper's bilinear elements), FP64.
+//
+// Storage.  A Q1 field has 4 coefficients per cell, row e = 4 c + m.  They
+// are stored scaled by s = (1, 1/sqrt3, 1/sqrt3, 1/3): the scaled basis is
+// orthonormal for (1/4) int int over the reference cell, so the L2 inner
+// product of two Q1 fields is hx hy times the plain dot product of their 4 N
+// stored rows.  Step 5 (CholeskyQR in the h^2 inner product) then runs
+// unchanged over 4 N rows, and the cell's own coefficients are the stored
+// ones divided by s.
+//
+//   k_q1_coeff      step 1 (per cell, as on DG0 cells) and step 3: psi0 at
+//                   the chosen angles from X0 C0, the fixed sources
+//                   q delta_m0 + psi0_j / (c dt), the starting phi, and the
+//                   row weights sigma_t, sigma_s of the step-7 mass Grams
+//   k_q1_sn_prep    the same for a full-rank SN instance (psi^n at every
+//                   angle, phi^n = sum_k w_k psi^n_k)
+//   k_q1_si         step 4: the collocation sweeps of the chosen angles and
+//                   the source iteration, one cooperative launch; a sweep
+//                   solves per cell the 4 x 4 upwind DG system, the upwind
+//                   neighbours entering through their face traces (constant
+//                   and slope)
+//   k_q1_transport  the Q1 transport operator of one axis direction applied
+//                   to every column of X (for the Galerkin operators of step
+//                   7, summed by the cross Grams of k_tsgram)
+//   k_q1_vec        step 7's q^ and unit-inflow edge vectors, then P S0
+//   k_q1_tupdate    step 9: T from the cell average of phi = X (L w),
+//                   X0 <- X U
+//   k_q1_sn_tupdate the full-rank SN step's temperature update
+#include <algorithm>
+
+#include "dlr_internal.cuh"
+
+namespace dlr {
+
+namespace {
+
+constexpr int kQ1NW = 4;       // sweeping warps per CTA
+constexpr int kQ1Pub = 8;      // columns per progress publication
+constexpr uint64_t kQ1WaitNs = 4000000000ull;
+constexpr unsigned kQ1Full = 0xffffffffu;
+
+// faces of the reference cell: xi = +1, xi = -1, eta = +1, eta = -1
+enum Q1Face { kFR = 0, kFL = 1, kFT = 2, kFB = 3 };
+
+}  // namespace
+
+// int over the reference cell of the squared basis function m
+__device__ __forceinline__ double q1_mass(int m) { return m == 0 ? 4.0 : (m == 3 ? 4.0 / 9.0 : 4.0 / 3.0); }
+
+// The trace of basis function i on a face, as (constant, slope along the
+// face): on xi = +-1 the slope is in eta, on eta = +-1 in xi.
+__device__ __forceinline__ void q1_basis_trace(int face, int i, double &t0, double &t1) {
+  const double sg = (face == kFR || face == kFT) ? 1.0 : -1.0;
+  if (face == kFR || face == kFL) {  // xi = sg: 1 -> 1, xi -> sg, eta -> eta, xi eta -> sg eta
+    t0 = i == 0 ? 1.0 : (i == 1 ? sg : 0.0);
+    t1 = i == 2 ? 1.0 : (i == 3 ? sg : 0.0);
+  } else {                           // eta = sg: 1 -> 1, xi -> xi, eta -> sg, xi eta -> sg xi
+    t0 = i == 0 ? 1.0 : (i == 2 ? sg : 0.0);
+    t1 = i == 1 ? 1.0 : (i == 3 ? sg : 0.0);
+  }
+}
+// The trace of the field u (unscaled coefficients) on a face.
+__device__ __forceinline__ void q1_trace(int face, const double *u, double &t0, double &t1) {
+  t0 = 0.0;
+  t1 = 0.0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    double a0, a1;
+    q1_basis_trace(face, i, a0, a1);
+    t0 += a0 * u[i];
+    t1 += a1 * u[i];
+  }
+}
+// int_{-1}^{1} (c0 + c1 s)(d0 + d1 s) ds
+__device__ __forceinline__ double q1_face_int(double c0, double c1, double d0, double d1) {
+  return 2.0 * c0 * d0 + (2.0 / 3.0) * c1 * d1;
+}
+
+// The transport part of the cell matrix of direction (ox, oy) on a cell of
+// half-widths a, b (A[i + 4 j], test function i, trial function j): the
+// volume term -int u (Om . grad v) and the outflow faces
+// |Om . n| (face length / 2) int trace_i trace_j.  The reference-cell
+// integrals of (d v_i / d xi) v_j are 4 for (i, j) = (1, 0) and 4/3 for
+// (3, 2); of (d v_i / d eta) v_j, 4 for (2, 0) and 4/3 for (3, 1).
+__device__ __forceinline__ void q1_cell_matrix(double ox, double oy, double a, double b, double *A) {
+#pragma unroll
+  for (int e = 0; e < 16; ++e) A[e] = 0.0;
+  A[1 + 4 * 0] -= ox * b * 4.0;
+  A[3 + 4 * 2] -= ox * b * (4.0 / 3.0);
+  A[2 + 4 * 0] -= oy * a * 4.0;
+  A[3 + 4 * 1] -= oy * a * (4.0 / 3.0);
+  const int fx = ox >= 0 ? kFR : kFL, fy = oy >= 0 ? kFT : kFB;
+  const double cx = fabs(ox) * b, cy = fabs(oy) * a;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      double xi0, xi1, xj0, xj1, yi0, yi1, yj0, yj1;
+      q1_basis_trace(fx, i, xi0, xi1);
+      q1_basis_trace(fx, j, xj0, xj1);
+      q1_basis_trace(fy, i, yi0, yi1);
+      q1_basis_trace(fy, j, yj0, yj1);
+      A[i + 4 * j] += cx * q1_face_int(xi0, xi1, xj0, xj1) + cy * q1_face_int(yi0, yi1, yj0, yj1);
+    }
+}
+// The inflow terms |Om . n| (length / 2) int u_in trace_i of the traces
+// (ux0, ux1) and (uy0, uy1) entering through the upwind x- and y-faces.
+__device__ __forceinline__ void q1_inflow(double ox, double oy, double a, double b, double ux0, double ux1,
+                                          double uy0, double uy1, double *r) {
+  const int fx = ox >= 0 ? kFL : kFR, fy = oy >= 0 ? kFB : kFT;
+  const double cx = fabs(ox) * b, cy = fabs(oy) * a;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    double x0, x1, y0, y1;
+    q1_basis_trace(fx, i, x0, x1);
+    q1_basis_trace(fy, i, y0, y1);
+    r[i] += cx * q1_face_int(x0, x1, ux0, ux1) + cy * q1_face_int(y0, y1, uy0, uy1);
+  }
+}
+// A x = r for the 4 x 4 cell matrix, Gaussian elimination without pivoting:
+// the symmetric part of an upwind DG cell matrix is positive definite (half
+// the inflow and outflow face terms plus the reaction), so no pivot
+// vanishes.  x overwrites r; A is destroyed.
+__device__ __forceinline__ void q1_solve4(double *A, double *r) {
+  double inv[4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    inv[p] = 1.0 / A[p + 4 * p];
+#pragma unroll
+    for (int i = p + 1; i < 4; ++i) {
+      const double f = A[i + 4 * p] * inv[p];
+#pragma unroll
+      for (int j = p + 1; j < 4; ++j) A[i + 4 * j] -= f * A[p + 4 * j];
+      r[i] -= f * r[p];
+    }
+  }
+#pragma unroll
+  for (int p = 3; p >= 0; --p) {
+    double x = r[p];
+#pragma unroll
+    for (int j = p + 1; j < 4; ++j) x -= A[p + 4 * j] * r[j];
+    r[p] = x * inv[p];
+  }
+}
+
+// ------------------------------------------------------------------
+// steps 1 and 3
+// ------------------------------------------------------------------
+// One thread per cell: the coefficients, the weights of the mass Grams, and
+// per chosen angle j and coefficient m: psi0 = sum_l X0(e, l) C0(l, j),
+// s0_j(e) = q delta_m0 + psi0 / (c dt), phi(e) = sum_j gamma_j psi0_j(e).
+__global__ void __launch_bounds__(128) k_q1_coeff(const Inst *__restrict__ insts) {
+  pdl_wait();
+  pdl_trigger();
+  const Inst &I = insts[blockIdx.y];
+  if (!I.q1) return;
+  __shared__ double C0s[kMaxRank * kMaxRank], gam[kMaxRank];
+  const int r = I.r;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) C0s[e] = I.small[I.lay.C0 + e];
+  for (int e = threadIdx.x; e < r; e += blockDim.x) gam[e] = I.small[I.lay.gamma + e];
+  __syncthreads();
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= I.N || *I.status != kOk) return;
+  const CellCoef cf = cell_coefficients(I, c);
+  I.B0[c] = cf.B;
+  I.D[c] = cf.D;
+  const double st = cf.sig + I.inv_cdt;
+  as<double>(I.sig_t)[c] = st;
+  as<double>(I.ss4)[c] = cf.ss / (4.0 * kPi);
+  as<double>(I.q)[c] = cf.q;
+  const size_t M = (size_t)4 * I.N;
+  const double *X0 = as_c<double>(I.X0);
+  double *s0 = as<double>(I.s0), *phi = as<double>(I.phi0);
+  for (int m = 0; m < 4; ++m) {
+    const size_t e = (size_t)4 * c + m;
+    I.q1_wt[e] = st;
+    I.q1_ws[e] = cf.ss;
+    double x[kMaxRank];
+#pragma unroll
+    for (int l = 0; l < kMaxRank; ++l) x[l] = l < r ? X0[e + M * l] : 0.0;
+    double ph = 0.0;
+    for (int j = 0; j < r; ++j) {
+      double p0 = 0.0;
+#pragma unroll
+      for (int l = 0; l < kMaxRank; ++l)
+        if (l < r) p0 += x[l] * C0s[l + r * j];
+      s0[e + M * j] = (m == 0 ? cf.q : 0.0) + I.inv_cdt * p0;
+      ph += gam[j] * p0;
+    }
+    phi[e] = ph;
+  }
+}
+
+// Full-rank SN on Q1: psi (4 N x K, scaled) holds psi^n; the same
+// coefficients, s0_k = q delta_m0 + psi^n_k / (c dt), phi^n = sum_k w_k psi^n_k.
+__global__ void __launch_bounds__(128) k_q1_sn_prep(const Inst *__restrict__ insts) {
+  pdl_wait();
+  pdl_trigger();
+  const Inst &I = insts[blockIdx.y];
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!I.q1 || c >= I.N || *I.status != kOk) return;
+  const CellCoef cf = cell_coefficients(I, c);
+  I.B0[c] = cf.B;
+  I.D[c] = cf.D;
+  as<double>(I.sig_t)[c] = cf.sig + I.inv_cdt;
+  as<double>(I.ss4)[c] = cf.ss / (4.0 * kPi);
+  as<double>(I.q)[c] = cf.q;
+  const size_t M = (size_t)4 * I.N;
+  const double *psi = as_c<double>(I.Psi);
+  double *s0 = as<double>(I.s0), *phi = as<double>(I.phi0);
+  for (int m = 0; m < 4; ++m) {
+    const size_t e = (size_t)4 * c + m;
+    double ph = 0.0;
+    for (int k = 0; k < I.K; ++k) {
+      const double p = psi[e + M * k];
+      s0[e + M * k] = (m == 0 ? cf.q : 0.0) + I.inv_cdt * p;
+      ph += I.w[k] * p;
+    }
+    phi[e] = ph;
+  }
+}
+
+// ------------------------------------------------------------------
+// step 4: collocation sweeps and source iteration
+// ------------------------------------------------------------------
+// Shared memory of k_q1_si: (kQ1NW + 1) edge rows of 2 x nx_max traces, the
+// band progress counters, the active flags and the scalar-flux weights.
+__host__ __device__ inline size_t q1_si_smem_bytes(int nx_max, int bands_max, int n_inst, int gam_max) {
+  return (size_t)(kQ1NW + 1) * 2 * nx_max * sizeof(double) + (size_t)(bands_max + 3) / 4 * 4 * sizeof(int) +
+         (size_t)(n_inst + 3) / 4 * 4 * sizeof(int) + (size_t)gam_max * sizeof(double);
+}
+
+struct Q1Smem {
+  double *edge;   // (kQ1NW + 1) x 2 x nx_max
+  int *prog;      // per band: columns published
+  int nx_max;
+};
+
+// Spins until band b's progress reaches `need` columns (bounded in time;
+// leaves on the abort flag).  Called by one lane.
+__device__ __forceinline__ bool q1_wait_prog(volatile int *prog, int b, int need, volatile int *abort_flag) {
+  if (prog[b] >= need) return true;
+  const uint64_t t0 = global_ns();
+  unsigned spins = 0;
+  while (prog[b] < need) {
+    if ((++spins & 15u) == 0) {
+      __nanosleep(32);
+      if (*abort_flag) return false;
+      if (global_ns() - t0 > kQ1WaitNs) return false;
+    }
+  }
+  __threadfence_block();
+  return true;
+}
+
+// The sweep of chosen angle j of instance I by one CTA: warp w takes the
+// bands w, w + kQ1NW, ... of 32 rows (lane i = row i of the band, mirrored
+// so that the direction points to +u, +v); lane i handles column u at step
+// t = u + i.  The left neighbour's face trace stays in the lane's
+// registers, the lower one comes from lane i - 1 by a shuffle, and lane 0
+// takes it from the edge row the band below published.  Returns false (in
+// every thread of the CTA) if a wait gave up.
+__device__ bool q1_sweep(const Inst &I, int j, const Q1Smem &S, const double *pold, volatile int *abort_flag) {
+  const int nx = I.nx, ny = I.ny, nb = (ny + 31) / 32;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) S.prog[b] = 0;
+  __syncthreads();
+  const int k = I.idx[j];
+  const double ox = I.ox[k], oy = I.oy[k];
+  const double a = 0.5 * I.hx, bh = 0.5 * I.hy;
+  const bool flx = ox < 0, fly = oy < 0;
+  const double inx = ox > 0 ? I.psi_edge[0] : (ox < 0 ? I.psi_edge[1] : 0.0);
+  const double iny = oy > 0 ? I.psi_edge[2] : (oy < 0 ? I.psi_edge[3] : 0.0);
+  double A0[16];
+  q1_cell_matrix(ox, oy, a, bh, A0);
+  const int fox = ox >= 0 ? kFR : kFL, foy = oy >= 0 ? kFT : kFB;
+  const size_t M = (size_t)4 * I.N;
+  const double *sig_t = as_c<double>(I.sig_t), *ss4 = as_c<double>(I.ss4);
+  const double *s0 = as_c<double>(I.s0) + M * j;
+  double *psi = as<double>(I.Psi) + M * j;
+  volatile int *prog = S.prog;
+  bool ok = true;
+  for (int b = wid; b < nb && ok; b += kQ1NW) {
+    const int v = b * 32 + lane;
+    const bool row_ok = v < ny;
+    const int iy = fly ? ny - 1 - v : v;
+    const double *ein = S.edge + (size_t)((b + kQ1NW) % (kQ1NW + 1)) * 2 * S.nx_max;
+    double *eout = S.edge + (size_t)(b % (kQ1NW + 1)) * 2 * S.nx_max;
+    double ux0 = inx, ux1 = 0.0;  // trace entering through the left face
+    double ty0 = 0.0, ty1 = 0.0;  // this lane's last top trace
+    for (int t = 0; t < nx + 31; ++t) {
+      if (b > 0 && t < nx && (t % kQ1Pub) == 0) {
+        int w_ok = 1;
+        if (lane == 0) w_ok = q1_wait_prog(prog, b - 1, min(nx, t + kQ1Pub), abort_flag) ? 1 : 0;
+        w_ok = __shfl_sync(kQ1Full, w_ok, 0);
+        if (!w_ok) { ok = false; break; }
+      }
+      const int u = t - lane;
+      double uy0 = __shfl_up_sync(kQ1Full, ty0, 1), uy1 = __shfl_up_sync(kQ1Full, ty1, 1);
+      if (lane == 0) {
+        if (b == 0) { uy0 = iny; uy1 = 0.0; }
+        else if (u < nx) { uy0 = ein[u]; uy1 = ein[S.nx_max + u]; }
+      }
+      if (row_ok && u >= 0 && u < nx) {
+        const int ix = flx ? nx - 1 - u : u;
+        const int c = iy * nx + ix;
+        const double st = sig_t[c], sv = ss4[c];
+        double A[16], rhs[4];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) A[e] = A0[e];
+        const double ab = a * bh;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const size_t e = (size_t)4 * c + m;
+          const double src = (sv * pold[e] + s0[e]) * q1_unscale(m);
+          A[m + 4 * m] += st * ab * q1_mass(m);
+          rhs[m] = ab * q1_mass(m) * src;
+        }
+        q1_inflow(ox, oy, a, bh, ux0, ux1, uy0, uy1, rhs);
+        q1_solve4(A, rhs);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) psi[(size_t)4 * c + m] = rhs[m] * q1_scale(m);
+        q1_trace(fox, rhs, ux0, ux1);
+        q1_trace(foy, rhs, ty0, ty1);
+        if (lane == 31) {
+          eout[u] = ty0;
+          eout[S.nx_max + u] = ty1;
+        }
+      }
+      // lane 31 finished column t - 31: publish every kQ1Pub columns
+      const int done = t - 30;
+      if (lane == 31 && done > 0 && (done % kQ1Pub == 0 || done == nx)) {
+        __threadfence_block();
+        prog[b] = done;
+      }
+      __syncwarp();
+    }
+  }
+  if (!ok) *abort_flag = 1;
+  return __syncthreads_and(ok) != 0;
+}
+
+// The whole source iteration of a batch of Q1 instances, one cooperative
+// launch: phase A sweeps every (instance, chosen angle) unit (units claimed
+// from a counter), phase B forms phi = sum_j gamma_j psi_j per coefficient
+// and the convergence maxima on the unscaled coefficients, phase C takes the
+// same decision in every CTA (as k_si).
+__global__ void __launch_bounds__(kQ1NW * 32) k_q1_si(const Inst *__restrict__ insts, SiCtl ctl) {
+  extern __shared__ __align__(16) unsigned char q1sm[];
+  Q1Smem S;
+  S.nx_max = ctl.nx_max;
+  S.edge = reinterpret_cast<double *>(q1sm);
+  size_t off = (size_t)(kQ1NW + 1) * 2 * ctl.nx_max * sizeof(double);
+  S.prog = reinterpret_cast<int *>(q1sm + off);
+  off += (size_t)(ctl.bands_max + 3) / 4 * 4 * sizeof(int);
+  int *active = reinterpret_cast<int *>(q1sm + off);
+  off += (size_t)(ctl.n_inst + 3) / 4 * 4 * sizeof(int);
+  double *gam = reinterpret_cast<double *>(q1sm + off);
+  __shared__ int unit_s, n_active_s;
+  volatile int *abort_flag = ctl.abort_flag;
+  for (int i = threadIdx.x; i < ctl.n_inst; i += blockDim.x) active[i] = (*insts[i].status == kOk) ? 1 : 0;
+  __syncthreads();
+  for (int it = 0;; ++it) {
+    if (threadIdx.x == 0) {
+      int n = 0;
+      for (int i = 0; i < ctl.n_inst; ++i) n += active[i];
+      n_active_s = n;
+    }
+    __syncthreads();
+    if (n_active_s == 0) break;
+    // ---- phase A ----
+    for (;;) {
+      if (threadIdx.x == 0) unit_s = (int)atomicAdd(ctl.work + (it & 1), 1u);
+      __syncthreads();
+      const int u = unit_s;
+      __syncthreads();
+      if (u >= ctl.n_units) break;
+      const SiUnit U = ctl.units[u];
+      if (!active[U.inst]) continue;
+      const Inst &I = insts[U.inst];
+      const double *pold = as_c<double>((it & 1) ? I.phi1 : I.phi0);
+      if (!q1_sweep(I, U.angle, S, pold, abort_flag)) break;
+    }
+    if (!grid_barrier(ctl.bar, abort_flag)) break;
+    // ---- phase B ----
+    if (blockIdx.x == 0) {
+      for (int i = threadIdx.x; i < ctl.n_inst; i += blockDim.x) {
+        insts[i].conv[((it + 1) & 1) * 2 + 0] = 0ull;
+        insts[i].conv[((it + 1) & 1) * 2 + 1] = 0ull;
+      }
+      if (threadIdx.x == 0) ctl.work[(it + 1) & 1] = 0u;
+    }
+    for (int i = 0; i < ctl.n_inst; ++i) {
+      if (!active[i]) continue;
+      const Inst &I = insts[i];
+      const int r = I.r;
+      const size_t M = (size_t)4 * I.N;
+      const double *psi = as_c<double>(I.Psi);
+      const double *pold = as_c<double>((it & 1) ? I.phi1 : I.phi0);
+      double *pnew = as<double>((it & 1) ? I.phi0 : I.phi1);
+      __syncthreads();
+      for (int q = threadIdx.x; q < r; q += blockDim.x)
+        gam[q] = I.gamma_ext ? I.gamma_ext[q] : I.small[I.lay.gamma + q];
+      __syncthreads();
+      double dmax = 0.0, pmax = 0.0;
+      for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < M; e += (size_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int q = 0; q < r; ++q) acc += gam[q] * psi[e + M * q];
+        const double us = q1_unscale((int)(e & 3));
+        dmax = fmax(dmax, fabs(acc - pold[e]) * us);
+        pmax = fmax(pmax, fabs(acc) * us);
+        pnew[e] = acc;
+      }
+      dmax = warp_max(dmax);
+      pmax = warp_max(pmax);
+      if ((threadIdx.x & 31) == 0) {
+        atomic_max_nonneg(I.conv + (it & 1) * 2 + 0, dmax);
+        atomic_max_nonneg(I.conv + (it & 1) * 2 + 1, pmax);
+      }
+    }
+    if (!grid_barrier(ctl.bar, abort_flag)) break;
+    // ---- phase C ----
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int i = 0; i < ctl.n_inst; ++i) {
+        if (!active[i]) continue;
+        const Inst &I = insts[i];
+        volatile unsigned long long *cv = I.conv + (it & 1) * 2;
+        const double d = __longlong_as_double((long long)cv[0]);
+        const double m = __longlong_as_double((long long)cv[1]);
+        const int done_iters = it + 1;
+        bool done;
+        if (ctl.force_iters > 0) {
+          if (done_iters >= ctl.force_iters) active[i] = 0;
+          continue;
+        }
+        if (I.fixed_iters > 0) {
+          done = done_iters >= I.fixed_iters;
+        } else {
+          done = d <= I.si_tol * m;
+          if (!done && done_iters >= I.max_iter) {
+            done = true;
+            if (blockIdx.x == 0) set_status(I.status, kENotConv);
+          }
+        }
+        if (done) {
+          active[i] = 0;
+          if (blockIdx.x == 0) {
+            *I.iters = done_iters;
+            atomicAdd(I.iters_total, (unsigned long long)done_iters);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (*abort_flag && blockIdx.x == 0 && threadIdx.x == 0) {
+    for (int i = 0; i < ctl.n_inst; ++i)
+      if (active[i]) set_status(insts[i].status, kETimeout);
+  }
+}
+
+// ------------------------------------------------------------------
+// step 7: Galerkin operators
+// ------------------------------------------------------------------
+// V = T X for the transport operator T of axis direction dir (0: +x,
+// 1: -x, 2: +y, 3: -y) with zero boundary inflow: per cell the cell matrix
+// times the cell's coefficients minus the inflow terms of the upwind
+// neighbour's trace.  Stored divided by s, so that the cross Gram
+// sum_e Xs_i(e) Vs_j(e) of the stored rows is X_i^T T X_j.
+__global__ void __launch_bounds__(128) k_q1_transport(const Inst *__restrict__ insts, int dir) {
+  pdl_wait();
+  pdl_trigger();
+  const Inst &I = insts[blockIdx.y];
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!I.q1 || c >= I.N || *I.status != kOk) return;
+  const double ox = dir == 0 ? 1.0 : (dir == 1 ? -1.0 : 0.0), oy = dir == 2 ? 1.0 : (dir == 3 ? -1.0 : 0.0);
+  const double a = 0.5 * I.hx, b = 0.5 * I.hy;
+  double A0[16];
+  q1_cell_matrix(ox, oy, a, b, A0);
+  const int nx = I.nx, ny = I.ny, ix = c % nx, iy = c / nx;
+  int nb = -1, face = kFR;
+  if (dir == 0 && ix > 0) { nb = c - 1; face = kFR; }
+  if (dir == 1 && ix < nx - 1) { nb = c + 1; face = kFL; }
+  if (dir == 2 && iy > 0) { nb = c - nx; face = kFT; }
+  if (dir == 3 && iy < ny - 1) { nb = c + nx; face = kFB; }
+  const size_t M = (size_t)4 * I.N;
+  const double *X = as_c<double>(I.X);
+  for (int j = 0; j < I.r; ++j) {
+    const double *Xj = X + M * j;
+    double u[4], out[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) u[m] = Xj[(size_t)4 * c + m] * q1_unscale(m);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      double t = 0.0;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) t += A0[i + 4 * m] * u[m];
+      out[i] = t;
+    }
+    if (nb >= 0) {
+      double un[4], t0, t1, inr[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int m = 0; m < 4; ++m) un[m] = Xj[(size_t)4 * nb + m] * q1_unscale(m);
+      q1_trace(face, un, t0, t1);
+      if (dir < 2) q1_inflow(ox, oy, a, b, t0, t1, 0.0, 0.0, inr);
+      else q1_inflow(ox, oy, a, b, 0.0, 0.0, t0, t1, inr);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) out[i] -= inr[i];
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) I.q1_v[(size_t)4 * c + m + M * j] = out[m] * q1_unscale(m);
+  }
+}
+
+// One CTA per instance: q^_j = hx hy sum_c q_c X_j(c, 0); the inflow vectors
+// of a unit isotropic inflow on each edge, (face length) x the trace's
+// constant summed along the edge (left: X0 - X1, right: X0 + X1, bottom:
+// X0 - X2, top: X0 + X2, unscaled); then P S0 (P reduced before).
+__global__ void __launch_bounds__(256) k_q1_vec(const Inst *__restrict__ insts) {
+  pdl_wait();
+  pdl_trigger();
+  const Inst &I = insts[blockIdx.x];
+  if (!I.q1 || *I.status != kOk) return;
+  __shared__ double red[256];
+  const int r = I.r, nx = I.nx, ny = I.ny, t = threadIdx.x;
+  const size_t M = (size_t)4 * I.N;
+  const double *X = as_c<double>(I.X), *q = as_c<double>(I.q);
+  double *vec = I.small + I.lay.vec;
+  auto block_sum = [&](double v) {
+    red[t] = v;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+      if (t < s) red[t] += red[t + s];
+      __syncthreads();
+    }
+    const double x = red[0];
+    __syncthreads();
+    return x;
+  };
+  for (int j = 0; j < r; ++j) {
+    const double *Xj = X + M * j;
+    double s = 0.0;
+    for (int c = t; c < I.N; c += blockDim.x) s += q[c] * Xj[(size_t)4 * c];
+    s = block_sum(s);
+    double l = 0.0, rr = 0.0;
+    for (int iy = t; iy < ny; iy += blockDim.x) {
+      const size_t cl = (size_t)4 * (iy * nx), cr = (size_t)4 * (iy * nx + nx - 1);
+      l += Xj[cl] - kQ1Sqrt3 * Xj[cl + 1];
+      rr += Xj[cr] + kQ1Sqrt3 * Xj[cr + 1];
+    }
+    l = block_sum(l);
+    rr = block_sum(rr);
+    double bo = 0.0, to = 0.0;
+    for (int ix = t; ix < nx; ix += blockDim.x) {
+      const size_t cb = (size_t)4 * ix, ct = (size_t)4 * ((ny - 1) * nx + ix);
+      bo += Xj[cb] - kQ1Sqrt3 * Xj[cb + 2];
+      to += Xj[ct] + kQ1Sqrt3 * Xj[ct + 2];
+    }
+    bo = block_sum(bo);
+    to = block_sum(to);
+    if (t == 0) {
+      vec[j] = I.h2 * s;
+      vec[r + j] = I.hy * l;
+      vec[2 * r + j] = I.hy * rr;
+      vec[3 * r + j] = I.hx * bo;
+      vec[4 * r + j] = I.hx * to;
+    }
+  }
+  const double *P = I.small + I.lay.P;
+  for (int e = t; e < r * r; e += blockDim.x) {
+    const int i = e % r, j = e / r;
+    double x = 0.0;
+    for (int l = 0; l < r; ++l) x += P[i + r * l] * I.S0[l + r * j];
+    I.small[I.lay.PS0 + e] = x;
+  }
+}
+
+// ------------------------------------------------------------------
+// step 9
+// ------------------------------------------------------------------
+// One thread per coefficient row: X0 <- X U, and in the rows m = 0 the
+// temperature update with the cell average phi = X(4c, :) (L w).
+__global__ void __launch_bounds__(128) k_q1_tupdate(const Inst *__restrict__ insts) {
+  pdl_wait();
+  pdl_trigger();
+  const Inst &I = insts[blockIdx.y];
+  if (!I.q1) return;
+  __shared__ double U[kMaxRank * kMaxRank], vp[kMaxRank];
+  const int r = I.r;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) U[e] = I.small[I.lay.U + e];
+  for (int e = threadIdx.x; e < r; e += blockDim.x) vp[e] = I.small[I.lay.vphi + e];
+  __syncthreads();
+  const size_t M = (size_t)4 * I.N;
+  const size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (e >= M || *I.status != kOk) return;
+  const double *X = as_c<double>(I.X);
+  double *X0 = as<double>(I.X0);
+  double x[kMaxRank];
+  double phi = 0.0;
+#pragma unroll
+  for (int i = 0; i < kMaxRank; ++i) {
+    x[i] = i < r ? X[e + M * i] : 0.0;
+    phi += x[i] * (i < r ? vp[i] : 0.0);
+  }
+  for (int j = 0; j < r; ++j) {
+    double v = 0.0;
+#pragma unroll
+    for (int i = 0; i < kMaxRank; ++i)
+      if (i < r) v += x[i] * U[i + r * j];
+    X0[e + M * j] = v;
+  }
+  if ((e & 3) != 0) return;
+  const int c = (int)(e >> 2);
+  const double T0 = I.T[c];
+  const double T = T0 + I.dt * sigma_at(I, c, T0) * (phi - 4.0 * kPi * I.B0[c]) / I.D[c];
+  I.T[c] = T;
+  if (!(T > 0.0)) {
+    atomicAdd(I.nonpos, 1);
+    if (!I.allow_nonpos) set_status(I.status, kENonPos);
+  }
+}
+
+// Full-rank SN on Q1: T from the cell average of the last source
+// iteration's phi.
+__global__ void __launch_bounds__(256) k_q1_sn_tupdate(const Inst *__restrict__ insts) {
+  pdl_wait();
+  pdl_trigger();
+  const Inst &I = insts[blockIdx.y];
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!I.q1 || c >= I.N || *I.status != kOk) return;
+  const int last = *I.iters - 1;  // iteration it writes phi1 (it even) or phi0 (odd)
+  const double *phi = as_c<double>((last & 1) ? I.phi0 : I.phi1);
+  const double T0 = I.T[c];
+  const double T = T0 + I.dt * sigma_at(I, c, T0) * (phi[(size_t)4 * c] - 4.0 * kPi * I.B0[c]) / I.D[c];
+  I.T[c] = T;
+  if (!(T > 0.0)) {
+    atomicAdd(I.nonpos, 1);
+    if (!I.allow_nonpos) set_status(I.status, kENonPos);
+  }
+}
+
+// Rows of a 4 N x cols Q1 matrix between stored (scaled) and plain Legendre
+// coefficients: to_plain = 1 divides by s, 0 multiplies.
+__global__ void k_q1_rescale(double *A, size_t rows, int cols, int to_plain) {
+  const size_t total = rows * (size_t)cols;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int m = (int)((e % rows) & 3);
+    A[e] *= to_plain ? q1_unscale(m) : q1_scale(m);
+  }
+}
+
+// ------------------------------------------------------------------
+// host launchers
+// ------------------------------------------------------------------
+cudaError_t launch_q1_coeff(const Inst *d, int n, int maxN, bool sn, cudaStream_t st) {
+  const dim3 g((maxN + 127) / 128, n);
+  return sn ? launch_pdl(k_q1_sn_prep, g, dim3(128), 0, st, d) : launch_pdl(k_q1_coeff, g, dim3(128), 0, st, d);
+}
+
+size_t q1_si_smem(int nx_max, int bands_max, int n_inst, int gam_max) {
+  return q1_si_smem_bytes(nx_max, bands_max, n_inst, gam_max);
+}
+
+// CTAs of the cooperative Q1 source iteration that fit at once (0: none).
+int q1_si_max_grid(int nx_max, int bands_max, int n_inst, int gam_max) {
+  const size_t smem = q1_si_smem_bytes(nx_max, bands_max, n_inst, gam_max);
+  if (cudaFuncSetAttribute(k_q1_si, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int per_sm = 0, dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_q1_si, kQ1NW * 32, smem) != cudaSuccess) return 0;
+  return per_sm * sms;
+}
+
+cudaError_t launch_q1_si(const Inst *d, const SiCtl &ctl, int grid, cudaStream_t st) {
+  const size_t smem = q1_si_smem_bytes(ctl.nx_max, ctl.bands_max, ctl.n_inst, ctl.gam_max);
+  cudaError_t e = cudaFuncSetAttribute(k_q1_si, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kQ1NW * 32);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_q1_si, d, ctl);
+}
+
+cudaError_t launch_q1_transport(const Inst *d, int n, int maxN, int dir, cudaStream_t st) {
+  return launch_pdl(k_q1_transport, dim3((maxN + 127) / 128, n), dim3(128), 0, st, d, dir);
+}
+cudaError_t launch_q1_vec(const Inst *d, int n, cudaStream_t st) {
+  return launch_pdl(k_q1_vec, dim3(n), dim3(256), 0, st, d);
+}
+cudaError_t launch_q1_tupdate(const Inst *d, int n, int maxN, bool sn, cudaStream_t st) {
+  if (sn) return launch_pdl(k_q1_sn_tupdate, dim3((maxN + 255) / 256, n), dim3(256), 0, st, d);
+  return launch_pdl(k_q1_tupdate, dim3((4 * maxN + 127) / 128, n), dim3(128), 0, st, d);
+}
+cudaError_t launch_q1_rescale(double *A, size_t rows, int cols, int to_plain, cudaStream_t st) {
+  const size_t total = rows * (size_t)cols;
+  const int blocks = (int)std::min<size_t>((total + 255) / 256, 4096);
+  k_q1_rescale<<<blocks, 256, 0, st>>>(A, rows, cols, to_plain);
+  return cudaGetLastError();
+}
+
+}  // namespace dlr
