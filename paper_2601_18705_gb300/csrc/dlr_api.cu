@@ -72,14 +72,14 @@ cudaError_t launch_aug_trunc(const Inst *, int, cudaStream_t);
 template <typename real> cudaError_t launch_refl_pre(const Inst *, int, int, int, cudaStream_t);
 template <typename real> cudaError_t launch_refl_kap(const Inst *, int, int, int, cudaStream_t);
 template <typename real> cudaError_t launch_refl_lstep(const Inst *, int, cudaStream_t);
-cudaError_t launch_q1_coeff(const Inst *, int, int, bool, cudaStream_t);
-size_t q1_si_smem(int, int, int, int);
-int q1_si_max_grid(int, int, int, int);
-cudaError_t launch_q1_si(const Inst *, const SiCtl &, int, cudaStream_t);
-cudaError_t launch_q1_transport(const Inst *, int, int, int, cudaStream_t);
-cudaError_t launch_q1_vec(const Inst *, int, cudaStream_t);
-cudaError_t launch_q1_tupdate(const Inst *, int, int, bool, cudaStream_t);
-cudaError_t launch_q1_rescale(double *, size_t, int, int, cudaStream_t);
+template <typename real> cudaError_t launch_q1_coeff(const Inst *, int, int, bool, cudaStream_t);
+template <typename real> size_t q1_si_smem(int, int, int, int);
+template <typename real> int q1_si_max_grid(int, int, int, int);
+template <typename real> cudaError_t launch_q1_si(const Inst *, const SiCtl &, int, cudaStream_t);
+template <typename real> cudaError_t launch_q1_transport(const Inst *, int, int, int, cudaStream_t);
+template <typename real> cudaError_t launch_q1_vec(const Inst *, int, cudaStream_t);
+template <typename real> cudaError_t launch_q1_tupdate(const Inst *, int, int, bool, cudaStream_t);
+cudaError_t launch_q1_rescale(void *, bool, size_t, int, int, cudaStream_t);
 }  // namespace dlr
 
 using namespace dlr;
@@ -445,7 +445,7 @@ static Sizes sizes_of(const dlr_problem *p, int sms) {
     if (p->reflect[0] || p->reflect[1] || p->reflect[2] || p->reflect[3])
       s.total += al((size_t)s.K * (p->nx + p->ny) * s.rs);  // boundary sources of reflective edges
     if (p->element == 1)  // Q1: psi, s0 and phi with 4 coefficients per cell
-      s.total += 2 * al((size_t)3 * s.N * s.K * 8) + 2 * al((size_t)3 * s.N * 8);
+      s.total += 2 * al((size_t)3 * s.N * s.K * s.rs) + 2 * al((size_t)3 * s.N * s.rs);
     return s;
   }
   // CTAs of the cell and angle reductions: whole clusters of kCl CTAs,
@@ -484,8 +484,8 @@ static Sizes sizes_of(const dlr_problem *p, int sms) {
   t += al(64) * 4 + al(sizeof(Inst));           // status, iters, conv, totals, inst
   if (p->dsa) t += kDsaArrays * al((size_t)s.N * s.rs) + al(64);  // DSA coefficients, CG vectors
   if (p->element == 1)  // Q1: X0, X, Psi, s0, phi with 4 rows per cell, Gram weights, T X
-    t += 3 * al((size_t)3 * s.N * r * 8) + al((size_t)3 * s.N * r1 * 8) + 2 * al((size_t)3 * s.N * 8) +
-         2 * al((size_t)4 * s.N * 8) + al((size_t)4 * s.N * r * 8);
+    t += 3 * al((size_t)3 * s.N * r * s.rs) + al((size_t)3 * s.N * r1 * s.rs) + 2 * al((size_t)3 * s.N * s.rs) +
+         2 * al((size_t)4 * s.N * 8) + al((size_t)4 * s.N * r * s.rs);
   if (p->reflect[0] || p->reflect[1] || p->reflect[2] || p->reflect[3]) {
     const size_t LB = (size_t)p->nx + p->ny;
     t += al(r1 * LB * s.rs) + al(2 * LB * r1 * 8) + al((size_t)s.K * LB * 8) + 2 * al((size_t)s.K * r1 * 8) +
@@ -542,7 +542,6 @@ static int validate(const dlr_problem *p) {
   if (p->sweep_mode < 0 || p->sweep_mode > 2) return fail(DLR_EINVAL, "sweep_mode must be 0, 1 or 2");
   if (p->element != 0 && p->element != 1) return fail(DLR_EINVAL, "element must be 0 or 1");
   if (p->element == 1) {
-    if (p->precision != DLR_FP64) return fail(DLR_EINVAL, "bilinear elements need precision DLR_FP64");
     if (p->dsa || p->augment || p->reflect[0] || p->reflect[1] || p->reflect[2] || p->reflect[3])
       return fail(DLR_EINVAL, "bilinear elements: no DSA, augmented step or reflective edges");
     if (!sn && p->selection != DLR_SEL_QDEIM)
@@ -568,7 +567,9 @@ static int validate(const dlr_problem *p) {
   const size_t need = p->precision == DLR_MIXED ? si_smem_bytes<float>(p->nx, (p->ny + 31) / 32, 256, gam, p->dsa)
                                                 : si_smem_bytes<double>(p->nx, (p->ny + 31) / 32, 256, gam, p->dsa);
   if (optin > 0 && need > (size_t)optin) return fail(DLR_EINVAL, "nx = %d too large for the sweep's shared memory", p->nx);
-  if (p->element == 1 && optin > 0 && q1_si_smem(p->nx, (p->ny + 31) / 32, 256, gam) > (size_t)optin)
+  const size_t need_q1 = p->precision == DLR_MIXED ? q1_si_smem<float>(p->nx, (p->ny + 31) / 32, 256, gam)
+                                                   : q1_si_smem<double>(p->nx, (p->ny + 31) / 32, 256, gam);
+  if (p->element == 1 && optin > 0 && need_q1 > (size_t)optin)
     return fail(DLR_EINVAL, "nx = %d too large for the bilinear sweep's shared memory", p->nx);
   return DLR_OK;
 }
@@ -628,7 +629,8 @@ static void fill_common(dlr_handle *h, const dlr_problem *problem) {
   I.refl_kap = I.refl_data = I.refl_y = I.refl_u = nullptr;
   I.refl_passes = nullptr;
   I.q1 = problem->element == 1 ? 1 : 0;
-  I.q1_wt = I.q1_ws = I.q1_v = nullptr;
+  I.q1_wt = I.q1_ws = nullptr;
+  I.q1_v = nullptr;
   I.grp = 0;
   I.grp_ng = 0;
   I.grp_tab = nullptr;
@@ -737,7 +739,13 @@ static int create_sn(dlr_handle *h, const dlr_problem *problem, dlr_handle **out
     for (int k = 0; k < K; ++k)
       for (int c = 0; c < N; ++c)
         psi_q1[(size_t)4 * c + rowsN * k] = planck(problem->a_rad, problem->c, problem->T0[c]);
-    chain(up(I.Psi, psi_q1.data(), psi_q1.size() * 8));
+    if (h->mixed) {
+      std::vector<float> pf(psi_q1.begin(), psi_q1.end());
+      chain(up(I.Psi, pf.data(), pf.size() * 4));
+      chain(cudaStreamSynchronize(h->st));
+    } else {
+      chain(up(I.Psi, psi_q1.data(), psi_q1.size() * 8));
+    }
   } else if (e == cudaSuccess) {
     e = h->mixed ? launch_sn_init<float>(I.Psi, I.T, N, K, problem->a_rad, problem->c, h->st)
                  : launch_sn_init<double>(I.Psi, I.T, N, K, problem->a_rad, problem->c, h->st);
@@ -843,7 +851,7 @@ int dlr_create(const dlr_problem *problem, const dlr_runtime *runtime, dlr_handl
     I.phi1 = A(rowsN * rs);
     I.q1_wt = (double *)A(rowsN * 8);
     I.q1_ws = (double *)A(rowsN * 8);
-    I.q1_v = (double *)A(rowsN * r * 8);
+    I.q1_v = A(rowsN * r * rs);
   }
   I.X0 = A(rowsN * m * rs);
   I.X = A(rowsN * m * rs);
@@ -936,7 +944,7 @@ int dlr_create(const dlr_problem *problem, const dlr_runtime *runtime, dlr_handl
     chain(cudaMemsetAsync(I.sgk, 0, (size_t)I.grp_ng * (kGA + 1) * I.glay * 4, h->st));
     chain(cudaMemsetAsync(I.spk, 0, 8 * I.glay * 4, h->st));
   }
-  std::vector<double> X0q;
+  std::vector<double> X0q;  // the Q1 basis (rows 4 c + m), uploaded in place of X0
   if (I.q1) {
     // the DG0 basis as Q1 fields: each cell's constant coefficient (stored
     // scale 1), slopes zero; still orthonormal in the h^2 inner product
@@ -950,13 +958,12 @@ int dlr_create(const dlr_problem *problem, const dlr_runtime *runtime, dlr_handl
       X0q[(size_t)4 * c + m + (size_t)4 * N * l] = 1.0 / std::sqrt(I.h2);
     }
   }
+  const std::vector<double> &X0u = I.q1 ? X0q : X0;
   if (h->mixed) {
-    std::vector<float> Xf(X0.begin(), X0.end());
+    std::vector<float> Xf(X0u.begin(), X0u.end());
     chain(up(I.X0, Xf.data(), Xf.size() * 4));
-  } else if (I.q1) {
-    chain(up(I.X0, X0q.data(), X0q.size() * 8));
   } else {
-    chain(up(I.X0, X0.data(), X0.size() * 8));
+    chain(up(I.X0, X0u.data(), X0u.size() * 8));
   }
   chain(cudaMemsetAsync(I.status, 0, 64, h->st));
   chain(cudaMemsetAsync(I.nonpos, 0, 64, h->st));
@@ -1178,7 +1185,9 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
                            : si_max_grid<double>(b->nx_max, b->bands_max, n, gam_max, any_dsa);
   b->grid_grp = b->grp_ok ? si_grp_max_grid(b->nx_max, b->bands_max, n, b->grp_stages) : 0;
   if (b->grp_ok && b->grid_grp <= 0) b->grp_ok = false;
-  if (b->q1) b->grid_angle = q1_si_max_grid(b->nx_max, b->bands_max, n, gam_max);
+  if (b->q1)
+    b->grid_angle = b->mixed ? q1_si_max_grid<float>(b->nx_max, b->bands_max, n, gam_max)
+                             : q1_si_max_grid<double>(b->nx_max, b->bands_max, n, gam_max);
   if (b->grid_angle <= 0) {
     delete b;
     return fail(DLR_ECUDA, "the source-iteration kernel does not fit on this GPU");
@@ -1505,14 +1514,14 @@ static int enqueue_pre(Batch *b) {
   const Inst *d = b->d_insts;
   const int n = b->n;
   if (b->sn) {  // full-rank SN: coefficients, fixed sources, starting phi
-    if (b->q1) LK(launch_q1_coeff(d, n, b->maxN, true, b->st));
+    if (b->q1) LK(launch_q1_coeff<real>(d, n, b->maxN, true, b->st));
     else LK(launch_sn_prep<real>(d, n, b->maxN, b->st));
     LK(launch_si_prep(d, n, b->ctl, b->st));
     return DLR_OK;
   }
   LK(launch_select(d, n, b->sel_slice_max, b->st));
   if (b->q1) {  // bilinear elements: coefficients, psi0, fixed sources, starting phi
-    LK(launch_q1_coeff(d, n, b->maxN, false, b->st));
+    LK(launch_q1_coeff<real>(d, n, b->maxN, false, b->st));
     LK(launch_si_prep(d, n, b->ctl, b->st));
     return DLR_OK;
   }
@@ -1532,7 +1541,7 @@ static int enqueue_post(Batch *b) {
   const int n = b->n;
   cudaStream_t st = b->st;
   if (b->sn) {
-    if (b->q1) LK(launch_q1_tupdate(d, n, b->maxN, true, st));
+    if (b->q1) LK(launch_q1_tupdate<real>(d, n, b->maxN, true, st));
     else LK(launch_sn_tupdate<real>(d, n, b->maxN, st));
     return DLR_OK;
   }
@@ -1564,12 +1573,12 @@ static int enqueue_post(Batch *b) {
     // refilled for each), M_t, M_s, P, the seven reductions, q^, the edge
     // vectors and P S0
     for (int dir = 0; dir < 4; ++dir) {
-      LK(launch_q1_transport(d, n, b->maxN, dir, st));
-      LK(launch_tsgram<double>(b->g_q1t + (size_t)dir * n, n, b->pbmax, 0, st));
+      LK(launch_q1_transport<real>(d, n, b->maxN, dir, st));
+      LK(launch_tsgram<real>(b->g_q1t + (size_t)dir * n, n, b->pbmax, 0, st));
     }
-    LK(launch_tsgram<double>(b->g_q1t + (size_t)4 * n, 3 * n, b->pbmax, 0, st));
+    LK(launch_tsgram<real>(b->g_q1t + (size_t)4 * n, 3 * n, b->pbmax, 0, st));
     LK(launch_reduce(b->r_q1, 7 * n, b->rmax * b->rmax, st));
-    LK(launch_q1_vec(d, n, st));
+    LK(launch_q1_vec<real>(d, n, st));
   } else {
     LK(launch_project<real>(d, n, b->pbmax, b->rmax, st));
     LK(launch_reduce(b->r_proj, n, proj_count(b->rmax), st));
@@ -1608,7 +1617,7 @@ static int enqueue_post(Batch *b) {
     LKM((launch_apply<double, double>(b->a_cw, n, b->maxK, b->rmask, st)), b->rmask);
   }
   // step 9
-  if (b->q1) LK(launch_q1_tupdate(d, n, b->maxN, false, st));
+  if (b->q1) LK(launch_q1_tupdate<real>(d, n, b->maxN, false, st));
   else LKM(launch_tupdate<real>(d, n, b->maxN, b->rmask, st), b->rmask);
   return DLR_OK;
 }
@@ -1696,7 +1705,9 @@ static cudaError_t launch_si_batch(const Batch *b, const SiCtl &c) {
                                               b->st);
     return e == cudaSuccess ? cudaGraphLaunch(b->si, b->st) : e;
   }
-  if (b->q1) return launch_q1_si(b->d_insts, c, b->si_grid, b->st);
+  if (b->q1)
+    return b->mixed ? launch_q1_si<float>(b->d_insts, c, b->si_grid, b->st)
+                    : launch_q1_si<double>(b->d_insts, c, b->si_grid, b->st);
   return b->mixed ? launch_si<float>(b->d_insts, c, b->si_grid, b->st)
                   : launch_si<double>(b->d_insts, c, b->si_grid, b->st);
 }
@@ -2016,9 +2027,61 @@ static int canonicalize(dlr_handle *h) {
   CK(launch_svd(b->d_insts, 1, 2, h->st));
   CK((launch_apply<double, double>(b->a_cw, 1, h->K, rank_mask(h->r), h->st)));
   CK(launch_sign(b->d_insts, 1, h->K, h->st));
-  if (h->mixed) CK((launch_apply<float, float>(b->a_cx, 1, h->N, rank_mask(h->r), h->st)));
-  else CK((launch_apply<double, double>(b->a_cx, 1, h->inst.q1 ? 4 * h->N : h->N, rank_mask(h->r), h->st)));
+  const int rowsX = h->inst.q1 ? 4 * h->N : h->N;  // rows of X0 (Q1: 4 per cell)
+  if (h->mixed) CK((launch_apply<float, float>(b->a_cx, 1, rowsX, rank_mask(h->r), h->st)));
+  else CK((launch_apply<double, double>(b->a_cx, 1, rowsX, rank_mask(h->r), h->st)));
   h->canonical = true;
+  return DLR_OK;
+}
+
+// A rows x cols matrix of the working precision on the device, copied out
+// to FP64 (host or device memory); with bilinear elements the stored rows
+// are scaled and go out as plain Legendre coefficients.
+static int copy_out(dlr_handle *h, const void *src, double *dst, size_t rows, int cols, bool on_device) {
+  const size_t n = rows * cols;
+  if (!h->mixed) {
+    CK(cudaMemcpyAsync(dst, src, n * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
+  } else if (on_device) {
+    k_widen<<<1024, 256, 0, h->st>>>((const float *)src, dst, n);
+    CK(cudaGetLastError());
+  } else {
+    std::vector<float> tmp(n);
+    CK(cudaMemcpyAsync(tmp.data(), src, n * 4, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    for (size_t i = 0; i < n; ++i) dst[i] = tmp[i];
+  }
+  if (h->inst.q1) {
+    if (on_device) {
+      CK(launch_q1_rescale(dst, false, rows, cols, 1, h->st));
+    } else {
+      CK(cudaStreamSynchronize(h->st));
+      for (size_t e = 0; e < n; ++e) dst[e] *= q1_unscale((int)((e % rows) & 3));
+    }
+  }
+  return DLR_OK;
+}
+
+// The reverse of copy_out: FP64 (host or device) into the working precision.
+static int copy_in(dlr_handle *h, void *dst, const double *src, size_t rows, int cols, bool on_device) {
+  const size_t n = rows * cols;
+  std::vector<double> scaled;
+  if (h->inst.q1 && !on_device) {
+    scaled.assign(src, src + n);
+    for (size_t e = 0; e < n; ++e) scaled[e] *= q1_scale((int)((e % rows) & 3));
+    src = scaled.data();
+  }
+  if (!h->mixed) {
+    CK(cudaMemcpyAsync(dst, src, n * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+    if (!on_device) CK(cudaStreamSynchronize(h->st));
+  } else if (on_device) {
+    k_narrow<<<1024, 256, 0, h->st>>>(src, (float *)dst, n);
+    CK(cudaGetLastError());
+  } else {
+    std::vector<float> tmp(src, src + n);
+    CK(cudaMemcpyAsync(dst, tmp.data(), n * 4, cudaMemcpyHostToDevice, h->st));
+    CK(cudaStreamSynchronize(h->st));
+  }
+  if (h->inst.q1 && on_device) CK(launch_q1_rescale(dst, h->mixed, rows, cols, 0, h->st));
   return DLR_OK;
 }
 
@@ -2030,29 +2093,11 @@ int dlr_get_factors(dlr_handle *h, double *X, double *S, double *W, int32_t *r_o
     if (rc) return rc;
   }
   const size_t rowsX = h->inst.q1 ? (size_t)4 * h->N : (size_t)h->N;
-  const size_t nX = rowsX * h->r;
   const cudaMemcpyKind k = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (r_out) *r_out = h->r;
   if (X) {
-    if (h->inst.q1) {  // plain Legendre coefficients out (stored scaled)
-      CK(cudaMemcpyAsync(X, h->inst.X0, nX * 8, k, h->st));
-      if (out_on_device) {
-        CK(launch_q1_rescale(X, rowsX, h->r, 1, h->st));
-      } else {
-        CK(cudaStreamSynchronize(h->st));
-        for (size_t e = 0; e < nX; ++e) X[e] *= q1_unscale((int)((e % rowsX) & 3));
-      }
-    } else if (!h->mixed) {
-      CK(cudaMemcpyAsync(X, h->inst.X0, nX * 8, k, h->st));
-    } else if (out_on_device) {
-      k_widen<<<1024, 256, 0, h->st>>>((const float *)h->inst.X0, X, nX);
-      CK(cudaGetLastError());
-    } else {
-      std::vector<float> tmp(nX);
-      CK(cudaMemcpyAsync(tmp.data(), h->inst.X0, nX * 4, cudaMemcpyDeviceToHost, h->st));
-      CK(cudaStreamSynchronize(h->st));
-      for (size_t i = 0; i < nX; ++i) X[i] = tmp[i];
-    }
+    const int rc = copy_out(h, h->inst.X0, X, rowsX, h->r, out_on_device != 0);
+    if (rc) return rc;
   }
   if (S) CK(cudaMemcpyAsync(S, h->inst.S0, (size_t)h->r * h->r * 8, k, h->st));
   if (W) CK(cudaMemcpyAsync(W, h->inst.W0, (size_t)h->K * h->r * 8, k, h->st));
@@ -2064,27 +2109,10 @@ int dlr_set_factors(dlr_handle *h, const double *X, const double *S, const doubl
   if (h->sn) return fail(DLR_EINVAL, "a full-rank SN handle has no factors (dlr_set_psi)");
   h->canonical = false;
   const size_t rowsX = h->inst.q1 ? (size_t)4 * h->N : (size_t)h->N;
-  const size_t nX = rowsX * h->r;
   const cudaMemcpyKind k = in_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  if (h->inst.q1) {  // plain Legendre coefficients in, stored scaled
-    if (in_on_device) {
-      CK(cudaMemcpyAsync(h->inst.X0, X, nX * 8, k, h->st));
-      CK(launch_q1_rescale((double *)h->inst.X0, rowsX, h->r, 0, h->st));
-    } else {
-      std::vector<double> tmp(X, X + nX);
-      for (size_t e = 0; e < nX; ++e) tmp[e] *= q1_scale((int)((e % rowsX) & 3));
-      CK(cudaMemcpyAsync(h->inst.X0, tmp.data(), nX * 8, cudaMemcpyHostToDevice, h->st));
-      CK(cudaStreamSynchronize(h->st));
-    }
-  } else if (!h->mixed) {
-    CK(cudaMemcpyAsync(h->inst.X0, X, nX * 8, k, h->st));
-  } else if (in_on_device) {
-    k_narrow<<<1024, 256, 0, h->st>>>(X, (float *)h->inst.X0, nX);
-    CK(cudaGetLastError());
-  } else {
-    std::vector<float> tmp(X, X + nX);
-    CK(cudaMemcpyAsync(h->inst.X0, tmp.data(), nX * 4, cudaMemcpyHostToDevice, h->st));
-    CK(cudaStreamSynchronize(h->st));
+  {
+    const int rc = copy_in(h, h->inst.X0, X, rowsX, h->r, in_on_device != 0);
+    if (rc) return rc;
   }
   CK(cudaMemcpyAsync(h->inst.S0, S, (size_t)h->r * h->r * 8, k, h->st));
   CK(cudaMemcpyAsync(h->inst.W0, W, (size_t)h->K * h->r * 8, k, h->st));
@@ -2116,27 +2144,9 @@ int dlr_get_psi(dlr_handle *h, double *out, int32_t out_on_device) {
   if (!h || !out) return fail(DLR_EINVAL, "NULL argument");
   if (!h->sn) return fail(DLR_EINVAL, "dlr_get_psi needs a full-rank SN handle (dlr_get_factors)");
   const size_t rows = h->inst.q1 ? (size_t)4 * h->N : (size_t)h->N;
-  const size_t n = rows * h->K;
-  if (h->inst.q1) {  // plain Legendre coefficients out (stored scaled)
-    CK(cudaMemcpyAsync(out, h->inst.Psi, n * 8, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                       h->st));
-    if (out_on_device) {
-      CK(launch_q1_rescale(out, rows, h->K, 1, h->st));
-    } else {
-      CK(cudaStreamSynchronize(h->st));
-      for (size_t e = 0; e < n; ++e) out[e] *= q1_unscale((int)((e % rows) & 3));
-    }
-  } else if (!h->mixed) {
-    CK(cudaMemcpyAsync(out, h->inst.Psi, n * 8, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                       h->st));
-  } else if (out_on_device) {
-    k_widen<<<1024, 256, 0, h->st>>>((const float *)h->inst.Psi, out, n);
-    CK(cudaGetLastError());
-  } else {
-    std::vector<float> tmp(n);
-    CK(cudaMemcpyAsync(tmp.data(), h->inst.Psi, n * 4, cudaMemcpyDeviceToHost, h->st));
-    CK(cudaStreamSynchronize(h->st));
-    for (size_t i = 0; i < n; ++i) out[i] = tmp[i];
+  {
+    const int rc = copy_out(h, h->inst.Psi, out, rows, h->K, out_on_device != 0);
+    if (rc) return rc;
   }
   return sync_status(h);
 }
@@ -2145,28 +2155,9 @@ int dlr_set_psi(dlr_handle *h, const double *in, int32_t in_on_device) {
   if (!h || !in) return fail(DLR_EINVAL, "NULL argument");
   if (!h->sn) return fail(DLR_EINVAL, "dlr_set_psi needs a full-rank SN handle (dlr_set_factors)");
   const size_t rows = h->inst.q1 ? (size_t)4 * h->N : (size_t)h->N;
-  const size_t n = rows * h->K;
-  if (h->inst.q1) {  // plain Legendre coefficients in, stored scaled
-    if (in_on_device) {
-      CK(cudaMemcpyAsync(h->inst.Psi, in, n * 8, cudaMemcpyDeviceToDevice, h->st));
-      CK(launch_q1_rescale((double *)h->inst.Psi, rows, h->K, 0, h->st));
-    } else {
-      std::vector<double> tmp(in, in + n);
-      for (size_t e = 0; e < n; ++e) tmp[e] *= q1_scale((int)((e % rows) & 3));
-      CK(cudaMemcpyAsync(h->inst.Psi, tmp.data(), n * 8, cudaMemcpyHostToDevice, h->st));
-      CK(cudaStreamSynchronize(h->st));
-    }
-  } else if (!h->mixed) {
-    CK(cudaMemcpyAsync(h->inst.Psi, in, n * 8, in_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                       h->st));
-    if (!in_on_device) CK(cudaStreamSynchronize(h->st));
-  } else if (in_on_device) {
-    k_narrow<<<1024, 256, 0, h->st>>>(in, (float *)h->inst.Psi, n);
-    CK(cudaGetLastError());
-  } else {
-    std::vector<float> tmp(in, in + n);
-    CK(cudaMemcpyAsync(h->inst.Psi, tmp.data(), n * 4, cudaMemcpyHostToDevice, h->st));
-    CK(cudaStreamSynchronize(h->st));
+  {
+    const int rc = copy_in(h, h->inst.Psi, in, rows, h->K, in_on_device != 0);
+    if (rc) return rc;
   }
   return DLR_OK;
 }

@@ -164,12 +164,13 @@ struct Inst {
   // g_k, refl_passes the fixed-point passes of the last step.
   double *refl_kap, *refl_data, *refl_y, *refl_u;
   int *refl_passes;
-  // bilinear (Q1) elements (k_q1.cu; FP64): X0, X, Psi, s0 are 4 N x r,
-  // phi0, phi1 4 N, rows e = 4 c + m scaled by (1, 1/sqrt3, 1/sqrt3, 1/3);
-  // q1_wt, q1_ws (4 N) the row weights sigma_t, sigma_s of the step-7 mass
-  // Grams, q1_v (4 N x r) the transport operator applied to X
+  // bilinear (Q1) elements (k_q1.cu): X0, X, Psi, s0 are 4 N x r, phi0,
+  // phi1 4 N (real), rows e = 4 c + m scaled by (1, 1/sqrt3, 1/sqrt3, 1/3);
+  // q1_wt, q1_ws (FP64, 4 N) the row weights sigma_t, sigma_s of the step-7
+  // mass Grams, q1_v (real, 4 N x r) the transport operator applied to X
   int q1;
-  double *q1_wt, *q1_ws, *q1_v;
+  double *q1_wt, *q1_ws;
+  void *q1_v;
   // grouped-angle sweep (mixed-precision DLR instances without DSA or
   // reflective edges, grp = 1): the chosen angles are grouped by quadrant
   // (kGA per group, table grp_tab of grp_ng records, ordered by quadrant),

@@ -1,7 +1,9 @@
 // k_q1.cu -- the SN-like DLR step (Algorithm 1) and the full-rank SN step on
 // bilinear (Q1) elements: upwind DG with the Legendre basis 1, xi, eta,
 // xi eta on each cell (Section 4.4's volume term G_j and face matrices F_d
-// with the paper's bilinear elements), FP64.
+// with the paper's bilinear elements).  "real" is the working precision of
+// the O(N) work (float in mixed precision, double in FP64); the r x r and
+// per-angle algebra of steps 2, 5, 7, 8 stays in FP64 as on DG0 cells.
 //
 // Storage.  A Q1 field has 4 coefficients per cell, row e = 4 c + m.  They
 // are stored scaled by s = (1, 1/sqrt3, 1/sqrt3, 1/3): the scaled basis is
@@ -37,7 +39,7 @@ namespace dlr {
 
 namespace {
 
-constexpr int kQ1NW = 4;       // sweeping warps per CTA
+constexpr int kQ1NW = 8;       // sweeping warps per CTA (bands in flight per angle)
 constexpr int kQ1Pub = 8;      // columns per progress publication
 constexpr uint64_t kQ1WaitNs = 4000000000ull;
 constexpr unsigned kQ1Full = 0xffffffffu;
@@ -63,15 +65,16 @@ __device__ __forceinline__ void q1_basis_trace(int face, int i, double &t0, doub
   }
 }
 // The trace of the field u (unscaled coefficients) on a face.
-__device__ __forceinline__ void q1_trace(int face, const double *u, double &t0, double &t1) {
-  t0 = 0.0;
-  t1 = 0.0;
+template <typename real>
+__device__ __forceinline__ void q1_trace(int face, const real *u, real &t0, real &t1) {
+  t0 = real(0);
+  t1 = real(0);
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     double a0, a1;
     q1_basis_trace(face, i, a0, a1);
-    t0 += a0 * u[i];
-    t1 += a1 * u[i];
+    if (a0 != 0.0) t0 += real(a0) * u[i];
+    if (a1 != 0.0) t1 += real(a1) * u[i];
   }
 }
 // int_{-1}^{1} (c0 + c1 s)(d0 + d1 s) ds
@@ -106,10 +109,11 @@ __device__ __forceinline__ void q1_cell_matrix(double ox, double oy, double a, d
       A[i + 4 * j] += cx * q1_face_int(xi0, xi1, xj0, xj1) + cy * q1_face_int(yi0, yi1, yj0, yj1);
     }
 }
-// The inflow terms |Om . n| (length / 2) int u_in trace_i of the traces
-// (ux0, ux1) and (uy0, uy1) entering through the upwind x- and y-faces.
-__device__ __forceinline__ void q1_inflow(double ox, double oy, double a, double b, double ux0, double ux1,
-                                          double uy0, double uy1, double *r) {
+// The inflow coefficients: the terms |Om . n| (length / 2) int u_in trace_i
+// of the traces (ux0, ux1), (uy0, uy1) entering through the upwind x- and
+// y-faces are Fx[i] ux0 + Gx[i] ux1 + Fy[i] uy0 + Gy[i] uy1.
+__device__ __forceinline__ void q1_inflow_coef(double ox, double oy, double a, double b, double *Fx, double *Gx,
+                                               double *Fy, double *Gy) {
   const int fx = ox >= 0 ? kFL : kFR, fy = oy >= 0 ? kFB : kFT;
   const double cx = fabs(ox) * b, cy = fabs(oy) * a;
 #pragma unroll
@@ -117,29 +121,37 @@ __device__ __forceinline__ void q1_inflow(double ox, double oy, double a, double
     double x0, x1, y0, y1;
     q1_basis_trace(fx, i, x0, x1);
     q1_basis_trace(fy, i, y0, y1);
-    r[i] += cx * q1_face_int(x0, x1, ux0, ux1) + cy * q1_face_int(y0, y1, uy0, uy1);
+    Fx[i] = cx * 2.0 * x0;
+    Gx[i] = cx * (2.0 / 3.0) * x1;
+    Fy[i] = cy * 2.0 * y0;
+    Gy[i] = cy * (2.0 / 3.0) * y1;
   }
 }
-// A x = r for the 4 x 4 cell matrix, Gaussian elimination without pivoting:
-// the symmetric part of an upwind DG cell matrix is positive definite (half
-// the inflow and outflow face terms plus the reaction), so no pivot
-// vanishes.  x overwrites r; A is destroyed.
-__device__ __forceinline__ void q1_solve4(double *A, double *r) {
-  double inv[4];
+// A x = r for the 4 x 4 cell matrix by division-free elimination: row i
+// becomes d_p row_i - a_ip row_p (no pivoting: the symmetric part of an
+// upwind DG cell matrix is positive definite -- half the inflow and outflow
+// face terms plus the reaction -- so no pivot vanishes), then the four
+// reciprocals of the diagonal at once and the back substitution.  x
+// overwrites r; A is destroyed.
+template <typename real>
+__device__ __forceinline__ void q1_solve4(real *A, real *r) {
 #pragma unroll
-  for (int p = 0; p < 4; ++p) {
-    inv[p] = 1.0 / A[p + 4 * p];
+  for (int p = 0; p < 3; ++p) {
+    const real d = A[p + 4 * p];
 #pragma unroll
     for (int i = p + 1; i < 4; ++i) {
-      const double f = A[i + 4 * p] * inv[p];
+      const real f = A[i + 4 * p];
 #pragma unroll
-      for (int j = p + 1; j < 4; ++j) A[i + 4 * j] -= f * A[p + 4 * j];
-      r[i] -= f * r[p];
+      for (int j = p + 1; j < 4; ++j) A[i + 4 * j] = d * A[i + 4 * j] - f * A[p + 4 * j];
+      r[i] = d * r[i] - f * r[p];
     }
   }
+  real inv[4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) inv[p] = real(1) / A[p + 4 * p];
 #pragma unroll
   for (int p = 3; p >= 0; --p) {
-    double x = r[p];
+    real x = r[p];
 #pragma unroll
     for (int j = p + 1; j < 4; ++j) x -= A[p + 4 * j] * r[j];
     r[p] = x * inv[p];
@@ -152,15 +164,16 @@ __device__ __forceinline__ void q1_solve4(double *A, double *r) {
 // One thread per cell: the coefficients, the weights of the mass Grams, and
 // per chosen angle j and coefficient m: psi0 = sum_l X0(e, l) C0(l, j),
 // s0_j(e) = q delta_m0 + psi0 / (c dt), phi(e) = sum_j gamma_j psi0_j(e).
+template <typename real>
 __global__ void __launch_bounds__(128) k_q1_coeff(const Inst *__restrict__ insts) {
   pdl_wait();
   pdl_trigger();
   const Inst &I = insts[blockIdx.y];
   if (!I.q1) return;
-  __shared__ double C0s[kMaxRank * kMaxRank], gam[kMaxRank];
+  __shared__ real C0s[kMaxRank * kMaxRank], gam[kMaxRank];
   const int r = I.r;
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) C0s[e] = I.small[I.lay.C0 + e];
-  for (int e = threadIdx.x; e < r; e += blockDim.x) gam[e] = I.small[I.lay.gamma + e];
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) C0s[e] = real(I.small[I.lay.C0 + e]);
+  for (int e = threadIdx.x; e < r; e += blockDim.x) gam[e] = real(I.small[I.lay.gamma + e]);
   __syncthreads();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= I.N || *I.status != kOk) return;
@@ -168,27 +181,28 @@ __global__ void __launch_bounds__(128) k_q1_coeff(const Inst *__restrict__ insts
   I.B0[c] = cf.B;
   I.D[c] = cf.D;
   const double st = cf.sig + I.inv_cdt;
-  as<double>(I.sig_t)[c] = st;
-  as<double>(I.ss4)[c] = cf.ss / (4.0 * kPi);
-  as<double>(I.q)[c] = cf.q;
+  as<real>(I.sig_t)[c] = real(st);
+  as<real>(I.ss4)[c] = real(cf.ss / (4.0 * kPi));
+  as<real>(I.q)[c] = real(cf.q);
   const size_t M = (size_t)4 * I.N;
-  const double *X0 = as_c<double>(I.X0);
-  double *s0 = as<double>(I.s0), *phi = as<double>(I.phi0);
+  const real *X0 = as_c<real>(I.X0);
+  real *s0 = as<real>(I.s0), *phi = as<real>(I.phi0);
+  const real qr = real(cf.q), icdt = real(I.inv_cdt);
   for (int m = 0; m < 4; ++m) {
     const size_t e = (size_t)4 * c + m;
     I.q1_wt[e] = st;
     I.q1_ws[e] = cf.ss;
-    double x[kMaxRank];
+    real x[kMaxRank];
 #pragma unroll
-    for (int l = 0; l < kMaxRank; ++l) x[l] = l < r ? X0[e + M * l] : 0.0;
-    double ph = 0.0;
+    for (int l = 0; l < kMaxRank; ++l) x[l] = l < r ? X0[e + M * l] : real(0);
+    real ph = real(0);
     for (int j = 0; j < r; ++j) {
-      double p0 = 0.0;
+      real p0 = real(0);
 #pragma unroll
       for (int l = 0; l < kMaxRank; ++l)
-        if (l < r) p0 += x[l] * C0s[l + r * j];
-      s0[e + M * j] = (m == 0 ? cf.q : 0.0) + I.inv_cdt * p0;
-      ph += gam[j] * p0;
+        if (l < r) p0 = fmadd(x[l], C0s[l + r * j], p0);
+      s0[e + M * j] = fmadd(icdt, p0, m == 0 ? qr : real(0));
+      ph = fmadd(gam[j], p0, ph);
     }
     phi[e] = ph;
   }
@@ -196,6 +210,7 @@ __global__ void __launch_bounds__(128) k_q1_coeff(const Inst *__restrict__ insts
 
 // Full-rank SN on Q1: psi (4 N x K, scaled) holds psi^n; the same
 // coefficients, s0_k = q delta_m0 + psi^n_k / (c dt), phi^n = sum_k w_k psi^n_k.
+template <typename real>
 __global__ void __launch_bounds__(128) k_q1_sn_prep(const Inst *__restrict__ insts) {
   pdl_wait();
   pdl_trigger();
@@ -205,19 +220,20 @@ __global__ void __launch_bounds__(128) k_q1_sn_prep(const Inst *__restrict__ ins
   const CellCoef cf = cell_coefficients(I, c);
   I.B0[c] = cf.B;
   I.D[c] = cf.D;
-  as<double>(I.sig_t)[c] = cf.sig + I.inv_cdt;
-  as<double>(I.ss4)[c] = cf.ss / (4.0 * kPi);
-  as<double>(I.q)[c] = cf.q;
+  as<real>(I.sig_t)[c] = real(cf.sig + I.inv_cdt);
+  as<real>(I.ss4)[c] = real(cf.ss / (4.0 * kPi));
+  as<real>(I.q)[c] = real(cf.q);
   const size_t M = (size_t)4 * I.N;
-  const double *psi = as_c<double>(I.Psi);
-  double *s0 = as<double>(I.s0), *phi = as<double>(I.phi0);
+  const real *psi = as_c<real>(I.Psi);
+  real *s0 = as<real>(I.s0), *phi = as<real>(I.phi0);
+  const real qr = real(cf.q), icdt = real(I.inv_cdt);
   for (int m = 0; m < 4; ++m) {
     const size_t e = (size_t)4 * c + m;
-    double ph = 0.0;
+    real ph = real(0);
     for (int k = 0; k < I.K; ++k) {
-      const double p = psi[e + M * k];
-      s0[e + M * k] = (m == 0 ? cf.q : 0.0) + I.inv_cdt * p;
-      ph += I.w[k] * p;
+      const real p = psi[e + M * k];
+      s0[e + M * k] = fmadd(icdt, p, m == 0 ? qr : real(0));
+      ph = fmadd(real(I.w[k]), p, ph);
     }
     phi[e] = ph;
   }
@@ -228,13 +244,15 @@ __global__ void __launch_bounds__(128) k_q1_sn_prep(const Inst *__restrict__ ins
 // ------------------------------------------------------------------
 // Shared memory of k_q1_si: (kQ1NW + 1) edge rows of 2 x nx_max traces, the
 // band progress counters, the active flags and the scalar-flux weights.
+template <typename real>
 __host__ __device__ inline size_t q1_si_smem_bytes(int nx_max, int bands_max, int n_inst, int gam_max) {
-  return (size_t)(kQ1NW + 1) * 2 * nx_max * sizeof(double) + (size_t)(bands_max + 3) / 4 * 4 * sizeof(int) +
-         (size_t)(n_inst + 3) / 4 * 4 * sizeof(int) + (size_t)gam_max * sizeof(double);
+  return (size_t)(kQ1NW + 1) * 2 * nx_max * sizeof(real) + (size_t)(bands_max + 3) / 4 * 4 * sizeof(int) +
+         (size_t)(n_inst + 3) / 4 * 4 * sizeof(int) + (size_t)gam_max * sizeof(real) + 16;
 }
 
+template <typename real>
 struct Q1Smem {
-  double *edge;   // (kQ1NW + 1) x 2 x nx_max
+  real *edge;     // (kQ1NW + 1) x 2 x nx_max
   int *prog;      // per band: columns published
   int nx_max;
 };
@@ -263,7 +281,8 @@ __device__ __forceinline__ bool q1_wait_prog(volatile int *prog, int b, int need
 // registers, the lower one comes from lane i - 1 by a shuffle, and lane 0
 // takes it from the edge row the band below published.  Returns false (in
 // every thread of the CTA) if a wait gave up.
-__device__ bool q1_sweep(const Inst &I, int j, const Q1Smem &S, const double *pold, volatile int *abort_flag) {
+template <typename real>
+__device__ bool q1_sweep(const Inst &I, int j, const Q1Smem<real> &S, const real *pold, volatile int *abort_flag) {
   const int nx = I.nx, ny = I.ny, nb = (ny + 31) / 32;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   __syncthreads();
@@ -273,25 +292,39 @@ __device__ bool q1_sweep(const Inst &I, int j, const Q1Smem &S, const double *po
   const double ox = I.ox[k], oy = I.oy[k];
   const double a = 0.5 * I.hx, bh = 0.5 * I.hy;
   const bool flx = ox < 0, fly = oy < 0;
-  const double inx = ox > 0 ? I.psi_edge[0] : (ox < 0 ? I.psi_edge[1] : 0.0);
-  const double iny = oy > 0 ? I.psi_edge[2] : (oy < 0 ? I.psi_edge[3] : 0.0);
-  double A0[16];
-  q1_cell_matrix(ox, oy, a, bh, A0);
+  const real inx = real(ox > 0 ? I.psi_edge[0] : (ox < 0 ? I.psi_edge[1] : 0.0));
+  const real iny = real(oy > 0 ? I.psi_edge[2] : (oy < 0 ? I.psi_edge[3] : 0.0));
+  real A0[16], dm[4], Fx[4], Gx[4], Fy[4], Gy[4];
+  {
+    double Ad[16], f0[4], f1[4], f2[4], f3[4];
+    q1_cell_matrix(ox, oy, a, bh, Ad);
+    q1_inflow_coef(ox, oy, a, bh, f0, f1, f2, f3);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) A0[e] = real(Ad[e]);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      dm[m] = real(a * bh * q1_mass(m));
+      Fx[m] = real(f0[m]);
+      Gx[m] = real(f1[m]);
+      Fy[m] = real(f2[m]);
+      Gy[m] = real(f3[m]);
+    }
+  }
   const int fox = ox >= 0 ? kFR : kFL, foy = oy >= 0 ? kFT : kFB;
   const size_t M = (size_t)4 * I.N;
-  const double *sig_t = as_c<double>(I.sig_t), *ss4 = as_c<double>(I.ss4);
-  const double *s0 = as_c<double>(I.s0) + M * j;
-  double *psi = as<double>(I.Psi) + M * j;
+  const real *sig_t = as_c<real>(I.sig_t), *ss4 = as_c<real>(I.ss4);
+  const real *s0 = as_c<real>(I.s0) + M * j;
+  real *psi = as<real>(I.Psi) + M * j;
   volatile int *prog = S.prog;
   bool ok = true;
   for (int b = wid; b < nb && ok; b += kQ1NW) {
     const int v = b * 32 + lane;
     const bool row_ok = v < ny;
     const int iy = fly ? ny - 1 - v : v;
-    const double *ein = S.edge + (size_t)((b + kQ1NW) % (kQ1NW + 1)) * 2 * S.nx_max;
-    double *eout = S.edge + (size_t)(b % (kQ1NW + 1)) * 2 * S.nx_max;
-    double ux0 = inx, ux1 = 0.0;  // trace entering through the left face
-    double ty0 = 0.0, ty1 = 0.0;  // this lane's last top trace
+    const real *ein = S.edge + (size_t)((b + kQ1NW) % (kQ1NW + 1)) * 2 * S.nx_max;
+    real *eout = S.edge + (size_t)(b % (kQ1NW + 1)) * 2 * S.nx_max;
+    real ux0 = inx, ux1 = real(0);  // trace entering through the left face
+    real ty0 = real(0), ty1 = real(0);  // this lane's last top trace
     for (int t = 0; t < nx + 31; ++t) {
       if (b > 0 && t < nx && (t % kQ1Pub) == 0) {
         int w_ok = 1;
@@ -300,32 +333,34 @@ __device__ bool q1_sweep(const Inst &I, int j, const Q1Smem &S, const double *po
         if (!w_ok) { ok = false; break; }
       }
       const int u = t - lane;
-      double uy0 = __shfl_up_sync(kQ1Full, ty0, 1), uy1 = __shfl_up_sync(kQ1Full, ty1, 1);
+      real uy0 = __shfl_up_sync(kQ1Full, ty0, 1), uy1 = __shfl_up_sync(kQ1Full, ty1, 1);
       if (lane == 0) {
-        if (b == 0) { uy0 = iny; uy1 = 0.0; }
+        if (b == 0) { uy0 = iny; uy1 = real(0); }
         else if (u < nx) { uy0 = ein[u]; uy1 = ein[S.nx_max + u]; }
       }
       if (row_ok && u >= 0 && u < nx) {
         const int ix = flx ? nx - 1 - u : u;
         const int c = iy * nx + ix;
-        const double st = sig_t[c], sv = ss4[c];
-        double A[16], rhs[4];
+        const real st = sig_t[c], sv = ss4[c];
+        real A[16], x[4];
 #pragma unroll
         for (int e = 0; e < 16; ++e) A[e] = A0[e];
-        const double ab = a * bh;
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
           const size_t e = (size_t)4 * c + m;
-          const double src = (sv * pold[e] + s0[e]) * q1_unscale(m);
-          A[m + 4 * m] += st * ab * q1_mass(m);
-          rhs[m] = ab * q1_mass(m) * src;
+          const real src = fmadd(sv, pold[e], s0[e]) * real(q1_unscale(m));
+          A[m + 4 * m] = fmadd(st, dm[m], A[m + 4 * m]);
+          real rr = dm[m] * src;
+          rr = fmadd(Fx[m], ux0, rr);
+          rr = fmadd(Gx[m], ux1, rr);
+          rr = fmadd(Fy[m], uy0, rr);
+          x[m] = fmadd(Gy[m], uy1, rr);
         }
-        q1_inflow(ox, oy, a, bh, ux0, ux1, uy0, uy1, rhs);
-        q1_solve4(A, rhs);
+        q1_solve4(A, x);
 #pragma unroll
-        for (int m = 0; m < 4; ++m) psi[(size_t)4 * c + m] = rhs[m] * q1_scale(m);
-        q1_trace(fox, rhs, ux0, ux1);
-        q1_trace(foy, rhs, ty0, ty1);
+        for (int m = 0; m < 4; ++m) psi[(size_t)4 * c + m] = x[m] * real(q1_scale(m));
+        q1_trace(fox, x, ux0, ux1);
+        q1_trace(foy, x, ty0, ty1);
         if (lane == 31) {
           eout[u] = ty0;
           eout[S.nx_max + u] = ty1;
@@ -349,17 +384,19 @@ __device__ bool q1_sweep(const Inst &I, int j, const Q1Smem &S, const double *po
 // from a counter), phase B forms phi = sum_j gamma_j psi_j per coefficient
 // and the convergence maxima on the unscaled coefficients, phase C takes the
 // same decision in every CTA (as k_si).
+template <typename real>
 __global__ void __launch_bounds__(kQ1NW * 32) k_q1_si(const Inst *__restrict__ insts, SiCtl ctl) {
   extern __shared__ __align__(16) unsigned char q1sm[];
-  Q1Smem S;
+  Q1Smem<real> S;
   S.nx_max = ctl.nx_max;
-  S.edge = reinterpret_cast<double *>(q1sm);
-  size_t off = (size_t)(kQ1NW + 1) * 2 * ctl.nx_max * sizeof(double);
+  S.edge = reinterpret_cast<real *>(q1sm);
+  size_t off = (size_t)(kQ1NW + 1) * 2 * ctl.nx_max * sizeof(real);
   S.prog = reinterpret_cast<int *>(q1sm + off);
   off += (size_t)(ctl.bands_max + 3) / 4 * 4 * sizeof(int);
   int *active = reinterpret_cast<int *>(q1sm + off);
   off += (size_t)(ctl.n_inst + 3) / 4 * 4 * sizeof(int);
-  double *gam = reinterpret_cast<double *>(q1sm + off);
+  off = (off + 15) & ~size_t(15);
+  real *gam = reinterpret_cast<real *>(q1sm + off);
   __shared__ int unit_s, n_active_s;
   volatile int *abort_flag = ctl.abort_flag;
   for (int i = threadIdx.x; i < ctl.n_inst; i += blockDim.x) active[i] = (*insts[i].status == kOk) ? 1 : 0;
@@ -382,8 +419,8 @@ __global__ void __launch_bounds__(kQ1NW * 32) k_q1_si(const Inst *__restrict__ i
       const SiUnit U = ctl.units[u];
       if (!active[U.inst]) continue;
       const Inst &I = insts[U.inst];
-      const double *pold = as_c<double>((it & 1) ? I.phi1 : I.phi0);
-      if (!q1_sweep(I, U.angle, S, pold, abort_flag)) break;
+      const real *pold = as_c<real>((it & 1) ? I.phi1 : I.phi0);
+      if (!q1_sweep<real>(I, U.angle, S, pold, abort_flag)) break;
     }
     if (!grid_barrier(ctl.bar, abort_flag)) break;
     // ---- phase B ----
@@ -399,27 +436,27 @@ __global__ void __launch_bounds__(kQ1NW * 32) k_q1_si(const Inst *__restrict__ i
       const Inst &I = insts[i];
       const int r = I.r;
       const size_t M = (size_t)4 * I.N;
-      const double *psi = as_c<double>(I.Psi);
-      const double *pold = as_c<double>((it & 1) ? I.phi1 : I.phi0);
-      double *pnew = as<double>((it & 1) ? I.phi0 : I.phi1);
+      const real *psi = as_c<real>(I.Psi);
+      const real *pold = as_c<real>((it & 1) ? I.phi1 : I.phi0);
+      real *pnew = as<real>((it & 1) ? I.phi0 : I.phi1);
       __syncthreads();
       for (int q = threadIdx.x; q < r; q += blockDim.x)
-        gam[q] = I.gamma_ext ? I.gamma_ext[q] : I.small[I.lay.gamma + q];
+        gam[q] = real(I.gamma_ext ? I.gamma_ext[q] : I.small[I.lay.gamma + q]);
       __syncthreads();
-      double dmax = 0.0, pmax = 0.0;
+      real dmax = real(0), pmax = real(0);
       for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < M; e += (size_t)gridDim.x * blockDim.x) {
-        double acc = 0.0;
-        for (int q = 0; q < r; ++q) acc += gam[q] * psi[e + M * q];
-        const double us = q1_unscale((int)(e & 3));
-        dmax = fmax(dmax, fabs(acc - pold[e]) * us);
-        pmax = fmax(pmax, fabs(acc) * us);
+        real acc = real(0);
+        for (int q = 0; q < r; ++q) acc = fmadd(gam[q], psi[e + M * q], acc);
+        const real us = real(q1_unscale((int)(e & 3)));
+        dmax = max(dmax, abs(acc - pold[e]) * us);
+        pmax = max(pmax, abs(acc) * us);
         pnew[e] = acc;
       }
       dmax = warp_max(dmax);
       pmax = warp_max(pmax);
       if ((threadIdx.x & 31) == 0) {
-        atomic_max_nonneg(I.conv + (it & 1) * 2 + 0, dmax);
-        atomic_max_nonneg(I.conv + (it & 1) * 2 + 1, pmax);
+        atomic_max_nonneg(I.conv + (it & 1) * 2 + 0, (double)dmax);
+        atomic_max_nonneg(I.conv + (it & 1) * 2 + 1, (double)pmax);
       }
     }
     if (!grid_barrier(ctl.bar, abort_flag)) break;
@@ -472,6 +509,7 @@ __global__ void __launch_bounds__(kQ1NW * 32) k_q1_si(const Inst *__restrict__ i
 // times the cell's coefficients minus the inflow terms of the upwind
 // neighbour's trace.  Stored divided by s, so that the cross Gram
 // sum_e Xs_i(e) Vs_j(e) of the stored rows is X_i^T T X_j.
+template <typename real>
 __global__ void __launch_bounds__(128) k_q1_transport(const Inst *__restrict__ insts, int dir) {
   pdl_wait();
   pdl_trigger();
@@ -480,8 +518,19 @@ __global__ void __launch_bounds__(128) k_q1_transport(const Inst *__restrict__ i
   if (!I.q1 || c >= I.N || *I.status != kOk) return;
   const double ox = dir == 0 ? 1.0 : (dir == 1 ? -1.0 : 0.0), oy = dir == 2 ? 1.0 : (dir == 3 ? -1.0 : 0.0);
   const double a = 0.5 * I.hx, b = 0.5 * I.hy;
-  double A0[16];
-  q1_cell_matrix(ox, oy, a, b, A0);
+  real A0[16], F[4], G[4];
+  {
+    double Ad[16], fx[4], gx[4], fy[4], gy[4];
+    q1_cell_matrix(ox, oy, a, b, Ad);
+    q1_inflow_coef(ox, oy, a, b, fx, gx, fy, gy);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) A0[e] = real(Ad[e]);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      F[m] = real(dir < 2 ? fx[m] : fy[m]);
+      G[m] = real(dir < 2 ? gx[m] : gy[m]);
+    }
+  }
   const int nx = I.nx, ny = I.ny, ix = c % nx, iy = c / nx;
   int nb = -1, face = kFR;
   if (dir == 0 && ix > 0) { nb = c - 1; face = kFR; }
@@ -489,38 +538,39 @@ __global__ void __launch_bounds__(128) k_q1_transport(const Inst *__restrict__ i
   if (dir == 2 && iy > 0) { nb = c - nx; face = kFT; }
   if (dir == 3 && iy < ny - 1) { nb = c + nx; face = kFB; }
   const size_t M = (size_t)4 * I.N;
-  const double *X = as_c<double>(I.X);
+  const real *X = as_c<real>(I.X);
+  real *V = as<real>(I.q1_v);
   for (int j = 0; j < I.r; ++j) {
-    const double *Xj = X + M * j;
-    double u[4], out[4];
+    const real *Xj = X + M * j;
+    real u[4], out[4];
 #pragma unroll
-    for (int m = 0; m < 4; ++m) u[m] = Xj[(size_t)4 * c + m] * q1_unscale(m);
+    for (int m = 0; m < 4; ++m) u[m] = Xj[(size_t)4 * c + m] * real(q1_unscale(m));
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      double t = 0.0;
+      real t = real(0);
 #pragma unroll
-      for (int m = 0; m < 4; ++m) t += A0[i + 4 * m] * u[m];
+      for (int m = 0; m < 4; ++m) t = fmadd(A0[i + 4 * m], u[m], t);
       out[i] = t;
     }
     if (nb >= 0) {
-      double un[4], t0, t1, inr[4] = {0.0, 0.0, 0.0, 0.0};
+      real un[4], t0, t1;
 #pragma unroll
-      for (int m = 0; m < 4; ++m) un[m] = Xj[(size_t)4 * nb + m] * q1_unscale(m);
+      for (int m = 0; m < 4; ++m) un[m] = Xj[(size_t)4 * nb + m] * real(q1_unscale(m));
       q1_trace(face, un, t0, t1);
-      if (dir < 2) q1_inflow(ox, oy, a, b, t0, t1, 0.0, 0.0, inr);
-      else q1_inflow(ox, oy, a, b, 0.0, 0.0, t0, t1, inr);
 #pragma unroll
-      for (int i = 0; i < 4; ++i) out[i] -= inr[i];
+      for (int i = 0; i < 4; ++i) out[i] -= F[i] * t0 + G[i] * t1;
     }
 #pragma unroll
-    for (int m = 0; m < 4; ++m) I.q1_v[(size_t)4 * c + m + M * j] = out[m] * q1_unscale(m);
+    for (int m = 0; m < 4; ++m) V[(size_t)4 * c + m + M * j] = out[m] * real(q1_unscale(m));
   }
 }
 
 // One CTA per instance: q^_j = hx hy sum_c q_c X_j(c, 0); the inflow vectors
 // of a unit isotropic inflow on each edge, (face length) x the trace's
 // constant summed along the edge (left: X0 - X1, right: X0 + X1, bottom:
-// X0 - X2, top: X0 + X2, unscaled); then P S0 (P reduced before).
+// X0 - X2, top: X0 + X2, unscaled); then P S0 (P reduced before).  Sums in
+// FP64, in a fixed order.
+template <typename real>
 __global__ void __launch_bounds__(256) k_q1_vec(const Inst *__restrict__ insts) {
   pdl_wait();
   pdl_trigger();
@@ -529,7 +579,7 @@ __global__ void __launch_bounds__(256) k_q1_vec(const Inst *__restrict__ insts) 
   __shared__ double red[256];
   const int r = I.r, nx = I.nx, ny = I.ny, t = threadIdx.x;
   const size_t M = (size_t)4 * I.N;
-  const double *X = as_c<double>(I.X), *q = as_c<double>(I.q);
+  const real *X = as_c<real>(I.X), *q = as_c<real>(I.q);
   double *vec = I.small + I.lay.vec;
   auto block_sum = [&](double v) {
     red[t] = v;
@@ -543,23 +593,23 @@ __global__ void __launch_bounds__(256) k_q1_vec(const Inst *__restrict__ insts) 
     return x;
   };
   for (int j = 0; j < r; ++j) {
-    const double *Xj = X + M * j;
+    const real *Xj = X + M * j;
     double s = 0.0;
-    for (int c = t; c < I.N; c += blockDim.x) s += q[c] * Xj[(size_t)4 * c];
+    for (int c = t; c < I.N; c += blockDim.x) s += (double)q[c] * (double)Xj[(size_t)4 * c];
     s = block_sum(s);
     double l = 0.0, rr = 0.0;
     for (int iy = t; iy < ny; iy += blockDim.x) {
       const size_t cl = (size_t)4 * (iy * nx), cr = (size_t)4 * (iy * nx + nx - 1);
-      l += Xj[cl] - kQ1Sqrt3 * Xj[cl + 1];
-      rr += Xj[cr] + kQ1Sqrt3 * Xj[cr + 1];
+      l += (double)Xj[cl] - kQ1Sqrt3 * (double)Xj[cl + 1];
+      rr += (double)Xj[cr] + kQ1Sqrt3 * (double)Xj[cr + 1];
     }
     l = block_sum(l);
     rr = block_sum(rr);
     double bo = 0.0, to = 0.0;
     for (int ix = t; ix < nx; ix += blockDim.x) {
       const size_t cb = (size_t)4 * ix, ct = (size_t)4 * ((ny - 1) * nx + ix);
-      bo += Xj[cb] - kQ1Sqrt3 * Xj[cb + 2];
-      to += Xj[ct] + kQ1Sqrt3 * Xj[ct + 2];
+      bo += (double)Xj[cb] - kQ1Sqrt3 * (double)Xj[cb + 2];
+      to += (double)Xj[ct] + kQ1Sqrt3 * (double)Xj[ct + 2];
     }
     bo = block_sum(bo);
     to = block_sum(to);
@@ -585,39 +635,40 @@ __global__ void __launch_bounds__(256) k_q1_vec(const Inst *__restrict__ insts) 
 // ------------------------------------------------------------------
 // One thread per coefficient row: X0 <- X U, and in the rows m = 0 the
 // temperature update with the cell average phi = X(4c, :) (L w).
+template <typename real>
 __global__ void __launch_bounds__(128) k_q1_tupdate(const Inst *__restrict__ insts) {
   pdl_wait();
   pdl_trigger();
   const Inst &I = insts[blockIdx.y];
   if (!I.q1) return;
-  __shared__ double U[kMaxRank * kMaxRank], vp[kMaxRank];
+  __shared__ real U[kMaxRank * kMaxRank], vp[kMaxRank];
   const int r = I.r;
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) U[e] = I.small[I.lay.U + e];
-  for (int e = threadIdx.x; e < r; e += blockDim.x) vp[e] = I.small[I.lay.vphi + e];
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) U[e] = real(I.small[I.lay.U + e]);
+  for (int e = threadIdx.x; e < r; e += blockDim.x) vp[e] = real(I.small[I.lay.vphi + e]);
   __syncthreads();
   const size_t M = (size_t)4 * I.N;
   const size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (e >= M || *I.status != kOk) return;
-  const double *X = as_c<double>(I.X);
-  double *X0 = as<double>(I.X0);
-  double x[kMaxRank];
-  double phi = 0.0;
+  const real *X = as_c<real>(I.X);
+  real *X0 = as<real>(I.X0);
+  real x[kMaxRank];
+  real phi = real(0);
 #pragma unroll
   for (int i = 0; i < kMaxRank; ++i) {
-    x[i] = i < r ? X[e + M * i] : 0.0;
-    phi += x[i] * (i < r ? vp[i] : 0.0);
+    x[i] = i < r ? X[e + M * i] : real(0);
+    if (i < r) phi = fmadd(x[i], vp[i], phi);
   }
   for (int j = 0; j < r; ++j) {
-    double v = 0.0;
+    real v = real(0);
 #pragma unroll
     for (int i = 0; i < kMaxRank; ++i)
-      if (i < r) v += x[i] * U[i + r * j];
+      if (i < r) v = fmadd(x[i], U[i + r * j], v);
     X0[e + M * j] = v;
   }
   if ((e & 3) != 0) return;
   const int c = (int)(e >> 2);
   const double T0 = I.T[c];
-  const double T = T0 + I.dt * sigma_at(I, c, T0) * (phi - 4.0 * kPi * I.B0[c]) / I.D[c];
+  const double T = T0 + I.dt * sigma_at(I, c, T0) * ((double)phi - 4.0 * kPi * I.B0[c]) / I.D[c];
   I.T[c] = T;
   if (!(T > 0.0)) {
     atomicAdd(I.nonpos, 1);
@@ -627,6 +678,7 @@ __global__ void __launch_bounds__(128) k_q1_tupdate(const Inst *__restrict__ ins
 
 // Full-rank SN on Q1: T from the cell average of the last source
 // iteration's phi.
+template <typename real>
 __global__ void __launch_bounds__(256) k_q1_sn_tupdate(const Inst *__restrict__ insts) {
   pdl_wait();
   pdl_trigger();
@@ -634,9 +686,9 @@ __global__ void __launch_bounds__(256) k_q1_sn_tupdate(const Inst *__restrict__ 
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (!I.q1 || c >= I.N || *I.status != kOk) return;
   const int last = *I.iters - 1;  // iteration it writes phi1 (it even) or phi0 (odd)
-  const double *phi = as_c<double>((last & 1) ? I.phi0 : I.phi1);
+  const real *phi = as_c<real>((last & 1) ? I.phi0 : I.phi1);
   const double T0 = I.T[c];
-  const double T = T0 + I.dt * sigma_at(I, c, T0) * (phi[(size_t)4 * c] - 4.0 * kPi * I.B0[c]) / I.D[c];
+  const double T = T0 + I.dt * sigma_at(I, c, T0) * ((double)phi[(size_t)4 * c] - 4.0 * kPi * I.B0[c]) / I.D[c];
   I.T[c] = T;
   if (!(T > 0.0)) {
     atomicAdd(I.nonpos, 1);
@@ -644,45 +696,52 @@ __global__ void __launch_bounds__(256) k_q1_sn_tupdate(const Inst *__restrict__ 
   }
 }
 
-// Rows of a 4 N x cols Q1 matrix between stored (scaled) and plain Legendre
-// coefficients: to_plain = 1 divides by s, 0 multiplies.
-__global__ void k_q1_rescale(double *A, size_t rows, int cols, int to_plain) {
+// Rows of a 4 N x cols Q1 matrix between stored (scaled) and plain
+// Legendre coefficients: to_plain = 1 divides by s, 0 multiplies.
+template <typename T>
+__global__ void k_q1_rescale(T *A, size_t rows, int cols, int to_plain) {
   const size_t total = rows * (size_t)cols;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int m = (int)((e % rows) & 3);
-    A[e] *= to_plain ? q1_unscale(m) : q1_scale(m);
+    A[e] = T(A[e] * (to_plain ? q1_unscale(m) : q1_scale(m)));
   }
 }
 
 // ------------------------------------------------------------------
 // host launchers
 // ------------------------------------------------------------------
+template <typename real>
 cudaError_t launch_q1_coeff(const Inst *d, int n, int maxN, bool sn, cudaStream_t st) {
   const dim3 g((maxN + 127) / 128, n);
-  return sn ? launch_pdl(k_q1_sn_prep, g, dim3(128), 0, st, d) : launch_pdl(k_q1_coeff, g, dim3(128), 0, st, d);
+  return sn ? launch_pdl(k_q1_sn_prep<real>, g, dim3(128), 0, st, d)
+            : launch_pdl(k_q1_coeff<real>, g, dim3(128), 0, st, d);
 }
 
+template <typename real>
 size_t q1_si_smem(int nx_max, int bands_max, int n_inst, int gam_max) {
-  return q1_si_smem_bytes(nx_max, bands_max, n_inst, gam_max);
+  return q1_si_smem_bytes<real>(nx_max, bands_max, n_inst, gam_max);
 }
 
 // CTAs of the cooperative Q1 source iteration that fit at once (0: none).
+template <typename real>
 int q1_si_max_grid(int nx_max, int bands_max, int n_inst, int gam_max) {
-  const size_t smem = q1_si_smem_bytes(nx_max, bands_max, n_inst, gam_max);
-  if (cudaFuncSetAttribute(k_q1_si, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+  const size_t smem = q1_si_smem_bytes<real>(nx_max, bands_max, n_inst, gam_max);
+  if (cudaFuncSetAttribute(k_q1_si<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   int per_sm = 0, dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_q1_si, kQ1NW * 32, smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_q1_si<real>, kQ1NW * 32, smem) != cudaSuccess)
+    return 0;
   return per_sm * sms;
 }
 
+template <typename real>
 cudaError_t launch_q1_si(const Inst *d, const SiCtl &ctl, int grid, cudaStream_t st) {
-  const size_t smem = q1_si_smem_bytes(ctl.nx_max, ctl.bands_max, ctl.n_inst, ctl.gam_max);
-  cudaError_t e = cudaFuncSetAttribute(k_q1_si, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = q1_si_smem_bytes<real>(ctl.nx_max, ctl.bands_max, ctl.n_inst, ctl.gam_max);
+  cudaError_t e = cudaFuncSetAttribute(k_q1_si<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
@@ -694,24 +753,40 @@ cudaError_t launch_q1_si(const Inst *d, const SiCtl &ctl, int grid, cudaStream_t
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_q1_si, d, ctl);
+  return cudaLaunchKernelEx(&cfg, k_q1_si<real>, d, ctl);
 }
 
+template <typename real>
 cudaError_t launch_q1_transport(const Inst *d, int n, int maxN, int dir, cudaStream_t st) {
-  return launch_pdl(k_q1_transport, dim3((maxN + 127) / 128, n), dim3(128), 0, st, d, dir);
+  return launch_pdl(k_q1_transport<real>, dim3((maxN + 127) / 128, n), dim3(128), 0, st, d, dir);
 }
+template <typename real>
 cudaError_t launch_q1_vec(const Inst *d, int n, cudaStream_t st) {
-  return launch_pdl(k_q1_vec, dim3(n), dim3(256), 0, st, d);
+  return launch_pdl(k_q1_vec<real>, dim3(n), dim3(256), 0, st, d);
 }
+template <typename real>
 cudaError_t launch_q1_tupdate(const Inst *d, int n, int maxN, bool sn, cudaStream_t st) {
-  if (sn) return launch_pdl(k_q1_sn_tupdate, dim3((maxN + 255) / 256, n), dim3(256), 0, st, d);
-  return launch_pdl(k_q1_tupdate, dim3((4 * maxN + 127) / 128, n), dim3(128), 0, st, d);
+  if (sn) return launch_pdl(k_q1_sn_tupdate<real>, dim3((maxN + 255) / 256, n), dim3(256), 0, st, d);
+  return launch_pdl(k_q1_tupdate<real>, dim3((4 * maxN + 127) / 128, n), dim3(128), 0, st, d);
 }
-cudaError_t launch_q1_rescale(double *A, size_t rows, int cols, int to_plain, cudaStream_t st) {
+cudaError_t launch_q1_rescale(void *A, bool is_float, size_t rows, int cols, int to_plain, cudaStream_t st) {
   const size_t total = rows * (size_t)cols;
   const int blocks = (int)std::min<size_t>((total + 255) / 256, 4096);
-  k_q1_rescale<<<blocks, 256, 0, st>>>(A, rows, cols, to_plain);
+  if (is_float) k_q1_rescale<float><<<blocks, 256, 0, st>>>(static_cast<float *>(A), rows, cols, to_plain);
+  else k_q1_rescale<double><<<blocks, 256, 0, st>>>(static_cast<double *>(A), rows, cols, to_plain);
   return cudaGetLastError();
 }
+
+#define Q1_INSTANTIATE(real)                                                                   \
+  template cudaError_t launch_q1_coeff<real>(const Inst *, int, int, bool, cudaStream_t);      \
+  template size_t q1_si_smem<real>(int, int, int, int);                                        \
+  template int q1_si_max_grid<real>(int, int, int, int);                                       \
+  template cudaError_t launch_q1_si<real>(const Inst *, const SiCtl &, int, cudaStream_t);     \
+  template cudaError_t launch_q1_transport<real>(const Inst *, int, int, int, cudaStream_t);   \
+  template cudaError_t launch_q1_vec<real>(const Inst *, int, cudaStream_t);                   \
+  template cudaError_t launch_q1_tupdate<real>(const Inst *, int, int, bool, cudaStream_t);
+Q1_INSTANTIATE(float)
+Q1_INSTANTIATE(double)
+#undef Q1_INSTANTIATE
 
 }  // namespace dlr

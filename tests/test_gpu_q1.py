@@ -3,9 +3,10 @@ elements; the upwind DG system per cell in the Legendre basis 1, xi, eta,
 xi eta): the SN-like DLR step against oracle_dlr_step_q1 and the full-rank SN
 step against oracle_sn_step_q1, through the C ABI, on ragged meshes and on
 the full lattice32 mesh; relative L2 on T and on psi (4 Nx coefficients x
-NOm) within 1e-10 (FP64, the only precision built for Q1).  Also: at full
-rank (r = 4 Nx) the GPU DLR step equals the GPU SN step, a uniform medium
-follows the 0-D recurrence, and the unsupported combinations are refused."""
+NOm) within 1e-10 (FP64) and 2e-5 (mixed: FP32 sweeps and projections).
+Also: at full rank (r = 4 Nx) the GPU DLR step equals the GPU SN step, a
+uniform medium follows the 0-D recurrence, batches equal single runs, and
+the unsupported combinations are refused."""
 import numpy as np
 import pytest
 
@@ -15,7 +16,7 @@ from gpu_util import rel_l2
 
 pytestmark = pytest.mark.gpu
 
-TOL = 1e-10
+TOL = {0: 1e-10, 1: 2e-5}
 
 
 @pytest.fixture(scope="module")
@@ -42,11 +43,11 @@ def _hot(nx, ny, r, npol, naz, edges=(0.6, -1.0, 0.3, -1.0)):
     return case
 
 
-def _dlr_pair(orc, dlr, case, steps):
+def _dlr_pair(orc, dlr, case, steps, prec=0):
     p = oracle_problem(case)
     T = case["T0"].reshape(-1).copy()
     X, S, W = _q1_start(orc, p, T, case["r"])
-    spec = dlr.problem_from_case(case, precision=0, element=1, si_tol=1e-13)
+    spec = dlr.problem_from_case(case, precision=prec, element=1, si_tol=1e-13 if prec == 0 else 0.0)
     out = []
     with dlr.Solver(spec) as s:
         s.set_factors(X, S, W)
@@ -60,28 +61,32 @@ def _dlr_pair(orc, dlr, case, steps):
     return out
 
 
+@pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("shape,r", [((12, 10, 2, 8), 4), ((37, 29, 2, 8), 6), ((5, 64, 4, 8), 8),
                                      ((70, 33, 2, 6), 5), ((1, 40, 2, 8), 3)])
-def test_dlr_q1_matches_oracle(orc, dlr, shape, r):
+def test_dlr_q1_matches_oracle(orc, dlr, shape, r, prec):
     nx, ny, npol, naz = shape
-    out = _dlr_pair(orc, dlr, _hot(nx, ny, r, npol, naz), 3)
+    out = _dlr_pair(orc, dlr, _hot(nx, ny, r, npol, naz), 3, prec)
     for eT, ep, it, git in out:
-        assert eT < TOL and ep < TOL, out
-        assert abs(it - git) <= 1, out
+        assert eT < TOL[prec] and ep < TOL[prec], out
+        if prec == 0:
+            assert abs(it - git) <= 1, out
 
 
-def test_dlr_q1_rank32_many_angles(orc, dlr):
+@pytest.mark.parametrize("prec", [0, 1])
+def test_dlr_q1_rank32_many_angles(orc, dlr, prec):
     # rank class 32 and more than 1024 angles (the unfused step 8)
-    out = _dlr_pair(orc, dlr, _hot(24, 20, 32, 16, 72), 2)
+    out = _dlr_pair(orc, dlr, _hot(24, 20, 32, 16, 72), 2, prec)
     for eT, ep, *_ in out:
-        assert eT < TOL and ep < TOL, out
+        assert eT < TOL[prec] and ep < TOL[prec], out
 
 
-def test_dlr_q1_lattice32_full_size(orc, dlr):
+@pytest.mark.parametrize("prec", [0, 1])
+def test_dlr_q1_lattice32_full_size(orc, dlr, prec):
     case = workloads.lattice32()
-    out = _dlr_pair(orc, dlr, case, 2)
+    out = _dlr_pair(orc, dlr, case, 2, prec)
     for eT, ep, *_ in out:
-        assert eT < TOL and ep < TOL, out
+        assert eT < TOL[prec] and ep < TOL[prec], out
 
 
 def _q1_planck(case, K):
@@ -92,24 +97,27 @@ def _q1_planck(case, K):
     return psi
 
 
+@pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("shape", [(12, 10, 2, 8), (37, 29, 2, 4), (5, 64, 2, 8)])
-def test_sn_q1_matches_oracle(orc, dlr, shape):
+def test_sn_q1_matches_oracle(orc, dlr, shape, prec):
     nx, ny, npol, naz = shape
     case = _hot(nx, ny, 1, npol, naz)
     p = oracle_problem(case)
     K = npol * naz
     T = case["T0"].reshape(-1).copy()
     psi = _q1_planck(case, K)
-    spec = dlr.problem_from_case(case, precision=0, element=1, method=dlr.DLR_METHOD_SN, si_tol=1e-13)
+    spec = dlr.problem_from_case(case, precision=prec, element=1, method=dlr.DLR_METHOD_SN,
+                                 si_tol=1e-13 if prec == 0 else 0.0)
     with dlr.Solver(spec) as s:
-        np.testing.assert_allclose(s.psi(), psi.reshape(K, -1).T, rtol=1e-14)
+        np.testing.assert_allclose(s.psi(), psi.reshape(K, -1).T, rtol=1e-14 if prec == 0 else 1e-7)
         for _ in range(3):
             psi, T, phi, it, *_ = orc.sn_step_q1(p, psi, T, si_tol=1e-13, si_max_iter=20000)
             assert it > 0
             s.step(1)
-            assert rel_l2(s.T(), T) < TOL
-            assert rel_l2(s.psi(), psi.reshape(K, -1).T) < TOL
-            assert abs(s.stats()["si_iters_last"] - it) <= 1
+            assert rel_l2(s.T(), T) < TOL[prec]
+            assert rel_l2(s.psi(), psi.reshape(K, -1).T) < TOL[prec]
+            if prec == 0:
+                assert abs(s.stats()["si_iters_last"] - it) <= 1
 
 
 def test_dlr_q1_full_rank_equals_sn_q1(dlr):
@@ -156,16 +164,17 @@ def test_q1_uniform_medium_recurrence(dlr, method):
             np.testing.assert_allclose(s.T(), Tz, rtol=1e-12)
 
 
-def test_q1_batch_equals_alone(dlr):
+@pytest.mark.parametrize("prec", [0, 1])
+def test_q1_batch_equals_alone(dlr, prec):
     import torch
     cases = [_hot(33, 20, 6, 2, 8), _hot(19, 23, 4, 4, 8)]
     alone = []
     for c in cases:
-        with dlr.Solver(dlr.problem_from_case(c, precision=0, element=1)) as s:
+        with dlr.Solver(dlr.problem_from_case(c, precision=prec, element=1)) as s:
             s.step(2)
             alone.append((s.T(), s.psi()))
     st = torch.cuda.Stream()
-    ss = [dlr.Solver(dlr.problem_from_case(c, precision=0, element=1), stream=st) for c in cases]
+    ss = [dlr.Solver(dlr.problem_from_case(c, precision=prec, element=1), stream=st) for c in cases]
     try:
         dlr.step_batch(ss, 2)
         got = [(s.T(), s.psi()) for s in ss]
@@ -174,12 +183,12 @@ def test_q1_batch_equals_alone(dlr):
             s.close()
     for (Ta, pa), (Tg, pg) in zip(alone, got):
         assert np.array_equal(Ta, Tg)
-        assert rel_l2(pg, pa) < 1e-12
+        assert rel_l2(pg, pa) < (1e-12 if prec == 0 else 1e-6)
 
 
 def test_q1_refusals(dlr):
     case = workloads.small_case(8, 8, 2, 2, 6)
-    for kw in (dict(precision=1), dict(precision=0, dsa=1), dict(precision=0, augment=1),
+    for kw in (dict(precision=0, dsa=1), dict(precision=0, augment=1),
                dict(precision=0, reflect=(1, 0, 0, 0)), dict(precision=0, selection=1),
                dict(precision=0, element=2)):
         kw.setdefault("element", 1)
