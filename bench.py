@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-sn", action="store_true", help="skip the full-rank SN comparator")
     ap.add_argument("--no-aug", action="store_true", help="skip the augmented (rank-2r) step")
     ap.add_argument("--no-dsa", action="store_true", help="skip the DSA-accelerated step")
+    ap.add_argument("--no-q1", action="store_true", help="skip the step on bilinear (Q1) elements")
     ap.add_argument("--dsa", action="store_true", help="served: every request with DSA")
     ap.add_argument("--dsa-max-iter", type=int, default=0, help="CG cap per DSA solve (0: the library's)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
@@ -545,6 +546,38 @@ def run_gpu(args):
                "T_rel_l2_vs_plain": float(np.linalg.norm(T_dsa - T_mixed) / np.linalg.norm(T_mixed)),
                "cell_angle_updates_per_s": ud / (td / 1e3)}
 
+    # ---- the same steps on bilinear (Q1) elements (Section 4.4), mixed ----
+    q1 = None
+    if not args.no_q1 and rank == 0:
+        s8 = dlr.Solver(dlr.problem_from_case(case, precision=dlr.DLR_MIXED, allow_nonpositive=1, element=1))
+        s8.step(args.warmup)
+        s8.stream.synchronize()
+        s8.set_timing(True)
+        q0 = s8.stats()
+        ms_q1 = timed_steps(dlr, torch, s8, args.steps, flush)
+        q1s = s8.stats()
+        T_q1 = s8.T()
+        s8.close()
+        uq = q1s["cell_angle_updates"] - q0["cell_angle_updates"]
+        tq = sum(ms_q1)
+        nlq = max(q1s["si_launches"] - q0["si_launches"], 1)
+        lq_ms = (q1s["ms_si_total"] - q0["ms_si_total"]) / nlq
+        # per cell-angle update (FP32): the 4 fixed-source coefficients read,
+        # the 4 psi coefficients written by the sweep and read back by the
+        # scalar-flux phase; per cell sigma_t, sigma_s/4pi, phi read by the
+        # sweep and the scalar-flux phase and written once, amortised over r
+        bpq = 48.0 + 56.0 / case["r"]
+        achq = uq / nlq * bpq / (lq_ms / 1e3) / 1e9
+        hbm_q, kind_q = peaks()
+        q1 = {"method": "SN-like DLR step on bilinear (Q1) elements, 4 coefficients per cell, mixed",
+              "value": uq / (tq / 1e3), "unit": METRIC, "ms_per_step": tq / args.steps,
+              "dlr_steps_per_s": args.steps / (tq / 1e3),
+              "si_iters_per_step": (q1s["si_iters_total"] - q0["si_iters_total"]) / args.steps,
+              "T_rel_l2_vs_dg0": float(np.linalg.norm(T_q1 - T_mixed) / np.linalg.norm(T_mixed)),
+              "roofline": {"bound": "hbm", "achieved": achq, "peak": hbm_q, "unit": "GB/s",
+                           "frac": achq / hbm_q, "kernel": "k_q1_si<float>", "peak_kind": kind_q,
+                           "bytes_per_update": bpq, "avg_launch_ms": lq_ms}}
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -576,7 +609,7 @@ def run_gpu(args):
             "data": "synthetic", "config": case_config(case, "mixed: FP32 sweeps/projections, FP64 small LA and T"),
             "dlr_steps_per_s": world * args.steps / (total_ms / 1e3),
             "si_iters_per_step": iters / args.steps,
-            "roofline": roofline, "cpu_baseline": cpu, "vs_oracle": vs_oracle, "e2e": e2e, "fp64_gpu": fp64, "sn_gpu": sn, "sn_dsa_gpu": sn_dsa, "augmented_gpu": aug, "dsa_gpu": dsa,
+            "roofline": roofline, "cpu_baseline": cpu, "vs_oracle": vs_oracle, "e2e": e2e, "fp64_gpu": fp64, "sn_gpu": sn, "sn_dsa_gpu": sn_dsa, "augmented_gpu": aug, "dsa_gpu": dsa, "q1_gpu": q1,
             "clocks": clocks, "gpu_launches": int(launches),
             "nonpositive_cells_at_end": int(nonpos), "sweep_plan": tuned}
     print(json.dumps(line))

@@ -77,7 +77,7 @@ template <typename real> size_t q1_si_smem(int, int, int, int);
 template <typename real> int q1_si_max_grid(int, int, int, int);
 template <typename real> cudaError_t launch_q1_si(const Inst *, const SiCtl &, int, cudaStream_t);
 template <typename real> cudaError_t launch_q1_transport(const Inst *, int, int, int, cudaStream_t);
-template <typename real> cudaError_t launch_q1_vec(const Inst *, int, cudaStream_t);
+template <typename real> cudaError_t launch_q1_vec(const Inst *, int, int, cudaStream_t);
 template <typename real> cudaError_t launch_q1_tupdate(const Inst *, int, int, bool, cudaStream_t);
 cudaError_t launch_q1_rescale(void *, bool, size_t, int, int, cudaStream_t);
 }  // namespace dlr
@@ -419,12 +419,13 @@ static int reduce_cta_cap() {
   return cap;
 }
 
-// The grouped sweep (k_sweepg.cu) serves mixed-precision DLR steps without
-// DSA, reflective edges or the augmented step, unless sweep_mode asks for
-// the per-angle kernel.
+// The grouped sweep (k_sweepg.cu) serves mixed-precision DLR steps on DG0
+// cells without DSA, reflective edges or the augmented step, unless
+// sweep_mode asks for the per-angle kernel.
 static bool grp_eligible(const dlr_problem *p) {
   return p->precision == DLR_MIXED && p->method == DLR_METHOD_DLR && !p->dsa && !p->augment &&
-         !(p->reflect[0] || p->reflect[1] || p->reflect[2] || p->reflect[3]) && p->sweep_mode != 1;
+         !(p->reflect[0] || p->reflect[1] || p->reflect[2] || p->reflect[3]) && p->sweep_mode != 1 &&
+         p->element == 0;
 }
 
 static Sizes sizes_of(const dlr_problem *p, int sms) {
@@ -467,7 +468,8 @@ static Sizes sizes_of(const dlr_problem *p, int sms) {
   s.partial_doubles = std::max({(size_t)(s.pb / kCl) * proj_count((int)r), (size_t)(s.pb / kCl) * r * r,
                                 (size_t)(s.pbl / kCl) * r * r, (size_t)(s.lb / kCl) * (r * r + r),
                                 (size_t)(s.pbg / kCl) * r * r,
-                                p->element == 1 ? (size_t)7 * (s.pb / kCl) * r * r : (size_t)0});
+                                p->element == 1 ? (size_t)7 * (s.pb / kCl) * r * r : (size_t)0,
+                                p->element == 1 ? (size_t)s.pb * r : (size_t)0});
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
   size_t t = 0;
   t += 5 * al((size_t)s.N * 8);                 // sigma, rho_cv, T, B0, D
@@ -1578,7 +1580,8 @@ static int enqueue_post(Batch *b) {
     }
     LK(launch_tsgram<real>(b->g_q1t + (size_t)4 * n, 3 * n, b->pbmax, 0, st));
     LK(launch_reduce(b->r_q1, 7 * n, b->rmax * b->rmax, st));
-    LK(launch_q1_vec<real>(d, n, st));
+    LK(launch_q1_vec<real>(d, n, b->pbmax, st));
+    ++b->kcount;  // two kernels
   } else {
     LK(launch_project<real>(d, n, b->pbmax, b->rmax, st));
     LK(launch_reduce(b->r_proj, n, proj_count(b->rmax), st));

@@ -39,7 +39,6 @@ namespace dlr {
 
 namespace {
 
-constexpr int kQ1NW = 8;       // sweeping warps per CTA (bands in flight per angle)
 constexpr int kQ1Pub = 8;      // columns per progress publication
 constexpr uint64_t kQ1WaitNs = 4000000000ull;
 constexpr unsigned kQ1Full = 0xffffffffu;
@@ -48,6 +47,13 @@ constexpr unsigned kQ1Full = 0xffffffffu;
 enum Q1Face { kFR = 0, kFL = 1, kFT = 2, kFB = 3 };
 
 }  // namespace
+
+// Sweeping warps per CTA (bands in flight per angle): 16 in FP32; 8 in FP64,
+// whose edge rows would not fit in shared memory at 16.
+template <typename real>
+struct Q1Cfg {
+  static constexpr int NW = sizeof(real) == 4 ? 16 : 8;
+};
 
 // int over the reference cell of the squared basis function m
 __device__ __forceinline__ double q1_mass(int m) { return m == 0 ? 4.0 : (m == 3 ? 4.0 / 9.0 : 4.0 / 3.0); }
@@ -242,17 +248,40 @@ __global__ void __launch_bounds__(128) k_q1_sn_prep(const Inst *__restrict__ ins
 // ------------------------------------------------------------------
 // step 4: collocation sweeps and source iteration
 // ------------------------------------------------------------------
-// Shared memory of k_q1_si: (kQ1NW + 1) edge rows of 2 x nx_max traces, the
+// Shared memory of k_q1_si: (NW + 1) edge rows of 2 x nx_max traces, the
 // band progress counters, the active flags and the scalar-flux weights.
 template <typename real>
 __host__ __device__ inline size_t q1_si_smem_bytes(int nx_max, int bands_max, int n_inst, int gam_max) {
-  return (size_t)(kQ1NW + 1) * 2 * nx_max * sizeof(real) + (size_t)(bands_max + 3) / 4 * 4 * sizeof(int) +
+  return (size_t)(Q1Cfg<real>::NW + 1) * 2 * nx_max * sizeof(real) + (size_t)(bands_max + 3) / 4 * 4 * sizeof(int) +
          (size_t)(n_inst + 3) / 4 * 4 * sizeof(int) + (size_t)gam_max * sizeof(real) + 16;
+}
+
+// The inputs of one cell of a sweep: sigma_t, sigma_s / 4pi, and the 4
+// coefficients of phi and of the fixed source (16-byte vector loads in FP32,
+// two 16-byte loads each in FP64).
+template <typename real>
+struct Q1In {
+  real st, sv, p[4], s[4];
+};
+__device__ __forceinline__ void q1_ld4(const float *a, float *v) {
+  const float4 x = *reinterpret_cast<const float4 *>(a);
+  v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+}
+__device__ __forceinline__ void q1_ld4(const double *a, double *v) {
+  const double2 x = reinterpret_cast<const double2 *>(a)[0], y = reinterpret_cast<const double2 *>(a)[1];
+  v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
+}
+__device__ __forceinline__ void q1_st4(float *a, const float *v) {
+  *reinterpret_cast<float4 *>(a) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void q1_st4(double *a, const double *v) {
+  reinterpret_cast<double2 *>(a)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2 *>(a)[1] = make_double2(v[2], v[3]);
 }
 
 template <typename real>
 struct Q1Smem {
-  real *edge;     // (kQ1NW + 1) x 2 x nx_max
+  real *edge;     // (NW + 1) x 2 x nx_max
   int *prog;      // per band: columns published
   int nx_max;
 };
@@ -275,14 +304,16 @@ __device__ __forceinline__ bool q1_wait_prog(volatile int *prog, int b, int need
 }
 
 // The sweep of chosen angle j of instance I by one CTA: warp w takes the
-// bands w, w + kQ1NW, ... of 32 rows (lane i = row i of the band, mirrored
+// bands w, w + NW, ... of 32 rows (lane i = row i of the band, mirrored
 // so that the direction points to +u, +v); lane i handles column u at step
 // t = u + i.  The left neighbour's face trace stays in the lane's
 // registers, the lower one comes from lane i - 1 by a shuffle, and lane 0
-// takes it from the edge row the band below published.  Returns false (in
-// every thread of the CTA) if a wait gave up.
+// takes it from the edge row the band below published.  Each lane loads
+// its cell inputs two steps ahead.  Returns false (in every thread of the
+// CTA) if a wait gave up.
 template <typename real>
 __device__ bool q1_sweep(const Inst &I, int j, const Q1Smem<real> &S, const real *pold, volatile int *abort_flag) {
+  constexpr int NW = Q1Cfg<real>::NW;
   const int nx = I.nx, ny = I.ny, nb = (ny + 31) / 32;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   __syncthreads();
@@ -310,22 +341,46 @@ __device__ bool q1_sweep(const Inst &I, int j, const Q1Smem<real> &S, const real
       Gy[m] = real(f3[m]);
     }
   }
-  const int fox = ox >= 0 ? kFR : kFL, foy = oy >= 0 ? kFT : kFB;
+  // outflow traces: x-face (u0 + gx u1, u2 + gx u3), y-face
+  // (u0 + gy u2, u1 + gy u3) with g = +1 on the +x / +y face, -1 opposite
+  const real gx = real(ox >= 0 ? 1 : -1), gy = real(oy >= 0 ? 1 : -1);
+  real us[4], sc[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    us[m] = real(q1_unscale(m));
+    sc[m] = real(q1_scale(m));
+  }
   const size_t M = (size_t)4 * I.N;
   const real *sig_t = as_c<real>(I.sig_t), *ss4 = as_c<real>(I.ss4);
   const real *s0 = as_c<real>(I.s0) + M * j;
   real *psi = as<real>(I.Psi) + M * j;
   volatile int *prog = S.prog;
   bool ok = true;
-  for (int b = wid; b < nb && ok; b += kQ1NW) {
+  for (int b = wid; b < nb && ok; b += NW) {
     const int v = b * 32 + lane;
     const bool row_ok = v < ny;
     const int iy = fly ? ny - 1 - v : v;
-    const real *ein = S.edge + (size_t)((b + kQ1NW) % (kQ1NW + 1)) * 2 * S.nx_max;
-    real *eout = S.edge + (size_t)(b % (kQ1NW + 1)) * 2 * S.nx_max;
+    const real *ein = S.edge + (size_t)((b + NW) % (NW + 1)) * 2 * S.nx_max;
+    real *eout = S.edge + (size_t)(b % (NW + 1)) * 2 * S.nx_max;
     real ux0 = inx, ux1 = real(0);  // trace entering through the left face
     real ty0 = real(0), ty1 = real(0);  // this lane's last top trace
+    // the inputs of column u of this lane's row (zero outside the mesh)
+    auto load = [&](int u, Q1In<real> &in) {
+      if (row_ok && u >= 0 && u < nx) {
+        const int c = iy * nx + (flx ? nx - 1 - u : u);
+        in.st = sig_t[c];
+        in.sv = ss4[c];
+        q1_ld4(pold + (size_t)4 * c, in.p);
+        q1_ld4(s0 + (size_t)4 * c, in.s);
+      }
+    };
+    Q1In<real> n1 = {}, n2 = {};
+    load(-lane, n1);
+    load(1 - lane, n2);
     for (int t = 0; t < nx + 31; ++t) {
+      const Q1In<real> cur = n1;
+      n1 = n2;
+      load(t + 2 - lane, n2);
       if (b > 0 && t < nx && (t % kQ1Pub) == 0) {
         int w_ok = 1;
         if (lane == 0) w_ok = q1_wait_prog(prog, b - 1, min(nx, t + kQ1Pub), abort_flag) ? 1 : 0;
@@ -341,15 +396,13 @@ __device__ bool q1_sweep(const Inst &I, int j, const Q1Smem<real> &S, const real
       if (row_ok && u >= 0 && u < nx) {
         const int ix = flx ? nx - 1 - u : u;
         const int c = iy * nx + ix;
-        const real st = sig_t[c], sv = ss4[c];
         real A[16], x[4];
 #pragma unroll
         for (int e = 0; e < 16; ++e) A[e] = A0[e];
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-          const size_t e = (size_t)4 * c + m;
-          const real src = fmadd(sv, pold[e], s0[e]) * real(q1_unscale(m));
-          A[m + 4 * m] = fmadd(st, dm[m], A[m + 4 * m]);
+          const real src = fmadd(cur.sv, cur.p[m], cur.s[m]) * us[m];
+          A[m + 4 * m] = fmadd(cur.st, dm[m], A[m + 4 * m]);
           real rr = dm[m] * src;
           rr = fmadd(Fx[m], ux0, rr);
           rr = fmadd(Gx[m], ux1, rr);
@@ -357,10 +410,14 @@ __device__ bool q1_sweep(const Inst &I, int j, const Q1Smem<real> &S, const real
           x[m] = fmadd(Gy[m], uy1, rr);
         }
         q1_solve4(A, x);
+        real xs[4];
 #pragma unroll
-        for (int m = 0; m < 4; ++m) psi[(size_t)4 * c + m] = x[m] * real(q1_scale(m));
-        q1_trace(fox, x, ux0, ux1);
-        q1_trace(foy, x, ty0, ty1);
+        for (int m = 0; m < 4; ++m) xs[m] = x[m] * sc[m];
+        q1_st4(psi + (size_t)4 * c, xs);
+        ux0 = fmadd(gx, x[1], x[0]);
+        ux1 = fmadd(gx, x[3], x[2]);
+        ty0 = fmadd(gy, x[2], x[0]);
+        ty1 = fmadd(gy, x[3], x[1]);
         if (lane == 31) {
           eout[u] = ty0;
           eout[S.nx_max + u] = ty1;
@@ -385,12 +442,12 @@ __device__ bool q1_sweep(const Inst &I, int j, const Q1Smem<real> &S, const real
 // and the convergence maxima on the unscaled coefficients, phase C takes the
 // same decision in every CTA (as k_si).
 template <typename real>
-__global__ void __launch_bounds__(kQ1NW * 32) k_q1_si(const Inst *__restrict__ insts, SiCtl ctl) {
+__global__ void __launch_bounds__(Q1Cfg<real>::NW * 32) k_q1_si(const Inst *__restrict__ insts, SiCtl ctl) {
   extern __shared__ __align__(16) unsigned char q1sm[];
   Q1Smem<real> S;
   S.nx_max = ctl.nx_max;
   S.edge = reinterpret_cast<real *>(q1sm);
-  size_t off = (size_t)(kQ1NW + 1) * 2 * ctl.nx_max * sizeof(real);
+  size_t off = (size_t)(Q1Cfg<real>::NW + 1) * 2 * ctl.nx_max * sizeof(real);
   S.prog = reinterpret_cast<int *>(q1sm + off);
   off += (size_t)(ctl.bands_max + 3) / 4 * 4 * sizeof(int);
   int *active = reinterpret_cast<int *>(q1sm + off);
@@ -565,11 +622,48 @@ __global__ void __launch_bounds__(128) k_q1_transport(const Inst *__restrict__ i
   }
 }
 
-// One CTA per instance: q^_j = hx hy sum_c q_c X_j(c, 0); the inflow vectors
-// of a unit isotropic inflow on each edge, (face length) x the trace's
-// constant summed along the edge (left: X0 - X1, right: X0 + X1, bottom:
-// X0 - X2, top: X0 + X2, unscaled); then P S0 (P reduced before).  Sums in
-// FP64, in a fixed order.
+// Per CTA b (of I.partial_blocks) and column j: sum_c q_c X_j(c, 0) over the
+// CTA's cells (FP64, fixed order), into partials[b r + j].
+template <typename real>
+__global__ void __launch_bounds__(256) k_q1_qsum(const Inst *__restrict__ insts) {
+  pdl_wait();
+  pdl_trigger();
+  const Inst &I = insts[blockIdx.y];
+  if (!I.q1 || (int)blockIdx.x >= I.partial_blocks || *I.status != kOk) return;
+  __shared__ double ws[8][kMaxRank];
+  const int r = I.r, t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const size_t M = (size_t)4 * I.N;
+  const real *X = as_c<real>(I.X), *q = as_c<real>(I.q);
+  double acc[kMaxRank];
+#pragma unroll
+  for (int j = 0; j < kMaxRank; ++j) acc[j] = 0.0;
+  const int per = (I.N + I.partial_blocks - 1) / I.partial_blocks;
+  const int c0 = blockIdx.x * per, c1 = min(I.N, c0 + per);
+  for (int c = c0 + t; c < c1; c += blockDim.x) {
+    const double qc = (double)q[c];
+#pragma unroll
+    for (int j = 0; j < kMaxRank; ++j)
+      if (j < r) acc[j] += qc * (double)X[(size_t)4 * c + M * j];
+  }
+#pragma unroll
+  for (int j = 0; j < kMaxRank; ++j) {
+    double v = acc[j];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kQ1Full, v, o);
+    if (lane == 0) ws[wid][j] = v;
+  }
+  __syncthreads();
+  if (t < r) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += ws[w][t];
+    I.partials[(size_t)blockIdx.x * r + t] = s;
+  }
+}
+
+// One CTA per instance: q^_j = hx hy sum over the partials of k_q1_qsum; the
+// inflow vectors of a unit isotropic inflow on each edge, (face length) x
+// the trace's constant summed along the edge (left: X0 - X1, right: X0 + X1,
+// bottom: X0 - X2, top: X0 + X2, unscaled); then P S0 (P reduced before).
+// Sums in FP64, in a fixed order.
 template <typename real>
 __global__ void __launch_bounds__(256) k_q1_vec(const Inst *__restrict__ insts) {
   pdl_wait();
@@ -579,7 +673,7 @@ __global__ void __launch_bounds__(256) k_q1_vec(const Inst *__restrict__ insts) 
   __shared__ double red[256];
   const int r = I.r, nx = I.nx, ny = I.ny, t = threadIdx.x;
   const size_t M = (size_t)4 * I.N;
-  const real *X = as_c<real>(I.X), *q = as_c<real>(I.q);
+  const real *X = as_c<real>(I.X);
   double *vec = I.small + I.lay.vec;
   auto block_sum = [&](double v) {
     red[t] = v;
@@ -592,11 +686,13 @@ __global__ void __launch_bounds__(256) k_q1_vec(const Inst *__restrict__ insts) 
     __syncthreads();
     return x;
   };
+  for (int j = t; j < r; j += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < I.partial_blocks; ++b) s += I.partials[(size_t)b * r + j];
+    vec[j] = I.h2 * s;
+  }
   for (int j = 0; j < r; ++j) {
     const real *Xj = X + M * j;
-    double s = 0.0;
-    for (int c = t; c < I.N; c += blockDim.x) s += (double)q[c] * (double)Xj[(size_t)4 * c];
-    s = block_sum(s);
     double l = 0.0, rr = 0.0;
     for (int iy = t; iy < ny; iy += blockDim.x) {
       const size_t cl = (size_t)4 * (iy * nx), cr = (size_t)4 * (iy * nx + nx - 1);
@@ -614,7 +710,6 @@ __global__ void __launch_bounds__(256) k_q1_vec(const Inst *__restrict__ insts) 
     bo = block_sum(bo);
     to = block_sum(to);
     if (t == 0) {
-      vec[j] = I.h2 * s;
       vec[r + j] = I.hy * l;
       vec[2 * r + j] = I.hy * rr;
       vec[3 * r + j] = I.hx * bo;
@@ -733,7 +828,8 @@ int q1_si_max_grid(int nx_max, int bands_max, int n_inst, int gam_max) {
   int per_sm = 0, dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_q1_si<real>, kQ1NW * 32, smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_q1_si<real>, Q1Cfg<real>::NW * 32, smem) !=
+      cudaSuccess)
     return 0;
   return per_sm * sms;
 }
@@ -745,7 +841,7 @@ cudaError_t launch_q1_si(const Inst *d, const SiCtl &ctl, int grid, cudaStream_t
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kQ1NW * 32);
+  cfg.blockDim = dim3(Q1Cfg<real>::NW * 32);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -761,7 +857,9 @@ cudaError_t launch_q1_transport(const Inst *d, int n, int maxN, int dir, cudaStr
   return launch_pdl(k_q1_transport<real>, dim3((maxN + 127) / 128, n), dim3(128), 0, st, d, dir);
 }
 template <typename real>
-cudaError_t launch_q1_vec(const Inst *d, int n, cudaStream_t st) {
+cudaError_t launch_q1_vec(const Inst *d, int n, int maxblocks, cudaStream_t st) {
+  cudaError_t e = launch_pdl(k_q1_qsum<real>, dim3(maxblocks, n), dim3(256), 0, st, d);
+  if (e != cudaSuccess) return e;
   return launch_pdl(k_q1_vec<real>, dim3(n), dim3(256), 0, st, d);
 }
 template <typename real>
@@ -783,7 +881,7 @@ cudaError_t launch_q1_rescale(void *A, bool is_float, size_t rows, int cols, int
   template int q1_si_max_grid<real>(int, int, int, int);                                       \
   template cudaError_t launch_q1_si<real>(const Inst *, const SiCtl &, int, cudaStream_t);     \
   template cudaError_t launch_q1_transport<real>(const Inst *, int, int, int, cudaStream_t);   \
-  template cudaError_t launch_q1_vec<real>(const Inst *, int, cudaStream_t);                   \
+  template cudaError_t launch_q1_vec<real>(const Inst *, int, int, cudaStream_t);              \
   template cudaError_t launch_q1_tupdate<real>(const Inst *, int, int, bool, cudaStream_t);
 Q1_INSTANTIATE(float)
 Q1_INSTANTIATE(double)
