@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-aug", action="store_true", help="skip the augmented (rank-2r) step")
     ap.add_argument("--no-dsa", action="store_true", help="skip the DSA-accelerated step")
     ap.add_argument("--no-q1", action="store_true", help="skip the step on bilinear (Q1) elements")
+    ap.add_argument("--q1", action="store_true", help="--kernel si: bilinear (Q1) elements")
     ap.add_argument("--dsa", action="store_true", help="served: every request with DSA")
     ap.add_argument("--dsa-max-iter", type=int, default=0, help="CG cap per DSA solve (0: the library's)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
@@ -655,19 +656,22 @@ def run_kernel_sweep(args):
 
 
 def run_kernel_si(args):
-    """Two DLR steps of the workload (mixed precision, splitting threshold 2)
-    with the source iteration fixed at --si-iters iterations: a short,
-    repeatable run for profilers (e.g. ncu --graph-profiling graph)."""
+    """Two DLR steps of the workload (mixed precision, splitting threshold 2;
+    --q1: on bilinear elements) with the source iteration fixed at
+    --si-iters iterations: a short, repeatable run for profilers (e.g. ncu
+    --graph-profiling graph)."""
     import paper_2601_18705_gb300 as dlr
     case = workloads.CONFIGS[args.workload]()
-    spec = dlr.problem_from_case(case, precision=dlr.DLR_MIXED, si_fixed_iters=args.si_iters)
+    spec = dlr.problem_from_case(case, precision=dlr.DLR_MIXED, si_fixed_iters=args.si_iters,
+                                 element=1 if args.q1 else 0)
     with dlr.Solver(spec) as s:
-        dlr.set_split([s], 2.0)
+        if not args.q1:
+            dlr.set_split([s], 2.0)
         s.step(2)
         st = s.stats()
-        print(json.dumps({"kernel": "si", "workload": args.workload, "si_iters_per_step": args.si_iters,
-                          "steps": st["steps"], "sweep_grouped": st["sweep_grouped"],
-                          "T_min": float(s.T().min())}))
+        print(json.dumps({"kernel": "si", "workload": args.workload, "element": "q1" if args.q1 else "dg0",
+                          "si_iters_per_step": args.si_iters, "steps": st["steps"],
+                          "sweep_grouped": st["sweep_grouped"], "T_min": float(s.T().min())}))
 
 
 def run_batch64(args):
