@@ -363,7 +363,8 @@ def qdeim(W) -> np.ndarray:
     W = _fortran(W)
     n, r = W.shape
     idx = np.zeros(r, dtype=np.int32)
-    lib().oracle_qdeim(n, r, _fptr(W), idx.ctypes.data_as(_ip))
+    if lib().oracle_qdeim(n, r, _fptr(W), idx.ctypes.data_as(_ip)):
+        raise np.linalg.LinAlgError("no finite pivot")
     return idx
 
 

@@ -482,10 +482,13 @@ int oracle_sn_step_q1(const oracle_problem *p, double *psi, double *T,
     }
     iters++;
     double dmax = 0, pmax = 0;
+    int bad = 0;  /* a non-finite scalar flux: the iteration diverged */
     for (size_t e = 0; e < 4 * (size_t)Nx; e++) {
+      if (!isfinite(phin[e])) bad = 1;
       if (fabs(phin[e] - phi[e]) > dmax) dmax = fabs(phin[e] - phi[e]);
       if (fabs(phin[e]) > pmax) pmax = fabs(phin[e]);
     }
+    if (bad) break;
     if (p->dsa) dsa_correct_q1(p, sig_t, sig_s, phi, phin);  /* R17, R20 */
     memcpy(phi, phin, sizeof(double) * 4 * Nx);
     if (dmax <= si_tol * pmax) { converged = 1; break; }
@@ -552,7 +555,7 @@ int oracle_dlr_step_q1(const oracle_problem *p, int r, double *X, double *S, dou
   for (int c = 0; c < Nx; c++) sig_t[c] = oracle_sigma_at(p, c, T[c]) + inv_cdt;
 
   /* step 2: angles, What, beta */
-  int *idx = (int *)malloc(sizeof(int) * r);
+  int *idx = (int *)calloc(r, sizeof(int)); /* valid indices even if the choice fails */
   double *WLU = (double *)malloc(sizeof(double) * r * r);
   int *wpiv = (int *)malloc(sizeof(int) * r);
   double *beta = (double *)calloc(r, sizeof(double));
@@ -610,15 +613,18 @@ int oracle_dlr_step_q1(const oracle_problem *p, int r, double *X, double *S, dou
       }
       iters++;
       double dmax = 0, pmax = 0;
+      int bad = 0;  /* a non-finite scalar flux: the iteration diverged */
       for (int e = 0; e < M4; e++) {
         for (int j = 0; j < r; j++) Kc[j] = Psi[e + (size_t)M4 * j];
         lu_solve_inplace(r, WLU, wpiv, Kc);
         double t = 0;
         for (int j = 0; j < r; j++) t += beta[j] * Kc[j];
         phin[e] = t;
+        if (!isfinite(t)) bad = 1;
         if (fabs(t - phi[e]) > dmax) dmax = fabs(t - phi[e]);
         if (fabs(t) > pmax) pmax = fabs(t);
       }
+      if (bad) break;
       if (p->dsa) dsa_correct_q1(p, sig_t, sig_s, phi, phin);  /* R17, R20 */
       memcpy(phi, phin, sizeof(double) * M4);
       if (dmax <= si_tol * pmax) { converged = 1; break; }
@@ -1306,6 +1312,10 @@ int oracle_qdeim(int n, int r, const double *W, int *idx) {
       nrm[k] = sqrt(t);
     }
     int piv = argmax_tie(n, nrm, used);
+    if (piv < 0) {  /* no finite column norm left: W is not finite */
+      free(A); free(nrm); free(used); free(v);
+      return -1;
+    }
     idx[s] = piv;
     used[piv] = 1;
     /* Householder reflector zeroing A[s+1:, piv]; applied to every column */
@@ -1352,6 +1362,7 @@ int oracle_deim(int n, int r, const double *W, int *idx) {
     }
     for (int k = 0; k < n; k++) res[k] = fabs(res[k]);
     idx[j] = argmax_tie(n, res, used);
+    if (idx[j] < 0) { rc = -1; break; }  /* no finite residual left: W is not finite */
     used[idx[j]] = 1;
   }
   free(res);
@@ -1807,7 +1818,8 @@ static int collocation_si(const oracle_problem *p, int r, const double *X0,
     }
     iters++;
     double dmax = 0, pmax = 0;
-#pragma omp parallel if (par && !refl) reduction(max : dmax, pmax)
+    int bad = 0;  /* a non-finite scalar flux: the iteration diverged */
+#pragma omp parallel if (par && !refl) reduction(max : dmax, pmax) reduction(|| : bad)
     {
       double *Kc = (double *)malloc(sizeof(double) * r);
 #pragma omp for schedule(static)
@@ -1818,11 +1830,13 @@ static int collocation_si(const oracle_problem *p, int r, const double *X0,
         for (int j = 0; j < r; j++) t += beta[j] * Kc[j];
         phin[c] = t;
         if (refl) reflected_inflow(p, r, idx, ox, oy, W, NOm, c, Kc, in_x, in_y);
+        if (!isfinite(t)) bad = 1;
         if (fabs(t - phi[c]) > dmax) dmax = fabs(t - phi[c]);
         if (fabs(t) > pmax) pmax = fabs(t);
       }
       free(Kc);
     }
+    if (bad) break;
     if (p->dsa) dsa_iters += dsa_correct(p, sig_t, sig_s, phi, phin);
     memcpy(phi, phin, sizeof(double) * Nx);
     if (fixed <= 0 && dmax <= tol * pmax) { converged = 1; break; }
@@ -1990,7 +2004,7 @@ int oracle_dlr_step(const oracle_problem *p, int r, double *X, double *S,
   for (int c = 0; c < Nx; c++) sig_t[c] = oracle_sigma_at(p, c, T[c]) + inv_cdt;
 
   /* Step 2: select r angles from W0 (Section 4.2; reading R8). */
-  int *idx = (int *)malloc(sizeof(int) * r);
+  int *idx = (int *)calloc(r, sizeof(int)); /* valid indices even if the choice fails */
   if (opt && opt->forced_idx) memcpy(idx, opt->forced_idx, sizeof(int) * r);
   else if (opt && opt->selection == 1) rc = oracle_deim(NOm, r, W, idx);
   else rc = oracle_qdeim(NOm, r, W, idx);
@@ -2242,10 +2256,13 @@ int oracle_sn_step(const oracle_problem *p, double *psi, double *T,
     }
     iters++;
     double dmax = 0, pmax = 0;
+    int bad = 0;  /* a non-finite scalar flux: the iteration diverged */
     for (int c = 0; c < Nx; c++) {
+      if (!isfinite(phin[c])) bad = 1;
       if (fabs(phin[c] - phi[c]) > dmax) dmax = fabs(phin[c] - phi[c]);
       if (fabs(phin[c]) > pmax) pmax = fabs(phin[c]);
     }
+    if (bad) break;
     if (p->dsa) dsa_correct(p, sig_t, sig_s, phi, phin);
     memcpy(phi, phin, sizeof(double) * Nx);
     if (dmax <= si_tol * pmax) { converged = 1; break; }

@@ -314,3 +314,24 @@ def test_threads_do_not_change_results(orc):
         orc.set_threads(0)
     for a, b in zip(*out):
         assert np.array_equal(a, b)
+
+
+def test_diverged_iteration_is_not_convergence(orc):
+    # Algorithm 1 step 4 with the stopping test of reading R7: a scalar flux
+    # that is no longer finite (a diverged collocation iteration) must end the
+    # step as not converged, never pass the test (NaN compares false)
+    c = workloads.small_case(9, 7, 3, 2, 8, seed=3, T0=0.5)
+    p = oracle_problem(c)
+    T = c["T0"].reshape(-1).copy()
+    X, S, W = orc.initial_factors(p, T, 3)
+    T[4] = np.nan
+    *_, res = orc.dlr_step(p, X, S, W, T, si_tol=1e-13)
+    assert res.rc != 0
+
+
+def test_angle_choice_of_non_finite_factors_fails(orc):
+    # Algorithm 1 step 2: with no finite column norm there is no pivot
+    W = np.full((16, 3), np.nan)
+    for fn in (orc.qdeim, orc.deim):
+        with pytest.raises(Exception):
+            fn(W)
