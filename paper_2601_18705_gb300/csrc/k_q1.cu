@@ -507,6 +507,7 @@ __global__ void __launch_bounds__(Q1Cfg<real>::NW * 32) k_q1_si(const Inst *__re
         const real us = real(q1_unscale((int)(e & 3)));
         dmax = max(dmax, abs(acc - pold[e]) * us);
         pmax = max(pmax, abs(acc) * us);
+        if (!isfinite(acc)) dmax = real(INFINITY);  // diverged (max() drops NaN)
         pnew[e] = acc;
       }
       dmax = warp_max(dmax);
@@ -532,7 +533,10 @@ __global__ void __launch_bounds__(Q1Cfg<real>::NW * 32) k_q1_si(const Inst *__re
           if (done_iters >= ctl.force_iters) active[i] = 0;
           continue;
         }
-        if (I.fixed_iters > 0) {
+        if (!(d <= 1.0e308)) {  // a non-finite scalar flux: the iteration diverged
+          done = true;
+          if (blockIdx.x == 0) set_status(I.status, kENotConv);
+        } else if (I.fixed_iters > 0) {
           done = done_iters >= I.fixed_iters;
         } else {
           done = d <= I.si_tol * m;

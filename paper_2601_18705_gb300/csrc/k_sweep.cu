@@ -633,6 +633,7 @@ k_si(const Inst *__restrict__ insts, SiCtl ctl) {
           dsa_rhs<real>(I, c, acc, po, rz, bb);
           dmax = max(dmax, abs(acc - po));
           pmax = max(pmax, abs(acc));
+          if (!isfinite(acc)) dmax = real(INFINITY);  // diverged (max() drops NaN)
         }
         __shared__ double red[64];
         block_sum2(rz, bb, red);
@@ -648,6 +649,7 @@ k_si(const Inst *__restrict__ insts, SiCtl ctl) {
           sphi[c] = ss4[c] * acc;
           dmax = max(dmax, abs(acc - pold[c]));
           pmax = max(pmax, abs(acc));
+          if (!isfinite(acc)) dmax = real(INFINITY);  // diverged (max() drops NaN)
         }
       }
       dmax = warp_max(dmax);
@@ -704,7 +706,10 @@ k_si(const Inst *__restrict__ insts, SiCtl ctl) {
           if (done) active[i] = 0;
           continue;
         }
-        if (I.fixed_iters > 0) {
+        if (!(d <= 1.0e308)) {  // a non-finite scalar flux: the iteration diverged
+          done = true;
+          if (blockIdx.x == 0) set_status(I.status, kENotConv);
+        } else if (I.fixed_iters > 0) {
           done = done_iters >= I.fixed_iters;
         } else {
           done = d <= I.si_tol * m;

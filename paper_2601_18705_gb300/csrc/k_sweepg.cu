@@ -725,6 +725,7 @@ __global__ void __launch_bounds__(256) k_grp_phi(const Inst *__restrict__ insts,
       for (int q = 0; q < 4; ++q) spn[(size_t)q * I.glay + o[q]] = sp;
       dmax = fmaxf(dmax, fabsf(acc - pold[c]));
       pmax = fmaxf(pmax, fabsf(acc));
+      if (!isfinite(acc)) dmax = INFINITY;  // diverged (fmaxf drops NaN)
     }
     dmax = warp_max(dmax);
     pmax = warp_max(pmax);
@@ -765,7 +766,10 @@ __global__ void __launch_bounds__(256) k_grp_phi(const Inst *__restrict__ insts,
       I.conv[((it + 1) & 1) * 2 + 1] = 0ull;
       continue;
     }
-    if (I.fixed_iters > 0) {
+    if (!(d <= 1.0e308)) {  // a non-finite scalar flux: the iteration diverged
+      done = true;
+      set_status(I.status, kENotConv);
+    } else if (I.fixed_iters > 0) {
       done = done_iters >= I.fixed_iters;
     } else {
       done = d <= I.si_tol * m;
