@@ -306,6 +306,7 @@ static int lstep_solve(const oracle_problem *p, int r, double *const *Ax, double
                        double *const *bE, const double *Lt0, const double *gext, double *L);
 static int dsa_correct_q1(const oracle_problem *p, const double *sig_t, const double *sig_s,
                           const double *phi_old, double *phi_half);
+static void relax_track(double dmax, double pmax, double *dprev, int *grow, double *omega);
 
 /* int_{-1}^{1} of the products of two face traces, each trace written as
  * (c + d s) with (c, d) = (t0, t1): the face trace of basis function i is
@@ -600,6 +601,8 @@ int oracle_dlr_step_q1(const oracle_problem *p, int r, double *X, double *S, dou
       phi[e] = t;
     }
     int converged = 0;
+    double omega = 1.0, dprev = -1.0;  /* relaxation state (reading R22) */
+    int grow = 0;
     while (iters < si_max_iter) {
       for (int j = 0; j < r; j++) {
         int k = idx[j];
@@ -625,8 +628,15 @@ int oracle_dlr_step_q1(const oracle_problem *p, int r, double *X, double *S, dou
         if (fabs(t) > pmax) pmax = fabs(t);
       }
       if (bad) break;
-      if (p->dsa) dsa_correct_q1(p, sig_t, sig_s, phi, phin);  /* R17, R20 */
-      memcpy(phi, phin, sizeof(double) * M4);
+      if (p->dsa) {
+        dsa_correct_q1(p, sig_t, sig_s, phi, phin);  /* R17, R20 */
+        memcpy(phi, phin, sizeof(double) * M4);
+      } else {
+        if (omega == 1.0) memcpy(phi, phin, sizeof(double) * M4);
+        else
+          for (int e = 0; e < M4; e++) phi[e] += omega * (phin[e] - phi[e]);
+        relax_track(dmax, pmax, &dprev, &grow, &omega);
+      }
       if (dmax <= si_tol * pmax) { converged = 1; break; }
     }
     if (!converged) rc = -2;
@@ -1754,6 +1764,29 @@ static void reflected_inflow(const oracle_problem *p, int r, const int *idx, con
   }
 }
 
+/* Relaxation of the collocation source iteration (reading R22): the
+ * iteration phi <- phi + omega (phi^{l+1/2} - phi) starts with omega = 1
+ * (plain source iteration); each time the sweeps' change max|phi^{l+1/2} -
+ * phi| has grown by more than RELAX_GROW for RELAX_RUN consecutive
+ * iterations while above RELAX_MIN max|phi^{l+1/2}|, omega is halved.  The
+ * fixed point and the stopping test are unchanged; only a growing
+ * (diverging) iteration is affected.  The omega of an update is the one
+ * decided after the previous iteration. */
+#define RELAX_GROW 1.05
+#define RELAX_MIN 1e-4
+#define RELAX_RUN 3
+static void relax_track(double dmax, double pmax, double *dprev, int *grow, double *omega) {
+  if (*dprev >= 0 && dmax > RELAX_GROW * *dprev && dmax > RELAX_MIN * pmax) {
+    if (++*grow >= RELAX_RUN) {
+      *omega *= 0.5;
+      *grow = 0;
+    }
+  } else {
+    *grow = 0;
+  }
+  *dprev = dmax;
+}
+
 static int collocation_si(const oracle_problem *p, int r, const double *X0,
                           const double *L0, const int *idx, const double *WLU,
                           const int *wpiv, const double *beta, const double *ox,
@@ -1802,6 +1835,8 @@ static int collocation_si(const oracle_problem *p, int r, const double *X0,
   }
   int cap = fixed > 0 ? fixed : max_iter;
   int iters = 0, converged = 0, dsa_iters = 0;
+  double omega = 1.0, dprev = -1.0;  /* relaxation state (reading R22) */
+  int grow = 0;
   while (iters < cap) {
 #pragma omp parallel if (par)
     {
@@ -1837,8 +1872,15 @@ static int collocation_si(const oracle_problem *p, int r, const double *X0,
       free(Kc);
     }
     if (bad) break;
-    if (p->dsa) dsa_iters += dsa_correct(p, sig_t, sig_s, phi, phin);
-    memcpy(phi, phin, sizeof(double) * Nx);
+    if (p->dsa) {
+      dsa_iters += dsa_correct(p, sig_t, sig_s, phi, phin);
+      memcpy(phi, phin, sizeof(double) * Nx);
+    } else {
+      if (omega == 1.0) memcpy(phi, phin, sizeof(double) * Nx);
+      else
+        for (int c = 0; c < Nx; c++) phi[c] += omega * (phin[c] - phi[c]);
+      relax_track(dmax, pmax, &dprev, &grow, &omega);
+    }
     if (fixed <= 0 && dmax <= tol * pmax) { converged = 1; break; }
   }
   *iters_out = iters;

@@ -1234,7 +1234,7 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   bytes += sz(sizeof(unsigned long long) * gedge_ld * (rows_cap + 1));
   const size_t dsa_part = any_dsa ? (size_t)n * kDsaSlots * gmax : 0;  // per-CTA CG partials
   bytes += sz(sizeof(double) * std::max<size_t>(1, dsa_part));
-  bytes += sz(sizeof(GrpSi)) + 2 * sz(sizeof(int) * n);  // loop state of the grouped sweep
+  bytes += sz(sizeof(GrpSi)) + 2 * sz(sizeof(int) * n) + sz(sizeof(double) * 3 * n);  // loop state of the grouped sweep
   if (cudaMalloc(&b->d_mem, bytes) != cudaSuccess) {
     delete b;
     return fail(DLR_ENOMEM, "batch table allocation failed");
@@ -1300,6 +1300,7 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
     g.n_units = b->ctl.n_units;
     g.active = carve<int>(cur, n);
     g.par_of = carve<int>(cur, n);
+    g.relax = carve<double>(cur, 3 * n);
     if (cudaMemcpyAsync(b->gs, &g, sizeof g, cudaMemcpyHostToDevice, hs[0]->st) != cudaSuccess ||
         cudaStreamSynchronize(hs[0]->st) != cudaSuccess) {
       cudaFree(b->d_mem);

@@ -372,6 +372,7 @@ struct GrpSi {
   int n_units;
   int *active;
   int *par_of;
+  double *relax;  // relaxation state per instance (3 each, see relax_track)
 };
 
 // partial sums of one DSA CG iteration: p.q, r.z, r.r, and b.b of the
@@ -557,6 +558,34 @@ __device__ __forceinline__ void refl_inject(const Inst &I, const real *psi, int 
     const int c = G.by * I.nx + ix;
     s0[c] = fmadd(G.ay, refl_in<real>(I, psi, j, k, c, 1), base[o]);
   }
+}
+
+// Relaxation of the collocation source iteration (reading R22): the update
+// phi <- phi + omega (phi^{l+1/2} - phi) starts with omega = 1 (the plain
+// iteration); each time the sweeps' change d = max|phi^{l+1/2} - phi| has
+// grown by more than kRelaxGrow for kRelaxRun consecutive iterations while
+// above kRelaxMin max|phi^{l+1/2}|, omega is halved (a diverging iteration
+// whose dominant eigenvalue is below -1 becomes a contraction).  The omega
+// of an update is the one decided after the previous iteration; the state
+// per instance is (omega, the previous d, the growth run).
+constexpr double kRelaxGrow = 1.05, kRelaxMin = 1e-4;
+constexpr int kRelaxRun = 3;
+__host__ __device__ inline void relax_track(double d, double m, double *st) {
+  if (st[1] >= 0.0 && d > kRelaxGrow * st[1] && d > kRelaxMin * m) {
+    st[2] += 1.0;
+    if (st[2] >= kRelaxRun) {
+      st[0] *= 0.5;
+      st[2] = 0.0;
+    }
+  } else {
+    st[2] = 0.0;
+  }
+  st[1] = d;
+}
+__host__ __device__ inline void relax_reset(double *st) {
+  st[0] = 1.0;
+  st[1] = -1.0;
+  st[2] = 0.0;
 }
 
 constexpr uint64_t kGridWaitNs = 4000000000ull;  // bound of a grid-barrier wait

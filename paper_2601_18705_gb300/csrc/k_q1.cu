@@ -253,7 +253,8 @@ __global__ void __launch_bounds__(128) k_q1_sn_prep(const Inst *__restrict__ ins
 template <typename real>
 __host__ __device__ inline size_t q1_si_smem_bytes(int nx_max, int bands_max, int n_inst, int gam_max) {
   return (size_t)(Q1Cfg<real>::NW + 1) * 2 * nx_max * sizeof(real) + (size_t)(bands_max + 3) / 4 * 4 * sizeof(int) +
-         (size_t)(n_inst + 3) / 4 * 4 * sizeof(int) + (size_t)gam_max * sizeof(real) + 16;
+         (size_t)(n_inst + 3) / 4 * 4 * sizeof(int) + (size_t)3 * n_inst * sizeof(double) +
+         (size_t)gam_max * sizeof(real) + 16;
 }
 
 // The inputs of one cell of a sweep: sigma_t, sigma_s / 4pi, and the 4
@@ -452,11 +453,16 @@ __global__ void __launch_bounds__(Q1Cfg<real>::NW * 32) k_q1_si(const Inst *__re
   off += (size_t)(ctl.bands_max + 3) / 4 * 4 * sizeof(int);
   int *active = reinterpret_cast<int *>(q1sm + off);
   off += (size_t)(ctl.n_inst + 3) / 4 * 4 * sizeof(int);
+  double *relax = reinterpret_cast<double *>(q1sm + off);  // relaxation state, 3 per instance
+  off += (size_t)3 * ctl.n_inst * sizeof(double);
   off = (off + 15) & ~size_t(15);
   real *gam = reinterpret_cast<real *>(q1sm + off);
   __shared__ int unit_s, n_active_s;
   volatile int *abort_flag = ctl.abort_flag;
-  for (int i = threadIdx.x; i < ctl.n_inst; i += blockDim.x) active[i] = (*insts[i].status == kOk) ? 1 : 0;
+  for (int i = threadIdx.x; i < ctl.n_inst; i += blockDim.x) {
+    active[i] = (*insts[i].status == kOk) ? 1 : 0;
+    relax_reset(relax + 3 * i);
+  }
   __syncthreads();
   for (int it = 0;; ++it) {
     if (threadIdx.x == 0) {
@@ -501,14 +507,16 @@ __global__ void __launch_bounds__(Q1Cfg<real>::NW * 32) k_q1_si(const Inst *__re
         gam[q] = real(I.gamma_ext ? I.gamma_ext[q] : I.small[I.lay.gamma + q]);
       __syncthreads();
       real dmax = real(0), pmax = real(0);
+      const real om = real(I.gamma_ext ? 1.0 : relax[3 * i]);  // relaxation (DLR; 1: the plain iteration)
       for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < M; e += (size_t)gridDim.x * blockDim.x) {
         real acc = real(0);
         for (int q = 0; q < r; ++q) acc = fmadd(gam[q], psi[e + M * q], acc);
         const real us = real(q1_unscale((int)(e & 3)));
-        dmax = max(dmax, abs(acc - pold[e]) * us);
+        const real po = pold[e];
+        dmax = max(dmax, abs(acc - po) * us);
         pmax = max(pmax, abs(acc) * us);
         if (!isfinite(acc)) dmax = real(INFINITY);  // diverged (max() drops NaN)
-        pnew[e] = acc;
+        pnew[e] = om == real(1) ? acc : fmadd(om, acc - po, po);
       }
       dmax = warp_max(dmax);
       pmax = warp_max(pmax);
@@ -533,6 +541,7 @@ __global__ void __launch_bounds__(Q1Cfg<real>::NW * 32) k_q1_si(const Inst *__re
           if (done_iters >= ctl.force_iters) active[i] = 0;
           continue;
         }
+        if (!I.gamma_ext) relax_track(d, m, relax + 3 * i);  // DLR only (SN: gamma = w > 0)
         if (!(d <= 1.0e308)) {  // a non-finite scalar flux: the iteration diverged
           done = true;
           if (blockIdx.x == 0) set_status(I.status, kENotConv);

@@ -548,6 +548,8 @@ k_si(const Inst *__restrict__ insts, SiCtl ctl) {
   off += (size_t)(ctl.bands_max + 3) / 4 * 4 * sizeof(int);
   int *active = reinterpret_cast<int *>(smem + off);
   off += (size_t)(ctl.n_inst + 3) / 4 * 4 * sizeof(int);
+  double *relax = reinterpret_cast<double *>(smem + off);  // relaxation state, 3 per instance
+  off += (size_t)3 * ctl.n_inst * sizeof(double);
   double *dsa_sc = reinterpret_cast<double *>(smem + off);  // CG scalars (DSA)
   int *dsa_on = reinterpret_cast<int *>(smem + off + dsa_scalar_bytes(ctl.n_inst, ctl.any_dsa));
   off += dsa_smem_bytes(ctl.n_inst, ctl.any_dsa);
@@ -556,8 +558,10 @@ k_si(const Inst *__restrict__ insts, SiCtl ctl) {
   __shared__ int unit_s, n_active_s;
   volatile int *abort_flag = ctl.abort_flag;
 
-  for (int i = threadIdx.x; i < ctl.n_inst; i += blockDim.x)
+  for (int i = threadIdx.x; i < ctl.n_inst; i += blockDim.x) {
     active[i] = (*insts[i].status == kOk) ? 1 : 0;
+    relax_reset(relax + 3 * i);
+  }
   // tags of the edge words: 20 bits of the launch counter, 12 of the iteration
   const unsigned epoch_tag = (*(volatile unsigned *)ctl.epoch & 0xfffffu) << 12;
   __syncthreads();
@@ -642,12 +646,15 @@ k_si(const Inst *__restrict__ insts, SiCtl ctl) {
           dsa_slot(ctl, i, kDsaBb)[blockIdx.x] = bb;
         }
       } else {
+        const real om = real(relax[3 * i]);  // relaxation (1: the plain iteration)
         for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
           real acc = real(0);
           for (int j = 0; j < r; ++j) acc = fmadd(gam[j], psi[(size_t)N * j + c], acc);
-          pnew[c] = acc;
-          sphi[c] = ss4[c] * acc;
-          dmax = max(dmax, abs(acc - pold[c]));
+          const real po = pold[c];
+          const real pn = om == real(1) ? acc : fmadd(om, acc - po, po);
+          pnew[c] = pn;
+          sphi[c] = ss4[c] * pn;
+          dmax = max(dmax, abs(acc - po));
           pmax = max(pmax, abs(acc));
           if (!isfinite(acc)) dmax = real(INFINITY);  // diverged (max() drops NaN)
         }
@@ -706,6 +713,7 @@ k_si(const Inst *__restrict__ insts, SiCtl ctl) {
           if (done) active[i] = 0;
           continue;
         }
+        if (!I.dsa && !I.gamma_ext) relax_track(d, m, relax + 3 * i);  // DLR only (SN: gamma = w > 0)
         if (!(d <= 1.0e308)) {  // a non-finite scalar flux: the iteration diverged
           done = true;
           if (blockIdx.x == 0) set_status(I.status, kENotConv);
@@ -807,7 +815,7 @@ size_t si_smem_bytes(int nx_max, int bands_max, int n_inst, int gam_max, int dsa
   using real2 = typename Real2<real>::type;
   return (size_t)NW * kRing * kRingLd * sizeof(real2) + (size_t)(NW + 1) * edge_ld(nx_max) * sizeof(real) +
          (size_t)(bands_max + 3) / 4 * 4 * sizeof(int) + (size_t)(n_inst + 3) / 4 * 4 * sizeof(int) +
-         dsa_smem_bytes(n_inst, dsa) + (size_t)gam_max * sizeof(real);
+         (size_t)3 * n_inst * sizeof(double) + dsa_smem_bytes(n_inst, dsa) + (size_t)gam_max * sizeof(real);
 }
 
 template <typename real>

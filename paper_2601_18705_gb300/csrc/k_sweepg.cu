@@ -608,6 +608,7 @@ __global__ void k_grp_prep(const Inst *__restrict__ insts, int n, SiCtl ctl, Grp
     *insts[t].nonpos = 0;
     gs->active[t] = *insts[t].status == kOk ? 1 : 0;
     gs->par_of[t] = -1;
+    relax_reset(gs->relax + 3 * t);
   }
 }
 
@@ -708,6 +709,7 @@ __global__ void __launch_bounds__(256) k_grp_phi(const Inst *__restrict__ insts,
     const float *pold = as_c<float>((it & 1) ? I.phi1 : I.phi0);
     float *pnew = as<float>((it & 1) ? I.phi0 : I.phi1);
     float *spn = I.spk + (size_t)((it + 1) & 1) * 4 * I.glay;
+    const float om = (float)gs->relax[3 * i];  // relaxation (1: the plain iteration)
     float dmax = 0.f, pmax = 0.f;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
       const int y = c / nx, x = c - y * nx;
@@ -719,11 +721,13 @@ __global__ void __launch_bounds__(256) k_grp_phi(const Inst *__restrict__ insts,
         v[q] = (qmask >> q) & 1 ? qs[(size_t)q * I.glay + o[q]] : 0.f;
       }
       const float acc = ((v[0] + v[1]) + v[2]) + v[3];
-      pnew[c] = acc;
-      const float sp = ss4[c] * acc;
+      const float po = pold[c];
+      const float pn = om == 1.f ? acc : fmaf(om, acc - po, po);
+      pnew[c] = pn;
+      const float sp = ss4[c] * pn;
 #pragma unroll
       for (int q = 0; q < 4; ++q) spn[(size_t)q * I.glay + o[q]] = sp;
-      dmax = fmaxf(dmax, fabsf(acc - pold[c]));
+      dmax = fmaxf(dmax, fabsf(acc - po));
       pmax = fmaxf(pmax, fabsf(acc));
       if (!isfinite(acc)) dmax = INFINITY;  // diverged (fmaxf drops NaN)
     }
@@ -766,6 +770,7 @@ __global__ void __launch_bounds__(256) k_grp_phi(const Inst *__restrict__ insts,
       I.conv[((it + 1) & 1) * 2 + 1] = 0ull;
       continue;
     }
+    relax_track(d, m, gs->relax + 3 * i);
     if (!(d <= 1.0e308)) {  // a non-finite scalar flux: the iteration diverged
       done = true;
       set_status(I.status, kENotConv);

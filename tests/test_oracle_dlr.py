@@ -335,3 +335,73 @@ def test_angle_choice_of_non_finite_factors_fails(orc):
     for fn in (orc.qdeim, orc.deim):
         with pytest.raises(Exception):
             fn(W)
+
+
+def _negative_T_case(orc):
+    # a uniform thick medium at T0 < 0 (the state Algorithm 1 reaches after a
+    # loss of positivity): -rho c_v < 4 pi dt sigma B'(T0) < 0 makes the
+    # effective scattering sigma_s = sigma 4 pi dt sigma B' / D negative,
+    # sigma_s / sigma_t = -1.44, so the plain source iteration diverges
+    nx = ny = 6
+    c = workloads.small_case(nx, ny, 4, 2, 8, seed=1, T0=0.5)
+    c["sigma"] = np.full((ny, nx), 100.0)
+    p = oracle_problem(c)
+    T0 = np.full(nx * ny, -0.714)
+    X0, S0, W0 = orc.initial_factors(p, -T0, 4)
+    return c, p, T0, X0, S0, W0
+
+
+def test_relaxed_iteration_converges_to_the_dense_solution(orc):
+    # reading R22: the collocation iteration is relaxed when it grows; its
+    # plain form diverges here (an eigenvalue of the iteration map below -1),
+    # the relaxed one reaches the solution of the collocation system
+    c, p, T0, X0, S0, W0 = _negative_T_case(orc)
+    r = 4
+    idx = orc.qdeim(W0)
+    ox, oy, oz, w = orc.quadrature(c["n_polar"], c["n_azim"])
+    coef = orc.coefficients(p, T0)
+    assert (coef["sigma_s"] / coef["sigma_t"]).max() < -1.4
+    N = p.Nx
+    What = W0[idx, :]
+    gamma = np.linalg.solve(What.T, w @ W0)
+    Psi0 = X0 @ S0 @ What.T
+    M = np.zeros((N, N))
+    A = np.zeros((N * r, N * r))
+    b = np.zeros(N * r)
+    for j in range(r):
+        Tj, g = transport_block(p.nx, p.ny, p.lx / p.nx, p.ly / p.ny, ox[idx[j]], oy[idx[j]],
+                                coef["sigma_t"], p.psi_edge)
+        M += gamma[j] * np.linalg.solve(Tj, np.diag(coef["sigma_s"] / (4 * np.pi)))
+        A[j * N:(j + 1) * N, j * N:(j + 1) * N] += Tj
+        for l in range(r):
+            A[j * N:(j + 1) * N, l * N:(l + 1) * N] -= np.diag(coef["sigma_s"] / (4 * np.pi) * gamma[l])
+        b[j * N:(j + 1) * N] = coef["q"] + Psi0[:, j] / (p.c * p.dt) + g
+    assert np.linalg.eigvals(M).real.min() < -1.3
+    ref = np.linalg.solve(A, b).reshape(r, N).T
+    Psi, it, rc = orc.collocation(p, X0, S0, W0, T0, idx, si_tol=1e-15, si_max_iter=2000)
+    assert rc == 0 and it < 200
+    np.testing.assert_allclose(Psi, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def test_relaxation_leaves_a_contracting_iteration_alone(orc):
+    # the same problem at T0 > 0 contracts: the relaxation never engages, so
+    # k iterations of the oracle equal k plain source iterations written out
+    # here (sweeps of every chosen angle, phi = Psi gamma)
+    c, p, T0, X0, S0, W0 = _negative_T_case(orc)
+    T0 = -T0
+    idx = orc.qdeim(W0)
+    ox, oy, oz, w = orc.quadrature(c["n_polar"], c["n_azim"])
+    coef = orc.coefficients(p, T0)
+    What = W0[idx, :]
+    gamma = np.linalg.solve(What.T, w @ W0)
+    Psi0 = X0 @ S0 @ What.T
+    phi = Psi0 @ gamma
+    for k in range(12):
+        Psi = np.column_stack([
+            orc.sweep(p, ox[idx[j]], oy[idx[j]], coef["sigma_t"],
+                      coef["sigma_s"] * phi / (4 * np.pi) + coef["q"] + Psi0[:, j] / (p.c * p.dt))
+            for j in range(len(idx))])
+        phi = Psi @ gamma
+    got, it, rc = orc.collocation(p, X0, S0, W0, T0, idx, si_fixed_iters=12)
+    assert rc == 0
+    np.testing.assert_allclose(got, Psi, rtol=1e-12, atol=1e-13 * np.abs(Psi).max())
