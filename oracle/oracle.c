@@ -306,7 +306,7 @@ static int lstep_solve(const oracle_problem *p, int r, double *const *Ax, double
                        double *const *bE, const double *Lt0, const double *gext, double *L);
 static int dsa_correct_q1(const oracle_problem *p, const double *sig_t, const double *sig_s,
                           const double *phi_old, double *phi_half);
-static void relax_track(double dmax, double pmax, double *dprev, int *grow, double *omega);
+static int relax_track(double dmax, double pmax, double *dprev, int *grow, double *omega);
 
 /* int_{-1}^{1} of the products of two face traces, each trace written as
  * (c + d s) with (c, d) = (t0, t1): the face trace of basis function i is
@@ -635,7 +635,7 @@ int oracle_dlr_step_q1(const oracle_problem *p, int r, double *X, double *S, dou
         if (omega == 1.0) memcpy(phi, phin, sizeof(double) * M4);
         else
           for (int e = 0; e < M4; e++) phi[e] += omega * (phin[e] - phi[e]);
-        relax_track(dmax, pmax, &dprev, &grow, &omega);
+        if (relax_track(dmax, pmax, &dprev, &grow, &omega)) break;
       }
       if (dmax <= si_tol * pmax) { converged = 1; break; }
     }
@@ -1768,16 +1768,21 @@ static void reflected_inflow(const oracle_problem *p, int r, const int *idx, con
  * iteration phi <- phi + omega (phi^{l+1/2} - phi) starts with omega = 1
  * (plain source iteration); each time the sweeps' change max|phi^{l+1/2} -
  * phi| has grown by more than RELAX_GROW for RELAX_RUN consecutive
- * iterations while above RELAX_MIN max|phi^{l+1/2}|, omega is halved.  The
- * fixed point and the stopping test are unchanged; only a growing
- * (diverging) iteration is affected.  The omega of an update is the one
- * decided after the previous iteration. */
+ * iterations while above RELAX_MIN max|phi^{l+1/2}|, omega is halved, down
+ * to RELAX_FLOOR; a further such run means the relaxed iteration diverges
+ * too, and the step ends as not converged (returns 1).  The fixed point and
+ * the stopping test are unchanged; only a growing (diverging) iteration is
+ * affected.  The omega of an update is the one decided after the previous
+ * iteration. */
 #define RELAX_GROW 1.05
 #define RELAX_MIN 1e-4
 #define RELAX_RUN 3
-static void relax_track(double dmax, double pmax, double *dprev, int *grow, double *omega) {
+#define RELAX_FLOOR 0.125
+static int relax_track(double dmax, double pmax, double *dprev, int *grow, double *omega) {
+  int give_up = 0;
   if (*dprev >= 0 && dmax > RELAX_GROW * *dprev && dmax > RELAX_MIN * pmax) {
     if (++*grow >= RELAX_RUN) {
+      if (*omega <= RELAX_FLOOR) give_up = 1;
       *omega *= 0.5;
       *grow = 0;
     }
@@ -1785,6 +1790,7 @@ static void relax_track(double dmax, double pmax, double *dprev, int *grow, doub
     *grow = 0;
   }
   *dprev = dmax;
+  return give_up;
 }
 
 static int collocation_si(const oracle_problem *p, int r, const double *X0,
@@ -1879,7 +1885,7 @@ static int collocation_si(const oracle_problem *p, int r, const double *X0,
       if (omega == 1.0) memcpy(phi, phin, sizeof(double) * Nx);
       else
         for (int c = 0; c < Nx; c++) phi[c] += omega * (phin[c] - phi[c]);
-      relax_track(dmax, pmax, &dprev, &grow, &omega);
+      if (relax_track(dmax, pmax, &dprev, &grow, &omega)) break;
     }
     if (fixed <= 0 && dmax <= tol * pmax) { converged = 1; break; }
   }

@@ -627,6 +627,18 @@ static void fill_common(dlr_handle *h, const dlr_problem *problem) {
   I.dsa_iters_total = nullptr;
   for (int e = 0; e < 4; ++e) I.reflect[e] = problem->reflect[e];
   I.n_azim = problem->n_azim;
+  {
+    // polar pairs for step 7: an even n_polar whose mirrored polar levels
+    // give bitwise equal Om_x, Om_y (the Gauss nodes are symmetric)
+    const int np = problem->n_polar, na = problem->n_azim;
+    bool pairs = np % 2 == 0 && np >= 2;
+    for (int p = 0; pairs && p < np / 2; ++p)
+      for (int a = 0; a < na; ++a) {
+        const int k = p * na + a, kp = (np - 1 - p) * na + a;
+        if (h->ox[k] != h->ox[kp] || h->oy[k] != h->oy[kp]) pairs = false;
+      }
+    I.polar_pairs = pairs ? 1 : 0;
+  }
   I.refl_base = nullptr;
   I.refl_kap = I.refl_data = I.refl_y = I.refl_u = nullptr;
   I.refl_passes = nullptr;

@@ -150,6 +150,9 @@ struct Inst {
   // and for boundary column o - ny of its y-edge
   int reflect[4];
   int n_azim;
+  // 1: the angles of polar cosines +-mu (polar indices p and n_polar - 1 - p)
+  // have bitwise equal Om_x, Om_y, so step 7 forms B_k^{-1} once per pair
+  int polar_pairs;
   void *refl_base;
   // reflective edges of a DLR instance (reading R19; refl_base then holds
   // r x (ny + nx) entries, one per chosen angle j).  In the source iteration
@@ -565,15 +568,19 @@ __device__ __forceinline__ void refl_inject(const Inst &I, const real *psi, int 
 // iteration); each time the sweeps' change d = max|phi^{l+1/2} - phi| has
 // grown by more than kRelaxGrow for kRelaxRun consecutive iterations while
 // above kRelaxMin max|phi^{l+1/2}|, omega is halved (a diverging iteration
-// whose dominant eigenvalue is below -1 becomes a contraction).  The omega
-// of an update is the one decided after the previous iteration; the state
-// per instance is (omega, the previous d, the growth run).
-constexpr double kRelaxGrow = 1.05, kRelaxMin = 1e-4;
+// whose dominant eigenvalue is below -1 becomes a contraction), down to
+// kRelaxFloor; a further such run means the relaxed iteration diverges too
+// (returns true: the step ends with DLR_ENOTCONV).  The omega of an update
+// is the one decided after the previous iteration; the state per instance
+// is (omega, the previous d, the growth run).
+constexpr double kRelaxGrow = 1.05, kRelaxMin = 1e-4, kRelaxFloor = 0.125;
 constexpr int kRelaxRun = 3;
-__host__ __device__ inline void relax_track(double d, double m, double *st) {
+__host__ __device__ inline bool relax_track(double d, double m, double *st) {
+  bool give_up = false;
   if (st[1] >= 0.0 && d > kRelaxGrow * st[1] && d > kRelaxMin * m) {
     st[2] += 1.0;
     if (st[2] >= kRelaxRun) {
+      if (st[0] <= kRelaxFloor) give_up = true;
       st[0] *= 0.5;
       st[2] = 0.0;
     }
@@ -581,6 +588,7 @@ __host__ __device__ inline void relax_track(double d, double m, double *st) {
     st[2] = 0.0;
   }
   st[1] = d;
+  return give_up;
 }
 __host__ __device__ inline void relax_reset(double *st) {
   st[0] = 1.0;

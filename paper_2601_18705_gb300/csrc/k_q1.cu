@@ -541,8 +541,9 @@ __global__ void __launch_bounds__(Q1Cfg<real>::NW * 32) k_q1_si(const Inst *__re
           if (done_iters >= ctl.force_iters) active[i] = 0;
           continue;
         }
-        if (!I.gamma_ext) relax_track(d, m, relax + 3 * i);  // DLR only (SN: gamma = w > 0)
-        if (!(d <= 1.0e308)) {  // a non-finite scalar flux: the iteration diverged
+        // DLR only (SN: gamma = w > 0); true: diverging even when relaxed
+        const bool diverged = !I.gamma_ext && relax_track(d, m, relax + 3 * i);
+        if (diverged || !(d <= 1.0e308)) {  // or a non-finite scalar flux
           done = true;
           if (blockIdx.x == 0) set_status(I.status, kENotConv);
         } else if (I.fixed_iters > 0) {

@@ -511,7 +511,12 @@ k_lstep_angle(const Inst *__restrict__ insts) {
   double *cols = colsw + wid * NC * LDC;
   const double *Mt = sm + 4 * r * r;
   const int gw = blockIdx.x * kLsWarps + wid, nwarps = nblk * kLsWarps;
-  for (int k = gw; active && k < K; k += nwarps) {
+  // with polar pairs (angles of polar cosines +-mu share Om_x, Om_y, hence
+  // B_k, bit for bit) one elimination serves both angles of a pair
+  const int na = I.n_azim, np2 = I.polar_pairs ? (K / na) / 2 : 0;
+  const int items = I.polar_pairs ? np2 * na : K;
+  for (int it = gw; active && it < items; it += nwarps) {
+    const int k = it, kp = I.polar_pairs ? (K / na - 1 - it / na) * na + it % na : -1;
     const AngleOps o = angle_ops(I, sm, k);
     for (int c = lane; c < NC; c += 32) {
 #pragma unroll
@@ -565,27 +570,31 @@ k_lstep_angle(const Inst *__restrict__ insts) {
     }
     // B_k^{-1} column j is cols column RB + j
     const double *binv = cols + RB * LDC;
-    const double qk = lane < r ? angle_q(I, sm, o, k, lane) : 0.0;
-    double y0 = 0.0, y1 = 0.0;
+    for (int u = 0; u < (kp >= 0 ? 2 : 1); ++u) {
+      const int kk = u == 0 ? k : kp;
+      const double qk = lane < r ? angle_q(I, sm, o, kk, lane) : 0.0;
+      double y0 = 0.0, y1 = 0.0;
 #pragma unroll
-    for (int jj = 0; jj < RB; ++jj) {
-      if (jj < r) {
-        const double qj = __shfl_sync(kFullMask, qk, jj);
-        if (lane < r) {
-          const double t = binv[jj * LDC + lane] * qj;
-          if (jj & 1) y1 += t; else y0 += t;
+      for (int jj = 0; jj < RB; ++jj) {
+        if (jj < r) {
+          const double qj = __shfl_sync(kFullMask, qk, jj);
+          if (lane < r) {
+            const double t = binv[jj * LDC + lane] * qj;
+            if (jj & 1) y1 += t; else y0 += t;
+          }
         }
       }
+      if (lane < r) {
+        const double y = y0 + y1;
+        I.L[(size_t)r * kk + lane] = y;
+        myacc[r * r + lane] += I.w[kk] * y;
+      }
+      double *B = I.lu + (size_t)kk * r * r;
+      for (int e = lane; e < r * r; e += 32) B[e] = binv[(e / r) * LDC + (e % r)];
     }
-    const double wk = I.w[k];
-    if (lane < r) {
-      const double y = y0 + y1;
-      I.L[(size_t)r * k + lane] = y;
-      myacc[r * r + lane] += wk * y;
+    const double wk = kp >= 0 ? I.w[k] + I.w[kp] : I.w[k];
+    if (lane < r)
       for (int jj = 0; jj < r; ++jj) myacc[lane + r * jj] += wk * binv[jj * LDC + lane];
-    }
-    double *B = I.lu + (size_t)k * r * r;
-    for (int e = lane; e < r * r; e += 32) B[e] = binv[(e / r) * LDC + (e % r)];
     __syncwarp();
   }
   __syncthreads();

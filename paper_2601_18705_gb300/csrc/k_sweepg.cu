@@ -770,8 +770,8 @@ __global__ void __launch_bounds__(256) k_grp_phi(const Inst *__restrict__ insts,
       I.conv[((it + 1) & 1) * 2 + 1] = 0ull;
       continue;
     }
-    relax_track(d, m, gs->relax + 3 * i);
-    if (!(d <= 1.0e308)) {  // a non-finite scalar flux: the iteration diverged
+    const bool diverged = relax_track(d, m, gs->relax + 3 * i);  // true: diverging even when relaxed
+    if (diverged || !(d <= 1.0e308)) {  // or a non-finite scalar flux
       done = true;
       set_status(I.status, kENotConv);
     } else if (I.fixed_iters > 0) {
