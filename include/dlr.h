@@ -264,28 +264,38 @@ int dlr_set_split(dlr_handle *const *hs, int32_t n, double split);
  * Synchronises. */
 int dlr_debug_lose_edge(dlr_handle *const *hs, int32_t n);
 
-/* Copies T (nx*ny FP64) into out; synchronises. */
+/* Copies the material temperature T (Section 2.1, the T of Eq. (temperature
+ * update) after the last step; nx*ny FP64, cell c = iy nx + ix) into out;
+ * synchronises.  Returns the sticky device status if a step failed. */
 int dlr_get_T(dlr_handle *h, double *out, int32_t out_on_device);
 
-/* Replaces T (nx*ny FP64) with in; enqueued on the stream.  A pageable host
- * buffer is consumed before return; a pinned one must stay unchanged until
- * the stream has executed the copy. */
+/* Replaces the temperature T (Section 2.1; nx*ny FP64) with in: the T0 of
+ * the next step's linearisation (Section 2.2).  Enqueued on the stream.  A
+ * pageable host buffer is consumed before return; a pinned one must stay
+ * unchanged until the stream has executed the copy. */
 int dlr_set_T(dlr_handle *h, const double *in, int32_t in_on_device);
 
-/* Copies the factors: X (nx*ny x r, column-major, hx*hy*X^T X = I), S (r x
- * r, column-major), W (NOm x r, column-major, sum_k w_k W_ki W_kj = d_ij), all
- * FP64 (X is widened in mixed precision); *r_out = r.  Any pointer may be
- * NULL.  Synchronises. */
+/* Copies the low-rank factors of psi = X S W^T (Section 4: the rank-r
+ * representation Algorithm 1 advances; W in the quadrature's discrete inner
+ * product): X (rows x r, column-major, hx*hy*X^T X = I; rows = nx*ny, or
+ * 4*nx*ny plain Legendre coefficients with element = 1), S (r x r,
+ * column-major), W (NOm x r, column-major, sum_k w_k W_ki W_kj = d_ij), all
+ * FP64 (X is widened in mixed precision); rotated to the SVD basis of S
+ * first when the step keeps S general.  *r_out = r.  Any pointer may be NULL.
+ * Synchronises; DLR_EINVAL for a full-rank SN handle. */
 int dlr_get_factors(dlr_handle *h, double *X, double *S, double *W,
                     int32_t *r_out, int32_t out_on_device);
 
-/* Replaces the factors (same layouts as dlr_get_factors).  Used to start
- * from a given state. */
+/* Replaces the factors (same layouts as dlr_get_factors): the X0, S0, W0 the
+ * next step of Algorithm 1 starts from.  Used to start from a given state.
+ * DLR_EINVAL for a full-rank SN handle. */
 int dlr_set_factors(dlr_handle *h, const double *X, const double *S,
                     const double *W, int32_t in_on_device);
 
-/* Copies the quadrature: omega_xyz (NOm x 3 row-major: Om_x, Om_y, Om_z per
- * angle) and weights w (NOm, summing to 4 pi).  Either may be NULL. */
+/* Copies the angular quadrature of the discrete ordinates (Section 2.2; the
+ * product rule of Gauss-Legendre polar cosines and equispaced azimuths):
+ * omega_xyz (NOm x 3 row-major: Om_x, Om_y, Om_z of angle k = p n_azim + a)
+ * and weights w (NOm, summing to 4 pi).  Either may be NULL. */
 int dlr_get_quadrature(dlr_handle *h, double *omega_xyz, double *w);
 
 /* The r angle indices chosen in the last step (Algorithm 1 step 2), or -1

@@ -304,7 +304,8 @@ static void lu_solve_inplace(int n, const double *LU, const int *piv, double *b)
 static int lstep_solve(const oracle_problem *p, int r, double *const *Ax, double *const *Ay,
                        const double *Mt, const double *Ms, const double *qh,
                        double *const *bE, const double *Lt0, const double *gext, double *L);
-static int dsa_correct_q1(const oracle_problem *p, const double *sig_t, const double *sig_s,
+static double *dsa_matrix_q1_new(const oracle_problem *p, const double *sig_t, const double *sig_s);
+static int dsa_correct_q1(const oracle_problem *p, const double *A, const double *sig_s,
                           const double *phi_old, double *phi_half);
 static int relax_track(double dmax, double pmax, double *dprev, int *grow, double *omega);
 
@@ -468,6 +469,7 @@ int oracle_sn_step_q1(const oracle_problem *p, double *psi, double *T,
   for (int k = 0; k < NOm; k++)
     for (size_t e = 0; e < 4 * (size_t)Nx; e++) phi[e] += w[k] * psi0[4 * (size_t)Nx * k + e];
   int iters = 0, converged = 0;
+  double *Adsa = p->dsa ? dsa_matrix_q1_new(p, sig_t, sig_s) : NULL;
   while (iters < si_max_iter) {
     for (size_t e = 0; e < 4 * (size_t)Nx; e++) phin[e] = 0;
     for (int k = 0; k < NOm; k++) {
@@ -490,7 +492,7 @@ int oracle_sn_step_q1(const oracle_problem *p, double *psi, double *T,
       if (fabs(phin[e]) > pmax) pmax = fabs(phin[e]);
     }
     if (bad) break;
-    if (p->dsa) dsa_correct_q1(p, sig_t, sig_s, phi, phin);  /* R17, R20 */
+    if (p->dsa) dsa_correct_q1(p, Adsa, sig_s, phi, phin);  /* R17, R20 */
     memcpy(phi, phin, sizeof(double) * 4 * Nx);
     if (dmax <= si_tol * pmax) { converged = 1; break; }
   }
@@ -518,7 +520,7 @@ int oracle_sn_step_q1(const oracle_problem *p, double *psi, double *T,
     *inflow = i_;
   }
   free(ox); free(oy); free(oz); free(w); free(sig_s); free(q); free(B0); free(D);
-  free(sig_t); free(phi); free(phin); free(src); free(psi0); free(in_x); free(in_y);
+  free(sig_t); free(phi); free(phin); free(src); free(psi0); free(in_x); free(in_y); free(Adsa);
   return converged ? iters : -2;
 }
 
@@ -592,6 +594,7 @@ int oracle_dlr_step_q1(const oracle_problem *p, int r, double *X, double *S, dou
   double *in_x = (double *)malloc(sizeof(double) * 2 * ny);
   double *in_y = (double *)malloc(sizeof(double) * 2 * nx);
   int iters = 0;
+  double *Adsa = p->dsa ? dsa_matrix_q1_new(p, sig_t, sig_s) : NULL;
   if (rc == 0) {
     for (int e = 0; e < M4; e++) {
       for (int j = 0; j < r; j++) Kc[j] = Psi0[e + (size_t)M4 * j];
@@ -629,7 +632,7 @@ int oracle_dlr_step_q1(const oracle_problem *p, int r, double *X, double *S, dou
       }
       if (bad) break;
       if (p->dsa) {
-        dsa_correct_q1(p, sig_t, sig_s, phi, phin);  /* R17, R20 */
+        dsa_correct_q1(p, Adsa, sig_s, phi, phin);  /* R17, R20 */
         memcpy(phi, phin, sizeof(double) * M4);
       } else {
         if (omega == 1.0) memcpy(phi, phin, sizeof(double) * M4);
@@ -772,7 +775,7 @@ int oracle_dlr_step_q1(const oracle_problem *p, int r, double *X, double *S, dou
   free(ox); free(oy); free(oz); free(w); free(wq); free(sig_s); free(q); free(B0); free(D);
   free(sig_t); free(idx); free(WLU); free(wpiv); free(beta); free(L0); free(Psi0); free(Psi);
   free(phi); free(phin); free(src); free(Kc); free(in_x); free(in_y); free(Xn); free(R); free(A);
-  free(Lt0); free(P); free(L);
+  free(Lt0); free(P); free(L); free(Adsa);
   return rc;
 }
 
@@ -1042,15 +1045,24 @@ void oracle_dsa_matrix_q1(const oracle_problem *p, const double *sig_t, const do
 /* The DSA step of the Q1 SN step: phi_half += delta,
  * A delta = M_s (phi_half - phi_old), by Jacobi-preconditioned CG as in
  * R17 (dsa_tol, dsa_max_iter).  Returns the CG iterations. */
-static int dsa_correct_q1(const oracle_problem *p, const double *sig_t, const double *sig_s,
-                          const double *phi_old, double *phi_half) {
+/* The Q1 diffusion matrix of the step (its coefficients sig_t and
+ * sig_a = sig_t - sig_s are fixed for the whole source iteration), built
+ * once and handed to every correction; the caller frees it. */
+static double *dsa_matrix_q1_new(const oracle_problem *p, const double *sig_t, const double *sig_s) {
   int Nx = p->nx * p->ny;
   size_t n = 4 * (size_t)Nx;
-  double hx = p->lx / p->nx, hy = p->ly / p->ny;
   double *sig_a = (double *)malloc(sizeof(double) * Nx);
   for (int c = 0; c < Nx; c++) sig_a[c] = sig_t[c] - sig_s[c];
   double *A = (double *)malloc(sizeof(double) * n * n);
   oracle_dsa_matrix_q1(p, sig_t, sig_a, A);
+  free(sig_a);
+  return A;
+}
+static int dsa_correct_q1(const oracle_problem *p, const double *A, const double *sig_s,
+                          const double *phi_old, double *phi_half) {
+  int Nx = p->nx * p->ny;
+  size_t n = 4 * (size_t)Nx;
+  double hx = p->lx / p->nx, hy = p->ly / p->ny;
   double *b = (double *)malloc(sizeof(double) * n);
   double *x = (double *)calloc(n, sizeof(double));
   double *r = (double *)malloc(sizeof(double) * n);
@@ -1085,7 +1097,7 @@ static int dsa_correct_q1(const oracle_problem *p, const double *sig_t, const do
     for (size_t k = 0; k < n; k++) pp[k] = z[k] + beta * pp[k];
   }
   for (size_t k = 0; k < n; k++) phi_half[k] += x[k];
-  free(sig_a); free(A); free(b); free(x); free(r); free(z); free(pp); free(q);
+  free(b); free(x); free(r); free(z); free(pp); free(q);
   return it;
 }
 
