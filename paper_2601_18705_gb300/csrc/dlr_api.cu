@@ -51,9 +51,10 @@ template <typename real> cudaError_t launch_tsgram(const GramJob *, int, int, in
 template <typename real> cudaError_t launch_fill(const FillJob *, int, int, cudaStream_t);
 template <typename rin, typename rout>
 cudaError_t launch_apply(const ApplyJob *, int, int, int, cudaStream_t);
-template <typename real> cudaError_t launch_project(const Inst *, int, int, int, cudaStream_t);
+template <typename real> cudaError_t launch_project(const Inst *, int, int, int, int, cudaStream_t);
 cudaError_t prepare_dense(int);
 cudaError_t prepare_lside(int, int);
+int lside_max_k();
 cudaError_t launch_lside(const Inst *, int, int, int, cudaStream_t);
 int reduce_cluster_cap();
 cudaError_t launch_reduce(const ReduceJob *, int, int, cudaStream_t);
@@ -196,7 +197,7 @@ struct Batch {
   bool aug = false;           // a batch of augmented instances (steps 5-10 on d_insts2)
   Inst *d_insts2 = nullptr;   // the instances of steps 5-10 (rank 2r when augmented)
   int sel_slice_max = 1;      // most angles one CTA of the selection cluster owns
-  bool lside_fused = false;   // step 8 by the one-cluster kernel (pivoted-QR choice, K <= 1024)
+  bool lside_fused = false;   // step 8 by the one-cluster kernel (pivoted-QR choice, K <= lside_max_k())
   bool refl = false;          // some DLR instance has reflective edges (k_reflect.cu)
   bool q1 = false;            // a batch of bilinear-element instances (k_q1.cu)
   int maxRows = 0;            // most rows of X (4 N with Q1 elements)
@@ -1484,7 +1485,7 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   // angle selection: one cluster of kCl CTAs per instance
   b->sel_slice_max = std::max(1, (b->maxK + kCl - 1) / kCl);
   // step 8 in one cluster kernel when the angles fit its shared memory
-  b->lside_fused = b->svd_mode == 0 && b->maxK <= 1024;
+  b->lside_fused = b->svd_mode == 0 && b->maxK <= lside_max_k();
   if (e != cudaSuccess) {
     destroy_batch(b);
     return fail(DLR_ECUDA, "batch table upload failed: %s", cudaGetErrorString(e));
@@ -1596,7 +1597,8 @@ static int enqueue_post(Batch *b) {
     LK(launch_q1_vec<real>(d, n, b->pbmax, st));
     ++b->kcount;  // two kernels
   } else {
-    LK(launch_project<real>(d, n, b->pbmax, b->rmax, st));
+    // mixed precision: the tensor-core kernel, one launch per rank class
+    LKM(launch_project<real>(d, n, b->pbmax, b->rmax, b->rmask, st), sizeof(real) == 4 ? b->rmask : 1);
     LK(launch_reduce(b->r_proj, n, proj_count(b->rmax), st));
     LK(launch_proj_post(d, n, st));
   }

@@ -632,6 +632,311 @@ k_project(const Inst *__restrict__ insts) {
   cluster.sync();
 }
 
+// cp.async helpers (4- and 16-byte copies, zero-filled past src_bytes)
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// ------------------------------------------------------------------
+// step 6 / step 7 projections on the tensor cores (mixed precision).  The
+// same sums as k_project<float>, written as one product per CTA slice of
+// cells, D = X^T B with
+//   B = [X, X_L, X_B, sig_t X, (sigma_s / 4 pi) X, X0]   (r columns each)
+// (X_L(c) = X(c - 1) on cells with ix >= 1, X_B(c) = X(c - nx) on cells
+// with iy >= 1, zero elsewhere) and the vector part D_v = X^T [q, e_L, e_R,
+// e_B, e_T] (e_* the indicators of the four edges' cells).  Per cell this is
+// 6 r^2 + 5 r multiply-adds on 8 r + 12 bytes, too dense for the FP32 pipe
+// to keep up with HBM, so it runs as mma.sync m16n8k8 with TF32 operands
+// and FP32 accumulation: every operand is split as x = hi + lo (both TF32;
+// x - hi is exact in FP32) and a product is summed as hi lo + lo hi + hi hi,
+// whose error (the dropped lo lo and the rounding of lo, about 2^-21 of the
+// product) stays near FP32 rounding.
+//
+// Cells stream through two shared-memory stages of 64 cells filled by
+// 4-byte cp.async (zero-filled past the slice, past rank r and where the
+// shifted neighbour does not exist); a stage keeps column i of X at
+// i * 68 + 4 + k (one cell of halo in front for X_L), of X_B and X0 likewise,
+// so the fragment reads (8 rows x 4 cells per warp) fall in distinct banks.
+// Warp w owns the 8-column tiles w, w + 8, w + 16 of the 6 r columns, for
+// every 16-row tile of X^T, so each entry of the six matrices has exactly
+// one owner; the vector tile is taken by warp w on the chunk's k-step w and
+// the eight warps' vector sums are added in warp order.  FP32 sums: the
+// chunk (in the accumulator), 8 chunks, the slice; FP64 once; then the
+// cluster's CTAs in rank order as in k_project.
+// ------------------------------------------------------------------
+constexpr int kPKC = 64;          // cells per stage (8 k-steps of 8)
+constexpr int kPH = 4;            // front halo: cell base - 1 sits at kPH - 1
+constexpr int kPLD = kPKC + kPH;  // 68 = 4 mod 32
+constexpr int kPV = 8;            // per-cell rows: sig_t, sigma_s/4pi, q, mL, eL, eR, eB, eT
+
+template <int RB>
+constexpr int projtc_stage_floats() { return 3 * RB * kPLD + kPV * kPKC; }
+template <int RB>
+constexpr int projtc_smem_bytes() {
+  return 2 * projtc_stage_floats<RB>() * 4 > (6 * RB * RB + 5 * RB + (kTB / 32) * 8 * RB) * 8
+             ? 2 * projtc_stage_floats<RB>() * 4
+             : (6 * RB * RB + 5 * RB + (kTB / 32) * 8 * RB) * 8;
+}
+
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t y;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
+  return y;
+}
+// x = hi + lo, both TF32
+__device__ __forceinline__ void tf32_split(float x, uint32_t &hi, uint32_t &lo) {
+  hi = tf32_rna(x);
+  lo = tf32_rna(x - __uint_as_float(hi));
+}
+// d += a b (16 x 8 x 8, TF32 in, FP32 accumulate)
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+// the three-term split product: d += a b at about FP32 accuracy
+__device__ __forceinline__ void mma_3xtf32(float (&d)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4],
+                                           float b0, float b1) {
+  uint32_t h0, l0, h1, l1;
+  tf32_split(b0, h0, l0);
+  tf32_split(b1, h1, l1);
+  mma_tf32(d, ah, l0, l1);
+  mma_tf32(d, al, h0, h1);
+  mma_tf32(d, ah, h0, h1);
+}
+
+__device__ __forceinline__ void cp_async4z(float *dst, const float *src, bool ok) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(ok ? 4 : 0)
+               : "memory");
+}
+
+template <int RB>
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kTB, 1)
+k_project_tc(const Inst *__restrict__ insts) {
+  pdl_wait();
+  pdl_trigger();
+  constexpr int NW = kTB / 32;
+  constexpr int MT = RB >= 16 ? RB / 16 : 1;  // 16-row tiles of X^T
+  constexpr int NTM = RB / 8;                 // 8-column tiles of one matrix
+  constexpr int NT = 6 * NTM;                 // matrix tiles (the vector tile apart)
+  constexpr int OWN = (NT + NW - 1) / NW;     // matrix tiles per warp, at most
+  constexpr int SF = projtc_stage_floats<RB>();
+  static_assert(kPKC / 8 == NW, "one vector k-step per warp and chunk");
+  const Inst &I = insts[blockIdx.y];
+  if (rank_class(I.r) != RB) return;
+  const int nblk = I.partial_blocks;
+  if ((int)blockIdx.x >= nblk) return;  // whole clusters
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char dyn[];
+  float *stg = reinterpret_cast<float *>(dyn);
+  const int r = I.r, N = I.N, nx = I.nx, ny = I.ny, t = threadIdx.x;
+  const int lane = t & 31, w = t >> 5, g = lane >> 2, tg = lane & 3;
+  const float *__restrict__ X = as_c<float>(I.X);
+  const float *__restrict__ X0 = as_c<float>(I.X0);
+  const float *__restrict__ sig_t = as_c<float>(I.sig_t);
+  const float *__restrict__ ss4 = as_c<float>(I.ss4);
+  const float *__restrict__ qv = as_c<float>(I.q);
+  double *const partials = I.partials;
+  const int per = (N + nblk - 1) / nblk;
+  const int c0 = min(N, (int)blockIdx.x * per), c1 = min(N, c0 + per);
+  const int nchunk = (c1 - c0 + kPKC - 1) / kPKC;
+
+  // chunk ch into stage ch & 1 (this thread's share of the copies)
+  auto issue = [&](int ch) {
+    float *S = stg + (ch & 1) * SF;
+    const int base = c0 + ch * kPKC;
+    constexpr int HX = kPKC + 1;  // X with the cell in front
+    for (int e = t; e < RB * HX; e += kTB) {
+      const int i = e / HX, h = e - i * HX + kPH - 1;
+      const int c = base - kPH + h;
+      const bool ok = i < r && c >= 0 && c < c1;
+      cp_async4z(S + i * kPLD + h, ok ? X + (size_t)N * i + c : X, ok);
+    }
+    for (int e = t; e < RB * kPKC; e += kTB) {
+      const int i = e / kPKC, k = e - i * kPKC;
+      const int c = base + k;
+      const bool okc = i < r && c < c1, okb = okc && c >= nx;
+      cp_async4z(S + (RB + i) * kPLD + kPH + k, okb ? X + (size_t)N * i + (c - nx) : X, okb);
+      cp_async4z(S + (2 * RB + i) * kPLD + kPH + k, okc ? X0 + (size_t)N * i + c : X0, okc);
+    }
+    float *V = S + 3 * RB * kPLD;
+    for (int k = t; k < kPKC; k += kTB) {
+      const int c = base + k;
+      const bool ok = c < c1;
+      cp_async4z(V + k, ok ? sig_t + c : sig_t, ok);
+      cp_async4z(V + kPKC + k, ok ? ss4 + c : ss4, ok);
+      cp_async4z(V + 2 * kPKC + k, ok ? qv + c : qv, ok);
+      const int iy = ok ? c / nx : 0, ix = ok ? c - iy * nx : 0;
+      V[3 * kPKC + k] = (ok && ix >= 1) ? 1.f : 0.f;
+      V[4 * kPKC + k] = (ok && ix == 0) ? 1.f : 0.f;
+      V[5 * kPKC + k] = (ok && ix == nx - 1) ? 1.f : 0.f;
+      V[6 * kPKC + k] = (ok && iy == 0) ? 1.f : 0.f;
+      V[7 * kPKC + k] = (ok && iy == ny - 1) ? 1.f : 0.f;
+    }
+  };
+
+  float d1[OWN][MT][4], d2[OWN][MT][4], d3[OWN][MT][4];  // chunk, 8 chunks, slice
+  float v1[MT][4], v2[MT][4], v3[MT][4];                 // the vector tile
+#pragma unroll
+  for (int o = 0; o < OWN; ++o)
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) { d1[o][mt][e] = 0.f; d2[o][mt][e] = 0.f; d3[o][mt][e] = 0.f; }
+#pragma unroll
+  for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) { v1[mt][e] = 0.f; v2[mt][e] = 0.f; v3[mt][e] = 0.f; }
+
+  if (nchunk > 0) issue(0);
+  cp_async_commit();
+  for (int ch = 0; ch < nchunk; ++ch) {
+    // the stage of chunk ch + 1 was last read in iteration ch - 1, before
+    // its closing barrier
+    if (ch + 1 < nchunk) issue(ch + 1);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();  // chunk ch has landed, every thread's copies and flags
+    const float *S = stg + (ch & 1) * SF;
+    const float *Xs = S, *XBs = S + RB * kPLD, *X0s = S + 2 * RB * kPLD, *V = S + 3 * RB * kPLD;
+#pragma unroll 2
+    for (int ks = 0; ks < kPKC / 8; ++ks) {
+      const int ka = kPH + 8 * ks + tg, kb = ka + 4;  // stage columns of cells 8 ks + tg (+ 4)
+      const int va = 8 * ks + tg, vb = va + 4;
+      uint32_t ah[MT][4], al[MT][4];
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt) {
+        const int m = 16 * mt + g;
+        tf32_split(Xs[m * kPLD + ka], ah[mt][0], al[mt][0]);
+        tf32_split(Xs[m * kPLD + kb], ah[mt][2], al[mt][2]);
+        if (RB >= 16) {
+          tf32_split(Xs[(m + 8) * kPLD + ka], ah[mt][1], al[mt][1]);
+          tf32_split(Xs[(m + 8) * kPLD + kb], ah[mt][3], al[mt][3]);
+        } else {
+          ah[mt][1] = ah[mt][3] = al[mt][1] = al[mt][3] = 0u;
+        }
+      }
+#pragma unroll
+      for (int o = 0; o < OWN; ++o) {
+        const int nt = w + NW * o;
+        if (nt < NT) {  // warp-uniform
+          const int mat = nt / NTM, col = (nt - mat * NTM) * 8 + g;
+          float b0, b1;
+          if (mat == 1) {  // X_L: the cell in front, masked on the first column
+            b0 = Xs[col * kPLD + ka - 1] * V[3 * kPKC + va];
+            b1 = Xs[col * kPLD + kb - 1] * V[3 * kPKC + vb];
+          } else if (mat == 2) {  // X_B: zero-filled below the first row
+            b0 = XBs[col * kPLD + ka];
+            b1 = XBs[col * kPLD + kb];
+          } else if (mat == 5) {
+            b0 = X0s[col * kPLD + ka];
+            b1 = X0s[col * kPLD + kb];
+          } else {
+            b0 = Xs[col * kPLD + ka];
+            b1 = Xs[col * kPLD + kb];
+            if (mat == 3) { b0 *= V[va]; b1 *= V[vb]; }
+            if (mat == 4) { b0 *= V[kPKC + va]; b1 *= V[kPKC + vb]; }
+          }
+#pragma unroll
+          for (int mt = 0; mt < MT; ++mt) mma_3xtf32(d1[o][mt], ah[mt], al[mt], b0, b1);
+        }
+      }
+      if (ks == w) {  // the vector tile: columns q, eL, eR, eB, eT, 0, 0, 0
+        const int row = g == 0 ? 2 : g + 3;
+        const float b0 = g < 5 ? V[row * kPKC + va] : 0.f;
+        const float b1 = g < 5 ? V[row * kPKC + vb] : 0.f;
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) mma_3xtf32(v1[mt], ah[mt], al[mt], b0, b1);
+      }
+    }
+#pragma unroll
+    for (int o = 0; o < OWN; ++o)
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) { d2[o][mt][e] += d1[o][mt][e]; d1[o][mt][e] = 0.f; }
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) { v2[mt][e] += v1[mt][e]; v1[mt][e] = 0.f; }
+    if ((ch + 1) % 8 == 0) {
+#pragma unroll
+      for (int o = 0; o < OWN; ++o)
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) { d3[o][mt][e] += d2[o][mt][e]; d2[o][mt][e] = 0.f; }
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) { v3[mt][e] += v2[mt][e]; v2[mt][e] = 0.f; }
+    }
+    __syncthreads();  // stage ch & 1 is free again
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  // the CTA partial: each matrix entry from its owner, the vector sums of
+  // the eight warps in warp order
+  double *part_s = reinterpret_cast<double *>(dyn);
+  double *vbuf = part_s + proj_count(r);  // NW x 8 x RB
+  const int rr2 = r * r;
+#pragma unroll
+  for (int o = 0; o < OWN; ++o) {
+    const int nt = w + NW * o;
+    if (nt < NT) {
+      const int mat = nt / NTM, j0 = (nt - mat * NTM) * 8 + 2 * tg;
+      const double sc = mat == 4 ? 4.0 * kPi : 1.0;
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int i = 16 * mt + g + (e >= 2 ? 8 : 0), j = j0 + (e & 1);
+          if (i < r && j < r)
+            part_s[mat * rr2 + i + r * j] =
+                sc * ((double)d1[o][mt][e] + ((double)d2[o][mt][e] + (double)d3[o][mt][e]));
+        }
+    }
+  }
+#pragma unroll
+  for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int i = 16 * mt + g + (e >= 2 ? 8 : 0), v = 2 * tg + (e & 1);
+      if (i < RB) vbuf[(w * 8 + v) * RB + i] = (double)v1[mt][e] + ((double)v2[mt][e] + (double)v3[mt][e]);
+    }
+  __syncthreads();
+  for (int e = t; e < 5 * r; e += kTB) {
+    const int v = e / r, i = e - v * r;
+    double x = 0.0;
+    for (int ww = 0; ww < NW; ++ww) x += vbuf[(ww * 8 + v) * RB + i];
+    part_s[6 * rr2 + e] = x;
+  }
+  cluster.sync();
+  const int rank = (int)cluster.block_rank();
+  const int cnt = proj_count(r), share = (cnt + kCl - 1) / kCl;
+  double *out = partials + (size_t)(blockIdx.x / kCl) * cnt;
+  for (int e = rank * share + t; e < min(cnt, (rank + 1) * share); e += kTB) {
+    double v = 0.0;
+#pragma unroll
+    for (int q = 0; q < kCl; ++q) v += cluster.map_shared_rank(part_s, q)[e];
+    out[e] = v;
+  }
+  cluster.sync();
+}
+
 // Sum of per-block partials: out[e] = scale * sum_b part[b*stride + e].
 __global__ void __launch_bounds__(256) k_reduce(const ReduceJob *__restrict__ jobs) {
   pdl_wait();
@@ -730,20 +1035,6 @@ constexpr int kGR = 128, kGS = 4;
 constexpr int gram32_smem_bytes() { return kGS * 32 * kGR * 4; }
 // position of (column c, row q) of a stage
 __device__ __forceinline__ int g32_at(int c, int q) { return c * kGR + ((q + 4 * ((c >> 2) & 7)) & (kGR - 1)); }
-
-__device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
-               "l"(src), "r"(src_bytes)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async4(void *dst, const void *src, int src_bytes) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
-               "l"(src), "r"(src_bytes)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kTB, 2) k_gram32(const GramJob *__restrict__ jobs) {
   pdl_wait();
@@ -922,9 +1213,18 @@ cudaError_t launch_apply(const ApplyJob *d_jobs, int n, int maxm, int rmask, cud
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
+// FP64: k_project; mixed precision: k_project_tc, one launch per rank
+// class in rmask
 template <typename real>
-cudaError_t launch_project(const Inst *d, int n, int maxblocks, int rmax, cudaStream_t st) {
-  return launch_pdl(k_project<real>, dim3(maxblocks, n), dim3(kTB), proj_smem_bytes(rmax, sizeof(real)), st, d);
+cudaError_t launch_project(const Inst *d, int n, int maxblocks, int rmax, int rmask, cudaStream_t st) {
+  if (sizeof(real) == 8)
+    return launch_pdl(k_project<double>, dim3(maxblocks, n), dim3(kTB), proj_smem_bytes(rmax, 8), st, d);
+  const dim3 g(maxblocks, n);
+#define L_(RB) (e = launch_pdl(k_project_tc<RB>, g, dim3(kTB), projtc_smem_bytes<RB>(), st, d))
+  cudaError_t e = cudaSuccess;
+  DLR_RB_DISPATCH(rmask, L_);
+#undef L_
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t prepare_dense(int rmax);
@@ -956,7 +1256,7 @@ int reduce_cluster_cap() {
   c = std::min(c, cap((const void *)k_tsgram<double, 0>, 0));
   c = std::min(c, cap((const void *)k_tsgram<double, 1>, 0));
   if (prepare_dense(kMaxRank) == cudaSuccess) {
-    c = std::min(c, cap((const void *)k_project<float>, proj_smem_bytes(kMaxRank, 4)));
+    c = std::min(c, cap((const void *)k_project_tc<32>, projtc_smem_bytes<32>()));
     c = std::min(c, cap((const void *)k_project<double>, proj_smem_bytes(kMaxRank, 8)));
   }
   return c;
@@ -964,8 +1264,14 @@ int reduce_cluster_cap() {
 
 // Kernel attributes, set before any launch is captured into a graph.
 cudaError_t prepare_dense(int rmax) {
-  cudaError_t e = cudaFuncSetAttribute(k_project<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       proj_smem_bytes(rmax, 4));
+  cudaError_t e = cudaFuncSetAttribute(k_project_tc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       projtc_smem_bytes<8>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_project_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             projtc_smem_bytes<16>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_project_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             projtc_smem_bytes<32>());
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_project<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               proj_smem_bytes(rmax, 8));
@@ -993,8 +1299,8 @@ template cudaError_t launch_fill<float>(const FillJob *, int, int, cudaStream_t)
 template cudaError_t launch_fill<double>(const FillJob *, int, int, cudaStream_t);
 template cudaError_t launch_apply<float, float>(const ApplyJob *, int, int, int, cudaStream_t);
 template cudaError_t launch_apply<double, double>(const ApplyJob *, int, int, int, cudaStream_t);
-template cudaError_t launch_project<float>(const Inst *, int, int, int, cudaStream_t);
-template cudaError_t launch_project<double>(const Inst *, int, int, int, cudaStream_t);
+template cudaError_t launch_project<float>(const Inst *, int, int, int, int, cudaStream_t);
+template cudaError_t launch_project<double>(const Inst *, int, int, int, int, cudaStream_t);
 template cudaError_t launch_tupdate<float>(const Inst *, int, int, int, cudaStream_t);
 template cudaError_t launch_tupdate<double>(const Inst *, int, int, int, cudaStream_t);
 

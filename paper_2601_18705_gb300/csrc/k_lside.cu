@@ -15,7 +15,11 @@
 
 namespace dlr {
 
-constexpr int kLsideMaxK = 1024;
+// Step 8 runs in one cluster for up to this many angles: the rows of M and
+// Q (2 x 256 x 32 FP64 per CTA at 2048 angles and rank 32) stay in shared
+// memory.
+constexpr int kLsideMaxK = 2048;
+int lside_max_k() { return kLsideMaxK; }
 
 // out[e] = sum over the cluster's CTAs (rank order) of part[e], e < n, in
 // every CTA
