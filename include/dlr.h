@@ -235,7 +235,9 @@ int dlr_step_batch(dlr_handle *const *hs, int32_t n, int32_t nsteps);
  * are halved while the longest is longer than threshold x the average load
  * of one resident CTA) -- are timed on the device, each as reps
  * source-iteration launches of exactly iters iterations on the state the
- * next step starts from, and the fastest is kept for this handle set and
+ * next step starts from (iters near a step's own count: a launch's fixed
+ * cost, such as the grouped kernel's last sweep, then weighs as in a step),
+ * and the fastest is kept for this handle set and
  * for later batches of the same shape (sorted nx, ny, r, precision).
  * Nothing the next step reads is changed.  *chosen (may be NULL) receives
  * the chosen threshold (0 = no split; dlr_stats.sweep_grouped tells the

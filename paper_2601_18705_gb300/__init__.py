@@ -274,11 +274,14 @@ def step_batch(solvers, nsteps: int = 1) -> None:
 AUTOTUNE_CANDIDATES = (0.0, 2.0, 1.0, 0.5)  # splitting thresholds, in dlr_autotune's order
 
 
-def autotune(solvers, *, iters: int = 2, reps: int = 3) -> dict:
+def autotune(solvers, *, iters: int = 12, reps: int = 3) -> dict:
     """Autotunes the sweep work plan of the batch `solvers` (the same list
     later passed to step_batch; one solver for Solver.step): times each
     candidate -- the per-angle and the grouped source-iteration kernel, each
     with every splitting threshold -- on the device and keeps the fastest.
+    Each timed launch runs `iters` source iterations: a count near a step's
+    own, so that the fixed cost of a launch (the grouped kernel's set-up and
+    its last sweep, which writes psi) weighs as it does in a step.
     Returns {"split": chosen threshold (0 = no split), "grouped": whether
     the grouped kernel was chosen, "ms": {threshold: ms per launch} of the
     per-angle kernel, "ms_grouped": the same for the grouped kernel (-1:

@@ -657,58 +657,69 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // e_B, e_T] (e_* the indicators of the four edges' cells).  Per cell this is
 // 6 r^2 + 5 r multiply-adds on 8 r + 12 bytes, too dense for the FP32 pipe
 // to keep up with HBM, so it runs as mma.sync m16n8k8 with TF32 operands
-// and FP32 accumulation: every operand is split as x = hi + lo (both TF32;
-// x - hi is exact in FP32) and a product is summed as hi lo + lo hi + hi hi,
-// whose error (the dropped lo lo and the rounding of lo, about 2^-21 of the
-// product) stays near FP32 rounding.
+// and FP32 accumulation: every operand is split as x = hi + lo, hi = x
+// rounded to TF32 (to nearest, ties away, by integer arithmetic on the
+// bits), lo = x - hi (exact in FP32, of which the tensor core reads the TF32
+// part), and a product is summed as hi lo + lo hi + hi hi; the error (the
+// dropped lo lo and the truncation of lo, at most about 2^-20 of the
+// product and of either sign) stays near FP32 rounding.
 //
 // Cells stream through two shared-memory stages of 64 cells filled by
-// 4-byte cp.async (zero-filled past the slice, past rank r and where the
+// cp.async (16-byte copies when the columns and rows are 4-cell aligned,
+// else 4-byte ones; zero-filled past the slice, past rank r and where the
 // shifted neighbour does not exist); a stage keeps column i of X at
 // i * 68 + 4 + k (one cell of halo in front for X_L), of X_B and X0 likewise,
 // so the fragment reads (8 rows x 4 cells per warp) fall in distinct banks.
-// Warp w owns the 8-column tiles w, w + 8, w + 16 of the 6 r columns, for
-// every 16-row tile of X^T, so each entry of the six matrices has exactly
-// one owner; the vector tile is taken by warp w on the chunk's k-step w and
-// the eight warps' vector sums are added in warp order.  FP32 sums: the
-// chunk (in the accumulator), 8 chunks, the slice; FP64 once; then the
-// cluster's CTAs in rank order as in k_project.
+// Once a stage has landed, the X^T fragments of its 8 k-steps are split
+// into TF32 parts once for the CTA and stored in fragment order (two
+// 16-byte reads per fragment).  With 16 warps, warp w takes the 16-row tile
+// mt = w / (16 / MT) of X^T and the 8-column tiles w % (16 / MT) + j 16 / MT
+// of B, so each entry of the six matrices has one owner; the vector tile of
+// k-step ks and row tile mt goes to warp 8 mt + ks, and the eight k-step
+// sums of a row tile are added in k-step order.  FP32 sums: the chunk (in
+// the accumulator), 8 chunks, the slice; FP64 once; then the cluster's CTAs
+// in rank order as in k_project.
 // ------------------------------------------------------------------
+constexpr int kPT = 512;          // threads of k_project_tc (16 warps)
 constexpr int kPKC = 64;          // cells per stage (8 k-steps of 8)
 constexpr int kPH = 4;            // front halo: cell base - 1 sits at kPH - 1
 constexpr int kPLD = kPKC + kPH;  // 68 = 4 mod 32
-constexpr int kPV = 8;            // per-cell rows: sig_t, sigma_s/4pi, q, mL, eL, eR, eB, eT
+constexpr int kPV = 9;            // per-cell rows: sig_t, sigma_s/4pi, q, mL, eL, eR, eB, eT, 1
 
+template <int RB>
+constexpr int projtc_mt() { return RB >= 16 ? RB / 16 : 1; }
 template <int RB>
 constexpr int projtc_stage_floats() { return 3 * RB * kPLD + kPV * kPKC; }
+// two stages, then the split X^T fragments (MT x 8 k-steps x 32 lanes x 8)
+template <int RB>
+constexpr int projtc_work_floats() { return 2 * projtc_stage_floats<RB>() + projtc_mt<RB>() * 8 * 32 * 8; }
 template <int RB>
 constexpr int projtc_smem_bytes() {
-  return 2 * projtc_stage_floats<RB>() * 4 > (6 * RB * RB + 5 * RB + (kTB / 32) * 8 * RB) * 8
-             ? 2 * projtc_stage_floats<RB>() * 4
-             : (6 * RB * RB + 5 * RB + (kTB / 32) * 8 * RB) * 8;
+  return projtc_work_floats<RB>() * 4 > (6 * RB * RB + 5 * RB + (kPT / 32) * 8 * RB) * 8
+             ? projtc_work_floats<RB>() * 4
+             : (6 * RB * RB + 5 * RB + (kPT / 32) * 8 * RB) * 8;
 }
 
-__device__ __forceinline__ uint32_t tf32_rna(float x) {
-  uint32_t y;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
-  return y;
-}
-// x = hi + lo, both TF32
+// x = hi + lo: hi is x rounded to TF32 (10 fraction bits; adding half an
+// ulp to the magnitude's bit pattern and clearing the 13 low bits rounds to
+// nearest with ties away from zero, carrying into the exponent where
+// needed; x is finite), lo = x - hi exactly, handed to the tensor core as
+// FP32 bits (it reads the TF32 part)
 __device__ __forceinline__ void tf32_split(float x, uint32_t &hi, uint32_t &lo) {
-  hi = tf32_rna(x);
-  lo = tf32_rna(x - __uint_as_float(hi));
+  hi = (__float_as_uint(x) + 0x1000u) & 0xffffe000u;
+  lo = __float_as_uint(x - __uint_as_float(hi));
 }
-// d += a b (16 x 8 x 8, TF32 in, FP32 accumulate)
-__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
+// d += a b (16 x 8 x 8, TF32 in, FP32 accumulate); not volatile, so the
+// compiler may interleave the products of independent tiles
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint4 &a, uint32_t b0, uint32_t b1) {
+  asm(
       "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
       "{%0, %1, %2, %3};"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+      : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
 }
 // the three-term split product: d += a b at about FP32 accuracy
-__device__ __forceinline__ void mma_3xtf32(float (&d)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4],
-                                           float b0, float b1) {
+__device__ __forceinline__ void mma_3xtf32(float (&d)[4], const uint4 &ah, const uint4 &al, float b0, float b1) {
   uint32_t h0, l0, h1, l1;
   tf32_split(b0, h0, l0);
   tf32_split(b1, h1, l1);
@@ -717,40 +728,46 @@ __device__ __forceinline__ void mma_3xtf32(float (&d)[4], const uint32_t (&ah)[4
   mma_tf32(d, ah, h0, h1);
 }
 
-__device__ __forceinline__ void cp_async4z(float *dst, const float *src, bool ok) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
-               "l"(src), "r"(ok ? 4 : 0)
-               : "memory");
-}
-
 template <int RB>
-__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kTB, 1)
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kPT, 1)
 k_project_tc(const Inst *__restrict__ insts) {
   pdl_wait();
   pdl_trigger();
-  constexpr int NW = kTB / 32;
-  constexpr int MT = RB >= 16 ? RB / 16 : 1;  // 16-row tiles of X^T
+  constexpr int NW = kPT / 32;
+  constexpr int MT = projtc_mt<RB>();         // 16-row tiles of X^T
   constexpr int NTM = RB / 8;                 // 8-column tiles of one matrix
   constexpr int NT = 6 * NTM;                 // matrix tiles (the vector tile apart)
-  constexpr int OWN = (NT + NW - 1) / NW;     // matrix tiles per warp, at most
+  constexpr int WPM = NW / MT;                // warps per row tile
+  constexpr int OWN = (NT + WPM - 1) / WPM;   // matrix tiles per warp, at most
   constexpr int SF = projtc_stage_floats<RB>();
-  static_assert(kPKC / 8 == NW, "one vector k-step per warp and chunk");
+  static_assert(kPKC / 8 == 8 && NW == 16, "8 k-steps per chunk, 16 warps");
   const Inst &I = insts[blockIdx.y];
   if (rank_class(I.r) != RB) return;
   const int nblk = I.partial_blocks;
   if ((int)blockIdx.x >= nblk) return;  // whole clusters
   cg::cluster_group cluster = cg::this_cluster();
-  extern __shared__ __align__(16) unsigned char dyn[];
+  extern __shared__ __align__(32) unsigned char dyn[];
   float *stg = reinterpret_cast<float *>(dyn);
+  // split X^T fragments of the current chunk: hi parts, then lo parts
+  uint4 *AFh = reinterpret_cast<uint4 *>(stg + 2 * SF);
+  uint4 *AFl = AFh + MT * 8 * 32;
   const int r = I.r, N = I.N, nx = I.nx, ny = I.ny, t = threadIdx.x;
   const int lane = t & 31, w = t >> 5, g = lane >> 2, tg = lane & 3;
+  const int mt = w / WPM;      // this warp's row tile
+  const int wt = w - mt * WPM;  // and its first column tile
+  const bool vown = w < 8 * MT;  // the vector tile of k-step w % 8, row tile w / 8
   const float *__restrict__ X = as_c<float>(I.X);
   const float *__restrict__ X0 = as_c<float>(I.X0);
   const float *__restrict__ sig_t = as_c<float>(I.sig_t);
   const float *__restrict__ ss4 = as_c<float>(I.ss4);
   const float *__restrict__ qv = as_c<float>(I.q);
   double *const partials = I.partials;
-  const int per = (N + nblk - 1) / nblk;
+  // slices of whole 4-cell groups: with N and nx multiples of 4 every
+  // 16-byte copy is either wholly inside or wholly outside the data
+  const bool vec = (N & 3) == 0 && (nx & 3) == 0 && ((reinterpret_cast<uintptr_t>(X) & 15) == 0) &&
+                   ((reinterpret_cast<uintptr_t>(X0) & 15) == 0) && ((reinterpret_cast<uintptr_t>(sig_t) & 15) == 0) &&
+                   ((reinterpret_cast<uintptr_t>(ss4) & 15) == 0) && ((reinterpret_cast<uintptr_t>(qv) & 15) == 0);
+  const int per = ((N + nblk - 1) / nblk + 3) & ~3;
   const int c0 = min(N, (int)blockIdx.x * per), c1 = min(N, c0 + per);
   const int nchunk = (c1 - c0 + kPKC - 1) / kPKC;
 
@@ -758,48 +775,86 @@ k_project_tc(const Inst *__restrict__ insts) {
   auto issue = [&](int ch) {
     float *S = stg + (ch & 1) * SF;
     const int base = c0 + ch * kPKC;
-    constexpr int HX = kPKC + 1;  // X with the cell in front
-    for (int e = t; e < RB * HX; e += kTB) {
-      const int i = e / HX, h = e - i * HX + kPH - 1;
-      const int c = base - kPH + h;
-      const bool ok = i < r && c >= 0 && c < c1;
-      cp_async4z(S + i * kPLD + h, ok ? X + (size_t)N * i + c : X, ok);
+    if (vec) {
+      constexpr int QX = (kPKC + kPH) / 4;  // X with the 4 cells in front
+      for (int e = t; e < RB * QX; e += kPT) {
+        const int i = e / QX, h = 4 * (e - i * QX);
+        const int c = base - kPH + h;
+        const bool ok = i < r && c >= 0 && c < c1;
+        cp_async16(S + i * kPLD + h, ok ? X + (size_t)N * i + c : X, ok ? 16 : 0);
+      }
+      constexpr int QK = kPKC / 4;
+      for (int e = t; e < RB * QK; e += kPT) {
+        const int i = e / QK, k = 4 * (e - i * QK);
+        const int c = base + k;
+        const bool okc = i < r && c < c1, okb = okc && c >= nx;
+        cp_async16(S + (RB + i) * kPLD + kPH + k, okb ? X + (size_t)N * i + (c - nx) : X, okb ? 16 : 0);
+        cp_async16(S + (2 * RB + i) * kPLD + kPH + k, okc ? X0 + (size_t)N * i + c : X0, okc ? 16 : 0);
+      }
+      float *V = S + 3 * RB * kPLD;
+      if (t < 3 * QK) {
+        const int row = t / QK, k = 4 * (t - row * QK), c = base + k;
+        const float *src = row == 0 ? sig_t : row == 1 ? ss4 : qv;
+        cp_async16(V + row * kPKC + k, c < c1 ? src + c : src, c < c1 ? 16 : 0);
+      }
+    } else {
+      constexpr int HX = kPKC + 1;  // X with the cell in front
+      for (int e = t; e < RB * HX; e += kPT) {
+        const int i = e / HX, h = e - i * HX + kPH - 1;
+        const int c = base - kPH + h;
+        const bool ok = i < r && c >= 0 && c < c1;
+        cp_async4(S + i * kPLD + h, ok ? X + (size_t)N * i + c : X, ok ? 4 : 0);
+      }
+      for (int e = t; e < RB * kPKC; e += kPT) {
+        const int i = e / kPKC, k = e - i * kPKC;
+        const int c = base + k;
+        const bool okc = i < r && c < c1, okb = okc && c >= nx;
+        cp_async4(S + (RB + i) * kPLD + kPH + k, okb ? X + (size_t)N * i + (c - nx) : X, okb ? 4 : 0);
+        cp_async4(S + (2 * RB + i) * kPLD + kPH + k, okc ? X0 + (size_t)N * i + c : X0, okc ? 4 : 0);
+      }
+      float *V = S + 3 * RB * kPLD;
+      if (t < 3 * kPKC) {
+        const int row = t / kPKC, k = t - row * kPKC, c = base + k;
+        const float *src = row == 0 ? sig_t : row == 1 ? ss4 : qv;
+        cp_async4(V + row * kPKC + k, c < c1 ? src + c : src, c < c1 ? 4 : 0);
+      }
     }
-    for (int e = t; e < RB * kPKC; e += kTB) {
-      const int i = e / kPKC, k = e - i * kPKC;
-      const int c = base + k;
-      const bool okc = i < r && c < c1, okb = okc && c >= nx;
-      cp_async4z(S + (RB + i) * kPLD + kPH + k, okb ? X + (size_t)N * i + (c - nx) : X, okb);
-      cp_async4z(S + (2 * RB + i) * kPLD + kPH + k, okc ? X0 + (size_t)N * i + c : X0, okc);
-    }
-    float *V = S + 3 * RB * kPLD;
-    for (int k = t; k < kPKC; k += kTB) {
-      const int c = base + k;
+    if (t >= kPT - kPKC) {  // the masks (plain stores; the stage is not read before its barrier)
+      float *V = S + 3 * RB * kPLD;
+      const int k = t - (kPT - kPKC), c = base + k;
       const bool ok = c < c1;
-      cp_async4z(V + k, ok ? sig_t + c : sig_t, ok);
-      cp_async4z(V + kPKC + k, ok ? ss4 + c : ss4, ok);
-      cp_async4z(V + 2 * kPKC + k, ok ? qv + c : qv, ok);
       const int iy = ok ? c / nx : 0, ix = ok ? c - iy * nx : 0;
       V[3 * kPKC + k] = (ok && ix >= 1) ? 1.f : 0.f;
       V[4 * kPKC + k] = (ok && ix == 0) ? 1.f : 0.f;
       V[5 * kPKC + k] = (ok && ix == nx - 1) ? 1.f : 0.f;
       V[6 * kPKC + k] = (ok && iy == 0) ? 1.f : 0.f;
       V[7 * kPKC + k] = (ok && iy == ny - 1) ? 1.f : 0.f;
+      V[8 * kPKC + k] = 1.f;
     }
   };
 
-  float d1[OWN][MT][4], d2[OWN][MT][4], d3[OWN][MT][4];  // chunk, 8 chunks, slice
-  float v1[MT][4], v2[MT][4], v3[MT][4];                 // the vector tile
+  // this warp's column tiles: operand rows (stage offsets) and scale rows
+  int boff[OWN], soff[OWN], dmat[OWN], dcol[OWN];
+#pragma unroll
+  for (int o = 0; o < OWN; ++o) {
+    const int nt = wt + WPM * o;
+    const int mat = nt < NT ? nt / NTM : 0, col = nt < NT ? (nt - mat * NTM) * 8 + g : 0;
+    dmat[o] = nt < NT ? mat : -1;
+    dcol[o] = (nt - mat * NTM) * 8 + 2 * tg;
+    // X, X_L (one cell back), X_B, sig_t X, sigma_s X / 4 pi, X0
+    boff[o] = (mat == 2 ? RB + col : mat == 5 ? 2 * RB + col : col) * kPLD + (mat == 1 ? -1 : 0);
+    const int srow = mat == 1 ? 3 : mat == 3 ? 0 : mat == 4 ? 1 : 8;
+    soff[o] = 3 * RB * kPLD + srow * kPKC;
+  }
+
+  float d1[OWN][4], d2[OWN][4], d3[OWN][4];  // chunk, 8 chunks, slice
+  float v1[4], v2[4], v3[4];                 // the vector tile
 #pragma unroll
   for (int o = 0; o < OWN; ++o)
 #pragma unroll
-    for (int mt = 0; mt < MT; ++mt)
+    for (int e = 0; e < 4; ++e) { d1[o][e] = 0.f; d2[o][e] = 0.f; d3[o][e] = 0.f; }
 #pragma unroll
-      for (int e = 0; e < 4; ++e) { d1[o][mt][e] = 0.f; d2[o][mt][e] = 0.f; d3[o][mt][e] = 0.f; }
-#pragma unroll
-  for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) { v1[mt][e] = 0.f; v2[mt][e] = 0.f; v3[mt][e] = 0.f; }
+  for (int e = 0; e < 4; ++e) { v1[e] = 0.f; v2[e] = 0.f; v3[e] = 0.f; }
 
   if (nchunk > 0) issue(0);
   cp_async_commit();
@@ -811,124 +866,110 @@ k_project_tc(const Inst *__restrict__ insts) {
     cp_async_wait<1>();
     __syncthreads();  // chunk ch has landed, every thread's copies and flags
     const float *S = stg + (ch & 1) * SF;
-    const float *Xs = S, *XBs = S + RB * kPLD, *X0s = S + 2 * RB * kPLD, *V = S + 3 * RB * kPLD;
-#pragma unroll 2
-    for (int ks = 0; ks < kPKC / 8; ++ks) {
-      const int ka = kPH + 8 * ks + tg, kb = ka + 4;  // stage columns of cells 8 ks + tg (+ 4)
-      const int va = 8 * ks + tg, vb = va + 4;
-      uint32_t ah[MT][4], al[MT][4];
-#pragma unroll
-      for (int mt = 0; mt < MT; ++mt) {
-        const int m = 16 * mt + g;
-        tf32_split(Xs[m * kPLD + ka], ah[mt][0], al[mt][0]);
-        tf32_split(Xs[m * kPLD + kb], ah[mt][2], al[mt][2]);
-        if (RB >= 16) {
-          tf32_split(Xs[(m + 8) * kPLD + ka], ah[mt][1], al[mt][1]);
-          tf32_split(Xs[(m + 8) * kPLD + kb], ah[mt][3], al[mt][3]);
-        } else {
-          ah[mt][1] = ah[mt][3] = al[mt][1] = al[mt][3] = 0u;
-        }
+    // the X^T fragments of the chunk, split once: entry (m, ks, lane) holds
+    // hi and lo of rows 16 m + g (+ 8), cells 8 ks + tg (+ 4)
+    for (int e = t; e < MT * 8 * 32; e += kPT) {
+      const int m = e >> 8, ks = (e >> 5) & 7, ln = e & 31;
+      const int row = 16 * m + (ln >> 2), k = kPH + 8 * ks + (ln & 3);
+      uint32_t h[4], l[4];
+      tf32_split(S[row * kPLD + k], h[0], l[0]);
+      tf32_split(S[row * kPLD + k + 4], h[2], l[2]);
+      if (RB >= 16) {
+        tf32_split(S[(row + 8) * kPLD + k], h[1], l[1]);
+        tf32_split(S[(row + 8) * kPLD + k + 4], h[3], l[3]);
+      } else {
+        h[1] = h[3] = l[1] = l[3] = 0u;
       }
+      AFh[e] = make_uint4(h[0], h[1], h[2], h[3]);
+      AFl[e] = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < 8; ++ks) {
+      const uint4 ah = AFh[(mt * 8 + ks) * 32 + lane], al = AFl[(mt * 8 + ks) * 32 + lane];
+      const int ka = kPH + 8 * ks + tg, va = 8 * ks + tg;
+      // the tiles' operands first, then the three products tile by tile
+      // in rounds, so that no product waits on the one just issued
+      uint32_t bh[OWN][2], bl[OWN][2];
 #pragma unroll
       for (int o = 0; o < OWN; ++o) {
-        const int nt = w + NW * o;
-        if (nt < NT) {  // warp-uniform
-          const int mat = nt / NTM, col = (nt - mat * NTM) * 8 + g;
-          float b0, b1;
-          if (mat == 1) {  // X_L: the cell in front, masked on the first column
-            b0 = Xs[col * kPLD + ka - 1] * V[3 * kPKC + va];
-            b1 = Xs[col * kPLD + kb - 1] * V[3 * kPKC + vb];
-          } else if (mat == 2) {  // X_B: zero-filled below the first row
-            b0 = XBs[col * kPLD + ka];
-            b1 = XBs[col * kPLD + kb];
-          } else if (mat == 5) {
-            b0 = X0s[col * kPLD + ka];
-            b1 = X0s[col * kPLD + kb];
-          } else {
-            b0 = Xs[col * kPLD + ka];
-            b1 = Xs[col * kPLD + kb];
-            if (mat == 3) { b0 *= V[va]; b1 *= V[vb]; }
-            if (mat == 4) { b0 *= V[kPKC + va]; b1 *= V[kPKC + vb]; }
-          }
-#pragma unroll
-          for (int mt = 0; mt < MT; ++mt) mma_3xtf32(d1[o][mt], ah[mt], al[mt], b0, b1);
-        }
+        const float b0 = S[boff[o] + ka] * S[soff[o] + va];
+        const float b1 = S[boff[o] + ka + 4] * S[soff[o] + va + 4];
+        tf32_split(b0, bh[o][0], bl[o][0]);
+        tf32_split(b1, bh[o][1], bl[o][1]);
       }
-      if (ks == w) {  // the vector tile: columns q, eL, eR, eB, eT, 0, 0, 0
-        const int row = g == 0 ? 2 : g + 3;
-        const float b0 = g < 5 ? V[row * kPKC + va] : 0.f;
-        const float b1 = g < 5 ? V[row * kPKC + vb] : 0.f;
 #pragma unroll
-        for (int mt = 0; mt < MT; ++mt) mma_3xtf32(v1[mt], ah[mt], al[mt], b0, b1);
+      for (int o = 0; o < OWN; ++o)
+        if (dmat[o] >= 0) mma_tf32(d1[o], ah, bl[o][0], bl[o][1]);  // warp-uniform
+#pragma unroll
+      for (int o = 0; o < OWN; ++o)
+        if (dmat[o] >= 0) mma_tf32(d1[o], al, bh[o][0], bh[o][1]);
+#pragma unroll
+      for (int o = 0; o < OWN; ++o)
+        if (dmat[o] >= 0) mma_tf32(d1[o], ah, bh[o][0], bh[o][1]);
+      if (vown && ks == (w & 7)) {  // the vector tile: columns q, eL, eR, eB, eT, 0, 0, 0
+        const int vrow = g == 0 ? 2 : g + 3;
+        const float *V = S + 3 * RB * kPLD;
+        const float b0 = g < 5 ? V[vrow * kPKC + va] : 0.f;
+        const float b1 = g < 5 ? V[vrow * kPKC + va + 4] : 0.f;
+        mma_3xtf32(v1, ah, al, b0, b1);
       }
     }
 #pragma unroll
     for (int o = 0; o < OWN; ++o)
 #pragma unroll
-      for (int mt = 0; mt < MT; ++mt)
+      for (int e = 0; e < 4; ++e) { d2[o][e] += d1[o][e]; d1[o][e] = 0.f; }
 #pragma unroll
-        for (int e = 0; e < 4; ++e) { d2[o][mt][e] += d1[o][mt][e]; d1[o][mt][e] = 0.f; }
-#pragma unroll
-    for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) { v2[mt][e] += v1[mt][e]; v1[mt][e] = 0.f; }
+    for (int e = 0; e < 4; ++e) { v2[e] += v1[e]; v1[e] = 0.f; }
     if ((ch + 1) % 8 == 0) {
 #pragma unroll
       for (int o = 0; o < OWN; ++o)
 #pragma unroll
-        for (int mt = 0; mt < MT; ++mt)
+        for (int e = 0; e < 4; ++e) { d3[o][e] += d2[o][e]; d2[o][e] = 0.f; }
 #pragma unroll
-          for (int e = 0; e < 4; ++e) { d3[o][mt][e] += d2[o][mt][e]; d2[o][mt][e] = 0.f; }
-#pragma unroll
-      for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) { v3[mt][e] += v2[mt][e]; v2[mt][e] = 0.f; }
+      for (int e = 0; e < 4; ++e) { v3[e] += v2[e]; v2[e] = 0.f; }
     }
-    __syncthreads();  // stage ch & 1 is free again
+    __syncthreads();  // stage ch & 1 and the fragments are free again
   }
   cp_async_wait<0>();
   __syncthreads();
   // the CTA partial: each matrix entry from its owner, the vector sums of
-  // the eight warps in warp order
+  // the k-steps of a row tile in k-step order
   double *part_s = reinterpret_cast<double *>(dyn);
   double *vbuf = part_s + proj_count(r);  // NW x 8 x RB
   const int rr2 = r * r;
 #pragma unroll
   for (int o = 0; o < OWN; ++o) {
-    const int nt = w + NW * o;
-    if (nt < NT) {
-      const int mat = nt / NTM, j0 = (nt - mat * NTM) * 8 + 2 * tg;
+    if (dmat[o] >= 0) {
+      const int mat = dmat[o];
       const double sc = mat == 4 ? 4.0 * kPi : 1.0;
 #pragma unroll
-      for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int i = 16 * mt + g + (e >= 2 ? 8 : 0), j = j0 + (e & 1);
-          if (i < r && j < r)
-            part_s[mat * rr2 + i + r * j] =
-                sc * ((double)d1[o][mt][e] + ((double)d2[o][mt][e] + (double)d3[o][mt][e]));
-        }
+      for (int e = 0; e < 4; ++e) {
+        const int i = 16 * mt + g + (e >= 2 ? 8 : 0), j = dcol[o] + (e & 1);
+        if (i < r && j < r)
+          part_s[mat * rr2 + i + r * j] = sc * ((double)d1[o][e] + ((double)d2[o][e] + (double)d3[o][e]));
+      }
     }
   }
-#pragma unroll
-  for (int mt = 0; mt < MT; ++mt)
+  if (vown) {
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      const int i = 16 * mt + g + (e >= 2 ? 8 : 0), v = 2 * tg + (e & 1);
-      if (i < RB) vbuf[(w * 8 + v) * RB + i] = (double)v1[mt][e] + ((double)v2[mt][e] + (double)v3[mt][e]);
+      const int i = 16 * (w >> 3) + g + (e >= 2 ? 8 : 0), v = 2 * tg + (e & 1);
+      if (i < RB) vbuf[(w * 8 + v) * RB + i] = (double)v1[e] + ((double)v2[e] + (double)v3[e]);
     }
+  }
   __syncthreads();
-  for (int e = t; e < 5 * r; e += kTB) {
-    const int v = e / r, i = e - v * r;
+  for (int e = t; e < 5 * r; e += kPT) {
+    const int v = e / r, i = e - v * r, m = i >> 4;
     double x = 0.0;
-    for (int ww = 0; ww < NW; ++ww) x += vbuf[(ww * 8 + v) * RB + i];
+    for (int ks = 0; ks < 8; ++ks) x += vbuf[((8 * m + ks) * 8 + v) * RB + i];
     part_s[6 * rr2 + e] = x;
   }
   cluster.sync();
   const int rank = (int)cluster.block_rank();
   const int cnt = proj_count(r), share = (cnt + kCl - 1) / kCl;
   double *out = partials + (size_t)(blockIdx.x / kCl) * cnt;
-  for (int e = rank * share + t; e < min(cnt, (rank + 1) * share); e += kTB) {
+  for (int e = rank * share + t; e < min(cnt, (rank + 1) * share); e += kPT) {
     double v = 0.0;
 #pragma unroll
     for (int q = 0; q < kCl; ++q) v += cluster.map_shared_rank(part_s, q)[e];
@@ -1220,7 +1261,7 @@ cudaError_t launch_project(const Inst *d, int n, int maxblocks, int rmax, int rm
   if (sizeof(real) == 8)
     return launch_pdl(k_project<double>, dim3(maxblocks, n), dim3(kTB), proj_smem_bytes(rmax, 8), st, d);
   const dim3 g(maxblocks, n);
-#define L_(RB) (e = launch_pdl(k_project_tc<RB>, g, dim3(kTB), projtc_smem_bytes<RB>(), st, d))
+#define L_(RB) (e = launch_pdl(k_project_tc<RB>, g, dim3(kPT), projtc_smem_bytes<RB>(), st, d))
   cudaError_t e = cudaSuccess;
   DLR_RB_DISPATCH(rmask, L_);
 #undef L_
@@ -1233,10 +1274,10 @@ cudaError_t prepare_dense(int rmax);
 // count of a reduction is kept to that many clusters, so it runs in one
 // wave); 0 if it cannot be determined.
 int reduce_cluster_cap() {
-  auto cap = [](const void *fn, size_t smem) {
+  auto cap = [](const void *fn, size_t smem, int threads = kTB) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(kCl);
-    cfg.blockDim = dim3(kTB);
+    cfg.blockDim = dim3(threads);
     cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1256,7 +1297,7 @@ int reduce_cluster_cap() {
   c = std::min(c, cap((const void *)k_tsgram<double, 0>, 0));
   c = std::min(c, cap((const void *)k_tsgram<double, 1>, 0));
   if (prepare_dense(kMaxRank) == cudaSuccess) {
-    c = std::min(c, cap((const void *)k_project_tc<32>, projtc_smem_bytes<32>()));
+    c = std::min(c, cap((const void *)k_project_tc<32>, projtc_smem_bytes<32>(), kPT));
     c = std::min(c, cap((const void *)k_project<double>, proj_smem_bytes(kMaxRank, 8)));
   }
   return c;

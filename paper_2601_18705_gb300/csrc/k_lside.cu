@@ -15,10 +15,11 @@
 
 namespace dlr {
 
-// Step 8 runs in one cluster for up to this many angles: the rows of M and
-// Q (2 x 256 x 32 FP64 per CTA at 2048 angles and rank 32) stay in shared
-// memory.
-constexpr int kLsideMaxK = 2048;
+// Step 8 runs in one cluster for up to this many angles.  The cluster's FP64
+// work grows with the angles while it holds 8 SMs: at 2048 angles and rank
+// 32 it took 0.56 ms against 0.38 ms for the chain of kernels spread over
+// the whole GPU (lognormal1024, mixed), at 1024 and below it is the faster.
+constexpr int kLsideMaxK = 1024;
 int lside_max_k() { return kLsideMaxK; }
 
 // out[e] = sum over the cluster's CTAs (rank order) of part[e], e < n, in

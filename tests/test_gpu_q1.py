@@ -75,7 +75,7 @@ def test_dlr_q1_matches_oracle(orc, dlr, shape, r, prec):
 
 @pytest.mark.parametrize("prec", [0, 1])
 def test_dlr_q1_rank32_many_angles(orc, dlr, prec):
-    # rank class 32 and 1152 angles (step 8 in one cluster at 144 rows per CTA)
+    # rank class 32 and more than 1024 angles (the unfused step 8)
     out = _dlr_pair(orc, dlr, _hot(24, 20, 32, 16, 72), 2, prec)
     for eT, ep, *_ in out:
         assert eT < TOL[prec] and ep < TOL[prec], out

@@ -1,8 +1,8 @@
 """GPU parity at the shape of the lognormal1024 workload: rank 32 and
 32 x 64 = 2048 angles, so every kernel runs at rank class 32 and step 8
-runs in one cluster at its largest angle count, on meshes the oracle steps
-in seconds; the unfused step-8 chain (more than 2048 angles); one
-full-size lognormal1024 step against the oracle; and the
+takes its unfused path (more than 1024 angles), on meshes the oracle steps
+in seconds, also at 32 x 72 angles; one full-size lognormal1024 step
+against the oracle; and the
 library's own initial factors (dlr_create without set_factors) against the
 oracle's (reading R11), including the first step taken from them.
 Tolerances: relative L2 on T and psi = X S W^T of 1e-10 (FP64 path) and
@@ -37,8 +37,8 @@ def test_rank32_2048_angles(orc, dlr, prec, shape):
 
 @pytest.mark.parametrize("prec", [0, 1])
 def test_rank32_unfused_step8(orc, dlr, prec):
-    # 32 x 72 = 2304 angles: step 8 by the chain of Gram, Cholesky,
-    # completion and apply kernels
+    # 32 x 72 = 2304 angles and a ragged mesh: step 8 by the chain of Gram,
+    # Cholesky, completion and apply kernels
     case = workloads.lognormal_small(48, ny=40, n_azim=72)
     out, stats = run_pair(case, prec, 3, orc=orc, dlr=dlr)
     for k, (eT, ep, oi, gi) in enumerate(out):

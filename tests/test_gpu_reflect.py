@@ -175,7 +175,7 @@ def test_dlr_reflective_matches_oracle(orc, dlr, prec, shape, r, reflect):
 
 @pytest.mark.parametrize("prec", [0, 1])
 def test_dlr_reflective_rank32_matches_oracle(orc, dlr, prec):
-    # rank class 32 and 1152 angles
+    # rank class 32 and more than 1024 angles (the unfused step 8)
     case = _hot_case(24, 20, 32, 16, 72)
     out, stats = run_pair(case, prec, 2, orc=orc, dlr=dlr, reflect=(1, 0, 1, 1),
                           si_tol=1e-13 if prec == 0 else None)
