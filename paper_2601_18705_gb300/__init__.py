@@ -17,7 +17,7 @@ from ._lib import (DLR_FP64, DLR_METHOD_DLR, DLR_METHOD_SN, DLR_MIXED, DLR_SEL_D
                    DLR_SEL_QDEIM, DlrError,
                    check, load)
 
-__all__ = ["Solver", "step_batch", "autotune", "set_split", "sweep", "footprint_bytes", "DlrError", "DLR_FP64",
+__all__ = ["Solver", "step_batch", "autotune", "set_split", "sweep", "tc_gemm", "footprint_bytes", "DlrError", "DLR_FP64",
            "DLR_MIXED", "DLR_SEL_QDEIM", "DLR_SEL_DEIM", "DLR_METHOD_DLR", "DLR_METHOD_SN",
            "problem_from_case"]
 
@@ -303,6 +303,20 @@ def debug_lose_edge(solvers) -> None:
     that nothing writes, gives up after its time bound and reports ETIMEOUT."""
     arr = (C.c_void_p * len(solvers))(*[s.h.value for s in solvers])
     check(load().dlr_debug_lose_edge(arr, len(solvers)))
+
+
+def tc_gemm(A, B, *, stream=None):
+    """Testing aid: D = A B^T (A: m x k, B: n x k, contiguous float32 CUDA
+    tensors; m in {128, 256}, n in {16, 32}, k a multiple of 32) by the
+    tensor-core contraction of the mixed-precision projections."""
+    import torch
+    m, k = A.shape
+    n = B.shape[0]
+    D = torch.empty(m, n, dtype=torch.float32, device=A.device)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    check(load().dlr_debug_tc_gemm(C.c_void_p(A.data_ptr()), C.c_void_p(B.data_ptr()), m, n, k,
+                                   C.c_void_p(D.data_ptr()), C.c_void_p(st.cuda_stream)))
+    return D
 
 
 def set_split(solvers, split: float) -> None:

@@ -23,7 +23,7 @@ SYMBOLS = ["dlr_create", "dlr_step", "dlr_step_batch", "dlr_autotune", "dlr_set_
            "dlr_get_T", "dlr_set_T", "dlr_get_factors", "dlr_set_factors", "dlr_get_quadrature", "dlr_get_selected",
            "dlr_get_psi", "dlr_set_psi",
            "dlr_get_stats", "dlr_set_timing", "dlr_set_edge_inflow", "dlr_footprint_bytes",
-           "dlr_destroy", "dlr_last_error", "dlr_sweep", "dlr_sweep_noalloc"]
+           "dlr_destroy", "dlr_last_error", "dlr_sweep", "dlr_sweep_noalloc", "dlr_debug_tc_gemm"]
 
 
 class DlrProblem(C.Structure):
@@ -100,6 +100,8 @@ def load() -> C.CDLL:
     L.dlr_sweep.argtypes = [C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_int32, dp, dp,
                             C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     L.dlr_sweep_noalloc.argtypes = L.dlr_sweep.argtypes
+    L.dlr_debug_tc_gemm.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
+                                    C.c_void_p]
     for name in SYMBOLS:
         if name not in ("dlr_destroy", "dlr_last_error", "dlr_footprint_bytes"):
             getattr(L, name).restype = C.c_int
