@@ -308,7 +308,7 @@ def debug_lose_edge(solvers) -> None:
 def tc_gemm(A, B, *, stream=None):
     """Testing aid: D = A B^T (A: m x k, B: n x k, contiguous float32 CUDA
     tensors; m in {128, 256}, n in {16, 32}, k a multiple of 32) by the
-    tensor-core contraction of the mixed-precision projections."""
+    fifth-generation tensor cores (tcgen05, split TF32 products)."""
     import torch
     m, k = A.shape
     n = B.shape[0]

@@ -18,7 +18,6 @@
 #include <algorithm>
 
 #include "dlr_internal.cuh"
-#include "tc_core.cuh"
 
 namespace dlr {
 
@@ -979,360 +978,6 @@ k_project_tc(const Inst *__restrict__ insts) {
   cluster.sync();
 }
 
-// ------------------------------------------------------------------
-// The same projections on the fifth-generation tensor cores (tcgen05;
-// tc_core.cuh): per CTA slice of cells D^T = B^T X with the 6 r + 5 operand
-// columns B (as in k_project_tc, plus the vector columns) as the M side
-// (128 or 256 rows, two M = 128 accumulators at rank 32) and the r columns
-// of X as the N side (16 or 32), the FP32 accumulators in tensor memory.
-// Cells come in chunks of 32 (4 k-steps): 4-byte or 16-byte cp.async into a
-// raw stage (as k_project_tc), then every thread forms 4-cell groups of the
-// operands (scaled, shifted, split into TF32 parts) in the tensor core's
-// layout, in one of two operand buffers, while the MMAs of the previous
-// chunk run; one thread issues the chunk's 24 MMAs (3 split products per
-// k-step and half) and commits them to the buffer's mbarrier.  Pairs of
-// chunks (64 cells) accumulate alternately in two sets of accumulators; a
-// pair's set is read into FP32 registers (the owner of D row m, lane
-// m % 128 of half m / 128) once its products have completed, while the next
-// pair accumulates; FP32 sums per 8 pairs and per slice, FP64 once at the
-// end; the cluster sum in rank order as in k_project.
-// ------------------------------------------------------------------
-constexpr int kQT = 512;         // threads (16 warps)
-constexpr int kQKC = 32;         // cells per chunk (4 k-steps)
-constexpr int kQLD = kQKC + 4;   // raw stage column stride: 4 cells of halo in front
-constexpr uint64_t kQWaitNs = 2000000000ull;
-
-template <int RB> struct Q5 {
-  static constexpr int H = RB == 32 ? 2 : 1;          // M = 128 halves
-  static constexpr int M = 128 * H;                   // operand rows (6 RB + 5 used)
-  static constexpr int N = RB < 16 ? 16 : RB;         // X columns (padded to 16)
-  static constexpr int RAW = 3 * RB * kQLD + 9 * kQKC;  // floats of a raw stage
-  static constexpr int OPA = M * kQKC;                // floats of one A copy (hi or lo)
-  static constexpr int OPB = N * kQKC;
-  static constexpr int BUF = 2 * OPA + 2 * OPB;       // floats of one operand buffer
-  static constexpr int NCOL = 2 * H * N <= 32 ? 32 : 2 * H * N <= 64 ? 64 : 128;  // two accumulator sets
-  // operand-forming threads: A rows padded to whole warps, JA (JB) groups
-  // of 4 cells in parallel per row, within the CTA's kQT threads
-  static constexpr int MRP = (6 * RB + 5 + 31) / 32 * 32;
-  static constexpr int JA = RB == 32 ? 2 : RB == 16 ? 2 : 4;
-  static constexpr int JB = RB == 32 ? 2 : 8;
-  static_assert(MRP * JA + RB * JB <= kQT, "operand roles exceed the CTA");
-  // bytes: two raw stages, two operand buffers (1 KB aligned), two mbarriers
-  static constexpr int OFF_BUF = ((2 * RAW * 4 + 1023) / 1024) * 1024;
-  static constexpr int OFF_BAR = OFF_BUF + 2 * BUF * 4;
-  static constexpr int WORK = OFF_BAR + 16;
-  static constexpr int RED = (6 * RB * RB + 5 * RB) * 8;
-  static constexpr int SMEM = WORK > RED ? WORK : RED;
-};
-
-template <int RB>
-__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kQT, 1)
-k_project_tc5(const Inst *__restrict__ insts) {
-  pdl_wait();
-  pdl_trigger();
-  using C = Q5<RB>;
-  const Inst &I = insts[blockIdx.y];
-  if (rank_class(I.r) != RB) return;
-  const int nblk = I.partial_blocks;
-  if ((int)blockIdx.x >= nblk) return;  // whole clusters
-  cg::cluster_group cluster = cg::this_cluster();
-  extern __shared__ __align__(1024) unsigned char dyn5[];
-  float *raw = reinterpret_cast<float *>(dyn5);
-  unsigned char *opbuf = dyn5 + C::OFF_BUF;
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(dyn5 + C::OFF_BAR);
-  __shared__ uint32_t tslot;
-  __shared__ int bad;
-  const int r = I.r, N = I.N, nx = I.nx, ny = I.ny, t = threadIdx.x, w = t >> 5, lane = t & 31;
-  const float *__restrict__ X = as_c<float>(I.X);
-  const float *__restrict__ X0 = as_c<float>(I.X0);
-  const float *__restrict__ sig_t = as_c<float>(I.sig_t);
-  const float *__restrict__ ss4 = as_c<float>(I.ss4);
-  const float *__restrict__ qv = as_c<float>(I.q);
-  const bool vec = (N & 3) == 0 && (nx & 3) == 0 && ((reinterpret_cast<uintptr_t>(X) & 15) == 0) &&
-                   ((reinterpret_cast<uintptr_t>(X0) & 15) == 0) && ((reinterpret_cast<uintptr_t>(sig_t) & 15) == 0) &&
-                   ((reinterpret_cast<uintptr_t>(ss4) & 15) == 0) && ((reinterpret_cast<uintptr_t>(qv) & 15) == 0);
-  const int per = ((N + nblk - 1) / nblk + 3) & ~3;
-  const int c0 = min(N, (int)blockIdx.x * per), c1 = min(N, c0 + per);
-  const int nchunk = (c1 - c0 + kQKC - 1) / kQKC;
-
-  // the operand buffers' padding rows (6 RB + 5 .. M - 1, and X columns
-  // r .. N - 1 come zero-filled from the raw stage) stay zero throughout
-  for (int e = t; e < C::BUF / 2; e += kQT)
-    reinterpret_cast<float4 *>(opbuf)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (t == 0) {
-    tc::mbar_init(mbar, 1);
-    tc::mbar_init(mbar + 1, 1);
-    bad = 0;
-  }
-  if (w == 0) tc::alloc(&tslot, C::NCOL);
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
-  const uint32_t tmem = tslot;
-  constexpr uint32_t idesc = tc::idesc_tf32(128, C::N);
-
-  auto issue = [&](int ch) {
-    float *S = raw + (ch & 1) * C::RAW;
-    const int base = c0 + ch * kQKC;
-    if (vec) {
-      constexpr int QX = kQLD / 4;
-      for (int e = t; e < RB * QX; e += kQT) {
-        const int i = e / QX, h = 4 * (e - i * QX), c = base - 4 + h;
-        const bool ok = i < r && c >= 0 && c < c1;
-        cp_async16(S + i * kQLD + h, ok ? X + (size_t)N * i + c : X, ok ? 16 : 0);
-      }
-      constexpr int QK = kQKC / 4;
-      for (int e = t; e < RB * QK; e += kQT) {
-        const int i = e / QK, k = 4 * (e - i * QK), c = base + k;
-        const bool okc = i < r && c < c1, okb = okc && c >= nx;
-        cp_async16(S + (RB + i) * kQLD + 4 + k, okb ? X + (size_t)N * i + (c - nx) : X, okb ? 16 : 0);
-        cp_async16(S + (2 * RB + i) * kQLD + 4 + k, okc ? X0 + (size_t)N * i + c : X0, okc ? 16 : 0);
-      }
-      if (t < 3 * QK) {
-        const int row = t / QK, k = 4 * (t - row * QK), c = base + k;
-        const float *src = row == 0 ? sig_t : row == 1 ? ss4 : qv;
-        cp_async16(S + 3 * RB * kQLD + row * kQKC + k, c < c1 ? src + c : src, c < c1 ? 16 : 0);
-      }
-    } else {
-      for (int e = t; e < RB * (kQKC + 1); e += kQT) {
-        const int i = e / (kQKC + 1), h = e - i * (kQKC + 1) + 3, c = base - 4 + h;
-        const bool ok = i < r && c >= 0 && c < c1;
-        cp_async4(S + i * kQLD + h, ok ? X + (size_t)N * i + c : X, ok ? 4 : 0);
-      }
-      for (int e = t; e < RB * kQKC; e += kQT) {
-        const int i = e / kQKC, k = e - i * kQKC, c = base + k;
-        const bool okc = i < r && c < c1, okb = okc && c >= nx;
-        cp_async4(S + (RB + i) * kQLD + 4 + k, okb ? X + (size_t)N * i + (c - nx) : X, okb ? 4 : 0);
-        cp_async4(S + (2 * RB + i) * kQLD + 4 + k, okc ? X0 + (size_t)N * i + c : X0, okc ? 4 : 0);
-      }
-      if (t < 3 * kQKC) {
-        const int row = t / kQKC, k = t - row * kQKC, c = base + k;
-        const float *src = row == 0 ? sig_t : row == 1 ? ss4 : qv;
-        cp_async4(S + 3 * RB * kQLD + row * kQKC + k, c < c1 ? src + c : src, c < c1 ? 4 : 0);
-      }
-    }
-    if (t >= kQT - kQKC) {  // masks: rows 3 .. 8 of the per-cell block
-      float *V = S + 3 * RB * kQLD;
-      const int k = t - (kQT - kQKC), c = base + k;
-      const bool ok = c < c1;
-      const int iy = ok ? c / nx : 0, ix = ok ? c - iy * nx : 0;
-      V[3 * kQKC + k] = (ok && ix >= 1) ? 1.f : 0.f;
-      V[4 * kQKC + k] = (ok && ix == 0) ? 1.f : 0.f;
-      V[5 * kQKC + k] = (ok && ix == nx - 1) ? 1.f : 0.f;
-      V[6 * kQKC + k] = (ok && iy == 0) ? 1.f : 0.f;
-      V[7 * kQKC + k] = (ok && iy == ny - 1) ? 1.f : 0.f;
-      V[8 * kQKC + k] = 1.f;
-    }
-  };
-
-  // Accumulation: chunk pairs (64 cells) alternate between two sets of
-  // accumulators in tensor memory; a pair's set is read out once its
-  // products have completed (while the next pair accumulates in the other
-  // set) into FP32 sums per 8 pairs and per slice, held by the owner of D
-  // row m (warp w reads half w / 4, lanes 32 (w % 4) + lane).
-  float acc2[C::N], acc3[C::N];
-#pragma unroll
-  for (int e = 0; e < C::N; ++e) { acc2[e] = 0.f; acc3[e] = 0.f; }
-  const bool reader = w < 4 * C::H;
-  int nflush = 0;
-  auto flush_set = [&](int set) {  // all threads; the set's products have completed
-    tc::fence_after_sync();
-    if (reader) {
-      const uint32_t ta =
-          tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(set * C::H * C::N + (w >> 2) * C::N);
-      if (C::N == 32) {
-        float v[32];
-        tc::ld32(ta, v);
-#pragma unroll
-        for (int e = 0; e < C::N; ++e) acc2[e] += v[e % 32];
-      } else {
-        float v[16];
-        tc::ld16(ta, v);
-#pragma unroll
-        for (int e = 0; e < C::N; ++e) acc2[e] += v[e % 16];
-      }
-      if (++nflush % 8 == 0) {
-#pragma unroll
-        for (int e = 0; e < C::N; ++e) { acc3[e] += acc2[e]; acc2[e] = 0.f; }
-      }
-    }
-    tc::fence_before_sync();
-  };
-
-  // Operand roles (fixed for the kernel).  A: thread t < MRP JA owns row
-  // m = t % MRP (of the 6 RB operand columns and the 5 vector columns;
-  // rows past them idle) and the groups t / MRP + JA p; B: the next RB JB
-  // threads own X column n and the groups (t - MRP JA) / RB + JB p.
-  constexpr int MRP = C::MRP;
-  const bool arole = t < MRP * C::JA && (t % MRP) < 6 * RB + 5;
-  const bool brole = t >= MRP * C::JA && t < MRP * C::JA + RB * C::JB;
-  int ajg = 0, arow_s = 0, arow_c = 0, bjg = 0, brow_c = 0;
-  uint32_t arow_o = 0, brow_o = 0;
-  bool avec = false, ashift = false;
-  if (t < MRP * C::JA) {
-    const int m = t % MRP;
-    ajg = t / MRP;
-    arow_o = (uint32_t)((m >> 3) * 256 + (m & 7) * 16);
-    if (m < 6 * RB) {
-      const int mat = m / RB, col = m - mat * RB;
-      const int srow = mat == 1 ? 3 : mat == 3 ? 0 : mat == 4 ? 1 : 8;  // mL, sig_t, sigma_s/4pi, 1
-      arow_s = 3 * RB * kQLD + srow * kQKC;
-      arow_c = (mat == 2 ? RB + col : mat == 5 ? 2 * RB + col : col) * kQLD + 4;
-      ashift = mat == 1;
-    } else {
-      const int v = m - 6 * RB;  // q, eL, eR, eB, eT
-      arow_s = 3 * RB * kQLD + (v == 0 ? 2 : v + 3) * kQKC;
-      avec = true;
-    }
-  } else if (brole) {
-    const int tb = t - MRP * C::JA, n = tb % RB;
-    bjg = tb / RB;
-    brow_c = n * kQLD + 4;
-    brow_o = (uint32_t)((n >> 3) * 256 + (n & 7) * 16);
-  }
-
-  unsigned par[2] = {0u, 0u};  // next completion parity of each buffer's mbarrier
-  bool pend[2] = {false, false};
-  bool dirty[2] = {false, false};  // accumulator sets holding products not yet read
-  auto wait_buf = [&](int b) {
-    if (!pend[b]) return;
-    if (!tc::mbar_wait(mbar + b, par[b], kQWaitNs)) bad = 1;
-    par[b] ^= 1u;
-    pend[b] = false;
-  };
-  if (nchunk > 0) issue(0);
-  cp_async_commit();
-  for (int ch = 0; ch < nchunk; ++ch) {
-    if (ch + 1 < nchunk) issue(ch + 1);
-    cp_async_commit();
-    cp_async_wait<1>();
-    const int b = ch & 1, set = (ch >> 1) & 1;
-    // the buffer's previous products (chunk ch - 2) must have read it; when
-    // ch - 2 closed a pair, that pair's set is complete and is read out
-    // before the next pair but one restarts it
-    wait_buf(b);
-    __syncthreads();  // chunk ch has landed; buffer b is free
-    if (bad) break;
-    if ((ch & 1) && ch >= 3 && dirty[set ^ 1]) {  // (restarted by chunk ch + 1)
-      flush_set(set ^ 1);
-      dirty[set ^ 1] = false;
-    }
-    const float *S = raw + b * C::RAW;
-    unsigned char *Ah = opbuf + (size_t)b * C::BUF * 4, *Al = Ah + C::OPA * 4;
-    unsigned char *Bh = Al + C::OPA * 4, *Bl = Bh + C::OPB * 4;
-    // this chunk's operands, 4-cell groups: thread t owns one operand row
-    // (fixed for the kernel) and every JA-th (JB-th) group of the chunk
-    if (arole) {
-#pragma unroll
-      for (int p = 0; p < 8 / C::JA; ++p) {
-        const int jg = ajg + C::JA * p, jj = 4 * jg;
-        float4 x;
-        if (avec) {
-          x = *reinterpret_cast<const float4 *>(S + arow_s + jj);
-        } else {
-          const float4 sc = *reinterpret_cast<const float4 *>(S + arow_s + jj);
-          const float4 a = *reinterpret_cast<const float4 *>(S + arow_c + jj);
-          x = ashift ? make_float4(S[arow_c + jj - 1], a.x, a.y, a.z) : a;  // X_L: one cell back
-          x.x *= sc.x;
-          x.y *= sc.y;
-          x.z *= sc.z;
-          x.w *= sc.w;
-        }
-        float4 h, l;
-        tc::split(x.x, h.x, l.x);
-        tc::split(x.y, h.y, l.y);
-        tc::split(x.z, h.z, l.z);
-        tc::split(x.w, h.w, l.w);
-        const uint32_t off = (uint32_t)((jg >> 1) * C::M * 32 + (jg & 1) * 128) + arow_o;
-        *reinterpret_cast<float4 *>(Ah + off) = h;
-        *reinterpret_cast<float4 *>(Al + off) = l;
-      }
-    } else if (brole) {
-#pragma unroll
-      for (int p = 0; p < 8 / C::JB; ++p) {
-        const int jg = bjg + C::JB * p, jj = 4 * jg;
-        const float4 x = *reinterpret_cast<const float4 *>(S + brow_c + jj);
-        float4 h, l;
-        tc::split(x.x, h.x, l.x);
-        tc::split(x.y, h.y, l.y);
-        tc::split(x.z, h.z, l.z);
-        tc::split(x.w, h.w, l.w);
-        const uint32_t off = (uint32_t)((jg >> 1) * C::N * 32 + (jg & 1) * 128) + brow_o;
-        *reinterpret_cast<float4 *>(Bh + off) = h;
-        *reinterpret_cast<float4 *>(Bl + off) = l;
-      }
-    }
-    tc::fence_smem_to_async();
-    __syncthreads();  // the operands are written; the raw stage b is free
-    if (t == 0) {
-      tc::fence_after_sync();
-#pragma unroll
-      for (int s = 0; s < kQKC / 8; ++s)
-#pragma unroll
-        for (int hf = 0; hf < C::H; ++hf) {
-          const uint32_t d = tmem + (uint32_t)(set * C::H * C::N + hf * C::N);
-          const uint32_t ao = (uint32_t)(s * C::M * 32 + hf * 4096), bo = (uint32_t)(s * C::N * 32);
-          tc::mma(d, tc::smem_desc(tc::saddr(Ah + ao)), tc::smem_desc(tc::saddr(Bl + bo)), idesc,
-                  !((ch & 1) == 0 && s == 0));
-          tc::mma(d, tc::smem_desc(tc::saddr(Al + ao)), tc::smem_desc(tc::saddr(Bh + bo)), idesc, true);
-          tc::mma(d, tc::smem_desc(tc::saddr(Ah + ao)), tc::smem_desc(tc::saddr(Bh + bo)), idesc, true);
-        }
-      tc::commit(mbar + b);
-    }
-    pend[b] = true;
-    dirty[set] = true;
-  }
-  // the last products: the older buffer's commit first, then read out the
-  // older pair's set before the newer one
-  if (nchunk > 0 && !bad) {
-    const int last = nchunk - 1;
-    if (last >= 1) wait_buf((last - 1) & 1);
-    wait_buf(last & 1);
-    const int lset = (last >> 1) & 1;
-    __syncthreads();
-    if (!bad) {
-      if (dirty[lset ^ 1]) flush_set(lset ^ 1);
-      if (dirty[lset]) flush_set(lset);
-    }
-  }
-  cp_async_wait<0>();
-  if (bad && t == 0) set_status(I.status, kETimeout);
-  tc::fence_before_sync();
-  __syncthreads();
-  if (w == 0) tc::dealloc(tmem, C::NCOL);
-  // the CTA partial: D row m (operand column) and column n (X column):
-  // G_nj for m = mat RB + j, the vector sums for m >= 6 RB
-  double *part_s = reinterpret_cast<double *>(dyn5);
-  const int rr2 = r * r;
-  if (reader) {
-    const int m = 128 * (w >> 2) + 32 * (w & 3) + lane;
-    if (m < 6 * RB) {
-      const int mat = m / RB, j = m - mat * RB;
-      const double sc = mat == 4 ? 4.0 * kPi : 1.0;
-      if (j < r)
-#pragma unroll
-        for (int n = 0; n < C::N; ++n)
-          if (n < r) part_s[mat * rr2 + n + r * j] = sc * ((double)acc2[n] + (double)acc3[n]);
-    } else if (m < 6 * RB + 5) {
-      const int v = m - 6 * RB;
-#pragma unroll
-      for (int n = 0; n < C::N; ++n)
-        if (n < r) part_s[6 * rr2 + v * r + n] = (double)acc2[n] + (double)acc3[n];
-    }
-  }
-  cluster.sync();
-  const int rank = (int)cluster.block_rank();
-  const int cnt = proj_count(r), share = (cnt + kCl - 1) / kCl;
-  double *out = I.partials + (size_t)(blockIdx.x / kCl) * cnt;
-  for (int e = rank * share + t; e < min(cnt, (rank + 1) * share); e += kQT) {
-    double v = 0.0;
-#pragma unroll
-    for (int q = 0; q < kCl; ++q) v += cluster.map_shared_rank(part_s, q)[e];
-    out[e] = v;
-  }
-  cluster.sync();
-}
-
 // Sum of per-block partials: out[e] = scale * sum_b part[b*stride + e].
 __global__ void __launch_bounds__(256) k_reduce(const ReduceJob *__restrict__ jobs) {
   pdl_wait();
@@ -1609,18 +1254,14 @@ cudaError_t launch_apply(const ApplyJob *d_jobs, int n, int maxm, int rmask, cud
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-constexpr bool kProjTcgen05 = false; // mixed-precision projections: tcgen05 (else mma.sync)
-
-// FP64: k_project; mixed precision: k_project_tc5 or k_project_tc, one
-// launch per rank class in rmask
+// FP64: k_project; mixed precision: k_project_tc, one launch per rank
+// class in rmask
 template <typename real>
 cudaError_t launch_project(const Inst *d, int n, int maxblocks, int rmax, int rmask, cudaStream_t st) {
   if (sizeof(real) == 8)
     return launch_pdl(k_project<double>, dim3(maxblocks, n), dim3(kTB), proj_smem_bytes(rmax, 8), st, d);
   const dim3 g(maxblocks, n);
-#define L_(RB)                                                                         \
-  (e = kProjTcgen05 ? launch_pdl(k_project_tc5<RB>, g, dim3(kQT), Q5<RB>::SMEM, st, d) \
-                    : launch_pdl(k_project_tc<RB>, g, dim3(kPT), projtc_smem_bytes<RB>(), st, d))
+#define L_(RB) (e = launch_pdl(k_project_tc<RB>, g, dim3(kPT), projtc_smem_bytes<RB>(), st, d))
   cudaError_t e = cudaSuccess;
   DLR_RB_DISPATCH(rmask, L_);
 #undef L_
@@ -1656,8 +1297,7 @@ int reduce_cluster_cap() {
   c = std::min(c, cap((const void *)k_tsgram<double, 0>, 0));
   c = std::min(c, cap((const void *)k_tsgram<double, 1>, 0));
   if (prepare_dense(kMaxRank) == cudaSuccess) {
-    c = std::min(c, kProjTcgen05 ? cap((const void *)k_project_tc5<32>, Q5<32>::SMEM, kQT)
-                                 : cap((const void *)k_project_tc<32>, projtc_smem_bytes<32>(), kPT));
+    c = std::min(c, cap((const void *)k_project_tc<32>, projtc_smem_bytes<32>(), kPT));
     c = std::min(c, cap((const void *)k_project<double>, proj_smem_bytes(kMaxRank, 8)));
   }
   return c;
@@ -1665,14 +1305,8 @@ int reduce_cluster_cap() {
 
 // Kernel attributes, set before any launch is captured into a graph.
 cudaError_t prepare_dense(int rmax) {
-  cudaError_t e = cudaFuncSetAttribute(k_project_tc5<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       Q5<8>::SMEM);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_project_tc5<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, Q5<16>::SMEM);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_project_tc5<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, Q5<32>::SMEM);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_project_tc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, projtc_smem_bytes<8>());
+  cudaError_t e =
+      cudaFuncSetAttribute(k_project_tc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, projtc_smem_bytes<8>());
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_project_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, projtc_smem_bytes<16>());
   if (e == cudaSuccess)

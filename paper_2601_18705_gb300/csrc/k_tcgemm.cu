@@ -1,9 +1,12 @@
-// k_tcgemm.cu -- dlr_debug_tc_gemm: the tensor-core (tcgen05) contraction
-// that the mixed-precision projections of steps 6 and 7 use (split TF32
-// products, operands in shared memory, the FP32 accumulator in tensor
-// memory; tc_core.cuh), on plain device arrays, so that a test can check
-// the operand layout, the descriptors and the split products against a
-// reference.
+// k_tcgemm.cu -- dlr_debug_tc_gemm: the tcgen05 form of the TF32
+// contraction of the mixed-precision projections of steps 6 and 7 (split
+// TF32 products, operands in shared memory, the FP32 accumulator in tensor
+// memory; tc_core.cuh) on plain device arrays, so that a test can check the
+// operand layout, the descriptors and the split products against a
+// reference.  The projections themselves run the mma.sync kernel
+// k_project_tc: a tcgen05 version of that kernel, built on these helpers
+// with one issuing thread and CTA barriers around the operand staging, was
+// slower (560 against 394 us per 1024^2-cell, rank-32 launch).
 #include <cuda_runtime.h>
 
 #include "../../include/dlr.h"

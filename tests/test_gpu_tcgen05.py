@@ -1,6 +1,7 @@
-"""The tensor-core contraction of the mixed-precision projections (tcgen05
-MMAs of kind TF32, operands split into two TF32 parts, FP32 accumulator in
-tensor memory) on plain arrays, against an FP64 product: D = A B^T.  The
+"""The fifth-generation tensor-core (tcgen05) form of the contraction of the
+mixed-precision projections (MMAs of kind TF32, operands split into two
+TF32 parts, FP32 accumulator in tensor memory) on plain arrays, against an
+FP64 product: D = A B^T.  The
 bound per entry is relative to sum_k |a_ik| |b_jk|: about 2^-20 for the
 split products plus FP32 accumulation over k (k 2^-24), written below with
 a factor 4 of margin.  On failure the message tells which layout mistakes
