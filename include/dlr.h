@@ -267,11 +267,11 @@ int dlr_set_split(dlr_handle *const *hs, int32_t n, double split);
 int dlr_debug_lose_edge(dlr_handle *const *hs, int32_t n);
 
 /* Testing aid (no paper counterpart): the fifth-generation tensor-core
- * form of the contraction of the mixed-precision projections of Algorithm 1
- * steps 6 and 7 (tcgen05 MMAs of kind TF32 with the operands in shared
- * memory and the FP32 accumulator in tensor memory; each operand split into
- * two TF32 parts and a product summed as hi lo + lo hi + hi hi; the steps
- * themselves use the mma.sync form) on plain device arrays:
+ * contraction of the mixed-precision projections of Algorithm 1 steps 6
+ * and 7 (tcgen05 MMAs of kind TF32 with the operands in shared memory and
+ * the FP32 accumulator in tensor memory; each operand split into two TF32
+ * parts and a product summed as hi lo + lo hi + hi hi) on plain device
+ * arrays:
  * D (m x n, row-major FP32) = A (m x k, row-major) times B^T (B: n x k,
  * row-major), with m in {128, 256}, n in {16, 32}, k a multiple of 32, A
  * and B 16-byte aligned (DLR_EINVAL otherwise).  All pointers are device

@@ -10,7 +10,8 @@
 //                  A R^{-1} for a CholeskyQR factor R (forward substitution)
 //   k_project      step 6 P = <X, X0> and the step 7 Galerkin operators:
 //                  Gram, x/y neighbour Grams, <sigma_t X, X>, <sigma_s X, X>,
-//                  <q, X> and the four edge sums
+//                  <q, X> and the four edge sums (FP64); k_project_tc5 the
+//                  same in mixed precision on the tcgen05 tensor cores
 //   k_tupdate      step 9 temperature update (Eq. temperature update, Newton
 //                  form) with phi = X (L w), fused with the rotation X0 <- X U
 // Mixed precision: products and sums over one staging round (at most 128
@@ -18,6 +19,7 @@
 #include <algorithm>
 
 #include "dlr_internal.cuh"
+#include "tc_core.cuh"
 
 namespace dlr {
 
@@ -648,328 +650,385 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // ------------------------------------------------------------------
-// step 6 / step 7 projections on the tensor cores (mixed precision).  The
-// same sums as k_project<float>, written as one product per CTA slice of
-// cells, D = X^T B with
-//   B = [X, X_L, X_B, sig_t X, (sigma_s / 4 pi) X, X0]   (r columns each)
-// (X_L(c) = X(c - 1) on cells with ix >= 1, X_B(c) = X(c - nx) on cells
-// with iy >= 1, zero elsewhere) and the vector part D_v = X^T [q, e_L, e_R,
-// e_B, e_T] (e_* the indicators of the four edges' cells).  Per cell this is
-// 6 r^2 + 5 r multiply-adds on 8 r + 12 bytes, too dense for the FP32 pipe
-// to keep up with HBM, so it runs as mma.sync m16n8k8 with TF32 operands
-// and FP32 accumulation: every operand is split as x = hi + lo, hi = x
-// rounded to TF32 (to nearest, ties away, by integer arithmetic on the
-// bits), lo = x - hi (exact in FP32, of which the tensor core reads the TF32
-// part), and a product is summed as hi lo + lo hi + hi hi; the error (the
-// dropped lo lo and the truncation of lo, at most about 2^-20 of the
-// product and of either sign) stays near FP32 rounding.
-//
-// Cells stream through two shared-memory stages of 64 cells filled by
-// cp.async (16-byte copies when the columns and rows are 4-cell aligned,
-// else 4-byte ones; zero-filled past the slice, past rank r and where the
-// shifted neighbour does not exist); a stage keeps column i of X at
-// i * 68 + 4 + k (one cell of halo in front for X_L), of X_B and X0 likewise,
-// so the fragment reads (8 rows x 4 cells per warp) fall in distinct banks.
-// Once a stage has landed, the X^T fragments of its 8 k-steps are split
-// into TF32 parts once for the CTA and stored in fragment order (two
-// 16-byte reads per fragment).  With 16 warps, warp w takes the 16-row tile
-// mt = w / (16 / MT) of X^T and the 8-column tiles w % (16 / MT) + j 16 / MT
-// of B, so each entry of the six matrices has one owner; the vector tile of
-// k-step ks and row tile mt goes to warp 8 mt + ks, and the eight k-step
-// sums of a row tile are added in k-step order.  FP32 sums: the chunk (in
-// the accumulator), 8 chunks, the slice; FP64 once; then the cluster's CTAs
-// in rank order as in k_project.
+// step 6 / step 7 projections on the fifth-generation tensor cores
+// (tcgen05; tc_core.cuh), mixed precision.  The same sums as
+// k_project<float> (G, Nx, Ny, Mt, Ms, P and the vector sums), written as
+// one product per CTA slice of cells, D^T = B^T X with the operand columns
+//   B = [X, X_L, X_B, sig_t X, (sigma_s / 4 pi) X, X0, q, e_L, e_R, e_B, e_T]
+// (X_L(c) = X(c - 1) on cells with ix >= 1, X_B(c) = X(c - nx) on cells with
+// iy >= 1, zero elsewhere; e_* the indicators of the four edges' cells).
+// Per cell this is 6 r^2 + 5 r multiply-adds on 8 r + 12 bytes, too dense
+// for the FP32 pipe to keep up with HBM.  The 6 r + 5 operand columns are
+// the M side (128 or 256 rows, two M = 128 accumulators at rank
+// 32) and the r columns of X as the N side (16 or 32), the FP32
+// accumulators in tensor memory.  16 producer warps stage cells in chunks of
+// 32 (4 k-steps) into three raw stages (cp.async; 16-byte copies when N and
+// nx are multiples of 4, else 4-byte ones; zero-filled past the slice, past
+// rank r and where the shifted neighbour does not exist) and form
+// the operands of a chunk (scaled, shifted, split into TF32 parts) in the
+// tensor core's layout in one of two operand buffers, each thread owning
+// one operand row for the whole kernel; a 17th warp issues the chunk's 24
+// MMAs (3 split products per k-step and half) once the producers have
+// arrived on the buffer's "full" mbarrier and commits them to its "empty"
+// mbarrier, which the producers wait on before refilling it.  TF32 split
+// products (tc_core.cuh): each operand value x is stored as hi = x rounded
+// to TF32 and lo = x - hi, a product summed as hi lo + lo hi + hi hi.
+// Producers meet on one named barrier per chunk; the MMA warp never joins
+// it.  Pairs
+// of chunks (64 cells) accumulate alternately in two sets of accumulators;
+// a pair's set is read into FP32 registers (the owner of D row m, lane
+// m % 128 of half m / 128) once its products have completed; FP32 sums per
+// 8 pairs and per slice, FP64 once; the cluster sum in rank order as in
+// k_project.  Every mbarrier wait is bounded; a wait that runs out marks
+// the instance DLR_ETIMEOUT.
 // ------------------------------------------------------------------
-constexpr int kPT = 512;          // threads of k_project_tc (16 warps)
-constexpr int kPKC = 64;          // cells per stage (8 k-steps of 8)
-constexpr int kPH = 4;            // front halo: cell base - 1 sits at kPH - 1
-constexpr int kPLD = kPKC + kPH;  // 68 = 4 mod 32
-constexpr int kPV = 9;            // per-cell rows: sig_t, sigma_s/4pi, q, mL, eL, eR, eB, eT, 1
+constexpr int kQP = 512;          // producer threads (16 warps)
+constexpr int kQT = kQP + 32;     // and the MMA warp
+constexpr int kQKC = 32;          // cells per chunk (4 k-steps)
+constexpr int kQLD = kQKC + 4;    // raw stage column stride: 4 cells of halo in front
+constexpr int kQS = 3;            // raw stages
+constexpr uint64_t kQWaitNs = 2000000000ull;
 
-template <int RB>
-constexpr int projtc_mt() { return RB >= 16 ? RB / 16 : 1; }
-template <int RB>
-constexpr int projtc_stage_floats() { return 3 * RB * kPLD + kPV * kPKC; }
-// two stages, then the split X^T fragments (MT x 8 k-steps x 32 lanes x 8)
-template <int RB>
-constexpr int projtc_work_floats() { return 2 * projtc_stage_floats<RB>() + projtc_mt<RB>() * 8 * 32 * 8; }
-template <int RB>
-constexpr int projtc_smem_bytes() {
-  return projtc_work_floats<RB>() * 4 > (6 * RB * RB + 5 * RB + (kPT / 32) * 8 * RB) * 8
-             ? projtc_work_floats<RB>() * 4
-             : (6 * RB * RB + 5 * RB + (kPT / 32) * 8 * RB) * 8;
-}
+template <int RB> struct Q5 {
+  static constexpr int H = RB == 32 ? 2 : 1;          // M = 128 halves
+  static constexpr int M = 128 * H;                   // operand rows (6 RB + 5 used)
+  static constexpr int N = RB < 16 ? 16 : RB;         // X columns (padded to 16)
+  static constexpr int RAW = 3 * RB * kQLD + 9 * kQKC;  // floats of a raw stage
+  static constexpr int OPA = M * kQKC;                // floats of one A copy (hi or lo)
+  static constexpr int OPB = N * kQKC;
+  static constexpr int BUF = 2 * OPA + 2 * OPB;       // floats of one operand buffer
+  static constexpr int NCOL = 2 * H * N <= 32 ? 32 : 2 * H * N <= 64 ? 64 : 128;  // two accumulator sets
+  // operand-forming threads: A rows padded to whole warps, JA (JB) groups
+  // of 4 cells in parallel per row
+  static constexpr int MRP = (6 * RB + 5 + 31) / 32 * 32;
+  static constexpr int JA = RB == 32 ? 2 : RB == 16 ? 2 : 4;
+  static constexpr int JB = RB == 32 ? 2 : 8;
+  static_assert(MRP * JA + RB * JB <= kQP, "operand roles exceed the producers");
+  static constexpr int OFF_BUF = ((kQS * RAW * 4 + 1023) / 1024) * 1024;
+  static constexpr int OFF_BAR = OFF_BUF + 2 * BUF * 4;  // full[2], empty[2]
+  // the readers' per-slice FP32 sums: N values of 128 H threads, column-major
+  static constexpr int OFF_ACC = OFF_BAR + 32;
+  static constexpr int WORK = OFF_ACC + N * 128 * H * 4;
+  static constexpr int RED = (6 * RB * RB + 5 * RB) * 8;
+  static constexpr int SMEM = WORK > RED ? WORK : RED;
+};
 
-// x = hi + lo: hi is x rounded to TF32 (10 fraction bits; adding half an
-// ulp to the magnitude's bit pattern and clearing the 13 low bits rounds to
-// nearest with ties away from zero, carrying into the exponent where
-// needed; x is finite), lo = x - hi exactly, handed to the tensor core as
-// FP32 bits (it reads the TF32 part)
-__device__ __forceinline__ void tf32_split(float x, uint32_t &hi, uint32_t &lo) {
-  hi = (__float_as_uint(x) + 0x1000u) & 0xffffe000u;
-  lo = __float_as_uint(x - __uint_as_float(hi));
-}
-// d += a b (16 x 8 x 8, TF32 in, FP32 accumulate); not volatile, so the
-// compiler may interleave the products of independent tiles
-__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint4 &a, uint32_t b0, uint32_t b1) {
-  asm(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-      "{%0, %1, %2, %3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
-}
-// the three-term split product: d += a b at about FP32 accuracy
-__device__ __forceinline__ void mma_3xtf32(float (&d)[4], const uint4 &ah, const uint4 &al, float b0, float b1) {
-  uint32_t h0, l0, h1, l1;
-  tf32_split(b0, h0, l0);
-  tf32_split(b1, h1, l1);
-  mma_tf32(d, ah, l0, l1);
-  mma_tf32(d, al, h0, h1);
-  mma_tf32(d, ah, h0, h1);
+__device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, %0;" ::"r"(kQP) : "memory"); }
+__device__ __forceinline__ void mbar_arrive(uint64_t *m) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(tc::saddr(m)) : "memory");
 }
 
 template <int RB>
-__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kPT, 1)
-k_project_tc(const Inst *__restrict__ insts) {
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kQT, 1)
+k_project_tc5(const Inst *__restrict__ insts) {
   pdl_wait();
   pdl_trigger();
-  constexpr int NW = kPT / 32;
-  constexpr int MT = projtc_mt<RB>();         // 16-row tiles of X^T
-  constexpr int NTM = RB / 8;                 // 8-column tiles of one matrix
-  constexpr int NT = 6 * NTM;                 // matrix tiles (the vector tile apart)
-  constexpr int WPM = NW / MT;                // warps per row tile
-  constexpr int OWN = (NT + WPM - 1) / WPM;   // matrix tiles per warp, at most
-  constexpr int SF = projtc_stage_floats<RB>();
-  static_assert(kPKC / 8 == 8 && NW == 16, "8 k-steps per chunk, 16 warps");
+  using C = Q5<RB>;
   const Inst &I = insts[blockIdx.y];
   if (rank_class(I.r) != RB) return;
   const int nblk = I.partial_blocks;
   if ((int)blockIdx.x >= nblk) return;  // whole clusters
   cg::cluster_group cluster = cg::this_cluster();
-  extern __shared__ __align__(32) unsigned char dyn[];
-  float *stg = reinterpret_cast<float *>(dyn);
-  // split X^T fragments of the current chunk: hi parts, then lo parts
-  uint4 *AFh = reinterpret_cast<uint4 *>(stg + 2 * SF);
-  uint4 *AFl = AFh + MT * 8 * 32;
-  const int r = I.r, N = I.N, nx = I.nx, ny = I.ny, t = threadIdx.x;
-  const int lane = t & 31, w = t >> 5, g = lane >> 2, tg = lane & 3;
-  const int mt = w / WPM;      // this warp's row tile
-  const int wt = w - mt * WPM;  // and its first column tile
-  const bool vown = w < 8 * MT;  // the vector tile of k-step w % 8, row tile w / 8
+  extern __shared__ __align__(1024) unsigned char dyn5[];
+  float *raw = reinterpret_cast<float *>(dyn5);
+  unsigned char *opbuf = dyn5 + C::OFF_BUF;
+  uint64_t *full = reinterpret_cast<uint64_t *>(dyn5 + C::OFF_BAR), *empty = full + 2;
+  __shared__ uint32_t tslot;
+  __shared__ int bad;
+  const int r = I.r, N = I.N, nx = I.nx, ny = I.ny, t = threadIdx.x, w = t >> 5, lane = t & 31;
   const float *__restrict__ X = as_c<float>(I.X);
   const float *__restrict__ X0 = as_c<float>(I.X0);
   const float *__restrict__ sig_t = as_c<float>(I.sig_t);
   const float *__restrict__ ss4 = as_c<float>(I.ss4);
   const float *__restrict__ qv = as_c<float>(I.q);
-  double *const partials = I.partials;
-  // slices of whole 4-cell groups: with N and nx multiples of 4 every
-  // 16-byte copy is either wholly inside or wholly outside the data
   const bool vec = (N & 3) == 0 && (nx & 3) == 0 && ((reinterpret_cast<uintptr_t>(X) & 15) == 0) &&
                    ((reinterpret_cast<uintptr_t>(X0) & 15) == 0) && ((reinterpret_cast<uintptr_t>(sig_t) & 15) == 0) &&
                    ((reinterpret_cast<uintptr_t>(ss4) & 15) == 0) && ((reinterpret_cast<uintptr_t>(qv) & 15) == 0);
   const int per = ((N + nblk - 1) / nblk + 3) & ~3;
   const int c0 = min(N, (int)blockIdx.x * per), c1 = min(N, c0 + per);
-  const int nchunk = (c1 - c0 + kPKC - 1) / kPKC;
+  const int nchunk = (c1 - c0 + kQKC - 1) / kQKC;
 
-  // chunk ch into stage ch & 1 (this thread's share of the copies)
-  auto issue = [&](int ch) {
-    float *S = stg + (ch & 1) * SF;
-    const int base = c0 + ch * kPKC;
-    if (vec) {
-      constexpr int QX = (kPKC + kPH) / 4;  // X with the 4 cells in front
-      for (int e = t; e < RB * QX; e += kPT) {
-        const int i = e / QX, h = 4 * (e - i * QX);
-        const int c = base - kPH + h;
-        const bool ok = i < r && c >= 0 && c < c1;
-        cp_async16(S + i * kPLD + h, ok ? X + (size_t)N * i + c : X, ok ? 16 : 0);
-      }
-      constexpr int QK = kPKC / 4;
-      for (int e = t; e < RB * QK; e += kPT) {
-        const int i = e / QK, k = 4 * (e - i * QK);
-        const int c = base + k;
-        const bool okc = i < r && c < c1, okb = okc && c >= nx;
-        cp_async16(S + (RB + i) * kPLD + kPH + k, okb ? X + (size_t)N * i + (c - nx) : X, okb ? 16 : 0);
-        cp_async16(S + (2 * RB + i) * kPLD + kPH + k, okc ? X0 + (size_t)N * i + c : X0, okc ? 16 : 0);
-      }
-      float *V = S + 3 * RB * kPLD;
-      if (t < 3 * QK) {
-        const int row = t / QK, k = 4 * (t - row * QK), c = base + k;
-        const float *src = row == 0 ? sig_t : row == 1 ? ss4 : qv;
-        cp_async16(V + row * kPKC + k, c < c1 ? src + c : src, c < c1 ? 16 : 0);
-      }
-    } else {
-      constexpr int HX = kPKC + 1;  // X with the cell in front
-      for (int e = t; e < RB * HX; e += kPT) {
-        const int i = e / HX, h = e - i * HX + kPH - 1;
-        const int c = base - kPH + h;
-        const bool ok = i < r && c >= 0 && c < c1;
-        cp_async4(S + i * kPLD + h, ok ? X + (size_t)N * i + c : X, ok ? 4 : 0);
-      }
-      for (int e = t; e < RB * kPKC; e += kPT) {
-        const int i = e / kPKC, k = e - i * kPKC;
-        const int c = base + k;
-        const bool okc = i < r && c < c1, okb = okc && c >= nx;
-        cp_async4(S + (RB + i) * kPLD + kPH + k, okb ? X + (size_t)N * i + (c - nx) : X, okb ? 4 : 0);
-        cp_async4(S + (2 * RB + i) * kPLD + kPH + k, okc ? X0 + (size_t)N * i + c : X0, okc ? 4 : 0);
-      }
-      float *V = S + 3 * RB * kPLD;
-      if (t < 3 * kPKC) {
-        const int row = t / kPKC, k = t - row * kPKC, c = base + k;
-        const float *src = row == 0 ? sig_t : row == 1 ? ss4 : qv;
-        cp_async4(V + row * kPKC + k, c < c1 ? src + c : src, c < c1 ? 4 : 0);
-      }
-    }
-    if (t >= kPT - kPKC) {  // the masks (plain stores; the stage is not read before its barrier)
-      float *V = S + 3 * RB * kPLD;
-      const int k = t - (kPT - kPKC), c = base + k;
-      const bool ok = c < c1;
-      const int iy = ok ? c / nx : 0, ix = ok ? c - iy * nx : 0;
-      V[3 * kPKC + k] = (ok && ix >= 1) ? 1.f : 0.f;
-      V[4 * kPKC + k] = (ok && ix == 0) ? 1.f : 0.f;
-      V[5 * kPKC + k] = (ok && ix == nx - 1) ? 1.f : 0.f;
-      V[6 * kPKC + k] = (ok && iy == 0) ? 1.f : 0.f;
-      V[7 * kPKC + k] = (ok && iy == ny - 1) ? 1.f : 0.f;
-      V[8 * kPKC + k] = 1.f;
-    }
-  };
-
-  // this warp's column tiles: operand rows (stage offsets) and scale rows
-  int boff[OWN], soff[OWN], dmat[OWN], dcol[OWN];
-#pragma unroll
-  for (int o = 0; o < OWN; ++o) {
-    const int nt = wt + WPM * o;
-    const int mat = nt < NT ? nt / NTM : 0, col = nt < NT ? (nt - mat * NTM) * 8 + g : 0;
-    dmat[o] = nt < NT ? mat : -1;
-    dcol[o] = (nt - mat * NTM) * 8 + 2 * tg;
-    // X, X_L (one cell back), X_B, sig_t X, sigma_s X / 4 pi, X0
-    boff[o] = (mat == 2 ? RB + col : mat == 5 ? 2 * RB + col : col) * kPLD + (mat == 1 ? -1 : 0);
-    const int srow = mat == 1 ? 3 : mat == 3 ? 0 : mat == 4 ? 1 : 8;
-    soff[o] = 3 * RB * kPLD + srow * kPKC;
+  // the operand buffers' padding rows stay zero throughout
+  for (int e = t; e < C::BUF / 2; e += kQT)
+    reinterpret_cast<float4 *>(opbuf)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (t == 0) {
+    tc::mbar_init(full, kQP / 32);
+    tc::mbar_init(full + 1, kQP / 32);
+    tc::mbar_init(empty, 1);
+    tc::mbar_init(empty + 1, 1);
+    bad = 0;
   }
+  if (w == 0) tc::alloc(&tslot, C::NCOL);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tslot;
+  constexpr uint32_t idesc = tc::idesc_tf32(128, C::N);
 
-  float d1[OWN][4], d2[OWN][4], d3[OWN][4];  // chunk, 8 chunks, slice
-  float v1[4], v2[4], v3[4];                 // the vector tile
+  // this thread's FP32 sums of the accumulator rows it reads: per 8 pairs
+  // in registers, per slice in shared memory (acc3[e * 128 H + t])
+  float acc2[C::N];
 #pragma unroll
-  for (int o = 0; o < OWN; ++o)
+  for (int e = 0; e < C::N; ++e) acc2[e] = 0.f;
+  const bool reader = w < 4 * C::H;
+  float *acc3 = reinterpret_cast<float *>(dyn5 + C::OFF_ACC);
+  constexpr int NR = 128 * C::H;
+  if (reader)
 #pragma unroll
-    for (int e = 0; e < 4; ++e) { d1[o][e] = 0.f; d2[o][e] = 0.f; d3[o][e] = 0.f; }
-#pragma unroll
-  for (int e = 0; e < 4; ++e) { v1[e] = 0.f; v2[e] = 0.f; v3[e] = 0.f; }
+    for (int e = 0; e < C::N; ++e) acc3[e * NR + t] = 0.f;
 
-  if (nchunk > 0) issue(0);
-  cp_async_commit();
-  for (int ch = 0; ch < nchunk; ++ch) {
-    // the stage of chunk ch + 1 was last read in iteration ch - 1, before
-    // its closing barrier
-    if (ch + 1 < nchunk) issue(ch + 1);
-    cp_async_commit();
-    cp_async_wait<1>();
-    __syncthreads();  // chunk ch has landed, every thread's copies and flags
-    const float *S = stg + (ch & 1) * SF;
-    // the X^T fragments of the chunk, split once: entry (m, ks, lane) holds
-    // hi and lo of rows 16 m + g (+ 8), cells 8 ks + tg (+ 4)
-    for (int e = t; e < MT * 8 * 32; e += kPT) {
-      const int m = e >> 8, ks = (e >> 5) & 7, ln = e & 31;
-      const int row = 16 * m + (ln >> 2), k = kPH + 8 * ks + (ln & 3);
-      uint32_t h[4], l[4];
-      tf32_split(S[row * kPLD + k], h[0], l[0]);
-      tf32_split(S[row * kPLD + k + 4], h[2], l[2]);
-      if (RB >= 16) {
-        tf32_split(S[(row + 8) * kPLD + k], h[1], l[1]);
-        tf32_split(S[(row + 8) * kPLD + k + 4], h[3], l[3]);
+  if (w == kQP / 32) {
+    // the MMA warp
+    if (lane == 0) {
+      unsigned fpar[2] = {0u, 0u};
+      for (int ch = 0; ch < nchunk; ++ch) {
+        const int b = ch & 1, set = (ch >> 1) & 1;
+        if (!tc::mbar_wait(full + b, fpar[b], kQWaitNs)) break;  // the producers gave up
+        fpar[b] ^= 1u;
+        tc::fence_after_sync();
+        const unsigned char *Ah = opbuf + (size_t)b * C::BUF * 4, *Al = Ah + C::OPA * 4;
+        const unsigned char *Bh = Al + C::OPA * 4, *Bl = Bh + C::OPB * 4;
+#pragma unroll
+        for (int s = 0; s < kQKC / 8; ++s)
+#pragma unroll
+          for (int hf = 0; hf < C::H; ++hf) {
+            const uint32_t d = tmem + (uint32_t)(set * C::H * C::N + hf * C::N);
+            const uint32_t ao = (uint32_t)(s * C::M * 32 + hf * 4096), bo = (uint32_t)(s * C::N * 32);
+            tc::mma(d, tc::smem_desc(tc::saddr(Ah + ao)), tc::smem_desc(tc::saddr(Bl + bo)), idesc,
+                    !((ch & 1) == 0 && s == 0));
+            tc::mma(d, tc::smem_desc(tc::saddr(Al + ao)), tc::smem_desc(tc::saddr(Bh + bo)), idesc, true);
+            tc::mma(d, tc::smem_desc(tc::saddr(Ah + ao)), tc::smem_desc(tc::saddr(Bh + bo)), idesc, true);
+          }
+        tc::commit(empty + b);
+      }
+    }
+    __syncwarp();
+  } else {
+    // the producers
+    auto issue = [&](int ch) {
+      float *S = raw + (ch % kQS) * C::RAW;
+      const int base = c0 + ch * kQKC;
+      if (vec) {
+        constexpr int QX = kQLD / 4;
+        for (int e = t; e < RB * QX; e += kQP) {
+          const int i = e / QX, h = 4 * (e - i * QX), c = base - 4 + h;
+          const bool ok = i < r && c >= 0 && c < c1;
+          cp_async16(S + i * kQLD + h, ok ? X + (size_t)N * i + c : X, ok ? 16 : 0);
+        }
+        constexpr int QK = kQKC / 4;
+        for (int e = t; e < RB * QK; e += kQP) {
+          const int i = e / QK, k = 4 * (e - i * QK), c = base + k;
+          const bool okc = i < r && c < c1, okb = okc && c >= nx;
+          cp_async16(S + (RB + i) * kQLD + 4 + k, okb ? X + (size_t)N * i + (c - nx) : X, okb ? 16 : 0);
+          cp_async16(S + (2 * RB + i) * kQLD + 4 + k, okc ? X0 + (size_t)N * i + c : X0, okc ? 16 : 0);
+        }
+        if (t < 3 * QK) {
+          const int row = t / QK, k = 4 * (t - row * QK), c = base + k;
+          const float *src = row == 0 ? sig_t : row == 1 ? ss4 : qv;
+          cp_async16(S + 3 * RB * kQLD + row * kQKC + k, c < c1 ? src + c : src, c < c1 ? 16 : 0);
+        }
       } else {
-        h[1] = h[3] = l[1] = l[3] = 0u;
+        for (int e = t; e < RB * (kQKC + 1); e += kQP) {
+          const int i = e / (kQKC + 1), h = e - i * (kQKC + 1) + 3, c = base - 4 + h;
+          const bool ok = i < r && c >= 0 && c < c1;
+          cp_async4(S + i * kQLD + h, ok ? X + (size_t)N * i + c : X, ok ? 4 : 0);
+        }
+        for (int e = t; e < RB * kQKC; e += kQP) {
+          const int i = e / kQKC, k = e - i * kQKC, c = base + k;
+          const bool okc = i < r && c < c1, okb = okc && c >= nx;
+          cp_async4(S + (RB + i) * kQLD + 4 + k, okb ? X + (size_t)N * i + (c - nx) : X, okb ? 4 : 0);
+          cp_async4(S + (2 * RB + i) * kQLD + 4 + k, okc ? X0 + (size_t)N * i + c : X0, okc ? 4 : 0);
+        }
+        if (t < 3 * kQKC) {
+          const int row = t / kQKC, k = t - row * kQKC, c = base + k;
+          const float *src = row == 0 ? sig_t : row == 1 ? ss4 : qv;
+          cp_async4(S + 3 * RB * kQLD + row * kQKC + k, c < c1 ? src + c : src, c < c1 ? 4 : 0);
+        }
       }
-      AFh[e] = make_uint4(h[0], h[1], h[2], h[3]);
-      AFl[e] = make_uint4(l[0], l[1], l[2], l[3]);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int ks = 0; ks < 8; ++ks) {
-      const uint4 ah = AFh[(mt * 8 + ks) * 32 + lane], al = AFl[(mt * 8 + ks) * 32 + lane];
-      const int ka = kPH + 8 * ks + tg, va = 8 * ks + tg;
-      // the tiles' operands first, then the three products tile by tile
-      // in rounds, so that no product waits on the one just issued
-      uint32_t bh[OWN][2], bl[OWN][2];
-#pragma unroll
-      for (int o = 0; o < OWN; ++o) {
-        const float b0 = S[boff[o] + ka] * S[soff[o] + va];
-        const float b1 = S[boff[o] + ka + 4] * S[soff[o] + va + 4];
-        tf32_split(b0, bh[o][0], bl[o][0]);
-        tf32_split(b1, bh[o][1], bl[o][1]);
+      if (t >= kQP - kQKC) {  // masks: rows 3 .. 8 of the per-cell block
+        float *V = S + 3 * RB * kQLD;
+        const int k = t - (kQP - kQKC), c = base + k;
+        const bool ok = c < c1;
+        const int iy = ok ? c / nx : 0, ix = ok ? c - iy * nx : 0;
+        V[3 * kQKC + k] = (ok && ix >= 1) ? 1.f : 0.f;
+        V[4 * kQKC + k] = (ok && ix == 0) ? 1.f : 0.f;
+        V[5 * kQKC + k] = (ok && ix == nx - 1) ? 1.f : 0.f;
+        V[6 * kQKC + k] = (ok && iy == 0) ? 1.f : 0.f;
+        V[7 * kQKC + k] = (ok && iy == ny - 1) ? 1.f : 0.f;
+        V[8 * kQKC + k] = 1.f;
       }
+    };
+    // operand roles (fixed for the kernel): A: thread t < MRP JA owns row
+    // m = t % MRP and the groups t / MRP + JA p; B: the next RB JB threads
+    // own X column n and the groups (t - MRP JA) / RB + JB p
+    constexpr int MRP = C::MRP;
+    const bool arole = t < MRP * C::JA && (t % MRP) < 6 * RB + 5;
+    const bool brole = t >= MRP * C::JA && t < MRP * C::JA + RB * C::JB;
+    int ajg = 0, arow_s = 0, arow_c = 0, bjg = 0, brow_c = 0;
+    uint32_t arow_o = 0, brow_o = 0;
+    bool avec = false, ashift = false;
+    if (t < MRP * C::JA) {
+      const int m = t % MRP;
+      ajg = t / MRP;
+      arow_o = (uint32_t)((m >> 3) * 256 + (m & 7) * 16);
+      if (m < 6 * RB) {
+        const int mat = m / RB, col = m - mat * RB;
+        const int srow = mat == 1 ? 3 : mat == 3 ? 0 : mat == 4 ? 1 : 8;  // mL, sig_t, sigma_s/4pi, 1
+        arow_s = 3 * RB * kQLD + srow * kQKC;
+        arow_c = (mat == 2 ? RB + col : mat == 5 ? 2 * RB + col : col) * kQLD + 4;
+        ashift = mat == 1;
+      } else {
+        const int v = m - 6 * RB;  // q, eL, eR, eB, eT
+        arow_s = 3 * RB * kQLD + (v == 0 ? 2 : v + 3) * kQKC;
+        avec = true;
+      }
+    } else if (brole) {
+      const int tb = t - MRP * C::JA, n = tb % RB;
+      bjg = tb / RB;
+      brow_c = n * kQLD + 4;
+      brow_o = (uint32_t)((n >> 3) * 256 + (n & 7) * 16);
+    }
+    int nflush = 0;
+    auto flush_set = [&](int set) {  // the set's products have completed
+      tc::fence_after_sync();
+      if (reader) {
+        const uint32_t ta =
+            tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(set * C::H * C::N + (w >> 2) * C::N);
+        if (C::N == 32) {
+          float v[32];
+          tc::ld32(ta, v);
 #pragma unroll
-      for (int o = 0; o < OWN; ++o)
-        if (dmat[o] >= 0) mma_tf32(d1[o], ah, bl[o][0], bl[o][1]);  // warp-uniform
+          for (int e = 0; e < C::N; ++e) acc2[e] += v[e % 32];
+        } else {
+          float v[16];
+          tc::ld16(ta, v);
 #pragma unroll
-      for (int o = 0; o < OWN; ++o)
-        if (dmat[o] >= 0) mma_tf32(d1[o], al, bh[o][0], bh[o][1]);
+          for (int e = 0; e < C::N; ++e) acc2[e] += v[e % 16];
+        }
+        if (++nflush % 8 == 0) {
 #pragma unroll
-      for (int o = 0; o < OWN; ++o)
-        if (dmat[o] >= 0) mma_tf32(d1[o], ah, bh[o][0], bh[o][1]);
-      if (vown && ks == (w & 7)) {  // the vector tile: columns q, eL, eR, eB, eT, 0, 0, 0
-        const int vrow = g == 0 ? 2 : g + 3;
-        const float *V = S + 3 * RB * kPLD;
-        const float b0 = g < 5 ? V[vrow * kPKC + va] : 0.f;
-        const float b1 = g < 5 ? V[vrow * kPKC + va + 4] : 0.f;
-        mma_3xtf32(v1, ah, al, b0, b1);
+          for (int e = 0; e < C::N; ++e) { acc3[e * NR + t] += acc2[e]; acc2[e] = 0.f; }
+        }
+      }
+      tc::fence_before_sync();
+    };
+    unsigned epar[2] = {0u, 0u};
+    bool pend[2] = {false, false}, dirty[2] = {false, false};
+    auto wait_empty = [&](int b) {
+      if (!pend[b]) return;
+      if (!tc::mbar_wait(empty + b, epar[b], kQWaitNs)) bad = 1;
+      epar[b] ^= 1u;
+      pend[b] = false;
+    };
+    if (nchunk > 0) issue(0);
+    cp_async_commit();
+    if (nchunk > 1) issue(1);
+    cp_async_commit();
+    for (int ch = 0; ch < nchunk; ++ch) {
+      cp_async_wait<1>();  // chunk ch has landed (this thread's copies)
+      const int b = ch & 1, set = (ch >> 1) & 1;
+      wait_empty(b);       // the products of chunk ch - 2 have read buffer b
+      producers_sync();    // every copy of chunk ch; chunk ch - 1 fully formed
+      if (*reinterpret_cast<volatile int *>(&bad)) break;
+      if (ch + 2 < nchunk) issue(ch + 2);  // into the stage chunk ch - 1 came from
+      cp_async_commit();
+      if ((ch & 1) && ch >= 3 && dirty[set ^ 1]) {  // (restarted by chunk ch + 1)
+        flush_set(set ^ 1);
+        dirty[set ^ 1] = false;
+      }
+      const float *S = raw + (ch % kQS) * C::RAW;
+      unsigned char *Ah = opbuf + (size_t)b * C::BUF * 4, *Al = Ah + C::OPA * 4;
+      unsigned char *Bh = Al + C::OPA * 4, *Bl = Bh + C::OPB * 4;
+      if (arole) {
+#pragma unroll
+        for (int p = 0; p < 8 / C::JA; ++p) {
+          const int jg = ajg + C::JA * p, jj = 4 * jg;
+          float4 x;
+          if (avec) {
+            x = *reinterpret_cast<const float4 *>(S + arow_s + jj);
+          } else {
+            const float4 sc = *reinterpret_cast<const float4 *>(S + arow_s + jj);
+            const float4 a = *reinterpret_cast<const float4 *>(S + arow_c + jj);
+            x = ashift ? make_float4(S[arow_c + jj - 1], a.x, a.y, a.z) : a;  // X_L: one cell back
+            x.x *= sc.x;
+            x.y *= sc.y;
+            x.z *= sc.z;
+            x.w *= sc.w;
+          }
+          float4 h, l;
+          tc::split(x.x, h.x, l.x);
+          tc::split(x.y, h.y, l.y);
+          tc::split(x.z, h.z, l.z);
+          tc::split(x.w, h.w, l.w);
+          const uint32_t off = (uint32_t)((jg >> 1) * C::M * 32 + (jg & 1) * 128) + arow_o;
+          *reinterpret_cast<float4 *>(Ah + off) = h;
+          *reinterpret_cast<float4 *>(Al + off) = l;
+        }
+      } else if (brole) {
+#pragma unroll
+        for (int p = 0; p < 8 / C::JB; ++p) {
+          const int jg = bjg + C::JB * p, jj = 4 * jg;
+          const float4 x = *reinterpret_cast<const float4 *>(S + brow_c + jj);
+          float4 h, l;
+          tc::split(x.x, h.x, l.x);
+          tc::split(x.y, h.y, l.y);
+          tc::split(x.z, h.z, l.z);
+          tc::split(x.w, h.w, l.w);
+          const uint32_t off = (uint32_t)((jg >> 1) * C::N * 32 + (jg & 1) * 128) + brow_o;
+          *reinterpret_cast<float4 *>(Bh + off) = h;
+          *reinterpret_cast<float4 *>(Bl + off) = l;
+        }
+      }
+      tc::fence_smem_to_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(full + b);
+      pend[b] = true;
+      dirty[set] = true;
+    }
+    // the last products: the older buffer's commit first, then the older
+    // pair's set before the newer one
+    if (nchunk > 0 && !*reinterpret_cast<volatile int *>(&bad)) {
+      const int last = nchunk - 1;
+      if (last >= 1) wait_empty((last - 1) & 1);
+      wait_empty(last & 1);
+      producers_sync();
+      if (!*reinterpret_cast<volatile int *>(&bad)) {
+        const int lset = (last >> 1) & 1;
+        if (dirty[lset ^ 1]) flush_set(lset ^ 1);
+        if (dirty[lset]) flush_set(lset);
       }
     }
-#pragma unroll
-    for (int o = 0; o < OWN; ++o)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) { d2[o][e] += d1[o][e]; d1[o][e] = 0.f; }
-#pragma unroll
-    for (int e = 0; e < 4; ++e) { v2[e] += v1[e]; v1[e] = 0.f; }
-    if ((ch + 1) % 8 == 0) {
-#pragma unroll
-      for (int o = 0; o < OWN; ++o)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) { d3[o][e] += d2[o][e]; d2[o][e] = 0.f; }
-#pragma unroll
-      for (int e = 0; e < 4; ++e) { v3[e] += v2[e]; v2[e] = 0.f; }
-    }
-    __syncthreads();  // stage ch & 1 and the fragments are free again
+    cp_async_wait<0>();
   }
-  cp_async_wait<0>();
+  tc::fence_before_sync();
   __syncthreads();
-  // the CTA partial: each matrix entry from its owner, the vector sums of
-  // the k-steps of a row tile in k-step order
-  double *part_s = reinterpret_cast<double *>(dyn);
-  double *vbuf = part_s + proj_count(r);  // NW x 8 x RB
+  if (bad && t == 0) set_status(I.status, kETimeout);
+  if (w == 0) tc::dealloc(tmem, C::NCOL);
+  // the CTA partial: D row m (operand column) and column n (X column):
+  // G_nj for m = mat RB + j, the vector sums for m >= 6 RB
+  double *part_s = reinterpret_cast<double *>(dyn5);
   const int rr2 = r * r;
-#pragma unroll
-  for (int o = 0; o < OWN; ++o) {
-    if (dmat[o] >= 0) {
-      const int mat = dmat[o];
+  if (reader) {
+    const int m = 128 * (w >> 2) + 32 * (w & 3) + lane;
+    if (m < 6 * RB) {
+      const int mat = m / RB, j = m - mat * RB;
       const double sc = mat == 4 ? 4.0 * kPi : 1.0;
+      if (j < r)
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int i = 16 * mt + g + (e >= 2 ? 8 : 0), j = dcol[o] + (e & 1);
-        if (i < r && j < r)
-          part_s[mat * rr2 + i + r * j] = sc * ((double)d1[o][e] + ((double)d2[o][e] + (double)d3[o][e]));
-      }
-    }
-  }
-  if (vown) {
+        for (int n = 0; n < C::N; ++n)
+          if (n < r) part_s[mat * rr2 + n + r * j] = sc * ((double)acc2[n] + (double)acc3[n * NR + t]);
+    } else if (m < 6 * RB + 5) {
+      const int v = m - 6 * RB;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int i = 16 * (w >> 3) + g + (e >= 2 ? 8 : 0), v = 2 * tg + (e & 1);
-      if (i < RB) vbuf[(w * 8 + v) * RB + i] = (double)v1[e] + ((double)v2[e] + (double)v3[e]);
+      for (int n = 0; n < C::N; ++n)
+        if (n < r) part_s[6 * rr2 + v * r + n] = (double)acc2[n] + (double)acc3[n * NR + t];
     }
-  }
-  __syncthreads();
-  for (int e = t; e < 5 * r; e += kPT) {
-    const int v = e / r, i = e - v * r, m = i >> 4;
-    double x = 0.0;
-    for (int ks = 0; ks < 8; ++ks) x += vbuf[((8 * m + ks) * 8 + v) * RB + i];
-    part_s[6 * rr2 + e] = x;
   }
   cluster.sync();
   const int rank = (int)cluster.block_rank();
   const int cnt = proj_count(r), share = (cnt + kCl - 1) / kCl;
-  double *out = partials + (size_t)(blockIdx.x / kCl) * cnt;
-  for (int e = rank * share + t; e < min(cnt, (rank + 1) * share); e += kPT) {
+  double *out = I.partials + (size_t)(blockIdx.x / kCl) * cnt;
+  for (int e = rank * share + t; e < min(cnt, (rank + 1) * share); e += kQT) {
     double v = 0.0;
 #pragma unroll
     for (int q = 0; q < kCl; ++q) v += cluster.map_shared_rank(part_s, q)[e];
@@ -1254,14 +1313,14 @@ cudaError_t launch_apply(const ApplyJob *d_jobs, int n, int maxm, int rmask, cud
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-// FP64: k_project; mixed precision: k_project_tc, one launch per rank
+// FP64: k_project; mixed precision: k_project_tc5, one launch per rank
 // class in rmask
 template <typename real>
 cudaError_t launch_project(const Inst *d, int n, int maxblocks, int rmax, int rmask, cudaStream_t st) {
   if (sizeof(real) == 8)
     return launch_pdl(k_project<double>, dim3(maxblocks, n), dim3(kTB), proj_smem_bytes(rmax, 8), st, d);
   const dim3 g(maxblocks, n);
-#define L_(RB) (e = launch_pdl(k_project_tc<RB>, g, dim3(kPT), projtc_smem_bytes<RB>(), st, d))
+#define L_(RB) (e = launch_pdl(k_project_tc5<RB>, g, dim3(kQT), Q5<RB>::SMEM, st, d))
   cudaError_t e = cudaSuccess;
   DLR_RB_DISPATCH(rmask, L_);
 #undef L_
@@ -1297,7 +1356,7 @@ int reduce_cluster_cap() {
   c = std::min(c, cap((const void *)k_tsgram<double, 0>, 0));
   c = std::min(c, cap((const void *)k_tsgram<double, 1>, 0));
   if (prepare_dense(kMaxRank) == cudaSuccess) {
-    c = std::min(c, cap((const void *)k_project_tc<32>, projtc_smem_bytes<32>(), kPT));
+    c = std::min(c, cap((const void *)k_project_tc5<32>, Q5<32>::SMEM, kQT));
     c = std::min(c, cap((const void *)k_project<double>, proj_smem_bytes(kMaxRank, 8)));
   }
   return c;
@@ -1305,12 +1364,13 @@ int reduce_cluster_cap() {
 
 // Kernel attributes, set before any launch is captured into a graph.
 cudaError_t prepare_dense(int rmax) {
-  cudaError_t e =
-      cudaFuncSetAttribute(k_project_tc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, projtc_smem_bytes<8>());
+  cudaError_t e = cudaFuncSetAttribute(k_project_tc5<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       Q5<8>::SMEM);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_project_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, projtc_smem_bytes<16>());
+    e = cudaFuncSetAttribute(k_project_tc5<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, Q5<16>::SMEM);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_project_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, projtc_smem_bytes<32>());
+    e = cudaFuncSetAttribute(k_project_tc5<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, Q5<32>::SMEM);
+
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_project<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               proj_smem_bytes(rmax, 8));

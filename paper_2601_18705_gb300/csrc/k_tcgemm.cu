@@ -1,12 +1,9 @@
-// k_tcgemm.cu -- dlr_debug_tc_gemm: the tcgen05 form of the TF32
-// contraction of the mixed-precision projections of steps 6 and 7 (split
-// TF32 products, operands in shared memory, the FP32 accumulator in tensor
-// memory; tc_core.cuh) on plain device arrays, so that a test can check the
-// operand layout, the descriptors and the split products against a
-// reference.  The projections themselves run the mma.sync kernel
-// k_project_tc: a tcgen05 version of that kernel, built on these helpers
-// with one issuing thread and CTA barriers around the operand staging, was
-// slower (560 against 394 us per 1024^2-cell, rank-32 launch).
+// k_tcgemm.cu -- dlr_debug_tc_gemm: the tcgen05 TF32 contraction that the
+// mixed-precision projections of steps 6 and 7 (k_project_tc5) are built
+// on (split TF32 products, operands in shared memory, the FP32 accumulator
+// in tensor memory; tc_core.cuh), on plain device arrays, so that a test
+// can check the operand layout, the descriptors and the split products
+// against a reference.
 #include <cuda_runtime.h>
 
 #include "../../include/dlr.h"

@@ -1,7 +1,7 @@
 // tc_core.cuh -- the fifth-generation tensor cores (tcgen05) for TF32
 // contractions: D (FP32, in tensor memory) += A B^T with A (M x K) and
-// B (N x K) in shared memory, both K-major without swizzle (used by
-// dlr_debug_tc_gemm, k_tcgemm.cu).
+// B (N x K) in shared memory, both K-major without swizzle (the projections
+// k_project_tc5 in k_dense.cu, and dlr_debug_tc_gemm in k_tcgemm.cu).
 //
 // Operand layout.  An operand tile of R rows and 8 TF32 columns (one
 // k-step of an MMA) is made of core matrices of 8 rows x 16 bytes (4 TF32
