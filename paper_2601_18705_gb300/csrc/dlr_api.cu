@@ -455,6 +455,11 @@ static Sizes sizes_of(const dlr_problem *p, int sms) {
   const int cap = std::min(reduce_cta_cap(), 2 * sms / kCl * kCl);
   auto clusters = [&](int x) { return std::min(cap, (x + kCl - 1) / kCl * kCl); };
   s.pb = clusters(std::max(1, (s.N + 511) / 512));
+  // mixed-precision DG0 steps use pb only for the projections of steps 6
+  // and 7 (k_project_tc5): one CTA per SM at most, no clusters, one partial
+  // per CTA, about 2048 cells per CTA
+  const bool proj_tc = p->precision == DLR_MIXED && p->element == 0;
+  if (proj_tc) s.pb = std::min(sms, std::max(1, (s.N + 2047) / 2048));
   s.pbl = clusters(std::max(1, (s.K + 15) / 16));
   s.lb = std::min(2 * sms / kCl * kCl, (std::max(1, (s.K + 3) / 4) + kCl - 1) / kCl * kCl);  // 4 warps, one angle each
   const size_t r1 = s.r;
@@ -466,7 +471,8 @@ static Sizes sizes_of(const dlr_problem *p, int sms) {
     if (!gcap) gcap = std::max(kCl, gram32_cta_cap());
     s.pbg = std::min(gcap, std::max(kCl, (s.N / 2048) / kCl * kCl));
   }
-  s.partial_doubles = std::max({(size_t)(s.pb / kCl) * proj_count((int)r), (size_t)(s.pb / kCl) * r * r,
+  s.partial_doubles = std::max({(size_t)(proj_tc ? s.pb : s.pb / kCl) * proj_count((int)r),
+                                (size_t)(s.pb / kCl) * r * r,
                                 (size_t)(s.pbl / kCl) * r * r, (size_t)(s.lb / kCl) * (r * r + r),
                                 (size_t)(s.pbg / kCl) * r * r,
                                 p->element == 1 ? (size_t)7 * (s.pb / kCl) * r * r : (size_t)0,
@@ -1417,7 +1423,8 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
     cl2[i] = chol(pcl, 1.0, sm + L.R2, 2);
     cl3[i] = chol(pcl, 1.0, sm + L.R3, 3);
     ReduceJob red{};
-    red.part = I.partials; red.nblocks = pc; red.stride = proj_count(r);
+    // (mixed DG0: one partial per CTA of k_project_tc5; else one per cluster)
+    red.part = I.partials; red.nblocks = h->mixed && !I.q1 ? h->pb : pc; red.stride = proj_count(r);
     red.count = proj_count(r); red.out = sm + L.G; red.scale = 1.0;
     rp[i] = red;
     if (I.q1) {

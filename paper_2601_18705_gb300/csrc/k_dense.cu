@@ -678,9 +678,9 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // of chunks (64 cells) accumulate alternately in two sets of accumulators;
 // a pair's set is read into FP32 registers (the owner of D row m, lane
 // m % 128 of half m / 128) once its products have completed; FP32 sums per
-// 8 pairs and per slice, FP64 once; the cluster sum in rank order as in
-// k_project.  Every mbarrier wait is bounded; a wait that runs out marks
-// the instance DLR_ETIMEOUT.
+// 8 pairs and per slice, FP64 once, one partial per CTA (at most one CTA
+// per SM and no cluster, so every SM takes a slice).  Every mbarrier wait
+// is bounded; a wait that runs out marks the instance DLR_ETIMEOUT.
 // ------------------------------------------------------------------
 constexpr int kQP = 512;          // producer threads (16 warps)
 constexpr int kQT = kQP + 32;     // and the MMA warp
@@ -708,9 +708,7 @@ template <int RB> struct Q5 {
   static constexpr int OFF_BAR = OFF_BUF + 2 * BUF * 4;  // full[2], empty[2]
   // the readers' per-slice FP32 sums: N values of 128 H threads, column-major
   static constexpr int OFF_ACC = OFF_BAR + 32;
-  static constexpr int WORK = OFF_ACC + N * 128 * H * 4;
-  static constexpr int RED = (6 * RB * RB + 5 * RB) * 8;
-  static constexpr int SMEM = WORK > RED ? WORK : RED;
+  static constexpr int SMEM = OFF_ACC + N * 128 * H * 4;
 };
 
 __device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, %0;" ::"r"(kQP) : "memory"); }
@@ -719,16 +717,14 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *m) {
 }
 
 template <int RB>
-__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kQT, 1)
-k_project_tc5(const Inst *__restrict__ insts) {
+__global__ void __launch_bounds__(kQT, 1) k_project_tc5(const Inst *__restrict__ insts) {
   pdl_wait();
   pdl_trigger();
   using C = Q5<RB>;
   const Inst &I = insts[blockIdx.y];
   if (rank_class(I.r) != RB) return;
   const int nblk = I.partial_blocks;
-  if ((int)blockIdx.x >= nblk) return;  // whole clusters
-  cg::cluster_group cluster = cg::this_cluster();
+  if ((int)blockIdx.x >= nblk) return;
   extern __shared__ __align__(1024) unsigned char dyn5[];
   float *raw = reinterpret_cast<float *>(dyn5);
   unsigned char *opbuf = dyn5 + C::OFF_BUF;
@@ -1004,9 +1000,10 @@ k_project_tc5(const Inst *__restrict__ insts) {
   __syncthreads();
   if (bad && t == 0) set_status(I.status, kETimeout);
   if (w == 0) tc::dealloc(tmem, C::NCOL);
-  // the CTA partial: D row m (operand column) and column n (X column):
-  // G_nj for m = mat RB + j, the vector sums for m >= 6 RB
-  double *part_s = reinterpret_cast<double *>(dyn5);
+  // this CTA's partial (one per CTA, summed over the CTAs by k_reduce): D
+  // row m (operand column) and column n (X column) give G_nj for
+  // m = mat RB + j and the vector sums for m >= 6 RB, each from its owner
+  double *out = I.partials + (size_t)blockIdx.x * proj_count(r);
   const int rr2 = r * r;
   if (reader) {
     const int m = 128 * (w >> 2) + 32 * (w & 3) + lane;
@@ -1016,25 +1013,14 @@ k_project_tc5(const Inst *__restrict__ insts) {
       if (j < r)
 #pragma unroll
         for (int n = 0; n < C::N; ++n)
-          if (n < r) part_s[mat * rr2 + n + r * j] = sc * ((double)acc2[n] + (double)acc3[n * NR + t]);
+          if (n < r) out[mat * rr2 + n + r * j] = sc * ((double)acc2[n] + (double)acc3[n * NR + t]);
     } else if (m < 6 * RB + 5) {
       const int v = m - 6 * RB;
 #pragma unroll
       for (int n = 0; n < C::N; ++n)
-        if (n < r) part_s[6 * rr2 + v * r + n] = (double)acc2[n] + (double)acc3[n * NR + t];
+        if (n < r) out[6 * rr2 + v * r + n] = (double)acc2[n] + (double)acc3[n * NR + t];
     }
   }
-  cluster.sync();
-  const int rank = (int)cluster.block_rank();
-  const int cnt = proj_count(r), share = (cnt + kCl - 1) / kCl;
-  double *out = I.partials + (size_t)(blockIdx.x / kCl) * cnt;
-  for (int e = rank * share + t; e < min(cnt, (rank + 1) * share); e += kQT) {
-    double v = 0.0;
-#pragma unroll
-    for (int q = 0; q < kCl; ++q) v += cluster.map_shared_rank(part_s, q)[e];
-    out[e] = v;
-  }
-  cluster.sync();
 }
 
 // Sum of per-block partials: out[e] = scale * sum_b part[b*stride + e].
@@ -1355,10 +1341,8 @@ int reduce_cluster_cap() {
   int c = cap((const void *)k_tsgram<float, 0>, 0);
   c = std::min(c, cap((const void *)k_tsgram<double, 0>, 0));
   c = std::min(c, cap((const void *)k_tsgram<double, 1>, 0));
-  if (prepare_dense(kMaxRank) == cudaSuccess) {
-    c = std::min(c, cap((const void *)k_project_tc5<32>, Q5<32>::SMEM, kQT));
+  if (prepare_dense(kMaxRank) == cudaSuccess)
     c = std::min(c, cap((const void *)k_project<double>, proj_smem_bytes(kMaxRank, 8)));
-  }
   return c;
 }
 
