@@ -318,10 +318,15 @@ int dlr_get_quadrature(dlr_handle *h, double *omega_xyz, double *w);
  * before the first step.  Synchronises. */
 int dlr_get_selected(dlr_handle *h, int32_t *idx);
 
-/* Full-rank SN handles only (DLR_METHOD_SN; DLR_EINVAL otherwise): copy the
- * angular flux psi (nx*ny x NOm, column-major: psi[c + nx*ny*k] for cell c and
- * angle k of dlr_get_quadrature, FP64; widened from FP32 in mixed precision)
- * out of / into the handle.  dlr_get_psi synchronises; dlr_set_psi is
+/* The angular flux psi (rows x NOm, column-major: psi[c + rows*k] for row c
+ * and angle k of dlr_get_quadrature, FP64; rows = nx*ny, or 4*nx*ny plain
+ * Legendre coefficients with element = 1).  dlr_get_psi copies the state of
+ * a full-rank SN handle (widened from FP32 in mixed precision), or forms
+ * psi = X S W^T of a DLR handle on the device (Section 4: the low-rank
+ * form; like dlr_get_factors it first rotates the factors to the SVD basis
+ * of S; a host destination goes through a temporary device array of the
+ * same size); it synchronises.  dlr_set_psi replaces the state of a
+ * full-rank SN handle (DLR_EINVAL for a DLR handle: dlr_set_factors); it is
  * enqueued (a pageable host buffer is consumed before return). */
 int dlr_get_psi(dlr_handle *h, double *out, int32_t out_on_device);
 int dlr_set_psi(dlr_handle *h, const double *in, int32_t in_on_device);

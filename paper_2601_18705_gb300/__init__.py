@@ -227,13 +227,10 @@ class Solver:
     def psi(self) -> np.ndarray:
         """psi (rows x NOm; rows = Nx, or 4 Nx Legendre coefficients on
         bilinear elements): the full-rank state of an SN instance, or X S W^T
-        from the current factors of a DLR instance."""
-        if self.sn:
-            out = np.empty((self.rows, self.K), order="F")
-            check(load().dlr_get_psi(self.h, out.ctypes.data, 0))
-            return out
-        X, S, W = self.factors()
-        return X @ S @ W.T
+        of a DLR instance (formed on the device)."""
+        out = np.empty((self.rows, self.K), order="F")
+        check(load().dlr_get_psi(self.h, out.ctypes.data, 0))
+        return out
 
     def set_psi(self, psi) -> None:
         """Replaces the angular flux of an SN instance (rows x NOm)."""

@@ -95,6 +95,29 @@ __global__ void k_narrow(const double *a, float *b, size_t n) {
     b[i] = (float)a[i];
 }
 
+// psi = X S W^T of a DLR state (Section 4: the low-rank form of the angular
+// flux), FP64, column-major rows x K: CTA (bx, k) forms l = S W_k^T (r
+// values) and then rows 128 bx .. of column k; X in the working precision
+// (Q1 coefficients stored scaled are returned plain)
+template <typename real>
+__global__ void __launch_bounds__(128) k_form_psi(const real *__restrict__ X, size_t rows, int r,
+                                                  const double *__restrict__ S, const double *__restrict__ W,
+                                                  int K, int q1, double *__restrict__ out) {
+  __shared__ double l[32];
+  const int k = blockIdx.y;
+  if (threadIdx.x < r) {
+    double v = 0.0;
+    for (int j = 0; j < r; ++j) v += S[threadIdx.x + r * j] * W[k + (size_t)K * j];
+    l[threadIdx.x] = v;
+  }
+  __syncthreads();
+  const size_t row = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (row >= rows) return;
+  double v = 0.0;
+  for (int i = 0; i < r; ++i) v += (double)X[row + rows * i] * l[i];
+  out[row + rows * k] = q1 ? v * q1_unscale((int)(row & 3)) : v;
+}
+
 
 // ------------------------------------------------------------------
 // errors
@@ -2167,12 +2190,35 @@ int dlr_get_selected(dlr_handle *h, int32_t *idx) {
 
 int dlr_get_psi(dlr_handle *h, double *out, int32_t out_on_device) {
   if (!h || !out) return fail(DLR_EINVAL, "NULL argument");
-  if (!h->sn) return fail(DLR_EINVAL, "dlr_get_psi needs a full-rank SN handle (dlr_get_factors)");
   const size_t rows = h->inst.q1 ? (size_t)4 * h->N : (size_t)h->N;
-  {
+  if (h->sn) {
     const int rc = copy_out(h, h->inst.Psi, out, rows, h->K, out_on_device != 0);
     if (rc) return rc;
+    return sync_status(h);
   }
+  // a DLR state: X S W^T formed on the device, into out or a scratch array,
+  // from the factors in the SVD basis of S (as dlr_get_factors leaves them)
+  {
+    const int rc = canonicalize(h);
+    if (rc) return rc;
+  }
+  const size_t bytes = rows * (size_t)h->K * 8;
+  double *dst = out;
+  if (!out_on_device) CK(cudaMallocAsync(reinterpret_cast<void **>(&dst), bytes, h->st));
+  const dim3 g((unsigned)((rows + 127) / 128), (unsigned)h->K);
+  if (h->mixed)
+    k_form_psi<float><<<g, 128, 0, h->st>>>((const float *)h->inst.X0, rows, h->r, h->inst.S0, h->inst.W0, h->K,
+                                             h->inst.q1, dst);
+  else
+    k_form_psi<double><<<g, 128, 0, h->st>>>((const double *)h->inst.X0, rows, h->r, h->inst.S0, h->inst.W0,
+                                              h->K, h->inst.q1, dst);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && !out_on_device) {
+    e = cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, h->st);
+    const cudaError_t f = cudaFreeAsync(dst, h->st);
+    if (e == cudaSuccess) e = f;
+  }
+  if (e != cudaSuccess) return fail(DLR_ECUDA, "dlr_get_psi: %s", cudaGetErrorString(e));
   return sync_status(h);
 }
 
