@@ -236,7 +236,7 @@ struct Batch {
   GramJob *g_psi1, *g_psire, *g_x, *g_x3, *g_l1, *g_lf, *g_w, *g_w3, *g_cross;
   FillJob *f_psi, *f_l;
   ApplyJob *a_psi, *a_x2, *a_x3, *a_l1, *a_w2, *a_w3, *a_wv, *a_cw, *a_cx;
-  int svd_mode = 0;  // 0: S kept general (pivoted-QR selection), 1: SVD every step (DEIM)
+  int svd_mode = 0;  // 0: S kept general (pivoted-QR selection), 1: SVD every step (DEIM, r = NOm)
   CholJob *c_p1, *c_p1b, *c_p2, *c_p3, *c_l1, *c_l1b, *c_l2, *c_l3;
   ReduceJob *r_proj;
   cudaGraphExec_t pre = nullptr, post = nullptr;
@@ -1193,7 +1193,14 @@ static int build_batch(dlr_handle *const *hs, int n, Batch **out) {
   b->n = n;
   b->mixed = hs[0]->mixed;
   b->st = hs[0]->st;
+  // the SVD of S every step for DEIM (its angles depend on the basis) and
+  // at full angular rank (r = NOm) on DG0 cells: there the factors kept in
+  // the CholeskyQR basis between steps lost the weighted orthonormality of
+  // W enough for the source iteration to stop converging (a 12 x 10 mesh
+  // with 8 angles, FP64, third step), while the SVD basis keeps it
   b->svd_mode = hs[0]->prob.selection == DLR_SEL_DEIM ? 1 : 0;
+  for (int i = 0; i < n; ++i)
+    if (!hs[i]->sn && !hs[i]->inst.q1 && hs[i]->r == hs[i]->K) b->svd_mode = 1;
   b->sn = hs[0]->sn;
   b->aug = hs[0]->aug;
   b->q1 = hs[0]->inst.q1 != 0;

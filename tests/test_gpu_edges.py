@@ -70,6 +70,26 @@ def test_rank_equal_to_the_number_of_angles(orc, dlr, prec):
         assert eT < TOL[prec] and ep < TOL[prec], (eT, ep)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_full_angular_rank_without_readouts(orc, dlr, prec):
+    # r = NOm stepped three times with no factor read-out in between (no
+    # rotation to the SVD basis from outside): the step itself keeps the
+    # SVD basis at full angular rank, and T follows the oracle
+    from conftest import oracle_problem
+    case = workloads.small_case(12, 10, 8, 2, 4, seed=14, T0=0.55)
+    p = oracle_problem(case)
+    T = case["T0"].reshape(-1).copy()
+    X, S, W = orc.initial_factors(p, T, case["r"])
+    with dlr.Solver(dlr.problem_from_case(case, precision=prec)) as s:
+        s.set_factors(X, S, W)
+        s.step(3)
+        assert s.stats()["status"] == 0
+        Tg = s.T()
+    for _ in range(3):
+        X, S, W, T, *_ = orc.dlr_step(p, X, S, W, T, si_tol=1e-13)
+    assert rel_l2(Tg, T) < TOL[prec]
+
+
 def test_zero_steps_is_a_no_op(dlr):
     case = workloads.small_case(9, 7, 3, 2, 4, seed=15, T0=0.3)
     with dlr.Solver(dlr.problem_from_case(case, precision=1)) as s:
